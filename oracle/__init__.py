@@ -1,0 +1,272 @@
+"""FP64 CPU oracle for the PQMC auxiliary-field update sweep -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  The CUDA
+library never calls it and shares no code with it.
+
+The arithmetic lives in ``afqmc_oracle.c`` (plain C, FP64, plain loops, its
+own LU and Householder QR).  This module only compiles it with gcc and
+marshals numpy arrays through ctypes.  Every function cites the paper's
+passage it follows (see the C source for the formulas).
+
+Parity status of each function (what pins it in ``tests/test_oracle_pins.py``):
+  expK            -- scipy.linalg.expm of an independently built K; closed-form spectrum
+  setup (HS)      -- the decoupling identity checked for all four occupations
+  green_scratch   -- numpy products + solve (unstabilised), projector invariants
+  wrap            -- numpy from-scratch G at the next slice
+  local_slice     -- brute-force det ratio of the walker overlap; from-scratch G
+  delayed_slice   -- identical decisions to local; from-scratch G
+  blockfb_slice   -- brute-force stripped force bias, det ratio, exact detailed
+                     balance on an enumerable toy, from-scratch G
+  energy          -- U=0 closed form; Fock-space brute force on <= 3 sites
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "afqmc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+HS_SZ_REAL = 0
+HS_CHARGE_REAL = 1
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("N", ctypes.c_int), ("M", ctypes.c_int),
+        ("hs", ctypes.c_int),
+        ("t", ctypes.c_double), ("U", ctypes.c_double), ("dtau", ctypes.c_double),
+        ("lam", ctypes.c_double), ("c", ctypes.c_double * 2),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into oracle/_build/liboracle.so."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            os.makedirs(_BUILD, exist_ok=True)
+            tmp = _LIB + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=gnu11", "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        i8p = ctypes.POINTER(ctypes.c_int8)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        pp = ctypes.POINTER(Params)
+        lib.or_setup.argtypes = [pp]
+        lib.or_expK.argtypes = [pp, ctypes.c_double, dp]
+        lib.or_hopping.argtypes = [pp, dp]
+        lib.or_green_scratch.argtypes = [pp, dp, i8p, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, dp, dp, dp, dp]
+        lib.or_green_scratch.restype = ctypes.c_int
+        lib.or_wrap.argtypes = [pp, dp, dp, i8p, ctypes.c_int, ctypes.c_int, dp]
+        lib.or_local_slice.argtypes = [pp, dp, dp, i8p, dp, u8p, u8p, dp, dp]
+        lib.or_delayed_slice.argtypes = [pp, dp, dp, i8p, dp, ctypes.c_int, ctypes.c_int, u8p, u8p, dp,
+                                         dp, ctypes.POINTER(ctypes.c_int)]
+        lib.or_block_force_bias.argtypes = [pp, dp, i8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+        lib.or_blockfb_slice.argtypes = [pp, dp, dp, i8p, dp, dp, ctypes.c_int, u8p, i8p, dp, u8p, dp, dp]
+        lib.or_energy.argtypes = [pp, dp, dp, dp]
+        lib.or_energy.restype = ctypes.c_double
+        _lib = lib
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i8(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
+
+
+def _u8(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Model:
+    """Physical parameters + E = exp(-dtau K), Einv = exp(+dtau K) (Eq. 2DHubbard, Eq. BlMat)."""
+
+    def __init__(self, Lx, Ly, t, U, dtau, M, hs=HS_SZ_REAL):
+        self.p = Params(Lx=Lx, Ly=Ly, N=Lx * Ly, M=M, hs=hs, t=t, U=U, dtau=dtau)
+        if _load().or_setup(ctypes.byref(self.p)) != 0:
+            raise ValueError("unsupported HS mode / sign of U")
+        self.N = Lx * Ly
+        self.M = M
+        self.E = self.expK(dtau)
+        self.Einv = self.expK(-dtau)
+        self.K = np.zeros((self.N, self.N))
+        _load().or_hopping(ctypes.byref(self.p), _d(self.K))
+
+    @property
+    def lam(self):
+        return self.p.lam
+
+    @property
+    def c(self):
+        return (self.p.c[0], self.p.c[1])
+
+    def expK(self, tau):
+        E = np.zeros((self.N, self.N))
+        _load().or_expK(ctypes.byref(self.p), float(tau), _d(E))
+        return E
+
+    def green_scratch(self, x, P, spin, ell, stab=10, want_factors=False):
+        """G(ell) = 1 - R (L R)^{-1} L from scratch (Eqs. GrFMat, GrFMatNew).
+        Returns (G, sign(det L R), log|det L R|[, U_R, U_L])."""
+        N = self.N
+        x = np.ascontiguousarray(x, dtype=np.int8)
+        P = _f64(P)
+        ns = P.shape[1]
+        G = np.zeros((N, N))
+        la = np.zeros(1)
+        UR = np.zeros((N, ns))
+        UL = np.zeros((ns, N))
+        sg = _load().or_green_scratch(ctypes.byref(self.p), _d(self.E), _i8(x), _d(P), ns, spin, ell, stab,
+                                      _d(G), _d(la), _d(UR), _d(UL))
+        if want_factors:
+            return G, sg, la[0], UR, UL
+        return G, sg, la[0]
+
+    def wrap(self, G, xl, spin, direction):
+        """Forward (direction=+1): G <- B_l G B_l^{-1}; backward: G <- B_l^{-1} G B_l (Eq. BlMat)."""
+        G = _f64(G).copy()
+        xl = np.ascontiguousarray(xl, dtype=np.int8)
+        _load().or_wrap(ctypes.byref(self.p), _d(self.E), _d(self.Einv), _i8(xl), spin, direction, _d(G))
+        return G
+
+    def local_slice(self, Gu, Gd, xl, u, replay=None):
+        """Local update of one slice (Eqs. DetRatiolocal, UpdateLTRlocal); returns (Gu, Gd, xl, dec, ratio, sign)."""
+        N = self.N
+        Gu, Gd = _f64(Gu).copy(), _f64(Gd).copy()
+        xl = np.ascontiguousarray(xl, dtype=np.int8).copy()
+        u = _f64(u)
+        rep = None if replay is None else np.ascontiguousarray(replay, dtype=np.uint8)
+        dec = np.zeros(N, np.uint8)
+        ratio = np.zeros(N)
+        sg = np.ones(1)
+        _load().or_local_slice(ctypes.byref(self.p), _d(Gu), _d(Gd), _i8(xl), _d(u), _u8(rep), _u8(dec),
+                               _d(ratio), _d(sg))
+        return Gu, Gd, xl, dec, ratio, sg[0]
+
+    def delayed_slice(self, Gu, Gd, xl, u, k, strategy=2, replay=None):
+        """Delayed update of one slice (Eqs. DelayRatio, DelayRgenk, FinalDelay)."""
+        N = self.N
+        Gu, Gd = _f64(Gu).copy(), _f64(Gd).copy()
+        xl = np.ascontiguousarray(xl, dtype=np.int8).copy()
+        u = _f64(u)
+        rep = None if replay is None else np.ascontiguousarray(replay, dtype=np.uint8)
+        dec = np.zeros(N, np.uint8)
+        ratio = np.zeros(N)
+        sg = np.ones(1)
+        nfl = ctypes.c_int(0)
+        _load().or_delayed_slice(ctypes.byref(self.p), _d(Gu), _d(Gd), _i8(xl), _d(u), int(k), int(strategy),
+                                 _u8(rep), _u8(dec), _d(ratio), _d(sg), ctypes.byref(nfl))
+        return Gu, Gd, xl, dec, ratio, sg[0], nfl.value
+
+    def block_force_bias(self, G, xl, spin, s0, n):
+        """Stripped force bias nbar of block [s0, s0+n) (Eq. BlkFrcBsTnew1, G form)."""
+        nbar = np.zeros(n)
+        xl = np.ascontiguousarray(xl, dtype=np.int8)
+        _load().or_block_force_bias(ctypes.byref(self.p), _d(_f64(G)), _i8(xl), spin, s0, n, _d(nbar))
+        return nbar
+
+    def blockfb_slice(self, Gu, Gd, xl, u_prop, u_acc, nb, replay=None):
+        """Block force-bias update of one slice (Sec. III.B).
+        Returns (Gu, Gd, xl, xprop, lam_plus, dec[nblocks], ratio[nblocks], sign)."""
+        N = self.N
+        nblocks = (N + nb - 1) // nb
+        Gu, Gd = _f64(Gu).copy(), _f64(Gd).copy()
+        xl = np.ascontiguousarray(xl, dtype=np.int8).copy()
+        rep = None if replay is None else np.ascontiguousarray(replay, dtype=np.uint8)
+        xprop = np.zeros(N, np.int8)
+        lamp = np.zeros(N)
+        dec = np.zeros(nblocks, np.uint8)
+        ratio = np.zeros(nblocks)
+        sg = np.ones(1)
+        _load().or_blockfb_slice(ctypes.byref(self.p), _d(Gu), _d(Gd), _i8(xl), _d(_f64(u_prop)),
+                                 _d(_f64(u_acc)), int(nb), _u8(rep), _i8(xprop), _d(lamp), _u8(dec), _d(ratio),
+                                 _d(sg))
+        return Gu, Gd, xl, xprop, lamp, dec, ratio, sg[0]
+
+    def energy(self, Gu, Gd):
+        """Mixed-estimator energy from G by Wick's theorem (Eqs. 2DHubbard, Oxformula)."""
+        return _load().or_energy(ctypes.byref(self.p), _d(self.K), _d(_f64(Gu)), _d(_f64(Gd)))
+
+
+class Walker:
+    """One Markov chain driven by the oracle: fields X (M x N), G per spin, sweep position.
+
+    The sweep follows the paper's order (Sec. II.B, Sec. IV): forward l = 1..M (wrap to l, then
+    update slice l), backward l = M..1 (update slice l, then wrap down to l-1)."""
+
+    def __init__(self, model: Model, P_up, P_dn, x):
+        self.m = model
+        self.P = (_f64(P_up), _f64(P_dn))
+        self.x = np.ascontiguousarray(x, dtype=np.int8).copy()
+        self.pos = 0
+        self.G = [None, None]
+        self.sign = 1.0
+        self.recompute()
+
+    def recompute(self, stab=10):
+        sg = 1
+        drift = []
+        for s in range(2):
+            G, s_, _ = self.m.green_scratch(self.x, self.P[s], s, self.pos, stab)
+            if self.G[s] is not None:
+                drift.append(np.linalg.norm(self.G[s] - G) / np.linalg.norm(G))
+            self.G[s] = G
+            sg *= s_
+        self.sign = float(sg)
+        return drift
+
+    def sweep_slice(self, ell, direction, mode, u, k=32, nb=4, strategy=2, replay=None, u_acc=None):
+        m, N = self.m, self.m.N
+        xl = self.x[ell - 1]
+        if direction > 0:
+            assert self.pos == ell - 1
+            self.G = [m.wrap(self.G[s], xl, s, +1) for s in range(2)]
+            self.pos = ell
+        else:
+            assert self.pos == ell
+        if mode == "local":
+            Gu, Gd, xn, dec, ratio, sg = m.local_slice(self.G[0], self.G[1], xl, u[:N], replay)
+            extra = {}
+        elif mode == "delayed":
+            Gu, Gd, xn, dec, ratio, sg, nfl = m.delayed_slice(self.G[0], self.G[1], xl, u[:N], k, strategy,
+                                                              replay)
+            extra = {"flushes": nfl}
+        elif mode == "blockfb":
+            nblocks = (N + nb - 1) // nb
+            ua = u[N:N + nblocks] if u_acc is None else u_acc
+            Gu, Gd, xn, xprop, lamp, dec, ratio, sg = m.blockfb_slice(self.G[0], self.G[1], xl, u[:N], ua, nb,
+                                                                     replay)
+            extra = {"xprop": xprop, "lam_plus": lamp}
+        else:
+            raise ValueError(mode)
+        self.G = [Gu, Gd]
+        self.x[ell - 1] = xn
+        self.sign *= sg
+        if direction < 0:
+            self.G = [m.wrap(self.G[s], xn, s, -1) for s in range(2)]
+            self.pos = ell - 1
+        return dec, ratio, extra

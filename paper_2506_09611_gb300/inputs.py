@@ -1,0 +1,74 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle legs.
+
+This module holds none of the update method's arithmetic: it only produces
+the inputs the paper's workloads are made of (Sec. II.A, II.B):
+
+* ``trial_state``  -- the trial Slater determinant P (N x n_sigma): the lowest
+  n_sigma orbitals of the nearest-neighbour hopping matrix.  Every lattice of
+  interest has an open shell at the Fermi level, so a fixed 1e-6 symmetric
+  perturbation (seed 0) picks one orthonormal set inside the degenerate shell.
+* ``initial_fields`` -- i.i.d. +-1 auxiliary fields (p = 1/2) for M slices.
+* ``uniforms``      -- the Metropolis / proposal uniforms of one slice visit.
+  They come from the counter-based Philox4x64-10 generator (Salmon et al.,
+  SC'11) as implemented by numpy: block counter (j + 1, visit, 0, 0), key
+  (seed, walker), word 0 of each block, u = (word >> 11) * 2^-53.  The CUDA
+  library draws the same stream on the device with its own Philox; a GPU test
+  checks the two bit for bit.
+* ``batch_lattices`` -- the mixed-size walker population.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def hopping_matrix(Lx: int, Ly: int, t: float = 1.0) -> np.ndarray:
+    """Periodic nearest-neighbour hopping, K_ij = -t per bond (site i = x + Lx*y)."""
+    N = Lx * Ly
+    K = np.zeros((N, N))
+    for y in range(Ly):
+        for x in range(Lx):
+            i = x + Lx * y
+            for (xx, yy) in (((x + 1) % Lx, y), ((x - 1) % Lx, y), (x, (y + 1) % Ly), (x, (y - 1) % Ly)):
+                K[i, xx + Lx * yy] -= t
+    return K
+
+
+def trial_state(Lx: int, Ly: int, n_sigma: int, t: float = 1.0, seed: int = 0) -> np.ndarray:
+    """Lowest n_sigma eigenvectors of K + 1e-6 * S (S a fixed random symmetric matrix)."""
+    K = hopping_matrix(Lx, Ly, t)
+    rng = np.random.Generator(np.random.Philox(key=np.array([seed, 0xC0FFEE], dtype=np.uint64)))
+    S = rng.standard_normal(K.shape)
+    S = 0.5 * (S + S.T)
+    w, v = np.linalg.eigh(K + 1e-6 * S)
+    return np.ascontiguousarray(v[:, :n_sigma])
+
+
+def initial_fields(M: int, N: int, seed: int = 1, walker: int = 0) -> np.ndarray:
+    """M x N int8 fields, i.i.d. +-1 with probability 1/2."""
+    rng = np.random.Generator(np.random.Philox(key=np.array([seed, 0xF1E1D + walker], dtype=np.uint64)))
+    return np.where(rng.random((M, N)) < 0.5, 1, -1).astype(np.int8)
+
+
+def philox_words(seed: int, walker: int, visit: int, count: int) -> np.ndarray:
+    """Word 0 of the Philox4x64-10 blocks with counters (j+1, visit, 0, 0), j < count."""
+    bg = np.random.Philox(key=np.array([seed, walker], dtype=np.uint64),
+                          counter=np.array([0, visit, 0, 0], dtype=np.uint64))
+    raw = bg.random_raw(4 * count)
+    return raw[0::4].copy()
+
+
+def uniforms(seed: int, walker: int, visit: int, count: int) -> np.ndarray:
+    """Uniforms in [0, 1) with 53 random bits, in the device generator's layout."""
+    w = philox_words(seed, walker, visit, count)
+    return (w >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def batch_lattices(n_walkers: int, seed: int = 5, sizes=(8, 12, 16, 24)) -> np.ndarray:
+    """Linear sizes drawn uniformly from `sizes` for a mixed walker population."""
+    rng = np.random.Generator(np.random.Philox(key=np.array([seed, 0xBA7C4], dtype=np.uint64)))
+    return np.asarray(sizes)[rng.integers(0, len(sizes), n_walkers)].astype(np.int32)
+
+
+def n_sigma_for(L: int, filling: float) -> int:
+    """Particles per spin at total filling n = N_e / N_s (N_up = N_dn)."""
+    return int(round(filling * L * L / 2))

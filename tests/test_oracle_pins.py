@@ -1,0 +1,305 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test compares the oracle with something that is not the oracle: scipy's
+matrix exponential, numpy determinants of the walker overlap (Eq. ConfgWeight),
+the closed-form free-fermion energy, the Fock-space expectation value, or the
+exact transition kernel of an enumerable toy chain.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_09611_gb300 import inputs
+from tests import bruteforce as bf
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def _model(Lx, Ly, U=4.0, dtau=0.05, M=8, hs=oracle.HS_SZ_REAL, t=1.0):
+    return oracle.Model(Lx, Ly, t, U, dtau, M, hs)
+
+
+def _log_scalar(m):
+    if m.p.hs == oracle.HS_CHARGE_REAL:
+        return lambda v: -m.lam * v
+    return None
+
+
+# ---------------------------------------------------------------- model (Eq. 2DHubbard)
+
+@pytest.mark.parametrize("Lx,Ly", [(4, 4), (5, 3), (2, 3), (3, 1)])
+def test_expK_matches_expm(Lx, Ly):
+    m = _model(Lx, Ly, dtau=0.07)
+    K = inputs.hopping_matrix(Lx, Ly)
+    np.testing.assert_allclose(m.K, K, atol=0)
+    np.testing.assert_allclose(m.E, bf.expK(K, 0.07), atol=1e-13)
+    np.testing.assert_allclose(m.Einv, bf.expK(K, -0.07), atol=1e-13)
+    np.testing.assert_allclose(m.E @ m.Einv, np.eye(Lx * Ly), atol=1e-13)
+
+
+def test_hopping_spectrum_is_dispersion():
+    Lx, Ly = 6, 4
+    m = _model(Lx, Ly)
+    eps = sorted(-2 * (np.cos(2 * np.pi * nx / Lx) + np.cos(2 * np.pi * ny / Ly))
+                 for nx in range(Lx) for ny in range(Ly))
+    np.testing.assert_allclose(np.linalg.eigvalsh(m.K), eps, atol=1e-12)
+
+
+@pytest.mark.parametrize("hs,U", [(oracle.HS_SZ_REAL, 4.0), (oracle.HS_SZ_REAL, 6.0),
+                                  (oracle.HS_CHARGE_REAL, -4.0)])
+def test_hs_identity_all_occupations(hs, U):
+    """(1/2) sum_x s(x) exp(x (c_up n_up + c_dn n_dn)) = C exp(-dtau U (n_up n_dn - (n_up+n_dn)/2))
+    with one occupation-independent constant C (C = 1 for the spin channel)."""
+    dtau = 0.05
+    m = _model(2, 2, U=U, dtau=dtau, hs=hs)
+    ls = _log_scalar(m) or (lambda v: 0.0)
+    ratios = []
+    for nu, nd in itertools.product((0, 1), repeat=2):
+        rhs = 0.5 * sum(np.exp(ls(x) + x * (m.c[0] * nu + m.c[1] * nd)) for x in (-1, 1))
+        lhs = np.exp(-dtau * U * (nu * nd - 0.5 * (nu + nd)))
+        ratios.append(rhs / lhs)
+    np.testing.assert_allclose(ratios, ratios[0], rtol=1e-14)
+    if hs == oracle.HS_SZ_REAL:
+        assert abs(ratios[0] - 1.0) < 1e-14
+
+
+# ---------------------------------------------------------------- G (Eqs. GrFMat, GrFMatNew)
+
+def _setup(Lx, Ly, ns, M, seed=3, U=4.0, hs=oracle.HS_SZ_REAL, dtau=0.1):
+    m = _model(Lx, Ly, U=U, M=M, hs=hs, dtau=dtau)
+    P = inputs.trial_state(Lx, Ly, ns)
+    X = inputs.initial_fields(M, Lx * Ly, seed=seed)
+    return m, P, X
+
+
+@pytest.mark.parametrize("ell", [0, 3, 8])
+def test_green_scratch_matches_plain_products(ell):
+    m, P, X = _setup(3, 3, 4, 8)
+    for s in range(2):
+        G, sg, la = m.green_scratch(X, P, s, ell, stab=2)
+        np.testing.assert_allclose(G, bf.green(m.E, m.c[s], X, P, ell), atol=1e-12)
+        det = bf.overlap(m.E, m.c[s], X, P)
+        assert sg == np.sign(det)
+        assert abs(la - np.log(abs(det))) < 1e-10
+
+
+def test_projector_invariants():
+    """A = 1 - G is a rank-n_sigma projector: G^2 = G and tr(1 - G) = n_sigma."""
+    m, P, X = _setup(4, 4, 7, 12)
+    for ell in (0, 5, 12):
+        for s in range(2):
+            G, _, _ = m.green_scratch(X, P, s, ell, stab=3)
+            np.testing.assert_allclose(G @ G, G, atol=1e-11)
+            assert abs(np.trace(np.eye(16) - G) - 7) < 1e-11
+
+
+def test_wrap_matches_scratch():
+    m, P, X = _setup(3, 3, 4, 8)
+    for s in range(2):
+        G3 = bf.green(m.E, m.c[s], X, P, 3)
+        np.testing.assert_allclose(m.wrap(G3, X[3], s, +1), bf.green(m.E, m.c[s], X, P, 4), atol=1e-12)
+        np.testing.assert_allclose(m.wrap(G3, X[2], s, -1), bf.green(m.E, m.c[s], X, P, 2), atol=1e-12)
+
+
+# ---------------------------------------------------------------- local update
+
+@pytest.mark.parametrize("hs,U", [(oracle.HS_SZ_REAL, 4.0), (oracle.HS_CHARGE_REAL, -4.0)])
+def test_local_ratio_is_bruteforce_weight_ratio(hs, U):
+    """R_i = W(X with x_{l,i} flipped) / W(X)  (Eqs. DetailBalance, DetRatio00, DetRatiolocal)."""
+    m, P, X = _setup(3, 2, 2, 6, U=U, hs=hs)
+    ell = 3
+    Gs = [bf.green(m.E, m.c[s], X, P, ell) for s in range(2)]
+    ls = _log_scalar(m)
+    W0 = bf.weight(m.E, m.c, X, P, P, ls)
+    # forced decisions: accept sites 1 and 4 only; every ratio is checked against brute force
+    forced = np.zeros(m.N, np.uint8)
+    forced[[1, 4]] = 1
+    u = np.zeros(m.N)
+    Gu, Gd, xl, dec, ratio, sg = m.local_slice(Gs[0], Gs[1], X[ell - 1], u, replay=forced)
+    Xc = X.copy()
+    Wc = W0
+    for i in range(m.N):
+        Xf = Xc.copy()
+        Xf[ell - 1, i] *= -1
+        Wf = bf.weight(m.E, m.c, Xf, P, P, ls)
+        assert abs(ratio[i] - Wf / Wc) < 1e-10 * max(1, abs(Wf / Wc))
+        if forced[i]:
+            Xc, Wc = Xf, Wf
+    np.testing.assert_array_equal(xl, Xc[ell - 1])
+    np.testing.assert_allclose(Gu, bf.green(m.E, m.c[0], Xc, P, ell), atol=1e-11)
+    np.testing.assert_allclose(Gd, bf.green(m.E, m.c[1], Xc, P, ell), atol=1e-11)
+    assert sg == np.sign(Wc / W0)
+
+
+def test_local_free_running_sweep_tracks_scratch_and_weight():
+    """A forward sweep of local updates: after every slice G equals the from-scratch G of the
+    current fields, and the product of accepted ratios telescopes to W(X_end)/W(X_start)."""
+    Lx, Ly, ns, M = 4, 4, 7, 6
+    m, P, X = _setup(Lx, Ly, ns, M, dtau=0.05)
+    w = oracle.Walker(m, P, P, X)
+    logprod = 0.0
+    W0 = bf.weight(m.E, m.c, X, P, P)
+    for ell in range(1, M + 1):
+        u = inputs.uniforms(1, 0, ell, 2 * m.N)
+        dec, ratio, _ = w.sweep_slice(ell, +1, "local", u)
+        logprod += np.sum(np.log(np.abs(ratio[dec == 1])))
+        for s in range(2):
+            np.testing.assert_allclose(w.G[s], bf.green(m.E, m.c[s], w.x, P, ell), atol=1e-10)
+    W1 = bf.weight(m.E, m.c, w.x, P, P)
+    assert abs(logprod - np.log(abs(W1 / W0))) < 1e-9
+    assert w.sign == np.sign(W1 / W0)
+
+
+# ---------------------------------------------------------------- delayed update
+
+@pytest.mark.parametrize("k,strategy", [(1, 2), (3, 2), (8, 2), (5, 1), (16, 1)])
+def test_delayed_equals_local(k, strategy):
+    """Same uniforms -> identical decisions; G agrees with the local update to 1e-12."""
+    Lx, Ly, ns, M = 4, 4, 7, 4
+    m, P, X = _setup(Lx, Ly, ns, M, dtau=0.05)
+    wl = oracle.Walker(m, P, P, X)
+    wd = oracle.Walker(m, P, P, X)
+    for ell in range(1, M + 1):
+        u = inputs.uniforms(7, 0, ell, 2 * m.N)
+        dl, rl, _ = wl.sweep_slice(ell, +1, "local", u)
+        dd, rd, ex = wd.sweep_slice(ell, +1, "delayed", u, k=k, strategy=strategy)
+        np.testing.assert_array_equal(dl, dd)
+        np.testing.assert_allclose(rd, rl, rtol=1e-11)
+        for s in range(2):
+            assert np.linalg.norm(wd.G[s] - wl.G[s]) / np.linalg.norm(wl.G[s]) < 1e-12
+            np.testing.assert_allclose(wd.G[s], bf.green(m.E, m.c[s], wd.x, P, ell), atol=1e-10)
+    assert wl.sign == wd.sign
+
+
+# ---------------------------------------------------------------- block force-bias update
+
+def test_block_force_bias_is_bruteforce_stripped_density():
+    """nbar_i = [R~ (L R~)^{-1} L]_ii with R~ = B_I^(b)(x_l)^{-1} R  (Eq. BlockFrcbsPhiLPhiR)."""
+    m, P, X = _setup(3, 3, 4, 6)
+    ell, s0, n = 4, 2, 4
+    for s in range(2):
+        G = bf.green(m.E, m.c[s], X, P, ell)
+        R, L = bf.products(m.E, m.c[s], X, P, ell)
+        strip = np.ones(m.N)
+        strip[s0:s0 + n] = np.exp(-m.c[s] * X[ell - 1, s0:s0 + n])
+        Rt = np.diag(strip) @ R
+        At = Rt @ np.linalg.solve(L @ Rt, L)
+        np.testing.assert_allclose(m.block_force_bias(G, X[ell - 1], s, s0, n), np.diag(At)[s0:s0 + n],
+                                   atol=1e-12)
+
+
+def test_blockfb_ratio_and_update_bruteforce():
+    """Forced proposals: the Metropolis ratio equals W(X')/W(X) times the prior ratio
+    prod bbar(x)/bbar(x'); accepted blocks give the from-scratch G (Eq. BlkFrcBsTnew2)."""
+    m, P, X = _setup(3, 3, 4, 6)
+    ell, nb = 3, 4
+    N = m.N
+    nblocks = (N + nb - 1) // nb
+    Gs = [bf.green(m.E, m.c[s], X, P, ell) for s in range(2)]
+    rng = np.random.default_rng(11)
+    rep = np.zeros(N + nblocks, np.uint8)
+    rep[:N] = rng.integers(0, 2, N)
+    rep[N:] = [1, 0, 1]
+    Gu, Gd, xl, xprop, lamp, dec, ratio, sg = m.blockfb_slice(Gs[0], Gs[1], X[ell - 1], np.zeros(N),
+                                                             np.zeros(nblocks), nb, replay=rep)
+    Xc = X.copy()
+    for b in range(nblocks):
+        S = list(range(b * nb, min(N, b * nb + nb)))
+        Xp = Xc.copy()
+        Xp[ell - 1, S] = xprop[S]
+        W = bf.weight(m.E, m.c, Xc, P, P)
+        Wp = bf.weight(m.E, m.c, Xp, P, P)
+        # proposal probabilities: lambda_i(x') from the oracle, lambda_i(x) = complement
+        q_fwd = np.prod([lamp[i] if xprop[i] > 0 else 1 - lamp[i] for i in S])
+        q_bwd = np.prod([lamp[i] if Xc[ell - 1, i] > 0 else 1 - lamp[i] for i in S])
+        assert abs(ratio[b] - (Wp / W) * (q_bwd / q_fwd)) < 1e-10 * max(1.0, abs(ratio[b]))
+        if rep[N + b]:
+            Xc = Xp
+    np.testing.assert_array_equal(xl, Xc[ell - 1])
+    np.testing.assert_allclose(Gu, bf.green(m.E, m.c[0], Xc, P, ell), atol=1e-11)
+    np.testing.assert_allclose(Gd, bf.green(m.E, m.c[1], Xc, P, ell), atol=1e-11)
+
+
+def test_blockfb_exact_detailed_balance():
+    """Exact enumeration on a 2-site, 2-slice toy (16 configurations): the block move's
+    kernel T(X->X') = q(X->X') min(1, |R|) satisfies |W(X)| T(X->X') = |W(X')| T(X'->X)."""
+    Lx, Ly, M, nb = 2, 1, 2, 2
+    m = _model(Lx, Ly, U=6.0, M=M, dtau=0.3)
+    P = inputs.trial_state(Lx, Ly, 1)
+    N = m.N
+    ell = 2
+    configs = [np.array(c, np.int8).reshape(M, N) for c in itertools.product((-1, 1), repeat=M * N)]
+    key = lambda X: tuple(X.ravel())
+    W = {key(X): bf.weight(m.E, m.c, X, P, P) for X in configs}
+    T = {}
+    for X in configs:
+        Gs = [bf.green(m.E, m.c[s], X, P, ell) for s in range(2)]
+        for xp in itertools.product((-1, 1), repeat=N):
+            rep = np.zeros(N + 1, np.uint8)
+            rep[:N] = [1 if v > 0 else 0 for v in xp]
+            _, _, _, xprop, lamp, dec, ratio, _ = m.blockfb_slice(Gs[0], Gs[1], X[ell - 1], np.zeros(N),
+                                                                 np.zeros(1), nb, replay=rep)
+            q = np.prod([lamp[i] if xp[i] > 0 else 1 - lamp[i] for i in range(N)])
+            Xp = X.copy()
+            Xp[ell - 1] = xp
+            T[(key(X), key(Xp))] = q * min(1.0, abs(ratio[0]))
+    checked = 0
+    for (a, b), tab in T.items():
+        if a == b:
+            continue
+        lhs = abs(W[a]) * tab
+        rhs = abs(W[b]) * T[(b, a)]
+        assert abs(lhs - rhs) < 1e-12 * max(abs(lhs), abs(rhs), 1e-300)
+        checked += 1
+    assert checked == 16 * 3
+
+
+def test_blockfb_nb1_is_heatbath_local_move():
+    """With n_b = 1 the block move proposes x' from lambda and its ratio for a flip is the
+    local ratio times the prior ratio bbar(x)/bbar(-x)."""
+    m, P, X = _setup(3, 3, 4, 6)
+    ell = 2
+    N = m.N
+    Gs = [bf.green(m.E, m.c[s], X, P, ell) for s in range(2)]
+    rep = np.zeros(2 * N, np.uint8)
+    rep[:N] = (X[ell - 1] < 0).astype(np.uint8)  # propose the flip everywhere, reject all
+    _, _, _, xprop, lamp, dec, ratio, _ = m.blockfb_slice(Gs[0], Gs[1], X[ell - 1], np.zeros(N),
+                                                         np.zeros(N), 1, replay=rep)
+    _, _, _, _, rl, _ = m.local_slice(Gs[0], Gs[1], X[ell - 1], np.zeros(N), replay=np.zeros(N, np.uint8))
+    for i in range(N):
+        x = X[ell - 1, i]
+        lam_x = lamp[i] if x > 0 else 1 - lamp[i]
+        assert abs(ratio[i] - rl[i] * lam_x / (1 - lam_x)) < 1e-12 * max(1, abs(ratio[i]))
+
+
+# ---------------------------------------------------------------- energy (Eq. Oxformula)
+
+@pytest.mark.parametrize("L,ns,expect", [(4, 7, -24.0), (6, 13, None)])
+def test_energy_free_fermion_closed_form(L, ns, expect):
+    """U = 0: E = 2 * (sum of the lowest n_sigma single-particle energies eps_k)."""
+    m = _model(L, L, U=0.0, M=10)
+    P = inputs.trial_state(L, L, ns)
+    X = inputs.initial_fields(10, L * L)
+    Gs = [m.green_scratch(X, P, s, 5)[0] for s in range(2)]
+    eps = sorted(-2 * (np.cos(2 * np.pi * a / L) + np.cos(2 * np.pi * b / L)) for a in range(L) for b in range(L))
+    closed = 2 * sum(eps[:ns])
+    if expect is not None:
+        assert abs(closed - expect) < 1e-12
+    assert abs(m.energy(Gs[0], Gs[1]) - closed) < 1e-10
+
+
+@pytest.mark.parametrize("U", [4.0, -3.0])
+def test_energy_matches_fock_space(U):
+    """Wick-contracted mixed estimator = <psi_l|H|psi_r>/<psi_l|psi_r> on the Fock space (3 sites)."""
+    Lx, Ly = 3, 1
+    hs = oracle.HS_SZ_REAL if U >= 0 else oracle.HS_CHARGE_REAL
+    m = _model(Lx, Ly, U=U, hs=hs)
+    rng = np.random.default_rng(5)
+    Ru, Rd = rng.standard_normal((3, 1)), rng.standard_normal((3, 2))
+    Lu, Ld = rng.standard_normal((1, 3)), rng.standard_normal((2, 3))
+    Gu = np.eye(3) - Ru @ np.linalg.solve(Lu @ Ru, Lu)
+    Gd = np.eye(3) - Rd @ np.linalg.solve(Ld @ Rd, Ld)
+    e_fock = bf.fock_energy(m.K, U, Ru, Lu, Rd, Ld)
+    assert abs(m.energy(Gu, Gd) - e_fock) < 1e-10
