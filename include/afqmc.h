@@ -1,0 +1,150 @@
+/*
+ * afqmc.h -- C ABI of libafqmc.so: the ground-state AFQMC (PQMC) auxiliary-field
+ * update sweep on the walker's equal-time Green's function G, on one GB300
+ * (sm_103a).
+ *
+ * The method: H. Du and Y.-Y. He, "Accelerating ground-state auxiliary-field
+ * quantum Monte Carlo simulations by delayed update and block force-bias
+ * update" (arXiv:2506.09611).  Section / equation names below are the paper's.
+ *
+ * Conventions.
+ *   Sites i = x + Lx*y on an L x L periodic lattice, N = L*L.
+ *   G_ij = <c_i c_j^+> (Eq. GrFMat); A = 1 - G.  Both spins are stored.
+ *   Slices l = 1..M (Eq. ExpDtH); B_l^s = diag(exp(c_s x_{l,i})) exp(-dtau K)
+ *   (Eq. BlMat).  Fields x_{l,i} = +-1.
+ *   Matrices crossing the ABI are dense row-major unless stated otherwise.
+ *
+ * Ownership.  The library owns every device buffer it allocates (in
+ * afqmc_create / afqmc_init_walkers) and frees them in afqmc_destroy.  Host
+ * pointers passed in are only read (or written, for outputs) during the call;
+ * the caller keeps ownership.  `stream` is a cudaStream_t passed as void*
+ * (NULL = the legacy default stream); all device work of a call is enqueued
+ * on it.  Calls on one context are not thread-safe.
+ *
+ * Errors.  Every call returns 0 on success or a negative AFQMC_ERR_* code.
+ * An error other than AFQMC_ERR_ARG / AFQMC_ERR_STATE is sticky: later calls
+ * on the context return it until afqmc_destroy.  afqmc_strerror gives text.
+ */
+#ifndef AFQMC_H
+#define AFQMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AFQMC_OK 0
+#define AFQMC_ERR_ARG (-1)      /* bad argument (sizes, modes, null pointers) */
+#define AFQMC_ERR_OOM (-2)      /* device allocation failed */
+#define AFQMC_ERR_CUDA (-3)     /* a CUDA runtime call or kernel launch failed */
+#define AFQMC_ERR_NUMERIC (-4)  /* non-finite ratio / singular matrix on the device */
+#define AFQMC_ERR_TIMEOUT (-5)  /* a bounded device-side wait expired */
+#define AFQMC_ERR_STATE (-6)    /* call out of sequence (wrong slice / direction) */
+#define AFQMC_ERR_NODEV (-7)    /* no sm_103 device */
+
+/* Hubbard-Stratonovich decouplings (Sec. II.B, Eq. HSspinDecomp and Hirsch's real channels). */
+#define AFQMC_HS_SZ_REAL 0      /* U >= 0: cosh(lam) = exp(dtau U/2), c_up = lam, c_dn = -lam */
+#define AFQMC_HS_CHARGE_REAL 1  /* U <= 0: cosh(lam) = exp(dtau|U|/2), c_up = c_dn = lam, prefactor exp(-lam x) */
+
+/* Bulk precision of G and of the update / wrap arithmetic. */
+#define AFQMC_PREC_FP64 0       /* FP64 everywhere (parity mode) */
+#define AFQMC_PREC_FP32 1       /* FP32 G; GEMMs at FP32 accuracy */
+
+/* Update schemes of afqmc_sweep_slice (Sec. II.D and Sec. III). */
+#define AFQMC_MODE_LOCAL 0      /* conventional local update (Eqs. DetRatiolocal, UpdateLTRlocal) */
+#define AFQMC_MODE_DELAYED 1    /* delayed update (Eqs. DelayRatio, DelayRgenk, FinalDelay) */
+#define AFQMC_MODE_BLOCKFB 2    /* block force-bias update (Eqs. BlockFrcbsRatio, BlkFrcBsTnew1/2) */
+
+typedef struct afqmc_ctx afqmc_ctx;
+
+/* Physical and numerical parameters shared by all walkers of a context. */
+typedef struct {
+    int hs;             /* AFQMC_HS_* */
+    int precision;      /* AFQMC_PREC_* */
+    int M;              /* number of imaginary-time slices, 2 Theta = M dtau */
+    int stab_every;     /* slices between QR/LU re-orthonormalisations and G recomputes (k_tau) */
+    double t;           /* nearest-neighbour hopping */
+    double U;           /* Hubbard interaction */
+    double dtau;        /* imaginary-time step */
+    uint64_t seed;      /* Philox4x64-10 key word 0 (word 1 = walker index) */
+} afqmc_params;
+
+/* Per-walker statistics of the last afqmc_sweep_slice (valid after a stream sync). */
+typedef struct {
+    int32_t proposals;  /* Metropolis tests (sites, or blocks for block FB) */
+    int32_t accepts;    /* accepted tests */
+    int32_t flipped;    /* fields changed */
+    int32_t flushes;    /* rank-m updates applied to the full G */
+    double max_abs_ratio;
+    double sign;        /* sign of the walker weight W(X) after the slice */
+} afqmc_slice_stats;
+
+/* Create a context.  Checks for an sm_103 device; allocates nothing on it yet.
+ * p is copied.  Returns AFQMC_ERR_ARG for M < 1, stab_every < 1, a bad mode or
+ * a sign of U the decoupling does not allow. */
+int afqmc_create(afqmc_ctx** out, const afqmc_params* p);
+
+/* Free every device and host resource of the context.  NULL is a no-op. */
+int afqmc_destroy(afqmc_ctx* ctx);
+
+/* Allocate and initialise n_walkers walkers (Sec. II.B, Eqs. ConfgWeight, GrFMatNew).
+ *   L[w]       linear lattice size of walker w (N_w = L[w]^2, 2 <= L <= 64).
+ *   n_up[w], n_dn[w]  particles per spin, 1 <= n <= N_w.
+ *   P          host, caller-owned: the trial determinants, concatenated per walker then
+ *              per spin (up, dn), each N_w x n_s row-major (the columns are orbitals).
+ *   fields     host, nullable: M x N_w int8 (+-1) per walker, concatenated; NULL draws
+ *              i.i.d. +-1 fields from Philox(seed, walker).
+ * Builds exp(-+dtau K), the left (U_L) stack of the slices, and G(0) on the device in
+ * FP64, then stores G in the bulk precision.  The walker is left at slice 0, forward. */
+int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n_up, const int* n_dn,
+                       const double* P, const int8_t* fields, void* stream);
+
+/* One slice of the sweep for every walker (Sec. II.C; forward l = 1..M, backward l = M..1).
+ *   dir = +1: wrap G(l-1) -> G(l) = B_l G B_l^{-1}, then update the fields of slice l.
+ *   dir = -1: update the fields of slice l, then wrap G(l) -> G(l-1) = B_l^{-1} G B_l.
+ *   mode  AFQMC_MODE_*;  k  delay rank (sites per delayed step, 1 <= k <= 128 for FP32,
+ *         <= 64 for FP64);  nb  block size for block FB (1 <= nb <= 32).
+ *   replay  host, nullable: forced decisions, 2*N bytes per walker (concatenated):
+ *         local / delayed: replay[i] = accept site i;  block FB: replay[i] = propose
+ *         x'_i = +1 (else -1), replay[N + b] = accept block b.
+ *   stats  host, nullable: one afqmc_slice_stats per walker (the call syncs the stream).
+ * Uniforms come from Philox4x64-10, key (seed, walker), counter (j + 1, visit, 0, 0), where
+ * visit counts the afqmc_sweep_slice calls of the walker; j < N are the site uniforms,
+ * j = N + b the block-acceptance uniforms.  Returns AFQMC_ERR_STATE if the walker is not
+ * at slice l-1 (forward) / l (backward), or if a re-orthonormalisation point was passed
+ * without afqmc_recompute_G. */
+int afqmc_sweep_slice(afqmc_ctx* ctx, int slice, int dir, int mode, int k, int nb, const uint8_t* replay,
+                      afqmc_slice_stats* stats, void* stream);
+
+/* FP64 recompute of G at the current slice (Sec. II.B, Eq. GrFMatNew): propagate the right
+ * (forward) or left (backward) factor from the last re-orthonormalisation point, re-orthonormalise
+ * it (pivoted LU in FP64), and form G = 1 - U_R (U_L U_R)^{-1} U_L, replacing the bulk G.
+ * Must be called whenever the walker sits at a multiple of stab_every (and may be called only
+ * there).  rel_drift (host, nullable, one per walker): ||G_bulk - G_new||_F / ||G_new||_F,
+ * averaged over the spins (the call syncs the stream). */
+int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream);
+
+/* Mixed-estimator energy of every walker from its current G by Wick's theorem
+ * (Eqs. 2DHubbard, Oxformula): E = sum_s tr(K A^s) + U sum_i (A^up_ii A^dn_ii - (A^up_ii + A^dn_ii)/2).
+ * energy, sign: host, one double per walker (sign of W(X)).  Syncs the stream. */
+int afqmc_measure_energy(afqmc_ctx* ctx, double* energy, double* sign, void* stream);
+
+/* Accessors for tests and replay; all sync the stream of the last call. */
+int afqmc_get_G(afqmc_ctx* ctx, int walker, int spin, double* host_out);          /* N x N row-major */
+int afqmc_set_G(afqmc_ctx* ctx, int walker, int spin, const double* host_in);     /* N x N row-major */
+int afqmc_get_fields(afqmc_ctx* ctx, int walker, int8_t* host_out);              /* M x N */
+int afqmc_get_decisions(afqmc_ctx* ctx, int walker, uint8_t* host_out);          /* 2N, replay layout */
+int afqmc_get_ratios(afqmc_ctx* ctx, int walker, double* host_out);              /* 2N: per site / N + block */
+int afqmc_get_info(afqmc_ctx* ctx, int walker, int* N, int* n_up, int* n_dn, int* slice, int* dir);
+
+/* Philox4x64-10 uniforms of the device generator, for checking the stream:
+ * out[j] = u(seed, walker, visit, j) for j < count (device generator, copied to the host). */
+int afqmc_debug_uniforms(uint64_t seed, uint64_t walker, uint64_t visit, int count, double* host_out);
+
+const char* afqmc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFQMC_H */

@@ -1,0 +1,251 @@
+"""Thin ctypes binding of libafqmc.so (include/afqmc.h): argument marshalling only.
+
+Every function mirrors the C entry point of the same name; all arithmetic runs
+in the library's CUDA kernels.  ``load()`` raises if the in-tree library is
+missing or cannot be loaded -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libafqmc.so")
+
+AFQMC_OK = 0
+ERRORS = {-1: "ARG", -2: "OOM", -3: "CUDA", -4: "NUMERIC", -5: "TIMEOUT", -6: "STATE", -7: "NODEV"}
+HS_SZ_REAL, HS_CHARGE_REAL = 0, 1
+PREC_FP64, PREC_FP32 = 0, 1
+MODE_LOCAL, MODE_DELAYED, MODE_BLOCKFB = 0, 1, 2
+MODES = {"local": MODE_LOCAL, "delayed": MODE_DELAYED, "blockfb": MODE_BLOCKFB}
+PRECS = {"fp64": PREC_FP64, "fp32": PREC_FP32}
+
+EXPORTS = ["afqmc_create", "afqmc_destroy", "afqmc_init_walkers", "afqmc_sweep_slice", "afqmc_recompute_G",
+           "afqmc_measure_energy", "afqmc_get_G", "afqmc_set_G", "afqmc_get_fields", "afqmc_get_decisions",
+           "afqmc_get_ratios", "afqmc_get_info", "afqmc_debug_uniforms", "afqmc_strerror"]
+
+
+class afqmc_params(ctypes.Structure):
+    _fields_ = [("hs", ctypes.c_int), ("precision", ctypes.c_int), ("M", ctypes.c_int),
+                ("stab_every", ctypes.c_int), ("t", ctypes.c_double), ("U", ctypes.c_double),
+                ("dtau", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class afqmc_slice_stats(ctypes.Structure):
+    _fields_ = [("proposals", ctypes.c_int32), ("accepts", ctypes.c_int32), ("flipped", ctypes.c_int32),
+                ("flushes", ctypes.c_int32), ("max_abs_ratio", ctypes.c_double), ("sign", ctypes.c_double)]
+
+
+class AfqmcError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn} failed: {code} ({ERRORS.get(code, '?')}): {strerror(code)}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it is missing: there is no CPU path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is missing; build it with paper_2506_09611_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    lib.afqmc_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(afqmc_params)]
+    lib.afqmc_destroy.argtypes = [vp]
+    lib.afqmc_init_walkers.argtypes = [vp, ctypes.c_int, ip, ip, ip, dp, ctypes.POINTER(ctypes.c_int8), vp]
+    lib.afqmc_sweep_slice.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(afqmc_slice_stats), vp]
+    lib.afqmc_recompute_G.argtypes = [vp, dp, vp]
+    lib.afqmc_measure_energy.argtypes = [vp, dp, dp, vp]
+    lib.afqmc_get_G.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
+    lib.afqmc_set_G.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp]
+    lib.afqmc_get_fields.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int8)]
+    lib.afqmc_get_decisions.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8)]
+    lib.afqmc_get_ratios.argtypes = [vp, ctypes.c_int, dp]
+    lib.afqmc_get_info.argtypes = [vp, ctypes.c_int, ip, ip, ip, ip, ip]
+    lib.afqmc_debug_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, dp]
+    lib.afqmc_strerror.argtypes = [ctypes.c_int]
+    lib.afqmc_strerror.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "afqmc_strerror":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().afqmc_strerror(code).decode()
+
+
+def _ck(fn, code):
+    if code != AFQMC_OK:
+        raise AfqmcError(fn, code)
+
+
+def _ptr(a, ct):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)  # torch.cuda.Stream
+
+
+# ---------------------------------------------------------------- C-named entry points
+
+def afqmc_create(hs, precision, M, stab_every, t, U, dtau, seed):
+    p = afqmc_params(hs=hs, precision=precision, M=M, stab_every=stab_every, t=t, U=U, dtau=dtau, seed=seed)
+    h = ctypes.c_void_p()
+    _ck("afqmc_create", load().afqmc_create(ctypes.byref(h), ctypes.byref(p)))
+    return h
+
+
+def afqmc_destroy(ctx):
+    _ck("afqmc_destroy", load().afqmc_destroy(ctx))
+
+
+def afqmc_init_walkers(ctx, L, n_up, n_dn, P, fields=None, stream=None):
+    L = np.ascontiguousarray(L, np.int32)
+    nu = np.ascontiguousarray(n_up, np.int32)
+    nd = np.ascontiguousarray(n_dn, np.int32)
+    P = np.ascontiguousarray(P, np.float64)
+    f = None if fields is None else np.ascontiguousarray(fields, np.int8)
+    _ck("afqmc_init_walkers", load().afqmc_init_walkers(ctx, len(L), _ptr(L, ctypes.c_int), _ptr(nu, ctypes.c_int),
+                                                        _ptr(nd, ctypes.c_int), _ptr(P, ctypes.c_double),
+                                                        _ptr(f, ctypes.c_int8), _stream(stream)))
+
+
+def afqmc_sweep_slice(ctx, slice_, direction, mode, k=32, nb=4, replay=None, stats=None, stream=None):
+    rep = None if replay is None else np.ascontiguousarray(replay, np.uint8)
+    st = None if stats is None else stats
+    _ck("afqmc_sweep_slice", load().afqmc_sweep_slice(ctx, slice_, direction, mode, k, nb, _ptr(rep, ctypes.c_uint8),
+                                                      st, _stream(stream)))
+
+
+def afqmc_recompute_G(ctx, n_walkers=None, stream=None):
+    out = None if n_walkers is None else np.zeros(n_walkers)
+    _ck("afqmc_recompute_G", load().afqmc_recompute_G(ctx, _ptr(out, ctypes.c_double), _stream(stream)))
+    return out
+
+
+def afqmc_measure_energy(ctx, n_walkers, stream=None):
+    e = np.zeros(n_walkers)
+    s = np.zeros(n_walkers)
+    _ck("afqmc_measure_energy", load().afqmc_measure_energy(ctx, _ptr(e, ctypes.c_double), _ptr(s, ctypes.c_double),
+                                                            _stream(stream)))
+    return e, s
+
+
+def afqmc_get_info(ctx, walker):
+    v = [ctypes.c_int() for _ in range(5)]
+    _ck("afqmc_get_info", load().afqmc_get_info(ctx, walker, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("N", "n_up", "n_dn", "slice", "dir"), (x.value for x in v)))
+
+
+def afqmc_get_G(ctx, walker, spin):
+    N = afqmc_get_info(ctx, walker)["N"]
+    out = np.zeros((N, N))
+    _ck("afqmc_get_G", load().afqmc_get_G(ctx, walker, spin, _ptr(out, ctypes.c_double)))
+    return out
+
+
+def afqmc_set_G(ctx, walker, spin, G):
+    G = np.ascontiguousarray(G, np.float64)
+    _ck("afqmc_set_G", load().afqmc_set_G(ctx, walker, spin, _ptr(G, ctypes.c_double)))
+
+
+def afqmc_get_fields(ctx, walker, M):
+    N = afqmc_get_info(ctx, walker)["N"]
+    out = np.zeros((M, N), np.int8)
+    _ck("afqmc_get_fields", load().afqmc_get_fields(ctx, walker, _ptr(out, ctypes.c_int8)))
+    return out
+
+
+def afqmc_get_decisions(ctx, walker):
+    N = afqmc_get_info(ctx, walker)["N"]
+    out = np.zeros(2 * N, np.uint8)
+    _ck("afqmc_get_decisions", load().afqmc_get_decisions(ctx, walker, _ptr(out, ctypes.c_uint8)))
+    return out
+
+
+def afqmc_get_ratios(ctx, walker):
+    N = afqmc_get_info(ctx, walker)["N"]
+    out = np.zeros(2 * N)
+    _ck("afqmc_get_ratios", load().afqmc_get_ratios(ctx, walker, _ptr(out, ctypes.c_double)))
+    return out
+
+
+def afqmc_debug_uniforms(seed, walker, visit, count):
+    out = np.zeros(count)
+    _ck("afqmc_debug_uniforms", load().afqmc_debug_uniforms(seed, walker, visit, count, _ptr(out, ctypes.c_double)))
+    return out
+
+
+# ---------------------------------------------------------------- convenience wrapper
+
+class Context:
+    """Owns one afqmc_ctx; methods forward to the C entry points above."""
+
+    def __init__(self, M, dtau=0.05, U=4.0, t=1.0, precision="fp64", hs=HS_SZ_REAL, stab_every=10, seed=1):
+        self.M = M
+        self.h = afqmc_create(hs, PRECS.get(precision, precision), M, stab_every, t, U, dtau, seed)
+        self.n = 0
+
+    def init_walkers(self, L, n_up, n_dn, P, fields=None, stream=None):
+        self.n = len(L)
+        afqmc_init_walkers(self.h, L, n_up, n_dn, P, fields, stream)
+
+    def sweep_slice(self, ell, direction, mode, k=32, nb=4, replay=None, want_stats=False, stream=None):
+        stats = (afqmc_slice_stats * self.n)() if want_stats else None
+        afqmc_sweep_slice(self.h, ell, direction, MODES.get(mode, mode), k, nb, replay, stats, stream)
+        return stats
+
+    def recompute_G(self, stream=None):
+        return afqmc_recompute_G(self.h, self.n, stream)
+
+    def measure_energy(self, stream=None):
+        return afqmc_measure_energy(self.h, self.n, stream)
+
+    def G(self, walker, spin):
+        return afqmc_get_G(self.h, walker, spin)
+
+    def set_G(self, walker, spin, G):
+        afqmc_set_G(self.h, walker, spin, G)
+
+    def fields(self, walker):
+        return afqmc_get_fields(self.h, walker, self.M)
+
+    def decisions(self, walker):
+        return afqmc_get_decisions(self.h, walker)
+
+    def ratios(self, walker):
+        return afqmc_get_ratios(self.h, walker)
+
+    def info(self, walker):
+        return afqmc_get_info(self.h, walker)
+
+    def close(self):
+        if self.h is not None:
+            afqmc_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

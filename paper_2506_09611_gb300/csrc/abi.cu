@@ -1,0 +1,746 @@
+// abi.cu -- the C ABI of libafqmc.so (include/afqmc.h): contexts, walkers and
+// the orchestration of one slice of the PQMC sweep (Sec. II.B-II.D, III).
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "internal.h"
+
+using namespace afq;
+
+namespace {
+
+struct Lattice {
+    int L = 0, N = 0;
+    long ld = 0;
+    double* E64 = nullptr;
+    double* Einv64 = nullptr;
+    void* Eb = nullptr;
+    void* Einvb = nullptr;
+};
+
+struct Walker {
+    int L = 0, N = 0;
+    long ld = 0;
+    int ns[2] = {0, 0};
+    int pos = 0, last_dir = -1;
+    bool need_recompute = false;
+    uint64_t visit = 0;
+    Lattice* lat = nullptr;
+    void* G = nullptr;      // [2][N][ld] bulk
+    void* Tbuf = nullptr;   // [2][N][ld] bulk (wrap temporary)
+    int8_t* x = nullptr;    // M x N
+    double* u = nullptr;    // 2N uniforms
+    void* dvec = nullptr;   // bulk [2][N] d, then [2][N] dinv
+    double* d64 = nullptr;  // FP64 [2][N] d, [2][N] dinv
+    uint8_t* dec = nullptr;
+    double* ratio = nullptr;
+    int* stats = nullptr;   // 4 ints
+    double* maxr = nullptr;
+    double* sign = nullptr;
+    uint8_t* replay = nullptr;
+    void* colbuf = nullptr;
+    void* rowbuf = nullptr;
+    GridBar* bar = nullptr;
+    int* err = nullptr;
+    int* wm = nullptr;
+    int* widx = nullptr;
+    double* wdtot = nullptr;
+    void* Wm = nullptr;
+    void* X = nullptr;
+    void* Y = nullptr;
+    double* URs[2] = {nullptr, nullptr};
+    double* ULs[2] = {nullptr, nullptr};
+    double* Ucur = nullptr;
+    double* Utmp = nullptr;
+    double* aug = nullptr;
+    double* Z = nullptr;
+    double* Gnew = nullptr;
+    int* perm = nullptr;
+    void* elim = nullptr;
+    double* acc2 = nullptr;
+    std::vector<void*> allocs;
+};
+
+}  // namespace
+
+struct afqmc_ctx {
+    afqmc_params p;
+    double lam = 0.0, c[2] = {0.0, 0.0};
+    int sticky = 0;
+    int nsm = 0;
+    std::vector<Lattice*> lats;
+    std::vector<Walker*> w;
+    std::vector<void*> allocs;
+    cudaStream_t last = nullptr;
+};
+
+#define CK(call)                                        \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return fail(ctx, e_);    \
+    } while (0)
+
+static int fail(afqmc_ctx* ctx, cudaError_t e) {
+    int code = (e == cudaErrorMemoryAllocation) ? AFQMC_ERR_OOM : AFQMC_ERR_CUDA;
+    if (ctx && ctx->sticky == 0) ctx->sticky = code;
+    return code;
+}
+
+template <typename P>
+static cudaError_t dalloc(std::vector<void*>& list, P** out, size_t bytes) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes < 16 ? 16 : bytes);
+    if (e != cudaSuccess) return e;
+    list.push_back(p);
+    *out = (P*)p;
+    return cudaSuccess;
+}
+
+static size_t esize(const afqmc_ctx* ctx) { return ctx->p.precision == AFQMC_PREC_FP64 ? 8 : 4; }
+
+// ---------------------------------------------------------------------------
+// small kernels local to the ABI layer
+// ---------------------------------------------------------------------------
+__global__ void transpose_kernel(const double* A, int rows, int cols, double* B) {  // B = A^T
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)rows * cols; e += (long)gridDim.x * blockDim.x) {
+        int r = (int)(e / cols), c = (int)(e % cols);
+        B[(long)c * rows + r] = A[e];
+    }
+}
+
+__global__ void fields_kernel(uint64_t seed, uint64_t walker, long count, int8_t* x) {
+    long j = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < count) x[j] = philox_uniform(seed, walker, ~0ULL, (uint64_t)j) < 0.5 ? 1 : -1;
+}
+
+__global__ void set_double_kernel(double* p, double v) { *p = v; }
+
+__global__ void debug_uniforms_kernel(uint64_t seed, uint64_t walker, uint64_t visit, int count, double* out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < count) out[j] = philox_uniform(seed, walker, visit, (uint64_t)j);
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static int check_ctx(afqmc_ctx* ctx) {
+    if (!ctx) return AFQMC_ERR_ARG;
+    if (ctx->sticky) return ctx->sticky;
+    return 0;
+}
+
+static int read_dev_err(afqmc_ctx* ctx, Walker* w) {
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, w->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(ctx, e);
+    if (h == DEV_TIMEOUT) ctx->sticky = AFQMC_ERR_TIMEOUT;
+    else if (h == DEV_NUMERIC) ctx->sticky = AFQMC_ERR_NUMERIC;
+    else if (h != 0) ctx->sticky = AFQMC_ERR_CUDA;
+    return ctx->sticky;
+}
+
+static Lattice* get_lattice(afqmc_ctx* ctx, int L, cudaStream_t st, cudaError_t* err) {
+    for (auto* l : ctx->lats)
+        if (l->L == L) return l;
+    Lattice* l = new Lattice();
+    l->L = L;
+    l->N = L * L;
+    l->ld = ((l->N + 31) / 32) * 32;
+    size_t n2 = (size_t)l->N * l->ld;
+    *err = cudaSuccess;
+    if ((*err = dalloc(ctx->allocs, &l->E64, n2 * 8)) != cudaSuccess) return nullptr;
+    if ((*err = dalloc(ctx->allocs, &l->Einv64, n2 * 8)) != cudaSuccess) return nullptr;
+    if ((*err = dalloc(ctx->allocs, (char**)&l->Eb, n2 * esize(ctx))) != cudaSuccess) return nullptr;
+    if ((*err = dalloc(ctx->allocs, (char**)&l->Einvb, n2 * esize(ctx))) != cudaSuccess) return nullptr;
+    if ((*err = launch_expK(st, L, ctx->p.t, ctx->p.dtau, l->E64, l->ld)) != cudaSuccess) return nullptr;
+    if ((*err = launch_expK(st, L, ctx->p.t, -ctx->p.dtau, l->Einv64, l->ld)) != cudaSuccess) return nullptr;
+    if (ctx->p.precision == AFQMC_PREC_FP64) {
+        if ((*err = launch_cast<double>(st, l->E64, l->ld, (double*)l->Eb, l->ld, l->N, l->N)) != cudaSuccess) return nullptr;
+        if ((*err = launch_cast<double>(st, l->Einv64, l->ld, (double*)l->Einvb, l->ld, l->N, l->N)) != cudaSuccess) return nullptr;
+    } else {
+        if ((*err = launch_cast<float>(st, l->E64, l->ld, (float*)l->Eb, l->ld, l->N, l->N)) != cudaSuccess) return nullptr;
+        if ((*err = launch_cast<float>(st, l->Einv64, l->ld, (float*)l->Einvb, l->ld, l->N, l->N)) != cudaSuccess) return nullptr;
+    }
+    ctx->lats.push_back(l);
+    return l;
+}
+
+// G_new (FP64, N x ld) = 1 - UR (UL UR)^{-1} UL ; multiplies *sign by sign(det(UL UR)).
+static cudaError_t form_G(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, const double* UR, const double* UL,
+                          double* sign) {
+    const int N = w->N, ns = w->ns[s];
+    const long la = ns + N;
+    GemmArgs<double> g;
+    g.M = ns; g.N = ns; g.K = N;
+    g.A = UL; g.lda = N;
+    g.B = UR; g.ldb = ns;
+    g.C = w->aug; g.ldc = la;
+    cudaError_t e = gemm<double>(st, g);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy2DAsync(w->aug + ns, la * 8, UL, (size_t)N * 8, (size_t)N * 8, ns, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    e = launch_elim(st, 1, w->aug, ns, ns, la, 1, N, w->perm, sign, w->elim, w->err);
+    if (e != cudaSuccess) return e;
+    e = launch_gj_extract(st, w->aug, la, ns, N, w->perm, w->Z, N);
+    if (e != cudaSuccess) return e;
+    GemmArgs<double> h;
+    h.M = N; h.N = N; h.K = ns;
+    h.A = UR; h.lda = ns;
+    h.B = w->Z; h.ldb = N;
+    h.C = w->Gnew; h.ldc = w->ld;
+    e = gemm<double>(st, h);
+    if (e != cudaSuccess) return e;
+    return launch_identity_minus<double>(st, w->Gnew, w->ld, N);
+}
+
+// U (N x ns) <- B_l U  with B_l = diag(exp(c_s x_l)) E
+static cudaError_t prop_right(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, int ell, double* U, double* tmp) {
+    const int N = w->N, ns = w->ns[s];
+    cudaError_t e = launch_field_scales_T<double>(st, w->x + (size_t)(ell - 1) * N, N, ctx->c, w->d64, w->d64 + 2 * N, N);
+    if (e != cudaSuccess) return e;
+    GemmArgs<double> g;
+    g.M = N; g.N = ns; g.K = N;
+    g.A = w->lat->E64; g.lda = w->lat->ld;
+    g.B = U; g.ldb = ns;
+    g.C = tmp; g.ldc = ns;
+    g.rs = w->d64 + (size_t)s * N;
+    e = gemm<double>(st, g);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(U, tmp, (size_t)N * ns * 8, cudaMemcpyDeviceToDevice, st);
+}
+
+// U (ns x N) <- U B_l
+static cudaError_t prop_left(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, int ell, double* U, double* tmp) {
+    const int N = w->N, ns = w->ns[s];
+    cudaError_t e = launch_field_scales_T<double>(st, w->x + (size_t)(ell - 1) * N, N, ctx->c, w->d64, w->d64 + 2 * N, N);
+    if (e != cudaSuccess) return e;
+    GemmArgs<double> g;
+    g.M = ns; g.N = N; g.K = N;
+    g.A = U; g.lda = N;
+    g.B = w->lat->E64; g.ldb = w->lat->ld;
+    g.C = tmp; g.ldc = N;
+    g.bs = w->d64 + (size_t)s * N;
+    e = gemm<double>(st, g);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(U, tmp, (size_t)N * ns * 8, cudaMemcpyDeviceToDevice, st);
+}
+
+static cudaError_t stab_right(Walker* w, cudaStream_t st, int s, double* U, double* sign) {  // U: N x ns
+    return launch_elim(st, 0, U, w->N, w->ns[s], w->ns[s], 1, 0, w->perm, sign, w->elim, w->err);
+}
+static cudaError_t stab_left(Walker* w, cudaStream_t st, int s, double* U, double* sign) {  // U: ns x N
+    return launch_elim(st, 0, U, w->N, w->ns[s], 1, w->N, 0, w->perm, sign, w->elim, w->err);
+}
+
+template <typename T>
+static cudaError_t store_G(Walker* w, cudaStream_t st, int s) {
+    T* G = (T*)w->G + (size_t)s * w->N * w->ld;
+    return launch_cast<T>(st, w->Gnew, w->ld, G, w->ld, w->N, w->N);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* afqmc_strerror(int code) {
+    switch (code) {
+        case AFQMC_OK: return "ok";
+        case AFQMC_ERR_ARG: return "invalid argument";
+        case AFQMC_ERR_OOM: return "device allocation failed";
+        case AFQMC_ERR_CUDA: return "CUDA runtime error";
+        case AFQMC_ERR_NUMERIC: return "non-finite ratio or singular matrix on the device";
+        case AFQMC_ERR_TIMEOUT: return "a bounded device-side wait expired";
+        case AFQMC_ERR_STATE: return "call out of sequence";
+        case AFQMC_ERR_NODEV: return "no sm_103 device";
+        default: return "unknown error";
+    }
+}
+
+int afqmc_create(afqmc_ctx** out, const afqmc_params* p) {
+    if (!out || !p) return AFQMC_ERR_ARG;
+    *out = nullptr;
+    if (p->M < 1 || p->stab_every < 1 || p->M % p->stab_every != 0) return AFQMC_ERR_ARG;
+    if (p->precision != AFQMC_PREC_FP64 && p->precision != AFQMC_PREC_FP32) return AFQMC_ERR_ARG;
+    if (!(p->dtau > 0.0)) return AFQMC_ERR_ARG;
+    double lam;
+    double c0, c1;
+    if (p->hs == AFQMC_HS_SZ_REAL) {
+        if (p->U < 0) return AFQMC_ERR_ARG;
+        lam = acosh(exp(p->dtau * p->U / 2.0));
+        c0 = lam; c1 = -lam;
+    } else if (p->hs == AFQMC_HS_CHARGE_REAL) {
+        if (p->U > 0) return AFQMC_ERR_ARG;
+        lam = acosh(exp(p->dtau * fabs(p->U) / 2.0));
+        c0 = lam; c1 = lam;
+    } else {
+        return AFQMC_ERR_ARG;
+    }
+    int dev = 0, major = 0, minor = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return AFQMC_ERR_NODEV;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (major != 10 || minor != 3) return AFQMC_ERR_NODEV;
+    afqmc_ctx* ctx = new afqmc_ctx();
+    ctx->p = *p;
+    ctx->lam = lam;
+    ctx->c[0] = c0;
+    ctx->c[1] = c1;
+    ctx->nsm = nsm;
+    *out = ctx;
+    return AFQMC_OK;
+}
+
+int afqmc_destroy(afqmc_ctx* ctx) {
+    if (!ctx) return AFQMC_OK;
+    cudaDeviceSynchronize();
+    for (auto* w : ctx->w) {
+        for (void* p : w->allocs) cudaFree(p);
+        delete w;
+    }
+    for (void* p : ctx->allocs) cudaFree(p);
+    for (auto* l : ctx->lats) delete l;
+    delete ctx;
+    return AFQMC_OK;
+}
+
+int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n_up, const int* n_dn,
+                       const double* P, const int8_t* fields, void* stream) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (n_walkers < 1 || !L || !n_up || !n_dn || !P || !ctx->w.empty()) return AFQMC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->last = st;
+    const int M = ctx->p.M, S = ctx->p.stab_every, nst = M / S + 1;
+    const size_t es = esize(ctx);
+    size_t poff = 0, foff = 0;
+    for (int wi = 0; wi < n_walkers; ++wi) {
+        if (L[wi] < 2 || L[wi] > 64) return AFQMC_ERR_ARG;
+        int N = L[wi] * L[wi];
+        if (n_up[wi] < 1 || n_up[wi] > N || n_dn[wi] < 1 || n_dn[wi] > N) return AFQMC_ERR_ARG;
+    }
+    for (int wi = 0; wi < n_walkers; ++wi) {
+        Walker* w = new Walker();
+        ctx->w.push_back(w);
+        cudaError_t e;
+        w->lat = get_lattice(ctx, L[wi], st, &e);
+        if (!w->lat) return fail(ctx, e);
+        w->L = L[wi];
+        w->N = w->lat->N;
+        w->ld = w->lat->ld;
+        w->ns[0] = n_up[wi];
+        w->ns[1] = n_dn[wi];
+        const int N = w->N;
+        const long ld = w->ld;
+        const int nsm = w->ns[0] > w->ns[1] ? w->ns[0] : w->ns[1];
+        const int NW = (ctx->p.precision == AFQMC_PREC_FP64) ? window_max<double>() : window_max<float>();
+        auto& A = w->allocs;
+        CK(dalloc(A, (char**)&w->G, 2 * (size_t)N * ld * es));
+        CK(dalloc(A, (char**)&w->Tbuf, 2 * (size_t)N * ld * es));
+        CK(dalloc(A, &w->x, (size_t)M * N));
+        CK(dalloc(A, &w->u, 2 * (size_t)N * 8));
+        CK(dalloc(A, (char**)&w->dvec, 4 * (size_t)N * es));
+        CK(dalloc(A, &w->d64, 4 * (size_t)N * 8));
+        CK(dalloc(A, &w->dec, 2 * (size_t)N));
+        CK(dalloc(A, &w->ratio, 2 * (size_t)N * 8));
+        CK(dalloc(A, &w->stats, 8 * sizeof(int)));
+        CK(dalloc(A, &w->maxr, 8));
+        CK(dalloc(A, &w->sign, 8));
+        CK(dalloc(A, &w->replay, 2 * (size_t)N));
+        CK(dalloc(A, (char**)&w->colbuf, 4 * (size_t)N * es));
+        CK(dalloc(A, (char**)&w->rowbuf, 4 * (size_t)N * es));
+        CK(dalloc(A, &w->bar, sizeof(GridBar)));
+        CK(dalloc(A, &w->err, sizeof(int)));
+        CK(dalloc(A, &w->wm, sizeof(int)));
+        CK(dalloc(A, &w->widx, (size_t)NW * sizeof(int)));
+        CK(dalloc(A, &w->wdtot, 2 * (size_t)NW * 8));
+        CK(dalloc(A, (char**)&w->Wm, 2 * (size_t)NW * NW * es));
+        CK(dalloc(A, (char**)&w->X, 2 * (size_t)N * NW * es));
+        CK(dalloc(A, (char**)&w->Y, 4 * (size_t)NW * N * es));
+        for (int s = 0; s < 2; ++s) {
+            CK(dalloc(A, &w->URs[s], (size_t)nst * N * w->ns[s] * 8));
+            CK(dalloc(A, &w->ULs[s], (size_t)nst * N * w->ns[s] * 8));
+        }
+        CK(dalloc(A, &w->Ucur, (size_t)N * nsm * 8));
+        CK(dalloc(A, &w->Utmp, (size_t)N * nsm * 8));
+        CK(dalloc(A, &w->aug, (size_t)nsm * (nsm + N) * 8));
+        CK(dalloc(A, &w->Z, (size_t)nsm * N * 8));
+        CK(dalloc(A, &w->Gnew, (size_t)N * ld * 8));
+        CK(dalloc(A, &w->perm, (size_t)(N > nsm ? N : nsm) * sizeof(int)));
+        CK(dalloc(A, (char**)&w->elim, elim_scratch_bytes(N > nsm ? N : nsm)));
+        CK(dalloc(A, &w->acc2, 2 * 8));
+        CK(cudaMemsetAsync(w->err, 0, sizeof(int), st));
+        CK(cudaMemsetAsync(w->G, 0, 2 * (size_t)N * ld * es, st));
+        CK(cudaMemsetAsync(w->Tbuf, 0, 2 * (size_t)N * ld * es, st));
+        // fields
+        if (fields) {
+            CK(cudaMemcpyAsync(w->x, fields + foff, (size_t)M * N, cudaMemcpyHostToDevice, st));
+            foff += (size_t)M * N;
+        } else {
+            fields_kernel<<<(int)(((long)M * N + 255) / 256), 256, 0, st>>>(ctx->p.seed, (uint64_t)wi, (long)M * N, w->x);
+            CK(cudaGetLastError());
+        }
+        set_double_kernel<<<1, 1, 0, st>>>(w->sign, 1.0);
+        CK(cudaGetLastError());
+        // trial determinants -> stacks, G(0)  (Sec. II.B)
+        for (int s = 0; s < 2; ++s) {
+            const int ns = w->ns[s];
+            const double* Ph = P + poff;
+            poff += (size_t)N * ns;
+            // P into URs[s][0] (N x ns), re-orthonormalised
+            double* UR0 = w->URs[s];
+            CK(cudaMemcpyAsync(UR0, Ph, (size_t)N * ns * 8, cudaMemcpyHostToDevice, st));
+            transpose_kernel<<<256, 256, 0, st>>>(UR0, N, ns, w->Ucur);  // Ucur = P^T (ns x N)
+            CK(cudaGetLastError());
+            CK(stab_right(w, st, s, UR0, w->sign));
+            // left stack: U_L(M) = P^T, U_L(l-1) = U_L(l) B_l
+            CK(stab_left(w, st, s, w->Ucur, w->sign));
+            CK(cudaMemcpyAsync(w->ULs[s] + (size_t)(M / S) * N * ns, w->Ucur, (size_t)N * ns * 8,
+                               cudaMemcpyDeviceToDevice, st));
+            for (int ell = M; ell >= 1; --ell) {
+                CK(prop_left(ctx, w, st, s, ell, w->Ucur, w->Utmp));
+                if ((ell - 1) % S == 0) {
+                    CK(stab_left(w, st, s, w->Ucur, w->sign));
+                    CK(cudaMemcpyAsync(w->ULs[s] + (size_t)((ell - 1) / S) * N * ns, w->Ucur, (size_t)N * ns * 8,
+                                       cudaMemcpyDeviceToDevice, st));
+                }
+            }
+            CK(form_G(ctx, w, st, s, UR0, w->ULs[s], w->sign));
+            if (ctx->p.precision == AFQMC_PREC_FP64) CK(store_G<double>(w, st, s));
+            else CK(store_G<float>(w, st, s));
+        }
+        w->pos = 0;
+        w->last_dir = -1;
+        w->need_recompute = false;
+        w->visit = 0;
+    }
+    CK(cudaStreamSynchronize(st));
+    for (auto* w : ctx->w) {
+        int r = read_dev_err(ctx, w);
+        if (r) return r;
+    }
+    return AFQMC_OK;
+}
+
+}  // extern "C"
+
+template <typename T>
+static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k, int nb, const uint8_t* replay,
+                      cudaStream_t st) {
+    Walker* w = ctx->w[wi];
+    const int N = w->N;
+    const long ld = w->ld;
+    T* G0 = (T*)w->G;
+    T* G1 = G0 + (size_t)N * ld;
+    T* Tb = (T*)w->Tbuf;
+    int8_t* xl = w->x + (size_t)(ell - 1) * N;
+    T* d = (T*)w->dvec;
+    T* dinv = d + 2 * N;
+    const T* E = (const T*)w->lat->Eb;
+    const T* Einv = (const T*)w->lat->Einvb;
+    const int NW = window_max<T>();
+    CK(launch_uniforms(st, ctx->p.seed, (uint64_t)wi, w->visit, 2 * N, w->u));
+    CK(cudaMemsetAsync(w->stats, 0, 8 * sizeof(int), st));
+    CK(cudaMemsetAsync(w->maxr, 0, 8, st));
+    const uint8_t* rep = nullptr;
+    if (replay) {
+        CK(cudaMemcpyAsync(w->replay, replay + (size_t)wi * 2 * N, 2 * (size_t)N, cudaMemcpyHostToDevice, st));
+        rep = w->replay;
+    }
+    auto wrap = [&](int direction) -> cudaError_t {
+        cudaError_t e = launch_field_scales_T<T>(st, xl, N, ctx->c, d, dinv, N);
+        if (e != cudaSuccess) return e;
+        GemmArgs<T> g1, g2;
+        g1.M = N; g1.N = N; g1.K = N; g1.batch = 2;
+        g1.ldb = ld; g1.sB = (long)N * ld;
+        g1.C = Tb; g1.ldc = ld; g1.sC = (long)N * ld;
+        g1.lda = ld; g1.sA = 0;
+        g2 = g1;
+        if (direction > 0) {
+            // Tb = E G ; G = D (Tb Einv) D^{-1}
+            g1.A = E; g1.B = G0;
+            g2.A = Tb; g2.sA = (long)N * ld;
+            g2.B = Einv; g2.sB = 0;
+            g2.C = G0;
+            g2.rs = d; g2.srs = N;
+            g2.cs = dinv; g2.scs = N;
+        } else {
+            // Tb = Einv D^{-1} G D ; G = Tb E
+            g1.A = Einv; g1.B = G0;
+            g1.bs = dinv; g1.sbs = N;
+            g1.cs = d; g1.scs = N;
+            g2.A = Tb; g2.sA = (long)N * ld;
+            g2.B = E; g2.sB = 0;
+            g2.C = G0;
+        }
+        e = gemm<T>(st, g1);
+        if (e != cudaSuccess) return e;
+        return gemm<T>(st, g2);
+    };
+    if (dir > 0) CK(wrap(+1));
+    SiteParams sp;
+    sp.N = N;
+    sp.ld = ld;
+    sp.c[0] = ctx->c[0];
+    sp.c[1] = ctx->c[1];
+    sp.lam = ctx->lam;
+    sp.hs = ctx->p.hs;
+    sp.seed = ctx->p.seed;
+    sp.walker = (uint64_t)wi;
+    sp.visit = w->visit;
+    SliceOut so;
+    so.dec = w->dec;
+    so.ratio = w->ratio;
+    so.stats = w->stats;
+    so.maxr = w->maxr;
+    so.sign = w->sign;
+    if (mode == AFQMC_MODE_LOCAL) {
+        CK(cudaMemsetAsync(w->bar, 0, sizeof(GridBar), st));
+        CK(launch_local<T>(st, G0, G1, xl, w->u, rep, sp, so, (T*)w->colbuf, (T*)w->rowbuf, w->bar, w->err,
+                           ctx->nsm));
+    } else {
+        int nw = (mode == AFQMC_MODE_DELAYED) ? k : (NW / nb) * nb;
+        WindowBufs wb;
+        wb.m = w->wm;
+        wb.idx = w->widx;
+        wb.dtot = w->wdtot;
+        wb.Wm = w->Wm;
+        wb.X = w->X;
+        wb.Y = w->Y;
+        for (int s0 = 0; s0 < N; s0 += nw) {
+            int n = (N - s0 < nw) ? N - s0 : nw;
+            CK(launch_window_chain<T>(st, mode, G0, G1, xl, w->u, rep, sp, so, s0, n, nb, wb, w->err));
+            CK(launch_flush<T>(st, G0, G1, sp, wb, n));
+        }
+    }
+    if (dir < 0) CK(wrap(-1));
+    return AFQMC_OK;
+}
+
+extern "C" {
+
+int afqmc_sweep_slice(afqmc_ctx* ctx, int slice, int dir, int mode, int k, int nb, const uint8_t* replay,
+                      afqmc_slice_stats* stats, void* stream) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (ctx->w.empty() || slice < 1 || slice > ctx->p.M || (dir != 1 && dir != -1)) return AFQMC_ERR_ARG;
+    const bool f64 = ctx->p.precision == AFQMC_PREC_FP64;
+    const int NW = f64 ? window_max<double>() : window_max<float>();
+    if (mode == AFQMC_MODE_DELAYED && (k < 1 || k > NW)) return AFQMC_ERR_ARG;
+    if (mode == AFQMC_MODE_BLOCKFB && (nb < 1 || nb > 32)) return AFQMC_ERR_ARG;
+    if (mode != AFQMC_MODE_LOCAL && mode != AFQMC_MODE_DELAYED && mode != AFQMC_MODE_BLOCKFB) return AFQMC_ERR_ARG;
+    for (auto* w : ctx->w) {
+        if (w->need_recompute) return AFQMC_ERR_STATE;
+        if (dir > 0 && w->pos != slice - 1) return AFQMC_ERR_STATE;
+        if (dir < 0 && w->pos != slice) return AFQMC_ERR_STATE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->last = st;
+    for (int wi = 0; wi < (int)ctx->w.size(); ++wi) {
+        rc = f64 ? sweep_impl<double>(ctx, wi, slice, dir, mode, k, nb, replay, st)
+                 : sweep_impl<float>(ctx, wi, slice, dir, mode, k, nb, replay, st);
+        if (rc) return rc;
+        Walker* w = ctx->w[wi];
+        w->pos = (dir > 0) ? slice : slice - 1;
+        w->last_dir = dir;
+        w->visit++;
+        if (w->pos % ctx->p.stab_every == 0) w->need_recompute = true;
+    }
+    if (stats) {
+        CK(cudaStreamSynchronize(st));
+        for (int wi = 0; wi < (int)ctx->w.size(); ++wi) {
+            Walker* w = ctx->w[wi];
+            int r = read_dev_err(ctx, w);
+            if (r) return r;
+            int h[8];
+            CK(cudaMemcpy(h, w->stats, sizeof(h), cudaMemcpyDeviceToHost));
+            stats[wi].proposals = h[0];
+            stats[wi].accepts = h[1];
+            stats[wi].flipped = h[2];
+            stats[wi].flushes = h[3];
+            CK(cudaMemcpy(&stats[wi].max_abs_ratio, w->maxr, 8, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(&stats[wi].sign, w->sign, 8, cudaMemcpyDeviceToHost));
+        }
+    }
+    return AFQMC_OK;
+}
+
+int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (ctx->w.empty()) return AFQMC_ERR_ARG;
+    const int S = ctx->p.stab_every;
+    for (auto* w : ctx->w)
+        if (w->pos % S != 0) return AFQMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->last = st;
+    const bool f64 = ctx->p.precision == AFQMC_PREC_FP64;
+    std::vector<double> drift(ctx->w.size(), 0.0);
+    for (int wi = 0; wi < (int)ctx->w.size(); ++wi) {
+        Walker* w = ctx->w[wi];
+        const int N = w->N, j = w->pos / S;
+        CK(cudaMemsetAsync(w->acc2, 0, 16, st));
+        for (int s = 0; s < 2; ++s) {
+            const int ns = w->ns[s];
+            const size_t blk = (size_t)N * ns;
+            double* UR;
+            double* UL;
+            if (w->last_dir > 0) {
+                if (j == 0) {
+                    UR = w->URs[s];
+                } else {
+                    CK(cudaMemcpyAsync(w->Ucur, w->URs[s] + (size_t)(j - 1) * blk, blk * 8, cudaMemcpyDeviceToDevice, st));
+                    for (int ell = w->pos - S + 1; ell <= w->pos; ++ell) CK(prop_right(ctx, w, st, s, ell, w->Ucur, w->Utmp));
+                    CK(stab_right(w, st, s, w->Ucur, nullptr));
+                    CK(cudaMemcpyAsync(w->URs[s] + (size_t)j * blk, w->Ucur, blk * 8, cudaMemcpyDeviceToDevice, st));
+                    UR = w->URs[s] + (size_t)j * blk;
+                }
+                UL = w->ULs[s] + (size_t)j * blk;
+            } else {
+                const int M = ctx->p.M;
+                if (w->pos == M) {
+                    UL = w->ULs[s] + (size_t)j * blk;
+                } else {
+                    CK(cudaMemcpyAsync(w->Ucur, w->ULs[s] + (size_t)(j + 1) * blk, blk * 8, cudaMemcpyDeviceToDevice, st));
+                    for (int ell = w->pos + S; ell >= w->pos + 1; --ell) CK(prop_left(ctx, w, st, s, ell, w->Ucur, w->Utmp));
+                    CK(stab_left(w, st, s, w->Ucur, nullptr));
+                    CK(cudaMemcpyAsync(w->ULs[s] + (size_t)j * blk, w->Ucur, blk * 8, cudaMemcpyDeviceToDevice, st));
+                    UL = w->ULs[s] + (size_t)j * blk;
+                }
+                UR = w->URs[s] + (size_t)j * blk;
+            }
+            CK(form_G(ctx, w, st, s, UR, UL, nullptr));
+            if (f64) {
+                double* G = (double*)w->G + (size_t)s * N * w->ld;
+                CK(launch_drift<double>(st, G, (const double*)w->Gnew, w->ld, N, w->acc2));
+                CK(store_G<double>(w, st, s));
+            } else {
+                float* G = (float*)w->G + (size_t)s * N * w->ld;
+                CK(launch_drift<float>(st, G, (const float*)w->Gnew, w->ld, N, w->acc2));
+                CK(store_G<float>(w, st, s));
+            }
+        }
+        w->need_recompute = false;
+    }
+    if (rel_drift) {
+        CK(cudaStreamSynchronize(st));
+        for (int wi = 0; wi < (int)ctx->w.size(); ++wi) {
+            int r = read_dev_err(ctx, ctx->w[wi]);
+            if (r) return r;
+            double h[2];
+            CK(cudaMemcpy(h, ctx->w[wi]->acc2, 16, cudaMemcpyDeviceToHost));
+            rel_drift[wi] = h[1] > 0 ? sqrt(h[0] / h[1]) : 0.0;
+        }
+    }
+    return AFQMC_OK;
+}
+
+int afqmc_measure_energy(afqmc_ctx* ctx, double* energy, double* sign, void* stream) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (ctx->w.empty() || !energy) return AFQMC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->last = st;
+    for (auto* w : ctx->w) {
+        CK(cudaMemsetAsync(w->acc2, 0, 16, st));
+        if (ctx->p.precision == AFQMC_PREC_FP64) {
+            const double* G = (const double*)w->G;
+            CK(launch_energy<double>(st, G, G + (size_t)w->N * w->ld, w->ld, w->L, ctx->p.t, ctx->p.U, w->acc2));
+        } else {
+            const float* G = (const float*)w->G;
+            CK(launch_energy<float>(st, G, G + (size_t)w->N * w->ld, w->ld, w->L, ctx->p.t, ctx->p.U, w->acc2));
+        }
+    }
+    CK(cudaStreamSynchronize(st));
+    for (int wi = 0; wi < (int)ctx->w.size(); ++wi) {
+        Walker* w = ctx->w[wi];
+        int r = read_dev_err(ctx, w);
+        if (r) return r;
+        CK(cudaMemcpy(&energy[wi], w->acc2, 8, cudaMemcpyDeviceToHost));
+        if (sign) CK(cudaMemcpy(&sign[wi], w->sign, 8, cudaMemcpyDeviceToHost));
+    }
+    return AFQMC_OK;
+}
+
+int afqmc_get_G(afqmc_ctx* ctx, int walker, int spin, double* host_out) {
+    if (!ctx || walker < 0 || walker >= (int)ctx->w.size() || spin < 0 || spin > 1 || !host_out) return AFQMC_ERR_ARG;
+    Walker* w = ctx->w[walker];
+    CK(cudaStreamSynchronize(ctx->last));
+    const size_t es = esize(ctx);
+    std::vector<char> buf((size_t)w->N * w->ld * es);
+    CK(cudaMemcpy(buf.data(), (char*)w->G + (size_t)spin * w->N * w->ld * es, buf.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < w->N; ++i)
+        for (int j = 0; j < w->N; ++j) {
+            size_t o = (size_t)i * w->ld + j;
+            host_out[(size_t)i * w->N + j] = (es == 8) ? ((double*)buf.data())[o] : (double)((float*)buf.data())[o];
+        }
+    return read_dev_err(ctx, w);
+}
+
+int afqmc_set_G(afqmc_ctx* ctx, int walker, int spin, const double* host_in) {
+    if (!ctx || walker < 0 || walker >= (int)ctx->w.size() || spin < 0 || spin > 1 || !host_in) return AFQMC_ERR_ARG;
+    Walker* w = ctx->w[walker];
+    CK(cudaStreamSynchronize(ctx->last));
+    const size_t es = esize(ctx);
+    std::vector<char> buf((size_t)w->N * w->ld * es, 0);
+    for (int i = 0; i < w->N; ++i)
+        for (int j = 0; j < w->N; ++j) {
+            size_t o = (size_t)i * w->ld + j;
+            double v = host_in[(size_t)i * w->N + j];
+            if (es == 8) ((double*)buf.data())[o] = v;
+            else ((float*)buf.data())[o] = (float)v;
+        }
+    CK(cudaMemcpy((char*)w->G + (size_t)spin * w->N * w->ld * es, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+    return AFQMC_OK;
+}
+
+int afqmc_get_fields(afqmc_ctx* ctx, int walker, int8_t* host_out) {
+    if (!ctx || walker < 0 || walker >= (int)ctx->w.size() || !host_out) return AFQMC_ERR_ARG;
+    Walker* w = ctx->w[walker];
+    CK(cudaStreamSynchronize(ctx->last));
+    CK(cudaMemcpy(host_out, w->x, (size_t)ctx->p.M * w->N, cudaMemcpyDeviceToHost));
+    return AFQMC_OK;
+}
+
+int afqmc_get_decisions(afqmc_ctx* ctx, int walker, uint8_t* host_out) {
+    if (!ctx || walker < 0 || walker >= (int)ctx->w.size() || !host_out) return AFQMC_ERR_ARG;
+    Walker* w = ctx->w[walker];
+    CK(cudaStreamSynchronize(ctx->last));
+    CK(cudaMemcpy(host_out, w->dec, 2 * (size_t)w->N, cudaMemcpyDeviceToHost));
+    return AFQMC_OK;
+}
+
+int afqmc_get_ratios(afqmc_ctx* ctx, int walker, double* host_out) {
+    if (!ctx || walker < 0 || walker >= (int)ctx->w.size() || !host_out) return AFQMC_ERR_ARG;
+    Walker* w = ctx->w[walker];
+    CK(cudaStreamSynchronize(ctx->last));
+    CK(cudaMemcpy(host_out, w->ratio, 2 * (size_t)w->N * 8, cudaMemcpyDeviceToHost));
+    return AFQMC_OK;
+}
+
+int afqmc_get_info(afqmc_ctx* ctx, int walker, int* N, int* n_up, int* n_dn, int* slice, int* dir) {
+    if (!ctx || walker < 0 || walker >= (int)ctx->w.size()) return AFQMC_ERR_ARG;
+    Walker* w = ctx->w[walker];
+    if (N) *N = w->N;
+    if (n_up) *n_up = w->ns[0];
+    if (n_dn) *n_dn = w->ns[1];
+    if (slice) *slice = w->pos;
+    if (dir) *dir = w->last_dir;
+    return AFQMC_OK;
+}
+
+int afqmc_debug_uniforms(uint64_t seed, uint64_t walker, uint64_t visit, int count, double* host_out) {
+    if (count < 0 || (count > 0 && !host_out)) return AFQMC_ERR_ARG;
+    if (count == 0) return AFQMC_OK;
+    double* d = nullptr;
+    if (cudaMalloc(&d, (size_t)count * 8) != cudaSuccess) return AFQMC_ERR_OOM;
+    debug_uniforms_kernel<<<(count + 255) / 256, 256>>>(seed, walker, visit, count, d);
+    cudaError_t e = cudaMemcpy(host_out, d, (size_t)count * 8, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? AFQMC_OK : AFQMC_ERR_CUDA;
+}
+
+}  // extern "C"

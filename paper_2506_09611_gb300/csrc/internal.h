@@ -1,0 +1,110 @@
+// internal.h -- host-side declarations shared by the libafqmc translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace afq {
+
+// Row-major batched GEMM with diagonal scalings (all pointers device):
+//   C[z] = alpha * diag(rs[z]) * A[z] * diag(bs[z]) * B[z] * diag(cs[z]) + beta * C[z]
+// A is M x K (lda), B is K x N (ldb), C is M x N (ldc).  Null scale pointers
+// mean 1.  If Kdev is non-null the inner dimension is read from *Kdev on the
+// device (<= K).  beta == 0 never reads C.
+template <typename T>
+struct GemmArgs {
+    int M = 0, N = 0, K = 0;
+    const int* Kdev = nullptr;
+    const T* A = nullptr; long lda = 0, sA = 0;
+    const T* B = nullptr; long ldb = 0, sB = 0;
+    T* C = nullptr; long ldc = 0, sC = 0;
+    T alpha = 1, beta = 0;
+    const T* rs = nullptr; long srs = 0;
+    const T* cs = nullptr; long scs = 0;
+    const T* bs = nullptr; long sbs = 0;
+    int batch = 1;
+};
+
+template <typename T>
+cudaError_t gemm(cudaStream_t st, const GemmArgs<T>& g);
+
+// ---- setup / recompute kernels (setup.cu) ----
+cudaError_t launch_expK(cudaStream_t st, int L, double t, double tau, double* E, long ld);
+template <typename T>
+cudaError_t launch_cast(cudaStream_t st, const double* src, long lds, T* dst, long ldd, int rows, int cols);
+template <typename T>
+cudaError_t launch_to_double(cudaStream_t st, const T* src, long lds, double* dst, long ldd, int rows, int cols);
+cudaError_t launch_field_scales(cudaStream_t st, const int8_t* x, int N, double c, double* d, double* dinv);
+template <typename T>
+cudaError_t launch_field_scales_T(cudaStream_t st, const int8_t* x, int N, const double* c2, T* d, T* dinv, long sd);
+
+struct ElimScratch;  // defined in setup.cu
+// Pivoted elimination on the device (persistent cooperative kernel).
+//   mode 0 (tall LU re-orthonormalisation): A is R x C (element (r,c) at A[r*rs + c*cs]),
+//          R >= C; on return A holds L' with A_in = L' U, U upper triangular (the basis of
+//          the column space used as the new factor).  *sign_out *= sign(det U).
+//   mode 1 (Gauss-Jordan solve): A is R x (R + nrhs) row-major (ld = rs), left block square;
+//          on return rows hold the reduced system; `perm` gets the pivot row of each column;
+//          *sign_out *= sign(det of the left block).
+cudaError_t launch_elim(cudaStream_t st, int mode, double* A, int R, int C, long rs, long cs, int nrhs,
+                        int* perm, double* sign_out, void* scratch, int* err);
+size_t elim_scratch_bytes(int R);
+// Z[j, :] = A[perm[j], R:] / A[perm[j], j] for the Gauss-Jordan result.
+cudaError_t launch_gj_extract(cudaStream_t st, const double* A, long ld, int R, int nrhs, const int* perm,
+                              double* Z, long ldz);
+template <typename T>
+cudaError_t launch_identity_minus(cudaStream_t st, T* G, long ld, int N);  // G = I - G
+template <typename T>
+cudaError_t launch_drift(cudaStream_t st, const T* Gold, const T* Gnew, long ld, int N, double* acc2);
+template <typename T>
+cudaError_t launch_energy(cudaStream_t st, const T* Gu, const T* Gd, long ld, int L, double t, double U,
+                          double* out);
+
+// ---- sweep kernels (sweep.cu) ----
+struct SiteParams {
+    int N;
+    long ld;
+    double c[2];     // c_up, c_dn
+    double lam;      // HS coupling (for the scalar prior of the charge channel)
+    int hs;
+    uint64_t seed, walker, visit;
+};
+
+struct SliceOut {      // device-side per-walker outputs of one slice
+    uint8_t* dec;      // 2N replay-layout decisions
+    double* ratio;     // 2N ratios
+    int* stats;        // [proposals, accepts, flipped, flushes]
+    double* maxr;      // max |R|
+    double* sign;      // walker sign (updated in place)
+};
+
+cudaError_t launch_uniforms(cudaStream_t st, uint64_t seed, uint64_t walker, uint64_t visit, int count, double* u);
+
+template <typename T>
+cudaError_t launch_local(cudaStream_t st, T* Gu, T* Gd, int8_t* xl, const double* u, const uint8_t* replay,
+                         const SiteParams& sp, SliceOut so, T* colbuf, T* rowbuf, GridBar* bar, int* err,
+                         int max_blocks);
+
+struct WindowBufs {    // device scratch of the window chain + flush
+    int* m;            // accepted count of the window
+    int* idx;          // accepted site indices (global), capacity NW
+    double* dtot;      // per spin: total Delta of each accepted site, 2 x NW
+    void* Wm;          // per spin m x m (T), 2 x NW x NW
+    void* X;           // per spin N x NW panel G[:, I] (T)
+    void* Y;           // per spin NW x N panel Wm (E_I^T - G[I, :]) (T)
+};
+
+template <typename T>
+int window_max();      // largest window (sites) the chain kernel holds in shared memory
+
+template <typename T>
+cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T* Gd, int8_t* xl, const double* u,
+                                const uint8_t* replay, const SiteParams& sp, SliceOut so, int s0, int n, int nb,
+                                WindowBufs wb, int* err);
+template <typename T>
+cudaError_t launch_flush(cudaStream_t st, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw);
+
+}  // namespace afq

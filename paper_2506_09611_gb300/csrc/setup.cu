@@ -1,0 +1,323 @@
+// setup.cu -- model matrices, FP64 re-orthonormalisation / solve, measurements.
+//
+//   exp(-tau K) for the periodic square lattice (Eq. 2DHubbard): the dispersion
+//   eps_k = -2t(cos kx + cos ky) separates, so E = Ex (x) Ey with
+//   Ex_{x,x'} = L^{-1} sum_k exp(2 tau t cos k) cos(k (x - x')).
+//   Pivoted elimination (Sec. II.B, Eq. GrFMatNew): the stabilisation that
+//   keeps U_R / U_L well conditioned, and the solve (U_L U_R) Z = U_L.
+#include <math.h>
+
+#include "internal.h"
+
+namespace afq {
+
+// ---------------------------------------------------------------------------
+// exp(-tau K)
+// ---------------------------------------------------------------------------
+__global__ void expK_kernel(int L, double t, double tau, double* E, long ld) {
+    extern __shared__ double f1[];  // 1D factor by displacement
+    for (int d = threadIdx.x; d < L; d += blockDim.x) {
+        double acc = 0.0;
+        for (int q = 0; q < L; ++q) {
+            double k = 2.0 * M_PI * q / L;
+            acc += exp(2.0 * tau * t * cos(k)) * cos(k * d);
+        }
+        f1[d] = acc / L;
+    }
+    __syncthreads();
+    const int N = L * L;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)N * N; e += (long)gridDim.x * blockDim.x) {
+        int i = (int)(e / N), j = (int)(e % N);
+        int dx = ((i % L) - (j % L) + L) % L, dy = ((i / L) - (j / L) + L) % L;
+        E[(long)i * ld + j] = f1[dx] * f1[dy];
+    }
+}
+
+cudaError_t launch_expK(cudaStream_t st, int L, double t, double tau, double* E, long ld) {
+    expK_kernel<<<256, 256, L * sizeof(double), st>>>(L, t, tau, E, ld);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void cast_kernel(const double* src, long lds, T* dst, long ldd, int rows, int cols) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)rows * cols; e += (long)gridDim.x * blockDim.x) {
+        int r = (int)(e / cols), c = (int)(e % cols);
+        dst[(long)r * ldd + c] = (T)src[(long)r * lds + c];
+    }
+}
+template <typename T>
+cudaError_t launch_cast(cudaStream_t st, const double* src, long lds, T* dst, long ldd, int rows, int cols) {
+    cast_kernel<T><<<512, 256, 0, st>>>(src, lds, dst, ldd, rows, cols);
+    return cudaGetLastError();
+}
+template cudaError_t launch_cast<float>(cudaStream_t, const double*, long, float*, long, int, int);
+template cudaError_t launch_cast<double>(cudaStream_t, const double*, long, double*, long, int, int);
+
+template <typename T>
+__global__ void to_double_kernel(const T* src, long lds, double* dst, long ldd, int rows, int cols) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)rows * cols; e += (long)gridDim.x * blockDim.x) {
+        int r = (int)(e / cols), c = (int)(e % cols);
+        dst[(long)r * ldd + c] = (double)src[(long)r * lds + c];
+    }
+}
+template <typename T>
+cudaError_t launch_to_double(cudaStream_t st, const T* src, long lds, double* dst, long ldd, int rows, int cols) {
+    to_double_kernel<T><<<512, 256, 0, st>>>(src, lds, dst, ldd, rows, cols);
+    return cudaGetLastError();
+}
+template cudaError_t launch_to_double<float>(cudaStream_t, const float*, long, double*, long, int, int);
+template cudaError_t launch_to_double<double>(cudaStream_t, const double*, long, double*, long, int, int);
+
+// d_i = exp(c x_i), dinv_i = exp(-c x_i) for both spins; c2 = {c_up, c_dn}; outputs [2][N] with stride sd
+template <typename T>
+__global__ void field_scales_kernel(const int8_t* x, int N, double c0, double c1, T* d, T* dinv, long sd) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double xv = (double)x[i];
+    d[i] = (T)exp(c0 * xv);
+    dinv[i] = (T)exp(-c0 * xv);
+    d[sd + i] = (T)exp(c1 * xv);
+    dinv[sd + i] = (T)exp(-c1 * xv);
+}
+template <typename T>
+cudaError_t launch_field_scales_T(cudaStream_t st, const int8_t* x, int N, const double* c2, T* d, T* dinv, long sd) {
+    field_scales_kernel<T><<<(N + 255) / 256, 256, 0, st>>>(x, N, c2[0], c2[1], d, dinv, sd);
+    return cudaGetLastError();
+}
+template cudaError_t launch_field_scales_T<float>(cudaStream_t, const int8_t*, int, const double*, float*, float*, long);
+template cudaError_t launch_field_scales_T<double>(cudaStream_t, const int8_t*, int, const double*, double*, double*, long);
+
+// ---------------------------------------------------------------------------
+// pivoted elimination, persistent cooperative kernel (FP64)
+// ---------------------------------------------------------------------------
+struct Cand {
+    double v;
+    int r;
+    int pad;
+};
+
+struct ElimScratch {
+    GridBar bar;
+    int pad[2];
+    // followed by Cand cand[nblk], int8 piv_flag[R], int visited[R]
+};
+
+size_t elim_scratch_bytes(int R) {
+    return sizeof(ElimScratch) + 2048 * sizeof(Cand) + (size_t)R + (size_t)R * sizeof(int) + 64;
+}
+
+__device__ __forceinline__ void better(double& bv, int& br, double v, int r) {
+    if (v > bv || (v == bv && r < br)) { bv = v; br = r; }
+}
+
+// mode 0: tall LU on A (R x C, element (r,c) at A[r*rs + c*cs]), eliminate only non-pivoted rows.
+// mode 1: Gauss-Jordan on A (R x (R+nrhs), row-major ld = rs), eliminate every other row.
+__global__ void __launch_bounds__(256) elim_kernel(int mode, double* A, int R, int C, long rs, long cs, int nrhs,
+                                                   int* perm, double* sign_out, unsigned char* scratch, int* err) {
+    ElimScratch* sc = (ElimScratch*)scratch;
+    Cand* cand = (Cand*)(scratch + sizeof(ElimScratch));
+    int8_t* pflag = (int8_t*)(cand + 2048);  // cand is double-buffered by step parity
+    int* visited = (int*)(((uintptr_t)(pflag + R) + 15) & ~(uintptr_t)15);
+    const int nblk = gridDim.x, b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int r0 = (int)((long)R * b / nblk), r1 = (int)((long)R * (b + 1) / nblk);
+    const int ncols = (mode == 0) ? C : R + nrhs;
+    const int nsteps = (mode == 0) ? C : R;
+    __shared__ double s_l[64];
+    __shared__ double s_bv[8];
+    __shared__ int s_br[8];
+    __shared__ int s_p;
+    __shared__ double s_pv;
+    // row-local pivot flags
+    for (int r = r0 + tid; r < r1; r += nt) pflag[r] = 0;
+    auto elem = [&](int r, int c) -> double& {
+        return (mode == 0) ? A[(long)r * rs + (long)c * cs] : A[(long)r * rs + c];
+    };
+    auto block_candidate = [&](int j) {
+        double bv = -1.0;
+        int br = 0x7fffffff;
+        for (int r = r0 + tid; r < r1; r += nt)
+            if (!pflag[r]) better(bv, br, fabs(elem(r, j)), r);
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_down_sync(0xffffffffu, bv, o);
+            int orr = __shfl_down_sync(0xffffffffu, br, o);
+            better(bv, br, ov, orr);
+        }
+        if ((tid & 31) == 0) { s_bv[tid >> 5] = bv; s_br[tid >> 5] = br; }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < nt / 32; ++w) better(bv, br, s_bv[w], s_br[w]);
+            cand[(j & 1) * 1024 + b].v = bv;
+            cand[(j & 1) * 1024 + b].r = br;
+        }
+    };
+    block_candidate(0);
+    if (!grid_barrier(&sc->bar, nblk, err)) return;
+    double sgn = 1.0;
+    for (int j = 0; j < nsteps; ++j) {
+        if (tid == 0) {
+            double bv = -1.0;
+            int br = 0x7fffffff;
+            for (int q = 0; q < nblk; ++q) better(bv, br, cand[(j & 1) * 1024 + q].v, cand[(j & 1) * 1024 + q].r);
+            if (!(bv > 0.0) || br >= R) {
+                set_err(err, DEV_NUMERIC);
+                br = 0;
+            }
+            s_p = br;
+            s_pv = elem(br, j);
+        }
+        __syncthreads();
+        const int p = s_p;
+        const double pv = s_pv;
+        if (read_err(err) != 0) return;
+        if (b == 0 && tid == 0) {
+            perm[j] = p;
+            if (pv < 0) sgn = -sgn;
+        }
+        if (p >= r0 && p < r1 && tid == 0) pflag[p] = 1;
+        __syncthreads();
+        // multipliers of the own rows
+        const int nr = r1 - r0;
+        for (int q = tid; q < nr; q += nt) {
+            int r = r0 + q;
+            bool act = (mode == 0) ? !pflag[r] : (r != p);
+            s_l[q] = act ? elem(r, j) / pv : 0.0;
+        }
+        __syncthreads();
+        const int w = ncols - j - 1;
+        for (long e = tid; e < (long)nr * w; e += nt) {
+            int q = (int)(e / w), c = j + 1 + (int)(e % w);
+            int r = r0 + q;
+            double l = s_l[q];
+            if (l != 0.0) elem(r, c) -= l * elem(p, c);
+        }
+        for (int q = tid; q < nr; q += nt) {
+            int r = r0 + q;
+            bool act = (mode == 0) ? !pflag[r] : (r != p);
+            if (act) elem(r, j) = (mode == 0) ? s_l[q] : 0.0;
+        }
+        __syncthreads();
+        if (j + 1 < nsteps) block_candidate(j + 1);
+        if (!grid_barrier(&sc->bar, nblk, err)) return;
+    }
+    if (mode == 0) {
+        // pivot rows of L': 1 on the diagonal position, 0 to its right
+        for (long e = (long)b * nt + tid; e < (long)nsteps * C; e += (long)nblk * nt) {
+            int j = (int)(e / C), c = (int)(e % C);
+            if (c >= j) elem(perm[j], c) = (c == j) ? 1.0 : 0.0;
+        }
+    } else if (b == 0 && tid == 0) {
+        // parity of the row permutation j -> perm[j]
+        for (int r = 0; r < R; ++r) visited[r] = 0;
+        for (int r = 0; r < R; ++r) {
+            if (visited[r]) continue;
+            int len = 0, q = r;
+            while (!visited[q]) { visited[q] = 1; q = perm[q]; ++len; }
+            if ((len & 1) == 0) sgn = -sgn;
+        }
+    }
+    if (b == 0 && tid == 0 && sign_out) *sign_out *= sgn;
+}
+
+cudaError_t launch_elim(cudaStream_t st, int mode, double* A, int R, int C, long rs, long cs, int nrhs, int* perm,
+                        double* sign_out, void* scratch, int* err) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int nblk = nsm < 1024 ? nsm : 1024;
+    if (nblk > R) nblk = R;
+    // rows per block must fit the multiplier cache
+    while ((R + nblk - 1) / nblk > 64) ++nblk;
+    if (nblk > nsm) return cudaErrorInvalidValue;
+    unsigned char* sc = (unsigned char*)scratch;
+    cudaError_t e = cudaMemsetAsync(sc, 0, sizeof(ElimScratch), st);
+    if (e != cudaSuccess) return e;
+    void* args[] = {&mode, &A, &R, &C, &rs, &cs, &nrhs, &perm, &sign_out, &sc, &err};
+    return cudaLaunchCooperativeKernel((void*)elim_kernel, dim3(nblk), dim3(256), args, 0, st);
+}
+
+__global__ void gj_extract_kernel(const double* A, long ld, int R, int nrhs, const int* perm, double* Z, long ldz) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)R * nrhs; e += (long)gridDim.x * blockDim.x) {
+        int j = (int)(e / nrhs), c = (int)(e % nrhs);
+        int p = perm[j];
+        Z[(long)j * ldz + c] = A[(long)p * ld + R + c] / A[(long)p * ld + j];
+    }
+}
+cudaError_t launch_gj_extract(cudaStream_t st, const double* A, long ld, int R, int nrhs, const int* perm, double* Z,
+                              long ldz) {
+    gj_extract_kernel<<<512, 256, 0, st>>>(A, ld, R, nrhs, perm, Z, ldz);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void identity_minus_kernel(T* G, long ld, int N) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)N * N; e += (long)gridDim.x * blockDim.x) {
+        int i = (int)(e / N), j = (int)(e % N);
+        G[(long)i * ld + j] = (i == j ? T(1) : T(0)) - G[(long)i * ld + j];
+    }
+}
+template <typename T>
+cudaError_t launch_identity_minus(cudaStream_t st, T* G, long ld, int N) {
+    identity_minus_kernel<T><<<512, 256, 0, st>>>(G, ld, N);
+    return cudaGetLastError();
+}
+template cudaError_t launch_identity_minus<float>(cudaStream_t, float*, long, int);
+template cudaError_t launch_identity_minus<double>(cudaStream_t, double*, long, int);
+
+// acc2[0] += sum (Gold - Gnew)^2, acc2[1] += sum Gnew^2; Gnew is FP64 with the same ld
+template <typename T>
+__global__ void drift_kernel(const T* Gold, const double* Gnew, long ld, int N, double* acc2) {
+    double a = 0.0, bsum = 0.0;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)N * N; e += (long)gridDim.x * blockDim.x) {
+        int i = (int)(e / N), j = (int)(e % N);
+        double gn = Gnew[(long)i * ld + j];
+        double d = (double)Gold[(long)i * ld + j] - gn;
+        a += d * d;
+        bsum += gn * gn;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        bsum += __shfl_down_sync(0xffffffffu, bsum, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(acc2, a);
+        atomicAdd(acc2 + 1, bsum);
+    }
+}
+template <typename T>
+cudaError_t launch_drift(cudaStream_t st, const T* Gold, const T* Gnew, long ld, int N, double* acc2) {
+    drift_kernel<T><<<256, 256, 0, st>>>(Gold, (const double*)Gnew, ld, N, acc2);
+    return cudaGetLastError();
+}
+template cudaError_t launch_drift<float>(cudaStream_t, const float*, const float*, long, int, double*);
+template cudaError_t launch_drift<double>(cudaStream_t, const double*, const double*, long, int, double*);
+
+// E = sum_s tr(K A^s) + U sum_i (n_up n_dn - (n_up + n_dn)/2), A = 1 - G, K_ij = -t per bond
+template <typename T>
+__global__ void energy_kernel(const T* Gu, const T* Gd, long ld, int L, double t, double U, double* out) {
+    const int N = L * L;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        int x = i % L, y = i / L;
+        int nbr[4] = {((x + 1) % L) + L * y, ((x - 1 + L) % L) + L * y, x + L * ((y + 1) % L), x + L * ((y - 1 + L) % L)};
+        for (int q = 0; q < 4; ++q) {
+            int j = nbr[q];
+            double aju = (j == i ? 1.0 : 0.0) - (double)Gu[(long)j * ld + i];
+            double ajd = (j == i ? 1.0 : 0.0) - (double)Gd[(long)j * ld + i];
+            acc += -t * (aju + ajd);
+        }
+        double nu = 1.0 - (double)Gu[(long)i * ld + i], nd = 1.0 - (double)Gd[(long)i * ld + i];
+        acc += U * (nu * nd - 0.5 * (nu + nd));
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+template <typename T>
+cudaError_t launch_energy(cudaStream_t st, const T* Gu, const T* Gd, long ld, int L, double t, double U, double* out) {
+    energy_kernel<T><<<64, 256, 0, st>>>(Gu, Gd, ld, L, t, U, out);
+    return cudaGetLastError();
+}
+template cudaError_t launch_energy<float>(cudaStream_t, const float*, const float*, long, int, double, double, double*);
+template cudaError_t launch_energy<double>(cudaStream_t, const double*, const double*, long, int, double, double,
+                                           double*);
+
+}  // namespace afq

@@ -1,0 +1,582 @@
+// sweep.cu -- the per-slice site loop of the PQMC update sweep in G form.
+//
+//   local   : persistent cooperative kernel, one grid barrier per site, the
+//             rank-1 update G <- G - (d/r) G_{:,i} (e_i^T - G_{i,:}) applied to
+//             the whole of G on every accepted flip (Eqs. DetRatiolocal,
+//             UpdateLTRlocal restated for G).
+//   delayed : a window of n consecutive sites is decided by ONE CTA on the
+//   blockfb   n x n diagonal block of G held in shared memory; the accepted
+//             flips I are then applied to the full G as one rank-|I| product
+//                 G <- G - G[:, I] W (E_I^T - G[I, :]),  W = D_I (1 + A0_II D_I)^{-1}
+//             which equals the buffered sum of the paper's delayed vectors
+//             (Eqs. DelayTMat00, DelayRgenk, FinalDelay) and the block
+//             force-bias upgrade (Eq. BlkFrcBsTnew2).
+#include <math.h>
+
+#include "internal.h"
+
+namespace afq {
+
+// ---------------------------------------------------------------------------
+// uniforms of one slice visit
+// ---------------------------------------------------------------------------
+__global__ void uniforms_kernel(uint64_t seed, uint64_t walker, uint64_t visit, int count, double* u) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < count) u[j] = philox_uniform(seed, walker, visit, (uint64_t)j);
+}
+
+cudaError_t launch_uniforms(cudaStream_t st, uint64_t seed, uint64_t walker, uint64_t visit, int count,
+                            double* u) {
+    uniforms_kernel<<<(count + 255) / 256, 256, 0, st>>>(seed, walker, visit, count, u);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ double hs_log_scalar(const SiteParams& sp, int x) {
+    return sp.hs == AFQMC_HS_CHARGE_REAL ? -sp.lam * (double)x : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// local update: persistent cooperative kernel
+// ---------------------------------------------------------------------------
+// colbuf / rowbuf: [2 buffers][2 spins][N] snapshots of column i / row i of
+// the current G, written by the owners of the rows during the previous site
+// and read by every CTA after the grid barrier.
+template <typename T>
+__global__ void __launch_bounds__(512) local_kernel(T* Gu, T* Gd, int8_t* xl_g, const double* u,
+                                                    const uint8_t* replay, SiteParams sp, SliceOut so,
+                                                    T* colbuf, T* rowbuf, GridBar* bar, int* err) {
+    extern __shared__ unsigned char smem_raw[];
+    int8_t* xs = (int8_t*)smem_raw;
+    const int N = sp.N;
+    const long ld = sp.ld;
+    const int nblk = gridDim.x, b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int r0 = (int)((long)N * b / nblk), r1 = (int)((long)N * (b + 1) / nblk);
+    const int nrows = r1 - r0;
+    T* G[2] = {Gu, Gd};
+    for (int i = tid; i < N; i += nt) xs[i] = xl_g[i];
+    // snapshot of column 0 and row 0
+    for (int e = tid; e < 2 * nrows; e += nt) {
+        int s = e / nrows, r = r0 + e % nrows;
+        colbuf[(0 * 2 + s) * N + r] = G[s][(long)r * ld + 0];
+    }
+    if (r0 == 0 && nrows > 0)
+        for (int e = tid; e < 2 * N; e += nt) {
+            int s = e / N, c = e % N;
+            rowbuf[(0 * 2 + s) * N + c] = G[s][c];
+        }
+    if (!grid_barrier(bar, nblk, err)) return;
+
+    double sign = so.sign ? *so.sign : 1.0;
+    int n_acc = 0;
+    double maxr = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const int cur = i & 1, nxt = cur ^ 1;
+        const T* col0 = colbuf + (cur * 2 + 0) * N;
+        const T* col1 = colbuf + (cur * 2 + 1) * N;
+        const T* row0 = rowbuf + (cur * 2 + 0) * N;
+        const T* row1 = rowbuf + (cur * 2 + 1) * N;
+        const int x = xs[i], xp = -x;
+        double R = exp(hs_log_scalar(sp, xp) - hs_log_scalar(sp, x));
+        double d0 = field_delta(sp.c[0], x, xp), d1 = field_delta(sp.c[1], x, xp);
+        double rr0 = 1.0 + d0 * (1.0 - (double)col0[i]);
+        double rr1 = 1.0 + d1 * (1.0 - (double)col1[i]);
+        R *= rr0 * rr1;
+        bool acc = replay ? (replay[i] != 0) : (u[i] < fabs(R));
+        if (!isfinite(R)) {
+            if (b == 0 && tid == 0) set_err(err, DEV_NUMERIC);
+            acc = false;
+        }
+        if (b == 0 && tid == 0) {
+            so.dec[i] = acc ? 1 : 0;
+            so.ratio[i] = R;
+            if (acc) {
+                xl_g[i] = (int8_t)xp;
+                if (R < 0) sign = -sign;
+            }
+        }
+        if (acc) {
+            ++n_acc;
+            maxr = fmax(maxr, fabs(R));
+            const T f0 = (T)(d0 / rr0), f1 = (T)(d1 / rr1);
+            const int tot = 2 * nrows * N;
+            for (int e = tid; e < tot; e += nt) {
+                const int s = e / (nrows * N);
+                const int rem = e - s * nrows * N;
+                const int r = r0 + rem / N, c = rem % N;
+                const T* cl = s ? col1 : col0;
+                const T* rw = s ? row1 : row0;
+                const T f = s ? f1 : f0;
+                const T rowv = (c == i ? T(1) : T(0)) - rw[c];
+                T* gp = G[s] + (long)r * ld + c;
+                const T nv = *gp - f * cl[r] * rowv;
+                *gp = nv;
+                if (c == i + 1) colbuf[(nxt * 2 + s) * N + r] = nv;
+                if (r == i + 1) rowbuf[(nxt * 2 + s) * N + c] = nv;
+            }
+        } else if (i + 1 < N) {
+            for (int e = tid; e < 2 * nrows; e += nt) {
+                int s = e / nrows, r = r0 + e % nrows;
+                colbuf[(nxt * 2 + s) * N + r] = G[s][(long)r * ld + (i + 1)];
+            }
+            if (i + 1 >= r0 && i + 1 < r1)
+                for (int e = tid; e < 2 * N; e += nt) {
+                    int s = e / N, c = e % N;
+                    rowbuf[(nxt * 2 + s) * N + c] = G[s][(long)(i + 1) * ld + c];
+                }
+        }
+        if (!grid_barrier(bar, nblk, err)) return;
+    }
+    if (b == 0 && tid == 0) {
+        if (so.sign) *so.sign = sign;
+        so.stats[0] += N;
+        so.stats[1] += n_acc;
+        so.stats[2] += n_acc;
+        *so.maxr = fmax(*so.maxr, maxr);
+    }
+}
+
+template <typename T>
+cudaError_t launch_local(cudaStream_t st, T* Gu, T* Gd, int8_t* xl, const double* u, const uint8_t* replay,
+                         const SiteParams& sp, SliceOut so, T* colbuf, T* rowbuf, GridBar* bar, int* err,
+                         int max_blocks) {
+    int nblk = max_blocks < sp.N ? max_blocks : sp.N;
+    size_t shm = (size_t)sp.N;
+    SiteParams spc = sp;
+    void* args[] = {&Gu, &Gd, &xl, &u, &replay, &spc, &so, &colbuf, &rowbuf, &bar, &err};
+    return cudaLaunchCooperativeKernel((void*)local_kernel<T>, dim3(nblk), dim3(512), args, shm, st);
+}
+
+// ---------------------------------------------------------------------------
+// window chain: delayed (MODE 1) and block force-bias (MODE 2)
+// ---------------------------------------------------------------------------
+template <typename T> struct WinCap;
+template <> struct WinCap<float> { static constexpr int NW = 128; };
+template <> struct WinCap<double> { static constexpr int NW = 64; };
+constexpr int NBMAX = 32;
+constexpr int WIN_THREADS = 1024;
+
+template <typename T>
+int window_max() { return WinCap<T>::NW; }
+template int window_max<float>();
+template int window_max<double>();
+
+template <typename T>
+static size_t window_smem(int n) {
+    size_t P = (size_t)n + 1;
+    size_t g = 2 * (size_t)n * P * sizeof(T);                // Gs[2][n][n+1]
+    size_t aug = (size_t)n * (2 * (size_t)n + 1) * sizeof(T);  // Gauss-Jordan [M | I] for one spin
+    if (aug > g) g = aug;
+    size_t s1 = 2 * (size_t)NBMAX * (NBMAX + 1) * sizeof(T);
+    size_t vec = 4 * (size_t)n * sizeof(T) + 2 * (size_t)NBMAX * sizeof(T);  // staging vectors
+    size_t misc = (size_t)n * (sizeof(int) + 2 * sizeof(double) + 1) + 8 * (size_t)NBMAX * sizeof(double) + 256;
+    return g + s1 + vec + misc;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict__ Gu, const T* __restrict__ Gd,
+                                                             int8_t* xl_g, const double* u,
+                                                             const uint8_t* replay, SiteParams sp, SliceOut so,
+                                                             int s0, int n, int nb, WindowBufs wb, int* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int P = n + 1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int N = sp.N;
+    const long ld = sp.ld;
+    T* Gs = (T*)smem_raw;  // [2][n][P]
+    size_t off = 2 * (size_t)n * P * sizeof(T);
+    size_t aug = (size_t)n * (2 * (size_t)n + 1) * sizeof(T);
+    if (aug > off) off = aug;
+    T* S1 = (T*)(smem_raw + off);  // [2][NBMAX][NBMAX+1]
+    off += 2 * (size_t)NBMAX * (NBMAX + 1) * sizeof(T);
+    T* stc = (T*)(smem_raw + off);  // staging: col[2][n], row[2][n]
+    off += 4 * (size_t)n * sizeof(T);
+    T* stb = (T*)(smem_raw + off);  // small staging [2][NBMAX]
+    off += 2 * (size_t)NBMAX * sizeof(T);
+    double* dl = (double*)(smem_raw + ((off + 7) & ~(size_t)7));  // [2][n]
+    off = ((off + 7) & ~(size_t)7) + 2 * (size_t)n * sizeof(double);
+    double* fb = (double*)(smem_raw + off);  // block-FB scalars [8][NBMAX]
+    off += 8 * (size_t)NBMAX * sizeof(double);
+    int* idx = (int*)(smem_raw + off);  // accepted positions [n]
+    off += (size_t)n * sizeof(int);
+    int8_t* xw = (int8_t*)(smem_raw + off);  // window fields [n]
+    off += (size_t)n;
+    __shared__ int s_m, s_piv, s_nF;
+    __shared__ int s_F[NBMAX];
+    __shared__ double s_R;
+
+    const T* G[2] = {Gu, Gd};
+    for (int e = tid; e < 2 * n * n; e += nt) {
+        int s = e / (n * n), rem = e % (n * n), a = rem / n, c = rem % n;
+        Gs[(s * n + a) * P + c] = G[s][(long)(s0 + a) * ld + (s0 + c)];
+    }
+    for (int p = tid; p < n; p += nt) xw[p] = xl_g[s0 + p];
+    if (tid == 0) s_m = 0;
+    __syncthreads();
+
+    double sign = so.sign ? *so.sign : 1.0;
+    int n_prop = 0, n_acc = 0, n_flip = 0;
+    double maxr = 0.0;
+
+    if (MODE == AFQMC_MODE_DELAYED) {
+        for (int p = 0; p < n; ++p) {
+            const int i = s0 + p;
+            const int x = xw[p], xp = -x;
+            double R = exp(hs_log_scalar(sp, xp) - hs_log_scalar(sp, x));
+            const double d0 = field_delta(sp.c[0], x, xp), d1 = field_delta(sp.c[1], x, xp);
+            const double r0 = 1.0 + d0 * (1.0 - (double)Gs[(0 * n + p) * P + p]);
+            const double r1 = 1.0 + d1 * (1.0 - (double)Gs[(1 * n + p) * P + p]);
+            R *= r0 * r1;
+            bool acc = replay ? (replay[i] != 0) : (u[i] < fabs(R));
+            if (!isfinite(R)) acc = false;
+            ++n_prop;
+            if (tid == 0) {
+                so.dec[i] = acc ? 1 : 0;
+                so.ratio[i] = R;
+                if (!isfinite(R)) set_err(err, DEV_NUMERIC);
+            }
+            if (!acc) continue;
+            // trailing update of the block: G[a][b] += (d/r) G[a][p] G[p][b], a, b > p
+            const T f0 = (T)(d0 / r0), f1 = (T)(d1 / r1);
+            const int q = n - p - 1;
+            for (int e = tid; e < 2 * q * q; e += nt) {
+                int s = e / (q * q), rem = e % (q * q);
+                int a = p + 1 + rem / q, c = p + 1 + rem % q;
+                T* Gb = Gs + s * n * P;
+                Gb[a * P + c] += (s ? f1 : f0) * Gb[a * P + p] * Gb[p * P + c];
+            }
+            if (tid == 0) {
+                idx[s_m] = p;
+                dl[0 * n + s_m] = d0;
+                dl[1 * n + s_m] = d1;
+                s_m = s_m + 1;
+                if (R < 0) sign = -sign;
+            }
+            ++n_acc;
+            ++n_flip;
+            maxr = fmax(maxr, fabs(R));
+            __syncthreads();
+        }
+    } else {
+        // ---- block force-bias (Sec. III.B) ----
+        T* stcol = stc;          // [2][n]
+        T* strow = stc + 2 * n;  // [2][n]
+        for (int p0 = 0; p0 < n; p0 += nb) {
+            const int nbk = min(nb, n - p0);
+            const int blk = (s0 + p0) / nb;
+            // (a) stripped force bias: remove the block's fields one site at a time
+            for (int e = tid; e < 2 * nbk * nbk; e += nt) {
+                int s = e / (nbk * nbk), rem = e % (nbk * nbk), a = rem / nbk, c = rem % nbk;
+                S1[(s * NBMAX + a) * (NBMAX + 1) + c] = Gs[(s * n + p0 + a) * P + p0 + c];
+            }
+            __syncthreads();
+            for (int a = 0; a < nbk; ++a) {
+                for (int e = tid; e < 2 * nbk; e += nt) {
+                    int s = e / nbk, c = e % nbk;
+                    T* Sb = S1 + s * NBMAX * (NBMAX + 1);
+                    stb[s * NBMAX + c] = Sb[c * (NBMAX + 1) + a];                       // column a
+                    strow[s * n + c] = (c == a ? T(1) : T(0)) - Sb[a * (NBMAX + 1) + c];  // e_a^T - row a
+                }
+                __syncthreads();
+                const int xa = xw[p0 + a];
+                for (int e = tid; e < 2 * nbk * nbk; e += nt) {
+                    int s = e / (nbk * nbk), rem = e % (nbk * nbk), r = rem / nbk, c = rem % nbk;
+                    T* Sb = S1 + s * NBMAX * (NBMAX + 1);
+                    double db = exp(-sp.c[s] * (double)xa) - 1.0;
+                    double rr = 1.0 + db * (1.0 - (double)stb[s * NBMAX + a]);
+                    T f = (T)(db / rr);
+                    Sb[r * (NBMAX + 1) + c] -= f * stb[s * NBMAX + r] * strow[s * n + c];
+                }
+                __syncthreads();
+            }
+            // (b) proposals from lambda(x') = bbar(x') / sum bbar, bbar(x) = s(x) e^{x h}
+            if (tid < nbk) {
+                const int a = tid, i = s0 + p0 + a;
+                const double nb0 = 1.0 - (double)S1[(0 * NBMAX + a) * (NBMAX + 1) + a];
+                const double nb1 = 1.0 - (double)S1[(1 * NBMAX + a) * (NBMAX + 1) + a];
+                const double h = sp.c[0] * nb0 + sp.c[1] * nb1;
+                const double lp = hs_log_scalar(sp, +1) + h, lm = hs_log_scalar(sp, -1) - h;
+                const double lamp = 1.0 / (1.0 + exp(lm - lp));
+                const int x = xw[p0 + a];
+                const int xp = replay ? (replay[i] ? 1 : -1) : (u[i] < lamp ? 1 : -1);
+                so.dec[i] = xp > 0 ? 1 : 0;
+                so.ratio[i] = lamp;
+                double lpr = 0.0;
+                if (xp != x) {
+                    double lbx = hs_log_scalar(sp, x) + x * h, lbxp = hs_log_scalar(sp, xp) + xp * h;
+                    lpr = (hs_log_scalar(sp, xp) - hs_log_scalar(sp, x)) + (lbx - lbxp);
+                }
+                fb[0 * NBMAX + a] = lpr;
+                fb[1 * NBMAX + a] = (xp != x) ? 1.0 : 0.0;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int nF = 0;
+                double lpr = 0.0;
+                for (int a = 0; a < nbk; ++a)
+                    if (fb[1 * NBMAX + a] != 0.0) {
+                        s_F[nF++] = a;
+                        lpr += fb[0 * NBMAX + a];
+                    }
+                s_nF = nF;
+                s_R = exp(lpr);
+            }
+            __syncthreads();
+            const int nF = s_nF;
+            ++n_prop;
+            if (nF == 0) {
+                if (tid == 0) {
+                    so.dec[N + blk] = 1;
+                    so.ratio[N + blk] = 1.0;
+                }
+                ++n_acc;
+                continue;
+            }
+            // (c) determinant ratio det(1 + D_F A_FF) as a product of sequential rank-1 ratios
+            for (int e = tid; e < 2 * nbk * nbk; e += nt) {
+                int s = e / (nbk * nbk), rem = e % (nbk * nbk), a = rem / nbk, c = rem % nbk;
+                S1[(s * NBMAX + a) * (NBMAX + 1) + c] = Gs[(s * n + p0 + a) * P + p0 + c];
+            }
+            __syncthreads();
+            double rs0 = 1.0, rs1 = 1.0;
+            for (int q = 0; q < nF; ++q) {
+                const int a = s_F[q];
+                const int xa = xw[p0 + a];
+                for (int e = tid; e < 2 * nbk; e += nt) {
+                    int s = e / nbk, c = e % nbk;
+                    T* Sb = S1 + s * NBMAX * (NBMAX + 1);
+                    stb[s * NBMAX + c] = Sb[c * (NBMAX + 1) + a];
+                    strow[s * n + c] = (c == a ? T(1) : T(0)) - Sb[a * (NBMAX + 1) + c];
+                }
+                __syncthreads();
+                double dd[2], rr[2];
+                for (int s = 0; s < 2; ++s) {
+                    dd[s] = field_delta(sp.c[s], xa, -xa);
+                    rr[s] = 1.0 + dd[s] * (1.0 - (double)stb[s * NBMAX + a]);
+                }
+                rs0 *= rr[0];
+                rs1 *= rr[1];
+                if (tid == 0) {
+                    fb[2 * NBMAX + q] = dd[0] / rr[0];
+                    fb[3 * NBMAX + q] = dd[1] / rr[1];
+                    fb[4 * NBMAX + q] = dd[0];
+                    fb[5 * NBMAX + q] = dd[1];
+                }
+                for (int e = tid; e < 2 * nbk * nbk; e += nt) {
+                    int s = e / (nbk * nbk), rem = e % (nbk * nbk), r = rem / nbk, c = rem % nbk;
+                    T* Sb = S1 + s * NBMAX * (NBMAX + 1);
+                    Sb[r * (NBMAX + 1) + c] -= (T)(dd[s] / rr[s]) * stb[s * NBMAX + r] * strow[s * n + c];
+                }
+                __syncthreads();
+            }
+            const double R = s_R * rs0 * rs1;
+            bool acc = replay ? (replay[N + blk] != 0) : (u[N + blk] < fabs(R));
+            if (!isfinite(R)) acc = false;
+            if (tid == 0) {
+                so.dec[N + blk] = acc ? 1 : 0;
+                so.ratio[N + blk] = R;
+                if (!isfinite(R)) set_err(err, DEV_NUMERIC);
+            }
+            if (!acc) continue;
+            ++n_acc;
+            n_flip += nF;
+            maxr = fmax(maxr, fabs(R));
+            if (tid == 0 && R < 0) sign = -sign;
+            // (d) apply the flips to the trailing block [p0, n)^2 of the window, one rank-1 step each
+            const int q0 = p0, w = n - p0;
+            for (int q = 0; q < nF; ++q) {
+                const int a = p0 + s_F[q];
+                for (int e = tid; e < 2 * w; e += nt) {
+                    int s = e / w, c = q0 + e % w;
+                    T* Gb = Gs + s * n * P;
+                    stcol[s * n + c] = Gb[c * P + a];
+                    strow[s * n + c] = (c == a ? T(1) : T(0)) - Gb[a * P + c];
+                }
+                __syncthreads();
+                for (int e = tid; e < 2 * w * w; e += nt) {
+                    int s = e / (w * w), rem = e % (w * w), r = q0 + rem / w, c = q0 + rem % w;
+                    T* Gb = Gs + s * n * P;
+                    Gb[r * P + c] -= (T)fb[(2 + s) * NBMAX + q] * stcol[s * n + r] * strow[s * n + c];
+                }
+                if (tid == 0) {
+                    idx[s_m] = a;
+                    dl[0 * n + s_m] = fb[4 * NBMAX + q];
+                    dl[1 * n + s_m] = fb[5 * NBMAX + q];
+                    s_m = s_m + 1;
+                    xw[a] = (int8_t)(-xw[a]);
+                }
+                __syncthreads();
+            }
+        }
+    }
+    __syncthreads();
+    const int m = s_m;
+    if (MODE == AFQMC_MODE_DELAYED) {  // apply the accepted flips (deferred: xw[p] was read by every thread)
+        for (int q = tid; q < m; q += nt) xw[idx[q]] = (int8_t)(-xw[idx[q]]);
+        __syncthreads();
+    }
+    for (int p = tid; p < n; p += nt) xl_g[s0 + p] = xw[p];
+    for (int q = tid; q < m; q += nt) {
+        wb.idx[q] = s0 + idx[q];
+        wb.dtot[q] = dl[q];
+        wb.dtot[WinCap<T>::NW + q] = dl[n + q];
+    }
+    if (tid == 0) {
+        *wb.m = m;
+        if (so.sign) *so.sign = sign;
+        so.stats[0] += n_prop;
+        so.stats[1] += n_acc;
+        so.stats[2] += n_flip;
+        so.stats[3] += (m > 0) ? 1 : 0;
+        *so.maxr = fmax(*so.maxr, maxr);
+    }
+    __syncthreads();
+    if (m == 0) return;
+
+    // ---- W = D_I (1 + A0_II D_I)^{-1} per spin, A0 = 1 - G0 (G0 = global G, not yet flushed) ----
+    const int NWC = WinCap<T>::NW;
+    T* Aug = Gs;  // m x (2m), pitch 2m+1
+    const int AP = 2 * m + 1;
+    for (int s = 0; s < 2; ++s) {
+        for (int e = tid; e < m * m; e += nt) {
+            int a = e / m, c = e % m;
+            double g0 = (double)G[s][(long)(s0 + idx[a]) * ld + (s0 + idx[c])];
+            double A0 = (a == c ? 1.0 : 0.0) - g0;
+            Aug[a * AP + c] = (T)((a == c ? 1.0 : 0.0) + A0 * dl[s * n + c]);
+            Aug[a * AP + m + c] = (a == c) ? T(1) : T(0);
+        }
+        __syncthreads();
+        for (int k = 0; k < m; ++k) {
+            if (tid < 32) {  // pivot search in column k, rows k..m-1
+                double best = -1.0;
+                int br = k;
+                for (int r = k + tid; r < m; r += 32) {
+                    double v = fabs((double)Aug[r * AP + k]);
+                    if (v > best) { best = v; br = r; }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    double ob = __shfl_down_sync(0xffffffffu, best, o);
+                    int orr = __shfl_down_sync(0xffffffffu, br, o);
+                    if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
+                }
+                if (tid == 0) {
+                    s_piv = br;
+                    if (!(best > 0.0)) set_err(err, DEV_NUMERIC);
+                }
+            }
+            __syncthreads();
+            const int pr = s_piv;
+            if (pr != k)
+                for (int c = tid; c < 2 * m; c += nt) {
+                    T t0 = Aug[k * AP + c];
+                    Aug[k * AP + c] = Aug[pr * AP + c];
+                    Aug[pr * AP + c] = t0;
+                }
+            __syncthreads();
+            const T inv = T(1) / Aug[k * AP + k];
+            for (int r = tid; r < m; r += nt) stc[r] = Aug[r * AP + k];
+            __syncthreads();
+            for (int c = tid; c < 2 * m; c += nt) Aug[k * AP + c] *= inv;
+            __syncthreads();
+            for (int e = tid; e < m * 2 * m; e += nt) {
+                int r = e / (2 * m), c = e % (2 * m);
+                if (r == k) continue;
+                Aug[r * AP + c] -= stc[r] * Aug[k * AP + c];
+            }
+            __syncthreads();
+        }
+        T* Wm = (T*)wb.Wm + (size_t)s * NWC * NWC;
+        for (int e = tid; e < m * m; e += nt) {
+            int a = e / m, c = e % m;
+            Wm[a * NWC + c] = (T)(dl[s * n + a] * (double)Aug[a * AP + m + c]);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T* Gd, int8_t* xl,
+                                const double* u, const uint8_t* replay, const SiteParams& sp, SliceOut so,
+                                int s0, int n, int nb, WindowBufs wb, int* err) {
+    size_t shm = window_smem<T>(n);
+    static bool attr_set[2] = {false, false};
+    const int mi = (mode == AFQMC_MODE_DELAYED) ? 0 : 1;
+    auto kfn = (mode == AFQMC_MODE_DELAYED) ? (void*)window_kernel<T, AFQMC_MODE_DELAYED>
+                                            : (void*)window_kernel<T, AFQMC_MODE_BLOCKFB>;
+    if (!attr_set[mi]) {
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)window_smem<T>(WinCap<T>::NW));
+        if (e != cudaSuccess) return e;
+        attr_set[mi] = true;
+    }
+    if (mode == AFQMC_MODE_DELAYED)
+        window_kernel<T, AFQMC_MODE_DELAYED><<<1, WIN_THREADS, shm, st>>>(Gu, Gd, xl, u, replay, sp, so, s0, n, nb,
+                                                                          wb, err);
+    else
+        window_kernel<T, AFQMC_MODE_BLOCKFB><<<1, WIN_THREADS, shm, st>>>(Gu, Gd, xl, u, replay, sp, so, s0, n, nb,
+                                                                          wb, err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// flush: X = G[:, I], Yraw = E_I^T - G[I, :], Y = W Yraw, G <- G - X Y
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void gather_kernel(const T* __restrict__ Gu, const T* __restrict__ Gd, long ld, int N, WindowBufs wb,
+                              int NW) {
+    const int m = *wb.m;
+    const int s = blockIdx.y;
+    const T* G = s ? Gd : Gu;
+    T* X = (T*)wb.X + (size_t)s * N * NW;
+    T* Y = (T*)wb.Y + (size_t)s * NW * N;  // Yraw here; the product with W comes after
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * N; e += gridDim.x * blockDim.x) {
+        int a = e / N, j = e % N;
+        int I = wb.idx[a];
+        Y[(size_t)a * N + j] = (j == I ? T(1) : T(0)) - G[(long)I * ld + j];
+        int r = e / m, q = e % m;  // X row r, column q (coalesced over q is poor; rows are short)
+        X[(size_t)r * NW + q] = G[(long)r * ld + wb.idx[q]];
+    }
+}
+
+template <typename T>
+cudaError_t launch_flush(cudaStream_t st, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw) {
+    const int N = sp.N;
+    const int NWC = WinCap<T>::NW;
+    gather_kernel<T><<<dim3(256, 2), 256, 0, st>>>(Gu, Gd, sp.ld, N, wb, NWC);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // Y <- W * Yraw  (rows >= m are never read); written into the X buffer's tail? use a separate pass:
+    // compute in place is unsafe, so the product goes to the second half of the Y buffer.
+    GemmArgs<T> g;
+    g.M = nw; g.N = N; g.K = nw; g.Kdev = wb.m;
+    g.A = (const T*)wb.Wm; g.lda = NWC; g.sA = (long)NWC * NWC;
+    g.B = (const T*)wb.Y; g.ldb = N; g.sB = (long)NWC * N;
+    g.C = (T*)wb.Y + (size_t)2 * NWC * N; g.ldc = N; g.sC = (long)NWC * N;
+    g.alpha = T(1); g.beta = T(0);
+    g.batch = 2;
+    e = gemm<T>(st, g);
+    if (e != cudaSuccess) return e;
+    // G <- G - X Y
+    GemmArgs<T> h;
+    h.M = N; h.N = N; h.K = nw; h.Kdev = wb.m;
+    h.A = (const T*)wb.X; h.lda = NWC; h.sA = (long)N * NWC;
+    h.B = (const T*)wb.Y + (size_t)2 * NWC * N; h.ldb = N; h.sB = (long)NWC * N;
+    h.C = Gu; h.ldc = sp.ld; h.sC = (long)(Gd - Gu);
+    h.alpha = T(-1); h.beta = T(1);
+    h.batch = 2;
+    return gemm<T>(st, h);
+}
+
+template cudaError_t launch_local<float>(cudaStream_t, float*, float*, int8_t*, const double*, const uint8_t*,
+                                         const SiteParams&, SliceOut, float*, float*, GridBar*, int*, int);
+template cudaError_t launch_local<double>(cudaStream_t, double*, double*, int8_t*, const double*, const uint8_t*,
+                                          const SiteParams&, SliceOut, double*, double*, GridBar*, int*, int);
+template cudaError_t launch_window_chain<float>(cudaStream_t, int, const float*, const float*, int8_t*,
+                                                const double*, const uint8_t*, const SiteParams&, SliceOut, int,
+                                                int, int, WindowBufs, int*);
+template cudaError_t launch_window_chain<double>(cudaStream_t, int, const double*, const double*, int8_t*,
+                                                 const double*, const uint8_t*, const SiteParams&, SliceOut, int,
+                                                 int, int, WindowBufs, int*);
+template cudaError_t launch_flush<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int);
+template cudaError_t launch_flush<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs, int);
+
+}  // namespace afq

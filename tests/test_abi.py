@@ -1,0 +1,53 @@
+"""The C-ABI library builds, loads and exports every entry point include/afqmc.h declares
+(no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2506_09611_gb300 import afqmc, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "afqmc.h")).read()
+    return sorted(set(re.findall(r"\b(afqmc_[a-z_A-Z]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ("afqmc_create", "afqmc_destroy", "afqmc_init_walkers", "afqmc_sweep_slice",
+                 "afqmc_recompute_G", "afqmc_measure_energy", "afqmc_strerror"):
+        assert name in syms
+    assert set(syms) == set(afqmc.EXPORTS)
+
+
+def test_library_builds_and_exports_every_symbol():
+    lib_path = build.build()
+    lib = ctypes.CDLL(lib_path)
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    for name in declared_symbols():
+        assert re.search(rf"\bT {name}\b", out), name
+
+
+def test_strerror_without_gpu():
+    afqmc.load()
+    assert afqmc.strerror(-6) == "call out of sequence"
+    assert afqmc.strerror(0) == "ok"
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device():
+    lib = afqmc.load()
+    h = ctypes.c_void_p()
+    bad = afqmc.afqmc_params(hs=0, precision=1, M=10, stab_every=3, t=1.0, U=4.0, dtau=0.05, seed=1)
+    assert lib.afqmc_create(ctypes.byref(h), ctypes.byref(bad)) == -1  # M not a multiple of stab_every
+    bad2 = afqmc.afqmc_params(hs=0, precision=1, M=10, stab_every=5, t=1.0, U=-4.0, dtau=0.05, seed=1)
+    assert lib.afqmc_create(ctypes.byref(h), ctypes.byref(bad2)) == -1  # spin channel needs U >= 0
+    bad3 = afqmc.afqmc_params(hs=7, precision=1, M=10, stab_every=5, t=1.0, U=4.0, dtau=0.05, seed=1)
+    assert lib.afqmc_create(ctypes.byref(h), ctypes.byref(bad3)) == -1
+    assert lib.afqmc_destroy(None) == 0
