@@ -1,0 +1,374 @@
+"""Benchmark: field updates/s of the PQMC auxiliary-field sweep at 40x40 on GB300.
+
+Workload (one step = one full sweep, forward l = 1..M then backward l = M..1):
+  standard 2D Hubbard, 40 x 40 periodic (N = 1600), t = 1, U = 6 (real spin decoupling),
+  filling 0.875 (700 particles per spin), dtau = 0.05, M = 80 slices, FP32 bulk G,
+  delayed update (k sites per delayed step), FP64 re-orthonormalisation and G recompute
+  every 10 slices.  One walker per GPU (weak scaling across ranks, no collective on the
+  data path).  Inputs are synthetic and seeded (trial state, fields, Philox uniforms).
+
+The JSON line reports the device-timed sweep throughput (value), the update-only rate,
+local and block-force-bias comparisons on a bounded sample of slices, the FP32 drift of G
+against the FP64 recompute, the roofline of the dominant kernel (measured live with CUDA
+events on the launching stream), the clocks seen during the timed region, an end-to-end
+number through the C ABI with host buffers, and the FP64 oracle timed on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2506_09611_gb300 import inputs  # noqa: E402
+
+METRIC = "field updates/s at 40x40 Hubbard on 1 GB300, delayed/blockFB vs local; G err"
+UNIT = "field updates/s"
+L, U, T_HOP, DTAU, M, STAB, FILLING = 40, 6.0, 1.0, 0.05, 80, 10, 0.875
+NS = inputs.n_sigma_for(L, FILLING)
+N = L * L
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--k", type=int, default=64, help="delay rank (sites per delayed step)")
+    ap.add_argument("--nb", type=int, default=16, help="block size of the block force-bias sample")
+    ap.add_argument("--cmp-slices", type=int, default=20, help="slices of the local / block-FB samples")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_oracle_sample(n_slices, k, warm=0):
+    """The FP64 oracle on the host cores: G(0) of the 40x40 workload (M = 10, not timed), then
+    n_slices slice-steps (wrap + delayed update) timed.  Returns (field updates/s, cores, secs)."""
+    import oracle
+
+    Ms = 10
+    P = inputs.trial_state(L, L, NS)
+    X = inputs.initial_fields(Ms, N, seed=1)
+    model = oracle.Model(L, L, T_HOP, U, DTAU, Ms)
+    w = oracle.Walker(model, P, P, X)
+    order = [(l, +1) for l in range(1, Ms + 1)] + [(l, -1) for l in range(Ms, 0, -1)]
+    times = []
+    for it in range(warm + n_slices):
+        ell, d = order[it % len(order)]
+        u = inputs.uniforms(1, 0, it, 2 * N)
+        t0 = time.perf_counter()
+        w.sweep_slice(ell, d, "delayed", u, k=k)
+        if it >= warm:
+            times.append(time.perf_counter() - t0)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return N * len(times) / sum(times), cores, sum(times)
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    v, cores, secs = run_oracle_sample(args.steps, args.k, warm=args.warmup)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{L}x{L} Hubbard U={U} n={FILLING} dtau={DTAU}, delayed k={args.k}",
+                   "step": "one slice-step (wrap + delayed update of 1600 sites) of the FP64 oracle"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} slice-steps at 40x40 after {args.warmup} warm-up slice-steps; "
+                                   f"G(0) from the oracle's own FP64 init with M=10 (not timed)"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_2506_09611_gb300 import afqmc
+
+    afqmc.load()
+    stream = torch.cuda.current_stream()
+    seed = 1 + rank
+    P = inputs.trial_state(L, L, NS)
+    X = inputs.initial_fields(M, N, seed=seed)
+    Pcat = np.concatenate([P.ravel(), P.ravel()])
+    ctx = afqmc.Context(M, dtau=DTAU, U=U, t=T_HOP, precision="fp32", stab_every=STAB, seed=seed)
+    ctx.init_walkers([L], [NS], [NS], Pcat, X, stream=stream)
+    order = [(l, +1) for l in range(1, M + 1)] + [(l, -1) for l in range(M, 0, -1)]
+
+    def sweep(mode, k, nb, drift=None, slices=None):
+        for (ell, d) in (order if slices is None else slices):
+            ctx.sweep_slice(ell, d, mode, k=k, nb=nb, stream=stream)
+            pos = ell if d > 0 else ell - 1
+            if pos % STAB == 0:  # FP64 re-orthonormalisation + recompute point
+                if drift is not None:
+                    drift.append(float(ctx.recompute_G(stream=stream)[0]))
+                else:
+                    afqmc.afqmc_recompute_G(ctx.h, None, stream)
+
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    drifts = []
+    for _ in range(args.warmup):
+        sweep("delayed", args.k, args.nb, drift=drifts)
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: K full sweeps ----------------
+    ctx.set_profiling(True)
+    launches0 = afqmc.afqmc_launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local_rank) as clk:
+        for i in range(args.steps):
+            flush_buf.zero_()  # L2 flush between timed steps (256 MB > 129 MB L2), outside the events
+            ev[i][0].record(stream)
+            sweep("delayed", args.k, args.nb)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    launches = afqmc.afqmc_launch_count() - launches0 - 0
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    ms_total = sum(ms_steps)
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    updates_per_step = N * M * 2
+    value = world * updates_per_step * args.steps / (ms_total / 1e3)
+    clocks = clk.summary()
+
+    # update-only (the paper's "time for update per sweep"): prep + window chains + flushes
+    upd_ms = prof["prep"]["ms"] + prof["chain"]["ms"] + prof["flush"]["ms"]
+    update_only = updates_per_step * args.steps / (upd_ms / 1e3)
+
+    # ---------------- bounded comparison samples (same context, continuing the chain) ------------
+    cmp = {}
+    sample = [(l, +1) for l in range(1, args.cmp_slices + 1)]
+    back = [(l, -1) for l in range(args.cmp_slices, 0, -1)]
+    for mode, k, nb in (("local", args.k, args.nb), ("blockfb", args.k, args.nb), ("delayed", args.k, args.nb)):
+        ctx.set_profiling(True)
+        stats = []
+        for (ell, d) in sample:
+            st = ctx.sweep_slice(ell, d, mode, k=k, nb=nb, want_stats=True, stream=stream)
+            stats.append((st[0].proposals, st[0].accepts, st[0].flipped))
+            if ell % STAB == 0:
+                afqmc.afqmc_recompute_G(ctx.h, None, stream)
+        p = ctx.profile()
+        ctx.set_profiling(False)
+        # walk back to slice 0 so the next sample starts from the same position
+        for (ell, d) in back:
+            ctx.sweep_slice(ell, d, "delayed", k=args.k, nb=nb, stream=stream)
+            if (ell - 1) % STAB == 0:
+                afqmc.afqmc_recompute_G(ctx.h, None, stream)
+        umode = p["local"]["ms"] if mode == "local" else p["chain"]["ms"] + p["flush"]["ms"]
+        umode += p["prep"]["ms"]
+        n_upd = N * len(sample)
+        props = sum(s[0] for s in stats)
+        acc = sum(s[1] for s in stats)
+        cmp[mode] = {"update_only": n_upd / (umode / 1e3),
+                     "with_wrap": n_upd / ((umode + p["wrap"]["ms"]) / 1e3),
+                     "acceptance": acc / max(props, 1), "slices": len(sample),
+                     "k" if mode == "delayed" else ("nb" if mode == "blockfb" else "kind"):
+                         (k if mode == "delayed" else (nb if mode == "blockfb" else "rank-1 GER per accept"))}
+    speedup = {m: cmp[m]["update_only"] / cmp["local"]["update_only"] for m in ("delayed", "blockfb")}
+
+    # ---------------- roofline of the dominant kernel ----------------
+    pk, pk_src = peaks()
+    phases = {k: v for k, v in prof.items() if v["ms"] > 0}
+    dom = max(phases, key=lambda k: phases[k]["ms"])
+    roof = roofline_for(dom, prof, args, pk, pk_src)
+
+    # ---------------- end to end through the C ABI with host buffers ----------------
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(afqmc, torch, stream, args, seed, rank)
+
+    ctx.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, secs = run_oracle_sample(3, args.k)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "3 slice-steps (wrap + delayed update, k=%d) of the FP64 oracle at 40x40 from its own "
+                         "G(0) (M=10 init not timed); %.1f s of CPU work" % (args.k, secs)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{L}x{L} standard Hubbard, U/t={U}, n={FILLING} ({NS} per spin), "
+                                   f"dtau={DTAU}, M={M}, FP32 bulk G, delayed k={args.k}, FP64 recompute "
+                                   f"every {STAB} slices",
+                       "step": "one full sweep (2M = 160 slice-steps: wrap + delayed update) + 16 FP64 recomputes",
+                       "walkers_per_gpu": 1, "l2": "flushed between timed steps (256 MB write)"},
+            "update_only": {"value": update_only, "unit": UNIT,
+                            "note": "prep + window decisions + rank-m flushes (the paper's update time)"},
+            "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
+            "compare_sample": cmp,
+            "speedup_update_only_vs_local": speedup,
+            "G_err_fp32_vs_fp64_recompute": {"max": max(drifts) if drifts else None,
+                                             "median": statistics.median(drifts) if drifts else None,
+                                             "slices_between_recomputes": STAB},
+            "roofline": roof,
+            "clocks": clocks,
+            "gpu_launches": launches,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def roofline_for(dom, prof, args, pk, pk_src):
+    """Achieved throughput of the dominant kernel: algorithmic work per launch / mean launch time."""
+    p = prof[dom]
+    if dom == "wrap":
+        # 2 batched GEMM launches per interval (+ one tiny scale kernel); each GEMM does 2 N^3 per spin
+        per_launch_ms = p["ms"] / (2 * p["intervals"])
+        flops = 2.0 * N ** 3 * 2
+        ach = flops / (per_launch_ms / 1e3) / 1e12
+        peak = fp32_alu_peak(pk)
+        return {"kernel": "wrap GEMM (SIMT FP32, batched over spins)", "bound": "alu", "achieved": ach,
+                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_source": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x %.0f MHz (sm_max_mhz of %s peaks)"
+                               % (pk.get("sm_max_mhz", 2070.0), pk_src)}
+    if dom == "recompute":
+        return {"kernel": "FP64 recompute (propagation GEMMs, pivoted elimination, G formation)",
+                "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "note": "phase-level only; see profiles/"}
+    if dom in ("chain", "flush"):
+        # flush: read + write G (both spins, FP32) per window
+        nwin = p["intervals"]
+        per_ms = p["ms"] / nwin
+        byts = 2 * 2 * N * N * 4
+        ach = byts / (per_ms / 1e3) / 1e9
+        return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None}
+    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None}
+
+
+def fp32_alu_peak(pk):
+    return 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+def end_to_end(afqmc, torch, stream, args, seed, rank):
+    """Per step through the public API with pinned host buffers: afqmc_create +
+    afqmc_init_walkers (H2D trial state and fields) + one full sweep + afqmc_measure_energy +
+    afqmc_get_fields (D2H configuration) + afqmc_destroy, wall-clock."""
+    P = inputs.trial_state(L, L, NS)
+    X = inputs.initial_fields(M, N, seed=seed)
+    Ph = torch.from_numpy(np.concatenate([P.ravel(), P.ravel()])).pin_memory().numpy()
+    Xh = torch.from_numpy(X.copy()).pin_memory().numpy()
+    order = [(l, +1) for l in range(1, M + 1)] + [(l, -1) for l in range(M, 0, -1)]
+    times = []
+    for it in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c = afqmc.Context(M, dtau=DTAU, U=U, t=T_HOP, precision="fp32", stab_every=STAB, seed=seed)
+        c.init_walkers([L], [NS], [NS], Ph, Xh, stream=stream)
+        for (ell, d) in order:
+            c.sweep_slice(ell, d, "delayed", k=args.k, nb=args.nb, stream=stream)
+            pos = ell if d > 0 else ell - 1
+            if pos % STAB == 0:
+                afqmc.afqmc_recompute_G(c.h, None, stream)
+        e, s = c.measure_energy(stream=stream)
+        Xout = c.fields(0)
+        c.close()
+        times.append(time.perf_counter() - t0)
+    t = times[-1]
+    return {"value": N * M * 2 / t, "unit": UNIT, "h2d_bytes_per_step": int(Ph.nbytes + Xh.nbytes),
+            "d2h_bytes_per_step": int(Xout.nbytes + 16),
+            "note": "create + init_walkers (FP64 left stack and G(0)) + 1 sweep + energy + fields readback"}
+
+
+if __name__ == "__main__":
+    main()

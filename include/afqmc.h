@@ -142,6 +142,25 @@ int afqmc_get_info(afqmc_ctx* ctx, int walker, int* N, int* n_up, int* n_dn, int
  * out[j] = u(seed, walker, visit, j) for j < count (device generator, copied to the host). */
 int afqmc_debug_uniforms(uint64_t seed, uint64_t walker, uint64_t visit, int count, double* host_out);
 
+/* Profiling.  With profiling on, every phase of afqmc_sweep_slice / afqmc_recompute_G is
+ * bracketed by CUDA events recorded on the call's stream (the stream its kernels run on).
+ * Phases: */
+#define AFQMC_PHASE_PREP 0       /* uniforms, field scales, stats reset */
+#define AFQMC_PHASE_WRAP 1       /* the two wrap products G <- B G B^{-1} (Eq. BlMat) */
+#define AFQMC_PHASE_LOCAL 2      /* the local-update site loop */
+#define AFQMC_PHASE_CHAIN 3      /* delayed / block-FB window decisions (one CTA per window) */
+#define AFQMC_PHASE_FLUSH 4      /* panel gather + rank-m product of the delayed / block-FB update */
+#define AFQMC_PHASE_RECOMPUTE 5  /* FP64 propagation, re-orthonormalisation and G = 1 - U_R T U_L */
+#define AFQMC_NPHASE 6
+/* on != 0 enables profiling and clears the accumulators; on == 0 disables it. */
+int afqmc_set_profiling(afqmc_ctx* ctx, int on);
+/* Sync the last stream and return, per phase, the summed device milliseconds, the number of
+ * bracketed intervals, and the number of library kernels launched in that phase.  Each array
+ * has AFQMC_NPHASE entries; any pointer may be NULL. */
+int afqmc_get_profile(afqmc_ctx* ctx, double* ms, int64_t* intervals, int64_t* launches);
+/* Number of library kernels launched by this process so far (every launch site counts). */
+int64_t afqmc_launch_count(void);
+
 const char* afqmc_strerror(int code);
 
 #ifdef __cplusplus

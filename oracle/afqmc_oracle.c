@@ -17,6 +17,10 @@
  *   HS_CHARGE_REAL (U < 0): cosh(lam) = exp(dtau |U| / 2), c_up = c_dn = +lam, s(x) = exp(-lam x).
  * where e^{-dtau U (n_up n_dn - (n_up+n_dn)/2)} = C * sum_x s(x) e^{x (c_up n_up + c_dn n_dn)} / 2.
  *
+ * Loops over independent output rows carry OpenMP pragmas; every output element
+ * is still accumulated by one thread in the written order, so results do not
+ * depend on the thread count.
+ *
  * Every function below follows the paper's equations, restated in the G form
  * (the identity G = 1 - U_R T U_L of Eq. GrFMatNew turns the paper's T-matrix
  * updates into updates of G):
@@ -130,6 +134,7 @@ static int lu_factor(double* a, int n, int* piv, double* logabs) {
         double d = a[(size_t)k * n + k];
         if (d < 0) sgn = -sgn;
         la += log(fabs(d));
+#pragma omp parallel for schedule(static)
         for (int r = k + 1; r < n; r++) {
             double l = a[(size_t)r * n + k] / d;
             a[(size_t)r * n + k] = l;
@@ -197,6 +202,7 @@ static int qr_orth(double* a, int m, int n, size_t rs, size_t cs, double* logabs
         for (int r = j; r < m; r++) vn += vj[r] * vj[r];
         beta[j] = (vn > 0) ? 2.0 / vn : 0.0;
         /* apply H_j = 1 - beta v v^T to columns j..n-1 */
+#pragma omp parallel for schedule(static)
         for (int c = j; c < n; c++) {
             double s = 0.0;
             for (int r = j; r < m; r++) s += vj[r] * A_(r, c);
@@ -212,6 +218,7 @@ static int qr_orth(double* a, int m, int n, size_t rs, size_t cs, double* logabs
         for (int c = 0; c < n; c++) A_(r, c) = (r == c) ? 1.0 : 0.0;
     for (int j = n - 1; j >= 0; j--) {
         double* vj = v + (size_t)j * m;
+#pragma omp parallel for schedule(static)
         for (int c = 0; c < n; c++) {
             double s = 0.0;
             for (int r = j; r < m; r++) s += vj[r] * A_(r, c);
@@ -237,13 +244,16 @@ static int qr_orth(double* a, int m, int n, size_t rs, size_t cs, double* logabs
 static void apply_B_left(const or_params* p, const double* E, const int8_t* xl, int s,
                          const double* X, double* Y, int ns) {
     int N = p->N;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < N; i++) {
         double d = exp(p->c[s] * xl[i]);
-        for (int c = 0; c < ns; c++) {
-            double acc = 0.0;
-            for (int k = 0; k < N; k++) acc += E[(size_t)i * N + k] * X[(size_t)k * ns + c];
-            Y[(size_t)i * ns + c] = d * acc;
+        double* y = Y + (size_t)i * ns;
+        for (int c = 0; c < ns; c++) y[c] = 0.0;
+        for (int k = 0; k < N; k++) {
+            double e = E[(size_t)i * N + k];
+            for (int c = 0; c < ns; c++) y[c] += e * X[(size_t)k * ns + c];
         }
+        for (int c = 0; c < ns; c++) y[c] *= d;
     }
 }
 
@@ -254,12 +264,15 @@ static void apply_B_right(const or_params* p, const double* E, const int8_t* xl,
     double* XD = (double*)malloc(sizeof(double) * (size_t)ns * N + 1);
     for (int r = 0; r < ns; r++)
         for (int k = 0; k < N; k++) XD[(size_t)r * N + k] = X[(size_t)r * N + k] * exp(p->c[s] * xl[k]);
-    for (int r = 0; r < ns; r++)
-        for (int j = 0; j < N; j++) {
-            double acc = 0.0;
-            for (int k = 0; k < N; k++) acc += XD[(size_t)r * N + k] * E[(size_t)k * N + j];
-            Y[(size_t)r * N + j] = acc;
+#pragma omp parallel for schedule(static)
+    for (int r = 0; r < ns; r++) {
+        double* y = Y + (size_t)r * N;
+        for (int j = 0; j < N; j++) y[j] = 0.0;
+        for (int k = 0; k < N; k++) {
+            double a = XD[(size_t)r * N + k];
+            for (int j = 0; j < N; j++) y[j] += a * E[(size_t)k * N + j];
         }
+    }
     free(XD);
 }
 
@@ -298,12 +311,15 @@ int or_green_scratch(const or_params* p, const double* E, const int8_t* x, const
     sgn *= qr_orth(UL, N, ns, 1, (size_t)N, &la);
     /* O = U_L U_R (ns x ns); T = O^{-1}; G = 1 - U_R T U_L */
     double* O = (double*)malloc(sizeof(double) * (size_t)ns * ns + 1);
-    for (int a = 0; a < ns; a++)
-        for (int b = 0; b < ns; b++) {
-            double acc = 0.0;
-            for (int k = 0; k < N; k++) acc += UL[(size_t)a * N + k] * UR[(size_t)k * ns + b];
-            O[(size_t)a * ns + b] = acc;
+#pragma omp parallel for schedule(static)
+    for (int a = 0; a < ns; a++) {
+        double* o = O + (size_t)a * ns;
+        for (int b = 0; b < ns; b++) o[b] = 0.0;
+        for (int k = 0; k < N; k++) {
+            double l = UL[(size_t)a * N + k];
+            for (int b = 0; b < ns; b++) o[b] += l * UR[(size_t)k * ns + b];
         }
+    }
     int* piv = (int*)malloc(sizeof(int) * (size_t)ns + 1);
     double lo;
     sgn *= lu_factor(O, ns, piv, &lo);
@@ -311,17 +327,34 @@ int or_green_scratch(const or_params* p, const double* E, const int8_t* x, const
     /* Z = O^{-1} U_L  (ns x N) */
     memcpy(tmp, UL, sizeof(double) * nn);
     lu_solve(O, ns, piv, tmp, N);
-    for (int i = 0; i < N; i++)
-        for (int j = 0; j < N; j++) {
-            double acc = 0.0;
-            for (int k = 0; k < ns; k++) acc += UR[(size_t)i * ns + k] * tmp[(size_t)k * N + j];
-            G[(size_t)i * N + j] = (i == j ? 1.0 : 0.0) - acc;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < N; i++) {
+        double* g = G + (size_t)i * N;
+        for (int j = 0; j < N; j++) g[j] = 0.0;
+        for (int k = 0; k < ns; k++) {
+            double r = UR[(size_t)i * ns + k];
+            for (int j = 0; j < N; j++) g[j] += r * tmp[(size_t)k * N + j];
         }
+        for (int j = 0; j < N; j++) g[j] = (i == j ? 1.0 : 0.0) - g[j];
+    }
     if (UR_out) memcpy(UR_out, UR, sizeof(double) * nn);
     if (UL_out) memcpy(UL_out, UL, sizeof(double) * nn);
     *logabs = la;
     free(UR); free(UL); free(tmp); free(O); free(piv);
     return sgn;
+}
+
+/* C = A B for N x N row-major matrices; each C_ij sums k = 0..N-1 in order. */
+static void matmul(const double* A, const double* B, double* C, int N) {
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < N; i++) {
+        double* c = C + (size_t)i * N;
+        for (int j = 0; j < N; j++) c[j] = 0.0;
+        for (int k = 0; k < N; k++) {
+            double a = A[(size_t)i * N + k];
+            for (int j = 0; j < N; j++) c[j] += a * B[(size_t)k * N + j];
+        }
+    }
 }
 
 /* ------------------------------------------------------------------ */
@@ -338,35 +371,17 @@ void or_wrap(const or_params* p, const double* E, const double* Einv, const int8
     for (int i = 0; i < N; i++) d[i] = exp(p->c[s] * xl[i]);
     if (dir > 0) {
         /* T = E G ; G = D (T Einv) D^{-1} */
+        matmul(E, G, T, N);
+        matmul(T, Einv, G, N);
         for (int i = 0; i < N; i++)
-            for (int j = 0; j < N; j++) {
-                double acc = 0.0;
-                for (int k = 0; k < N; k++) acc += E[(size_t)i * N + k] * G[(size_t)k * N + j];
-                T[(size_t)i * N + j] = acc;
-            }
-        for (int i = 0; i < N; i++)
-            for (int j = 0; j < N; j++) {
-                double acc = 0.0;
-                for (int k = 0; k < N; k++) acc += T[(size_t)i * N + k] * Einv[(size_t)k * N + j];
-                G[(size_t)i * N + j] = d[i] * acc / d[j];
-            }
+            for (int j = 0; j < N; j++) G[(size_t)i * N + j] = d[i] * G[(size_t)i * N + j] / d[j];
     } else {
         /* T = D^{-1} G D ; G = Einv T E */
         for (int i = 0; i < N; i++)
             for (int j = 0; j < N; j++) T[(size_t)i * N + j] = G[(size_t)i * N + j] * d[j] / d[i];
         double* T2 = (double*)malloc(sizeof(double) * (size_t)N * N + 1);
-        for (int i = 0; i < N; i++)
-            for (int j = 0; j < N; j++) {
-                double acc = 0.0;
-                for (int k = 0; k < N; k++) acc += Einv[(size_t)i * N + k] * T[(size_t)k * N + j];
-                T2[(size_t)i * N + j] = acc;
-            }
-        for (int i = 0; i < N; i++)
-            for (int j = 0; j < N; j++) {
-                double acc = 0.0;
-                for (int k = 0; k < N; k++) acc += T2[(size_t)i * N + k] * E[(size_t)k * N + j];
-                G[(size_t)i * N + j] = acc;
-            }
+        matmul(Einv, T, T2, N);
+        matmul(T2, E, G, N);
         free(T2);
     }
     free(T);
@@ -407,6 +422,7 @@ void or_local_slice(const or_params* p, double* G0, double* G1, int8_t* xl, cons
             for (int a = 0; a < N; a++) col[a] = g[(size_t)a * N + i];
             for (int b = 0; b < N; b++) row[b] = (b == i ? 1.0 : 0.0) - g[(size_t)i * N + b];
             double f = d[s] / r[s];
+#pragma omp parallel for schedule(static)
             for (int a = 0; a < N; a++)
                 for (int b = 0; b < N; b++) g[(size_t)a * N + b] -= f * col[a] * row[b];
         }
@@ -467,6 +483,7 @@ void or_delayed_slice(const or_params* p, double* G0, double* G1, int8_t* xl, co
                     double* U = Ub[s];
                     double* V = Vb[s];
                     double f = -d[s] / r[s];
+#pragma omp parallel for schedule(static)
                     for (int j = 0; j < N; j++) {
                         double colj = g[(size_t)j * N + i], rowj = g[(size_t)i * N + j];
                         for (int q = 0; q < m; q++) {
@@ -489,6 +506,7 @@ void or_delayed_slice(const or_params* p, double* G0, double* G1, int8_t* xl, co
         if (want_flush) {
             for (int s = 0; s < 2; s++) {
                 double* g = G[s];
+#pragma omp parallel for schedule(static)
                 for (int a = 0; a < N; a++)
                     for (int b = 0; b < N; b++) {
                         double acc2 = 0.0;
@@ -630,6 +648,7 @@ void or_blockfb_slice(const or_params* p, double* G0, double* G1, int8_t* xl, co
                     for (int a = 0; a < nF; a++) acc2 += X[(size_t)j * nF + a] * W[(size_t)a * nF + b];
                     XW[(size_t)j * nF + b] = acc2;
                 }
+#pragma omp parallel for schedule(static)
             for (int a = 0; a < N; a++)
                 for (int b = 0; b < N; b++) {
                     double acc2 = 0.0;

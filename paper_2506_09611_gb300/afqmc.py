@@ -24,7 +24,9 @@ PRECS = {"fp64": PREC_FP64, "fp32": PREC_FP32}
 
 EXPORTS = ["afqmc_create", "afqmc_destroy", "afqmc_init_walkers", "afqmc_sweep_slice", "afqmc_recompute_G",
            "afqmc_measure_energy", "afqmc_get_G", "afqmc_set_G", "afqmc_get_fields", "afqmc_get_decisions",
-           "afqmc_get_ratios", "afqmc_get_info", "afqmc_debug_uniforms", "afqmc_strerror"]
+           "afqmc_get_ratios", "afqmc_get_info", "afqmc_debug_uniforms", "afqmc_set_profiling",
+           "afqmc_get_profile", "afqmc_launch_count", "afqmc_strerror"]
+PHASES = ["prep", "wrap", "local", "chain", "flush", "recompute"]
 
 
 class afqmc_params(ctypes.Structure):
@@ -70,11 +72,15 @@ def load(path: str = LIB_PATH):
     lib.afqmc_get_ratios.argtypes = [vp, ctypes.c_int, dp]
     lib.afqmc_get_info.argtypes = [vp, ctypes.c_int, ip, ip, ip, ip, ip]
     lib.afqmc_debug_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, dp]
+    lib.afqmc_set_profiling.argtypes = [vp, ctypes.c_int]
+    lib.afqmc_get_profile.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.afqmc_launch_count.argtypes = []
     lib.afqmc_strerror.argtypes = [ctypes.c_int]
     lib.afqmc_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name != "afqmc_strerror":
+        if name not in ("afqmc_strerror", "afqmc_launch_count"):
             getattr(lib, name).restype = ctypes.c_int
+    lib.afqmc_launch_count.restype = ctypes.c_int64
     _lib = lib
     return lib
 
@@ -190,6 +196,24 @@ def afqmc_debug_uniforms(seed, walker, visit, count):
     return out
 
 
+def afqmc_set_profiling(ctx, on):
+    _ck("afqmc_set_profiling", load().afqmc_set_profiling(ctx, int(on)))
+
+
+def afqmc_get_profile(ctx):
+    n = len(PHASES)
+    ms = np.zeros(n)
+    iv = np.zeros(n, np.int64)
+    la = np.zeros(n, np.int64)
+    _ck("afqmc_get_profile", load().afqmc_get_profile(ctx, _ptr(ms, ctypes.c_double), _ptr(iv, ctypes.c_int64),
+                                                      _ptr(la, ctypes.c_int64)))
+    return {p: {"ms": float(ms[i]), "intervals": int(iv[i]), "launches": int(la[i])} for i, p in enumerate(PHASES)}
+
+
+def afqmc_launch_count():
+    return int(load().afqmc_launch_count())
+
+
 # ---------------------------------------------------------------- convenience wrapper
 
 class Context:
@@ -232,6 +256,12 @@ class Context:
 
     def info(self, walker):
         return afqmc_get_info(self.h, walker)
+
+    def set_profiling(self, on=True):
+        afqmc_set_profiling(self.h, on)
+
+    def profile(self):
+        return afqmc_get_profile(self.h)
 
     def close(self):
         if self.h is not None:

@@ -3,9 +3,15 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <vector>
 
 #include "internal.h"
+
+namespace afq {
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches += n; }
+}  // namespace afq
 
 using namespace afq;
 
@@ -65,7 +71,21 @@ struct Walker {
 
 }  // namespace
 
+struct Prof {
+    bool on = false;
+    double ms[AFQMC_NPHASE] = {};
+    int64_t intervals[AFQMC_NPHASE] = {};
+    int64_t launches[AFQMC_NPHASE] = {};
+    std::vector<cudaEvent_t> pool;
+    struct Pend {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pend> pending;
+};
+
 struct afqmc_ctx {
+    Prof prof;
     afqmc_params p;
     double lam = 0.0, c[2] = {0.0, 0.0};
     int sticky = 0;
@@ -130,6 +150,39 @@ static int check_ctx(afqmc_ctx* ctx) {
     if (ctx->sticky) return ctx->sticky;
     return 0;
 }
+
+static cudaEvent_t prof_event(afqmc_ctx* ctx) {
+    if (!ctx->prof.pool.empty()) {
+        cudaEvent_t e = ctx->prof.pool.back();
+        ctx->prof.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one phase with CUDA events on the launching stream (when profiling is on).
+struct PhaseScope {
+    afqmc_ctx* ctx;
+    int ph;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    long long l0;
+    PhaseScope(afqmc_ctx* c, int phase, cudaStream_t s) : ctx(c), ph(phase), st(s), l0(g_launches.load()) {
+        if (ctx->prof.on) {
+            a = prof_event(ctx);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~PhaseScope() {
+        if (!ctx->prof.on || !a) return;
+        cudaEvent_t b = prof_event(ctx);
+        cudaEventRecord(b, st);
+        ctx->prof.pending.push_back({ph, a, b});
+        ctx->prof.launches[ph] += g_launches.load() - l0;
+    }
+};
 
 static int read_dev_err(afqmc_ctx* ctx, Walker* w) {
     int h = 0;
@@ -303,6 +356,11 @@ int afqmc_destroy(afqmc_ctx* ctx) {
     }
     for (void* p : ctx->allocs) cudaFree(p);
     for (auto* l : ctx->lats) delete l;
+    for (auto& pe : ctx->prof.pending) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    for (auto e : ctx->prof.pool) cudaEventDestroy(e);
     delete ctx;
     return AFQMC_OK;
 }
@@ -380,9 +438,11 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
             CK(cudaMemcpyAsync(w->x, fields + foff, (size_t)M * N, cudaMemcpyHostToDevice, st));
             foff += (size_t)M * N;
         } else {
+            count_launch();
             fields_kernel<<<(int)(((long)M * N + 255) / 256), 256, 0, st>>>(ctx->p.seed, (uint64_t)wi, (long)M * N, w->x);
             CK(cudaGetLastError());
         }
+        count_launch();
         set_double_kernel<<<1, 1, 0, st>>>(w->sign, 1.0);
         CK(cudaGetLastError());
         // trial determinants -> stacks, G(0)  (Sec. II.B)
@@ -393,6 +453,7 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
             // P into URs[s][0] (N x ns), re-orthonormalised
             double* UR0 = w->URs[s];
             CK(cudaMemcpyAsync(UR0, Ph, (size_t)N * ns * 8, cudaMemcpyHostToDevice, st));
+            count_launch();
             transpose_kernel<<<256, 256, 0, st>>>(UR0, N, ns, w->Ucur);  // Ucur = P^T (ns x N)
             CK(cudaGetLastError());
             CK(stab_right(w, st, s, UR0, w->sign));
@@ -442,15 +503,19 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
     const T* E = (const T*)w->lat->Eb;
     const T* Einv = (const T*)w->lat->Einvb;
     const int NW = window_max<T>();
-    CK(launch_uniforms(st, ctx->p.seed, (uint64_t)wi, w->visit, 2 * N, w->u));
-    CK(cudaMemsetAsync(w->stats, 0, 8 * sizeof(int), st));
-    CK(cudaMemsetAsync(w->maxr, 0, 8, st));
     const uint8_t* rep = nullptr;
-    if (replay) {
-        CK(cudaMemcpyAsync(w->replay, replay + (size_t)wi * 2 * N, 2 * (size_t)N, cudaMemcpyHostToDevice, st));
-        rep = w->replay;
+    {
+        PhaseScope ps(ctx, AFQMC_PHASE_PREP, st);
+        CK(launch_uniforms(st, ctx->p.seed, (uint64_t)wi, w->visit, 2 * N, w->u));
+        CK(cudaMemsetAsync(w->stats, 0, 8 * sizeof(int), st));
+        CK(cudaMemsetAsync(w->maxr, 0, 8, st));
+        if (replay) {
+            CK(cudaMemcpyAsync(w->replay, replay + (size_t)wi * 2 * N, 2 * (size_t)N, cudaMemcpyHostToDevice, st));
+            rep = w->replay;
+        }
     }
     auto wrap = [&](int direction) -> cudaError_t {
+        PhaseScope ps(ctx, AFQMC_PHASE_WRAP, st);
         cudaError_t e = launch_field_scales_T<T>(st, xl, N, ctx->c, d, dinv, N);
         if (e != cudaSuccess) return e;
         GemmArgs<T> g1, g2;
@@ -491,6 +556,16 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
     sp.seed = ctx->p.seed;
     sp.walker = (uint64_t)wi;
     sp.visit = w->visit;
+    for (int s = 0; s < 2; ++s)
+        for (int xi = 0; xi < 2; ++xi) {
+            const double x = xi == 0 ? 1.0 : -1.0;
+            sp.dflip[s][xi] = exp(-2.0 * ctx->c[s] * x) - 1.0;
+            sp.dstrip[s][xi] = exp(-ctx->c[s] * x) - 1.0;
+        }
+    for (int xi = 0; xi < 2; ++xi) {
+        const double x = xi == 0 ? 1.0 : -1.0;
+        sp.sflip[xi] = (ctx->p.hs == AFQMC_HS_CHARGE_REAL) ? exp(2.0 * ctx->lam * x) : 1.0;
+    }
     SliceOut so;
     so.dec = w->dec;
     so.ratio = w->ratio;
@@ -498,6 +573,7 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
     so.maxr = w->maxr;
     so.sign = w->sign;
     if (mode == AFQMC_MODE_LOCAL) {
+        PhaseScope ps(ctx, AFQMC_PHASE_LOCAL, st);
         CK(cudaMemsetAsync(w->bar, 0, sizeof(GridBar), st));
         CK(launch_local<T>(st, G0, G1, xl, w->u, rep, sp, so, (T*)w->colbuf, (T*)w->rowbuf, w->bar, w->err,
                            ctx->nsm));
@@ -512,8 +588,14 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
         wb.Y = w->Y;
         for (int s0 = 0; s0 < N; s0 += nw) {
             int n = (N - s0 < nw) ? N - s0 : nw;
-            CK(launch_window_chain<T>(st, mode, G0, G1, xl, w->u, rep, sp, so, s0, n, nb, wb, w->err));
-            CK(launch_flush<T>(st, G0, G1, sp, wb, n));
+            {
+                PhaseScope ps(ctx, AFQMC_PHASE_CHAIN, st);
+                CK(launch_window_chain<T>(st, mode, G0, G1, xl, w->u, rep, sp, so, s0, n, nb, wb, w->err));
+            }
+            {
+                PhaseScope ps(ctx, AFQMC_PHASE_FLUSH, st);
+                CK(launch_flush<T>(st, G0, G1, sp, wb, n));
+            }
         }
     }
     if (dir < 0) CK(wrap(-1));
@@ -582,6 +664,7 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
     for (int wi = 0; wi < (int)ctx->w.size(); ++wi) {
         Walker* w = ctx->w[wi];
         const int N = w->N, j = w->pos / S;
+        PhaseScope ps(ctx, AFQMC_PHASE_RECOMPUTE, st);
         CK(cudaMemsetAsync(w->acc2, 0, 16, st));
         for (int s = 0; s < 2; ++s) {
             const int ns = w->ns[s];
@@ -732,11 +815,51 @@ int afqmc_get_info(afqmc_ctx* ctx, int walker, int* N, int* n_up, int* n_dn, int
     return AFQMC_OK;
 }
 
+int afqmc_set_profiling(afqmc_ctx* ctx, int on) {
+    if (!ctx) return AFQMC_ERR_ARG;
+    if (ctx->last) cudaStreamSynchronize(ctx->last);
+    for (auto& pe : ctx->prof.pending) {
+        ctx->prof.pool.push_back(pe.a);
+        ctx->prof.pool.push_back(pe.b);
+    }
+    ctx->prof.pending.clear();
+    for (int i = 0; i < AFQMC_NPHASE; ++i) {
+        ctx->prof.ms[i] = 0.0;
+        ctx->prof.intervals[i] = 0;
+        ctx->prof.launches[i] = 0;
+    }
+    ctx->prof.on = on != 0;
+    return AFQMC_OK;
+}
+
+int afqmc_get_profile(afqmc_ctx* ctx, double* ms, int64_t* intervals, int64_t* launches) {
+    if (!ctx) return AFQMC_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->last));
+    for (auto& pe : ctx->prof.pending) {
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, pe.a, pe.b));
+        ctx->prof.ms[pe.phase] += t;
+        ctx->prof.intervals[pe.phase] += 1;
+        ctx->prof.pool.push_back(pe.a);
+        ctx->prof.pool.push_back(pe.b);
+    }
+    ctx->prof.pending.clear();
+    for (int i = 0; i < AFQMC_NPHASE; ++i) {
+        if (ms) ms[i] = ctx->prof.ms[i];
+        if (intervals) intervals[i] = ctx->prof.intervals[i];
+        if (launches) launches[i] = ctx->prof.launches[i];
+    }
+    return AFQMC_OK;
+}
+
+int64_t afqmc_launch_count(void) { return (int64_t)g_launches.load(); }
+
 int afqmc_debug_uniforms(uint64_t seed, uint64_t walker, uint64_t visit, int count, double* host_out) {
     if (count < 0 || (count > 0 && !host_out)) return AFQMC_ERR_ARG;
     if (count == 0) return AFQMC_OK;
     double* d = nullptr;
     if (cudaMalloc(&d, (size_t)count * 8) != cudaSuccess) return AFQMC_ERR_OOM;
+    count_launch();
     debug_uniforms_kernel<<<(count + 255) / 256, 256>>>(seed, walker, visit, count, d);
     cudaError_t e = cudaMemcpy(host_out, d, (size_t)count * 8, cudaMemcpyDeviceToHost);
     cudaFree(d);

@@ -90,6 +90,7 @@ template <typename T>
 cudaError_t gemm(cudaStream_t st, const GemmArgs<T>& g) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
+    count_launch();
     gemm_kernel<T><<<grid, NT, 0, st>>>(g);
     return cudaGetLastError();
 }

@@ -9,6 +9,9 @@
 
 namespace afq {
 
+// Every kernel launch site calls count_launch() (the counter behind afqmc_launch_count()).
+void count_launch(int n = 1);
+
 // Row-major batched GEMM with diagonal scalings (all pointers device):
 //   C[z] = alpha * diag(rs[z]) * A[z] * diag(bs[z]) * B[z] * diag(cs[z]) + beta * C[z]
 // A is M x K (lda), B is K x N (ldb), C is M x N (ldc).  Null scale pointers
@@ -64,6 +67,12 @@ cudaError_t launch_energy(cudaStream_t st, const T* Gu, const T* Gd, long ld, in
                           double* out);
 
 // ---- sweep kernels (sweep.cu) ----
+// Per-slice constants of the site loop.  The field-change factors depend only on the
+// spin and the current field value, so they are four numbers computed once on the host:
+//   dflip[s][xi]  = exp(-2 c_s x) - 1   (flip x -> -x; Sec. II.D)
+//   dstrip[s][xi] = exp(-c_s x) - 1     (remove the field: the stripped force bias, Sec. III.B)
+//   sflip[xi]     = s(-x) / s(x)        (scalar prefactor of the decoupling)
+// with xi = 0 for x = +1 and xi = 1 for x = -1.
 struct SiteParams {
     int N;
     long ld;
@@ -71,6 +80,9 @@ struct SiteParams {
     double lam;      // HS coupling (for the scalar prior of the charge channel)
     int hs;
     uint64_t seed, walker, visit;
+    double dflip[2][2];
+    double dstrip[2][2];
+    double sflip[2];
 };
 
 struct SliceOut {      // device-side per-walker outputs of one slice

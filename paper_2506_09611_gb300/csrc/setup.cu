@@ -34,6 +34,7 @@ __global__ void expK_kernel(int L, double t, double tau, double* E, long ld) {
 }
 
 cudaError_t launch_expK(cudaStream_t st, int L, double t, double tau, double* E, long ld) {
+    count_launch();
     expK_kernel<<<256, 256, L * sizeof(double), st>>>(L, t, tau, E, ld);
     return cudaGetLastError();
 }
@@ -47,6 +48,7 @@ __global__ void cast_kernel(const double* src, long lds, T* dst, long ldd, int r
 }
 template <typename T>
 cudaError_t launch_cast(cudaStream_t st, const double* src, long lds, T* dst, long ldd, int rows, int cols) {
+    count_launch();
     cast_kernel<T><<<512, 256, 0, st>>>(src, lds, dst, ldd, rows, cols);
     return cudaGetLastError();
 }
@@ -62,6 +64,7 @@ __global__ void to_double_kernel(const T* src, long lds, double* dst, long ldd, 
 }
 template <typename T>
 cudaError_t launch_to_double(cudaStream_t st, const T* src, long lds, double* dst, long ldd, int rows, int cols) {
+    count_launch();
     to_double_kernel<T><<<512, 256, 0, st>>>(src, lds, dst, ldd, rows, cols);
     return cudaGetLastError();
 }
@@ -81,6 +84,7 @@ __global__ void field_scales_kernel(const int8_t* x, int N, double c0, double c1
 }
 template <typename T>
 cudaError_t launch_field_scales_T(cudaStream_t st, const int8_t* x, int N, const double* c2, T* d, T* dinv, long sd) {
+    count_launch();
     field_scales_kernel<T><<<(N + 255) / 256, 256, 0, st>>>(x, N, c2[0], c2[1], d, dinv, sd);
     return cudaGetLastError();
 }
@@ -232,6 +236,7 @@ cudaError_t launch_elim(cudaStream_t st, int mode, double* A, int R, int C, long
     cudaError_t e = cudaMemsetAsync(sc, 0, sizeof(ElimScratch), st);
     if (e != cudaSuccess) return e;
     void* args[] = {&mode, &A, &R, &C, &rs, &cs, &nrhs, &perm, &sign_out, &sc, &err};
+    count_launch();
     return cudaLaunchCooperativeKernel((void*)elim_kernel, dim3(nblk), dim3(256), args, 0, st);
 }
 
@@ -244,6 +249,7 @@ __global__ void gj_extract_kernel(const double* A, long ld, int R, int nrhs, con
 }
 cudaError_t launch_gj_extract(cudaStream_t st, const double* A, long ld, int R, int nrhs, const int* perm, double* Z,
                               long ldz) {
+    count_launch();
     gj_extract_kernel<<<512, 256, 0, st>>>(A, ld, R, nrhs, perm, Z, ldz);
     return cudaGetLastError();
 }
@@ -257,6 +263,7 @@ __global__ void identity_minus_kernel(T* G, long ld, int N) {
 }
 template <typename T>
 cudaError_t launch_identity_minus(cudaStream_t st, T* G, long ld, int N) {
+    count_launch();
     identity_minus_kernel<T><<<512, 256, 0, st>>>(G, ld, N);
     return cudaGetLastError();
 }
@@ -285,6 +292,7 @@ __global__ void drift_kernel(const T* Gold, const double* Gnew, long ld, int N, 
 }
 template <typename T>
 cudaError_t launch_drift(cudaStream_t st, const T* Gold, const T* Gnew, long ld, int N, double* acc2) {
+    count_launch();
     drift_kernel<T><<<256, 256, 0, st>>>(Gold, (const double*)Gnew, ld, N, acc2);
     return cudaGetLastError();
 }
@@ -313,6 +321,7 @@ __global__ void energy_kernel(const T* Gu, const T* Gd, long ld, int L, double t
 }
 template <typename T>
 cudaError_t launch_energy(cudaStream_t st, const T* Gu, const T* Gd, long ld, int L, double t, double U, double* out) {
+    count_launch();
     energy_kernel<T><<<64, 256, 0, st>>>(Gu, Gd, ld, L, t, U, out);
     return cudaGetLastError();
 }

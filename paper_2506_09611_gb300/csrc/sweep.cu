@@ -27,6 +27,7 @@ __global__ void uniforms_kernel(uint64_t seed, uint64_t walker, uint64_t visit, 
 
 cudaError_t launch_uniforms(cudaStream_t st, uint64_t seed, uint64_t walker, uint64_t visit, int count,
                             double* u) {
+    count_launch();
     uniforms_kernel<<<(count + 255) / 256, 256, 0, st>>>(seed, walker, visit, count, u);
     return cudaGetLastError();
 }
@@ -47,6 +48,8 @@ __global__ void __launch_bounds__(512) local_kernel(T* Gu, T* Gd, int8_t* xl_g, 
                                                     T* colbuf, T* rowbuf, GridBar* bar, int* err) {
     extern __shared__ unsigned char smem_raw[];
     int8_t* xs = (int8_t*)smem_raw;
+    __shared__ int s_acc;
+    __shared__ T s_f[2];
     const int N = sp.N;
     const long ld = sp.ld;
     const int nblk = gridDim.x, b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
@@ -69,49 +72,59 @@ __global__ void __launch_bounds__(512) local_kernel(T* Gu, T* Gd, int8_t* xl_g, 
     double sign = so.sign ? *so.sign : 1.0;
     int n_acc = 0;
     double maxr = 0.0;
+    const int per_spin = nrows * N;
     for (int i = 0; i < N; ++i) {
         const int cur = i & 1, nxt = cur ^ 1;
         const T* col0 = colbuf + (cur * 2 + 0) * N;
         const T* col1 = colbuf + (cur * 2 + 1) * N;
         const T* row0 = rowbuf + (cur * 2 + 0) * N;
         const T* row1 = rowbuf + (cur * 2 + 1) * N;
-        const int x = xs[i], xp = -x;
-        double R = exp(hs_log_scalar(sp, xp) - hs_log_scalar(sp, x));
-        double d0 = field_delta(sp.c[0], x, xp), d1 = field_delta(sp.c[1], x, xp);
-        double rr0 = 1.0 + d0 * (1.0 - (double)col0[i]);
-        double rr1 = 1.0 + d1 * (1.0 - (double)col1[i]);
-        R *= rr0 * rr1;
-        bool acc = replay ? (replay[i] != 0) : (u[i] < fabs(R));
-        if (!isfinite(R)) {
-            if (b == 0 && tid == 0) set_err(err, DEV_NUMERIC);
-            acc = false;
-        }
-        if (b == 0 && tid == 0) {
-            so.dec[i] = acc ? 1 : 0;
-            so.ratio[i] = R;
-            if (acc) {
-                xl_g[i] = (int8_t)xp;
-                if (R < 0) sign = -sign;
+        // one thread per CTA takes the Metropolis decision (every CTA reaches the same one)
+        if (tid == 0) {
+            const int xi = xs[i] > 0 ? 0 : 1;
+            const double rr0 = 1.0 + sp.dflip[0][xi] * (1.0 - (double)col0[i]);
+            const double rr1 = 1.0 + sp.dflip[1][xi] * (1.0 - (double)col1[i]);
+            const double R = sp.sflip[xi] * rr0 * rr1;
+            bool acc = replay ? (replay[i] != 0) : (u[i] < fabs(R));
+            if (!isfinite(R)) {
+                if (b == 0) set_err(err, DEV_NUMERIC);
+                acc = false;
+            }
+            s_acc = acc ? 1 : 0;
+            s_f[0] = (T)(sp.dflip[0][xi] / rr0);
+            s_f[1] = (T)(sp.dflip[1][xi] / rr1);
+            if (b == 0) {
+                so.dec[i] = acc ? 1 : 0;
+                so.ratio[i] = R;
+                if (acc) {
+                    xl_g[i] = (int8_t)(-xs[i]);
+                    if (R < 0) sign = -sign;
+                    maxr = fmax(maxr, fabs(R));
+                }
             }
         }
-        if (acc) {
+        __syncthreads();
+        if (s_acc) {
             ++n_acc;
-            maxr = fmax(maxr, fabs(R));
-            const T f0 = (T)(d0 / rr0), f1 = (T)(d1 / rr1);
-            const int tot = 2 * nrows * N;
-            for (int e = tid; e < tot; e += nt) {
-                const int s = e / (nrows * N);
-                const int rem = e - s * nrows * N;
-                const int r = r0 + rem / N, c = rem % N;
+            // G_s[r, c] -= f_s * G_s[r, i] * (delta_ic - G_s[i, c]) over the own rows of both spins
+            for (int s = 0; s < 2; ++s) {
                 const T* cl = s ? col1 : col0;
                 const T* rw = s ? row1 : row0;
-                const T f = s ? f1 : f0;
-                const T rowv = (c == i ? T(1) : T(0)) - rw[c];
-                T* gp = G[s] + (long)r * ld + c;
-                const T nv = *gp - f * cl[r] * rowv;
-                *gp = nv;
-                if (c == i + 1) colbuf[(nxt * 2 + s) * N + r] = nv;
-                if (r == i + 1) rowbuf[(nxt * 2 + s) * N + c] = nv;
+                const T f = s_f[s];
+                T* Gsp = G[s];
+                int r = r0 + tid / N, c = tid % N;
+                const int rstep = nt / N, cstep = nt % N;
+                for (int e = tid; e < per_spin; e += nt) {
+                    const T rowv = (c == i ? T(1) : T(0)) - rw[c];
+                    T* gp = Gsp + (long)r * ld + c;
+                    const T nv = *gp - f * cl[r] * rowv;
+                    *gp = nv;
+                    if (c == i + 1) colbuf[(nxt * 2 + s) * N + r] = nv;
+                    if (r == i + 1) rowbuf[(nxt * 2 + s) * N + c] = nv;
+                    r += rstep;
+                    c += cstep;
+                    if (c >= N) { c -= N; ++r; }
+                }
             }
         } else if (i + 1 < N) {
             for (int e = tid; e < 2 * nrows; e += nt) {
@@ -143,6 +156,7 @@ cudaError_t launch_local(cudaStream_t st, T* Gu, T* Gd, int8_t* xl, const double
     size_t shm = (size_t)sp.N;
     SiteParams spc = sp;
     void* args[] = {&Gu, &Gd, &xl, &u, &replay, &spc, &so, &colbuf, &rowbuf, &bar, &err};
+    count_launch();
     return cudaLaunchCooperativeKernel((void*)local_kernel<T>, dim3(nblk), dim3(512), args, shm, st);
 }
 
@@ -213,57 +227,90 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
     if (tid == 0) s_m = 0;
     __syncthreads();
 
-    double sign = so.sign ? *so.sign : 1.0;
+    __shared__ double s_sign, s_maxr;  // walker sign and max |R|, owned by one thread at a time
+    if (tid == 0) {
+        s_sign = so.sign ? *so.sign : 1.0;
+        s_maxr = 0.0;
+    }
+    __syncthreads();
     int n_prop = 0, n_acc = 0, n_flip = 0;
-    double maxr = 0.0;
 
     if (MODE == AFQMC_MODE_DELAYED) {
-        for (int p = 0; p < n; ++p) {
-            const int i = s0 + p;
-            const int x = xw[p], xp = -x;
-            double R = exp(hs_log_scalar(sp, xp) - hs_log_scalar(sp, x));
-            const double d0 = field_delta(sp.c[0], x, xp), d1 = field_delta(sp.c[1], x, xp);
-            const double r0 = 1.0 + d0 * (1.0 - (double)Gs[(0 * n + p) * P + p]);
-            const double r1 = 1.0 + d1 * (1.0 - (double)Gs[(1 * n + p) * P + p]);
-            R *= r0 * r1;
-            bool acc = replay ? (replay[i] != 0) : (u[i] < fabs(R));
-            if (!isfinite(R)) acc = false;
-            ++n_prop;
-            if (tid == 0) {
-                so.dec[i] = acc ? 1 : 0;
-                so.ratio[i] = R;
-                if (!isfinite(R)) set_err(err, DEV_NUMERIC);
+        // Warp-serial Metropolis: rejections leave G unchanged, so warp 0 evaluates the next
+        // 32 sites on the current block at once and a ballot finds the first acceptance.
+        __shared__ int s_next, s_apos;
+        __shared__ T s_fa[2];
+        int p = 0;
+        while (p < n) {
+            if (tid < 32) {
+                const int q = p + tid;
+                bool acc = false;
+                double R = 0.0, rr0 = 1.0, rr1 = 1.0;
+                int xi = 0;
+                if (q < n) {
+                    const int i = s0 + q;
+                    xi = xw[q] > 0 ? 0 : 1;
+                    rr0 = 1.0 + sp.dflip[0][xi] * (1.0 - (double)Gs[(0 * n + q) * P + q]);
+                    rr1 = 1.0 + sp.dflip[1][xi] * (1.0 - (double)Gs[(1 * n + q) * P + q]);
+                    R = sp.sflip[xi] * rr0 * rr1;
+                    acc = replay ? (replay[i] != 0) : (u[i] < fabs(R));
+                    if (!isfinite(R)) {
+                        acc = false;
+                        set_err(err, DEV_NUMERIC);
+                    }
+                }
+                const unsigned ball = __ballot_sync(0xffffffffu, acc);
+                const int first = ball ? __ffs(ball) - 1 : 32;
+                if (q < n && tid <= first) {
+                    so.dec[s0 + q] = (tid == first) ? 1 : 0;
+                    so.ratio[s0 + q] = R;
+                }
+                if (tid == first) {
+                    s_fa[0] = (T)(sp.dflip[0][xi] / rr0);
+                    s_fa[1] = (T)(sp.dflip[1][xi] / rr1);
+                    idx[s_m] = q;
+                    dl[0 * n + s_m] = sp.dflip[0][xi];
+                    dl[1 * n + s_m] = sp.dflip[1][xi];
+                    s_m = s_m + 1;
+                    if (R < 0) s_sign = -s_sign;
+                    s_maxr = fmax(s_maxr, fabs(R));
+                }
+                if (tid == 0) {
+                    s_apos = (first < 32) ? q + first : -1;
+                    s_next = (first < 32) ? q + first + 1 : min(n, q + 32);
+                }
             }
-            if (!acc) continue;
-            // trailing update of the block: G[a][b] += (d/r) G[a][p] G[p][b], a, b > p
-            const T f0 = (T)(d0 / r0), f1 = (T)(d1 / r1);
-            const int q = n - p - 1;
-            for (int e = tid; e < 2 * q * q; e += nt) {
-                int s = e / (q * q), rem = e % (q * q);
-                int a = p + 1 + rem / q, c = p + 1 + rem % q;
-                T* Gb = Gs + s * n * P;
-                Gb[a * P + c] += (s ? f1 : f0) * Gb[a * P + p] * Gb[p * P + c];
-            }
-            if (tid == 0) {
-                idx[s_m] = p;
-                dl[0 * n + s_m] = d0;
-                dl[1 * n + s_m] = d1;
-                s_m = s_m + 1;
-                if (R < 0) sign = -sign;
-            }
+            __syncthreads();
+            const int a = s_apos;
+            n_prop += s_next - p;
+            p = s_next;
+            if (a < 0) continue;
             ++n_acc;
             ++n_flip;
-            maxr = fmax(maxr, fabs(R));
+            // trailing update of the block: G[r][c] += (d/r) G[r][a] G[a][c], r, c > a
+            const T f0 = s_fa[0], f1 = s_fa[1];
+            const int qn = n - a - 1;
+            for (int e = tid; e < 2 * qn * qn; e += nt) {
+                int sp2 = e / (qn * qn), rem = e - sp2 * qn * qn;
+                int r = a + 1 + rem / qn, c = a + 1 + rem % qn;
+                T* Gb = Gs + sp2 * n * P;
+                Gb[r * P + c] += (sp2 ? f1 : f0) * Gb[r * P + a] * Gb[a * P + c];
+            }
             __syncthreads();
         }
     } else {
         // ---- block force-bias (Sec. III.B) ----
+        __shared__ T s_fs[2];
+        __shared__ double s_rs[2];
+        __shared__ int s_accb;
+        __shared__ T s_phi[2][NBMAX];
         T* stcol = stc;          // [2][n]
         T* strow = stc + 2 * n;  // [2][n]
         for (int p0 = 0; p0 < n; p0 += nb) {
             const int nbk = min(nb, n - p0);
             const int blk = (s0 + p0) / nb;
-            // (a) stripped force bias: remove the block's fields one site at a time
+            // (a) stripped force bias (Eq. BlkFrcBsTnew1): remove the block's fields one site at a time,
+            //     each a rank-1 step G <- G - (d/r) G_{:,a} (e_a^T - G_{a,:}) with d = exp(-c x_a) - 1
             for (int e = tid; e < 2 * nbk * nbk; e += nt) {
                 int s = e / (nbk * nbk), rem = e % (nbk * nbk), a = rem / nbk, c = rem % nbk;
                 S1[(s * NBMAX + a) * (NBMAX + 1) + c] = Gs[(s * n + p0 + a) * P + p0 + c];
@@ -276,15 +323,17 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                     stb[s * NBMAX + c] = Sb[c * (NBMAX + 1) + a];                       // column a
                     strow[s * n + c] = (c == a ? T(1) : T(0)) - Sb[a * (NBMAX + 1) + c];  // e_a^T - row a
                 }
+                if (tid < 2) {
+                    const int xi = xw[p0 + a] > 0 ? 0 : 1;
+                    const double db = sp.dstrip[tid][xi];
+                    const double rr = 1.0 + db * (1.0 - (double)S1[(tid * NBMAX + a) * (NBMAX + 1) + a]);
+                    s_fs[tid] = (T)(db / rr);
+                }
                 __syncthreads();
-                const int xa = xw[p0 + a];
                 for (int e = tid; e < 2 * nbk * nbk; e += nt) {
                     int s = e / (nbk * nbk), rem = e % (nbk * nbk), r = rem / nbk, c = rem % nbk;
                     T* Sb = S1 + s * NBMAX * (NBMAX + 1);
-                    double db = exp(-sp.c[s] * (double)xa) - 1.0;
-                    double rr = 1.0 + db * (1.0 - (double)stb[s * NBMAX + a]);
-                    T f = (T)(db / rr);
-                    Sb[r * (NBMAX + 1) + c] -= f * stb[s * NBMAX + r] * strow[s * n + c];
+                    Sb[r * (NBMAX + 1) + c] -= s_fs[s] * stb[s * NBMAX + r] * strow[s * n + c];
                 }
                 __syncthreads();
             }
@@ -319,6 +368,8 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                     }
                 s_nF = nF;
                 s_R = exp(lpr);
+                s_rs[0] = 1.0;
+                s_rs[1] = 1.0;
             }
             __syncthreads();
             const int nF = s_nF;
@@ -331,56 +382,55 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                 ++n_acc;
                 continue;
             }
-            // (c) determinant ratio det(1 + D_F A_FF) as a product of sequential rank-1 ratios
+            // (c) det(1 + D_F A_FF) (Eq. BlkFrcBsTnew2's ratio) as the product of sequential rank-1 ratios
             for (int e = tid; e < 2 * nbk * nbk; e += nt) {
                 int s = e / (nbk * nbk), rem = e % (nbk * nbk), a = rem / nbk, c = rem % nbk;
                 S1[(s * NBMAX + a) * (NBMAX + 1) + c] = Gs[(s * n + p0 + a) * P + p0 + c];
             }
             __syncthreads();
-            double rs0 = 1.0, rs1 = 1.0;
             for (int q = 0; q < nF; ++q) {
                 const int a = s_F[q];
-                const int xa = xw[p0 + a];
                 for (int e = tid; e < 2 * nbk; e += nt) {
                     int s = e / nbk, c = e % nbk;
                     T* Sb = S1 + s * NBMAX * (NBMAX + 1);
                     stb[s * NBMAX + c] = Sb[c * (NBMAX + 1) + a];
                     strow[s * n + c] = (c == a ? T(1) : T(0)) - Sb[a * (NBMAX + 1) + c];
                 }
+                if (tid < 2) {
+                    const int xi = xw[p0 + a] > 0 ? 0 : 1;
+                    const double dd = sp.dflip[tid][xi];
+                    const double rr = 1.0 + dd * (1.0 - (double)S1[(tid * NBMAX + a) * (NBMAX + 1) + a]);
+                    s_rs[tid] *= rr;
+                    s_phi[tid][q] = (T)(dd / rr);
+                    fb[(4 + tid) * NBMAX + q] = dd;
+                }
                 __syncthreads();
-                double dd[2], rr[2];
-                for (int s = 0; s < 2; ++s) {
-                    dd[s] = field_delta(sp.c[s], xa, -xa);
-                    rr[s] = 1.0 + dd[s] * (1.0 - (double)stb[s * NBMAX + a]);
-                }
-                rs0 *= rr[0];
-                rs1 *= rr[1];
-                if (tid == 0) {
-                    fb[2 * NBMAX + q] = dd[0] / rr[0];
-                    fb[3 * NBMAX + q] = dd[1] / rr[1];
-                    fb[4 * NBMAX + q] = dd[0];
-                    fb[5 * NBMAX + q] = dd[1];
-                }
                 for (int e = tid; e < 2 * nbk * nbk; e += nt) {
                     int s = e / (nbk * nbk), rem = e % (nbk * nbk), r = rem / nbk, c = rem % nbk;
                     T* Sb = S1 + s * NBMAX * (NBMAX + 1);
-                    Sb[r * (NBMAX + 1) + c] -= (T)(dd[s] / rr[s]) * stb[s * NBMAX + r] * strow[s * n + c];
+                    Sb[r * (NBMAX + 1) + c] -= s_phi[s][q] * stb[s * NBMAX + r] * strow[s * n + c];
                 }
                 __syncthreads();
             }
-            const double R = s_R * rs0 * rs1;
-            bool acc = replay ? (replay[N + blk] != 0) : (u[N + blk] < fabs(R));
-            if (!isfinite(R)) acc = false;
             if (tid == 0) {
+                const double R = s_R * s_rs[0] * s_rs[1];
+                bool acc = replay ? (replay[N + blk] != 0) : (u[N + blk] < fabs(R));
+                if (!isfinite(R)) {
+                    acc = false;
+                    set_err(err, DEV_NUMERIC);
+                }
                 so.dec[N + blk] = acc ? 1 : 0;
                 so.ratio[N + blk] = R;
-                if (!isfinite(R)) set_err(err, DEV_NUMERIC);
+                s_accb = acc ? 1 : 0;
+                if (acc) {
+                    if (R < 0) s_sign = -s_sign;
+                    s_maxr = fmax(s_maxr, fabs(R));
+                }
             }
-            if (!acc) continue;
+            __syncthreads();
+            if (!s_accb) continue;
             ++n_acc;
             n_flip += nF;
-            maxr = fmax(maxr, fabs(R));
-            if (tid == 0 && R < 0) sign = -sign;
             // (d) apply the flips to the trailing block [p0, n)^2 of the window, one rank-1 step each
             const int q0 = p0, w = n - p0;
             for (int q = 0; q < nF; ++q) {
@@ -395,7 +445,7 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                 for (int e = tid; e < 2 * w * w; e += nt) {
                     int s = e / (w * w), rem = e % (w * w), r = q0 + rem / w, c = q0 + rem % w;
                     T* Gb = Gs + s * n * P;
-                    Gb[r * P + c] -= (T)fb[(2 + s) * NBMAX + q] * stcol[s * n + r] * strow[s * n + c];
+                    Gb[r * P + c] -= s_phi[s][q] * stcol[s * n + r] * strow[s * n + c];
                 }
                 if (tid == 0) {
                     idx[s_m] = a;
@@ -422,12 +472,12 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
     }
     if (tid == 0) {
         *wb.m = m;
-        if (so.sign) *so.sign = sign;
+        if (so.sign) *so.sign = s_sign;
         so.stats[0] += n_prop;
         so.stats[1] += n_acc;
         so.stats[2] += n_flip;
         so.stats[3] += (m > 0) ? 1 : 0;
-        *so.maxr = fmax(*so.maxr, maxr);
+        *so.maxr = fmax(*so.maxr, s_maxr);
     }
     __syncthreads();
     if (m == 0) return;
@@ -447,20 +497,20 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
         __syncthreads();
         for (int k = 0; k < m; ++k) {
             if (tid < 32) {  // pivot search in column k, rows k..m-1
-                double best = -1.0;
+                T best = T(-1);
                 int br = k;
                 for (int r = k + tid; r < m; r += 32) {
-                    double v = fabs((double)Aug[r * AP + k]);
+                    T v = fabs(Aug[r * AP + k]);
                     if (v > best) { best = v; br = r; }
                 }
                 for (int o = 16; o > 0; o >>= 1) {
-                    double ob = __shfl_down_sync(0xffffffffu, best, o);
+                    T ob = __shfl_down_sync(0xffffffffu, best, o);
                     int orr = __shfl_down_sync(0xffffffffu, br, o);
                     if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
                 }
                 if (tid == 0) {
                     s_piv = br;
-                    if (!(best > 0.0)) set_err(err, DEV_NUMERIC);
+                    if (!(best > T(0))) set_err(err, DEV_NUMERIC);
                 }
             }
             __syncthreads();
@@ -508,6 +558,7 @@ cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T*
         if (e != cudaSuccess) return e;
         attr_set[mi] = true;
     }
+    count_launch();
     if (mode == AFQMC_MODE_DELAYED)
         window_kernel<T, AFQMC_MODE_DELAYED><<<1, WIN_THREADS, shm, st>>>(Gu, Gd, xl, u, replay, sp, so, s0, n, nb,
                                                                           wb, err);
@@ -541,6 +592,7 @@ template <typename T>
 cudaError_t launch_flush(cudaStream_t st, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw) {
     const int N = sp.N;
     const int NWC = WinCap<T>::NW;
+    count_launch();
     gather_kernel<T><<<dim3(256, 2), 256, 0, st>>>(Gu, Gd, sp.ld, N, wb, NWC);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -170,28 +170,47 @@ def test_charge_channel_fp64():
         _run_sweep.__doc__  # keep flake quiet
 
 
-def test_full_size_40x40_first_slice():
-    """40x40 (N = 1600, 700 per spin) in the launch configuration of the bench: G(0) from the
-    device FP64 init is checked by the projector invariants; one forward delayed slice on the
-    device is compared decision by decision with the oracle's local update started from the
-    same G(0) and the same uniforms."""
-    L, ns, M = 40, 700, 80
+def test_full_size_40x40_first_slices():
+    """40x40 (N = 1600, 700 per spin) with the kernels and launch configuration of the bench
+    (delayed windows of 64 sites; FP64 here, FP32 replay below).  M = 10 keeps the oracle's own
+    FP64 G(0) cheap; the slice kernels do not depend on M.  G(0), the decisions of two forward
+    slices and G after each are compared with the oracle; projector invariants hold."""
+    L, ns, M, stab = 40, 700, 10, 10
     N = L * L
     P = inputs.trial_state(L, L, ns)
     X = inputs.initial_fields(M, N, seed=1)
-    with afqmc.Context(M, U=6.0, precision="fp64", stab_every=10, seed=1) as ctx:
+    model = oracle.Model(L, L, 1.0, 6.0, 0.05, M)
+    w = oracle.Walker(model, P, P, X)
+    with afqmc.Context(M, U=6.0, precision="fp64", stab_every=stab, seed=1) as ctx:
         ctx.init_walkers([L], [ns], [ns], np.concatenate([P.ravel(), P.ravel()]), X)
-        G0 = [ctx.G(0, s) for s in range(2)]
         for s in range(2):
-            assert abs(np.trace(np.eye(N) - G0[s]) - ns) < 1e-8
-            sample = np.random.default_rng(0).choice(N, 64, replace=False)
-            GG = G0[s][sample] @ G0[s]
-            np.testing.assert_allclose(GG, G0[s][sample], atol=1e-9)
-        model = oracle.Model(L, L, 1.0, 6.0, 0.05, M)
-        Gw = [model.wrap(G0[s], X[0], s, +1) for s in range(2)]
-        u = inputs.uniforms(1, 0, 0, 2 * N)
-        Gu, Gd, xl, dec, ratio, sg = model.local_slice(Gw[0], Gw[1], X[0], u)
-        ctx.sweep_slice(1, +1, "delayed", k=64)
-        np.testing.assert_array_equal(ctx.decisions(0)[:N], dec)
-        assert rel(ctx.G(0, 0), Gu) < FP64_TOL
-        assert rel(ctx.G(0, 1), Gd) < FP64_TOL
+            G0 = ctx.G(0, s)
+            assert rel(G0, w.G[s]) < FP64_TOL
+            assert abs(np.trace(np.eye(N) - G0) - ns) < 1e-8
+        for ell in (1, 2):
+            u = inputs.uniforms(1, 0, ell - 1, 2 * N)
+            dec, _, _ = w.sweep_slice(ell, +1, "delayed", u, k=64)
+            ctx.sweep_slice(ell, +1, "delayed", k=64)
+            np.testing.assert_array_equal(ctx.decisions(0)[:N], dec)
+            for s in range(2):
+                assert rel(ctx.G(0, s), w.G[s]) < FP64_TOL
+
+
+def test_full_size_40x40_fp32_replay():
+    L, ns, M, stab = 40, 700, 10, 10
+    N = L * L
+    P = inputs.trial_state(L, L, ns)
+    X = inputs.initial_fields(M, N, seed=2)
+    model = oracle.Model(L, L, 1.0, 6.0, 0.05, M)
+    w = oracle.Walker(model, P, P, X)
+    with afqmc.Context(M, U=6.0, precision="fp32", stab_every=stab, seed=2) as ctx:
+        ctx.init_walkers([L], [ns], [ns], np.concatenate([P.ravel(), P.ravel()]), X)
+        for ell in (1, 2, 3):
+            u = inputs.uniforms(2, 0, ell - 1, 2 * N)
+            dec, _, _ = w.sweep_slice(ell, +1, "delayed", u, k=64)
+            rep = np.zeros(2 * N, np.uint8)
+            rep[:N] = dec
+            ctx.sweep_slice(ell, +1, "delayed", k=64, replay=rep)
+            for s in range(2):
+                r = rel(ctx.G(0, s), w.G[s])
+                assert r < FP32_TOL, (ell, s, r)
