@@ -142,6 +142,21 @@ int afqmc_get_info(afqmc_ctx* ctx, int walker, int* N, int* n_up, int* n_dn, int
  * out[j] = u(seed, walker, visit, j) for j < count (device generator, copied to the host). */
 int afqmc_debug_uniforms(uint64_t seed, uint64_t walker, uint64_t visit, int count, double* host_out);
 
+/* Apply accepted field changes at the sites I to both spins' G in one rank-m product -- the G form
+ * of the delayed flush (Eq. FinalDelay) and of the block force-bias upgrade (Eq. BlkFrcBsTnew2):
+ *     G_s <- G_s - G_s[:, I] W_s (E_I^T - G_s[I, :]),  W_s = D_s (1 + (1 - G_s[I, I]) D_s)^{-1}.
+ * Stateless (no context).  All pointers are device pointers, caller-owned:
+ *   G_up, G_dn  N x N row-major with leading dimension ld (>= N), double for AFQMC_PREC_FP64 and
+ *               float for AFQMC_PREC_FP32; updated in place.
+ *   sites       m distinct site indices in [0, N), in the order the changes were accepted.
+ *   delta       2*m doubles, delta[s*m + a] = exp(c_s (x'_a - x_a)) - 1 (spin s = 0 up, 1 down).
+ *   m           0 <= m <= 128 (FP32) or 64 (FP64); 0 is a no-op.
+ * Work is enqueued on `stream`; device scratch comes from cudaMallocAsync on that stream and is freed
+ * there.  Returns AFQMC_ERR_ARG for bad sizes or null pointers; a site outside [0, N) makes the call
+ * a no-op on the device; a singular (1 + (1 - G_II) D) leaves non-finite values in G. */
+int afqmc_apply_flips(int precision, int N, long long ld, void* G_up, void* G_dn, const int* sites,
+                      const double* delta, int m, void* stream);
+
 /* Profiling.  With profiling on, every phase of afqmc_sweep_slice / afqmc_recompute_G is
  * bracketed by CUDA events recorded on the call's stream (the stream its kernels run on).
  * Phases: */

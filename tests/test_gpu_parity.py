@@ -214,3 +214,46 @@ def test_full_size_40x40_fp32_replay():
             for s in range(2):
                 r = rel(ctx.G(0, s), w.G[s])
                 assert r < FP32_TOL, (ell, s, r)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
+def test_apply_flips_matches_oracle(precision, tol):
+    """afqmc_apply_flips (stateless Woodbury rank-m update) = the oracle's sequential rank-1
+    updates with the same sites forced to accept; m = 0 and an out-of-range site are no-ops."""
+    torch = pytest.importorskip("torch")
+    L, ns, M, ell = 6, 15, 6, 3
+    N = L * L
+    P = inputs.trial_state(L, L, ns)
+    X = inputs.initial_fields(M, N, seed=9)
+    model = oracle.Model(L, L, 1.0, 6.0, 0.05, M)
+    G = [model.green_scratch(X, P, s, ell)[0] for s in range(2)]
+    sites = np.array([2, 5, 11, 12, 30, 35], np.int32)
+    rep = np.zeros(N, np.uint8)
+    rep[sites] = 1
+    Gu_ref, Gd_ref, _, _, _, _ = model.local_slice(G[0], G[1], X[ell - 1], np.zeros(N), replay=rep)
+    x = X[ell - 1, sites].astype(np.float64)
+    delta = np.concatenate([np.exp(-2.0 * model.c[s] * x) - 1.0 for s in range(2)])
+    ld = N + 7
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    Gd_dev = [torch.zeros((N, ld), dtype=dt, device="cuda") for _ in range(2)]
+    for s in range(2):
+        Gd_dev[s][:, :N] = torch.from_numpy(G[s]).to(dt)
+    s_dev = torch.from_numpy(sites).cuda()
+    d_dev = torch.from_numpy(delta).cuda()
+    stream = torch.cuda.current_stream()
+    afqmc.afqmc_apply_flips(precision, N, ld, Gd_dev[0].data_ptr(), Gd_dev[1].data_ptr(), s_dev.data_ptr(),
+                            d_dev.data_ptr(), len(sites), stream)
+    # no-ops
+    afqmc.afqmc_apply_flips(precision, N, ld, Gd_dev[0].data_ptr(), Gd_dev[1].data_ptr(), s_dev.data_ptr(),
+                            d_dev.data_ptr(), 0, stream)
+    bad = torch.tensor([3, N + 4], dtype=torch.int32, device="cuda")
+    afqmc.afqmc_apply_flips(precision, N, ld, Gd_dev[0].data_ptr(), Gd_dev[1].data_ptr(), bad.data_ptr(),
+                            d_dev.data_ptr(), 2, stream)
+    torch.cuda.synchronize()
+    for s, ref in enumerate((Gu_ref, Gd_ref)):
+        got = Gd_dev[s][:, :N].double().cpu().numpy()
+        assert rel(got, ref) < tol
+        assert float(Gd_dev[s][:, N:].abs().max()) == 0.0  # padding untouched
+    with pytest.raises(afqmc.AfqmcError):
+        afqmc.afqmc_apply_flips(precision, N, N - 1, Gd_dev[0].data_ptr(), Gd_dev[1].data_ptr(), s_dev.data_ptr(),
+                                d_dev.data_ptr(), len(sites), stream)
