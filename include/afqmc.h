@@ -157,6 +157,24 @@ int afqmc_debug_uniforms(uint64_t seed, uint64_t walker, uint64_t visit, int cou
 int afqmc_apply_flips(int precision, int N, long long ld, void* G_up, void* G_dn, const int* sites,
                       const double* delta, int m, void* stream);
 
+/* afqmc_apply_flips without any device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory where they apply an update -- code
+ * running under a fixed device-memory budget owned by a host framework, a real-time loop in which
+ * cudaMalloc / cudaMallocAsync (and the synchronisation they may cause) is not allowed, or a plugin
+ * whose host process gives it no allocator.  It computes exactly what afqmc_apply_flips computes,
+ * with the same arguments and limits, plus:
+ *   N <= AFQMC_NOALLOC_MAX_N, else AFQMC_ERR_ARG.
+ * Its scratch is one file-scope __device__ array of about 12.7 MB (enough for N = 4096 in either
+ * precision); every GPU that loads libafqmc.so holds that array until the process exits.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current, so make the first call on each device before any stream capture.  All calls
+ * share the array and it keeps the last call's contents; nothing in it has to start at zero, but
+ * calls whose work overlaps on the GPU (e.g. on two streams) race on it.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine. */
+#define AFQMC_NOALLOC_MAX_N 4096
+int afqmc_apply_flips_noalloc(int precision, int N, long long ld, void* G_up, void* G_dn, const int* sites,
+                              const double* delta, int m, void* stream);
+
 /* Profiling.  With profiling on, every phase of afqmc_sweep_slice / afqmc_recompute_G is
  * bracketed by CUDA events recorded on the call's stream (the stream its kernels run on).
  * Phases: */

@@ -25,7 +25,8 @@ PRECS = {"fp64": PREC_FP64, "fp32": PREC_FP32}
 EXPORTS = ["afqmc_create", "afqmc_destroy", "afqmc_init_walkers", "afqmc_sweep_slice", "afqmc_recompute_G",
            "afqmc_measure_energy", "afqmc_get_G", "afqmc_set_G", "afqmc_get_fields", "afqmc_get_decisions",
            "afqmc_get_ratios", "afqmc_get_info", "afqmc_debug_uniforms", "afqmc_set_profiling",
-           "afqmc_get_profile", "afqmc_launch_count", "afqmc_apply_flips", "afqmc_strerror"]
+           "afqmc_get_profile", "afqmc_launch_count", "afqmc_apply_flips", "afqmc_apply_flips_noalloc",
+           "afqmc_strerror"]
 PHASES = ["prep", "wrap", "local", "chain", "flush", "recompute"]
 
 
@@ -76,6 +77,7 @@ def load(path: str = LIB_PATH):
     lib.afqmc_get_profile.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.afqmc_launch_count.argtypes = []
     lib.afqmc_apply_flips.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, vp, vp, vp, vp, ctypes.c_int, vp]
+    lib.afqmc_apply_flips_noalloc.argtypes = lib.afqmc_apply_flips.argtypes
     lib.afqmc_strerror.argtypes = [ctypes.c_int]
     lib.afqmc_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -216,6 +218,14 @@ def afqmc_apply_flips(precision, N, ld, G_up, G_dn, sites, delta, m, stream=None
     _ck("afqmc_apply_flips", load().afqmc_apply_flips(PRECS.get(precision, precision), N, ld, ctypes.c_void_p(G_up),
                                                       ctypes.c_void_p(G_dn), ctypes.c_void_p(sites),
                                                       ctypes.c_void_p(delta), m, _stream(stream)))
+
+
+def afqmc_apply_flips_noalloc(precision, N, ld, G_up, G_dn, sites, delta, m, stream=None):
+    """Same as afqmc_apply_flips with no device allocation (static device scratch, N <= 4096)."""
+    _ck("afqmc_apply_flips_noalloc",
+        load().afqmc_apply_flips_noalloc(PRECS.get(precision, precision), N, ld, ctypes.c_void_p(G_up),
+                                         ctypes.c_void_p(G_dn), ctypes.c_void_p(sites), ctypes.c_void_p(delta), m,
+                                         _stream(stream)))
 
 
 def afqmc_launch_count():

@@ -183,3 +183,75 @@ extern "C" int afqmc_apply_flips(int precision, int N, long long ld, void* G_up,
     if (e != cudaSuccess || e2 != cudaSuccess) return AFQMC_ERR_CUDA;
     return AFQMC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// No-allocation variant.
+//
+// Some callers cannot allocate device memory at the point where they apply an
+// update: code that runs under a fixed device-memory budget owned by a host
+// framework, code inside a real-time loop where an allocation (and the
+// synchronisation cudaMalloc may imply) is not allowed, or a plugin whose host
+// process gives it no allocator.  afqmc_apply_flips_noalloc does exactly the
+// work of afqmc_apply_flips, with its scratch in the file-scope device array
+// below instead of cudaMallocAsync.
+//
+// The array is sized for lattices up to NOALLOC_MAX_N sites in either
+// precision; every GPU that loads this library holds it until the process
+// exits.  Host code cannot use the array's name as a device address, so the
+// first call on each device looks the address up with cudaGetSymbolAddress
+// while that device is current and caches it.
+// ---------------------------------------------------------------------------
+namespace afq {
+
+constexpr int NOALLOC_MAX_N = 4096;
+
+constexpr size_t noalloc_align(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t noalloc_bytes_for(size_t NW, size_t esz, size_t N) {
+    return 256 + noalloc_align(NW * sizeof(int)) + noalloc_align(2 * NW * NW * esz) + noalloc_align(2 * N * NW * esz) +
+           noalloc_align(4 * NW * N * esz);
+}
+constexpr size_t NOALLOC_BYTES_F32 = noalloc_bytes_for(128, 4, NOALLOC_MAX_N);
+constexpr size_t NOALLOC_BYTES_F64 = noalloc_bytes_for(64, 8, NOALLOC_MAX_N);
+constexpr size_t NOALLOC_BYTES = NOALLOC_BYTES_F32 > NOALLOC_BYTES_F64 ? NOALLOC_BYTES_F32 : NOALLOC_BYTES_F64;
+
+static __device__ __align__(256) unsigned char g_flips_scratch[NOALLOC_BYTES];
+
+}  // namespace afq
+
+#include <mutex>
+
+namespace {
+constexpr int NOALLOC_MAXDEV = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[NOALLOC_MAXDEV] = {};
+}  // namespace
+
+extern "C" int afqmc_apply_flips_noalloc(int precision, int N, long long ld, void* G_up, void* G_dn,
+                                         const int* sites, const double* delta, int m, void* stream) {
+    int rc = afq::flips_check(precision, N, ld, G_up, G_dn, sites, delta, m);
+    if (rc) return rc;
+    if (N > afq::NOALLOC_MAX_N) return AFQMC_ERR_ARG;
+    const size_t need = precision == AFQMC_PREC_FP64 ? afq::flips_scratch_bytes<double>(N)
+                                                     : afq::flips_scratch_bytes<float>(N);
+    if (need > afq::NOALLOC_BYTES) return AFQMC_ERR_ARG;
+    if (m == 0) return AFQMC_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAXDEV) return AFQMC_ERR_CUDA;
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, afq::g_flips_scratch) != cudaSuccess || !p) return AFQMC_ERR_CUDA;
+            g_noalloc_addr[dev] = p;
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = precision == AFQMC_PREC_FP64
+                        ? afq::apply_flips_impl<double>(st, N, (long)ld, (double*)G_up, (double*)G_dn, sites, delta,
+                                                        m, (unsigned char*)scratch)
+                        : afq::apply_flips_impl<float>(st, N, (long)ld, (float*)G_up, (float*)G_dn, sites, delta, m,
+                                                       (unsigned char*)scratch);
+    return e == cudaSuccess ? AFQMC_OK : AFQMC_ERR_CUDA;
+}
