@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--cmp-slices", type=int, default=20, help="slices of the local / block-FB samples")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--gemm", default="tc3", choices=["tc3", "simt", "tf32"],
+                    help="FP32 GEMM engine: tcgen05 three-term TF32 split, FP32 SIMT, or one TF32 pass")
     return ap.parse_args()
 
 
@@ -177,7 +179,7 @@ def main():
     P = inputs.trial_state(L, L, NS)
     X = inputs.initial_fields(M, N, seed=seed)
     Pcat = np.concatenate([P.ravel(), P.ravel()])
-    ctx = afqmc.Context(M, dtau=DTAU, U=U, t=T_HOP, precision="fp32", stab_every=STAB, seed=seed)
+    ctx = afqmc.Context(M, dtau=DTAU, U=U, t=T_HOP, precision="fp32", stab_every=STAB, seed=seed, gemm=args.gemm)
     ctx.init_walkers([L], [NS], [NS], Pcat, X, stream=stream)
     order = [(l, +1) for l in range(1, M + 1)] + [(l, -1) for l in range(M, 0, -1)]
 

@@ -68,7 +68,13 @@ typedef struct {
     double U;           /* Hubbard interaction */
     double dtau;        /* imaginary-time step */
     uint64_t seed;      /* Philox4x64-10 key word 0 (word 1 = walker index) */
+    int gemm;           /* FP32 bulk only: AFQMC_GEMM_* engine of the wrap and flush products */
 } afqmc_params;
+
+/* GEMM engines for the FP32 bulk (FP64 bulk always uses FP64 SIMT products). */
+#define AFQMC_GEMM_TC3 0        /* tcgen05 tensor cores, three-term TF32 split (FP32 accuracy; default) */
+#define AFQMC_GEMM_SIMT 1       /* FP32 FMA pipes */
+#define AFQMC_GEMM_TF32 2       /* tcgen05 tensor cores, one TF32 pass (drift reported, not gated) */
 
 /* Per-walker statistics of the last afqmc_sweep_slice (valid after a stream sync). */
 typedef struct {
@@ -193,6 +199,13 @@ int afqmc_set_profiling(afqmc_ctx* ctx, int on);
 int afqmc_get_profile(afqmc_ctx* ctx, double* ms, int64_t* intervals, int64_t* launches);
 /* Number of library kernels launched by this process so far (every launch site counts). */
 int64_t afqmc_launch_count(void);
+
+/* Validation hook for the tensor-core GEMM: C = A * Bt^T (FP32, device pointers, row-major
+ * A: M x K, Bt: N x K, C: M x N; c_trans = 1 writes C^T), with kind 1 = tcgen05 one-pass TF32,
+ * kind 2 = tcgen05 three-term TF32 split (FP32 accuracy).  Pointers and leading dimensions
+ * must be 16-byte aligned.  Syncs the stream; AFQMC_ERR_TIMEOUT if a device wait expired. */
+int afqmc_debug_gemm(int kind, int M, int N, int K, const float* A, long long lda, const float* Bt,
+                     long long ldb, float* C, long long ldc, int c_trans, void* stream);
 
 const char* afqmc_strerror(int code);
 

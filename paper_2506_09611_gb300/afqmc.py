@@ -21,19 +21,20 @@ PREC_FP64, PREC_FP32 = 0, 1
 MODE_LOCAL, MODE_DELAYED, MODE_BLOCKFB = 0, 1, 2
 MODES = {"local": MODE_LOCAL, "delayed": MODE_DELAYED, "blockfb": MODE_BLOCKFB}
 PRECS = {"fp64": PREC_FP64, "fp32": PREC_FP32}
+GEMMS = {"tc3": 0, "simt": 1, "tf32": 2}
 
 EXPORTS = ["afqmc_create", "afqmc_destroy", "afqmc_init_walkers", "afqmc_sweep_slice", "afqmc_recompute_G",
            "afqmc_measure_energy", "afqmc_get_G", "afqmc_set_G", "afqmc_get_fields", "afqmc_get_decisions",
            "afqmc_get_ratios", "afqmc_get_info", "afqmc_debug_uniforms", "afqmc_set_profiling",
            "afqmc_get_profile", "afqmc_launch_count", "afqmc_apply_flips", "afqmc_apply_flips_noalloc",
-           "afqmc_strerror"]
+           "afqmc_debug_gemm", "afqmc_strerror"]
 PHASES = ["prep", "wrap", "local", "chain", "flush", "recompute"]
 
 
 class afqmc_params(ctypes.Structure):
     _fields_ = [("hs", ctypes.c_int), ("precision", ctypes.c_int), ("M", ctypes.c_int),
                 ("stab_every", ctypes.c_int), ("t", ctypes.c_double), ("U", ctypes.c_double),
-                ("dtau", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("dtau", ctypes.c_double), ("seed", ctypes.c_uint64), ("gemm", ctypes.c_int)]
 
 
 class afqmc_slice_stats(ctypes.Structure):
@@ -78,6 +79,9 @@ def load(path: str = LIB_PATH):
     lib.afqmc_launch_count.argtypes = []
     lib.afqmc_apply_flips.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, vp, vp, vp, vp, ctypes.c_int, vp]
     lib.afqmc_apply_flips_noalloc.argtypes = lib.afqmc_apply_flips.argtypes
+    ll = ctypes.c_longlong
+    lib.afqmc_debug_gemm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ll, vp, ll, vp, ll,
+                                     ctypes.c_int, vp]
     lib.afqmc_strerror.argtypes = [ctypes.c_int]
     lib.afqmc_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -111,8 +115,9 @@ def _stream(stream):
 
 # ---------------------------------------------------------------- C-named entry points
 
-def afqmc_create(hs, precision, M, stab_every, t, U, dtau, seed):
-    p = afqmc_params(hs=hs, precision=precision, M=M, stab_every=stab_every, t=t, U=U, dtau=dtau, seed=seed)
+def afqmc_create(hs, precision, M, stab_every, t, U, dtau, seed, gemm=0):
+    p = afqmc_params(hs=hs, precision=precision, M=M, stab_every=stab_every, t=t, U=U, dtau=dtau, seed=seed,
+                     gemm=gemm)
     h = ctypes.c_void_p()
     _ck("afqmc_create", load().afqmc_create(ctypes.byref(h), ctypes.byref(p)))
     return h
@@ -228,6 +233,12 @@ def afqmc_apply_flips_noalloc(precision, N, ld, G_up, G_dn, sites, delta, m, str
                                          _stream(stream)))
 
 
+def afqmc_debug_gemm(kind, M, N, K, A, lda, Bt, ldb, C, ldc, c_trans=0, stream=None):
+    """C = A @ Bt.T with the tensor-core kernel (kind 1: TF32, 2: three-term TF32 split); device pointers."""
+    _ck("afqmc_debug_gemm", load().afqmc_debug_gemm(kind, M, N, K, ctypes.c_void_p(A), lda, ctypes.c_void_p(Bt), ldb,
+                                                    ctypes.c_void_p(C), ldc, c_trans, _stream(stream)))
+
+
 def afqmc_launch_count():
     return int(load().afqmc_launch_count())
 
@@ -237,9 +248,11 @@ def afqmc_launch_count():
 class Context:
     """Owns one afqmc_ctx; methods forward to the C entry points above."""
 
-    def __init__(self, M, dtau=0.05, U=4.0, t=1.0, precision="fp64", hs=HS_SZ_REAL, stab_every=10, seed=1):
+    def __init__(self, M, dtau=0.05, U=4.0, t=1.0, precision="fp64", hs=HS_SZ_REAL, stab_every=10, seed=1,
+                 gemm="tc3"):
         self.M = M
-        self.h = afqmc_create(hs, PRECS.get(precision, precision), M, stab_every, t, U, dtau, seed)
+        self.h = afqmc_create(hs, PRECS.get(precision, precision), M, stab_every, t, U, dtau, seed,
+                              GEMMS.get(gemm, gemm))
         self.n = 0
 
     def init_walkers(self, L, n_up, n_dn, P, fields=None, stream=None):

@@ -24,6 +24,7 @@ struct Lattice {
     double* Einv64 = nullptr;
     void* Eb = nullptr;
     void* Einvb = nullptr;
+    double* Ex64 = nullptr;  // L x L: exp(-dtau K) = Ex (x) Ex for the periodic square lattice
 };
 
 struct Walker {
@@ -207,6 +208,8 @@ static Lattice* get_lattice(afqmc_ctx* ctx, int L, cudaStream_t st, cudaError_t*
     if ((*err = dalloc(ctx->allocs, &l->Einv64, n2 * 8)) != cudaSuccess) return nullptr;
     if ((*err = dalloc(ctx->allocs, (char**)&l->Eb, n2 * esize(ctx))) != cudaSuccess) return nullptr;
     if ((*err = dalloc(ctx->allocs, (char**)&l->Einvb, n2 * esize(ctx))) != cudaSuccess) return nullptr;
+    if ((*err = dalloc(ctx->allocs, &l->Ex64, (size_t)L * L * 8)) != cudaSuccess) return nullptr;
+    if ((*err = launch_expK1d(st, L, ctx->p.t, ctx->p.dtau, l->Ex64)) != cudaSuccess) return nullptr;
     if ((*err = launch_expK(st, L, ctx->p.t, ctx->p.dtau, l->E64, l->ld)) != cudaSuccess) return nullptr;
     if ((*err = launch_expK(st, L, ctx->p.t, -ctx->p.dtau, l->Einv64, l->ld)) != cudaSuccess) return nullptr;
     if (ctx->p.precision == AFQMC_PREC_FP64) {
@@ -238,6 +241,9 @@ static cudaError_t form_G(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, con
     if (e != cudaSuccess) return e;
     e = launch_gj_extract(st, w->aug, la, ns, N, w->perm, w->Z, N);
     if (e != cudaSuccess) return e;
+    // The N x N product stays in FP64 for both bulk precisions: the pivoted-LU factors are not
+    // orthonormal, so 1 - U_R Z cancels large terms and an FP32 product would lose the digits
+    // the recompute exists to restore.
     GemmArgs<double> h;
     h.M = N; h.N = N; h.K = ns;
     h.A = UR; h.lda = ns;
@@ -248,36 +254,45 @@ static cudaError_t form_G(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, con
     return launch_identity_minus<double>(st, w->Gnew, w->ld, N);
 }
 
-// U (N x ns) <- B_l U  with B_l = diag(exp(c_s x_l)) E
+// U (N x ns) <- B_l U, B_l = diag(exp(c_s x_l)) E.  E = Ex (x) Ex on the square lattice, so
+// E U is two small products: along x for every row block y, then along y.
 static cudaError_t prop_right(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, int ell, double* U, double* tmp) {
-    const int N = w->N, ns = w->ns[s];
+    const int N = w->N, ns = w->ns[s], L = w->L;
     cudaError_t e = launch_field_scales_T<double>(st, w->x + (size_t)(ell - 1) * N, N, ctx->c, w->d64, w->d64 + 2 * N, N);
     if (e != cudaSuccess) return e;
-    GemmArgs<double> g;
-    g.M = N; g.N = ns; g.K = N;
-    g.A = w->lat->E64; g.lda = w->lat->ld;
-    g.B = U; g.ldb = ns;
-    g.C = tmp; g.ldc = ns;
-    g.rs = w->d64 + (size_t)s * N;
-    e = gemm<double>(st, g);
-    if (e != cudaSuccess) return e;
-    return cudaMemcpyAsync(U, tmp, (size_t)N * ns * 8, cudaMemcpyDeviceToDevice, st);
+    GemmArgs<double> gx;  // tmp[(x,y), c] = sum_x' Ex[x, x'] U[(x',y), c]
+    gx.M = L; gx.N = ns; gx.K = L; gx.batch = L;
+    gx.A = w->lat->Ex64; gx.lda = L; gx.sA = 0;
+    gx.B = U; gx.ldb = ns; gx.sB = (long)L * ns;
+    gx.C = tmp; gx.ldc = ns; gx.sC = (long)L * ns;
+    if ((e = gemm<double>(st, gx)) != cudaSuccess) return e;
+    GemmArgs<double> gy;  // U[(x,y), c] = sum_y' Ex[y, y'] tmp[(x,y'), c]
+    gy.M = L; gy.N = L * ns; gy.K = L;
+    gy.A = w->lat->Ex64; gy.lda = L;
+    gy.B = tmp; gy.ldb = (long)L * ns;
+    gy.C = U; gy.ldc = (long)L * ns;
+    if ((e = gemm<double>(st, gy)) != cudaSuccess) return e;
+    return launch_scale_rows(st, U, N, ns, w->d64 + (size_t)s * N);
 }
 
-// U (ns x N) <- U B_l
+// U (ns x N) <- U B_l = (U diag(exp(c_s x_l))) E, with the same separable product.
 static cudaError_t prop_left(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, int ell, double* U, double* tmp) {
-    const int N = w->N, ns = w->ns[s];
+    const int N = w->N, ns = w->ns[s], L = w->L;
     cudaError_t e = launch_field_scales_T<double>(st, w->x + (size_t)(ell - 1) * N, N, ctx->c, w->d64, w->d64 + 2 * N, N);
     if (e != cudaSuccess) return e;
-    GemmArgs<double> g;
-    g.M = ns; g.N = N; g.K = N;
-    g.A = U; g.lda = N;
-    g.B = w->lat->E64; g.ldb = w->lat->ld;
-    g.C = tmp; g.ldc = N;
-    g.bs = w->d64 + (size_t)s * N;
-    e = gemm<double>(st, g);
-    if (e != cudaSuccess) return e;
-    return cudaMemcpyAsync(U, tmp, (size_t)N * ns * 8, cudaMemcpyDeviceToDevice, st);
+    if ((e = launch_scale_cols(st, U, ns, N, w->d64 + (size_t)s * N)) != cudaSuccess) return e;
+    GemmArgs<double> gx;  // tmp[(a,y), x] = sum_x' U[a, (x',y)] Ex[x', x]
+    gx.M = ns * L; gx.N = L; gx.K = L;
+    gx.A = U; gx.lda = L;
+    gx.B = w->lat->Ex64; gx.ldb = L;
+    gx.C = tmp; gx.ldc = L;
+    if ((e = gemm<double>(st, gx)) != cudaSuccess) return e;
+    GemmArgs<double> gy;  // U[a, (x,y)] = sum_y' Ex[y, y'] tmp[(a,y'), x]
+    gy.M = L; gy.N = L; gy.K = L; gy.batch = ns;
+    gy.A = w->lat->Ex64; gy.lda = L; gy.sA = 0;
+    gy.B = tmp; gy.ldb = L; gy.sB = N;
+    gy.C = U; gy.ldc = L; gy.sC = N;
+    return gemm<double>(st, gy);
 }
 
 static cudaError_t stab_right(Walker* w, cudaStream_t st, int s, double* U, double* sign) {  // U: N x ns
@@ -318,6 +333,7 @@ int afqmc_create(afqmc_ctx** out, const afqmc_params* p) {
     if (p->M < 1 || p->stab_every < 1 || p->M % p->stab_every != 0) return AFQMC_ERR_ARG;
     if (p->precision != AFQMC_PREC_FP64 && p->precision != AFQMC_PREC_FP32) return AFQMC_ERR_ARG;
     if (!(p->dtau > 0.0)) return AFQMC_ERR_ARG;
+    if (p->gemm < AFQMC_GEMM_TC3 || p->gemm > AFQMC_GEMM_TF32) return AFQMC_ERR_ARG;
     double lam;
     double c0, c1;
     if (p->hs == AFQMC_HS_SZ_REAL) {
@@ -431,6 +447,9 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
         CK(dalloc(A, (char**)&w->elim, elim_scratch_bytes(N > nsm ? N : nsm)));
         CK(dalloc(A, &w->acc2, 2 * 8));
         CK(cudaMemsetAsync(w->err, 0, sizeof(int), st));
+        CK(cudaMemsetAsync(w->Wm, 0, 2 * (size_t)NW * NW * es, st));
+        CK(cudaMemsetAsync(w->X, 0, 2 * (size_t)N * NW * es, st));
+        CK(cudaMemsetAsync(w->Y, 0, 4 * (size_t)NW * N * es, st));
         CK(cudaMemsetAsync(w->G, 0, 2 * (size_t)N * ld * es, st));
         CK(cudaMemsetAsync(w->Tbuf, 0, 2 * (size_t)N * ld * es, st));
         // fields
@@ -514,10 +533,45 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
             rep = w->replay;
         }
     }
+    const bool use_tc = (sizeof(T) == 4) && ctx->p.gemm != AFQMC_GEMM_SIMT;
+    const int split3 = ctx->p.gemm != AFQMC_GEMM_TF32;
     auto wrap = [&](int direction) -> cudaError_t {
         PhaseScope ps(ctx, AFQMC_PHASE_WRAP, st);
         cudaError_t e = launch_field_scales_T<T>(st, xl, N, ctx->c, d, dinv, N);
         if (e != cudaSuccess) return e;
+        if (use_tc) {
+            // E and Einv are symmetric, so both products are A * Bt^T with K-major operands:
+            //   forward : S^T = (G Einv)^T ;  G = D (E S) D^{-1}
+            //   backward: G <- D^{-1} G D ;  S^T = (G E)^T ;  G = Einv S
+            const float* Ef = (const float*)E;
+            const float* Eif = (const float*)Einv;
+            float* Gf = (float*)G0;
+            float* Tf = (float*)Tb;
+            if (direction < 0) {
+                e = launch_scale2<T>(st, G0, ld, N, (long)N * ld, dinv, d);
+                if (e != cudaSuccess) return e;
+            }
+            TcGemmArgs t1;
+            t1.M = N; t1.N = N; t1.K = N; t1.batch = 2;
+            t1.A = Gf; t1.lda = ld; t1.sA = (long)N * ld;
+            t1.Bt = direction > 0 ? Eif : Ef; t1.ldb = ld; t1.sB = 0;
+            t1.C = Tf; t1.ldc = ld; t1.sC = (long)N * ld; t1.c_trans = 1;
+            t1.split3 = split3;
+            t1.err = w->err;
+            if ((e = tc_gemm(st, t1)) != cudaSuccess) return e;
+            TcGemmArgs t2;
+            t2.M = N; t2.N = N; t2.K = N; t2.batch = 2;
+            t2.A = direction > 0 ? Ef : Eif; t2.lda = ld; t2.sA = 0;
+            t2.Bt = Tf; t2.ldb = ld; t2.sB = (long)N * ld;
+            t2.C = Gf; t2.ldc = ld; t2.sC = (long)N * ld;
+            if (direction > 0) {
+                t2.rs = (const float*)d; t2.srs = N;
+                t2.cs = (const float*)dinv; t2.scs = N;
+            }
+            t2.split3 = split3;
+            t2.err = w->err;
+            return tc_gemm(st, t2);
+        }
         GemmArgs<T> g1, g2;
         g1.M = N; g1.N = N; g1.K = N; g1.batch = 2;
         g1.ldb = ld; g1.sB = (long)N * ld;
@@ -594,7 +648,7 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
             }
             {
                 PhaseScope ps(ctx, AFQMC_PHASE_FLUSH, st);
-                CK(launch_flush<T>(st, G0, G1, sp, wb, n));
+                CK(launch_flush_rec<T>(st, G0, G1, sp, wb, n));
             }
         }
     }
@@ -853,6 +907,30 @@ int afqmc_get_profile(afqmc_ctx* ctx, double* ms, int64_t* intervals, int64_t* l
 }
 
 int64_t afqmc_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int afqmc_debug_gemm(int kind, int M, int N, int K, const float* A, long long lda, const float* Bt, long long ldb,
+                     float* C, long long ldc, int c_trans, void* stream) {
+    if ((kind != 1 && kind != 2) || M < 1 || N < 1 || K < 1 || !A || !Bt || !C) return AFQMC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return AFQMC_ERR_OOM;
+    cudaMemsetAsync(err, 0, sizeof(int), st);
+    TcGemmArgs g;
+    g.M = M; g.N = N; g.K = K;
+    g.A = A; g.lda = lda;
+    g.Bt = Bt; g.ldb = ldb;
+    g.C = C; g.ldc = ldc; g.c_trans = c_trans;
+    g.split3 = kind == 2;
+    g.err = err;
+    cudaError_t e = tc_gemm(st, g);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(err);
+    if (e != cudaSuccess) return AFQMC_ERR_CUDA;
+    if (h == DEV_TIMEOUT) return AFQMC_ERR_TIMEOUT;
+    return h ? AFQMC_ERR_CUDA : AFQMC_OK;
+}
 
 int afqmc_debug_uniforms(uint64_t seed, uint64_t walker, uint64_t visit, int count, double* host_out) {
     if (count < 0 || (count > 0 && !host_out)) return AFQMC_ERR_ARG;

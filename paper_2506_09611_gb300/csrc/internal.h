@@ -34,8 +34,32 @@ struct GemmArgs {
 template <typename T>
 cudaError_t gemm(cudaStream_t st, const GemmArgs<T>& g);
 
+// tcgen05 tensor-core GEMM (tc_gemm.cu), FP32 in/out:
+//   C[z] = alpha * diag(rs[z]) * A[z] * Bt[z]^T * diag(cs[z]) + beta * C[z]
+// A (M x K) and Bt (N x K) row-major (K contiguous); sA / sB = 0 share one matrix across the
+// batch.  c_trans writes C^T (C[n * ldc + m]).  split3 selects the three-term TF32 split (FP32
+// accuracy); otherwise one TF32 pass.  Base pointers and leading dimensions must be 16-byte
+// aligned (TMA).  err receives DEV_TIMEOUT if a bounded wait expires.
+struct TcGemmArgs {
+    int M = 0, N = 0, K = 0, batch = 1;
+    const float* A = nullptr; long lda = 0, sA = 0;
+    const float* Bt = nullptr; long ldb = 0, sB = 0;
+    float* C = nullptr; long ldc = 0, sC = 0;
+    int c_trans = 0;
+    const float* rs = nullptr; long srs = 0;
+    const float* cs = nullptr; long scs = 0;
+    float alpha = 1.0f, beta = 0.0f;
+    int split3 = 1;
+    int* err = nullptr;
+};
+cudaError_t tc_gemm(cudaStream_t st, const TcGemmArgs& g);
+
 // ---- setup / recompute kernels (setup.cu) ----
 cudaError_t launch_expK(cudaStream_t st, int L, double t, double tau, double* E, long ld);
+cudaError_t launch_expK1d(cudaStream_t st, int L, double t, double tau, double* Ex);  // L x L factor
+cudaError_t launch_scale_rows(cudaStream_t st, double* U, int rows, int cols, const double* d);  // U[r,:] *= d[r]
+cudaError_t launch_scale_cols(cudaStream_t st, double* U, int rows, int cols, const double* d);  // U[:,c] *= d[c]
+
 template <typename T>
 cudaError_t launch_cast(cudaStream_t st, const double* src, long lds, T* dst, long ldd, int rows, int cols);
 template <typename T>
@@ -103,10 +127,10 @@ cudaError_t launch_local(cudaStream_t st, T* Gu, T* Gd, int8_t* xl, const double
 struct WindowBufs {    // device scratch of the window chain + flush
     int* m;            // accepted count of the window
     int* idx;          // accepted site indices (global), capacity NW
-    double* dtot;      // per spin: total Delta of each accepted site, 2 x NW
-    void* Wm;          // per spin m x m (T), 2 x NW x NW
-    void* X;           // per spin N x NW panel G[:, I] (T)
-    void* Y;           // per spin NW x N panel Wm (E_I^T - G[I, :]) (T)
+    double* dtot;      // per spin, 2 x NW: sweep: recursion factor -Delta/r; apply_flips: unused
+    void* Wm;          // per spin NW x NW (T): sweep: frozen block coefficients; apply_flips: W
+    void* X;           // per spin N x NW column panel (T)
+    void* Y;           // per spin NW x N row panel (T), plus room for a second product
 };
 
 template <typename T>
@@ -118,5 +142,14 @@ cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T*
                                 WindowBufs wb, int* err);
 template <typename T>
 cudaError_t launch_flush(cudaStream_t st, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw);
+// Flush of a window by the delayed-update recursion on the frozen block coefficients.
+template <typename T>
+cudaError_t launch_flush_rec(cudaStream_t st, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw);
+// FP32 flush through the tensor-core GEMM (window buffers must start zeroed).
+cudaError_t launch_flush_tc(cudaStream_t st, float* Gu, float* Gd, const SiteParams& sp, WindowBufs wb, int* err,
+                            int split3);
+// G_s[i][j] *= a_s[i] * b_s[j] for both spins (a, b: [2][N], spin stride N)
+template <typename T>
+cudaError_t launch_scale2(cudaStream_t st, T* G, long ld, int N, long sG, const T* a, const T* b);
 
 }  // namespace afq

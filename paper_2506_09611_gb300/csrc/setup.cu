@@ -39,6 +39,65 @@ cudaError_t launch_expK(cudaStream_t st, int L, double t, double tau, double* E,
     return cudaGetLastError();
 }
 
+__global__ void expK1d_kernel(int L, double t, double tau, double* Ex) {
+    // Ex[x][x'] = L^{-1} sum_k exp(2 tau t cos k) cos(k (x - x')), k = 2 pi q / L
+    for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
+        int x = e / L, xp = e % L;
+        int d = ((x - xp) % L + L) % L;
+        double acc = 0.0;
+        for (int q = 0; q < L; ++q) {
+            double k = 2.0 * M_PI * q / L;
+            acc += exp(2.0 * tau * t * cos(k)) * cos(k * d);
+        }
+        Ex[e] = acc / L;
+    }
+}
+
+cudaError_t launch_expK1d(cudaStream_t st, int L, double t, double tau, double* Ex) {
+    count_launch();
+    expK1d_kernel<<<1, 256, 0, st>>>(L, t, tau, Ex);
+    return cudaGetLastError();
+}
+
+__global__ void scale_rows_kernel(double* U, int rows, int cols, const double* d) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)rows * cols; e += (long)gridDim.x * blockDim.x)
+        U[e] *= d[e / cols];
+}
+__global__ void scale_cols_kernel(double* U, int rows, int cols, const double* d) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)rows * cols; e += (long)gridDim.x * blockDim.x)
+        U[e] *= d[e % cols];
+}
+cudaError_t launch_scale_rows(cudaStream_t st, double* U, int rows, int cols, const double* d) {
+    count_launch();
+    scale_rows_kernel<<<512, 256, 0, st>>>(U, rows, cols, d);
+    return cudaGetLastError();
+}
+cudaError_t launch_scale_cols(cudaStream_t st, double* U, int rows, int cols, const double* d) {
+    count_launch();
+    scale_cols_kernel<<<512, 256, 0, st>>>(U, rows, cols, d);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void scale2_kernel(T* G, long ld, int N, long sG, const T* a, const T* b) {
+    const int s = blockIdx.y;
+    T* g = G + s * sG;
+    const T* as = a + (size_t)s * N;
+    const T* bs = b + (size_t)s * N;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)N * N; e += (long)gridDim.x * blockDim.x) {
+        int i = (int)(e / N), j = (int)(e % N);
+        g[(long)i * ld + j] *= as[i] * bs[j];
+    }
+}
+template <typename T>
+cudaError_t launch_scale2(cudaStream_t st, T* G, long ld, int N, long sG, const T* a, const T* b) {
+    count_launch();
+    scale2_kernel<T><<<dim3(512, 2), 256, 0, st>>>(G, ld, N, sG, a, b);
+    return cudaGetLastError();
+}
+template cudaError_t launch_scale2<float>(cudaStream_t, float*, long, int, long, const float*, const float*);
+template cudaError_t launch_scale2<double>(cudaStream_t, double*, long, int, long, const double*, const double*);
+
 template <typename T>
 __global__ void cast_kernel(const double* src, long lds, T* dst, long ldd, int rows, int cols) {
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)rows * cols; e += (long)gridDim.x * blockDim.x) {
@@ -158,16 +217,23 @@ __global__ void __launch_bounds__(256) elim_kernel(int mode, double* A, int R, i
     if (!grid_barrier(&sc->bar, nblk, err)) return;
     double sgn = 1.0;
     for (int j = 0; j < nsteps; ++j) {
-        if (tid == 0) {
+        if (tid < 32) {  // warp 0 reduces the per-CTA candidates (loads in flight together)
             double bv = -1.0;
             int br = 0x7fffffff;
-            for (int q = 0; q < nblk; ++q) better(bv, br, cand[(j & 1) * 1024 + q].v, cand[(j & 1) * 1024 + q].r);
-            if (!(bv > 0.0) || br >= R) {
-                set_err(err, DEV_NUMERIC);
-                br = 0;
+            for (int q = tid; q < nblk; q += 32) better(bv, br, cand[(j & 1) * 1024 + q].v, cand[(j & 1) * 1024 + q].r);
+            for (int o = 16; o > 0; o >>= 1) {
+                double ov = __shfl_down_sync(0xffffffffu, bv, o);
+                int orr = __shfl_down_sync(0xffffffffu, br, o);
+                better(bv, br, ov, orr);
             }
-            s_p = br;
-            s_pv = elem(br, j);
+            if (tid == 0) {
+                if (!(bv > 0.0) || br >= R) {
+                    set_err(err, DEV_NUMERIC);
+                    br = 0;
+                }
+                s_p = br;
+                s_pv = elem(br, j);
+            }
         }
         __syncthreads();
         const int p = s_p;
@@ -188,11 +254,20 @@ __global__ void __launch_bounds__(256) elim_kernel(int mode, double* A, int R, i
         }
         __syncthreads();
         const int w = ncols - j - 1;
-        for (long e = tid; e < (long)nr * w; e += nt) {
-            int q = (int)(e / w), c = j + 1 + (int)(e % w);
-            int r = r0 + q;
-            double l = s_l[q];
-            if (l != 0.0) elem(r, c) -= l * elem(p, c);
+        if (mode == 0 && rs == 1) {
+            // rows are contiguous in memory: consecutive threads take consecutive rows
+            for (int e = tid; e < nr * w; e += nt) {
+                const int q = e % nr, c = j + 1 + e / nr;
+                const double l = s_l[q];
+                if (l != 0.0) elem(r0 + q, c) -= l * elem(p, c);
+            }
+        } else {
+            for (int q = 0; q < nr; ++q) {
+                const double l = s_l[q];
+                if (l == 0.0) continue;
+                const int r = r0 + q;
+                for (int c = j + 1 + tid; c < ncols; c += nt) elem(r, c) -= l * elem(p, c);
+            }
         }
         for (int q = tid; q < nr; q += nt) {
             int r = r0 + q;
@@ -297,6 +372,7 @@ cudaError_t launch_drift(cudaStream_t st, const T* Gold, const T* Gnew, long ld,
     return cudaGetLastError();
 }
 template cudaError_t launch_drift<float>(cudaStream_t, const float*, const float*, long, int, double*);
+
 template cudaError_t launch_drift<double>(cudaStream_t, const double*, const double*, long, int, double*);
 
 // E = sum_s tr(K A^s) + U sum_i (n_up n_dn - (n_up + n_dn)/2), A = 1 - G, K_ij = -t per bond

@@ -177,13 +177,25 @@ template int window_max<double>();
 template <typename T>
 static size_t window_smem(int n) {
     size_t P = (size_t)n + 1;
-    size_t g = 2 * (size_t)n * P * sizeof(T);                // Gs[2][n][n+1]
-    size_t aug = (size_t)n * (2 * (size_t)n + 1) * sizeof(T);  // Gauss-Jordan [M | I] for one spin
-    if (aug > g) g = aug;
+    size_t g = 2 * (size_t)n * P * sizeof(T);  // Gs[2][n][n+1]
     size_t s1 = 2 * (size_t)NBMAX * (NBMAX + 1) * sizeof(T);
     size_t vec = 4 * (size_t)n * sizeof(T) + 2 * (size_t)NBMAX * sizeof(T);  // staging vectors
     size_t misc = (size_t)n * (sizeof(int) + 2 * sizeof(double) + 1) + 8 * (size_t)NBMAX * sizeof(double) + 256;
     return g + s1 + vec + misc;
+}
+
+// G_s[r][c] += f_s * G_s[r][a] * G_s[a][c] for r, c in (a, n), both spins; 32 x 32 thread tiles.
+template <typename T>
+__device__ __forceinline__ void trailing_update(T* Gs, int n, int P, int a, T f0, T f1, int tid, int nt) {
+    const int tx = tid & 31, ty = tid >> 5, ny = nt >> 5;
+    for (int s = 0; s < 2; ++s) {
+        T* Gb = Gs + (size_t)s * n * P;
+        const T f = s ? f1 : f0;
+        for (int r = a + 1 + ty; r < n; r += ny) {
+            const T g = f * Gb[r * P + a];
+            for (int c = a + 1 + tx; c < n; c += 32) Gb[r * P + c] += g * Gb[a * P + c];
+        }
+    }
 }
 
 template <typename T, int MODE>
@@ -198,8 +210,6 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
     const long ld = sp.ld;
     T* Gs = (T*)smem_raw;  // [2][n][P]
     size_t off = 2 * (size_t)n * P * sizeof(T);
-    size_t aug = (size_t)n * (2 * (size_t)n + 1) * sizeof(T);
-    if (aug > off) off = aug;
     T* S1 = (T*)(smem_raw + off);  // [2][NBMAX][NBMAX+1]
     off += 2 * (size_t)NBMAX * (NBMAX + 1) * sizeof(T);
     T* stc = (T*)(smem_raw + off);  // staging: col[2][n], row[2][n]
@@ -224,6 +234,20 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
         Gs[(s * n + a) * P + c] = G[s][(long)(s0 + a) * ld + (s0 + c)];
     }
     for (int p = tid; p < n; p += nt) xw[p] = xl_g[s0 + p];
+    // the window's site uniforms (and forced decisions) live in shared memory: the scan reads
+    // them on its critical path
+    __shared__ double s_u[WinCap<float>::NW];
+    __shared__ uint8_t s_rep[WinCap<float>::NW];
+    for (int p = tid; p < n; p += nt) {
+        s_u[p] = u[s0 + p];
+        s_rep[p] = replay ? replay[s0 + p] : 0;
+    }
+    __shared__ double c_dflip[2][2], c_dstrip[2][2], c_sflip[2];
+    if (tid < 4) {
+        c_dflip[tid >> 1][tid & 1] = sp.dflip[tid >> 1][tid & 1];
+        c_dstrip[tid >> 1][tid & 1] = sp.dstrip[tid >> 1][tid & 1];
+    }
+    if (tid < 2) c_sflip[tid] = sp.sflip[tid];
     if (tid == 0) s_m = 0;
     __syncthreads();
 
@@ -250,10 +274,10 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                 if (q < n) {
                     const int i = s0 + q;
                     xi = xw[q] > 0 ? 0 : 1;
-                    rr0 = 1.0 + sp.dflip[0][xi] * (1.0 - (double)Gs[(0 * n + q) * P + q]);
-                    rr1 = 1.0 + sp.dflip[1][xi] * (1.0 - (double)Gs[(1 * n + q) * P + q]);
-                    R = sp.sflip[xi] * rr0 * rr1;
-                    acc = replay ? (replay[i] != 0) : (u[i] < fabs(R));
+                    rr0 = 1.0 + c_dflip[0][xi] * (1.0 - (double)Gs[(0 * n + q) * P + q]);
+                    rr1 = 1.0 + c_dflip[1][xi] * (1.0 - (double)Gs[(1 * n + q) * P + q]);
+                    R = c_sflip[xi] * rr0 * rr1;
+                    acc = replay ? (s_rep[q] != 0) : (s_u[q] < fabs(R));
                     if (!isfinite(R)) {
                         acc = false;
                         set_err(err, DEV_NUMERIC);
@@ -266,11 +290,11 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                     so.ratio[s0 + q] = R;
                 }
                 if (tid == first) {
-                    s_fa[0] = (T)(sp.dflip[0][xi] / rr0);
-                    s_fa[1] = (T)(sp.dflip[1][xi] / rr1);
+                    s_fa[0] = (T)(c_dflip[0][xi] / rr0);
+                    s_fa[1] = (T)(c_dflip[1][xi] / rr1);
                     idx[s_m] = q;
-                    dl[0 * n + s_m] = sp.dflip[0][xi];
-                    dl[1 * n + s_m] = sp.dflip[1][xi];
+                    dl[0 * n + s_m] = -c_dflip[0][xi] / rr0;  // recursion factor f = -Delta / r
+                    dl[1 * n + s_m] = -c_dflip[1][xi] / rr1;
                     s_m = s_m + 1;
                     if (R < 0) s_sign = -s_sign;
                     s_maxr = fmax(s_maxr, fabs(R));
@@ -287,15 +311,10 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
             if (a < 0) continue;
             ++n_acc;
             ++n_flip;
-            // trailing update of the block: G[r][c] += (d/r) G[r][a] G[a][c], r, c > a
-            const T f0 = s_fa[0], f1 = s_fa[1];
-            const int qn = n - a - 1;
-            for (int e = tid; e < 2 * qn * qn; e += nt) {
-                int sp2 = e / (qn * qn), rem = e - sp2 * qn * qn;
-                int r = a + 1 + rem / qn, c = a + 1 + rem % qn;
-                T* Gb = Gs + sp2 * n * P;
-                Gb[r * P + c] += (sp2 ? f1 : f0) * Gb[r * P + a] * Gb[a * P + c];
-            }
+            // trailing update of the block: G[r][c] += (d/r) G[r][a] G[a][c], r, c > a.  Rows and
+            // columns <= a are never touched again, so the block keeps row a and column a as they
+            // were when site a was accepted (the coefficients of the flush recursion).
+            trailing_update(Gs, n, P, a, s_fa[0], s_fa[1], tid, nt);
             __syncthreads();
         }
     } else {
@@ -325,7 +344,7 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                 }
                 if (tid < 2) {
                     const int xi = xw[p0 + a] > 0 ? 0 : 1;
-                    const double db = sp.dstrip[tid][xi];
+                    const double db = c_dstrip[tid][xi];
                     const double rr = 1.0 + db * (1.0 - (double)S1[(tid * NBMAX + a) * (NBMAX + 1) + a]);
                     s_fs[tid] = (T)(db / rr);
                 }
@@ -398,7 +417,7 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                 }
                 if (tid < 2) {
                     const int xi = xw[p0 + a] > 0 ? 0 : 1;
-                    const double dd = sp.dflip[tid][xi];
+                    const double dd = c_dflip[tid][xi];
                     const double rr = 1.0 + dd * (1.0 - (double)S1[(tid * NBMAX + a) * (NBMAX + 1) + a]);
                     s_rs[tid] *= rr;
                     s_phi[tid][q] = (T)(dd / rr);
@@ -431,26 +450,16 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
             if (!s_accb) continue;
             ++n_acc;
             n_flip += nF;
-            // (d) apply the flips to the trailing block [p0, n)^2 of the window, one rank-1 step each
-            const int q0 = p0, w = n - p0;
+            // (d) apply the flips in increasing site order, each as the trailing rank-1 step of the
+            //     delayed update (rows / columns after the flipped site): the same product of
+            //     rank-1 factors as Eq. BlkFrcBsTnew2, and the frozen rows / columns feed the flush
             for (int q = 0; q < nF; ++q) {
                 const int a = p0 + s_F[q];
-                for (int e = tid; e < 2 * w; e += nt) {
-                    int s = e / w, c = q0 + e % w;
-                    T* Gb = Gs + s * n * P;
-                    stcol[s * n + c] = Gb[c * P + a];
-                    strow[s * n + c] = (c == a ? T(1) : T(0)) - Gb[a * P + c];
-                }
-                __syncthreads();
-                for (int e = tid; e < 2 * w * w; e += nt) {
-                    int s = e / (w * w), rem = e % (w * w), r = q0 + rem / w, c = q0 + rem % w;
-                    T* Gb = Gs + s * n * P;
-                    Gb[r * P + c] -= s_phi[s][q] * stcol[s * n + r] * strow[s * n + c];
-                }
+                trailing_update(Gs, n, P, a, s_phi[0][q], s_phi[1][q], tid, nt);
                 if (tid == 0) {
                     idx[s_m] = a;
-                    dl[0 * n + s_m] = fb[4 * NBMAX + q];
-                    dl[1 * n + s_m] = fb[5 * NBMAX + q];
+                    dl[0 * n + s_m] = -(double)s_phi[0][q];
+                    dl[1 * n + s_m] = -(double)s_phi[1][q];
                     s_m = s_m + 1;
                     xw[a] = (int8_t)(-xw[a]);
                 }
@@ -470,6 +479,13 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
         wb.dtot[q] = dl[q];
         wb.dtot[WinCap<T>::NW + q] = dl[n + q];
     }
+    // coefficients of the flush recursion: the block entries at accepted positions, frozen
+    // at acceptance time (row of the earlier site, column of the earlier site)
+    const int NWC = WinCap<T>::NW;
+    for (int e = tid; e < 2 * m * m; e += nt) {
+        const int sp2 = e / (m * m), rem = e - sp2 * m * m, a = rem / m, c = rem - (rem / m) * m;
+        ((T*)wb.Wm)[(size_t)sp2 * NWC * NWC + a * NWC + c] = Gs[(sp2 * n + idx[a]) * P + idx[c]];
+    }
     if (tid == 0) {
         *wb.m = m;
         if (so.sign) *so.sign = s_sign;
@@ -478,68 +494,6 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
         so.stats[2] += n_flip;
         so.stats[3] += (m > 0) ? 1 : 0;
         *so.maxr = fmax(*so.maxr, s_maxr);
-    }
-    __syncthreads();
-    if (m == 0) return;
-
-    // ---- W = D_I (1 + A0_II D_I)^{-1} per spin, A0 = 1 - G0 (G0 = global G, not yet flushed) ----
-    const int NWC = WinCap<T>::NW;
-    T* Aug = Gs;  // m x (2m), pitch 2m+1
-    const int AP = 2 * m + 1;
-    for (int s = 0; s < 2; ++s) {
-        for (int e = tid; e < m * m; e += nt) {
-            int a = e / m, c = e % m;
-            double g0 = (double)G[s][(long)(s0 + idx[a]) * ld + (s0 + idx[c])];
-            double A0 = (a == c ? 1.0 : 0.0) - g0;
-            Aug[a * AP + c] = (T)((a == c ? 1.0 : 0.0) + A0 * dl[s * n + c]);
-            Aug[a * AP + m + c] = (a == c) ? T(1) : T(0);
-        }
-        __syncthreads();
-        for (int k = 0; k < m; ++k) {
-            if (tid < 32) {  // pivot search in column k, rows k..m-1
-                T best = T(-1);
-                int br = k;
-                for (int r = k + tid; r < m; r += 32) {
-                    T v = fabs(Aug[r * AP + k]);
-                    if (v > best) { best = v; br = r; }
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    T ob = __shfl_down_sync(0xffffffffu, best, o);
-                    int orr = __shfl_down_sync(0xffffffffu, br, o);
-                    if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
-                }
-                if (tid == 0) {
-                    s_piv = br;
-                    if (!(best > T(0))) set_err(err, DEV_NUMERIC);
-                }
-            }
-            __syncthreads();
-            const int pr = s_piv;
-            if (pr != k)
-                for (int c = tid; c < 2 * m; c += nt) {
-                    T t0 = Aug[k * AP + c];
-                    Aug[k * AP + c] = Aug[pr * AP + c];
-                    Aug[pr * AP + c] = t0;
-                }
-            __syncthreads();
-            const T inv = T(1) / Aug[k * AP + k];
-            for (int r = tid; r < m; r += nt) stc[r] = Aug[r * AP + k];
-            __syncthreads();
-            for (int c = tid; c < 2 * m; c += nt) Aug[k * AP + c] *= inv;
-            __syncthreads();
-            for (int e = tid; e < m * 2 * m; e += nt) {
-                int r = e / (2 * m), c = e % (2 * m);
-                if (r == k) continue;
-                Aug[r * AP + c] -= stc[r] * Aug[k * AP + c];
-            }
-            __syncthreads();
-        }
-        T* Wm = (T*)wb.Wm + (size_t)s * NWC * NWC;
-        for (int e = tid; e < m * m; e += nt) {
-            int a = e / m, c = e % m;
-            Wm[a * NWC + c] = (T)(dl[s * n + a] * (double)Aug[a * AP + m + c]);
-        }
-        __syncthreads();
     }
 }
 
@@ -628,6 +582,135 @@ template cudaError_t launch_window_chain<float>(cudaStream_t, int, const float*,
 template cudaError_t launch_window_chain<double>(cudaStream_t, int, const double*, const double*, int8_t*,
                                                  const double*, const uint8_t*, const SiteParams&, SliceOut, int,
                                                  int, int, WindowBufs, int*);
+// Tensor-core flush (FP32 bulk): panels gathered K-major and zero-padded to the window pitch NW,
+//   X (N x NW) = G[:, I],  YrT (N x NW) = (E_I^T - G[I, :])^T,  X' = X W  (SIMT, K = m),
+//   G <- G - X' YrT^T      (tcgen05, K = NW; the padding columns of YrT are zero).
+__global__ void gather_tc_kernel(const float* __restrict__ Gu, const float* __restrict__ Gd, long ld, int N,
+                                 WindowBufs wb, int NW, float* YrT) {
+    const int m = *wb.m;
+    const int s = blockIdx.y;
+    const float* G = s ? Gd : Gu;
+    float* X = (float*)wb.X + (size_t)s * N * NW;
+    float* Yt = YrT + (size_t)s * N * NW;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N * NW; e += gridDim.x * blockDim.x) {
+        const int j = e / NW, a = e % NW;
+        if (a < m) {
+            const int I = wb.idx[a];
+            Yt[e] = (j == I ? 1.0f : 0.0f) - G[(long)I * ld + j];
+            X[e] = G[(long)j * ld + I];
+        } else {
+            Yt[e] = 0.0f;
+        }
+    }
+}
+
+cudaError_t launch_flush_tc(cudaStream_t st, float* Gu, float* Gd, const SiteParams& sp, WindowBufs wb, int* err,
+                            int split3) {
+    const int N = sp.N;
+    const int NW = WinCap<float>::NW;
+    float* YrT = (float*)wb.Y;                      // [2][N][NW]
+    float* Xp = (float*)wb.Y + (size_t)2 * N * NW;  // [2][N][NW]
+    count_launch();
+    gather_tc_kernel<<<dim3(256, 2), 256, 0, st>>>(Gu, Gd, sp.ld, N, wb, NW, YrT);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    GemmArgs<float> g;  // X' = X W (columns >= m of X' multiply zero columns of YrT)
+    g.M = N; g.N = NW; g.K = NW; g.Kdev = wb.m;
+    g.A = (const float*)wb.X; g.lda = NW; g.sA = (long)N * NW;
+    g.B = (const float*)wb.Wm; g.ldb = NW; g.sB = (long)NW * NW;
+    g.C = Xp; g.ldc = NW; g.sC = (long)N * NW;
+    g.batch = 2;
+    if ((e = gemm<float>(st, g)) != cudaSuccess) return e;
+    TcGemmArgs t;
+    t.M = N; t.N = N; t.K = NW; t.batch = 2;
+    t.A = Xp; t.lda = NW; t.sA = (long)N * NW;
+    t.Bt = YrT; t.ldb = NW; t.sB = (long)N * NW;
+    t.C = Gu; t.ldc = sp.ld; t.sC = (long)(Gd - Gu);
+    t.alpha = -1.0f; t.beta = 1.0f;
+    t.split3 = split3;
+    t.err = err;
+    return tc_gemm(st, t);
+}
+
+// ---------------------------------------------------------------------------
+// flush by the delayed-update recursion (Eq. DelayRgenk restated for G): with the accepted sites
+// i_1 < ... < i_m of the window, f_k = -Delta_k / r_k and the frozen block entries
+// C[k][k'] = G_{at acceptance}[i_k, i_k'],
+//   a_k[r] = f_k ( G0[r, i_k] - sum_{k'<k} a_k'[r] C[k'][k] )                 (column panel)
+//   b_k[j] = delta(i_k, j) - G0[i_k, j] - sum_{k'<k} f_k' C[k][k'] b_k'[j]      (row panel)
+// and G = G0 + sum_k a_k b_k^T is one rank-m product.  Every row r and column j is an
+// independent recursion: one thread each, no synchronisation.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128) panels_kernel(const T* __restrict__ Gu, const T* __restrict__ Gd, long ld,
+                                                     int N, WindowBufs wb, T* Ap, T* Bp) {
+    constexpr int NW = WinCap<T>::NW;
+    extern __shared__ __align__(16) unsigned char panels_smem[];
+    T* Cs = (T*)panels_smem;  // [NW][NW + 1]
+    __shared__ T fs[NW];
+    __shared__ int Is[NW];
+    const int m = *wb.m;
+    if (m == 0) return;
+    const int s = blockIdx.y, kind = blockIdx.z;
+    const T* G = s ? Gd : Gu;
+    const T* Cg = (const T*)wb.Wm + (size_t)s * NW * NW;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Cs[(e / m) * (NW + 1) + e % m] = Cg[(e / m) * NW + e % m];
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        fs[k] = (T)wb.dtot[s * NW + k];
+        Is[k] = wb.idx[k];
+    }
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    T v[NW];
+    if (kind == 0) {  // column panel, row t: A[s][t][k] = a_k[t]
+        T* out = Ap + (size_t)s * N * NW + (size_t)t * NW;
+        for (int k = 0; k < m; ++k) {
+            T acc = G[(long)t * ld + Is[k]];
+            for (int q = 0; q < k; ++q) acc -= v[q] * Cs[q * (NW + 1) + k];
+            v[k] = fs[k] * acc;
+            out[k] = v[k];
+        }
+    } else {  // row panel, column t: B[s][k][t] = b_k[t]
+        T* out = Bp + (size_t)s * NW * N;
+        for (int k = 0; k < m; ++k) {
+            T acc = (Is[k] == t ? T(1) : T(0)) - G[(long)Is[k] * ld + t];
+            for (int q = 0; q < k; ++q) acc -= fs[q] * Cs[k * (NW + 1) + q] * v[q];
+            v[k] = acc;
+            out[(size_t)k * N + t] = acc;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_flush_rec(cudaStream_t st, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw) {
+    const int N = sp.N;
+    constexpr int NW = WinCap<T>::NW;
+    T* Ap = (T*)wb.X;  // [2][N][NW]
+    T* Bp = (T*)wb.Y;  // [2][NW][N]
+    const size_t shm = (size_t)NW * (NW + 1) * sizeof(T);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t ea = cudaFuncSetAttribute((void*)panels_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        if (ea != cudaSuccess) return ea;
+        attr = true;
+    }
+    count_launch();
+    panels_kernel<T><<<dim3((N + 127) / 128, 2, 2), 128, shm, st>>>(Gu, Gd, sp.ld, N, wb, Ap, Bp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    GemmArgs<T> h;  // G += A B (inner dimension m, read on the device)
+    h.M = N; h.N = N; h.K = nw; h.Kdev = wb.m;
+    h.A = Ap; h.lda = NW; h.sA = (long)N * NW;
+    h.B = Bp; h.ldb = N; h.sB = (long)NW * N;
+    h.C = Gu; h.ldc = sp.ld; h.sC = (long)(Gd - Gu);
+    h.alpha = T(1); h.beta = T(1);
+    h.batch = 2;
+    return gemm<T>(st, h);
+}
+
+template cudaError_t launch_flush_rec<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int);
+template cudaError_t launch_flush_rec<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs, int);
 template cudaError_t launch_flush<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int);
 template cudaError_t launch_flush<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs, int);
 

@@ -1,0 +1,384 @@
+// tc_gemm.cu -- 5th-generation tensor-core GEMM for sm_103a (tcgen05 + TMA + TMEM).
+//
+//   C[z] = alpha * diag(rs[z]) * A[z] * Bt[z]^T * diag(cs[z]) + beta * C[z]      (FP32 in / out)
+//
+// A is M x K and Bt is N x K, both row-major (K contiguous: the "K-major" operand layout), so
+// every product of the wrap and of the rank-m flush is fed without a transpose pass.  C may be
+// written row-major or transposed.  Tiles of 128 x BN are accumulated in TMEM by tcgen05.mma
+// (kind::tf32, issued by one thread), operands arrive in 128-byte-swizzled shared memory by
+// cp.async.bulk.tensor (TMA) through a multi-stage mbarrier pipeline, and the epilogue reads the
+// accumulator back with tcgen05.ld.
+//
+// FP32 accuracy (split3): each operand x is split into hi = x with the low 13 mantissa bits
+// cleared (exactly representable in TF32) and lo = x - hi, and the tile product is accumulated
+// as hi*hi + lo*hi + hi*lo in FP32 (the three-term TF32 split of Ootomo and Yokota, 2022).  The
+// split is done in shared memory after each stage lands.
+//
+// Every wait is bounded (about two seconds of %globaltimer); on expiry the kernel records
+// DEV_TIMEOUT, stops issuing work, waits (again bounded) for its copies in flight, frees its
+// TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "internal.h"
+
+namespace afq {
+
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 32;  // 32 FP32 = 128 bytes = one swizzle atom row
+constexpr unsigned long long WAIT_NS = 2000000000ULL;
+
+template <int BN, bool SPLIT>
+struct TcCfg {
+    static constexpr int A_BYTES = TC_BM * TC_BK * 4;
+    static constexpr int B_BYTES = BN * TC_BK * 4;
+    static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (SPLIT ? 2 : 1);
+    static constexpr int STAGES = SPLIT ? 3 : 4;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on phase `parity`; false on timeout (DEV_TIMEOUT recorded) or a recorded error.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > WAIT_NS) {
+            set_err(err, DEV_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_u32(dst)),
+        "l"((const void*)tm), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, rows of 128 bytes, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (stride byte offset); the leading byte offset is unused for this layout.
+__device__ __forceinline__ uint64_t desc_sw128(const void* tile) {
+    const uint64_t addr = smem_u32(tile);
+    uint64_t d = (addr & 0x3FFFFull) >> 4;
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+        "[%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+struct TcArgs {
+    int M, N, K;
+    float* C;
+    long ldc, sC;
+    int c_trans;
+    const float* rs;
+    long srs;
+    const float* cs;
+    long scs;
+    float alpha, beta;
+    int a_batched, b_batched;
+    int* err;
+};
+
+template <int BN, bool SPLIT>
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                         const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+    using Cfg = TcCfg<BN, SPLIT>;
+    constexpr int S = Cfg::STAGES;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[S], empty[S], done;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * TC_BM, z = blockIdx.z;
+    const int KT = (a.K + TC_BK - 1) / TC_BK;
+    const int za = a.a_batched ? z : 0, zb = a.b_batched ? z : 0;
+    const uint32_t idesc = idesc_tf32(TC_BM, BN);
+    const uint32_t stage_tx = Cfg::A_BYTES + Cfg::B_BYTES;
+
+    auto Ahi = [&](int s) { return base + (size_t)s * Cfg::STAGE_BYTES; };
+    auto Bhi = [&](int s) { return base + (size_t)s * Cfg::STAGE_BYTES + Cfg::A_BYTES; };
+    auto Alo = [&](int s) { return base + (size_t)s * Cfg::STAGE_BYTES + Cfg::A_BYTES + Cfg::B_BYTES; };
+    auto Blo = [&](int s) { return base + (size_t)s * Cfg::STAGE_BYTES + 2 * Cfg::A_BYTES + Cfg::B_BYTES; };
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // The split product rotates k-tiles over NACC accumulators (summed in FP32 by the epilogue):
+    // a shorter chain of in-pipe accumulations per accumulator keeps the result at FP32 accuracy.
+    constexpr int NACC = SPLIT ? 4 : 1;
+    constexpr uint32_t TMEM_COLS = (uint32_t)(BN * NACC);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_holder;
+
+    int issued = 0;  // k-tiles whose TMA was issued (thread 0 only)
+    if (tid == 0) {
+        for (int s = 0; s < S && s < KT; ++s) {
+            mbar_expect_tx(&full[s], stage_tx);
+            tma_load_3d(Ahi(s), &tmA, s * TC_BK, m0, za, &full[s]);
+            tma_load_3d(Bhi(s), &tmB, s * TC_BK, n0, zb, &full[s]);
+            ++issued;
+        }
+    }
+    int consumed = 0;   // k-tiles whose data every thread has waited for
+    int committed = 0;  // k-tiles whose MMAs were issued and committed (thread 0 only)
+    for (int kt = 0; kt < KT; ++kt) {
+        const int s = kt % S;
+        const uint32_t ph = (uint32_t)(kt / S) & 1u;
+        if (!mbar_wait(&full[s], ph, a.err)) s_abort = 1;
+        __syncthreads();
+        if (s_abort) break;
+        ++consumed;
+        if (SPLIT) {
+            // hi = x with the low 13 mantissa bits cleared, lo = x - hi, for both tiles of the stage
+            uint32_t* ah = (uint32_t*)Ahi(s);
+            uint32_t* al = (uint32_t*)Alo(s);
+            for (int e = tid; e < TC_BM * TC_BK; e += 128) {
+                const uint32_t x = ah[e];
+                const uint32_t h = x & 0xFFFFE000u;
+                ah[e] = h;
+                al[e] = __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
+            }
+            uint32_t* bh = (uint32_t*)Bhi(s);
+            uint32_t* bl = (uint32_t*)Blo(s);
+            for (int e = tid; e < BN * TC_BK; e += 128) {
+                const uint32_t x = bh[e];
+                const uint32_t h = x & 0xFFFFE000u;
+                bh[e] = h;
+                bl[e] = __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+        }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t dah = desc_sw128(Ahi(s)), dbh = desc_sw128(Bhi(s));
+            const uint64_t dal = SPLIT ? desc_sw128(Alo(s)) : 0, dbl = SPLIT ? desc_sw128(Blo(s)) : 0;
+            const uint32_t dacc = tmem + (uint32_t)((kt % NACC) * BN);
+#pragma unroll
+            for (int j = 0; j < TC_BK / 8; ++j) {
+                const uint64_t kofs = (uint64_t)(j * 32) >> 4;  // 8 TF32 = 32 bytes along K
+                mma_tf32(dacc, dah + kofs, dbh + kofs, idesc, (kt >= NACC || j > 0) ? 1u : 0u);
+                if (SPLIT) {
+                    mma_tf32(dacc, dal + kofs, dbh + kofs, idesc, 1u);
+                    mma_tf32(dacc, dah + kofs, dbl + kofs, idesc, 1u);
+                }
+            }
+            mma_commit(&empty[s]);
+            ++committed;
+            if (kt == KT - 1) mma_commit(&done);
+            // refill the stage consumed one iteration ago (its MMAs are queued ahead of these)
+            const int kr = kt - 1 + S;
+            if (kt >= 1 && kr < KT) {
+                const int sr = (kt - 1) % S;
+                const uint32_t phr = (uint32_t)((kt - 1) / S) & 1u;
+                if (mbar_wait(&empty[sr], phr, a.err)) {
+                    mbar_expect_tx(&full[sr], stage_tx);
+                    tma_load_3d(Ahi(sr), &tmA, kr * TC_BK, m0, za, &full[sr]);
+                    tma_load_3d(Bhi(sr), &tmB, kr * TC_BK, n0, zb, &full[sr]);
+                    ++issued;
+                } else {
+                    s_abort = 1;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (!s_abort) {
+        if (!mbar_wait(&done, 0, a.err)) s_abort = 1;
+    }
+    __syncthreads();
+    if (!s_abort) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int m = m0 + warp * 32 + lane;
+        float* C = a.C + (size_t)z * a.sC;
+        const float* rs = a.rs ? a.rs + (size_t)z * a.srs : nullptr;
+        const float* cs = a.cs ? a.cs + (size_t)z * a.scs : nullptr;
+        const float rsm = (rs && m < a.M) ? rs[m] : 1.0f;
+#pragma unroll 1
+        for (int cb = 0; cb < BN / 16; ++cb) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 16), v);
+            const int nacc = KT < NACC ? KT : NACC;
+            for (int q = 1; q < nacc; ++q) {
+                float v2[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * BN + cb * 16), v2);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] += v2[j];
+            }
+            if (m < a.M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + cb * 16 + j;
+                    if (n >= a.N) continue;
+                    float val = a.alpha * rsm * v[j];
+                    if (cs) val *= cs[n];
+                    const size_t o = a.c_trans ? (size_t)n * a.ldc + m : (size_t)m * a.ldc + n;
+                    C[o] = (a.beta == 0.0f) ? val : val + a.beta * C[o];
+                }
+            }
+        }
+    } else if (tid == 0) {
+        // drain (bounded): every issued copy must land and the last committed MMAs must finish
+        // before the CTA frees its TMEM and exits
+        for (int t = consumed; t < issued; ++t) mbar_wait(&full[t % S], (uint32_t)(t / S) & 1u, a.err);
+        if (committed > 0) {
+            const int t = committed - 1;
+            mbar_wait(&empty[t % S], (uint32_t)(t / S) & 1u, a.err);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 3D map over a row-major (rows x cols) FP32 matrix with leading dimension ld, batch stride sb
+// (elements), box = 32 columns x box_rows rows, 128-byte swizzle, zero fill out of bounds.
+bool make_tmap(CUtensorMap* tm, const float* ptr, int rows, int cols, long ld, int batch, long sb, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    if (((uintptr_t)ptr & 15) || ((ld * 4) & 15) || ((sb * 4) & 15)) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)sb * 4};
+    cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)ptr, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int BN, bool SPLIT>
+cudaError_t tc_launch(cudaStream_t st, const TcGemmArgs& g) {
+    using Cfg = TcCfg<BN, SPLIT>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute((void*)tc_gemm_kernel<BN, SPLIT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    CUtensorMap tmA, tmB;
+    const int ba = g.sA ? g.batch : 1, bb = g.sB ? g.batch : 1;
+    const long sA = g.sA ? g.sA : (long)g.M * g.lda, sB = g.sB ? g.sB : (long)g.N * g.ldb;
+    if (!make_tmap(&tmA, g.A, g.M, g.K, g.lda, ba, sA, TC_BM)) return cudaErrorInvalidValue;
+    if (!make_tmap(&tmB, g.Bt, g.N, g.K, g.ldb, bb, sB, BN)) return cudaErrorInvalidValue;
+    TcArgs a;
+    a.M = g.M; a.N = g.N; a.K = g.K;
+    a.C = g.C; a.ldc = g.ldc; a.sC = g.sC; a.c_trans = g.c_trans;
+    a.rs = g.rs; a.srs = g.srs; a.cs = g.cs; a.scs = g.scs;
+    a.alpha = g.alpha; a.beta = g.beta;
+    a.a_batched = g.sA != 0; a.b_batched = g.sB != 0;
+    a.err = g.err;
+    dim3 grid((g.N + BN - 1) / BN, (g.M + TC_BM - 1) / TC_BM, g.batch);
+    count_launch();
+    tc_gemm_kernel<BN, SPLIT><<<grid, 128, Cfg::SMEM, st>>>(tmA, tmB, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tc_gemm(cudaStream_t st, const TcGemmArgs& g) {
+    if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0) return cudaSuccess;
+    return g.split3 ? tc_launch<128, true>(st, g) : tc_launch<128, false>(st, g);
+}
+
+}  // namespace afq
