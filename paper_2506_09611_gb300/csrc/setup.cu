@@ -238,6 +238,7 @@ __global__ void __launch_bounds__(256) elim_kernel(int mode, double* A, int R, i
         __syncthreads();
         const int p = s_p;
         const double pv = s_pv;
+        const double pinv = 1.0 / pv;  // one division per step; the rows multiply
         if (read_err(err) != 0) return;
         if (b == 0 && tid == 0) {
             perm[j] = p;
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(256) elim_kernel(int mode, double* A, int R, i
         for (int q = tid; q < nr; q += nt) {
             int r = r0 + q;
             bool act = (mode == 0) ? !pflag[r] : (r != p);
-            s_l[q] = act ? elem(r, j) / pv : 0.0;
+            s_l[q] = act ? elem(r, j) * pinv : 0.0;
         }
         __syncthreads();
         const int w = ncols - j - 1;

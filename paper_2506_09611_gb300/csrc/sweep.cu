@@ -73,6 +73,9 @@ __global__ void __launch_bounds__(512) local_kernel(T* Gu, T* Gd, int8_t* xl_g, 
     int n_acc = 0;
     double maxr = 0.0;
     const int per_spin = nrows * N;
+    // flip constants in T: {dflip[0][+], dflip[0][-], dflip[1][+], dflip[1][-], sflip[+], sflip[-]}
+    const T cd[6] = {(T)sp.dflip[0][0], (T)sp.dflip[0][1], (T)sp.dflip[1][0], (T)sp.dflip[1][1], (T)sp.sflip[0],
+                     (T)sp.sflip[1]};
     for (int i = 0; i < N; ++i) {
         const int cur = i & 1, nxt = cur ^ 1;
         const T* col0 = colbuf + (cur * 2 + 0) * N;
@@ -81,25 +84,27 @@ __global__ void __launch_bounds__(512) local_kernel(T* Gu, T* Gd, int8_t* xl_g, 
         const T* row1 = rowbuf + (cur * 2 + 1) * N;
         // one thread per CTA takes the Metropolis decision (every CTA reaches the same one)
         if (tid == 0) {
+            // ratio arithmetic in the bulk precision T (no FP64 division on the FP32 path)
             const int xi = xs[i] > 0 ? 0 : 1;
-            const double rr0 = 1.0 + sp.dflip[0][xi] * (1.0 - (double)col0[i]);
-            const double rr1 = 1.0 + sp.dflip[1][xi] * (1.0 - (double)col1[i]);
-            const double R = sp.sflip[xi] * rr0 * rr1;
-            bool acc = replay ? (replay[i] != 0) : (u[i] < fabs(R));
+            const T d0 = xi ? cd[1] : cd[0], d1 = xi ? cd[3] : cd[2], sfl = xi ? cd[5] : cd[4];
+            const T rr0 = T(1) + d0 * (T(1) - col0[i]);
+            const T rr1 = T(1) + d1 * (T(1) - col1[i]);
+            const T R = sfl * rr0 * rr1;
+            bool acc = replay ? (replay[i] != 0) : (u[i] < (double)fabs(R));
             if (!isfinite(R)) {
                 if (b == 0) set_err(err, DEV_NUMERIC);
                 acc = false;
             }
             s_acc = acc ? 1 : 0;
-            s_f[0] = (T)(sp.dflip[0][xi] / rr0);
-            s_f[1] = (T)(sp.dflip[1][xi] / rr1);
+            s_f[0] = d0 / rr0;
+            s_f[1] = d1 / rr1;
             if (b == 0) {
                 so.dec[i] = acc ? 1 : 0;
-                so.ratio[i] = R;
+                so.ratio[i] = (double)R;
                 if (acc) {
                     xl_g[i] = (int8_t)(-xs[i]);
-                    if (R < 0) sign = -sign;
-                    maxr = fmax(maxr, fabs(R));
+                    if (R < T(0)) sign = -sign;
+                    maxr = fmax(maxr, (double)fabs(R));
                 }
             }
         }
@@ -267,17 +272,18 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
         int p = 0;
         while (p < n) {
             if (tid < 32) {
+                // ratio arithmetic in the bulk precision T (FP64 division on this critical path
+                // would cost thousands of cycles on GB300's FP64 pipe)
                 const int q = p + tid;
                 bool acc = false;
-                double R = 0.0, rr0 = 1.0, rr1 = 1.0;
+                T R = T(0), rr0 = T(1), rr1 = T(1);
                 int xi = 0;
                 if (q < n) {
-                    const int i = s0 + q;
                     xi = xw[q] > 0 ? 0 : 1;
-                    rr0 = 1.0 + c_dflip[0][xi] * (1.0 - (double)Gs[(0 * n + q) * P + q]);
-                    rr1 = 1.0 + c_dflip[1][xi] * (1.0 - (double)Gs[(1 * n + q) * P + q]);
-                    R = c_sflip[xi] * rr0 * rr1;
-                    acc = replay ? (s_rep[q] != 0) : (s_u[q] < fabs(R));
+                    rr0 = T(1) + (T)c_dflip[0][xi] * (T(1) - Gs[(0 * n + q) * P + q]);
+                    rr1 = T(1) + (T)c_dflip[1][xi] * (T(1) - Gs[(1 * n + q) * P + q]);
+                    R = (T)c_sflip[xi] * rr0 * rr1;
+                    acc = replay ? (s_rep[q] != 0) : (s_u[q] < (double)fabs(R));
                     if (!isfinite(R)) {
                         acc = false;
                         set_err(err, DEV_NUMERIC);
@@ -290,14 +296,15 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                     so.ratio[s0 + q] = R;
                 }
                 if (tid == first) {
-                    s_fa[0] = (T)(c_dflip[0][xi] / rr0);
-                    s_fa[1] = (T)(c_dflip[1][xi] / rr1);
+                    const T f0 = (T)c_dflip[0][xi] / rr0, f1 = (T)c_dflip[1][xi] / rr1;
+                    s_fa[0] = f0;
+                    s_fa[1] = f1;
                     idx[s_m] = q;
-                    dl[0 * n + s_m] = -c_dflip[0][xi] / rr0;  // recursion factor f = -Delta / r
-                    dl[1 * n + s_m] = -c_dflip[1][xi] / rr1;
+                    dl[0 * n + s_m] = -(double)f0;  // recursion factor f = -Delta / r
+                    dl[1 * n + s_m] = -(double)f1;
                     s_m = s_m + 1;
-                    if (R < 0) s_sign = -s_sign;
-                    s_maxr = fmax(s_maxr, fabs(R));
+                    if (R < T(0)) s_sign = -s_sign;
+                    s_maxr = fmax(s_maxr, (double)fabs(R));
                 }
                 if (tid == 0) {
                     s_apos = (first < 32) ? q + first : -1;
@@ -344,9 +351,9 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                 }
                 if (tid < 2) {
                     const int xi = xw[p0 + a] > 0 ? 0 : 1;
-                    const double db = c_dstrip[tid][xi];
-                    const double rr = 1.0 + db * (1.0 - (double)S1[(tid * NBMAX + a) * (NBMAX + 1) + a]);
-                    s_fs[tid] = (T)(db / rr);
+                    const T db = (T)c_dstrip[tid][xi];
+                    const T rr = T(1) + db * (T(1) - S1[(tid * NBMAX + a) * (NBMAX + 1) + a]);
+                    s_fs[tid] = db / rr;
                 }
                 __syncthreads();
                 for (int e = tid; e < 2 * nbk * nbk; e += nt) {
@@ -417,11 +424,11 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                 }
                 if (tid < 2) {
                     const int xi = xw[p0 + a] > 0 ? 0 : 1;
-                    const double dd = c_dflip[tid][xi];
-                    const double rr = 1.0 + dd * (1.0 - (double)S1[(tid * NBMAX + a) * (NBMAX + 1) + a]);
-                    s_rs[tid] *= rr;
-                    s_phi[tid][q] = (T)(dd / rr);
-                    fb[(4 + tid) * NBMAX + q] = dd;
+                    const T dd = (T)c_dflip[tid][xi];
+                    const T rr = T(1) + dd * (T(1) - S1[(tid * NBMAX + a) * (NBMAX + 1) + a]);
+                    s_rs[tid] *= (double)rr;
+                    s_phi[tid][q] = dd / rr;
+                    fb[(4 + tid) * NBMAX + q] = (double)dd;
                 }
                 __syncthreads();
                 for (int e = tid; e < 2 * nbk * nbk; e += nt) {
