@@ -51,12 +51,17 @@ struct Walker {
     void* rowbuf = nullptr;
     GridBar* bar = nullptr;
     int* err = nullptr;
-    int* wm = nullptr;
-    int* widx = nullptr;
-    double* wdtot = nullptr;
-    void* Wm = nullptr;
-    void* X = nullptr;
-    void* Y = nullptr;
+    // window buffers, double-buffered by window parity (the flush of window w overlaps the
+    // decisions of window w + 1), and the corrected snapshots of the next window's block
+    int* wm[2] = {nullptr, nullptr};
+    int* widx[2] = {nullptr, nullptr};
+    double* wdtot[2] = {nullptr, nullptr};
+    void* Wm[2] = {nullptr, nullptr};
+    void* X[2] = {nullptr, nullptr};
+    void* Y[2] = {nullptr, nullptr};
+    void* snap[2] = {nullptr, nullptr};
+    cudaStream_t sf = nullptr;  // flush stream
+    cudaEvent_t ev_chain[2] = {nullptr, nullptr}, ev_block[2] = {nullptr, nullptr}, ev_done = nullptr;
     double* URs[2] = {nullptr, nullptr};
     double* ULs[2] = {nullptr, nullptr};
     double* Ucur = nullptr;
@@ -368,6 +373,12 @@ int afqmc_destroy(afqmc_ctx* ctx) {
     cudaDeviceSynchronize();
     for (auto* w : ctx->w) {
         for (void* p : w->allocs) cudaFree(p);
+        for (int q = 0; q < 2; ++q) {
+            if (w->ev_chain[q]) cudaEventDestroy(w->ev_chain[q]);
+            if (w->ev_block[q]) cudaEventDestroy(w->ev_block[q]);
+        }
+        if (w->ev_done) cudaEventDestroy(w->ev_done);
+        if (w->sf) cudaStreamDestroy(w->sf);
         delete w;
     }
     for (void* p : ctx->allocs) cudaFree(p);
@@ -428,12 +439,23 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
         CK(dalloc(A, (char**)&w->rowbuf, 4 * (size_t)N * es));
         CK(dalloc(A, &w->bar, sizeof(GridBar)));
         CK(dalloc(A, &w->err, sizeof(int)));
-        CK(dalloc(A, &w->wm, sizeof(int)));
-        CK(dalloc(A, &w->widx, (size_t)NW * sizeof(int)));
-        CK(dalloc(A, &w->wdtot, 2 * (size_t)NW * 8));
-        CK(dalloc(A, (char**)&w->Wm, 2 * (size_t)NW * NW * es));
-        CK(dalloc(A, (char**)&w->X, 2 * (size_t)N * NW * es));
-        CK(dalloc(A, (char**)&w->Y, 4 * (size_t)NW * N * es));
+        for (int q = 0; q < 2; ++q) {
+            CK(dalloc(A, &w->wm[q], 2 * sizeof(int)));
+            CK(dalloc(A, &w->widx[q], (size_t)NW * sizeof(int)));
+            CK(dalloc(A, &w->wdtot[q], 2 * (size_t)NW * 8));
+            CK(dalloc(A, (char**)&w->Wm[q], 2 * (size_t)NW * NW * es));
+            CK(dalloc(A, (char**)&w->X[q], 2 * (size_t)N * NW * es));
+            CK(dalloc(A, (char**)&w->Y[q], 4 * (size_t)NW * N * es));
+            CK(dalloc(A, (char**)&w->snap[q], 2 * (size_t)NW * NW * es));
+            CK(cudaEventCreateWithFlags(&w->ev_chain[q], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&w->ev_block[q], cudaEventDisableTiming));
+        }
+        CK(cudaEventCreateWithFlags(&w->ev_done, cudaEventDisableTiming));
+        {
+            int lo = 0, hi = 0;
+            CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            CK(cudaStreamCreateWithPriority(&w->sf, cudaStreamNonBlocking, lo));
+        }
         for (int s = 0; s < 2; ++s) {
             CK(dalloc(A, &w->URs[s], (size_t)nst * N * w->ns[s] * 8));
             CK(dalloc(A, &w->ULs[s], (size_t)nst * N * w->ns[s] * 8));
@@ -447,9 +469,11 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
         CK(dalloc(A, (char**)&w->elim, elim_scratch_bytes(N > nsm ? N : nsm)));
         CK(dalloc(A, &w->acc2, 2 * 8));
         CK(cudaMemsetAsync(w->err, 0, sizeof(int), st));
-        CK(cudaMemsetAsync(w->Wm, 0, 2 * (size_t)NW * NW * es, st));
-        CK(cudaMemsetAsync(w->X, 0, 2 * (size_t)N * NW * es, st));
-        CK(cudaMemsetAsync(w->Y, 0, 4 * (size_t)NW * N * es, st));
+        for (int q = 0; q < 2; ++q) {
+            CK(cudaMemsetAsync(w->Wm[q], 0, 2 * (size_t)NW * NW * es, st));
+            CK(cudaMemsetAsync(w->X[q], 0, 2 * (size_t)N * NW * es, st));
+            CK(cudaMemsetAsync(w->Y[q], 0, 4 * (size_t)NW * N * es, st));
+        }
         CK(cudaMemsetAsync(w->G, 0, 2 * (size_t)N * ld * es, st));
         CK(cudaMemsetAsync(w->Tbuf, 0, 2 * (size_t)N * ld * es, st));
         // fields
@@ -633,24 +657,37 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
                            ctx->nsm));
     } else {
         int nw = (mode == AFQMC_MODE_DELAYED) ? k : (NW / nb) * nb;
-        WindowBufs wb;
-        wb.m = w->wm;
-        wb.idx = w->widx;
-        wb.dtot = w->wdtot;
-        wb.Wm = w->Wm;
-        wb.X = w->X;
-        wb.Y = w->Y;
-        for (int s0 = 0; s0 < N; s0 += nw) {
-            int n = (N - s0 < nw) ? N - s0 : nw;
-            {
-                PhaseScope ps(ctx, AFQMC_PHASE_CHAIN, st);
-                CK(launch_window_chain<T>(st, mode, G0, G1, xl, w->u, rep, sp, so, s0, n, nb, wb, w->err));
-            }
-            {
-                PhaseScope ps(ctx, AFQMC_PHASE_FLUSH, st);
-                CK(launch_flush_rec<T>(st, G0, G1, sp, wb, n));
-            }
+        // Window w's decisions run on st; its flush runs on the walker's flush stream sf and
+        // first publishes the corrected block of window w + 1, so the rank-m product of window
+        // w overlaps the decisions of window w + 1.
+        WindowBufs wb[2];
+        for (int q = 0; q < 2; ++q) {
+            wb[q].m = w->wm[q];
+            wb[q].idx = w->widx[q];
+            wb[q].dtot = w->wdtot[q];
+            wb[q].Wm = w->Wm[q];
+            wb[q].X = w->X[q];
+            wb[q].Y = w->Y[q];
         }
+        PhaseScope ps(ctx, AFQMC_PHASE_CHAIN, st);
+        int wi = 0;
+        for (int s0 = 0; s0 < N; s0 += nw, ++wi) {
+            const int n = (N - s0 < nw) ? N - s0 : nw;
+            const int par = wi & 1;
+            const T* blk = nullptr;
+            if (wi > 0) {
+                CK(cudaStreamWaitEvent(st, w->ev_block[par ^ 1], 0));
+                blk = (const T*)w->snap[par ^ 1];
+            }
+            CK(launch_window_chain<T>(st, mode, G0, G1, xl, w->u, rep, sp, so, s0, n, nb, wb[par], blk, w->err));
+            CK(cudaEventRecord(w->ev_chain[par], st));
+            CK(cudaStreamWaitEvent(w->sf, w->ev_chain[par], 0));
+            const int sn = s0 + n, nn = (sn < N) ? ((N - sn < nw) ? N - sn : nw) : 0;
+            PhaseScope pf(ctx, AFQMC_PHASE_FLUSH, w->sf);
+            CK(launch_flush_pipelined<T>(w->sf, G0, G1, sp, wb[par], n, sn, nn, (T*)w->snap[par], w->ev_block[par]));
+        }
+        CK(cudaEventRecord(w->ev_done, w->sf));
+        CK(cudaStreamWaitEvent(st, w->ev_done, 0));
     }
     if (dir < 0) CK(wrap(-1));
     return AFQMC_OK;
@@ -889,6 +926,8 @@ int afqmc_set_profiling(afqmc_ctx* ctx, int on) {
 int afqmc_get_profile(afqmc_ctx* ctx, double* ms, int64_t* intervals, int64_t* launches) {
     if (!ctx) return AFQMC_ERR_ARG;
     CK(cudaStreamSynchronize(ctx->last));
+    for (auto* w : ctx->w)
+        if (w->sf) CK(cudaStreamSynchronize(w->sf));
     for (auto& pe : ctx->prof.pending) {
         float t = 0.0f;
         CK(cudaEventElapsedTime(&t, pe.a, pe.b));

@@ -139,15 +139,15 @@ int window_max();      // largest window (sites) the chain kernel holds in share
 template <typename T>
 cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T* Gd, int8_t* xl, const double* u,
                                 const uint8_t* replay, const SiteParams& sp, SliceOut so, int s0, int n, int nb,
-                                WindowBufs wb, int* err);
+                                WindowBufs wb, const T* blk, int* err);
 template <typename T>
 cudaError_t launch_flush(cudaStream_t st, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw);
-// Flush of a window by the delayed-update recursion on the frozen block coefficients.
+// Pipelined flush of a window on stream sf: W from the frozen coefficients, panel gathers,
+// Y' = Wm Yraw, the corrected snapshot of the next window's block [sn, sn + nn) (skipped when
+// nn == 0), an event `block_ready`, then the rank-m product G <- G - X Y'.
 template <typename T>
-cudaError_t launch_flush_rec(cudaStream_t st, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw);
-// FP32 flush through the tensor-core GEMM (window buffers must start zeroed).
-cudaError_t launch_flush_tc(cudaStream_t st, float* Gu, float* Gd, const SiteParams& sp, WindowBufs wb, int* err,
-                            int split3);
+cudaError_t launch_flush_pipelined(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw,
+                                   int sn, int nn, T* snap, cudaEvent_t block_ready);
 // G_s[i][j] *= a_s[i] * b_s[j] for both spins (a, b: [2][N], spin stride N)
 template <typename T>
 cudaError_t launch_scale2(cudaStream_t st, T* G, long ld, int N, long sG, const T* a, const T* b);

@@ -173,9 +173,14 @@ __device__ __forceinline__ void better(double& bv, int& br, double v, int r) {
     if (v > bv || (v == bv && r < br)) { bv = v; br = r; }
 }
 
-// mode 0: tall LU on A (R x C, element (r,c) at A[r*rs + c*cs]), eliminate only non-pivoted rows.
-// mode 1: Gauss-Jordan on A (R x (R+nrhs), row-major ld = rs), eliminate every other row.
-__global__ void __launch_bounds__(256) elim_kernel(int mode, double* A, int R, int C, long rs, long cs, int nrhs,
+// MODE 0: tall LU on A (R x C), eliminate only non-pivoted rows (the multipliers stay in place).
+// MODE 1: Gauss-Jordan on A (R x (R + nrhs)), eliminate every row but the pivot row.
+// COLMAJ: element (r, c) at A[r + c * cs] (rows contiguous); else at A[r * rs + c].
+// Each CTA owns at most ELIM_ROWS consecutive rows; one grid barrier per pivot.
+constexpr int ELIM_ROWS = 16;
+
+template <int MODE, bool COLMAJ>
+__global__ void __launch_bounds__(256) elim_kernel(double* __restrict__ A, int R, int C, long rs, long cs, int nrhs,
                                                    int* perm, double* sign_out, unsigned char* scratch, int* err) {
     ElimScratch* sc = (ElimScratch*)scratch;
     Cand* cand = (Cand*)(scratch + sizeof(ElimScratch));
@@ -183,23 +188,23 @@ __global__ void __launch_bounds__(256) elim_kernel(int mode, double* A, int R, i
     int* visited = (int*)(((uintptr_t)(pflag + R) + 15) & ~(uintptr_t)15);
     const int nblk = gridDim.x, b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const int r0 = (int)((long)R * b / nblk), r1 = (int)((long)R * (b + 1) / nblk);
-    const int ncols = (mode == 0) ? C : R + nrhs;
-    const int nsteps = (mode == 0) ? C : R;
-    __shared__ double s_l[64];
+    const int nr = r1 - r0;
+    const int ncols = (MODE == 0) ? C : R + nrhs;
+    const int nsteps = (MODE == 0) ? C : R;
+    __shared__ double s_l[ELIM_ROWS];
     __shared__ double s_bv[8];
     __shared__ int s_br[8];
     __shared__ int s_p;
     __shared__ double s_pv;
-    // row-local pivot flags
-    for (int r = r0 + tid; r < r1; r += nt) pflag[r] = 0;
-    auto elem = [&](int r, int c) -> double& {
-        return (mode == 0) ? A[(long)r * rs + (long)c * cs] : A[(long)r * rs + c];
-    };
+    __shared__ int8_t s_flag[ELIM_ROWS];
+    auto at = [=](int r, int c) -> double* { return COLMAJ ? A + (size_t)c * cs + r : A + (size_t)r * rs + c; };
+    for (int q = tid; q < nr; q += nt) s_flag[q] = 0;
+    __syncthreads();
     auto block_candidate = [&](int j) {
         double bv = -1.0;
         int br = 0x7fffffff;
-        for (int r = r0 + tid; r < r1; r += nt)
-            if (!pflag[r]) better(bv, br, fabs(elem(r, j)), r);
+        for (int q = tid; q < nr; q += nt)
+            if (!s_flag[q]) better(bv, br, fabs(*at(r0 + q, j)), r0 + q);
         for (int o = 16; o > 0; o >>= 1) {
             double ov = __shfl_down_sync(0xffffffffu, bv, o);
             int orr = __shfl_down_sync(0xffffffffu, br, o);
@@ -232,58 +237,62 @@ __global__ void __launch_bounds__(256) elim_kernel(int mode, double* A, int R, i
                     br = 0;
                 }
                 s_p = br;
-                s_pv = elem(br, j);
+                s_pv = *at(br, j);
             }
         }
         __syncthreads();
         const int p = s_p;
-        const double pv = s_pv;
-        const double pinv = 1.0 / pv;  // one division per step; the rows multiply
+        const double pinv = 1.0 / s_pv;  // one division per step; the rows multiply
         if (read_err(err) != 0) return;
         if (b == 0 && tid == 0) {
             perm[j] = p;
-            if (pv < 0) sgn = -sgn;
+            if (s_pv < 0) sgn = -sgn;
         }
-        if (p >= r0 && p < r1 && tid == 0) pflag[p] = 1;
+        if (p >= r0 && p < r1 && tid == 0) s_flag[p - r0] = 1;
         __syncthreads();
-        // multipliers of the own rows
-        const int nr = r1 - r0;
-        for (int q = tid; q < nr; q += nt) {
-            int r = r0 + q;
-            bool act = (mode == 0) ? !pflag[r] : (r != p);
-            s_l[q] = act ? elem(r, j) * pinv : 0.0;
+        for (int q = tid; q < nr; q += nt) {  // multipliers of the own rows
+            const int r = r0 + q;
+            const bool act = (MODE == 0) ? !s_flag[q] : (r != p);
+            s_l[q] = act ? *at(r, j) * pinv : 0.0;
         }
         __syncthreads();
-        const int w = ncols - j - 1;
-        if (mode == 0 && rs == 1) {
-            // rows are contiguous in memory: consecutive threads take consecutive rows
-            for (int e = tid; e < nr * w; e += nt) {
-                const int q = e % nr, c = j + 1 + e / nr;
+        if (COLMAJ) {
+            // own rows are contiguous in each column: 16 threads per column, 16 columns at a time
+            const int q = tid & (ELIM_ROWS - 1);
+            if (q < nr) {
                 const double l = s_l[q];
-                if (l != 0.0) elem(r0 + q, c) -= l * elem(p, c);
+                if (l != 0.0) {
+                    double* a = A + (size_t)(r0 + q);
+                    const double* pc = A + (size_t)p;
+                    for (int c = j + 1 + (tid >> 4); c < ncols; c += nt >> 4) {
+                        const size_t o = (size_t)c * cs;
+                        a[o] -= l * pc[o];
+                    }
+                }
             }
         } else {
+            const double* prow = A + (size_t)p * rs;
             for (int q = 0; q < nr; ++q) {
                 const double l = s_l[q];
                 if (l == 0.0) continue;
-                const int r = r0 + q;
-                for (int c = j + 1 + tid; c < ncols; c += nt) elem(r, c) -= l * elem(p, c);
+                double* row = A + (size_t)(r0 + q) * rs;
+                for (int c = j + 1 + tid; c < ncols; c += nt) row[c] -= l * prow[c];
             }
         }
         for (int q = tid; q < nr; q += nt) {
-            int r = r0 + q;
-            bool act = (mode == 0) ? !pflag[r] : (r != p);
-            if (act) elem(r, j) = (mode == 0) ? s_l[q] : 0.0;
+            const int r = r0 + q;
+            const bool act = (MODE == 0) ? !s_flag[q] : (r != p);
+            if (act) *at(r, j) = (MODE == 0) ? s_l[q] : 0.0;
         }
         __syncthreads();
         if (j + 1 < nsteps) block_candidate(j + 1);
         if (!grid_barrier(&sc->bar, nblk, err)) return;
     }
-    if (mode == 0) {
+    if (MODE == 0) {
         // pivot rows of L': 1 on the diagonal position, 0 to its right
         for (long e = (long)b * nt + tid; e < (long)nsteps * C; e += (long)nblk * nt) {
             int j = (int)(e / C), c = (int)(e % C);
-            if (c >= j) elem(perm[j], c) = (c == j) ? 1.0 : 0.0;
+            if (c >= j) *at(perm[j], c) = (c == j) ? 1.0 : 0.0;
         }
     } else if (b == 0 && tid == 0) {
         // parity of the row permutation j -> perm[j]
@@ -296,6 +305,7 @@ __global__ void __launch_bounds__(256) elim_kernel(int mode, double* A, int R, i
         }
     }
     if (b == 0 && tid == 0 && sign_out) *sign_out *= sgn;
+    (void)pflag;
 }
 
 cudaError_t launch_elim(cudaStream_t st, int mode, double* A, int R, int C, long rs, long cs, int nrhs, int* perm,
@@ -303,17 +313,20 @@ cudaError_t launch_elim(cudaStream_t st, int mode, double* A, int R, int C, long
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int nblk = nsm < 1024 ? nsm : 1024;
-    if (nblk > R) nblk = R;
-    // rows per block must fit the multiplier cache
-    while ((R + nblk - 1) / nblk > 64) ++nblk;
-    if (nblk > nsm) return cudaErrorInvalidValue;
-    unsigned char* sc = (unsigned char*)scratch;
-    cudaError_t e = cudaMemsetAsync(sc, 0, sizeof(ElimScratch), st);
+    const bool colmaj = (mode == 0 && rs == 1);
+    void* fn = mode == 1 ? (void*)elim_kernel<1, false> : (colmaj ? (void*)elim_kernel<0, true> : (void*)elim_kernel<0, false>);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
     if (e != cudaSuccess) return e;
-    void* args[] = {&mode, &A, &R, &C, &rs, &cs, &nrhs, &perm, &sign_out, &sc, &err};
+    int nblk = nsm < R ? nsm : R;
+    if ((R + nblk - 1) / nblk > ELIM_ROWS) nblk = (R + ELIM_ROWS - 1) / ELIM_ROWS;  // at most ELIM_ROWS rows each
+    if (nblk > per_sm * nsm || nblk > 1024) return cudaErrorInvalidValue;            // must be co-resident
+    unsigned char* sc = (unsigned char*)scratch;
+    e = cudaMemsetAsync(sc, 0, sizeof(ElimScratch), st);
+    if (e != cudaSuccess) return e;
+    void* args[] = {&A, &R, &C, &rs, &cs, &nrhs, &perm, &sign_out, &sc, &err};
     count_launch();
-    return cudaLaunchCooperativeKernel((void*)elim_kernel, dim3(nblk), dim3(256), args, 0, st);
+    return cudaLaunchCooperativeKernel(fn, dim3(nblk), dim3(256), args, 0, st);
 }
 
 __global__ void gj_extract_kernel(const double* A, long ld, int R, int nrhs, const int* perm, double* Z, long ldz) {

@@ -172,7 +172,10 @@ template <typename T> struct WinCap;
 template <> struct WinCap<float> { static constexpr int NW = 128; };
 template <> struct WinCap<double> { static constexpr int NW = 64; };
 constexpr int NBMAX = 32;
-constexpr int WIN_THREADS = 1024;
+#ifndef AFQMC_WIN_THREADS
+#define AFQMC_WIN_THREADS 1024
+#endif
+constexpr int WIN_THREADS = AFQMC_WIN_THREADS;
 
 template <typename T>
 int window_max() { return WinCap<T>::NW; }
@@ -207,7 +210,8 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict__ Gu, const T* __restrict__ Gd,
                                                              int8_t* xl_g, const double* u,
                                                              const uint8_t* replay, SiteParams sp, SliceOut so,
-                                                             int s0, int n, int nb, WindowBufs wb, int* err) {
+                                                             int s0, int n, int nb, WindowBufs wb, const T* blk,
+                                                             int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = n + 1;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -234,18 +238,30 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
     __shared__ double s_R;
 
     const T* G[2] = {Gu, Gd};
+    // the n x n diagonal block of both spins: from G, or from the corrected snapshot the
+    // previous window's flush prepared (pitch NW, spin stride NW^2)
     for (int e = tid; e < 2 * n * n; e += nt) {
         int s = e / (n * n), rem = e % (n * n), a = rem / n, c = rem % n;
-        Gs[(s * n + a) * P + c] = G[s][(long)(s0 + a) * ld + (s0 + c)];
+        Gs[(s * n + a) * P + c] = blk ? blk[((size_t)s * WinCap<T>::NW + a) * WinCap<T>::NW + c]
+                                      : G[s][(long)(s0 + a) * ld + (s0 + c)];
     }
     for (int p = tid; p < n; p += nt) xw[p] = xl_g[s0 + p];
     // the window's site uniforms (and forced decisions) live in shared memory: the scan reads
     // them on its critical path
-    __shared__ double s_u[WinCap<float>::NW];
+    // (in the bulk precision: the delayed scan compares them with ratios computed in T)
+    __shared__ T s_u[WinCap<float>::NW];
     __shared__ uint8_t s_rep[WinCap<float>::NW];
+    __shared__ T s_rat[WinCap<float>::NW];    // ratio of every decided site, written out after the scan
+    __shared__ uint8_t s_dec[WinCap<float>::NW];
+    __shared__ int s_nneg;                    // number of accepted negative ratios (sign parity)
+    __shared__ T s_maxrT;
     for (int p = tid; p < n; p += nt) {
-        s_u[p] = u[s0 + p];
+        s_u[p] = (T)u[s0 + p];
         s_rep[p] = replay ? replay[s0 + p] : 0;
+    }
+    if (tid == 0) {
+        s_nneg = 0;
+        s_maxrT = T(0);
     }
     __shared__ double c_dflip[2][2], c_dstrip[2][2], c_sflip[2];
     if (tid < 4) {
@@ -269,6 +285,7 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
         // 32 sites on the current block at once and a ballot finds the first acceptance.
         __shared__ int s_next, s_apos;
         __shared__ T s_fa[2];
+        __shared__ T s_fT[2][WinCap<float>::NW];
         int p = 0;
         while (p < n) {
             if (tid < 32) {
@@ -283,7 +300,7 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                     rr0 = T(1) + (T)c_dflip[0][xi] * (T(1) - Gs[(0 * n + q) * P + q]);
                     rr1 = T(1) + (T)c_dflip[1][xi] * (T(1) - Gs[(1 * n + q) * P + q]);
                     R = (T)c_sflip[xi] * rr0 * rr1;
-                    acc = replay ? (s_rep[q] != 0) : (s_u[q] < (double)fabs(R));
+                    acc = replay ? (s_rep[q] != 0) : (s_u[q] < fabs(R));
                     if (!isfinite(R)) {
                         acc = false;
                         set_err(err, DEV_NUMERIC);
@@ -292,19 +309,19 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                 const unsigned ball = __ballot_sync(0xffffffffu, acc);
                 const int first = ball ? __ffs(ball) - 1 : 32;
                 if (q < n && tid <= first) {
-                    so.dec[s0 + q] = (tid == first) ? 1 : 0;
-                    so.ratio[s0 + q] = R;
+                    s_dec[q] = (tid == first) ? 1 : 0;
+                    s_rat[q] = R;
                 }
                 if (tid == first) {
                     const T f0 = (T)c_dflip[0][xi] / rr0, f1 = (T)c_dflip[1][xi] / rr1;
                     s_fa[0] = f0;
                     s_fa[1] = f1;
+                    s_fT[0][s_m] = -f0;  // recursion factor f = -Delta / r
+                    s_fT[1][s_m] = -f1;
                     idx[s_m] = q;
-                    dl[0 * n + s_m] = -(double)f0;  // recursion factor f = -Delta / r
-                    dl[1 * n + s_m] = -(double)f1;
                     s_m = s_m + 1;
-                    if (R < T(0)) s_sign = -s_sign;
-                    s_maxr = fmax(s_maxr, (double)fabs(R));
+                    if (R < T(0)) s_nneg = s_nneg + 1;
+                    s_maxrT = fmax(s_maxrT, fabs(R));
                 }
                 if (tid == 0) {
                     s_apos = (first < 32) ? q + first : -1;
@@ -324,6 +341,20 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
             trailing_update(Gs, n, P, a, s_fa[0], s_fa[1], tid, nt);
             __syncthreads();
         }
+        // off the critical path: decisions, ratios, factors and the sign in their ABI types
+        for (int q = tid; q < n; q += nt) {
+            so.dec[s0 + q] = s_dec[q];
+            so.ratio[s0 + q] = (double)s_rat[q];
+        }
+        for (int q = tid; q < s_m; q += nt) {
+            dl[0 * n + q] = (double)s_fT[0][q];
+            dl[1 * n + q] = (double)s_fT[1][q];
+        }
+        if (tid == 0) {
+            if (s_nneg & 1) s_sign = -s_sign;
+            s_maxr = fmax(s_maxr, (double)s_maxrT);
+        }
+        __syncthreads();
     } else {
         // ---- block force-bias (Sec. III.B) ----
         __shared__ T s_fs[2];
@@ -507,7 +538,7 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
 template <typename T>
 cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T* Gd, int8_t* xl,
                                 const double* u, const uint8_t* replay, const SiteParams& sp, SliceOut so,
-                                int s0, int n, int nb, WindowBufs wb, int* err) {
+                                int s0, int n, int nb, WindowBufs wb, const T* blk, int* err) {
     size_t shm = window_smem<T>(n);
     static bool attr_set[2] = {false, false};
     const int mi = (mode == AFQMC_MODE_DELAYED) ? 0 : 1;
@@ -522,10 +553,10 @@ cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T*
     count_launch();
     if (mode == AFQMC_MODE_DELAYED)
         window_kernel<T, AFQMC_MODE_DELAYED><<<1, WIN_THREADS, shm, st>>>(Gu, Gd, xl, u, replay, sp, so, s0, n, nb,
-                                                                          wb, err);
+                                                                          wb, blk, err);
     else
         window_kernel<T, AFQMC_MODE_BLOCKFB><<<1, WIN_THREADS, shm, st>>>(Gu, Gd, xl, u, replay, sp, so, s0, n, nb,
-                                                                          wb, err);
+                                                                          wb, blk, err);
     return cudaGetLastError();
 }
 
@@ -585,139 +616,126 @@ template cudaError_t launch_local<double>(cudaStream_t, double*, double*, int8_t
                                           const SiteParams&, SliceOut, double*, double*, GridBar*, int*, int);
 template cudaError_t launch_window_chain<float>(cudaStream_t, int, const float*, const float*, int8_t*,
                                                 const double*, const uint8_t*, const SiteParams&, SliceOut, int,
-                                                int, int, WindowBufs, int*);
+                                                int, int, WindowBufs, const float*, int*);
 template cudaError_t launch_window_chain<double>(cudaStream_t, int, const double*, const double*, int8_t*,
                                                  const double*, const uint8_t*, const SiteParams&, SliceOut, int,
-                                                 int, int, WindowBufs, int*);
-// Tensor-core flush (FP32 bulk): panels gathered K-major and zero-padded to the window pitch NW,
-//   X (N x NW) = G[:, I],  YrT (N x NW) = (E_I^T - G[I, :])^T,  X' = X W  (SIMT, K = m),
-//   G <- G - X' YrT^T      (tcgen05, K = NW; the padding columns of YrT are zero).
-__global__ void gather_tc_kernel(const float* __restrict__ Gu, const float* __restrict__ Gd, long ld, int N,
-                                 WindowBufs wb, int NW, float* YrT) {
-    const int m = *wb.m;
-    const int s = blockIdx.y;
-    const float* G = s ? Gd : Gu;
-    float* X = (float*)wb.X + (size_t)s * N * NW;
-    float* Yt = YrT + (size_t)s * N * NW;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N * NW; e += gridDim.x * blockDim.x) {
-        const int j = e / NW, a = e % NW;
-        if (a < m) {
-            const int I = wb.idx[a];
-            Yt[e] = (j == I ? 1.0f : 0.0f) - G[(long)I * ld + j];
-            X[e] = G[(long)j * ld + I];
-        } else {
-            Yt[e] = 0.0f;
-        }
-    }
-}
-
-cudaError_t launch_flush_tc(cudaStream_t st, float* Gu, float* Gd, const SiteParams& sp, WindowBufs wb, int* err,
-                            int split3) {
-    const int N = sp.N;
-    const int NW = WinCap<float>::NW;
-    float* YrT = (float*)wb.Y;                      // [2][N][NW]
-    float* Xp = (float*)wb.Y + (size_t)2 * N * NW;  // [2][N][NW]
-    count_launch();
-    gather_tc_kernel<<<dim3(256, 2), 256, 0, st>>>(Gu, Gd, sp.ld, N, wb, NW, YrT);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    GemmArgs<float> g;  // X' = X W (columns >= m of X' multiply zero columns of YrT)
-    g.M = N; g.N = NW; g.K = NW; g.Kdev = wb.m;
-    g.A = (const float*)wb.X; g.lda = NW; g.sA = (long)N * NW;
-    g.B = (const float*)wb.Wm; g.ldb = NW; g.sB = (long)NW * NW;
-    g.C = Xp; g.ldc = NW; g.sC = (long)N * NW;
-    g.batch = 2;
-    if ((e = gemm<float>(st, g)) != cudaSuccess) return e;
-    TcGemmArgs t;
-    t.M = N; t.N = N; t.K = NW; t.batch = 2;
-    t.A = Xp; t.lda = NW; t.sA = (long)N * NW;
-    t.Bt = YrT; t.ldb = NW; t.sB = (long)N * NW;
-    t.C = Gu; t.ldc = sp.ld; t.sC = (long)(Gd - Gu);
-    t.alpha = -1.0f; t.beta = 1.0f;
-    t.split3 = split3;
-    t.err = err;
-    return tc_gemm(st, t);
-}
-
+                                                 int, int, WindowBufs, const double*, int*);
 // ---------------------------------------------------------------------------
-// flush by the delayed-update recursion (Eq. DelayRgenk restated for G): with the accepted sites
-// i_1 < ... < i_m of the window, f_k = -Delta_k / r_k and the frozen block entries
-// C[k][k'] = G_{at acceptance}[i_k, i_k'],
-//   a_k[r] = f_k ( G0[r, i_k] - sum_{k'<k} a_k'[r] C[k'][k] )                 (column panel)
-//   b_k[j] = delta(i_k, j) - G0[i_k, j] - sum_{k'<k} f_k' C[k][k'] b_k'[j]      (row panel)
-// and G = G0 + sum_k a_k b_k^T is one rank-m product.  Every row r and column j is an
-// independent recursion: one thread each, no synchronisation.
+// Pipelined flush of one window (all on the flush stream).
+//
+// W from the frozen coefficients (the delayed-update recursion, Eq. DelayRgenk in G form):
+// with f_k = -Delta_k / r_k and C[k][k'] the block entry of sites i_k, i_k' frozen at
+// acceptance time, the accepted rank-1 vectors are a_k = G0[:, I] alpha_k and
+// b_k^T = beta_k^T (E_I^T - G0[I, :]), where per component c
+//   alpha_k[c] = f_k (delta_kc - sum_{k'<k} C[k'][k] alpha_k'[c]),
+//   beta_k[c]  = delta_kc - sum_{k'<k} f_k' C[k][k'] beta_k'[c],
+// so G = G0 + G0[:, I] (Ta Lb) (E_I^T - G0[I, :]) with Ta[c][k] = alpha_k[c], Lb[k][c] = beta_k[c].
+// w2_kernel stores Wm = -(Ta Lb) for the product G <- G - X (Wm Yraw).  Each component's
+// recursion is independent: one thread per component, no synchronisation.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(128) panels_kernel(const T* __restrict__ Gu, const T* __restrict__ Gd, long ld,
-                                                     int N, WindowBufs wb, T* Ap, T* Bp) {
+__global__ void __launch_bounds__(256) w2_kernel(WindowBufs wb) {
     constexpr int NW = WinCap<T>::NW;
-    extern __shared__ __align__(16) unsigned char panels_smem[];
-    T* Cs = (T*)panels_smem;  // [NW][NW + 1]
-    __shared__ T fs[NW];
-    __shared__ int Is[NW];
     const int m = *wb.m;
     if (m == 0) return;
-    const int s = blockIdx.y, kind = blockIdx.z;
-    const T* G = s ? Gd : Gu;
-    const T* Cg = (const T*)wb.Wm + (size_t)s * NW * NW;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Cs[(e / m) * (NW + 1) + e % m] = Cg[(e / m) * NW + e % m];
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        fs[k] = (T)wb.dtot[s * NW + k];
-        Is[k] = wb.idx[k];
+    const int s = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int Pm = m + 1;
+    extern __shared__ __align__(16) unsigned char w2_smem[];
+    T* Cs = (T*)w2_smem;  // [m][m+1]
+    T* Ta = Cs + (size_t)m * Pm;
+    T* Lb = Ta + (size_t)m * Pm;
+    __shared__ T fs[NW];
+    T* Wg = (T*)wb.Wm + (size_t)s * NW * NW;
+    for (int e = tid; e < m * m; e += nt) Cs[(e / m) * Pm + e % m] = Wg[(e / m) * NW + e % m];
+    for (int k = tid; k < m; k += nt) fs[k] = (T)wb.dtot[s * NW + k];
+    __syncthreads();
+    if (tid < m) {
+        const int c = tid;
+        for (int k = 0; k < m; ++k) {  // row c of Ta
+            T acc = (k == c) ? T(1) : T(0);
+            for (int kp = c; kp < k; ++kp) acc -= Cs[kp * Pm + k] * Ta[c * Pm + kp];
+            Ta[c * Pm + k] = (k < c) ? T(0) : fs[k] * acc;
+        }
+        for (int k = 0; k < m; ++k) {  // column c of Lb
+            T acc = (k == c) ? T(1) : T(0);
+            for (int kp = c; kp < k; ++kp) acc -= fs[kp] * Cs[k * Pm + kp] * Lb[kp * Pm + c];
+            Lb[k * Pm + c] = (k < c) ? T(0) : acc;
+        }
     }
     __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= N) return;
-    T v[NW];
-    if (kind == 0) {  // column panel, row t: A[s][t][k] = a_k[t]
-        T* out = Ap + (size_t)s * N * NW + (size_t)t * NW;
-        for (int k = 0; k < m; ++k) {
-            T acc = G[(long)t * ld + Is[k]];
-            for (int q = 0; q < k; ++q) acc -= v[q] * Cs[q * (NW + 1) + k];
-            v[k] = fs[k] * acc;
-            out[k] = v[k];
-        }
-    } else {  // row panel, column t: B[s][k][t] = b_k[t]
-        T* out = Bp + (size_t)s * NW * N;
-        for (int k = 0; k < m; ++k) {
-            T acc = (Is[k] == t ? T(1) : T(0)) - G[(long)Is[k] * ld + t];
-            for (int q = 0; q < k; ++q) acc -= fs[q] * Cs[k * (NW + 1) + q] * v[q];
-            v[k] = acc;
-            out[(size_t)k * N + t] = acc;
-        }
+    for (int e = tid; e < m * m; e += nt) {
+        const int a = e / m, b = e % m;
+        T acc = T(0);
+        for (int k = (a > b ? a : b); k < m; ++k) acc += Ta[a * Pm + k] * Lb[k * Pm + b];
+        Wg[a * NW + b] = -acc;
+    }
+}
+
+// snap[s][a][c] = G[s][sn + a][sn + c] - sum_{k<m} X[s][sn + a][k] Y'[s][k][sn + c]: the next
+// window's block as it will be after this window's product (taken before the product runs).
+template <typename T>
+__global__ void next_block_kernel(const T* __restrict__ Gu, const T* __restrict__ Gd, long ld, int N, WindowBufs wb,
+                                  int sn, int nn, T* snap) {
+    constexpr int NW = WinCap<T>::NW;
+    const int m = *wb.m;
+    const int s = blockIdx.y;
+    const T* G = s ? Gd : Gu;
+    const T* X = (const T*)wb.X + (size_t)s * N * NW;
+    const T* Yp = (const T*)wb.Y + (size_t)2 * NW * N + (size_t)s * NW * N;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nn * nn; e += gridDim.x * blockDim.x) {
+        const int a = e / nn, c = e % nn;
+        T v = G[(long)(sn + a) * ld + (sn + c)];
+        for (int k = 0; k < m; ++k) v -= X[(size_t)(sn + a) * NW + k] * Yp[(size_t)k * N + (sn + c)];
+        snap[((size_t)s * NW + a) * NW + c] = v;
     }
 }
 
 template <typename T>
-cudaError_t launch_flush_rec(cudaStream_t st, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw) {
-    const int N = sp.N;
+cudaError_t launch_flush_pipelined(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw,
+                                   int sn, int nn, T* snap, cudaEvent_t block_ready) {
     constexpr int NW = WinCap<T>::NW;
-    T* Ap = (T*)wb.X;  // [2][N][NW]
-    T* Bp = (T*)wb.Y;  // [2][NW][N]
-    const size_t shm = (size_t)NW * (NW + 1) * sizeof(T);
+    const int N = sp.N;
+    const size_t shm = 3 * (size_t)NW * (NW + 1) * sizeof(T);
     static bool attr = false;
     if (!attr) {
-        cudaError_t ea = cudaFuncSetAttribute((void*)panels_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        cudaError_t ea = cudaFuncSetAttribute((void*)w2_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         if (ea != cudaSuccess) return ea;
         attr = true;
     }
     count_launch();
-    panels_kernel<T><<<dim3((N + 127) / 128, 2, 2), 128, shm, st>>>(Gu, Gd, sp.ld, N, wb, Ap, Bp);
+    w2_kernel<T><<<2, 256, shm, sf>>>(wb);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    GemmArgs<T> h;  // G += A B (inner dimension m, read on the device)
+    count_launch();
+    gather_kernel<T><<<dim3(256, 2), 256, 0, sf>>>(Gu, Gd, sp.ld, N, wb, NW);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    GemmArgs<T> g;  // Y' = Wm Yraw
+    g.M = nw; g.N = N; g.K = nw; g.Kdev = wb.m;
+    g.A = (const T*)wb.Wm; g.lda = NW; g.sA = (long)NW * NW;
+    g.B = (const T*)wb.Y; g.ldb = N; g.sB = (long)NW * N;
+    g.C = (T*)wb.Y + (size_t)2 * NW * N; g.ldc = N; g.sC = (long)NW * N;
+    g.batch = 2;
+    if ((e = gemm<T>(sf, g)) != cudaSuccess) return e;
+    if (nn > 0) {
+        count_launch();
+        next_block_kernel<T><<<dim3((nn * nn + 255) / 256, 2), 256, 0, sf>>>(Gu, Gd, sp.ld, N, wb, sn, nn, snap);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = cudaEventRecord(block_ready, sf)) != cudaSuccess) return e;
+    GemmArgs<T> h;  // G <- G - X Y'
     h.M = N; h.N = N; h.K = nw; h.Kdev = wb.m;
-    h.A = Ap; h.lda = NW; h.sA = (long)N * NW;
-    h.B = Bp; h.ldb = N; h.sB = (long)NW * N;
+    h.A = (const T*)wb.X; h.lda = NW; h.sA = (long)N * NW;
+    h.B = (const T*)wb.Y + (size_t)2 * NW * N; h.ldb = N; h.sB = (long)NW * N;
     h.C = Gu; h.ldc = sp.ld; h.sC = (long)(Gd - Gu);
-    h.alpha = T(1); h.beta = T(1);
+    h.alpha = T(-1); h.beta = T(1);
     h.batch = 2;
-    return gemm<T>(st, h);
+    return gemm<T>(sf, h);
 }
 
-template cudaError_t launch_flush_rec<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int);
-template cudaError_t launch_flush_rec<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs, int);
+template cudaError_t launch_flush_pipelined<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int,
+                                                   int, int, float*, cudaEvent_t);
+template cudaError_t launch_flush_pipelined<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs,
+                                                    int, int, int, double*, cudaEvent_t);
 template cudaError_t launch_flush<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int);
 template cudaError_t launch_flush<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs, int);
 

@@ -20,6 +20,10 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "internal.h"
 
 namespace afq {
@@ -346,6 +350,34 @@ bool make_tmap(CUtensorMap* tm, const float* ptr, int rows, int cols, long ld, i
     return r == CUDA_SUCCESS;
 }
 
+// Encoded tensor maps are cached by their full description: the sweep reuses the same
+// buffers every slice, and encoding on every launch would starve the GPU of work.
+struct TmapKey {
+    const float* ptr;
+    int rows, cols, batch, box;
+    long ld, sb;
+    bool operator==(const TmapKey& o) const {
+        return ptr == o.ptr && rows == o.rows && cols == o.cols && batch == o.batch && box == o.box && ld == o.ld &&
+               sb == o.sb;
+    }
+};
+
+bool cached_tmap(CUtensorMap* tm, const float* ptr, int rows, int cols, long ld, int batch, long sb, int box_rows) {
+    static std::vector<std::pair<TmapKey, CUtensorMap>> cache;
+    static std::mutex mu;
+    const TmapKey k{ptr, rows, cols, batch, box_rows, ld, sb};
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& e : cache)
+        if (e.first == k) {
+            *tm = e.second;
+            return true;
+        }
+    if (!make_tmap(tm, ptr, rows, cols, ld, batch, sb, box_rows)) return false;
+    if (cache.size() >= 4096) cache.clear();
+    cache.emplace_back(k, *tm);
+    return true;
+}
+
 template <int BN, bool SPLIT>
 cudaError_t tc_launch(cudaStream_t st, const TcGemmArgs& g) {
     using Cfg = TcCfg<BN, SPLIT>;
@@ -359,8 +391,8 @@ cudaError_t tc_launch(cudaStream_t st, const TcGemmArgs& g) {
     CUtensorMap tmA, tmB;
     const int ba = g.sA ? g.batch : 1, bb = g.sB ? g.batch : 1;
     const long sA = g.sA ? g.sA : (long)g.M * g.lda, sB = g.sB ? g.sB : (long)g.N * g.ldb;
-    if (!make_tmap(&tmA, g.A, g.M, g.K, g.lda, ba, sA, TC_BM)) return cudaErrorInvalidValue;
-    if (!make_tmap(&tmB, g.Bt, g.N, g.K, g.ldb, bb, sB, BN)) return cudaErrorInvalidValue;
+    if (!cached_tmap(&tmA, g.A, g.M, g.K, g.lda, ba, sA, TC_BM)) return cudaErrorInvalidValue;
+    if (!cached_tmap(&tmB, g.Bt, g.N, g.K, g.ldb, bb, sB, BN)) return cudaErrorInvalidValue;
     TcArgs a;
     a.M = g.M; a.N = g.N; a.K = g.K;
     a.C = g.C; a.ldc = g.ldc; a.sC = g.sC; a.c_trans = g.c_trans;
