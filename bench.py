@@ -38,6 +38,7 @@ L, U, T_HOP, DTAU, M, STAB, FILLING = 40, 6.0, 1.0, 0.05, 80, 10, 0.875
 NS = inputs.n_sigma_for(L, FILLING)
 N = L * L
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+CPU_SLICES = 16  # oracle slice-steps of the cpu_baseline sample (about 10 s on 16 Arm cores)
 
 
 def parse():
@@ -265,9 +266,8 @@ def main():
 
     # ---------------- roofline of the dominant kernel ----------------
     pk, pk_src = peaks()
-    phases = {k: v for k, v in prof.items() if v["ms"] > 0}
-    dom = max(phases, key=lambda k: phases[k]["ms"])
-    roof = roofline_for(dom, prof, args, pk, pk_src)
+    kernels = kernel_rooflines(prof, args.gemm, pk, pk_src, args.steps)
+    roof = dict(kernels[0]) if kernels else None
 
     # ---------------- end to end through the C ABI with host buffers ----------------
     e2e = None
@@ -277,10 +277,10 @@ def main():
     ctx.close()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, secs = run_oracle_sample(3, args.k)
+        v, cores, secs = run_oracle_sample(CPU_SLICES, args.k)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "3 slice-steps (wrap + delayed update, k=%d) of the FP64 oracle at 40x40 from its own "
-                         "G(0) (M=10 init not timed); %.1f s of CPU work" % (args.k, secs)}
+               "sample": "%d slice-steps (wrap + delayed update, k=%d) of the FP64 oracle at 40x40 from its own "
+                         "G(0) (M=10 init not timed); %.1f s of CPU work" % (CPU_SLICES, args.k, secs)}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -294,13 +294,15 @@ def main():
             "update_only": {"value": update_only, "unit": UNIT,
                             "note": "prep + the window loop (decisions; the rank-m flushes overlap on a second "
                                     "stream): the paper's update time"},
-            "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
+            "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()
+                                   if k not in ("elim", "wrap_gemm", "flush_gemm")},
             "compare_sample": cmp,
             "speedup_update_only_vs_local": speedup,
             "G_err_fp32_vs_fp64_recompute": {"max": max(drifts) if drifts else None,
                                              "median": statistics.median(drifts) if drifts else None,
                                              "slices_between_recomputes": STAB},
             "roofline": roof,
+            "roofline_kernels": kernels[1:],
             "clocks": clocks,
             "gpu_launches": launches,
             "e2e": e2e,
@@ -311,37 +313,74 @@ def main():
         dist.destroy_process_group()
 
 
-def roofline_for(dom, prof, args, pk, pk_src):
-    """Achieved throughput of the dominant kernel: algorithmic work per launch / mean launch time."""
-    p = prof[dom]
-    if dom == "wrap":
-        # 2 batched GEMM launches per interval (+ one tiny scale kernel); each GEMM does 2 N^3 per spin
-        per_launch_ms = p["ms"] / (2 * p["intervals"])
-        flops = 2.0 * N ** 3 * 2
-        ach = flops / (per_launch_ms / 1e3) / 1e12
-        peak = fp32_alu_peak(pk)
-        return {"kernel": "wrap GEMM (SIMT FP32, batched over spins)", "bound": "alu", "achieved": ach,
-                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_source": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x %.0f MHz (sm_max_mhz of %s peaks)"
-                               % (pk.get("sm_max_mhz", 2070.0), pk_src)}
-    if dom == "recompute":
-        return {"kernel": "FP64 recompute (propagation GEMMs, pivoted elimination, G formation)",
-                "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
-                "traffic": None, "note": "phase-level only; see profiles/"}
-    if dom in ("chain", "flush"):
-        # flush: read + write G (both spins, FP32) per window
-        nwin = p["intervals"]
-        per_ms = p["ms"] / nwin
-        byts = 2 * 2 * N * N * 4
-        ach = byts / (per_ms / 1e3) / 1e9
-        return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": None}
-    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
-            "traffic": None}
+# Nominal dense FP64 rate of a GB300 (no measured FP64 peak is available): 1.25 TFLOP/s at
+# the 2070 MHz maximum SM clock, i.e. 2 FP64 FMA per SM per clock on 152 SMs.
+FP64_FMA_PER_SM_CLK = 2
+# TF32 tensor rate relative to bf16 (nominal dense 1.1 vs 2.25 PFLOP/s).
+TF32_OVER_BF16 = 1.1 / 2.25
+# DRAM bytes per launch (read + write) from one ncu capture of the current kernel, in bytes;
+# None when no capture of the current kernel exists.
+NCU_TRAFFIC = {"elim": None, "wrap_gemm": None, "flush_gemm": None}
 
 
 def fp32_alu_peak(pk):
     return 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+def fp64_alu_peak(pk):
+    return 152 * FP64_FMA_PER_SM_CLK * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+def kernel_rooflines(prof, gemm, pk, pk_src, steps):
+    """Per-kernel rooflines from the nested per-launch intervals of the timed region:
+    achieved = algorithmic work of the launches / their summed CUDA-event durations.
+    Returns a list sorted by total time (the first entry is the dominant kernel)."""
+    out = []
+    # Pivoted eliminations of the FP64 recompute: per spin and recompute one Gauss-Jordan
+    # solve of [O | U_L] (ns x (ns + N)): ns^3 + 2 ns^2 N flop; the remaining launches are the
+    # re-orthonormalisation LUs of the propagated N x ns factor: N ns^2 - ns^3 / 3 flop.
+    el = prof.get("elim", {"ms": 0.0, "intervals": 0})
+    if el["intervals"] > 0:
+        n_gj = 2 * prof["recompute"]["intervals"]
+        n_lu = el["intervals"] - n_gj
+        flop = n_gj * (NS ** 3 + 2.0 * NS ** 2 * N) + n_lu * (N * NS ** 2 - NS ** 3 / 3.0)
+        ach = flop / (el["ms"] / 1e3) / 1e12
+        peak = fp64_alu_peak(pk)
+        out.append({"kernel": "elim_kernel (FP64 pivoted LU / Gauss-Jordan of the recompute)", "bound": "alu",
+                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": NCU_TRAFFIC["elim"], "launches": el["intervals"],
+                    "ms_per_launch": el["ms"] / el["intervals"], "ms_per_step": el["ms"] / steps,
+                    "work_per_launch": flop / el["intervals"],
+                    "peak_source": "nominal FP64 1.25 TFLOP/s: 152 SMs x %d FMA x 2 flop x %.0f MHz (of %s "
+                                   "peaks)" % (FP64_FMA_PER_SM_CLK, pk.get("sm_max_mhz", 2070.0), pk_src)})
+    wg = prof.get("wrap_gemm", {"ms": 0.0, "intervals": 0})
+    if wg["intervals"] > 0:
+        flop = 2.0 * 2.0 * N ** 3  # one launch = one N x N x N product for both spins
+        ach = flop * wg["intervals"] / (wg["ms"] / 1e3) / 1e12
+        if gemm == "simt":
+            peak, src, bound = fp32_alu_peak(pk), "FP32 FMA pipes: 152 x 128 x 2 x sm_max_mhz", "alu"
+        else:
+            peak = pk["bf16_tflops"] * TF32_OVER_BF16
+            src = "TF32 = measured bf16 burst %.1f x nominal 1.1/2.25 (of %s)" % (pk["bf16_tflops"], pk_src)
+            if gemm == "tc3":
+                src += "; three TF32 MMAs per product (hi*hi + hi*lo + lo*hi), so frac <= 1/3"
+            bound = "tensor"
+        out.append({"kernel": "wrap GEMM (%s, both spins per launch)" % gemm, "bound": bound, "achieved": ach,
+                    "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": NCU_TRAFFIC["wrap_gemm"],
+                    "launches": wg["intervals"], "ms_per_launch": wg["ms"] / wg["intervals"],
+                    "ms_per_step": wg["ms"] / steps, "work_per_launch": flop, "peak_source": src})
+    fg = prof.get("flush_gemm", {"ms": 0.0, "intervals": 0})
+    if fg["intervals"] > 0:
+        byts = 2 * 2 * N * N * 4  # read + write of both spins' G (FP32); X and Y' panels are O(N m)
+        ach = byts * fg["intervals"] / (fg["ms"] / 1e3) / 1e9
+        out.append({"kernel": "rank-m flush product G -= X Y' (SIMT FP32, both spins)", "bound": "hbm",
+                    "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                    "traffic": NCU_TRAFFIC["flush_gemm"], "launches": fg["intervals"],
+                    "ms_per_launch": fg["ms"] / fg["intervals"], "ms_per_step": fg["ms"] / steps,
+                    "work_per_launch": byts,
+                    "peak_source": "measured copy bandwidth (of %s); G (2 x 10 MB) is L2-resident" % pk_src})
+    out.sort(key=lambda r: -r["ms_per_step"])
+    return out
 
 
 def end_to_end(afqmc, torch, stream, args, seed, rank):

@@ -190,7 +190,11 @@ int afqmc_apply_flips_noalloc(int precision, int N, long long ld, void* G_up, vo
 #define AFQMC_PHASE_CHAIN 3      /* delayed / block-FB window decisions (one CTA per window) */
 #define AFQMC_PHASE_FLUSH 4      /* panel gather + rank-m product of the delayed / block-FB update */
 #define AFQMC_PHASE_RECOMPUTE 5  /* FP64 propagation, re-orthonormalisation and G = 1 - U_R T U_L */
-#define AFQMC_NPHASE 6
+/* Nested intervals inside the phases above, one per kernel launch (for per-kernel rooflines): */
+#define AFQMC_PHASE_ELIM 6       /* each pivoted-elimination launch (inside RECOMPUTE) */
+#define AFQMC_PHASE_WRAP_GEMM 7  /* each wrap product launch (inside WRAP) */
+#define AFQMC_PHASE_FLUSH_GEMM 8 /* each rank-m product launch of the flush (inside FLUSH) */
+#define AFQMC_NPHASE 9
 /* on != 0 enables profiling and clears the accumulators; on == 0 disables it. */
 int afqmc_set_profiling(afqmc_ctx* ctx, int on);
 /* Sync the last stream and return, per phase, the summed device milliseconds, the number of

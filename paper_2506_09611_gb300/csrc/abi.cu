@@ -57,11 +57,12 @@ struct Walker {
     int* widx[2] = {nullptr, nullptr};
     double* wdtot[2] = {nullptr, nullptr};
     void* Wm[2] = {nullptr, nullptr};
+    void* Wx[2] = {nullptr, nullptr};
     void* X[2] = {nullptr, nullptr};
     void* Y[2] = {nullptr, nullptr};
     void* snap[2] = {nullptr, nullptr};
     cudaStream_t sf = nullptr;  // flush stream
-    cudaEvent_t ev_chain[2] = {nullptr, nullptr}, ev_block[2] = {nullptr, nullptr}, ev_done = nullptr;
+    cudaEvent_t ev_chain[2] = {nullptr, nullptr}, ev_prod[2] = {nullptr, nullptr}, ev_done = nullptr;
     double* URs[2] = {nullptr, nullptr};
     double* ULs[2] = {nullptr, nullptr};
     double* Ucur = nullptr;
@@ -242,7 +243,10 @@ static cudaError_t form_G(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, con
     if (e != cudaSuccess) return e;
     e = cudaMemcpy2DAsync(w->aug + ns, la * 8, UL, (size_t)N * 8, (size_t)N * 8, ns, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
-    e = launch_elim(st, 1, w->aug, ns, ns, la, 1, N, w->perm, sign, w->elim, w->err);
+    {
+        PhaseScope ps(ctx, AFQMC_PHASE_ELIM, st);
+        e = launch_elim(st, 1, w->aug, ns, ns, la, 1, N, w->perm, sign, w->elim, w->err);
+    }
     if (e != cudaSuccess) return e;
     e = launch_gj_extract(st, w->aug, la, ns, N, w->perm, w->Z, N);
     if (e != cudaSuccess) return e;
@@ -300,10 +304,12 @@ static cudaError_t prop_left(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, 
     return gemm<double>(st, gy);
 }
 
-static cudaError_t stab_right(Walker* w, cudaStream_t st, int s, double* U, double* sign) {  // U: N x ns
+static cudaError_t stab_right(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, double* U, double* sign) {
+    PhaseScope ps(ctx, AFQMC_PHASE_ELIM, st);  // U: N x ns
     return launch_elim(st, 0, U, w->N, w->ns[s], w->ns[s], 1, 0, w->perm, sign, w->elim, w->err);
 }
-static cudaError_t stab_left(Walker* w, cudaStream_t st, int s, double* U, double* sign) {  // U: ns x N
+static cudaError_t stab_left(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, double* U, double* sign) {
+    PhaseScope ps(ctx, AFQMC_PHASE_ELIM, st);  // U: ns x N
     return launch_elim(st, 0, U, w->N, w->ns[s], 1, w->N, 0, w->perm, sign, w->elim, w->err);
 }
 
@@ -375,7 +381,7 @@ int afqmc_destroy(afqmc_ctx* ctx) {
         for (void* p : w->allocs) cudaFree(p);
         for (int q = 0; q < 2; ++q) {
             if (w->ev_chain[q]) cudaEventDestroy(w->ev_chain[q]);
-            if (w->ev_block[q]) cudaEventDestroy(w->ev_block[q]);
+            if (w->ev_prod[q]) cudaEventDestroy(w->ev_prod[q]);
         }
         if (w->ev_done) cudaEventDestroy(w->ev_done);
         if (w->sf) cudaStreamDestroy(w->sf);
@@ -444,11 +450,12 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
             CK(dalloc(A, &w->widx[q], (size_t)NW * sizeof(int)));
             CK(dalloc(A, &w->wdtot[q], 2 * (size_t)NW * 8));
             CK(dalloc(A, (char**)&w->Wm[q], 2 * (size_t)NW * NW * es));
+            CK(dalloc(A, (char**)&w->Wx[q], 2 * (size_t)NW * NW * es));
             CK(dalloc(A, (char**)&w->X[q], 2 * (size_t)N * NW * es));
             CK(dalloc(A, (char**)&w->Y[q], 4 * (size_t)NW * N * es));
             CK(dalloc(A, (char**)&w->snap[q], 2 * (size_t)NW * NW * es));
             CK(cudaEventCreateWithFlags(&w->ev_chain[q], cudaEventDisableTiming));
-            CK(cudaEventCreateWithFlags(&w->ev_block[q], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&w->ev_prod[q], cudaEventDisableTiming));
         }
         CK(cudaEventCreateWithFlags(&w->ev_done, cudaEventDisableTiming));
         {
@@ -499,15 +506,15 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
             count_launch();
             transpose_kernel<<<256, 256, 0, st>>>(UR0, N, ns, w->Ucur);  // Ucur = P^T (ns x N)
             CK(cudaGetLastError());
-            CK(stab_right(w, st, s, UR0, w->sign));
+            CK(stab_right(ctx, w, st, s, UR0, w->sign));
             // left stack: U_L(M) = P^T, U_L(l-1) = U_L(l) B_l
-            CK(stab_left(w, st, s, w->Ucur, w->sign));
+            CK(stab_left(ctx, w, st, s, w->Ucur, w->sign));
             CK(cudaMemcpyAsync(w->ULs[s] + (size_t)(M / S) * N * ns, w->Ucur, (size_t)N * ns * 8,
                                cudaMemcpyDeviceToDevice, st));
             for (int ell = M; ell >= 1; --ell) {
                 CK(prop_left(ctx, w, st, s, ell, w->Ucur, w->Utmp));
                 if ((ell - 1) % S == 0) {
-                    CK(stab_left(w, st, s, w->Ucur, w->sign));
+                    CK(stab_left(ctx, w, st, s, w->Ucur, w->sign));
                     CK(cudaMemcpyAsync(w->ULs[s] + (size_t)((ell - 1) / S) * N * ns, w->Ucur, (size_t)N * ns * 8,
                                        cudaMemcpyDeviceToDevice, st));
                 }
@@ -582,7 +589,10 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
             t1.C = Tf; t1.ldc = ld; t1.sC = (long)N * ld; t1.c_trans = 1;
             t1.split3 = split3;
             t1.err = w->err;
-            if ((e = tc_gemm(st, t1)) != cudaSuccess) return e;
+            {
+                PhaseScope pg(ctx, AFQMC_PHASE_WRAP_GEMM, st);
+                if ((e = tc_gemm(st, t1)) != cudaSuccess) return e;
+            }
             TcGemmArgs t2;
             t2.M = N; t2.N = N; t2.K = N; t2.batch = 2;
             t2.A = direction > 0 ? Ef : Eif; t2.lda = ld; t2.sA = 0;
@@ -594,6 +604,7 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
             }
             t2.split3 = split3;
             t2.err = w->err;
+            PhaseScope pg(ctx, AFQMC_PHASE_WRAP_GEMM, st);
             return tc_gemm(st, t2);
         }
         GemmArgs<T> g1, g2;
@@ -619,8 +630,12 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
             g2.B = E; g2.sB = 0;
             g2.C = G0;
         }
-        e = gemm<T>(st, g1);
+        {
+            PhaseScope pg(ctx, AFQMC_PHASE_WRAP_GEMM, st);
+            e = gemm<T>(st, g1);
+        }
         if (e != cudaSuccess) return e;
+        PhaseScope pg(ctx, AFQMC_PHASE_WRAP_GEMM, st);
         return gemm<T>(st, g2);
     };
     if (dir > 0) CK(wrap(+1));
@@ -657,15 +672,18 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
                            ctx->nsm));
     } else {
         int nw = (mode == AFQMC_MODE_DELAYED) ? k : (NW / nb) * nb;
-        // Window w's decisions run on st; its flush runs on the walker's flush stream sf and
-        // first publishes the corrected block of window w + 1, so the rank-m product of window
-        // w overlaps the decisions of window w + 1.
+        // Window w's decisions and the corrected block of window w + 1 run on st; window w's
+        // panels and rank-m product run on the walker's flush stream sf and overlap the
+        // decisions of window w + 1.  Before building window w + 1's block, st waits for the
+        // product of window w - 1 (ev_prod), which is also what frees the window buffers of
+        // parity (w + 1) & 1 for reuse.
         WindowBufs wb[2];
         for (int q = 0; q < 2; ++q) {
             wb[q].m = w->wm[q];
             wb[q].idx = w->widx[q];
             wb[q].dtot = w->wdtot[q];
             wb[q].Wm = w->Wm[q];
+            wb[q].Wx = w->Wx[q];
             wb[q].X = w->X[q];
             wb[q].Y = w->Y[q];
         }
@@ -674,17 +692,22 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
         for (int s0 = 0; s0 < N; s0 += nw, ++wi) {
             const int n = (N - s0 < nw) ? N - s0 : nw;
             const int par = wi & 1;
-            const T* blk = nullptr;
-            if (wi > 0) {
-                CK(cudaStreamWaitEvent(st, w->ev_block[par ^ 1], 0));
-                blk = (const T*)w->snap[par ^ 1];
-            }
+            const T* blk = (wi > 0) ? (const T*)w->snap[par ^ 1] : nullptr;
             CK(launch_window_chain<T>(st, mode, G0, G1, xl, w->u, rep, sp, so, s0, n, nb, wb[par], blk, w->err));
+            const int sn = s0 + n, nn = (sn < N) ? ((N - sn < nw) ? N - sn : nw) : 0;
+            if (nn > 0) {  // the next window's block
+                if (wi > 0) CK(cudaStreamWaitEvent(st, w->ev_prod[par ^ 1], 0));
+                CK(launch_next_block<T>(st, G0, G1, sp, wb[par], sn, nn, (T*)w->snap[par]));
+            }
             CK(cudaEventRecord(w->ev_chain[par], st));
             CK(cudaStreamWaitEvent(w->sf, w->ev_chain[par], 0));
-            const int sn = s0 + n, nn = (sn < N) ? ((N - sn < nw) ? N - sn : nw) : 0;
             PhaseScope pf(ctx, AFQMC_PHASE_FLUSH, w->sf);
-            CK(launch_flush_pipelined<T>(w->sf, G0, G1, sp, wb[par], n, sn, nn, (T*)w->snap[par], w->ev_block[par]));
+            CK(launch_flush_panels<T>(w->sf, G0, G1, sp, wb[par], n));
+            {
+                PhaseScope pg(ctx, AFQMC_PHASE_FLUSH_GEMM, w->sf);
+                CK(launch_flush_gemm<T>(w->sf, G0, G1, sp, wb[par], n));
+            }
+            CK(cudaEventRecord(w->ev_prod[par], w->sf));
         }
         CK(cudaEventRecord(w->ev_done, w->sf));
         CK(cudaStreamWaitEvent(st, w->ev_done, 0));
@@ -768,7 +791,7 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
                 } else {
                     CK(cudaMemcpyAsync(w->Ucur, w->URs[s] + (size_t)(j - 1) * blk, blk * 8, cudaMemcpyDeviceToDevice, st));
                     for (int ell = w->pos - S + 1; ell <= w->pos; ++ell) CK(prop_right(ctx, w, st, s, ell, w->Ucur, w->Utmp));
-                    CK(stab_right(w, st, s, w->Ucur, nullptr));
+                    CK(stab_right(ctx, w, st, s, w->Ucur, nullptr));
                     CK(cudaMemcpyAsync(w->URs[s] + (size_t)j * blk, w->Ucur, blk * 8, cudaMemcpyDeviceToDevice, st));
                     UR = w->URs[s] + (size_t)j * blk;
                 }
@@ -780,7 +803,7 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
                 } else {
                     CK(cudaMemcpyAsync(w->Ucur, w->ULs[s] + (size_t)(j + 1) * blk, blk * 8, cudaMemcpyDeviceToDevice, st));
                     for (int ell = w->pos + S; ell >= w->pos + 1; --ell) CK(prop_left(ctx, w, st, s, ell, w->Ucur, w->Utmp));
-                    CK(stab_left(w, st, s, w->Ucur, nullptr));
+                    CK(stab_left(ctx, w, st, s, w->Ucur, nullptr));
                     CK(cudaMemcpyAsync(w->ULs[s] + (size_t)j * blk, w->Ucur, blk * 8, cudaMemcpyDeviceToDevice, st));
                     UL = w->ULs[s] + (size_t)j * blk;
                 }

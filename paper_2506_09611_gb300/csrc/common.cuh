@@ -97,6 +97,11 @@ __device__ __forceinline__ bool grid_barrier(GridBar* b, unsigned int nblocks, i
     return s_ok != 0;
 }
 
+// Barrier `id` (1..15) over the first `nthreads` threads of the block (whole warps).
+__device__ __forceinline__ void named_barrier_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 // Field-change factor Delta = exp(c (x' - x)) - 1 for one site and spin (Sec. II.C).
 __device__ __forceinline__ double field_delta(double c, int x, int xp) {
     return exp(c * (double)(xp - x)) - 1.0;

@@ -32,6 +32,7 @@ static WindowBufs flips_layout(unsigned char* scratch, int N) {
     wb.idx = (int*)(scratch + off);
     off += al(NW * sizeof(int));
     wb.Wm = scratch + off;
+    wb.Wx = nullptr;
     off += al(2 * NW * NW * sizeof(T));
     wb.X = scratch + off;
     off += al(2 * (size_t)N * NW * sizeof(T));

@@ -129,6 +129,7 @@ struct WindowBufs {    // device scratch of the window chain + flush
     int* idx;          // accepted site indices (global), capacity NW
     double* dtot;      // per spin, 2 x NW: sweep: recursion factor -Delta/r; apply_flips: unused
     void* Wm;          // per spin NW x NW (T): sweep: frozen block coefficients; apply_flips: W
+    void* Wx;          // per spin NW x NW (T): sweep: the window's update matrix W
     void* X;           // per spin N x NW column panel (T)
     void* Y;           // per spin NW x N row panel (T), plus room for a second product
 };
@@ -142,12 +143,18 @@ cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T*
                                 WindowBufs wb, const T* blk, int* err);
 template <typename T>
 cudaError_t launch_flush(cudaStream_t st, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw);
-// Pipelined flush of a window on stream sf: W from the frozen coefficients, panel gathers,
-// Y' = Wm Yraw, the corrected snapshot of the next window's block [sn, sn + nn) (skipped when
-// nn == 0), an event `block_ready`, then the rank-m product G <- G - X Y'.
+// Pipelined flush of a window (the window kernel leaves its update matrix W in wb.Wx):
+//   launch_next_block   -- the next window's block [sn, sn + nn) of both spins as it will be
+//                          after this window's update; run right after the window kernel;
+//   launch_flush_panels -- X = G[:, I], Yraw = E_I^T - G[I, :], Y' = W Yraw;
+//   launch_flush_gemm   -- G <- G - X Y'.
 template <typename T>
-cudaError_t launch_flush_pipelined(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw,
-                                   int sn, int nn, T* snap, cudaEvent_t block_ready);
+cudaError_t launch_next_block(cudaStream_t st, const T* Gu, const T* Gd, const SiteParams& sp, WindowBufs wb, int sn,
+                              int nn, T* snap);
+template <typename T>
+cudaError_t launch_flush_panels(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw);
+template <typename T>
+cudaError_t launch_flush_gemm(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw);
 // G_s[i][j] *= a_s[i] * b_s[j] for both spins (a, b: [2][N], spin stride N)
 template <typename T>
 cudaError_t launch_scale2(cudaStream_t st, T* G, long ld, int N, long sG, const T* a, const T* b);

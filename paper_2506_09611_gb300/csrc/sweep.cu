@@ -172,10 +172,7 @@ template <typename T> struct WinCap;
 template <> struct WinCap<float> { static constexpr int NW = 128; };
 template <> struct WinCap<double> { static constexpr int NW = 64; };
 constexpr int NBMAX = 32;
-#ifndef AFQMC_WIN_THREADS
-#define AFQMC_WIN_THREADS 1024
-#endif
-constexpr int WIN_THREADS = AFQMC_WIN_THREADS;
+constexpr int WIN_THREADS = 1024;  // 32 warps: the tail's W solve assigns 16 warps to each spin
 
 template <typename T>
 int window_max() { return WinCap<T>::NW; }
@@ -202,6 +199,89 @@ __device__ __forceinline__ void trailing_update(T* Gs, int n, int P, int a, T f0
         for (int r = a + 1 + ty; r < n; r += ny) {
             const T g = f * Gb[r * P + a];
             for (int c = a + 1 + tx; c < n; c += 32) Gb[r * P + c] += g * Gb[a * P + c];
+        }
+    }
+}
+
+// W = -F U1^{-1} L1^{-1} of the window from the frozen coefficients in the block (see the window
+// kernel's tail); written to Wx[s][k][j] (pitch NW).  32 warps: spin = warp / 16, columns
+// (warp % 16) * WCPW + c.
+template <typename T>
+__device__ __forceinline__ void window_w(const T* Gs, int n, int P, const int* idx, const T (*fk)[WinCap<T>::NW],
+                                         int m, T* Wx, int tid) {
+    constexpr int NW = WinCap<T>::NW, RPL = NW / 32, WCPW = NW / 16;
+    const int lane = tid & 31, w = tid >> 5;
+    if (w >= 32) return;
+    const int s = w >> 4, j0 = (w & 15) * WCPW;
+    if (j0 >= m) return;
+    const T* Gb = Gs + (size_t)s * n * P;
+    const int rmax = (m + 31) >> 5;
+    int ik[RPL];
+    T y[RPL][WCPW];
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        const int k = lane + 32 * r;
+        ik[r] = (k < m) ? idx[k] : 0;
+#pragma unroll
+        for (int c = 0; c < WCPW; ++c) y[r][c] = (k == j0 + c) ? T(1) : T(0);
+    }
+    // forward: rows k > kp
+    for (int kp = 0; kp + 1 < m; ++kp) {
+        const int ikp = idx[kp], ro = kp >> 5, lo = kp & 31;
+        const T fkp = fk[s][kp];
+        T v[WCPW];
+#pragma unroll
+        for (int c = 0; c < WCPW; ++c) {
+            T src = y[0][c];
+#pragma unroll
+            for (int r = 1; r < RPL; ++r)
+                if (ro == r) src = y[r][c];
+            v[c] = __shfl_sync(0xffffffffu, src, lo);
+        }
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            if (r >= rmax) break;
+            const int k = lane + 32 * r;
+            if (k > kp && k < m) {
+                const T cf = Gb[ik[r] * P + ikp] * fkp;
+#pragma unroll
+                for (int c = 0; c < WCPW; ++c) y[r][c] -= cf * v[c];
+            }
+        }
+    }
+    // backward: rows k < kp
+    for (int kp = m - 1; kp >= 1; --kp) {
+        const int ikp = idx[kp], ro = kp >> 5, lo = kp & 31;
+        const T fkp = fk[s][kp];
+        T v[WCPW];
+#pragma unroll
+        for (int c = 0; c < WCPW; ++c) {
+            T src = y[0][c];
+#pragma unroll
+            for (int r = 1; r < RPL; ++r)
+                if (ro == r) src = y[r][c];
+            v[c] = __shfl_sync(0xffffffffu, src, lo);
+        }
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            if (r >= rmax) break;
+            const int k = lane + 32 * r;
+            if (k < kp) {
+                const T cf = Gb[ik[r] * P + ikp] * fkp;
+#pragma unroll
+                for (int c = 0; c < WCPW; ++c) y[r][c] -= cf * v[c];
+            }
+        }
+    }
+    T* Wd = Wx + (size_t)s * NW * NW;
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        const int k = lane + 32 * r;
+        if (k < m) {
+            const T fkk = -fk[s][k];
+#pragma unroll
+            for (int c = 0; c < WCPW; ++c)
+                if (j0 + c < m) Wd[k * NW + j0 + c] = fkk * y[r][c];
         }
     }
 }
@@ -233,9 +313,11 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
     off += (size_t)n * sizeof(int);
     int8_t* xw = (int8_t*)(smem_raw + off);  // window fields [n]
     off += (size_t)n;
-    __shared__ int s_m, s_piv, s_nF;
+    __shared__ int s_m, s_nF;
     __shared__ int s_F[NBMAX];
     __shared__ double s_R;
+    constexpr int NWC = WinCap<T>::NW;
+    __shared__ T s_fk[2][NWC];  // f_k = -Delta_k / r_k of accept k, both spins
 
     const T* G[2] = {Gu, Gd};
     // the n x n diagonal block of both spins: from G, or from the corrected snapshot the
@@ -285,7 +367,6 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
         // 32 sites on the current block at once and a ballot finds the first acceptance.
         __shared__ int s_next, s_apos;
         __shared__ T s_fa[2];
-        __shared__ T s_fT[2][WinCap<float>::NW];
         int p = 0;
         while (p < n) {
             if (tid < 32) {
@@ -316,8 +397,8 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                     const T f0 = (T)c_dflip[0][xi] / rr0, f1 = (T)c_dflip[1][xi] / rr1;
                     s_fa[0] = f0;
                     s_fa[1] = f1;
-                    s_fT[0][s_m] = -f0;  // recursion factor f = -Delta / r
-                    s_fT[1][s_m] = -f1;
+                    s_fk[0][s_m] = -f0;  // recursion factor f = -Delta / r
+                    s_fk[1][s_m] = -f1;
                     idx[s_m] = q;
                     s_m = s_m + 1;
                     if (R < T(0)) s_nneg = s_nneg + 1;
@@ -347,8 +428,8 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
             so.ratio[s0 + q] = (double)s_rat[q];
         }
         for (int q = tid; q < s_m; q += nt) {
-            dl[0 * n + q] = (double)s_fT[0][q];
-            dl[1 * n + q] = (double)s_fT[1][q];
+            dl[0 * n + q] = (double)s_fk[0][q];
+            dl[1 * n + q] = (double)s_fk[1][q];
         }
         if (tid == 0) {
             if (s_nneg & 1) s_sign = -s_sign;
@@ -361,7 +442,6 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
         __shared__ double s_rs[2];
         __shared__ int s_accb;
         __shared__ T s_phi[2][NBMAX];
-        T* stcol = stc;          // [2][n]
         T* strow = stc + 2 * n;  // [2][n]
         for (int p0 = 0; p0 < n; p0 += nb) {
             const int nbk = min(nb, n - p0);
@@ -491,18 +571,22 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
             // (d) apply the flips in increasing site order, each as the trailing rank-1 step of the
             //     delayed update (rows / columns after the flipped site): the same product of
             //     rank-1 factors as Eq. BlkFrcBsTnew2, and the frozen rows / columns feed the flush
+            const int mb = s_m;
             for (int q = 0; q < nF; ++q) {
-                const int a = p0 + s_F[q];
-                trailing_update(Gs, n, P, a, s_phi[0][q], s_phi[1][q], tid, nt);
+                const int a = p0 + s_F[q], k = mb + q;
                 if (tid == 0) {
-                    idx[s_m] = a;
-                    dl[0 * n + s_m] = -(double)s_phi[0][q];
-                    dl[1 * n + s_m] = -(double)s_phi[1][q];
-                    s_m = s_m + 1;
+                    idx[k] = a;
+                    s_fk[0][k] = -s_phi[0][q];
+                    s_fk[1][k] = -s_phi[1][q];
+                    dl[0 * n + k] = -(double)s_phi[0][q];
+                    dl[1 * n + k] = -(double)s_phi[1][q];
                     xw[a] = (int8_t)(-xw[a]);
                 }
+                trailing_update(Gs, n, P, a, s_phi[0][q], s_phi[1][q], tid, nt);
                 __syncthreads();
             }
+            if (tid == 0) s_m = mb + nF;
+            __syncthreads();
         }
     }
     __syncthreads();
@@ -517,13 +601,16 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
         wb.dtot[q] = dl[q];
         wb.dtot[WinCap<T>::NW + q] = dl[n + q];
     }
-    // coefficients of the flush recursion: the block entries at accepted positions, frozen
-    // at acceptance time (row of the earlier site, column of the earlier site)
-    const int NWC = WinCap<T>::NW;
-    for (int e = tid; e < 2 * m * m; e += nt) {
-        const int sp2 = e / (m * m), rem = e - sp2 * m * m, a = rem / m, c = rem - (rem / m) * m;
-        ((T*)wb.Wm)[(size_t)sp2 * NWC * NWC + a * NWC + c] = Gs[(sp2 * n + idx[a]) * P + idx[c]];
-    }
+    // The window's update matrix W (Eq. DelayRgenk in G form).  With C[k][k'] = Gs[idx[k]][idx[k']]
+    // the block entries frozen at acceptance time (rows and columns at or before an accepted site
+    // are never touched again), f_k = -Delta_k / r_k, L1 = I + Cl F and U1 = I + Cu F (Cl, Cu the
+    // strictly lower / upper parts of C, F = diag f), the delayed-update recursions give
+    // W = -F U1^{-1} L1^{-1}: per column of the identity a forward and a backward substitution,
+    //   y_k = b_k - sum_{k'<k} C[k][k'] f_k' y_k',   z_k = y_k - sum_{k'>k} C[k][k'] f_k' z_k',
+    //   W_k = -f_k z_k.
+    // Each warp owns WCPW columns of one spin in registers (lane l holds rows l, l + 32, ...) and
+    // broadcasts the finished row of every step with a shuffle: no block-wide barrier per step.
+    window_w<T>(Gs, n, P, idx, s_fk, m, (T*)wb.Wx, tid);
     if (tid == 0) {
         *wb.m = m;
         if (so.sign) *so.sign = s_sign;
@@ -621,108 +708,107 @@ template cudaError_t launch_window_chain<double>(cudaStream_t, int, const double
                                                  const double*, const uint8_t*, const SiteParams&, SliceOut, int,
                                                  int, int, WindowBufs, const double*, int*);
 // ---------------------------------------------------------------------------
-// Pipelined flush of one window (all on the flush stream).
+// Pipelined flush of one window.
 //
-// W from the frozen coefficients (the delayed-update recursion, Eq. DelayRgenk in G form):
-// with f_k = -Delta_k / r_k and C[k][k'] the block entry of sites i_k, i_k' frozen at
-// acceptance time, the accepted rank-1 vectors are a_k = G0[:, I] alpha_k and
-// b_k^T = beta_k^T (E_I^T - G0[I, :]), where per component c
-//   alpha_k[c] = f_k (delta_kc - sum_{k'<k} C[k'][k] alpha_k'[c]),
-//   beta_k[c]  = delta_kc - sum_{k'<k} f_k' C[k][k'] beta_k'[c],
-// so G = G0 + G0[:, I] (Ta Lb) (E_I^T - G0[I, :]) with Ta[c][k] = alpha_k[c], Lb[k][c] = beta_k[c].
-// w2_kernel stores Wm = -(Ta Lb) for the product G <- G - X (Wm Yraw).  Each component's
-// recursion is independent: one thread per component, no synchronisation.
+// The window kernel leaves W (m x m) in wb.Wm: the accumulated update of the window is
+// G <- G - X W Yraw with X = G[:, I] and Yraw = E_I^T - G[I, :] (I the accepted sites).
+//   * next_block_kernel (main stream, right after the window): the next window's n' x n' block
+//     of G as it will be after this window's update, from three small gathers of G and two
+//     small products in shared memory.  The next window starts from it at once.
+//   * launch_flush_panels + launch_flush_gemm (flush stream): the panel gathers, Y' = W Yraw
+//     and the rank-m product over all of G, overlapping the next window's decisions.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) w2_kernel(WindowBufs wb) {
-    constexpr int NW = WinCap<T>::NW;
-    const int m = *wb.m;
-    if (m == 0) return;
-    const int s = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-    const int Pm = m + 1;
-    extern __shared__ __align__(16) unsigned char w2_smem[];
-    T* Cs = (T*)w2_smem;  // [m][m+1]
-    T* Ta = Cs + (size_t)m * Pm;
-    T* Lb = Ta + (size_t)m * Pm;
-    __shared__ T fs[NW];
-    T* Wg = (T*)wb.Wm + (size_t)s * NW * NW;
-    for (int e = tid; e < m * m; e += nt) Cs[(e / m) * Pm + e % m] = Wg[(e / m) * NW + e % m];
-    for (int k = tid; k < m; k += nt) fs[k] = (T)wb.dtot[s * NW + k];
-    __syncthreads();
-    if (tid < m) {
-        const int c = tid;
-        for (int k = 0; k < m; ++k) {  // row c of Ta
-            T acc = (k == c) ? T(1) : T(0);
-            for (int kp = c; kp < k; ++kp) acc -= Cs[kp * Pm + k] * Ta[c * Pm + kp];
-            Ta[c * Pm + k] = (k < c) ? T(0) : fs[k] * acc;
-        }
-        for (int k = 0; k < m; ++k) {  // column c of Lb
-            T acc = (k == c) ? T(1) : T(0);
-            for (int kp = c; kp < k; ++kp) acc -= fs[kp] * Cs[k * Pm + kp] * Lb[kp * Pm + c];
-            Lb[k * Pm + c] = (k < c) ? T(0) : acc;
-        }
-    }
-    __syncthreads();
-    for (int e = tid; e < m * m; e += nt) {
-        const int a = e / m, b = e % m;
-        T acc = T(0);
-        for (int k = (a > b ? a : b); k < m; ++k) acc += Ta[a * Pm + k] * Lb[k * Pm + b];
-        Wg[a * NW + b] = -acc;
-    }
-}
 
-// snap[s][a][c] = G[s][sn + a][sn + c] - sum_{k<m} X[s][sn + a][k] Y'[s][k][sn + c]: the next
-// window's block as it will be after this window's product (taken before the product runs).
+// snap[s][a][c] = G[sn + a][sn + c] - sum_k X[sn + a][k] Y'[k][sn + c], with X = G[:, I],
+// Y' = W Yraw and Yraw[l][sn + c] = -G[I_l][sn + c] (the next window's sites are not in I): the
+// block of the next window as it will be after this window's product.  Grid (row blocks of
+// NB_ROWS, spin); each CTA forms (X_blk W) and then (X_blk W) Yraw_n for its rows.
+constexpr int NB_ROWS = 16;
 template <typename T>
-__global__ void next_block_kernel(const T* __restrict__ Gu, const T* __restrict__ Gd, long ld, int N, WindowBufs wb,
-                                  int sn, int nn, T* snap) {
-    constexpr int NW = WinCap<T>::NW;
+__global__ void __launch_bounds__(256) next_block_kernel(const T* __restrict__ Gu, const T* __restrict__ Gd, long ld,
+                                                         WindowBufs wb, int sn, int nn, T* snap) {
+    constexpr int NW = WinCap<T>::NW, PP = NW + 1;
     const int m = *wb.m;
-    const int s = blockIdx.y;
+    const int s = blockIdx.y, a0 = blockIdx.x * NB_ROWS, tid = threadIdx.x, nt = blockDim.x;
+    const int ra = min(NB_ROWS, nn - a0);
     const T* G = s ? Gd : Gu;
-    const T* X = (const T*)wb.X + (size_t)s * N * NW;
-    const T* Yp = (const T*)wb.Y + (size_t)2 * NW * N + (size_t)s * NW * N;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nn * nn; e += gridDim.x * blockDim.x) {
-        const int a = e / nn, c = e % nn;
-        T v = G[(long)(sn + a) * ld + (sn + c)];
-        for (int k = 0; k < m; ++k) v -= X[(size_t)(sn + a) * NW + k] * Yp[(size_t)k * N + (sn + c)];
-        snap[((size_t)s * NW + a) * NW + c] = v;
+    T* out = snap + (size_t)s * NW * NW;
+    extern __shared__ __align__(16) unsigned char nb_smem[];
+    T* Ws = (T*)nb_smem;         // [m][PP]
+    T* Ys = Ws + NW * PP;        // [m][PP]   Yraw_n
+    T* Xs = Ys + NW * PP;        // [NB_ROWS][PP]
+    T* Ts = Xs + NB_ROWS * PP;   // [NB_ROWS][PP]  X_blk W
+    __shared__ int sidx[NW];
+    for (int q = tid; q < m; q += nt) sidx[q] = wb.idx[q];
+    __syncthreads();
+    const T* W = (const T*)wb.Wx + (size_t)s * NW * NW;
+    for (int e = tid; e < m * m; e += nt) Ws[(e / m) * PP + e % m] = W[(e / m) * NW + e % m];
+    for (int e = tid; e < m * nn; e += nt) {
+        const int l = e / nn, c = e - l * nn;
+        Ys[l * PP + c] = -G[(long)sidx[l] * ld + sn + c];
+    }
+    for (int e = tid; e < ra * m; e += nt) {
+        const int a = e / m, k = e - a * m;
+        Xs[a * PP + k] = G[(long)(sn + a0 + a) * ld + sidx[k]];
+    }
+    __syncthreads();
+    for (int e = tid; e < ra * m; e += nt) {  // T = X_blk W
+        const int a = e / m, k = e - a * m;
+        T acc = T(0);
+        for (int l = 0; l < m; ++l) acc += Xs[a * PP + l] * Ws[l * PP + k];
+        Ts[a * PP + k] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < ra * nn; e += nt) {  // snap = G_nn - T Yraw_n
+        const int a = e / nn, c = e - a * nn;
+        T acc = T(0);
+        for (int l = 0; l < m; ++l) acc += Ts[a * PP + l] * Ys[l * PP + c];
+        out[(a0 + a) * NW + c] = G[(long)(sn + a0 + a) * ld + sn + c] - acc;
     }
 }
 
 template <typename T>
-cudaError_t launch_flush_pipelined(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw,
-                                   int sn, int nn, T* snap, cudaEvent_t block_ready) {
+cudaError_t launch_next_block(cudaStream_t st, const T* Gu, const T* Gd, const SiteParams& sp, WindowBufs wb, int sn,
+                              int nn, T* snap) {
     constexpr int NW = WinCap<T>::NW;
-    const int N = sp.N;
-    const size_t shm = 3 * (size_t)NW * (NW + 1) * sizeof(T);
+    const size_t shm = (2 * (size_t)NW + 2 * NB_ROWS) * (NW + 1) * sizeof(T);
     static bool attr = false;
     if (!attr) {
-        cudaError_t ea = cudaFuncSetAttribute((void*)w2_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        cudaError_t ea =
+            cudaFuncSetAttribute((void*)next_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         if (ea != cudaSuccess) return ea;
         attr = true;
     }
     count_launch();
-    w2_kernel<T><<<2, 256, shm, sf>>>(wb);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    const int nbx = nn > 0 ? (nn + NB_ROWS - 1) / NB_ROWS : 1;
+    next_block_kernel<T><<<dim3(nbx, 2), 256, shm, st>>>(Gu, Gd, sp.ld, wb, sn, nn, snap);
+    return cudaGetLastError();
+}
+
+// The panel gathers X = G[:, I], Yraw = E_I^T - G[I, :] and Y' = W Yraw of one window.
+template <typename T>
+cudaError_t launch_flush_panels(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw) {
+    constexpr int NW = WinCap<T>::NW;
+    const int N = sp.N;
     count_launch();
     gather_kernel<T><<<dim3(256, 2), 256, 0, sf>>>(Gu, Gd, sp.ld, N, wb, NW);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    GemmArgs<T> g;  // Y' = Wm Yraw
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    GemmArgs<T> g;  // Y' = W Yraw
     g.M = nw; g.N = N; g.K = nw; g.Kdev = wb.m;
-    g.A = (const T*)wb.Wm; g.lda = NW; g.sA = (long)NW * NW;
+    g.A = (const T*)wb.Wx; g.lda = NW; g.sA = (long)NW * NW;
     g.B = (const T*)wb.Y; g.ldb = N; g.sB = (long)NW * N;
     g.C = (T*)wb.Y + (size_t)2 * NW * N; g.ldc = N; g.sC = (long)NW * N;
     g.batch = 2;
-    if ((e = gemm<T>(sf, g)) != cudaSuccess) return e;
-    if (nn > 0) {
-        count_launch();
-        next_block_kernel<T><<<dim3((nn * nn + 255) / 256, 2), 256, 0, sf>>>(Gu, Gd, sp.ld, N, wb, sn, nn, snap);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    if ((e = cudaEventRecord(block_ready, sf)) != cudaSuccess) return e;
-    GemmArgs<T> h;  // G <- G - X Y'
+    return gemm<T>(sf, g);
+}
+
+// G <- G - X Y' (the N x N rank-m product, after launch_flush_panels on the same stream).
+template <typename T>
+cudaError_t launch_flush_gemm(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw) {
+    constexpr int NW = WinCap<T>::NW;
+    const int N = sp.N;
+    GemmArgs<T> h;
     h.M = N; h.N = N; h.K = nw; h.Kdev = wb.m;
     h.A = (const T*)wb.X; h.lda = NW; h.sA = (long)N * NW;
     h.B = (const T*)wb.Y + (size_t)2 * NW * N; h.ldb = N; h.sB = (long)NW * N;
@@ -731,11 +817,14 @@ cudaError_t launch_flush_pipelined(cudaStream_t sf, T* Gu, T* Gd, const SitePara
     h.batch = 2;
     return gemm<T>(sf, h);
 }
-
-template cudaError_t launch_flush_pipelined<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int,
-                                                   int, int, float*, cudaEvent_t);
-template cudaError_t launch_flush_pipelined<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs,
-                                                    int, int, int, double*, cudaEvent_t);
+template cudaError_t launch_flush_panels<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int);
+template cudaError_t launch_flush_panels<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs, int);
+template cudaError_t launch_flush_gemm<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int);
+template cudaError_t launch_flush_gemm<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs, int);
+template cudaError_t launch_next_block<float>(cudaStream_t, const float*, const float*, const SiteParams&, WindowBufs,
+                                              int, int, float*);
+template cudaError_t launch_next_block<double>(cudaStream_t, const double*, const double*, const SiteParams&,
+                                               WindowBufs, int, int, double*);
 template cudaError_t launch_flush<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int);
 template cudaError_t launch_flush<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs, int);
 

@@ -1,0 +1,69 @@
+"""Command-line driver: one walker of the square-lattice Hubbard model swept for a given number
+of slice-steps through the C ABI (used for kernel profiling and quick timing).
+
+    python -m paper_2506_09611_gb300.run --L 40 --U 6 --slices 20 --mode delayed --k 64
+
+The walk goes forward from slice 1 and turns at slice M, with the FP64 recompute at every
+multiple of --stab, exactly as in a full sweep; the inputs are the seeded synthetic trial
+state and fields of the package's input module.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import afqmc, inputs
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--L", type=int, default=40)
+    ap.add_argument("--U", type=float, default=6.0)
+    ap.add_argument("--t", type=float, default=1.0)
+    ap.add_argument("--dtau", type=float, default=0.05)
+    ap.add_argument("--M", type=int, default=80)
+    ap.add_argument("--filling", type=float, default=0.875)
+    ap.add_argument("--stab", type=int, default=10)
+    ap.add_argument("--slices", type=int, default=20, help="slice-steps to run after initialisation")
+    ap.add_argument("--mode", default="delayed", choices=["local", "delayed", "blockfb"])
+    ap.add_argument("--k", type=int, default=64)
+    ap.add_argument("--nb", type=int, default=16)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--gemm", default="tc3", choices=["tc3", "simt", "tf32"])
+    ap.add_argument("--seed", type=int, default=1)
+    a = ap.parse_args(argv)
+
+    import torch
+
+    afqmc.load()
+    stream = torch.cuda.current_stream()
+    L, N = a.L, a.L * a.L
+    ns = inputs.n_sigma_for(L, a.filling)
+    P = inputs.trial_state(L, L, ns)
+    X = inputs.initial_fields(a.M, N, seed=a.seed)
+    ctx = afqmc.Context(a.M, dtau=a.dtau, U=a.U, t=a.t, precision=a.precision, stab_every=a.stab, seed=a.seed,
+                        gemm=a.gemm)
+    ctx.init_walkers([L], [ns], [ns], np.concatenate([P.ravel(), P.ravel()]), X, stream=stream)
+    order = [(l, +1) for l in range(1, a.M + 1)] + [(l, -1) for l in range(a.M, 0, -1)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(a.slices):
+        ell, d = order[i % len(order)]
+        ctx.sweep_slice(ell, d, a.mode, k=a.k, nb=a.nb, stream=stream)
+        pos = ell if d > 0 else ell - 1
+        if pos % a.stab == 0:
+            afqmc.afqmc_recompute_G(ctx.h, None, stream)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    e, s = ctx.measure_energy(stream=stream)
+    ctx.close()
+    print(json.dumps({"L": L, "slices": a.slices, "mode": a.mode, "k": a.k, "nb": a.nb,
+                      "precision": a.precision, "gemm": a.gemm, "seconds": dt,
+                      "field_updates_per_s": N * a.slices / dt, "energy": float(e[0])}))
+
+
+if __name__ == "__main__":
+    main()
