@@ -295,7 +295,7 @@ def main():
                             "note": "prep + the window loop (decisions; the rank-m flushes overlap on a second "
                                     "stream): the paper's update time"},
             "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()
-                                   if k not in ("elim", "wrap_gemm", "flush_gemm")},
+                                   if k not in ("elim", "wrap_gemm", "flush_gemm", "lu_o", "solve")},
             "compare_sample": cmp,
             "speedup_update_only_vs_local": speedup,
             "G_err_fp32_vs_fp64_recompute": {"max": max(drifts) if drifts else None,
@@ -320,7 +320,7 @@ FP64_FMA_PER_SM_CLK = 2
 TF32_OVER_BF16 = 1.1 / 2.25
 # DRAM bytes per launch (read + write) from one ncu capture of the current kernel, in bytes;
 # None when no capture of the current kernel exists.
-NCU_TRAFFIC = {"elim": None, "wrap_gemm": None, "flush_gemm": None}
+NCU_TRAFFIC = {"elim": None, "lu_o": None, "solve": None, "wrap_gemm": None, "flush_gemm": None}
 
 
 def fp32_alu_peak(pk):
@@ -336,23 +336,25 @@ def kernel_rooflines(prof, gemm, pk, pk_src, steps):
     achieved = algorithmic work of the launches / their summed CUDA-event durations.
     Returns a list sorted by total time (the first entry is the dominant kernel)."""
     out = []
-    # Pivoted eliminations of the FP64 recompute: per spin and recompute one Gauss-Jordan
-    # solve of [O | U_L] (ns x (ns + N)): ns^3 + 2 ns^2 N flop; the remaining launches are the
-    # re-orthonormalisation LUs of the propagated N x ns factor: N ns^2 - ns^3 / 3 flop.
-    el = prof.get("elim", {"ms": 0.0, "intervals": 0})
-    if el["intervals"] > 0:
-        n_gj = 2 * prof["recompute"]["intervals"]
-        n_lu = el["intervals"] - n_gj
-        flop = n_gj * (NS ** 3 + 2.0 * NS ** 2 * N) + n_lu * (N * NS ** 2 - NS ** 3 / 3.0)
-        ach = flop / (el["ms"] / 1e3) / 1e12
-        peak = fp64_alu_peak(pk)
-        out.append({"kernel": "elim_kernel (FP64 pivoted LU / Gauss-Jordan of the recompute)", "bound": "alu",
-                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": NCU_TRAFFIC["elim"], "launches": el["intervals"],
-                    "ms_per_launch": el["ms"] / el["intervals"], "ms_per_step": el["ms"] / steps,
-                    "work_per_launch": flop / el["intervals"],
-                    "peak_source": "nominal FP64 1.25 TFLOP/s: 152 SMs x %d FMA x 2 flop x %.0f MHz (of %s "
-                                   "peaks)" % (FP64_FMA_PER_SM_CLK, pk.get("sm_max_mhz", 2070.0), pk_src)})
+    # FP64 recompute: blocked pivoted LU of the propagated N x ns factor (both spins per
+    # interval), LU of U_L U_R (ns x ns) and the solve (U_L U_R) Z = U_L with N right-hand sides.
+    fp64 = fp64_alu_peak(pk)
+    src64 = ("nominal FP64 1.25 TFLOP/s: 152 SMs x %d FMA x 2 flop x %.0f MHz (of %s peaks)"
+             % (FP64_FMA_PER_SM_CLK, pk.get("sm_max_mhz", 2070.0), pk_src))
+    for name, label, flop in (
+            ("elim", "lu_panel_kernel + lu_update_kernel (FP64 LU of the propagated N x ns factor, both spins)",
+             2 * (N * NS ** 2 - NS ** 3 / 3.0)),
+            ("lu_o", "lu_panel_kernel + lu_update_kernel (FP64 LU of U_L U_R, ns x ns, both spins)",
+             2 * (2.0 / 3.0) * NS ** 3),
+            ("solve", "lu_solve_kernel (FP64 (U_L U_R) Z = U_L, N right-hand sides, both spins)",
+             2 * 2.0 * NS ** 2 * N)):
+        ph = prof.get(name, {"ms": 0.0, "intervals": 0})
+        if ph["intervals"] > 0:
+            ach = flop * ph["intervals"] / (ph["ms"] / 1e3) / 1e12
+            out.append({"kernel": label, "bound": "alu", "achieved": ach, "peak": fp64, "unit": "TFLOP/s",
+                        "frac": ach / fp64, "traffic": NCU_TRAFFIC.get(name), "launches": ph["intervals"],
+                        "ms_per_launch": ph["ms"] / ph["intervals"], "ms_per_step": ph["ms"] / steps,
+                        "work_per_launch": flop, "peak_source": src64})
     wg = prof.get("wrap_gemm", {"ms": 0.0, "intervals": 0})
     if wg["intervals"] > 0:
         flop = 2.0 * 2.0 * N ** 3  # one launch = one N x N x N product for both spins

@@ -191,10 +191,12 @@ int afqmc_apply_flips_noalloc(int precision, int N, long long ld, void* G_up, vo
 #define AFQMC_PHASE_FLUSH 4      /* panel gather + rank-m product of the delayed / block-FB update */
 #define AFQMC_PHASE_RECOMPUTE 5  /* FP64 propagation, re-orthonormalisation and G = 1 - U_R T U_L */
 /* Nested intervals inside the phases above, one per kernel launch (for per-kernel rooflines): */
-#define AFQMC_PHASE_ELIM 6       /* each pivoted-elimination launch (inside RECOMPUTE) */
+#define AFQMC_PHASE_ELIM 6       /* each re-orthonormalisation LU, N x Nsigma, both spins (inside RECOMPUTE) */
 #define AFQMC_PHASE_WRAP_GEMM 7  /* each wrap product launch (inside WRAP) */
 #define AFQMC_PHASE_FLUSH_GEMM 8 /* each rank-m product launch of the flush (inside FLUSH) */
-#define AFQMC_NPHASE 9
+#define AFQMC_PHASE_LU_O 9       /* each LU of U_L U_R, Nsigma x Nsigma, both spins (inside RECOMPUTE) */
+#define AFQMC_PHASE_SOLVE 10     /* each solve (U_L U_R) Z = U_L, both spins (inside RECOMPUTE) */
+#define AFQMC_NPHASE 11
 /* on != 0 enables profiling and clears the accumulators; on == 0 disables it. */
 int afqmc_set_profiling(afqmc_ctx* ctx, int on);
 /* Sync the last stream and return, per phase, the summed device milliseconds, the number of

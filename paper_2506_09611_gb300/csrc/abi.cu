@@ -65,13 +65,16 @@ struct Walker {
     cudaEvent_t ev_chain[2] = {nullptr, nullptr}, ev_prod[2] = {nullptr, nullptr}, ev_done = nullptr;
     double* URs[2] = {nullptr, nullptr};
     double* ULs[2] = {nullptr, nullptr};
-    double* Ucur = nullptr;
-    double* Utmp = nullptr;
-    double* aug = nullptr;
-    double* Z = nullptr;
-    double* Gnew = nullptr;
-    int* perm = nullptr;
-    void* elim = nullptr;
+    int nsm = 0;                 // max(ns[0], ns[1])
+    double* Ucur = nullptr;      // 2 x N x nsm: the factor being propagated, per spin
+    double* Utmp = nullptr;      // N x nsm: propagation scratch
+    double* Ut2 = nullptr;       // 2 x N x nsm: transposed left factors for the LU
+    double* Ob = nullptr;        // 2 x nsm x nsm: U_L U_R, then its LU
+    double* Z = nullptr;         // 2 x nsm x N: (U_L U_R)^{-1} U_L
+    double* Gnew = nullptr;      // N x ld: the recomputed G of one spin
+    int* perm2 = nullptr;        // 2 x max(N, nsm): pivot rows
+    int8_t* flag2 = nullptr;     // 2 x max(N, nsm): pivoted-row flags
+    int* visited = nullptr;      // max(N, nsm): permutation-parity scratch
     double* acc2 = nullptr;
     std::vector<void*> allocs;
 };
@@ -229,36 +232,123 @@ static Lattice* get_lattice(afqmc_ctx* ctx, int L, cudaStream_t st, cudaError_t*
     return l;
 }
 
-// G_new (FP64, N x ld) = 1 - UR (UL UR)^{-1} UL ; multiplies *sign by sign(det(UL UR)).
-static cudaError_t form_G(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, const double* UR, const double* UL,
-                          double* sign) {
-    const int N = w->N, ns = w->ns[s];
-    const long la = ns + N;
-    GemmArgs<double> g;
-    g.M = ns; g.N = ns; g.K = N;
-    g.A = UL; g.lda = N;
-    g.B = UR; g.ldb = ns;
-    g.C = w->aug; g.ldc = la;
-    cudaError_t e = gemm<double>(st, g);
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpy2DAsync(w->aug + ns, la * 8, UL, (size_t)N * 8, (size_t)N * 8, ns, cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return e;
+// Spin groups for the batched FP64 steps: both spins in one launch when they have the same
+// particle number, else one at a time.
+static int spin_groups(const Walker* w, int grp[2][2], int ng[2]) {
+    if (w->ns[0] == w->ns[1]) {
+        grp[0][0] = 0;
+        grp[0][1] = 1;
+        ng[0] = 2;
+        return 1;
+    }
+    grp[0][0] = 0;
+    ng[0] = 1;
+    grp[1][0] = 1;
+    ng[1] = 1;
+    return 2;
+}
+
+static LuArgs lu_args(Walker* w, double* const* A, int nmat, long lda, int m, int n) {
+    const int maxr = w->N > w->nsm ? w->N : w->nsm;
+    LuArgs a;
+    for (int q = 0; q < nmat; ++q) {
+        a.A[q] = A[q];
+        a.perm[q] = w->perm2 + (size_t)q * maxr;
+        a.flag[q] = w->flag2 + (size_t)q * maxr;
+    }
+    a.lda = lda;
+    a.m = m;
+    a.n = n;
+    a.nmat = nmat;
+    a.err = w->err;
+    return a;
+}
+
+// Re-orthonormalisation (Sec. II.C): every U[q] (N x ns, row-major) becomes P L from its
+// partially pivoted LU, a basis of the same column space with entries of magnitude <= 1 (only
+// the column space enters G, Eq. GrFMatNew).  *sign (nullable) is multiplied by the sign of the
+// discarded triangular factor.
+static cudaError_t stab_rows(afqmc_ctx* ctx, Walker* w, cudaStream_t st, double* const* U, int nmat, int ns,
+                             double* sign) {
+    LuArgs a = lu_args(w, U, nmat, ns, w->N, ns);
+    cudaError_t e;
     {
         PhaseScope ps(ctx, AFQMC_PHASE_ELIM, st);
-        e = launch_elim(st, 1, w->aug, ns, ns, la, 1, N, w->perm, sign, w->elim, w->err);
+        if ((e = launch_lu(st, a)) != cudaSuccess) return e;
     }
-    if (e != cudaSuccess) return e;
-    e = launch_gj_extract(st, w->aug, la, ns, N, w->perm, w->Z, N);
-    if (e != cudaSuccess) return e;
-    // The N x N product stays in FP64 for both bulk precisions: the pivoted-LU factors are not
-    // orthonormal, so 1 - U_R Z cancels large terms and an FP32 product would lose the digits
-    // the recompute exists to restore.
+    if (sign && (e = launch_lu_sign(st, a, 0, sign, w->visited)) != cudaSuccess) return e;
+    return launch_lu_unit_rows(st, a);
+}
+
+// The same for left factors U[q] (ns x N): through their transposes.
+static cudaError_t stab_cols(afqmc_ctx* ctx, Walker* w, cudaStream_t st, double* const* U, int nmat, int ns,
+                             double* sign) {
+    const int N = w->N;
+    double* T[2] = {w->Ut2, w->Ut2 + (size_t)N * w->nsm};
+    cudaError_t e;
+    for (int q = 0; q < nmat; ++q) {
+        count_launch();
+        transpose_kernel<<<256, 256, 0, st>>>(U[q], ns, N, T[q]);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = stab_rows(ctx, w, st, T, nmat, ns, sign)) != cudaSuccess) return e;
+    for (int q = 0; q < nmat; ++q) {
+        count_launch();
+        transpose_kernel<<<256, 256, 0, st>>>(T[q], N, ns, U[q]);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Z[q] = (UL[q] UR[q])^{-1} UL[q] (ns x N) for the spins of a group (Eq. GrFMatNew):
+// O = UL UR (FP64), its pivoted LU, then the substitutions with UL as right-hand side.
+// *sign (nullable) is multiplied by sign(det O) of every spin.
+static cudaError_t form_Z(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const double* const* UR, const double* const* UL,
+                          int nmat, int ns, double* sign) {
+    const int N = w->N;
+    double* O[2] = {w->Ob, w->Ob + (size_t)w->nsm * w->nsm};
+    double* Z[2] = {w->Z, w->Z + (size_t)w->nsm * N};
+    cudaError_t e;
+    for (int q = 0; q < nmat; ++q) {
+        GemmArgs<double> g;
+        g.M = ns; g.N = ns; g.K = N;
+        g.A = UL[q]; g.lda = N;
+        g.B = UR[q]; g.ldb = ns;
+        g.C = O[q]; g.ldc = ns;
+        if ((e = gemm<double>(st, g)) != cudaSuccess) return e;
+    }
+    LuArgs a = lu_args(w, O, nmat, ns, ns, ns);
+    {
+        PhaseScope ps(ctx, AFQMC_PHASE_LU_O, st);
+        if ((e = launch_lu(st, a)) != cudaSuccess) return e;
+    }
+    if (sign && (e = launch_lu_sign(st, a, 1, sign, w->visited)) != cudaSuccess) return e;
+    SolveArgs sa;
+    for (int q = 0; q < nmat; ++q) {
+        sa.LU[q] = O[q];
+        sa.perm[q] = a.perm[q];
+        sa.B[q] = UL[q];
+        sa.Z[q] = Z[q];
+    }
+    sa.ldl = ns;
+    sa.ns = ns;
+    sa.N = N;
+    sa.nmat = nmat;
+    PhaseScope pv(ctx, AFQMC_PHASE_SOLVE, st);
+    return launch_lu_solve(st, sa);
+}
+
+// G_new (FP64, N x ld) = 1 - UR Z for the spin whose Z sits at slot q of form_Z.  The N x N
+// product stays in FP64 for both bulk precisions: the LU bases are not orthonormal, so 1 - UR Z
+// cancels large terms and an FP32 product would lose the digits the recompute restores.
+static cudaError_t finish_G(Walker* w, cudaStream_t st, const double* UR, int q, int ns) {
+    const int N = w->N;
     GemmArgs<double> h;
     h.M = N; h.N = N; h.K = ns;
     h.A = UR; h.lda = ns;
-    h.B = w->Z; h.ldb = N;
+    h.B = w->Z + (size_t)q * w->nsm * N; h.ldb = N;
     h.C = w->Gnew; h.ldc = w->ld;
-    e = gemm<double>(st, h);
+    cudaError_t e = gemm<double>(st, h);
     if (e != cudaSuccess) return e;
     return launch_identity_minus<double>(st, w->Gnew, w->ld, N);
 }
@@ -302,15 +392,6 @@ static cudaError_t prop_left(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, 
     gy.B = tmp; gy.ldb = L; gy.sB = N;
     gy.C = U; gy.ldc = L; gy.sC = N;
     return gemm<double>(st, gy);
-}
-
-static cudaError_t stab_right(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, double* U, double* sign) {
-    PhaseScope ps(ctx, AFQMC_PHASE_ELIM, st);  // U: N x ns
-    return launch_elim(st, 0, U, w->N, w->ns[s], w->ns[s], 1, 0, w->perm, sign, w->elim, w->err);
-}
-static cudaError_t stab_left(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, double* U, double* sign) {
-    PhaseScope ps(ctx, AFQMC_PHASE_ELIM, st);  // U: ns x N
-    return launch_elim(st, 0, U, w->N, w->ns[s], 1, w->N, 0, w->perm, sign, w->elim, w->err);
 }
 
 template <typename T>
@@ -467,13 +548,17 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
             CK(dalloc(A, &w->URs[s], (size_t)nst * N * w->ns[s] * 8));
             CK(dalloc(A, &w->ULs[s], (size_t)nst * N * w->ns[s] * 8));
         }
-        CK(dalloc(A, &w->Ucur, (size_t)N * nsm * 8));
+        const int maxr = N > nsm ? N : nsm;
+        w->nsm = nsm;
+        CK(dalloc(A, &w->Ucur, 2 * (size_t)N * nsm * 8));
         CK(dalloc(A, &w->Utmp, (size_t)N * nsm * 8));
-        CK(dalloc(A, &w->aug, (size_t)nsm * (nsm + N) * 8));
-        CK(dalloc(A, &w->Z, (size_t)nsm * N * 8));
+        CK(dalloc(A, &w->Ut2, 2 * (size_t)N * nsm * 8));
+        CK(dalloc(A, &w->Ob, 2 * (size_t)nsm * nsm * 8));
+        CK(dalloc(A, &w->Z, 2 * (size_t)nsm * N * 8));
         CK(dalloc(A, &w->Gnew, (size_t)N * ld * 8));
-        CK(dalloc(A, &w->perm, (size_t)(N > nsm ? N : nsm) * sizeof(int)));
-        CK(dalloc(A, (char**)&w->elim, elim_scratch_bytes(N > nsm ? N : nsm)));
+        CK(dalloc(A, (char**)&w->perm2, 2 * (size_t)maxr * sizeof(int)));
+        CK(dalloc(A, (char**)&w->flag2, 2 * (size_t)maxr));
+        CK(dalloc(A, (char**)&w->visited, (size_t)maxr * sizeof(int)));
         CK(dalloc(A, &w->acc2, 2 * 8));
         CK(cudaMemsetAsync(w->err, 0, sizeof(int), st));
         for (int q = 0; q < 2; ++q) {
@@ -496,32 +581,52 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
         set_double_kernel<<<1, 1, 0, st>>>(w->sign, 1.0);
         CK(cudaGetLastError());
         // trial determinants -> stacks, G(0)  (Sec. II.B)
+        double* ULc[2] = {w->Ucur, w->Ucur + (size_t)N * w->nsm};
         for (int s = 0; s < 2; ++s) {
             const int ns = w->ns[s];
             const double* Ph = P + poff;
             poff += (size_t)N * ns;
-            // P into URs[s][0] (N x ns), re-orthonormalised
-            double* UR0 = w->URs[s];
-            CK(cudaMemcpyAsync(UR0, Ph, (size_t)N * ns * 8, cudaMemcpyHostToDevice, st));
+            // P into URs[s][0] (N x ns); its transpose starts the left stack, U_L(M) = P^T
+            CK(cudaMemcpyAsync(w->URs[s], Ph, (size_t)N * ns * 8, cudaMemcpyHostToDevice, st));
             count_launch();
-            transpose_kernel<<<256, 256, 0, st>>>(UR0, N, ns, w->Ucur);  // Ucur = P^T (ns x N)
+            transpose_kernel<<<256, 256, 0, st>>>(w->URs[s], N, ns, ULc[s]);
             CK(cudaGetLastError());
-            CK(stab_right(ctx, w, st, s, UR0, w->sign));
-            // left stack: U_L(M) = P^T, U_L(l-1) = U_L(l) B_l
-            CK(stab_left(ctx, w, st, s, w->Ucur, w->sign));
-            CK(cudaMemcpyAsync(w->ULs[s] + (size_t)(M / S) * N * ns, w->Ucur, (size_t)N * ns * 8,
+        }
+        int grp[2][2], ng[2];
+        const int ngr = spin_groups(w, grp, ng);
+        for (int gi = 0; gi < ngr; ++gi) {
+            double* R[2] = {w->URs[grp[gi][0]], ng[gi] > 1 ? w->URs[grp[gi][1]] : nullptr};
+            double* Lc[2] = {ULc[grp[gi][0]], ng[gi] > 1 ? ULc[grp[gi][1]] : nullptr};
+            CK(stab_rows(ctx, w, st, R, ng[gi], w->ns[grp[gi][0]], w->sign));
+            CK(stab_cols(ctx, w, st, Lc, ng[gi], w->ns[grp[gi][0]], w->sign));
+        }
+        for (int s = 0; s < 2; ++s)
+            CK(cudaMemcpyAsync(w->ULs[s] + (size_t)(M / S) * N * w->ns[s], ULc[s], (size_t)N * w->ns[s] * 8,
                                cudaMemcpyDeviceToDevice, st));
-            for (int ell = M; ell >= 1; --ell) {
-                CK(prop_left(ctx, w, st, s, ell, w->Ucur, w->Utmp));
-                if ((ell - 1) % S == 0) {
-                    CK(stab_left(ctx, w, st, s, w->Ucur, w->sign));
-                    CK(cudaMemcpyAsync(w->ULs[s] + (size_t)((ell - 1) / S) * N * ns, w->Ucur, (size_t)N * ns * 8,
-                                       cudaMemcpyDeviceToDevice, st));
+        // U_L(l - 1) = U_L(l) B_l, re-orthonormalised and stored at every recompute point
+        for (int ell = M; ell >= 1; --ell) {
+            for (int s = 0; s < 2; ++s) CK(prop_left(ctx, w, st, s, ell, ULc[s], w->Utmp));
+            if ((ell - 1) % S == 0) {
+                for (int gi = 0; gi < ngr; ++gi) {
+                    double* Lc[2] = {ULc[grp[gi][0]], ng[gi] > 1 ? ULc[grp[gi][1]] : nullptr};
+                    CK(stab_cols(ctx, w, st, Lc, ng[gi], w->ns[grp[gi][0]], w->sign));
                 }
+                for (int s = 0; s < 2; ++s)
+                    CK(cudaMemcpyAsync(w->ULs[s] + (size_t)((ell - 1) / S) * N * w->ns[s], ULc[s],
+                                       (size_t)N * w->ns[s] * 8, cudaMemcpyDeviceToDevice, st));
             }
-            CK(form_G(ctx, w, st, s, UR0, w->ULs[s], w->sign));
-            if (ctx->p.precision == AFQMC_PREC_FP64) CK(store_G<double>(w, st, s));
-            else CK(store_G<float>(w, st, s));
+        }
+        // G(0) = 1 - U_R (U_L U_R)^{-1} U_L
+        for (int gi = 0; gi < ngr; ++gi) {
+            const double* R[2] = {w->URs[grp[gi][0]], ng[gi] > 1 ? w->URs[grp[gi][1]] : nullptr};
+            const double* Lf[2] = {w->ULs[grp[gi][0]], ng[gi] > 1 ? w->ULs[grp[gi][1]] : nullptr};
+            CK(form_Z(ctx, w, st, R, Lf, ng[gi], w->ns[grp[gi][0]], w->sign));
+            for (int q = 0; q < ng[gi]; ++q) {
+                const int s = grp[gi][q];
+                CK(finish_G(w, st, w->URs[s], q, w->ns[s]));
+                if (ctx->p.precision == AFQMC_PREC_FP64) CK(store_G<double>(w, st, s));
+                else CK(store_G<float>(w, st, s));
+            }
         }
         w->pos = 0;
         w->last_dir = -1;
@@ -780,44 +885,64 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
         const int N = w->N, j = w->pos / S;
         PhaseScope ps(ctx, AFQMC_PHASE_RECOMPUTE, st);
         CK(cudaMemsetAsync(w->acc2, 0, 16, st));
+        // the factors of the current position: one side from the stacks, the other propagated
+        // over the last S slices from the previous stack entry and re-orthonormalised
+        double* UR[2];
+        double* UL[2];
+        double* Uc[2] = {w->Ucur, w->Ucur + (size_t)N * w->nsm};
+        bool prop = false;
         for (int s = 0; s < 2; ++s) {
-            const int ns = w->ns[s];
-            const size_t blk = (size_t)N * ns;
-            double* UR;
-            double* UL;
+            const size_t blk = (size_t)N * w->ns[s];
             if (w->last_dir > 0) {
+                UL[s] = w->ULs[s] + (size_t)j * blk;
                 if (j == 0) {
-                    UR = w->URs[s];
+                    UR[s] = w->URs[s];
                 } else {
-                    CK(cudaMemcpyAsync(w->Ucur, w->URs[s] + (size_t)(j - 1) * blk, blk * 8, cudaMemcpyDeviceToDevice, st));
-                    for (int ell = w->pos - S + 1; ell <= w->pos; ++ell) CK(prop_right(ctx, w, st, s, ell, w->Ucur, w->Utmp));
-                    CK(stab_right(ctx, w, st, s, w->Ucur, nullptr));
-                    CK(cudaMemcpyAsync(w->URs[s] + (size_t)j * blk, w->Ucur, blk * 8, cudaMemcpyDeviceToDevice, st));
-                    UR = w->URs[s] + (size_t)j * blk;
+                    CK(cudaMemcpyAsync(Uc[s], w->URs[s] + (size_t)(j - 1) * blk, blk * 8, cudaMemcpyDeviceToDevice, st));
+                    for (int ell = w->pos - S + 1; ell <= w->pos; ++ell) CK(prop_right(ctx, w, st, s, ell, Uc[s], w->Utmp));
+                    UR[s] = w->URs[s] + (size_t)j * blk;
+                    prop = true;
                 }
-                UL = w->ULs[s] + (size_t)j * blk;
             } else {
-                const int M = ctx->p.M;
-                if (w->pos == M) {
-                    UL = w->ULs[s] + (size_t)j * blk;
+                UR[s] = w->URs[s] + (size_t)j * blk;
+                if (w->pos == ctx->p.M) {
+                    UL[s] = w->ULs[s] + (size_t)j * blk;
                 } else {
-                    CK(cudaMemcpyAsync(w->Ucur, w->ULs[s] + (size_t)(j + 1) * blk, blk * 8, cudaMemcpyDeviceToDevice, st));
-                    for (int ell = w->pos + S; ell >= w->pos + 1; --ell) CK(prop_left(ctx, w, st, s, ell, w->Ucur, w->Utmp));
-                    CK(stab_left(ctx, w, st, s, w->Ucur, nullptr));
-                    CK(cudaMemcpyAsync(w->ULs[s] + (size_t)j * blk, w->Ucur, blk * 8, cudaMemcpyDeviceToDevice, st));
-                    UL = w->ULs[s] + (size_t)j * blk;
+                    CK(cudaMemcpyAsync(Uc[s], w->ULs[s] + (size_t)(j + 1) * blk, blk * 8, cudaMemcpyDeviceToDevice, st));
+                    for (int ell = w->pos + S; ell >= w->pos + 1; --ell) CK(prop_left(ctx, w, st, s, ell, Uc[s], w->Utmp));
+                    UL[s] = w->ULs[s] + (size_t)j * blk;
+                    prop = true;
                 }
-                UR = w->URs[s] + (size_t)j * blk;
             }
-            CK(form_G(ctx, w, st, s, UR, UL, nullptr));
-            if (f64) {
-                double* G = (double*)w->G + (size_t)s * N * w->ld;
-                CK(launch_drift<double>(st, G, (const double*)w->Gnew, w->ld, N, w->acc2));
-                CK(store_G<double>(w, st, s));
-            } else {
-                float* G = (float*)w->G + (size_t)s * N * w->ld;
-                CK(launch_drift<float>(st, G, (const float*)w->Gnew, w->ld, N, w->acc2));
-                CK(store_G<float>(w, st, s));
+        }
+        int grp[2][2], ng[2];
+        const int ngr = spin_groups(w, grp, ng);
+        if (prop) {
+            for (int gi = 0; gi < ngr; ++gi) {
+                double* Cg[2] = {Uc[grp[gi][0]], ng[gi] > 1 ? Uc[grp[gi][1]] : nullptr};
+                if (w->last_dir > 0) CK(stab_rows(ctx, w, st, Cg, ng[gi], w->ns[grp[gi][0]], nullptr));
+                else CK(stab_cols(ctx, w, st, Cg, ng[gi], w->ns[grp[gi][0]], nullptr));
+            }
+            for (int s = 0; s < 2; ++s)
+                CK(cudaMemcpyAsync(w->last_dir > 0 ? UR[s] : UL[s], Uc[s], (size_t)N * w->ns[s] * 8,
+                                   cudaMemcpyDeviceToDevice, st));
+        }
+        for (int gi = 0; gi < ngr; ++gi) {
+            const double* R[2] = {UR[grp[gi][0]], ng[gi] > 1 ? UR[grp[gi][1]] : nullptr};
+            const double* Lf[2] = {UL[grp[gi][0]], ng[gi] > 1 ? UL[grp[gi][1]] : nullptr};
+            CK(form_Z(ctx, w, st, R, Lf, ng[gi], w->ns[grp[gi][0]], nullptr));
+            for (int q = 0; q < ng[gi]; ++q) {
+                const int s = grp[gi][q];
+                CK(finish_G(w, st, UR[s], q, w->ns[s]));
+                if (f64) {
+                    double* G = (double*)w->G + (size_t)s * N * w->ld;
+                    CK(launch_drift<double>(st, G, (const double*)w->Gnew, w->ld, N, w->acc2));
+                    CK(store_G<double>(w, st, s));
+                } else {
+                    float* G = (float*)w->G + (size_t)s * N * w->ld;
+                    CK(launch_drift<float>(st, G, (const float*)w->Gnew, w->ld, N, w->acc2));
+                    CK(store_G<float>(w, st, s));
+                }
             }
         }
         w->need_recompute = false;

@@ -68,20 +68,35 @@ cudaError_t launch_field_scales(cudaStream_t st, const int8_t* x, int N, double 
 template <typename T>
 cudaError_t launch_field_scales_T(cudaStream_t st, const int8_t* x, int N, const double* c2, T* d, T* dinv, long sd);
 
-struct ElimScratch;  // defined in setup.cu
-// Pivoted elimination on the device (persistent cooperative kernel).
-//   mode 0 (tall LU re-orthonormalisation): A is R x C (element (r,c) at A[r*rs + c*cs]),
-//          R >= C; on return A holds L' with A_in = L' U, U upper triangular (the basis of
-//          the column space used as the new factor).  *sign_out *= sign(det U).
-//   mode 1 (Gauss-Jordan solve): A is R x (R + nrhs) row-major (ld = rs), left block square;
-//          on return rows hold the reduced system; `perm` gets the pivot row of each column;
-//          *sign_out *= sign(det of the left block).
-cudaError_t launch_elim(cudaStream_t st, int mode, double* A, int R, int C, long rs, long cs, int nrhs,
-                        int* perm, double* sign_out, void* scratch, int* err);
-size_t elim_scratch_bytes(int R);
-// Z[j, :] = A[perm[j], R:] / A[perm[j], j] for the Gauss-Jordan result.
-cudaError_t launch_gj_extract(cudaStream_t st, const double* A, long ld, int R, int nrhs, const int* perm,
-                              double* Z, long ldz);
+// Blocked partially pivoted LU in FP64 (lu.cu) of nmat (1 or 2) row-major m x n matrices
+// (m >= n) without row swaps: after launch_lu, perm[j] is the pivot row of column j; a pivot
+// row holds its multipliers left of its column and its U entries from there on; unpivoted rows
+// hold multipliers.  flag: m bytes per matrix (scratch).  err receives DEV_NUMERIC on a zero
+// pivot.
+struct LuArgs {
+    double* A[2] = {nullptr, nullptr};
+    int* perm[2] = {nullptr, nullptr};
+    int8_t* flag[2] = {nullptr, nullptr};
+    long lda = 0;
+    int m = 0, n = 0, nmat = 1;
+    int* err = nullptr;
+};
+cudaError_t launch_lu(cudaStream_t st, const LuArgs& a);
+// After launch_lu: pivot rows become unit rows, so A = P L spans the factored columns.
+cudaError_t launch_lu_unit_rows(cudaStream_t st, const LuArgs& a);
+// After launch_lu: *sign_out *= sign(prod of pivots) (times the row permutation's parity when
+// parity != 0), over all matrices; visited: m ints of scratch.
+cudaError_t launch_lu_sign(cudaStream_t st, const LuArgs& a, int parity, double* sign_out, int* visited);
+// Z = O^{-1} B for O factored by launch_lu (ns x ns, leading dimension ldl), B and Z ns x N.
+struct SolveArgs {
+    const double* LU[2] = {nullptr, nullptr};
+    const int* perm[2] = {nullptr, nullptr};
+    const double* B[2] = {nullptr, nullptr};
+    double* Z[2] = {nullptr, nullptr};
+    long ldl = 0;
+    int ns = 0, N = 0, nmat = 1;
+};
+cudaError_t launch_lu_solve(cudaStream_t st, const SolveArgs& a);
 template <typename T>
 cudaError_t launch_identity_minus(cudaStream_t st, T* G, long ld, int N);  // G = I - G
 template <typename T>

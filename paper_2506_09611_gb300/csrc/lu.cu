@@ -1,0 +1,481 @@
+// lu.cu -- blocked, partially pivoted LU in FP64 for the recompute (Sec. II.C, Eq. GrFMatNew).
+//
+// The re-orthonormalisation of the propagated factor U (N x Nsigma) and the solve
+// (U_L U_R) Z = U_L both rest on an LU factorisation with partial pivoting.  GB300 runs FP64
+// at a small fraction of its FP32 rate and every pivot is a grid-wide dependency, so the
+// factorisation is blocked:
+//   * a panel of LU_NB columns is factored by one thread-block cluster per matrix: each CTA
+//     keeps its share of the rows in shared memory and the CTAs agree on every pivot through
+//     distributed shared memory and one cluster barrier per column;
+//   * the pivot rows' trailing part is finished inside the cluster (U12 = L11^{-1} A12);
+//   * the trailing update A22 -= L21 U12 is an FP64 tiled product over the whole GPU.
+// Rows are not swapped: a pivoted row is flagged, keeps its multipliers left of its pivot
+// column and its U entries from there on, and perm[j] names the pivot row of column j.  Both
+// spins go through every launch (two independent matrices).
+#include <cooperative_groups.h>
+#include <limits.h>
+
+#include "internal.h"
+
+namespace afq {
+namespace cg = cooperative_groups;
+
+constexpr int LU_NB = 32;
+constexpr int LU_NBP = LU_NB + 1;
+
+struct LuCand {
+    double v;
+    int r;
+    int pad;
+    double row[LU_NB];
+};
+
+__device__ __forceinline__ void lu_better(double& bv, int& br, double v, int r) {
+    if (v > bv || (v == bv && r < br)) {
+        bv = v;
+        br = r;
+    }
+}
+
+// One cluster of CS CTAs per matrix (blockIdx.x / CS = matrix).  Factors columns
+// [j0, j0 + nbk) over the rows not yet pivoted and finishes the pivot rows' columns
+// [j0 + nbk, n).
+template <int CS>
+__global__ void __launch_bounds__(256) lu_panel_kernel(LuArgs a, int j0, int nbk) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int mat = blockIdx.x / CS;
+    double* A = a.A[mat];
+    int* perm = a.perm[mat];
+    int8_t* flag = a.flag[mat];
+    const int m = a.m, n = a.n;
+    const long lda = a.lda;
+    const int r0 = (int)((long)m * rank / CS), r1 = (int)((long)m * (rank + 1) / CS), nr = r1 - r0;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    extern __shared__ __align__(16) double lu_smem[];
+    double* Pn = lu_smem;                    // [nr][LU_NBP] own rows of the panel
+    int8_t* fl = (int8_t*)(Pn + (size_t)nr * LU_NBP);
+    __shared__ LuCand cand[2];               // this CTA's pivot candidate, by step parity
+    __shared__ double L11[LU_NB][LU_NBP];    // pivot rows' panel values at their pivot step
+    __shared__ int s_prow[LU_NB];            // pivot row of each step
+    __shared__ double s_bv[8];
+    __shared__ int s_br[8];
+    __shared__ int s_p, s_owner, s_bad;
+    for (int e = tid; e < nr * nbk; e += nt) {
+        const int q = e / nbk, c = e - q * nbk;
+        Pn[q * LU_NBP + c] = A[(long)(r0 + q) * lda + j0 + c];
+    }
+    for (int q = tid; q < nr; q += nt) fl[q] = flag[r0 + q];
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    for (int jj = 0; jj < nbk; ++jj) {
+        const int par = jj & 1;
+        // this CTA's candidate: largest |a| in column jj over its unpivoted rows (ties: lower row)
+        double bv = -1.0;
+        int br = INT_MAX;
+        for (int q = tid; q < nr; q += nt)
+            if (!fl[q]) lu_better(bv, br, fabs(Pn[q * LU_NBP + jj]), r0 + q);
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+            const int orr = __shfl_down_sync(0xffffffffu, br, o);
+            lu_better(bv, br, ov, orr);
+        }
+        if (lane == 0) {
+            s_bv[wid] = bv;
+            s_br[wid] = br;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < (nt >> 5); ++w) lu_better(bv, br, s_bv[w], s_br[w]);
+            cand[par].v = bv;
+            cand[par].r = br;
+        }
+        __syncthreads();
+        {
+            const int crow = cand[par].r;
+            if (tid < nbk) cand[par].row[tid] = (crow >= r0 && crow < r1) ? Pn[(crow - r0) * LU_NBP + tid] : 0.0;
+        }
+        cl.sync();  // every CTA's candidate is published
+        if (tid < 32) {
+            double v = -1.0;
+            int r = INT_MAX, ow = 0;
+            if (tid < CS) {
+                const LuCand* rc = cl.map_shared_rank(&cand[par], tid);
+                v = rc->v;
+                r = rc->r;
+                ow = tid;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_down_sync(0xffffffffu, v, o);
+                const int orr = __shfl_down_sync(0xffffffffu, r, o);
+                const int oow = __shfl_down_sync(0xffffffffu, ow, o);
+                if (ov > v || (ov == v && orr < r)) {
+                    v = ov;
+                    r = orr;
+                    ow = oow;
+                }
+            }
+            if (tid == 0) {
+                if (!(v > 0.0) || r >= m) {
+                    s_bad = 1;
+                    r = (r >= m) ? 0 : r;
+                }
+                s_p = r;
+                s_owner = ow;
+                s_prow[jj] = r;
+            }
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (tid < nbk) {
+            const LuCand* rc = cl.map_shared_rank(&cand[par], s_owner);
+            L11[jj][tid] = rc->row[tid];
+        }
+        if (tid == 0 && p >= r0 && p < r1) fl[p - r0] = 1;
+        if (tid == 0 && rank == 0) perm[j0 + jj] = p;
+        __syncthreads();
+        const double pv = L11[jj][jj];
+        const double pinv = (s_bad || pv == 0.0) ? 0.0 : 1.0 / pv;
+        // own unpivoted rows: multiplier into column jj, rank-1 step on the panel's later columns
+        for (int q = tid; q < nr; q += nt) {
+            if (fl[q]) continue;
+            double* row = Pn + q * LU_NBP;
+            const double l = row[jj] * pinv;
+            row[jj] = l;
+            for (int c = jj + 1; c < nbk; ++c) row[c] -= l * L11[jj][c];
+        }
+        __syncthreads();
+    }
+    cl.sync();  // no CTA leaves while another may still read its candidate slots
+    if (s_bad && tid == 0 && rank == 0) set_err(a.err, DEV_NUMERIC);
+    for (int e = tid; e < nr * nbk; e += nt) {
+        const int q = e / nbk, c = e - q * nbk;
+        A[(long)(r0 + q) * lda + j0 + c] = Pn[q * LU_NBP + c];
+    }
+    for (int q = tid; q < nr; q += nt) flag[r0 + q] = fl[q];
+    // U12 = L11^{-1} A12 on the pivot rows, columns split over the cluster
+    for (int c = j0 + nbk + rank * nt + tid; c < n; c += CS * nt) {
+        double x[LU_NB];
+#pragma unroll
+        for (int k = 0; k < LU_NB; ++k) x[k] = (k < nbk) ? A[(long)s_prow[k] * lda + c] : 0.0;
+#pragma unroll
+        for (int k = 1; k < LU_NB; ++k) {
+            if (k < nbk) {
+                double acc = x[k];
+#pragma unroll
+                for (int kp = 0; kp < k; ++kp) acc -= L11[k][kp] * x[kp];
+                x[k] = acc;
+            }
+        }
+#pragma unroll
+        for (int k = 1; k < LU_NB; ++k)
+            if (k < nbk) A[(long)s_prow[k] * lda + c] = x[k];
+    }
+}
+
+// A[r][c] -= sum_k A[r][j0 + k] U12[k][c] for the unpivoted rows r and c in [j0 + nbk, n), with
+// U12[k] the pivot row perm[j0 + k].  64 x 64 tiles, 4 x 4 outputs per thread; grid (row tiles,
+// column tiles, matrix).
+__global__ void __launch_bounds__(256) lu_update_kernel(LuArgs a, int j0, int nbk) {
+    const int mat = blockIdx.z;
+    double* A = a.A[mat];
+    const int* perm = a.perm[mat];
+    const int8_t* flag = a.flag[mat];
+    const long lda = a.lda;
+    const int m = a.m, n = a.n;
+    const int r0 = blockIdx.x * 64, c0 = j0 + nbk + blockIdx.y * 64;
+    __shared__ double Ls[64][LU_NBP];
+    __shared__ double Us[LU_NB][64 + 1];
+    __shared__ int8_t fl[64];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int q = tid; q < 64; q += nt) fl[q] = (r0 + q < m) ? flag[r0 + q] : 1;
+    __syncthreads();
+    for (int e = tid; e < 64 * LU_NB; e += nt) {
+        const int q = e / LU_NB, k = e - q * LU_NB;
+        Ls[q][k] = (k < nbk && !fl[q]) ? A[(long)(r0 + q) * lda + j0 + k] : 0.0;
+    }
+    for (int e = tid; e < LU_NB * 64; e += nt) {
+        const int k = e >> 6, c = e & 63;
+        Us[k][c] = (k < nbk && c0 + c < n) ? A[(long)perm[j0 + k] * lda + c0 + c] : 0.0;
+    }
+    __syncthreads();
+    const int tx = tid & 15, ty = tid >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k = 0; k < nbk; ++k) {
+        double lv[4], uv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) lv[i] = Ls[ty + 16 * i][k];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) uv[j] = Us[k][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += lv[i] * uv[j];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int q = ty + 16 * i;
+        if (fl[q]) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = c0 + tx + 16 * j;
+            if (c < n) A[(long)(r0 + q) * lda + c] -= acc[i][j];
+        }
+    }
+}
+
+// Pivot rows of the factored tall matrix become unit rows: A[perm[j]][c] = (c == j) for c >= j,
+// so A = P L (unit lower trapezoidal, rows in the original order) spans the same columns.
+__global__ void lu_unit_rows_kernel(LuArgs a) {
+    const int mat = blockIdx.y;
+    double* A = a.A[mat];
+    const int* perm = a.perm[mat];
+    const int n = a.n;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)n * n; e += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / n), c = (int)(e % n);
+        if (c >= j) A[(long)perm[j] * a.lda + c] = (c == j) ? 1.0 : 0.0;
+    }
+}
+
+// *sign_out *= the sign of the product of the pivots of every matrix (times each permutation's
+// parity when `parity`): the sign of det(A) for square A.  One thread; visited holds m ints.
+__global__ void lu_sign_kernel(LuArgs a, int parity, double* sign_out, int* visited) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double sg = 1.0;
+    for (int mat = 0; mat < a.nmat; ++mat) {
+        const double* A = a.A[mat];
+        const int* perm = a.perm[mat];
+        for (int j = 0; j < a.n; ++j)
+            if (A[(long)perm[j] * a.lda + j] < 0.0) sg = -sg;
+        if (parity) {
+            for (int r = 0; r < a.m; ++r) visited[r] = 0;
+            for (int r = 0; r < a.m; ++r) {
+                if (visited[r]) continue;
+                int len = 0, q = r;
+                while (!visited[q]) {
+                    visited[q] = 1;
+                    q = perm[q];
+                    ++len;
+                }
+                if ((len & 1) == 0) sg = -sg;
+            }
+        }
+    }
+    *sign_out *= sg;
+}
+
+template <int CS>
+static cudaError_t launch_panel(cudaStream_t st, const LuArgs& a, int j0, int nbk) {
+    const int rpc = (a.m + CS - 1) / CS;
+    const size_t shm = (size_t)rpc * LU_NBP * sizeof(double) + (size_t)rpc + 16;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute((void*)lu_panel_kernel<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(227 * 1024 - 16 * 1024));
+        if (e != cudaSuccess) return e;
+        if (CS > 8) {
+            e = cudaFuncSetAttribute((void*)lu_panel_kernel<CS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+        }
+        attr = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CS * a.nmat);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = shm;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    count_launch();
+    return cudaLaunchKernelEx(&cfg, lu_panel_kernel<CS>, a, j0, nbk);
+}
+
+static int lu_cluster_size(const LuArgs& a) {
+    static int cs = 0;
+    if (cs) return cs;
+    // 16-CTA clusters if two of them fit at once, else the portable 8
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(32);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = (size_t)((a.m + 15) / 16) * LU_NBP * sizeof(double) + (a.m + 15) / 16 + 16;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    cudaFuncSetAttribute((void*)lu_panel_kernel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute((void*)lu_panel_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(227 * 1024 - 16 * 1024));
+    if (cudaOccupancyMaxActiveClusters(&ncl, (void*)lu_panel_kernel<16>, &cfg) == cudaSuccess && ncl >= 2) cs = 16;
+    else cs = 8;
+    cudaGetLastError();
+    return cs;
+}
+
+cudaError_t launch_lu(cudaStream_t st, const LuArgs& a) {
+    if (a.m < a.n || a.n < 1 || a.nmat < 1 || a.nmat > 2) return cudaErrorInvalidValue;
+    const int cs = lu_cluster_size(a);
+    if ((a.m + cs - 1) / cs * (LU_NBP * sizeof(double) + 1) > 200 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e;
+    for (int q = 0; q < a.nmat; ++q)
+        if ((e = cudaMemsetAsync(a.flag[q], 0, (size_t)a.m, st)) != cudaSuccess) return e;
+    for (int j0 = 0; j0 < a.n; j0 += LU_NB) {
+        const int nbk = (a.n - j0 < LU_NB) ? a.n - j0 : LU_NB;
+        e = (cs == 16) ? launch_panel<16>(st, a, j0, nbk) : launch_panel<8>(st, a, j0, nbk);
+        if (e != cudaSuccess) return e;
+        const int nc = a.n - j0 - nbk;
+        if (nc > 0) {
+            count_launch();
+            lu_update_kernel<<<dim3((a.m + 63) / 64, (nc + 63) / 64, a.nmat), 256, 0, st>>>(a, j0, nbk);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_lu_unit_rows(cudaStream_t st, const LuArgs& a) {
+    count_launch();
+    lu_unit_rows_kernel<<<dim3(256, a.nmat), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lu_sign(cudaStream_t st, const LuArgs& a, int parity, double* sign_out, int* visited) {
+    if (!sign_out) return cudaSuccess;
+    count_launch();
+    lu_sign_kernel<<<1, 1, 0, st>>>(a, parity, sign_out, visited);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Z = O^{-1} B for a factored square O (ns x ns, no-swap form: row perm[j] holds L[j][0..j)
+// and U[j][j..ns)) and B (ns x N), both matrices of the batch:
+//   forward  y_j = B[perm[j]] - sum_{k<j} L[j][k] y_k,
+//   backward z_j = (y_j - sum_{k>j} U[j][k] z_k) / U[j][j],   Z[j] = z_j.
+// The right-hand sides are independent: each CTA owns SV_COLS columns in shared memory and
+// walks the rows in blocks of 32 (a product with the finished rows, then the 32 x 32 diagonal
+// block column by column).  Grid (column blocks, matrix).
+// ---------------------------------------------------------------------------
+constexpr int SV_COLS = 11, SV_YP = SV_COLS + 1, SV_KB = 64;
+
+__global__ void __launch_bounds__(256) lu_solve_kernel(SolveArgs a) {
+    const int mat = blockIdx.y;
+    const double* LU = a.LU[mat];
+    const int* perm = a.perm[mat];
+    const double* B = a.B[mat];
+    double* Z = a.Z[mat];
+    const int ns = a.ns, N = a.N;
+    const long ldl = a.ldl;
+    const int c0 = blockIdx.x * SV_COLS, nc = min(SV_COLS, N - c0);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    extern __shared__ __align__(16) double sv_smem[];
+    double* y = sv_smem;                        // [ns][SV_YP]
+    double* Lc = y + (size_t)ns * SV_YP;        // [32][SV_KB + 1]
+    double* rinv = Lc + 32 * (SV_KB + 1);       // [ns]
+    int* sp = (int*)(rinv + ns);                // [ns]
+    for (int j = tid; j < ns; j += nt) sp[j] = perm[j];
+    __syncthreads();
+    for (int e = tid; e < ns * SV_COLS; e += nt) {
+        const int j = e / SV_COLS, c = e - j * SV_COLS;
+        y[j * SV_YP + c] = (c < nc) ? B[(long)sp[j] * N + c0 + c] : 0.0;
+    }
+    for (int j = tid; j < ns; j += nt) rinv[j] = 1.0 / LU[(long)sp[j] * ldl + j];
+    __syncthreads();
+    // forward substitution (unit lower L)
+    for (int J0 = 0; J0 < ns; J0 += 32) {
+        const int jb = min(32, ns - J0);
+        for (int k0 = 0; k0 < J0; k0 += SV_KB) {
+            const int kb = min(SV_KB, J0 - k0);
+            for (int e = tid; e < jb * SV_KB; e += nt) {
+                const int r = e / SV_KB, k = e - r * SV_KB;
+                Lc[r * (SV_KB + 1) + k] = (k < kb) ? LU[(long)sp[J0 + r] * ldl + k0 + k] : 0.0;
+            }
+            __syncthreads();
+            for (int e = tid; e < jb * SV_COLS; e += nt) {
+                const int r = e / SV_COLS, c = e - r * SV_COLS;
+                double acc = 0.0;
+                for (int k = 0; k < kb; ++k) acc += Lc[r * (SV_KB + 1) + k] * y[(k0 + k) * SV_YP + c];
+                y[(J0 + r) * SV_YP + c] -= acc;
+            }
+            __syncthreads();
+        }
+        for (int e = tid; e < jb * 32; e += nt) {
+            const int r = e >> 5, k = e & 31;
+            Lc[r * (SV_KB + 1) + k] = (k < jb) ? LU[(long)sp[J0 + r] * ldl + J0 + k] : 0.0;
+        }
+        __syncthreads();
+        if (tid < SV_COLS) {
+            for (int r = 1; r < jb; ++r) {
+                double acc = 0.0;
+                for (int k = 0; k < r; ++k) acc += Lc[r * (SV_KB + 1) + k] * y[(J0 + k) * SV_YP + tid];
+                y[(J0 + r) * SV_YP + tid] -= acc;
+            }
+        }
+        __syncthreads();
+    }
+    // backward substitution (U)
+    const int nblk = (ns + 31) / 32;
+    for (int bj = nblk - 1; bj >= 0; --bj) {
+        const int J0 = bj * 32, jb = min(32, ns - J0), J1 = J0 + jb;
+        for (int k0 = J1; k0 < ns; k0 += SV_KB) {
+            const int kb = min(SV_KB, ns - k0);
+            for (int e = tid; e < jb * SV_KB; e += nt) {
+                const int r = e / SV_KB, k = e - r * SV_KB;
+                Lc[r * (SV_KB + 1) + k] = (k < kb) ? LU[(long)sp[J0 + r] * ldl + k0 + k] : 0.0;
+            }
+            __syncthreads();
+            for (int e = tid; e < jb * SV_COLS; e += nt) {
+                const int r = e / SV_COLS, c = e - r * SV_COLS;
+                double acc = 0.0;
+                for (int k = 0; k < kb; ++k) acc += Lc[r * (SV_KB + 1) + k] * y[(k0 + k) * SV_YP + c];
+                y[(J0 + r) * SV_YP + c] -= acc;
+            }
+            __syncthreads();
+        }
+        for (int e = tid; e < jb * 32; e += nt) {
+            const int r = e >> 5, k = e & 31;
+            Lc[r * (SV_KB + 1) + k] = (k < jb) ? LU[(long)sp[J0 + r] * ldl + J0 + k] : 0.0;
+        }
+        __syncthreads();
+        if (tid < SV_COLS) {
+            for (int r = jb - 1; r >= 0; --r) {
+                double acc = y[(J0 + r) * SV_YP + tid];
+                for (int k = r + 1; k < jb; ++k) acc -= Lc[r * (SV_KB + 1) + k] * y[(J0 + k) * SV_YP + tid];
+                y[(J0 + r) * SV_YP + tid] = acc * rinv[J0 + r];
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < ns * SV_COLS; e += nt) {
+        const int j = e / SV_COLS, c = e - j * SV_COLS;
+        if (c < nc) Z[(long)j * N + c0 + c] = y[j * SV_YP + c];
+    }
+}
+
+cudaError_t launch_lu_solve(cudaStream_t st, const SolveArgs& a) {
+    const size_t shm = ((size_t)a.ns * SV_YP + 32 * (SV_KB + 1) + a.ns) * sizeof(double) + (size_t)a.ns * sizeof(int);
+    if (shm > 220 * 1024) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute((void*)lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             220 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    count_launch();
+    lu_solve_kernel<<<dim3((a.N + SV_COLS - 1) / SV_COLS, a.nmat), 256, shm, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace afq

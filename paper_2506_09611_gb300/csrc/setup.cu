@@ -3,8 +3,6 @@
 //   exp(-tau K) for the periodic square lattice (Eq. 2DHubbard): the dispersion
 //   eps_k = -2t(cos kx + cos ky) separates, so E = Ex (x) Ey with
 //   Ex_{x,x'} = L^{-1} sum_k exp(2 tau t cos k) cos(k (x - x')).
-//   Pivoted elimination (Sec. II.B, Eq. GrFMatNew): the stabilisation that
-//   keeps U_R / U_L well conditioned, and the solve (U_L U_R) Z = U_L.
 #include <math.h>
 
 #include "internal.h"
@@ -149,199 +147,6 @@ cudaError_t launch_field_scales_T(cudaStream_t st, const int8_t* x, int N, const
 }
 template cudaError_t launch_field_scales_T<float>(cudaStream_t, const int8_t*, int, const double*, float*, float*, long);
 template cudaError_t launch_field_scales_T<double>(cudaStream_t, const int8_t*, int, const double*, double*, double*, long);
-
-// ---------------------------------------------------------------------------
-// pivoted elimination, persistent cooperative kernel (FP64)
-// ---------------------------------------------------------------------------
-struct Cand {
-    double v;
-    int r;
-    int pad;
-};
-
-struct ElimScratch {
-    GridBar bar;
-    int pad[2];
-    // followed by Cand cand[nblk], int8 piv_flag[R], int visited[R]
-};
-
-size_t elim_scratch_bytes(int R) {
-    return sizeof(ElimScratch) + 2048 * sizeof(Cand) + (size_t)R + (size_t)R * sizeof(int) + 64;
-}
-
-__device__ __forceinline__ void better(double& bv, int& br, double v, int r) {
-    if (v > bv || (v == bv && r < br)) { bv = v; br = r; }
-}
-
-// MODE 0: tall LU on A (R x C), eliminate only non-pivoted rows (the multipliers stay in place).
-// MODE 1: Gauss-Jordan on A (R x (R + nrhs)), eliminate every row but the pivot row.
-// COLMAJ: element (r, c) at A[r + c * cs] (rows contiguous); else at A[r * rs + c].
-// Each CTA owns at most ELIM_ROWS consecutive rows; one grid barrier per pivot.
-constexpr int ELIM_ROWS = 16;
-
-template <int MODE, bool COLMAJ>
-__global__ void __launch_bounds__(256) elim_kernel(double* __restrict__ A, int R, int C, long rs, long cs, int nrhs,
-                                                   int* perm, double* sign_out, unsigned char* scratch, int* err) {
-    ElimScratch* sc = (ElimScratch*)scratch;
-    Cand* cand = (Cand*)(scratch + sizeof(ElimScratch));
-    int8_t* pflag = (int8_t*)(cand + 2048);  // cand is double-buffered by step parity
-    int* visited = (int*)(((uintptr_t)(pflag + R) + 15) & ~(uintptr_t)15);
-    const int nblk = gridDim.x, b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-    const int r0 = (int)((long)R * b / nblk), r1 = (int)((long)R * (b + 1) / nblk);
-    const int nr = r1 - r0;
-    const int ncols = (MODE == 0) ? C : R + nrhs;
-    const int nsteps = (MODE == 0) ? C : R;
-    __shared__ double s_l[ELIM_ROWS];
-    __shared__ double s_bv[8];
-    __shared__ int s_br[8];
-    __shared__ int s_p;
-    __shared__ double s_pv;
-    __shared__ int8_t s_flag[ELIM_ROWS];
-    auto at = [=](int r, int c) -> double* { return COLMAJ ? A + (size_t)c * cs + r : A + (size_t)r * rs + c; };
-    for (int q = tid; q < nr; q += nt) s_flag[q] = 0;
-    __syncthreads();
-    auto block_candidate = [&](int j) {
-        double bv = -1.0;
-        int br = 0x7fffffff;
-        for (int q = tid; q < nr; q += nt)
-            if (!s_flag[q]) better(bv, br, fabs(*at(r0 + q, j)), r0 + q);
-        for (int o = 16; o > 0; o >>= 1) {
-            double ov = __shfl_down_sync(0xffffffffu, bv, o);
-            int orr = __shfl_down_sync(0xffffffffu, br, o);
-            better(bv, br, ov, orr);
-        }
-        if ((tid & 31) == 0) { s_bv[tid >> 5] = bv; s_br[tid >> 5] = br; }
-        __syncthreads();
-        if (tid == 0) {
-            for (int w = 1; w < nt / 32; ++w) better(bv, br, s_bv[w], s_br[w]);
-            cand[(j & 1) * 1024 + b].v = bv;
-            cand[(j & 1) * 1024 + b].r = br;
-        }
-    };
-    block_candidate(0);
-    if (!grid_barrier(&sc->bar, nblk, err)) return;
-    double sgn = 1.0;
-    for (int j = 0; j < nsteps; ++j) {
-        if (tid < 32) {  // warp 0 reduces the per-CTA candidates (loads in flight together)
-            double bv = -1.0;
-            int br = 0x7fffffff;
-            for (int q = tid; q < nblk; q += 32) better(bv, br, cand[(j & 1) * 1024 + q].v, cand[(j & 1) * 1024 + q].r);
-            for (int o = 16; o > 0; o >>= 1) {
-                double ov = __shfl_down_sync(0xffffffffu, bv, o);
-                int orr = __shfl_down_sync(0xffffffffu, br, o);
-                better(bv, br, ov, orr);
-            }
-            if (tid == 0) {
-                if (!(bv > 0.0) || br >= R) {
-                    set_err(err, DEV_NUMERIC);
-                    br = 0;
-                }
-                s_p = br;
-                s_pv = *at(br, j);
-            }
-        }
-        __syncthreads();
-        const int p = s_p;
-        const double pinv = 1.0 / s_pv;  // one division per step; the rows multiply
-        if (read_err(err) != 0) return;
-        if (b == 0 && tid == 0) {
-            perm[j] = p;
-            if (s_pv < 0) sgn = -sgn;
-        }
-        if (p >= r0 && p < r1 && tid == 0) s_flag[p - r0] = 1;
-        __syncthreads();
-        for (int q = tid; q < nr; q += nt) {  // multipliers of the own rows
-            const int r = r0 + q;
-            const bool act = (MODE == 0) ? !s_flag[q] : (r != p);
-            s_l[q] = act ? *at(r, j) * pinv : 0.0;
-        }
-        __syncthreads();
-        if (COLMAJ) {
-            // own rows are contiguous in each column: 16 threads per column, 16 columns at a time
-            const int q = tid & (ELIM_ROWS - 1);
-            if (q < nr) {
-                const double l = s_l[q];
-                if (l != 0.0) {
-                    double* a = A + (size_t)(r0 + q);
-                    const double* pc = A + (size_t)p;
-                    for (int c = j + 1 + (tid >> 4); c < ncols; c += nt >> 4) {
-                        const size_t o = (size_t)c * cs;
-                        a[o] -= l * pc[o];
-                    }
-                }
-            }
-        } else {
-            const double* prow = A + (size_t)p * rs;
-            for (int q = 0; q < nr; ++q) {
-                const double l = s_l[q];
-                if (l == 0.0) continue;
-                double* row = A + (size_t)(r0 + q) * rs;
-                for (int c = j + 1 + tid; c < ncols; c += nt) row[c] -= l * prow[c];
-            }
-        }
-        for (int q = tid; q < nr; q += nt) {
-            const int r = r0 + q;
-            const bool act = (MODE == 0) ? !s_flag[q] : (r != p);
-            if (act) *at(r, j) = (MODE == 0) ? s_l[q] : 0.0;
-        }
-        __syncthreads();
-        if (j + 1 < nsteps) block_candidate(j + 1);
-        if (!grid_barrier(&sc->bar, nblk, err)) return;
-    }
-    if (MODE == 0) {
-        // pivot rows of L': 1 on the diagonal position, 0 to its right
-        for (long e = (long)b * nt + tid; e < (long)nsteps * C; e += (long)nblk * nt) {
-            int j = (int)(e / C), c = (int)(e % C);
-            if (c >= j) *at(perm[j], c) = (c == j) ? 1.0 : 0.0;
-        }
-    } else if (b == 0 && tid == 0) {
-        // parity of the row permutation j -> perm[j]
-        for (int r = 0; r < R; ++r) visited[r] = 0;
-        for (int r = 0; r < R; ++r) {
-            if (visited[r]) continue;
-            int len = 0, q = r;
-            while (!visited[q]) { visited[q] = 1; q = perm[q]; ++len; }
-            if ((len & 1) == 0) sgn = -sgn;
-        }
-    }
-    if (b == 0 && tid == 0 && sign_out) *sign_out *= sgn;
-    (void)pflag;
-}
-
-cudaError_t launch_elim(cudaStream_t st, int mode, double* A, int R, int C, long rs, long cs, int nrhs, int* perm,
-                        double* sign_out, void* scratch, int* err) {
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const bool colmaj = (mode == 0 && rs == 1);
-    void* fn = mode == 1 ? (void*)elim_kernel<1, false> : (colmaj ? (void*)elim_kernel<0, true> : (void*)elim_kernel<0, false>);
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
-    if (e != cudaSuccess) return e;
-    int nblk = nsm < R ? nsm : R;
-    if ((R + nblk - 1) / nblk > ELIM_ROWS) nblk = (R + ELIM_ROWS - 1) / ELIM_ROWS;  // at most ELIM_ROWS rows each
-    if (nblk > per_sm * nsm || nblk > 1024) return cudaErrorInvalidValue;            // must be co-resident
-    unsigned char* sc = (unsigned char*)scratch;
-    e = cudaMemsetAsync(sc, 0, sizeof(ElimScratch), st);
-    if (e != cudaSuccess) return e;
-    void* args[] = {&A, &R, &C, &rs, &cs, &nrhs, &perm, &sign_out, &sc, &err};
-    count_launch();
-    return cudaLaunchCooperativeKernel(fn, dim3(nblk), dim3(256), args, 0, st);
-}
-
-__global__ void gj_extract_kernel(const double* A, long ld, int R, int nrhs, const int* perm, double* Z, long ldz) {
-    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)R * nrhs; e += (long)gridDim.x * blockDim.x) {
-        int j = (int)(e / nrhs), c = (int)(e % nrhs);
-        int p = perm[j];
-        Z[(long)j * ldz + c] = A[(long)p * ld + R + c] / A[(long)p * ld + j];
-    }
-}
-cudaError_t launch_gj_extract(cudaStream_t st, const double* A, long ld, int R, int nrhs, const int* perm, double* Z,
-                              long ldz) {
-    count_launch();
-    gj_extract_kernel<<<512, 256, 0, st>>>(A, ld, R, nrhs, perm, Z, ldz);
-    return cudaGetLastError();
-}
 
 template <typename T>
 __global__ void identity_minus_kernel(T* G, long ld, int N) {
