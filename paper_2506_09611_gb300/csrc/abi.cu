@@ -232,6 +232,43 @@ static Lattice* get_lattice(afqmc_ctx* ctx, int L, cudaStream_t st, cudaError_t*
     return l;
 }
 
+static cudaError_t prop_right(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, int ell, double* U, double* tmp);
+static cudaError_t prop_left(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, int ell, double* U, double* tmp);
+// Propagate both spins' factors U[s] over nsl slices l = l_first, l_first + l_step, ...
+// (right factors N x ns: B_l U; left factors ns x N: U B_l) with the fused kernel; lattices too
+// large for it take the per-slice separable products.
+static cudaError_t propagate(afqmc_ctx* ctx, Walker* w, cudaStream_t st, double* const* U, int left, int l_first,
+                             int l_step, int nsl) {
+    const int N = w->N;
+    PropArgs a;
+    for (int s = 0; s < 2; ++s) {
+        a.U[s] = U[s];
+        a.nvec[s] = w->ns[s];
+        a.vs[s] = left ? N : 1;
+        a.es[s] = left ? 1 : w->ns[s];
+        a.dplus[s] = exp(ctx->c[s]);
+        a.dminus[s] = exp(-ctx->c[s]);
+    }
+    a.Ex = w->lat->Ex64;
+    a.x = w->x;
+    a.L = w->L;
+    a.l_first = l_first;
+    a.l_step = l_step;
+    a.nsl = nsl;
+    a.left = left;
+    a.nmat = 2;
+    cudaError_t e = launch_prop(st, a);
+    if (e != cudaErrorInvalidValue) return e;
+    cudaGetLastError();
+    for (int t = 0; t < nsl; ++t)
+        for (int s = 0; s < 2; ++s) {
+            const int ell = l_first + t * l_step;
+            e = left ? prop_left(ctx, w, st, s, ell, U[s], w->Utmp) : prop_right(ctx, w, st, s, ell, U[s], w->Utmp);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
 // Spin groups for the batched FP64 steps: both spins in one launch when they have the same
 // particle number, else one at a time.
 static int spin_groups(const Walker* w, int grp[2][2], int ng[2]) {
@@ -605,7 +642,7 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
                                cudaMemcpyDeviceToDevice, st));
         // U_L(l - 1) = U_L(l) B_l, re-orthonormalised and stored at every recompute point
         for (int ell = M; ell >= 1; --ell) {
-            for (int s = 0; s < 2; ++s) CK(prop_left(ctx, w, st, s, ell, ULc[s], w->Utmp));
+            if (ell % S == 0) CK(propagate(ctx, w, st, ULc, 1, ell, -1, S));  // slices ell .. ell - S + 1
             if ((ell - 1) % S == 0) {
                 for (int gi = 0; gi < ngr; ++gi) {
                     double* Lc[2] = {ULc[grp[gi][0]], ng[gi] > 1 ? ULc[grp[gi][1]] : nullptr};
@@ -899,7 +936,6 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
                     UR[s] = w->URs[s];
                 } else {
                     CK(cudaMemcpyAsync(Uc[s], w->URs[s] + (size_t)(j - 1) * blk, blk * 8, cudaMemcpyDeviceToDevice, st));
-                    for (int ell = w->pos - S + 1; ell <= w->pos; ++ell) CK(prop_right(ctx, w, st, s, ell, Uc[s], w->Utmp));
                     UR[s] = w->URs[s] + (size_t)j * blk;
                     prop = true;
                 }
@@ -909,7 +945,6 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
                     UL[s] = w->ULs[s] + (size_t)j * blk;
                 } else {
                     CK(cudaMemcpyAsync(Uc[s], w->ULs[s] + (size_t)(j + 1) * blk, blk * 8, cudaMemcpyDeviceToDevice, st));
-                    for (int ell = w->pos + S; ell >= w->pos + 1; --ell) CK(prop_left(ctx, w, st, s, ell, Uc[s], w->Utmp));
                     UL[s] = w->ULs[s] + (size_t)j * blk;
                     prop = true;
                 }
@@ -918,6 +953,8 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
         int grp[2][2], ng[2];
         const int ngr = spin_groups(w, grp, ng);
         if (prop) {
+            if (w->last_dir > 0) CK(propagate(ctx, w, st, Uc, 0, w->pos - S + 1, 1, S));
+            else CK(propagate(ctx, w, st, Uc, 1, w->pos + S, -1, S));
             for (int gi = 0; gi < ngr; ++gi) {
                 double* Cg[2] = {Uc[grp[gi][0]], ng[gi] > 1 ? Uc[grp[gi][1]] : nullptr};
                 if (w->last_dir > 0) CK(stab_rows(ctx, w, st, Cg, ng[gi], w->ns[grp[gi][0]], nullptr));

@@ -68,6 +68,21 @@ cudaError_t launch_field_scales(cudaStream_t st, const int8_t* x, int N, double 
 template <typename T>
 cudaError_t launch_field_scales_T(cudaStream_t st, const int8_t* x, int N, const double* c2, T* d, T* dinv, long sd);
 
+// Fused FP64 propagation over nsl slices l = l_first, l_first + l_step, ... (setup.cu): for each
+// of nvec vectors of length N = L*L (element i of vector v at U[v * vs + i * es]),
+// right factors: v <- D_l (E v); left factors (left != 0): v <- E (D_l v); E = Ex (x) Ex,
+// D_l = diag(x_{l,i} > 0 ? dplus : dminus) with x the M x N fields.  nmat (1 or 2) spins.
+struct PropArgs {
+    double* U[2] = {nullptr, nullptr};
+    long vs[2] = {0, 0}, es[2] = {0, 0};
+    int nvec[2] = {0, 0};
+    double dplus[2] = {1.0, 1.0}, dminus[2] = {1.0, 1.0};
+    const double* Ex = nullptr;
+    const int8_t* x = nullptr;
+    int L = 0, l_first = 1, l_step = 1, nsl = 0, left = 0, nmat = 1;
+};
+cudaError_t launch_prop(cudaStream_t st, const PropArgs& a);
+
 // Blocked partially pivoted LU in FP64 (lu.cu) of nmat (1 or 2) row-major m x n matrices
 // (m >= n) without row swaps: after launch_lu, perm[j] is the pivot row of column j; a pivot
 // row holds its multipliers left of its column and its U entries from there on; unpivoted rows

@@ -23,23 +23,24 @@ namespace cg = cooperative_groups;
 constexpr int LU_NB = 32;
 constexpr int LU_NBP = LU_NB + 1;
 
-struct LuCand {
-    double v;
-    int r;
-    int pad;
-    double row[LU_NB];
-};
-
-__device__ __forceinline__ void lu_better(double& bv, int& br, double v, int r) {
-    if (v > bv || (v == bv && r < br)) {
-        bv = v;
-        br = r;
-    }
-}
-
 // One cluster of CS CTAs per matrix (blockIdx.x / CS = matrix).  Factors columns
 // [j0, j0 + nbk) over the rows not yet pivoted and finishes the pivot rows' columns
 // [j0 + nbk, n).
+// Pivot candidates compare |a| through the bit pattern of the double with the sign cleared:
+// for finite non-negative doubles the integer order is the numeric order, and integer compares
+// avoid the long FP64 latency on the pivot search's critical path.  Ties go to the lower row.
+__device__ __forceinline__ unsigned long long lu_key(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+}
+__device__ __forceinline__ void lu_pick(unsigned long long& k, int& r, double& x, unsigned long long ok, int orr,
+                                        double ox) {
+    if (ok > k || (ok == k && orr < r)) {
+        k = ok;
+        r = orr;
+        x = ox;
+    }
+}
+
 template <int CS>
 __global__ void __launch_bounds__(256) lu_panel_kernel(LuArgs a, int j0, int nbk) {
     cg::cluster_group cl = cg::this_cluster();
@@ -55,12 +56,14 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(LuArgs a, int j0, int nbk
     extern __shared__ __align__(16) double lu_smem[];
     double* Pn = lu_smem;                    // [nr][LU_NBP] own rows of the panel
     int8_t* fl = (int8_t*)(Pn + (size_t)nr * LU_NBP);
-    __shared__ LuCand cand[2];               // this CTA's pivot candidate, by step parity
+    // each warp's candidate of the step (by step parity): key, row, signed value
+    __shared__ unsigned long long cand_k[2][8];
+    __shared__ int cand_r[2][8];
+    __shared__ double cand_x[2][8];
     __shared__ double L11[LU_NB][LU_NBP];    // pivot rows' panel values at their pivot step
     __shared__ int s_prow[LU_NB];            // pivot row of each step
-    __shared__ double s_bv[8];
-    __shared__ int s_br[8];
-    __shared__ int s_p, s_owner, s_bad;
+    __shared__ int s_bad;
+    __shared__ double s_pinv;
     for (int e = tid; e < nr * nbk; e += nt) {
         const int q = e / nbk, c = e - q * nbk;
         Pn[q * LU_NBP + c] = A[(long)(r0 + q) * lda + j0 + c];
@@ -68,105 +71,116 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(LuArgs a, int j0, int nbk
     for (int q = tid; q < nr; q += nt) fl[q] = flag[r0 + q];
     if (tid == 0) s_bad = 0;
     __syncthreads();
+    // candidate of column 0 (later columns: found during the previous step's row update)
+    unsigned long long bk = 0;
+    int br = INT_MAX;
+    double bx = 0.0;
+    for (int q = tid; q < nr; q += nt)
+        if (!fl[q]) {
+            const double x = Pn[q * LU_NBP];
+            lu_pick(bk, br, bx, lu_key(x), r0 + q, x);
+        }
     for (int jj = 0; jj < nbk; ++jj) {
         const int par = jj & 1;
-        // this CTA's candidate: largest |a| in column jj over its unpivoted rows (ties: lower row)
-        double bv = -1.0;
-        int br = INT_MAX;
-        for (int q = tid; q < nr; q += nt)
-            if (!fl[q]) lu_better(bv, br, fabs(Pn[q * LU_NBP + jj]), r0 + q);
         for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_down_sync(0xffffffffu, bv, o);
-            const int orr = __shfl_down_sync(0xffffffffu, br, o);
-            lu_better(bv, br, ov, orr);
+            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+            const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+            const double ox = __shfl_xor_sync(0xffffffffu, bx, o);
+            lu_pick(bk, br, bx, ok, orr, ox);
         }
         if (lane == 0) {
-            s_bv[wid] = bv;
-            s_br[wid] = br;
+            cand_k[par][wid] = (br == INT_MAX) ? 0ULL : bk;
+            cand_r[par][wid] = br;
+            cand_x[par][wid] = bx;
         }
-        __syncthreads();
-        if (tid == 0) {
-            for (int w = 1; w < (nt >> 5); ++w) lu_better(bv, br, s_bv[w], s_br[w]);
-            cand[par].v = bv;
-            cand[par].r = br;
-        }
-        __syncthreads();
-        {
-            const int crow = cand[par].r;
-            if (tid < nbk) cand[par].row[tid] = (crow >= r0 && crow < r1) ? Pn[(crow - r0) * LU_NBP + tid] : 0.0;
-        }
-        cl.sync();  // every CTA's candidate is published
-        if (tid < 32) {
-            double v = -1.0;
-            int r = INT_MAX, ow = 0;
-            if (tid < CS) {
-                const LuCand* rc = cl.map_shared_rank(&cand[par], tid);
-                v = rc->v;
-                r = rc->r;
-                ow = tid;
+        cl.sync();  // every warp's candidate is published
+        if (wid == 0) {
+            // the winner over the cluster's 8 x CS warp candidates (4 per lane), then the pivot
+            // row straight from the owner's shared memory (a pivoted row is never written again)
+            unsigned long long k = 0;
+            int r = INT_MAX;
+            double x = 0.0;
+#pragma unroll
+            for (int t = 0; t < (8 * CS + 31) / 32; ++t) {
+                const int slot = lane + 32 * t;
+                if (slot < 8 * CS) {
+                    const int cta = slot % CS, w = slot / CS;
+                    const unsigned long long ok = *cl.map_shared_rank(&cand_k[par][w], cta);
+                    const int orr = *cl.map_shared_rank(&cand_r[par][w], cta);
+                    const double ox = *cl.map_shared_rank(&cand_x[par][w], cta);
+                    if (orr != INT_MAX) lu_pick(k, r, x, ok, orr, ox);
+                }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_down_sync(0xffffffffu, v, o);
-                const int orr = __shfl_down_sync(0xffffffffu, r, o);
-                const int oow = __shfl_down_sync(0xffffffffu, ow, o);
-                if (ov > v || (ov == v && orr < r)) {
-                    v = ov;
-                    r = orr;
-                    ow = oow;
-                }
+                const unsigned long long ok = __shfl_xor_sync(0xffffffffu, k, o);
+                const int orr = __shfl_xor_sync(0xffffffffu, r, o);
+                const double ox = __shfl_xor_sync(0xffffffffu, x, o);
+                lu_pick(k, r, x, ok, orr, ox);
             }
-            if (tid == 0) {
-                if (!(v > 0.0) || r >= m) {
-                    s_bad = 1;
-                    r = (r >= m) ? 0 : r;
-                }
-                s_p = r;
-                s_owner = ow;
-                s_prow[jj] = r;
+            const bool bad = (k == 0ULL) || (k >= 0x7ff0000000000000ULL) || r >= m;
+            const int p = (r >= m) ? 0 : r;
+            if (lane == jj) s_pinv = bad ? 0.0 : 1.0 / x;  // one FP64 division, overlapping the row read
+            int own = (int)(((long)p * CS) / m);
+            while (own > 0 && (int)((long)m * own / CS) > p) --own;
+            while (own < CS - 1 && (int)((long)m * (own + 1) / CS) <= p) ++own;
+            const int pr0 = (int)((long)m * own / CS);
+            const double* prow = cl.map_shared_rank(Pn, own) + (size_t)(p - pr0) * LU_NBP;
+            if (lane < nbk) L11[jj][lane] = prow[lane];
+            if (lane == 0) {
+                if (bad) s_bad = 1;
+                s_prow[jj] = p;
+                if (p >= r0 && p < r1) fl[p - r0] = 1;
+                if (rank == 0) perm[j0 + jj] = p;
             }
         }
         __syncthreads();
-        const int p = s_p;
-        if (tid < nbk) {
-            const LuCand* rc = cl.map_shared_rank(&cand[par], s_owner);
-            L11[jj][tid] = rc->row[tid];
-        }
-        if (tid == 0 && p >= r0 && p < r1) fl[p - r0] = 1;
-        if (tid == 0 && rank == 0) perm[j0 + jj] = p;
-        __syncthreads();
-        const double pv = L11[jj][jj];
-        const double pinv = (s_bad || pv == 0.0) ? 0.0 : 1.0 / pv;
-        // own unpivoted rows: multiplier into column jj, rank-1 step on the panel's later columns
+        const double pinv = s_pinv;
+        // own unpivoted rows: multiplier into column jj, rank-1 step on the later panel columns
+        // (four independent multiply-adds at a time: FP64 latency is long on this part), and the
+        // candidate for column jj + 1
+        bk = 0;
+        br = INT_MAX;
+        bx = 0.0;
         for (int q = tid; q < nr; q += nt) {
             if (fl[q]) continue;
-            double* row = Pn + q * LU_NBP;
+            double* __restrict__ row = Pn + q * LU_NBP;
             const double l = row[jj] * pinv;
             row[jj] = l;
-            for (int c = jj + 1; c < nbk; ++c) row[c] -= l * L11[jj][c];
+            int c = jj + 1;
+            for (; c + 3 < nbk; c += 4) {
+                const double u0 = L11[jj][c], u1 = L11[jj][c + 1], u2 = L11[jj][c + 2], u3 = L11[jj][c + 3];
+                const double v0 = row[c], v1 = row[c + 1], v2 = row[c + 2], v3 = row[c + 3];
+                row[c] = v0 - l * u0;
+                row[c + 1] = v1 - l * u1;
+                row[c + 2] = v2 - l * u2;
+                row[c + 3] = v3 - l * u3;
+            }
+            for (; c < nbk; ++c) row[c] -= l * L11[jj][c];
+            if (jj + 1 < nbk) {
+                const double x = row[jj + 1];
+                lu_pick(bk, br, bx, lu_key(x), r0 + q, x);
+            }
         }
-        __syncthreads();
     }
-    cl.sync();  // no CTA leaves while another may still read its candidate slots
+    cl.sync();  // no CTA leaves while another may still read its shared memory
     if (s_bad && tid == 0 && rank == 0) set_err(a.err, DEV_NUMERIC);
     for (int e = tid; e < nr * nbk; e += nt) {
         const int q = e / nbk, c = e - q * nbk;
         A[(long)(r0 + q) * lda + j0 + c] = Pn[q * LU_NBP + c];
     }
     for (int q = tid; q < nr; q += nt) flag[r0 + q] = fl[q];
-    // U12 = L11^{-1} A12 on the pivot rows, columns split over the cluster
-    for (int c = j0 + nbk + rank * nt + tid; c < n; c += CS * nt) {
+    // U12 = L11^{-1} A12 on the pivot rows, columns dealt round-robin over the cluster's CTAs
+    // (the FP64 work of a column is sequential, so every SM should get a share)
+    for (int c = j0 + nbk + rank + CS * tid; c < n; c += CS * nt) {
         double x[LU_NB];
 #pragma unroll
         for (int k = 0; k < LU_NB; ++k) x[k] = (k < nbk) ? A[(long)s_prow[k] * lda + c] : 0.0;
+        // right-looking: each step's updates are independent of one another
 #pragma unroll
-        for (int k = 1; k < LU_NB; ++k) {
-            if (k < nbk) {
-                double acc = x[k];
+        for (int kp = 0; kp + 1 < LU_NB; ++kp)
 #pragma unroll
-                for (int kp = 0; kp < k; ++kp) acc -= L11[k][kp] * x[kp];
-                x[k] = acc;
-            }
-        }
+            for (int k = kp + 1; k < LU_NB; ++k)
+                if (k < nbk) x[k] -= L11[k][kp] * x[kp];
 #pragma unroll
         for (int k = 1; k < LU_NB; ++k)
             if (k < nbk) A[(long)s_prow[k] * lda + c] = x[k];
@@ -404,9 +418,16 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(SolveArgs a) {
             __syncthreads();
             for (int e = tid; e < jb * SV_COLS; e += nt) {
                 const int r = e / SV_COLS, c = e - r * SV_COLS;
-                double acc = 0.0;
-                for (int k = 0; k < kb; ++k) acc += Lc[r * (SV_KB + 1) + k] * y[(k0 + k) * SV_YP + c];
-                y[(J0 + r) * SV_YP + c] -= acc;
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;  // independent chains (FP64 latency)
+                int k = 0;
+                for (; k + 3 < kb; k += 4) {
+                    a0 += Lc[r * (SV_KB + 1) + k] * y[(k0 + k) * SV_YP + c];
+                    a1 += Lc[r * (SV_KB + 1) + k + 1] * y[(k0 + k + 1) * SV_YP + c];
+                    a2 += Lc[r * (SV_KB + 1) + k + 2] * y[(k0 + k + 2) * SV_YP + c];
+                    a3 += Lc[r * (SV_KB + 1) + k + 3] * y[(k0 + k + 3) * SV_YP + c];
+                }
+                for (; k < kb; ++k) a0 += Lc[r * (SV_KB + 1) + k] * y[(k0 + k) * SV_YP + c];
+                y[(J0 + r) * SV_YP + c] -= (a0 + a1) + (a2 + a3);
             }
             __syncthreads();
         }
@@ -415,14 +436,13 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(SolveArgs a) {
             Lc[r * (SV_KB + 1) + k] = (k < jb) ? LU[(long)sp[J0 + r] * ldl + J0 + k] : 0.0;
         }
         __syncthreads();
-        if (tid < SV_COLS) {
-            for (int r = 1; r < jb; ++r) {
-                double acc = 0.0;
-                for (int k = 0; k < r; ++k) acc += Lc[r * (SV_KB + 1) + k] * y[(J0 + k) * SV_YP + tid];
-                y[(J0 + r) * SV_YP + tid] -= acc;
+        for (int rp = 0; rp + 1 < jb; ++rp) {  // diagonal block, right-looking
+            for (int e = tid; e < (jb - rp - 1) * SV_COLS; e += nt) {
+                const int r = rp + 1 + e / SV_COLS, c = e % SV_COLS;
+                y[(J0 + r) * SV_YP + c] -= Lc[r * (SV_KB + 1) + rp] * y[(J0 + rp) * SV_YP + c];
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
     // backward substitution (U)
     const int nblk = (ns + 31) / 32;
@@ -437,9 +457,16 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(SolveArgs a) {
             __syncthreads();
             for (int e = tid; e < jb * SV_COLS; e += nt) {
                 const int r = e / SV_COLS, c = e - r * SV_COLS;
-                double acc = 0.0;
-                for (int k = 0; k < kb; ++k) acc += Lc[r * (SV_KB + 1) + k] * y[(k0 + k) * SV_YP + c];
-                y[(J0 + r) * SV_YP + c] -= acc;
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+                int k = 0;
+                for (; k + 3 < kb; k += 4) {
+                    a0 += Lc[r * (SV_KB + 1) + k] * y[(k0 + k) * SV_YP + c];
+                    a1 += Lc[r * (SV_KB + 1) + k + 1] * y[(k0 + k + 1) * SV_YP + c];
+                    a2 += Lc[r * (SV_KB + 1) + k + 2] * y[(k0 + k + 2) * SV_YP + c];
+                    a3 += Lc[r * (SV_KB + 1) + k + 3] * y[(k0 + k + 3) * SV_YP + c];
+                }
+                for (; k < kb; ++k) a0 += Lc[r * (SV_KB + 1) + k] * y[(k0 + k) * SV_YP + c];
+                y[(J0 + r) * SV_YP + c] -= (a0 + a1) + (a2 + a3);
             }
             __syncthreads();
         }
@@ -448,12 +475,16 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(SolveArgs a) {
             Lc[r * (SV_KB + 1) + k] = (k < jb) ? LU[(long)sp[J0 + r] * ldl + J0 + k] : 0.0;
         }
         __syncthreads();
-        if (tid < SV_COLS) {
-            for (int r = jb - 1; r >= 0; --r) {
-                double acc = y[(J0 + r) * SV_YP + tid];
-                for (int k = r + 1; k < jb; ++k) acc -= Lc[r * (SV_KB + 1) + k] * y[(J0 + k) * SV_YP + tid];
-                y[(J0 + r) * SV_YP + tid] = acc * rinv[J0 + r];
+        for (int rp = jb - 1; rp >= 1; --rp) {  // diagonal block, right-looking: z_rp = y_rp / U_rp,rp
+            for (int e = tid; e < rp * SV_COLS; e += nt) {
+                const int r = e / SV_COLS, c = e % SV_COLS;
+                y[(J0 + r) * SV_YP + c] -= Lc[r * (SV_KB + 1) + rp] * (y[(J0 + rp) * SV_YP + c] * rinv[J0 + rp]);
             }
+            __syncthreads();
+        }
+        for (int e = tid; e < jb * SV_COLS; e += nt) {
+            const int r = e / SV_COLS, c = e % SV_COLS;
+            y[(J0 + r) * SV_YP + c] *= rinv[J0 + r];
         }
         __syncthreads();
     }

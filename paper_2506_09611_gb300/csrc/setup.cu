@@ -148,6 +148,103 @@ cudaError_t launch_field_scales_T(cudaStream_t st, const int8_t* x, int N, const
 template cudaError_t launch_field_scales_T<float>(cudaStream_t, const int8_t*, int, const double*, float*, float*, long);
 template cudaError_t launch_field_scales_T<double>(cudaStream_t, const int8_t*, int, const double*, double*, double*, long);
 
+// ---------------------------------------------------------------------------
+// FP64 propagation of the walker factors over several slices (Sec. II.C), fused.
+// A factor is a set of vectors of length N = L*L (columns of U_R, rows of U_L), vector v element
+// i = x + L*y at U[v * vs + i * es].  E = exp(-dtau K) = Ex (x) Ex on the periodic square lattice,
+// so E v is Ex M Ex for the L x L matrix M[y][x] = v[x + L*y].  Per slice l (in the given order):
+//   right factor (B_l U):  v <- D_l (E v);      left factor (U B_l): v <- E (D_l v),
+// with D_l = diag(exp(c x_{l,i})) (x = +-1, so D_l picks exp(+c) or exp(-c)).  Each CTA keeps
+// PV_VEC vectors in shared memory for all slices.  Grid (vector blocks, spin).
+// ---------------------------------------------------------------------------
+constexpr int PV_VEC = 10;
+__global__ void __launch_bounds__(256) prop_kernel(PropArgs a, int vpc) {
+    const int s = blockIdx.y;
+    double* U = a.U[s];
+    const int L = a.L, N = L * L, nvec = a.nvec[s];
+    const long vs = a.vs[s], es = a.es[s];
+    const int v0 = blockIdx.x * vpc;
+    if (v0 >= nvec) return;
+    const int nv = min(vpc, nvec - v0);
+    const double dp = a.dplus[s], dm = a.dminus[s];
+    extern __shared__ __align__(16) double pv_smem[];
+    double* Ex = pv_smem;            // [L][L]
+    double* T = Ex + L * L;          // [L][L]
+    double* V = T + L * L;           // [nv][N]
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < L * L; e += nt) Ex[e] = a.Ex[e];
+    for (int e = tid; e < nv * N; e += nt) {
+        const int v = e / N, i = e - v * N;
+        V[e] = U[(long)(v0 + v) * vs + (long)i * es];
+    }
+    __syncthreads();
+    for (int t = 0; t < a.nsl; ++t) {
+        const int ell = a.l_first + t * a.l_step;
+        const int8_t* xl = a.x + (size_t)(ell - 1) * N;
+        if (a.left)
+            for (int e = tid; e < nv * N; e += nt) V[e] *= (xl[e % N] > 0) ? dp : dm;
+        __syncthreads();
+        for (int v = 0; v < nv; ++v) {
+            double* M = V + (size_t)v * N;
+            // (four independent accumulators: FP64 multiply-add latency is long on this part)
+            for (int e = tid; e < N; e += nt) {  // T = Ex M  (along y)
+                const int y = e / L, x = e - y * L;
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+                int yp = 0;
+                for (; yp + 3 < L; yp += 4) {
+                    a0 += Ex[y * L + yp] * M[yp * L + x];
+                    a1 += Ex[y * L + yp + 1] * M[(yp + 1) * L + x];
+                    a2 += Ex[y * L + yp + 2] * M[(yp + 2) * L + x];
+                    a3 += Ex[y * L + yp + 3] * M[(yp + 3) * L + x];
+                }
+                for (; yp < L; ++yp) a0 += Ex[y * L + yp] * M[yp * L + x];
+                T[e] = (a0 + a1) + (a2 + a3);
+            }
+            __syncthreads();
+            for (int e = tid; e < N; e += nt) {  // M = T Ex  (along x)
+                const int y = e / L, x = e - y * L;
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+                int xp = 0;
+                for (; xp + 3 < L; xp += 4) {
+                    a0 += T[y * L + xp] * Ex[xp * L + x];
+                    a1 += T[y * L + xp + 1] * Ex[(xp + 1) * L + x];
+                    a2 += T[y * L + xp + 2] * Ex[(xp + 2) * L + x];
+                    a3 += T[y * L + xp + 3] * Ex[(xp + 3) * L + x];
+                }
+                for (; xp < L; ++xp) a0 += T[y * L + xp] * Ex[xp * L + x];
+                M[e] = (a0 + a1) + (a2 + a3);
+            }
+            __syncthreads();
+        }
+        if (!a.left) {
+            for (int e = tid; e < nv * N; e += nt) V[e] *= (xl[e % N] > 0) ? dp : dm;
+            __syncthreads();
+        }
+    }
+    for (int e = tid; e < nv * N; e += nt) {
+        const int v = e / N, i = e - v * N;
+        U[(long)(v0 + v) * vs + (long)i * es] = V[e];
+    }
+}
+
+cudaError_t launch_prop(cudaStream_t st, const PropArgs& a) {
+    const int N = a.L * a.L;
+    const long room = 220 * 1024 / 8 - 2L * a.L * a.L;  // doubles left for the vectors
+    const int vpc = (int)((room / N < PV_VEC) ? room / N : PV_VEC);
+    if (vpc < 1) return cudaErrorInvalidValue;  // lattice too large to keep one vector on chip
+    const size_t shm = ((size_t)2 * a.L * a.L + (size_t)vpc * N) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute((void*)prop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int nv = a.nvec[0] > a.nvec[1] ? a.nvec[0] : a.nvec[1];
+    count_launch();
+    prop_kernel<<<dim3((nv + vpc - 1) / vpc, a.nmat), 256, shm, st>>>(a, vpc);
+    return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void identity_minus_kernel(T* G, long ld, int N) {
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)N * N; e += (long)gridDim.x * blockDim.x) {
