@@ -318,9 +318,12 @@ def main():
 FP64_FMA_PER_SM_CLK = 2
 # TF32 tensor rate relative to bf16 (nominal dense 1.1 vs 2.25 PFLOP/s).
 TF32_OVER_BF16 = 1.1 / 2.25
-# DRAM bytes per launch (read + write) from one ncu capture of the current kernel, in bytes;
-# None when no capture of the current kernel exists.
-NCU_TRAFFIC = {"elim": None, "lu_o": None, "solve": None, "wrap_gemm": None, "flush_gemm": None}
+# DRAM bytes per launch (read + write) from one ncu capture of the current kernel on this
+# workload; None where the phase spans several kernels or no capture of the current kernel exists.
+NCU_TRAFFIC = {"elim": None, "lu_o": None,
+               "solve": 25.807104e6 + 0.080896e6,      # lu_solve_kernel, 700 x 700, 1600 right-hand sides
+               "wrap_gemm": 30.75968e6 + 0.092928e6,   # tc_gemm_kernel<128, split3>, 1600^3, both spins
+               "flush_gemm": None}
 
 
 def fp32_alu_peak(pk):
