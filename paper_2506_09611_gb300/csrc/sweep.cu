@@ -205,17 +205,17 @@ __device__ __forceinline__ void trailing_update(T* Gs, int n, int P, int a, T f0
 
 // W = -F U1^{-1} L1^{-1} of the window from the frozen coefficients in the block (see the window
 // kernel's tail); written to Wx[s][k][j] (pitch NW).  32 warps: spin = warp / 16, columns
-// (warp % 16) * WCPW + c.
-template <typename T>
-__device__ __forceinline__ void window_w(const T* Gs, int n, int P, const int* idx, const T (*fk)[WinCap<T>::NW],
-                                         int m, T* Wx, int tid) {
-    constexpr int NW = WinCap<T>::NW, RPL = NW / 32, WCPW = NW / 16;
-    const int lane = tid & 31, w = tid >> 5;
-    if (w >= 32) return;
+// (warp % 16) * WCPW + c; lane l holds rows l + 32 r, r < RPL (RPL >= ceil(m / 32)).  The
+// coefficient of the next step is fetched while the current one is applied, and the forward
+// pass of a warp starts at its first column (identity columns are zero above the diagonal).
+template <typename T, int RPL>
+__device__ __forceinline__ void window_w_rpl(const T* Gs, int n, int P, const int* idx, const T (*fk)[WinCap<T>::NW],
+                                             int m, T* Wx, int lane, int w) {
+    constexpr int NW = WinCap<T>::NW, WCPW = NW / 16;
     const int s = w >> 4, j0 = (w & 15) * WCPW;
     if (j0 >= m) return;
     const T* Gb = Gs + (size_t)s * n * P;
-    const int rmax = (m + 31) >> 5;
+    const T* fks = fk[s];
     int ik[RPL];
     T y[RPL][WCPW];
 #pragma unroll
@@ -225,10 +225,19 @@ __device__ __forceinline__ void window_w(const T* Gs, int n, int P, const int* i
 #pragma unroll
         for (int c = 0; c < WCPW; ++c) y[r][c] = (k == j0 + c) ? T(1) : T(0);
     }
+    // coefficient cf[r] = C[k][kp] f_kp of this lane's rows for step kp
+    auto coef = [&](int kp, T* cf) {
+        const int ikp = idx[kp];
+        const T f = fks[kp];
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) cf[r] = Gb[ik[r] * P + ikp] * f;
+    };
+    T cf[RPL], cfn[RPL];
     // forward: rows k > kp
-    for (int kp = 0; kp + 1 < m; ++kp) {
-        const int ikp = idx[kp], ro = kp >> 5, lo = kp & 31;
-        const T fkp = fk[s][kp];
+    if (j0 + 1 < m) coef(j0, cf);
+    for (int kp = j0; kp + 1 < m; ++kp) {
+        if (kp + 2 < m) coef(kp + 1, cfn);
+        const int ro = kp >> 5, lo = kp & 31;
         T v[WCPW];
 #pragma unroll
         for (int c = 0; c < WCPW; ++c) {
@@ -240,19 +249,20 @@ __device__ __forceinline__ void window_w(const T* Gs, int n, int P, const int* i
         }
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
-            if (r >= rmax) break;
             const int k = lane + 32 * r;
             if (k > kp && k < m) {
-                const T cf = Gb[ik[r] * P + ikp] * fkp;
 #pragma unroll
-                for (int c = 0; c < WCPW; ++c) y[r][c] -= cf * v[c];
+                for (int c = 0; c < WCPW; ++c) y[r][c] -= cf[r] * v[c];
             }
         }
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) cf[r] = cfn[r];
     }
     // backward: rows k < kp
+    if (m >= 2) coef(m - 1, cf);
     for (int kp = m - 1; kp >= 1; --kp) {
-        const int ikp = idx[kp], ro = kp >> 5, lo = kp & 31;
-        const T fkp = fk[s][kp];
+        if (kp >= 2) coef(kp - 1, cfn);
+        const int ro = kp >> 5, lo = kp & 31;
         T v[WCPW];
 #pragma unroll
         for (int c = 0; c < WCPW; ++c) {
@@ -264,26 +274,38 @@ __device__ __forceinline__ void window_w(const T* Gs, int n, int P, const int* i
         }
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
-            if (r >= rmax) break;
             const int k = lane + 32 * r;
             if (k < kp) {
-                const T cf = Gb[ik[r] * P + ikp] * fkp;
 #pragma unroll
-                for (int c = 0; c < WCPW; ++c) y[r][c] -= cf * v[c];
+                for (int c = 0; c < WCPW; ++c) y[r][c] -= cf[r] * v[c];
             }
         }
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) cf[r] = cfn[r];
     }
     T* Wd = Wx + (size_t)s * NW * NW;
 #pragma unroll
     for (int r = 0; r < RPL; ++r) {
         const int k = lane + 32 * r;
         if (k < m) {
-            const T fkk = -fk[s][k];
+            const T fkk = -fks[k];
 #pragma unroll
             for (int c = 0; c < WCPW; ++c)
                 if (j0 + c < m) Wd[k * NW + j0 + c] = fkk * y[r][c];
         }
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void window_w(const T* Gs, int n, int P, const int* idx, const T (*fk)[WinCap<T>::NW],
+                                         int m, T* Wx, int tid) {
+    constexpr int NW = WinCap<T>::NW;
+    const int lane = tid & 31, w = tid >> 5;
+    if (w >= 32) return;
+    if (m <= 32) window_w_rpl<T, 1>(Gs, n, P, idx, fk, m, Wx, lane, w);
+    else if (m <= 64) window_w_rpl<T, 2>(Gs, n, P, idx, fk, m, Wx, lane, w);
+    else if (NW > 64 && m <= 96) window_w_rpl<T, (NW > 64 ? 3 : 2)>(Gs, n, P, idx, fk, m, Wx, lane, w);
+    else window_w_rpl<T, NW / 32>(Gs, n, P, idx, fk, m, Wx, lane, w);
 }
 
 template <typename T, int MODE>
@@ -346,11 +368,14 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
         s_maxrT = T(0);
     }
     __shared__ double c_dflip[2][2], c_dstrip[2][2], c_sflip[2];
+    __shared__ T c_dflipT[2][2], c_sflipT[2];  // the same in T for the scan's critical path
     if (tid < 4) {
         c_dflip[tid >> 1][tid & 1] = sp.dflip[tid >> 1][tid & 1];
         c_dstrip[tid >> 1][tid & 1] = sp.dstrip[tid >> 1][tid & 1];
     }
     if (tid < 2) c_sflip[tid] = sp.sflip[tid];
+    if (tid < 4) c_dflipT[tid >> 1][tid & 1] = (T)sp.dflip[tid >> 1][tid & 1];
+    if (tid < 2) c_sflipT[tid] = (T)sp.sflip[tid];
     if (tid == 0) s_m = 0;
     __syncthreads();
 
@@ -378,9 +403,9 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                 int xi = 0;
                 if (q < n) {
                     xi = xw[q] > 0 ? 0 : 1;
-                    rr0 = T(1) + (T)c_dflip[0][xi] * (T(1) - Gs[(0 * n + q) * P + q]);
-                    rr1 = T(1) + (T)c_dflip[1][xi] * (T(1) - Gs[(1 * n + q) * P + q]);
-                    R = (T)c_sflip[xi] * rr0 * rr1;
+                    rr0 = T(1) + c_dflipT[0][xi] * (T(1) - Gs[(0 * n + q) * P + q]);
+                    rr1 = T(1) + c_dflipT[1][xi] * (T(1) - Gs[(1 * n + q) * P + q]);
+                    R = c_sflipT[xi] * rr0 * rr1;
                     acc = replay ? (s_rep[q] != 0) : (s_u[q] < fabs(R));
                     if (!isfinite(R)) {
                         acc = false;
@@ -394,7 +419,7 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                     s_rat[q] = R;
                 }
                 if (tid == first) {
-                    const T f0 = (T)c_dflip[0][xi] / rr0, f1 = (T)c_dflip[1][xi] / rr1;
+                    const T f0 = c_dflipT[0][xi] / rr0, f1 = c_dflipT[1][xi] / rr1;
                     s_fa[0] = f0;
                     s_fa[1] = f1;
                     s_fk[0][s_m] = -f0;  // recursion factor f = -Delta / r
