@@ -27,25 +27,33 @@ struct Lattice {
     double* Ex64 = nullptr;  // L x L: exp(-dtau K) = Ex (x) Ex for the periodic square lattice
 };
 
+// A group of walkers with the same lattice and particle numbers.  Every per-walker buffer holds
+// nwk back-to-back copies laid out [walker][spin][...], so the walker and spin indices of a
+// launch merge into one batch index with a uniform stride.
 struct Walker {
+    int nwk = 1;             // walkers in the group
+    std::vector<int> gid;    // their indices in the context (also their Philox key)
+    int* gid_d = nullptr;
     int L = 0, N = 0;
     long ld = 0;
     int ns[2] = {0, 0};
+    int nsm = 0;             // max(ns[0], ns[1])
+    int nst = 0;             // stack entries (M / stab_every + 1)
     int pos = 0, last_dir = -1;
     bool need_recompute = false;
     uint64_t visit = 0;
     Lattice* lat = nullptr;
-    void* G = nullptr;      // [2][N][ld] bulk
-    void* Tbuf = nullptr;   // [2][N][ld] bulk (wrap temporary)
-    int8_t* x = nullptr;    // M x N
-    double* u = nullptr;    // 2N uniforms
-    void* dvec = nullptr;   // bulk [2][N] d, then [2][N] dinv
-    double* d64 = nullptr;  // FP64 [2][N] d, [2][N] dinv
-    uint8_t* dec = nullptr;
-    double* ratio = nullptr;
-    int* stats = nullptr;   // 4 ints
-    double* maxr = nullptr;
-    double* sign = nullptr;
+    void* G = nullptr;       // [nwk][2][N][ld] bulk
+    void* Tbuf = nullptr;    // [nwk][2][N][ld] bulk (wrap temporary)
+    int8_t* x = nullptr;     // [nwk][M][N]
+    double* u = nullptr;     // [nwk][2N] uniforms
+    void* dvec = nullptr;    // bulk [nwk][2][N] d, then [nwk][2][N] dinv
+    double* d64 = nullptr;   // FP64 [2][N] d, [2][N] dinv (one walker at a time)
+    uint8_t* dec = nullptr;  // [nwk][2N]
+    double* ratio = nullptr; // [nwk][2N]
+    int* stats = nullptr;    // [nwk][8]
+    double* maxr = nullptr;  // [nwk]
+    double* sign = nullptr;  // [nwk]
     uint8_t* replay = nullptr;
     void* colbuf = nullptr;
     void* rowbuf = nullptr;
@@ -63,20 +71,26 @@ struct Walker {
     void* snap[2] = {nullptr, nullptr};
     cudaStream_t sf = nullptr;  // flush stream
     cudaEvent_t ev_chain[2] = {nullptr, nullptr}, ev_prod[2] = {nullptr, nullptr}, ev_done = nullptr;
-    double* URs[2] = {nullptr, nullptr};
-    double* ULs[2] = {nullptr, nullptr};
-    int nsm = 0;                 // max(ns[0], ns[1])
-    double* Ucur = nullptr;      // 2 x N x nsm: the factor being propagated, per spin
-    double* Utmp = nullptr;      // N x nsm: propagation scratch
-    double* Ut2 = nullptr;       // 2 x N x nsm: transposed left factors for the LU
-    double* Ob = nullptr;        // 2 x nsm x nsm: U_L U_R, then its LU
-    double* Z = nullptr;         // 2 x nsm x N: (U_L U_R)^{-1} U_L
-    double* Gnew = nullptr;      // N x ld: the recomputed G of one spin
-    int* perm2 = nullptr;        // 2 x max(N, nsm): pivot rows
-    int8_t* flag2 = nullptr;     // 2 x max(N, nsm): pivoted-row flags
-    int* visited = nullptr;      // max(N, nsm): permutation-parity scratch
-    double* acc2 = nullptr;
+    double* URs = nullptr;   // [nwk][2][nst][N x nsm]: right factors at every recompute point
+    double* ULs = nullptr;   // [nwk][2][nst][nsm x N]: left factors
+    double* Ucur = nullptr;  // [nwk][2][N x nsm]: the factors being propagated
+    double* Utmp = nullptr;  // N x nsm: propagation scratch (per-slice path)
+    double* Ut2 = nullptr;   // [nwk][2][N x nsm]: transposed left factors for the LU
+    double* Ob = nullptr;    // [nwk][2][nsm x nsm]: U_L U_R, then its LU
+    double* Z = nullptr;     // [nwk][2][nsm x N]: (U_L U_R)^{-1} U_L
+    double* Gnew = nullptr;  // [nwk][2][N][ld]: the recomputed G
+    int* perm2 = nullptr;    // [nwk][2][maxr]: pivot rows
+    int8_t* flag2 = nullptr; // [nwk][2][maxr]: pivoted-row flags
+    int* visited = nullptr;  // [nwk][maxr]: permutation-parity scratch
+    double* acc2 = nullptr;  // [nwk][2]
     std::vector<void*> allocs;
+    long gstride() const { return 2L * N * ld; }
+    int rows_max() const { return N > nsm ? N : nsm; }
+    long fsz() const { return (long)N * nsm; }                  // one factor
+    long st_s() const { return (long)nst * fsz(); }             // spin stride in a stack
+    long st_w() const { return 2 * st_s(); }                    // walker stride in a stack
+    double* stackR(int j) const { return URs + (size_t)j * fsz(); }
+    double* stackL(int j) const { return ULs + (size_t)j * fsz(); }
 };
 
 }  // namespace
@@ -101,7 +115,9 @@ struct afqmc_ctx {
     int sticky = 0;
     int nsm = 0;
     std::vector<Lattice*> lats;
-    std::vector<Walker*> w;
+    std::vector<Walker*> w;                        // walker groups
+    std::vector<std::pair<int, int>> wmap;         // context walker -> (group, member)
+    std::vector<size_t> roff;                      // context walker -> offset of its 2N replay bytes
     std::vector<void*> allocs;
     cudaStream_t last = nullptr;
 };
@@ -133,7 +149,10 @@ static size_t esize(const afqmc_ctx* ctx) { return ctx->p.precision == AFQMC_PRE
 // ---------------------------------------------------------------------------
 // small kernels local to the ABI layer
 // ---------------------------------------------------------------------------
-__global__ void transpose_kernel(const double* A, int rows, int cols, double* B) {  // B = A^T
+// B[b] = A[b]^T (A[b]: rows x cols) for the batch b = blockIdx.y, A[b] at A + b sa, B[b] at B + b sb
+__global__ void transpose_kernel(const double* A, int rows, int cols, double* B, long sa, long sb) {
+    A += blockIdx.y * sa;
+    B += blockIdx.y * sb;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)rows * cols; e += (long)gridDim.x * blockDim.x) {
         int r = (int)(e / cols), c = (int)(e % cols);
         B[(long)c * rows + r] = A[e];
@@ -145,7 +164,10 @@ __global__ void fields_kernel(uint64_t seed, uint64_t walker, long count, int8_t
     if (j < count) x[j] = philox_uniform(seed, walker, ~0ULL, (uint64_t)j) < 0.5 ? 1 : -1;
 }
 
-__global__ void set_double_kernel(double* p, double v) { *p = v; }
+__global__ void set_double_kernel(double* p, double v, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
 
 __global__ void debug_uniforms_kernel(uint64_t seed, uint64_t walker, uint64_t visit, int count, double* out) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -232,17 +254,20 @@ static Lattice* get_lattice(afqmc_ctx* ctx, int L, cudaStream_t st, cudaError_t*
     return l;
 }
 
-static cudaError_t prop_right(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, int ell, double* U, double* tmp);
-static cudaError_t prop_left(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, int ell, double* U, double* tmp);
-// Propagate both spins' factors U[s] over nsl slices l = l_first, l_first + l_step, ...
-// (right factors N x ns: B_l U; left factors ns x N: U B_l) with the fused kernel; lattices too
-// large for it take the per-slice separable products.
-static cudaError_t propagate(afqmc_ctx* ctx, Walker* w, cudaStream_t st, double* const* U, int left, int l_first,
-                             int l_step, int nsl) {
+static cudaError_t prop_right(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int j, int s, int ell, double* U,
+                              double* tmp);
+static cudaError_t prop_left(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int j, int s, int ell, double* U, double* tmp);
+
+// Propagate the group's factors in Ucur ([walker][spin][N x nsm]) over nsl slices
+// l = l_first, l_first + l_step, ... (right factors N x ns: B_l U; left factors ns x N: U B_l)
+// with the fused kernel; lattices too large for it take the per-slice separable products.
+static cudaError_t propagate(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int left, int l_first, int l_step, int nsl) {
     const int N = w->N;
     PropArgs a;
+    a.U0 = w->Ucur;
+    a.sstride = w->fsz();
+    a.wstride = 2 * w->fsz();
     for (int s = 0; s < 2; ++s) {
-        a.U[s] = U[s];
         a.nvec[s] = w->ns[s];
         a.vs[s] = left ? N : 1;
         a.es[s] = left ? 1 : w->ns[s];
@@ -251,21 +276,24 @@ static cudaError_t propagate(afqmc_ctx* ctx, Walker* w, cudaStream_t st, double*
     }
     a.Ex = w->lat->Ex64;
     a.x = w->x;
+    a.xstride = (long)ctx->p.M * N;
     a.L = w->L;
     a.l_first = l_first;
     a.l_step = l_step;
     a.nsl = nsl;
     a.left = left;
-    a.nmat = 2;
+    a.nmat = 2 * w->nwk;
     cudaError_t e = launch_prop(st, a);
     if (e != cudaErrorInvalidValue) return e;
     cudaGetLastError();
     for (int t = 0; t < nsl; ++t)
-        for (int s = 0; s < 2; ++s) {
-            const int ell = l_first + t * l_step;
-            e = left ? prop_left(ctx, w, st, s, ell, U[s], w->Utmp) : prop_right(ctx, w, st, s, ell, U[s], w->Utmp);
-            if (e != cudaSuccess) return e;
-        }
+        for (int j = 0; j < w->nwk; ++j)
+            for (int s = 0; s < 2; ++s) {
+                const int ell = l_first + t * l_step;
+                double* U = w->Ucur + ((size_t)j * 2 + s) * w->fsz();
+                e = left ? prop_left(ctx, w, st, j, s, ell, U, w->Utmp) : prop_right(ctx, w, st, j, s, ell, U, w->Utmp);
+                if (e != cudaSuccess) return e;
+            }
     return cudaSuccess;
 }
 
@@ -285,29 +313,42 @@ static int spin_groups(const Walker* w, int grp[2][2], int ng[2]) {
     return 2;
 }
 
-static LuArgs lu_args(Walker* w, double* const* A, int nmat, long lda, int m, int n) {
-    const int maxr = w->N > w->nsm ? w->N : w->nsm;
+// A factor set of the group: matrix (walker j, spin s0 + q) at base + j wstride + (s0 + q) sstride
+// for q < ng; layouts here always have wstride = 2 sstride, so the batch stride is uniform.
+struct Fac {
+    double* base;
+    long wstride, sstride;
+    double* at(int s0) const { return base + (size_t)s0 * sstride; }
+    long bstride(int ng) const { return ng == 2 ? sstride : wstride; }
+};
+static Fac fac_cur(Walker* w) { return {w->Ucur, 2 * w->fsz(), w->fsz()}; }
+static Fac fac_R(Walker* w, int j) { return {w->stackR(j), w->st_w(), w->st_s()}; }
+static Fac fac_L(Walker* w, int j) { return {w->stackL(j), w->st_w(), w->st_s()}; }
+
+static LuArgs lu_args(Walker* w, const Fac& f, int s0, int ng, long lda, int m, int n) {
     LuArgs a;
-    for (int q = 0; q < nmat; ++q) {
-        a.A[q] = A[q];
-        a.perm[q] = w->perm2 + (size_t)q * maxr;
-        a.flag[q] = w->flag2 + (size_t)q * maxr;
-    }
+    a.A0 = f.at(s0);
+    a.wstride = f.wstride;
+    a.sstride = f.sstride;
+    a.ng = ng;
+    a.perm0 = w->perm2;
+    a.flag0 = w->flag2;
+    a.pstride = w->rows_max();
     a.lda = lda;
     a.m = m;
     a.n = n;
-    a.nmat = nmat;
+    a.nmat = w->nwk * ng;
     a.err = w->err;
     return a;
 }
 
-// Re-orthonormalisation (Sec. II.C): every U[q] (N x ns, row-major) becomes P L from its
-// partially pivoted LU, a basis of the same column space with entries of magnitude <= 1 (only
-// the column space enters G, Eq. GrFMatNew).  *sign (nullable) is multiplied by the sign of the
-// discarded triangular factor.
-static cudaError_t stab_rows(afqmc_ctx* ctx, Walker* w, cudaStream_t st, double* const* U, int nmat, int ns,
-                             double* sign) {
-    LuArgs a = lu_args(w, U, nmat, ns, w->N, ns);
+// Re-orthonormalisation (Sec. II.C): every right factor U (N x ns, row-major) of the spin group
+// becomes P L from its partially pivoted LU, a basis of the same column space with entries of
+// magnitude <= 1 (only the column space enters G, Eq. GrFMatNew).  sign[j] (nullable) is
+// multiplied by the sign of the discarded triangular factor of walker j.
+static cudaError_t stab_rows(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac& f, int s0, int ng, double* sign) {
+    const int ns = w->ns[s0];
+    LuArgs a = lu_args(w, f, s0, ng, ns, w->N, ns);
     cudaError_t e;
     {
         PhaseScope ps(ctx, AFQMC_PHASE_ELIM, st);
@@ -317,56 +358,53 @@ static cudaError_t stab_rows(afqmc_ctx* ctx, Walker* w, cudaStream_t st, double*
     return launch_lu_unit_rows(st, a);
 }
 
-// The same for left factors U[q] (ns x N): through their transposes.
-static cudaError_t stab_cols(afqmc_ctx* ctx, Walker* w, cudaStream_t st, double* const* U, int nmat, int ns,
-                             double* sign) {
-    const int N = w->N;
-    double* T[2] = {w->Ut2, w->Ut2 + (size_t)N * w->nsm};
+// The same for left factors (ns x N): through their transposes.
+static cudaError_t stab_cols(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac& f, int s0, int ng, double* sign) {
+    const int N = w->N, ns = w->ns[s0], nmat = w->nwk * ng;
+    const long bs = f.bstride(ng);
     cudaError_t e;
-    for (int q = 0; q < nmat; ++q) {
-        count_launch();
-        transpose_kernel<<<256, 256, 0, st>>>(U[q], ns, N, T[q]);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    if ((e = stab_rows(ctx, w, st, T, nmat, ns, sign)) != cudaSuccess) return e;
-    for (int q = 0; q < nmat; ++q) {
-        count_launch();
-        transpose_kernel<<<256, 256, 0, st>>>(T[q], N, ns, U[q]);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    count_launch();
+    transpose_kernel<<<dim3(256, nmat), 256, 0, st>>>(f.at(s0), ns, N, w->Ut2, bs, w->fsz());
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const Fac t{w->Ut2, ng * w->fsz(), w->fsz()};
+    if ((e = stab_rows(ctx, w, st, t, 0, ng, sign)) != cudaSuccess) return e;
+    count_launch();
+    transpose_kernel<<<dim3(256, nmat), 256, 0, st>>>(w->Ut2, N, ns, f.at(s0), w->fsz(), bs);
+    return cudaGetLastError();
 }
 
-// Z[q] = (UL[q] UR[q])^{-1} UL[q] (ns x N) for the spins of a group (Eq. GrFMatNew):
-// O = UL UR (FP64), its pivoted LU, then the substitutions with UL as right-hand side.
-// *sign (nullable) is multiplied by sign(det O) of every spin.
-static cudaError_t form_Z(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const double* const* UR, const double* const* UL,
-                          int nmat, int ns, double* sign) {
-    const int N = w->N;
-    double* O[2] = {w->Ob, w->Ob + (size_t)w->nsm * w->nsm};
-    double* Z[2] = {w->Z, w->Z + (size_t)w->nsm * N};
+// Z[b] = (U_L U_R)^{-1} U_L (ns x N) for every (walker, spin) of a spin group (Eq. GrFMatNew):
+// O = U_L U_R (FP64), its pivoted LU, then the substitutions with U_L as right-hand side.
+// sign[j] (nullable) is multiplied by sign(det O) of walker j's spins.
+static cudaError_t form_Z(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac& R, const Fac& Lf, int s0, int ng,
+                          double* sign) {
+    const int N = w->N, ns = w->ns[s0], nmat = w->nwk * ng;
+    const long os = (long)w->nsm * w->nsm, zs = (long)w->nsm * N;
     cudaError_t e;
-    for (int q = 0; q < nmat; ++q) {
-        GemmArgs<double> g;
-        g.M = ns; g.N = ns; g.K = N;
-        g.A = UL[q]; g.lda = N;
-        g.B = UR[q]; g.ldb = ns;
-        g.C = O[q]; g.ldc = ns;
-        if ((e = gemm<double>(st, g)) != cudaSuccess) return e;
-    }
-    LuArgs a = lu_args(w, O, nmat, ns, ns, ns);
+    GemmArgs<double> g;
+    g.M = ns; g.N = ns; g.K = N; g.batch = nmat;
+    g.A = Lf.at(s0); g.lda = N; g.sA = Lf.bstride(ng);
+    g.B = R.at(s0); g.ldb = ns; g.sB = R.bstride(ng);
+    g.C = w->Ob; g.ldc = ns; g.sC = os;
+    if ((e = gemm<double>(st, g)) != cudaSuccess) return e;
+    const Fac O{w->Ob, ng * os, os};
+    LuArgs a = lu_args(w, O, 0, ng, ns, ns, ns);
     {
         PhaseScope ps(ctx, AFQMC_PHASE_LU_O, st);
         if ((e = launch_lu(st, a)) != cudaSuccess) return e;
     }
     if (sign && (e = launch_lu_sign(st, a, 1, sign, w->visited)) != cudaSuccess) return e;
     SolveArgs sa;
-    for (int q = 0; q < nmat; ++q) {
-        sa.LU[q] = O[q];
-        sa.perm[q] = a.perm[q];
-        sa.B[q] = UL[q];
-        sa.Z[q] = Z[q];
-    }
+    sa.LU0 = w->Ob;
+    sa.ostride = os;
+    sa.perm0 = w->perm2;
+    sa.pstride = w->rows_max();
+    sa.B0 = Lf.at(s0);
+    sa.wstride = Lf.wstride;
+    sa.sstride = Lf.sstride;
+    sa.ng = ng;
+    sa.Z0 = w->Z;
+    sa.zstride = zs;
     sa.ldl = ns;
     sa.ns = ns;
     sa.N = N;
@@ -375,26 +413,36 @@ static cudaError_t form_Z(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const doub
     return launch_lu_solve(st, sa);
 }
 
-// G_new (FP64, N x ld) = 1 - UR Z for the spin whose Z sits at slot q of form_Z.  The N x N
-// product stays in FP64 for both bulk precisions: the LU bases are not orthonormal, so 1 - UR Z
-// cancels large terms and an FP32 product would lose the digits the recompute restores.
-static cudaError_t finish_G(Walker* w, cudaStream_t st, const double* UR, int q, int ns) {
-    const int N = w->N;
+// Gnew[b] (FP64, N x ld) = 1 - U_R Z[b] for the spin group of form_Z; then the drift against the
+// bulk G (acc2 per walker, nullable) and the store into the bulk G.  The N x N product stays in
+// FP64 for both bulk precisions: the LU bases are not orthonormal, so 1 - U_R Z cancels large
+// terms and an FP32 product would lose the digits the recompute restores.
+template <typename T>
+static cudaError_t finish_G(Walker* w, cudaStream_t st, const Fac& R, int s0, int ng, bool drift) {
+    const int N = w->N, ns = w->ns[s0], nmat = w->nwk * ng;
+    const long gs = (long)N * w->ld;
+    cudaError_t e;
     GemmArgs<double> h;
-    h.M = N; h.N = N; h.K = ns;
-    h.A = UR; h.lda = ns;
-    h.B = w->Z + (size_t)q * w->nsm * N; h.ldb = N;
-    h.C = w->Gnew; h.ldc = w->ld;
-    cudaError_t e = gemm<double>(st, h);
-    if (e != cudaSuccess) return e;
-    return launch_identity_minus<double>(st, w->Gnew, w->ld, N);
+    h.M = N; h.N = N; h.K = ns; h.batch = nmat;
+    h.A = R.at(s0); h.lda = ns; h.sA = R.bstride(ng);
+    h.B = w->Z; h.ldb = N; h.sB = (long)w->nsm * N;
+    h.C = w->Gnew; h.ldc = w->ld; h.sC = gs;
+    if ((e = gemm<double>(st, h)) != cudaSuccess) return e;
+    if ((e = launch_identity_minus<double>(st, w->Gnew, w->ld, N, nmat, gs)) != cudaSuccess) return e;
+    T* Gb = (T*)w->G + (size_t)s0 * gs;                 // bulk G of (walker 0, spin s0)
+    const long bs = (ng == 2) ? gs : 2 * gs;            // batch stride in the bulk G
+    if (drift && (e = launch_drift<T>(st, Gb, (const T*)w->Gnew, w->ld, N, w->acc2, nmat, bs, gs, ng)) != cudaSuccess)
+        return e;
+    return launch_cast<T>(st, w->Gnew, w->ld, Gb, w->ld, N, N, nmat, gs, bs);
 }
 
-// U (N x ns) <- B_l U, B_l = diag(exp(c_s x_l)) E.  E = Ex (x) Ex on the square lattice, so
-// E U is two small products: along x for every row block y, then along y.
-static cudaError_t prop_right(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, int ell, double* U, double* tmp) {
+// U (N x ns) <- B_l U for walker j, spin s, B_l = diag(exp(c_s x_l)) E.  E = Ex (x) Ex on the
+// square lattice, so E U is two small products: along x for every row block y, then along y.
+static cudaError_t prop_right(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int j, int s, int ell, double* U,
+                              double* tmp) {
     const int N = w->N, ns = w->ns[s], L = w->L;
-    cudaError_t e = launch_field_scales_T<double>(st, w->x + (size_t)(ell - 1) * N, N, ctx->c, w->d64, w->d64 + 2 * N, N);
+    const int8_t* xl = w->x + (size_t)j * ctx->p.M * N + (size_t)(ell - 1) * N;
+    cudaError_t e = launch_field_scales_T<double>(st, xl, N, ctx->c, w->d64, w->d64 + 2 * N, N);
     if (e != cudaSuccess) return e;
     GemmArgs<double> gx;  // tmp[(x,y), c] = sum_x' Ex[x, x'] U[(x',y), c]
     gx.M = L; gx.N = ns; gx.K = L; gx.batch = L;
@@ -411,10 +459,11 @@ static cudaError_t prop_right(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s,
     return launch_scale_rows(st, U, N, ns, w->d64 + (size_t)s * N);
 }
 
-// U (ns x N) <- U B_l = (U diag(exp(c_s x_l))) E, with the same separable product.
-static cudaError_t prop_left(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, int ell, double* U, double* tmp) {
+// U (ns x N) <- U B_l = (U diag(exp(c_s x_l))) E for walker j, spin s, with the same products.
+static cudaError_t prop_left(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int j, int s, int ell, double* U, double* tmp) {
     const int N = w->N, ns = w->ns[s], L = w->L;
-    cudaError_t e = launch_field_scales_T<double>(st, w->x + (size_t)(ell - 1) * N, N, ctx->c, w->d64, w->d64 + 2 * N, N);
+    const int8_t* xl = w->x + (size_t)j * ctx->p.M * N + (size_t)(ell - 1) * N;
+    cudaError_t e = launch_field_scales_T<double>(st, xl, N, ctx->c, w->d64, w->d64 + 2 * N, N);
     if (e != cudaSuccess) return e;
     if ((e = launch_scale_cols(st, U, ns, N, w->d64 + (size_t)s * N)) != cudaSuccess) return e;
     GemmArgs<double> gx;  // tmp[(a,y), x] = sum_x' U[a, (x',y)] Ex[x', x]
@@ -431,10 +480,16 @@ static cudaError_t prop_left(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int s, 
     return gemm<double>(st, gy);
 }
 
-template <typename T>
-static cudaError_t store_G(Walker* w, cudaStream_t st, int s) {
-    T* G = (T*)w->G + (size_t)s * w->N * w->ld;
-    return launch_cast<T>(st, w->Gnew, w->ld, G, w->ld, w->N, w->N);
+// Copy the group's Ucur into stack entry j of URs (right) or ULs (left): one strided copy.
+static cudaError_t to_stack(Walker* w, cudaStream_t st, bool right, int j) {
+    double* dst = right ? w->stackR(j) : w->stackL(j);
+    return cudaMemcpy2DAsync(dst, w->st_s() * 8, w->Ucur, w->fsz() * 8, w->fsz() * 8, 2 * (size_t)w->nwk,
+                             cudaMemcpyDeviceToDevice, st);
+}
+static cudaError_t from_stack(Walker* w, cudaStream_t st, bool right, int j) {
+    const double* src = right ? w->stackR(j) : w->stackL(j);
+    return cudaMemcpy2DAsync(w->Ucur, w->fsz() * 8, src, w->st_s() * 8, w->fsz() * 8, 2 * (size_t)w->nwk,
+                             cudaMemcpyDeviceToDevice, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -525,53 +580,87 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
     ctx->last = st;
     const int M = ctx->p.M, S = ctx->p.stab_every, nst = M / S + 1;
     const size_t es = esize(ctx);
-    size_t poff = 0, foff = 0;
     for (int wi = 0; wi < n_walkers; ++wi) {
         if (L[wi] < 2 || L[wi] > 64) return AFQMC_ERR_ARG;
         int N = L[wi] * L[wi];
         if (n_up[wi] < 1 || n_up[wi] > N || n_dn[wi] < 1 || n_dn[wi] > N) return AFQMC_ERR_ARG;
     }
+    // host offsets of every walker's trial state and fields in the caller's arrays
+    std::vector<size_t> poff(n_walkers), foff(n_walkers);
+    {
+        size_t po = 0, fo = 0;
+        for (int wi = 0; wi < n_walkers; ++wi) {
+            const size_t N = (size_t)L[wi] * L[wi];
+            poff[wi] = po;
+            foff[wi] = fo;
+            po += N * (n_up[wi] + n_dn[wi]);
+            fo += (size_t)M * N;
+        }
+    }
+    ctx->roff.assign(n_walkers, 0);
+    for (int wi = 1; wi < n_walkers; ++wi) ctx->roff[wi] = ctx->roff[wi - 1] + 2 * (size_t)L[wi - 1] * L[wi - 1];
+    // groups: walkers with the same (L, n_up, n_dn), in order of first appearance
+    ctx->wmap.assign(n_walkers, {-1, -1});
     for (int wi = 0; wi < n_walkers; ++wi) {
-        Walker* w = new Walker();
-        ctx->w.push_back(w);
+        int g = -1;
+        for (int q = 0; q < (int)ctx->w.size(); ++q) {
+            Walker* w = ctx->w[q];
+            if (w->L == L[wi] && w->ns[0] == n_up[wi] && w->ns[1] == n_dn[wi]) g = q;
+        }
+        if (g < 0) {
+            Walker* w = new Walker();
+            w->L = L[wi];
+            w->ns[0] = n_up[wi];
+            w->ns[1] = n_dn[wi];
+            w->nwk = 0;
+            ctx->w.push_back(w);
+            g = (int)ctx->w.size() - 1;
+        }
+        Walker* w = ctx->w[g];
+        ctx->wmap[wi] = {g, w->nwk};
+        w->gid.push_back(wi);
+        w->nwk++;
+    }
+    for (auto* w : ctx->w) {
         cudaError_t e;
-        w->lat = get_lattice(ctx, L[wi], st, &e);
+        w->lat = get_lattice(ctx, w->L, st, &e);
         if (!w->lat) return fail(ctx, e);
-        w->L = L[wi];
         w->N = w->lat->N;
         w->ld = w->lat->ld;
-        w->ns[0] = n_up[wi];
-        w->ns[1] = n_dn[wi];
-        const int N = w->N;
+        w->nsm = w->ns[0] > w->ns[1] ? w->ns[0] : w->ns[1];
+        w->nst = nst;
+        const int N = w->N, nsm = w->nsm, nwk = w->nwk;
         const long ld = w->ld;
-        const int nsm = w->ns[0] > w->ns[1] ? w->ns[0] : w->ns[1];
         const int NW = (ctx->p.precision == AFQMC_PREC_FP64) ? window_max<double>() : window_max<float>();
+        const size_t maxr = (size_t)w->rows_max();
         auto& A = w->allocs;
-        CK(dalloc(A, (char**)&w->G, 2 * (size_t)N * ld * es));
-        CK(dalloc(A, (char**)&w->Tbuf, 2 * (size_t)N * ld * es));
-        CK(dalloc(A, &w->x, (size_t)M * N));
-        CK(dalloc(A, &w->u, 2 * (size_t)N * 8));
-        CK(dalloc(A, (char**)&w->dvec, 4 * (size_t)N * es));
+        CK(dalloc(A, &w->gid_d, (size_t)nwk * sizeof(int)));
+        CK(cudaMemcpyAsync(w->gid_d, w->gid.data(), (size_t)nwk * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(dalloc(A, (char**)&w->G, (size_t)nwk * 2 * N * ld * es));
+        CK(dalloc(A, (char**)&w->Tbuf, (size_t)nwk * 2 * N * ld * es));
+        CK(dalloc(A, &w->x, (size_t)nwk * M * N));
+        CK(dalloc(A, &w->u, (size_t)nwk * 2 * N * 8));
+        CK(dalloc(A, (char**)&w->dvec, (size_t)nwk * 4 * N * es));
         CK(dalloc(A, &w->d64, 4 * (size_t)N * 8));
-        CK(dalloc(A, &w->dec, 2 * (size_t)N));
-        CK(dalloc(A, &w->ratio, 2 * (size_t)N * 8));
-        CK(dalloc(A, &w->stats, 8 * sizeof(int)));
-        CK(dalloc(A, &w->maxr, 8));
-        CK(dalloc(A, &w->sign, 8));
-        CK(dalloc(A, &w->replay, 2 * (size_t)N));
-        CK(dalloc(A, (char**)&w->colbuf, 4 * (size_t)N * es));
+        CK(dalloc(A, &w->dec, (size_t)nwk * 2 * N));
+        CK(dalloc(A, &w->ratio, (size_t)nwk * 2 * N * 8));
+        CK(dalloc(A, &w->stats, (size_t)nwk * 8 * sizeof(int)));
+        CK(dalloc(A, &w->maxr, (size_t)nwk * 8));
+        CK(dalloc(A, &w->sign, (size_t)nwk * 8));
+        CK(dalloc(A, &w->replay, (size_t)nwk * 2 * N));
+        CK(dalloc(A, (char**)&w->colbuf, 4 * (size_t)N * es));  // [2 buffers][2 spins][N]
         CK(dalloc(A, (char**)&w->rowbuf, 4 * (size_t)N * es));
         CK(dalloc(A, &w->bar, sizeof(GridBar)));
         CK(dalloc(A, &w->err, sizeof(int)));
         for (int q = 0; q < 2; ++q) {
-            CK(dalloc(A, &w->wm[q], 2 * sizeof(int)));
-            CK(dalloc(A, &w->widx[q], (size_t)NW * sizeof(int)));
-            CK(dalloc(A, &w->wdtot[q], 2 * (size_t)NW * 8));
-            CK(dalloc(A, (char**)&w->Wm[q], 2 * (size_t)NW * NW * es));
-            CK(dalloc(A, (char**)&w->Wx[q], 2 * (size_t)NW * NW * es));
-            CK(dalloc(A, (char**)&w->X[q], 2 * (size_t)N * NW * es));
-            CK(dalloc(A, (char**)&w->Y[q], 4 * (size_t)NW * N * es));
-            CK(dalloc(A, (char**)&w->snap[q], 2 * (size_t)NW * NW * es));
+            CK(dalloc(A, &w->wm[q], (size_t)nwk * sizeof(int)));
+            CK(dalloc(A, &w->widx[q], (size_t)nwk * NW * sizeof(int)));
+            CK(dalloc(A, &w->wdtot[q], (size_t)nwk * 2 * NW * 8));
+            CK(dalloc(A, (char**)&w->Wm[q], (size_t)nwk * 2 * NW * NW * es));
+            CK(dalloc(A, (char**)&w->Wx[q], (size_t)nwk * 2 * NW * NW * es));
+            CK(dalloc(A, (char**)&w->X[q], (size_t)nwk * 2 * N * NW * es));
+            CK(dalloc(A, (char**)&w->Y[q], (size_t)nwk * 4 * NW * N * es));
+            CK(dalloc(A, (char**)&w->snap[q], (size_t)nwk * 2 * NW * NW * es));
             CK(cudaEventCreateWithFlags(&w->ev_chain[q], cudaEventDisableTiming));
             CK(cudaEventCreateWithFlags(&w->ev_prod[q], cudaEventDisableTiming));
         }
@@ -581,89 +670,75 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
             CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
             CK(cudaStreamCreateWithPriority(&w->sf, cudaStreamNonBlocking, lo));
         }
-        for (int s = 0; s < 2; ++s) {
-            CK(dalloc(A, &w->URs[s], (size_t)nst * N * w->ns[s] * 8));
-            CK(dalloc(A, &w->ULs[s], (size_t)nst * N * w->ns[s] * 8));
-        }
-        const int maxr = N > nsm ? N : nsm;
-        w->nsm = nsm;
-        CK(dalloc(A, &w->Ucur, 2 * (size_t)N * nsm * 8));
+        CK(dalloc(A, &w->URs, (size_t)nwk * 2 * nst * N * nsm * 8));
+        CK(dalloc(A, &w->ULs, (size_t)nwk * 2 * nst * N * nsm * 8));
+        CK(dalloc(A, &w->Ucur, (size_t)nwk * 2 * N * nsm * 8));
         CK(dalloc(A, &w->Utmp, (size_t)N * nsm * 8));
-        CK(dalloc(A, &w->Ut2, 2 * (size_t)N * nsm * 8));
-        CK(dalloc(A, &w->Ob, 2 * (size_t)nsm * nsm * 8));
-        CK(dalloc(A, &w->Z, 2 * (size_t)nsm * N * 8));
-        CK(dalloc(A, &w->Gnew, (size_t)N * ld * 8));
-        CK(dalloc(A, (char**)&w->perm2, 2 * (size_t)maxr * sizeof(int)));
-        CK(dalloc(A, (char**)&w->flag2, 2 * (size_t)maxr));
-        CK(dalloc(A, (char**)&w->visited, (size_t)maxr * sizeof(int)));
-        CK(dalloc(A, &w->acc2, 2 * 8));
+        CK(dalloc(A, &w->Ut2, (size_t)nwk * 2 * N * nsm * 8));
+        CK(dalloc(A, &w->Ob, (size_t)nwk * 2 * nsm * nsm * 8));
+        CK(dalloc(A, &w->Z, (size_t)nwk * 2 * nsm * N * 8));
+        CK(dalloc(A, &w->Gnew, (size_t)nwk * 2 * N * ld * 8));
+        CK(dalloc(A, (char**)&w->perm2, (size_t)nwk * 2 * maxr * sizeof(int)));
+        CK(dalloc(A, (char**)&w->flag2, (size_t)nwk * 2 * maxr));
+        CK(dalloc(A, (char**)&w->visited, (size_t)nwk * maxr * sizeof(int)));
+        CK(dalloc(A, &w->acc2, (size_t)nwk * 2 * 8));
         CK(cudaMemsetAsync(w->err, 0, sizeof(int), st));
+        CK(cudaMemsetAsync(w->G, 0, (size_t)nwk * 2 * N * ld * es, st));
+        CK(cudaMemsetAsync(w->Tbuf, 0, (size_t)nwk * 2 * N * ld * es, st));
+        CK(cudaMemsetAsync(w->Gnew, 0, (size_t)nwk * 2 * N * ld * 8, st));
         for (int q = 0; q < 2; ++q) {
-            CK(cudaMemsetAsync(w->Wm[q], 0, 2 * (size_t)NW * NW * es, st));
-            CK(cudaMemsetAsync(w->X[q], 0, 2 * (size_t)N * NW * es, st));
-            CK(cudaMemsetAsync(w->Y[q], 0, 4 * (size_t)NW * N * es, st));
+            CK(cudaMemsetAsync(w->Wm[q], 0, (size_t)nwk * 2 * NW * NW * es, st));
+            CK(cudaMemsetAsync(w->Wx[q], 0, (size_t)nwk * 2 * NW * NW * es, st));
+            CK(cudaMemsetAsync(w->X[q], 0, (size_t)nwk * 2 * N * NW * es, st));
+            CK(cudaMemsetAsync(w->Y[q], 0, (size_t)nwk * 4 * NW * N * es, st));
         }
-        CK(cudaMemsetAsync(w->G, 0, 2 * (size_t)N * ld * es, st));
-        CK(cudaMemsetAsync(w->Tbuf, 0, 2 * (size_t)N * ld * es, st));
-        // fields
-        if (fields) {
-            CK(cudaMemcpyAsync(w->x, fields + foff, (size_t)M * N, cudaMemcpyHostToDevice, st));
-            foff += (size_t)M * N;
-        } else {
-            count_launch();
-            fields_kernel<<<(int)(((long)M * N + 255) / 256), 256, 0, st>>>(ctx->p.seed, (uint64_t)wi, (long)M * N, w->x);
-            CK(cudaGetLastError());
+        // fields: the caller's, else Philox-drawn +-1 per walker
+        for (int j = 0; j < nwk; ++j) {
+            const int wi = w->gid[j];
+            int8_t* xw = w->x + (size_t)j * M * N;
+            if (fields) {
+                CK(cudaMemcpyAsync(xw, fields + foff[wi], (size_t)M * N, cudaMemcpyHostToDevice, st));
+            } else {
+                count_launch();
+                fields_kernel<<<(int)(((long)M * N + 255) / 256), 256, 0, st>>>(ctx->p.seed, (uint64_t)wi, (long)M * N, xw);
+                CK(cudaGetLastError());
+            }
         }
         count_launch();
-        set_double_kernel<<<1, 1, 0, st>>>(w->sign, 1.0);
+        set_double_kernel<<<(nwk + 255) / 256, 256, 0, st>>>(w->sign, 1.0, nwk);
         CK(cudaGetLastError());
-        // trial determinants -> stacks, G(0)  (Sec. II.B)
-        double* ULc[2] = {w->Ucur, w->Ucur + (size_t)N * w->nsm};
+        // trial determinants -> stacks, G(0)  (Sec. II.B): P into URs entry 0 (N x ns), its
+        // transpose starts the left stack, U_L(M) = P^T
+        for (int j = 0; j < nwk; ++j)
+            for (int s = 0; s < 2; ++s) {
+                const double* Ph = P + poff[w->gid[j]] + (s ? (size_t)N * w->ns[0] : 0);
+                CK(cudaMemcpyAsync(w->URs + ((size_t)j * 2 + s) * w->st_s(), Ph, (size_t)N * w->ns[s] * 8,
+                                   cudaMemcpyHostToDevice, st));
+            }
         for (int s = 0; s < 2; ++s) {
-            const int ns = w->ns[s];
-            const double* Ph = P + poff;
-            poff += (size_t)N * ns;
-            // P into URs[s][0] (N x ns); its transpose starts the left stack, U_L(M) = P^T
-            CK(cudaMemcpyAsync(w->URs[s], Ph, (size_t)N * ns * 8, cudaMemcpyHostToDevice, st));
             count_launch();
-            transpose_kernel<<<256, 256, 0, st>>>(w->URs[s], N, ns, ULc[s]);
+            transpose_kernel<<<dim3(256, nwk), 256, 0, st>>>(w->URs + (size_t)s * w->st_s(), N, w->ns[s],
+                                                            w->Ucur + (size_t)s * w->fsz(), w->st_w(), 2 * w->fsz());
             CK(cudaGetLastError());
         }
         int grp[2][2], ng[2];
         const int ngr = spin_groups(w, grp, ng);
         for (int gi = 0; gi < ngr; ++gi) {
-            double* R[2] = {w->URs[grp[gi][0]], ng[gi] > 1 ? w->URs[grp[gi][1]] : nullptr};
-            double* Lc[2] = {ULc[grp[gi][0]], ng[gi] > 1 ? ULc[grp[gi][1]] : nullptr};
-            CK(stab_rows(ctx, w, st, R, ng[gi], w->ns[grp[gi][0]], w->sign));
-            CK(stab_cols(ctx, w, st, Lc, ng[gi], w->ns[grp[gi][0]], w->sign));
+            CK(stab_rows(ctx, w, st, fac_R(w, 0), grp[gi][0], ng[gi], w->sign));
+            CK(stab_cols(ctx, w, st, fac_cur(w), grp[gi][0], ng[gi], w->sign));
         }
-        for (int s = 0; s < 2; ++s)
-            CK(cudaMemcpyAsync(w->ULs[s] + (size_t)(M / S) * N * w->ns[s], ULc[s], (size_t)N * w->ns[s] * 8,
-                               cudaMemcpyDeviceToDevice, st));
+        CK(to_stack(w, st, false, M / S));
         // U_L(l - 1) = U_L(l) B_l, re-orthonormalised and stored at every recompute point
-        for (int ell = M; ell >= 1; --ell) {
-            if (ell % S == 0) CK(propagate(ctx, w, st, ULc, 1, ell, -1, S));  // slices ell .. ell - S + 1
-            if ((ell - 1) % S == 0) {
-                for (int gi = 0; gi < ngr; ++gi) {
-                    double* Lc[2] = {ULc[grp[gi][0]], ng[gi] > 1 ? ULc[grp[gi][1]] : nullptr};
-                    CK(stab_cols(ctx, w, st, Lc, ng[gi], w->ns[grp[gi][0]], w->sign));
-                }
-                for (int s = 0; s < 2; ++s)
-                    CK(cudaMemcpyAsync(w->ULs[s] + (size_t)((ell - 1) / S) * N * w->ns[s], ULc[s],
-                                       (size_t)N * w->ns[s] * 8, cudaMemcpyDeviceToDevice, st));
-            }
+        for (int jj = M / S; jj >= 1; --jj) {
+            CK(propagate(ctx, w, st, 1, jj * S, -1, S));  // slices jj S .. (jj - 1) S + 1
+            for (int gi = 0; gi < ngr; ++gi) CK(stab_cols(ctx, w, st, fac_cur(w), grp[gi][0], ng[gi], w->sign));
+            CK(to_stack(w, st, false, jj - 1));
         }
         // G(0) = 1 - U_R (U_L U_R)^{-1} U_L
         for (int gi = 0; gi < ngr; ++gi) {
-            const double* R[2] = {w->URs[grp[gi][0]], ng[gi] > 1 ? w->URs[grp[gi][1]] : nullptr};
-            const double* Lf[2] = {w->ULs[grp[gi][0]], ng[gi] > 1 ? w->ULs[grp[gi][1]] : nullptr};
-            CK(form_Z(ctx, w, st, R, Lf, ng[gi], w->ns[grp[gi][0]], w->sign));
-            for (int q = 0; q < ng[gi]; ++q) {
-                const int s = grp[gi][q];
-                CK(finish_G(w, st, w->URs[s], q, w->ns[s]));
-                if (ctx->p.precision == AFQMC_PREC_FP64) CK(store_G<double>(w, st, s));
-                else CK(store_G<float>(w, st, s));
-            }
+            CK(form_Z(ctx, w, st, fac_R(w, 0), fac_L(w, 0), grp[gi][0], ng[gi], w->sign));
+            if (ctx->p.precision == AFQMC_PREC_FP64) CK(finish_G<double>(w, st, fac_R(w, 0), grp[gi][0], ng[gi], false));
+            else CK(finish_G<float>(w, st, fac_R(w, 0), grp[gi][0], ng[gi], false));
         }
         w->pos = 0;
         w->last_dir = -1;
@@ -680,29 +755,40 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
 
 }  // extern "C"
 
+static size_t ctx_replay_offset(const afqmc_ctx* ctx, int walker) { return ctx->roff[walker]; }
+
 template <typename T>
-static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k, int nb, const uint8_t* replay,
+static int sweep_impl(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int k, int nb, const uint8_t* replay,
                       cudaStream_t st) {
-    Walker* w = ctx->w[wi];
-    const int N = w->N;
+    Walker* w = ctx->w[gi];
+    const int N = w->N, nwk = w->nwk;
     const long ld = w->ld;
     T* G0 = (T*)w->G;
     T* G1 = G0 + (size_t)N * ld;
     T* Tb = (T*)w->Tbuf;
     int8_t* xl = w->x + (size_t)(ell - 1) * N;
     T* d = (T*)w->dvec;
-    T* dinv = d + 2 * N;
+    T* dinv = d + (size_t)nwk * 2 * N;
     const T* E = (const T*)w->lat->Eb;
     const T* Einv = (const T*)w->lat->Einvb;
     const int NW = window_max<T>();
     const uint8_t* rep = nullptr;
+    Batch bt;
+    bt.nwk = nwk;
+    bt.gstride = w->gstride();
+    bt.xstride = (long)ctx->p.M * N;
+    const int nb2 = 2 * nwk;  // (walker, spin) batch of the G products
     {
         PhaseScope ps(ctx, AFQMC_PHASE_PREP, st);
-        CK(launch_uniforms(st, ctx->p.seed, (uint64_t)wi, w->visit, 2 * N, w->u));
-        CK(cudaMemsetAsync(w->stats, 0, 8 * sizeof(int), st));
-        CK(cudaMemsetAsync(w->maxr, 0, 8, st));
+        CK(launch_uniforms(st, ctx->p.seed, w->gid_d, w->visit, 2 * N, w->u, nwk));
+        CK(cudaMemsetAsync(w->stats, 0, (size_t)nwk * 8 * sizeof(int), st));
+        CK(cudaMemsetAsync(w->maxr, 0, (size_t)nwk * 8, st));
         if (replay) {
-            CK(cudaMemcpyAsync(w->replay, replay + (size_t)wi * 2 * N, 2 * (size_t)N, cudaMemcpyHostToDevice, st));
+            std::vector<uint8_t> h((size_t)nwk * 2 * N);
+            for (int j = 0; j < nwk; ++j)
+                memcpy(h.data() + (size_t)j * 2 * N, replay + (size_t)ctx_replay_offset(ctx, w->gid[j]), 2 * (size_t)N);
+            CK(cudaMemcpyAsync(w->replay, h.data(), h.size(), cudaMemcpyHostToDevice, st));
+            CK(cudaStreamSynchronize(st));  // the host staging buffer goes out of scope
             rep = w->replay;
         }
     }
@@ -710,7 +796,7 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
     const int split3 = ctx->p.gemm != AFQMC_GEMM_TF32;
     auto wrap = [&](int direction) -> cudaError_t {
         PhaseScope ps(ctx, AFQMC_PHASE_WRAP, st);
-        cudaError_t e = launch_field_scales_T<T>(st, xl, N, ctx->c, d, dinv, N);
+        cudaError_t e = launch_field_scales_T<T>(st, xl, N, ctx->c, d, dinv, N, nwk, bt.xstride);
         if (e != cudaSuccess) return e;
         if (use_tc) {
             // E and Einv are symmetric, so both products are A * Bt^T with K-major operands:
@@ -721,11 +807,11 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
             float* Gf = (float*)G0;
             float* Tf = (float*)Tb;
             if (direction < 0) {
-                e = launch_scale2<T>(st, G0, ld, N, (long)N * ld, dinv, d);
+                e = launch_scale2<T>(st, G0, ld, N, (long)N * ld, dinv, d, nb2);
                 if (e != cudaSuccess) return e;
             }
             TcGemmArgs t1;
-            t1.M = N; t1.N = N; t1.K = N; t1.batch = 2;
+            t1.M = N; t1.N = N; t1.K = N; t1.batch = nb2;
             t1.A = Gf; t1.lda = ld; t1.sA = (long)N * ld;
             t1.Bt = direction > 0 ? Eif : Ef; t1.ldb = ld; t1.sB = 0;
             t1.C = Tf; t1.ldc = ld; t1.sC = (long)N * ld; t1.c_trans = 1;
@@ -736,7 +822,7 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
                 if ((e = tc_gemm(st, t1)) != cudaSuccess) return e;
             }
             TcGemmArgs t2;
-            t2.M = N; t2.N = N; t2.K = N; t2.batch = 2;
+            t2.M = N; t2.N = N; t2.K = N; t2.batch = nb2;
             t2.A = direction > 0 ? Ef : Eif; t2.lda = ld; t2.sA = 0;
             t2.Bt = Tf; t2.ldb = ld; t2.sB = (long)N * ld;
             t2.C = Gf; t2.ldc = ld; t2.sC = (long)N * ld;
@@ -750,7 +836,7 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
             return tc_gemm(st, t2);
         }
         GemmArgs<T> g1, g2;
-        g1.M = N; g1.N = N; g1.K = N; g1.batch = 2;
+        g1.M = N; g1.N = N; g1.K = N; g1.batch = nb2;
         g1.ldb = ld; g1.sB = (long)N * ld;
         g1.C = Tb; g1.ldc = ld; g1.sC = (long)N * ld;
         g1.lda = ld; g1.sA = 0;
@@ -789,7 +875,7 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
     sp.lam = ctx->lam;
     sp.hs = ctx->p.hs;
     sp.seed = ctx->p.seed;
-    sp.walker = (uint64_t)wi;
+    sp.walker = (uint64_t)w->gid[0];
     sp.visit = w->visit;
     for (int s = 0; s < 2; ++s)
         for (int xi = 0; xi < 2; ++xi) {
@@ -808,17 +894,30 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
     so.maxr = w->maxr;
     so.sign = w->sign;
     if (mode == AFQMC_MODE_LOCAL) {
+        // one persistent cooperative launch per walker (its grid barriers are walker-wide)
         PhaseScope ps(ctx, AFQMC_PHASE_LOCAL, st);
-        CK(cudaMemsetAsync(w->bar, 0, sizeof(GridBar), st));
-        CK(launch_local<T>(st, G0, G1, xl, w->u, rep, sp, so, (T*)w->colbuf, (T*)w->rowbuf, w->bar, w->err,
-                           ctx->nsm));
+        for (int j = 0; j < nwk; ++j) {
+            SliceOut sj = so;
+            sj.dec += (size_t)j * 2 * N;
+            sj.ratio += (size_t)j * 2 * N;
+            sj.stats += (size_t)j * 8;
+            sj.maxr += j;
+            sj.sign += j;
+            SiteParams spj = sp;
+            spj.walker = (uint64_t)w->gid[j];
+            T* Gj = G0 + (size_t)j * bt.gstride;
+            CK(cudaMemsetAsync(w->bar, 0, sizeof(GridBar), st));
+            CK(launch_local<T>(st, Gj, Gj + (size_t)N * ld, xl + (size_t)j * bt.xstride, w->u + (size_t)j * 2 * N,
+                               rep ? rep + (size_t)j * 2 * N : nullptr, spj, sj, (T*)w->colbuf, (T*)w->rowbuf, w->bar,
+                               w->err, ctx->nsm));
+        }
     } else {
         int nw = (mode == AFQMC_MODE_DELAYED) ? k : (NW / nb) * nb;
         // Window w's decisions and the corrected block of window w + 1 run on st; window w's
-        // panels and rank-m product run on the walker's flush stream sf and overlap the
+        // panels and rank-m product run on the group's flush stream sf and overlap the
         // decisions of window w + 1.  Before building window w + 1's block, st waits for the
         // product of window w - 1 (ev_prod), which is also what frees the window buffers of
-        // parity (w + 1) & 1 for reuse.
+        // parity (w + 1) & 1 for reuse.  Every launch covers all walkers of the group.
         WindowBufs wb[2];
         for (int q = 0; q < 2; ++q) {
             wb[q].m = w->wm[q];
@@ -828,6 +927,7 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
             wb[q].Wx = w->Wx[q];
             wb[q].X = w->X[q];
             wb[q].Y = w->Y[q];
+            wb[q].nwk = nwk;
         }
         PhaseScope ps(ctx, AFQMC_PHASE_CHAIN, st);
         int wi = 0;
@@ -835,19 +935,19 @@ static int sweep_impl(afqmc_ctx* ctx, int wi, int ell, int dir, int mode, int k,
             const int n = (N - s0 < nw) ? N - s0 : nw;
             const int par = wi & 1;
             const T* blk = (wi > 0) ? (const T*)w->snap[par ^ 1] : nullptr;
-            CK(launch_window_chain<T>(st, mode, G0, G1, xl, w->u, rep, sp, so, s0, n, nb, wb[par], blk, w->err));
+            CK(launch_window_chain<T>(st, mode, G0, G1, xl, w->u, rep, sp, so, s0, n, nb, wb[par], blk, w->err, bt));
             const int sn = s0 + n, nn = (sn < N) ? ((N - sn < nw) ? N - sn : nw) : 0;
             if (nn > 0) {  // the next window's block
                 if (wi > 0) CK(cudaStreamWaitEvent(st, w->ev_prod[par ^ 1], 0));
-                CK(launch_next_block<T>(st, G0, G1, sp, wb[par], sn, nn, (T*)w->snap[par]));
+                CK(launch_next_block<T>(st, G0, G1, sp, wb[par], sn, nn, (T*)w->snap[par], bt));
             }
             CK(cudaEventRecord(w->ev_chain[par], st));
             CK(cudaStreamWaitEvent(w->sf, w->ev_chain[par], 0));
             PhaseScope pf(ctx, AFQMC_PHASE_FLUSH, w->sf);
-            CK(launch_flush_panels<T>(w->sf, G0, G1, sp, wb[par], n));
+            CK(launch_flush_panels<T>(w->sf, G0, G1, sp, wb[par], n, bt));
             {
                 PhaseScope pg(ctx, AFQMC_PHASE_FLUSH_GEMM, w->sf);
-                CK(launch_flush_gemm<T>(w->sf, G0, G1, sp, wb[par], n));
+                CK(launch_flush_gemm<T>(w->sf, G0, G1, sp, wb[par], n, bt));
             }
             CK(cudaEventRecord(w->ev_prod[par], w->sf));
         }
@@ -877,11 +977,11 @@ int afqmc_sweep_slice(afqmc_ctx* ctx, int slice, int dir, int mode, int k, int n
     }
     cudaStream_t st = (cudaStream_t)stream;
     ctx->last = st;
-    for (int wi = 0; wi < (int)ctx->w.size(); ++wi) {
-        rc = f64 ? sweep_impl<double>(ctx, wi, slice, dir, mode, k, nb, replay, st)
-                 : sweep_impl<float>(ctx, wi, slice, dir, mode, k, nb, replay, st);
+    for (int gi = 0; gi < (int)ctx->w.size(); ++gi) {
+        rc = f64 ? sweep_impl<double>(ctx, gi, slice, dir, mode, k, nb, replay, st)
+                 : sweep_impl<float>(ctx, gi, slice, dir, mode, k, nb, replay, st);
         if (rc) return rc;
-        Walker* w = ctx->w[wi];
+        Walker* w = ctx->w[gi];
         w->pos = (dir > 0) ? slice : slice - 1;
         w->last_dir = dir;
         w->visit++;
@@ -889,18 +989,23 @@ int afqmc_sweep_slice(afqmc_ctx* ctx, int slice, int dir, int mode, int k, int n
     }
     if (stats) {
         CK(cudaStreamSynchronize(st));
-        for (int wi = 0; wi < (int)ctx->w.size(); ++wi) {
-            Walker* w = ctx->w[wi];
+        for (auto* w : ctx->w) {
             int r = read_dev_err(ctx, w);
             if (r) return r;
-            int h[8];
-            CK(cudaMemcpy(h, w->stats, sizeof(h), cudaMemcpyDeviceToHost));
-            stats[wi].proposals = h[0];
-            stats[wi].accepts = h[1];
-            stats[wi].flipped = h[2];
-            stats[wi].flushes = h[3];
-            CK(cudaMemcpy(&stats[wi].max_abs_ratio, w->maxr, 8, cudaMemcpyDeviceToHost));
-            CK(cudaMemcpy(&stats[wi].sign, w->sign, 8, cudaMemcpyDeviceToHost));
+            std::vector<int> h((size_t)w->nwk * 8);
+            std::vector<double> mr(w->nwk), sg(w->nwk);
+            CK(cudaMemcpy(h.data(), w->stats, h.size() * sizeof(int), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(mr.data(), w->maxr, (size_t)w->nwk * 8, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(sg.data(), w->sign, (size_t)w->nwk * 8, cudaMemcpyDeviceToHost));
+            for (int j = 0; j < w->nwk; ++j) {
+                afqmc_slice_stats& o = stats[w->gid[j]];
+                o.proposals = h[j * 8 + 0];
+                o.accepts = h[j * 8 + 1];
+                o.flipped = h[j * 8 + 2];
+                o.flushes = h[j * 8 + 3];
+                o.max_abs_ratio = mr[j];
+                o.sign = sg[j];
+            }
         }
     }
     return AFQMC_OK;
@@ -916,82 +1021,42 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     ctx->last = st;
     const bool f64 = ctx->p.precision == AFQMC_PREC_FP64;
-    std::vector<double> drift(ctx->w.size(), 0.0);
-    for (int wi = 0; wi < (int)ctx->w.size(); ++wi) {
-        Walker* w = ctx->w[wi];
-        const int N = w->N, j = w->pos / S;
+    for (auto* w : ctx->w) {
+        const int j = w->pos / S;
         PhaseScope ps(ctx, AFQMC_PHASE_RECOMPUTE, st);
-        CK(cudaMemsetAsync(w->acc2, 0, 16, st));
+        CK(cudaMemsetAsync(w->acc2, 0, (size_t)w->nwk * 16, st));
         // the factors of the current position: one side from the stacks, the other propagated
         // over the last S slices from the previous stack entry and re-orthonormalised
-        double* UR[2];
-        double* UL[2];
-        double* Uc[2] = {w->Ucur, w->Ucur + (size_t)N * w->nsm};
-        bool prop = false;
-        for (int s = 0; s < 2; ++s) {
-            const size_t blk = (size_t)N * w->ns[s];
-            if (w->last_dir > 0) {
-                UL[s] = w->ULs[s] + (size_t)j * blk;
-                if (j == 0) {
-                    UR[s] = w->URs[s];
-                } else {
-                    CK(cudaMemcpyAsync(Uc[s], w->URs[s] + (size_t)(j - 1) * blk, blk * 8, cudaMemcpyDeviceToDevice, st));
-                    UR[s] = w->URs[s] + (size_t)j * blk;
-                    prop = true;
-                }
-            } else {
-                UR[s] = w->URs[s] + (size_t)j * blk;
-                if (w->pos == ctx->p.M) {
-                    UL[s] = w->ULs[s] + (size_t)j * blk;
-                } else {
-                    CK(cudaMemcpyAsync(Uc[s], w->ULs[s] + (size_t)(j + 1) * blk, blk * 8, cudaMemcpyDeviceToDevice, st));
-                    UL[s] = w->ULs[s] + (size_t)j * blk;
-                    prop = true;
-                }
-            }
-        }
+        const bool fwd = w->last_dir > 0;
+        const bool prop = fwd ? (j > 0) : (w->pos != ctx->p.M);
         int grp[2][2], ng[2];
         const int ngr = spin_groups(w, grp, ng);
         if (prop) {
-            if (w->last_dir > 0) CK(propagate(ctx, w, st, Uc, 0, w->pos - S + 1, 1, S));
-            else CK(propagate(ctx, w, st, Uc, 1, w->pos + S, -1, S));
+            CK(from_stack(w, st, fwd, fwd ? j - 1 : j + 1));
+            if (fwd) CK(propagate(ctx, w, st, 0, w->pos - S + 1, 1, S));
+            else CK(propagate(ctx, w, st, 1, w->pos + S, -1, S));
             for (int gi = 0; gi < ngr; ++gi) {
-                double* Cg[2] = {Uc[grp[gi][0]], ng[gi] > 1 ? Uc[grp[gi][1]] : nullptr};
-                if (w->last_dir > 0) CK(stab_rows(ctx, w, st, Cg, ng[gi], w->ns[grp[gi][0]], nullptr));
-                else CK(stab_cols(ctx, w, st, Cg, ng[gi], w->ns[grp[gi][0]], nullptr));
+                if (fwd) CK(stab_rows(ctx, w, st, fac_cur(w), grp[gi][0], ng[gi], nullptr));
+                else CK(stab_cols(ctx, w, st, fac_cur(w), grp[gi][0], ng[gi], nullptr));
             }
-            for (int s = 0; s < 2; ++s)
-                CK(cudaMemcpyAsync(w->last_dir > 0 ? UR[s] : UL[s], Uc[s], (size_t)N * w->ns[s] * 8,
-                                   cudaMemcpyDeviceToDevice, st));
+            CK(to_stack(w, st, fwd, j));
         }
         for (int gi = 0; gi < ngr; ++gi) {
-            const double* R[2] = {UR[grp[gi][0]], ng[gi] > 1 ? UR[grp[gi][1]] : nullptr};
-            const double* Lf[2] = {UL[grp[gi][0]], ng[gi] > 1 ? UL[grp[gi][1]] : nullptr};
-            CK(form_Z(ctx, w, st, R, Lf, ng[gi], w->ns[grp[gi][0]], nullptr));
-            for (int q = 0; q < ng[gi]; ++q) {
-                const int s = grp[gi][q];
-                CK(finish_G(w, st, UR[s], q, w->ns[s]));
-                if (f64) {
-                    double* G = (double*)w->G + (size_t)s * N * w->ld;
-                    CK(launch_drift<double>(st, G, (const double*)w->Gnew, w->ld, N, w->acc2));
-                    CK(store_G<double>(w, st, s));
-                } else {
-                    float* G = (float*)w->G + (size_t)s * N * w->ld;
-                    CK(launch_drift<float>(st, G, (const float*)w->Gnew, w->ld, N, w->acc2));
-                    CK(store_G<float>(w, st, s));
-                }
-            }
+            CK(form_Z(ctx, w, st, fac_R(w, j), fac_L(w, j), grp[gi][0], ng[gi], nullptr));
+            if (f64) CK(finish_G<double>(w, st, fac_R(w, j), grp[gi][0], ng[gi], true));
+            else CK(finish_G<float>(w, st, fac_R(w, j), grp[gi][0], ng[gi], true));
         }
         w->need_recompute = false;
     }
     if (rel_drift) {
         CK(cudaStreamSynchronize(st));
-        for (int wi = 0; wi < (int)ctx->w.size(); ++wi) {
-            int r = read_dev_err(ctx, ctx->w[wi]);
+        for (auto* w : ctx->w) {
+            int r = read_dev_err(ctx, w);
             if (r) return r;
-            double h[2];
-            CK(cudaMemcpy(h, ctx->w[wi]->acc2, 16, cudaMemcpyDeviceToHost));
-            rel_drift[wi] = h[1] > 0 ? sqrt(h[0] / h[1]) : 0.0;
+            std::vector<double> h((size_t)w->nwk * 2);
+            CK(cudaMemcpy(h.data(), w->acc2, h.size() * 8, cudaMemcpyDeviceToHost));
+            for (int jw = 0; jw < w->nwk; ++jw)
+                rel_drift[w->gid[jw]] = h[2 * jw + 1] > 0 ? sqrt(h[2 * jw] / h[2 * jw + 1]) : 0.0;
         }
     }
     return AFQMC_OK;
@@ -1004,85 +1069,103 @@ int afqmc_measure_energy(afqmc_ctx* ctx, double* energy, double* sign, void* str
     cudaStream_t st = (cudaStream_t)stream;
     ctx->last = st;
     for (auto* w : ctx->w) {
-        CK(cudaMemsetAsync(w->acc2, 0, 16, st));
-        if (ctx->p.precision == AFQMC_PREC_FP64) {
-            const double* G = (const double*)w->G;
-            CK(launch_energy<double>(st, G, G + (size_t)w->N * w->ld, w->ld, w->L, ctx->p.t, ctx->p.U, w->acc2));
-        } else {
-            const float* G = (const float*)w->G;
-            CK(launch_energy<float>(st, G, G + (size_t)w->N * w->ld, w->ld, w->L, ctx->p.t, ctx->p.U, w->acc2));
-        }
+        CK(cudaMemsetAsync(w->acc2, 0, (size_t)w->nwk * 16, st));
+        if (ctx->p.precision == AFQMC_PREC_FP64)
+            CK(launch_energy<double>(st, (const double*)w->G, w->ld, w->L, ctx->p.t, ctx->p.U, w->acc2, w->nwk,
+                                     w->gstride()));
+        else
+            CK(launch_energy<float>(st, (const float*)w->G, w->ld, w->L, ctx->p.t, ctx->p.U, w->acc2, w->nwk,
+                                    w->gstride()));
     }
     CK(cudaStreamSynchronize(st));
-    for (int wi = 0; wi < (int)ctx->w.size(); ++wi) {
-        Walker* w = ctx->w[wi];
+    for (auto* w : ctx->w) {
         int r = read_dev_err(ctx, w);
         if (r) return r;
-        CK(cudaMemcpy(&energy[wi], w->acc2, 8, cudaMemcpyDeviceToHost));
-        if (sign) CK(cudaMemcpy(&sign[wi], w->sign, 8, cudaMemcpyDeviceToHost));
+        std::vector<double> e(w->nwk), sg(w->nwk);
+        CK(cudaMemcpy(e.data(), w->acc2, (size_t)w->nwk * 8, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(sg.data(), w->sign, (size_t)w->nwk * 8, cudaMemcpyDeviceToHost));
+        for (int j = 0; j < w->nwk; ++j) {
+            energy[w->gid[j]] = e[j];
+            if (sign) sign[w->gid[j]] = sg[j];
+        }
     }
     return AFQMC_OK;
 }
 
+static bool walker_of(afqmc_ctx* ctx, int walker, Walker** w, int* j) {
+    if (!ctx || walker < 0 || walker >= (int)ctx->wmap.size()) return false;
+    *w = ctx->w[ctx->wmap[walker].first];
+    *j = ctx->wmap[walker].second;
+    return true;
+}
+
 int afqmc_get_G(afqmc_ctx* ctx, int walker, int spin, double* host_out) {
-    if (!ctx || walker < 0 || walker >= (int)ctx->w.size() || spin < 0 || spin > 1 || !host_out) return AFQMC_ERR_ARG;
-    Walker* w = ctx->w[walker];
+    Walker* w;
+    int j;
+    if (!walker_of(ctx, walker, &w, &j) || spin < 0 || spin > 1 || !host_out) return AFQMC_ERR_ARG;
     CK(cudaStreamSynchronize(ctx->last));
     const size_t es = esize(ctx);
     std::vector<char> buf((size_t)w->N * w->ld * es);
-    CK(cudaMemcpy(buf.data(), (char*)w->G + (size_t)spin * w->N * w->ld * es, buf.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(buf.data(), (char*)w->G + ((size_t)j * 2 + spin) * w->N * w->ld * es, buf.size(),
+                  cudaMemcpyDeviceToHost));
     for (int i = 0; i < w->N; ++i)
-        for (int j = 0; j < w->N; ++j) {
-            size_t o = (size_t)i * w->ld + j;
-            host_out[(size_t)i * w->N + j] = (es == 8) ? ((double*)buf.data())[o] : (double)((float*)buf.data())[o];
+        for (int c = 0; c < w->N; ++c) {
+            size_t o = (size_t)i * w->ld + c;
+            host_out[(size_t)i * w->N + c] = (es == 8) ? ((double*)buf.data())[o] : (double)((float*)buf.data())[o];
         }
     return read_dev_err(ctx, w);
 }
 
 int afqmc_set_G(afqmc_ctx* ctx, int walker, int spin, const double* host_in) {
-    if (!ctx || walker < 0 || walker >= (int)ctx->w.size() || spin < 0 || spin > 1 || !host_in) return AFQMC_ERR_ARG;
-    Walker* w = ctx->w[walker];
+    Walker* w;
+    int j;
+    if (!walker_of(ctx, walker, &w, &j) || spin < 0 || spin > 1 || !host_in) return AFQMC_ERR_ARG;
     CK(cudaStreamSynchronize(ctx->last));
     const size_t es = esize(ctx);
     std::vector<char> buf((size_t)w->N * w->ld * es, 0);
     for (int i = 0; i < w->N; ++i)
-        for (int j = 0; j < w->N; ++j) {
-            size_t o = (size_t)i * w->ld + j;
-            double v = host_in[(size_t)i * w->N + j];
+        for (int c = 0; c < w->N; ++c) {
+            size_t o = (size_t)i * w->ld + c;
+            double v = host_in[(size_t)i * w->N + c];
             if (es == 8) ((double*)buf.data())[o] = v;
             else ((float*)buf.data())[o] = (float)v;
         }
-    CK(cudaMemcpy((char*)w->G + (size_t)spin * w->N * w->ld * es, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((char*)w->G + ((size_t)j * 2 + spin) * w->N * w->ld * es, buf.data(), buf.size(),
+                  cudaMemcpyHostToDevice));
     return AFQMC_OK;
 }
 
 int afqmc_get_fields(afqmc_ctx* ctx, int walker, int8_t* host_out) {
-    if (!ctx || walker < 0 || walker >= (int)ctx->w.size() || !host_out) return AFQMC_ERR_ARG;
-    Walker* w = ctx->w[walker];
+    Walker* w;
+    int j;
+    if (!walker_of(ctx, walker, &w, &j) || !host_out) return AFQMC_ERR_ARG;
     CK(cudaStreamSynchronize(ctx->last));
-    CK(cudaMemcpy(host_out, w->x, (size_t)ctx->p.M * w->N, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(host_out, w->x + (size_t)j * ctx->p.M * w->N, (size_t)ctx->p.M * w->N, cudaMemcpyDeviceToHost));
     return AFQMC_OK;
 }
 
 int afqmc_get_decisions(afqmc_ctx* ctx, int walker, uint8_t* host_out) {
-    if (!ctx || walker < 0 || walker >= (int)ctx->w.size() || !host_out) return AFQMC_ERR_ARG;
-    Walker* w = ctx->w[walker];
+    Walker* w;
+    int j;
+    if (!walker_of(ctx, walker, &w, &j) || !host_out) return AFQMC_ERR_ARG;
     CK(cudaStreamSynchronize(ctx->last));
-    CK(cudaMemcpy(host_out, w->dec, 2 * (size_t)w->N, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(host_out, w->dec + (size_t)j * 2 * w->N, 2 * (size_t)w->N, cudaMemcpyDeviceToHost));
     return AFQMC_OK;
 }
 
 int afqmc_get_ratios(afqmc_ctx* ctx, int walker, double* host_out) {
-    if (!ctx || walker < 0 || walker >= (int)ctx->w.size() || !host_out) return AFQMC_ERR_ARG;
-    Walker* w = ctx->w[walker];
+    Walker* w;
+    int j;
+    if (!walker_of(ctx, walker, &w, &j) || !host_out) return AFQMC_ERR_ARG;
     CK(cudaStreamSynchronize(ctx->last));
-    CK(cudaMemcpy(host_out, w->ratio, 2 * (size_t)w->N * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(host_out, w->ratio + (size_t)j * 2 * w->N, 2 * (size_t)w->N * 8, cudaMemcpyDeviceToHost));
     return AFQMC_OK;
 }
 
 int afqmc_get_info(afqmc_ctx* ctx, int walker, int* N, int* n_up, int* n_dn, int* slice, int* dir) {
-    if (!ctx || walker < 0 || walker >= (int)ctx->w.size()) return AFQMC_ERR_ARG;
-    Walker* w = ctx->w[walker];
+    Walker* w;
+    int j;
+    if (!walker_of(ctx, walker, &w, &j)) return AFQMC_ERR_ARG;
     if (N) *N = w->N;
     if (n_up) *n_up = w->ns[0];
     if (n_dn) *n_dn = w->ns[1];

@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
     const T* rs = g.rs ? g.rs + z * g.srs : nullptr;
     const T* cs = g.cs ? g.cs + z * g.scs : nullptr;
     const T* bs = g.bs ? g.bs + z * g.sbs : nullptr;
-    const int K = g.Kdev ? min(*g.Kdev, g.K) : g.K;
+    const int K = g.Kdev ? min(g.Kdev[g.kdiv > 0 ? z / g.kdiv : 0], g.K) : g.K;
 
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN + 1];

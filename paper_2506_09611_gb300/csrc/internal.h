@@ -20,7 +20,8 @@ void count_launch(int n = 1);
 template <typename T>
 struct GemmArgs {
     int M = 0, N = 0, K = 0;
-    const int* Kdev = nullptr;
+    const int* Kdev = nullptr;  // device K (min with K); with kdiv > 0, batch z reads Kdev[z / kdiv]
+    int kdiv = 0;
     const T* A = nullptr; long lda = 0, sA = 0;
     const T* B = nullptr; long ldb = 0, sB = 0;
     T* C = nullptr; long ldc = 0, sC = 0;
@@ -61,37 +62,46 @@ cudaError_t launch_scale_rows(cudaStream_t st, double* U, int rows, int cols, co
 cudaError_t launch_scale_cols(cudaStream_t st, double* U, int rows, int cols, const double* d);  // U[:,c] *= d[c]
 
 template <typename T>
-cudaError_t launch_cast(cudaStream_t st, const double* src, long lds, T* dst, long ldd, int rows, int cols);
+cudaError_t launch_cast(cudaStream_t st, const double* src, long lds, T* dst, long ldd, int rows, int cols,
+                        int nbatch = 1, long ssrc = 0, long sdst = 0);
 template <typename T>
 cudaError_t launch_to_double(cudaStream_t st, const T* src, long lds, double* dst, long ldd, int rows, int cols);
 cudaError_t launch_field_scales(cudaStream_t st, const int8_t* x, int N, double c, double* d, double* dinv);
 template <typename T>
-cudaError_t launch_field_scales_T(cudaStream_t st, const int8_t* x, int N, const double* c2, T* d, T* dinv, long sd);
+cudaError_t launch_field_scales_T(cudaStream_t st, const int8_t* x, int N, const double* c2, T* d, T* dinv, long sd,
+                                  int nwk = 1, long xstride = 0);
 
-// Fused FP64 propagation over nsl slices l = l_first, l_first + l_step, ... (setup.cu): for each
-// of nvec vectors of length N = L*L (element i of vector v at U[v * vs + i * es]),
+// Fused FP64 propagation over nsl slices l = l_first, l_first + l_step, ... (setup.cu) of nmat
+// factors: factor b (walker j = b / 2, spin s = b % 2) at U0 + j wstride + s sstride holds
+// nvec[s] vectors of length N = L*L (element i of vector v at [v * vs[s] + i * es[s]]);
 // right factors: v <- D_l (E v); left factors (left != 0): v <- E (D_l v); E = Ex (x) Ex,
-// D_l = diag(x_{l,i} > 0 ? dplus : dminus) with x the M x N fields.  nmat (1 or 2) spins.
+// D_l = diag(x_{l,i} > 0 ? dplus[s] : dminus[s]) with x the walker's M x N fields.
 struct PropArgs {
-    double* U[2] = {nullptr, nullptr};
+    double* U0 = nullptr;
+    long wstride = 0, sstride = 0;
     long vs[2] = {0, 0}, es[2] = {0, 0};
     int nvec[2] = {0, 0};
     double dplus[2] = {1.0, 1.0}, dminus[2] = {1.0, 1.0};
     const double* Ex = nullptr;
     const int8_t* x = nullptr;
-    int L = 0, l_first = 1, l_step = 1, nsl = 0, left = 0, nmat = 1;
+    long xstride = 0;
+    int L = 0, l_first = 1, l_step = 1, nsl = 0, left = 0, nmat = 2;
 };
 cudaError_t launch_prop(cudaStream_t st, const PropArgs& a);
 
-// Blocked partially pivoted LU in FP64 (lu.cu) of nmat (1 or 2) row-major m x n matrices
-// (m >= n) without row swaps: after launch_lu, perm[j] is the pivot row of column j; a pivot
-// row holds its multipliers left of its column and its U entries from there on; unpivoted rows
-// hold multipliers.  flag: m bytes per matrix (scratch).  err receives DEV_NUMERIC on a zero
-// pivot.
+// Blocked partially pivoted LU in FP64 (lu.cu) of nmat row-major m x n matrices (m >= n) without
+// row swaps.  Matrix b (walker j = b / ng, spin q = b % ng) sits at A0 + j wstride + q sstride;
+// its pivot rows go to perm0 + b pstride (perm[c] = pivot row of column c) and flag0 + b pstride
+// is m bytes of scratch.  After launch_lu a pivot row holds its multipliers left of its column
+// and its U entries from there on; unpivoted rows hold multipliers.  err receives DEV_NUMERIC
+// on a zero pivot.
 struct LuArgs {
-    double* A[2] = {nullptr, nullptr};
-    int* perm[2] = {nullptr, nullptr};
-    int8_t* flag[2] = {nullptr, nullptr};
+    double* A0 = nullptr;
+    long wstride = 0, sstride = 0;
+    int ng = 1;
+    int* perm0 = nullptr;
+    int8_t* flag0 = nullptr;
+    long pstride = 0;
     long lda = 0;
     int m = 0, n = 0, nmat = 1;
     int* err = nullptr;
@@ -99,26 +109,34 @@ struct LuArgs {
 cudaError_t launch_lu(cudaStream_t st, const LuArgs& a);
 // After launch_lu: pivot rows become unit rows, so A = P L spans the factored columns.
 cudaError_t launch_lu_unit_rows(cudaStream_t st, const LuArgs& a);
-// After launch_lu: *sign_out *= sign(prod of pivots) (times the row permutation's parity when
-// parity != 0), over all matrices; visited: m ints of scratch.
+// After launch_lu: sign_out[j] *= sign(prod of pivots) (times the row permutation's parity when
+// parity != 0) over the ng matrices of walker j; visited: nmat * m ints of scratch.
 cudaError_t launch_lu_sign(cudaStream_t st, const LuArgs& a, int parity, double* sign_out, int* visited);
-// Z = O^{-1} B for O factored by launch_lu (ns x ns, leading dimension ldl), B and Z ns x N.
+// Z = O^{-1} B for the O factored by launch_lu (ns x ns, leading dimension ldl, matrix b at
+// LU0 + b ostride with pivots perm0 + b pstride), B (ns x N) at B0 + j wstride + q sstride
+// (b = j ng + q) and Z (ns x N) at Z0 + b zstride.
 struct SolveArgs {
-    const double* LU[2] = {nullptr, nullptr};
-    const int* perm[2] = {nullptr, nullptr};
-    const double* B[2] = {nullptr, nullptr};
-    double* Z[2] = {nullptr, nullptr};
+    const double* LU0 = nullptr;
+    long ostride = 0;
+    const int* perm0 = nullptr;
+    long pstride = 0;
+    const double* B0 = nullptr;
+    long wstride = 0, sstride = 0;
+    int ng = 1;
+    double* Z0 = nullptr;
+    long zstride = 0;
     long ldl = 0;
     int ns = 0, N = 0, nmat = 1;
 };
 cudaError_t launch_lu_solve(cudaStream_t st, const SolveArgs& a);
 template <typename T>
-cudaError_t launch_identity_minus(cudaStream_t st, T* G, long ld, int N);  // G = I - G
+cudaError_t launch_identity_minus(cudaStream_t st, T* G, long ld, int N, int nbatch = 1, long sG = 0);  // G = I - G
 template <typename T>
-cudaError_t launch_drift(cudaStream_t st, const T* Gold, const T* Gnew, long ld, int N, double* acc2);
+cudaError_t launch_drift(cudaStream_t st, const T* Gold, const T* Gnew, long ld, int N, double* acc2, int nbatch = 1,
+                         long sold = 0, long snew = 0, int adiv = 1);
 template <typename T>
-cudaError_t launch_energy(cudaStream_t st, const T* Gu, const T* Gd, long ld, int L, double t, double U,
-                          double* out);
+cudaError_t launch_energy(cudaStream_t st, const T* Gu, long ld, int L, double t, double U, double* out, int nwk = 1,
+                          long gstride = 0);
 
 // ---- sweep kernels (sweep.cu) ----
 // Per-slice constants of the site loop.  The field-change factors depend only on the
@@ -147,7 +165,9 @@ struct SliceOut {      // device-side per-walker outputs of one slice
     double* sign;      // walker sign (updated in place)
 };
 
-cudaError_t launch_uniforms(cudaStream_t st, uint64_t seed, uint64_t walker, uint64_t visit, int count, double* u);
+// u[j][0..count) for the walkers gid[j] (device array), j < nwk.
+cudaError_t launch_uniforms(cudaStream_t st, uint64_t seed, const int* gid, uint64_t visit, int count, double* u,
+                            int nwk);
 
 template <typename T>
 cudaError_t launch_local(cudaStream_t st, T* Gu, T* Gd, int8_t* xl, const double* u, const uint8_t* replay,
@@ -162,6 +182,15 @@ struct WindowBufs {    // device scratch of the window chain + flush
     void* Wx;          // per spin NW x NW (T): sweep: the window's update matrix W
     void* X;           // per spin N x NW column panel (T)
     void* Y;           // per spin NW x N row panel (T), plus room for a second product
+    int nwk = 1;       // walkers in the group: every buffer above holds nwk back-to-back copies
+};
+
+// A group of walkers with the same lattice and particle numbers: their per-walker buffers are
+// laid out back to back and every launch of a slice covers the whole group.
+struct Batch {
+    int nwk = 1;        // walkers in the group
+    long gstride = 0;   // elements between consecutive walkers' G ([2][N][ld])
+    long xstride = 0;   // bytes between consecutive walkers' fields (M x N)
 };
 
 template <typename T>
@@ -170,7 +199,7 @@ int window_max();      // largest window (sites) the chain kernel holds in share
 template <typename T>
 cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T* Gd, int8_t* xl, const double* u,
                                 const uint8_t* replay, const SiteParams& sp, SliceOut so, int s0, int n, int nb,
-                                WindowBufs wb, const T* blk, int* err);
+                                WindowBufs wb, const T* blk, int* err, Batch bt = Batch());
 template <typename T>
 cudaError_t launch_flush(cudaStream_t st, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw);
 // Pipelined flush of a window (the window kernel leaves its update matrix W in wb.Wx):
@@ -180,13 +209,15 @@ cudaError_t launch_flush(cudaStream_t st, T* Gu, T* Gd, const SiteParams& sp, Wi
 //   launch_flush_gemm   -- G <- G - X Y'.
 template <typename T>
 cudaError_t launch_next_block(cudaStream_t st, const T* Gu, const T* Gd, const SiteParams& sp, WindowBufs wb, int sn,
-                              int nn, T* snap);
+                              int nn, T* snap, Batch bt = Batch());
 template <typename T>
-cudaError_t launch_flush_panels(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw);
+cudaError_t launch_flush_panels(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw,
+                                Batch bt = Batch());
 template <typename T>
-cudaError_t launch_flush_gemm(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw);
+cudaError_t launch_flush_gemm(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw,
+                              Batch bt = Batch());
 // G_s[i][j] *= a_s[i] * b_s[j] for both spins (a, b: [2][N], spin stride N)
 template <typename T>
-cudaError_t launch_scale2(cudaStream_t st, T* G, long ld, int N, long sG, const T* a, const T* b);
+cudaError_t launch_scale2(cudaStream_t st, T* G, long ld, int N, long sG, const T* a, const T* b, int nbatch = 2);
 
 }  // namespace afq

@@ -20,6 +20,10 @@
 namespace afq {
 namespace cg = cooperative_groups;
 
+__device__ __forceinline__ double* lu_A(const LuArgs& a, int b) {
+    return a.A0 + (long)(b / a.ng) * a.wstride + (long)(b % a.ng) * a.sstride;
+}
+
 constexpr int LU_NB = 32;
 constexpr int LU_NBP = LU_NB + 1;
 
@@ -46,9 +50,9 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(LuArgs a, int j0, int nbk
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int mat = blockIdx.x / CS;
-    double* A = a.A[mat];
-    int* perm = a.perm[mat];
-    int8_t* flag = a.flag[mat];
+    double* A = lu_A(a, mat);
+    int* perm = a.perm0 + (long)mat * a.pstride;
+    int8_t* flag = a.flag0 + (long)mat * a.pstride;
     const int m = a.m, n = a.n;
     const long lda = a.lda;
     const int r0 = (int)((long)m * rank / CS), r1 = (int)((long)m * (rank + 1) / CS), nr = r1 - r0;
@@ -192,9 +196,9 @@ __global__ void __launch_bounds__(256) lu_panel_kernel(LuArgs a, int j0, int nbk
 // column tiles, matrix).
 __global__ void __launch_bounds__(256) lu_update_kernel(LuArgs a, int j0, int nbk) {
     const int mat = blockIdx.z;
-    double* A = a.A[mat];
-    const int* perm = a.perm[mat];
-    const int8_t* flag = a.flag[mat];
+    double* A = lu_A(a, mat);
+    const int* perm = a.perm0 + (long)mat * a.pstride;
+    const int8_t* flag = a.flag0 + (long)mat * a.pstride;
     const long lda = a.lda;
     const int m = a.m, n = a.n;
     const int r0 = blockIdx.x * 64, c0 = j0 + nbk + blockIdx.y * 64;
@@ -246,8 +250,8 @@ __global__ void __launch_bounds__(256) lu_update_kernel(LuArgs a, int j0, int nb
 // so A = P L (unit lower trapezoidal, rows in the original order) spans the same columns.
 __global__ void lu_unit_rows_kernel(LuArgs a) {
     const int mat = blockIdx.y;
-    double* A = a.A[mat];
-    const int* perm = a.perm[mat];
+    double* A = lu_A(a, mat);
+    const int* perm = a.perm0 + (long)mat * a.pstride;
     const int n = a.n;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)n * n; e += (long)gridDim.x * blockDim.x) {
         const int j = (int)(e / n), c = (int)(e % n);
@@ -258,28 +262,31 @@ __global__ void lu_unit_rows_kernel(LuArgs a) {
 // *sign_out *= the sign of the product of the pivots of every matrix (times each permutation's
 // parity when `parity`): the sign of det(A) for square A.  One thread; visited holds m ints.
 __global__ void lu_sign_kernel(LuArgs a, int parity, double* sign_out, int* visited) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int wk = blockIdx.x * blockDim.x + threadIdx.x;  // one thread per walker
+    if (wk * a.ng >= a.nmat) return;
+    int* vis = visited + (size_t)wk * a.m;
     double sg = 1.0;
-    for (int mat = 0; mat < a.nmat; ++mat) {
-        const double* A = a.A[mat];
-        const int* perm = a.perm[mat];
+    for (int q = 0; q < a.ng; ++q) {
+        const int mat = wk * a.ng + q;
+        const double* A = lu_A(a, mat);
+        const int* perm = a.perm0 + (long)mat * a.pstride;
         for (int j = 0; j < a.n; ++j)
             if (A[(long)perm[j] * a.lda + j] < 0.0) sg = -sg;
         if (parity) {
-            for (int r = 0; r < a.m; ++r) visited[r] = 0;
+            for (int r = 0; r < a.m; ++r) vis[r] = 0;
             for (int r = 0; r < a.m; ++r) {
-                if (visited[r]) continue;
-                int len = 0, q = r;
-                while (!visited[q]) {
-                    visited[q] = 1;
-                    q = perm[q];
+                if (vis[r]) continue;
+                int len = 0, p = r;
+                while (!vis[p]) {
+                    vis[p] = 1;
+                    p = perm[p];
                     ++len;
                 }
                 if ((len & 1) == 0) sg = -sg;
             }
         }
     }
-    *sign_out *= sg;
+    sign_out[wk] *= sg;
 }
 
 template <int CS>
@@ -313,10 +320,15 @@ static cudaError_t launch_panel(cudaStream_t st, const LuArgs& a, int j0, int nb
     return cudaLaunchKernelEx(&cfg, lu_panel_kernel<CS>, a, j0, nbk);
 }
 
+// Cluster size by the number of rows: enough CTAs that a panel step's FP64 work per SM stays
+// small, few enough that many matrices of a walker group factor at once.  16-CTA clusters are
+// used only if two of them fit on the device at once (else 8).
 static int lu_cluster_size(const LuArgs& a) {
-    static int cs = 0;
-    if (cs) return cs;
-    // 16-CTA clusters if two of them fit at once, else the portable 8
+    static int big = 0;
+    if (a.m <= 96) return 2;
+    if (a.m <= 256) return 4;
+    if (a.m <= 512) return 8;
+    if (big) return big;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(32);
     cfg.blockDim = dim3(256);
@@ -332,22 +344,26 @@ static int lu_cluster_size(const LuArgs& a) {
     cudaFuncSetAttribute((void*)lu_panel_kernel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute((void*)lu_panel_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(227 * 1024 - 16 * 1024));
-    if (cudaOccupancyMaxActiveClusters(&ncl, (void*)lu_panel_kernel<16>, &cfg) == cudaSuccess && ncl >= 2) cs = 16;
-    else cs = 8;
+    if (cudaOccupancyMaxActiveClusters(&ncl, (void*)lu_panel_kernel<16>, &cfg) == cudaSuccess && ncl >= 2) big = 16;
+    else big = 8;
     cudaGetLastError();
-    return cs;
+    return big;
 }
 
 cudaError_t launch_lu(cudaStream_t st, const LuArgs& a) {
-    if (a.m < a.n || a.n < 1 || a.nmat < 1 || a.nmat > 2) return cudaErrorInvalidValue;
+    if (a.m < a.n || a.n < 1 || a.nmat < 1 || a.pstride < a.m) return cudaErrorInvalidValue;
     const int cs = lu_cluster_size(a);
     if ((a.m + cs - 1) / cs * (LU_NBP * sizeof(double) + 1) > 200 * 1024) return cudaErrorInvalidValue;
     cudaError_t e;
-    for (int q = 0; q < a.nmat; ++q)
-        if ((e = cudaMemsetAsync(a.flag[q], 0, (size_t)a.m, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.flag0, 0, (size_t)(a.nmat - 1) * a.pstride + a.m, st)) != cudaSuccess) return e;
     for (int j0 = 0; j0 < a.n; j0 += LU_NB) {
         const int nbk = (a.n - j0 < LU_NB) ? a.n - j0 : LU_NB;
-        e = (cs == 16) ? launch_panel<16>(st, a, j0, nbk) : launch_panel<8>(st, a, j0, nbk);
+        switch (cs) {
+            case 2: e = launch_panel<2>(st, a, j0, nbk); break;
+            case 4: e = launch_panel<4>(st, a, j0, nbk); break;
+            case 8: e = launch_panel<8>(st, a, j0, nbk); break;
+            default: e = launch_panel<16>(st, a, j0, nbk); break;
+        }
         if (e != cudaSuccess) return e;
         const int nc = a.n - j0 - nbk;
         if (nc > 0) {
@@ -368,7 +384,8 @@ cudaError_t launch_lu_unit_rows(cudaStream_t st, const LuArgs& a) {
 cudaError_t launch_lu_sign(cudaStream_t st, const LuArgs& a, int parity, double* sign_out, int* visited) {
     if (!sign_out) return cudaSuccess;
     count_launch();
-    lu_sign_kernel<<<1, 1, 0, st>>>(a, parity, sign_out, visited);
+    const int nw = (a.nmat + a.ng - 1) / a.ng;
+    lu_sign_kernel<<<(nw + 63) / 64, 64, 0, st>>>(a, parity, sign_out, visited);
     return cudaGetLastError();
 }
 
@@ -385,10 +402,10 @@ constexpr int SV_COLS = 11, SV_YP = SV_COLS + 1, SV_KB = 64;
 
 __global__ void __launch_bounds__(256) lu_solve_kernel(SolveArgs a) {
     const int mat = blockIdx.y;
-    const double* LU = a.LU[mat];
-    const int* perm = a.perm[mat];
-    const double* B = a.B[mat];
-    double* Z = a.Z[mat];
+    const double* LU = a.LU0 + (long)mat * a.ostride;
+    const int* perm = a.perm0 + (long)mat * a.pstride;
+    const double* B = a.B0 + (long)(mat / a.ng) * a.wstride + (long)(mat % a.ng) * a.sstride;
+    double* Z = a.Z0 + (long)mat * a.zstride;
     const int ns = a.ns, N = a.N;
     const long ldl = a.ldl;
     const int c0 = blockIdx.x * SV_COLS, nc = min(SV_COLS, N - c0);

@@ -78,7 +78,7 @@ cudaError_t launch_scale_cols(cudaStream_t st, double* U, int rows, int cols, co
 
 template <typename T>
 __global__ void scale2_kernel(T* G, long ld, int N, long sG, const T* a, const T* b) {
-    const int s = blockIdx.y;
+    const int s = blockIdx.y;  // batch entry (walker, spin)
     T* g = G + s * sG;
     const T* as = a + (size_t)s * N;
     const T* bs = b + (size_t)s * N;
@@ -88,29 +88,32 @@ __global__ void scale2_kernel(T* G, long ld, int N, long sG, const T* a, const T
     }
 }
 template <typename T>
-cudaError_t launch_scale2(cudaStream_t st, T* G, long ld, int N, long sG, const T* a, const T* b) {
+cudaError_t launch_scale2(cudaStream_t st, T* G, long ld, int N, long sG, const T* a, const T* b, int nbatch) {
     count_launch();
-    scale2_kernel<T><<<dim3(512, 2), 256, 0, st>>>(G, ld, N, sG, a, b);
+    scale2_kernel<T><<<dim3(512, nbatch), 256, 0, st>>>(G, ld, N, sG, a, b);
     return cudaGetLastError();
 }
-template cudaError_t launch_scale2<float>(cudaStream_t, float*, long, int, long, const float*, const float*);
-template cudaError_t launch_scale2<double>(cudaStream_t, double*, long, int, long, const double*, const double*);
+template cudaError_t launch_scale2<float>(cudaStream_t, float*, long, int, long, const float*, const float*, int);
+template cudaError_t launch_scale2<double>(cudaStream_t, double*, long, int, long, const double*, const double*, int);
 
 template <typename T>
-__global__ void cast_kernel(const double* src, long lds, T* dst, long ldd, int rows, int cols) {
+__global__ void cast_kernel(const double* src, long lds, T* dst, long ldd, int rows, int cols, long ssrc, long sdst) {
+    src += blockIdx.y * ssrc;
+    dst += blockIdx.y * sdst;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)rows * cols; e += (long)gridDim.x * blockDim.x) {
         int r = (int)(e / cols), c = (int)(e % cols);
         dst[(long)r * ldd + c] = (T)src[(long)r * lds + c];
     }
 }
 template <typename T>
-cudaError_t launch_cast(cudaStream_t st, const double* src, long lds, T* dst, long ldd, int rows, int cols) {
+cudaError_t launch_cast(cudaStream_t st, const double* src, long lds, T* dst, long ldd, int rows, int cols, int nbatch,
+                        long ssrc, long sdst) {
     count_launch();
-    cast_kernel<T><<<512, 256, 0, st>>>(src, lds, dst, ldd, rows, cols);
+    cast_kernel<T><<<dim3(512, nbatch), 256, 0, st>>>(src, lds, dst, ldd, rows, cols, ssrc, sdst);
     return cudaGetLastError();
 }
-template cudaError_t launch_cast<float>(cudaStream_t, const double*, long, float*, long, int, int);
-template cudaError_t launch_cast<double>(cudaStream_t, const double*, long, double*, long, int, int);
+template cudaError_t launch_cast<float>(cudaStream_t, const double*, long, float*, long, int, int, int, long, long);
+template cudaError_t launch_cast<double>(cudaStream_t, const double*, long, double*, long, int, int, int, long, long);
 
 template <typename T>
 __global__ void to_double_kernel(const T* src, long lds, double* dst, long ldd, int rows, int cols) {
@@ -130,9 +133,12 @@ template cudaError_t launch_to_double<double>(cudaStream_t, const double*, long,
 
 // d_i = exp(c x_i), dinv_i = exp(-c x_i) for both spins; c2 = {c_up, c_dn}; outputs [2][N] with stride sd
 template <typename T>
-__global__ void field_scales_kernel(const int8_t* x, int N, double c0, double c1, T* d, T* dinv, long sd) {
+__global__ void field_scales_kernel(const int8_t* x, int N, double c0, double c1, T* d, T* dinv, long sd, long xstride) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    x += blockIdx.y * xstride;  // walker blockIdx.y of a group: outputs [walker][2][N]
+    d += (size_t)blockIdx.y * 2 * sd;
+    dinv += (size_t)blockIdx.y * 2 * sd;
     double xv = (double)x[i];
     d[i] = (T)exp(c0 * xv);
     dinv[i] = (T)exp(-c0 * xv);
@@ -140,13 +146,16 @@ __global__ void field_scales_kernel(const int8_t* x, int N, double c0, double c1
     dinv[sd + i] = (T)exp(-c1 * xv);
 }
 template <typename T>
-cudaError_t launch_field_scales_T(cudaStream_t st, const int8_t* x, int N, const double* c2, T* d, T* dinv, long sd) {
+cudaError_t launch_field_scales_T(cudaStream_t st, const int8_t* x, int N, const double* c2, T* d, T* dinv, long sd,
+                                  int nwk, long xstride) {
     count_launch();
-    field_scales_kernel<T><<<(N + 255) / 256, 256, 0, st>>>(x, N, c2[0], c2[1], d, dinv, sd);
+    field_scales_kernel<T><<<dim3((N + 255) / 256, nwk), 256, 0, st>>>(x, N, c2[0], c2[1], d, dinv, sd, xstride);
     return cudaGetLastError();
 }
-template cudaError_t launch_field_scales_T<float>(cudaStream_t, const int8_t*, int, const double*, float*, float*, long);
-template cudaError_t launch_field_scales_T<double>(cudaStream_t, const int8_t*, int, const double*, double*, double*, long);
+template cudaError_t launch_field_scales_T<float>(cudaStream_t, const int8_t*, int, const double*, float*, float*, long,
+                                                  int, long);
+template cudaError_t launch_field_scales_T<double>(cudaStream_t, const int8_t*, int, const double*, double*, double*,
+                                                   long, int, long);
 
 // ---------------------------------------------------------------------------
 // FP64 propagation of the walker factors over several slices (Sec. II.C), fused.
@@ -159,10 +168,11 @@ template cudaError_t launch_field_scales_T<double>(cudaStream_t, const int8_t*, 
 // ---------------------------------------------------------------------------
 constexpr int PV_VEC = 10;
 __global__ void __launch_bounds__(256) prop_kernel(PropArgs a, int vpc) {
-    const int s = blockIdx.y;
-    double* U = a.U[s];
+    const int s = blockIdx.y & 1, wk = blockIdx.y >> 1;  // factor (walker, spin)
+    double* U = a.U0 + wk * a.wstride + s * a.sstride;
     const int L = a.L, N = L * L, nvec = a.nvec[s];
     const long vs = a.vs[s], es = a.es[s];
+    const int8_t* xw = a.x + wk * a.xstride;
     const int v0 = blockIdx.x * vpc;
     if (v0 >= nvec) return;
     const int nv = min(vpc, nvec - v0);
@@ -180,7 +190,7 @@ __global__ void __launch_bounds__(256) prop_kernel(PropArgs a, int vpc) {
     __syncthreads();
     for (int t = 0; t < a.nsl; ++t) {
         const int ell = a.l_first + t * a.l_step;
-        const int8_t* xl = a.x + (size_t)(ell - 1) * N;
+        const int8_t* xl = xw + (size_t)(ell - 1) * N;
         if (a.left)
             for (int e = tid; e < nv * N; e += nt) V[e] *= (xl[e % N] > 0) ? dp : dm;
         __syncthreads();
@@ -246,24 +256,29 @@ cudaError_t launch_prop(cudaStream_t st, const PropArgs& a) {
 }
 
 template <typename T>
-__global__ void identity_minus_kernel(T* G, long ld, int N) {
+__global__ void identity_minus_kernel(T* G, long ld, int N, long sG) {
+    G += blockIdx.y * sG;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)N * N; e += (long)gridDim.x * blockDim.x) {
         int i = (int)(e / N), j = (int)(e % N);
         G[(long)i * ld + j] = (i == j ? T(1) : T(0)) - G[(long)i * ld + j];
     }
 }
 template <typename T>
-cudaError_t launch_identity_minus(cudaStream_t st, T* G, long ld, int N) {
+cudaError_t launch_identity_minus(cudaStream_t st, T* G, long ld, int N, int nbatch, long sG) {
     count_launch();
-    identity_minus_kernel<T><<<512, 256, 0, st>>>(G, ld, N);
+    identity_minus_kernel<T><<<dim3(512, nbatch), 256, 0, st>>>(G, ld, N, sG);
     return cudaGetLastError();
 }
-template cudaError_t launch_identity_minus<float>(cudaStream_t, float*, long, int);
-template cudaError_t launch_identity_minus<double>(cudaStream_t, double*, long, int);
+template cudaError_t launch_identity_minus<float>(cudaStream_t, float*, long, int, int, long);
+template cudaError_t launch_identity_minus<double>(cudaStream_t, double*, long, int, int, long);
 
 // acc2[0] += sum (Gold - Gnew)^2, acc2[1] += sum Gnew^2; Gnew is FP64 with the same ld
 template <typename T>
-__global__ void drift_kernel(const T* Gold, const double* Gnew, long ld, int N, double* acc2) {
+__global__ void drift_kernel(const T* Gold, const double* Gnew, long ld, int N, double* acc2, long sold, long snew,
+                             int adiv) {
+    Gold += blockIdx.y * sold;
+    Gnew += blockIdx.y * snew;
+    acc2 += 2 * (blockIdx.y / adiv);
     double a = 0.0, bsum = 0.0;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)N * N; e += (long)gridDim.x * blockDim.x) {
         int i = (int)(e / N), j = (int)(e % N);
@@ -282,19 +297,24 @@ __global__ void drift_kernel(const T* Gold, const double* Gnew, long ld, int N, 
     }
 }
 template <typename T>
-cudaError_t launch_drift(cudaStream_t st, const T* Gold, const T* Gnew, long ld, int N, double* acc2) {
+cudaError_t launch_drift(cudaStream_t st, const T* Gold, const T* Gnew, long ld, int N, double* acc2, int nbatch,
+                         long sold, long snew, int adiv) {
     count_launch();
-    drift_kernel<T><<<256, 256, 0, st>>>(Gold, (const double*)Gnew, ld, N, acc2);
+    drift_kernel<T><<<dim3(256, nbatch), 256, 0, st>>>(Gold, (const double*)Gnew, ld, N, acc2, sold, snew, adiv);
     return cudaGetLastError();
 }
-template cudaError_t launch_drift<float>(cudaStream_t, const float*, const float*, long, int, double*);
-
-template cudaError_t launch_drift<double>(cudaStream_t, const double*, const double*, long, int, double*);
+template cudaError_t launch_drift<float>(cudaStream_t, const float*, const float*, long, int, double*, int, long, long,
+                                         int);
+template cudaError_t launch_drift<double>(cudaStream_t, const double*, const double*, long, int, double*, int, long,
+                                          long, int);
 
 // E = sum_s tr(K A^s) + U sum_i (n_up n_dn - (n_up + n_dn)/2), A = 1 - G, K_ij = -t per bond
 template <typename T>
-__global__ void energy_kernel(const T* Gu, const T* Gd, long ld, int L, double t, double U, double* out) {
+__global__ void energy_kernel(const T* Gu0, long ld, int L, double t, double U, double* out, long gstride) {
     const int N = L * L;
+    const T* Gu = Gu0 + blockIdx.y * gstride;  // walker blockIdx.y of a group
+    const T* Gd = Gu + (size_t)N * ld;
+    out += blockIdx.y;
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         int x = i % L, y = i / L;
@@ -312,13 +332,13 @@ __global__ void energy_kernel(const T* Gu, const T* Gd, long ld, int L, double t
     if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 template <typename T>
-cudaError_t launch_energy(cudaStream_t st, const T* Gu, const T* Gd, long ld, int L, double t, double U, double* out) {
+cudaError_t launch_energy(cudaStream_t st, const T* Gu, long ld, int L, double t, double U, double* out, int nwk,
+                          long gstride) {
     count_launch();
-    energy_kernel<T><<<64, 256, 0, st>>>(Gu, Gd, ld, L, t, U, out);
+    energy_kernel<T><<<dim3(64, nwk), 256, 0, st>>>(Gu, ld, L, t, U, out, gstride);
     return cudaGetLastError();
 }
-template cudaError_t launch_energy<float>(cudaStream_t, const float*, const float*, long, int, double, double, double*);
-template cudaError_t launch_energy<double>(cudaStream_t, const double*, const double*, long, int, double, double,
-                                           double*);
+template cudaError_t launch_energy<float>(cudaStream_t, const float*, long, int, double, double, double*, int, long);
+template cudaError_t launch_energy<double>(cudaStream_t, const double*, long, int, double, double, double*, int, long);
 
 }  // namespace afq

@@ -20,16 +20,29 @@ namespace afq {
 // ---------------------------------------------------------------------------
 // uniforms of one slice visit
 // ---------------------------------------------------------------------------
-__global__ void uniforms_kernel(uint64_t seed, uint64_t walker, uint64_t visit, int count, double* u) {
+__global__ void uniforms_kernel(uint64_t seed, const int* gid, uint64_t visit, int count, double* u) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < count) u[j] = philox_uniform(seed, walker, visit, (uint64_t)j);
+    const int w = blockIdx.y;
+    if (j < count) u[(size_t)w * count + j] = philox_uniform(seed, (uint64_t)gid[w], visit, (uint64_t)j);
 }
 
-cudaError_t launch_uniforms(cudaStream_t st, uint64_t seed, uint64_t walker, uint64_t visit, int count,
-                            double* u) {
+cudaError_t launch_uniforms(cudaStream_t st, uint64_t seed, const int* gid, uint64_t visit, int count, double* u,
+                            int nwk) {
     count_launch();
-    uniforms_kernel<<<(count + 255) / 256, 256, 0, st>>>(seed, walker, visit, count, u);
+    uniforms_kernel<<<dim3((count + 255) / 256, nwk), 256, 0, st>>>(seed, gid, visit, count, u);
     return cudaGetLastError();
+}
+
+// Buffers of walker j of a group (see Batch).
+template <typename T>
+__device__ __forceinline__ WindowBufs wb_walker(WindowBufs wb, int j, int N);
+__device__ __forceinline__ SliceOut so_walker(SliceOut so, int j, int N) {
+    so.dec += (size_t)j * 2 * N;
+    so.ratio += (size_t)j * 2 * N;
+    so.stats += (size_t)j * 8;
+    so.maxr += j;
+    if (so.sign) so.sign += j;
+    return so;
 }
 
 __device__ __forceinline__ double hs_log_scalar(const SiteParams& sp, int x) {
@@ -180,6 +193,19 @@ template int window_max<float>();
 template int window_max<double>();
 
 template <typename T>
+__device__ __forceinline__ WindowBufs wb_walker(WindowBufs wb, int j, int N) {
+    constexpr int NW = WinCap<T>::NW;
+    wb.m += j;
+    wb.idx += (size_t)j * NW;
+    wb.dtot += (size_t)j * 2 * NW;
+    wb.Wm = (T*)wb.Wm + (size_t)j * 2 * NW * NW;
+    if (wb.Wx) wb.Wx = (T*)wb.Wx + (size_t)j * 2 * NW * NW;
+    wb.X = (T*)wb.X + (size_t)j * 2 * N * NW;
+    wb.Y = (T*)wb.Y + (size_t)j * 2 * NW * N;  // this walker's Yraw (the products follow all walkers' Yraw)
+    return wb;
+}
+
+template <typename T>
 static size_t window_smem(int n) {
     size_t P = (size_t)n + 1;
     size_t g = 2 * (size_t)n * P * sizeof(T);  // Gs[2][n][n+1]
@@ -309,16 +335,25 @@ __device__ __forceinline__ void window_w(const T* Gs, int n, int P, const int* i
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict__ Gu, const T* __restrict__ Gd,
-                                                             int8_t* xl_g, const double* u,
-                                                             const uint8_t* replay, SiteParams sp, SliceOut so,
-                                                             int s0, int n, int nb, WindowBufs wb, const T* blk,
-                                                             int* err) {
+__global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict__ Gu0, int8_t* xl0, const double* u0,
+                                                             const uint8_t* replay0, SiteParams sp, SliceOut so0,
+                                                             int s0, int n, int nb, WindowBufs wb0, const T* blk0,
+                                                             int* err, Batch bt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = n + 1;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int N = sp.N;
     const long ld = sp.ld;
+    // walker blockIdx.x of the group
+    const int wk = blockIdx.x;
+    const T* __restrict__ Gu = Gu0 + (size_t)wk * bt.gstride;
+    const T* __restrict__ Gd = Gu + (size_t)N * ld;
+    int8_t* xl_g = xl0 + (size_t)wk * bt.xstride;
+    const double* u = u0 + (size_t)wk * 2 * N;
+    const uint8_t* replay = replay0 ? replay0 + (size_t)wk * 2 * N : nullptr;
+    const SliceOut so = so_walker(so0, wk, N);
+    const WindowBufs wb = wb_walker<T>(wb0, wk, N);
+    const T* blk = blk0 ? blk0 + (size_t)wk * 2 * WinCap<T>::NW * WinCap<T>::NW : nullptr;
     T* Gs = (T*)smem_raw;  // [2][n][P]
     size_t off = 2 * (size_t)n * P * sizeof(T);
     T* S1 = (T*)(smem_raw + off);  // [2][NBMAX][NBMAX+1]
@@ -650,7 +685,8 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
 template <typename T>
 cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T* Gd, int8_t* xl,
                                 const double* u, const uint8_t* replay, const SiteParams& sp, SliceOut so,
-                                int s0, int n, int nb, WindowBufs wb, const T* blk, int* err) {
+                                int s0, int n, int nb, WindowBufs wb, const T* blk, int* err, Batch bt) {
+    (void)Gd;  // spin down follows spin up (N x ld) in every walker's G
     size_t shm = window_smem<T>(n);
     static bool attr_set[2] = {false, false};
     const int mi = (mode == AFQMC_MODE_DELAYED) ? 0 : 1;
@@ -662,13 +698,14 @@ cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T*
         if (e != cudaSuccess) return e;
         attr_set[mi] = true;
     }
+    if (bt.nwk < 1) bt.nwk = 1;
     count_launch();
     if (mode == AFQMC_MODE_DELAYED)
-        window_kernel<T, AFQMC_MODE_DELAYED><<<1, WIN_THREADS, shm, st>>>(Gu, Gd, xl, u, replay, sp, so, s0, n, nb,
-                                                                          wb, blk, err);
+        window_kernel<T, AFQMC_MODE_DELAYED><<<bt.nwk, WIN_THREADS, shm, st>>>(Gu, xl, u, replay, sp, so, s0, n, nb,
+                                                                              wb, blk, err, bt);
     else
-        window_kernel<T, AFQMC_MODE_BLOCKFB><<<1, WIN_THREADS, shm, st>>>(Gu, Gd, xl, u, replay, sp, so, s0, n, nb,
-                                                                          wb, blk, err);
+        window_kernel<T, AFQMC_MODE_BLOCKFB><<<bt.nwk, WIN_THREADS, shm, st>>>(Gu, xl, u, replay, sp, so, s0, n, nb,
+                                                                              wb, blk, err, bt);
     return cudaGetLastError();
 }
 
@@ -676,11 +713,13 @@ cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T*
 // flush: X = G[:, I], Yraw = E_I^T - G[I, :], Y = W Yraw, G <- G - X Y
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void gather_kernel(const T* __restrict__ Gu, const T* __restrict__ Gd, long ld, int N, WindowBufs wb,
-                              int NW) {
+__global__ void gather_kernel(const T* __restrict__ Gu0, long ld, int N, WindowBufs wb0, int NW, long gstride,
+                              long sstride) {
+    const int wk = blockIdx.z;
+    const WindowBufs wb = wb_walker<T>(wb0, wk, N);
     const int m = *wb.m;
     const int s = blockIdx.y;
-    const T* G = s ? Gd : Gu;
+    const T* G = Gu0 + (size_t)wk * gstride + (long)s * sstride;
     T* X = (T*)wb.X + (size_t)s * N * NW;
     T* Y = (T*)wb.Y + (size_t)s * NW * N;  // Yraw here; the product with W comes after
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * N; e += gridDim.x * blockDim.x) {
@@ -697,7 +736,7 @@ cudaError_t launch_flush(cudaStream_t st, T* Gu, T* Gd, const SiteParams& sp, Wi
     const int N = sp.N;
     const int NWC = WinCap<T>::NW;
     count_launch();
-    gather_kernel<T><<<dim3(256, 2), 256, 0, st>>>(Gu, Gd, sp.ld, N, wb, NWC);
+    gather_kernel<T><<<dim3(256, 2, 1), 256, 0, st>>>(Gu, sp.ld, N, wb, NWC, 0, (long)(Gd - Gu));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // Y <- W * Yraw  (rows >= m are never read); written into the X buffer's tail? use a separate pass:
@@ -728,10 +767,10 @@ template cudaError_t launch_local<double>(cudaStream_t, double*, double*, int8_t
                                           const SiteParams&, SliceOut, double*, double*, GridBar*, int*, int);
 template cudaError_t launch_window_chain<float>(cudaStream_t, int, const float*, const float*, int8_t*,
                                                 const double*, const uint8_t*, const SiteParams&, SliceOut, int,
-                                                int, int, WindowBufs, const float*, int*);
+                                                int, int, WindowBufs, const float*, int*, Batch);
 template cudaError_t launch_window_chain<double>(cudaStream_t, int, const double*, const double*, int8_t*,
                                                  const double*, const uint8_t*, const SiteParams&, SliceOut, int,
-                                                 int, int, WindowBufs, const double*, int*);
+                                                 int, int, WindowBufs, const double*, int*, Batch);
 // ---------------------------------------------------------------------------
 // Pipelined flush of one window.
 //
@@ -750,14 +789,16 @@ template cudaError_t launch_window_chain<double>(cudaStream_t, int, const double
 // NB_ROWS, spin); each CTA forms (X_blk W) and then (X_blk W) Yraw_n for its rows.
 constexpr int NB_ROWS = 16;
 template <typename T>
-__global__ void __launch_bounds__(256) next_block_kernel(const T* __restrict__ Gu, const T* __restrict__ Gd, long ld,
-                                                         WindowBufs wb, int sn, int nn, T* snap) {
+__global__ void __launch_bounds__(256) next_block_kernel(const T* __restrict__ Gu0, long ld, int N, WindowBufs wb0,
+                                                         int sn, int nn, T* snap0, long gstride) {
     constexpr int NW = WinCap<T>::NW, PP = NW + 1;
+    const int wk = blockIdx.z;
+    const WindowBufs wb = wb_walker<T>(wb0, wk, N);
     const int m = *wb.m;
     const int s = blockIdx.y, a0 = blockIdx.x * NB_ROWS, tid = threadIdx.x, nt = blockDim.x;
     const int ra = min(NB_ROWS, nn - a0);
-    const T* G = s ? Gd : Gu;
-    T* out = snap + (size_t)s * NW * NW;
+    const T* G = Gu0 + (size_t)wk * gstride + (size_t)s * N * ld;
+    T* out = snap0 + (size_t)wk * 2 * NW * NW + (size_t)s * NW * NW;
     extern __shared__ __align__(16) unsigned char nb_smem[];
     T* Ws = (T*)nb_smem;         // [m][PP]
     T* Ys = Ws + NW * PP;        // [m][PP]   Yraw_n
@@ -794,7 +835,8 @@ __global__ void __launch_bounds__(256) next_block_kernel(const T* __restrict__ G
 
 template <typename T>
 cudaError_t launch_next_block(cudaStream_t st, const T* Gu, const T* Gd, const SiteParams& sp, WindowBufs wb, int sn,
-                              int nn, T* snap) {
+                              int nn, T* snap, Batch bt) {
+    (void)Gd;
     constexpr int NW = WinCap<T>::NW;
     const size_t shm = (2 * (size_t)NW + 2 * NB_ROWS) * (NW + 1) * sizeof(T);
     static bool attr = false;
@@ -805,51 +847,56 @@ cudaError_t launch_next_block(cudaStream_t st, const T* Gu, const T* Gd, const S
         attr = true;
     }
     count_launch();
-    const int nbx = nn > 0 ? (nn + NB_ROWS - 1) / NB_ROWS : 1;
-    next_block_kernel<T><<<dim3(nbx, 2), 256, shm, st>>>(Gu, Gd, sp.ld, wb, sn, nn, snap);
+    const int nbx = (nn + NB_ROWS - 1) / NB_ROWS;
+    next_block_kernel<T><<<dim3(nbx, 2, bt.nwk), 256, shm, st>>>(Gu, sp.ld, sp.N, wb, sn, nn, snap, bt.gstride);
     return cudaGetLastError();
 }
 
 // The panel gathers X = G[:, I], Yraw = E_I^T - G[I, :] and Y' = W Yraw of one window.
 template <typename T>
-cudaError_t launch_flush_panels(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw) {
+cudaError_t launch_flush_panels(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw, Batch bt) {
+    (void)Gd;
     constexpr int NW = WinCap<T>::NW;
     const int N = sp.N;
     count_launch();
-    gather_kernel<T><<<dim3(256, 2), 256, 0, sf>>>(Gu, Gd, sp.ld, N, wb, NW);
+    gather_kernel<T><<<dim3(256, 2, bt.nwk), 256, 0, sf>>>(Gu, sp.ld, N, wb, NW, bt.gstride, (long)N * sp.ld);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    GemmArgs<T> g;  // Y' = W Yraw
-    g.M = nw; g.N = N; g.K = nw; g.Kdev = wb.m;
+    GemmArgs<T> g;  // Y' = W Yraw, batch (walker, spin)
+    g.M = nw; g.N = N; g.K = nw; g.Kdev = wb.m; g.kdiv = 2;
     g.A = (const T*)wb.Wx; g.lda = NW; g.sA = (long)NW * NW;
     g.B = (const T*)wb.Y; g.ldb = N; g.sB = (long)NW * N;
-    g.C = (T*)wb.Y + (size_t)2 * NW * N; g.ldc = N; g.sC = (long)NW * N;
-    g.batch = 2;
+    g.C = (T*)wb.Y + (size_t)2 * bt.nwk * NW * N; g.ldc = N; g.sC = (long)NW * N;
+    g.batch = 2 * bt.nwk;
     return gemm<T>(sf, g);
 }
 
 // G <- G - X Y' (the N x N rank-m product, after launch_flush_panels on the same stream).
 template <typename T>
-cudaError_t launch_flush_gemm(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw) {
+cudaError_t launch_flush_gemm(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw, Batch bt) {
+    (void)Gd;
     constexpr int NW = WinCap<T>::NW;
     const int N = sp.N;
     GemmArgs<T> h;
-    h.M = N; h.N = N; h.K = nw; h.Kdev = wb.m;
+    h.M = N; h.N = N; h.K = nw; h.Kdev = wb.m; h.kdiv = 2;
     h.A = (const T*)wb.X; h.lda = NW; h.sA = (long)N * NW;
-    h.B = (const T*)wb.Y + (size_t)2 * NW * N; h.ldb = N; h.sB = (long)NW * N;
-    h.C = Gu; h.ldc = sp.ld; h.sC = (long)(Gd - Gu);
+    h.B = (const T*)wb.Y + (size_t)2 * bt.nwk * NW * N; h.ldb = N; h.sB = (long)NW * N;
+    h.C = Gu; h.ldc = sp.ld; h.sC = (long)N * sp.ld;
     h.alpha = T(-1); h.beta = T(1);
-    h.batch = 2;
+    h.batch = 2 * bt.nwk;
     return gemm<T>(sf, h);
 }
-template cudaError_t launch_flush_panels<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int);
-template cudaError_t launch_flush_panels<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs, int);
-template cudaError_t launch_flush_gemm<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int);
-template cudaError_t launch_flush_gemm<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs, int);
+template cudaError_t launch_flush_panels<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int,
+                                               Batch);
+template cudaError_t launch_flush_panels<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs, int,
+                                                Batch);
+template cudaError_t launch_flush_gemm<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int, Batch);
+template cudaError_t launch_flush_gemm<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs, int,
+                                              Batch);
 template cudaError_t launch_next_block<float>(cudaStream_t, const float*, const float*, const SiteParams&, WindowBufs,
-                                              int, int, float*);
+                                              int, int, float*, Batch);
 template cudaError_t launch_next_block<double>(cudaStream_t, const double*, const double*, const SiteParams&,
-                                               WindowBufs, int, int, double*);
+                                               WindowBufs, int, int, double*, Batch);
 template cudaError_t launch_flush<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int);
 template cudaError_t launch_flush<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs, int);
 

@@ -257,3 +257,53 @@ def test_apply_flips_matches_oracle(precision, tol):
     with pytest.raises(afqmc.AfqmcError):
         afqmc.afqmc_apply_flips(precision, N, N - 1, Gd_dev[0].data_ptr(), Gd_dev[1].data_ptr(), s_dev.data_ptr(),
                                 d_dev.data_ptr(), len(sites), stream)
+
+
+@pytest.mark.parametrize("mode,k,nb", [("delayed", 5, 4), ("local", 16, 4), ("blockfb", 16, 3)])
+def test_mixed_walker_groups_fp64(mode, k, nb):
+    """Walkers of mixed lattices in one context.  Walkers with the same lattice form a group
+    whose every launch covers them all; each walker still takes its own oracle's decisions
+    (its uniforms are keyed by its index in the context) and G agrees to 1e-10 after every
+    slice of a forward and a backward sweep, recomputes included."""
+    Ls = [4, 6, 4, 6, 4]
+    M, stab, U, seed = 8, 4, 4.0, 21
+    ns_of = {4: 7, 6: 16}
+    walkers, Ps, Xs = [], [], []
+    for wi, L in enumerate(Ls):
+        P = inputs.trial_state(L, L, ns_of[L])
+        X = inputs.initial_fields(M, L * L, seed=seed, walker=wi)
+        Ps.append(np.concatenate([P.ravel(), P.ravel()]))
+        Xs.append(X.ravel())
+        walkers.append(oracle.Walker(oracle.Model(L, L, 1.0, U, 0.05, M), P, P, X))
+    ns = [ns_of[L] for L in Ls]
+    with afqmc.Context(M, U=U, precision="fp64", stab_every=stab, seed=seed) as ctx:
+        ctx.init_walkers(Ls, ns, ns, np.concatenate(Ps), np.concatenate(Xs))
+        for wi, w in enumerate(walkers):
+            for s in range(2):
+                assert rel(ctx.G(wi, s), w.G[s]) < FP64_TOL
+        order = [(ell, +1) for ell in range(1, M + 1)] + [(ell, -1) for ell in range(M, 0, -1)]
+        for visit, (ell, d) in enumerate(order):
+            ctx.sweep_slice(ell, d, mode, k=k, nb=nb)
+            for wi, w in enumerate(walkers):
+                N = Ls[wi] ** 2
+                dec_o, _, extra = w.sweep_slice(ell, d, mode, inputs.uniforms(seed, wi, visit, 2 * N), k=k, nb=nb)
+                dec_g = ctx.decisions(wi)
+                if mode == "blockfb":
+                    nblocks = (N + nb - 1) // nb
+                    np.testing.assert_array_equal(dec_g[N:N + nblocks], dec_o)
+                else:
+                    np.testing.assert_array_equal(dec_g[:N], dec_o, err_msg=f"walker {wi} slice {ell} dir {d}")
+                for s in range(2):
+                    r = rel(ctx.G(wi, s), w.G[s])
+                    assert r < FP64_TOL, f"walker {wi} slice {ell} dir {d} spin {s}: {r}"
+            if walkers[0].pos % stab == 0:
+                ctx.recompute_G()
+                for wi, w in enumerate(walkers):
+                    w.recompute(stab)
+                    for s in range(2):
+                        assert rel(ctx.G(wi, s), w.G[s]) < FP64_TOL
+        e, sg = ctx.measure_energy()
+        for wi, w in enumerate(walkers):
+            np.testing.assert_array_equal(ctx.fields(wi), w.x)
+            assert abs(e[wi] - w.m.energy(w.G[0], w.G[1])) < 1e-9 * max(1.0, abs(e[wi]))
+            assert sg[wi] == w.sign
