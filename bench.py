@@ -39,6 +39,7 @@ NS = inputs.n_sigma_for(L, FILLING)
 N = L * L
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 CPU_SLICES = 16  # oracle slice-steps of the cpu_baseline sample (about 10 s on 16 Arm cores)
+BATCH_WALKERS = 256
 
 
 def parse():
@@ -52,6 +53,7 @@ def parse():
     ap.add_argument("--cmp-slices", type=int, default=20, help="slices of the local / block-FB samples")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the mixed walker population leg")
     ap.add_argument("--gemm", default="tc3", choices=["tc3", "simt", "tf32"],
                     help="FP32 GEMM engine: tcgen05 three-term TF32 split, FP32 SIMT, or one TF32 pass")
     return ap.parse_args()
@@ -269,12 +271,30 @@ def main():
     kernels = kernel_rooflines(prof, args.gemm, pk, pk_src, args.steps)
     roof = dict(kernels[0]) if kernels else None
 
+    # ---------------- the same sweep with CUDA-graph replay (profiling off) ----------------
+    ctx.set_graphs(True)
+    sweep("delayed", args.k, args.nb)  # captures every slice-step
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        sweep("delayed", args.k, args.nb)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    ms_graph = g0.elapsed_time(g1) / args.steps
+    ctx.set_graphs(False)
+    graphs = {"value": updates_per_step / (ms_graph / 1e3), "ms_per_step": ms_graph,
+              "note": "the same sweeps with every slice-step replayed from a captured CUDA graph (profiling off)"}
+
     # ---------------- end to end through the C ABI with host buffers ----------------
     e2e = None
     if not args.no_e2e:
         e2e = end_to_end(afqmc, torch, stream, args, seed, rank)
 
     ctx.close()
+    batch = None
+    if not args.no_batch:
+        batch = batched_population(afqmc, torch, stream, args, seed)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, secs = run_oracle_sample(CPU_SLICES, args.k)
@@ -306,6 +326,8 @@ def main():
             "clocks": clocks,
             "gpu_launches": launches,
             "e2e": e2e,
+            "cuda_graphs": graphs,
+            "batched_population": batch,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -386,6 +408,62 @@ def kernel_rooflines(prof, gemm, pk, pk_src, steps):
                     "peak_source": "measured copy bandwidth (of %s); G (2 x 10 MB) is L2-resident" % pk_src})
     out.sort(key=lambda r: -r["ms_per_step"])
     return out
+
+
+def batched_population(afqmc, torch, stream, args, seed):
+    """The mixed walker population: BATCH_WALKERS walkers with L drawn uniformly from
+    {8, 12, 16, 24} (seeded), U/t = 4, filling 0.875, M = 40, FP32 bulk with the FP64 recompute every
+    10 slices, delayed update.  Walkers of one lattice form a group whose launches cover them all;
+    the groups run concurrently.  k is tuned over {16, 32, 64} on one warm-up sweep each; the
+    timed sweeps run with and without CUDA-graph replay."""
+    Ls = inputs.batch_lattices(BATCH_WALKERS, seed=5)
+    Mb, Sb, Ub = 40, 10, 4.0
+    ns = [inputs.n_sigma_for(int(L), FILLING) for L in Ls]
+    P = np.concatenate([np.concatenate([inputs.trial_state(int(L), int(L), n).ravel()] * 2)
+                        for L, n in zip(Ls, ns)])
+    X = np.concatenate([inputs.initial_fields(Mb, int(L) * int(L), seed=seed, walker=wi).ravel()
+                        for wi, L in enumerate(Ls)])
+    ctx = afqmc.Context(Mb, dtau=DTAU, U=Ub, t=T_HOP, precision="fp32", stab_every=Sb, seed=seed, gemm=args.gemm)
+    ctx.init_walkers([int(L) for L in Ls], ns, ns, P, X, stream=stream)
+    order = [(l, +1) for l in range(1, Mb + 1)] + [(l, -1) for l in range(Mb, 0, -1)]
+
+    def sweep(k):
+        for (ell, d) in order:
+            ctx.sweep_slice(ell, d, "delayed", k=k, stream=stream)
+            pos = ell if d > 0 else ell - 1
+            if pos % Sb == 0:
+                afqmc.afqmc_recompute_G(ctx.h, None, stream)
+
+    def timed(k, n):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            sweep(k)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    tune = {}
+    for k in (16, 32, 64):
+        sweep(k)  # first sweep with this k (warm-up)
+        tune[k] = timed(k, 1)
+    kbest = min(tune, key=tune.get)
+    upd = sum(int(L) * int(L) for L in Ls) * 2 * Mb
+    ms_direct = timed(kbest, 2)
+    ctx.set_graphs(True)
+    sweep(kbest)  # captures every slice
+    ms_graph = timed(kbest, 2)
+    ctx.close()
+    sizes = {int(L): int((Ls == L).sum()) for L in sorted(set(Ls.tolist()))}
+    return {"metric": "field updates/s, mixed walker population, delayed update", "unit": UNIT,
+            "walkers": int(len(Ls)), "walkers_per_L": sizes, "M": Mb, "U": Ub, "stab_every": Sb,
+            "k_tuning_ms_per_sweep": tune, "k": kbest,
+            "value": upd / (min(ms_direct, ms_graph) / 1e3),
+            "direct_launches": {"value": upd / (ms_direct / 1e3), "ms_per_sweep": ms_direct},
+            "cuda_graphs": {"value": upd / (ms_graph / 1e3), "ms_per_sweep": ms_graph},
+            "note": "one sweep = 2M slice-steps of every walker + 8 FP64 recomputes; walkers of one lattice "
+                    "share every launch, groups run on concurrent streams"}
 
 
 def end_to_end(afqmc, torch, stream, args, seed, rank):

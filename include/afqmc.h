@@ -199,6 +199,14 @@ int afqmc_apply_flips_noalloc(int precision, int N, long long ld, void* G_up, vo
 #define AFQMC_NPHASE 11
 /* on != 0 enables profiling and clears the accumulators; on == 0 disables it. */
 int afqmc_set_profiling(afqmc_ctx* ctx, int on);
+
+/* CUDA graphs (a deployment option, not in the paper).  With on != 0, afqmc_sweep_slice captures
+ * each walker group's slice -- uniforms, wrap, window chain, the flush stream's panels and
+ * products -- the first time it meets a given (slice, dir, mode, k, nb), and replays the graph
+ * from then on: one graph launch per group and slice.  Calls with replay decisions or with
+ * profiling on run uncaptured.  The uniforms stay fresh because the visit counter that keys them
+ * lives on the device.  Returns AFQMC_ERR_ARG for a NULL ctx. */
+int afqmc_set_graphs(afqmc_ctx* ctx, int on);
 /* Sync the last stream and return, per phase, the summed device milliseconds, the number of
  * bracketed intervals, and the number of library kernels launched in that phase.  Each array
  * has AFQMC_NPHASE entries; any pointer may be NULL. */

@@ -25,7 +25,7 @@ GEMMS = {"tc3": 0, "simt": 1, "tf32": 2}
 
 EXPORTS = ["afqmc_create", "afqmc_destroy", "afqmc_init_walkers", "afqmc_sweep_slice", "afqmc_recompute_G",
            "afqmc_measure_energy", "afqmc_get_G", "afqmc_set_G", "afqmc_get_fields", "afqmc_get_decisions",
-           "afqmc_get_ratios", "afqmc_get_info", "afqmc_debug_uniforms", "afqmc_set_profiling",
+           "afqmc_get_ratios", "afqmc_get_info", "afqmc_debug_uniforms", "afqmc_set_profiling", "afqmc_set_graphs",
            "afqmc_get_profile", "afqmc_launch_count", "afqmc_apply_flips", "afqmc_apply_flips_noalloc",
            "afqmc_debug_gemm", "afqmc_strerror"]
 PHASES = ["prep", "wrap", "local", "chain", "flush", "recompute", "elim", "wrap_gemm", "flush_gemm", "lu_o",
@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH):
     lib.afqmc_get_info.argtypes = [vp, ctypes.c_int, ip, ip, ip, ip, ip]
     lib.afqmc_debug_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, dp]
     lib.afqmc_set_profiling.argtypes = [vp, ctypes.c_int]
+    lib.afqmc_set_graphs.argtypes = [vp, ctypes.c_int]
     lib.afqmc_get_profile.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.afqmc_launch_count.argtypes = []
     lib.afqmc_apply_flips.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, vp, vp, vp, vp, ctypes.c_int, vp]
@@ -209,6 +210,10 @@ def afqmc_set_profiling(ctx, on):
     _ck("afqmc_set_profiling", load().afqmc_set_profiling(ctx, int(on)))
 
 
+def afqmc_set_graphs(ctx, on):
+    _ck("afqmc_set_graphs", load().afqmc_set_graphs(ctx, int(on)))
+
+
 def afqmc_get_profile(ctx):
     n = len(PHASES)
     ms = np.zeros(n)
@@ -291,6 +296,9 @@ class Context:
 
     def set_profiling(self, on=True):
         afqmc_set_profiling(self.h, on)
+
+    def set_graphs(self, on):
+        afqmc_set_graphs(self.h, on)
 
     def profile(self):
         return afqmc_get_profile(self.h)

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
 #include <vector>
 
 #include "internal.h"
@@ -70,7 +71,15 @@ struct Walker {
     void* Y[2] = {nullptr, nullptr};
     void* snap[2] = {nullptr, nullptr};
     cudaStream_t sf = nullptr;  // flush stream
+    cudaStream_t sm = nullptr;  // the group's main stream (forked from the caller's stream)
     cudaEvent_t ev_chain[2] = {nullptr, nullptr}, ev_prod[2] = {nullptr, nullptr}, ev_done = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    unsigned long long* visit_d = nullptr;  // device visit counter (keys the uniforms)
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        long long launches = 0;
+    };
+    std::map<long long, Graph> graphs;  // captured slices by (slice, dir, mode, k, nb)
     double* URs = nullptr;   // [nwk][2][nst][N x nsm]: right factors at every recompute point
     double* ULs = nullptr;   // [nwk][2][nst][nsm x N]: left factors
     double* Ucur = nullptr;  // [nwk][2][N x nsm]: the factors being propagated
@@ -114,6 +123,7 @@ struct afqmc_ctx {
     double lam = 0.0, c[2] = {0.0, 0.0};
     int sticky = 0;
     int nsm = 0;
+    bool graphs = false;  // replay captured slices (afqmc_set_graphs)
     std::vector<Lattice*> lats;
     std::vector<Walker*> w;                        // walker groups
     std::vector<std::pair<int, int>> wmap;         // context walker -> (group, member)
@@ -557,7 +567,12 @@ int afqmc_destroy(afqmc_ctx* ctx) {
             if (w->ev_prod[q]) cudaEventDestroy(w->ev_prod[q]);
         }
         if (w->ev_done) cudaEventDestroy(w->ev_done);
+        if (w->ev_fork) cudaEventDestroy(w->ev_fork);
+        if (w->ev_join) cudaEventDestroy(w->ev_join);
+        for (auto& kv : w->graphs)
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         if (w->sf) cudaStreamDestroy(w->sf);
+        if (w->sm) cudaStreamDestroy(w->sm);
         delete w;
     }
     for (void* p : ctx->allocs) cudaFree(p);
@@ -665,11 +680,16 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
             CK(cudaEventCreateWithFlags(&w->ev_prod[q], cudaEventDisableTiming));
         }
         CK(cudaEventCreateWithFlags(&w->ev_done, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming));
         {
             int lo = 0, hi = 0;
             CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
             CK(cudaStreamCreateWithPriority(&w->sf, cudaStreamNonBlocking, lo));
+            CK(cudaStreamCreateWithFlags(&w->sm, cudaStreamNonBlocking));
         }
+        CK(dalloc(A, &w->visit_d, sizeof(unsigned long long)));
+        CK(cudaMemsetAsync(w->visit_d, 0, sizeof(unsigned long long), st));
         CK(dalloc(A, &w->URs, (size_t)nwk * 2 * nst * N * nsm * 8));
         CK(dalloc(A, &w->ULs, (size_t)nwk * 2 * nst * N * nsm * 8));
         CK(dalloc(A, &w->Ucur, (size_t)nwk * 2 * N * nsm * 8));
@@ -780,7 +800,7 @@ static int sweep_impl(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int k,
     const int nb2 = 2 * nwk;  // (walker, spin) batch of the G products
     {
         PhaseScope ps(ctx, AFQMC_PHASE_PREP, st);
-        CK(launch_uniforms(st, ctx->p.seed, w->gid_d, w->visit, 2 * N, w->u, nwk));
+        CK(launch_uniforms(st, ctx->p.seed, w->gid_d, w->visit_d, 2 * N, w->u, nwk));
         CK(cudaMemsetAsync(w->stats, 0, (size_t)nwk * 8 * sizeof(int), st));
         CK(cudaMemsetAsync(w->maxr, 0, (size_t)nwk * 8, st));
         if (replay) {
@@ -955,6 +975,7 @@ static int sweep_impl(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int k,
         CK(cudaStreamWaitEvent(st, w->ev_done, 0));
     }
     if (dir < 0) CK(wrap(-1));
+    CK(launch_bump(st, w->visit_d));
     return AFQMC_OK;
 }
 
@@ -977,11 +998,53 @@ int afqmc_sweep_slice(afqmc_ctx* ctx, int slice, int dir, int mode, int k, int n
     }
     cudaStream_t st = (cudaStream_t)stream;
     ctx->last = st;
+    // Groups run concurrently, each on its own stream forked from (and joined back into) st.
+    // With graphs on, a group's slice is captured once per (slice, dir, mode, k, nb) and then
+    // replayed: every launch of the slice, the flush stream's included, in one graph launch.
+    const bool fork = ctx->w.size() > 1;
+    const bool use_graph = ctx->graphs && !replay && !ctx->prof.on;
     for (int gi = 0; gi < (int)ctx->w.size(); ++gi) {
-        rc = f64 ? sweep_impl<double>(ctx, gi, slice, dir, mode, k, nb, replay, st)
-                 : sweep_impl<float>(ctx, gi, slice, dir, mode, k, nb, replay, st);
-        if (rc) return rc;
         Walker* w = ctx->w[gi];
+        cudaStream_t sg = st;
+        if (fork || use_graph) {
+            CK(cudaEventRecord(w->ev_fork, st));
+            CK(cudaStreamWaitEvent(w->sm, w->ev_fork, 0));
+            sg = w->sm;
+        }
+        if (use_graph) {
+            const long long key = ((((long long)slice * 4 + (dir > 0 ? 1 : 0)) * 4 + mode) * 512 + k) * 64 + nb;
+            auto it = w->graphs.find(key);
+            if (it == w->graphs.end()) {
+                Walker::Graph gr;
+                cudaGraph_t graph = nullptr;
+                const long long l0 = afqmc_launch_count();
+                CK(cudaStreamBeginCapture(sg, cudaStreamCaptureModeRelaxed));
+                rc = f64 ? sweep_impl<double>(ctx, gi, slice, dir, mode, k, nb, nullptr, sg)
+                         : sweep_impl<float>(ctx, gi, slice, dir, mode, k, nb, nullptr, sg);
+                cudaError_t ec = cudaStreamEndCapture(sg, &graph);
+                if (rc) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return rc;
+                }
+                CK(ec);
+                gr.launches = afqmc_launch_count() - l0;
+                cudaError_t ei = cudaGraphInstantiate(&gr.exec, graph, 0);
+                cudaGraphDestroy(graph);
+                CK(ei);
+                it = w->graphs.emplace(key, gr).first;
+            } else {
+                count_launch((int)it->second.launches);
+            }
+            CK(cudaGraphLaunch(it->second.exec, sg));
+        } else {
+            rc = f64 ? sweep_impl<double>(ctx, gi, slice, dir, mode, k, nb, replay, sg)
+                     : sweep_impl<float>(ctx, gi, slice, dir, mode, k, nb, replay, sg);
+            if (rc) return rc;
+        }
+        if (sg != st) {
+            CK(cudaEventRecord(w->ev_join, sg));
+            CK(cudaStreamWaitEvent(st, w->ev_join, 0));
+        }
         w->pos = (dir > 0) ? slice : slice - 1;
         w->last_dir = dir;
         w->visit++;
@@ -1021,8 +1084,15 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     ctx->last = st;
     const bool f64 = ctx->p.precision == AFQMC_PREC_FP64;
+    const bool fork = ctx->w.size() > 1;
+    cudaStream_t st0 = st;
     for (auto* w : ctx->w) {
         const int j = w->pos / S;
+        if (fork) {  // groups recompute concurrently
+            CK(cudaEventRecord(w->ev_fork, st0));
+            CK(cudaStreamWaitEvent(w->sm, w->ev_fork, 0));
+            st = w->sm;
+        }
         PhaseScope ps(ctx, AFQMC_PHASE_RECOMPUTE, st);
         CK(cudaMemsetAsync(w->acc2, 0, (size_t)w->nwk * 16, st));
         // the factors of the current position: one side from the stacks, the other propagated
@@ -1047,7 +1117,12 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
             else CK(finish_G<float>(w, st, fac_R(w, j), grp[gi][0], ng[gi], true));
         }
         w->need_recompute = false;
+        if (fork) {
+            CK(cudaEventRecord(w->ev_join, st));
+            CK(cudaStreamWaitEvent(st0, w->ev_join, 0));
+        }
     }
+    st = st0;
     if (rel_drift) {
         CK(cudaStreamSynchronize(st));
         for (auto* w : ctx->w) {
@@ -1171,6 +1246,12 @@ int afqmc_get_info(afqmc_ctx* ctx, int walker, int* N, int* n_up, int* n_dn, int
     if (n_dn) *n_dn = w->ns[1];
     if (slice) *slice = w->pos;
     if (dir) *dir = w->last_dir;
+    return AFQMC_OK;
+}
+
+int afqmc_set_graphs(afqmc_ctx* ctx, int on) {
+    if (!ctx) return AFQMC_ERR_ARG;
+    ctx->graphs = on != 0;
     return AFQMC_OK;
 }
 

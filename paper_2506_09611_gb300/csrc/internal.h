@@ -165,9 +165,11 @@ struct SliceOut {      // device-side per-walker outputs of one slice
     double* sign;      // walker sign (updated in place)
 };
 
-// u[j][0..count) for the walkers gid[j] (device array), j < nwk.
-cudaError_t launch_uniforms(cudaStream_t st, uint64_t seed, const int* gid, uint64_t visit, int count, double* u,
-                            int nwk);
+// u[j][0..count) for the walkers gid[j] (device array), j < nwk, at the device visit counter;
+// launch_bump advances the counter by one.
+cudaError_t launch_uniforms(cudaStream_t st, uint64_t seed, const int* gid, const unsigned long long* visit, int count,
+                            double* u, int nwk);
+cudaError_t launch_bump(cudaStream_t st, unsigned long long* visit);
 
 template <typename T>
 cudaError_t launch_local(cudaStream_t st, T* Gu, T* Gd, int8_t* xl, const double* u, const uint8_t* replay,

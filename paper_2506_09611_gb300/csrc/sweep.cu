@@ -20,16 +20,25 @@ namespace afq {
 // ---------------------------------------------------------------------------
 // uniforms of one slice visit
 // ---------------------------------------------------------------------------
-__global__ void uniforms_kernel(uint64_t seed, const int* gid, uint64_t visit, int count, double* u) {
+// The visit counter lives on the device so that a captured slice replays with fresh uniforms.
+__global__ void uniforms_kernel(uint64_t seed, const int* gid, const unsigned long long* visit, int count, double* u) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int w = blockIdx.y;
-    if (j < count) u[(size_t)w * count + j] = philox_uniform(seed, (uint64_t)gid[w], visit, (uint64_t)j);
+    if (j < count) u[(size_t)w * count + j] = philox_uniform(seed, (uint64_t)gid[w], (uint64_t)*visit, (uint64_t)j);
 }
 
-cudaError_t launch_uniforms(cudaStream_t st, uint64_t seed, const int* gid, uint64_t visit, int count, double* u,
-                            int nwk) {
+__global__ void bump_kernel(unsigned long long* visit) { *visit += 1ULL; }
+
+cudaError_t launch_uniforms(cudaStream_t st, uint64_t seed, const int* gid, const unsigned long long* visit, int count,
+                            double* u, int nwk) {
     count_launch();
     uniforms_kernel<<<dim3((count + 255) / 256, nwk), 256, 0, st>>>(seed, gid, visit, count, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bump(cudaStream_t st, unsigned long long* visit) {
+    count_launch();
+    bump_kernel<<<1, 1, 0, st>>>(visit);
     return cudaGetLastError();
 }
 

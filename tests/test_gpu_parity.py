@@ -307,3 +307,39 @@ def test_mixed_walker_groups_fp64(mode, k, nb):
             np.testing.assert_array_equal(ctx.fields(wi), w.x)
             assert abs(e[wi] - w.m.energy(w.G[0], w.G[1])) < 1e-9 * max(1.0, abs(e[wi]))
             assert sg[wi] == w.sign
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_graph_replay_matches_direct_launches(precision):
+    """With CUDA graphs on, every slice is captured on its first visit and replayed after that
+    (the second sweep below is all replays); decisions and G are bit-identical to direct launches
+    because the uniforms are keyed by a device-side visit counter."""
+    Ls = [4, 6, 4]
+    M, stab, seed = 4, 2, 9
+    ns_of = {4: 7, 6: 16}
+    P = np.concatenate([np.concatenate([inputs.trial_state(L, L, ns_of[L]).ravel()] * 2) for L in Ls])
+    X = np.concatenate([inputs.initial_fields(M, L * L, seed=seed, walker=wi).ravel() for wi, L in enumerate(Ls)])
+    ns = [ns_of[L] for L in Ls]
+    ctxs = [afqmc.Context(M, U=4.0, precision=precision, stab_every=stab, seed=seed) for _ in range(2)]
+    try:
+        for c in ctxs:
+            c.init_walkers(Ls, ns, ns, P, X)
+        ctxs[1].set_graphs(True)
+        order = [(ell, +1) for ell in range(1, M + 1)] + [(ell, -1) for ell in range(M, 0, -1)]
+        for sweep in range(2):
+            for (ell, d) in order:
+                for c in ctxs:
+                    c.sweep_slice(ell, d, "delayed", k=8)
+                for wi in range(len(Ls)):
+                    np.testing.assert_array_equal(ctxs[0].decisions(wi), ctxs[1].decisions(wi))
+                    for s in range(2):
+                        np.testing.assert_array_equal(ctxs[0].G(wi, s), ctxs[1].G(wi, s))
+                pos = ell if d > 0 else ell - 1
+                if pos % stab == 0:
+                    for c in ctxs:
+                        c.recompute_G()
+        for wi in range(len(Ls)):
+            np.testing.assert_array_equal(ctxs[0].fields(wi), ctxs[1].fields(wi))
+    finally:
+        for c in ctxs:
+            c.close()
