@@ -320,14 +320,12 @@ static cudaError_t launch_panel(cudaStream_t st, const LuArgs& a, int j0, int nb
     return cudaLaunchKernelEx(&cfg, lu_panel_kernel<CS>, a, j0, nbk);
 }
 
-// Cluster size by the number of rows: enough CTAs that a panel step's FP64 work per SM stays
-// small, few enough that many matrices of a walker group factor at once.  16-CTA clusters are
-// used only if two of them fit on the device at once (else 8).
-static int lu_cluster_size(const LuArgs& a) {
+// Cluster size: enough CTAs per matrix that a panel step's FP64 work per SM stays small, few
+// enough that all nmat clusters of a batch are resident together (about two CTAs per SM).
+// Rows per CTA stay at or below 512 (shared memory); 16-CTA clusters are used only if two of
+// them fit on the device at once (else 8).
+static int lu_big_cluster(const LuArgs& a) {
     static int big = 0;
-    if (a.m <= 96) return 2;
-    if (a.m <= 256) return 4;
-    if (a.m <= 512) return 8;
     if (big) return big;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(32);
@@ -350,6 +348,16 @@ static int lu_cluster_size(const LuArgs& a) {
     return big;
 }
 
+static int lu_cluster_size(const LuArgs& a) {
+    int nsm = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int cs = 1;
+    while (cs < 16 && (a.m + cs - 1) / cs > 64 && cs * a.nmat <= nsm) cs *= 2;  // spread rows
+    while (cs < 16 && (a.m + cs - 1) / cs > 512) cs *= 2;                              // shared memory
+    if (cs == 16) cs = lu_big_cluster(a);
+    return cs;
+}
+
 cudaError_t launch_lu(cudaStream_t st, const LuArgs& a) {
     if (a.m < a.n || a.n < 1 || a.nmat < 1 || a.pstride < a.m) return cudaErrorInvalidValue;
     const int cs = lu_cluster_size(a);
@@ -359,6 +367,7 @@ cudaError_t launch_lu(cudaStream_t st, const LuArgs& a) {
     for (int j0 = 0; j0 < a.n; j0 += LU_NB) {
         const int nbk = (a.n - j0 < LU_NB) ? a.n - j0 : LU_NB;
         switch (cs) {
+            case 1: e = launch_panel<1>(st, a, j0, nbk); break;
             case 2: e = launch_panel<2>(st, a, j0, nbk); break;
             case 4: e = launch_panel<4>(st, a, j0, nbk); break;
             case 8: e = launch_panel<8>(st, a, j0, nbk); break;
