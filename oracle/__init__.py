@@ -5,7 +5,8 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
 library never calls it and shares no code with it.
 
 The arithmetic lives in ``afqmc_oracle.c`` (plain C, FP64, plain loops, its
-own LU and Householder QR).  This module only compiles it with gcc and
+own LU and Householder QR) and ``soc_oracle.c`` (the spin-orbit-coupled model
+in double complex, its own complex LU and Gram-Schmidt).  This module only compiles it with gcc and
 marshals numpy arrays through ctypes.  Every function cites the paper's
 passage it follows (see the C source for the formulas).
 
@@ -19,6 +20,20 @@ Parity status of each function (what pins it in ``tests/test_oracle_pins.py``):
   blockfb_slice   -- brute-force stripped force bias, det ratio, exact detailed
                      balance on an enumerable toy, from-scratch G
   energy          -- U=0 closed form; Fock-space brute force on <= 3 sites
+
+Spin-orbit-coupled model (``soc_oracle.c``, Appendix A), pinned in
+``tests/test_soc_oracle_pins.py``:
+  H0, expH        -- bond-by-bond real-space H0; split dispersion eps_k +- |L_k|; expm
+  HS spin-y       -- the decoupling identity and the one-body rotation on the Fock space
+  green_scratch   -- plain products of expm propagators; projector invariants; the weight of a
+                     time-reversal-invariant trial state is real positive
+  wrap            -- from-scratch G at the next / previous slice
+  local_slice     -- every ratio equals the brute-force weight ratio; from-scratch G
+  delayed_slice   -- identical decisions, ratios and G to the local update
+  block_force_bias-- finite difference of the stripped overlap (fixes the index order)
+  blockfb_slice   -- brute-force ratio with the proposal ratio; from-scratch G; exact detailed
+                     balance on an enumerable 2 x 2 lattice
+  energy          -- U=0 closed form; Fock-space brute force with a random spin-mixing H0
 """
 from __future__ import annotations
 
@@ -30,7 +45,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "afqmc_oracle.c")
+_SRCS = [os.path.join(_HERE, "afqmc_oracle.c"), os.path.join(_HERE, "soc_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -49,13 +64,21 @@ class Params(ctypes.Structure):
     ]
 
 
+class SocParams(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_int), ("N", ctypes.c_int),
+        ("t", ctypes.c_double), ("lam", ctypes.c_double), ("U", ctypes.c_double), ("dtau", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+    ]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc into oracle/_build/liboracle.so."""
     with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(s) for s in _SRCS):
             os.makedirs(_BUILD, exist_ok=True)
             tmp = _LIB + f".{os.getpid()}.tmp"
-            subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11", "-o", tmp, _SRC, "-lm"])
+            subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11", "-o", tmp, *_SRCS, "-lm"])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -82,6 +105,20 @@ def _load():
         lib.or_blockfb_slice.argtypes = [pp, dp, dp, i8p, dp, dp, ctypes.c_int, u8p, i8p, dp, u8p, dp, dp]
         lib.or_energy.argtypes = [pp, dp, dp, dp]
         lib.or_energy.restype = ctypes.c_double
+        sp = ctypes.POINTER(SocParams)
+        vp = ctypes.c_void_p
+        lib.soc_setup.argtypes = [sp]
+        lib.soc_H0.argtypes = [sp, vp]
+        lib.soc_expH.argtypes = [sp, ctypes.c_double, vp]
+        lib.soc_green_scratch.argtypes = [sp, vp, i8p, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          vp, dp, vp]
+        lib.soc_green_scratch.restype = ctypes.c_int
+        lib.soc_wrap.argtypes = [sp, vp, vp, i8p, vp, ctypes.c_int]
+        lib.soc_local_slice.argtypes = [sp, vp, i8p, dp, u8p, u8p, dp]
+        lib.soc_delayed_slice.argtypes = [sp, vp, i8p, dp, ctypes.c_int, u8p, u8p, dp]
+        lib.soc_block_force_bias.argtypes = [sp, vp, i8p, ctypes.c_int, ctypes.c_int, vp]
+        lib.soc_blockfb_slice.argtypes = [sp, vp, i8p, dp, dp, ctypes.c_int, u8p, i8p, dp, u8p, dp]
+        lib.soc_energy.argtypes = [sp, vp, vp, dp]
         _lib = lib
     return _lib
 
@@ -268,5 +305,158 @@ class Walker:
         self.sign *= sg
         if direction < 0:
             self.G = [m.wrap(self.G[s], xn, s, -1) for s in range(2)]
+            self.pos = ell - 1
+        return dec, ratio, extra
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _vp(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+class SocModel:
+    """Spin-orbit-coupled Hubbard model on the 2N x 2N complex orbital basis (Appendix A,
+    Eq. 2DSocHubbard): orbitals i (spin up) and N + i (spin down).  E = exp(-dtau H0),
+    Einv = exp(+dtau H0) from the closed-form 2 x 2 exponential per momentum."""
+
+    def __init__(self, L, t, lam, U, dtau, M):
+        self.p = SocParams(L=L, N=L * L, t=t, lam=lam, U=U, dtau=dtau)
+        if _load().soc_setup(ctypes.byref(self.p)) != 0:
+            raise ValueError("the spin-y decoupling needs U <= 0")
+        self.N = L * L
+        self.M = M
+        self.H0 = np.zeros((2 * self.N, 2 * self.N), np.complex128)
+        _load().soc_H0(ctypes.byref(self.p), _vp(self.H0))
+        self.E = self.expH(dtau)
+        self.Einv = self.expH(-dtau)
+
+    @property
+    def gamma(self):
+        return self.p.gamma
+
+    def expH(self, tau):
+        E = np.zeros((2 * self.N, 2 * self.N), np.complex128)
+        _load().soc_expH(ctypes.byref(self.p), float(tau), _vp(E))
+        return E
+
+    def green_scratch(self, x, P, ell, stab=10):
+        """G(ell) = 1 - R (L R)^{-1} L from scratch; returns (G, log|det L R|, phase of det L R)."""
+        x = np.ascontiguousarray(x, dtype=np.int8)
+        P = _c128(P)
+        G = np.zeros((2 * self.N, 2 * self.N), np.complex128)
+        la = np.zeros(1)
+        ph = np.zeros(1, np.complex128)
+        rc = _load().soc_green_scratch(ctypes.byref(self.p), _vp(self.E), _i8(x), self.M, _vp(P), P.shape[1], ell,
+                                       stab, _vp(G), _d(la), _vp(ph))
+        if rc != 0:
+            raise np.linalg.LinAlgError("singular overlap")
+        return G, la[0], ph[0]
+
+    def wrap(self, G, xl, direction):
+        """Forward: G <- B_l G B_l^{-1}; backward: G <- B_l^{-1} G B_l, B_l = D(x_l) E."""
+        G = _c128(G).copy()
+        _load().soc_wrap(ctypes.byref(self.p), _vp(self.E), _vp(self.Einv),
+                         _i8(np.ascontiguousarray(xl, dtype=np.int8)), _vp(G), int(direction))
+        return G
+
+    def local_slice(self, G, xl, u, replay=None):
+        """Rank-2 local update of one slice (Eqs. DetRatioSOC, LocalSOC); returns (G, xl, dec, ratio)."""
+        N = self.N
+        G = _c128(G).copy()
+        xl = np.ascontiguousarray(xl, dtype=np.int8).copy()
+        rep = None if replay is None else np.ascontiguousarray(replay, dtype=np.uint8)
+        dec = np.zeros(N, np.uint8)
+        ratio = np.zeros(2 * N)
+        _load().soc_local_slice(ctypes.byref(self.p), _vp(G), _i8(xl), _d(_f64(u)), _u8(rep), _u8(dec), _d(ratio))
+        return G, xl, dec, ratio[0::2] + 1j * ratio[1::2]
+
+    def delayed_slice(self, G, xl, u, k, replay=None):
+        """Delayed update of one slice, windows of k sites; returns (G, xl, dec, ratio)."""
+        N = self.N
+        G = _c128(G).copy()
+        xl = np.ascontiguousarray(xl, dtype=np.int8).copy()
+        rep = None if replay is None else np.ascontiguousarray(replay, dtype=np.uint8)
+        dec = np.zeros(N, np.uint8)
+        ratio = np.zeros(2 * N)
+        _load().soc_delayed_slice(ctypes.byref(self.p), _vp(G), _i8(xl), _d(_f64(u)), int(k), _u8(rep), _u8(dec),
+                                  _d(ratio))
+        return G, xl, dec, ratio[0::2] + 1j * ratio[1::2]
+
+    def block_force_bias(self, G, xl, s0, n):
+        """Stripped spin-flip expectations obar_i of block [s0, s0 + n)."""
+        ob = np.zeros(n, np.complex128)
+        _load().soc_block_force_bias(ctypes.byref(self.p), _vp(_c128(G)),
+                                     _i8(np.ascontiguousarray(xl, dtype=np.int8)), s0, n, _vp(ob))
+        return ob
+
+    def blockfb_slice(self, G, xl, u_prop, u_acc, nb, replay=None):
+        """Block force-bias update of one slice; returns (G, xl, xprop, lam_plus, dec, ratio)."""
+        N = self.N
+        nblocks = (N + nb - 1) // nb
+        G = _c128(G).copy()
+        xl = np.ascontiguousarray(xl, dtype=np.int8).copy()
+        rep = None if replay is None else np.ascontiguousarray(replay, dtype=np.uint8)
+        xprop = np.zeros(N, np.int8)
+        lamp = np.zeros(N)
+        dec = np.zeros(nblocks, np.uint8)
+        ratio = np.zeros(2 * nblocks)
+        _load().soc_blockfb_slice(ctypes.byref(self.p), _vp(G), _i8(xl), _d(_f64(u_prop)), _d(_f64(u_acc)), int(nb),
+                                  _u8(rep), _i8(xprop), _d(lamp), _u8(dec), _d(ratio))
+        return G, xl, xprop, lamp, dec, ratio[0::2] + 1j * ratio[1::2]
+
+    def energy(self, G, H0=None):
+        """Mixed-estimator energy with the spin-coupled Wick contraction (complex); H0 defaults to
+        the model's hopping matrix."""
+        r = np.zeros(2)
+        H0 = self.H0 if H0 is None else _c128(H0)
+        _load().soc_energy(ctypes.byref(self.p), _vp(H0), _vp(_c128(G)), _d(r))
+        return complex(r[0], r[1])
+
+
+class SocWalker:
+    """One spin-coupled Markov chain driven by the oracle, in the same sweep order as ``Walker``."""
+
+    def __init__(self, model: SocModel, P, x):
+        self.m = model
+        self.P = _c128(P)
+        self.x = np.ascontiguousarray(x, dtype=np.int8).copy()
+        self.pos = 0
+        self.G = None
+        self.recompute()
+
+    def recompute(self, stab=10):
+        G, _, _ = self.m.green_scratch(self.x, self.P, self.pos, stab)
+        drift = None if self.G is None else np.linalg.norm(self.G - G) / np.linalg.norm(G)
+        self.G = G
+        return drift
+
+    def sweep_slice(self, ell, direction, mode, u, k=32, nb=4, replay=None):
+        m, N = self.m, self.m.N
+        xl = self.x[ell - 1]
+        if direction > 0:
+            assert self.pos == ell - 1
+            self.G = m.wrap(self.G, xl, +1)
+            self.pos = ell
+        else:
+            assert self.pos == ell
+        if mode == "local":
+            G, xn, dec, ratio = m.local_slice(self.G, xl, u[:N], replay)
+            extra = {}
+        elif mode == "delayed":
+            G, xn, dec, ratio = m.delayed_slice(self.G, xl, u[:N], k, replay)
+            extra = {}
+        elif mode == "blockfb":
+            nblocks = (N + nb - 1) // nb
+            G, xn, xprop, lamp, dec, ratio = m.blockfb_slice(self.G, xl, u[:N], u[N:N + nblocks], nb, replay)
+            extra = {"xprop": xprop, "lam_plus": lamp}
+        else:
+            raise ValueError(mode)
+        self.G = G
+        self.x[ell - 1] = xn
+        if direction < 0:
+            self.G = m.wrap(self.G, xn, -1)
             self.pos = ell - 1
         return dec, ratio, extra

@@ -15,6 +15,11 @@ the inputs the paper's workloads are made of (Sec. II.A, II.B):
   library draws the same stream on the device with its own Philox; a GPU test
   checks the two bit for bit.
 * ``batch_lattices`` -- the mixed-size walker population.
+* ``soc_hamiltonian`` / ``soc_trial_state`` -- the spin-orbit-coupled model of
+  Appendix A on the 2N orbital basis (i spin up, N + i spin down) and its trial
+  state: the lowest N_e orbitals of H0 + 1e-6 * S with S a fixed random
+  time-reversal-invariant Hermitian matrix, so the occupied set is closed under
+  time reversal (the condition for a sign-free weight with the spin-y fields).
 """
 from __future__ import annotations
 
@@ -72,3 +77,40 @@ def batch_lattices(n_walkers: int, seed: int = 5, sizes=(8, 12, 16, 24)) -> np.n
 def n_sigma_for(L: int, filling: float) -> int:
     """Particles per spin at total filling n = N_e / N_s (N_up = N_dn)."""
     return int(round(filling * L * L / 2))
+
+
+def soc_hamiltonian(L: int, t: float = 1.0, lam: float = 0.5) -> np.ndarray:
+    """Real-space 2N x 2N H0 of the Rashba-coupled square lattice (Eq. 2DSocHubbard), written bond
+    by bond: -t per nearest-neighbour bond in each spin block, and the spin-flip hopping
+    (H0)[(dn, r), (up, r')] = -i lam for r' = r + y, +i lam for r' = r - y, -lam for r' = r + x,
+    +lam for r' = r - x, with the up-down block its Hermitian conjugate."""
+    N = L * L
+    H = np.zeros((2 * N, 2 * N), np.complex128)
+    H[:N, :N] = hopping_matrix(L, L, t)
+    H[N:, N:] = hopping_matrix(L, L, t)
+    for y in range(L):
+        for x in range(L):
+            r = x + L * y
+            for (dx, dy, amp) in ((0, 1, -1j * lam), (0, -1, 1j * lam), (1, 0, -lam), (-1, 0, lam)):
+                rp = (x + dx) % L + L * ((y + dy) % L)
+                H[N + r, rp] += amp
+                H[rp, N + r] += np.conj(amp)
+    return H
+
+
+def soc_trs_perturbation(N: int, seed: int = 0) -> np.ndarray:
+    """A fixed random Hermitian S = [[A, B], [-conj(B), conj(A)]] (A Hermitian, B antisymmetric):
+    the general time-reversal-invariant one-body matrix on the 2N orbitals."""
+    rng = np.random.Generator(np.random.Philox(key=np.array([seed, 0x50C], dtype=np.uint64)))
+    A = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    A = 0.5 * (A + A.conj().T)
+    B = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    B = 0.5 * (B - B.T)
+    return np.block([[A, B], [-B.conj(), A.conj()]])
+
+
+def soc_trial_state(L: int, n_e: int, t: float = 1.0, lam: float = 0.5, seed: int = 0) -> np.ndarray:
+    """Lowest n_e orbitals (2N x n_e, complex, orthonormal columns) of H0 + 1e-6 S."""
+    H = soc_hamiltonian(L, t, lam) + 1e-6 * soc_trs_perturbation(L * L, seed)
+    w, v = np.linalg.eigh(H)
+    return np.ascontiguousarray(v[:, :n_e])

@@ -91,3 +91,87 @@ def fock_energy(K, U, Ru, Lu, Rd, Ld):
         nd = cd[i + N] @ cs[i + N]
         H += U * (nu @ nd - 0.5 * (nu + nd))
     return float(psi_l @ H @ psi_r) / float(psi_l @ psi_r)
+
+
+# ---------------- spin-orbit-coupled model (Appendix A) ----------------
+
+def soc_HI(gamma, xl):
+    """Exponent matrix of B_I(x_l) on the 2N orbitals (Eq. BIOpForSy):
+    gamma x_i (c+_{i,up} c_{i,dn} - c+_{i,dn} c_{i,up}) has entries +gamma x_i at (up i, dn i) and
+    -gamma x_i at (dn i, up i)."""
+    N = xl.shape[0]
+    H = np.zeros((2 * N, 2 * N))
+    for i in range(N):
+        H[i, N + i] = gamma * xl[i]
+        H[N + i, i] = -gamma * xl[i]
+    return H
+
+
+def soc_B(E, gamma, xl):
+    return scipy.linalg.expm(soc_HI(gamma, xl.astype(np.float64))) @ E
+
+
+def soc_products(E, gamma, X, P, ell):
+    M = X.shape[0]
+    R = P.copy()
+    for j in range(1, ell + 1):
+        R = soc_B(E, gamma, X[j - 1]) @ R
+    L = P.conj().T.copy()
+    for j in range(M, ell, -1):
+        L = L @ soc_B(E, gamma, X[j - 1])
+    return R, L
+
+
+def soc_green(E, gamma, X, P, ell):
+    R, L = soc_products(E, gamma, X, P, ell)
+    return np.eye(E.shape[0]) - R @ np.linalg.solve(L @ R, L)
+
+
+def soc_overlap(E, gamma, X, P):
+    """det(P^+ B_M ... B_1 P): the configuration weight up to the uniform prior."""
+    R, L = soc_products(E, gamma, X, P, 0)
+    return np.linalg.det(L @ R)
+
+
+def fock_ops(nm):
+    """Annihilation operators of nm fermion modes in the occupation basis (Jordan-Wigner)."""
+    dim = 1 << nm
+    cs = []
+    for q in range(nm):
+        C = np.zeros((dim, dim))
+        for st in range(dim):
+            if st >> q & 1:
+                C[st ^ (1 << q), st] = (-1) ** bin(st & ((1 << q) - 1)).count("1")
+        cs.append(C)
+    return cs
+
+
+def soc_fock_energy(H0, U, R, L):
+    """<psi_l| H |psi_r> / <psi_l|psi_r> on the Fock space of the 2N orbitals, with
+    H = c+ H0 c + U sum_i (n_iu n_id - (n_iu + n_id)/2), |psi_r> = prod_m (c+ R)_m |0> and
+    <psi_l| the bra whose orbitals are the rows of L."""
+    nm = H0.shape[0]
+    N = nm // 2
+    cs = fock_ops(nm)
+    cd = [C.T for C in cs]
+    vac = np.zeros(1 << nm, np.complex128)
+    vac[0] = 1.0
+
+    def ket(V):
+        v = vac.copy()
+        for m in range(V.shape[1]):
+            v = sum(V[a, m] * cd[a] for a in range(nm)) @ v
+        return v
+
+    psi_r = ket(R)
+    bra = ket(L.conj().T).conj()
+    H = np.zeros((1 << nm, 1 << nm), np.complex128)
+    for a in range(nm):
+        for b in range(nm):
+            if H0[a, b] != 0:
+                H += H0[a, b] * cd[a] @ cs[b]
+    for i in range(N):
+        nu = cd[i] @ cs[i]
+        nd = cd[N + i] @ cs[N + i]
+        H += U * (nu @ nd - 0.5 * (nu + nd))
+    return complex(bra @ H @ psi_r / (bra @ psi_r))
