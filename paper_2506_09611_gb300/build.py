@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libafqmc.so")
-SOURCES = ["abi.cu", "sweep.cu", "gemm.cu", "setup.cu", "flips.cu", "tc_gemm.cu", "lu.cu"]
+SOURCES = ["abi.cu", "sweep.cu", "gemm.cu", "setup.cu", "flips.cu", "tc_gemm.cu", "lu.cu", "soc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
@@ -24,7 +24,7 @@ def _nvcc():
 
 def _deps():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [
-        os.path.join(HERE, "..", "include", "afqmc.h")]
+        os.path.join(HERE, "..", "include", "afqmc.h"), os.path.join(HERE, "..", "include", "afqmc_soc.h")]
 
 
 def _compile(src, extra):

@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs<T> g) {
     const T* cs = g.cs ? g.cs + z * g.scs : nullptr;
     const T* bs = g.bs ? g.bs + z * g.sbs : nullptr;
     const int K = g.Kdev ? min(g.Kdev[g.kdiv > 0 ? z / g.kdiv : 0], g.K) : g.K;
+    if (K <= 0 && g.beta == T(1) && g.cs == nullptr && g.rs == nullptr) return;  // C unchanged
 
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN + 1];

@@ -114,7 +114,7 @@ cudaError_t launch_lu_unit_rows(cudaStream_t st, const LuArgs& a);
 cudaError_t launch_lu_sign(cudaStream_t st, const LuArgs& a, int parity, double* sign_out, int* visited);
 // Z = O^{-1} B for the O factored by launch_lu (ns x ns, leading dimension ldl, matrix b at
 // LU0 + b ostride with pivots perm0 + b pstride), B (ns x N) at B0 + j wstride + q sstride
-// (b = j ng + q) and Z (ns x N) at Z0 + b zstride.
+// (b = j ng + q), row stride ldb (0: N), and Z (ns x N) at Z0 + b zstride.
 struct SolveArgs {
     const double* LU0 = nullptr;
     long ostride = 0;
@@ -126,6 +126,7 @@ struct SolveArgs {
     double* Z0 = nullptr;
     long zstride = 0;
     long ldl = 0;
+    long ldb = 0;  // row stride of B (0: N)
     int ns = 0, N = 0, nmat = 1;
 };
 cudaError_t launch_lu_solve(cudaStream_t st, const SolveArgs& a);

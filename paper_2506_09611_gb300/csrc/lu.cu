@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(SolveArgs a) {
     const double* B = a.B0 + (long)(mat / a.ng) * a.wstride + (long)(mat % a.ng) * a.sstride;
     double* Z = a.Z0 + (long)mat * a.zstride;
     const int ns = a.ns, N = a.N;
-    const long ldl = a.ldl;
+    const long ldl = a.ldl, ldb = a.ldb ? a.ldb : N;
     const int c0 = blockIdx.x * SV_COLS, nc = min(SV_COLS, N - c0);
     const int tid = threadIdx.x, nt = blockDim.x;
     extern __shared__ __align__(16) double sv_smem[];
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(SolveArgs a) {
     __syncthreads();
     for (int e = tid; e < ns * SV_COLS; e += nt) {
         const int j = e / SV_COLS, c = e - j * SV_COLS;
-        y[j * SV_YP + c] = (c < nc) ? B[(long)sp[j] * N + c0 + c] : 0.0;
+        y[j * SV_YP + c] = (c < nc) ? B[(long)sp[j] * ldb + c0 + c] : 0.0;
     }
     for (int j = tid; j < ns; j += nt) rinv[j] = 1.0 / LU[(long)sp[j] * ldl + j];
     __syncthreads();

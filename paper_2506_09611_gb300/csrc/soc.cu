@@ -1,0 +1,1682 @@
+// soc.cu -- the spin-orbit-coupled sweep (Appendix A): the complex Green's function of the 2N
+// orbitals (i spin up, N + i spin down), spin-y auxiliary fields acting as real 2 x 2 rotations
+// on the pairs (i, N + i), rank-2 updates per site.
+//
+// Layout.  A complex matrix with C columns is stored "row-split": row r holds the real parts of
+// its C entries, padded to ldz, then the imaginary parts, padded to ldz (2 ldz elements per row).
+// The bulk G of walker j is 2N rows of 2 ldz elements in the bulk precision T.  With that layout
+// a product X C by a constant complex C is one real product with the realified
+//   C~ = [[Re C, Im C], [-Im C, Re C]]   (2 ldz x 2 ldz),
+// and a product E S is the real product [Re E | Im E] . [[Re S, Im S], [-Im S, Re S]], whose
+// right operand is filled from S by one copy pass.  The wrap is therefore two real GEMMs of
+// 2N x 2ldz x 2ldz (the four real products of a complex GEMM) plus the rotation pass D G D^{-1}.
+//
+// Updates.  A window of n sites holds the 2n x 2n block of G on its orbitals (ordered site by
+// site: up, down) in shared memory.  Delayed / local: the sites are tested one after another on
+// that block (ratio R = det(1 + delta A_SS), Eqs. DetRatioSOC, LocalSOC) and accepted sites update
+// the block by the rank-2 formula.  Block force bias: the stripped spin-flip expectations come
+// from (1 + Delta_s) (1 + A_bb Delta_s)^{-1} A_bb of the block, the flipped set F is proposed
+// jointly and tested with det(1 + A_FF Delta_F).  Either way the window ends with
+//   W = Delta_F (1 + A_FF Delta_F)^{-1}   (in-place Gauss-Jordan with 2 x 2 pivot blocks; the pivot
+// determinants are the successive ratios, non-zero for accepted moves) and the full G takes the
+// rank-2m product  G <- G - (G[:, F] W)(E_F^T - G[F, :])  as real GEMMs.
+//
+// FP64 recompute.  The factors U_R (2N x n_e) and U_L^+ are carried realified, as 4N x 2n_e real
+// matrices (rows: real parts, then imaginary parts); the column space of the realified factor
+// determines G exactly, so the realified factor is re-orthonormalised by the blocked pivoted LU
+// of lu.cu like the spin-decoupled factors.  Propagation applies B_l = D(x_l) exp(-dtau H0) to
+// each column in shared memory through the lattice Fourier transform (exp(-dtau H0) is the 2 x 2
+// block e^{-dtau h_k} per momentum), in FP64.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/afqmc_soc.h"
+#include "internal.h"
+
+namespace afq {
+namespace {
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+struct cx {
+    T r, i;
+};
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cmk(T r, T i) {
+    cx<T> z;
+    z.r = r;
+    z.i = i;
+    return z;
+}
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return cmk(a.r + b.r, a.i + b.i); }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return cmk(a.r - b.r, a.i - b.i); }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+    return cmk(a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r);
+}
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return cmk(a.r * s, a.i * s); }
+// a += b c
+template <typename T>
+__host__ __device__ __forceinline__ void cfma(cx<T>& a, cx<T> b, cx<T> c) {
+    a.r = fma(b.r, c.r, fma(-b.i, c.i, a.r));
+    a.i = fma(b.r, c.i, fma(b.i, c.r, a.i));
+}
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cinv(cx<T> a) {
+    const T d = a.r * a.r + a.i * a.i;
+    return cmk(a.r / d, -a.i / d);
+}
+
+// 2 x 2 complex block, row-major
+template <typename T>
+struct c22 {
+    cx<T> a[2][2];
+};
+
+// The flip of site field x (-> -x): delta = A(-2 gamma x) - 1 = [[c2m1, -x s2], [x s2, c2m1]];
+// stripping the field (x -> 0): A(-gamma x) - 1 = [[c1m1, -x s1], [x s1, c1m1]].
+struct SocConsts {
+    double c2m1, s2;  // cos(2 gamma) - 1, sin(2 gamma)
+    double c1m1, s1;  // cos(gamma) - 1, sin(gamma)
+    double gamma;
+};
+
+template <typename T>
+__device__ __forceinline__ void real_delta(double cm1, double s, int x, T d[2][2]) {
+    d[0][0] = (T)cm1;
+    d[1][1] = (T)cm1;
+    d[0][1] = (T)(-x * s);
+    d[1][0] = (T)(x * s);
+}
+
+// ---------------------------------------------------------------------------
+// wrap kernels
+// ---------------------------------------------------------------------------
+
+// G <- A_r G A_c on every pair block {i, N+i} x {j, N+j}, both parts: rows by A(rs gamma x_i),
+// columns by right multiplication with A(cs gamma x_j).  Forward wrap: rs = +1, cs = -1
+// (D G D^{-1}); backward: rs = -1, cs = +1.
+template <typename T>
+__global__ void soc_rot_kernel(T* G0, long ldz, int N, long gstride, const int8_t* x0, long xstride, T cg, T sg,
+                               int rs, int cs) {
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int i = blockIdx.y * 8 + threadIdx.y;
+    if (i >= N || j >= N) return;
+    T* G = G0 + (long)blockIdx.z * gstride;
+    const int8_t* x = x0 + (long)blockIdx.z * xstride;
+    const T sr = (T)(rs * x[i]) * sg, sc = (T)(cs * x[j]) * sg;
+    const long ld2 = 2 * ldz;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        T* g = G + p * ldz;
+        const T a = g[(long)i * ld2 + j], b = g[(long)i * ld2 + N + j];
+        const T c = g[(long)(N + i) * ld2 + j], d = g[(long)(N + i) * ld2 + N + j];
+        const T a1 = cg * a + sr * c, b1 = cg * b + sr * d;
+        const T c1 = cg * c - sr * a, d1 = cg * d - sr * b;
+        g[(long)i * ld2 + j] = a1 * cg - b1 * sc;
+        g[(long)i * ld2 + N + j] = a1 * sc + b1 * cg;
+        g[(long)(N + i) * ld2 + j] = c1 * cg - d1 * sc;
+        g[(long)(N + i) * ld2 + N + j] = c1 * sc + d1 * cg;
+    }
+}
+
+// Fill the second half of the realified right operand of E S.
+//   rows == 1 (row-major S~, 2 ldz x 2 ldz, rows [0, n) hold [Re S | Im S]):
+//       row ldz + r = [-Im S[r] | Re S[r]]
+//   rows == 0 (its transpose, the K-major operand of the tensor-core product, columns [0, n)
+//       hold [[Re S^T], [Im S^T]]): column ldz + m = [[-Im S^T], [Re S^T]] column m.
+template <typename T>
+__global__ void soc_realify_kernel(T* S0, long ldz, int n, long sstride, int rows) {
+    T* S = S0 + (long)blockIdx.z * sstride;
+    const long ld2 = 2 * ldz;
+    if (rows) {
+        const int r = blockIdx.y;
+        for (long c = blockIdx.x * blockDim.x + threadIdx.x; c < ld2; c += (long)gridDim.x * blockDim.x)
+            S[(ldz + r) * ld2 + c] = (c < ldz) ? -S[(long)r * ld2 + ldz + c] : S[(long)r * ld2 + c - ldz];
+    } else {
+        const long nrow = blockIdx.y;  // rows of the K-major operand: 2 ldz of them
+        for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x)
+            S[nrow * ld2 + ldz + m] = (nrow < ldz) ? -S[(nrow + ldz) * ld2 + m] : S[(nrow - ldz) * ld2 + m];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the window chain
+// ---------------------------------------------------------------------------
+struct SocWinArgs {
+    const void* G0;
+    long gstride, ldz;
+    int N;
+    int8_t* x0;
+    long xstride;        // fields of the slice, walker j at x0 + j xstride
+    const double* u0;    // uniforms, 2N per walker
+    const uint8_t* rep;  // nullable, 2N per walker
+    int mode;            // 0: site chain (local / delayed), 1: block force bias
+    int s0, n, blk;      // window sites [s0, s0 + n), block index (mode 1)
+    SocConsts k;
+    uint8_t* dec0;       // 2N per walker
+    double* ratio0;      // 2N complex per walker
+    double* lam0;        // N per walker
+    int* sites0;         // kmax per walker: accepted (flipped) sites in order
+    int kmax;
+    void* W0;            // realified W, (4 kmax)^2 per walker
+    int* Kdev;           // per walker: 4 m (real inner dimension of the flush), 0 = no flush
+    int* err;
+};
+
+template <typename T>
+__device__ __forceinline__ cx<T> g_at(const T* G, long ldz, int r, int c) {
+    return cmk(G[(long)r * 2 * ldz + c], G[(long)r * 2 * ldz + ldz + c]);
+}
+
+// In-place inverse of the 2m x 2m complex matrix M (row stride ldm) by Gauss-Jordan with the
+// 2 x 2 diagonal blocks as pivots.  det (thread 0 only) receives the product of the pivot block
+// determinants, i.e. det M.  colF: 2 * 2m complex scratch.  Returns false (on every thread) if a
+// pivot block is singular or not finite.
+template <typename T>
+__device__ bool gj_inverse_2x2(cx<T>* M, int m2, int ldm, cx<T>* colF, cx<double>* det, c22<T>* s_pi, int* s_ok) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) {
+        *s_ok = 1;
+        if (det) *det = cmk(1.0, 0.0);
+    }
+    for (int t = 0; t < m2 / 2; ++t) {
+        const int q0 = 2 * t;
+        __syncthreads();
+        if (tid == 0) {
+            const cx<T> a = M[q0 * ldm + q0], b = M[q0 * ldm + q0 + 1];
+            const cx<T> c = M[(q0 + 1) * ldm + q0], d = M[(q0 + 1) * ldm + q0 + 1];
+            const cx<T> dt = csub(cmul(a, d), cmul(b, c));
+            const T mag = dt.r * dt.r + dt.i * dt.i;
+            if (!(mag > (T)0) || !isfinite(mag)) *s_ok = 0;
+            const cx<T> di = cinv(dt);
+            s_pi->a[0][0] = cmul(d, di);
+            s_pi->a[0][1] = cmul(cmk(-b.r, -b.i), di);
+            s_pi->a[1][0] = cmul(cmk(-c.r, -c.i), di);
+            s_pi->a[1][1] = cmul(a, di);
+            if (det) *det = cmul(*det, cmk((double)dt.r, (double)dt.i));
+        }
+        __syncthreads();
+        if (!*s_ok) return false;
+        const c22<T> P = *s_pi;
+        // pivot rows: M[q0 + p][j] <- sum P[p][p'] M[q0 + p'][j] (j outside the pivot block);
+        // save the pivot columns of the other rows
+        for (int j = tid; j < m2; j += nt) {
+            if (j == q0 || j == q0 + 1) {
+                colF[2 * j] = cmk((T)0, (T)0);
+                colF[2 * j + 1] = cmk((T)0, (T)0);
+                continue;
+            }
+            const cx<T> u = M[q0 * ldm + j], v = M[(q0 + 1) * ldm + j];
+            cx<T> nu = cmul(P.a[0][0], u), nv = cmul(P.a[1][0], u);
+            cfma(nu, P.a[0][1], v);
+            cfma(nv, P.a[1][1], v);
+            M[q0 * ldm + j] = nu;
+            M[(q0 + 1) * ldm + j] = nv;
+            colF[2 * j] = M[j * ldm + q0];
+            colF[2 * j + 1] = M[j * ldm + q0 + 1];
+        }
+        __syncthreads();
+        // other rows: M[i][j] -= F_i . M[pivot rows][j];  M[i][pivot cols] = -F_i P
+        for (int e = tid; e < m2 * m2; e += nt) {
+            const int i = e / m2, j = e - i * m2;
+            if (i == q0 || i == q0 + 1) {
+                if (j == q0 || j == q0 + 1) M[i * ldm + j] = P.a[i - q0][j - q0];
+                continue;
+            }
+            const cx<T> f0 = colF[2 * i], f1 = colF[2 * i + 1];
+            if (j == q0 || j == q0 + 1) {
+                const int p = j - q0;
+                cx<T> w = cmul(f0, P.a[0][p]);
+                cfma(w, f1, P.a[1][p]);
+                M[i * ldm + j] = cmk(-w.r, -w.i);
+            } else {
+                cx<T> w = M[i * ldm + j];
+                const cx<T> nf0 = cmk(-f0.r, -f0.i), nf1 = cmk(-f1.r, -f1.i);
+                cfma(w, nf0, M[q0 * ldm + j]);
+                cfma(w, nf1, M[(q0 + 1) * ldm + j]);
+                M[i * ldm + j] = w;
+            }
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// W = Delta_F Minv as the realified, K-interleaved (4m x 4m) right operand of the flush:
+//   Wr[2q][2q'] = Re W, [2q][2q'+1] = Im W, [2q+1][2q'] = -Im W, [2q+1][2q'+1] = Re W.
+// Delta_F is block diagonal: the 2 x 2 block dl[t] of flipped site t (real).
+template <typename T>
+__device__ void write_W(const cx<T>* Minv, int m2, int ldm, const T (*dl)[2][2], T* W, int ldw) {
+    for (int e = threadIdx.x; e < m2 * m2; e += blockDim.x) {
+        const int q = e / m2, qq = e - q * m2;
+        const int t = q >> 1, p = q & 1;
+        cx<T> w = cscale(Minv[(2 * t) * ldm + qq], dl[t][p][0]);
+        const cx<T> w1 = cscale(Minv[(2 * t + 1) * ldm + qq], dl[t][p][1]);
+        w = cadd(w, w1);
+        W[(long)(2 * q) * ldw + 2 * qq] = w.r;
+        W[(long)(2 * q) * ldw + 2 * qq + 1] = w.i;
+        W[(long)(2 * q + 1) * ldw + 2 * qq] = -w.i;
+        W[(long)(2 * q + 1) * ldw + 2 * qq + 1] = w.r;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
+    extern __shared__ __align__(16) unsigned char soc_smem[];
+    const int z = blockIdx.x;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int N = a.N, n = a.n, s0 = a.s0, n2 = 2 * n;
+    const long ldz = a.ldz;
+    const T* G = (const T*)a.G0 + (long)z * a.gstride;
+    int8_t* x = a.x0 + (long)z * a.xstride;
+    const double* u = a.u0 + (long)z * 2 * N;
+    const uint8_t* rep = a.rep ? a.rep + (long)z * 2 * N : nullptr;
+    uint8_t* dec = a.dec0 + (long)z * 2 * N;
+    double* ratio = a.ratio0 + (long)z * 4 * N;
+    double* lam = a.lam0 + (long)z * N;
+    int* sites = a.sites0 + (long)z * a.kmax;
+    T* W = (T*)a.W0 + (long)z * 16 * a.kmax * a.kmax;
+    const int ldw = 4 * a.kmax;
+
+    cx<T>* Mw = (cx<T>*)soc_smem;               // (2 kmax)^2: the window block / the LU matrix
+    cx<T>* aux = Mw + 4 * a.kmax * a.kmax;      // 8 kmax: column / row snapshots, GJ scratch
+    __shared__ T s_dl[64][2][2];                // flip deltas of the flipped sites
+    __shared__ int s_site[64];
+    __shared__ int s_m, s_acc, s_ok;
+    __shared__ c22<T> s_w2, s_pi;
+    __shared__ cx<double> s_det;
+    __shared__ cx<T> s_ob[64];
+    auto orb = [&](int q) { return (q & 1) ? N + s0 + (q >> 1) : s0 + (q >> 1); };
+
+    if (tid == 0) s_m = 0;
+    if (a.mode == 0) {
+        // ---- sites one after another on the 2n x 2n block ----
+        for (int e = tid; e < n2 * n2; e += nt) {
+            const int r = e / n2, c = e - r * n2;
+            Mw[e] = g_at(G, ldz, orb(r), orb(c));
+        }
+        __syncthreads();
+        for (int t = 0; t < n; ++t) {
+            const int i = s0 + t;
+            if (tid == 0) {
+                const int xi = x[i];
+                T dl[2][2];
+                real_delta<T>(a.k.c2m1, a.k.s2, xi, dl);
+                cx<T> A[2][2];
+                for (int p = 0; p < 2; ++p)
+                    for (int q = 0; q < 2; ++q) {
+                        const cx<T> g = Mw[(2 * t + p) * n2 + 2 * t + q];
+                        A[p][q] = cmk((p == q ? (T)1 : (T)0) - g.r, -g.i);
+                    }
+                // m1 = 1 + delta A (ratio), m2 = 1 + A delta (for W)
+                cx<T> m1[2][2], m2[2][2];
+                for (int p = 0; p < 2; ++p)
+                    for (int q = 0; q < 2; ++q) {
+                        m1[p][q] = cmk(p == q ? (T)1 : (T)0, (T)0);
+                        m2[p][q] = m1[p][q];
+                        for (int r = 0; r < 2; ++r) {
+                            m1[p][q] = cadd(m1[p][q], cscale(A[r][q], dl[p][r]));
+                            m2[p][q] = cadd(m2[p][q], cscale(A[p][r], dl[r][q]));
+                        }
+                    }
+                const cx<T> R = csub(cmul(m1[0][0], m1[1][1]), cmul(m1[0][1], m1[1][0]));
+                const cx<T> d2 = csub(cmul(m2[0][0], m2[1][1]), cmul(m2[0][1], m2[1][0]));
+                const double absR = sqrt((double)R.r * R.r + (double)R.i * R.i);
+                ratio[2 * i] = (double)R.r;
+                ratio[2 * i + 1] = (double)R.i;
+                if (!isfinite(absR)) set_err(a.err, DEV_NUMERIC);
+                const int acc = rep ? (rep[i] != 0) : (u[i] < absR);
+                dec[i] = (uint8_t)acc;
+                s_acc = acc && isfinite(absR) && absR > 0.0;
+                if (s_acc) {
+                    const cx<T> di = cinv(d2);
+                    const cx<T> inv[2][2] = {{cmul(m2[1][1], di), cmul(cmk(-m2[0][1].r, -m2[0][1].i), di)},
+                                             {cmul(cmk(-m2[1][0].r, -m2[1][0].i), di), cmul(m2[0][0], di)}};
+                    for (int p = 0; p < 2; ++p)
+                        for (int q = 0; q < 2; ++q)
+                            s_w2.a[p][q] = cadd(cscale(inv[0][q], dl[p][0]), cscale(inv[1][q], dl[p][1]));
+                    const int mm = s_m;
+                    for (int p = 0; p < 2; ++p)
+                        for (int q = 0; q < 2; ++q) s_dl[mm][p][q] = dl[p][q];
+                    s_site[mm] = i;
+                    sites[mm] = i;
+                    s_m = mm + 1;
+                    x[i] = (int8_t)(-xi);
+                }
+            }
+            __syncthreads();
+            if (!s_acc) continue;
+            // snapshot: (G[:, S] W) and (E_S^T - G[S, :]) on the block
+            cx<T>* colW = aux;           // [n2][2]
+            cx<T>* rowY = aux + 2 * n2;  // [2][n2]
+            const c22<T> w2 = s_w2;
+            for (int r = tid; r < n2; r += nt) {
+                const cx<T> g0 = Mw[r * n2 + 2 * t], g1 = Mw[r * n2 + 2 * t + 1];
+                for (int q = 0; q < 2; ++q) {
+                    cx<T> v = cmul(g0, w2.a[0][q]);
+                    cfma(v, g1, w2.a[1][q]);
+                    colW[2 * r + q] = v;
+                }
+                for (int p = 0; p < 2; ++p) {
+                    const cx<T> g = Mw[(2 * t + p) * n2 + r];
+                    rowY[p * n2 + r] = cmk((r == 2 * t + p ? (T)1 : (T)0) - g.r, -g.i);
+                }
+            }
+            __syncthreads();
+            for (int e = tid; e < n2 * n2; e += nt) {
+                const int r = e / n2, c = e - r * n2;
+                cx<T> v = Mw[e];
+                const cx<T> c0 = colW[2 * r], c1 = colW[2 * r + 1];
+                cfma(v, cmk(-c0.r, -c0.i), rowY[c]);
+                cfma(v, cmk(-c1.r, -c1.i), rowY[n2 + c]);
+                Mw[e] = v;
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        const int m = s_m;
+        if (m == 0) {
+            if (tid == 0) a.Kdev[z] = 0;
+            return;
+        }
+        // M = 1 + A_FF Delta_F from the window's starting G (the bulk G is unchanged so far);
+        // the flipped sites' old fields are -x now
+        const int m2 = 2 * m;
+        for (int e = tid; e < m2 * m2; e += nt) {
+            const int q = e / m2, qq = e - q * m2;
+            const int t2 = qq >> 1, p2 = qq & 1;
+            const int rq = (q & 1) ? N + s_site[q >> 1] : s_site[q >> 1];
+            cx<T> v = cmk((q == qq) ? (T)1 : (T)0, (T)0);
+            for (int p = 0; p < 2; ++p) {
+                const int cq = p ? N + s_site[t2] : s_site[t2];
+                const cx<T> g = g_at(G, ldz, rq, cq);
+                const cx<T> Aq = cmk((rq == cq ? (T)1 : (T)0) - g.r, -g.i);
+                v = cadd(v, cscale(Aq, s_dl[t2][p][p2]));
+            }
+            Mw[e] = v;
+        }
+        if (!gj_inverse_2x2<T>(Mw, m2, m2, aux, nullptr, &s_pi, &s_ok)) {
+            if (tid == 0) {
+                set_err(a.err, DEV_NUMERIC);
+                a.Kdev[z] = 0;
+            }
+            return;
+        }
+        write_W<T>(Mw, m2, m2, s_dl, W, ldw);
+        if (tid == 0) a.Kdev[z] = 2 * m2;
+        return;
+    }
+
+    // ---- block force bias over the block [s0, s0 + n) ----
+    // stripped matrix Mb = 1 + A_bb Delta_s, Delta_s = A(-gamma x) - 1 per site
+    for (int e = tid; e < n2 * n2; e += nt) {
+        const int q = e / n2, qq = e - q * n2;
+        const int t2 = qq >> 1, p2 = qq & 1;
+        T ds[2][2];
+        real_delta<T>(a.k.c1m1, a.k.s1, x[s0 + t2], ds);
+        cx<T> v = cmk((q == qq) ? (T)1 : (T)0, (T)0);
+        for (int p = 0; p < 2; ++p) {
+            const int cq = 2 * t2 + p;
+            const cx<T> g = g_at(G, ldz, orb(q), orb(cq));
+            const cx<T> Aq = cmk((q == cq ? (T)1 : (T)0) - g.r, -g.i);
+            v = cadd(v, cscale(Aq, ds[p][p2]));
+        }
+        Mw[e] = v;
+    }
+    if (!gj_inverse_2x2<T>(Mw, n2, n2, aux, nullptr, &s_pi, &s_ok)) {
+        if (tid == 0) {
+            set_err(a.err, DEV_NUMERIC);
+            a.Kdev[z] = 0;
+        }
+        return;
+    }
+    // (Minv A)[2t + p][2t + q] for the four entries of every site: one warp per (t, p, q)
+    {
+        const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+        for (int e = wid; e < 4 * n; e += nw) {
+            const int t = e >> 2, p = (e >> 1) & 1, q = e & 1;
+            const int row = 2 * t + p, col = 2 * t + q;
+            cx<T> acc = cmk((T)0, (T)0);
+            for (int r = lane; r < n2; r += 32) {
+                const cx<T> g = g_at(G, ldz, orb(r), orb(col));
+                const cx<T> Ar = cmk((r == col ? (T)1 : (T)0) - g.r, -g.i);
+                cfma(acc, Mw[row * n2 + r], Ar);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                acc.r += __shfl_xor_sync(0xffffffffu, acc.r, o);
+                acc.i += __shfl_xor_sync(0xffffffffu, acc.i, o);
+            }
+            if (lane == 0) aux[e] = acc;  // aux[4t + 2p + q]
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // obar_t = Abar[dn t, up t] - Abar[up t, dn t], Abar = (1 + Delta_s) Minv A, 1 + Delta_s = A(-gamma x)
+        double logq = 0.0;
+        int m = 0;
+        for (int t = 0; t < n; ++t) {
+            const int i = s0 + t, xi = x[i];
+            const T c = (T)(a.k.c1m1 + 1.0), s = (T)(-xi * a.k.s1);  // A(-gamma x) = [[c, s], [-s, c]]
+            const cx<T> MA00 = aux[4 * t], MA01 = aux[4 * t + 1], MA10 = aux[4 * t + 2], MA11 = aux[4 * t + 3];
+            const cx<T> dn_up = cadd(cscale(MA00, -s), cscale(MA10, c));
+            const cx<T> up_dn = cadd(cscale(MA01, c), cscale(MA11, s));
+            const cx<T> ob = csub(dn_up, up_dn);
+            s_ob[t] = ob;
+            const double h = a.k.gamma * (double)ob.r;
+            const double lp = 1.0 / (1.0 + exp(-2.0 * h));
+            lam[i] = lp;
+            const int xp = rep ? (rep[i] ? 1 : -1) : (u[i] < lp ? 1 : -1);
+            dec[i] = (uint8_t)(xp > 0);
+            if (xp != xi) {
+                T dl[2][2];
+                real_delta<T>(a.k.c2m1, a.k.s2, xi, dl);
+                for (int p = 0; p < 2; ++p)
+                    for (int q = 0; q < 2; ++q) s_dl[m][p][q] = dl[p][q];
+                s_site[m] = i;
+                logq += (double)(xi - xp) * h;
+                ++m;
+            }
+        }
+        s_m = m;
+        s_det = cmk(logq, 0.0);  // carries log q to the ratio below
+    }
+    __syncthreads();
+    const int m = s_m, m2 = 2 * m;
+    if (m == 0) {
+        if (tid == 0) {
+            dec[N + a.blk] = 1;
+            ratio[2 * (N + a.blk)] = 1.0;
+            ratio[2 * (N + a.blk) + 1] = 0.0;
+            a.Kdev[z] = 0;
+        }
+        return;
+    }
+    const double logq = s_det.r;
+    __syncthreads();
+    for (int e = tid; e < m2 * m2; e += nt) {
+        const int q = e / m2, qq = e - q * m2;
+        const int t2 = qq >> 1, p2 = qq & 1;
+        const int rq = (q & 1) ? N + s_site[q >> 1] : s_site[q >> 1];
+        cx<T> v = cmk((q == qq) ? (T)1 : (T)0, (T)0);
+        for (int p = 0; p < 2; ++p) {
+            const int cq = p ? N + s_site[t2] : s_site[t2];
+            const cx<T> g = g_at(G, ldz, rq, cq);
+            const cx<T> Aq = cmk((rq == cq ? (T)1 : (T)0) - g.r, -g.i);
+            v = cadd(v, cscale(Aq, s_dl[t2][p][p2]));
+        }
+        Mw[e] = v;
+    }
+    const bool ok = gj_inverse_2x2<T>(Mw, m2, m2, aux, &s_det, &s_pi, &s_ok);
+    if (tid == 0) {
+        const cx<double> dt = ok ? s_det : cmk(0.0, 0.0);
+        const double f = exp(logq);
+        const double Rr = dt.r * f, Ri = dt.i * f;
+        const double absR = sqrt(Rr * Rr + Ri * Ri);
+        ratio[2 * (N + a.blk)] = Rr;
+        ratio[2 * (N + a.blk) + 1] = Ri;
+        if (!isfinite(absR)) set_err(a.err, DEV_NUMERIC);
+        const int acc = rep ? (rep[N + a.blk] != 0) : (u[N + a.blk] < absR);
+        dec[N + a.blk] = (uint8_t)acc;
+        s_acc = acc && ok && absR > 0.0 && isfinite(absR);
+        if (s_acc) {
+            for (int t = 0; t < m; ++t) {
+                sites[t] = s_site[t];
+                x[s_site[t]] = (int8_t)(-x[s_site[t]]);
+            }
+            a.Kdev[z] = 2 * m2;
+        } else {
+            a.Kdev[z] = 0;
+        }
+    }
+    __syncthreads();
+    if (!s_acc) return;
+    write_W<T>(Mw, m2, m2, s_dl, W, ldw);
+}
+
+// ---------------------------------------------------------------------------
+// flush panels: X (2N x 4m, K-interleaved) = G[:, F] and the realified rows of E_F^T - G[F, :]
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void soc_gather_kernel(const T* G0, long gstride, long ldz, int N, const int* sites0, int kmax,
+                                  const int* Kdev, T* X0, T* Y0) {
+    const int z = blockIdx.z;
+    const int K4 = Kdev[z];
+    if (K4 == 0) return;
+    const int m2 = K4 / 2;  // complex orbitals of F
+    const T* G = G0 + (long)z * gstride;
+    const int* sites = sites0 + (long)z * kmax;
+    const int ldx = 4 * kmax;
+    T* X = X0 + (long)z * 2 * N * ldx;
+    T* Y = Y0 + (long)z * ldx * 2 * ldz;
+    const long ld2 = 2 * ldz;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    if (blockIdx.y == 0) {
+        for (int e = tid; e < 2 * N * m2; e += nt) {
+            const int r = e / m2, q = e - r * m2;
+            const int o = (q & 1) ? N + sites[q >> 1] : sites[q >> 1];
+            X[(long)r * ldx + 2 * q] = G[(long)r * ld2 + o];
+            X[(long)r * ldx + 2 * q + 1] = G[(long)r * ld2 + ldz + o];
+        }
+    } else {
+        for (long e = tid; e < (long)m2 * ldz; e += nt) {
+            const int q = (int)(e / ldz);
+            const long c = e - (long)q * ldz;
+            const int o = (q & 1) ? N + sites[q >> 1] : sites[q >> 1];
+            const T yr = (c == o ? (T)1 : (T)0) - G[(long)o * ld2 + c];
+            const T yi = -G[(long)o * ld2 + ldz + c];
+            Y[(long)(2 * q) * ld2 + c] = yr;
+            Y[(long)(2 * q) * ld2 + ldz + c] = yi;
+            Y[(long)(2 * q + 1) * ld2 + c] = -yi;
+            Y[(long)(2 * q + 1) * ld2 + ldz + c] = yr;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 propagation of realified factors through exp(-dtau H0) in momentum space
+// ---------------------------------------------------------------------------
+struct SocPropArgs {
+    double* F0;
+    long wstride;             // factor of walker j at F0 + j wstride: 4N x nv row-major
+    int nv, L, N;
+    const double* dft;        // L x L complex: exp(-2 pi i k x / L)
+    const double* lam;        // N x 2 x 2 complex: exp(-dtau h_k) / N, k = kx + L ky
+    const int8_t* x;
+    long xstride;             // fields M x N of walker j at x + j xstride
+    int l_first, l_step, nsl;
+    int left;                 // 0: v <- D_l E v (right factor); 1: v <- E D_l^T v (left factor, transposed)
+    double cg, sg;
+};
+
+constexpr int PROP_VPC_MAX = 4;
+
+__device__ __forceinline__ void prop_pass(const cx<double>* in, cx<double>* out, const cx<double>* F, int L, int N,
+                                          int vpc, int axis, int inverse) {
+    // axis 0 transforms x (stride 1), axis 1 transforms y (stride L); inverse uses conj(F)^T
+    const int n2 = 2 * N;
+    for (int e = threadIdx.x; e < vpc * n2; e += blockDim.x) {
+        const int v = e / n2, a = e - v * n2;
+        const int s = a / N, i = a - s * N;
+        const int xx = i % L, yy = i / L;
+        const int kout = axis ? yy : xx;
+        const cx<double>* src = in + v * n2 + s * N + (axis ? xx : yy * L);
+        const int stride = axis ? L : 1;
+        cx<double> acc0 = cmk(0.0, 0.0), acc1 = cmk(0.0, 0.0);
+        int q = 0;
+        for (; q + 1 < L; q += 2) {
+            cx<double> f0 = inverse ? F[q * L + kout] : F[kout * L + q];
+            cx<double> f1 = inverse ? F[(q + 1) * L + kout] : F[kout * L + q + 1];
+            if (inverse) {
+                f0.i = -f0.i;
+                f1.i = -f1.i;
+            }
+            cfma(acc0, f0, src[q * stride]);
+            cfma(acc1, f1, src[(q + 1) * stride]);
+        }
+        if (q < L) {
+            cx<double> f0 = inverse ? F[q * L + kout] : F[kout * L + q];
+            if (inverse) f0.i = -f0.i;
+            cfma(acc0, f0, src[q * stride]);
+        }
+        out[e] = cadd(acc0, acc1);
+    }
+}
+
+__global__ void __launch_bounds__(256) soc_prop_kernel(SocPropArgs a, int vpc) {
+    extern __shared__ __align__(16) unsigned char prop_smem[];
+    const int N = a.N, L = a.L, n2 = 2 * N;
+    cx<double>* b0 = (cx<double>*)prop_smem;
+    cx<double>* b1 = b0 + vpc * n2;
+    cx<double>* F = b1 + vpc * n2;
+    const int z = blockIdx.y;
+    double* U = a.F0 + (long)z * a.wstride;
+    const int8_t* xw = a.x + (long)z * a.xstride;
+    const int c0 = blockIdx.x * vpc;
+    const int nv = a.nv;
+    for (int e = threadIdx.x; e < L * L; e += blockDim.x) F[e] = cmk(a.dft[2 * e], a.dft[2 * e + 1]);
+    for (int e = threadIdx.x; e < vpc * n2; e += blockDim.x) {
+        const int r = e / vpc, v = e - r * vpc;  // v fastest: consecutive columns
+        const int c = c0 + v;
+        b0[v * n2 + r] = (c < nv) ? cmk(U[(long)r * nv + c], U[(long)(n2 + r) * nv + c]) : cmk(0.0, 0.0);
+    }
+    __syncthreads();
+    const cx<double>* lamk = (const cx<double>*)a.lam;
+    for (int q = 0; q < a.nsl; ++q) {
+        const int ell = a.l_first + q * a.l_step;
+        const int8_t* xl = xw + (long)(ell - 1) * N;
+        if (a.left) {  // v <- D^T v: rotation by A(-gamma x)
+            for (int e = threadIdx.x; e < vpc * N; e += blockDim.x) {
+                const int v = e / N, i = e - v * N;
+                const double s = -xl[i] * a.sg;
+                const cx<double> p0 = b0[v * n2 + i], p1 = b0[v * n2 + N + i];
+                b0[v * n2 + i] = cadd(cscale(p0, a.cg), cscale(p1, s));
+                b0[v * n2 + N + i] = csub(cscale(p1, a.cg), cscale(p0, s));
+            }
+            __syncthreads();
+        }
+        prop_pass(b0, b1, F, L, N, vpc, 0, 0);
+        __syncthreads();
+        prop_pass(b1, b0, F, L, N, vpc, 1, 0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < vpc * N; e += blockDim.x) {
+            const int v = e / N, k = e - v * N;
+            const cx<double>* l4 = lamk + 4 * k;
+            const cx<double> u0 = b0[v * n2 + k], u1 = b0[v * n2 + N + k];
+            cx<double> w0 = cmul(l4[0], u0), w1 = cmul(l4[2], u0);
+            cfma(w0, l4[1], u1);
+            cfma(w1, l4[3], u1);
+            b1[v * n2 + k] = w0;
+            b1[v * n2 + N + k] = w1;
+        }
+        __syncthreads();
+        prop_pass(b1, b0, F, L, N, vpc, 1, 1);
+        __syncthreads();
+        prop_pass(b0, b1, F, L, N, vpc, 0, 1);
+        __syncthreads();
+        if (!a.left) {  // v <- D v: rotation by A(gamma x)
+            for (int e = threadIdx.x; e < vpc * N; e += blockDim.x) {
+                const int v = e / N, i = e - v * N;
+                const double s = xl[i] * a.sg;
+                const cx<double> p0 = b1[v * n2 + i], p1 = b1[v * n2 + N + i];
+                b1[v * n2 + i] = cadd(cscale(p0, a.cg), cscale(p1, s));
+                b1[v * n2 + N + i] = csub(cscale(p1, a.cg), cscale(p0, s));
+            }
+        }
+        __syncthreads();
+        cx<double>* t = b0;  // the result is in b1: swap so that b0 holds the vectors
+        b0 = b1;
+        b1 = t;
+    }
+    for (int e = threadIdx.x; e < vpc * n2; e += blockDim.x) {
+        const int r = e / vpc, v = e - r * vpc;
+        const int c = c0 + v;
+        if (c < nv) {
+            const cx<double> w = b0[v * n2 + r];
+            U[(long)r * nv + c] = w.r;
+            U[(long)(n2 + r) * nv + c] = w.i;
+        }
+    }
+}
+
+// B (cols x rows per walker) = A^T
+__global__ void soc_transpose_kernel(const double* A0, int rows, int cols, long sa, double* B0, long sb) {
+    __shared__ double tile[32][33];
+    const double* A = A0 + (long)blockIdx.z * sa;
+    double* B = B0 + (long)blockIdx.z * sb;
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int r = by + k, c = bx + threadIdx.x;
+        tile[k][threadIdx.x] = (r < rows && c < cols) ? A[(long)r * cols + c] : 0.0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int c = bx + k, r = by + threadIdx.x;
+        if (c < cols && r < rows) B[(long)c * rows + r] = tile[threadIdx.x][k];
+    }
+}
+
+// Bulk G (row-split, T) from P = U_R Z (4N x 2N, FP64): Re G = 1 - P[0:2N], Im G = -P[2N:4N];
+// acc2[j] += (||G_old - G_new||^2, ||G_new||^2) when drift != 0.
+template <typename T>
+__global__ void soc_store_G_kernel(const double* P0, long pstride, int N2, T* G0, long ldz, long gstride, double* acc2,
+                                   int drift) {
+    const int z = blockIdx.y;
+    const double* P = P0 + (long)z * pstride;
+    T* G = G0 + (long)z * gstride;
+    double d2 = 0.0, n2 = 0.0;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < (long)N2 * N2; e += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / N2), c = (int)(e - (long)r * N2);
+        const double gr = (r == c ? 1.0 : 0.0) - P[(long)r * N2 + c];
+        const double gi = -P[(long)(N2 + r) * N2 + c];
+        T* pr = G + (long)r * 2 * ldz + c;
+        if (drift) {
+            const double er = (double)pr[0] - gr, ei = (double)pr[ldz] - gi;
+            d2 += er * er + ei * ei;
+            n2 += gr * gr + gi * gi;
+        }
+        pr[0] = (T)gr;
+        pr[ldz] = (T)gi;
+    }
+    if (!drift) return;
+    for (int o = 16; o > 0; o >>= 1) {
+        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(acc2 + 2 * z, d2);
+        atomicAdd(acc2 + 2 * z + 1, n2);
+    }
+}
+
+// Energy with the spin-coupled Wick contraction; H0 is applied bond by bond (hopping -t in each
+// spin block; spin-flip hopping (dn r, up r+d) = -i lam (d = +y), +i lam (-y), -lam (+x), +lam (-x)
+// and its Hermitian conjugate).  out[j] = (Re E, Im E).
+template <typename T>
+__global__ void soc_energy_kernel(const T* G0, long ldz, long gstride, int L, double t, double lam, double U,
+                                  double* out) {
+    const int z = blockIdx.x;
+    const T* G = G0 + (long)z * gstride;
+    const int N = L * L;
+    auto A = [&](int r, int c) {
+        const cx<T> g = g_at(G, ldz, r, c);
+        return cmk((r == c ? 1.0 : 0.0) - (double)g.r, -(double)g.i);
+    };
+    cx<double> acc = cmk(0.0, 0.0);
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+        const int x = r % L, y = r / L;
+        const int dx[4] = {0, 0, 1, -1}, dy[4] = {1, -1, 0, 0};
+        const cx<double> amp[4] = {cmk(0.0, -lam), cmk(0.0, lam), cmk(-lam, 0.0), cmk(lam, 0.0)};
+        for (int d = 0; d < 4; ++d) {
+            const int rp = (x + dx[d] + L) % L + L * ((y + dy[d] + L) % L);
+            // kinetic: H0[(s, r)][(s, rp)] = -t  ->  -t A[(s, rp)][(s, r)]
+            acc = cadd(acc, cscale(A(rp, r), -t));
+            acc = cadd(acc, cscale(A(N + rp, N + r), -t));
+            // H0[(dn, r)][(up, rp)] = amp -> amp A[(up, rp)][(dn, r)]; its conjugate entry
+            cfma(acc, amp[d], A(rp, N + r));
+            cfma(acc, cmk(amp[d].r, -amp[d].i), A(N + r, rp));
+        }
+        const cx<double> Auu = A(r, r), Add = A(N + r, N + r), Adu = A(N + r, r), Aud = A(r, N + r);
+        cx<double> v = csub(cmul(Auu, Add), cmul(Adu, Aud));
+        v = csub(v, cscale(cadd(Auu, Add), 0.5));
+        acc = cadd(acc, cscale(v, U));
+    }
+    __shared__ double sr[32], si[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.r += __shfl_xor_sync(0xffffffffu, acc.r, o);
+        acc.i += __shfl_xor_sync(0xffffffffu, acc.i, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sr[wid] = acc.r;
+        si[wid] = acc.i;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += sr[w];
+            b += si[w];
+        }
+        out[2 * z] = a;
+        out[2 * z + 1] = b;
+    }
+}
+
+__global__ void soc_fields_kernel(uint64_t seed, long count, int8_t* x) {
+    const long j = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const int w = blockIdx.y;
+    if (j < count) x[(long)w * count + j] = philox_uniform(seed, (uint64_t)w, 0x5F1E1DULL, (uint64_t)j) < 0.5 ? 1 : -1;
+}
+
+__global__ void soc_iota_kernel(int* g, int n) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) g[j] = j;
+}
+
+}  // namespace
+}  // namespace afq
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+using namespace afq;
+
+struct afqmc_soc_ctx {
+    afqmc_soc_params p;
+    int N = 0, N2 = 0, ne = 0, nv = 0, nwk = 0, kmax = 0, nst = 0;
+    long ldz = 0;
+    SocConsts k{};
+    bool f64 = true, use_tc = false;
+    int sticky = 0;
+    int pos = 0, last_dir = -1;
+    bool need_recompute = false, inited = false;
+    cudaStream_t last = nullptr;
+    std::vector<void*> allocs;
+    // constants
+    void *Ers = nullptr, *Einvrs = nullptr;   // [Re E | Im E] rows, bulk precision
+    void *Ech = nullptr, *Einvch = nullptr;   // realified right operands (transposed for tensor cores)
+    double *dft = nullptr, *lamk = nullptr;   // momentum-space propagation (FP64)
+    // walkers
+    void* G = nullptr;
+    void* S = nullptr;
+    int8_t* x = nullptr;
+    double* u = nullptr;
+    uint8_t *rep = nullptr, *dec = nullptr;
+    double *ratio = nullptr, *lamp = nullptr;
+    int* gid = nullptr;
+    unsigned long long* visit = nullptr;
+    void *X = nullptr, *Xp = nullptr, *Y = nullptr, *W = nullptr;
+    int *Kdev = nullptr, *sites = nullptr, *err = nullptr;
+    double *URs = nullptr, *ULs = nullptr, *Ucur = nullptr, *Lrow = nullptr, *O = nullptr, *Z = nullptr,
+           *Pb = nullptr, *acc2 = nullptr, *en = nullptr;
+    int* perm = nullptr;
+    int8_t* flag = nullptr;
+    // profiling
+    struct Ev {
+        int ph;
+        cudaEvent_t a, b;
+    };
+    bool prof_on = false;
+    std::vector<Ev> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[AFQMC_NPHASE] = {};
+    int64_t intervals[AFQMC_NPHASE] = {};
+    int64_t launches[AFQMC_NPHASE] = {};
+
+    long gstride() const { return (long)N2 * 2 * ldz; }
+    long fsz() const { return (long)2 * N2 * nv; }  // realified factor: 4N x 2 n_e
+    double* stackR(int j) const { return URs + (long)j * fsz(); }
+    double* stackL(int j) const { return ULs + (long)j * fsz(); }
+    long st_w() const { return (long)nst * fsz(); }
+};
+
+namespace {
+
+cudaEvent_t soc_event(afqmc_soc_ctx* c) {
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct SocPhase {
+    afqmc_soc_ctx* c;
+    int ph;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    long long l0;
+    SocPhase(afqmc_soc_ctx* ctx, int phase, cudaStream_t s) : c(ctx), ph(phase), st(s), l0(afqmc_launch_count()) {
+        if (c->prof_on) {
+            a = soc_event(c);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~SocPhase() {
+        if (!c->prof_on || !a) return;
+        cudaEvent_t b = soc_event(c);
+        cudaEventRecord(b, st);
+        c->pending.push_back({ph, a, b});
+        c->launches[ph] += afqmc_launch_count() - l0;
+    }
+};
+
+#define SCK(x)                                        \
+    do {                                              \
+        cudaError_t e_ = (x);                         \
+        if (e_ != cudaSuccess) return soc_fail(ctx, e_); \
+    } while (0)
+
+int soc_fail(afqmc_soc_ctx* ctx, cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) ctx->sticky = AFQMC_ERR_OOM;
+    else ctx->sticky = AFQMC_ERR_CUDA;
+    cudaGetLastError();
+    return ctx->sticky;
+}
+
+template <typename P>
+cudaError_t soc_alloc(afqmc_soc_ctx* ctx, P** out, size_t bytes, cudaStream_t st) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+    if (e != cudaSuccess) return e;
+    ctx->allocs.push_back(p);
+    *out = (P*)p;
+    return cudaMemsetAsync(p, 0, bytes ? bytes : 16, st);
+}
+
+int read_err(afqmc_soc_ctx* ctx) {
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return soc_fail(ctx, e);
+    if (h == DEV_TIMEOUT) ctx->sticky = AFQMC_ERR_TIMEOUT;
+    else if (h == DEV_NUMERIC) ctx->sticky = AFQMC_ERR_NUMERIC;
+    else if (h != 0) ctx->sticky = AFQMC_ERR_CUDA;
+    return ctx->sticky;
+}
+
+// exp(-tau h_k) / N per momentum k = kx + L ky (row-major 2 x 2 complex, interleaved doubles):
+// h_k = eps + [[0, conj Lk], [Lk, 0]] and the off-diagonal part squares to |Lk|^2, so
+// exp(-tau h_k) = e^{-tau eps} (cosh(tau |Lk|) - sinh(tau |Lk|) / |Lk| [[0, conj Lk], [Lk, 0]]).
+void host_lamk(int L, double t, double lam, double tau, std::vector<double>& out) {
+    const int N = L * L;
+    out.assign((size_t)N * 8, 0.0);
+    for (int ky = 0; ky < L; ++ky)
+        for (int kx = 0; kx < L; ++kx) {
+            const double ax = 2.0 * M_PI * kx / L, ay = 2.0 * M_PI * ky / L;
+            const double eps = -2.0 * t * (cos(ax) + cos(ay));
+            const double lr = 2.0 * lam * sin(ay), li = -2.0 * lam * sin(ax);  // Lk
+            const double mag = sqrt(lr * lr + li * li);
+            const double ch = cosh(tau * mag), sh = mag > 0.0 ? sinh(tau * mag) / mag : tau;
+            const double f = exp(-tau * eps) / N;
+            double* o = &out[(size_t)(kx + L * ky) * 8];
+            o[0] = f * ch;                       // [up][up]
+            o[2] = -f * sh * lr;                 // [up][dn] = conj Lk coefficient
+            o[3] = f * sh * li;
+            o[4] = -f * sh * lr;                 // [dn][up] = Lk coefficient
+            o[5] = -f * sh * li;
+            o[6] = f * ch;                       // [dn][dn]
+        }
+}
+
+// Dense exp(-tau H0) (2N x 2N complex, interleaved): entries depend on the displacement only.
+void host_expH(int L, double t, double lam, double tau, std::vector<double>& E) {
+    const int N = L * L, N2 = 2 * N;
+    std::vector<double> lk;
+    host_lamk(L, t, lam, tau, lk);
+    std::vector<double> tab((size_t)N * 8, 0.0);  // [dy][dx][s][s'] complex
+    std::vector<double> cs(L), sn(L);
+    for (int q = 0; q < L; ++q) {
+        cs[q] = cos(2.0 * M_PI * q / L);
+        sn[q] = sin(2.0 * M_PI * q / L);
+    }
+    for (int dy = 0; dy < L; ++dy)
+        for (int dx = 0; dx < L; ++dx) {
+            double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int ky = 0; ky < L; ++ky)
+                for (int kx = 0; kx < L; ++kx) {
+                    const int ph = (kx * dx + ky * dy) % L;
+                    const double er = cs[ph], ei = sn[ph];
+                    const double* o = &lk[(size_t)(kx + L * ky) * 8];
+                    for (int q = 0; q < 4; ++q) {
+                        acc[2 * q] += er * o[2 * q] - ei * o[2 * q + 1];
+                        acc[2 * q + 1] += er * o[2 * q + 1] + ei * o[2 * q];
+                    }
+                }
+            memcpy(&tab[(size_t)(dx + L * dy) * 8], acc, sizeof(acc));
+        }
+    E.assign((size_t)N2 * N2 * 2, 0.0);
+    for (int s = 0; s < 2; ++s)
+        for (int i = 0; i < N; ++i)
+            for (int sp = 0; sp < 2; ++sp)
+                for (int j = 0; j < N; ++j) {
+                    const int dx = ((i % L) - (j % L) + L) % L, dy = ((i / L) - (j / L) + L) % L;
+                    const double* v = &tab[(size_t)(dx + L * dy) * 8 + 2 * (2 * s + sp)];
+                    const size_t o = ((size_t)(s * N + i) * N2 + (sp * N + j)) * 2;
+                    E[o] = v[0];
+                    E[o + 1] = v[1];
+                }
+}
+
+template <typename T>
+cudaError_t upload_constants(afqmc_soc_ctx* ctx, cudaStream_t st) {
+    const int N2 = ctx->N2;
+    const long ldz = ctx->ldz, ld2 = 2 * ldz;
+    for (int inv = 0; inv < 2; ++inv) {
+        std::vector<double> E;
+        host_expH(ctx->p.L, ctx->p.t, ctx->p.lam, inv ? -ctx->p.dtau : ctx->p.dtau, E);
+        std::vector<T> rs((size_t)N2 * ld2, (T)0), ch((size_t)ld2 * ld2, (T)0);
+        for (int r = 0; r < N2; ++r)
+            for (int c = 0; c < N2; ++c) {
+                const double er = E[((size_t)r * N2 + c) * 2], ei = E[((size_t)r * N2 + c) * 2 + 1];
+                rs[(size_t)r * ld2 + c] = (T)er;
+                rs[(size_t)r * ld2 + ldz + c] = (T)ei;
+                // C~ = [[Re, Im], [-Im, Re]]; the tensor-core path stores its transpose
+                const size_t o00 = (size_t)r * ld2 + c, o01 = (size_t)r * ld2 + ldz + c;
+                const size_t o10 = (size_t)(ldz + r) * ld2 + c, o11 = (size_t)(ldz + r) * ld2 + ldz + c;
+                if (!ctx->use_tc) {
+                    ch[o00] = (T)er;
+                    ch[o01] = (T)ei;
+                    ch[o10] = (T)(-ei);
+                    ch[o11] = (T)er;
+                } else {
+                    ch[(size_t)c * ld2 + r] = (T)er;
+                    ch[(size_t)(ldz + c) * ld2 + r] = (T)ei;
+                    ch[(size_t)c * ld2 + ldz + r] = (T)(-ei);
+                    ch[(size_t)(ldz + c) * ld2 + ldz + r] = (T)er;
+                    (void)o00; (void)o01; (void)o10; (void)o11;
+                }
+            }
+        void* drs = inv ? ctx->Einvrs : ctx->Ers;
+        void* dch = inv ? ctx->Einvch : ctx->Ech;
+        cudaError_t e = cudaMemcpyAsync(drs, rs.data(), rs.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(dch, ch.data(), ch.size() * sizeof(T), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    }
+    const int L = ctx->p.L;
+    std::vector<double> F((size_t)L * L * 2), lk;
+    for (int k = 0; k < L; ++k)
+        for (int q = 0; q < L; ++q) {
+            const double ph = -2.0 * M_PI * (double)((k * q) % L) / L;
+            F[(size_t)(k * L + q) * 2] = cos(ph);
+            F[(size_t)(k * L + q) * 2 + 1] = sin(ph);
+        }
+    host_lamk(L, ctx->p.t, ctx->p.lam, ctx->p.dtau, lk);
+    cudaError_t e = cudaMemcpyAsync(ctx->dft, F.data(), F.size() * 8, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(ctx->lamk, lk.data(), lk.size() * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
+// ---- wrap ----
+template <typename T>
+cudaError_t soc_wrap(afqmc_soc_ctx* ctx, cudaStream_t st, const int8_t* xl, int dir) {
+    SocPhase ps(ctx, AFQMC_PHASE_WRAP, st);
+    const int N = ctx->N, N2 = ctx->N2, nwk = ctx->nwk;
+    const long ldz = ctx->ldz, ld2 = 2 * ldz, gs = ctx->gstride(), ss = ld2 * ld2;
+    const long xs = (long)ctx->p.M * N;
+    const T cg = (T)(ctx->k.c1m1 + 1.0), sg = (T)ctx->k.s1;
+    T* G = (T*)ctx->G;
+    T* S = (T*)ctx->S;
+    const dim3 rgrid((N + 31) / 32, (N + 7) / 8, nwk), rblk(32, 8);
+    cudaError_t e;
+    if (dir < 0) {  // G <- D^{-1} G D first
+        count_launch();
+        soc_rot_kernel<T><<<rgrid, rblk, 0, st>>>(G, ldz, N, gs, xl, xs, cg, sg, -1, +1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const T* Cright = (const T*)(dir > 0 ? ctx->Einvch : ctx->Ech);  // S = G E^{-1} (fwd) / G E (bwd)
+    const T* Aleft = (const T*)(dir > 0 ? ctx->Ers : ctx->Einvrs);   // G = E S (fwd) / E^{-1} S (bwd)
+    if (ctx->use_tc) {
+        TcGemmArgs t1;
+        t1.M = N2; t1.N = (int)ld2; t1.K = (int)ld2; t1.batch = nwk;
+        t1.A = (const float*)G; t1.lda = ld2; t1.sA = gs;
+        t1.Bt = (const float*)Cright; t1.ldb = ld2; t1.sB = 0;
+        t1.C = (float*)S; t1.ldc = ld2; t1.sC = ss; t1.c_trans = 1;
+        t1.split3 = ctx->p.gemm != AFQMC_GEMM_TF32;
+        t1.err = ctx->err;
+        {
+            SocPhase pg(ctx, AFQMC_PHASE_WRAP_GEMM, st);
+            if ((e = tc_gemm(st, t1)) != cudaSuccess) return e;
+        }
+        count_launch();
+        soc_realify_kernel<T><<<dim3((N2 + 255) / 256, (unsigned)ld2, nwk), 256, 0, st>>>(S, ldz, N2, ss, 0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        TcGemmArgs t2;
+        t2.M = N2; t2.N = (int)ld2; t2.K = (int)ld2; t2.batch = nwk;
+        t2.A = (const float*)Aleft; t2.lda = ld2; t2.sA = 0;
+        t2.Bt = (const float*)S; t2.ldb = ld2; t2.sB = ss;
+        t2.C = (float*)G; t2.ldc = ld2; t2.sC = gs;
+        t2.split3 = t1.split3;
+        t2.err = ctx->err;
+        SocPhase pg(ctx, AFQMC_PHASE_WRAP_GEMM, st);
+        if ((e = tc_gemm(st, t2)) != cudaSuccess) return e;
+    } else {
+        GemmArgs<T> g1;
+        g1.M = N2; g1.N = (int)ld2; g1.K = (int)ld2; g1.batch = nwk;
+        g1.A = G; g1.lda = ld2; g1.sA = gs;
+        g1.B = Cright; g1.ldb = ld2; g1.sB = 0;
+        g1.C = S; g1.ldc = ld2; g1.sC = ss;
+        {
+            SocPhase pg(ctx, AFQMC_PHASE_WRAP_GEMM, st);
+            if ((e = gemm<T>(st, g1)) != cudaSuccess) return e;
+        }
+        count_launch();
+        soc_realify_kernel<T><<<dim3((unsigned)((ld2 + 255) / 256), N2, nwk), 256, 0, st>>>(S, ldz, N2, ss, 1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        GemmArgs<T> g2;
+        g2.M = N2; g2.N = (int)ld2; g2.K = (int)ld2; g2.batch = nwk;
+        g2.A = Aleft; g2.lda = ld2; g2.sA = 0;
+        g2.B = S; g2.ldb = ld2; g2.sB = ss;
+        g2.C = G; g2.ldc = ld2; g2.sC = gs;
+        SocPhase pg(ctx, AFQMC_PHASE_WRAP_GEMM, st);
+        if ((e = gemm<T>(st, g2)) != cudaSuccess) return e;
+    }
+    if (dir > 0) {  // G <- D G D^{-1}
+        count_launch();
+        soc_rot_kernel<T><<<rgrid, rblk, 0, st>>>(G, ldz, N, gs, xl, xs, cg, sg, +1, -1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+size_t window_smem(int kmax) {
+    return (size_t)(4 * kmax * kmax + 8 * kmax) * sizeof(cx<T>);
+}
+
+// ---- one window: chain + flush ----
+template <typename T>
+cudaError_t soc_window(afqmc_soc_ctx* ctx, cudaStream_t st, int8_t* xl, const uint8_t* rep, int mode, int s0, int n,
+                       int blk) {
+    const int N = ctx->N, N2 = ctx->N2, nwk = ctx->nwk, kmax = ctx->kmax;
+    const long ldz = ctx->ldz, ld2 = 2 * ldz;
+    cudaError_t e;
+    SocWinArgs a;
+    a.G0 = ctx->G; a.gstride = ctx->gstride(); a.ldz = ldz; a.N = N;
+    a.x0 = xl; a.xstride = (long)ctx->p.M * N;
+    a.u0 = ctx->u; a.rep = rep;
+    a.mode = mode; a.s0 = s0; a.n = n; a.blk = blk;
+    a.k = ctx->k;
+    a.dec0 = ctx->dec; a.ratio0 = ctx->ratio; a.lam0 = ctx->lamp;
+    a.sites0 = ctx->sites; a.kmax = kmax;
+    a.W0 = ctx->W; a.Kdev = ctx->Kdev; a.err = ctx->err;
+    {
+        SocPhase ps(ctx, AFQMC_PHASE_CHAIN, st);
+        const size_t shm = window_smem<T>(kmax);
+        static bool attr[2] = {false, false};
+        if (!attr[sizeof(T) == 8]) {
+            if ((e = cudaFuncSetAttribute((void*)soc_window_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)shm)) != cudaSuccess)
+                return e;
+            attr[sizeof(T) == 8] = true;
+        }
+        count_launch();
+        soc_window_kernel<T><<<nwk, 512, shm, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    SocPhase pf(ctx, AFQMC_PHASE_FLUSH, st);
+    const int ldx = 4 * kmax;
+    count_launch();
+    soc_gather_kernel<T><<<dim3(64, 2, nwk), 256, 0, st>>>((const T*)ctx->G, ctx->gstride(), ldz, N, ctx->sites, kmax,
+                                                          ctx->Kdev, (T*)ctx->X, (T*)ctx->Y);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // X' = X W (K = 4m), then G -= X' Y~
+    GemmArgs<T> g1;
+    g1.M = N2; g1.N = 4 * n; g1.K = 4 * n; g1.Kdev = ctx->Kdev; g1.kdiv = 1; g1.batch = nwk;
+    g1.A = (const T*)ctx->X; g1.lda = ldx; g1.sA = (long)N2 * ldx;
+    g1.B = (const T*)ctx->W; g1.ldb = ldx; g1.sB = (long)ldx * ldx;
+    g1.C = (T*)ctx->Xp; g1.ldc = ldx; g1.sC = (long)N2 * ldx;
+    if ((e = gemm<T>(st, g1)) != cudaSuccess) return e;
+    GemmArgs<T> g2;
+    g2.M = N2; g2.N = (int)ld2; g2.K = 4 * n; g2.Kdev = ctx->Kdev; g2.kdiv = 1; g2.batch = nwk;
+    g2.A = (const T*)ctx->Xp; g2.lda = ldx; g2.sA = (long)N2 * ldx;
+    g2.B = (const T*)ctx->Y; g2.ldb = ld2; g2.sB = (long)ldx * ld2;
+    g2.C = (T*)ctx->G; g2.ldc = ld2; g2.sC = ctx->gstride();
+    g2.alpha = (T)-1; g2.beta = (T)1;
+    SocPhase pg(ctx, AFQMC_PHASE_FLUSH_GEMM, st);
+    return gemm<T>(st, g2);
+}
+
+template <typename T>
+int soc_sweep(afqmc_soc_ctx* ctx, int slice, int dir, int mode, int k, int nb, const uint8_t* rep, cudaStream_t st) {
+    const int N = ctx->N;
+    int8_t* xl = ctx->x + (long)(slice - 1) * N;
+    {
+        SocPhase ps(ctx, AFQMC_PHASE_PREP, st);
+        SCK(launch_uniforms(st, ctx->p.seed, ctx->gid, ctx->visit, 2 * N, ctx->u, ctx->nwk));
+        SCK(cudaMemsetAsync(ctx->dec, 0, (size_t)ctx->nwk * 2 * N, st));
+    }
+    if (dir > 0) SCK(soc_wrap<T>(ctx, st, xl, +1));
+    if (mode == AFQMC_MODE_BLOCKFB) {
+        for (int b = 0; b * nb < N; ++b) {
+            const int s0 = b * nb, n = std::min(nb, N - s0);
+            SCK(soc_window<T>(ctx, st, xl, rep, 1, s0, n, b));
+        }
+    } else {
+        const int w = (mode == AFQMC_MODE_LOCAL) ? 1 : k;
+        for (int s0 = 0; s0 < N; s0 += w) SCK(soc_window<T>(ctx, st, xl, rep, 0, s0, std::min(w, N - s0), 0));
+    }
+    if (dir < 0) SCK(soc_wrap<T>(ctx, st, xl, -1));
+    SCK(launch_bump(st, ctx->visit));
+    return AFQMC_OK;
+}
+
+// ---- FP64 recompute pieces ----
+cudaError_t soc_propagate(afqmc_soc_ctx* ctx, cudaStream_t st, double* F, long wstride, int left, int l_first,
+                          int l_step, int nsl) {
+    SocPropArgs a;
+    a.F0 = F; a.wstride = wstride; a.nv = ctx->nv; a.L = ctx->p.L; a.N = ctx->N;
+    a.dft = ctx->dft; a.lam = ctx->lamk;
+    a.x = ctx->x; a.xstride = (long)ctx->p.M * ctx->N;
+    a.l_first = l_first; a.l_step = l_step; a.nsl = nsl; a.left = left;
+    a.cg = ctx->k.c1m1 + 1.0; a.sg = ctx->k.s1;
+    // vectors per CTA: as many (<= 4) as two buffers of 2N complex doubles allow in 220 KB
+    const size_t per = (size_t)2 * ctx->N2 * sizeof(cx<double>), fix = (size_t)ctx->p.L * ctx->p.L * sizeof(cx<double>);
+    const int vpc = (int)std::min<size_t>(PROP_VPC_MAX, (220 * 1024 - fix) / per);
+    const size_t shm = vpc * per + fix;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute((void*)soc_prop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    count_launch();
+    soc_prop_kernel<<<dim3((ctx->nv + vpc - 1) / vpc, ctx->nwk), 256, shm, st>>>(a, vpc);
+    return cudaGetLastError();
+}
+
+LuArgs soc_lu_args(afqmc_soc_ctx* ctx, double* A, long wstride, long lda, int m, int n) {
+    LuArgs a;
+    a.A0 = A; a.wstride = wstride; a.sstride = 0; a.ng = 1;
+    a.perm0 = ctx->perm; a.flag0 = ctx->flag; a.pstride = 2L * ctx->N2;
+    a.lda = lda; a.m = m; a.n = n; a.nmat = ctx->nwk; a.err = ctx->err;
+    return a;
+}
+
+// realified factor (4N x 2 n_e) -> its P L basis
+cudaError_t soc_stab(afqmc_soc_ctx* ctx, cudaStream_t st, double* F, long wstride) {
+    LuArgs a = soc_lu_args(ctx, F, wstride, ctx->nv, 2 * ctx->N2, ctx->nv);
+    cudaError_t e;
+    {
+        SocPhase ps(ctx, AFQMC_PHASE_ELIM, st);
+        if ((e = launch_lu(st, a)) != cudaSuccess) return e;
+    }
+    return launch_lu_unit_rows(st, a);
+}
+
+// G = 1 - R (L R)^{-1} L from stack entries R = URs[j], L^+ = ULs[j] (both realified, 4N x 2 n_e)
+template <typename T>
+cudaError_t soc_form_G(afqmc_soc_ctx* ctx, cudaStream_t st, int j, bool drift) {
+    const int N2 = ctx->N2, nv = ctx->nv, nwk = ctx->nwk;
+    const long R4 = 2L * N2;
+    cudaError_t e;
+    double* R = ctx->stackR(j);
+    double* Lt = ctx->stackL(j);
+    count_launch();
+    soc_transpose_kernel<<<dim3((nv + 31) / 32, (unsigned)((R4 + 31) / 32), nwk), dim3(32, 8), 0, st>>>(
+        Lt, (int)R4, nv, ctx->st_w(), ctx->Lrow, ctx->fsz());
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    GemmArgs<double> g;
+    g.M = nv; g.N = nv; g.K = (int)R4; g.batch = nwk;
+    g.A = ctx->Lrow; g.lda = R4; g.sA = ctx->fsz();
+    g.B = R; g.ldb = nv; g.sB = ctx->st_w();
+    g.C = ctx->O; g.ldc = nv; g.sC = (long)nv * nv;
+    if ((e = gemm<double>(st, g)) != cudaSuccess) return e;
+    LuArgs a = soc_lu_args(ctx, ctx->O, (long)nv * nv, nv, nv, nv);
+    {
+        SocPhase ps(ctx, AFQMC_PHASE_LU_O, st);
+        if ((e = launch_lu(st, a)) != cudaSuccess) return e;
+    }
+    SolveArgs sa;
+    sa.LU0 = ctx->O; sa.ostride = (long)nv * nv;
+    sa.perm0 = ctx->perm; sa.pstride = a.pstride;
+    sa.B0 = ctx->Lrow; sa.wstride = ctx->fsz(); sa.sstride = 0; sa.ng = 1;
+    sa.ldb = R4;
+    sa.Z0 = ctx->Z; sa.zstride = (long)nv * N2;
+    sa.ldl = nv; sa.ns = nv; sa.N = N2; sa.nmat = nwk;
+    {
+        SocPhase ps(ctx, AFQMC_PHASE_SOLVE, st);
+        if ((e = launch_lu_solve(st, sa)) != cudaSuccess) return e;
+    }
+    GemmArgs<double> h;
+    h.M = (int)R4; h.N = N2; h.K = nv; h.batch = nwk;
+    h.A = R; h.lda = nv; h.sA = ctx->st_w();
+    h.B = ctx->Z; h.ldb = N2; h.sB = (long)nv * N2;
+    h.C = ctx->Pb; h.ldc = N2; h.sC = R4 * N2;
+    if ((e = gemm<double>(st, h)) != cudaSuccess) return e;
+    count_launch();
+    soc_store_G_kernel<T><<<dim3(256, nwk), 256, 0, st>>>(ctx->Pb, R4 * N2, N2, (T*)ctx->G, ctx->ldz, ctx->gstride(),
+                                                         ctx->acc2, drift ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t soc_to_stack(afqmc_soc_ctx* ctx, cudaStream_t st, bool right, int j) {
+    double* dst = right ? ctx->stackR(j) : ctx->stackL(j);
+    return cudaMemcpy2DAsync(dst, ctx->st_w() * 8, ctx->Ucur, ctx->fsz() * 8, ctx->fsz() * 8, ctx->nwk,
+                             cudaMemcpyDeviceToDevice, st);
+}
+cudaError_t soc_from_stack(afqmc_soc_ctx* ctx, cudaStream_t st, bool right, int j) {
+    const double* src = right ? ctx->stackR(j) : ctx->stackL(j);
+    return cudaMemcpy2DAsync(ctx->Ucur, ctx->fsz() * 8, src, ctx->st_w() * 8, ctx->fsz() * 8, ctx->nwk,
+                             cudaMemcpyDeviceToDevice, st);
+}
+
+int check(afqmc_soc_ctx* ctx) {
+    if (!ctx) return AFQMC_ERR_ARG;
+    return ctx->sticky;
+}
+
+}  // namespace
+
+extern "C" {
+
+int afqmc_soc_create(afqmc_soc_ctx** out, const afqmc_soc_params* p) {
+    if (!out || !p) return AFQMC_ERR_ARG;
+    *out = nullptr;
+    const int L = p->L, N = L * L;
+    if (L < 2 || L > 48 || p->M < 1 || p->stab_every < 1 || p->M % p->stab_every != 0 || p->n_e < 1 ||
+        p->n_e > 2 * N || p->n_walkers < 1 || !(p->U <= 0.0) || !(p->dtau > 0.0))
+        return AFQMC_ERR_ARG;
+    if (p->precision != AFQMC_PREC_FP64 && p->precision != AFQMC_PREC_FP32) return AFQMC_ERR_ARG;
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return AFQMC_ERR_NODEV;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) return AFQMC_ERR_NODEV;
+    afqmc_soc_ctx* c = new afqmc_soc_ctx();
+    c->p = *p;
+    c->N = N;
+    c->N2 = 2 * N;
+    c->ne = p->n_e;
+    c->nv = 2 * p->n_e;
+    c->nwk = p->n_walkers;
+    c->ldz = ((2L * N + 31) / 32) * 32;
+    c->f64 = p->precision == AFQMC_PREC_FP64;
+    c->use_tc = !c->f64 && p->gemm != AFQMC_GEMM_SIMT;
+    c->kmax = c->f64 ? AFQMC_SOC_KMAX_FP64 : AFQMC_SOC_KMAX_FP32;
+    c->nst = p->M / p->stab_every + 1;
+    const double g = acos(exp(p->dtau * p->U / 2.0));
+    c->k.gamma = g;
+    c->k.c2m1 = cos(2.0 * g) - 1.0;
+    c->k.s2 = sin(2.0 * g);
+    c->k.c1m1 = cos(g) - 1.0;
+    c->k.s1 = sin(g);
+    *out = c;
+    return AFQMC_OK;
+}
+
+int afqmc_soc_destroy(afqmc_soc_ctx* ctx) {
+    if (!ctx) return AFQMC_OK;
+    cudaDeviceSynchronize();
+    for (void* q : ctx->allocs) cudaFree(q);
+    for (auto& ev : ctx->pending) {
+        cudaEventDestroy(ev.a);
+        cudaEventDestroy(ev.b);
+    }
+    for (auto ev : ctx->pool) cudaEventDestroy(ev);
+    delete ctx;
+    return AFQMC_OK;
+}
+
+int afqmc_soc_init(afqmc_soc_ctx* ctx, const double* P, const int8_t* fields, void* stream) {
+    int rc = check(ctx);
+    if (rc) return rc;
+    if (!P || ctx->inited) return AFQMC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->last = st;
+    const int N = ctx->N, N2 = ctx->N2, M = ctx->p.M, S = ctx->p.stab_every, nwk = ctx->nwk, ne = ctx->ne;
+    const long ldz = ctx->ldz, ld2 = 2 * ldz;
+    const size_t es = ctx->f64 ? 8 : 4;
+    const int kmax = ctx->kmax;
+    SCK(soc_alloc(ctx, &ctx->Ers, (size_t)N2 * ld2 * es, st));
+    SCK(soc_alloc(ctx, &ctx->Einvrs, (size_t)N2 * ld2 * es, st));
+    SCK(soc_alloc(ctx, &ctx->Ech, (size_t)ld2 * ld2 * es, st));
+    SCK(soc_alloc(ctx, &ctx->Einvch, (size_t)ld2 * ld2 * es, st));
+    SCK(soc_alloc(ctx, &ctx->dft, (size_t)ctx->p.L * ctx->p.L * 16, st));
+    SCK(soc_alloc(ctx, &ctx->lamk, (size_t)N * 64, st));
+    SCK(soc_alloc(ctx, &ctx->G, (size_t)nwk * ctx->gstride() * es, st));
+    SCK(soc_alloc(ctx, &ctx->S, (size_t)nwk * ld2 * ld2 * es, st));
+    SCK(soc_alloc(ctx, &ctx->x, (size_t)nwk * M * N, st));
+    SCK(soc_alloc(ctx, &ctx->u, (size_t)nwk * 2 * N * 8, st));
+    SCK(soc_alloc(ctx, &ctx->rep, (size_t)nwk * 2 * N, st));
+    SCK(soc_alloc(ctx, &ctx->dec, (size_t)nwk * 2 * N, st));
+    SCK(soc_alloc(ctx, &ctx->ratio, (size_t)nwk * 4 * N * 8, st));
+    SCK(soc_alloc(ctx, &ctx->lamp, (size_t)nwk * N * 8, st));
+    SCK(soc_alloc(ctx, &ctx->gid, (size_t)nwk * sizeof(int), st));
+    SCK(soc_alloc(ctx, &ctx->visit, 8, st));
+    SCK(soc_alloc(ctx, &ctx->X, (size_t)nwk * N2 * 4 * kmax * es, st));
+    SCK(soc_alloc(ctx, &ctx->Xp, (size_t)nwk * N2 * 4 * kmax * es, st));
+    SCK(soc_alloc(ctx, &ctx->Y, (size_t)nwk * 4 * kmax * ld2 * es, st));
+    SCK(soc_alloc(ctx, &ctx->W, (size_t)nwk * 16 * kmax * kmax * es, st));
+    SCK(soc_alloc(ctx, &ctx->Kdev, (size_t)nwk * sizeof(int), st));
+    SCK(soc_alloc(ctx, &ctx->sites, (size_t)nwk * kmax * sizeof(int), st));
+    SCK(soc_alloc(ctx, &ctx->err, sizeof(int), st));
+    SCK(soc_alloc(ctx, &ctx->URs, (size_t)nwk * ctx->st_w() * 8, st));
+    SCK(soc_alloc(ctx, &ctx->ULs, (size_t)nwk * ctx->st_w() * 8, st));
+    SCK(soc_alloc(ctx, &ctx->Ucur, (size_t)nwk * ctx->fsz() * 8, st));
+    SCK(soc_alloc(ctx, &ctx->Lrow, (size_t)nwk * ctx->fsz() * 8, st));
+    SCK(soc_alloc(ctx, &ctx->O, (size_t)nwk * ctx->nv * ctx->nv * 8, st));
+    SCK(soc_alloc(ctx, &ctx->Z, (size_t)nwk * ctx->nv * N2 * 8, st));
+    SCK(soc_alloc(ctx, &ctx->Pb, (size_t)nwk * 2 * N2 * N2 * 8, st));
+    SCK(soc_alloc(ctx, &ctx->perm, (size_t)nwk * 2 * N2 * sizeof(int), st));
+    SCK(soc_alloc(ctx, &ctx->flag, (size_t)nwk * 2 * N2, st));
+    SCK(soc_alloc(ctx, &ctx->acc2, (size_t)nwk * 16, st));
+    SCK(soc_alloc(ctx, &ctx->en, (size_t)nwk * 16, st));
+    if (ctx->f64) SCK(upload_constants<double>(ctx, st));
+    else SCK(upload_constants<float>(ctx, st));
+    count_launch();
+    soc_iota_kernel<<<(nwk + 255) / 256, 256, 0, st>>>(ctx->gid, nwk);
+    SCK(cudaGetLastError());
+    if (fields) {
+        SCK(cudaMemcpyAsync(ctx->x, fields, (size_t)nwk * M * N, cudaMemcpyHostToDevice, st));
+    } else {
+        count_launch();
+        soc_fields_kernel<<<dim3((unsigned)(((long)M * N + 255) / 256), nwk), 256, 0, st>>>(ctx->p.seed, (long)M * N,
+                                                                                          ctx->x);
+        SCK(cudaGetLastError());
+    }
+    // realified trial determinant [[Re P, -Im P], [Im P, Re P]] (4N x 2 n_e): U_R(0), and also
+    // the realified U_L(M)^+ = realified(P)
+    std::vector<double> R0((size_t)ctx->fsz());
+    const int nv = ctx->nv;
+    for (int a = 0; a < N2; ++a)
+        for (int c = 0; c < ne; ++c) {
+            const double pr = P[((size_t)a * ne + c) * 2], pi = P[((size_t)a * ne + c) * 2 + 1];
+            R0[(size_t)a * nv + c] = pr;
+            R0[(size_t)a * nv + ne + c] = -pi;
+            R0[(size_t)(N2 + a) * nv + c] = pi;
+            R0[(size_t)(N2 + a) * nv + ne + c] = pr;
+        }
+    for (int j = 0; j < nwk; ++j) {
+        SCK(cudaMemcpyAsync(ctx->Ucur + (size_t)j * ctx->fsz(), R0.data(), R0.size() * 8, cudaMemcpyHostToDevice, st));
+    }
+    SCK(cudaStreamSynchronize(st));  // R0 goes out of scope
+    SCK(soc_stab(ctx, st, ctx->Ucur, ctx->fsz()));
+    SCK(soc_to_stack(ctx, st, true, 0));
+    SCK(soc_to_stack(ctx, st, false, M / S));
+    for (int jj = M / S; jj >= 1; --jj) {
+        SCK(soc_propagate(ctx, st, ctx->Ucur, ctx->fsz(), 1, jj * S, -1, S));
+        SCK(soc_stab(ctx, st, ctx->Ucur, ctx->fsz()));
+        SCK(soc_to_stack(ctx, st, false, jj - 1));
+    }
+    if (ctx->f64) SCK(soc_form_G<double>(ctx, st, 0, false));
+    else SCK(soc_form_G<float>(ctx, st, 0, false));
+    SCK(cudaStreamSynchronize(st));
+    ctx->pos = 0;
+    ctx->last_dir = -1;
+    ctx->need_recompute = false;
+    ctx->inited = true;
+    return read_err(ctx);
+}
+
+int afqmc_soc_sweep_slice(afqmc_soc_ctx* ctx, int slice, int dir, int mode, int k, int nb, const uint8_t* replay,
+                          void* stream) {
+    int rc = check(ctx);
+    if (rc) return rc;
+    if (!ctx->inited || slice < 1 || slice > ctx->p.M || (dir != 1 && dir != -1)) return AFQMC_ERR_ARG;
+    if (mode != AFQMC_MODE_LOCAL && mode != AFQMC_MODE_DELAYED && mode != AFQMC_MODE_BLOCKFB) return AFQMC_ERR_ARG;
+    if (mode == AFQMC_MODE_DELAYED && (k < 1 || k > ctx->kmax)) return AFQMC_ERR_ARG;
+    if (mode == AFQMC_MODE_BLOCKFB && (nb < 1 || nb > ctx->kmax)) return AFQMC_ERR_ARG;
+    if (ctx->need_recompute) return AFQMC_ERR_STATE;
+    if ((dir > 0 && ctx->pos != slice - 1) || (dir < 0 && ctx->pos != slice)) return AFQMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->last = st;
+    const uint8_t* rep = nullptr;
+    if (replay) {
+        SCK(cudaMemcpyAsync(ctx->rep, replay, (size_t)ctx->nwk * 2 * ctx->N, cudaMemcpyHostToDevice, st));
+        SCK(cudaStreamSynchronize(st));
+        rep = ctx->rep;
+    }
+    rc = ctx->f64 ? soc_sweep<double>(ctx, slice, dir, mode, k, nb, rep, st)
+                  : soc_sweep<float>(ctx, slice, dir, mode, k, nb, rep, st);
+    if (rc) return rc;
+    ctx->pos = dir > 0 ? slice : slice - 1;
+    ctx->last_dir = dir;
+    if (ctx->pos % ctx->p.stab_every == 0) ctx->need_recompute = true;
+    return AFQMC_OK;
+}
+
+int afqmc_soc_recompute_G(afqmc_soc_ctx* ctx, double* rel_drift, void* stream) {
+    int rc = check(ctx);
+    if (rc) return rc;
+    if (!ctx->inited) return AFQMC_ERR_ARG;
+    const int S = ctx->p.stab_every;
+    if (ctx->pos % S != 0) return AFQMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->last = st;
+    const int j = ctx->pos / S;
+    SocPhase ps(ctx, AFQMC_PHASE_RECOMPUTE, st);
+    SCK(cudaMemsetAsync(ctx->acc2, 0, (size_t)ctx->nwk * 16, st));
+    const bool fwd = ctx->last_dir > 0;
+    const bool prop = fwd ? (j > 0) : (ctx->pos != ctx->p.M);
+    if (prop) {
+        SCK(soc_from_stack(ctx, st, fwd, fwd ? j - 1 : j + 1));
+        if (fwd) SCK(soc_propagate(ctx, st, ctx->Ucur, ctx->fsz(), 0, ctx->pos - S + 1, 1, S));
+        else SCK(soc_propagate(ctx, st, ctx->Ucur, ctx->fsz(), 1, ctx->pos + S, -1, S));
+        SCK(soc_stab(ctx, st, ctx->Ucur, ctx->fsz()));
+        SCK(soc_to_stack(ctx, st, fwd, j));
+    }
+    if (ctx->f64) SCK(soc_form_G<double>(ctx, st, j, true));
+    else SCK(soc_form_G<float>(ctx, st, j, true));
+    ctx->need_recompute = false;
+    if (rel_drift) {
+        SCK(cudaStreamSynchronize(st));
+        rc = read_err(ctx);
+        if (rc) return rc;
+        std::vector<double> h((size_t)ctx->nwk * 2);
+        SCK(cudaMemcpy(h.data(), ctx->acc2, h.size() * 8, cudaMemcpyDeviceToHost));
+        for (int w = 0; w < ctx->nwk; ++w) rel_drift[w] = h[2 * w + 1] > 0 ? sqrt(h[2 * w] / h[2 * w + 1]) : 0.0;
+    }
+    return AFQMC_OK;
+}
+
+int afqmc_soc_measure_energy(afqmc_soc_ctx* ctx, double* energy, void* stream) {
+    int rc = check(ctx);
+    if (rc) return rc;
+    if (!ctx->inited || !energy) return AFQMC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->last = st;
+    count_launch();
+    if (ctx->f64)
+        soc_energy_kernel<double><<<ctx->nwk, 256, 0, st>>>((const double*)ctx->G, ctx->ldz, ctx->gstride(), ctx->p.L,
+                                                           ctx->p.t, ctx->p.lam, ctx->p.U, ctx->en);
+    else
+        soc_energy_kernel<float><<<ctx->nwk, 256, 0, st>>>((const float*)ctx->G, ctx->ldz, ctx->gstride(), ctx->p.L,
+                                                          ctx->p.t, ctx->p.lam, ctx->p.U, ctx->en);
+    SCK(cudaGetLastError());
+    SCK(cudaStreamSynchronize(st));
+    rc = read_err(ctx);
+    if (rc) return rc;
+    SCK(cudaMemcpy(energy, ctx->en, (size_t)ctx->nwk * 16, cudaMemcpyDeviceToHost));
+    return AFQMC_OK;
+}
+
+static int soc_sync_walker(afqmc_soc_ctx* ctx, int walker) {
+    int rc = check(ctx);
+    if (rc) return rc;
+    if (!ctx->inited || walker < 0 || walker >= ctx->nwk) return AFQMC_ERR_ARG;
+    if (cudaStreamSynchronize(ctx->last) != cudaSuccess) return soc_fail(ctx, cudaGetLastError());
+    return read_err(ctx);
+}
+
+int afqmc_soc_get_G(afqmc_soc_ctx* ctx, int walker, double* out) {
+    int rc = soc_sync_walker(ctx, walker);
+    if (rc) return rc;
+    if (!out) return AFQMC_ERR_ARG;
+    const int N2 = ctx->N2;
+    const long ld2 = 2 * ctx->ldz;
+    const size_t es = ctx->f64 ? 8 : 4;
+    std::vector<unsigned char> h((size_t)N2 * ld2 * es);
+    SCK(cudaMemcpy(h.data(), (char*)ctx->G + (size_t)walker * ctx->gstride() * es, h.size(), cudaMemcpyDeviceToHost));
+    for (int r = 0; r < N2; ++r)
+        for (int c = 0; c < N2; ++c) {
+            double re, im;
+            if (ctx->f64) {
+                re = ((double*)h.data())[(size_t)r * ld2 + c];
+                im = ((double*)h.data())[(size_t)r * ld2 + ctx->ldz + c];
+            } else {
+                re = ((float*)h.data())[(size_t)r * ld2 + c];
+                im = ((float*)h.data())[(size_t)r * ld2 + ctx->ldz + c];
+            }
+            out[((size_t)r * N2 + c) * 2] = re;
+            out[((size_t)r * N2 + c) * 2 + 1] = im;
+        }
+    return AFQMC_OK;
+}
+
+int afqmc_soc_set_G(afqmc_soc_ctx* ctx, int walker, const double* in) {
+    int rc = soc_sync_walker(ctx, walker);
+    if (rc) return rc;
+    if (!in) return AFQMC_ERR_ARG;
+    const int N2 = ctx->N2;
+    const long ld2 = 2 * ctx->ldz;
+    const size_t es = ctx->f64 ? 8 : 4;
+    std::vector<unsigned char> h((size_t)N2 * ld2 * es, 0);
+    for (int r = 0; r < N2; ++r)
+        for (int c = 0; c < N2; ++c) {
+            const double re = in[((size_t)r * N2 + c) * 2], im = in[((size_t)r * N2 + c) * 2 + 1];
+            if (ctx->f64) {
+                ((double*)h.data())[(size_t)r * ld2 + c] = re;
+                ((double*)h.data())[(size_t)r * ld2 + ctx->ldz + c] = im;
+            } else {
+                ((float*)h.data())[(size_t)r * ld2 + c] = (float)re;
+                ((float*)h.data())[(size_t)r * ld2 + ctx->ldz + c] = (float)im;
+            }
+        }
+    SCK(cudaMemcpy((char*)ctx->G + (size_t)walker * ctx->gstride() * es, h.data(), h.size(), cudaMemcpyHostToDevice));
+    return AFQMC_OK;
+}
+
+int afqmc_soc_get_fields(afqmc_soc_ctx* ctx, int walker, int8_t* out) {
+    int rc = soc_sync_walker(ctx, walker);
+    if (rc) return rc;
+    if (!out) return AFQMC_ERR_ARG;
+    const size_t n = (size_t)ctx->p.M * ctx->N;
+    SCK(cudaMemcpy(out, ctx->x + (size_t)walker * n, n, cudaMemcpyDeviceToHost));
+    return AFQMC_OK;
+}
+
+int afqmc_soc_get_decisions(afqmc_soc_ctx* ctx, int walker, uint8_t* out) {
+    int rc = soc_sync_walker(ctx, walker);
+    if (rc) return rc;
+    if (!out) return AFQMC_ERR_ARG;
+    SCK(cudaMemcpy(out, ctx->dec + (size_t)walker * 2 * ctx->N, 2 * (size_t)ctx->N, cudaMemcpyDeviceToHost));
+    return AFQMC_OK;
+}
+
+int afqmc_soc_get_ratios(afqmc_soc_ctx* ctx, int walker, double* out) {
+    int rc = soc_sync_walker(ctx, walker);
+    if (rc) return rc;
+    if (!out) return AFQMC_ERR_ARG;
+    SCK(cudaMemcpy(out, ctx->ratio + (size_t)walker * 4 * ctx->N, 4 * (size_t)ctx->N * 8, cudaMemcpyDeviceToHost));
+    return AFQMC_OK;
+}
+
+int afqmc_soc_get_lam_plus(afqmc_soc_ctx* ctx, int walker, double* out) {
+    int rc = soc_sync_walker(ctx, walker);
+    if (rc) return rc;
+    if (!out) return AFQMC_ERR_ARG;
+    SCK(cudaMemcpy(out, ctx->lamp + (size_t)walker * ctx->N, (size_t)ctx->N * 8, cudaMemcpyDeviceToHost));
+    return AFQMC_OK;
+}
+
+int afqmc_soc_get_info(afqmc_soc_ctx* ctx, int* N, int* slice, int* dir) {
+    if (!ctx) return AFQMC_ERR_ARG;
+    if (N) *N = ctx->N;
+    if (slice) *slice = ctx->pos;
+    if (dir) *dir = ctx->last_dir;
+    return AFQMC_OK;
+}
+
+int afqmc_soc_set_profiling(afqmc_soc_ctx* ctx, int on) {
+    if (!ctx) return AFQMC_ERR_ARG;
+    ctx->prof_on = on != 0;
+    for (int q = 0; q < AFQMC_NPHASE; ++q) {
+        ctx->ms[q] = 0.0;
+        ctx->intervals[q] = 0;
+        ctx->launches[q] = 0;
+    }
+    for (auto& ev : ctx->pending) {
+        ctx->pool.push_back(ev.a);
+        ctx->pool.push_back(ev.b);
+    }
+    ctx->pending.clear();
+    return AFQMC_OK;
+}
+
+int afqmc_soc_get_profile(afqmc_soc_ctx* ctx, double* ms, int64_t* intervals, int64_t* launches) {
+    if (!ctx) return AFQMC_ERR_ARG;
+    if (ctx->last) cudaStreamSynchronize(ctx->last);
+    cudaDeviceSynchronize();
+    for (auto& ev : ctx->pending) {
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, ev.a, ev.b);
+        ctx->ms[ev.ph] += t;
+        ctx->intervals[ev.ph] += 1;
+        ctx->pool.push_back(ev.a);
+        ctx->pool.push_back(ev.b);
+    }
+    ctx->pending.clear();
+    for (int q = 0; q < AFQMC_NPHASE; ++q) {
+        if (ms) ms[q] = ctx->ms[q];
+        if (intervals) intervals[q] = ctx->intervals[q];
+        if (launches) launches[q] = ctx->launches[q];
+    }
+    return AFQMC_OK;
+}
+
+}  // extern "C"

@@ -1,5 +1,5 @@
-"""The C-ABI library builds, loads and exports every entry point include/afqmc.h declares
-(no compute calls: this runs without a GPU)."""
+"""The C-ABI library builds, loads and exports every entry point include/afqmc.h and
+include/afqmc_soc.h declare (no compute calls: this runs without a GPU)."""
 import ctypes
 import os
 import re
@@ -7,22 +7,28 @@ import subprocess
 
 import pytest
 
-from paper_2506_09611_gb300 import afqmc, build
+from paper_2506_09611_gb300 import afqmc, build, soc
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "afqmc.h")).read()
-    return sorted(set(re.findall(r"\b(afqmc_[a-z_A-Z]+)\s*\(", src)))
+def declared_symbols(header=None):
+    names = [header] if header else ["afqmc.h", "afqmc_soc.h"]
+    syms = set()
+    for h in names:
+        src = open(os.path.join(ROOT, "include", h)).read()
+        syms |= set(re.findall(r"\b(afqmc_[a-z_A-Z]+)\s*\(", src))
+    return sorted(syms)
 
 
 def test_header_declares_the_boundary():
-    syms = declared_symbols()
+    syms = declared_symbols("afqmc.h")
     for name in ("afqmc_create", "afqmc_destroy", "afqmc_init_walkers", "afqmc_sweep_slice",
                  "afqmc_recompute_G", "afqmc_measure_energy", "afqmc_strerror"):
         assert name in syms
     assert set(syms) == set(afqmc.EXPORTS)
+    soc_syms = declared_symbols("afqmc_soc.h")
+    assert set(soc_syms) - set(syms) == set(soc.EXPORTS)
 
 
 def test_library_builds_and_exports_every_symbol():
@@ -51,3 +57,14 @@ def test_create_rejects_bad_arguments_before_touching_the_device():
     bad3 = afqmc.afqmc_params(hs=7, precision=1, M=10, stab_every=5, t=1.0, U=4.0, dtau=0.05, seed=1)
     assert lib.afqmc_create(ctypes.byref(h), ctypes.byref(bad3)) == -1
     assert lib.afqmc_destroy(None) == 0
+
+
+def test_soc_create_rejects_bad_arguments_before_touching_the_device():
+    lib = soc.load()
+    h = ctypes.c_void_p()
+    good = dict(L=4, M=10, n_e=8, n_walkers=1, precision=0, gemm=0, stab_every=5, t=1.0, lam=0.5, U=-4.0,
+                dtau=0.05, seed=1)
+    for bad in (dict(U=4.0), dict(stab_every=3), dict(L=1), dict(n_e=33), dict(precision=7), dict(n_walkers=0)):
+        p = soc.afqmc_soc_params(**{**good, **bad})
+        assert lib.afqmc_soc_create(ctypes.byref(h), ctypes.byref(p)) == -1, bad
+    assert lib.afqmc_soc_destroy(None) == 0
