@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed walker population leg")
+    ap.add_argument("--no-soc", action="store_true", help="skip the spin-orbit-coupled leg")
+    ap.add_argument("--soc-slices", type=int, default=20, help="timed slice-steps per mode of the SOC leg")
     ap.add_argument("--gemm", default="tc3", choices=["tc3", "simt", "tf32"],
                     help="FP32 GEMM engine: tcgen05 three-term TF32 split, FP32 SIMT, or one TF32 pass")
     return ap.parse_args()
@@ -295,6 +297,9 @@ def main():
     batch = None
     if not args.no_batch:
         batch = batched_population(afqmc, torch, stream, args, seed)
+    soc_res = None
+    if not args.no_soc:
+        soc_res = soc_leg(torch, stream, args, seed)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, secs = run_oracle_sample(CPU_SLICES, args.k)
@@ -328,6 +333,7 @@ def main():
             "e2e": e2e,
             "cuda_graphs": graphs,
             "batched_population": batch,
+            "soc": soc_res,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -464,6 +470,75 @@ def batched_population(afqmc, torch, stream, args, seed):
             "cuda_graphs": {"value": upd / (ms_graph / 1e3), "ms_per_sweep": ms_graph},
             "note": "one sweep = 2M slice-steps of every walker + 8 FP64 recomputes; walkers of one lattice "
                     "share every launch, groups run on concurrent streams"}
+
+
+SOC_L, SOC_LAM, SOC_U, SOC_M, SOC_STAB = 24, 0.5, -4.0, 80, 10
+
+
+def soc_leg(torch, stream, args, seed):
+    """The spin-orbit-coupled workload: 24 x 24 Rashba-Hubbard lattice (2N = 1152 complex orbitals),
+    lambda/t = 0.5, U/t = -4 (spin-y decoupling), half filling (576 particles), dtau = 0.05, M = 80,
+    FP32 (complex64) bulk G with the FP64 recompute every 10 slices.  Per mode, a fresh walker sweeps
+    slices 1..10 untimed, then the timed sample of slices 11..10+S (with its recomputes) under
+    per-phase CUDA events; the local update is the baseline."""
+    from paper_2506_09611_gb300 import soc
+
+    n_e = SOC_L * SOC_L
+    Ns = SOC_L * SOC_L
+    P = inputs.soc_trial_state(SOC_L, n_e, lam=SOC_LAM)
+    X = inputs.initial_fields(SOC_M, Ns, seed=seed)
+    out = {}
+    S = args.soc_slices
+    for name, mode, k, nb in (("local", "local", 1, 1), ("delayed_k32", "delayed", 32, 1),
+                              ("delayed_k64", "delayed", 64, 1), ("blockfb_nb4", "blockfb", 1, 4),
+                              ("blockfb_nb16", "blockfb", 1, 16), ("blockfb_nb64", "blockfb", 1, 64)):
+        ctx = soc.SocContext(SOC_L, SOC_M, n_e, 1, "fp32", args.gemm, SOC_STAB, T_HOP, SOC_LAM, SOC_U, DTAU, seed)
+        ctx.init(P, X, stream=stream)
+
+        def run(a, b, decisions=None):
+            for ell in range(a, b + 1):
+                ctx.sweep_slice(ell, +1, mode, k=k, nb=nb, stream=stream)
+                if decisions is not None:
+                    decisions.append(ctx.decisions(0))
+                if ell % SOC_STAB == 0:
+                    soc.afqmc_soc_recompute_G(ctx.h, None, stream)
+
+        run(1, 10)
+        torch.cuda.synchronize()
+        x0 = ctx.fields(0)
+        ctx.set_profiling(True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        run(11, 10 + S)
+        b.record(stream)
+        torch.cuda.synchronize()
+        prof = ctx.profile()
+        ctx.set_profiling(False)
+        ms = a.elapsed_time(b)
+        flips = int((ctx.fields(0) != x0).sum())
+        dec = []
+        run(11 + S, min(SOC_M, 12 + S), dec)  # decision sample (untimed): acceptance
+        if mode == "blockfb":
+            nbk = (Ns + nb - 1) // nb
+            acc = float(np.mean([d[Ns:Ns + nbk].mean() for d in dec]))
+        else:
+            acc = float(np.mean([d[:Ns].mean() for d in dec]))
+        upd = Ns * S
+        t_upd = prof["prep"]["ms"] + prof["chain"]["ms"] + prof["flush"]["ms"]
+        out[name] = {"update_only": upd / (t_upd / 1e3), "with_wrap": upd / ((t_upd + prof["wrap"]["ms"]) / 1e3),
+                     "with_recompute": upd / (ms / 1e3), "acceptance": acc, "flip_rate": flips / upd,
+                     "ms_per_slice": {p: prof[p]["ms"] / S for p in ("prep", "wrap", "chain", "flush", "recompute")},
+                     "launches_per_slice": sum(v["launches"] for v in prof.values()) / S}
+        ctx.close()
+    base = out["local"]["update_only"]
+    return {"metric": "field updates/s, spin-orbit-coupled Hubbard 24x24 (complex G 1152x1152)", "unit": UNIT,
+            "config": {"L": SOC_L, "lambda": SOC_LAM, "U": SOC_U, "n_e": n_e, "dtau": DTAU, "M": SOC_M,
+                       "stab_every": SOC_STAB, "precision": "fp32 (complex64) bulk, FP64 recompute",
+                       "gemm": args.gemm, "timed_slices": S},
+            "modes": out,
+            "speedup_update_only_vs_local": {m: v["update_only"] / base for m, v in out.items() if m != "local"},
+            "speedup_with_wrap_vs_local": {m: v["with_wrap"] / out["local"]["with_wrap"] for m, v in out.items()
+                                           if m != "local"}}
 
 
 def end_to_end(afqmc, torch, stream, args, seed, rank):
