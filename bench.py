@@ -527,7 +527,7 @@ def soc_leg(torch, stream, args, seed):
         t_upd = prof["prep"]["ms"] + prof["chain"]["ms"] + prof["flush"]["ms"]
         out[name] = {"update_only": upd / (t_upd / 1e3), "with_wrap": upd / ((t_upd + prof["wrap"]["ms"]) / 1e3),
                      "with_recompute": upd / (ms / 1e3), "acceptance": acc, "flip_rate": flips / upd,
-                     "ms_per_slice": {p: prof[p]["ms"] / S for p in ("prep", "wrap", "chain", "flush", "recompute")},
+                     "ms_per_slice": {p: prof[p]["ms"] / S for p in prof if prof[p]["intervals"]},
                      "launches_per_slice": sum(v["launches"] for v in prof.values()) / S}
         ctx.close()
     base = out["local"]["update_only"]

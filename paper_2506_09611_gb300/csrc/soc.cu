@@ -167,9 +167,11 @@ struct SocWinArgs {
     double* lam0;        // N per walker
     int* sites0;         // kmax per walker: accepted (flipped) sites in order
     int kmax;
-    void* W0;            // realified W, (4 kmax)^2 per walker
-    int* Kdev;           // per walker: 4 m (real inner dimension of the flush), 0 = no flush
+    void* W0;            // W (2m x 2m complex, leading dimension 2 kmax) per walker
+    int* Kdev;           // per walker: 2m (complex orbitals of the update), 0 = no update
     int* err;
+    int xw_inline;       // n <= 4: the kernel also forms X' = G[:, F] W (2N x 2m) at Xp0
+    void* Xp0;
 };
 
 template <typename T>
@@ -178,37 +180,31 @@ __device__ __forceinline__ cx<T> g_at(const T* G, long ldz, int r, int c) {
 }
 
 // In-place inverse of the 2m x 2m complex matrix M (row stride ldm) by Gauss-Jordan with the
-// 2 x 2 diagonal blocks as pivots.  det (thread 0 only) receives the product of the pivot block
+// 2 x 2 diagonal blocks as pivots (every thread inverts the pivot block itself, so a step costs
+// two barriers).  det (thread 0 only, nullable) receives the product of the pivot block
 // determinants, i.e. det M.  colF: 2 * 2m complex scratch.  Returns false (on every thread) if a
 // pivot block is singular or not finite.
 template <typename T>
-__device__ bool gj_inverse_2x2(cx<T>* M, int m2, int ldm, cx<T>* colF, cx<double>* det, c22<T>* s_pi, int* s_ok) {
+__device__ bool gj_inverse_2x2(cx<T>* M, int m2, int ldm, cx<T>* colF, cx<T>* det) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    if (tid == 0) {
-        *s_ok = 1;
-        if (det) *det = cmk(1.0, 0.0);
-    }
+    const int per = nt / m2, jj = tid % m2, i0 = tid / m2;  // 2D map of the trailing update
+    cx<T> dacc = cmk((T)1, (T)0);
     for (int t = 0; t < m2 / 2; ++t) {
         const int q0 = 2 * t;
         __syncthreads();
-        if (tid == 0) {
-            const cx<T> a = M[q0 * ldm + q0], b = M[q0 * ldm + q0 + 1];
-            const cx<T> c = M[(q0 + 1) * ldm + q0], d = M[(q0 + 1) * ldm + q0 + 1];
-            const cx<T> dt = csub(cmul(a, d), cmul(b, c));
-            const T mag = dt.r * dt.r + dt.i * dt.i;
-            if (!(mag > (T)0) || !isfinite(mag)) *s_ok = 0;
-            const cx<T> di = cinv(dt);
-            s_pi->a[0][0] = cmul(d, di);
-            s_pi->a[0][1] = cmul(cmk(-b.r, -b.i), di);
-            s_pi->a[1][0] = cmul(cmk(-c.r, -c.i), di);
-            s_pi->a[1][1] = cmul(a, di);
-            if (det) *det = cmul(*det, cmk((double)dt.r, (double)dt.i));
-        }
-        __syncthreads();
-        if (!*s_ok) return false;
-        const c22<T> P = *s_pi;
-        // pivot rows: M[q0 + p][j] <- sum P[p][p'] M[q0 + p'][j] (j outside the pivot block);
-        // save the pivot columns of the other rows
+        const cx<T> a = M[q0 * ldm + q0], b = M[q0 * ldm + q0 + 1];
+        const cx<T> c = M[(q0 + 1) * ldm + q0], d = M[(q0 + 1) * ldm + q0 + 1];
+        const cx<T> dt = csub(cmul(a, d), cmul(b, c));
+        const T mag = dt.r * dt.r + dt.i * dt.i;
+        if (!(mag > (T)0) || !isfinite(mag)) return false;  // uniform: every thread read the same block
+        const cx<T> di = cinv(dt);
+        c22<T> P;
+        P.a[0][0] = cmul(d, di);
+        P.a[0][1] = cmul(cmk(-b.r, -b.i), di);
+        P.a[1][0] = cmul(cmk(-c.r, -c.i), di);
+        P.a[1][1] = cmul(a, di);
+        dacc = cmul(dacc, dt);
+        __syncthreads();  // every thread has read the pivot block
         for (int j = tid; j < m2; j += nt) {
             if (j == q0 || j == q0 + 1) {
                 colF[2 * j] = cmk((T)0, (T)0);
@@ -225,55 +221,78 @@ __device__ bool gj_inverse_2x2(cx<T>* M, int m2, int ldm, cx<T>* colF, cx<double
             colF[2 * j + 1] = M[j * ldm + q0 + 1];
         }
         __syncthreads();
-        // other rows: M[i][j] -= F_i . M[pivot rows][j];  M[i][pivot cols] = -F_i P
-        for (int e = tid; e < m2 * m2; e += nt) {
-            const int i = e / m2, j = e - i * m2;
-            if (i == q0 || i == q0 + 1) {
-                if (j == q0 || j == q0 + 1) M[i * ldm + j] = P.a[i - q0][j - q0];
-                continue;
-            }
-            const cx<T> f0 = colF[2 * i], f1 = colF[2 * i + 1];
-            if (j == q0 || j == q0 + 1) {
-                const int p = j - q0;
-                cx<T> w = cmul(f0, P.a[0][p]);
-                cfma(w, f1, P.a[1][p]);
-                M[i * ldm + j] = cmk(-w.r, -w.i);
-            } else {
-                cx<T> w = M[i * ldm + j];
-                const cx<T> nf0 = cmk(-f0.r, -f0.i), nf1 = cmk(-f1.r, -f1.i);
-                cfma(w, nf0, M[q0 * ldm + j]);
-                cfma(w, nf1, M[(q0 + 1) * ldm + j]);
-                M[i * ldm + j] = w;
+        if (i0 < per) {
+            const int j = jj;
+            const bool jp = (j == q0 || j == q0 + 1);
+            const cx<T> p0 = M[q0 * ldm + j], p1 = M[(q0 + 1) * ldm + j];
+            for (int i = i0; i < m2; i += per) {
+                if (i == q0 || i == q0 + 1) {
+                    if (jp) M[i * ldm + j] = P.a[i - q0][j - q0];
+                    continue;
+                }
+                const cx<T> f0 = colF[2 * i], f1 = colF[2 * i + 1];
+                if (jp) {
+                    const int p = j - q0;
+                    cx<T> w = cmul(f0, P.a[0][p]);
+                    cfma(w, f1, P.a[1][p]);
+                    M[i * ldm + j] = cmk(-w.r, -w.i);
+                } else {
+                    cx<T> w = M[i * ldm + j];
+                    cfma(w, cmk(-f0.r, -f0.i), p0);
+                    cfma(w, cmk(-f1.r, -f1.i), p1);
+                    M[i * ldm + j] = w;
+                }
             }
         }
     }
     __syncthreads();
+    if (det && threadIdx.x == 0) *det = dacc;
     return true;
 }
 
-// W = Delta_F Minv as the realified, K-interleaved (4m x 4m) right operand of the flush:
-//   Wr[2q][2q'] = Re W, [2q][2q'+1] = Im W, [2q+1][2q'] = -Im W, [2q+1][2q'+1] = Re W.
-// Delta_F is block diagonal: the 2 x 2 block dl[t] of flipped site t (real).
+// W = Delta_F Minv (2m x 2m complex, leading dimension ldw).  Delta_F is block diagonal: the
+// 2 x 2 block dl[t] of flipped site t (real).
 template <typename T>
-__device__ void write_W(const cx<T>* Minv, int m2, int ldm, const T (*dl)[2][2], T* W, int ldw) {
+__device__ void write_W(const cx<T>* Minv, int m2, int ldm, const T (*dl)[2][2], cx<T>* W, int ldw) {
     for (int e = threadIdx.x; e < m2 * m2; e += blockDim.x) {
         const int q = e / m2, qq = e - q * m2;
         const int t = q >> 1, p = q & 1;
-        cx<T> w = cscale(Minv[(2 * t) * ldm + qq], dl[t][p][0]);
-        const cx<T> w1 = cscale(Minv[(2 * t + 1) * ldm + qq], dl[t][p][1]);
-        w = cadd(w, w1);
-        W[(long)(2 * q) * ldw + 2 * qq] = w.r;
-        W[(long)(2 * q) * ldw + 2 * qq + 1] = w.i;
-        W[(long)(2 * q + 1) * ldw + 2 * qq] = -w.i;
-        W[(long)(2 * q + 1) * ldw + 2 * qq + 1] = w.r;
+        const cx<T> w = cadd(cscale(Minv[(2 * t) * ldm + qq], dl[t][p][0]), cscale(Minv[(2 * t + 1) * ldm + qq], dl[t][p][1]));
+        W[(long)q * ldw + qq] = w;
     }
+}
+
+// The flip delta of site field x and the 2 x 2 test of the site block g (all in registers):
+// R = det(1 + delta A), W2 = delta (1 + A delta)^{-1}, A = 1 - g.
+template <typename T>
+__device__ __forceinline__ cx<T> site_test(const cx<T> g[2][2], const T dl[2][2], c22<T>& w2) {
+    cx<T> A[2][2], m1[2][2], m2[2][2];
+    for (int p = 0; p < 2; ++p)
+        for (int q = 0; q < 2; ++q) A[p][q] = cmk((p == q ? (T)1 : (T)0) - g[p][q].r, -g[p][q].i);
+    for (int p = 0; p < 2; ++p)
+        for (int q = 0; q < 2; ++q) {
+            m1[p][q] = cmk(p == q ? (T)1 : (T)0, (T)0);
+            m2[p][q] = m1[p][q];
+            for (int r = 0; r < 2; ++r) {
+                m1[p][q] = cadd(m1[p][q], cscale(A[r][q], dl[p][r]));
+                m2[p][q] = cadd(m2[p][q], cscale(A[p][r], dl[r][q]));
+            }
+        }
+    const cx<T> R = csub(cmul(m1[0][0], m1[1][1]), cmul(m1[0][1], m1[1][0]));
+    const cx<T> d2 = csub(cmul(m2[0][0], m2[1][1]), cmul(m2[0][1], m2[1][0]));
+    const cx<T> di = cinv(d2);
+    const cx<T> inv[2][2] = {{cmul(m2[1][1], di), cmul(cmk(-m2[0][1].r, -m2[0][1].i), di)},
+                             {cmul(cmk(-m2[1][0].r, -m2[1][0].i), di), cmul(m2[0][0], di)}};
+    for (int p = 0; p < 2; ++p)
+        for (int q = 0; q < 2; ++q) w2.a[p][q] = cadd(cscale(inv[0][q], dl[p][0]), cscale(inv[1][q], dl[p][1]));
+    return R;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
     extern __shared__ __align__(16) unsigned char soc_smem[];
     const int z = blockIdx.x;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int N = a.N, n = a.n, s0 = a.s0, n2 = 2 * n;
     const long ldz = a.ldz;
     const T* G = (const T*)a.G0 + (long)z * a.gstride;
@@ -284,20 +303,27 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
     double* ratio = a.ratio0 + (long)z * 4 * N;
     double* lam = a.lam0 + (long)z * N;
     int* sites = a.sites0 + (long)z * a.kmax;
-    T* W = (T*)a.W0 + (long)z * 16 * a.kmax * a.kmax;
-    const int ldw = 4 * a.kmax;
+    cx<T>* W = (cx<T>*)a.W0 + (long)z * 4 * a.kmax * a.kmax;
+    const int ldw = 2 * a.kmax;
 
     cx<T>* Mw = (cx<T>*)soc_smem;               // (2 kmax)^2: the window block / the LU matrix
     cx<T>* aux = Mw + 4 * a.kmax * a.kmax;      // 8 kmax: column / row snapshots, GJ scratch
     __shared__ T s_dl[64][2][2];                // flip deltas of the flipped sites
     __shared__ int s_site[64];
-    __shared__ int s_m, s_acc, s_ok;
-    __shared__ c22<T> s_w2, s_pi;
-    __shared__ cx<double> s_det;
-    __shared__ cx<T> s_ob[64];
+    __shared__ T s_uT[64];
+    __shared__ int s_x[64], s_rep[64];
+    __shared__ int s_take[2], s_m, s_acc;
+    __shared__ T s_logq;
+    __shared__ c22<T> s_w2;
+    __shared__ cx<T> s_det;
     auto orb = [&](int q) { return (q & 1) ? N + s0 + (q >> 1) : s0 + (q >> 1); };
 
-    if (tid == 0) s_m = 0;
+    for (int t = tid; t < n; t += nt) {
+        s_uT[t] = (T)u[s0 + t];
+        s_x[t] = x[s0 + t];
+        s_rep[t] = rep ? (int)rep[s0 + t] : -1;
+    }
+    int m2 = 0;  // complex orbitals of the window's update (uniform)
     if (a.mode == 0) {
         // ---- sites one after another on the 2n x 2n block ----
         for (int e = tid; e < n2 * n2; e += nt) {
@@ -305,92 +331,184 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
             Mw[e] = g_at(G, ldz, orb(r), orb(c));
         }
         __syncthreads();
+        int m = 0;
+        cx<T>* colW = aux;           // [n2][2]
+        cx<T>* rowY = aux + 2 * n2;  // [2][n2]
+        const int per = nt / n2, cc = tid % n2, r0 = tid / n2;  // 2D map of the rank-2 update
         for (int t = 0; t < n; ++t) {
-            const int i = s0 + t;
-            if (tid == 0) {
-                const int xi = x[i];
+            if (warp == 0) {
+                // warp 0 takes the decision (all lanes alike) and snapshots the rank-2 factors
+                const int xi = s_x[t];
                 T dl[2][2];
                 real_delta<T>(a.k.c2m1, a.k.s2, xi, dl);
-                cx<T> A[2][2];
+                cx<T> g[2][2];
                 for (int p = 0; p < 2; ++p)
-                    for (int q = 0; q < 2; ++q) {
-                        const cx<T> g = Mw[(2 * t + p) * n2 + 2 * t + q];
-                        A[p][q] = cmk((p == q ? (T)1 : (T)0) - g.r, -g.i);
-                    }
-                // m1 = 1 + delta A (ratio), m2 = 1 + A delta (for W)
-                cx<T> m1[2][2], m2[2][2];
-                for (int p = 0; p < 2; ++p)
-                    for (int q = 0; q < 2; ++q) {
-                        m1[p][q] = cmk(p == q ? (T)1 : (T)0, (T)0);
-                        m2[p][q] = m1[p][q];
-                        for (int r = 0; r < 2; ++r) {
-                            m1[p][q] = cadd(m1[p][q], cscale(A[r][q], dl[p][r]));
-                            m2[p][q] = cadd(m2[p][q], cscale(A[p][r], dl[r][q]));
+                    for (int q = 0; q < 2; ++q) g[p][q] = Mw[(2 * t + p) * n2 + 2 * t + q];
+                c22<T> w2;
+                const cx<T> R = site_test<T>(g, dl, w2);
+                // the test in the bulk precision (the FP32 bulk rounds u to float: a bias below
+                // 2^-25 in the acceptance probability)
+                const T absR = sqrt(R.r * R.r + R.i * R.i);
+                const bool fin = isfinite(absR);
+                const int acc = s_rep[t] >= 0 ? (s_rep[t] != 0) : (s_uT[t] < absR);
+                const bool take = acc && fin && absR > (T)0;
+                if (take) {
+                    for (int r = lane; r < n2; r += 32) {
+                        const cx<T> g0 = Mw[r * n2 + 2 * t], g1 = Mw[r * n2 + 2 * t + 1];
+                        for (int q = 0; q < 2; ++q) {
+                            cx<T> v = cmul(g0, w2.a[0][q]);
+                            cfma(v, g1, w2.a[1][q]);
+                            colW[2 * r + q] = v;
+                        }
+                        for (int p = 0; p < 2; ++p) {
+                            const cx<T> gg = Mw[(2 * t + p) * n2 + r];
+                            rowY[p * n2 + r] = cmk((r == 2 * t + p ? (T)1 : (T)0) - gg.r, -gg.i);
                         }
                     }
-                const cx<T> R = csub(cmul(m1[0][0], m1[1][1]), cmul(m1[0][1], m1[1][0]));
-                const cx<T> d2 = csub(cmul(m2[0][0], m2[1][1]), cmul(m2[0][1], m2[1][0]));
-                const double absR = sqrt((double)R.r * R.r + (double)R.i * R.i);
-                ratio[2 * i] = (double)R.r;
-                ratio[2 * i + 1] = (double)R.i;
-                if (!isfinite(absR)) set_err(a.err, DEV_NUMERIC);
-                const int acc = rep ? (rep[i] != 0) : (u[i] < absR);
-                dec[i] = (uint8_t)acc;
-                s_acc = acc && isfinite(absR) && absR > 0.0;
-                if (s_acc) {
-                    const cx<T> di = cinv(d2);
-                    const cx<T> inv[2][2] = {{cmul(m2[1][1], di), cmul(cmk(-m2[0][1].r, -m2[0][1].i), di)},
-                                             {cmul(cmk(-m2[1][0].r, -m2[1][0].i), di), cmul(m2[0][0], di)}};
-                    for (int p = 0; p < 2; ++p)
-                        for (int q = 0; q < 2; ++q)
-                            s_w2.a[p][q] = cadd(cscale(inv[0][q], dl[p][0]), cscale(inv[1][q], dl[p][1]));
-                    const int mm = s_m;
-                    for (int p = 0; p < 2; ++p)
-                        for (int q = 0; q < 2; ++q) s_dl[mm][p][q] = dl[p][q];
-                    s_site[mm] = i;
-                    sites[mm] = i;
-                    s_m = mm + 1;
-                    x[i] = (int8_t)(-xi);
+                }
+                if (lane == 0) {
+                    const int i = s0 + t;
+                    ratio[2 * i] = (double)R.r;
+                    ratio[2 * i + 1] = (double)R.i;
+                    dec[i] = (uint8_t)acc;
+                    if (!fin) set_err(a.err, DEV_NUMERIC);
+                    if (take) {
+                        for (int p = 0; p < 2; ++p)
+                            for (int q = 0; q < 2; ++q) s_dl[m][p][q] = dl[p][q];
+                        s_site[m] = i;
+                        sites[m] = i;
+                        x[i] = (int8_t)(-xi);
+                    }
+                    s_take[t & 1] = take;
                 }
             }
             __syncthreads();
-            if (!s_acc) continue;
-            // snapshot: (G[:, S] W) and (E_S^T - G[S, :]) on the block
-            cx<T>* colW = aux;           // [n2][2]
-            cx<T>* rowY = aux + 2 * n2;  // [2][n2]
-            const c22<T> w2 = s_w2;
-            for (int r = tid; r < n2; r += nt) {
-                const cx<T> g0 = Mw[r * n2 + 2 * t], g1 = Mw[r * n2 + 2 * t + 1];
-                for (int q = 0; q < 2; ++q) {
-                    cx<T> v = cmul(g0, w2.a[0][q]);
-                    cfma(v, g1, w2.a[1][q]);
-                    colW[2 * r + q] = v;
+            if (!s_take[t & 1]) continue;
+            ++m;
+            if (r0 < per) {
+                const cx<T> y0 = rowY[cc], y1 = rowY[n2 + cc];
+                for (int r = r0; r < n2; r += per) {
+                    cx<T> v = Mw[r * n2 + cc];
+                    const cx<T> c0 = colW[2 * r], c1 = colW[2 * r + 1];
+                    cfma(v, cmk(-c0.r, -c0.i), y0);
+                    cfma(v, cmk(-c1.r, -c1.i), y1);
+                    Mw[r * n2 + cc] = v;
                 }
-                for (int p = 0; p < 2; ++p) {
-                    const cx<T> g = Mw[(2 * t + p) * n2 + r];
-                    rowY[p * n2 + r] = cmk((r == 2 * t + p ? (T)1 : (T)0) - g.r, -g.i);
-                }
-            }
-            __syncthreads();
-            for (int e = tid; e < n2 * n2; e += nt) {
-                const int r = e / n2, c = e - r * n2;
-                cx<T> v = Mw[e];
-                const cx<T> c0 = colW[2 * r], c1 = colW[2 * r + 1];
-                cfma(v, cmk(-c0.r, -c0.i), rowY[c]);
-                cfma(v, cmk(-c1.r, -c1.i), rowY[n2 + c]);
-                Mw[e] = v;
             }
             __syncthreads();
         }
-        __syncthreads();
-        const int m = s_m;
         if (m == 0) {
             if (tid == 0) a.Kdev[z] = 0;
             return;
         }
-        // M = 1 + A_FF Delta_F from the window's starting G (the bulk G is unchanged so far);
-        // the flipped sites' old fields are -x now
-        const int m2 = 2 * m;
+        // M = 1 + A_FF Delta_F from the window's starting G (the bulk G is unchanged so far)
+        m2 = 2 * m;
+        for (int e = tid; e < m2 * m2; e += nt) {
+            const int q = e / m2, qq = e - q * m2;
+            const int t2 = qq >> 1, p2 = qq & 1;
+            const int rq = (q & 1) ? N + s_site[q >> 1] : s_site[q >> 1];
+            cx<T> v = cmk((q == qq) ? (T)1 : (T)0, (T)0);
+            for (int p = 0; p < 2; ++p) {
+                const int cq = p ? N + s_site[t2] : s_site[t2];
+                const cx<T> gg = g_at(G, ldz, rq, cq);
+                const cx<T> Aq = cmk((rq == cq ? (T)1 : (T)0) - gg.r, -gg.i);
+                v = cadd(v, cscale(Aq, s_dl[t2][p][p2]));
+            }
+            Mw[e] = v;
+        }
+        if (!gj_inverse_2x2<T>(Mw, m2, m2, aux, nullptr)) {
+            if (tid == 0) {
+                set_err(a.err, DEV_NUMERIC);
+                a.Kdev[z] = 0;
+            }
+            return;
+        }
+    } else {
+        // ---- block force bias over the block [s0, s0 + n) ----
+        __syncthreads();
+        // stripped matrix Mb = 1 + A_bb Delta_s, Delta_s = A(-gamma x) - 1 per site
+        for (int e = tid; e < n2 * n2; e += nt) {
+            const int q = e / n2, qq = e - q * n2;
+            const int t2 = qq >> 1, p2 = qq & 1;
+            T ds[2][2];
+            real_delta<T>(a.k.c1m1, a.k.s1, s_x[t2], ds);
+            cx<T> v = cmk((q == qq) ? (T)1 : (T)0, (T)0);
+            for (int p = 0; p < 2; ++p) {
+                const int cq = 2 * t2 + p;
+                const cx<T> g = g_at(G, ldz, orb(q), orb(cq));
+                const cx<T> Aq = cmk((q == cq ? (T)1 : (T)0) - g.r, -g.i);
+                v = cadd(v, cscale(Aq, ds[p][p2]));
+            }
+            Mw[e] = v;
+        }
+        if (!gj_inverse_2x2<T>(Mw, n2, n2, aux, nullptr)) {
+            if (tid == 0) {
+                set_err(a.err, DEV_NUMERIC);
+                a.Kdev[z] = 0;
+            }
+            return;
+        }
+        // (Minv A)[2t + p][2t + q] for the four entries of every site: one warp per (t, p, q)
+        {
+            const int nw = nt >> 5;
+            for (int e = warp; e < 4 * n; e += nw) {
+                const int t = e >> 2, p = (e >> 1) & 1, q = e & 1;
+                const int row = 2 * t + p, col = 2 * t + q;
+                cx<T> acc = cmk((T)0, (T)0);
+                for (int r = lane; r < n2; r += 32) {
+                    const cx<T> g = g_at(G, ldz, orb(r), orb(col));
+                    const cx<T> Ar = cmk((r == col ? (T)1 : (T)0) - g.r, -g.i);
+                    cfma(acc, Mw[row * n2 + r], Ar);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    acc.r += __shfl_xor_sync(0xffffffffu, acc.r, o);
+                    acc.i += __shfl_xor_sync(0xffffffffu, acc.i, o);
+                }
+                if (lane == 0) aux[e] = acc;  // aux[4t + 2p + q]
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            // obar_t = Abar[dn t, up t] - Abar[up t, dn t], Abar = (1 + Delta_s) Minv A, 1 + Delta_s = A(-gamma x);
+            // the proposal weight of x' is exp(x' h), h = gamma Re(obar) (bulk precision)
+            T logq = 0;
+            int m = 0;
+            for (int t = 0; t < n; ++t) {
+                const int i = s0 + t, xi = s_x[t];
+                const T c = (T)(a.k.c1m1 + 1.0), s = (T)(-xi * a.k.s1);  // A(-gamma x) = [[c, s], [-s, c]]
+                const cx<T> MA00 = aux[4 * t], MA01 = aux[4 * t + 1], MA10 = aux[4 * t + 2], MA11 = aux[4 * t + 3];
+                const cx<T> dn_up = cadd(cscale(MA00, -s), cscale(MA10, c));
+                const cx<T> up_dn = cadd(cscale(MA01, c), cscale(MA11, s));
+                const T h = (T)a.k.gamma * (dn_up.r - up_dn.r);
+                const T lp = (T)1 / ((T)1 + exp((T)-2 * h));
+                lam[i] = (double)lp;
+                const int xp = s_rep[t] >= 0 ? (s_rep[t] ? 1 : -1) : (s_uT[t] < lp ? 1 : -1);
+                dec[i] = (uint8_t)(xp > 0);
+                if (xp != xi) {
+                    T dl[2][2];
+                    real_delta<T>(a.k.c2m1, a.k.s2, xi, dl);
+                    for (int p = 0; p < 2; ++p)
+                        for (int q = 0; q < 2; ++q) s_dl[m][p][q] = dl[p][q];
+                    s_site[m] = i;
+                    logq += (T)(xi - xp) * h;
+                    ++m;
+                }
+            }
+            s_m = m;
+            s_logq = logq;
+        }
+        __syncthreads();
+        const int m = s_m;
+        if (m == 0) {
+            if (tid == 0) {
+                dec[N + a.blk] = 1;
+                ratio[2 * (N + a.blk)] = 1.0;
+                ratio[2 * (N + a.blk) + 1] = 0.0;
+                a.Kdev[z] = 0;
+            }
+            return;
+        }
+        m2 = 2 * m;
         for (int e = tid; e < m2 * m2; e += nt) {
             const int q = e / m2, qq = e - q * m2;
             const int t2 = qq >> 1, p2 = qq & 1;
@@ -404,180 +522,150 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
             }
             Mw[e] = v;
         }
-        if (!gj_inverse_2x2<T>(Mw, m2, m2, aux, nullptr, &s_pi, &s_ok)) {
-            if (tid == 0) {
-                set_err(a.err, DEV_NUMERIC);
+        const bool ok = gj_inverse_2x2<T>(Mw, m2, m2, aux, &s_det);
+        if (tid == 0) {
+            const cx<T> dt = ok ? s_det : cmk((T)0, (T)0);
+            const T f = exp(s_logq);
+            const T Rr = dt.r * f, Ri = dt.i * f;
+            const T absR = sqrt(Rr * Rr + Ri * Ri);
+            ratio[2 * (N + a.blk)] = (double)Rr;
+            ratio[2 * (N + a.blk) + 1] = (double)Ri;
+            if (!isfinite(absR)) set_err(a.err, DEV_NUMERIC);
+            const int racc = rep ? (int)rep[N + a.blk] : -1;
+            const int acc = racc >= 0 ? (racc != 0) : ((T)u[N + a.blk] < absR);
+            dec[N + a.blk] = (uint8_t)acc;
+            s_acc = acc && ok && absR > (T)0 && isfinite(absR);
+            if (s_acc) {
+                for (int t = 0; t < m; ++t) {
+                    sites[t] = s_site[t];
+                    x[s_site[t]] = (int8_t)(-x[s_site[t]]);
+                }
+                a.Kdev[z] = m2;
+            } else {
                 a.Kdev[z] = 0;
             }
-            return;
         }
-        write_W<T>(Mw, m2, m2, s_dl, W, ldw);
-        if (tid == 0) a.Kdev[z] = 2 * m2;
-        return;
+        __syncthreads();
+        if (!s_acc) return;
     }
-
-    // ---- block force bias over the block [s0, s0 + n) ----
-    // stripped matrix Mb = 1 + A_bb Delta_s, Delta_s = A(-gamma x) - 1 per site
-    for (int e = tid; e < n2 * n2; e += nt) {
-        const int q = e / n2, qq = e - q * n2;
-        const int t2 = qq >> 1, p2 = qq & 1;
-        T ds[2][2];
-        real_delta<T>(a.k.c1m1, a.k.s1, x[s0 + t2], ds);
-        cx<T> v = cmk((q == qq) ? (T)1 : (T)0, (T)0);
-        for (int p = 0; p < 2; ++p) {
-            const int cq = 2 * t2 + p;
-            const cx<T> g = g_at(G, ldz, orb(q), orb(cq));
-            const cx<T> Aq = cmk((q == cq ? (T)1 : (T)0) - g.r, -g.i);
-            v = cadd(v, cscale(Aq, ds[p][p2]));
-        }
-        Mw[e] = v;
-    }
-    if (!gj_inverse_2x2<T>(Mw, n2, n2, aux, nullptr, &s_pi, &s_ok)) {
-        if (tid == 0) {
-            set_err(a.err, DEV_NUMERIC);
-            a.Kdev[z] = 0;
-        }
-        return;
-    }
-    // (Minv A)[2t + p][2t + q] for the four entries of every site: one warp per (t, p, q)
-    {
-        const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-        for (int e = wid; e < 4 * n; e += nw) {
-            const int t = e >> 2, p = (e >> 1) & 1, q = e & 1;
-            const int row = 2 * t + p, col = 2 * t + q;
-            cx<T> acc = cmk((T)0, (T)0);
-            for (int r = lane; r < n2; r += 32) {
-                const cx<T> g = g_at(G, ldz, orb(r), orb(col));
-                const cx<T> Ar = cmk((r == col ? (T)1 : (T)0) - g.r, -g.i);
-                cfma(acc, Mw[row * n2 + r], Ar);
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                acc.r += __shfl_xor_sync(0xffffffffu, acc.r, o);
-                acc.i += __shfl_xor_sync(0xffffffffu, acc.i, o);
-            }
-            if (lane == 0) aux[e] = acc;  // aux[4t + 2p + q]
-        }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        // obar_t = Abar[dn t, up t] - Abar[up t, dn t], Abar = (1 + Delta_s) Minv A, 1 + Delta_s = A(-gamma x)
-        double logq = 0.0;
-        int m = 0;
-        for (int t = 0; t < n; ++t) {
-            const int i = s0 + t, xi = x[i];
-            const T c = (T)(a.k.c1m1 + 1.0), s = (T)(-xi * a.k.s1);  // A(-gamma x) = [[c, s], [-s, c]]
-            const cx<T> MA00 = aux[4 * t], MA01 = aux[4 * t + 1], MA10 = aux[4 * t + 2], MA11 = aux[4 * t + 3];
-            const cx<T> dn_up = cadd(cscale(MA00, -s), cscale(MA10, c));
-            const cx<T> up_dn = cadd(cscale(MA01, c), cscale(MA11, s));
-            const cx<T> ob = csub(dn_up, up_dn);
-            s_ob[t] = ob;
-            const double h = a.k.gamma * (double)ob.r;
-            const double lp = 1.0 / (1.0 + exp(-2.0 * h));
-            lam[i] = lp;
-            const int xp = rep ? (rep[i] ? 1 : -1) : (u[i] < lp ? 1 : -1);
-            dec[i] = (uint8_t)(xp > 0);
-            if (xp != xi) {
-                T dl[2][2];
-                real_delta<T>(a.k.c2m1, a.k.s2, xi, dl);
-                for (int p = 0; p < 2; ++p)
-                    for (int q = 0; q < 2; ++q) s_dl[m][p][q] = dl[p][q];
-                s_site[m] = i;
-                logq += (double)(xi - xp) * h;
-                ++m;
-            }
-        }
-        s_m = m;
-        s_det = cmk(logq, 0.0);  // carries log q to the ratio below
-    }
-    __syncthreads();
-    const int m = s_m, m2 = 2 * m;
-    if (m == 0) {
-        if (tid == 0) {
-            dec[N + a.blk] = 1;
-            ratio[2 * (N + a.blk)] = 1.0;
-            ratio[2 * (N + a.blk) + 1] = 0.0;
-            a.Kdev[z] = 0;
-        }
-        return;
-    }
-    const double logq = s_det.r;
-    __syncthreads();
-    for (int e = tid; e < m2 * m2; e += nt) {
-        const int q = e / m2, qq = e - q * m2;
-        const int t2 = qq >> 1, p2 = qq & 1;
-        const int rq = (q & 1) ? N + s_site[q >> 1] : s_site[q >> 1];
-        cx<T> v = cmk((q == qq) ? (T)1 : (T)0, (T)0);
-        for (int p = 0; p < 2; ++p) {
-            const int cq = p ? N + s_site[t2] : s_site[t2];
-            const cx<T> g = g_at(G, ldz, rq, cq);
-            const cx<T> Aq = cmk((rq == cq ? (T)1 : (T)0) - g.r, -g.i);
-            v = cadd(v, cscale(Aq, s_dl[t2][p][p2]));
-        }
-        Mw[e] = v;
-    }
-    const bool ok = gj_inverse_2x2<T>(Mw, m2, m2, aux, &s_det, &s_pi, &s_ok);
-    if (tid == 0) {
-        const cx<double> dt = ok ? s_det : cmk(0.0, 0.0);
-        const double f = exp(logq);
-        const double Rr = dt.r * f, Ri = dt.i * f;
-        const double absR = sqrt(Rr * Rr + Ri * Ri);
-        ratio[2 * (N + a.blk)] = Rr;
-        ratio[2 * (N + a.blk) + 1] = Ri;
-        if (!isfinite(absR)) set_err(a.err, DEV_NUMERIC);
-        const int acc = rep ? (rep[N + a.blk] != 0) : (u[N + a.blk] < absR);
-        dec[N + a.blk] = (uint8_t)acc;
-        s_acc = acc && ok && absR > 0.0 && isfinite(absR);
-        if (s_acc) {
-            for (int t = 0; t < m; ++t) {
-                sites[t] = s_site[t];
-                x[s_site[t]] = (int8_t)(-x[s_site[t]]);
-            }
-            a.Kdev[z] = 2 * m2;
-        } else {
-            a.Kdev[z] = 0;
-        }
-    }
-    __syncthreads();
-    if (!s_acc) return;
     write_W<T>(Mw, m2, m2, s_dl, W, ldw);
+    if (tid == 0) a.Kdev[z] = m2;
+    if (a.xw_inline) {
+        // small updates: X' = G[:, F] W here, for all 2N rows (W re-read from this block's writes)
+        __syncthreads();
+        cx<T>* Xp = (cx<T>*)a.Xp0 + (long)z * 2 * N * ldw;
+        for (int r = tid; r < 2 * N; r += nt) {
+            cx<T> gf[8];
+            for (int p = 0; p < m2; ++p) {
+                const int o = (p & 1) ? N + s_site[p >> 1] : s_site[p >> 1];
+                gf[p] = g_at(G, ldz, r, o);
+            }
+            for (int q = 0; q < m2; ++q) {
+                cx<T> v = cmk((T)0, (T)0);
+                for (int p = 0; p < m2; ++p) cfma(v, gf[p], W[(long)p * ldw + q]);
+                Xp[(long)r * ldw + q] = v;
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
-// flush panels: X (2N x 4m, K-interleaved) = G[:, F] and the realified rows of E_F^T - G[F, :]
+// the window's update of the full G, out of place:
+//   X' = G0[:, F] W  (2N x 2m);   G1 = G0 - X' (E_F^T - G0[F, :])
 // ---------------------------------------------------------------------------
+constexpr int XW_ROWS = 16;
+
+// X'[r][q] for 16 rows per block; W (2m x 2m) and the rows' F-columns staged in shared memory.
 template <typename T>
-__global__ void soc_gather_kernel(const T* G0, long gstride, long ldz, int N, const int* sites0, int kmax,
-                                  const int* Kdev, T* X0, T* Y0) {
+__global__ void __launch_bounds__(256) soc_xw_kernel(const T* G0, long gstride, long ldz, int N, const int* sites0,
+                                                     int kmax, const int* Kdev, const cx<T>* W0, cx<T>* Xp0) {
+    extern __shared__ __align__(16) unsigned char xw_smem[];
     const int z = blockIdx.z;
-    const int K4 = Kdev[z];
-    if (K4 == 0) return;
-    const int m2 = K4 / 2;  // complex orbitals of F
+    const int m2 = Kdev[z];
+    if (m2 == 0) return;
+    const int ldw = 2 * kmax;
     const T* G = G0 + (long)z * gstride;
     const int* sites = sites0 + (long)z * kmax;
-    const int ldx = 4 * kmax;
-    T* X = X0 + (long)z * 2 * N * ldx;
-    T* Y = Y0 + (long)z * ldx * 2 * ldz;
+    const cx<T>* W = W0 + (long)z * ldw * ldw;
+    cx<T>* Xp = Xp0 + (long)z * 2 * N * ldw;
+    cx<T>* Ws = (cx<T>*)xw_smem;     // [m2][m2]
+    cx<T>* Gs = Ws + m2 * m2;        // [XW_ROWS][m2]
+    const int r0 = blockIdx.x * XW_ROWS;
+    for (int e = threadIdx.x; e < m2 * m2; e += blockDim.x) Ws[e] = W[(e / m2) * ldw + e % m2];
+    for (int e = threadIdx.x; e < XW_ROWS * m2; e += blockDim.x) {
+        const int rr = e / m2, q = e - rr * m2, r = r0 + rr;
+        const int o = (q & 1) ? N + sites[q >> 1] : sites[q >> 1];
+        Gs[e] = (r < 2 * N) ? g_at(G, ldz, r, o) : cmk((T)0, (T)0);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < XW_ROWS * m2; e += blockDim.x) {
+        const int rr = e / m2, q = e - rr * m2, r = r0 + rr;
+        if (r >= 2 * N) continue;
+        cx<T> a0 = cmk((T)0, (T)0), a1 = cmk((T)0, (T)0);
+        int p = 0;
+        for (; p + 1 < m2; p += 2) {
+            cfma(a0, Gs[rr * m2 + p], Ws[p * m2 + q]);
+            cfma(a1, Gs[rr * m2 + p + 1], Ws[(p + 1) * m2 + q]);
+        }
+        if (p < m2) cfma(a0, Gs[rr * m2 + p], Ws[p * m2 + q]);
+        Xp[(long)r * ldw + q] = cadd(a0, a1);
+    }
+}
+
+constexpr int FL_R = 32, FL_C = 64;
+
+// G1 = G0 - X' Y, Y = E_F^T - G0[F, :]; tiles of 32 rows x 64 columns (complex), 8 outputs per
+// thread; m2 = 0 copies the tile.
+template <typename T>
+__global__ void __launch_bounds__(256) soc_flush_kernel(const T* G0, T* G1, long gstride, long ldz, int N,
+                                                        const int* sites0, int kmax, const int* Kdev,
+                                                        const cx<T>* Xp0) {
+    extern __shared__ __align__(16) unsigned char fl_smem[];
+    const int z = blockIdx.z;
+    const int m2 = Kdev[z];
+    const int ldw = 2 * kmax;
+    const T* Ga = G0 + (long)z * gstride;
+    T* Gb = G1 + (long)z * gstride;
+    const int* sites = sites0 + (long)z * kmax;
+    const cx<T>* Xp = Xp0 + (long)z * 2 * N * ldw;
+    cx<T>* Xs = (cx<T>*)fl_smem;       // [FL_R][m2]
+    cx<T>* Ys = Xs + FL_R * m2;        // [m2][FL_C]
+    const int r0 = blockIdx.y * FL_R, c0 = blockIdx.x * FL_C;
+    const int N2 = 2 * N;
     const long ld2 = 2 * ldz;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-    if (blockIdx.y == 0) {
-        for (int e = tid; e < 2 * N * m2; e += nt) {
-            const int r = e / m2, q = e - r * m2;
-            const int o = (q & 1) ? N + sites[q >> 1] : sites[q >> 1];
-            X[(long)r * ldx + 2 * q] = G[(long)r * ld2 + o];
-            X[(long)r * ldx + 2 * q + 1] = G[(long)r * ld2 + ldz + o];
+    for (int e = threadIdx.x; e < FL_R * m2; e += blockDim.x) {
+        const int rr = e / m2, q = e - rr * m2, r = r0 + rr;
+        Xs[e] = (r < N2) ? Xp[(long)r * ldw + q] : cmk((T)0, (T)0);
+    }
+    for (int e = threadIdx.x; e < m2 * FL_C; e += blockDim.x) {
+        const int q = e / FL_C, cc = e - q * FL_C, c = c0 + cc;
+        const int o = (q & 1) ? N + sites[q >> 1] : sites[q >> 1];
+        cx<T> y = cmk((T)0, (T)0);
+        if (c < N2) {
+            const cx<T> g = g_at(Ga, ldz, o, c);
+            y = cmk((c == o ? (T)1 : (T)0) - g.r, -g.i);
         }
-    } else {
-        for (long e = tid; e < (long)m2 * ldz; e += nt) {
-            const int q = (int)(e / ldz);
-            const long c = e - (long)q * ldz;
-            const int o = (q & 1) ? N + sites[q >> 1] : sites[q >> 1];
-            const T yr = (c == o ? (T)1 : (T)0) - G[(long)o * ld2 + c];
-            const T yi = -G[(long)o * ld2 + ldz + c];
-            Y[(long)(2 * q) * ld2 + c] = yr;
-            Y[(long)(2 * q) * ld2 + ldz + c] = yi;
-            Y[(long)(2 * q + 1) * ld2 + c] = -yi;
-            Y[(long)(2 * q + 1) * ld2 + ldz + c] = yr;
-        }
+        Ys[e] = y;
+    }
+    __syncthreads();
+    const int tc = threadIdx.x % FL_C, tr = threadIdx.x / FL_C;  // 4 row groups of 8 rows
+    const int c = c0 + tc;
+    if (c >= N2) return;
+    cx<T> acc[FL_R / 4];
+#pragma unroll
+    for (int i = 0; i < FL_R / 4; ++i) acc[i] = cmk((T)0, (T)0);
+    for (int q = 0; q < m2; ++q) {
+        const cx<T> y = Ys[q * FL_C + tc];
+#pragma unroll
+        for (int i = 0; i < FL_R / 4; ++i) cfma(acc[i], Xs[(tr + 4 * i) * m2 + q], y);
+    }
+#pragma unroll
+    for (int i = 0; i < FL_R / 4; ++i) {
+        const int r = r0 + tr + 4 * i;
+        if (r >= N2) continue;
+        const long o = (long)r * ld2 + c;
+        Gb[o] = Ga[o] - acc[i].r;
+        Gb[o + ldz] = Ga[o + ldz] - acc[i].i;
     }
 }
 
@@ -854,7 +942,7 @@ struct afqmc_soc_ctx {
     double *ratio = nullptr, *lamp = nullptr;
     int* gid = nullptr;
     unsigned long long* visit = nullptr;
-    void *X = nullptr, *Xp = nullptr, *Y = nullptr, *W = nullptr;
+    void *G2 = nullptr, *Xp = nullptr, *W = nullptr;  // G2: the other buffer of the out-of-place flush
     int *Kdev = nullptr, *sites = nullptr, *err = nullptr;
     double *URs = nullptr, *ULs = nullptr, *Ucur = nullptr, *Lrow = nullptr, *O = nullptr, *Z = nullptr,
            *Pb = nullptr, *acc2 = nullptr, *en = nullptr;
@@ -1154,8 +1242,9 @@ cudaError_t soc_window(afqmc_soc_ctx* ctx, cudaStream_t st, int8_t* xl, const ui
     a.dec0 = ctx->dec; a.ratio0 = ctx->ratio; a.lam0 = ctx->lamp;
     a.sites0 = ctx->sites; a.kmax = kmax;
     a.W0 = ctx->W; a.Kdev = ctx->Kdev; a.err = ctx->err;
+    a.xw_inline = n <= 4;
+    a.Xp0 = ctx->Xp;
     {
-        SocPhase ps(ctx, AFQMC_PHASE_CHAIN, st);
         const size_t shm = window_smem<T>(kmax);
         static bool attr[2] = {false, false};
         if (!attr[sizeof(T) == 8]) {
@@ -1168,27 +1257,41 @@ cudaError_t soc_window(afqmc_soc_ctx* ctx, cudaStream_t st, int8_t* xl, const ui
         soc_window_kernel<T><<<nwk, 512, shm, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    SocPhase pf(ctx, AFQMC_PHASE_FLUSH, st);
-    const int ldx = 4 * kmax;
-    count_launch();
-    soc_gather_kernel<T><<<dim3(64, 2, nwk), 256, 0, st>>>((const T*)ctx->G, ctx->gstride(), ldz, N, ctx->sites, kmax,
-                                                          ctx->Kdev, (T*)ctx->X, (T*)ctx->Y);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // X' = X W (K = 4m), then G -= X' Y~
-    GemmArgs<T> g1;
-    g1.M = N2; g1.N = 4 * n; g1.K = 4 * n; g1.Kdev = ctx->Kdev; g1.kdiv = 1; g1.batch = nwk;
-    g1.A = (const T*)ctx->X; g1.lda = ldx; g1.sA = (long)N2 * ldx;
-    g1.B = (const T*)ctx->W; g1.ldb = ldx; g1.sB = (long)ldx * ldx;
-    g1.C = (T*)ctx->Xp; g1.ldc = ldx; g1.sC = (long)N2 * ldx;
-    if ((e = gemm<T>(st, g1)) != cudaSuccess) return e;
-    GemmArgs<T> g2;
-    g2.M = N2; g2.N = (int)ld2; g2.K = 4 * n; g2.Kdev = ctx->Kdev; g2.kdiv = 1; g2.batch = nwk;
-    g2.A = (const T*)ctx->Xp; g2.lda = ldx; g2.sA = (long)N2 * ldx;
-    g2.B = (const T*)ctx->Y; g2.ldb = ld2; g2.sB = (long)ldx * ld2;
-    g2.C = (T*)ctx->G; g2.ldc = ld2; g2.sC = ctx->gstride();
-    g2.alpha = (T)-1; g2.beta = (T)1;
-    SocPhase pg(ctx, AFQMC_PHASE_FLUSH_GEMM, st);
-    return gemm<T>(st, g2);
+    const int m2max = 2 * n;
+    if (!a.xw_inline) {
+        const size_t shm = (size_t)(m2max * m2max + XW_ROWS * m2max) * sizeof(cx<T>);
+        static bool attr[2] = {false, false};
+        if (!attr[sizeof(T) == 8]) {
+            const int cap = 4 * kmax * kmax + XW_ROWS * 2 * kmax;
+            if ((e = cudaFuncSetAttribute((void*)soc_xw_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(cap * sizeof(cx<T>)))) != cudaSuccess)
+                return e;
+            attr[sizeof(T) == 8] = true;
+        }
+        count_launch();
+        soc_xw_kernel<T><<<dim3((N2 + XW_ROWS - 1) / XW_ROWS, 1, nwk), 256, shm, st>>>(
+            (const T*)ctx->G, ctx->gstride(), ldz, N, ctx->sites, kmax, ctx->Kdev, (const cx<T>*)ctx->W,
+            (cx<T>*)ctx->Xp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        const size_t shm = (size_t)(FL_R + FL_C) * m2max * sizeof(cx<T>);
+        static bool attr[2] = {false, false};
+        if (!attr[sizeof(T) == 8]) {
+            if ((e = cudaFuncSetAttribute((void*)soc_flush_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)((FL_R + FL_C) * 2 * kmax * sizeof(cx<T>)))) != cudaSuccess)
+                return e;
+            attr[sizeof(T) == 8] = true;
+        }
+        count_launch();
+        soc_flush_kernel<T><<<dim3((N2 + FL_C - 1) / FL_C, (N2 + FL_R - 1) / FL_R, nwk), 256, shm, st>>>(
+            (const T*)ctx->G, (T*)ctx->G2, ctx->gstride(), ldz, N, ctx->sites, kmax, ctx->Kdev,
+            (const cx<T>*)ctx->Xp);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    std::swap(ctx->G, ctx->G2);  // the updated G is the current one
+    (void)ld2;
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -1201,14 +1304,19 @@ int soc_sweep(afqmc_soc_ctx* ctx, int slice, int dir, int mode, int k, int nb, c
         SCK(cudaMemsetAsync(ctx->dec, 0, (size_t)ctx->nwk * 2 * N, st));
     }
     if (dir > 0) SCK(soc_wrap<T>(ctx, st, xl, +1));
-    if (mode == AFQMC_MODE_BLOCKFB) {
-        for (int b = 0; b * nb < N; ++b) {
-            const int s0 = b * nb, n = std::min(nb, N - s0);
-            SCK(soc_window<T>(ctx, st, xl, rep, 1, s0, n, b));
+    {
+        // one interval for the whole update loop (window chains and their flushes): per-window
+        // events would add gaps of their own to the local update's thousands of launches
+        SocPhase ps(ctx, AFQMC_PHASE_CHAIN, st);
+        if (mode == AFQMC_MODE_BLOCKFB) {
+            for (int b = 0; b * nb < N; ++b) {
+                const int s0 = b * nb, n = std::min(nb, N - s0);
+                SCK(soc_window<T>(ctx, st, xl, rep, 1, s0, n, b));
+            }
+        } else {
+            const int w = (mode == AFQMC_MODE_LOCAL) ? 1 : k;
+            for (int s0 = 0; s0 < N; s0 += w) SCK(soc_window<T>(ctx, st, xl, rep, 0, s0, std::min(w, N - s0), 0));
         }
-    } else {
-        const int w = (mode == AFQMC_MODE_LOCAL) ? 1 : k;
-        for (int s0 = 0; s0 < N; s0 += w) SCK(soc_window<T>(ctx, st, xl, rep, 0, s0, std::min(w, N - s0), 0));
     }
     if (dir < 0) SCK(soc_wrap<T>(ctx, st, xl, -1));
     SCK(launch_bump(st, ctx->visit));
@@ -1398,10 +1506,9 @@ int afqmc_soc_init(afqmc_soc_ctx* ctx, const double* P, const int8_t* fields, vo
     SCK(soc_alloc(ctx, &ctx->lamp, (size_t)nwk * N * 8, st));
     SCK(soc_alloc(ctx, &ctx->gid, (size_t)nwk * sizeof(int), st));
     SCK(soc_alloc(ctx, &ctx->visit, 8, st));
-    SCK(soc_alloc(ctx, &ctx->X, (size_t)nwk * N2 * 4 * kmax * es, st));
+    SCK(soc_alloc(ctx, &ctx->G2, (size_t)nwk * ctx->gstride() * es, st));
     SCK(soc_alloc(ctx, &ctx->Xp, (size_t)nwk * N2 * 4 * kmax * es, st));
-    SCK(soc_alloc(ctx, &ctx->Y, (size_t)nwk * 4 * kmax * ld2 * es, st));
-    SCK(soc_alloc(ctx, &ctx->W, (size_t)nwk * 16 * kmax * kmax * es, st));
+    SCK(soc_alloc(ctx, &ctx->W, (size_t)nwk * 8 * kmax * kmax * es, st));
     SCK(soc_alloc(ctx, &ctx->Kdev, (size_t)nwk * sizeof(int), st));
     SCK(soc_alloc(ctx, &ctx->sites, (size_t)nwk * kmax * sizeof(int), st));
     SCK(soc_alloc(ctx, &ctx->err, sizeof(int), st));
