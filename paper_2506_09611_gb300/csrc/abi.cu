@@ -703,6 +703,8 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
         CK(dalloc(A, (char**)&w->visited, (size_t)nwk * maxr * sizeof(int)));
         CK(dalloc(A, &w->acc2, (size_t)nwk * 2 * 8));
         CK(cudaMemsetAsync(w->err, 0, sizeof(int), st));
+        CK(cudaMemsetAsync(w->dec, 0, (size_t)nwk * 2 * N, st));  // the block half stays 0 outside block FB
+        CK(cudaMemsetAsync(w->ratio, 0, (size_t)nwk * 2 * N * 8, st));
         CK(cudaMemsetAsync(w->G, 0, (size_t)nwk * 2 * N * ld * es, st));
         CK(cudaMemsetAsync(w->Tbuf, 0, (size_t)nwk * 2 * N * ld * es, st));
         CK(cudaMemsetAsync(w->Gnew, 0, (size_t)nwk * 2 * N * ld * 8, st));

@@ -184,8 +184,9 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     }
     // The split product rotates k-tiles over NACC accumulators (summed in FP32 by the epilogue):
     // a shorter chain of in-pipe accumulations per accumulator keeps the result at FP32 accuracy.
-    constexpr int NACC = SPLIT ? 4 : 1;
-    constexpr uint32_t TMEM_COLS = (uint32_t)(BN * NACC);
+    // Four accumulators of 128 columns fill the 512 TMEM columns; wider tiles use three.
+    constexpr int NACC = SPLIT ? (BN <= 128 ? 4 : 3) : 1;
+    constexpr uint32_t TMEM_COLS = (BN * NACC <= 128) ? 128u : (BN * NACC <= 256 ? 256u : 512u);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
                      "r"(TMEM_COLS)
@@ -408,9 +409,42 @@ cudaError_t tc_launch(cudaStream_t st, const TcGemmArgs& g) {
 
 }  // namespace
 
+// Tile width: the BN in {128, 144, 160} that minimises (waves of 128 x BN tiles on the SMs) x BN,
+// i.e. the time of the last wave; e.g. 1600 x 1600 x 2 takes BN = 160 (260 tiles, 2 waves on 152
+// SMs, against 338 tiles and 3 waves at 128) and 1152 x 2304 takes BN = 144 (one wave of 144).
+static int pick_bn(const TcGemmArgs& g) {
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 148;
+    }
+    const long mt = (g.M + TC_BM - 1) / TC_BM;
+    int best = 128;
+    long best_cost = -1;
+    for (int bn : {128, 144, 160}) {
+        const long tiles = mt * ((g.N + bn - 1) / bn) * g.batch;
+        const long cost = ((tiles + nsm - 1) / nsm) * bn;
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = bn;
+        }
+    }
+    return best;
+}
+
 cudaError_t tc_gemm(cudaStream_t st, const TcGemmArgs& g) {
     if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0) return cudaSuccess;
-    return g.split3 ? tc_launch<128, true>(st, g) : tc_launch<128, false>(st, g);
+    const int bn = pick_bn(g);
+    if (g.split3) {
+        if (bn == 160) return tc_launch<160, true>(st, g);
+        if (bn == 144) return tc_launch<144, true>(st, g);
+        return tc_launch<128, true>(st, g);
+    }
+    if (bn == 160) return tc_launch<160, false>(st, g);
+    if (bn == 144) return tc_launch<144, false>(st, g);
+    return tc_launch<128, false>(st, g);
 }
 
 }  // namespace afq

@@ -1,7 +1,9 @@
-"""Command-line driver: one walker of the square-lattice Hubbard model swept for a given number
-of slice-steps through the C ABI (used for kernel profiling and quick timing).
+"""Command-line driver: one walker of the square-lattice Hubbard model (or, with --soc, of the
+spin-orbit-coupled model on the 2N complex orbitals) swept for a given number of slice-steps
+through the C ABI (used for kernel profiling and quick timing).
 
     python -m paper_2506_09611_gb300.run --L 40 --U 6 --slices 20 --mode delayed --k 64
+    python -m paper_2506_09611_gb300.run --soc --L 24 --U -4 --lam 0.5 --slices 12 --mode blockfb --nb 16
 
 The walk goes forward from slice 1 and turns at slice M, with the FP64 recompute at every
 multiple of --stab, exactly as in a full sweep; the inputs are the seeded synthetic trial
@@ -34,7 +36,11 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--gemm", default="tc3", choices=["tc3", "simt", "tf32"])
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--soc", action="store_true", help="the spin-orbit-coupled model at half filling")
+    ap.add_argument("--lam", type=float, default=0.5)
     a = ap.parse_args(argv)
+    if a.soc:
+        return main_soc(a)
 
     import torch
 
@@ -63,6 +69,37 @@ def main(argv=None):
     print(json.dumps({"L": L, "slices": a.slices, "mode": a.mode, "k": a.k, "nb": a.nb,
                       "precision": a.precision, "gemm": a.gemm, "seconds": dt,
                       "field_updates_per_s": N * a.slices / dt, "energy": float(e[0])}))
+
+
+def main_soc(a):
+    import torch
+
+    from . import soc
+
+    afqmc.load()
+    stream = torch.cuda.current_stream()
+    L, N = a.L, a.L * a.L
+    n_e = N  # half filling
+    P = inputs.soc_trial_state(L, n_e, t=a.t, lam=a.lam)
+    X = inputs.initial_fields(a.M, N, seed=a.seed)
+    ctx = soc.SocContext(L, a.M, n_e, 1, a.precision, a.gemm, a.stab, a.t, a.lam, a.U, a.dtau, a.seed)
+    ctx.init(P, X, stream=stream)
+    order = [(l, +1) for l in range(1, a.M + 1)] + [(l, -1) for l in range(a.M, 0, -1)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(a.slices):
+        ell, d = order[i % len(order)]
+        ctx.sweep_slice(ell, d, a.mode, k=a.k, nb=a.nb, stream=stream)
+        pos = ell if d > 0 else ell - 1
+        if pos % a.stab == 0:
+            soc.afqmc_soc_recompute_G(ctx.h, None, stream)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    e = ctx.measure_energy(stream=stream)
+    ctx.close()
+    print(json.dumps({"model": "soc", "L": L, "slices": a.slices, "mode": a.mode, "k": a.k, "nb": a.nb,
+                      "precision": a.precision, "gemm": a.gemm, "seconds": dt,
+                      "field_updates_per_s": N * a.slices / dt, "energy": [e[0].real, e[0].imag]}))
 
 
 if __name__ == "__main__":

@@ -1,4 +1,5 @@
-"""tcgen05 tensor-core GEMM against a plain PyTorch FP64 product of the same FP32 operands."""
+"""tcgen05 tensor-core GEMM against a plain PyTorch FP64 product of the same FP32 operands.
+The sizes cover each tile width the launcher picks (128, 144 and 160 columns) and ragged edges."""
 import numpy as np
 import pytest
 
@@ -42,14 +43,14 @@ def _fp32_reference_error(M, N, K, seed=0):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 128, 32), (256, 128, 64), (200, 136, 72), (1600, 1600, 1600),
-                                   (36, 36, 36), (130, 260, 100)])
+                                   (36, 36, 36), (130, 260, 100), (1152, 2304, 2304), (1500, 1590, 200)])
 def test_tc_gemm_split3_is_fp32_accurate(M, N, K):
     """The three-term split stays within a small factor of a plain FP32 product's error."""
     err = _run(2, M, N, K)
     assert err < max(2e-6, 8 * _fp32_reference_error(M, N, K))
 
 
-@pytest.mark.parametrize("M,N,K", [(256, 256, 256), (300, 170, 96)])
+@pytest.mark.parametrize("M,N,K", [(256, 256, 256), (300, 170, 96), (1600, 1600, 256), (1152, 2304, 128)])
 def test_tc_gemm_tf32_one_pass(M, N, K):
     err = _run(1, M, N, K)
     assert 1e-5 < err < 3e-3  # TF32 inputs: ~1e-3 relative, clearly not FP32
@@ -57,3 +58,5 @@ def test_tc_gemm_tf32_one_pass(M, N, K):
 
 def test_tc_gemm_transposed_output():
     assert _run(2, 300, 200, 160, c_trans=1) < 2e-6
+    assert _run(2, 1152, 2304, 96, c_trans=1) < 2e-6  # 144-wide tiles (one wave of 144 on 152 SMs)
+    assert _run(2, 1500, 1590, 64, c_trans=1) < 2e-6  # 160-wide tiles, ragged in both dimensions
