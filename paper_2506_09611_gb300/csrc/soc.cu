@@ -676,7 +676,8 @@ struct SocPropArgs {
     double* F0;
     long wstride;             // factor of walker j at F0 + j wstride: 4N x nv row-major
     int nv, L, N;
-    const double* dft;        // L x L complex: exp(-2 pi i k x / L)
+    int P, Q;                 // L = P Q: the two factors of the lattice DFT (Q = 1: a plain DFT)
+    const double* tab;        // complex tables: F_P (P x P), F_Q (Q x Q), twiddles (Q x P), see dft_stage
     const double* lam;        // N x 2 x 2 complex: exp(-dtau h_k) / N, k = kx + L ky
     const int8_t* x;
     long xstride;             // fields M x N of walker j at x + j xstride
@@ -687,50 +688,75 @@ struct SocPropArgs {
 
 constexpr int PROP_VPC_MAX = 4;
 
-__device__ __forceinline__ void prop_pass(const cx<double>* in, cx<double>* out, const cx<double>* F, int L, int N,
-                                          int vpc, int axis, int inverse) {
-    // axis 0 transforms x (stride 1), axis 1 transforms y (stride L); inverse uses conj(F)^T
+// One stage of the length-L DFT w = exp(-+2 pi i / L) along one lattice axis of every vector
+// (axis 0: x, element stride 1; axis 1: y, stride L), L = P Q, by the two-factor Cooley-Tukey
+// split (input index x = Q x1 + x2, output index k = k1 + P k2):
+//   stage 0:  Y[x2 + Q k1] = w^{x2 k1} sum_{x1 < P} w_P^{x1 k1} v[Q x1 + x2]
+//   stage 1:  X[k1 + P k2] = sum_{x2 < Q} w_Q^{x2 k2} Y[x2 + Q k1]
+// (P + Q + 1 complex multiply-adds per output instead of L).  inverse conjugates every table.
+// With Q = 1 stage 0 is the plain DFT and stage 1 is skipped.
+__device__ __forceinline__ void dft_stage(const cx<double>* in, cx<double>* out, const cx<double>* tab, int L, int P,
+                                          int Q, int N, int vpc, int axis, int inverse, int stage) {
+    const cx<double>* FP = tab;
+    const cx<double>* FQ = tab + P * P;
+    const cx<double>* TW = FQ + Q * Q;
+    const double cj = inverse ? -1.0 : 1.0;
     const int n2 = 2 * N;
     for (int e = threadIdx.x; e < vpc * n2; e += blockDim.x) {
         const int v = e / n2, a = e - v * n2;
         const int s = a / N, i = a - s * N;
         const int xx = i % L, yy = i / L;
-        const int kout = axis ? yy : xx;
-        const cx<double>* src = in + v * n2 + s * N + (axis ? xx : yy * L);
+        const int j = axis ? yy : xx;  // position along the transformed axis
         const int stride = axis ? L : 1;
+        const cx<double>* src = in + v * n2 + s * N + (axis ? xx : yy * L);
         cx<double> acc0 = cmk(0.0, 0.0), acc1 = cmk(0.0, 0.0);
-        int q = 0;
-        for (; q + 1 < L; q += 2) {
-            cx<double> f0 = inverse ? F[q * L + kout] : F[kout * L + q];
-            cx<double> f1 = inverse ? F[(q + 1) * L + kout] : F[kout * L + q + 1];
-            if (inverse) {
-                f0.i = -f0.i;
-                f1.i = -f1.i;
+        if (stage == 0) {
+            const int x2 = j % Q, k1 = j / Q;  // output slot x2 + Q k1
+            int x1 = 0;
+            for (; x1 + 1 < P; x1 += 2) {
+                cx<double> f0 = FP[k1 * P + x1], f1 = FP[k1 * P + x1 + 1];
+                f0.i *= cj;
+                f1.i *= cj;
+                cfma(acc0, f0, src[(Q * x1 + x2) * stride]);
+                cfma(acc1, f1, src[(Q * (x1 + 1) + x2) * stride]);
             }
-            cfma(acc0, f0, src[q * stride]);
-            cfma(acc1, f1, src[(q + 1) * stride]);
+            if (x1 < P) {
+                cx<double> f0 = FP[k1 * P + x1];
+                f0.i *= cj;
+                cfma(acc0, f0, src[(Q * x1 + x2) * stride]);
+            }
+            acc0 = cadd(acc0, acc1);
+            if (Q > 1) {
+                cx<double> t = TW[x2 * P + k1];
+                t.i *= cj;
+                acc0 = cmul(acc0, t);
+            }
+        } else {
+            const int k1 = j % P, k2 = j / P;  // output k1 + P k2 reads Y[x2 + Q k1]
+            for (int x2 = 0; x2 < Q; ++x2) {
+                cx<double> f = FQ[k2 * Q + x2];
+                f.i *= cj;
+                cfma((x2 & 1) ? acc1 : acc0, f, src[(x2 + Q * k1) * stride]);
+            }
+            acc0 = cadd(acc0, acc1);
         }
-        if (q < L) {
-            cx<double> f0 = inverse ? F[q * L + kout] : F[kout * L + q];
-            if (inverse) f0.i = -f0.i;
-            cfma(acc0, f0, src[q * stride]);
-        }
-        out[e] = cadd(acc0, acc1);
+        out[e] = acc0;
     }
 }
 
 __global__ void __launch_bounds__(256) soc_prop_kernel(SocPropArgs a, int vpc) {
     extern __shared__ __align__(16) unsigned char prop_smem[];
-    const int N = a.N, L = a.L, n2 = 2 * N;
+    const int N = a.N, L = a.L, n2 = 2 * N, P = a.P, Q = a.Q;
     cx<double>* b0 = (cx<double>*)prop_smem;
     cx<double>* b1 = b0 + vpc * n2;
-    cx<double>* F = b1 + vpc * n2;
+    cx<double>* tab = b1 + vpc * n2;
+    const int ntab = P * P + Q * Q + Q * P;
     const int z = blockIdx.y;
     double* U = a.F0 + (long)z * a.wstride;
     const int8_t* xw = a.x + (long)z * a.xstride;
     const int c0 = blockIdx.x * vpc;
     const int nv = a.nv;
-    for (int e = threadIdx.x; e < L * L; e += blockDim.x) F[e] = cmk(a.dft[2 * e], a.dft[2 * e + 1]);
+    for (int e = threadIdx.x; e < ntab; e += blockDim.x) tab[e] = cmk(a.tab[2 * e], a.tab[2 * e + 1]);
     for (int e = threadIdx.x; e < vpc * n2; e += blockDim.x) {
         const int r = e / vpc, v = e - r * vpc;  // v fastest: consecutive columns
         const int c = c0 + v;
@@ -738,6 +764,19 @@ __global__ void __launch_bounds__(256) soc_prop_kernel(SocPropArgs a, int vpc) {
     }
     __syncthreads();
     const cx<double>* lamk = (const cx<double>*)a.lam;
+    // one DFT along an axis: the data moves b0 -> b1 (-> b0 again for the two-factor split)
+    auto dft = [&](int axis, int inverse) {
+        dft_stage(b0, b1, tab, L, P, Q, N, vpc, axis, inverse, 0);
+        __syncthreads();
+        if (Q > 1) {
+            dft_stage(b1, b0, tab, L, P, Q, N, vpc, axis, inverse, 1);
+            __syncthreads();
+        } else {
+            cx<double>* t = b0;
+            b0 = b1;
+            b1 = t;
+        }
+    };
     for (int q = 0; q < a.nsl; ++q) {
         const int ell = a.l_first + q * a.l_step;
         const int8_t* xl = xw + (long)(ell - 1) * N;
@@ -751,10 +790,8 @@ __global__ void __launch_bounds__(256) soc_prop_kernel(SocPropArgs a, int vpc) {
             }
             __syncthreads();
         }
-        prop_pass(b0, b1, F, L, N, vpc, 0, 0);
-        __syncthreads();
-        prop_pass(b1, b0, F, L, N, vpc, 1, 0);
-        __syncthreads();
+        dft(0, 0);
+        dft(1, 0);
         for (int e = threadIdx.x; e < vpc * N; e += blockDim.x) {
             const int v = e / N, k = e - v * N;
             const cx<double>* l4 = lamk + 4 * k;
@@ -766,23 +803,23 @@ __global__ void __launch_bounds__(256) soc_prop_kernel(SocPropArgs a, int vpc) {
             b1[v * n2 + N + k] = w1;
         }
         __syncthreads();
-        prop_pass(b1, b0, F, L, N, vpc, 1, 1);
-        __syncthreads();
-        prop_pass(b0, b1, F, L, N, vpc, 0, 1);
-        __syncthreads();
+        {
+            cx<double>* t = b0;
+            b0 = b1;
+            b1 = t;
+        }
+        dft(1, 1);
+        dft(0, 1);
         if (!a.left) {  // v <- D v: rotation by A(gamma x)
             for (int e = threadIdx.x; e < vpc * N; e += blockDim.x) {
                 const int v = e / N, i = e - v * N;
                 const double s = xl[i] * a.sg;
-                const cx<double> p0 = b1[v * n2 + i], p1 = b1[v * n2 + N + i];
-                b1[v * n2 + i] = cadd(cscale(p0, a.cg), cscale(p1, s));
-                b1[v * n2 + N + i] = csub(cscale(p1, a.cg), cscale(p0, s));
+                const cx<double> p0 = b0[v * n2 + i], p1 = b0[v * n2 + N + i];
+                b0[v * n2 + i] = cadd(cscale(p0, a.cg), cscale(p1, s));
+                b0[v * n2 + N + i] = csub(cscale(p1, a.cg), cscale(p0, s));
             }
         }
         __syncthreads();
-        cx<double>* t = b0;  // the result is in b1: swap so that b0 holds the vectors
-        b0 = b1;
-        b1 = t;
     }
     for (int e = threadIdx.x; e < vpc * n2; e += blockDim.x) {
         const int r = e / vpc, v = e - r * vpc;
@@ -932,7 +969,8 @@ struct afqmc_soc_ctx {
     // constants
     void *Ers = nullptr, *Einvrs = nullptr;   // [Re E | Im E] rows, bulk precision
     void *Ech = nullptr, *Einvch = nullptr;   // realified right operands (transposed for tensor cores)
-    double *dft = nullptr, *lamk = nullptr;   // momentum-space propagation (FP64)
+    double *dft = nullptr, *lamk = nullptr;   // momentum-space propagation (FP64): DFT tables, e^{-dtau h_k}/N
+    int dP = 1, dQ = 1;                       // the lattice DFT as L = dP dQ
     // walkers
     void* G = nullptr;
     void* S = nullptr;
@@ -1134,14 +1172,20 @@ cudaError_t upload_constants(afqmc_soc_ctx* ctx, cudaStream_t st) {
             return e;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
     }
-    const int L = ctx->p.L;
-    std::vector<double> F((size_t)L * L * 2), lk;
-    for (int k = 0; k < L; ++k)
-        for (int q = 0; q < L; ++q) {
-            const double ph = -2.0 * M_PI * (double)((k * q) % L) / L;
-            F[(size_t)(k * L + q) * 2] = cos(ph);
-            F[(size_t)(k * L + q) * 2 + 1] = sin(ph);
-        }
+    const int L = ctx->p.L, P = ctx->dP, Q = ctx->dQ;
+    // tables of the two-factor DFT: F_P (P x P), F_Q (Q x Q), twiddles w^{x2 k1} (Q x P)
+    std::vector<double> F, lk;
+    auto root = [&](int num, int den) {
+        const double ph = -2.0 * M_PI * (double)(num % den) / den;
+        F.push_back(cos(ph));
+        F.push_back(sin(ph));
+    };
+    for (int k = 0; k < P; ++k)
+        for (int q = 0; q < P; ++q) root(k * q, P);
+    for (int k = 0; k < Q; ++k)
+        for (int q = 0; q < Q; ++q) root(k * q, Q);
+    for (int x2 = 0; x2 < Q; ++x2)
+        for (int k1 = 0; k1 < P; ++k1) root(x2 * k1, L);
     host_lamk(L, ctx->p.t, ctx->p.lam, ctx->p.dtau, lk);
     cudaError_t e = cudaMemcpyAsync(ctx->dft, F.data(), F.size() * 8, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
@@ -1328,12 +1372,13 @@ cudaError_t soc_propagate(afqmc_soc_ctx* ctx, cudaStream_t st, double* F, long w
                           int l_step, int nsl) {
     SocPropArgs a;
     a.F0 = F; a.wstride = wstride; a.nv = ctx->nv; a.L = ctx->p.L; a.N = ctx->N;
-    a.dft = ctx->dft; a.lam = ctx->lamk;
+    a.tab = ctx->dft; a.P = ctx->dP; a.Q = ctx->dQ; a.lam = ctx->lamk;
     a.x = ctx->x; a.xstride = (long)ctx->p.M * ctx->N;
     a.l_first = l_first; a.l_step = l_step; a.nsl = nsl; a.left = left;
     a.cg = ctx->k.c1m1 + 1.0; a.sg = ctx->k.s1;
     // vectors per CTA: as many (<= 4) as two buffers of 2N complex doubles allow in 220 KB
-    const size_t per = (size_t)2 * ctx->N2 * sizeof(cx<double>), fix = (size_t)ctx->p.L * ctx->p.L * sizeof(cx<double>);
+    const size_t per = (size_t)2 * ctx->N2 * sizeof(cx<double>),
+                 fix = (size_t)(ctx->dP * ctx->dP + ctx->dQ * ctx->dQ + ctx->dP * ctx->dQ) * sizeof(cx<double>);
     const int vpc = (int)std::min<size_t>(PROP_VPC_MAX, (220 * 1024 - fix) / per);
     const size_t shm = vpc * per + fix;
     static bool attr = false;
@@ -1457,6 +1502,15 @@ int afqmc_soc_create(afqmc_soc_ctx** out, const afqmc_soc_params* p) {
     c->use_tc = !c->f64 && p->gemm != AFQMC_GEMM_SIMT;
     c->kmax = c->f64 ? AFQMC_SOC_KMAX_FP64 : AFQMC_SOC_KMAX_FP32;
     c->nst = p->M / p->stab_every + 1;
+    // the lattice DFT: the factor pair L = P Q with the fewest multiply-adds per output
+    // (P + Q + 1 with a twiddle), else the plain L-term sum
+    c->dP = L;
+    c->dQ = 1;
+    for (int q = 2; q < L; ++q)
+        if (L % q == 0 && L / q + q + 1 < c->dP + (c->dQ > 1 ? c->dQ + 1 : 0)) {
+            c->dP = L / q;
+            c->dQ = q;
+        }
     const double g = acos(exp(p->dtau * p->U / 2.0));
     c->k.gamma = g;
     c->k.c2m1 = cos(2.0 * g) - 1.0;
@@ -1494,7 +1548,7 @@ int afqmc_soc_init(afqmc_soc_ctx* ctx, const double* P, const int8_t* fields, vo
     SCK(soc_alloc(ctx, &ctx->Einvrs, (size_t)N2 * ld2 * es, st));
     SCK(soc_alloc(ctx, &ctx->Ech, (size_t)ld2 * ld2 * es, st));
     SCK(soc_alloc(ctx, &ctx->Einvch, (size_t)ld2 * ld2 * es, st));
-    SCK(soc_alloc(ctx, &ctx->dft, (size_t)ctx->p.L * ctx->p.L * 16, st));
+    SCK(soc_alloc(ctx, &ctx->dft, (size_t)(ctx->p.L * ctx->p.L + 2 * ctx->p.L + 2) * 16, st));
     SCK(soc_alloc(ctx, &ctx->lamk, (size_t)N * 64, st));
     SCK(soc_alloc(ctx, &ctx->G, (size_t)nwk * ctx->gstride() * es, st));
     SCK(soc_alloc(ctx, &ctx->S, (size_t)nwk * ld2 * ld2 * es, st));
