@@ -143,6 +143,22 @@ def run_oracle_sample(n_slices, k, warm=0):
     return N * len(times) / sum(times), cores, sum(times)
 
 
+def soc_oracle_sample():
+    """The FP64 SOC oracle on the host cores: G(0) of the 24 x 24 workload with M = 2 (not timed),
+    then four slice-steps (wrap + block force bias, nb = 16: forward 1, 2, backward 2, 1) timed."""
+    import oracle
+
+    Ns = SOC_L * SOC_L
+    m = oracle.SocModel(SOC_L, T_HOP, SOC_LAM, SOC_U, DTAU, 2)
+    w = oracle.SocWalker(m, inputs.soc_trial_state(SOC_L, Ns, lam=SOC_LAM), inputs.initial_fields(2, Ns, seed=1))
+    t0 = time.perf_counter()
+    for visit, (ell, d) in enumerate(((1, +1), (2, +1), (2, -1), (1, -1))):
+        w.sweep_slice(ell, d, "blockfb", inputs.uniforms(1, 0, visit, 2 * Ns), nb=16)
+    secs = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return 4 * Ns / secs, cores, secs
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return
@@ -525,13 +541,48 @@ def soc_leg(torch, stream, args, seed):
             acc = float(np.mean([d[:Ns].mean() for d in dec]))
         upd = Ns * S
         t_upd = prof["prep"]["ms"] + prof["chain"]["ms"] + prof["flush"]["ms"]
+        if name == "blockfb_nb16":
+            soc_prof = prof
         out[name] = {"update_only": upd / (t_upd / 1e3), "with_wrap": upd / ((t_upd + prof["wrap"]["ms"]) / 1e3),
                      "with_recompute": upd / (ms / 1e3), "acceptance": acc, "flip_rate": flips / upd,
                      "ms_per_slice": {p: prof[p]["ms"] / S for p in prof if prof[p]["intervals"]},
                      "launches_per_slice": sum(v["launches"] for v in prof.values()) / S}
         ctx.close()
     base = out["local"]["update_only"]
+    # rooflines of the dominant SOC kernels, from the block force-bias (nb = 16) run's intervals
+    pk, pk_src = peaks()
+    fp64 = fp64_alu_peak(pk)
+    N2, ld2, nv = 2 * Ns, 2 * ((2 * Ns + 31) // 32 * 32), 2 * n_e
+    prof = soc_prof
+    roofs = []
+    wg = prof["wrap_gemm"]
+    if wg["intervals"]:
+        flop = 2.0 * N2 * ld2 * ld2  # one realified product: the four real products of a complex GEMM
+        ach = flop * wg["intervals"] / (wg["ms"] / 1e3) / 1e12
+        peak = pk["bf16_tflops"] * TF32_OVER_BF16
+        roofs.append({"kernel": "SOC wrap GEMM (realified complex, tc3)", "bound": "tensor", "achieved": ach,
+                      "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "launches": wg["intervals"],
+                      "ms_per_launch": wg["ms"] / wg["intervals"], "work_per_launch": flop,
+                      "peak_source": "TF32 = measured bf16 burst x 1.1/2.25 (of %s); three TF32 MMAs per product"
+                                     % pk_src})
+    for name, label, flop in (
+            ("elim", "FP64 LU of the realified 4N x 2N_e factor", 2 * (2 * N2 * nv ** 2 - nv ** 3 / 3.0)),
+            ("lu_o", "FP64 LU of the realified U_L U_R (2N_e x 2N_e)", (2.0 / 3.0) * nv ** 3),
+            ("solve", "FP64 solve with 2N right-hand sides", 2.0 * nv ** 2 * N2)):
+        ph = prof[name]
+        if ph["intervals"]:
+            ach = flop * ph["intervals"] / (ph["ms"] / 1e3) / 1e12
+            roofs.append({"kernel": label, "bound": "alu", "achieved": ach, "peak": fp64, "unit": "TFLOP/s",
+                          "frac": ach / fp64, "launches": ph["intervals"], "ms_per_launch": ph["ms"] / ph["intervals"],
+                          "work_per_launch": flop, "peak_source": "nominal FP64 1.25 TFLOP/s (of %s peaks)" % pk_src})
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, cores, secs = soc_oracle_sample()
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "four slice-steps (wrap + block force bias nb = 16) of the FP64 oracle at 24x24 from its "
+                         "own G(0) (M = 2 init not timed); %.1f s of CPU work" % secs}
     return {"metric": "field updates/s, spin-orbit-coupled Hubbard 24x24 (complex G 1152x1152)", "unit": UNIT,
+            "rooflines": roofs, "cpu_baseline": cpu,
             "config": {"L": SOC_L, "lambda": SOC_LAM, "U": SOC_U, "n_e": n_e, "dtau": DTAU, "M": SOC_M,
                        "stab_every": SOC_STAB, "precision": "fp32 (complex64) bulk, FP64 recompute",
                        "gemm": args.gemm, "timed_slices": S},
