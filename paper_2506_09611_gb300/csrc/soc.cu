@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
     __shared__ int s_site[64];
     __shared__ T s_uT[64];
     __shared__ int s_x[64], s_rep[64];
-    __shared__ int s_take[2], s_m, s_acc;
+    __shared__ int s_m, s_acc;
     __shared__ T s_logq;
     __shared__ c22<T> s_w2;
     __shared__ cx<T> s_det;
@@ -334,65 +334,96 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
         int m = 0;
         cx<T>* colW = aux;           // [n2][2]
         cx<T>* rowY = aux + 2 * n2;  // [2][n2]
-        const int per = nt / n2, cc = tid % n2, r0 = tid / n2;  // 2D map of the rank-2 update
-        for (int t = 0; t < n; ++t) {
+        __shared__ int s_next, s_apos;
+        int t = 0;
+        while (t < n) {
             if (warp == 0) {
-                // warp 0 takes the decision (all lanes alike) and snapshots the rank-2 factors
-                const int xi = s_x[t];
-                T dl[2][2];
-                real_delta<T>(a.k.c2m1, a.k.s2, xi, dl);
-                cx<T> g[2][2];
-                for (int p = 0; p < 2; ++p)
-                    for (int q = 0; q < 2; ++q) g[p][q] = Mw[(2 * t + p) * n2 + 2 * t + q];
+                // warp 0 tests the next 32 sites at once on the current block (a rejection leaves G
+                // unchanged) and a ballot finds the first acceptance; all lanes of a site agree
+                const int q = t + lane;
+                bool acc = false, fin = true;
+                cx<T> R = cmk((T)0, (T)0);
                 c22<T> w2;
-                const cx<T> R = site_test<T>(g, dl, w2);
-                // the test in the bulk precision (the FP32 bulk rounds u to float: a bias below
-                // 2^-25 in the acceptance probability)
-                const T absR = sqrt(R.r * R.r + R.i * R.i);
-                const bool fin = isfinite(absR);
-                const int acc = s_rep[t] >= 0 ? (s_rep[t] != 0) : (s_uT[t] < absR);
-                const bool take = acc && fin && absR > (T)0;
-                if (take) {
-                    for (int r = lane; r < n2; r += 32) {
-                        const cx<T> g0 = Mw[r * n2 + 2 * t], g1 = Mw[r * n2 + 2 * t + 1];
-                        for (int q = 0; q < 2; ++q) {
-                            cx<T> v = cmul(g0, w2.a[0][q]);
-                            cfma(v, g1, w2.a[1][q]);
-                            colW[2 * r + q] = v;
+                T dl[2][2];
+                int xi = 0;
+                if (q < n) {
+                    xi = s_x[q];
+                    real_delta<T>(a.k.c2m1, a.k.s2, xi, dl);
+                    cx<T> g[2][2];
+                    for (int p = 0; p < 2; ++p)
+                        for (int qq = 0; qq < 2; ++qq) g[p][qq] = Mw[(2 * q + p) * n2 + 2 * q + qq];
+                    R = site_test<T>(g, dl, w2);
+                    // the test in the bulk precision (the FP32 bulk rounds u to float: a bias below
+                    // 2^-25 in the acceptance probability)
+                    const T absR = sqrt(R.r * R.r + R.i * R.i);
+                    fin = isfinite(absR);
+                    acc = (s_rep[q] >= 0 ? (s_rep[q] != 0) : (s_uT[q] < absR)) && fin && absR > (T)0;
+                    if (!fin) set_err(a.err, DEV_NUMERIC);
+                }
+                const unsigned ball = __ballot_sync(0xffffffffu, acc);
+                const int first = ball ? __ffs(ball) - 1 : 32;
+                if (q < n && lane <= first) {
+                    const int i = s0 + q;
+                    ratio[2 * i] = (double)R.r;
+                    ratio[2 * i + 1] = (double)R.i;
+                    dec[i] = (uint8_t)(lane == first);
+                }
+                if (first < 32) {
+                    // snapshot of the accepted site's rank-2 factors on the trailing rows / columns
+                    c22<T> wv;
+#pragma unroll
+                    for (int p = 0; p < 2; ++p)
+#pragma unroll
+                        for (int qq = 0; qq < 2; ++qq) {
+                            wv.a[p][qq].r = __shfl_sync(0xffffffffu, w2.a[p][qq].r, first);
+                            wv.a[p][qq].i = __shfl_sync(0xffffffffu, w2.a[p][qq].i, first);
+                        }
+                    const int at = t + first, c0 = 2 * at + 2;
+                    for (int r = c0 + lane; r < n2; r += 32) {
+                        const cx<T> g0 = Mw[r * n2 + 2 * at], g1 = Mw[r * n2 + 2 * at + 1];
+                        for (int qq = 0; qq < 2; ++qq) {
+                            cx<T> v = cmul(g0, wv.a[0][qq]);
+                            cfma(v, g1, wv.a[1][qq]);
+                            colW[2 * r + qq] = v;
                         }
                         for (int p = 0; p < 2; ++p) {
-                            const cx<T> gg = Mw[(2 * t + p) * n2 + r];
-                            rowY[p * n2 + r] = cmk((r == 2 * t + p ? (T)1 : (T)0) - gg.r, -gg.i);
+                            const cx<T> gg = Mw[(2 * at + p) * n2 + r];
+                            rowY[p * n2 + r] = cmk(-gg.r, -gg.i);  // E_S^T - G[S, :] beyond the site
                         }
+                    }
+                    if (lane == first) {
+                        for (int p = 0; p < 2; ++p)
+                            for (int qq = 0; qq < 2; ++qq) s_dl[m][p][qq] = dl[p][qq];
+                        s_site[m] = s0 + q;
+                        sites[m] = s0 + q;
+                        x[s0 + q] = (int8_t)(-xi);
                     }
                 }
                 if (lane == 0) {
-                    const int i = s0 + t;
-                    ratio[2 * i] = (double)R.r;
-                    ratio[2 * i + 1] = (double)R.i;
-                    dec[i] = (uint8_t)acc;
-                    if (!fin) set_err(a.err, DEV_NUMERIC);
-                    if (take) {
-                        for (int p = 0; p < 2; ++p)
-                            for (int q = 0; q < 2; ++q) s_dl[m][p][q] = dl[p][q];
-                        s_site[m] = i;
-                        sites[m] = i;
-                        x[i] = (int8_t)(-xi);
-                    }
-                    s_take[t & 1] = take;
+                    s_apos = first < 32 ? t + first : -1;
+                    s_next = first < 32 ? t + first + 1 : min(n, t + 32);
                 }
             }
             __syncthreads();
-            if (!s_take[t & 1]) continue;
+            const int at = s_apos;
+            t = s_next;
+            if (at < 0) continue;
             ++m;
-            if (r0 < per) {
-                const cx<T> y0 = rowY[cc], y1 = rowY[n2 + cc];
-                for (int r = r0; r < n2; r += per) {
-                    cx<T> v = Mw[r * n2 + cc];
-                    const cx<T> c0 = colW[2 * r], c1 = colW[2 * r + 1];
-                    cfma(v, cmk(-c0.r, -c0.i), y0);
-                    cfma(v, cmk(-c1.r, -c1.i), y1);
-                    Mw[r * n2 + cc] = v;
+            // trailing rank-2 update: rows and columns after the accepted site (earlier ones are
+            // never read again; W comes from the window's starting G)
+            const int c0 = 2 * at + 2, w = n2 - c0;
+            if (w > 0) {
+                const int per = nt / w, cc = tid % w, r0 = tid / w;
+                if (r0 < per) {
+                    const int c = c0 + cc;
+                    const cx<T> y0 = rowY[c], y1 = rowY[n2 + c];
+                    for (int r = c0 + r0; r < n2; r += per) {
+                        cx<T> v = Mw[r * n2 + c];
+                        const cx<T> q0 = colW[2 * r], q1 = colW[2 * r + 1];
+                        cfma(v, cmk(-q0.r, -q0.i), y0);
+                        cfma(v, cmk(-q1.r, -q1.i), y1);
+                        Mw[r * n2 + c] = v;
+                    }
                 }
             }
             __syncthreads();
