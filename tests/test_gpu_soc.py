@@ -170,3 +170,35 @@ def test_fp32_full_size_24x24_one_slice(mode, k, nb):
         assert rel(ctx.G(0), w.G) < FP32_TOL
         if mode == "blockfb":  # proposal probabilities from the FP32 block
             np.testing.assert_allclose(ctx.lam_plus(0), extra["lam_plus"], atol=1e-4)
+
+
+def test_two_walkers_with_device_drawn_fields_fp64():
+    """Two walkers in one context, fields drawn on the device (read back and given to the oracle):
+    each walker's G(0) and its free-running slices match its own oracle chain."""
+    L, n_e, M, stab, seed = 4, 14, 4, 2, 31
+    P = inputs.soc_trial_state(L, n_e)
+    ctx = soc.SocContext(L, M, n_e, 2, "fp64", "tc3", stab, 1.0, 0.5, -4.0, 0.05, seed)
+    with ctx:
+        ctx.init(P, None)
+        model = oracle.SocModel(L, 1.0, 0.5, -4.0, 0.05, M)
+        ws = []
+        for j in range(2):
+            X = ctx.fields(j)
+            assert set(np.unique(X)) <= {-1, 1}
+            w = oracle.SocWalker(model, P, X)
+            assert rel(ctx.G(j), w.G) < FP64_TOL
+            ws.append(w)
+        assert not np.array_equal(ctx.fields(0), ctx.fields(1))
+        N = L * L
+        for visit, (ell, d) in enumerate(order(M)[:4]):
+            ctx.sweep_slice(ell, d, "blockfb", nb=4)
+            for j, w in enumerate(ws):
+                u = inputs.uniforms(seed, j, visit, 2 * N)
+                w.sweep_slice(ell, d, "blockfb", u, nb=4)
+                np.testing.assert_array_equal(ctx.fields(j), w.x)
+                assert rel(ctx.G(j), w.G) < FP64_TOL
+            if ws[0].pos % stab == 0:
+                ctx.recompute_G()
+                for j, w in enumerate(ws):
+                    w.recompute()
+                    assert rel(ctx.G(j), w.G) < FP64_TOL
