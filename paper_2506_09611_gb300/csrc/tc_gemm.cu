@@ -218,22 +218,29 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
         ++consumed;
         if (SPLIT) {
             // hi = x with the low 13 mantissa bits cleared, lo = x - hi, for both tiles of the stage
-            uint32_t* ah = (uint32_t*)Ahi(s);
-            uint32_t* al = (uint32_t*)Alo(s);
-            for (int e = tid; e < TC_BM * TC_BK; e += 128) {
-                const uint32_t x = ah[e];
-                const uint32_t h = x & 0xFFFFE000u;
-                ah[e] = h;
-                al[e] = __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
-            }
-            uint32_t* bh = (uint32_t*)Bhi(s);
-            uint32_t* bl = (uint32_t*)Blo(s);
-            for (int e = tid; e < BN * TC_BK; e += 128) {
-                const uint32_t x = bh[e];
-                const uint32_t h = x & 0xFFFFE000u;
-                bh[e] = h;
-                bl[e] = __float_as_uint(__uint_as_float(x) - __uint_as_float(h));
-            }
+            // (16-byte accesses: consecutive threads touch consecutive 16-byte chunks, and hi / lo
+            // tiles share the swizzled layout, so the split is position by position)
+            auto split = [&](unsigned char* hp, unsigned char* lp, int n4) {
+                uint4* h4 = (uint4*)hp;
+                uint4* l4 = (uint4*)lp;
+#pragma unroll 4
+                for (int e = tid; e < n4; e += 128) {
+                    const uint4 x = h4[e];
+                    uint4 h, l;
+                    h.x = x.x & 0xFFFFE000u;
+                    h.y = x.y & 0xFFFFE000u;
+                    h.z = x.z & 0xFFFFE000u;
+                    h.w = x.w & 0xFFFFE000u;
+                    l.x = __float_as_uint(__uint_as_float(x.x) - __uint_as_float(h.x));
+                    l.y = __float_as_uint(__uint_as_float(x.y) - __uint_as_float(h.y));
+                    l.z = __float_as_uint(__uint_as_float(x.z) - __uint_as_float(h.z));
+                    l.w = __float_as_uint(__uint_as_float(x.w) - __uint_as_float(h.w));
+                    h4[e] = h;
+                    l4[e] = l;
+                }
+            };
+            split(Ahi(s), Alo(s), TC_BM * TC_BK / 4);
+            split(Bhi(s), Blo(s), BN * TC_BK / 4);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
         }
