@@ -172,7 +172,17 @@ struct SocWinArgs {
     int* err;
     int xw_inline;       // n <= 4: the kernel also forms X' = G[:, F] W (2N x 2m) at Xp0
     void* Xp0;
+    // pipelined windows: G0 is the G before the previous window's update, which is applied to the
+    // window's block here from the previous window's W (pW), flipped sites (psites) and size
+    // (pKdev); corr = 0 reads G0 as the current G
+    int corr;
+    const void* pW;
+    const int* psites;
+    const int* pKdev;
+    void* Gw0;           // per walker (2 kmax)^2 complex: the window's block of the current G
 };
+
+constexpr int SOC_PIPE_N = 32;  // windows of up to 32 sites run pipelined (the correction's staging buffer)
 
 template <typename T>
 __device__ __forceinline__ cx<T> g_at(const T* G, long ldz, int r, int c) {
@@ -308,6 +318,8 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
 
     cx<T>* Mw = (cx<T>*)soc_smem;               // (2 kmax)^2: the window block / the LU matrix
     cx<T>* aux = Mw + 4 * a.kmax * a.kmax;      // 8 kmax: column / row snapshots, GJ scratch
+    cx<T>* Ys = aux + 8 * a.kmax;               // (2 SOC_PIPE_N)^2: staging of the correction
+    cx<T>* Gw = (cx<T>*)a.Gw0 + (long)z * 4 * a.kmax * a.kmax;  // n2 x n2: the block of the current G
     __shared__ T s_dl[64][2][2];                // flip deltas of the flipped sites
     __shared__ int s_site[64];
     __shared__ T s_uT[64];
@@ -323,13 +335,55 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
         s_x[t] = x[s0 + t];
         s_rep[t] = rep ? (int)rep[s0 + t] : -1;
     }
+    // ---- the window's block of the current G, into Gw ----
+    {
+        const int m2p = a.corr ? a.pKdev[z] : 0;
+        if (m2p == 0) {
+            for (int e = tid; e < n2 * n2; e += nt) {
+                const int r = e / n2, c = e - r * n2;
+                Gw[e] = g_at(G, ldz, orb(r), orb(c));
+            }
+        } else {
+            // G = G0 - (G0[:, Fp] Wp) (E_Fp^T - G0[Fp, :]) on the block (the previous window's update)
+            const int* ps = a.psites + (long)z * a.kmax;
+            const cx<T>* pW = (const cx<T>*)a.pW + (long)z * 4 * a.kmax * a.kmax;
+            auto porb = [&](int q) { return (q & 1) ? N + ps[q >> 1] : ps[q >> 1]; };
+            for (int e = tid; e < n2 * m2p; e += nt) {  // G0[block, Fp]
+                const int r = e / m2p, q = e - r * m2p;
+                Ys[e] = g_at(G, ldz, orb(r), porb(q));
+            }
+            __syncthreads();
+            for (int e = tid; e < n2 * m2p; e += nt) {  // T1 = G0[block, Fp] Wp
+                const int r = e / m2p, q = e - r * m2p;
+                cx<T> v = cmk((T)0, (T)0);
+                for (int p = 0; p < m2p; ++p) cfma(v, Ys[r * m2p + p], pW[(long)p * ldw + q]);
+                Mw[e] = v;
+            }
+            __syncthreads();
+            for (int e = tid; e < m2p * n2; e += nt) {  // E_Fp^T - G0[Fp, block]
+                const int q = e / n2, c = e - q * n2;
+                const int o = porb(q), oc = orb(c);
+                const cx<T> g = g_at(G, ldz, o, oc);
+                Ys[e] = cmk((o == oc ? (T)1 : (T)0) - g.r, -g.i);
+            }
+            __syncthreads();
+            for (int e = tid; e < n2 * n2; e += nt) {
+                const int r = e / n2, c = e - r * n2;
+                cx<T> v = g_at(G, ldz, orb(r), orb(c));
+                for (int q = 0; q < m2p; ++q) {
+                    const cx<T> t1 = Mw[r * m2p + q];
+                    cfma(v, cmk(-t1.r, -t1.i), Ys[q * n2 + c]);
+                }
+                Gw[e] = v;
+            }
+        }
+        __syncthreads();
+    }
+    auto gl = [&](int r, int c) { return Gw[r * n2 + c]; };  // local orbitals 2t + p
     int m2 = 0;  // complex orbitals of the window's update (uniform)
     if (a.mode == 0) {
         // ---- sites one after another on the 2n x 2n block ----
-        for (int e = tid; e < n2 * n2; e += nt) {
-            const int r = e / n2, c = e - r * n2;
-            Mw[e] = g_at(G, ldz, orb(r), orb(c));
-        }
+        for (int e = tid; e < n2 * n2; e += nt) Mw[e] = Gw[e];
         __syncthreads();
         int m = 0;
         cx<T>* colW = aux;           // [n2][2]
@@ -432,17 +486,17 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
             if (tid == 0) a.Kdev[z] = 0;
             return;
         }
-        // M = 1 + A_FF Delta_F from the window's starting G (the bulk G is unchanged so far)
+        // M = 1 + A_FF Delta_F from the window's starting block
         m2 = 2 * m;
         for (int e = tid; e < m2 * m2; e += nt) {
             const int q = e / m2, qq = e - q * m2;
             const int t2 = qq >> 1, p2 = qq & 1;
-            const int rq = (q & 1) ? N + s_site[q >> 1] : s_site[q >> 1];
+            const int lq = 2 * (s_site[q >> 1] - s0) + (q & 1);
             cx<T> v = cmk((q == qq) ? (T)1 : (T)0, (T)0);
             for (int p = 0; p < 2; ++p) {
-                const int cq = p ? N + s_site[t2] : s_site[t2];
-                const cx<T> gg = g_at(G, ldz, rq, cq);
-                const cx<T> Aq = cmk((rq == cq ? (T)1 : (T)0) - gg.r, -gg.i);
+                const int lc = 2 * (s_site[t2] - s0) + p;
+                const cx<T> gg = gl(lq, lc);
+                const cx<T> Aq = cmk((lq == lc ? (T)1 : (T)0) - gg.r, -gg.i);
                 v = cadd(v, cscale(Aq, s_dl[t2][p][p2]));
             }
             Mw[e] = v;
@@ -466,7 +520,7 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
             cx<T> v = cmk((q == qq) ? (T)1 : (T)0, (T)0);
             for (int p = 0; p < 2; ++p) {
                 const int cq = 2 * t2 + p;
-                const cx<T> g = g_at(G, ldz, orb(q), orb(cq));
+                const cx<T> g = gl(q, cq);
                 const cx<T> Aq = cmk((q == cq ? (T)1 : (T)0) - g.r, -g.i);
                 v = cadd(v, cscale(Aq, ds[p][p2]));
             }
@@ -487,7 +541,7 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
                 const int row = 2 * t + p, col = 2 * t + q;
                 cx<T> acc = cmk((T)0, (T)0);
                 for (int r = lane; r < n2; r += 32) {
-                    const cx<T> g = g_at(G, ldz, orb(r), orb(col));
+                    const cx<T> g = gl(r, col);
                     const cx<T> Ar = cmk((r == col ? (T)1 : (T)0) - g.r, -g.i);
                     cfma(acc, Mw[row * n2 + r], Ar);
                 }
@@ -543,12 +597,12 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
         for (int e = tid; e < m2 * m2; e += nt) {
             const int q = e / m2, qq = e - q * m2;
             const int t2 = qq >> 1, p2 = qq & 1;
-            const int rq = (q & 1) ? N + s_site[q >> 1] : s_site[q >> 1];
+            const int lq = 2 * (s_site[q >> 1] - s0) + (q & 1);
             cx<T> v = cmk((q == qq) ? (T)1 : (T)0, (T)0);
             for (int p = 0; p < 2; ++p) {
-                const int cq = p ? N + s_site[t2] : s_site[t2];
-                const cx<T> g = g_at(G, ldz, rq, cq);
-                const cx<T> Aq = cmk((rq == cq ? (T)1 : (T)0) - g.r, -g.i);
+                const int lc = 2 * (s_site[t2] - s0) + p;
+                const cx<T> g = gl(lq, lc);
+                const cx<T> Aq = cmk((lq == lc ? (T)1 : (T)0) - g.r, -g.i);
                 v = cadd(v, cscale(Aq, s_dl[t2][p][p2]));
             }
             Mw[e] = v;
@@ -1011,8 +1065,15 @@ struct afqmc_soc_ctx {
     double *ratio = nullptr, *lamp = nullptr;
     int* gid = nullptr;
     unsigned long long* visit = nullptr;
-    void *G2 = nullptr, *Xp = nullptr, *W = nullptr;  // G2: the other buffer of the out-of-place flush
-    int *Kdev = nullptr, *sites = nullptr, *err = nullptr;
+    void* G2 = nullptr;  // the other buffer of the out-of-place flush
+    // per-window sets, double-buffered by window parity (window w + 1 reads window w's set while
+    // window w's flush runs on sf)
+    void *Xp[2] = {nullptr, nullptr}, *W[2] = {nullptr, nullptr};
+    int *Kdev[2] = {nullptr, nullptr}, *sites[2] = {nullptr, nullptr};
+    int* err = nullptr;
+    void* Gw0 = nullptr;  // per walker: the window's block of the current G
+    cudaStream_t sf = nullptr;
+    cudaEvent_t ev_win[2] = {nullptr, nullptr}, ev_fl[2] = {nullptr, nullptr};
     double *URs = nullptr, *ULs = nullptr, *Ucur = nullptr, *Lrow = nullptr, *O = nullptr, *Z = nullptr,
            *Pb = nullptr, *acc2 = nullptr, *en = nullptr;
     int* perm = nullptr;
@@ -1298,27 +1359,37 @@ cudaError_t soc_wrap(afqmc_soc_ctx* ctx, cudaStream_t st, const int8_t* xl, int 
 
 template <typename T>
 size_t window_smem(int kmax) {
-    return (size_t)(4 * kmax * kmax + 8 * kmax) * sizeof(cx<T>);
+    return (size_t)(4 * kmax * kmax + 8 * kmax + 4 * SOC_PIPE_N * SOC_PIPE_N) * sizeof(cx<T>);
 }
 
-// ---- one window: chain + flush ----
+// ---- one window: chain, then X' = G[:, F] W and the out-of-place flush ----
+// Serial (pipe = false): everything on st; G reads the current G and the flush swaps the buffers.
+// Pipelined: the window kernel (on st) reads Gin, the G before the previous window's update, and
+// applies that update to its block itself; X' and the flush of this window run on sf from Gcur
+// (the G this window decided on) into Gnext, after the window kernel and after the previous flush.
 template <typename T>
 cudaError_t soc_window(afqmc_soc_ctx* ctx, cudaStream_t st, int8_t* xl, const uint8_t* rep, int mode, int s0, int n,
-                       int blk) {
+                       int blk, int w, bool pipe, void* Gin, void* Gcur, void* Gnext) {
     const int N = ctx->N, N2 = ctx->N2, nwk = ctx->nwk, kmax = ctx->kmax;
-    const long ldz = ctx->ldz, ld2 = 2 * ldz;
+    const long ldz = ctx->ldz;
+    const int b = w & 1, pb = (w + 1) & 1;
     cudaError_t e;
     SocWinArgs a;
-    a.G0 = ctx->G; a.gstride = ctx->gstride(); a.ldz = ldz; a.N = N;
+    a.G0 = pipe ? Gin : ctx->G; a.gstride = ctx->gstride(); a.ldz = ldz; a.N = N;
     a.x0 = xl; a.xstride = (long)ctx->p.M * N;
     a.u0 = ctx->u; a.rep = rep;
     a.mode = mode; a.s0 = s0; a.n = n; a.blk = blk;
     a.k = ctx->k;
     a.dec0 = ctx->dec; a.ratio0 = ctx->ratio; a.lam0 = ctx->lamp;
-    a.sites0 = ctx->sites; a.kmax = kmax;
-    a.W0 = ctx->W; a.Kdev = ctx->Kdev; a.err = ctx->err;
-    a.xw_inline = n <= 4;
-    a.Xp0 = ctx->Xp;
+    a.sites0 = ctx->sites[b]; a.kmax = kmax;
+    a.W0 = ctx->W[b]; a.Kdev = ctx->Kdev[b]; a.err = ctx->err;
+    a.xw_inline = !pipe && n <= 4;
+    a.Xp0 = ctx->Xp[b];
+    a.corr = pipe && w > 0;
+    a.pW = ctx->W[pb]; a.psites = ctx->sites[pb]; a.pKdev = ctx->Kdev[pb];
+    a.Gw0 = ctx->Gw0;
+    cudaStream_t sfl = pipe ? ctx->sf : st;
+    if (pipe && w >= 2 && (e = cudaStreamWaitEvent(st, ctx->ev_fl[b], 0)) != cudaSuccess) return e;
     {
         const size_t shm = window_smem<T>(kmax);
         static bool attr[2] = {false, false};
@@ -1332,6 +1403,12 @@ cudaError_t soc_window(afqmc_soc_ctx* ctx, cudaStream_t st, int8_t* xl, const ui
         soc_window_kernel<T><<<nwk, 512, shm, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    if (pipe) {
+        if ((e = cudaEventRecord(ctx->ev_win[b], st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(sfl, ctx->ev_win[b], 0)) != cudaSuccess) return e;
+    }
+    const T* Gsrc = (const T*)(pipe ? Gcur : ctx->G);
+    T* Gdst = (T*)(pipe ? Gnext : ctx->G2);
     const int m2max = 2 * n;
     if (!a.xw_inline) {
         const size_t shm = (size_t)(m2max * m2max + XW_ROWS * m2max) * sizeof(cx<T>);
@@ -1344,9 +1421,9 @@ cudaError_t soc_window(afqmc_soc_ctx* ctx, cudaStream_t st, int8_t* xl, const ui
             attr[sizeof(T) == 8] = true;
         }
         count_launch();
-        soc_xw_kernel<T><<<dim3((N2 + XW_ROWS - 1) / XW_ROWS, 1, nwk), 256, shm, st>>>(
-            (const T*)ctx->G, ctx->gstride(), ldz, N, ctx->sites, kmax, ctx->Kdev, (const cx<T>*)ctx->W,
-            (cx<T>*)ctx->Xp);
+        soc_xw_kernel<T><<<dim3((N2 + XW_ROWS - 1) / XW_ROWS, 1, nwk), 256, shm, sfl>>>(
+            Gsrc, ctx->gstride(), ldz, N, ctx->sites[b], kmax, ctx->Kdev[b], (const cx<T>*)ctx->W[b],
+            (cx<T>*)ctx->Xp[b]);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
@@ -1359,13 +1436,12 @@ cudaError_t soc_window(afqmc_soc_ctx* ctx, cudaStream_t st, int8_t* xl, const ui
             attr[sizeof(T) == 8] = true;
         }
         count_launch();
-        soc_flush_kernel<T><<<dim3((N2 + FL_C - 1) / FL_C, (N2 + FL_R - 1) / FL_R, nwk), 256, shm, st>>>(
-            (const T*)ctx->G, (T*)ctx->G2, ctx->gstride(), ldz, N, ctx->sites, kmax, ctx->Kdev,
-            (const cx<T>*)ctx->Xp);
+        soc_flush_kernel<T><<<dim3((N2 + FL_C - 1) / FL_C, (N2 + FL_R - 1) / FL_R, nwk), 256, shm, sfl>>>(
+            Gsrc, Gdst, ctx->gstride(), ldz, N, ctx->sites[b], kmax, ctx->Kdev[b], (const cx<T>*)ctx->Xp[b]);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    if (pipe) return cudaEventRecord(ctx->ev_fl[b], sfl);
     std::swap(ctx->G, ctx->G2);  // the updated G is the current one
-    (void)ld2;
     return cudaSuccess;
 }
 
@@ -1383,14 +1459,21 @@ int soc_sweep(afqmc_soc_ctx* ctx, int slice, int dir, int mode, int k, int nb, c
         // one interval for the whole update loop (window chains and their flushes): per-window
         // events would add gaps of their own to the local update's thousands of launches
         SocPhase ps(ctx, AFQMC_PHASE_CHAIN, st);
-        if (mode == AFQMC_MODE_BLOCKFB) {
-            for (int b = 0; b * nb < N; ++b) {
-                const int s0 = b * nb, n = std::min(nb, N - s0);
-                SCK(soc_window<T>(ctx, st, xl, rep, 1, s0, n, b));
-            }
-        } else {
-            const int w = (mode == AFQMC_MODE_LOCAL) ? 1 : k;
-            for (int s0 = 0; s0 < N; s0 += w) SCK(soc_window<T>(ctx, st, xl, rep, 0, s0, std::min(w, N - s0), 0));
+        const int wsz = (mode == AFQMC_MODE_BLOCKFB) ? nb : (mode == AFQMC_MODE_LOCAL ? 1 : k);
+        const bool pipe = wsz <= SOC_PIPE_N;
+        void* Gb[2] = {ctx->G, ctx->G2};  // G after window w's update: Gb[(w + 1) & 1]
+        int w = 0;
+        for (int s0 = 0; s0 < N; s0 += wsz, ++w) {
+            const int n = std::min(wsz, N - s0);
+            // window w decides on G after window w - 1's update: it reads the G before that update
+            // (Gb[(w - 1) & 1], complete once flush w - 2 is) and applies the update to its block
+            SCK(soc_window<T>(ctx, st, xl, rep, mode == AFQMC_MODE_BLOCKFB ? 1 : 0, s0, n, w, w, pipe,
+                              Gb[w == 0 ? 0 : (w + 1) & 1], Gb[w & 1], Gb[(w + 1) & 1]));
+        }
+        if (pipe) {
+            SCK(cudaStreamWaitEvent(st, ctx->ev_fl[(w - 1) & 1], 0));
+            ctx->G = Gb[w & 1];
+            ctx->G2 = Gb[(w + 1) & 1];
         }
     }
     if (dir < 0) SCK(soc_wrap<T>(ctx, st, xl, -1));
@@ -1556,6 +1639,11 @@ int afqmc_soc_destroy(afqmc_soc_ctx* ctx) {
     if (!ctx) return AFQMC_OK;
     cudaDeviceSynchronize();
     for (void* q : ctx->allocs) cudaFree(q);
+    for (int q = 0; q < 2; ++q) {
+        if (ctx->ev_win[q]) cudaEventDestroy(ctx->ev_win[q]);
+        if (ctx->ev_fl[q]) cudaEventDestroy(ctx->ev_fl[q]);
+    }
+    if (ctx->sf) cudaStreamDestroy(ctx->sf);
     for (auto& ev : ctx->pending) {
         cudaEventDestroy(ev.a);
         cudaEventDestroy(ev.b);
@@ -1592,10 +1680,16 @@ int afqmc_soc_init(afqmc_soc_ctx* ctx, const double* P, const int8_t* fields, vo
     SCK(soc_alloc(ctx, &ctx->gid, (size_t)nwk * sizeof(int), st));
     SCK(soc_alloc(ctx, &ctx->visit, 8, st));
     SCK(soc_alloc(ctx, &ctx->G2, (size_t)nwk * ctx->gstride() * es, st));
-    SCK(soc_alloc(ctx, &ctx->Xp, (size_t)nwk * N2 * 4 * kmax * es, st));
-    SCK(soc_alloc(ctx, &ctx->W, (size_t)nwk * 8 * kmax * kmax * es, st));
-    SCK(soc_alloc(ctx, &ctx->Kdev, (size_t)nwk * sizeof(int), st));
-    SCK(soc_alloc(ctx, &ctx->sites, (size_t)nwk * kmax * sizeof(int), st));
+    for (int q = 0; q < 2; ++q) {
+        SCK(soc_alloc(ctx, &ctx->Xp[q], (size_t)nwk * N2 * 4 * kmax * es, st));
+        SCK(soc_alloc(ctx, &ctx->W[q], (size_t)nwk * 8 * kmax * kmax * es, st));
+        SCK(soc_alloc(ctx, &ctx->Kdev[q], (size_t)nwk * sizeof(int), st));
+        SCK(soc_alloc(ctx, &ctx->sites[q], (size_t)nwk * kmax * sizeof(int), st));
+        SCK(cudaEventCreateWithFlags(&ctx->ev_win[q], cudaEventDisableTiming));
+        SCK(cudaEventCreateWithFlags(&ctx->ev_fl[q], cudaEventDisableTiming));
+    }
+    SCK(soc_alloc(ctx, &ctx->Gw0, (size_t)nwk * 8 * kmax * kmax * es, st));
+    SCK(cudaStreamCreateWithFlags(&ctx->sf, cudaStreamNonBlocking));
     SCK(soc_alloc(ctx, &ctx->err, sizeof(int), st));
     SCK(soc_alloc(ctx, &ctx->URs, (size_t)nwk * ctx->st_w() * 8, st));
     SCK(soc_alloc(ctx, &ctx->ULs, (size_t)nwk * ctx->st_w() * 8, st));

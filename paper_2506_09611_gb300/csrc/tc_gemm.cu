@@ -32,6 +32,7 @@ namespace {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 32;  // 32 FP32 = 128 bytes = one swizzle atom row
+constexpr int TC_NT = 256;  // 8 warps: all split the stages; warps w and w + 4 share TMEM lane quarter w % 4 in the epilogue
 constexpr unsigned long long WAIT_NS = 2000000000ULL;
 
 template <int BN, bool SPLIT>
@@ -152,7 +153,7 @@ struct TcArgs {
 };
 
 template <int BN, bool SPLIT>
-__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(TC_NT, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB, TcArgs a) {
     using Cfg = TcCfg<BN, SPLIT>;
     constexpr int S = Cfg::STAGES;
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
                 uint4* h4 = (uint4*)hp;
                 uint4* l4 = (uint4*)lp;
 #pragma unroll 4
-                for (int e = tid; e < n4; e += 128) {
+                for (int e = tid; e < n4; e += TC_NT) {
                     const uint4 x = h4[e];
                     uint4 h, l;
                     h.x = x.x & 0xFFFFE000u;
@@ -284,19 +285,20 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     __syncthreads();
     if (!s_abort) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int m = m0 + warp * 32 + lane;
+        const int quarter = warp & 3, half = warp >> 2;  // TMEM lanes 32 quarter .. + 31; column chunks by parity
+        const int m = m0 + quarter * 32 + lane;
         float* C = a.C + (size_t)z * a.sC;
         const float* rs = a.rs ? a.rs + (size_t)z * a.srs : nullptr;
         const float* cs = a.cs ? a.cs + (size_t)z * a.scs : nullptr;
         const float rsm = (rs && m < a.M) ? rs[m] : 1.0f;
 #pragma unroll 1
-        for (int cb = 0; cb < BN / 16; ++cb) {
+        for (int cb = half; cb < BN / 16; cb += 2) {
             float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 16), v);
+            tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cb * 16), v);
             const int nacc = KT < NACC ? KT : NACC;
             for (int q = 1; q < nacc; ++q) {
                 float v2[16];
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q * BN + cb * 16), v2);
+                tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(q * BN + cb * 16), v2);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] += v2[j];
             }
@@ -410,7 +412,7 @@ cudaError_t tc_launch(cudaStream_t st, const TcGemmArgs& g) {
     a.err = g.err;
     dim3 grid((g.N + BN - 1) / BN, (g.M + TC_BM - 1) / TC_BM, g.batch);
     count_launch();
-    tc_gemm_kernel<BN, SPLIT><<<grid, 128, Cfg::SMEM, st>>>(tmA, tmB, a);
+    tc_gemm_kernel<BN, SPLIT><<<grid, TC_NT, Cfg::SMEM, st>>>(tmA, tmB, a);
     return cudaGetLastError();
 }
 
