@@ -348,16 +348,30 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
             const int* ps = a.psites + (long)z * a.kmax;
             const cx<T>* pW = (const cx<T>*)a.pW + (long)z * 4 * a.kmax * a.kmax;
             auto porb = [&](int q) { return (q & 1) ? N + ps[q >> 1] : ps[q >> 1]; };
+            // Wp staged after T1 in the block buffer when it fits (the FP32 window buffer does)
+            const bool wsh = n2 * m2p + m2p * m2p <= 4 * a.kmax * a.kmax;
+            cx<T>* Wsh = Mw + n2 * m2p;
             for (int e = tid; e < n2 * m2p; e += nt) {  // G0[block, Fp]
                 const int r = e / m2p, q = e - r * m2p;
                 Ys[e] = g_at(G, ldz, orb(r), porb(q));
             }
+            if (wsh)
+                for (int e = tid; e < m2p * m2p; e += nt) Wsh[e] = pW[(long)(e / m2p) * ldw + e % m2p];
             __syncthreads();
             for (int e = tid; e < n2 * m2p; e += nt) {  // T1 = G0[block, Fp] Wp
                 const int r = e / m2p, q = e - r * m2p;
-                cx<T> v = cmk((T)0, (T)0);
-                for (int p = 0; p < m2p; ++p) cfma(v, Ys[r * m2p + p], pW[(long)p * ldw + q]);
-                Mw[e] = v;
+                cx<T> v0 = cmk((T)0, (T)0), v1 = cmk((T)0, (T)0);
+                int p = 0;
+                if (wsh) {
+                    for (; p + 1 < m2p; p += 2) {
+                        cfma(v0, Ys[r * m2p + p], Wsh[p * m2p + q]);
+                        cfma(v1, Ys[r * m2p + p + 1], Wsh[(p + 1) * m2p + q]);
+                    }
+                    if (p < m2p) cfma(v0, Ys[r * m2p + p], Wsh[p * m2p + q]);
+                } else {
+                    for (; p < m2p; ++p) cfma(v0, Ys[r * m2p + p], pW[(long)p * ldw + q]);
+                }
+                Mw[e] = cadd(v0, v1);
             }
             __syncthreads();
             for (int e = tid; e < m2p * n2; e += nt) {  // E_Fp^T - G0[Fp, block]
@@ -369,12 +383,18 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
             __syncthreads();
             for (int e = tid; e < n2 * n2; e += nt) {
                 const int r = e / n2, c = e - r * n2;
-                cx<T> v = g_at(G, ldz, orb(r), orb(c));
-                for (int q = 0; q < m2p; ++q) {
-                    const cx<T> t1 = Mw[r * m2p + q];
-                    cfma(v, cmk(-t1.r, -t1.i), Ys[q * n2 + c]);
+                cx<T> v = g_at(G, ldz, orb(r), orb(c)), v1 = cmk((T)0, (T)0);
+                int q = 0;
+                for (; q + 1 < m2p; q += 2) {
+                    const cx<T> t0 = Mw[r * m2p + q], t1 = Mw[r * m2p + q + 1];
+                    cfma(v, cmk(-t0.r, -t0.i), Ys[q * n2 + c]);
+                    cfma(v1, cmk(-t1.r, -t1.i), Ys[(q + 1) * n2 + c]);
                 }
-                Gw[e] = v;
+                if (q < m2p) {
+                    const cx<T> t0 = Mw[r * m2p + q];
+                    cfma(v, cmk(-t0.r, -t0.i), Ys[q * n2 + c]);
+                }
+                Gw[e] = cadd(v, v1);
             }
         }
         __syncthreads();
