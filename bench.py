@@ -61,6 +61,22 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(dist, ms, device):
+    """The slowest rank's time: every rank's timed region ends at the same barrier, so the job's
+    time is the maximum (all_reduce MAX over the process group)."""
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, updates_per_step, steps, ms_total):
+    """Whole-job field updates/s: each rank sweeps its own walker (weak scaling, no collective on the
+    data path), so the job does world x updates_per_step per step in the slowest rank's time."""
+    return world * updates_per_step * steps / (ms_total / 1e3)
+
+
 def peaks():
     try:
         with open(PEAKS_PATH) as f:
@@ -240,12 +256,10 @@ def main():
     ms_steps = [a.elapsed_time(b) for a, b in ev]
     ms_total = sum(ms_steps)
     if dist is not None:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+        ms_total = max_over_ranks(dist, ms_total, "cuda")
         dist.barrier()
     updates_per_step = N * M * 2
-    value = world * updates_per_step * args.steps / (ms_total / 1e3)
+    value = job_throughput(world, updates_per_step, args.steps, ms_total)
     clocks = clk.summary()
 
     # update-only (the paper's "time for update per sweep"): prep + window chains + flushes
