@@ -233,7 +233,7 @@ __device__ __forceinline__ void trailing_update(T* Gs, int n, int P, int a, T f0
         const T f = s ? f1 : f0;
         for (int r = a + 1 + ty; r < n; r += ny) {
             const T g = f * Gb[r * P + a];
-            for (int c = a + 1 + tx; c < n; c += 32) Gb[r * P + c] += g * Gb[a * P + c];
+            for (int c = a + 1 + tx; c < n; c += 32) Gb[r * P + c] = fma(g, Gb[a * P + c], Gb[r * P + c]);
         }
     }
 }
@@ -432,64 +432,89 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
     int n_prop = 0, n_acc = 0, n_flip = 0;
 
     if (MODE == AFQMC_MODE_DELAYED) {
-        // Warp-serial Metropolis: rejections leave G unchanged, so warp 0 evaluates the next
-        // 32 sites on the current block at once and a ballot finds the first acceptance.
-        __shared__ int s_next, s_apos;
-        __shared__ T s_fa[2];
-        int p = 0;
-        while (p < n) {
+        // Warp-serial Metropolis, one accept ahead of the block update: warp 0 keeps its own copy
+        // of the two diagonals, applies each accept's effect on them itself, and scans the next
+        // sites (32 at a time: a rejection leaves G unchanged, a ballot finds the first
+        // acceptance) while warps 1..31 apply the previous accept's trailing update to the block.
+        // Warp 0 reads only row a and column a of an accept a, which that accept's own update never
+        // writes; the earlier updates that do write them are complete at the barrier before.  One
+        // block barrier per accept.
+        T* dg = stc;  // [2][n] warp 0's diagonals (the block-FB path's column / row staging, unused here)
+        for (int q = tid; q < 2 * n; q += nt) dg[q] = Gs[((q / n) * n + q % n) * P + q % n];
+        __shared__ int s_pend[2];
+        __syncthreads();
+        int pend = -1;  // accept whose block update the workers apply in this iteration
+        int p = 0;      // next site to test (warp 0)
+        int m_w0 = 0;   // accepts so far (warp 0)
+        for (int it = 0;; ++it) {
             if (tid < 32) {
-                // ratio arithmetic in the bulk precision T (FP64 division on this critical path
-                // would cost thousands of cycles on GB300's FP64 pipe)
-                const int q = p + tid;
-                bool acc = false;
-                T R = T(0), rr0 = T(1), rr1 = T(1);
-                int xi = 0;
-                if (q < n) {
-                    xi = xw[q] > 0 ? 0 : 1;
-                    rr0 = T(1) + c_dflipT[0][xi] * (T(1) - Gs[(0 * n + q) * P + q]);
-                    rr1 = T(1) + c_dflipT[1][xi] * (T(1) - Gs[(1 * n + q) * P + q]);
-                    R = c_sflipT[xi] * rr0 * rr1;
-                    acc = replay ? (s_rep[q] != 0) : (s_u[q] < fabs(R));
-                    if (!isfinite(R)) {
-                        acc = false;
-                        set_err(err, DEV_NUMERIC);
+                if (pend >= 0) {  // the pending accept's effect on the later diagonals
+                    const int a = idx[pend];
+                    const T f0 = -s_fk[0][pend], f1 = -s_fk[1][pend];
+                    for (int q = a + 1 + tid; q < n; q += 32) {
+                        dg[q] = fma(f0 * Gs[(0 * n + q) * P + a], Gs[(0 * n + a) * P + q], dg[q]);
+                        dg[n + q] = fma(f1 * Gs[(1 * n + q) * P + a], Gs[(1 * n + a) * P + q], dg[n + q]);
                     }
+                    __syncwarp();
                 }
-                const unsigned ball = __ballot_sync(0xffffffffu, acc);
-                const int first = ball ? __ffs(ball) - 1 : 32;
-                if (q < n && tid <= first) {
-                    s_dec[q] = (tid == first) ? 1 : 0;
-                    s_rat[q] = R;
-                }
-                if (tid == first) {
-                    const T f0 = c_dflipT[0][xi] / rr0, f1 = c_dflipT[1][xi] / rr1;
-                    s_fa[0] = f0;
-                    s_fa[1] = f1;
-                    s_fk[0][s_m] = -f0;  // recursion factor f = -Delta / r
-                    s_fk[1][s_m] = -f1;
-                    idx[s_m] = q;
-                    s_m = s_m + 1;
-                    if (R < T(0)) s_nneg = s_nneg + 1;
-                    s_maxrT = fmax(s_maxrT, fabs(R));
+                int next = -1;
+                while (p < n) {
+                    // ratio arithmetic in the bulk precision T (FP64 division on this critical path
+                    // would cost thousands of cycles on GB300's FP64 pipe)
+                    const int q = p + tid;
+                    bool acc = false;
+                    T R = T(0), rr0 = T(1), rr1 = T(1);
+                    int xi = 0;
+                    if (q < n) {
+                        xi = xw[q] > 0 ? 0 : 1;
+                        rr0 = T(1) + c_dflipT[0][xi] * (T(1) - dg[q]);
+                        rr1 = T(1) + c_dflipT[1][xi] * (T(1) - dg[n + q]);
+                        R = c_sflipT[xi] * rr0 * rr1;
+                        acc = replay ? (s_rep[q] != 0) : (s_u[q] < fabs(R));
+                        if (!isfinite(R)) {
+                            acc = false;
+                            set_err(err, DEV_NUMERIC);
+                        }
+                    }
+                    const unsigned ball = __ballot_sync(0xffffffffu, acc);
+                    const int first = ball ? __ffs(ball) - 1 : 32;
+                    if (q < n && tid <= first) {
+                        s_dec[q] = (tid == first) ? 1 : 0;
+                        s_rat[q] = R;
+                    }
+                    if (tid == first) {
+                        s_fk[0][m_w0] = -(c_dflipT[0][xi] / rr0);  // recursion factor f = -Delta / r
+                        s_fk[1][m_w0] = -(c_dflipT[1][xi] / rr1);
+                        idx[m_w0] = q;
+                        if (R < T(0)) s_nneg = s_nneg + 1;
+                        s_maxrT = fmax(s_maxrT, fabs(R));
+                    }
+                    if (first < 32) {
+                        n_prop += first + 1;
+                        p = p + first + 1;
+                        next = m_w0++;
+                        ++n_acc;
+                        ++n_flip;
+                        break;
+                    }
+                    n_prop += min(32, n - p);
+                    p = min(n, p + 32);
                 }
                 if (tid == 0) {
-                    s_apos = (first < 32) ? q + first : -1;
-                    s_next = (first < 32) ? q + first + 1 : min(n, q + 32);
+                    s_pend[it & 1] = next;
+                    s_m = m_w0;
                 }
+                __syncwarp();
+            } else if (pend >= 0) {
+                // warps 1..31: G[r][c] += f G[r][a] G[a][c] for r, c > a, both spins.  Rows and
+                // columns <= a are never touched again, so the block keeps row a and column a as
+                // they were when site a was accepted (the coefficients of the flush recursion).
+                trailing_update(Gs, n, P, idx[pend], -s_fk[0][pend], -s_fk[1][pend], tid - 32, nt - 32);
             }
             __syncthreads();
-            const int a = s_apos;
-            n_prop += s_next - p;
-            p = s_next;
-            if (a < 0) continue;
-            ++n_acc;
-            ++n_flip;
-            // trailing update of the block: G[r][c] += (d/r) G[r][a] G[a][c], r, c > a.  Rows and
-            // columns <= a are never touched again, so the block keeps row a and column a as they
-            // were when site a was accepted (the coefficients of the flush recursion).
-            trailing_update(Gs, n, P, a, s_fa[0], s_fa[1], tid, nt);
-            __syncthreads();
+            const int np = s_pend[it & 1];
+            if (np < 0) break;  // nothing accepted in the rest of the window: the last update is applied
+            pend = np;
         }
         // off the critical path: decisions, ratios, factors and the sign in their ABI types
         for (int q = tid; q < n; q += nt) {
