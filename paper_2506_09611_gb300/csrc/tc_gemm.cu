@@ -302,16 +302,38 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_gemm_kernel(const __grid_constant
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] += v2[j];
             }
-            if (m < a.M) {
+            if (a.c_trans) {  // lanes are consecutive rows m: consecutive addresses of C^T
+                if (m < a.M) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int n = n0 + cb * 16 + j;
-                    if (n >= a.N) continue;
-                    float val = a.alpha * rsm * v[j];
-                    if (cs) val *= cs[n];
-                    const size_t o = a.c_trans ? (size_t)n * a.ldc + m : (size_t)m * a.ldc + n;
-                    C[o] = (a.beta == 0.0f) ? val : val + a.beta * C[o];
+                    for (int j = 0; j < 16; ++j) {
+                        const int n = n0 + cb * 16 + j;
+                        if (n >= a.N) continue;
+                        float val = a.alpha * rsm * v[j];
+                        if (cs) val *= cs[n];
+                        const size_t o = (size_t)n * a.ldc + m;
+                        C[o] = (a.beta == 0.0f) ? val : val + a.beta * C[o];
+                    }
                 }
+            } else {
+                // row-major C: the warp's 32 x 16 chunk goes through shared memory (the pipeline's
+                // stage buffers, idle once every MMA has completed) so that each store instruction
+                // writes two rows of 16 consecutive columns
+                float* stg = (float*)base + warp * (32 * 17);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = v[j];
+                __syncwarp();
+#pragma unroll 4
+                for (int i = 0; i < 16; ++i) {
+                    const int row = 2 * i + (lane >> 4), col = lane & 15;
+                    const int mm = m0 + quarter * 32 + row, n = n0 + cb * 16 + col;
+                    if (mm < a.M && n < a.N) {
+                        float val = a.alpha * (rs ? rs[mm] : 1.0f) * stg[row * 17 + col];
+                        if (cs) val *= cs[n];
+                        const size_t o = (size_t)mm * a.ldc + n;
+                        C[o] = (a.beta == 0.0f) ? val : val + a.beta * C[o];
+                    }
+                }
+                __syncwarp();
             }
         }
     } else if (tid == 0) {
