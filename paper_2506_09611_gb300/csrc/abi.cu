@@ -71,6 +71,10 @@ struct Walker {
     void* Y[2] = {nullptr, nullptr};
     void* snap[2] = {nullptr, nullptr};
     cudaStream_t sf = nullptr;  // flush stream
+    cudaStream_t sp = nullptr;  // propagation stream: the next recompute's factor, one slice behind the sweep
+    cudaEvent_t ev_wrap = nullptr, ev_prop = nullptr;  // after each slice's wrap; after the last propagation
+    int prop_pos = -1, prop_dir = 0;  // Ucur holds the factor at prop_pos (direction prop_dir) after ev_prop
+    int pend_slice = 0;               // forward slice whose propagation waits for the next slice's wrap
     cudaStream_t sm = nullptr;  // the group's main stream (forked from the caller's stream)
     cudaEvent_t ev_chain[2] = {nullptr, nullptr}, ev_prod[2] = {nullptr, nullptr}, ev_done = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -567,12 +571,15 @@ int afqmc_destroy(afqmc_ctx* ctx) {
             if (w->ev_prod[q]) cudaEventDestroy(w->ev_prod[q]);
         }
         if (w->ev_done) cudaEventDestroy(w->ev_done);
+        if (w->ev_wrap) cudaEventDestroy(w->ev_wrap);
+        if (w->ev_prop) cudaEventDestroy(w->ev_prop);
         if (w->ev_fork) cudaEventDestroy(w->ev_fork);
         if (w->ev_join) cudaEventDestroy(w->ev_join);
         for (auto& kv : w->graphs)
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         if (w->sf) cudaStreamDestroy(w->sf);
         if (w->sm) cudaStreamDestroy(w->sm);
+        if (w->sp) cudaStreamDestroy(w->sp);
         delete w;
     }
     for (void* p : ctx->allocs) cudaFree(p);
@@ -680,6 +687,8 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
             CK(cudaEventCreateWithFlags(&w->ev_prod[q], cudaEventDisableTiming));
         }
         CK(cudaEventCreateWithFlags(&w->ev_done, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&w->ev_wrap, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&w->ev_prop, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming));
         {
@@ -687,6 +696,7 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
             CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
             CK(cudaStreamCreateWithPriority(&w->sf, cudaStreamNonBlocking, lo));
             CK(cudaStreamCreateWithFlags(&w->sm, cudaStreamNonBlocking));
+            CK(cudaStreamCreateWithPriority(&w->sp, cudaStreamNonBlocking, lo));
         }
         CK(dalloc(A, &w->visit_d, sizeof(unsigned long long)));
         CK(cudaMemsetAsync(w->visit_d, 0, sizeof(unsigned long long), st));
@@ -778,6 +788,35 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
 }  // extern "C"
 
 static size_t ctx_replay_offset(const afqmc_ctx* ctx, int walker) { return ctx->roff[walker]; }
+
+// Record an event that work outside this stream (and outside a graph captured from it) waits on:
+// during stream capture as an external event node, else a plain record.
+static cudaError_t record_outside(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+                                               : cudaEventRecord(ev, st);
+}
+
+// One slice of the recompute's propagation, on stream sq after event ev (nullable): forward,
+// the right factor R(slice) = B_slice R(slice - 1); backward, the left factor L(slice - 1) =
+// L(slice) B_slice.  The first slice of an interval starts from its stack entry; a later slice
+// continues only the chain it follows (else the recompute propagates the interval itself).
+static cudaError_t prop_step(afqmc_ctx* ctx, Walker* w, int slice, int dir, cudaStream_t sq, cudaEvent_t ev) {
+    const int S = ctx->p.stab_every;
+    const bool first = dir > 0 ? ((slice - 1) % S == 0) : (slice % S == 0);
+    const int prev = dir > 0 ? slice - 1 : slice;
+    if (!first && !(w->prop_dir == dir && w->prop_pos == prev)) return cudaSuccess;
+    cudaError_t e;
+    if (ev && (e = cudaStreamWaitEvent(sq, ev, 0)) != cudaSuccess) return e;
+    if (first && (e = from_stack(w, sq, dir > 0, dir > 0 ? (slice - 1) / S : slice / S)) != cudaSuccess) return e;
+    if ((e = propagate(ctx, w, sq, dir > 0 ? 0 : 1, slice, 1, 1)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(w->ev_prop, sq)) != cudaSuccess) return e;
+    w->prop_pos = dir > 0 ? slice : slice - 1;
+    w->prop_dir = dir;
+    return cudaSuccess;
+}
 
 template <typename T>
 static int sweep_impl(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int k, int nb, const uint8_t* replay,
@@ -888,7 +927,10 @@ static int sweep_impl(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int k,
         PhaseScope pg(ctx, AFQMC_PHASE_WRAP_GEMM, st);
         return gemm<T>(st, g2);
     };
-    if (dir > 0) CK(wrap(+1));
+    if (dir > 0) {
+        CK(wrap(+1));
+        CK(record_outside(w->ev_wrap, st));
+    }
     SiteParams sp;
     sp.N = N;
     sp.ld = ld;
@@ -976,7 +1018,10 @@ static int sweep_impl(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int k,
         CK(cudaEventRecord(w->ev_done, w->sf));
         CK(cudaStreamWaitEvent(st, w->ev_done, 0));
     }
-    if (dir < 0) CK(wrap(-1));
+    if (dir < 0) {
+        CK(wrap(-1));
+        CK(record_outside(w->ev_wrap, st));
+    }
     CK(launch_bump(st, w->visit_d));
     return AFQMC_OK;
 }
@@ -1043,6 +1088,16 @@ int afqmc_sweep_slice(afqmc_ctx* ctx, int slice, int dir, int mode, int k, int n
                      : sweep_impl<float>(ctx, gi, slice, dir, mode, k, nb, replay, sg);
             if (rc) return rc;
         }
+        // the factor of the next recompute follows the sweep one slice behind, on sp, while the
+        // chain runs (not during a wrap): forward, slice l's right-factor step waits for slice
+        // l + 1's wrap; backward, slice l's left-factor step waits for slice l's own wrap down
+        if (dir > 0) {
+            if (w->pend_slice > 0) CK(prop_step(ctx, w, w->pend_slice, +1, w->sp, w->ev_wrap));
+            w->pend_slice = slice;
+        } else {
+            w->pend_slice = 0;
+            CK(prop_step(ctx, w, slice, -1, w->sp, w->ev_wrap));
+        }
         if (sg != st) {
             CK(cudaEventRecord(w->ev_join, sg));
             CK(cudaStreamWaitEvent(st, w->ev_join, 0));
@@ -1104,9 +1159,16 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
         int grp[2][2], ng[2];
         const int ngr = spin_groups(w, grp, ng);
         if (prop) {
-            CK(from_stack(w, st, fwd, fwd ? j - 1 : j + 1));
-            if (fwd) CK(propagate(ctx, w, st, 0, w->pos - S + 1, 1, S));
-            else CK(propagate(ctx, w, st, 1, w->pos + S, -1, S));
+            CK(cudaStreamWaitEvent(st, w->ev_prop, 0));
+            if (fwd && w->pend_slice == w->pos) {  // the interval's last slice: its step on st now
+                CK(prop_step(ctx, w, w->pend_slice, +1, st, nullptr));
+                w->pend_slice = 0;
+            }
+            if (w->prop_pos != w->pos || w->prop_dir != w->last_dir) {  // not followed slice by slice
+                CK(from_stack(w, st, fwd, fwd ? j - 1 : j + 1));
+                if (fwd) CK(propagate(ctx, w, st, 0, w->pos - S + 1, 1, S));
+                else CK(propagate(ctx, w, st, 1, w->pos + S, -1, S));
+            }
             for (int gi = 0; gi < ngr; ++gi) {
                 if (fwd) CK(stab_rows(ctx, w, st, fac_cur(w), grp[gi][0], ng[gi], nullptr));
                 else CK(stab_cols(ctx, w, st, fac_cur(w), grp[gi][0], ng[gi], nullptr));
