@@ -11,15 +11,19 @@
 // right operand is filled from S by one copy pass.  The wrap is therefore two real GEMMs of
 // 2N x 2ldz x 2ldz (the four real products of a complex GEMM) plus the rotation pass D G D^{-1}.
 //
-// Updates.  A window of n sites holds the 2n x 2n block of G on its orbitals (ordered site by
-// site: up, down) in shared memory.  Delayed / local: the sites are tested one after another on
-// that block (ratio R = det(1 + delta A_SS), Eqs. DetRatioSOC, LocalSOC) and accepted sites update
-// the block by the rank-2 formula.  Block force bias: the stripped spin-flip expectations come
-// from (1 + Delta_s) (1 + A_bb Delta_s)^{-1} A_bb of the block, the flipped set F is proposed
-// jointly and tested with det(1 + A_FF Delta_F).  Either way the window ends with
+// Updates.  A window of n sites works on the 2n x 2n block of the current G on its orbitals
+// (ordered site by site: up, down).  Delayed / local: warp 0 tests the sites on that block (ratio
+// R = det(1 + delta A_SS), Eqs. DetRatioSOC, LocalSOC; 32 at a time with a ballot) and an
+// accepted site updates the trailing rows and columns of the block by the rank-2 formula.  Block
+// force bias: the stripped spin-flip expectations come from (1 + Delta_s)(1 + A_bb Delta_s)^{-1}
+// A_bb of the block, the flipped set F is proposed jointly and tested with det(1 + A_FF Delta_F).
+// Either way the window ends with
 //   W = Delta_F (1 + A_FF Delta_F)^{-1}   (in-place Gauss-Jordan with 2 x 2 pivot blocks; the pivot
 // determinants are the successive ratios, non-zero for accepted moves) and the full G takes the
-// rank-2m product  G <- G - (G[:, F] W)(E_F^T - G[F, :])  as real GEMMs.
+// rank-2m update  G <- G - (G[:, F] W)(E_F^T - G[F, :]) out of place (soc_xw_kernel, then
+// soc_flush_kernel into the second G buffer).  Windows of up to 32 sites are pipelined: window
+// w + 1 reads the G before window w's update and applies that update to its own block, while
+// window w's X' and flush run on a second stream.
 //
 // FP64 recompute.  The factors U_R (2N x n_e) and U_L^+ are carried realified, as 4N x 2n_e real
 // matrices (rows: real parts, then imaginary parts); the column space of the realified factor
@@ -170,8 +174,6 @@ struct SocWinArgs {
     void* W0;            // W (2m x 2m complex, leading dimension 2 kmax) per walker
     int* Kdev;           // per walker: 2m (complex orbitals of the update), 0 = no update
     int* err;
-    int xw_inline;       // n <= 4: the kernel also forms X' = G[:, F] W (2N x 2m) at Xp0
-    void* Xp0;
     // pipelined windows: G0 is the G before the previous window's update, which is applied to the
     // window's block here from the previous window's W (pW), flipped sites (psites) and size
     // (pKdev); corr = 0 reads G0 as the current G
@@ -655,23 +657,6 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
     }
     write_W<T>(Mw, m2, m2, s_dl, W, ldw);
     if (tid == 0) a.Kdev[z] = m2;
-    if (a.xw_inline) {
-        // small updates: X' = G[:, F] W here, for all 2N rows (W re-read from this block's writes)
-        __syncthreads();
-        cx<T>* Xp = (cx<T>*)a.Xp0 + (long)z * 2 * N * ldw;
-        for (int r = tid; r < 2 * N; r += nt) {
-            cx<T> gf[8];
-            for (int p = 0; p < m2; ++p) {
-                const int o = (p & 1) ? N + s_site[p >> 1] : s_site[p >> 1];
-                gf[p] = g_at(G, ldz, r, o);
-            }
-            for (int q = 0; q < m2; ++q) {
-                cx<T> v = cmk((T)0, (T)0);
-                for (int p = 0; p < m2; ++p) cfma(v, gf[p], W[(long)p * ldw + q]);
-                Xp[(long)r * ldw + q] = v;
-            }
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1403,8 +1388,6 @@ cudaError_t soc_window(afqmc_soc_ctx* ctx, cudaStream_t st, int8_t* xl, const ui
     a.dec0 = ctx->dec; a.ratio0 = ctx->ratio; a.lam0 = ctx->lamp;
     a.sites0 = ctx->sites[b]; a.kmax = kmax;
     a.W0 = ctx->W[b]; a.Kdev = ctx->Kdev[b]; a.err = ctx->err;
-    a.xw_inline = !pipe && n <= 4;
-    a.Xp0 = ctx->Xp[b];
     a.corr = pipe && w > 0;
     a.pW = ctx->W[pb]; a.psites = ctx->sites[pb]; a.pKdev = ctx->Kdev[pb];
     a.Gw0 = ctx->Gw0;
@@ -1430,7 +1413,7 @@ cudaError_t soc_window(afqmc_soc_ctx* ctx, cudaStream_t st, int8_t* xl, const ui
     const T* Gsrc = (const T*)(pipe ? Gcur : ctx->G);
     T* Gdst = (T*)(pipe ? Gnext : ctx->G2);
     const int m2max = 2 * n;
-    if (!a.xw_inline) {
+    {
         const size_t shm = (size_t)(m2max * m2max + XW_ROWS * m2max) * sizeof(cx<T>);
         static bool attr[2] = {false, false};
         if (!attr[sizeof(T) == 8]) {
