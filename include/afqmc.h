@@ -68,10 +68,15 @@ typedef struct {
     double U;           /* Hubbard interaction */
     double dtau;        /* imaginary-time step */
     uint64_t seed;      /* Philox4x64-10 key word 0 (word 1 = walker index) */
-    int gemm;           /* FP32 bulk only: AFQMC_GEMM_* engine of the wrap and flush products */
+    int gemm;           /* AFQMC_GEMM_* engine of the wrap and flush products (FP32 bulk) and of
+                           the recompute's two FP64 products (both bulk precisions) */
 } afqmc_params;
 
-/* GEMM engines for the FP32 bulk (FP64 bulk always uses FP64 SIMT products). */
+/* GEMM engines.  The wrap and flush products of the FP64 bulk are always FP64 SIMT products.
+ * The recompute's FP64 products U_L U_R and U_R (U_L U_R)^{-1} U_L run on the FP64 pipe under
+ * AFQMC_GEMM_SIMT; under TC3 and TF32 they run on the tcgen05 tensor cores as FP64-accurate
+ * products of exact integer digit planes (error-free splitting; afqmc_debug_dgemm kind 1) where
+ * the shape makes that faster. */
 #define AFQMC_GEMM_TC3 0        /* tcgen05 tensor cores, three-term TF32 split (FP32 accuracy; default) */
 #define AFQMC_GEMM_SIMT 1       /* FP32 FMA pipes */
 #define AFQMC_GEMM_TF32 2       /* tcgen05 tensor cores, one TF32 pass (drift reported, not gated) */
@@ -220,6 +225,17 @@ int64_t afqmc_launch_count(void);
  * must be 16-byte aligned.  Syncs the stream; AFQMC_ERR_TIMEOUT if a device wait expired. */
 int afqmc_debug_gemm(int kind, int M, int N, int K, const float* A, long long lda, const float* Bt,
                      long long ldb, float* C, long long ldc, int c_trans, void* stream);
+
+/* Validation hook for the recompute's FP64 products: C = A * B (FP64, device pointers, row-major
+ * A: M x K, B: K x N, C: M x N with leading dimensions lda >= K, ldb >= N, ldc >= N), kind 0 =
+ * FP64 SIMT product, kind 1 = digit-split product on the tcgen05 tensor cores (every element of A
+ * and B split into b-bit integer digits relative to the largest exponent of its row of A or
+ * column of B; digit planes multiplied exactly in TF32 with FP32 accumulation; levels summed in
+ * FP64).  Allocates and frees its own workspace; syncs the stream.  AFQMC_ERR_NUMERIC for an
+ * element of magnitude >= 2^1023 or non-finite, AFQMC_ERR_TIMEOUT if a device wait expired,
+ * AFQMC_ERR_ARG for K beyond the exact range of the split. */
+int afqmc_debug_dgemm(int kind, int M, int N, int K, const double* A, long long lda, const double* B,
+                      long long ldb, double* C, long long ldc, void* stream);
 
 const char* afqmc_strerror(int code);
 

@@ -27,7 +27,7 @@ EXPORTS = ["afqmc_create", "afqmc_destroy", "afqmc_init_walkers", "afqmc_sweep_s
            "afqmc_measure_energy", "afqmc_get_G", "afqmc_set_G", "afqmc_get_fields", "afqmc_get_decisions",
            "afqmc_get_ratios", "afqmc_get_info", "afqmc_debug_uniforms", "afqmc_set_profiling", "afqmc_set_graphs",
            "afqmc_get_profile", "afqmc_launch_count", "afqmc_apply_flips", "afqmc_apply_flips_noalloc",
-           "afqmc_debug_gemm", "afqmc_strerror"]
+           "afqmc_debug_gemm", "afqmc_debug_dgemm", "afqmc_strerror"]
 PHASES = ["prep", "wrap", "local", "chain", "flush", "recompute", "elim", "wrap_gemm", "flush_gemm", "lu_o",
           "solve"]
 
@@ -84,6 +84,8 @@ def load(path: str = LIB_PATH):
     ll = ctypes.c_longlong
     lib.afqmc_debug_gemm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ll, vp, ll, vp, ll,
                                      ctypes.c_int, vp]
+    lib.afqmc_debug_dgemm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ll, vp, ll, vp, ll,
+                                      vp]
     lib.afqmc_strerror.argtypes = [ctypes.c_int]
     lib.afqmc_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -243,6 +245,12 @@ def afqmc_debug_gemm(kind, M, N, K, A, lda, Bt, ldb, C, ldc, c_trans=0, stream=N
     """C = A @ Bt.T with the tensor-core kernel (kind 1: TF32, 2: three-term TF32 split); device pointers."""
     _ck("afqmc_debug_gemm", load().afqmc_debug_gemm(kind, M, N, K, ctypes.c_void_p(A), lda, ctypes.c_void_p(Bt), ldb,
                                                     ctypes.c_void_p(C), ldc, c_trans, _stream(stream)))
+
+
+def afqmc_debug_dgemm(kind, M, N, K, A, lda, B, ldb, C, ldc, stream=None):
+    """C = A @ B in FP64 (kind 0: FP64 SIMT, 1: digit-split tensor-core product); device pointers."""
+    _ck("afqmc_debug_dgemm", load().afqmc_debug_dgemm(kind, M, N, K, ctypes.c_void_p(A), lda, ctypes.c_void_p(B), ldb,
+                                                      ctypes.c_void_p(C), ldc, _stream(stream)))
 
 
 def afqmc_launch_count():

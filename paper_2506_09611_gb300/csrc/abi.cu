@@ -96,6 +96,10 @@ struct Walker {
     int8_t* flag2 = nullptr; // [nwk][2][maxr]: pivoted-row flags
     int* visited = nullptr;  // [nwk][maxr]: permutation-parity scratch
     double* acc2 = nullptr;  // [nwk][2]
+    // the recompute's two FP64 products on the tensor cores (digit splitting, ozaki.cu)
+    bool oz_Z = false, oz_G = false;  // U_L U_R, and U_R Z
+    float* ozw = nullptr;             // digit planes, both products (the spin groups run in turn)
+    double* ozs = nullptr;            // row / column scales
     std::vector<void*> allocs;
     long gstride() const { return 2L * N * ld; }
     int rows_max() const { return N > nsm ? N : nsm; }
@@ -395,12 +399,22 @@ static cudaError_t form_Z(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac&
     const int N = w->N, ns = w->ns[s0], nmat = w->nwk * ng;
     const long os = (long)w->nsm * w->nsm, zs = (long)w->nsm * N;
     cudaError_t e;
-    GemmArgs<double> g;
-    g.M = ns; g.N = ns; g.K = N; g.batch = nmat;
-    g.A = Lf.at(s0); g.lda = N; g.sA = Lf.bstride(ng);
-    g.B = R.at(s0); g.ldb = ns; g.sB = R.bstride(ng);
-    g.C = w->Ob; g.ldc = ns; g.sC = os;
-    if ((e = gemm<double>(st, g)) != cudaSuccess) return e;
+    if (w->oz_Z) {
+        OzGemmArgs o;
+        o.M = ns; o.N = ns; o.K = N; o.batch = nmat;
+        o.A = Lf.at(s0); o.lda = N; o.sA = Lf.bstride(ng);
+        o.B = R.at(s0); o.ldb = ns; o.sB = R.bstride(ng);
+        o.C = w->Ob; o.ldc = ns; o.sC = os;
+        o.err = w->err;
+        if ((e = ozaki_gemm(st, o, w->ozw, w->ozs)) != cudaSuccess) return e;
+    } else {
+        GemmArgs<double> g;
+        g.M = ns; g.N = ns; g.K = N; g.batch = nmat;
+        g.A = Lf.at(s0); g.lda = N; g.sA = Lf.bstride(ng);
+        g.B = R.at(s0); g.ldb = ns; g.sB = R.bstride(ng);
+        g.C = w->Ob; g.ldc = ns; g.sC = os;
+        if ((e = gemm<double>(st, g)) != cudaSuccess) return e;
+    }
     const Fac O{w->Ob, ng * os, os};
     LuArgs a = lu_args(w, O, 0, ng, ns, ns, ns);
     {
@@ -428,20 +442,31 @@ static cudaError_t form_Z(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac&
 }
 
 // Gnew[b] (FP64, N x ld) = 1 - U_R Z[b] for the spin group of form_Z; then the drift against the
-// bulk G (acc2 per walker, nullable) and the store into the bulk G.  The N x N product stays in
-// FP64 for both bulk precisions: the LU bases are not orthonormal, so 1 - U_R Z cancels large
-// terms and an FP32 product would lose the digits the recompute restores.
+// bulk G (acc2 per walker, nullable) and the store into the bulk G.  The N x N product keeps
+// FP64 accuracy for both bulk precisions (FP64 SIMT, or the digit-split tensor-core product):
+// the LU bases are not orthonormal, so 1 - U_R Z cancels large terms and an FP32 product would
+// lose the digits the recompute restores.
 template <typename T>
 static cudaError_t finish_G(Walker* w, cudaStream_t st, const Fac& R, int s0, int ng, bool drift) {
     const int N = w->N, ns = w->ns[s0], nmat = w->nwk * ng;
     const long gs = (long)N * w->ld;
     cudaError_t e;
-    GemmArgs<double> h;
-    h.M = N; h.N = N; h.K = ns; h.batch = nmat;
-    h.A = R.at(s0); h.lda = ns; h.sA = R.bstride(ng);
-    h.B = w->Z; h.ldb = N; h.sB = (long)w->nsm * N;
-    h.C = w->Gnew; h.ldc = w->ld; h.sC = gs;
-    if ((e = gemm<double>(st, h)) != cudaSuccess) return e;
+    if (w->oz_G) {
+        OzGemmArgs o;
+        o.M = N; o.N = N; o.K = ns; o.batch = nmat;
+        o.A = R.at(s0); o.lda = ns; o.sA = R.bstride(ng);
+        o.B = w->Z; o.ldb = N; o.sB = (long)w->nsm * N;
+        o.C = w->Gnew; o.ldc = w->ld; o.sC = gs;
+        o.err = w->err;
+        if ((e = ozaki_gemm(st, o, w->ozw, w->ozs)) != cudaSuccess) return e;
+    } else {
+        GemmArgs<double> h;
+        h.M = N; h.N = N; h.K = ns; h.batch = nmat;
+        h.A = R.at(s0); h.lda = ns; h.sA = R.bstride(ng);
+        h.B = w->Z; h.ldb = N; h.sB = (long)w->nsm * N;
+        h.C = w->Gnew; h.ldc = w->ld; h.sC = gs;
+        if ((e = gemm<double>(st, h)) != cudaSuccess) return e;
+    }
     if ((e = launch_identity_minus<double>(st, w->Gnew, w->ld, N, nmat, gs)) != cudaSuccess) return e;
     T* Gb = (T*)w->G + (size_t)s0 * gs;                 // bulk G of (walker 0, spin s0)
     const long bs = (ng == 2) ? gs : 2 * gs;            // batch stride in the bulk G
@@ -712,6 +737,15 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
         CK(dalloc(A, (char**)&w->flag2, (size_t)nwk * 2 * maxr));
         CK(dalloc(A, (char**)&w->visited, (size_t)nwk * maxr * sizeof(int)));
         CK(dalloc(A, &w->acc2, (size_t)nwk * 2 * 8));
+        if (ctx->p.gemm != AFQMC_GEMM_SIMT) {
+            w->oz_Z = ozaki_pays(nsm, nsm, N, 2 * nwk);
+            w->oz_G = ozaki_pays(N, N, nsm, 2 * nwk);
+            if (w->oz_Z || w->oz_G) {
+                const size_t f1 = ozaki_ws_floats(nsm, nsm, N, 2 * nwk), f2 = ozaki_ws_floats(N, N, nsm, 2 * nwk);
+                CK(dalloc(A, &w->ozw, (f1 > f2 ? f1 : f2) * sizeof(float)));
+                CK(dalloc(A, &w->ozs, ozaki_sc_doubles(N > nsm ? N : nsm, N > nsm ? N : nsm, 2 * nwk) * 8));
+            }
+        }
         CK(cudaMemsetAsync(w->err, 0, sizeof(int), st));
         CK(cudaMemsetAsync(w->dec, 0, (size_t)nwk * 2 * N, st));  // the block half stays 0 outside block FB
         CK(cudaMemsetAsync(w->ratio, 0, (size_t)nwk * 2 * N * 8, st));
@@ -1381,6 +1415,51 @@ int afqmc_debug_gemm(int kind, int M, int N, int K, const float* A, long long ld
     cudaFree(err);
     if (e != cudaSuccess) return AFQMC_ERR_CUDA;
     if (h == DEV_TIMEOUT) return AFQMC_ERR_TIMEOUT;
+    return h ? AFQMC_ERR_CUDA : AFQMC_OK;
+}
+
+int afqmc_debug_dgemm(int kind, int M, int N, int K, const double* A, long long lda, const double* B, long long ldb,
+                      double* C, long long ldc, void* stream) {
+    if ((kind != 0 && kind != 1) || M < 1 || N < 1 || K < 1 || !A || !B || !C) return AFQMC_ERR_ARG;
+    if (lda < K || ldb < N || ldc < N) return AFQMC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* err = nullptr;
+    float* ws = nullptr;
+    double* sc = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return AFQMC_ERR_OOM;
+    if (kind == 1 && (cudaMalloc(&ws, ozaki_ws_floats(M, N, K, 1) * sizeof(float)) != cudaSuccess ||
+                      cudaMalloc(&sc, ozaki_sc_doubles(M, N, 1) * sizeof(double)) != cudaSuccess)) {
+        cudaFree(ws);
+        cudaFree(err);
+        return AFQMC_ERR_OOM;
+    }
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess && kind == 0) {
+        GemmArgs<double> g;
+        g.M = M; g.N = N; g.K = K;
+        g.A = A; g.lda = lda;
+        g.B = B; g.ldb = ldb;
+        g.C = C; g.ldc = ldc;
+        e = gemm<double>(st, g);
+    } else if (e == cudaSuccess) {
+        OzGemmArgs o;
+        o.M = M; o.N = N; o.K = K;
+        o.A = A; o.lda = lda;
+        o.B = B; o.ldb = ldb;
+        o.C = C; o.ldc = ldc;
+        o.err = err;
+        e = ozaki_gemm(st, o, ws, sc);
+    }
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(sc);
+    cudaFree(ws);
+    cudaFree(err);
+    if (e == cudaErrorInvalidValue) return AFQMC_ERR_ARG;
+    if (e != cudaSuccess) return AFQMC_ERR_CUDA;
+    if (h == DEV_TIMEOUT) return AFQMC_ERR_TIMEOUT;
+    if (h == DEV_NUMERIC) return AFQMC_ERR_NUMERIC;
     return h ? AFQMC_ERR_CUDA : AFQMC_OK;
 }
 

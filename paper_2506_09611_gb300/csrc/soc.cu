@@ -1083,6 +1083,10 @@ struct afqmc_soc_ctx {
            *Pb = nullptr, *acc2 = nullptr, *en = nullptr;
     int* perm = nullptr;
     int8_t* flag = nullptr;
+    // the recompute's two FP64 products on the tensor cores (digit splitting, ozaki.cu)
+    bool oz_O = false, oz_G = false;
+    float* ozw = nullptr;
+    double* ozs = nullptr;
     // profiling
     struct Ev {
         int ph;
@@ -1540,12 +1544,22 @@ cudaError_t soc_form_G(afqmc_soc_ctx* ctx, cudaStream_t st, int j, bool drift) {
     soc_transpose_kernel<<<dim3((nv + 31) / 32, (unsigned)((R4 + 31) / 32), nwk), dim3(32, 8), 0, st>>>(
         Lt, (int)R4, nv, ctx->st_w(), ctx->Lrow, ctx->fsz());
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    GemmArgs<double> g;
-    g.M = nv; g.N = nv; g.K = (int)R4; g.batch = nwk;
-    g.A = ctx->Lrow; g.lda = R4; g.sA = ctx->fsz();
-    g.B = R; g.ldb = nv; g.sB = ctx->st_w();
-    g.C = ctx->O; g.ldc = nv; g.sC = (long)nv * nv;
-    if ((e = gemm<double>(st, g)) != cudaSuccess) return e;
+    if (ctx->oz_O) {
+        OzGemmArgs o;
+        o.M = nv; o.N = nv; o.K = (int)R4; o.batch = nwk;
+        o.A = ctx->Lrow; o.lda = R4; o.sA = ctx->fsz();
+        o.B = R; o.ldb = nv; o.sB = ctx->st_w();
+        o.C = ctx->O; o.ldc = nv; o.sC = (long)nv * nv;
+        o.err = ctx->err;
+        if ((e = ozaki_gemm(st, o, ctx->ozw, ctx->ozs)) != cudaSuccess) return e;
+    } else {
+        GemmArgs<double> g;
+        g.M = nv; g.N = nv; g.K = (int)R4; g.batch = nwk;
+        g.A = ctx->Lrow; g.lda = R4; g.sA = ctx->fsz();
+        g.B = R; g.ldb = nv; g.sB = ctx->st_w();
+        g.C = ctx->O; g.ldc = nv; g.sC = (long)nv * nv;
+        if ((e = gemm<double>(st, g)) != cudaSuccess) return e;
+    }
     LuArgs a = soc_lu_args(ctx, ctx->O, (long)nv * nv, nv, nv, nv);
     {
         SocPhase ps(ctx, AFQMC_PHASE_LU_O, st);
@@ -1562,12 +1576,22 @@ cudaError_t soc_form_G(afqmc_soc_ctx* ctx, cudaStream_t st, int j, bool drift) {
         SocPhase ps(ctx, AFQMC_PHASE_SOLVE, st);
         if ((e = launch_lu_solve(st, sa)) != cudaSuccess) return e;
     }
-    GemmArgs<double> h;
-    h.M = (int)R4; h.N = N2; h.K = nv; h.batch = nwk;
-    h.A = R; h.lda = nv; h.sA = ctx->st_w();
-    h.B = ctx->Z; h.ldb = N2; h.sB = (long)nv * N2;
-    h.C = ctx->Pb; h.ldc = N2; h.sC = R4 * N2;
-    if ((e = gemm<double>(st, h)) != cudaSuccess) return e;
+    if (ctx->oz_G) {
+        OzGemmArgs o;
+        o.M = (int)R4; o.N = N2; o.K = nv; o.batch = nwk;
+        o.A = R; o.lda = nv; o.sA = ctx->st_w();
+        o.B = ctx->Z; o.ldb = N2; o.sB = (long)nv * N2;
+        o.C = ctx->Pb; o.ldc = N2; o.sC = R4 * N2;
+        o.err = ctx->err;
+        if ((e = ozaki_gemm(st, o, ctx->ozw, ctx->ozs)) != cudaSuccess) return e;
+    } else {
+        GemmArgs<double> h;
+        h.M = (int)R4; h.N = N2; h.K = nv; h.batch = nwk;
+        h.A = R; h.lda = nv; h.sA = ctx->st_w();
+        h.B = ctx->Z; h.ldb = N2; h.sB = (long)nv * N2;
+        h.C = ctx->Pb; h.ldc = N2; h.sC = R4 * N2;
+        if ((e = gemm<double>(st, h)) != cudaSuccess) return e;
+    }
     count_launch();
     soc_store_G_kernel<T><<<dim3(256, nwk), 256, 0, st>>>(ctx->Pb, R4 * N2, N2, (T*)ctx->G, ctx->ldz, ctx->gstride(),
                                                          ctx->acc2, drift ? 1 : 0);
@@ -1705,6 +1729,16 @@ int afqmc_soc_init(afqmc_soc_ctx* ctx, const double* P, const int8_t* fields, vo
     SCK(soc_alloc(ctx, &ctx->flag, (size_t)nwk * 2 * N2, st));
     SCK(soc_alloc(ctx, &ctx->acc2, (size_t)nwk * 16, st));
     SCK(soc_alloc(ctx, &ctx->en, (size_t)nwk * 16, st));
+    if (ctx->p.gemm != AFQMC_GEMM_SIMT) {
+        const int nv = ctx->nv, R4 = 2 * N2;
+        ctx->oz_O = ozaki_pays(nv, nv, R4, nwk);
+        ctx->oz_G = ozaki_pays(R4, N2, nv, nwk);
+        if (ctx->oz_O || ctx->oz_G) {
+            const size_t f1 = ozaki_ws_floats(nv, nv, R4, nwk), f2 = ozaki_ws_floats(R4, N2, nv, nwk);
+            SCK(soc_alloc(ctx, &ctx->ozw, (f1 > f2 ? f1 : f2) * sizeof(float), st));
+            SCK(soc_alloc(ctx, &ctx->ozs, ozaki_sc_doubles(R4, R4, nwk) * 8, st));
+        }
+    }
     if (ctx->f64) SCK(upload_constants<double>(ctx, st));
     else SCK(upload_constants<float>(ctx, st));
     count_launch();

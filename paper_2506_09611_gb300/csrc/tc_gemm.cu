@@ -14,6 +14,12 @@
 // as hi*hi + lo*hi + hi*lo in FP32 (the three-term TF32 split of Ootomo and Yokota, 2022).  The
 // split is done in shared memory after each stage lands.
 //
+// FP64 accuracy (the OZ instantiation, driven by ozaki.cu): the operands are stacks of integer
+// digit planes of FP64 matrices.  One launch runs the K loop over a list of (A plane, B plane)
+// pairs into one FP32 accumulator -- every partial sum is an integer below 2^24, so the tensor
+// cores compute it exactly -- and the epilogue adds 2^(e_row + e_col - b d) times it into an FP64
+// C.
+//
 // Every wait is bounded (about two seconds of %globaltimer); on expiry the kernel records
 // DEV_TIMEOUT, stops issuing work, waits (again bounded) for its copies in flight, frees its
 // TMEM and returns.
@@ -150,11 +156,24 @@ struct TcArgs {
     float alpha, beta;
     int a_batched, b_batched;
     int* err;
+    // digit-plane products (OZ): pairs of this launch, k-tiles per pair, planes per batch entry,
+    // the plane of A and of B of every pair, and the FP64 output with its power-of-two scales
+    int oz_np, oz_kt, oz_ns;
+    signed char oz_pa[TC_OZ_MAXP], oz_pb[TC_OZ_MAXP];
+    double* C64;
+    long ldc64, sC64;
+    const double* rsc;
+    long srsc;
+    const double* csc;
+    long scsc;
+    double gscale;
+    int first;
 };
 
-template <int BN, bool SPLIT>
+template <int BN, bool SPLIT, bool OZ>
 __global__ void __launch_bounds__(TC_NT, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+    static_assert(!(SPLIT && OZ), "digit-plane products are single TF32 passes");
     using Cfg = TcCfg<BN, SPLIT>;
     constexpr int S = Cfg::STAGES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -164,8 +183,21 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_gemm_kernel(const __grid_constant
     __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n0 = blockIdx.x * BN, m0 = blockIdx.y * TC_BM, z = blockIdx.z;
-    const int KT = (a.K + TC_BK - 1) / TC_BK;
+    const int KT = OZ ? a.oz_np * a.oz_kt : (a.K + TC_BK - 1) / TC_BK;
     const int za = a.a_batched ? z : 0, zb = a.b_batched ? z : 0;
+    // k-tile t: its K offset and the batch coordinates of its A and B tiles
+    auto tile_of = [&](int t, int& kx, int& ya, int& yb) {
+        if (OZ) {
+            const int pr = t / a.oz_kt, kk = t - pr * a.oz_kt;
+            kx = kk * TC_BK;
+            ya = z * a.oz_ns + a.oz_pa[pr];
+            yb = z * a.oz_ns + a.oz_pb[pr];
+        } else {
+            kx = t * TC_BK;
+            ya = za;
+            yb = zb;
+        }
+    };
     const uint32_t idesc = idesc_tf32(TC_BM, BN);
     const uint32_t stage_tx = Cfg::A_BYTES + Cfg::B_BYTES;
 
@@ -202,9 +234,11 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_gemm_kernel(const __grid_constant
     int issued = 0;  // k-tiles whose TMA was issued (thread 0 only)
     if (tid == 0) {
         for (int s = 0; s < S && s < KT; ++s) {
+            int kx, ya, yb;
+            tile_of(s, kx, ya, yb);
             mbar_expect_tx(&full[s], stage_tx);
-            tma_load_3d(Ahi(s), &tmA, s * TC_BK, m0, za, &full[s]);
-            tma_load_3d(Bhi(s), &tmB, s * TC_BK, n0, zb, &full[s]);
+            tma_load_3d(Ahi(s), &tmA, kx, m0, ya, &full[s]);
+            tma_load_3d(Bhi(s), &tmB, kx, n0, yb, &full[s]);
             ++issued;
         }
     }
@@ -268,9 +302,11 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_gemm_kernel(const __grid_constant
                 const int sr = (kt - 1) % S;
                 const uint32_t phr = (uint32_t)((kt - 1) / S) & 1u;
                 if (mbar_wait(&empty[sr], phr, a.err)) {
+                    int kx, ya, yb;
+                    tile_of(kr, kx, ya, yb);
                     mbar_expect_tx(&full[sr], stage_tx);
-                    tma_load_3d(Ahi(sr), &tmA, kr * TC_BK, m0, za, &full[sr]);
-                    tma_load_3d(Bhi(sr), &tmB, kr * TC_BK, n0, zb, &full[sr]);
+                    tma_load_3d(Ahi(sr), &tmA, kx, m0, ya, &full[sr]);
+                    tma_load_3d(Bhi(sr), &tmB, kx, n0, yb, &full[sr]);
                     ++issued;
                 } else {
                     s_abort = 1;
@@ -283,7 +319,39 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_gemm_kernel(const __grid_constant
         if (!mbar_wait(&done, 0, a.err)) s_abort = 1;
     }
     __syncthreads();
-    if (!s_abort) {
+    if (!s_abort && OZ) {
+        // FP64 epilogue: C64 (+)= (acc * 2^(-b d) * 2^e_row) * 2^e_col.  acc is an exact integer
+        // and the scales are powers of two, so the only rounding is the FP64 addition.  The warp's
+        // 32 x 16 chunk goes through shared memory so that every access covers 16 consecutive
+        // columns of two rows.
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int quarter = warp & 3, half = warp >> 2;
+        const int m = m0 + quarter * 32 + lane;
+        double* C = a.C64 + (size_t)z * a.sC64;
+        const double* csc = a.csc + (size_t)z * a.scsc;
+        float* stg = (float*)base + warp * (32 * 17);
+        double* srow = (double*)((float*)base + 8 * 32 * 17) + warp * 32;
+        srow[lane] = (m < a.M) ? a.rsc[(size_t)z * a.srsc + m] * a.gscale : 0.0;
+#pragma unroll 1
+        for (int cb = half; cb < BN / 16; cb += 2) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cb * 16), v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = v[j];
+            __syncwarp();
+#pragma unroll 4
+            for (int i = 0; i < 16; ++i) {
+                const int row = 2 * i + (lane >> 4), col = lane & 15;
+                const int mm = m0 + quarter * 32 + row, n = n0 + cb * 16 + col;
+                if (mm < a.M && n < a.N) {
+                    const double val = ((double)stg[row * 17 + col] * srow[row]) * csc[n];
+                    const size_t o = (size_t)mm * a.ldc64 + n;
+                    C[o] = a.first ? val : C[o] + val;
+                }
+            }
+            __syncwarp();
+        }
+    } else if (!s_abort) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int quarter = warp & 3, half = warp >> 2;  // TMEM lanes 32 quarter .. + 31; column chunks by parity
         const int m = m0 + quarter * 32 + lane;
@@ -415,7 +483,7 @@ cudaError_t tc_launch(cudaStream_t st, const TcGemmArgs& g) {
     using Cfg = TcCfg<BN, SPLIT>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute((void*)tc_gemm_kernel<BN, SPLIT>,
+        cudaError_t e = cudaFuncSetAttribute((void*)tc_gemm_kernel<BN, SPLIT, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
@@ -432,9 +500,48 @@ cudaError_t tc_launch(cudaStream_t st, const TcGemmArgs& g) {
     a.alpha = g.alpha; a.beta = g.beta;
     a.a_batched = g.sA != 0; a.b_batched = g.sB != 0;
     a.err = g.err;
+    a.oz_np = a.oz_kt = a.oz_ns = 0;
+    a.C64 = nullptr;
+    a.rsc = a.csc = nullptr;
     dim3 grid((g.N + BN - 1) / BN, (g.M + TC_BM - 1) / TC_BM, g.batch);
     count_launch();
-    tc_gemm_kernel<BN, SPLIT><<<grid, TC_NT, Cfg::SMEM, st>>>(tmA, tmB, a);
+    tc_gemm_kernel<BN, SPLIT, false><<<grid, TC_NT, Cfg::SMEM, st>>>(tmA, tmB, a);
+    return cudaGetLastError();
+}
+
+template <int BN>
+cudaError_t tc_oz_launch(cudaStream_t st, const TcOzArgs& g) {
+    using Cfg = TcCfg<BN, false>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute((void*)tc_gemm_kernel<BN, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    CUtensorMap tmA, tmB;
+    const long sa = (long)g.M * g.Kp, sb = (long)g.N * g.Kp;
+    if (!cached_tmap(&tmA, g.Ad, g.M, g.Kp, g.Kp, g.batch * g.ns, sa, TC_BM)) return cudaErrorInvalidValue;
+    if (!cached_tmap(&tmB, g.Bd, g.N, g.Kp, g.Kp, g.batch * g.ns, sb, BN)) return cudaErrorInvalidValue;
+    TcArgs a = {};
+    a.M = g.M; a.N = g.N; a.K = g.K;
+    a.err = g.err;
+    a.oz_np = g.np;
+    a.oz_kt = (g.K + TC_BK - 1) / TC_BK;
+    a.oz_ns = g.ns;
+    for (int i = 0; i < g.np; ++i) {
+        a.oz_pa[i] = (signed char)g.pa[i];
+        a.oz_pb[i] = (signed char)g.pb[i];
+    }
+    a.C64 = g.C; a.ldc64 = g.ldc; a.sC64 = g.sC;
+    a.rsc = g.rsc; a.srsc = g.M;
+    a.csc = g.csc; a.scsc = g.N;
+    a.gscale = g.gscale;
+    a.first = g.first;
+    dim3 grid((g.N + BN - 1) / BN, (g.M + TC_BM - 1) / TC_BM, g.batch);
+    count_launch();
+    tc_gemm_kernel<BN, false, true><<<grid, TC_NT, Cfg::SMEM, st>>>(tmA, tmB, a);
     return cudaGetLastError();
 }
 
@@ -463,6 +570,19 @@ static int pick_bn(const TcGemmArgs& g) {
         }
     }
     return best;
+}
+
+cudaError_t tc_gemm_oz(cudaStream_t st, const TcOzArgs& g) {
+    if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0) return cudaSuccess;
+    if (g.np < 1 || g.np > TC_OZ_MAXP || g.K > g.Kp || (g.Kp & 3)) return cudaErrorInvalidValue;
+    for (int i = 0; i < g.np; ++i)
+        if (g.pa[i] < 0 || g.pa[i] >= g.ns || g.pb[i] < 0 || g.pb[i] >= g.ns) return cudaErrorInvalidValue;
+    TcGemmArgs shape;
+    shape.M = g.M; shape.N = g.N; shape.batch = g.batch;
+    const int bn = pick_bn(shape);
+    if (bn == 160) return tc_oz_launch<160>(st, g);
+    if (bn == 144) return tc_oz_launch<144>(st, g);
+    return tc_oz_launch<128>(st, g);
 }
 
 cudaError_t tc_gemm(cudaStream_t st, const TcGemmArgs& g) {
