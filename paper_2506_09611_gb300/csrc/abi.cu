@@ -98,7 +98,7 @@ struct Walker {
     double* acc2 = nullptr;  // [nwk][2]
     // the recompute's two FP64 products on the tensor cores (digit splitting, ozaki.cu)
     bool oz_Z = false, oz_G = false;  // U_L U_R, and U_R Z
-    float* ozw = nullptr;             // digit planes, both products (the spin groups run in turn)
+    void* ozw = nullptr;              // digit planes, both products (the spin groups run in turn)
     double* ozs = nullptr;            // row / column scales
     std::vector<void*> allocs;
     long gstride() const { return 2L * N * ld; }
@@ -741,8 +741,8 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
             w->oz_Z = ozaki_pays(nsm, nsm, N, 2 * nwk);
             w->oz_G = ozaki_pays(N, N, nsm, 2 * nwk);
             if (w->oz_Z || w->oz_G) {
-                const size_t f1 = ozaki_ws_floats(nsm, nsm, N, 2 * nwk), f2 = ozaki_ws_floats(N, N, nsm, 2 * nwk);
-                CK(dalloc(A, &w->ozw, (f1 > f2 ? f1 : f2) * sizeof(float)));
+                const size_t f1 = ozaki_ws_bytes(nsm, nsm, N, 2 * nwk), f2 = ozaki_ws_bytes(N, N, nsm, 2 * nwk);
+                CK(dalloc(A, (char**)&w->ozw, f1 > f2 ? f1 : f2));
                 CK(dalloc(A, &w->ozs, ozaki_sc_doubles(N > nsm ? N : nsm, N > nsm ? N : nsm, 2 * nwk) * 8));
             }
         }
@@ -1424,10 +1424,10 @@ int afqmc_debug_dgemm(int kind, int M, int N, int K, const double* A, long long 
     if (lda < K || ldb < N || ldc < N) return AFQMC_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     int* err = nullptr;
-    float* ws = nullptr;
+    void* ws = nullptr;
     double* sc = nullptr;
     if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return AFQMC_ERR_OOM;
-    if (kind == 1 && (cudaMalloc(&ws, ozaki_ws_floats(M, N, K, 1) * sizeof(float)) != cudaSuccess ||
+    if (kind == 1 && (cudaMalloc(&ws, ozaki_ws_bytes(M, N, K, 1)) != cudaSuccess ||
                       cudaMalloc(&sc, ozaki_sc_doubles(M, N, 1) * sizeof(double)) != cudaSuccess)) {
         cudaFree(ws);
         cudaFree(err);

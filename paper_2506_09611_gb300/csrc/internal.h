@@ -57,15 +57,15 @@ cudaError_t tc_gemm(cudaStream_t st, const TcGemmArgs& g);
 
 // One group of digit-plane products on the tensor cores (tc_gemm.cu), for ozaki_gemm:
 //   C[z] (+)= gscale * diag(rsc[z]) * (sum_i Ad[z][pa[i]] * Bd[z][pb[i]]^T) * diag(csc[z])
-// Ad: [batch][ns][M][Kp] and Bd: [batch][ns][N][Kp] FP32 planes of small integers (K used,
-// zero-padded to Kp, a multiple of 4); rsc [batch][M], csc [batch][N]; C FP64 row-major
+// Ad: [batch][ns][M][Kp] and Bd: [batch][ns][N][Kp] bf16 planes of small integers (K used,
+// zero-padded to Kp, a multiple of 8); rsc [batch][M], csc [batch][N]; C FP64 row-major
 // (ldc, batch stride sC).  first = 1 overwrites C.  The caller guarantees that the sum of the
 // magnitudes of all products of one output stays below 2^24 (exact in the FP32 accumulator).
 constexpr int TC_OZ_MAXP = 16;
 struct TcOzArgs {
     int M = 0, N = 0, K = 0, Kp = 0, batch = 1, ns = 0;
-    const float* Ad = nullptr;
-    const float* Bd = nullptr;
+    const uint16_t* Ad = nullptr;  // bf16 bit patterns
+    const uint16_t* Bd = nullptr;
     int np = 0;
     int pa[TC_OZ_MAXP] = {}, pb[TC_OZ_MAXP] = {};
     double* C = nullptr; long ldc = 0, sC = 0;
@@ -79,7 +79,7 @@ cudaError_t tc_gemm_oz(cudaStream_t st, const TcOzArgs& g);
 
 // FP64 GEMM C[z] = A[z] B[z] (A: M x K, B: K x N, C: M x N, all row-major FP64 with the given
 // leading dimensions and batch strides) on the TF32 tensor cores by error-free digit splitting
-// (ozaki.cu).  ws / sc: workspace of ozaki_ws_floats / ozaki_sc_doubles elements.
+// (ozaki.cu).  ws / sc: workspace of ozaki_ws_bytes bytes / ozaki_sc_doubles elements.
 struct OzGemmArgs {
     int M = 0, N = 0, K = 0, batch = 1;
     const double* A = nullptr; long lda = 0, sA = 0;
@@ -87,11 +87,11 @@ struct OzGemmArgs {
     double* C = nullptr; long ldc = 0, sC = 0;
     int* err = nullptr;
 };
-size_t ozaki_ws_floats(int M, int N, int K, int batch);
+size_t ozaki_ws_bytes(int M, int N, int K, int batch);
 size_t ozaki_sc_doubles(int M, int N, int batch);
 // true when the digit-split product is expected to beat the FP64 SIMT GEMM at this shape
 bool ozaki_pays(int M, int N, int K, int batch);
-cudaError_t ozaki_gemm(cudaStream_t st, const OzGemmArgs& g, float* ws, double* sc);
+cudaError_t ozaki_gemm(cudaStream_t st, const OzGemmArgs& g, void* ws, double* sc);
 
 // ---- setup / recompute kernels (setup.cu) ----
 cudaError_t launch_expK(cudaStream_t st, int L, double t, double tau, double* E, long ld);

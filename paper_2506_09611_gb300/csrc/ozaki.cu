@@ -9,7 +9,7 @@
 //     A_ik = 2^E_i sum_{p=1..s} a_ik^(p) 2^(-b p) + (a remainder below 2^(E_i - b s)),
 //     with signed integer digits |a^(p)| < 2^b taken from the bits of the FP64 significand
 //     (integer shifts and masks only: no rounding anywhere).  B is split the same way by columns.
-//   * a digit plane holds small integers, exact in TF32, so the tensor cores multiply two planes
+//   * a digit plane holds small integers, exact in bf16, so the tensor cores multiply two planes
 //     exactly, and a sum of products stays exact in the FP32 accumulator as long as its terms
 //     add up to less than 2^24 in magnitude: the pairs (p, q) of one digit level d = p + q are
 //     accumulated together in groups of at most G = floor((2^24 - 1) / (K (2^b - 1)^2)).
@@ -35,7 +35,7 @@ struct OzSplitArgs {
     const double* src;
     long ld, sb;  // leading dimension and batch stride of the source
     int R, K, Kp, b, s;
-    float* out;     // [batch][s][R][Kp]
+    uint16_t* out;  // [batch][s][R][Kp] bf16 bit patterns
     double* scale;  // [batch][R]: 2^E of every output row
     int* err;
 };
@@ -58,9 +58,11 @@ __device__ __forceinline__ unsigned long long oz_fixed(double v, int ebmax, int 
     return m >> (-sh);
 }
 
-__device__ __forceinline__ float oz_digit(unsigned long long X, int F, int b, int p, bool neg) {
+// Digit p as a bf16 bit pattern: an integer below 2^8 converts to FP32 exactly and its FP32
+// pattern has 16 zero low bits, so the upper half is the exact bf16.
+__device__ __forceinline__ uint16_t oz_digit(unsigned long long X, int F, int b, int p, bool neg) {
     const float d = (float)((X >> (F - b * p)) & ((1ull << b) - 1ull));
-    return neg ? -d : d;
+    return (uint16_t)(__float_as_uint(neg ? -d : d) >> 16);
 }
 
 // Digit planes of the rows of a matrix (TRANS = false: output row r is source row r) or of its
@@ -73,9 +75,9 @@ __global__ void __launch_bounds__(256) oz_split_kernel(OzSplitArgs a) {
     const int z = blockIdx.y, r0 = blockIdx.x * 32;
     const int tid = threadIdx.x, lane = tid & 31, wy = tid >> 5;
     const double* src = a.src + (size_t)z * a.sb;
-    float* out = a.out + (size_t)z * a.s * a.R * a.Kp;
+    uint16_t* out = a.out + (size_t)z * a.s * a.R * a.Kp;
     __shared__ int s_emax[32];
-    __shared__ float tile[32][33];
+    __shared__ uint16_t tile[32][34];
     if (tid < 32) s_emax[tid] = 1;
     __syncthreads();
     if (!TRANS) {
@@ -146,8 +148,9 @@ struct OzPlan {
     double cost = 0.0;
 };
 
-// Estimated seconds: tensor passes at ~700 TFLOP/s, per group an FP64 epilogue (four FP64
-// operations and 16 bytes per output) and a launch.
+// Estimated seconds: tensor passes bound by their operand traffic (a 128 x BN tile reads
+// (128 + BN) x 2 bytes per K step: ~16 MACs per byte at ~6 TB/s), per group an FP64 epilogue
+// (four FP64 operations and 16 bytes per output) and a launch.
 static OzPlan oz_plan(int M, int N, int K, int batch) {
     OzPlan best;
     for (int b : {7, 6, 5}) {
@@ -171,19 +174,19 @@ static OzPlan oz_plan(int M, int N, int K, int batch) {
             if (!cur.empty()) p.groups.push_back(cur);
         }
         const double mn = (double)M * N * batch;
-        p.cost = p.pairs * 2.0 * mn * K / 700e12 + (double)p.groups.size() * (mn * (4.0 / 600e9 + 16.0 / 4e12) + 4e-6);
+        p.cost = p.pairs * mn * K / 100e12 + (double)p.groups.size() * (mn * (4.0 / 600e9 + 16.0 / 4e12) + 4e-6);
         if (best.b == 0 || p.cost < best.cost) best = p;
     }
     return best;
 }
 
-// plane row length: K rounded up to 16 bytes, and at least one 32-wide TMA box
-static int kpad(int K) { return K < 32 ? 32 : (K + 3) & ~3; }
+// plane row length: K rounded up to 16 bytes (8 bf16), and at least one 64-wide TMA box
+static int kpad(int K) { return K < 64 ? 64 : (K + 7) & ~7; }
 
 }  // namespace
 
-size_t ozaki_ws_floats(int M, int N, int K, int batch) {
-    return (size_t)OZ_SMAX * batch * ((size_t)M + N) * kpad(K);
+size_t ozaki_ws_bytes(int M, int N, int K, int batch) {
+    return (size_t)OZ_SMAX * batch * ((size_t)M + N) * kpad(K) * sizeof(uint16_t);
 }
 
 size_t ozaki_sc_doubles(int M, int N, int batch) { return (size_t)batch * ((size_t)M + N); }
@@ -192,19 +195,19 @@ bool ozaki_pays(int M, int N, int K, int batch) {
     if (M < 64 || N < 64 || K < 1) return false;
     const OzPlan p = oz_plan(M, N, K, batch);
     if (p.b == 0) return false;
-    const double split = ((double)M + N) * K * batch * (16.0 + 4.0 * p.s) / 4e12 + 8e-6;
+    const double split = ((double)M + N) * K * batch * (16.0 + 2.0 * p.s) / 4e12 + 8e-6;
     const double simt = 2.0 * M * N * (double)K * batch / 0.95e12;
     return p.cost + split < 0.8 * simt;
 }
 
-cudaError_t ozaki_gemm(cudaStream_t st, const OzGemmArgs& g, float* ws, double* sc) {
+cudaError_t ozaki_gemm(cudaStream_t st, const OzGemmArgs& g, void* ws, double* sc) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
     if (g.K <= 0) return cudaErrorInvalidValue;
     const OzPlan plan = oz_plan(g.M, g.N, g.K, g.batch);
     if (plan.b == 0) return cudaErrorInvalidValue;
     const int Kp = kpad(g.K);
-    float* Ad = ws;
-    float* Bd = ws + (size_t)g.batch * plan.s * g.M * Kp;
+    uint16_t* Ad = (uint16_t*)ws;
+    uint16_t* Bd = Ad + (size_t)g.batch * plan.s * g.M * Kp;
     double* rsc = sc;
     double* csc = sc + (size_t)g.batch * g.M;
     OzSplitArgs sa;

@@ -1085,7 +1085,7 @@ struct afqmc_soc_ctx {
     int8_t* flag = nullptr;
     // the recompute's two FP64 products on the tensor cores (digit splitting, ozaki.cu)
     bool oz_O = false, oz_G = false;
-    float* ozw = nullptr;
+    void* ozw = nullptr;
     double* ozs = nullptr;
     // profiling
     struct Ev {
@@ -1734,8 +1734,8 @@ int afqmc_soc_init(afqmc_soc_ctx* ctx, const double* P, const int8_t* fields, vo
         ctx->oz_O = ozaki_pays(nv, nv, R4, nwk);
         ctx->oz_G = ozaki_pays(R4, N2, nv, nwk);
         if (ctx->oz_O || ctx->oz_G) {
-            const size_t f1 = ozaki_ws_floats(nv, nv, R4, nwk), f2 = ozaki_ws_floats(R4, N2, nv, nwk);
-            SCK(soc_alloc(ctx, &ctx->ozw, (f1 > f2 ? f1 : f2) * sizeof(float), st));
+            const size_t f1 = ozaki_ws_bytes(nv, nv, R4, nwk), f2 = ozaki_ws_bytes(R4, N2, nv, nwk);
+            SCK(soc_alloc(ctx, (char**)&ctx->ozw, f1 > f2 ? f1 : f2, st));
             SCK(soc_alloc(ctx, &ctx->ozs, ozaki_sc_doubles(R4, R4, nwk) * 8, st));
         }
     }

@@ -15,10 +15,12 @@
 // split is done in shared memory after each stage lands.
 //
 // FP64 accuracy (the OZ instantiation, driven by ozaki.cu): the operands are stacks of integer
-// digit planes of FP64 matrices.  One launch runs the K loop over a list of (A plane, B plane)
-// pairs into one FP32 accumulator -- every partial sum is an integer below 2^24, so the tensor
-// cores compute it exactly -- and the epilogue adds 2^(e_row + e_col - b d) times it into an FP64
-// C.
+// digit planes of FP64 matrices, stored as bf16 (digits of at most 8 bits are exact) and
+// multiplied by tcgen05.mma kind::f16 with FP32 accumulation.  A 128-byte swizzle row holds 64
+// bf16, so a stage has the same bytes and the same 32-byte MMA steps as the TF32 path.  One
+// launch runs the K loop over a list of (A plane, B plane) pairs into one FP32 accumulator --
+// every partial sum is an integer below 2^24, so the tensor cores compute it exactly -- and the
+// epilogue adds 2^(e_row + e_col - b d) times it into an FP64 C.
 //
 // Every wait is bounded (about two seconds of %globaltimer); on expiry the kernel records
 // DEV_TIMEOUT, stops issuing work, waits (again bounded) for its copies in flight, frees its
@@ -38,6 +40,7 @@ namespace {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 32;  // 32 FP32 = 128 bytes = one swizzle atom row
+constexpr int TC_BK16 = 64;  // the same row in bf16
 constexpr int TC_NT = 256;  // 8 warps: all split the stages; warps w and w + 4 share TMEM lane quarter w % 4 in the epilogue
 constexpr unsigned long long WAIT_NS = 2000000000ULL;
 
@@ -126,6 +129,21 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
@@ -189,7 +207,7 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_gemm_kernel(const __grid_constant
     auto tile_of = [&](int t, int& kx, int& ya, int& yb) {
         if (OZ) {
             const int pr = t / a.oz_kt, kk = t - pr * a.oz_kt;
-            kx = kk * TC_BK;
+            kx = kk * TC_BK16;
             ya = z * a.oz_ns + a.oz_pa[pr];
             yb = z * a.oz_ns + a.oz_pb[pr];
         } else {
@@ -198,7 +216,7 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_gemm_kernel(const __grid_constant
             yb = zb;
         }
     };
-    const uint32_t idesc = idesc_tf32(TC_BM, BN);
+    const uint32_t idesc = OZ ? idesc_bf16(TC_BM, BN) : idesc_tf32(TC_BM, BN);
     const uint32_t stage_tx = Cfg::A_BYTES + Cfg::B_BYTES;
 
     auto Ahi = [&](int s) { return base + (size_t)s * Cfg::STAGE_BYTES; };
@@ -286,8 +304,9 @@ __global__ void __launch_bounds__(TC_NT, 1) tc_gemm_kernel(const __grid_constant
             const uint32_t dacc = tmem + (uint32_t)((kt % NACC) * BN);
 #pragma unroll
             for (int j = 0; j < TC_BK / 8; ++j) {
-                const uint64_t kofs = (uint64_t)(j * 32) >> 4;  // 8 TF32 = 32 bytes along K
-                mma_tf32(dacc, dah + kofs, dbh + kofs, idesc, (kt >= NACC || j > 0) ? 1u : 0u);
+                const uint64_t kofs = (uint64_t)(j * 32) >> 4;  // 8 TF32 (16 bf16) = 32 bytes along K
+                if (OZ) mma_bf16(dacc, dah + kofs, dbh + kofs, idesc, (kt >= NACC || j > 0) ? 1u : 0u);
+                else mma_tf32(dacc, dah + kofs, dbh + kofs, idesc, (kt >= NACC || j > 0) ? 1u : 0u);
                 if (SPLIT) {
                     mma_tf32(dacc, dal + kofs, dbh + kofs, idesc, 1u);
                     mma_tf32(dacc, dah + kofs, dbl + kofs, idesc, 1u);
@@ -434,17 +453,20 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 3D map over a row-major (rows x cols) FP32 matrix with leading dimension ld, batch stride sb
-// (elements), box = 32 columns x box_rows rows, 128-byte swizzle, zero fill out of bounds.
-bool make_tmap(CUtensorMap* tm, const float* ptr, int rows, int cols, long ld, int batch, long sb, int box_rows) {
+// 3D map over a row-major (rows x cols) matrix of FP32 (es = 4) or bf16 (es = 2) elements with
+// leading dimension ld, batch stride sb (elements), box = 128 bytes of columns x box_rows rows,
+// 128-byte swizzle, zero fill out of bounds.
+bool make_tmap(CUtensorMap* tm, const void* ptr, int es, int rows, int cols, long ld, int batch, long sb,
+               int box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
-    if (((uintptr_t)ptr & 15) || ((ld * 4) & 15) || ((sb * 4) & 15)) return false;
+    if (((uintptr_t)ptr & 15) || ((ld * es) & 15) || ((sb * es) & 15)) return false;
     cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
-    cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)sb * 4};
-    cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * es, (cuuint64_t)sb * es};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)ptr, dims, strides, box, estr,
+    CUresult r = fn(tm, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)ptr,
+                    dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -453,26 +475,27 @@ bool make_tmap(CUtensorMap* tm, const float* ptr, int rows, int cols, long ld, i
 // Encoded tensor maps are cached by their full description: the sweep reuses the same
 // buffers every slice, and encoding on every launch would starve the GPU of work.
 struct TmapKey {
-    const float* ptr;
-    int rows, cols, batch, box;
+    const void* ptr;
+    int es, rows, cols, batch, box;
     long ld, sb;
     bool operator==(const TmapKey& o) const {
-        return ptr == o.ptr && rows == o.rows && cols == o.cols && batch == o.batch && box == o.box && ld == o.ld &&
-               sb == o.sb;
+        return ptr == o.ptr && es == o.es && rows == o.rows && cols == o.cols && batch == o.batch && box == o.box &&
+               ld == o.ld && sb == o.sb;
     }
 };
 
-bool cached_tmap(CUtensorMap* tm, const float* ptr, int rows, int cols, long ld, int batch, long sb, int box_rows) {
+bool cached_tmap(CUtensorMap* tm, const void* ptr, int es, int rows, int cols, long ld, int batch, long sb,
+                 int box_rows) {
     static std::vector<std::pair<TmapKey, CUtensorMap>> cache;
     static std::mutex mu;
-    const TmapKey k{ptr, rows, cols, batch, box_rows, ld, sb};
+    const TmapKey k{ptr, es, rows, cols, batch, box_rows, ld, sb};
     std::lock_guard<std::mutex> lk(mu);
     for (auto& e : cache)
         if (e.first == k) {
             *tm = e.second;
             return true;
         }
-    if (!make_tmap(tm, ptr, rows, cols, ld, batch, sb, box_rows)) return false;
+    if (!make_tmap(tm, ptr, es, rows, cols, ld, batch, sb, box_rows)) return false;
     if (cache.size() >= 4096) cache.clear();
     cache.emplace_back(k, *tm);
     return true;
@@ -491,8 +514,8 @@ cudaError_t tc_launch(cudaStream_t st, const TcGemmArgs& g) {
     CUtensorMap tmA, tmB;
     const int ba = g.sA ? g.batch : 1, bb = g.sB ? g.batch : 1;
     const long sA = g.sA ? g.sA : (long)g.M * g.lda, sB = g.sB ? g.sB : (long)g.N * g.ldb;
-    if (!cached_tmap(&tmA, g.A, g.M, g.K, g.lda, ba, sA, TC_BM)) return cudaErrorInvalidValue;
-    if (!cached_tmap(&tmB, g.Bt, g.N, g.K, g.ldb, bb, sB, BN)) return cudaErrorInvalidValue;
+    if (!cached_tmap(&tmA, g.A, 4, g.M, g.K, g.lda, ba, sA, TC_BM)) return cudaErrorInvalidValue;
+    if (!cached_tmap(&tmB, g.Bt, 4, g.N, g.K, g.ldb, bb, sB, BN)) return cudaErrorInvalidValue;
     TcArgs a;
     a.M = g.M; a.N = g.N; a.K = g.K;
     a.C = g.C; a.ldc = g.ldc; a.sC = g.sC; a.c_trans = g.c_trans;
@@ -522,13 +545,13 @@ cudaError_t tc_oz_launch(cudaStream_t st, const TcOzArgs& g) {
     }
     CUtensorMap tmA, tmB;
     const long sa = (long)g.M * g.Kp, sb = (long)g.N * g.Kp;
-    if (!cached_tmap(&tmA, g.Ad, g.M, g.Kp, g.Kp, g.batch * g.ns, sa, TC_BM)) return cudaErrorInvalidValue;
-    if (!cached_tmap(&tmB, g.Bd, g.N, g.Kp, g.Kp, g.batch * g.ns, sb, BN)) return cudaErrorInvalidValue;
+    if (!cached_tmap(&tmA, g.Ad, 2, g.M, g.Kp, g.Kp, g.batch * g.ns, sa, TC_BM)) return cudaErrorInvalidValue;
+    if (!cached_tmap(&tmB, g.Bd, 2, g.N, g.Kp, g.Kp, g.batch * g.ns, sb, BN)) return cudaErrorInvalidValue;
     TcArgs a = {};
     a.M = g.M; a.N = g.N; a.K = g.K;
     a.err = g.err;
     a.oz_np = g.np;
-    a.oz_kt = (g.K + TC_BK - 1) / TC_BK;
+    a.oz_kt = (g.K + TC_BK16 - 1) / TC_BK16;
     a.oz_ns = g.ns;
     for (int i = 0; i < g.np; ++i) {
         a.oz_pa[i] = (signed char)g.pa[i];
@@ -574,7 +597,7 @@ static int pick_bn(const TcGemmArgs& g) {
 
 cudaError_t tc_gemm_oz(cudaStream_t st, const TcOzArgs& g) {
     if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0) return cudaSuccess;
-    if (g.np < 1 || g.np > TC_OZ_MAXP || g.K > g.Kp || (g.Kp & 3)) return cudaErrorInvalidValue;
+    if (g.np < 1 || g.np > TC_OZ_MAXP || g.K > g.Kp || (g.Kp & 7)) return cudaErrorInvalidValue;
     for (int i = 0; i < g.np; ++i)
         if (g.pa[i] < 0 || g.pa[i] >= g.ns || g.pb[i] < 0 || g.pb[i] >= g.ns) return cudaErrorInvalidValue;
     TcGemmArgs shape;
