@@ -350,7 +350,7 @@ def main():
                             "note": "prep + the window loop (decisions; the rank-m flushes overlap on a second "
                                     "stream): the paper's update time"},
             "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()
-                                   if k not in ("elim", "wrap_gemm", "flush_gemm", "lu_o", "solve")},
+                                   if k not in ("elim", "wrap_gemm", "flush_gemm", "lu_o", "solve", "dgemm")},
             "compare_sample": cmp,
             "speedup_update_only_vs_local": speedup,
             "G_err_fp32_vs_fp64_recompute": {"max": max(drifts) if drifts else None,
@@ -376,6 +376,10 @@ def main():
 FP64_FMA_PER_SM_CLK = 2
 # TF32 tensor rate relative to bf16 (nominal dense 1.1 vs 2.25 PFLOP/s).
 TF32_OVER_BF16 = 1.1 / 2.25
+# Digit-plane pairs of each FP64-accurate recompute product: the split's cost model picks 6-bit
+# digits (s = 9, levels p + q <= 10: 45 pairs) for U_L U_R and U_R Z at 40x40 and for both SOC
+# products at 24x24; each pair is one bf16 tensor-core pass over M x N x K.
+OZ_PAIRS = 45
 # DRAM bytes per launch (read + write) from one ncu capture of the current kernel on this
 # workload; None where the phase spans several kernels or no capture of the current kernel exists.
 NCU_TRAFFIC = {"elim": None, "lu_o": None,
@@ -416,6 +420,20 @@ def kernel_rooflines(prof, gemm, pk, pk_src, steps):
                         "frac": ach / fp64, "traffic": NCU_TRAFFIC.get(name), "launches": ph["intervals"],
                         "ms_per_launch": ph["ms"] / ph["intervals"], "ms_per_step": ph["ms"] / steps,
                         "work_per_launch": flop, "peak_source": src64})
+    dg = prof.get("dgemm", {"ms": 0.0, "intervals": 0})
+    if dg["intervals"] > 0:
+        # the two products alternate: U_L U_R (ns x ns x N) and U_R Z (N x N x ns), both spins
+        flop64 = 2.0 * NS * N * (NS + N)  # FP64-equivalent flop per product, averaged over the pair
+        ach64 = flop64 * dg["intervals"] / (dg["ms"] / 1e3) / 1e12
+        ach = OZ_PAIRS * ach64
+        out.append({"kernel": "digit-split FP64 products U_L U_R and U_R Z (bf16 tcgen05, 45 plane pairs, both spins)",
+                    "bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                    "frac": ach / pk["bf16_tflops"], "traffic": None, "launches": dg["intervals"],
+                    "ms_per_launch": dg["ms"] / dg["intervals"], "ms_per_step": dg["ms"] / steps,
+                    "work_per_launch": OZ_PAIRS * flop64, "fp64_equivalent_tflops": ach64,
+                    "fp64_equivalent_vs_fp64_peak": ach64 / fp64,
+                    "peak_source": "measured bf16 burst (of %s); achieved counts every plane-pair pass, includes "
+                                   "the digit split and the FP64 epilogues" % pk_src})
     wg = prof.get("wrap_gemm", {"ms": 0.0, "intervals": 0})
     if wg["intervals"] > 0:
         flop = 2.0 * 2.0 * N ** 3  # one launch = one N x N x N product for both spins
@@ -581,6 +599,17 @@ def soc_leg(torch, stream, args, seed):
                       "ms_per_launch": wg["ms"] / wg["intervals"], "work_per_launch": flop,
                       "peak_source": "TF32 = measured bf16 burst x 1.1/2.25 (of %s); three TF32 MMAs per product"
                                      % pk_src})
+    dg = prof.get("dgemm", {"ms": 0.0, "intervals": 0})
+    if dg["intervals"]:
+        R4 = 2 * N2
+        flop64 = (2.0 * nv * nv * R4 + 2.0 * R4 * N2 * nv) / 2.0  # O = L R and P = R Z, averaged
+        ach64 = flop64 * dg["intervals"] / (dg["ms"] / 1e3) / 1e12
+        roofs.append({"kernel": "digit-split FP64 products (bf16 tcgen05, 45 plane pairs)", "bound": "tensor",
+                      "achieved": OZ_PAIRS * ach64, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                      "frac": OZ_PAIRS * ach64 / pk["bf16_tflops"], "launches": dg["intervals"],
+                      "ms_per_launch": dg["ms"] / dg["intervals"], "work_per_launch": OZ_PAIRS * flop64,
+                      "fp64_equivalent_tflops": ach64, "fp64_equivalent_vs_fp64_peak": ach64 / fp64,
+                      "peak_source": "measured bf16 burst (of %s)" % pk_src})
     for name, label, flop in (
             ("elim", "FP64 LU of the realified 4N x 2N_e factor", 2 * (2 * N2 * nv ** 2 - nv ** 3 / 3.0)),
             ("lu_o", "FP64 LU of the realified U_L U_R (2N_e x 2N_e)", (2.0 / 3.0) * nv ** 3),

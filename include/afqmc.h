@@ -201,7 +201,8 @@ int afqmc_apply_flips_noalloc(int precision, int N, long long ld, void* G_up, vo
 #define AFQMC_PHASE_FLUSH_GEMM 8 /* each rank-m product launch of the flush (inside FLUSH) */
 #define AFQMC_PHASE_LU_O 9       /* each LU of U_L U_R, Nsigma x Nsigma, both spins (inside RECOMPUTE) */
 #define AFQMC_PHASE_SOLVE 10     /* each solve (U_L U_R) Z = U_L, both spins (inside RECOMPUTE) */
-#define AFQMC_NPHASE 11
+#define AFQMC_PHASE_DGEMM 11     /* each digit-split FP64 product U_L U_R or U_R Z, both spins (inside RECOMPUTE) */
+#define AFQMC_NPHASE 12
 /* on != 0 enables profiling and clears the accumulators; on == 0 disables it. */
 int afqmc_set_profiling(afqmc_ctx* ctx, int on);
 

@@ -29,7 +29,7 @@ EXPORTS = ["afqmc_create", "afqmc_destroy", "afqmc_init_walkers", "afqmc_sweep_s
            "afqmc_get_profile", "afqmc_launch_count", "afqmc_apply_flips", "afqmc_apply_flips_noalloc",
            "afqmc_debug_gemm", "afqmc_debug_dgemm", "afqmc_strerror"]
 PHASES = ["prep", "wrap", "local", "chain", "flush", "recompute", "elim", "wrap_gemm", "flush_gemm", "lu_o",
-          "solve"]
+          "solve", "dgemm"]
 
 
 class afqmc_params(ctypes.Structure):

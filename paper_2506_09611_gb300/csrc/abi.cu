@@ -406,6 +406,7 @@ static cudaError_t form_Z(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac&
         o.B = R.at(s0); o.ldb = ns; o.sB = R.bstride(ng);
         o.C = w->Ob; o.ldc = ns; o.sC = os;
         o.err = w->err;
+        PhaseScope pd(ctx, AFQMC_PHASE_DGEMM, st);
         if ((e = ozaki_gemm(st, o, w->ozw, w->ozs)) != cudaSuccess) return e;
     } else {
         GemmArgs<double> g;
@@ -447,7 +448,7 @@ static cudaError_t form_Z(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac&
 // the LU bases are not orthonormal, so 1 - U_R Z cancels large terms and an FP32 product would
 // lose the digits the recompute restores.
 template <typename T>
-static cudaError_t finish_G(Walker* w, cudaStream_t st, const Fac& R, int s0, int ng, bool drift) {
+static cudaError_t finish_G(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac& R, int s0, int ng, bool drift) {
     const int N = w->N, ns = w->ns[s0], nmat = w->nwk * ng;
     const long gs = (long)N * w->ld;
     cudaError_t e;
@@ -458,6 +459,7 @@ static cudaError_t finish_G(Walker* w, cudaStream_t st, const Fac& R, int s0, in
         o.B = w->Z; o.ldb = N; o.sB = (long)w->nsm * N;
         o.C = w->Gnew; o.ldc = w->ld; o.sC = gs;
         o.err = w->err;
+        PhaseScope pd(ctx, AFQMC_PHASE_DGEMM, st);
         if ((e = ozaki_gemm(st, o, w->ozw, w->ozs)) != cudaSuccess) return e;
     } else {
         GemmArgs<double> h;
@@ -803,8 +805,8 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
         // G(0) = 1 - U_R (U_L U_R)^{-1} U_L
         for (int gi = 0; gi < ngr; ++gi) {
             CK(form_Z(ctx, w, st, fac_R(w, 0), fac_L(w, 0), grp[gi][0], ng[gi], w->sign));
-            if (ctx->p.precision == AFQMC_PREC_FP64) CK(finish_G<double>(w, st, fac_R(w, 0), grp[gi][0], ng[gi], false));
-            else CK(finish_G<float>(w, st, fac_R(w, 0), grp[gi][0], ng[gi], false));
+            if (ctx->p.precision == AFQMC_PREC_FP64) CK(finish_G<double>(ctx, w, st, fac_R(w, 0), grp[gi][0], ng[gi], false));
+            else CK(finish_G<float>(ctx, w, st, fac_R(w, 0), grp[gi][0], ng[gi], false));
         }
         w->pos = 0;
         w->last_dir = -1;
@@ -1211,8 +1213,8 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
         }
         for (int gi = 0; gi < ngr; ++gi) {
             CK(form_Z(ctx, w, st, fac_R(w, j), fac_L(w, j), grp[gi][0], ng[gi], nullptr));
-            if (f64) CK(finish_G<double>(w, st, fac_R(w, j), grp[gi][0], ng[gi], true));
-            else CK(finish_G<float>(w, st, fac_R(w, j), grp[gi][0], ng[gi], true));
+            if (f64) CK(finish_G<double>(ctx, w, st, fac_R(w, j), grp[gi][0], ng[gi], true));
+            else CK(finish_G<float>(ctx, w, st, fac_R(w, j), grp[gi][0], ng[gi], true));
         }
         w->need_recompute = false;
         if (fork) {

@@ -1551,6 +1551,7 @@ cudaError_t soc_form_G(afqmc_soc_ctx* ctx, cudaStream_t st, int j, bool drift) {
         o.B = R; o.ldb = nv; o.sB = ctx->st_w();
         o.C = ctx->O; o.ldc = nv; o.sC = (long)nv * nv;
         o.err = ctx->err;
+        SocPhase pd(ctx, AFQMC_PHASE_DGEMM, st);
         if ((e = ozaki_gemm(st, o, ctx->ozw, ctx->ozs)) != cudaSuccess) return e;
     } else {
         GemmArgs<double> g;
@@ -1583,6 +1584,7 @@ cudaError_t soc_form_G(afqmc_soc_ctx* ctx, cudaStream_t st, int j, bool drift) {
         o.B = ctx->Z; o.ldb = N2; o.sB = (long)nv * N2;
         o.C = ctx->Pb; o.ldc = N2; o.sC = R4 * N2;
         o.err = ctx->err;
+        SocPhase pd(ctx, AFQMC_PHASE_DGEMM, st);
         if ((e = ozaki_gemm(st, o, ctx->ozw, ctx->ozs)) != cudaSuccess) return e;
     } else {
         GemmArgs<double> h;
