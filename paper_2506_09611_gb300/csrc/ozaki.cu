@@ -59,9 +59,10 @@ __device__ __forceinline__ unsigned long long oz_fixed(double v, int ebmax, int 
 }
 
 // Digit p as a bf16 bit pattern: an integer below 2^8 converts to FP32 exactly and its FP32
-// pattern has 16 zero low bits, so the upper half is the exact bf16.
+// pattern has 16 zero low bits, so the upper half is the exact bf16.  The digit is narrowed to 32
+// bits before the conversion (a 64-bit integer conversion would run on the FP64 pipe).
 __device__ __forceinline__ uint16_t oz_digit(unsigned long long X, int F, int b, int p, bool neg) {
-    const float d = (float)((X >> (F - b * p)) & ((1ull << b) - 1ull));
+    const float d = (float)(unsigned)((X >> (F - b * p)) & ((1ull << b) - 1ull));
     return (uint16_t)(__float_as_uint(neg ? -d : d) >> 16);
 }
 
