@@ -384,7 +384,7 @@ OZ_PAIRS = 45
 # workload; None where the phase spans several kernels or no capture of the current kernel exists.
 NCU_TRAFFIC = {"elim": None, "lu_o": None,
                "solve": 25.807104e6 + 0.080896e6,      # lu_solve_kernel, 700 x 700, 1600 right-hand sides
-               "wrap_gemm": 30.75968e6 + 0.013312e6,   # tc_gemm_kernel<160, split3>, 1600^3, both spins
+               "wrap_gemm": 30.749184e6 + 0.02432e6,   # tc_gemm_kernel<160, split3>, 1600^3, both spins
                "flush_gemm": None}
 
 
@@ -594,7 +594,7 @@ def soc_leg(torch, stream, args, seed):
         peak = pk["bf16_tflops"] * TF32_OVER_BF16
         roofs.append({"kernel": "SOC wrap GEMM (realified complex, tc3)", "bound": "tensor", "achieved": ach,
                       "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                      "traffic": 31.890176e6 + 0.004608e6 if args.gemm == "tc3" else None,  # ncu, tc_gemm<144, split3>
+                      "traffic": 31.897344e6 + 0.003072e6 if args.gemm == "tc3" else None,  # ncu, tc_gemm<144, split3>
                       "launches": wg["intervals"],
                       "ms_per_launch": wg["ms"] / wg["intervals"], "work_per_launch": flop,
                       "peak_source": "TF32 = measured bf16 burst x 1.1/2.25 (of %s); three TF32 MMAs per product"
