@@ -44,12 +44,14 @@ constexpr int TC_BK16 = 64;  // the same row in bf16
 constexpr int TC_NT = 256;  // 8 warps: all split the stages; warps w and w + 4 share TMEM lane quarter w % 4 in the epilogue
 constexpr unsigned long long WAIT_NS = 2000000000ULL;
 
-template <int BN, bool SPLIT>
+// Digit-plane products (OZ) take three stages, so two CTAs (three at BN = 64) share an SM: their
+// K loops are bound by operand latency, not by the MMA rate.
+template <int BN, bool SPLIT, bool OZ = false>
 struct TcCfg {
     static constexpr int A_BYTES = TC_BM * TC_BK * 4;
     static constexpr int B_BYTES = BN * TC_BK * 4;
     static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (SPLIT ? 2 : 1);
-    static constexpr int STAGES = SPLIT ? 3 : 4;
+    static constexpr int STAGES = (SPLIT || OZ) ? 3 : 4;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
 };
 
@@ -192,7 +194,7 @@ template <int BN, bool SPLIT, bool OZ>
 __global__ void __launch_bounds__(TC_NT, 1) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                          const __grid_constant__ CUtensorMap tmB, TcArgs a) {
     static_assert(!(SPLIT && OZ), "digit-plane products are single TF32 passes");
-    using Cfg = TcCfg<BN, SPLIT>;
+    using Cfg = TcCfg<BN, SPLIT, OZ>;
     constexpr int S = Cfg::STAGES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -534,7 +536,7 @@ cudaError_t tc_launch(cudaStream_t st, const TcGemmArgs& g) {
 
 template <int BN>
 cudaError_t tc_oz_launch(cudaStream_t st, const TcOzArgs& g) {
-    using Cfg = TcCfg<BN, false>;
+    using Cfg = TcCfg<BN, false, true>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e =
@@ -595,17 +597,42 @@ static int pick_bn(const TcGemmArgs& g) {
     return best;
 }
 
+// Tile width of a digit-plane product: the BN in {64, 128, 144, 160} that minimises (tiles per
+// SM, rounded up) x (128 + BN), the operand bytes an SM streams per K step -- the launches are
+// bound by operand traffic.  Small products (U_L U_R: 700 x 700 x 2) take 64 and spread over
+// every SM; U_R Z (1600 x 1600 x 2) keeps 160 (260 tiles, all resident at two per SM).
+static int pick_bn_oz(const TcOzArgs& g) {
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 148;
+    }
+    const long mt = (g.M + TC_BM - 1) / TC_BM;
+    int best = 160;
+    long best_cost = -1;
+    for (int bn : {160, 144, 128, 64}) {
+        const long tiles = mt * ((g.N + bn - 1) / bn) * g.batch;
+        const long cost = ((tiles + nsm - 1) / nsm) * (TC_BM + bn);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = bn;
+        }
+    }
+    return best;
+}
+
 cudaError_t tc_gemm_oz(cudaStream_t st, const TcOzArgs& g) {
     if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.batch <= 0) return cudaSuccess;
     if (g.np < 1 || g.np > TC_OZ_MAXP || g.K > g.Kp || (g.Kp & 7)) return cudaErrorInvalidValue;
     for (int i = 0; i < g.np; ++i)
         if (g.pa[i] < 0 || g.pa[i] >= g.ns || g.pb[i] < 0 || g.pb[i] >= g.ns) return cudaErrorInvalidValue;
-    TcGemmArgs shape;
-    shape.M = g.M; shape.N = g.N; shape.batch = g.batch;
-    const int bn = pick_bn(shape);
+    const int bn = pick_bn_oz(g);
     if (bn == 160) return tc_oz_launch<160>(st, g);
     if (bn == 144) return tc_oz_launch<144>(st, g);
-    return tc_oz_launch<128>(st, g);
+    if (bn == 128) return tc_oz_launch<128>(st, g);
+    return tc_oz_launch<64>(st, g);
 }
 
 cudaError_t tc_gemm(cudaStream_t st, const TcGemmArgs& g) {
