@@ -59,6 +59,16 @@ def test_create_rejects_bad_arguments_before_touching_the_device():
     assert lib.afqmc_destroy(None) == 0
 
 
+def test_dgemm_hook_rejects_bad_arguments_before_touching_the_device():
+    lib = afqmc.load()
+    p = ctypes.c_void_p(16)  # never dereferenced: the checks come first
+    assert lib.afqmc_debug_dgemm(2, 4, 4, 4, p, 4, p, 4, p, 4, None) == -1   # unknown engine
+    assert lib.afqmc_debug_dgemm(1, 0, 4, 4, p, 4, p, 4, p, 4, None) == -1   # empty M
+    assert lib.afqmc_debug_dgemm(1, 4, 4, 8, p, 4, p, 4, p, 4, None) == -1   # lda < K
+    assert lib.afqmc_debug_dgemm(0, 4, 8, 4, p, 4, p, 4, p, 8, None) == -1   # ldb < N
+    assert lib.afqmc_debug_dgemm(1, 4, 4, 4, None, 4, p, 4, p, 4, None) == -1  # null operand
+
+
 def test_soc_create_rejects_bad_arguments_before_touching_the_device():
     lib = soc.load()
     h = ctypes.c_void_p()
