@@ -175,6 +175,15 @@ def soc_oracle_sample():
     return 4 * Ns / secs, cores, secs
 
 
+def arm_config(k):
+    """The workload both arms report (the reference arm times a bounded sample of it)."""
+    return {"workload": f"{L}x{L} standard Hubbard, U/t={U}, n={FILLING} ({NS} per spin), "
+                        f"dtau={DTAU}, M={M}, FP32 bulk G, delayed k={k}, FP64 recompute "
+                        f"every {STAB} slices",
+            "step": "one full sweep (2M = 160 slice-steps: wrap + delayed update) + 16 FP64 recomputes",
+            "walkers_per_gpu": 1, "l2": "flushed between timed steps (256 MB write)"}
+
+
 def reference_arm(args, rank):
     if rank != 0:
         return
@@ -183,10 +192,10 @@ def reference_arm(args, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{L}x{L} Hubbard U={U} n={FILLING} dtau={DTAU}, delayed k={args.k}",
-                   "step": "one slice-step (wrap + delayed update of 1600 sites) of the FP64 oracle"},
+        "config": arm_config(args.k),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} slice-steps at 40x40 after {args.warmup} warm-up slice-steps; "
+                         "sample": f"each step one slice-step (wrap + delayed update of the {N} sites) of the "
+                                   f"FP64 oracle: {args.steps} timed after {args.warmup} warm-up slice-steps; "
                                    f"G(0) from the oracle's own FP64 init with M=10 (not timed)"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -341,11 +350,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{L}x{L} standard Hubbard, U/t={U}, n={FILLING} ({NS} per spin), "
-                                   f"dtau={DTAU}, M={M}, FP32 bulk G, delayed k={args.k}, FP64 recompute "
-                                   f"every {STAB} slices",
-                       "step": "one full sweep (2M = 160 slice-steps: wrap + delayed update) + 16 FP64 recomputes",
-                       "walkers_per_gpu": 1, "l2": "flushed between timed steps (256 MB write)"},
+            "config": arm_config(args.k),
             "update_only": {"value": update_only, "unit": UNIT,
                             "note": "prep + the window loop (decisions; the rank-m flushes overlap on a second "
                                     "stream): the paper's update time"},
