@@ -20,6 +20,11 @@ Parity status of each function (what pins it in ``tests/test_oracle_pins.py``):
   blockfb_slice   -- brute-force stripped force bias, det ratio, exact detailed
                      balance on an enumerable toy, from-scratch G
   energy          -- U=0 closed form; Fock-space brute force on <= 3 sites
+  tform_wrap      -- U_L U_R unchanged; 1 - U_R T U_L equals the wrapped G
+  tform_delayed_slice
+                  -- the paper's T-form delayed update (Sec. III.A): identical decisions and
+                     ratios to the G-form oracle and the same G = 1 - U_R T U_L after every
+                     slice; T stays (U_L U_R)^{-1} of the updated factors
 
 Spin-orbit-coupled model (``soc_oracle.c``, Appendix A), pinned in
 ``tests/test_soc_oracle_pins.py``:
@@ -104,6 +109,9 @@ def _load():
         lib.or_block_force_bias.argtypes = [pp, dp, i8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
         lib.or_blockfb_slice.argtypes = [pp, dp, dp, i8p, dp, dp, ctypes.c_int, u8p, i8p, dp, u8p, dp, dp]
         lib.or_energy.argtypes = [pp, dp, dp, dp]
+        lib.or_tform_wrap.argtypes = [pp, dp, dp, i8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.or_tform_delayed_slice.argtypes = [pp, dp, dp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int, i8p, dp,
+                                               ctypes.c_int, ctypes.c_int, u8p, u8p, dp, dp, ctypes.POINTER(ctypes.c_int)]
         lib.or_energy.restype = ctypes.c_double
         sp = ctypes.POINTER(SocParams)
         vp = ctypes.c_void_p
@@ -248,6 +256,34 @@ class Model:
         """Mixed-estimator energy from G by Wick's theorem (Eqs. 2DHubbard, Oxformula)."""
         return _load().or_energy(ctypes.byref(self.p), _d(self.K), _d(_f64(Gu)), _d(_f64(Gd)))
 
+    def tform_wrap(self, UR, UL, xl, spin, direction):
+        """T-form wrap (Sec. II.C): forward U_R <- B_l U_R, U_L <- U_L B_l^{-1}; backward the inverse
+        moves.  T = (U_L U_R)^{-1} is unchanged.  Returns (U_R, U_L)."""
+        UR, UL = _f64(UR).copy(), _f64(UL).copy()
+        xl = np.ascontiguousarray(xl, dtype=np.int8)
+        _load().or_tform_wrap(ctypes.byref(self.p), _d(self.E), _d(self.Einv), _i8(xl), spin, direction,
+                              UR.shape[1], _d(UR), _d(UL))
+        return UR, UL
+
+    def tform_delayed_slice(self, UR, UL, T, xl, u, k, strategy=1, replay=None):
+        """T-form delayed update of one slice (Eqs. DelayRatio, DelayRgenk, UpdateLTRMat, FinalDelay).
+        UR, UL, T: per-spin pairs.  Returns (UR pair, T pair, xl, dec, ratio, sign, flushes)."""
+        N = self.N
+        URu, URd = _f64(UR[0]).copy(), _f64(UR[1]).copy()
+        Tu, Td = _f64(T[0]).copy(), _f64(T[1]).copy()
+        ULu, ULd = _f64(UL[0]), _f64(UL[1])
+        xl = np.ascontiguousarray(xl, dtype=np.int8).copy()
+        u = _f64(u)
+        rep = None if replay is None else np.ascontiguousarray(replay, dtype=np.uint8)
+        dec = np.zeros(N, np.uint8)
+        ratio = np.zeros(N)
+        sg = np.ones(1)
+        nfl = ctypes.c_int(0)
+        _load().or_tform_delayed_slice(ctypes.byref(self.p), _d(URu), _d(URd), _d(ULu), _d(ULd), _d(Tu), _d(Td),
+                                       URu.shape[1], URd.shape[1], _i8(xl), _d(u), int(k), int(strategy), _u8(rep),
+                                       _u8(dec), _d(ratio), _d(sg), ctypes.byref(nfl))
+        return (URu, URd), (Tu, Td), xl, dec, ratio, sg[0], nfl.value
+
 
 class Walker:
     """One Markov chain driven by the oracle: fields X (M x N), G per spin, sweep position.
@@ -307,6 +343,57 @@ class Walker:
             self.G = [m.wrap(self.G[s], xn, s, -1) for s in range(2)]
             self.pos = ell - 1
         return dec, ratio, extra
+
+
+class TWalker:
+    """The paper's own walker (Sec. II.C): per spin U_R, U_L and T = (U_L U_R)^{-1}; G = 1 - U_R T U_L
+    (Eq. GrFMatNew) is formed only on request.  The same sweep order as Walker; delayed updates only
+    (k = 1 is the local update, Eq. UpdateLTRlocal).  T comes from the oracle's own stabilised
+    factors at every recompute."""
+
+    def __init__(self, model: Model, P_up, P_dn, x, stab=10):
+        self.m = model
+        self.P = (_f64(P_up), _f64(P_dn))
+        self.x = np.ascontiguousarray(x, dtype=np.int8).copy()
+        self.pos = 0
+        self.UR = [None, None]
+        self.UL = [None, None]
+        self.T = [None, None]
+        self.sign = 1.0
+        self.recompute(stab)
+
+    def recompute(self, stab=10):
+        sg = 1
+        for s in range(2):
+            _, s_, _, UR, UL = self.m.green_scratch(self.x, self.P[s], s, self.pos, stab, want_factors=True)
+            self.UR[s], self.UL[s] = UR, UL
+            self.T[s] = np.linalg.inv(UL @ UR)
+            sg *= s_
+        self.sign = float(sg)
+
+    def G(self, s):
+        return np.eye(self.m.N) - self.UR[s] @ self.T[s] @ self.UL[s]
+
+    def sweep_slice(self, ell, direction, u, k=32, strategy=1, replay=None):
+        m, N = self.m, self.m.N
+        xl = self.x[ell - 1]
+        if direction > 0:
+            assert self.pos == ell - 1
+            for s in range(2):
+                self.UR[s], self.UL[s] = m.tform_wrap(self.UR[s], self.UL[s], xl, s, +1)
+            self.pos = ell
+        else:
+            assert self.pos == ell
+        UR, T, xn, dec, ratio, sg, nfl = m.tform_delayed_slice(self.UR, self.UL, self.T, xl, u[:N], k, strategy,
+                                                               replay)
+        self.UR, self.T = list(UR), list(T)
+        self.x[ell - 1] = xn
+        self.sign *= sg
+        if direction < 0:
+            for s in range(2):
+                self.UR[s], self.UL[s] = m.tform_wrap(self.UR[s], self.UL[s], xn, s, -1)
+            self.pos = ell - 1
+        return dec, ratio, {"flushes": nfl}
 
 
 def _c128(a):

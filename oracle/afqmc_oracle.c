@@ -524,6 +524,179 @@ void or_delayed_slice(const or_params* p, double* G0, double* G1, int8_t* xl, co
 }
 
 /* ------------------------------------------------------------------ */
+/* T form  (Sec. II.C, Eq. GrFMatNew; Sec. II.D, Eqs. DetRatio10,      */
+/* UpdateLTRMat; Sec. III.A, Eqs. DelayTMat00, DelayRatio, DelayRgenk, */
+/* FinalDelay): the paper's own walker state                           */
+/* ------------------------------------------------------------------ */
+
+/* Per spin the walker is U_R (N x ns), U_L (ns x N) and T = (U_L U_R)^{-1} (ns x ns), with
+ * G = 1 - U_R T U_L (Eq. GrFMatNew) never formed.  Between slices the factors move and T stays:
+ *   forward  (l-1 -> l): U_R <- B_l U_R = D E U_R,           U_L <- U_L B_l^{-1} = U_L Einv D^{-1};
+ *   backward (l -> l-1): U_R <- B_l^{-1} U_R = Einv D^{-1} U_R, U_L <- U_L B_l = U_L D E;
+ * U_L U_R is unchanged by either. */
+void or_tform_wrap(const or_params* p, const double* E, const double* Einv, const int8_t* xl, int s, int dir,
+                   int ns, double* UR, double* UL) {
+    int N = p->N;
+    size_t nn = (size_t)N * ns;
+    double* d = (double*)malloc(sizeof(double) * (size_t)N + 1);
+    double* tmp = (double*)malloc(sizeof(double) * nn + 1);
+    for (int i = 0; i < N; i++) d[i] = exp(p->c[s] * xl[i]);
+    const double* ER = (dir > 0) ? E : Einv;  /* left factor of U_R */
+    const double* EL = (dir > 0) ? Einv : E;  /* right factor of U_L */
+    /* U_R: forward D (E U_R); backward Einv (D^{-1} U_R) */
+    if (dir < 0)
+        for (int i = 0; i < N; i++)
+            for (int c = 0; c < ns; c++) UR[(size_t)i * ns + c] /= d[i];
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < N; i++) {
+        double* t = tmp + (size_t)i * ns;
+        for (int c = 0; c < ns; c++) t[c] = 0.0;
+        for (int k = 0; k < N; k++) {
+            double e = ER[(size_t)i * N + k];
+            for (int c = 0; c < ns; c++) t[c] += e * UR[(size_t)k * ns + c];
+        }
+    }
+    for (int i = 0; i < N; i++)
+        for (int c = 0; c < ns; c++) UR[(size_t)i * ns + c] = (dir > 0 ? d[i] : 1.0) * tmp[(size_t)i * ns + c];
+    /* U_L: forward (U_L Einv) D^{-1}; backward (U_L D) E */
+    if (dir < 0)
+        for (int r = 0; r < ns; r++)
+            for (int k = 0; k < N; k++) UL[(size_t)r * N + k] *= d[k];
+#pragma omp parallel for schedule(static)
+    for (int r = 0; r < ns; r++) {
+        double* t = tmp + (size_t)r * N;
+        for (int j = 0; j < N; j++) t[j] = 0.0;
+        for (int k = 0; k < N; k++) {
+            double a = UL[(size_t)r * N + k];
+            for (int j = 0; j < N; j++) t[j] += a * EL[(size_t)k * N + j];
+        }
+    }
+    for (int r = 0; r < ns; r++)
+        for (int j = 0; j < N; j++) UL[(size_t)r * N + j] = tmp[(size_t)r * N + j] / (dir > 0 ? d[j] : 1.0);
+    free(d);
+    free(tmp);
+}
+
+/* Delayed update of one slice in the T form.  At a proposed site i, per spin s with
+ * Delta = e^{c_s (x' - x)} - 1 the only non-zero element of the Delta matrix of Eq. DetRatio10,
+ * u = U_R[i, :] (the row as it is now) and v = Delta U_L[:, i]:
+ *   r   = 1 + u T_[0] v - sum_{m<k} (u x_m)(y_m v)                          (Eq. DelayRatio)
+ * and, if the move is the k-th acceptance,
+ *   x_k = (T_[0] v - sum_{m<k} x_m (y_m v)) / r,
+ *   y_k = u T_[0] - sum_{m<k} (u x_m) y_m                                    (Eq. DelayRgenk)
+ *   U_R[i, :] <- (1 + Delta) U_R[i, :]                                       (Eq. UpdateLTRMat)
+ * T_[0] <- T_[0] - X Y (Eq. FinalDelay) after every k proposed sites (strategy 1, the paper's
+ * choice) or every k acceptances (strategy 2), and at the end of the slice.  Decisions and the
+ * weight ratio R = (P-ratio) r_up r_dn follow or_local_slice. */
+void or_tform_delayed_slice(const or_params* p, double* UR0, double* UR1, const double* UL0, const double* UL1,
+                            double* T0, double* T1, int ns0, int ns1, int8_t* xl, const double* u, int k,
+                            int strategy, const uint8_t* replay, uint8_t* dec, double* ratio, double* sign,
+                            int* nflush) {
+    int N = p->N;
+    double* UR[2] = {UR0, UR1};
+    const double* UL[2] = {UL0, UL1};
+    double* T[2] = {T0, T1};
+    int ns[2] = {ns0, ns1};
+    if (k < 1) k = 1;
+    double *X[2], *Y[2], *v[2], *Tv[2], *uT[2], *cm[2], *dm[2];
+    for (int s = 0; s < 2; s++) {
+        int n = ns[s];
+        X[s] = (double*)calloc((size_t)n * k + 1, sizeof(double));  /* X[a*k + m] = x_m[a] */
+        Y[s] = (double*)calloc((size_t)k * n + 1, sizeof(double));  /* Y[m*n + b] = y_m[b] */
+        v[s] = (double*)malloc(sizeof(double) * (size_t)n + 1);
+        Tv[s] = (double*)malloc(sizeof(double) * (size_t)n + 1);
+        uT[s] = (double*)malloc(sizeof(double) * (size_t)n + 1);
+        cm[s] = (double*)malloc(sizeof(double) * (size_t)k + 1);
+        dm[s] = (double*)malloc(sizeof(double) * (size_t)k + 1);
+    }
+    int m = 0, ntry = 0, flushes = 0;
+    for (int i = 0; i <= N; i++) {
+        int want_flush = (i == N) ? (m > 0) : 0;
+        if (i < N) {
+            int x = xl[i], xp = -x;
+            double R = exp(hs_log_scalar(p, xp) - hs_log_scalar(p, x));
+            double d[2], r[2];
+            for (int s = 0; s < 2; s++) {
+                int n = ns[s];
+                const double* us = UR[s] + (size_t)i * n;
+                const double* t = T[s];
+                d[s] = field_delta(p, s, x, xp);
+                for (int a = 0; a < n; a++) v[s][a] = d[s] * UL[s][(size_t)a * N + i];
+                for (int a = 0; a < n; a++) {
+                    double acc = 0.0;
+                    for (int b = 0; b < n; b++) acc += t[(size_t)a * n + b] * v[s][b];
+                    Tv[s][a] = acc;
+                }
+                for (int b = 0; b < n; b++) {
+                    double acc = 0.0;
+                    for (int a = 0; a < n; a++) acc += us[a] * t[(size_t)a * n + b];
+                    uT[s][b] = acc;
+                }
+                double uTv = 0.0;
+                for (int a = 0; a < n; a++) uTv += us[a] * Tv[s][a];
+                double corr = 0.0;
+                for (int q = 0; q < m; q++) {
+                    double c = 0.0, e = 0.0;
+                    for (int a = 0; a < n; a++) c += us[a] * X[s][(size_t)a * k + q];
+                    for (int b = 0; b < n; b++) e += Y[s][(size_t)q * n + b] * v[s][b];
+                    cm[s][q] = c;
+                    dm[s][q] = e;
+                    corr += c * e;
+                }
+                r[s] = 1.0 + uTv - corr;
+                R *= r[s];
+            }
+            int acc = replay ? (replay[i] != 0) : (u[i] < fabs(R));
+            dec[i] = (uint8_t)acc;
+            ratio[i] = R;
+            ntry++;
+            if (acc) {
+                for (int s = 0; s < 2; s++) {
+                    int n = ns[s];
+                    double* us = UR[s] + (size_t)i * n;
+                    for (int a = 0; a < n; a++) {
+                        double xa = Tv[s][a];
+                        for (int q = 0; q < m; q++) xa -= X[s][(size_t)a * k + q] * dm[s][q];
+                        X[s][(size_t)a * k + m] = xa / r[s];
+                    }
+                    for (int b = 0; b < n; b++) {
+                        double yb = uT[s][b];
+                        for (int q = 0; q < m; q++) yb -= cm[s][q] * Y[s][(size_t)q * n + b];
+                        Y[s][(size_t)m * n + b] = yb;
+                    }
+                    for (int a = 0; a < n; a++) us[a] *= 1.0 + d[s];
+                }
+                m++;
+                xl[i] = (int8_t)xp;
+                if (R < 0) *sign = -*sign;
+            }
+            if (strategy == 2 && m == k) want_flush = 1;
+            if (strategy == 1 && ntry == k && m > 0) want_flush = 1;
+            if (strategy == 1 && ntry == k) ntry = 0;
+        }
+        if (want_flush) {
+            for (int s = 0; s < 2; s++) {
+                int n = ns[s];
+                double* t = T[s];
+#pragma omp parallel for schedule(static)
+                for (int a = 0; a < n; a++)
+                    for (int b = 0; b < n; b++) {
+                        double acc2 = 0.0;
+                        for (int q = 0; q < m; q++) acc2 += X[s][(size_t)a * k + q] * Y[s][(size_t)q * n + b];
+                        t[(size_t)a * n + b] -= acc2;
+                    }
+            }
+            m = 0;
+            flushes++;
+        }
+    }
+    if (nflush) *nflush = flushes;
+    for (int s = 0; s < 2; s++) {
+        free(X[s]); free(Y[s]); free(v[s]); free(Tv[s]); free(uT[s]); free(cm[s]); free(dm[s]);
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* Block force-bias update  (Sec. III.B, Eqs. BlockFrcbsPhiLPhiR,      */
 /* BlockFrcbsRatio, BlkFrcBsErr, BlkFrcBsTnew1, BlkFrcBsTnew2)          */
 /* ------------------------------------------------------------------ */

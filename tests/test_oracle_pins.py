@@ -303,3 +303,79 @@ def test_energy_matches_fock_space(U):
     Gd = np.eye(3) - Rd @ np.linalg.solve(Ld @ Rd, Ld)
     e_fock = bf.fock_energy(m.K, U, Ru, Lu, Rd, Ld)
     assert abs(m.energy(Gu, Gd) - e_fock) < 1e-10
+
+
+# ---------------------------------------------------------------- T form (Sec. II.C, Sec. III.A)
+
+def test_tform_wrap_keeps_overlap_and_moves_G():
+    """Forward and backward T-form wraps leave U_L U_R (hence T) unchanged, and 1 - U_R T U_L of the
+    moved factors is the from-scratch G of the new slice (Eqs. BlMat, GrFMatNew)."""
+    m, P, X = _setup(3, 3, 4, 6)
+    ell = 2
+    for s in range(2):
+        _, _, _, UR, UL = m.green_scratch(X, P, s, ell, stab=2, want_factors=True)
+        T = np.linalg.inv(UL @ UR)
+        for direction, xl, target in ((+1, X[ell], ell + 1), (-1, X[ell - 1], ell - 1)):
+            URw, ULw = m.tform_wrap(UR, UL, xl, s, direction)
+            np.testing.assert_allclose(ULw @ URw, UL @ UR, atol=1e-12)
+            G = np.eye(m.N) - URw @ T @ ULw
+            np.testing.assert_allclose(G, bf.green(m.E, m.c[s], X, P, target), atol=1e-11)
+
+
+def test_tform_local_ratio_is_bruteforce_weight_ratio():
+    """k = 1 T-form steps (Eqs. DetRatiolocal, UpdateLTRlocal): every r_up r_dn equals the brute-force
+    weight ratio of the flip, with forced acceptances changing U_R and T along the way; T stays the
+    inverse overlap and 1 - U_R T U_L the from-scratch G."""
+    m, P, X = _setup(3, 2, 2, 6)
+    ell = 3
+    UR, UL, T = [], [], []
+    for s in range(2):
+        _, _, _, ur, ul = m.green_scratch(X, P, s, ell, stab=2, want_factors=True)
+        UR.append(ur)
+        UL.append(ul)
+        T.append(np.linalg.inv(ul @ ur))
+    W0 = bf.weight(m.E, m.c, X, P, P)
+    forced = np.zeros(m.N, np.uint8)
+    forced[[0, 3, 4]] = 1
+    URn, Tn, xl, dec, ratio, sg, nfl = m.tform_delayed_slice(UR, UL, T, X[ell - 1], np.zeros(m.N), 1, 1,
+                                                             replay=forced)
+    Xc, Wc = X.copy(), W0
+    for i in range(m.N):
+        Xf = Xc.copy()
+        Xf[ell - 1, i] *= -1
+        Wf = bf.weight(m.E, m.c, Xf, P, P)
+        assert abs(ratio[i] - Wf / Wc) < 1e-10 * max(1, abs(Wf / Wc))
+        if forced[i]:
+            Xc, Wc = Xf, Wf
+    np.testing.assert_array_equal(xl, Xc[ell - 1])
+    assert sg == np.sign(Wc / W0)
+    for s in range(2):
+        np.testing.assert_allclose(Tn[s], np.linalg.inv(UL[s] @ URn[s]), atol=1e-10)
+        np.testing.assert_allclose(np.eye(m.N) - URn[s] @ Tn[s] @ UL[s], bf.green(m.E, m.c[s], Xc, P, ell),
+                                   atol=1e-11)
+
+
+@pytest.mark.parametrize("k,strategy", [(1, 1), (5, 1), (16, 1), (3, 2), (8, 2)])
+def test_tform_delayed_equals_gform(k, strategy):
+    """The paper's T-form delayed update and the G-form oracle, driven by the same uniforms over a
+    forward and part of a backward sweep with FP64 recomputes: identical decisions, fields and sign,
+    ratios to 1e-12, G = 1 - U_R T U_L to 1e-11, and T = (U_L U_R)^{-1} after every slice."""
+    Lx, Ly, ns, M, stab = 4, 4, 7, 6, 3
+    m, P, X = _setup(Lx, Ly, ns, M, dtau=0.05)
+    w = oracle.Walker(m, P, P, X)
+    tw = oracle.TWalker(m, P, P, X, stab=stab)
+    order = [(ell, +1) for ell in range(1, M + 1)] + [(ell, -1) for ell in range(M, M - 3, -1)]
+    for visit, (ell, d) in enumerate(order):
+        u = inputs.uniforms(7, 0, visit, 2 * m.N)
+        d1, r1, _ = w.sweep_slice(ell, d, "delayed", u, k=k, strategy=strategy)
+        d2, r2, _ = tw.sweep_slice(ell, d, u, k=k, strategy=strategy)
+        np.testing.assert_array_equal(d1, d2)
+        np.testing.assert_allclose(r2, r1, rtol=1e-12, atol=1e-14)
+        np.testing.assert_array_equal(tw.x, w.x)
+        assert tw.sign == w.sign
+        for s in range(2):
+            np.testing.assert_allclose(tw.G(s), w.G[s], atol=1e-11)
+            np.testing.assert_allclose(tw.T[s], np.linalg.inv(tw.UL[s] @ tw.UR[s]), atol=1e-10)
+        if w.pos % stab == 0:
+            w.recompute(stab)
+            tw.recompute(stab)
