@@ -25,6 +25,9 @@ Parity status of each function (what pins it in ``tests/test_oracle_pins.py``):
                   -- the paper's T-form delayed update (Sec. III.A): identical decisions and
                      ratios to the G-form oracle and the same G = 1 - U_R T U_L after every
                      slice; T stays (U_L U_R)^{-1} of the updated factors
+  tform_blockfb_slice
+                  -- the T-form block force bias (Sec. III.B): the same stripped densities,
+                     proposals, decisions and ratios as the G-form oracle; the same G
 
 Spin-orbit-coupled model (``soc_oracle.c``, Appendix A), pinned in
 ``tests/test_soc_oracle_pins.py``:
@@ -112,6 +115,8 @@ def _load():
         lib.or_tform_wrap.argtypes = [pp, dp, dp, i8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
         lib.or_tform_delayed_slice.argtypes = [pp, dp, dp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int, i8p, dp,
                                                ctypes.c_int, ctypes.c_int, u8p, u8p, dp, dp, ctypes.POINTER(ctypes.c_int)]
+        lib.or_tform_blockfb_slice.argtypes = [pp, dp, dp, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int, i8p, dp, dp,
+                                               ctypes.c_int, u8p, i8p, dp, u8p, dp, dp]
         lib.or_energy.restype = ctypes.c_double
         sp = ctypes.POINTER(SocParams)
         vp = ctypes.c_void_p
@@ -284,6 +289,26 @@ class Model:
                                        _u8(dec), _d(ratio), _d(sg), ctypes.byref(nfl))
         return (URu, URd), (Tu, Td), xl, dec, ratio, sg[0], nfl.value
 
+    def tform_blockfb_slice(self, UR, UL, T, xl, u_prop, u_acc, nb, replay=None):
+        """T-form block force-bias update of one slice (Eqs. BlkFrcBsTnew1, DetRatio10, BlkFrcBsTnew2).
+        Returns (UR pair, T pair, xl, xprop, lam_plus, dec[nblocks], ratio[nblocks], sign)."""
+        N = self.N
+        nblocks = (N + nb - 1) // nb
+        URu, URd = _f64(UR[0]).copy(), _f64(UR[1]).copy()
+        Tu, Td = _f64(T[0]).copy(), _f64(T[1]).copy()
+        ULu, ULd = _f64(UL[0]), _f64(UL[1])
+        xl = np.ascontiguousarray(xl, dtype=np.int8).copy()
+        rep = None if replay is None else np.ascontiguousarray(replay, dtype=np.uint8)
+        xprop = np.zeros(N, np.int8)
+        lamp = np.zeros(N)
+        dec = np.zeros(nblocks, np.uint8)
+        ratio = np.zeros(nblocks)
+        sg = np.ones(1)
+        _load().or_tform_blockfb_slice(ctypes.byref(self.p), _d(URu), _d(URd), _d(ULu), _d(ULd), _d(Tu), _d(Td),
+                                       URu.shape[1], URd.shape[1], _i8(xl), _d(_f64(u_prop)), _d(_f64(u_acc)),
+                                       int(nb), _u8(rep), _i8(xprop), _d(lamp), _u8(dec), _d(ratio), _d(sg))
+        return (URu, URd), (Tu, Td), xl, xprop, lamp, dec, ratio, sg[0]
+
 
 class Walker:
     """One Markov chain driven by the oracle: fields X (M x N), G per spin, sweep position.
@@ -347,9 +372,9 @@ class Walker:
 
 class TWalker:
     """The paper's own walker (Sec. II.C): per spin U_R, U_L and T = (U_L U_R)^{-1}; G = 1 - U_R T U_L
-    (Eq. GrFMatNew) is formed only on request.  The same sweep order as Walker; delayed updates only
-    (k = 1 is the local update, Eq. UpdateLTRlocal).  T comes from the oracle's own stabilised
-    factors at every recompute."""
+    (Eq. GrFMatNew) is formed only on request.  The same sweep order as Walker; delayed (k = 1 is
+    the local update, Eq. UpdateLTRlocal) and block force-bias updates.  T comes from the oracle's
+    own stabilised factors at every recompute."""
 
     def __init__(self, model: Model, P_up, P_dn, x, stab=10):
         self.m = model
@@ -374,7 +399,8 @@ class TWalker:
     def G(self, s):
         return np.eye(self.m.N) - self.UR[s] @ self.T[s] @ self.UL[s]
 
-    def sweep_slice(self, ell, direction, u, k=32, strategy=1, replay=None):
+    def sweep_slice(self, ell, direction, mode, u, k=32, nb=4, strategy=1, replay=None, u_acc=None):
+        """mode "delayed" (k = 1: the local update) or "blockfb"; uniforms as Walker.sweep_slice."""
         m, N = self.m, self.m.N
         xl = self.x[ell - 1]
         if direction > 0:
@@ -384,8 +410,18 @@ class TWalker:
             self.pos = ell
         else:
             assert self.pos == ell
-        UR, T, xn, dec, ratio, sg, nfl = m.tform_delayed_slice(self.UR, self.UL, self.T, xl, u[:N], k, strategy,
-                                                               replay)
+        if mode == "delayed":
+            UR, T, xn, dec, ratio, sg, nfl = m.tform_delayed_slice(self.UR, self.UL, self.T, xl, u[:N], k, strategy,
+                                                                   replay)
+            extra = {"flushes": nfl}
+        elif mode == "blockfb":
+            nblocks = (N + nb - 1) // nb
+            ua = u[N:N + nblocks] if u_acc is None else u_acc
+            UR, T, xn, xprop, lamp, dec, ratio, sg = m.tform_blockfb_slice(self.UR, self.UL, self.T, xl, u[:N], ua,
+                                                                           nb, replay)
+            extra = {"xprop": xprop, "lam_plus": lamp}
+        else:
+            raise ValueError(mode)
         self.UR, self.T = list(UR), list(T)
         self.x[ell - 1] = xn
         self.sign *= sg
@@ -393,7 +429,7 @@ class TWalker:
             for s in range(2):
                 self.UR[s], self.UL[s] = m.tform_wrap(self.UR[s], self.UL[s], xn, s, -1)
             self.pos = ell - 1
-        return dec, ratio, {"flushes": nfl}
+        return dec, ratio, extra
 
 
 def _c128(a):

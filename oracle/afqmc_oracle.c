@@ -696,6 +696,173 @@ void or_tform_delayed_slice(const or_params* p, double* UR0, double* UR1, const 
     }
 }
 
+/* Block force-bias pass over one slice in the T form (Sec. III.B), with the conventions of
+ * or_blockfb_slice (blocks, uniforms, replay layout, proposal and acceptance).  Per block S and
+ * spin s, with u_i = U_R[i, :] and v_i = d_i U_L[:, i]:
+ *   stripped:  Db_ii = e^{-c_s x_i} - 1, U (rows u_i) and V (columns Db_ii U_L[:, i]), i in S,
+ *              Ttil = T - (T V)[1 + (U T) V]^{-1}(U T)                    (Eq. BlkFrcBsTnew1)
+ *              nbar_i = (1 + Db_ii) u_i Ttil U_L[:, i]   (the diagonal of (1+Db) U_R Ttil U_L);
+ *   ratio:     r_s = det[1 + (U' T) V'] over the flipped sites F, V' columns
+ *              (e^{c_s (x' - x)} - 1) U_L[:, i]                           (Eq. DetRatio10)
+ *   accepted:  T <- T - (T V')[1 + (U' T) V']^{-1}(U' T)                  (Eq. BlkFrcBsTnew2)
+ *              U_R[i, :] <- (1 + Delta_i) U_R[i, :] for i in F             (Eq. UpdateLTRMat). */
+void or_tform_blockfb_slice(const or_params* p, double* UR0, double* UR1, const double* UL0, const double* UL1,
+                            double* T0, double* T1, int ns0, int ns1, int8_t* xl, const double* u_prop,
+                            const double* u_acc, int nb, const uint8_t* replay, int8_t* xprop, double* lam_plus,
+                            uint8_t* dec, double* ratio, double* sign) {
+    int N = p->N;
+    double* UR[2] = {UR0, UR1};
+    const double* UL[2] = {UL0, UL1};
+    double* T[2] = {T0, T1};
+    int ns[2] = {ns0, ns1};
+    if (nb < 1) nb = 1;
+    int nsx = ns0 > ns1 ? ns0 : ns1;
+    double* nbar[2];
+    nbar[0] = (double*)malloc(sizeof(double) * (size_t)nb + 1);
+    nbar[1] = (double*)malloc(sizeof(double) * (size_t)nb + 1);
+    int* F = (int*)malloc(sizeof(int) * (size_t)nb + 1);
+    int* piv = (int*)malloc(sizeof(int) * (size_t)nb + 1);
+    double* TV = (double*)malloc(sizeof(double) * (size_t)nsx * nb + 1);  /* ns x n   */
+    double* UT = (double*)malloc(sizeof(double) * (size_t)nb * nsx + 1);  /* n x ns   */
+    double* Mx = (double*)malloc(sizeof(double) * (size_t)nb * nb + 1);   /* n x n    */
+    double* Tt = (double*)malloc(sizeof(double) * (size_t)nsx * nsx + 1); /* ns x ns  */
+    double* dv = (double*)malloc(sizeof(double) * (size_t)nb + 1);
+    int nblocks = (N + nb - 1) / nb;
+    for (int bk = 0; bk < nblocks; bk++) {
+        int s0 = bk * nb, n = (s0 + nb <= N) ? nb : N - s0;
+        /* (a) stripped force bias */
+        for (int s = 0; s < 2; s++) {
+            int m = ns[s];
+            const double* t = T[s];
+            for (int a = 0; a < n; a++) dv[a] = exp(-p->c[s] * xl[s0 + a]) - 1.0;
+            for (int c = 0; c < m; c++)
+                for (int a = 0; a < n; a++) {
+                    double acc = 0.0;
+                    for (int e = 0; e < m; e++) acc += t[(size_t)c * m + e] * dv[a] * UL[s][(size_t)e * N + s0 + a];
+                    TV[(size_t)c * n + a] = acc;
+                }
+            for (int a = 0; a < n; a++)
+                for (int c = 0; c < m; c++) {
+                    double acc = 0.0;
+                    for (int e = 0; e < m; e++) acc += UR[s][(size_t)(s0 + a) * m + e] * t[(size_t)e * m + c];
+                    UT[(size_t)a * m + c] = acc;
+                }
+            for (int a = 0; a < n; a++)
+                for (int b = 0; b < n; b++) {
+                    double acc = (a == b ? 1.0 : 0.0);
+                    for (int c = 0; c < m; c++) acc += UT[(size_t)a * m + c] * dv[b] * UL[s][(size_t)c * N + s0 + b];
+                    Mx[(size_t)a * n + b] = acc;
+                }
+            double la;
+            lu_factor(Mx, n, piv, &la);
+            lu_solve(Mx, n, piv, UT, m); /* UT <- [1 + (U T) V]^{-1} (U T) */
+            for (int c = 0; c < m; c++)
+                for (int e = 0; e < m; e++) {
+                    double acc = t[(size_t)c * m + e];
+                    for (int a = 0; a < n; a++) acc -= TV[(size_t)c * n + a] * UT[(size_t)a * m + e];
+                    Tt[(size_t)c * m + e] = acc;
+                }
+            for (int a = 0; a < n; a++) {
+                int i = s0 + a;
+                double acc = 0.0;
+                for (int c = 0; c < m; c++) {
+                    double w = 0.0;
+                    for (int e = 0; e < m; e++) w += Tt[(size_t)c * m + e] * UL[s][(size_t)e * N + i];
+                    acc += UR[s][(size_t)i * m + c] * w;
+                }
+                nbar[s][a] = (1.0 + dv[a]) * acc;
+            }
+        }
+        /* (b) proposals, as or_blockfb_slice */
+        double logprior = 0.0;
+        int nF = 0;
+        for (int a = 0; a < n; a++) {
+            int i = s0 + a;
+            double h = p->c[0] * nbar[0][a] + p->c[1] * nbar[1][a];
+            double lp = hs_log_scalar(p, +1) + h, lm = hs_log_scalar(p, -1) - h;
+            double lamp = 1.0 / (1.0 + exp(lm - lp));
+            lam_plus[i] = lamp;
+            int xp = replay ? (replay[i] ? +1 : -1) : (u_prop[i] < lamp ? +1 : -1);
+            xprop[i] = (int8_t)xp;
+            if (xp != xl[i]) {
+                F[nF++] = i;
+                double lbx = hs_log_scalar(p, xl[i]) + xl[i] * h;
+                double lbxp = hs_log_scalar(p, xp) + xp * h;
+                logprior += (hs_log_scalar(p, xp) - hs_log_scalar(p, xl[i])) + (lbx - lbxp);
+            }
+        }
+        if (nF == 0) {
+            dec[bk] = 1;
+            ratio[bk] = 1.0;
+            continue;
+        }
+        /* (c) r_s = det[1 + (U' T) V'] over the flipped sites */
+        double R = exp(logprior);
+        for (int s = 0; s < 2; s++) {
+            int m = ns[s];
+            const double* t = T[s];
+            for (int a = 0; a < nF; a++) dv[a] = field_delta(p, s, xl[F[a]], -xl[F[a]]);
+            for (int a = 0; a < nF; a++)
+                for (int c = 0; c < m; c++) {
+                    double acc = 0.0;
+                    for (int e = 0; e < m; e++) acc += UR[s][(size_t)F[a] * m + e] * t[(size_t)e * m + c];
+                    UT[(size_t)a * m + c] = acc;
+                }
+            for (int a = 0; a < nF; a++)
+                for (int b = 0; b < nF; b++) {
+                    double acc = (a == b ? 1.0 : 0.0);
+                    for (int c = 0; c < m; c++) acc += UT[(size_t)a * m + c] * dv[b] * UL[s][(size_t)c * N + F[b]];
+                    Mx[(size_t)a * nF + b] = acc;
+                }
+            double la;
+            int sg = det_sign_log(Mx, nF, &la);
+            R *= sg * exp(la);
+        }
+        int acc = replay ? (replay[N + bk] != 0) : (u_acc[bk] < fabs(R));
+        dec[bk] = (uint8_t)acc;
+        ratio[bk] = R;
+        if (!acc) continue;
+        /* (d) T <- T - (T V')[1 + (U' T) V']^{-1}(U' T);  U_R rows of F scaled by 1 + Delta */
+        for (int s = 0; s < 2; s++) {
+            int m = ns[s];
+            double* t = T[s];
+            for (int a = 0; a < nF; a++) dv[a] = field_delta(p, s, xl[F[a]], -xl[F[a]]);
+            for (int c = 0; c < m; c++)
+                for (int a = 0; a < nF; a++) {
+                    double acc2 = 0.0;
+                    for (int e = 0; e < m; e++) acc2 += t[(size_t)c * m + e] * dv[a] * UL[s][(size_t)e * N + F[a]];
+                    TV[(size_t)c * nF + a] = acc2;
+                }
+            for (int a = 0; a < nF; a++)
+                for (int c = 0; c < m; c++) {
+                    double acc2 = 0.0;
+                    for (int e = 0; e < m; e++) acc2 += UR[s][(size_t)F[a] * m + e] * t[(size_t)e * m + c];
+                    UT[(size_t)a * m + c] = acc2;
+                }
+            for (int a = 0; a < nF; a++)
+                for (int b = 0; b < nF; b++) {
+                    double acc2 = (a == b ? 1.0 : 0.0);
+                    for (int c = 0; c < m; c++) acc2 += UT[(size_t)a * m + c] * dv[b] * UL[s][(size_t)c * N + F[b]];
+                    Mx[(size_t)a * nF + b] = acc2;
+                }
+            double la;
+            lu_factor(Mx, nF, piv, &la);
+            lu_solve(Mx, nF, piv, UT, m);
+            for (int c = 0; c < m; c++)
+                for (int e = 0; e < m; e++) {
+                    double acc2 = 0.0;
+                    for (int a = 0; a < nF; a++) acc2 += TV[(size_t)c * nF + a] * UT[(size_t)a * m + e];
+                    t[(size_t)c * m + e] -= acc2;
+                }
+            for (int a = 0; a < nF; a++)
+                for (int c = 0; c < m; c++) UR[s][(size_t)F[a] * m + c] *= 1.0 + dv[a];
+        }
+        for (int a = 0; a < nF; a++) xl[F[a]] = (int8_t)(-xl[F[a]]);
+        if (R < 0) *sign = -*sign;
+    }
+    free(nbar[0]); free(nbar[1]); free(F); free(piv); free(TV); free(UT); free(Mx); free(Tt); free(dv);
+}
+
 /* ------------------------------------------------------------------ */
 /* Block force-bias update  (Sec. III.B, Eqs. BlockFrcbsPhiLPhiR,      */
 /* BlockFrcbsRatio, BlkFrcBsErr, BlkFrcBsTnew1, BlkFrcBsTnew2)          */

@@ -368,7 +368,36 @@ def test_tform_delayed_equals_gform(k, strategy):
     for visit, (ell, d) in enumerate(order):
         u = inputs.uniforms(7, 0, visit, 2 * m.N)
         d1, r1, _ = w.sweep_slice(ell, d, "delayed", u, k=k, strategy=strategy)
-        d2, r2, _ = tw.sweep_slice(ell, d, u, k=k, strategy=strategy)
+        d2, r2, _ = tw.sweep_slice(ell, d, "delayed", u, k=k, strategy=strategy)
+        np.testing.assert_array_equal(d1, d2)
+        np.testing.assert_allclose(r2, r1, rtol=1e-12, atol=1e-14)
+        np.testing.assert_array_equal(tw.x, w.x)
+        assert tw.sign == w.sign
+        for s in range(2):
+            np.testing.assert_allclose(tw.G(s), w.G[s], atol=1e-11)
+            np.testing.assert_allclose(tw.T[s], np.linalg.inv(tw.UL[s] @ tw.UR[s]), atol=1e-10)
+        if w.pos % stab == 0:
+            w.recompute(stab)
+            tw.recompute(stab)
+
+
+@pytest.mark.parametrize("nb", [1, 4, 7, 16])
+def test_tform_blockfb_equals_gform(nb):
+    """The T-form block force bias (Eqs. BlkFrcBsTnew1, DetRatio10, BlkFrcBsTnew2) and the G-form oracle
+    on the same uniforms: the same stripped-bias proposal probabilities, proposals, decisions and
+    ratios, G = 1 - U_R T U_L to 1e-11 and T = (U_L U_R)^{-1} after every slice, over a forward and
+    part of a backward sweep with recomputes; nb = 7 leaves a ragged last block."""
+    Lx, Ly, ns, M, stab = 4, 4, 7, 6, 3
+    m, P, X = _setup(Lx, Ly, ns, M, dtau=0.05)
+    w = oracle.Walker(m, P, P, X)
+    tw = oracle.TWalker(m, P, P, X, stab=stab)
+    order = [(ell, +1) for ell in range(1, M + 1)] + [(ell, -1) for ell in range(M, M - 3, -1)]
+    for visit, (ell, d) in enumerate(order):
+        u = inputs.uniforms(11, 0, visit, 2 * m.N)
+        d1, r1, e1 = w.sweep_slice(ell, d, "blockfb", u, nb=nb)
+        d2, r2, e2 = tw.sweep_slice(ell, d, "blockfb", u, nb=nb)
+        np.testing.assert_allclose(e2["lam_plus"], e1["lam_plus"], rtol=1e-12, atol=1e-14)
+        np.testing.assert_array_equal(e2["xprop"], e1["xprop"])
         np.testing.assert_array_equal(d1, d2)
         np.testing.assert_allclose(r2, r1, rtol=1e-12, atol=1e-14)
         np.testing.assert_array_equal(tw.x, w.x)
