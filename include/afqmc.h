@@ -238,6 +238,16 @@ int afqmc_debug_gemm(int kind, int M, int N, int K, const float* A, long long ld
 int afqmc_debug_dgemm(int kind, int M, int N, int K, const double* A, long long lda, const double* B,
                       long long ldb, double* C, long long ldc, void* stream);
 
+/* The digit-split plan of afqmc_debug_dgemm kind 1 (and of the recompute) for an M x N x K
+ * product with `batch` entries; host only, no device use.  Writes the digit width *b (bits), the
+ * digits per element *s and the number of groups *ngroups (one tensor-core pass each); for the first
+ * `cap` groups, np[g] plane pairs with 1-based digit indices pa[16 g + i], pb[16 g + i] (host,
+ * caller-owned, 16 slots per group).  Every pair of a group has the same level p + q, and
+ * np[g] K (2^b - 1)^2 < 2^24 (the FP32 accumulator stays exact).  AFQMC_ERR_ARG for K beyond the
+ * exact range or bad pointers. */
+int afqmc_debug_ozaki_plan(int M, int N, int K, int batch, int* b, int* s, int* ngroups, int cap, int* np,
+                           int* pa, int* pb);
+
 const char* afqmc_strerror(int code);
 
 #ifdef __cplusplus

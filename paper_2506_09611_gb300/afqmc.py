@@ -27,7 +27,7 @@ EXPORTS = ["afqmc_create", "afqmc_destroy", "afqmc_init_walkers", "afqmc_sweep_s
            "afqmc_measure_energy", "afqmc_get_G", "afqmc_set_G", "afqmc_get_fields", "afqmc_get_decisions",
            "afqmc_get_ratios", "afqmc_get_info", "afqmc_debug_uniforms", "afqmc_set_profiling", "afqmc_set_graphs",
            "afqmc_get_profile", "afqmc_launch_count", "afqmc_apply_flips", "afqmc_apply_flips_noalloc",
-           "afqmc_debug_gemm", "afqmc_debug_dgemm", "afqmc_strerror"]
+           "afqmc_debug_gemm", "afqmc_debug_dgemm", "afqmc_debug_ozaki_plan", "afqmc_strerror"]
 PHASES = ["prep", "wrap", "local", "chain", "flush", "recompute", "elim", "wrap_gemm", "flush_gemm", "lu_o",
           "solve", "dgemm"]
 
@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH):
                                      ctypes.c_int, vp]
     lib.afqmc_debug_dgemm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ll, vp, ll, vp, ll,
                                       vp]
+    lib.afqmc_debug_ozaki_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip, ip,
+                                           ctypes.c_int, ip, ip, ip]
     lib.afqmc_strerror.argtypes = [ctypes.c_int]
     lib.afqmc_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -251,6 +253,19 @@ def afqmc_debug_dgemm(kind, M, N, K, A, lda, B, ldb, C, ldc, stream=None):
     """C = A @ B in FP64 (kind 0: FP64 SIMT, 1: digit-split tensor-core product); device pointers."""
     _ck("afqmc_debug_dgemm", load().afqmc_debug_dgemm(kind, M, N, K, ctypes.c_void_p(A), lda, ctypes.c_void_p(B), ldb,
                                                       ctypes.c_void_p(C), ldc, _stream(stream)))
+
+
+def afqmc_debug_ozaki_plan(M, N, K, batch=1, cap=64):
+    """The digit-split plan for an M x N x K product: (b, s, [[(p, q), ...] per group])."""
+    b, s, ng = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    npa = np.zeros(cap, np.int32)
+    pa = np.zeros(cap * 16, np.int32)
+    pb = np.zeros(cap * 16, np.int32)
+    _ck("afqmc_debug_ozaki_plan", load().afqmc_debug_ozaki_plan(M, N, K, batch, ctypes.byref(b), ctypes.byref(s),
+                                                                ctypes.byref(ng), cap, _ptr(npa, ctypes.c_int),
+                                                                _ptr(pa, ctypes.c_int), _ptr(pb, ctypes.c_int)))
+    groups = [[(int(pa[16 * g + i]), int(pb[16 * g + i])) for i in range(int(npa[g]))] for g in range(min(ng.value, cap))]
+    return b.value, s.value, groups
 
 
 def afqmc_launch_count():

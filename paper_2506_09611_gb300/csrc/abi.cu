@@ -1465,6 +1465,12 @@ int afqmc_debug_dgemm(int kind, int M, int N, int K, const double* A, long long 
     return h ? AFQMC_ERR_CUDA : AFQMC_OK;
 }
 
+int afqmc_debug_ozaki_plan(int M, int N, int K, int batch, int* b, int* s, int* ngroups, int cap, int* np, int* pa,
+                           int* pb) {
+    if (!b || !s || !ngroups || cap < 0 || (cap > 0 && (!np || !pa || !pb))) return AFQMC_ERR_ARG;
+    return ozaki_plan_info(M, N, K, batch, b, s, ngroups, cap, np, pa, pb) == 0 ? AFQMC_OK : AFQMC_ERR_ARG;
+}
+
 int afqmc_debug_uniforms(uint64_t seed, uint64_t walker, uint64_t visit, int count, double* host_out) {
     if (count < 0 || (count > 0 && !host_out)) return AFQMC_ERR_ARG;
     if (count == 0) return AFQMC_OK;

@@ -92,6 +92,11 @@ size_t ozaki_sc_doubles(int M, int N, int batch);
 // true when the digit-split product is expected to beat the FP64 SIMT GEMM at this shape
 bool ozaki_pays(int M, int N, int K, int batch);
 cudaError_t ozaki_gemm(cudaStream_t st, const OzGemmArgs& g, void* ws, double* sc);
+// The plan ozaki_gemm uses for a shape (host only): digit width b, digits s, and per group its
+// pairs (1-based digit indices, TC_OZ_MAXP slots per group, the first `cap` groups).  -1 when K is
+// beyond the exact range of every digit width.
+int ozaki_plan_info(int M, int N, int K, int batch, int* b, int* s, int* ngroups, int cap, int* np, int* pa,
+                    int* pb);
 
 // ---- setup / recompute kernels (setup.cu) ----
 cudaError_t launch_expK(cudaStream_t st, int L, double t, double tau, double* E, long ld);

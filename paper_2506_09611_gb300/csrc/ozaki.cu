@@ -201,6 +201,24 @@ bool ozaki_pays(int M, int N, int K, int batch) {
     return p.cost + split < 0.8 * simt;
 }
 
+int ozaki_plan_info(int M, int N, int K, int batch, int* b, int* s, int* ngroups, int cap, int* np, int* pa,
+                    int* pb) {
+    if (M < 1 || N < 1 || K < 1 || batch < 1) return -1;
+    const OzPlan plan = oz_plan(M, N, K, batch);
+    if (plan.b == 0) return -1;
+    *b = plan.b;
+    *s = plan.s;
+    *ngroups = (int)plan.groups.size();
+    for (int g = 0; g < (int)plan.groups.size() && g < cap; ++g) {
+        np[g] = (int)plan.groups[g].size();
+        for (int i = 0; i < np[g]; ++i) {
+            pa[g * TC_OZ_MAXP + i] = plan.groups[g][i].first;
+            pb[g * TC_OZ_MAXP + i] = plan.groups[g][i].second;
+        }
+    }
+    return 0;
+}
+
 cudaError_t ozaki_gemm(cudaStream_t st, const OzGemmArgs& g, void* ws, double* sc) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
     if (g.K <= 0) return cudaErrorInvalidValue;
