@@ -255,7 +255,7 @@ def afqmc_debug_dgemm(kind, M, N, K, A, lda, B, ldb, C, ldc, stream=None):
                                                       ctypes.c_void_p(C), ldc, _stream(stream)))
 
 
-def afqmc_debug_ozaki_plan(M, N, K, batch=1, cap=64):
+def afqmc_debug_ozaki_plan(M, N, K, batch=1, cap=128):
     """The digit-split plan for an M x N x K product: (b, s, [[(p, q), ...] per group])."""
     b, s, ng = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     npa = np.zeros(cap, np.int32)
