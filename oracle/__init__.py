@@ -20,6 +20,7 @@ Parity status of each function (what pins it in ``tests/test_oracle_pins.py``):
   blockfb_slice   -- brute-force stripped force bias, det ratio, exact detailed
                      balance on an enumerable toy, from-scratch G
   energy          -- U=0 closed form; Fock-space brute force on <= 3 sites
+  wrap_fft        -- the momentum-space wrap (FFT propagation) equals the dense wrap
   tform_wrap      -- U_L U_R unchanged; 1 - U_R T U_L equals the wrapped G
   tform_delayed_slice
                   -- the paper's T-form delayed update (Sec. III.A): identical decisions and
@@ -202,6 +203,33 @@ class Model:
         xl = np.ascontiguousarray(xl, dtype=np.int8)
         _load().or_wrap(ctypes.byref(self.p), _d(self.E), _d(self.Einv), _i8(xl), spin, direction, _d(G))
         return G
+
+    def wrap_fft(self, G, xl, spin, direction):
+        """The wrap of Eq. BlMat with exp(-+dtau K) applied in momentum space (the paper's FFT
+        propagation, Sec. II.C): on the periodic lattice K is diagonal in the 2D Fourier basis with
+        eigenvalues eps_k = -2t (cos kx + cos ky), so E X = F^{-1} diag(e^{-dtau eps_k}) F X for every
+        column of X (numpy's FFT over the site index reshaped to (Ly, Lx)).  G E^{-1} = (E^{-1} G^T)^T
+        because E is symmetric.  The same moves as `wrap`."""
+        Lx, Ly, N = self.p.Lx, self.p.Ly, self.N
+        kx = 2 * np.pi * np.arange(Lx) / Lx
+        ky = 2 * np.pi * np.arange(Ly) / Ly
+        eps = -2.0 * self.p.t * (np.cos(kx)[None, :] + np.cos(ky)[:, None])  # (Ly, Lx)
+
+        def apply_E(X, tau):  # exp(-tau K) X, X: N x m, site index = x + Lx y
+            Xr = X.reshape(Ly, Lx, -1)
+            Xk = np.fft.fft2(Xr, axes=(0, 1))
+            return np.real(np.fft.ifft2(Xk * np.exp(-tau * eps)[:, :, None], axes=(0, 1))).reshape(N, -1)
+
+        d = np.exp(self.c[spin] * np.asarray(xl, dtype=np.float64))
+        G = _f64(G)
+        tau = self.p.dtau
+        if direction > 0:  # D E G Einv D^{-1}
+            T = apply_E(G, tau)
+            T = apply_E(T.T, -tau).T
+            return d[:, None] * T / d[None, :]
+        T = G * d[None, :] / d[:, None]  # D^{-1} G D, then Einv (.) E
+        T = apply_E(T, -tau)
+        return apply_E(T.T, tau).T
 
     def local_slice(self, Gu, Gd, xl, u, replay=None):
         """Local update of one slice (Eqs. DetRatiolocal, UpdateLTRlocal); returns (Gu, Gd, xl, dec, ratio, sign)."""

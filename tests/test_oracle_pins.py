@@ -408,3 +408,18 @@ def test_tform_blockfb_equals_gform(nb):
         if w.pos % stab == 0:
             w.recompute(stab)
             tw.recompute(stab)
+
+
+# ---------------------------------------------------------------- momentum-space wrap (§8(f) F2)
+
+@pytest.mark.parametrize("Lx,Ly", [(4, 4), (6, 4), (5, 3)])
+def test_fft_wrap_equals_dense_wrap(Lx, Ly):
+    """The wrap with exp(-+dtau K) applied through the 2D lattice DFT equals the dense-matrix wrap
+    in both directions and both spins, and moves the from-scratch G to the next slice."""
+    m, P, X = _setup(Lx, Ly, 3, 4, dtau=0.08)
+    ell = 1
+    for s in range(2):
+        G = bf.green(m.E, m.c[s], X, P, ell)
+        for d, xl in ((+1, X[ell]), (-1, X[ell - 1])):
+            np.testing.assert_allclose(m.wrap_fft(G, xl, s, d), m.wrap(G, xl, s, d), atol=1e-12)
+        np.testing.assert_allclose(m.wrap_fft(G, X[ell], s, +1), bf.green(m.E, m.c[s], X, P, ell + 1), atol=1e-11)
