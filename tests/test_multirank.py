@@ -35,7 +35,7 @@ def _rank(rank, world, port, out):
 
 def test_two_gloo_ranks_take_the_max_time_and_sum_the_work():
     world, port = 2, _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:  # no fork of a process that already runs threads
         out = mgr.dict()
         mp.start_processes(_rank, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
         res = dict(out)
