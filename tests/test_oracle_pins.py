@@ -423,3 +423,39 @@ def test_fft_wrap_equals_dense_wrap(Lx, Ly):
         for d, xl in ((+1, X[ell]), (-1, X[ell - 1])):
             np.testing.assert_allclose(m.wrap_fft(G, xl, s, d), m.wrap(G, xl, s, d), atol=1e-12)
         np.testing.assert_allclose(m.wrap_fft(G, X[ell], s, +1), bf.green(m.E, m.c[s], X, P, ell + 1), atol=1e-11)
+
+
+@pytest.mark.parametrize("k", [4, 5, 16])
+def test_tform_window_update_is_block_update_of_its_accepts(k):
+    """A delayed window's accumulated change of T and U_R (Eqs. DelayRgenk, FinalDelay) equals one
+    rank-n_F block update over the window's accepted sites (Eq. BlkFrcBsTnew2 with F = the accepts):
+    the T-form block force-bias pass, forced to propose exactly the final fields window by window and
+    to accept every block, reproduces the delayed pass's T and U_R.  This is the window flush of a
+    T-form GPU path."""
+    Lx, Ly, ns, M = 4, 4, 7, 4
+    m, P, X = _setup(Lx, Ly, ns, M, dtau=0.05)
+    tw = oracle.TWalker(m, P, P, X)
+    ell = 1
+    for s in range(2):
+        tw.UR[s], tw.UL[s] = m.tform_wrap(tw.UR[s], tw.UL[s], X[ell - 1], s, +1)
+    u = inputs.uniforms(5, 0, 0, 2 * m.N)
+    UR1, T1, x1, dec, ratio, sg, nfl = m.tform_delayed_slice(tw.UR, tw.UL, tw.T, X[ell - 1], u[:m.N], k, 1)
+    nblocks = (m.N + k - 1) // k
+    rep = np.zeros(m.N + nblocks, np.uint8)
+    rep[:m.N] = x1 > 0  # propose the delayed pass's final fields
+    rep[m.N:] = 1       # accept every block
+    UR2, T2, x2, xprop, lamp, bdec, bratio, bsg = m.tform_blockfb_slice(tw.UR, tw.UL, tw.T, X[ell - 1], u[:m.N],
+                                                                       np.zeros(nblocks), k, replay=rep)
+    np.testing.assert_array_equal(x2, x1)
+    assert dec.sum() > 0 and sg == bsg
+    for s in range(2):
+        np.testing.assert_allclose(T2[s], T1[s], atol=1e-12)
+        np.testing.assert_allclose(UR2[s], UR1[s], atol=1e-12)
+    # the product of a window's accepted local ratios is its block ratio (without the proposal factor)
+    for b in range(nblocks):
+        sl = slice(b * k, min(m.N, (b + 1) * k))
+        acc = dec[sl] == 1
+        if acc.any():
+            lam_x = np.where(X[ell - 1, sl] > 0, lamp[sl], 1 - lamp[sl])[acc]
+            lam_xp = np.where(x1[sl] > 0, lamp[sl], 1 - lamp[sl])[acc]
+            assert bratio[b] == pytest.approx(np.prod(ratio[sl][acc]) * np.prod(lam_x / lam_xp), rel=1e-10)
