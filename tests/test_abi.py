@@ -78,3 +78,46 @@ def test_soc_create_rejects_bad_arguments_before_touching_the_device():
         p = soc.afqmc_soc_params(**{**good, **bad})
         assert lib.afqmc_soc_create(ctypes.byref(h), ctypes.byref(p)) == -1, bad
     assert lib.afqmc_soc_destroy(None) == 0
+
+
+def test_every_entry_point_rejects_a_null_context_without_the_device():
+    """Each stateful call of both headers returns AFQMC_ERR_ARG for a NULL context before any CUDA
+    call (destroy of NULL is a no-op)."""
+    lib = afqmc.load()
+    soc.load()
+    ARG = -1
+    ip = ctypes.c_int()
+    d = ctypes.c_double()
+    i8 = ctypes.c_int8()
+    u8 = ctypes.c_uint8()
+    i64 = ctypes.c_int64()
+    one = ctypes.c_int(1)
+    p = ctypes.byref
+    assert lib.afqmc_destroy(None) == 0
+    assert lib.afqmc_init_walkers(None, 1, p(one), p(one), p(one), p(d), None, None) == ARG
+    assert lib.afqmc_sweep_slice(None, 1, 1, 1, 8, 4, None, None, None) == ARG
+    assert lib.afqmc_recompute_G(None, None, None) == ARG
+    assert lib.afqmc_measure_energy(None, p(d), p(d), None) == ARG
+    assert lib.afqmc_get_G(None, 0, 0, p(d)) == ARG
+    assert lib.afqmc_set_G(None, 0, 0, p(d)) == ARG
+    assert lib.afqmc_get_fields(None, 0, p(i8)) == ARG
+    assert lib.afqmc_get_decisions(None, 0, p(u8)) == ARG
+    assert lib.afqmc_get_ratios(None, 0, p(d)) == ARG
+    assert lib.afqmc_get_info(None, 0, p(ip), p(ip), p(ip), p(ip), p(ip)) == ARG
+    assert lib.afqmc_set_graphs(None, 1) == ARG
+    assert lib.afqmc_set_profiling(None, 1) == ARG
+    assert lib.afqmc_get_profile(None, p(d), p(i64), p(i64)) == ARG
+    assert lib.afqmc_soc_destroy(None) == 0
+    assert lib.afqmc_soc_init(None, p(d), None, None) == ARG
+    assert lib.afqmc_soc_sweep_slice(None, 1, 1, 1, 8, 4, None, None) == ARG
+    assert lib.afqmc_soc_recompute_G(None, None, None) == ARG
+    assert lib.afqmc_soc_measure_energy(None, p(d), None) == ARG
+    assert lib.afqmc_soc_get_G(None, 0, p(d)) == ARG
+    assert lib.afqmc_soc_set_G(None, 0, p(d)) == ARG
+    assert lib.afqmc_soc_get_fields(None, 0, p(i8)) == ARG
+    assert lib.afqmc_soc_get_decisions(None, 0, p(u8)) == ARG
+    assert lib.afqmc_soc_get_ratios(None, 0, p(d)) == ARG
+    assert lib.afqmc_soc_get_lam_plus(None, 0, p(d)) == ARG
+    assert lib.afqmc_soc_get_info(None, p(ip), p(ip), p(ip)) == ARG
+    assert lib.afqmc_soc_set_profiling(None, 1) == ARG
+    assert lib.afqmc_soc_get_profile(None, p(d), p(i64), p(i64)) == ARG
