@@ -459,3 +459,31 @@ def test_tform_window_update_is_block_update_of_its_accepts(k):
             lam_x = np.where(X[ell - 1, sl] > 0, lamp[sl], 1 - lamp[sl])[acc]
             lam_xp = np.where(x1[sl] > 0, lamp[sl], 1 - lamp[sl])[acc]
             assert bratio[b] == pytest.approx(np.prod(ratio[sl][acc]) * np.prod(lam_x / lam_xp), rel=1e-10)
+
+
+def test_full_force_bias_rejection_is_linear_in_dtau():
+    """The full force-bias update (n_b = N) accepts with probability 1 - O(dtau U f_x) (Eqs.
+    RatioApprox, AcceptRatio): over seeded 4 x 4 chains the mean rejection probability
+    1 - <min(1, |R|)> falls linearly with dtau (log-log slope near 1) and stays below 0.1 at
+    dtau = 0.08.  A force bias of the wrong sign or size breaks this scaling."""
+    L, ns, U, M = 4, 7, 4.0, 8
+    N = L * L
+    dtaus = (0.01, 0.02, 0.04, 0.08)
+    rej = []
+    for dtau in dtaus:
+        probs = []
+        for seed in range(1, 7):
+            m = _model(L, L, U=U, M=M, dtau=dtau)
+            P = inputs.trial_state(L, L, ns)
+            X = inputs.initial_fields(M, N, seed=seed)
+            w = oracle.Walker(m, P, P, X)
+            for visit, ell in enumerate(range(1, M + 1)):
+                u = inputs.uniforms(seed, 0, visit, 2 * N)
+                dec, ratio, _ = w.sweep_slice(ell, +1, "blockfb", u, nb=N)
+                probs.append(min(1.0, abs(ratio[0])))
+                if w.pos % 4 == 0:
+                    w.recompute(4)
+        rej.append(1.0 - np.mean(probs))
+    slope = np.polyfit(np.log(dtaus), np.log(rej), 1)[0]
+    assert 0.8 < slope < 1.2, (rej, slope)
+    assert rej[-1] < 0.1
