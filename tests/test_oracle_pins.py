@@ -487,3 +487,29 @@ def test_full_force_bias_rejection_is_linear_in_dtau():
     slope = np.polyfit(np.log(dtaus), np.log(rej), 1)[0]
     assert 0.8 < slope < 1.2, (rej, slope)
     assert rej[-1] < 0.1
+
+
+def test_block_force_bias_rejection_set_by_block_size_not_lattice():
+    """The block force bias's rejection grows with the block size n_b and, at fixed n_b, hardly
+    depends on the lattice size (Sec. III.B): seeded chains at 6 x 6 and 8 x 8 (filling ~0.44,
+    U = 4, dtau = 0.1)."""
+    U, M, dtau = 4.0, 4, 0.1
+    rej = {}
+    for L, ns in ((6, 16), (8, 28)):
+        N = L * L
+        for nb in (2, 4, 8):
+            probs = []
+            for seed in (1, 2, 3):
+                m = _model(L, L, U=U, M=M, dtau=dtau)
+                P = inputs.trial_state(L, L, ns)
+                X = inputs.initial_fields(M, N, seed=seed)
+                w = oracle.Walker(m, P, P, X)
+                for visit, ell in enumerate(range(1, M + 1)):
+                    u = inputs.uniforms(seed, 0, visit, 2 * N)
+                    _, ratio, _ = w.sweep_slice(ell, +1, "blockfb", u, nb=nb)
+                    probs.extend(np.minimum(1.0, np.abs(ratio)))
+            rej[(L, nb)] = 1.0 - np.mean(probs)
+    for L in (6, 8):
+        assert rej[(L, 2)] < rej[(L, 4)] < rej[(L, 8)], rej
+    for nb in (2, 4, 8):
+        assert 0.7 < rej[(8, nb)] / rej[(6, nb)] < 1.4, rej
