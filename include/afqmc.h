@@ -221,9 +221,11 @@ int afqmc_get_profile(afqmc_ctx* ctx, double* ms, int64_t* intervals, int64_t* l
 int64_t afqmc_launch_count(void);
 
 /* Validation hook for the tensor-core GEMM: C = A * Bt^T (FP32, device pointers, row-major
- * A: M x K, Bt: N x K, C: M x N; c_trans = 1 writes C^T), with kind 1 = tcgen05 one-pass TF32,
- * kind 2 = tcgen05 three-term TF32 split (FP32 accuracy).  Pointers and leading dimensions
- * must be 16-byte aligned.  Syncs the stream; AFQMC_ERR_TIMEOUT if a device wait expired. */
+ * A: M x K, Bt: N x K, C: M x N; c_trans = 1 writes C^T, N x M), with kind 1 = tcgen05 one-pass
+ * TF32, kind 2 = tcgen05 three-term TF32 split (FP32 accuracy).  lda, ldb >= K and ldc >= N
+ * (>= M with c_trans); pointers and leading dimensions must be 16-byte aligned.  Syncs the
+ * stream.  AFQMC_ERR_ARG for bad sizes, pointers or strides; AFQMC_ERR_TIMEOUT if a device wait
+ * expired. */
 int afqmc_debug_gemm(int kind, int M, int N, int K, const float* A, long long lda, const float* Bt,
                      long long ldb, float* C, long long ldc, int c_trans, void* stream);
 
@@ -231,8 +233,8 @@ int afqmc_debug_gemm(int kind, int M, int N, int K, const float* A, long long ld
  * A: M x K, B: K x N, C: M x N with leading dimensions lda >= K, ldb >= N, ldc >= N), kind 0 =
  * FP64 SIMT product, kind 1 = digit-split product on the tcgen05 tensor cores (every element of A
  * and B split into b-bit integer digits relative to the largest exponent of its row of A or
- * column of B; digit planes multiplied exactly in TF32 with FP32 accumulation; levels summed in
- * FP64).  Allocates and frees its own workspace; syncs the stream.  AFQMC_ERR_NUMERIC for an
+ * column of B; digit planes stored as bf16, which holds such small integers exactly, and
+ * multiplied by tcgen05 kind::f16 with exact FP32 accumulation; levels summed in FP64).  Allocates and frees its own workspace; syncs the stream.  AFQMC_ERR_NUMERIC for an
  * element of magnitude >= 2^1023 or non-finite, AFQMC_ERR_TIMEOUT if a device wait expired,
  * AFQMC_ERR_ARG for K beyond the exact range of the split. */
 int afqmc_debug_dgemm(int kind, int M, int N, int K, const double* A, long long lda, const double* B,

@@ -38,7 +38,10 @@ def _compile(src, extra):
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     """Build paper_2506_09611_gb300/libafqmc.so if any source is newer than it."""
-    srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
+    missing = [s for s in SOURCES if not os.path.exists(os.path.join(CSRC, s))]
+    if missing:
+        raise FileNotFoundError(f"missing CUDA sources in {CSRC}: {', '.join(missing)}")
+    srcs = list(SOURCES)
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(p) <= t for p in _deps()):

@@ -244,6 +244,28 @@ static int read_dev_err(afqmc_ctx* ctx, Walker* w) {
     return ctx->sticky;
 }
 
+// E = exp(-dtau K), E^{-1} and the one-dimensional factor Ex of the L x L lattice, in FP64 and
+// in the bulk precision.  Device buffers go to ctx->allocs (freed by afqmc_destroy).
+static cudaError_t fill_lattice(afqmc_ctx* ctx, Lattice* l, cudaStream_t st) {
+    const int L = l->L;
+    const size_t n2 = (size_t)l->N * l->ld;
+    cudaError_t e;
+    if ((e = dalloc(ctx->allocs, &l->E64, n2 * 8)) != cudaSuccess) return e;
+    if ((e = dalloc(ctx->allocs, &l->Einv64, n2 * 8)) != cudaSuccess) return e;
+    if ((e = dalloc(ctx->allocs, (char**)&l->Eb, n2 * esize(ctx))) != cudaSuccess) return e;
+    if ((e = dalloc(ctx->allocs, (char**)&l->Einvb, n2 * esize(ctx))) != cudaSuccess) return e;
+    if ((e = dalloc(ctx->allocs, &l->Ex64, (size_t)L * L * 8)) != cudaSuccess) return e;
+    if ((e = launch_expK1d(st, L, ctx->p.t, ctx->p.dtau, l->Ex64)) != cudaSuccess) return e;
+    if ((e = launch_expK(st, L, ctx->p.t, ctx->p.dtau, l->E64, l->ld)) != cudaSuccess) return e;
+    if ((e = launch_expK(st, L, ctx->p.t, -ctx->p.dtau, l->Einv64, l->ld)) != cudaSuccess) return e;
+    if (ctx->p.precision == AFQMC_PREC_FP64) {
+        if ((e = launch_cast<double>(st, l->E64, l->ld, (double*)l->Eb, l->ld, l->N, l->N)) != cudaSuccess) return e;
+        return launch_cast<double>(st, l->Einv64, l->ld, (double*)l->Einvb, l->ld, l->N, l->N);
+    }
+    if ((e = launch_cast<float>(st, l->E64, l->ld, (float*)l->Eb, l->ld, l->N, l->N)) != cudaSuccess) return e;
+    return launch_cast<float>(st, l->Einv64, l->ld, (float*)l->Einvb, l->ld, l->N, l->N);
+}
+
 static Lattice* get_lattice(afqmc_ctx* ctx, int L, cudaStream_t st, cudaError_t* err) {
     for (auto* l : ctx->lats)
         if (l->L == L) return l;
@@ -251,22 +273,9 @@ static Lattice* get_lattice(afqmc_ctx* ctx, int L, cudaStream_t st, cudaError_t*
     l->L = L;
     l->N = L * L;
     l->ld = ((l->N + 31) / 32) * 32;
-    size_t n2 = (size_t)l->N * l->ld;
-    *err = cudaSuccess;
-    if ((*err = dalloc(ctx->allocs, &l->E64, n2 * 8)) != cudaSuccess) return nullptr;
-    if ((*err = dalloc(ctx->allocs, &l->Einv64, n2 * 8)) != cudaSuccess) return nullptr;
-    if ((*err = dalloc(ctx->allocs, (char**)&l->Eb, n2 * esize(ctx))) != cudaSuccess) return nullptr;
-    if ((*err = dalloc(ctx->allocs, (char**)&l->Einvb, n2 * esize(ctx))) != cudaSuccess) return nullptr;
-    if ((*err = dalloc(ctx->allocs, &l->Ex64, (size_t)L * L * 8)) != cudaSuccess) return nullptr;
-    if ((*err = launch_expK1d(st, L, ctx->p.t, ctx->p.dtau, l->Ex64)) != cudaSuccess) return nullptr;
-    if ((*err = launch_expK(st, L, ctx->p.t, ctx->p.dtau, l->E64, l->ld)) != cudaSuccess) return nullptr;
-    if ((*err = launch_expK(st, L, ctx->p.t, -ctx->p.dtau, l->Einv64, l->ld)) != cudaSuccess) return nullptr;
-    if (ctx->p.precision == AFQMC_PREC_FP64) {
-        if ((*err = launch_cast<double>(st, l->E64, l->ld, (double*)l->Eb, l->ld, l->N, l->N)) != cudaSuccess) return nullptr;
-        if ((*err = launch_cast<double>(st, l->Einv64, l->ld, (double*)l->Einvb, l->ld, l->N, l->N)) != cudaSuccess) return nullptr;
-    } else {
-        if ((*err = launch_cast<float>(st, l->E64, l->ld, (float*)l->Eb, l->ld, l->N, l->N)) != cudaSuccess) return nullptr;
-        if ((*err = launch_cast<float>(st, l->Einv64, l->ld, (float*)l->Einvb, l->ld, l->N, l->N)) != cudaSuccess) return nullptr;
+    if ((*err = fill_lattice(ctx, l, st)) != cudaSuccess) {
+        delete l;
+        return nullptr;
     }
     ctx->lats.push_back(l);
     return l;
@@ -1399,6 +1408,7 @@ int64_t afqmc_launch_count(void) { return (int64_t)g_launches.load(); }
 int afqmc_debug_gemm(int kind, int M, int N, int K, const float* A, long long lda, const float* Bt, long long ldb,
                      float* C, long long ldc, int c_trans, void* stream) {
     if ((kind != 1 && kind != 2) || M < 1 || N < 1 || K < 1 || !A || !Bt || !C) return AFQMC_ERR_ARG;
+    if (lda < K || ldb < K || ldc < (c_trans ? M : N)) return AFQMC_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     int* err = nullptr;
     if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return AFQMC_ERR_OOM;
@@ -1415,6 +1425,7 @@ int afqmc_debug_gemm(int kind, int M, int N, int K, const float* A, long long ld
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(err);
+    if (e == cudaErrorInvalidValue) return AFQMC_ERR_ARG;  // a tensor map refused the pointers or strides
     if (e != cudaSuccess) return AFQMC_ERR_CUDA;
     if (h == DEV_TIMEOUT) return AFQMC_ERR_TIMEOUT;
     return h ? AFQMC_ERR_CUDA : AFQMC_OK;

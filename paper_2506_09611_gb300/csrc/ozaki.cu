@@ -1,4 +1,4 @@
-// ozaki.cu -- FP64 matrix products on the TF32 tensor cores by error-free digit splitting.
+// ozaki.cu -- FP64 matrix products on the bf16 tensor cores by error-free digit splitting.
 //
 // GB300 runs FP64 at 1/64 of its FP32 rate, and the recompute of G (Sec. II.C, Eq. GrFMatNew)
 // spends most of its time in two FP64 products: U_L U_R and U_R (U_L U_R)^{-1} U_L.  Both are

@@ -69,6 +69,17 @@ def test_dgemm_hook_rejects_bad_arguments_before_touching_the_device():
     assert lib.afqmc_debug_dgemm(1, 4, 4, 4, None, 4, p, 4, p, 4, None) == -1  # null operand
 
 
+def test_gemm_hook_rejects_bad_arguments_before_touching_the_device():
+    lib = afqmc.load()
+    p = ctypes.c_void_p(16)  # never dereferenced: the checks come first
+    assert lib.afqmc_debug_gemm(3, 8, 8, 8, p, 8, p, 8, p, 8, 0, None) == -1   # unknown engine
+    assert lib.afqmc_debug_gemm(2, 8, 0, 8, p, 8, p, 8, p, 8, 0, None) == -1   # empty N
+    assert lib.afqmc_debug_gemm(2, 8, 8, 16, p, 8, p, 16, p, 8, 0, None) == -1  # lda < K
+    assert lib.afqmc_debug_gemm(2, 8, 8, 16, p, 16, p, 8, p, 8, 0, None) == -1  # ldb < K
+    assert lib.afqmc_debug_gemm(2, 16, 8, 8, p, 8, p, 8, p, 8, 1, None) == -1   # ldc < M for C^T
+    assert lib.afqmc_debug_gemm(1, 8, 8, 8, p, 8, None, 8, p, 8, 0, None) == -1  # null operand
+
+
 def test_soc_create_rejects_bad_arguments_before_touching_the_device():
     lib = soc.load()
     h = ctypes.c_void_p()
