@@ -30,7 +30,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2506_09611_gb300 import inputs  # noqa: E402
+from paper_2506_09611_gb300 import inputs, tune  # noqa: E402
 
 METRIC = "field updates/s at 40x40 Hubbard on 1 GB300, delayed/blockFB vs local; G err"
 UNIT = "field updates/s"
@@ -494,20 +494,15 @@ def batched_population(afqmc, torch, stream, args, seed):
                 afqmc.afqmc_recompute_G(ctx.h, None, stream)
 
     def timed(k, n):
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(n):
-            sweep(k)
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / n
+        return tune.time_on_stream(torch, stream, lambda: sweep(k), n)
 
-    tune = {}
-    for k in (16, 32, 64):
+    def trial(k):
         sweep(k)  # first sweep with this k (warm-up)
-        tune[k] = timed(k, 1)
-    kbest = min(tune, key=tune.get)
+        return timed(k, 1)
+
+    kchoice, ktrials = tune.tune(None, "", "k", (16, 32, 64), trial)
+    kbest = kchoice.value
+    k_ms = {t.value: t.ms for t in ktrials}
     upd = sum(int(L) * int(L) for L in Ls) * 2 * Mb
     ms_direct = timed(kbest, 2)
     ctx.set_graphs(True)
@@ -517,7 +512,7 @@ def batched_population(afqmc, torch, stream, args, seed):
     sizes = {int(L): int((Ls == L).sum()) for L in sorted(set(Ls.tolist()))}
     return {"metric": "field updates/s, mixed walker population, delayed update", "unit": UNIT,
             "walkers": int(len(Ls)), "walkers_per_L": sizes, "M": Mb, "U": Ub, "stab_every": Sb,
-            "k_tuning_ms_per_sweep": tune, "k": kbest,
+            "k_tuning_ms_per_sweep": k_ms, "k": kbest,
             "value": upd / (min(ms_direct, ms_graph) / 1e3),
             "direct_launches": {"value": upd / (ms_direct / 1e3), "ms_per_sweep": ms_direct},
             "cuda_graphs": {"value": upd / (ms_graph / 1e3), "ms_per_sweep": ms_graph},
