@@ -152,6 +152,68 @@ def test_local_free_running_sweep_tracks_scratch_and_weight():
     assert w.sign == np.sign(W1 / W0)
 
 
+def _negative_weight_case():
+    """A seeded 3 x 2 case (2 particles per spin, U = 8, dtau = 0.1) where flipping every field of
+    slice 3 takes the weight W(X) = prod_s det(P^T B_M..B_1 P) (Eq. ConfgWeight) to the opposite
+    sign: the real spin decoupling has a sign problem away from half filling."""
+    m, P, X = _setup(3, 2, 2, 6, seed=4, U=8.0, dtau=0.1)
+    ell = 3
+    Xf = X.copy()
+    Xf[ell - 1] *= -1
+    W0, W1 = bf.weight(m.E, m.c, X, P, P), bf.weight(m.E, m.c, Xf, P, P)
+    assert W1 / W0 < 0  # the case really crosses a sign change
+    return m, P, X, Xf, ell
+
+
+@pytest.mark.parametrize("scheme", ["local", "delayed-k2", "delayed-k4", "delayed-s1-k3", "blockfb-1", "blockfb-2",
+                                    "blockfb-6", "tform-delayed-k2", "tform-blockfb-2"])
+def test_sign_follows_the_weight_through_negative_ratios(scheme):
+    """Every scheme multiplies the walker sign by sign(R) of each accepted move (Eq. DetailBalance
+    with |R|): forcing every flip of a slice whose weight changes sign gives sign -1, with the
+    final G (or the T-form factors) equal to the from-scratch result."""
+    m, P, X, Xf, ell = _negative_weight_case()
+    N = m.N
+    Gs = [bf.green(m.E, m.c[s], X, P, ell) for s in range(2)]
+    zeros = np.zeros(N)
+    if scheme == "local" or scheme.startswith("delayed"):
+        forced = np.ones(N, np.uint8)
+        if scheme == "local":
+            Gu, Gd, xl, dec, ratio, sg = m.local_slice(Gs[0], Gs[1], X[ell - 1], zeros, replay=forced)
+        else:
+            k = int(scheme.split("k")[-1])
+            strategy = 1 if "-s1-" in scheme else 2
+            Gu, Gd, xl, dec, ratio, sg, _ = m.delayed_slice(Gs[0], Gs[1], X[ell - 1], zeros, k, strategy, forced)
+        assert (ratio < 0).any()
+    elif scheme.startswith("blockfb"):
+        nb = int(scheme.split("-")[1])
+        nblk = (N + nb - 1) // nb
+        rep = np.concatenate([(Xf[ell - 1] > 0).astype(np.uint8), np.ones(nblk, np.uint8)])
+        Gu, Gd, xl, xprop, _, dec, ratio, sg = m.blockfb_slice(Gs[0], Gs[1], X[ell - 1], zeros, np.zeros(nblk),
+                                                              nb, replay=rep)
+        np.testing.assert_array_equal(xprop, Xf[ell - 1])
+    else:
+        UR, UL, T = [], [], []
+        for s in range(2):
+            _, _, _, ur, ul = m.green_scratch(X, P, s, ell, stab=2, want_factors=True)
+            UR.append(ur)
+            UL.append(ul)
+            T.append(np.linalg.inv(ul @ ur))
+        if scheme == "tform-delayed-k2":
+            URn, Tn, xl, dec, ratio, sg, _ = m.tform_delayed_slice(UR, UL, T, X[ell - 1], zeros, 2, 2,
+                                                                   np.ones(N, np.uint8))
+        else:
+            nblk = (N + 1) // 2
+            rep = np.concatenate([(Xf[ell - 1] > 0).astype(np.uint8), np.ones(nblk, np.uint8)])
+            URn, Tn, xl, _, _, dec, ratio, sg = m.tform_blockfb_slice(UR, UL, T, X[ell - 1], zeros, np.zeros(nblk),
+                                                                      2, replay=rep)
+        Gu, Gd = (np.eye(N) - URn[s] @ Tn[s] @ UL[s] for s in range(2))
+    assert dec.all()
+    np.testing.assert_array_equal(xl, Xf[ell - 1])
+    assert sg == -1.0
+    np.testing.assert_allclose(Gu, bf.green(m.E, m.c[0], Xf, P, ell), atol=1e-9)
+    np.testing.assert_allclose(Gd, bf.green(m.E, m.c[1], Xf, P, ell), atol=1e-9)
+
+
 # ---------------------------------------------------------------- delayed update
 
 @pytest.mark.parametrize("k,strategy", [(1, 2), (3, 2), (8, 2), (5, 1), (16, 1)])
