@@ -214,6 +214,28 @@ def test_sign_follows_the_weight_through_negative_ratios(scheme):
     np.testing.assert_allclose(Gd, bf.green(m.E, m.c[1], Xf, P, ell), atol=1e-9)
 
 
+@pytest.mark.parametrize("nb", [1, 3, 16])
+def test_block_proposals_equal_to_the_current_fields_are_accepted_unchanged(nb):
+    """A block whose proposal repeats its current fields is the null move: no site flips, R = 1
+    and u < min(1, |R|) holds for every u in [0, 1).  It is accepted, with ratio 1, and G, the
+    fields and the sign stay exactly as they were."""
+    m, P, X = _setup(4, 4, 7, 6)
+    N, ell = m.N, 2
+    Gs = [bf.green(m.E, m.c[s], X, P, ell) for s in range(2)]
+    xl = X[ell - 1]
+    top = 1.0 - 2.0 ** -53  # the largest uniform below 1
+    u_prop = np.where(xl > 0, 0.0, top)  # x' = +1 iff u_prop < lambda(+1), which lies strictly inside (0, 1)
+    nblk = (N + nb - 1) // nb
+    Gu, Gd, x1, xprop, lamp, dec, ratio, sg = m.blockfb_slice(Gs[0], Gs[1], xl, u_prop, np.full(nblk, top), nb)
+    assert np.all((lamp > 0) & (lamp < top))
+    np.testing.assert_array_equal(xprop, xl)
+    assert dec.all() and sg == 1.0
+    np.testing.assert_array_equal(ratio, np.ones(nblk))
+    np.testing.assert_array_equal(x1, xl)
+    np.testing.assert_array_equal(Gu, Gs[0])
+    np.testing.assert_array_equal(Gd, Gs[1])
+
+
 # ---------------------------------------------------------------- delayed update
 
 @pytest.mark.parametrize("k,strategy", [(1, 2), (3, 2), (8, 2), (5, 1), (16, 1)])

@@ -312,3 +312,24 @@ def test_full_force_bias_rejection_is_linear_in_dtau():
         rej.append(1.0 - np.mean(probs))
     slope = np.polyfit(np.log(dtaus), np.log(rej), 1)[0]
     assert 0.75 < slope < 1.25, (rej, slope)
+
+
+@pytest.mark.parametrize("nb", [1, 4, 9])
+def test_block_proposals_equal_to_the_current_fields_are_accepted_unchanged(nb):
+    """A block whose proposal repeats its current fields is the null move: Delta_F is empty, so
+    R = 1 and u < min(1, |R|) holds for every u in [0, 1).  It is accepted, with ratio 1, and G and
+    the fields stay exactly as they were."""
+    m, P, X = _setup()
+    N, ell = m.N, 2
+    G, _, _ = m.green_scratch(X, P, ell)
+    xl = X[ell - 1]
+    top = 1.0 - 2.0 ** -53  # the largest uniform below 1
+    u_prop = np.where(xl > 0, 0.0, top)  # x' = +1 iff u_prop < lambda(+1), which lies strictly inside (0, 1)
+    nblk = (N + nb - 1) // nb
+    G1, x1, xprop, lamp, dec, ratio = m.blockfb_slice(G, xl, u_prop, np.full(nblk, top), nb)
+    assert np.all((lamp > 0) & (lamp < top))
+    np.testing.assert_array_equal(xprop, xl)
+    assert dec.all()
+    np.testing.assert_array_equal(ratio, np.ones(nblk))
+    np.testing.assert_array_equal(x1, xl)
+    np.testing.assert_array_equal(G1, G)
