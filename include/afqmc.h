@@ -153,6 +153,14 @@ int afqmc_get_info(afqmc_ctx* ctx, int walker, int* N, int* n_up, int* n_dn, int
  * out[j] = u(seed, walker, visit, j) for j < count (device generator, copied to the host). */
 int afqmc_debug_uniforms(uint64_t seed, uint64_t walker, uint64_t visit, int count, double* host_out);
 
+/* Validation hook for the bounded device waits: one thread waits on a device flag that nothing
+ * sets, for limit_ns nanoseconds of %globaltimer (1000 <= limit_ns <= 2e9), then records the device
+ * timeout code and returns.  Every bounded wait of the library (grid barriers, mbarrier waits)
+ * takes this path when it expires.  Allocates and frees 8 bytes of device memory; syncs the
+ * stream.  Returns AFQMC_ERR_TIMEOUT, the expected outcome, with the CUDA context still usable;
+ * AFQMC_ERR_ARG for a limit out of range (checked before any device call). */
+int afqmc_debug_wait_timeout(long long limit_ns, void* stream);
+
 /* Apply accepted field changes at the sites I to both spins' G in one rank-m product -- the G form
  * of the delayed flush (Eq. FinalDelay) and of the block force-bias upgrade (Eq. BlkFrcBsTnew2):
  *     G_s <- G_s - G_s[:, I] W_s (E_I^T - G_s[I, :]),  W_s = D_s (1 + (1 - G_s[I, I]) D_s)^{-1}.

@@ -27,7 +27,8 @@ EXPORTS = ["afqmc_create", "afqmc_destroy", "afqmc_init_walkers", "afqmc_sweep_s
            "afqmc_measure_energy", "afqmc_get_G", "afqmc_set_G", "afqmc_get_fields", "afqmc_get_decisions",
            "afqmc_get_ratios", "afqmc_get_info", "afqmc_debug_uniforms", "afqmc_set_profiling", "afqmc_set_graphs",
            "afqmc_get_profile", "afqmc_launch_count", "afqmc_apply_flips", "afqmc_apply_flips_noalloc",
-           "afqmc_debug_gemm", "afqmc_debug_dgemm", "afqmc_debug_ozaki_plan", "afqmc_strerror"]
+           "afqmc_debug_gemm", "afqmc_debug_dgemm", "afqmc_debug_ozaki_plan", "afqmc_debug_wait_timeout",
+           "afqmc_strerror"]
 PHASES = ["prep", "wrap", "local", "chain", "flush", "recompute", "elim", "wrap_gemm", "flush_gemm", "lu_o",
           "solve", "dgemm"]
 
@@ -75,6 +76,7 @@ def load(path: str = LIB_PATH):
     lib.afqmc_get_ratios.argtypes = [vp, ctypes.c_int, dp]
     lib.afqmc_get_info.argtypes = [vp, ctypes.c_int, ip, ip, ip, ip, ip]
     lib.afqmc_debug_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, dp]
+    lib.afqmc_debug_wait_timeout.argtypes = [ctypes.c_longlong, vp]
     lib.afqmc_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.afqmc_set_graphs.argtypes = [vp, ctypes.c_int]
     lib.afqmc_get_profile.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
@@ -208,6 +210,11 @@ def afqmc_debug_uniforms(seed, walker, visit, count):
     out = np.zeros(count)
     _ck("afqmc_debug_uniforms", load().afqmc_debug_uniforms(seed, walker, visit, count, _ptr(out, ctypes.c_double)))
     return out
+
+
+def afqmc_debug_wait_timeout(limit_ns, stream=None):
+    """Run the bounded-wait probe for limit_ns; returns the status code (AFQMC_ERR_TIMEOUT expected)."""
+    return int(load().afqmc_debug_wait_timeout(int(limit_ns), _stream(stream)))
 
 
 def afqmc_set_profiling(ctx, on):

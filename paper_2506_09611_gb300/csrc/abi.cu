@@ -187,6 +187,23 @@ __global__ void set_double_kernel(double* p, double v, int n) {
     if (i < n) p[i] = v;
 }
 
+// One thread waits for a flag that nothing sets, bounded by limit_ns of %globaltimer, then
+// records DEV_TIMEOUT and returns: the path every bounded wait of the library takes on expiry.
+__global__ void debug_wait_kernel(const unsigned int* flag, unsigned long long limit_ns, int* err) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        if (*((volatile const unsigned int*)flag) != 0u) return;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > limit_ns) {
+            set_err(err, DEV_TIMEOUT);
+            return;
+        }
+        __nanosleep(1000);
+    }
+}
+
 __global__ void debug_uniforms_kernel(uint64_t seed, uint64_t walker, uint64_t visit, int count, double* out) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < count) out[j] = philox_uniform(seed, walker, visit, (uint64_t)j);
@@ -1480,6 +1497,26 @@ int afqmc_debug_ozaki_plan(int M, int N, int K, int batch, int* b, int* s, int* 
                            int* pb) {
     if (!b || !s || !ngroups || cap < 0 || (cap > 0 && (!np || !pa || !pb))) return AFQMC_ERR_ARG;
     return ozaki_plan_info(M, N, K, batch, b, s, ngroups, cap, np, pa, pb) == 0 ? AFQMC_OK : AFQMC_ERR_ARG;
+}
+
+int afqmc_debug_wait_timeout(long long limit_ns, void* stream) {
+    if (limit_ns < 1000 || limit_ns > 2000000000LL) return AFQMC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* buf = nullptr;  // [0] the error word, [1] the flag that nothing sets
+    if (cudaMalloc(&buf, 2 * sizeof(int)) != cudaSuccess) return AFQMC_ERR_OOM;
+    cudaError_t e = cudaMemsetAsync(buf, 0, 2 * sizeof(int), st);
+    if (e == cudaSuccess) {
+        count_launch();
+        debug_wait_kernel<<<1, 32, 0, st>>>((const unsigned int*)(buf + 1), (unsigned long long)limit_ns, buf);
+        e = cudaGetLastError();
+    }
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, buf, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (e != cudaSuccess) return AFQMC_ERR_CUDA;
+    if (h == DEV_TIMEOUT) return AFQMC_ERR_TIMEOUT;
+    return h ? AFQMC_ERR_CUDA : AFQMC_OK;
 }
 
 int afqmc_debug_uniforms(uint64_t seed, uint64_t walker, uint64_t visit, int count, double* host_out) {

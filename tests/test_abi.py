@@ -80,6 +80,13 @@ def test_gemm_hook_rejects_bad_arguments_before_touching_the_device():
     assert lib.afqmc_debug_gemm(1, 8, 8, 8, p, 8, None, 8, p, 8, 0, None) == -1  # null operand
 
 
+def test_wait_probe_rejects_a_limit_out_of_range_before_touching_the_device():
+    lib = afqmc.load()
+    assert lib.afqmc_debug_wait_timeout(0, None) == -1
+    assert lib.afqmc_debug_wait_timeout(999, None) == -1
+    assert lib.afqmc_debug_wait_timeout(2_000_000_001, None) == -1
+
+
 def test_soc_create_rejects_bad_arguments_before_touching_the_device():
     lib = soc.load()
     h = ctypes.c_void_p()
