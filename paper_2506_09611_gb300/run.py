@@ -4,6 +4,11 @@ through the C ABI (used for kernel profiling and quick timing).
 
     python -m paper_2506_09611_gb300.run --L 40 --U 6 --slices 20 --mode delayed --k 64
     python -m paper_2506_09611_gb300.run --soc --L 24 --U -4 --lam 0.5 --slices 12 --mode blockfb --nb 16
+    python -m paper_2506_09611_gb300.run --L 40 --tune tune.json --slices 20 --mode blockfb
+
+With --tune CACHE (Hubbard model) the delay rank and the block size are first chosen by timed
+trial walks (tune.autotune_walker: k by time, n_b by time under the acceptance floor) or read
+from the JSON cache for this device and workload; the walk then runs with the chosen values.
 
 The walk goes forward from slice 1 and turns at slice M, with the FP64 recompute at every
 multiple of --stab, exactly as in a full sweep; the inputs are the seeded synthetic trial
@@ -17,7 +22,7 @@ import time
 
 import numpy as np
 
-from . import afqmc, inputs
+from . import afqmc, inputs, tune
 
 
 def main(argv=None):
@@ -38,7 +43,12 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--soc", action="store_true", help="the spin-orbit-coupled model at half filling")
     ap.add_argument("--lam", type=float, default=0.5)
+    ap.add_argument("--tune", metavar="CACHE", help="choose k and nb by timed trials (cached in this JSON file)")
+    ap.add_argument("--tune-slices", type=int, default=10, help="slices of each trial walk (out and back)")
+    ap.add_argument("--floor", type=float, default=tune.ACCEPTANCE_FLOOR, help="block force-bias acceptance floor")
     a = ap.parse_args(argv)
+    if a.tune and a.soc:
+        ap.error("--tune covers the Hubbard model only")
     if a.soc:
         return main_soc(a)
 
@@ -53,6 +63,16 @@ def main(argv=None):
     ctx = afqmc.Context(a.M, dtau=a.dtau, U=a.U, t=a.t, precision=a.precision, stab_every=a.stab, seed=a.seed,
                         gemm=a.gemm)
     ctx.init_walkers([L], [ns], [ns], np.concatenate([P.ravel(), P.ravel()]), X, stream=stream)
+    tuned = None
+    if a.tune:
+        key = tune.workload_key(device=torch.cuda.get_device_name(), L=L, n_up=ns, n_dn=ns, U=a.U, t=a.t,
+                                dtau=a.dtau, M=a.M, stab=a.stab, precision=a.precision, gemm=a.gemm)
+        r = tune.autotune_walker(ctx, torch, stream, lambda st: afqmc.afqmc_recompute_G(ctx.h, None, st),
+                                 min(a.tune_slices, a.M), a.stab, floor=a.floor, cache=tune.TuneCache(a.tune),
+                                 key=key, k_max=128 if a.precision == "fp32" else 64)
+        a.k, a.nb = r["k"].value, r["nb"].value
+        tuned = {"k": r["k"].value, "k_ms": r["k"].ms, "nb": r["nb"].value, "nb_ms": r["nb"].ms,
+                 "nb_acceptance": r["nb"].acceptance, "cached": not r["k_trials"] and not r["nb_trials"]}
     order = [(l, +1) for l in range(1, a.M + 1)] + [(l, -1) for l in range(a.M, 0, -1)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -66,9 +86,11 @@ def main(argv=None):
     dt = time.perf_counter() - t0
     e, s = ctx.measure_energy(stream=stream)
     ctx.close()
-    print(json.dumps({"L": L, "slices": a.slices, "mode": a.mode, "k": a.k, "nb": a.nb,
-                      "precision": a.precision, "gemm": a.gemm, "seconds": dt,
-                      "field_updates_per_s": N * a.slices / dt, "energy": float(e[0])}))
+    out = {"L": L, "slices": a.slices, "mode": a.mode, "k": a.k, "nb": a.nb, "precision": a.precision,
+           "gemm": a.gemm, "seconds": dt, "field_updates_per_s": N * a.slices / dt, "energy": float(e[0])}
+    if tuned is not None:
+        out["tuned"] = tuned
+    print(json.dumps(out))
 
 
 def main_soc(a):

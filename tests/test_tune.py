@@ -230,3 +230,65 @@ def test_autotune_walker_with_a_lower_floor_takes_larger_blocks():
     r = tune.autotune_walker(ctx, _ClockTorch(ctx), None, ctx.recompute, 5, 5, k_candidates=[32],
                              nb_candidates=[4, 16, 32], floor=0.3)
     assert r["k"].value == 32 and r["nb"].value == 16
+
+
+def test_run_cli_tunes_then_walks_with_the_choice(tmp_path, monkeypatch, capsys):
+    """`python -m paper_2506_09611_gb300.run --tune CACHE`: the trials run once, the walk uses the
+    chosen k and n_b, and a second run reads the cache without trial walks (fake device)."""
+    import json
+
+    import numpy as np
+
+    torch = pytest.importorskip("torch")
+    from paper_2506_09611_gb300 import afqmc, run
+
+    made = []
+
+    class Ctx(_FakeContext):
+        def __init__(self, M, **kw):
+            super().__init__(M=M, stab=kw["stab_every"], n_walkers=1)
+            self.h = object()
+            self.modes = []
+            made.append(self)
+
+        def init_walkers(self, *a, **kw):
+            pass
+
+        def sweep_slice(self, ell, direction, mode, k=32, nb=4, want_stats=False, stream=None):
+            self.modes.append((mode, k, nb))
+            return super().sweep_slice(ell, direction, mode, k, nb, want_stats, stream)
+
+        def measure_energy(self, stream=None):
+            return np.array([-1.0]), np.array([1.0])
+
+        def close(self):
+            pass
+
+    class Ev:
+        def __init__(self, enable_timing=True):
+            self.t = 0.0
+
+        def record(self, stream=None):
+            self.t = made[-1].clock
+
+        def elapsed_time(self, other):
+            return other.t - self.t
+
+    monkeypatch.setattr(afqmc, "load", lambda *a: None)
+    monkeypatch.setattr(afqmc, "Context", Ctx)
+    monkeypatch.setattr(afqmc, "afqmc_recompute_G", lambda h, n, st: made[-1].recompute(st))
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "Event", Ev)
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "fake")
+    cache = str(tmp_path / "tune.json")
+    argv = ["--L", "4", "--M", "10", "--stab", "5", "--slices", "4", "--mode", "blockfb", "--tune", cache,
+            "--tune-slices", "5"]
+    run.main(argv)
+    out = json.loads(capsys.readouterr().out)
+    assert (out["k"], out["nb"]) == (16, 8) and out["tuned"]["cached"] is False
+    assert made[-1].modes[-4:] == [("blockfb", 16, 8)] * 4  # the walk itself
+    run.main(argv)
+    out2 = json.loads(capsys.readouterr().out)
+    assert (out2["k"], out2["nb"]) == (16, 8) and out2["tuned"]["cached"] is True
+    assert made[-1].modes == [("blockfb", 16, 8)] * 4  # no trial walks with a cached choice
