@@ -221,6 +221,17 @@ int afqmc_set_profiling(afqmc_ctx* ctx, int on);
  * profiling on run uncaptured.  The uniforms stay fresh because the visit counter that keys them
  * lives on the device.  Returns AFQMC_ERR_ARG for a NULL ctx. */
 int afqmc_set_graphs(afqmc_ctx* ctx, int on);
+
+/* How the wrap G <- B G B^{-1} (Eqs. BlMat, GrFMat) forms E G and G E^{-1}, E = exp(-dtau K):
+ *   AFQMC_WRAP_DENSE      two dense N x N products (the default; tensor cores for FP32 bulk);
+ *   AFQMC_WRAP_SEPARABLE  the periodic L x L lattice has E = Ex (x) Ex, so each product is two
+ *                         L-point passes over one index of G (2 L N^2 instead of N^3 multiply-adds),
+ *                         in the bulk precision, with the field scalings folded into the passes.
+ * Applies to the following slices.  AFQMC_ERR_ARG for a NULL ctx, an unknown mode, or (separable)
+ * a walker lattice whose tile does not fit on chip. */
+#define AFQMC_WRAP_DENSE 0
+#define AFQMC_WRAP_SEPARABLE 1
+int afqmc_set_wrap(afqmc_ctx* ctx, int mode);
 /* Sync the last stream and return, per phase, the summed device milliseconds, the number of
  * bracketed intervals, and the number of library kernels launched in that phase.  Each array
  * has AFQMC_NPHASE entries; any pointer may be NULL. */

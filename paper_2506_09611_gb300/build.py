@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libafqmc.so")
-SOURCES = ["abi.cu", "sweep.cu", "gemm.cu", "setup.cu", "flips.cu", "tc_gemm.cu", "lu.cu", "soc.cu", "ozaki.cu"]
+SOURCES = ["abi.cu", "sweep.cu", "gemm.cu", "setup.cu", "flips.cu", "tc_gemm.cu", "lu.cu", "soc.cu", "ozaki.cu",
+           "sepwrap.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

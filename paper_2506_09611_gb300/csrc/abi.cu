@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "sepwrap.cuh"
 
 namespace afq {
 static std::atomic<long long> g_launches{0};
@@ -25,7 +26,8 @@ struct Lattice {
     double* Einv64 = nullptr;
     void* Eb = nullptr;
     void* Einvb = nullptr;
-    double* Ex64 = nullptr;  // L x L: exp(-dtau K) = Ex (x) Ex for the periodic square lattice
+    double* Ex64 = nullptr;   // L x L: exp(-dtau K) = Ex (x) Ex for the periodic square lattice
+    double* Exi64 = nullptr;  // L x L: exp(+dtau K) = Exi (x) Exi
 };
 
 // A group of walkers with the same lattice and particle numbers.  Every per-walker buffer holds
@@ -132,6 +134,7 @@ struct afqmc_ctx {
     int sticky = 0;
     int nsm = 0;
     bool graphs = false;  // replay captured slices (afqmc_set_graphs)
+    bool sep_wrap = false;  // wrap with the separable L-point passes (afqmc_set_wrap)
     std::vector<Lattice*> lats;
     std::vector<Walker*> w;                        // walker groups
     std::vector<std::pair<int, int>> wmap;         // context walker -> (group, member)
@@ -272,7 +275,9 @@ static cudaError_t fill_lattice(afqmc_ctx* ctx, Lattice* l, cudaStream_t st) {
     if ((e = dalloc(ctx->allocs, (char**)&l->Eb, n2 * esize(ctx))) != cudaSuccess) return e;
     if ((e = dalloc(ctx->allocs, (char**)&l->Einvb, n2 * esize(ctx))) != cudaSuccess) return e;
     if ((e = dalloc(ctx->allocs, &l->Ex64, (size_t)L * L * 8)) != cudaSuccess) return e;
+    if ((e = dalloc(ctx->allocs, &l->Exi64, (size_t)L * L * 8)) != cudaSuccess) return e;
     if ((e = launch_expK1d(st, L, ctx->p.t, ctx->p.dtau, l->Ex64)) != cudaSuccess) return e;
+    if ((e = launch_expK1d(st, L, ctx->p.t, -ctx->p.dtau, l->Exi64)) != cudaSuccess) return e;
     if ((e = launch_expK(st, L, ctx->p.t, ctx->p.dtau, l->E64, l->ld)) != cudaSuccess) return e;
     if ((e = launch_expK(st, L, ctx->p.t, -ctx->p.dtau, l->Einv64, l->ld)) != cudaSuccess) return e;
     if (ctx->p.precision == AFQMC_PREC_FP64) {
@@ -921,6 +926,15 @@ static int sweep_impl(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int k,
         PhaseScope ps(ctx, AFQMC_PHASE_WRAP, st);
         cudaError_t e = launch_field_scales_T<T>(st, xl, N, ctx->c, d, dinv, N, nwk, bt.xstride);
         if (e != cudaSuccess) return e;
+        if (ctx->sep_wrap) {
+            // E = Ex (x) Ex: two passes per product, in place, both spins of every walker
+            SepArgs a1, a2;
+            sep_wrap_passes(direction, G0, ld, (long)N * ld, w->L, nb2, w->lat->Ex64, w->lat->Exi64, d, dinv, N, &a1,
+                            &a2);
+            PhaseScope pg(ctx, AFQMC_PHASE_WRAP_GEMM, st);
+            if ((e = launch_sep<T>(st, a1)) != cudaSuccess) return e;
+            return launch_sep<T>(st, a2);
+        }
         if (use_tc) {
             // E and Einv are symmetric, so both products are A * Bt^T with K-major operands:
             //   forward : S^T = (G Einv)^T ;  G = D (E S) D^{-1}
@@ -1378,6 +1392,18 @@ int afqmc_get_info(afqmc_ctx* ctx, int walker, int* N, int* n_up, int* n_dn, int
 int afqmc_set_graphs(afqmc_ctx* ctx, int on) {
     if (!ctx) return AFQMC_ERR_ARG;
     ctx->graphs = on != 0;
+    return AFQMC_OK;
+}
+
+int afqmc_set_wrap(afqmc_ctx* ctx, int mode) {
+    if (!ctx || (mode != AFQMC_WRAP_DENSE && mode != AFQMC_WRAP_SEPARABLE)) return AFQMC_ERR_ARG;
+    if (mode == AFQMC_WRAP_SEPARABLE) {
+        for (auto* w : ctx->w) {
+            const int ok = ctx->p.precision == AFQMC_PREC_FP64 ? sep_width<double>(w->L, w->N) : sep_width<float>(w->L, w->N);
+            if (!ok) return AFQMC_ERR_ARG;
+        }
+    }
+    ctx->sep_wrap = mode == AFQMC_WRAP_SEPARABLE;
     return AFQMC_OK;
 }
 

@@ -242,6 +242,16 @@ struct Batch {
 template <typename T>
 int window_max();      // largest window (sites) the chain kernel holds in shared memory
 
+// Separable wrap products (sepwrap.cu, tile code in sepwrap.cuh): G <- (A (x) A) G (side 0) or
+// G <- G (A (x) A) (side 1) for the batch of N x N matrices of a SepArgs, with its optional row /
+// column scalings before and after.  cudaErrorInvalidValue when N != L^2 or no tile of at least
+// 4 columns fits on chip.  sep_width: the tile width launch_sep uses (0: none fits).
+struct SepArgs;
+template <typename T>
+int sep_width(int L, int N);
+template <typename T>
+cudaError_t launch_sep(cudaStream_t st, const SepArgs& a);
+
 template <typename T>
 cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T* Gd, int8_t* xl, const double* u,
                                 const uint8_t* replay, const SiteParams& sp, SliceOut so, int s0, int n, int nb,

@@ -1,0 +1,59 @@
+// sepwrap.cu -- the device kernel and launcher of the separable wrap (tile code in sepwrap.cuh):
+// one block per tile and matrix, 256 threads, the tile's two buffers in dynamic shared memory.
+#include "internal.h"
+#include "sepwrap.cuh"
+
+namespace afq {
+
+namespace {
+
+struct BlockSync {
+    SEP_HD void operator()() const {
+#ifdef __CUDA_ARCH__
+        __syncthreads();
+#endif
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) sep_kernel(SepArgs a) {
+    extern __shared__ __align__(16) unsigned char sep_smem[];
+    sep_tile<T>(a, blockIdx.x, blockIdx.y, threadIdx.x, blockDim.x, sep_smem, BlockSync());
+}
+
+constexpr size_t SEP_SMEM_CAP = 220 * 1024;
+
+}  // namespace
+
+template <typename T>
+int sep_width(int L, int N) {
+    int w = 16;
+    while (w > 4 && sep_smem_bytes<T>(L, N, w) > SEP_SMEM_CAP) w /= 2;
+    return sep_smem_bytes<T>(L, N, w) <= SEP_SMEM_CAP ? w : 0;
+}
+
+template <typename T>
+cudaError_t launch_sep(cudaStream_t st, const SepArgs& a0) {
+    SepArgs a = a0;
+    if (a.L < 2 || a.N != a.L * a.L || a.batch < 1 || a.ld < a.N || (a.side != 0 && a.side != 1) || !a.G || !a.A)
+        return cudaErrorInvalidValue;
+    a.w = sep_width<T>(a.L, a.N);
+    if (a.w == 0) return cudaErrorInvalidValue;  // the lattice is too large for an on-chip tile
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute((void*)sep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SEP_SMEM_CAP);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    count_launch();
+    sep_kernel<T><<<dim3((a.N + a.w - 1) / a.w, a.batch), 256, sep_smem_bytes<T>(a.L, a.N, a.w), st>>>(a);
+    return cudaGetLastError();
+}
+
+template int sep_width<float>(int, int);
+template int sep_width<double>(int, int);
+template cudaError_t launch_sep<float>(cudaStream_t, const SepArgs&);
+template cudaError_t launch_sep<double>(cudaStream_t, const SepArgs&);
+
+}  // namespace afq

@@ -123,6 +123,7 @@ def test_every_entry_point_rejects_a_null_context_without_the_device():
     assert lib.afqmc_get_ratios(None, 0, p(d)) == ARG
     assert lib.afqmc_get_info(None, 0, p(ip), p(ip), p(ip), p(ip), p(ip)) == ARG
     assert lib.afqmc_set_graphs(None, 1) == ARG
+    assert lib.afqmc_set_wrap(None, 1) == ARG
     assert lib.afqmc_set_profiling(None, 1) == ARG
     assert lib.afqmc_get_profile(None, p(d), p(i64), p(i64)) == ARG
     assert lib.afqmc_soc_destroy(None) == 0
