@@ -4,7 +4,8 @@ The no-allocation entry point serves callers that cannot allocate device memory 
 apply an update (a fixed memory budget owned by a host framework, a real-time loop that may not
 call cudaMalloc, a plugin without an allocator).  It must give the same G as the allocating entry
 point, on two calls in a row (its static scratch keeps the previous call's contents).  This file
-is collected last so that a run stopping at its first failure has run every other test first.
+sorts after the main GPU suite so that a run stopping at its first failure has run that suite
+first.
 """
 import numpy as np
 import pytest
