@@ -10,6 +10,8 @@
 // The tile is staged in shared memory with the optional input scaling G_ij *= rs_in[i] cs_in[j],
 // transformed by a pass along x into a second buffer and a pass along y back, and stored with the
 // optional output scaling.  A is symmetric.  Each block owns its tile, so the update is in place.
+// The passes are register-blocked (4 sites x 4 columns per thread, vector loads from shared
+// memory) when L is a multiple of 4, which every configured lattice is.
 //
 // The tile code is written once for the device kernel (sepwrap.cu) and for a host build that runs
 // it serially (one "thread", barriers as no-ops), which lets the index arithmetic be checked on a
@@ -25,6 +27,14 @@
 #endif
 
 namespace afq {
+
+#ifndef __CUDA_ARCH__
+// Host build only: the number of vector accesses so far that would be misaligned on the device.
+inline int& sep_misaligned_count() {
+    static int n = 0;
+    return n;
+}
+#endif
 
 struct SepArgs {
     void* G = nullptr;       // batch matrices N x N, row-major with leading dimension ld, batch stride sG
@@ -46,8 +56,89 @@ SEP_HD inline size_t sep_smem_bytes(int L, int N, int w) {
     return ((size_t)L * L + 2 * (size_t)N * w) * sizeof(T);
 }
 
+// Four consecutive elements, one vector access on the device (16-byte aligned: float4, or two
+// double2).  The host build counts accesses that would be misaligned, since those fault on the
+// device.
+template <typename T>
+SEP_HD inline void sep_ld4(const T* p, T v[4]) {
+#ifdef __CUDA_ARCH__
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = *(const float4*)p;
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const double2 q0 = *(const double2*)p, q1 = *((const double2*)p + 1);
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    }
+#else
+    if (((size_t)p) % 16 != 0) ++sep_misaligned_count();
+    for (int q = 0; q < 4; ++q) v[q] = p[q];
+#endif
+}
+template <typename T>
+SEP_HD inline void sep_st4(T* p, const T v[4]) {
+#ifdef __CUDA_ARCH__
+    if constexpr (sizeof(T) == 4) {
+        *(float4*)p = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        *(double2*)p = make_double2(v[0], v[1]);
+        *((double2*)p + 1) = make_double2(v[2], v[3]);
+    }
+#else
+    if (((size_t)p) % 16 != 0) ++sep_misaligned_count();
+    for (int q = 0; q < 4; ++q) p[q] = v[q];
+#endif
+}
+
+// One L-point pass over the site index k = x + L y of the N x w buffer src (row k, column c),
+// into dst: along x (dim 0) dst[(x, y)][c] = sum_x' A[x][x'] src[(x', y)][c]; along y (dim 1)
+// dst[(x, y)][c] = sum_y' A[y][y'] src[(x, y')][c].  With L and w multiples of 4 each thread
+// computes 4 sites x 4 columns from one vector load of A and one of src per step (A is
+// symmetric, so its row is also its column); otherwise one output at a time.
+template <typename T>
+SEP_HD inline void sep_pass(const T* As, const T* src, T* dst, int L, int N, int w, int dim, int tid, int nt) {
+    if (L % 4 == 0 && w % 4 == 0) {
+        const int L4 = L / 4, w4 = w / 4, items = L * L4 * w4;
+        for (int it = tid; it < items; it += nt) {
+            const int cb = it % w4, rest = it / w4, ob = rest % L4, fixed = rest / L4;
+            // dim 0: fixed = y, outputs x = 4 ob + r; dim 1: fixed = x, outputs y = 4 ob + r
+            const long step = dim == 0 ? (long)w : (long)L * w;             // next x' (dim 0) or y' (dim 1)
+            const long base = dim == 0 ? (long)L * fixed * w : (long)fixed * w;
+            T acc[4][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+            for (int p = 0; p < L; ++p) {
+                T a[4], b[4];
+                sep_ld4(As + (size_t)p * L + 4 * ob, a);                // A[4 ob + r][p] = A[p][4 ob + r]
+                sep_ld4(src + base + p * step + 4 * cb, b);             // src[site p][4 cb + j]
+                for (int r = 0; r < 4; ++r)
+                    for (int j = 0; j < 4; ++j) acc[r][j] += a[r] * b[j];
+            }
+            for (int r = 0; r < 4; ++r) {
+                const int k = dim == 0 ? (4 * ob + r) + L * fixed : fixed + L * (4 * ob + r);
+                sep_st4(dst + (size_t)k * w + 4 * cb, acc[r]);
+            }
+        }
+        return;
+    }
+    for (int e = tid; e < N * w; e += nt) {
+        const int k = e / w, c = e - k * w;
+        const int y = k / L, x = k - y * L;
+        T acc = 0;
+        if (dim == 0) {
+            const T* col = src + (size_t)(L * y) * w + c;
+            for (int p = 0; p < L; ++p) acc += As[x * L + p] * col[(size_t)p * w];
+        } else {
+            const T* col = src + (size_t)x * w + c;
+            for (int p = 0; p < L; ++p) acc += As[y * L + p] * col[(size_t)(L * p) * w];
+        }
+        dst[(size_t)k * w + c] = acc;
+    }
+}
+
 // One tile (index t along the tiled dimension) of matrix z.  tid / nt: this thread and the
-// block size; smem: sep_smem_bytes<T> bytes; sync(): a block-wide barrier.
+// block size; smem: sep_smem_bytes<T> bytes (16-byte aligned); sync(): a block-wide barrier.
+// The tile is held as an N x w buffer (row k = the transformed index, column c): side 0 keeps
+// G's columns o0 + c, side 1 holds G's rows o0 + c transposed, since (G A)[r][k] =
+// sum_k' A[k][k'] G[r][k'] for a symmetric A.  Columns c >= wt of a ragged tile are zero-filled
+// and never stored (each column is transformed on its own, so they do not reach the others).
 template <typename T, typename Sync>
 SEP_HD inline void sep_tile(const SepArgs& a, int t, int z, int tid, int nt, unsigned char* smem, Sync sync) {
     const int L = a.L, N = a.N, w = a.w;
@@ -60,67 +151,76 @@ SEP_HD inline void sep_tile(const SepArgs& a, int t, int z, int tid, int nt, uns
     const T* ro = a.rs_out ? (const T*)a.rs_out + (size_t)z * a.sv : nullptr;
     const T* co = a.cs_out ? (const T*)a.cs_out + (size_t)z * a.sv : nullptr;
     T* As = (T*)smem;                 // [L][L]
-    T* S0 = As + (size_t)L * L;       // the tile; side 0: [N][w] (k, c), side 1: [w][N] (r, k)
-    T* S1 = S0 + (size_t)N * w;       // after the pass along x
+    T* S0 = As + (size_t)L * L;       // [N][w]
+    T* S1 = S0 + (size_t)N * w;       // [N][w]
     for (int e = tid; e < L * L; e += nt) As[e] = (T)a.A[e];
-    // stage: consecutive e run along a row of G (coalesced)
+    // Side 1 moves four consecutive k of one row per thread (one 16-byte global access, a 2-way
+    // shared-memory conflict on the transposed store) when the lattice allows it.
+    const bool quad = a.side == 1 && L % 4 == 0 && a.ld % 4 == 0 && ((size_t)G) % 16 == 0;
+    if (quad) {
+        const int items = (N / 4) * w;
+        for (int it = tid; it < items; it += nt) {
+            const int c = it % w, k0 = 4 * (it / w);
+            T v[4] = {0, 0, 0, 0};
+            if (c < wt) {
+                const int row = o0 + c;
+                sep_ld4(G + (size_t)row * a.ld + k0, v);
+                for (int q = 0; q < 4; ++q) {
+                    if (ri) v[q] *= ri[row];
+                    if (ci) v[q] *= ci[k0 + q];
+                }
+            }
+            for (int q = 0; q < 4; ++q) S0[(size_t)(k0 + q) * w + c] = v[q];
+        }
+    } else {
+        // consecutive e run along a row of G (coalesced); side 1 stores transposed
+        for (int e = tid; e < N * w; e += nt) {
+            int row, col, s, c;
+            if (a.side == 0) {
+                const int k = e / w;
+                c = e - k * w;
+                row = k; col = o0 + c; s = k * w + c;
+            } else {
+                c = e / N;
+                const int k = e - c * N;
+                row = o0 + c; col = k; s = k * w + c;
+            }
+            T v = 0;
+            if (c < wt) {
+                v = G[(size_t)row * a.ld + col];
+                if (ri) v *= ri[row];
+                if (ci) v *= ci[col];
+            }
+            S0[s] = v;
+        }
+    }
+    sync();
+    sep_pass<T>(As, S0, S1, L, N, w, 0, tid, nt);
+    sync();
+    sep_pass<T>(As, S1, S0, L, N, w, 1, tid, nt);
+    sync();
+    if (quad) {
+        const int items = (N / 4) * wt;
+        for (int it = tid; it < items; it += nt) {
+            const int c = it % wt, k0 = 4 * (it / wt), row = o0 + c;
+            T v[4];
+            for (int q = 0; q < 4; ++q) {
+                v[q] = S0[(size_t)(k0 + q) * w + c];
+                if (ro) v[q] *= ro[row];
+                if (co) v[q] *= co[k0 + q];
+            }
+            sep_st4(G + (size_t)row * a.ld + k0, v);
+        }
+        return;
+    }
     for (int e = tid; e < N * wt; e += nt) {
         int row, col, s;
         if (a.side == 0) {
             const int k = e / wt, c = e - k * wt;
             row = k; col = o0 + c; s = k * w + c;
         } else {
-            const int r = e / N, k = e - r * N;
-            row = o0 + r; col = k; s = r * N + k;
-        }
-        T v = G[(size_t)row * a.ld + col];
-        if (ri) v *= ri[row];
-        if (ci) v *= ci[col];
-        S0[s] = v;
-    }
-    sync();
-    // pass along x: site k = x + L y takes sum_x' A[x][x'] S0[(x', y)]
-    for (int e = tid; e < N * wt; e += nt) {
-        int k, c;
-        if (a.side == 0) { k = e / wt; c = e - k * wt; } else { c = e / N; k = e - c * N; }
-        const int y = k / L, x = k - y * L;
-        T acc = 0;
-        if (a.side == 0) {
-            const T* src = S0 + (size_t)(L * y) * w + c;
-            for (int xp = 0; xp < L; ++xp) acc += As[x * L + xp] * src[(size_t)xp * w];
-            S1[(size_t)k * w + c] = acc;
-        } else {
-            const T* src = S0 + (size_t)c * N + L * y;
-            for (int xp = 0; xp < L; ++xp) acc += src[xp] * As[xp * L + x];
-            S1[(size_t)c * N + k] = acc;
-        }
-    }
-    sync();
-    // pass along y: site k = x + L y takes sum_y' A[y][y'] S1[(x, y')]
-    for (int e = tid; e < N * wt; e += nt) {
-        int k, c;
-        if (a.side == 0) { k = e / wt; c = e - k * wt; } else { c = e / N; k = e - c * N; }
-        const int y = k / L, x = k - y * L;
-        T acc = 0;
-        if (a.side == 0) {
-            const T* src = S1 + (size_t)x * w + c;
-            for (int yp = 0; yp < L; ++yp) acc += As[y * L + yp] * src[(size_t)(L * yp) * w];
-            S0[(size_t)k * w + c] = acc;
-        } else {
-            const T* src = S1 + (size_t)c * N + x;
-            for (int yp = 0; yp < L; ++yp) acc += src[L * yp] * As[yp * L + y];
-            S0[(size_t)c * N + k] = acc;
-        }
-    }
-    sync();
-    for (int e = tid; e < N * wt; e += nt) {
-        int row, col, s;
-        if (a.side == 0) {
-            const int k = e / wt, c = e - k * wt;
-            row = k; col = o0 + c; s = k * w + c;
-        } else {
-            const int r = e / N, k = e - r * N;
-            row = o0 + r; col = k; s = r * N + k;
+            const int c = e / N, k = e - c * N;
+            row = o0 + c; col = k; s = k * w + c;
         }
         T v = S0[s];
         if (ro) v *= ro[row];

@@ -28,6 +28,9 @@ extern "C" void sep_host_pass(int fp64, int side, int L, int w, int batch, void*
     if (fp64) run<double>(a); else run<float>(a);
 }
 
+// Vector accesses so far that would be misaligned on the device (must stay 0).
+extern "C" int sep_host_misaligned() { return afq::sep_misaligned_count(); }
+
 // The wrap as the library issues it (sep_wrap_passes), tile width w.
 extern "C" void sep_host_wrap(int fp64, int direction, int L, int w, int batch, void* G, long ld, long sG,
                               const double* Ex, const double* Exi, const void* d, const void* dinv, long sv) {

@@ -25,7 +25,8 @@ def lib(tmp_path_factory):
     vp, i, l = ctypes.c_void_p, ctypes.c_int, ctypes.c_long
     h.sep_host_pass.argtypes = [i, i, i, i, i, vp, l, l, vp, vp, vp, vp, vp, l]
     h.sep_host_wrap.argtypes = [i, i, i, i, i, vp, l, l, vp, vp, vp, vp, l]
-    return h
+    yield h
+    assert h.sep_host_misaligned() == 0  # no vector access that would fault on the device
 
 
 def chain_factor(L, t, tau):
@@ -42,19 +43,26 @@ def _p(a):
 
 
 def _padded(G, pad, dt):
+    """G in a NaN-padded buffer of leading dimension N + pad, starting on a 64-byte boundary (as
+    cudaMalloc'd memory does)."""
     batch, N, _ = G.shape
-    buf = np.full((batch, N, N + pad), np.nan, dt)
+    n = batch * N * (N + pad)
+    raw = np.full(n + 64, np.nan, dt)
+    off = (-raw.ctypes.data % 64) // raw.itemsize
+    buf = raw[off:off + n].reshape(batch, N, N + pad)
     buf[:, :, :N] = G
     return buf
 
 
 @pytest.mark.parametrize("fp64", [1, 0])
 @pytest.mark.parametrize("side", [0, 1])
-@pytest.mark.parametrize("L,w", [(2, 16), (3, 4), (4, 16), (5, 16), (5, 4), (6, 5), (8, 16)])
+@pytest.mark.parametrize("L,w", [(2, 16), (3, 4), (4, 16), (5, 16), (5, 4), (6, 5), (8, 16), (8, 8), (12, 16),
+                                 (12, 4)])
 @pytest.mark.parametrize("scaled", [False, True])
 def test_pass_is_the_kronecker_product(lib, fp64, side, L, w, scaled):
     rng = np.random.default_rng(100 * L + 10 * w + side)
-    N, batch, pad = L * L, 2, 3
+    N, batch = L * L, 2
+    pad = 4 if L % 2 == 0 else 3  # ld % 4 == 0 takes the vector path of the row tiles
     dt = np.float64 if fp64 else np.float32
     A = chain_factor(L, 1.0, 0.05 * (1 + L % 3))
     G = rng.standard_normal((batch, N, N))
@@ -76,10 +84,11 @@ def test_pass_is_the_kronecker_product(lib, fp64, side, L, w, scaled):
 
 @pytest.mark.parametrize("fp64", [1, 0])
 @pytest.mark.parametrize("direction", [+1, -1])
-@pytest.mark.parametrize("L,w", [(3, 16), (4, 16), (6, 16), (6, 4)])
+@pytest.mark.parametrize("L,w", [(3, 16), (4, 16), (6, 16), (6, 4), (8, 16), (8, 8)])
 def test_wrap_matches_the_oracle(lib, fp64, direction, L, w):
     rng = np.random.default_rng(7 * L + w + (direction > 0))
-    N, pad, t, U, dtau = L * L, 5, 1.0, 4.0, 0.05
+    N, t, U, dtau = L * L, 1.0, 4.0, 0.05
+    pad = (-N) % 32  # the library's leading dimension: N rounded up to 32
     dt = np.float64 if fp64 else np.float32
     m = oracle.Model(L, L, t, U, dtau, 4)
     xl = np.where(rng.random(N) < 0.5, 1, -1).astype(np.int8)
