@@ -61,6 +61,16 @@ def parse():
     return ap.parse_args()
 
 
+def optional_leg(name, fn):
+    """Run an auxiliary leg of the JSON line.  The device-timed sweep above it is the headline;
+    a leg that raises is reported in the line as {"error": ...} instead of losing the line."""
+    try:
+        return fn()
+    except Exception as ex:  # noqa: BLE001 -- reported, not swallowed
+        print(f"bench: {name} leg failed: {ex!r}", file=sys.stderr, flush=True)
+        return {"error": f"{type(ex).__name__}: {ex}"}
+
+
 def max_over_ranks(dist, ms, device):
     """The slowest rank's time: every rank's timed region ends at the same barrier, so the job's
     time is the maximum (all_reduce MAX over the process group)."""
@@ -330,21 +340,24 @@ def main():
     # ---------------- end to end through the C ABI with host buffers ----------------
     e2e = None
     if not args.no_e2e:
-        e2e = end_to_end(afqmc, torch, stream, args, seed, rank)
+        e2e = optional_leg("e2e", lambda: end_to_end(afqmc, torch, stream, args, seed, rank))
 
     ctx.close()
     batch = None
     if not args.no_batch:
-        batch = batched_population(afqmc, torch, stream, args, seed)
+        batch = optional_leg("batched_population", lambda: batched_population(afqmc, torch, stream, args, seed))
     soc_res = None
     if not args.no_soc:
-        soc_res = soc_leg(torch, stream, args, seed)
+        soc_res = optional_leg("soc", lambda: soc_leg(torch, stream, args, seed))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, secs = run_oracle_sample(CPU_SLICES, args.k)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%d slice-steps (wrap + delayed update, k=%d) of the FP64 oracle at 40x40 from its own "
-                         "G(0) (M=10 init not timed); %.1f s of CPU work" % (CPU_SLICES, args.k, secs)}
+        def cpu_leg():
+            v, cores, secs = run_oracle_sample(CPU_SLICES, args.k)
+            return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                    "sample": "%d slice-steps (wrap + delayed update, k=%d) of the FP64 oracle at 40x40 from its "
+                              "own G(0) (M=10 init not timed); %.1f s of CPU work" % (CPU_SLICES, args.k, secs)}
+
+        cpu = optional_leg("cpu_baseline", cpu_leg)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

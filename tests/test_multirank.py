@@ -50,3 +50,16 @@ def test_single_rank_throughput():
     import bench
 
     assert bench.job_throughput(1, 256000, 3, 1500.0) == pytest.approx(256000 * 3 / 1.5)
+
+
+def test_an_auxiliary_leg_that_fails_is_reported_in_the_line(capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.optional_leg("soc", lambda: {"value": 1.0}) == {"value": 1.0}
+
+    def boom():
+        raise RuntimeError("afqmc_soc_sweep_slice failed: -3")
+
+    assert bench.optional_leg("soc", boom) == {"error": "RuntimeError: afqmc_soc_sweep_slice failed: -3"}
+    assert "soc leg failed" in capsys.readouterr().err
