@@ -5,6 +5,7 @@ through the C ABI (used for kernel profiling and quick timing).
     python -m paper_2506_09611_gb300.run --L 40 --U 6 --slices 20 --mode delayed --k 64
     python -m paper_2506_09611_gb300.run --soc --L 24 --U -4 --lam 0.5 --slices 12 --mode blockfb --nb 16
     python -m paper_2506_09611_gb300.run --L 40 --tune tune.json --slices 20 --mode blockfb
+    python -m paper_2506_09611_gb300.run --L 40 --wrap separable --slices 20
 
 With --tune CACHE (Hubbard model) the delay rank and the block size are first chosen by timed
 trial walks (tune.autotune_walker: k by time, n_b by time under the acceptance floor) or read
@@ -43,12 +44,14 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--soc", action="store_true", help="the spin-orbit-coupled model at half filling")
     ap.add_argument("--lam", type=float, default=0.5)
+    ap.add_argument("--wrap", default="dense", choices=["dense", "separable"],
+                    help="wrap products: dense N x N, or two L-point passes with exp(-dtau K) = Ex (x) Ex")
     ap.add_argument("--tune", metavar="CACHE", help="choose k and nb by timed trials (cached in this JSON file)")
     ap.add_argument("--tune-slices", type=int, default=10, help="slices of each trial walk (out and back)")
     ap.add_argument("--floor", type=float, default=tune.ACCEPTANCE_FLOOR, help="block force-bias acceptance floor")
     a = ap.parse_args(argv)
-    if a.tune and a.soc:
-        ap.error("--tune covers the Hubbard model only")
+    if a.soc and (a.tune or a.wrap != "dense"):
+        ap.error("--tune and --wrap cover the Hubbard model only")
     if a.soc:
         return main_soc(a)
 
@@ -63,6 +66,8 @@ def main(argv=None):
     ctx = afqmc.Context(a.M, dtau=a.dtau, U=a.U, t=a.t, precision=a.precision, stab_every=a.stab, seed=a.seed,
                         gemm=a.gemm)
     ctx.init_walkers([L], [ns], [ns], np.concatenate([P.ravel(), P.ravel()]), X, stream=stream)
+    if a.wrap != "dense":
+        ctx.set_wrap(a.wrap)
     tuned = None
     if a.tune:
         key = tune.workload_key(device=torch.cuda.get_device_name(), L=L, n_up=ns, n_dn=ns, U=a.U, t=a.t,
@@ -87,7 +92,8 @@ def main(argv=None):
     e, s = ctx.measure_energy(stream=stream)
     ctx.close()
     out = {"L": L, "slices": a.slices, "mode": a.mode, "k": a.k, "nb": a.nb, "precision": a.precision,
-           "gemm": a.gemm, "seconds": dt, "field_updates_per_s": N * a.slices / dt, "energy": float(e[0])}
+           "gemm": a.gemm, "wrap": a.wrap, "seconds": dt, "field_updates_per_s": N * a.slices / dt,
+           "energy": float(e[0])}
     if tuned is not None:
         out["tuned"] = tuned
     print(json.dumps(out))

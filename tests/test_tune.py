@@ -261,6 +261,9 @@ def test_run_cli_tunes_then_walks_with_the_choice(tmp_path, monkeypatch, capsys)
         def measure_energy(self, stream=None):
             return np.array([-1.0]), np.array([1.0])
 
+        def set_wrap(self, mode):
+            self.wrap = mode
+
         def close(self):
             pass
 
@@ -292,3 +295,8 @@ def test_run_cli_tunes_then_walks_with_the_choice(tmp_path, monkeypatch, capsys)
     out2 = json.loads(capsys.readouterr().out)
     assert (out2["k"], out2["nb"]) == (16, 8) and out2["tuned"]["cached"] is True
     assert made[-1].modes == [("blockfb", 16, 8)] * 4  # no trial walks with a cached choice
+    run.main(argv + ["--wrap", "separable"])
+    out3 = json.loads(capsys.readouterr().out)
+    assert out3["wrap"] == "separable" and made[-1].wrap == "separable"
+    with pytest.raises(SystemExit):
+        run.main(["--soc", "--wrap", "separable"])
