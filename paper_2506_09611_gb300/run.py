@@ -7,9 +7,9 @@ through the C ABI (used for kernel profiling and quick timing).
     python -m paper_2506_09611_gb300.run --L 40 --tune tune.json --slices 20 --mode blockfb
     python -m paper_2506_09611_gb300.run --L 40 --wrap separable --slices 20
 
-With --tune CACHE (Hubbard model) the delay rank and the block size are first chosen by timed
-trial walks (tune.autotune_walker: k by time, n_b by time under the acceptance floor) or read
-from the JSON cache for this device and workload; the walk then runs with the chosen values.
+With --tune CACHE the delay rank and the block size are first chosen by timed trial walks
+(tune.autotune_walker: k by time, n_b by time under the acceptance floor) or read from the JSON
+cache for this device and workload; the walk then runs with the chosen values.
 
 The walk goes forward from slice 1 and turns at slice M, with the FP64 recompute at every
 multiple of --stab, exactly as in a full sweep; the inputs are the seeded synthetic trial
@@ -50,8 +50,8 @@ def main(argv=None):
     ap.add_argument("--tune-slices", type=int, default=10, help="slices of each trial walk (out and back)")
     ap.add_argument("--floor", type=float, default=tune.ACCEPTANCE_FLOOR, help="block force-bias acceptance floor")
     a = ap.parse_args(argv)
-    if a.soc and (a.tune or a.wrap != "dense"):
-        ap.error("--tune and --wrap cover the Hubbard model only")
+    if a.soc and a.wrap != "dense":
+        ap.error("--wrap covers the Hubbard model only (the spin-orbit propagator does not factor)")
     if a.soc:
         return main_soc(a)
 
@@ -112,6 +112,22 @@ def main_soc(a):
     X = inputs.initial_fields(a.M, N, seed=a.seed)
     ctx = soc.SocContext(L, a.M, n_e, 1, a.precision, a.gemm, a.stab, a.t, a.lam, a.U, a.dtau, a.seed)
     ctx.init(P, X, stream=stream)
+    tuned = None
+    if a.tune:
+        def counted(ell, d, nb):  # one block force-bias slice; accepted blocks from the decisions
+            ctx.sweep_slice(ell, d, "blockfb", k=a.k, nb=nb, stream=stream)
+            nblk = (N + nb - 1) // nb
+            return int(ctx.decisions(0)[N:N + nblk].sum()), nblk
+
+        key = tune.workload_key(device=torch.cuda.get_device_name(), model="soc", L=L, n_e=n_e, U=a.U, t=a.t,
+                                lam=a.lam, dtau=a.dtau, M=a.M, stab=a.stab, precision=a.precision, gemm=a.gemm)
+        kmax = soc.KMAX[a.precision]
+        r = tune.autotune_walker(ctx, torch, stream, lambda st: soc.afqmc_soc_recompute_G(ctx.h, None, st),
+                                 min(a.tune_slices, a.M), a.stab, floor=a.floor, cache=tune.TuneCache(a.tune),
+                                 key=key, k_max=kmax, nb_max=kmax, counted=counted)
+        a.k, a.nb = r["k"].value, r["nb"].value
+        tuned = {"k": r["k"].value, "k_ms": r["k"].ms, "nb": r["nb"].value, "nb_ms": r["nb"].ms,
+                 "nb_acceptance": r["nb"].acceptance, "cached": not r["k_trials"] and not r["nb_trials"]}
     order = [(l, +1) for l in range(1, a.M + 1)] + [(l, -1) for l in range(a.M, 0, -1)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -125,9 +141,12 @@ def main_soc(a):
     dt = time.perf_counter() - t0
     e = ctx.measure_energy(stream=stream)
     ctx.close()
-    print(json.dumps({"model": "soc", "L": L, "slices": a.slices, "mode": a.mode, "k": a.k, "nb": a.nb,
-                      "precision": a.precision, "gemm": a.gemm, "seconds": dt,
-                      "field_updates_per_s": N * a.slices / dt, "energy": [e[0].real, e[0].imag]}))
+    out = {"model": "soc", "L": L, "slices": a.slices, "mode": a.mode, "k": a.k, "nb": a.nb,
+           "precision": a.precision, "gemm": a.gemm, "seconds": dt, "field_updates_per_s": N * a.slices / dt,
+           "energy": [e[0].real, e[0].imag]}
+    if tuned is not None:
+        out["tuned"] = tuned
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

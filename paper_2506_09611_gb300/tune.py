@@ -181,17 +181,25 @@ def time_on_stream(torch, stream, fn: Callable[[], None], n: int = 1) -> float:
     return a.elapsed_time(b) / n
 
 
-def _walk(ctx, stream, mode, k, nb, slices, stab_every, recompute, direction, want_stats):
+def _walk(ctx, stream, mode, k, nb, slices, stab_every, recompute, direction, want_stats, counted=None):
     """Slices 1..slices forward (direction +1) or slices..1 backward, with the FP64 recompute at
     every multiple of stab_every the walker reaches; returns (accepts, proposals) summed over the
-    context's walkers when want_stats, else (0, 0)."""
+    context's walkers when want_stats, else (0, 0).  counted (nullable) runs one counted slice
+    itself, counted(ell, direction, nb) -> (accepts, proposals), for contexts whose sweep_slice
+    returns no statistics."""
     acc = prop = 0
     ells = range(1, slices + 1) if direction > 0 else range(slices, 0, -1)
     for ell in ells:
-        st = ctx.sweep_slice(ell, direction, mode, k=k, nb=nb, want_stats=want_stats, stream=stream)
-        if want_stats:
+        if want_stats and counted is not None:
+            a, p = counted(ell, direction, nb)
+            acc += a
+            prop += p
+        elif want_stats:
+            st = ctx.sweep_slice(ell, direction, mode, k=k, nb=nb, want_stats=True, stream=stream)
             acc += sum(s.accepts for s in st)
             prop += sum(s.proposals for s in st)
+        else:
+            ctx.sweep_slice(ell, direction, mode, k=k, nb=nb, stream=stream)
         pos = ell if direction > 0 else ell - 1
         if pos % stab_every == 0:
             recompute(stream)
@@ -200,7 +208,7 @@ def _walk(ctx, stream, mode, k, nb, slices, stab_every, recompute, direction, wa
 
 def autotune_walker(ctx, torch, stream, recompute, slices: int, stab_every: int, k_candidates=None,
                     nb_candidates=None, floor: float = ACCEPTANCE_FLOOR, cache: Optional[TuneCache] = None,
-                    key: str = "", k_max: int = 128) -> dict:
+                    key: str = "", k_max: int = 128, nb_max: int = 32, counted=None) -> dict:
     """Delay rank and block size for the walkers of an afqmc Context that sit at slice 0.
 
     Each candidate walks slices 1..`slices` forward and back down to slice 0, so the context
@@ -208,13 +216,14 @@ def autotune_walker(ctx, torch, stream, recompute, slices: int, stab_every: int,
     untimed walk, then the time of one delayed walk there and back.  n_b: the time of the
     block force-bias walk forward, and its acceptance (accepted over proposed blocks, all
     walkers) on the block force-bias walk back.  `recompute(stream)` runs the FP64 recompute
-    the context requires at every multiple of `stab_every` (afqmc_recompute_G).  Returns
-    {"k": Trial, "nb": Trial, "k_trials": [...], "nb_trials": [...]}; cached choices skip
-    their trials."""
+    the context requires at every multiple of `stab_every` (afqmc_recompute_G).  Contexts whose
+    sweep_slice reports no statistics (the spin-orbit-coupled one) pass `counted` (see _walk).
+    Returns {"k": Trial, "nb": Trial, "k_trials": [...], "nb_trials": [...]}; cached choices
+    skip their trials."""
     if not 1 <= slices:
         raise ValueError("slices must be >= 1")
     ks = list(k_candidates) if k_candidates is not None else delay_ranks(k_max, 16)
-    nbs = list(nb_candidates) if nb_candidates is not None else block_sizes()
+    nbs = list(nb_candidates) if nb_candidates is not None else block_sizes(nb_max)
 
     def delayed_round_trip(k):
         _walk(ctx, stream, "delayed", k, 1, slices, stab_every, recompute, +1, False)
@@ -227,7 +236,7 @@ def autotune_walker(ctx, torch, stream, recompute, slices: int, stab_every: int,
     def measure_nb(nb):
         ms = time_on_stream(torch, stream,
                             lambda: _walk(ctx, stream, "blockfb", 1, nb, slices, stab_every, recompute, +1, False))
-        acc, prop = _walk(ctx, stream, "blockfb", 1, nb, slices, stab_every, recompute, -1, True)
+        acc, prop = _walk(ctx, stream, "blockfb", 1, nb, slices, stab_every, recompute, -1, True, counted)
         if prop <= 0:
             raise RuntimeError(f"block size {nb}: no proposals counted")
         return ms, acc / prop

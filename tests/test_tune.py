@@ -300,3 +300,71 @@ def test_run_cli_tunes_then_walks_with_the_choice(tmp_path, monkeypatch, capsys)
     assert out3["wrap"] == "separable" and made[-1].wrap == "separable"
     with pytest.raises(SystemExit):
         run.main(["--soc", "--wrap", "separable"])
+
+
+def test_run_cli_tunes_the_soc_walker_from_its_decisions(tmp_path, monkeypatch, capsys):
+    """`run --soc --tune CACHE`: the spin-orbit-coupled context reports no slice statistics, so
+    the block acceptance comes from its decisions (replay layout: N proposals, then the blocks)."""
+    import json
+
+    import numpy as np
+
+    torch = pytest.importorskip("torch")
+    from paper_2506_09611_gb300 import afqmc, run, soc
+
+    made = []
+
+    class SocCtx:
+        def __init__(self, L, M, n_e, n_walkers, precision, gemm, stab, t, lam, U, dtau, seed):
+            self.inner = _FakeContext(M=M, stab=stab, n_walkers=n_walkers)
+            self.N, self.h, self.last_nb, self.modes = L * L, object(), None, []
+            made.append(self)
+
+        def init(self, P, X, stream=None):
+            pass
+
+        def sweep_slice(self, ell, direction, mode, k=32, nb=16, replay=None, stream=None):
+            self.modes.append((mode, k, nb))
+            self.last_nb = nb
+            self.inner.sweep_slice(ell, direction, mode, k, min(nb, 32), False, stream)
+
+        def decisions(self, walker=0):
+            nb = self.last_nb
+            nblk = (self.N + nb - 1) // nb
+            d = np.zeros(2 * self.N, np.uint8)
+            d[self.N:self.N + round(nblk * math.exp(-nb / 20.0))] = 1
+            return d
+
+        def measure_energy(self, stream=None):
+            return np.array([-1.0 + 0.0j])
+
+        def close(self):
+            pass
+
+    class Ev:
+        def __init__(self, enable_timing=True):
+            self.t = 0.0
+
+        def record(self, stream=None):
+            self.t = made[-1].inner.clock
+
+        def elapsed_time(self, other):
+            return other.t - self.t
+
+    monkeypatch.setattr(afqmc, "load", lambda *a: None)
+    monkeypatch.setattr(soc, "SocContext", SocCtx)
+    monkeypatch.setattr(soc, "afqmc_soc_recompute_G", lambda h, n, st: made[-1].inner.recompute(st))
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "Event", Ev)
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "fake")
+    argv = ["--soc", "--L", "4", "--M", "10", "--stab", "5", "--slices", "3", "--mode", "blockfb", "--tune",
+            str(tmp_path / "t.json"), "--tune-slices", "5"]
+    run.main(argv)
+    out = json.loads(capsys.readouterr().out)
+    # k from {16, 32, 64} (FP32 window limit 64); n_b from {2, ..., 64}: 8 is the largest block whose
+    # acceptance (1 of 2 blocks) reaches 0.5
+    assert out["model"] == "soc" and (out["k"], out["nb"]) == (16, 8)
+    assert out["tuned"]["nb_acceptance"] == 0.5 and out["tuned"]["cached"] is False
+    assert {nb for m, _, nb in made[-1].modes if m == "blockfb"} >= {2, 4, 8, 16, 32, 64}
+    assert made[-1].inner.pos == 3 and made[-1].modes[-3:] == [("blockfb", 16, 8)] * 3
