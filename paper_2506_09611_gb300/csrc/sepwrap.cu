@@ -35,8 +35,10 @@ int sep_width(int L, int N) {
 template <typename T>
 cudaError_t launch_sep(cudaStream_t st, const SepArgs& a0) {
     SepArgs a = a0;
-    if (a.L < 2 || a.N != a.L * a.L || a.batch < 1 || a.ld < a.N || (a.side != 0 && a.side != 1) || !a.G || !a.A)
+    const int ext = a.C > 0 ? a.C : a.N;  // the untransformed extent
+    if (a.L < 2 || a.N != a.L * a.L || a.batch < 1 || a.C < 0 || (a.side != 0 && a.side != 1) || !a.G || !a.A)
         return cudaErrorInvalidValue;
+    if (a.ld < (a.side == 0 ? ext : a.N)) return cudaErrorInvalidValue;
     a.w = sep_width<T>(a.L, a.N);
     if (a.w == 0) return cudaErrorInvalidValue;  // the lattice is too large for an on-chip tile
     static bool attr = false;
@@ -47,7 +49,7 @@ cudaError_t launch_sep(cudaStream_t st, const SepArgs& a0) {
         attr = true;
     }
     count_launch();
-    sep_kernel<T><<<dim3((a.N + a.w - 1) / a.w, a.batch), 256, sep_smem_bytes<T>(a.L, a.N, a.w), st>>>(a);
+    sep_kernel<T><<<dim3((ext + a.w - 1) / a.w, a.batch), 256, sep_smem_bytes<T>(a.L, a.N, a.w), st>>>(a);
     return cudaGetLastError();
 }
 

@@ -7,6 +7,8 @@
 // One tile of one matrix at a time:
 //   side 0 (G <- (A (x) A) G, the row index):    the tile is all N rows x w columns;
 //   side 1 (G <- G (A (x) A), the column index): the tile is h rows x all N columns.
+// The untransformed index may have any extent C (N x C matrices on side 0, C x N on side 1), so
+// the same tiles also move the factors U_R (N x N_sigma) and U_L (N_sigma x N) of the T form.
 // The tile is staged in shared memory with the optional input scaling G_ij *= rs_in[i] cs_in[j],
 // transformed by a pass along x into a second buffer and a pass along y back, and stored with the
 // optional output scaling.  A is symmetric.  Each block owns its tile, so the update is in place.
@@ -40,13 +42,15 @@ struct SepArgs {
     void* G = nullptr;       // batch matrices N x N, row-major with leading dimension ld, batch stride sG
     long ld = 0, sG = 0;
     int L = 0, N = 0, batch = 1;
+    int C = 0;                  // extent of the untransformed index (0: N): side 0 takes N x C
+                                // matrices (e.g. U_R, N x N_sigma), side 1 C x N ones (U_L)
     const double* A = nullptr;  // L x L one-dimensional factor (symmetric)
     int side = 0;               // 0: left product on the row index, 1: right product on the column index
     int w = 16;                 // tile width: columns (side 0) or rows (side 1)
-    const void* rs_in = nullptr;   // nullable, [batch] x N (stride sv): rows scaled before
-    const void* cs_in = nullptr;   //                                     columns scaled before
-    const void* rs_out = nullptr;  //                                     rows scaled after
-    const void* cs_out = nullptr;  //                                     columns scaled after
+    const void* rs_in = nullptr;   // nullable scale vectors, one entry per row (rs) or column (cs)
+    const void* cs_in = nullptr;   // of the matrix -- N for the transformed index, C for the other --
+    const void* rs_out = nullptr;  // applied before (in) or after (out) the product; matrix z uses
+    const void* cs_out = nullptr;  // the vector at offset z * sv (sv >= the vector's length)
     long sv = 0;
 };
 
@@ -142,8 +146,9 @@ SEP_HD inline void sep_pass(const T* As, const T* src, T* dst, int L, int N, int
 template <typename T, typename Sync>
 SEP_HD inline void sep_tile(const SepArgs& a, int t, int z, int tid, int nt, unsigned char* smem, Sync sync) {
     const int L = a.L, N = a.N, w = a.w;
+    const int ext = a.C > 0 ? a.C : N;            // columns (side 0) or rows (side 1) of the matrix
     const int o0 = t * w;                         // first column (side 0) or row (side 1) of the tile
-    const int wt = (N - o0 < w) ? N - o0 : w;     // its width (the last tile may be ragged)
+    const int wt = (ext - o0 < w) ? ext - o0 : w; // its width (the last tile may be ragged)
     if (wt <= 0) return;
     T* G = (T*)a.G + (size_t)z * a.sG;
     const T* ri = a.rs_in ? (const T*)a.rs_in + (size_t)z * a.sv : nullptr;

@@ -13,17 +13,19 @@ struct NoSync {
 template <typename T>
 void run(const afq::SepArgs& a) {
     std::vector<unsigned char> smem(afq::sep_smem_bytes<T>(a.L, a.N, a.w));
-    const int ntiles = (a.N + a.w - 1) / a.w;
+    const int ntiles = ((a.C > 0 ? a.C : a.N) + a.w - 1) / a.w;
     for (int z = 0; z < a.batch; ++z)
         for (int t = 0; t < ntiles; ++t) afq::sep_tile<T>(a, t, z, 0, 1, smem.data(), NoSync());
 }
 }  // namespace
 
-// One pass (side 0 or 1) with tile width w; the scale pointers are nullable.
-extern "C" void sep_host_pass(int fp64, int side, int L, int w, int batch, void* G, long ld, long sG, const double* A,
-                              const void* rs_in, const void* cs_in, const void* rs_out, const void* cs_out, long sv) {
+// One pass (side 0 or 1) with tile width w on N x C (side 0) or C x N (side 1) matrices (C = 0:
+// square); the scale pointers are nullable.
+extern "C" void sep_host_pass(int fp64, int side, int L, int C, int w, int batch, void* G, long ld, long sG,
+                              const double* A, const void* rs_in, const void* cs_in, const void* rs_out,
+                              const void* cs_out, long sv) {
     afq::SepArgs a;
-    a.G = G; a.ld = ld; a.sG = sG; a.L = L; a.N = L * L; a.batch = batch; a.A = A; a.side = side; a.w = w;
+    a.G = G; a.ld = ld; a.sG = sG; a.L = L; a.N = L * L; a.C = C; a.batch = batch; a.A = A; a.side = side; a.w = w;
     a.rs_in = rs_in; a.cs_in = cs_in; a.rs_out = rs_out; a.cs_out = cs_out; a.sv = sv;
     if (fp64) run<double>(a); else run<float>(a);
 }

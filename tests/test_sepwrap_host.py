@@ -23,7 +23,7 @@ def lib(tmp_path_factory):
                            os.path.join(ROOT, "tests", "sepwrap_host.cpp")])
     h = ctypes.CDLL(str(out))
     vp, i, l = ctypes.c_void_p, ctypes.c_int, ctypes.c_long
-    h.sep_host_pass.argtypes = [i, i, i, i, i, vp, l, l, vp, vp, vp, vp, vp, l]
+    h.sep_host_pass.argtypes = [i, i, i, i, i, i, vp, l, l, vp, vp, vp, vp, vp, l]
     h.sep_host_wrap.argtypes = [i, i, i, i, i, vp, l, l, vp, vp, vp, vp, l]
     yield h
     assert h.sep_host_misaligned() == 0  # no vector access that would fault on the device
@@ -69,7 +69,7 @@ def test_pass_is_the_kronecker_product(lib, fp64, side, L, w, scaled):
     sc = [rng.uniform(0.5, 2.0, (batch, N)) if scaled else None for _ in range(4)]  # rs_in, cs_in, rs_out, cs_out
     buf = _padded(G, pad, dt)
     scd = [None if s is None else np.ascontiguousarray(s, dt) for s in sc]
-    lib.sep_host_pass(fp64, side, L, w, batch, _p(buf), N + pad, N * (N + pad), _p(A), *[_p(s) for s in scd], N)
+    lib.sep_host_pass(fp64, side, L, 0, w, batch, _p(buf), N + pad, N * (N + pad), _p(A), *[_p(s) for s in scd], N)
     E = np.kron(A, A)  # site i = x + L y
     for z in range(batch):
         one = np.ones(N)
@@ -104,3 +104,38 @@ def test_wrap_matches_the_oracle(lib, fp64, direction, L, w):
         tol = 1e-12 if fp64 else 1e-5
         assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref), (s, np.linalg.norm(got - ref) / np.linalg.norm(ref))
         assert np.isnan(buf[s, :, N:]).all()
+
+
+@pytest.mark.parametrize("fp64", [1, 0])
+@pytest.mark.parametrize("L,C,w", [(4, 7, 16), (6, 13, 16), (8, 28, 16), (8, 3, 4), (5, 11, 5)])
+def test_factor_passes_move_the_t_form_factors(lib, fp64, L, C, w):
+    """The T form's factor wrap (forward slice l): U_R <- D E U_R (N x N_sigma, side 0 with the
+    rows scaled by d after) and U_L <- U_L E^{-1} D^{-1} (N_sigma x N, side 1 with the columns
+    scaled by dinv after); U_L U_R is unchanged (Sec. II.C)."""
+    rng = np.random.default_rng(L * 100 + C)
+    N = L * L
+    dt = np.float64 if fp64 else np.float32
+    dtau, c = 0.1, 0.4
+    Ex, Exi = chain_factor(L, 1.0, dtau), chain_factor(L, 1.0, -dtau)
+    x = np.where(rng.random(N) < 0.5, 1, -1)
+    d, dinv = np.exp(c * x), np.exp(-c * x)
+    UR = rng.standard_normal((N, C))
+    UL = rng.standard_normal((C, N))
+    E, Einv = np.kron(Ex, Ex), np.kron(Exi, Exi)
+    ldr, ldl = C + 4, N + 4  # 16-byte multiples of the row pitch for the vector path
+    bR = np.full((1, N, ldr), np.nan, dt)
+    bR[0, :, :C] = UR
+    bL = np.full((1, C, ldl), np.nan, dt)
+    bL[0, :, :N] = UL
+    dd, di = d.astype(dt), dinv.astype(dt)
+    lib.sep_host_pass(fp64, 0, L, C, w, 1, _p(bR), ldr, N * ldr, _p(Ex), None, None, _p(dd), None, N)
+    lib.sep_host_pass(fp64, 1, L, C, w, 1, _p(bL), ldl, C * ldl, _p(Exi), None, None, None, _p(di), N)
+    refR = d[:, None] * (E @ UR)
+    refL = (UL @ Einv) * dinv[None, :]
+    tol = 1e-12 if fp64 else 1e-5
+    gotR, gotL = bR[0, :, :C].astype(np.float64), bL[0, :, :N].astype(np.float64)
+    assert np.linalg.norm(gotR - refR) <= tol * np.linalg.norm(refR)
+    assert np.linalg.norm(gotL - refL) <= tol * np.linalg.norm(refL)
+    assert np.isnan(bR[0, :, C:]).all() and np.isnan(bL[0, :, N:]).all()
+    O0, O1 = UL @ UR, gotL @ gotR  # the overlap the T form keeps fixed across the wrap
+    assert np.linalg.norm(O1 - O0) <= 10 * tol * np.linalg.norm(O0) * np.sqrt(N)
