@@ -255,6 +255,35 @@ def test_local_acceptance_is_high_and_falls_with_the_coupling():
     assert a4 > 0.85 and a6 < a4
 
 
+@pytest.mark.parametrize("F", [[3], [1, 5, 6, 11], [0, 2, 7, 8, 9, 13, 15]])
+def test_t_form_update_with_the_g_form_w(F):
+    """The T-form window update a GPU path would apply with the window kernel's (G-form) W:
+    W = Delta_F (1 + A_FF Delta_F)^{-1} (Eq. BlkFrcBsTnew2), T' = T - (T U_L[:, F]) W (U_R[F, :] T)
+    and U_R's rows F scaled by 1 + Delta_F give 1 - U_R' T' U_L = the from-scratch G after the
+    flips at F, which is also the G-form update G - G[:, F] W (E_F^T - G[F, :])."""
+    m, P, X = _setup(4, 4, 7, 4)
+    ell, N = 2, m.N
+    Xf = X.copy()
+    Xf[ell - 1, F] *= -1
+    for s in range(2):
+        _, _, _, UR, UL = m.green_scratch(X, P, s, ell, stab=2, want_factors=True)
+        T = np.linalg.inv(UL @ UR)
+        G = np.eye(N) - UR @ T @ UL
+        dF = np.exp(-2.0 * m.c[s] * X[ell - 1, F]) - 1.0
+        AFF = np.eye(len(F)) - G[np.ix_(F, F)]
+        W = np.diag(dF) @ np.linalg.inv(np.eye(len(F)) + AFF @ np.diag(dF))
+        V, Y = T @ UL[:, F], UR[F, :] @ T
+        T1 = T - V @ W @ Y
+        UR1 = UR.copy()
+        UR1[F, :] *= (1.0 + dF)[:, None]
+        G_t = np.eye(N) - UR1 @ T1 @ UL
+        E_F = np.eye(N)[:, F]
+        G_g = G - G[:, F] @ W @ (E_F.T - G[F, :])
+        G_bf = bf.green(m.E, m.c[s], Xf, P, ell)
+        np.testing.assert_allclose(G_t, G_bf, atol=1e-10)
+        np.testing.assert_allclose(G_g, G_bf, atol=1e-10)
+
+
 # ---------------------------------------------------------------- delayed update
 
 @pytest.mark.parametrize("k,strategy", [(1, 2), (3, 2), (8, 2), (5, 1), (16, 1)])
