@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed walker population leg")
     ap.add_argument("--no-soc", action="store_true", help="skip the spin-orbit-coupled leg")
+    ap.add_argument("--no-separable", action="store_true", help="skip the separable-wrap leg")
     ap.add_argument("--soc-slices", type=int, default=20, help="timed slice-steps per mode of the SOC leg")
     ap.add_argument("--gemm", default="tc3", choices=["tc3", "simt", "tf32"],
                     help="FP32 GEMM engine: tcgen05 three-term TF32 split, FP32 SIMT, or one TF32 pass")
@@ -349,6 +350,10 @@ def main():
     soc_res = None
     if not args.no_soc:
         soc_res = optional_leg("soc", lambda: soc_leg(torch, stream, args, seed))
+    sep = None
+    if not args.no_separable:
+        sep = optional_leg("separable_wrap", lambda: separable_wrap_leg(afqmc, torch, stream, args, seed,
+                                                                        prof["wrap"]["ms"] / args.steps))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         def cpu_leg():
@@ -382,6 +387,7 @@ def main():
             "cuda_graphs": graphs,
             "batched_population": batch,
             "soc": soc_res,
+            "separable_wrap": sep,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -678,6 +684,46 @@ def end_to_end(afqmc, torch, stream, args, seed, rank):
     return {"value": N * M * 2 / t, "unit": UNIT, "h2d_bytes_per_step": int(Ph.nbytes + Xh.nbytes),
             "d2h_bytes_per_step": int(Xout.nbytes + 16),
             "note": "create + init_walkers (FP64 left stack and G(0)) + 1 sweep + energy + fields readback"}
+
+
+def separable_wrap_leg(afqmc, torch, stream, args, seed, dense_wrap_ms):
+    """The same 40 x 40 sweep with the wrap through the separable lattice propagator
+    (afqmc_set_wrap: exp(-dtau K) = Ex (x) Ex, two L-point passes per product; not the default):
+    one warm-up sweep, then `steps` timed sweeps with CUDA events on the launching stream (L2
+    flushed between them), and the wrap phase from the library's profiler next to the dense
+    wrap's.  Reported beside the headline, which keeps the dense tensor-core wrap."""
+    P = inputs.trial_state(L, L, NS)
+    X = inputs.initial_fields(M, N, seed=seed)
+    order = [(l, +1) for l in range(1, M + 1)] + [(l, -1) for l in range(M, 0, -1)]
+    c = afqmc.Context(M, dtau=DTAU, U=U, t=T_HOP, precision="fp32", stab_every=STAB, seed=seed, gemm=args.gemm)
+    try:
+        c.init_walkers([L], [NS], [NS], np.concatenate([P.ravel(), P.ravel()]), X, stream=stream)
+        c.set_wrap("separable")
+
+        def sweep():
+            for (ell, d) in order:
+                c.sweep_slice(ell, d, "delayed", k=args.k, nb=args.nb, stream=stream)
+                pos = ell if d > 0 else ell - 1
+                if pos % STAB == 0:
+                    afqmc.afqmc_recompute_G(c.h, None, stream)
+
+        sweep()  # warm-up
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        ms = []
+        for _ in range(max(1, args.steps)):
+            flush.zero_()
+            ms.append(tune.time_on_stream(torch, stream, sweep))
+        c.set_profiling(True)
+        sweep()
+        prof = c.profile()
+        c.set_profiling(False)
+        ms_sweep = statistics.median(ms)
+        return {"value": N * M * 2 / (ms_sweep / 1e3), "unit": UNIT, "ms_per_step": ms_sweep,
+                "wrap_ms_per_step": prof["wrap"]["ms"], "dense_wrap_ms_per_step": dense_wrap_ms,
+                "note": "the headline workload with afqmc_set_wrap(separable); the headline keeps the dense "
+                        "tensor-core wrap until this path's GPU parity is confirmed"}
+    finally:
+        c.close()
 
 
 if __name__ == "__main__":

@@ -63,3 +63,61 @@ def test_an_auxiliary_leg_that_fails_is_reported_in_the_line(capsys):
 
     assert bench.optional_leg("soc", boom) == {"error": "RuntimeError: afqmc_soc_sweep_slice failed: -3"}
     assert "soc leg failed" in capsys.readouterr().err
+
+
+def test_separable_wrap_leg_times_whole_sweeps_with_that_wrap():
+    """bench.separable_wrap_leg on a fake device: it switches the context to the separable wrap
+    before the first slice, times whole sweeps (2M slice-steps) and closes the context."""
+    import types
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    clock = {"t": 0.0}
+    made = []
+
+    class Ev:
+        def __init__(self, enable_timing=True):
+            self.t = 0.0
+
+        def record(self, stream=None):
+            self.t = clock["t"]
+
+        def elapsed_time(self, other):
+            return other.t - self.t
+
+    class Ctx:
+        def __init__(self, M, **kw):
+            self.h, self.wrap, self.closed, self.slices = object(), "dense", False, 0
+            made.append(self)
+
+        def init_walkers(self, *a, **kw):
+            pass
+
+        def set_wrap(self, mode):
+            self.wrap = mode
+
+        def sweep_slice(self, ell, d, mode, k=32, nb=4, stream=None):
+            assert self.wrap == "separable" and mode == "delayed"
+            self.slices += 1
+            clock["t"] += 2.0
+
+        def set_profiling(self, on):
+            pass
+
+        def profile(self):
+            return {"wrap": {"ms": 7.5}}
+
+        def close(self):
+            self.closed = True
+
+    fake_torch = types.SimpleNamespace(
+        cuda=types.SimpleNamespace(Event=Ev, synchronize=lambda: None),
+        empty=lambda *a, **k: types.SimpleNamespace(zero_=lambda: None), float32=None)
+    fake_afqmc = types.SimpleNamespace(Context=Ctx, afqmc_recompute_G=lambda h, n, s: None)
+    args = types.SimpleNamespace(gemm="tc3", steps=2, k=64, nb=16)
+    r = bench.separable_wrap_leg(fake_afqmc, fake_torch, None, args, 1, 52.0)
+    assert r["ms_per_step"] == 2.0 * 2 * bench.M
+    assert r["value"] == bench.N * bench.M * 2 / (r["ms_per_step"] / 1e3)
+    assert r["wrap_ms_per_step"] == 7.5 and r["dense_wrap_ms_per_step"] == 52.0
+    assert made[-1].closed and made[-1].slices == (1 + 2 + 1) * 2 * bench.M  # warm-up, timed, profiled
