@@ -121,3 +121,33 @@ def test_separable_wrap_leg_times_whole_sweeps_with_that_wrap():
     assert r["value"] == bench.N * bench.M * 2 / (r["ms_per_step"] / 1e3)
     assert r["wrap_ms_per_step"] == 7.5 and r["dense_wrap_ms_per_step"] == 52.0
     assert made[-1].closed and made[-1].slices == (1 + 2 + 1) * 2 * bench.M  # warm-up, timed, profiled
+
+
+def test_kernel_rooflines_use_the_documented_work_per_launch():
+    """bench.kernel_rooflines on a synthetic profile: the algorithmic work per launch is the
+    documented figure (wrap: 2 x 2 N^3 flop for both spins; flush: read + write of both spins' FP32
+    G; solve: 2 x 2 Nsigma^2 N), achieved = work x launches / summed time, frac = achieved / peak,
+    and the list is sorted by time per step (the dominant kernel first)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    N, NS = bench.N, bench.NS
+    assert (N, NS) == (1600, 700)
+    pk = {"hbm_gbs": 6789.6, "bf16_tflops": 1911.7, "sm_max_mhz": 2070.0}
+    prof = {"wrap_gemm": {"ms": 52.0, "intervals": 320}, "flush_gemm": {"ms": 160.0, "intervals": 4000},
+            "solve": {"ms": 13.0, "intervals": 16}, "elim": {"ms": 0.0, "intervals": 0}}
+    out = bench.kernel_rooflines(prof, "tc3", pk, "measured", steps=1)
+    by = {r["kernel"].split(" ")[0]: r for r in out}
+    wrap = by["wrap"]
+    assert wrap["work_per_launch"] == 2 * 2 * 1600 ** 3 == 1.6384e10
+    assert wrap["achieved"] == pytest.approx(1.6384e10 * 320 / 0.052 / 1e12)
+    assert wrap["peak"] == pytest.approx(1911.7 * 1.1 / 2.25) and wrap["bound"] == "tensor"
+    assert wrap["frac"] == pytest.approx(wrap["achieved"] / wrap["peak"])
+    flush = by["rank-m"]
+    assert flush["work_per_launch"] == 2 * 2 * 1600 * 1600 * 4 == 40960000
+    assert flush["achieved"] == pytest.approx(40960000 * 4000 / 0.160 / 1e9) and flush["unit"] == "GB/s"
+    solve = by["lu_solve_kernel"]
+    assert solve["work_per_launch"] == pytest.approx(2 * 2.0 * 700 ** 2 * 1600)
+    assert "elim" not in {r["kernel"] for r in out} and len(out) == 3
+    assert [r["ms_per_step"] for r in out] == sorted((r["ms_per_step"] for r in out), reverse=True)
+    assert out[0] is flush  # 160 ms per step: the dominant entry
