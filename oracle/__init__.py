@@ -506,6 +506,54 @@ class SocModel:
             raise np.linalg.LinAlgError("singular overlap")
         return G, la[0], ph[0]
 
+    def wrap_fft(self, G, xl, direction):
+        """The same wrap with exp(-+dtau H0) applied in momentum space (the paper's FFT
+        propagation, Sec. II.C, for the spin-orbit-coupled H0 of Appendix A).  H0 is block-diagonal
+        in the 2D Fourier basis: per momentum k the 2 x 2 block h_k = [[eps_k, conj(L_k)],
+        [L_k, eps_k]] in (up, down), eps_k = -2t (cos kx + cos ky), L_k = 2 lam (sin ky - i sin kx).
+        E X = F^{-1} (exp(-dtau h_k) (F X)_k) for every column of X (numpy's FFT over the site index
+        of each spin block, exp by numpy's batched eigh); X E^{-1} = (E^{-1} X^+)^+ since E is
+        Hermitian.  D(x) rotates each pair (i, N + i) by A(gamma x_i)."""
+        L, N = self.p.L, self.N
+        k = 2 * np.pi * np.arange(L) / L
+        kx, ky = k[None, :], k[:, None]  # (ky, kx) grid, site index x + L y
+        eps = -2.0 * self.p.t * (np.cos(kx) + np.cos(ky))
+        Lk = 2.0 * self.p.lam * (np.sin(ky) - 1j * np.sin(kx))
+        h = np.zeros((L, L, 2, 2), np.complex128)
+        h[..., 0, 0] = eps
+        h[..., 1, 1] = eps
+        h[..., 1, 0] = Lk
+        h[..., 0, 1] = np.conj(Lk)
+        w, v = np.linalg.eigh(h)
+
+        def expk(tau):
+            return np.einsum("...ab,...b,...cb->...ac", v, np.exp(-tau * w), np.conj(v))
+
+        def apply_E(X, tau):  # exp(-tau H0) X, X: 2N x m
+            Xk = np.fft.fft2(X.reshape(2, L, L, -1), axes=(1, 2))
+            Yk = np.einsum("yxab,byxm->ayxm", expk(tau), Xk)
+            return np.fft.ifft2(Yk, axes=(1, 2)).reshape(2 * N, -1)
+
+        th = self.p.gamma * np.asarray(xl, dtype=np.float64)
+        c, s = np.cos(th), np.sin(th)
+
+        def rot_rows(X, sgn):  # D(sgn x) X
+            up, dn = X[:N].copy(), X[N:].copy()
+            return np.concatenate([c[:, None] * up + sgn * s[:, None] * dn, -sgn * s[:, None] * up + c[:, None] * dn])
+
+        def rot_cols(X, sgn):  # X D(sgn x)
+            return rot_rows(X.T, -sgn).T  # (X D)^T = D^T X^T and A(t)^T = A(-t)
+
+        G = _c128(G)
+        tau = self.p.dtau
+        if direction > 0:  # D E G Einv D^{-1}
+            T = apply_E(G, tau)
+            T = apply_E(T.conj().T, -tau).conj().T
+            return rot_cols(rot_rows(T, +1.0), -1.0)
+        T = rot_cols(rot_rows(G, -1.0), +1.0)  # D^{-1} G D, then Einv (.) E
+        T = apply_E(T, -tau)
+        return apply_E(T.conj().T, tau).conj().T
+
     def wrap(self, G, xl, direction):
         """Forward: G <- B_l G B_l^{-1}; backward: G <- B_l^{-1} G B_l, B_l = D(x_l) E."""
         G = _c128(G).copy()

@@ -333,3 +333,22 @@ def test_block_proposals_equal_to_the_current_fields_are_accepted_unchanged(nb):
     np.testing.assert_array_equal(ratio, np.ones(nblk))
     np.testing.assert_array_equal(x1, xl)
     np.testing.assert_array_equal(G1, G)
+
+
+@pytest.mark.parametrize("L", [3, 4, 6])
+@pytest.mark.parametrize("direction", [+1, -1])
+def test_momentum_space_wrap_equals_the_dense_wrap(L, direction):
+    """SocModel.wrap_fft (exp(-dtau h_k) per momentum on FFT'd columns; the paper's FFT
+    propagation) equals the dense wrap with the real-space exp(-dtau H0), for the from-scratch G
+    and for an arbitrary complex matrix, forward and backward; and moves G(l-1) to G(l)."""
+    m, P, X = _setup(L=L, n_e=2 * (L * L // 2), M=4)
+    rng = np.random.default_rng(L)
+    ell = 2
+    G, _, _ = m.green_scratch(X, P, ell - 1 if direction > 0 else ell)
+    Z = rng.standard_normal(G.shape) + 1j * rng.standard_normal(G.shape)
+    for A in (G, Z):
+        ref = m.wrap(A, X[ell - 1], direction)
+        got = m.wrap_fft(A, X[ell - 1], direction)
+        assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+    G1, _, _ = m.green_scratch(X, P, ell if direction > 0 else ell - 1)
+    np.testing.assert_allclose(m.wrap_fft(G, X[ell - 1], direction), G1, atol=1e-10)
