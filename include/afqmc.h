@@ -171,8 +171,10 @@ int afqmc_debug_wait_timeout(long long limit_ns, void* stream);
  *   delta       2*m doubles, delta[s*m + a] = exp(c_s (x'_a - x_a)) - 1 (spin s = 0 up, 1 down).
  *   m           0 <= m <= 128 (FP32) or 64 (FP64); 0 is a no-op.
  * Work is enqueued on `stream`; device scratch comes from cudaMallocAsync on that stream and is freed
- * there.  Returns AFQMC_ERR_ARG for bad sizes or null pointers; a site outside [0, N) makes the call
- * a no-op on the device; a singular (1 + (1 - G_II) D) leaves non-finite values in G. */
+ * there.  The call then copies the device's status word back and waits for the stream, so it returns
+ * after the update.  Returns AFQMC_ERR_ARG for bad sizes or null pointers (checked before any device
+ * work) and for a site outside [0, N) (found on the device; G is left unchanged), and
+ * AFQMC_ERR_NUMERIC when 1 + (1 - G_II) D has a zero pivot for either spin (G is left unchanged). */
 int afqmc_apply_flips(int precision, int N, long long ld, void* G_up, void* G_dn, const int* sites,
                       const double* delta, int m, void* stream);
 
@@ -187,9 +189,11 @@ int afqmc_apply_flips(int precision, int N, long long ld, void* G_up, void* G_dn
  * precision); every GPU that loads libafqmc.so holds that array until the process exits.  The
  * first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
  * device current, so make the first call on each device before any stream capture.  All calls
- * share the array and it keeps the last call's contents; nothing in it has to start at zero, but
- * calls whose work overlaps on the GPU (e.g. on two streams) race on it.  It calls no cudaMalloc,
- * cudaFree or allocating library routine. */
+ * share the array and it keeps the last call's contents; nothing in it has to start at zero (every
+ * call rewrites the status word and the sizes it reads), but calls whose work overlaps on the GPU
+ * (e.g. on two streams) race on it.  Like afqmc_apply_flips it reads the status word back and waits
+ * for the stream, with the same error codes.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine. */
 #define AFQMC_NOALLOC_MAX_N 4096
 int afqmc_apply_flips_noalloc(int precision, int N, long long ld, void* G_up, void* G_dn, const int* sites,
                               const double* delta, int m, void* stream);

@@ -5,6 +5,8 @@
 
 #include <atomic>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -13,6 +15,24 @@
 namespace afq {
 static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches += n; }
+
+// A kernel attribute set by cudaFuncSetAttribute belongs to the kernel on the current device, so
+// the cache is keyed by (device, kernel, attribute) and guarded by a mutex; the attribute is set
+// again only when a larger value is asked for on that device.
+cudaError_t ensure_func_attr(const void* fn, cudaFuncAttribute attr, int value) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*, int>, int> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(dev, fn, (int)attr);
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= value) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, attr, value);
+    if (e == cudaSuccess) done[key] = value;
+    return e;
+}
 }  // namespace afq
 
 using namespace afq;

@@ -42,7 +42,9 @@ static WindowBufs flips_layout(unsigned char* scratch, int N) {
 }
 
 // One CTA: validate the sites, then W_s for both spins by Gauss-Jordan with partial pivoting
-// on [M | 1] in shared memory, M = 1 + (1 - G_II) D.
+// on [M | 1] in shared memory, M = 1 + (1 - G_II) D.  The status word wb.m[1] is rewritten by every
+// call: 0, DEV_ARG (a site outside [0, N)) or DEV_NUMERIC (a zero pivot); on either error wb.m[0]
+// (the product's inner dimension) is 0, so G is left unchanged.
 template <typename T>
 __global__ void __launch_bounds__(1024) flips_W_kernel(const T* __restrict__ Gu, const T* __restrict__ Gd, long ld,
                                                        int N, const int* sites, const double* delta, int m,
@@ -52,8 +54,11 @@ __global__ void __launch_bounds__(1024) flips_W_kernel(const T* __restrict__ Gu,
     const int AP = 2 * m + 1;
     T* Aug = (T*)smem_raw;
     T* colk = Aug + (size_t)m * AP;
-    __shared__ int s_piv, s_bad;
-    if (tid == 0) s_bad = 0;
+    __shared__ int s_piv, s_bad, s_num;
+    if (tid == 0) {
+        s_bad = 0;
+        s_num = 0;
+    }
     __syncthreads();
     for (int a = tid; a < m; a += nt) {
         int v = sites[a];
@@ -96,7 +101,7 @@ __global__ void __launch_bounds__(1024) flips_W_kernel(const T* __restrict__ Gu,
                 }
                 if (tid == 0) {
                     s_piv = br;
-                    if (!(best > T(0))) wb.m[1] = DEV_NUMERIC;
+                    if (!(best > T(0))) s_num = 1;
                 }
             }
             __syncthreads();
@@ -127,6 +132,10 @@ __global__ void __launch_bounds__(1024) flips_W_kernel(const T* __restrict__ Gu,
         }
         __syncthreads();
     }
+    if (tid == 0 && s_num) {  // singular: apply nothing
+        wb.m[0] = 0;
+        wb.m[1] = DEV_NUMERIC;
+    }
 }
 
 template <typename T>
@@ -135,22 +144,29 @@ static cudaError_t apply_flips_impl(cudaStream_t st, int N, long ld, T* Gu, T* G
     const int NWC = window_max<T>();
     WindowBufs wb = flips_layout<T>(scratch, N);
     size_t shm = (size_t)m * (2 * (size_t)m + 1) * sizeof(T) + (size_t)m * sizeof(T);
-    static bool attr = false;
-    if (!attr) {
-        size_t mx = (size_t)NWC * (2 * (size_t)NWC + 1) * sizeof(T) + (size_t)NWC * sizeof(T);
-        cudaError_t e = cudaFuncSetAttribute((void*)flips_W_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)mx);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    const size_t mx = (size_t)NWC * (2 * (size_t)NWC + 1) * sizeof(T) + (size_t)NWC * sizeof(T);
+    cudaError_t e = ensure_smem_attr((const void*)flips_W_kernel<T>, mx);
+    if (e != cudaSuccess) return e;
     count_launch();
     flips_W_kernel<T><<<1, 1024, shm, st>>>(Gu, Gd, ld, N, sites, delta, m, wb, NWC);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     SiteParams sp{};
     sp.N = N;
     sp.ld = ld;
     return launch_flush<T>(st, Gu, Gd, sp, wb, m);
+}
+
+// Copy the call's device status word (wb.m[1], at byte 4 of the scratch) to the host on the call's
+// stream, wait for the stream, and map it to an ABI code.
+static int flips_status(cudaStream_t st, const unsigned char* scratch) {
+    int h = 0;
+    if (cudaMemcpyAsync(&h, scratch + sizeof(int), sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return AFQMC_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return AFQMC_ERR_CUDA;
+    if (h == DEV_ARG) return AFQMC_ERR_ARG;
+    if (h == DEV_NUMERIC) return AFQMC_ERR_NUMERIC;
+    return h == 0 ? AFQMC_OK : AFQMC_ERR_CUDA;
 }
 
 static int flips_check(int precision, int N, long long ld, void* G_up, void* G_dn, const int* sites,
@@ -180,9 +196,10 @@ extern "C" int afqmc_apply_flips(int precision, int N, long long ld, void* G_up,
                                                    (unsigned char*)scratch)
                         : apply_flips_impl<float>(st, N, (long)ld, (float*)G_up, (float*)G_dn, sites, delta, m,
                                                   (unsigned char*)scratch);
+    const int rs = (e == cudaSuccess) ? flips_status(st, (const unsigned char*)scratch) : AFQMC_ERR_CUDA;
     cudaError_t e2 = cudaFreeAsync(scratch, st);
-    if (e != cudaSuccess || e2 != cudaSuccess) return AFQMC_ERR_CUDA;
-    return AFQMC_OK;
+    if (rs != AFQMC_OK) return rs;
+    return e2 == cudaSuccess ? AFQMC_OK : AFQMC_ERR_CUDA;
 }
 
 // ---------------------------------------------------------------------------
@@ -254,5 +271,6 @@ extern "C" int afqmc_apply_flips_noalloc(int precision, int N, long long ld, voi
                                                         m, (unsigned char*)scratch)
                         : afq::apply_flips_impl<float>(st, N, (long)ld, (float*)G_up, (float*)G_dn, sites, delta, m,
                                                        (unsigned char*)scratch);
-    return e == cudaSuccess ? AFQMC_OK : AFQMC_ERR_CUDA;
+    if (e != cudaSuccess) return AFQMC_ERR_CUDA;
+    return afq::flips_status(st, (const unsigned char*)scratch);
 }

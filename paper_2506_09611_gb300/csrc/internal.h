@@ -12,6 +12,13 @@ namespace afq {
 // Every kernel launch site calls count_launch() (the counter behind afqmc_launch_count()).
 void count_launch(int n = 1);
 
+// cudaFuncSetAttribute(fn, attr, value) once per (device, kernel, attribute), thread-safe; a
+// larger value than the one set before on the device sets it again.
+cudaError_t ensure_func_attr(const void* fn, cudaFuncAttribute attr, int value);
+inline cudaError_t ensure_smem_attr(const void* fn, size_t bytes) {
+    return ensure_func_attr(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 // Row-major batched GEMM with diagonal scalings (all pointers device):
 //   C[z] = alpha * diag(rs[z]) * A[z] * diag(bs[z]) * B[z] * diag(cs[z]) + beta * C[z]
 // A is M x K (lda), B is K x N (ldb), C is M x N (ldc).  Null scale pointers

@@ -293,16 +293,13 @@ template <int CS>
 static cudaError_t launch_panel(cudaStream_t st, const LuArgs& a, int j0, int nbk) {
     const int rpc = (a.m + CS - 1) / CS;
     const size_t shm = (size_t)rpc * LU_NBP * sizeof(double) + (size_t)rpc + 16;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute((void*)lu_panel_kernel<CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(227 * 1024 - 16 * 1024));
+    {
+        cudaError_t e = ensure_smem_attr((const void*)lu_panel_kernel<CS>, 227 * 1024 - 16 * 1024);
         if (e != cudaSuccess) return e;
         if (CS > 8) {
-            e = cudaFuncSetAttribute((void*)lu_panel_kernel<CS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            e = ensure_func_attr((const void*)lu_panel_kernel<CS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             if (e != cudaSuccess) return e;
         }
-        attr = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CS * a.nmat);
@@ -339,9 +336,8 @@ static int lu_big_cluster(const LuArgs& a) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int ncl = 0;
-    cudaFuncSetAttribute((void*)lu_panel_kernel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute((void*)lu_panel_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(227 * 1024 - 16 * 1024));
+    ensure_func_attr((const void*)lu_panel_kernel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    ensure_smem_attr((const void*)lu_panel_kernel<16>, 227 * 1024 - 16 * 1024);
     if (cudaOccupancyMaxActiveClusters(&ncl, (void*)lu_panel_kernel<16>, &cfg) == cudaSuccess && ncl >= 2) big = 16;
     else big = 8;
     cudaGetLastError();
@@ -523,12 +519,9 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(SolveArgs a) {
 cudaError_t launch_lu_solve(cudaStream_t st, const SolveArgs& a) {
     const size_t shm = ((size_t)a.ns * SV_YP + 32 * (SV_KB + 1) + a.ns) * sizeof(double) + (size_t)a.ns * sizeof(int);
     if (shm > 220 * 1024) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute((void*)lu_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             220 * 1024);
+    {
+        cudaError_t e = ensure_smem_attr((const void*)lu_solve_kernel, 220 * 1024);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     count_launch();
     lu_solve_kernel<<<dim3((a.N + SV_COLS - 1) / SV_COLS, a.nmat), 256, shm, st>>>(a);

@@ -41,12 +41,9 @@ cudaError_t launch_sep(cudaStream_t st, const SepArgs& a0) {
     if (a.ld < (a.side == 0 ? ext : a.N)) return cudaErrorInvalidValue;
     a.w = sep_width<T>(a.L, a.N);
     if (a.w == 0) return cudaErrorInvalidValue;  // the lattice is too large for an on-chip tile
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute((void*)sep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SEP_SMEM_CAP);
+    {
+        cudaError_t e = ensure_smem_attr((const void*)sep_kernel<T>, SEP_SMEM_CAP);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     count_launch();
     sep_kernel<T><<<dim3((ext + a.w - 1) / a.w, a.batch), 256, sep_smem_bytes<T>(a.L, a.N, a.w), st>>>(a);

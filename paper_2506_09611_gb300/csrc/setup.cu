@@ -243,11 +243,9 @@ cudaError_t launch_prop(cudaStream_t st, const PropArgs& a) {
     const int vpc = (int)((room / N < PV_VEC) ? room / N : PV_VEC);
     if (vpc < 1) return cudaErrorInvalidValue;  // lattice too large to keep one vector on chip
     const size_t shm = ((size_t)2 * a.L * a.L + (size_t)vpc * N) * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute((void*)prop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    {
+        cudaError_t e = ensure_smem_attr((const void*)prop_kernel, 220 * 1024);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const int nv = a.nvec[0] > a.nvec[1] ? a.nvec[0] : a.nvec[1];
     count_launch();

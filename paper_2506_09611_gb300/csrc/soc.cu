@@ -1399,13 +1399,7 @@ cudaError_t soc_window(afqmc_soc_ctx* ctx, cudaStream_t st, int8_t* xl, const ui
     if (pipe && w >= 2 && (e = cudaStreamWaitEvent(st, ctx->ev_fl[b], 0)) != cudaSuccess) return e;
     {
         const size_t shm = window_smem<T>(kmax);
-        static bool attr[2] = {false, false};
-        if (!attr[sizeof(T) == 8]) {
-            if ((e = cudaFuncSetAttribute((void*)soc_window_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)shm)) != cudaSuccess)
-                return e;
-            attr[sizeof(T) == 8] = true;
-        }
+        if ((e = ensure_smem_attr((const void*)soc_window_kernel<T>, shm)) != cudaSuccess) return e;
         count_launch();
         soc_window_kernel<T><<<nwk, 512, shm, st>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1419,13 +1413,9 @@ cudaError_t soc_window(afqmc_soc_ctx* ctx, cudaStream_t st, int8_t* xl, const ui
     const int m2max = 2 * n;
     {
         const size_t shm = (size_t)(m2max * m2max + XW_ROWS * m2max) * sizeof(cx<T>);
-        static bool attr[2] = {false, false};
-        if (!attr[sizeof(T) == 8]) {
+        {
             const int cap = 4 * kmax * kmax + XW_ROWS * 2 * kmax;
-            if ((e = cudaFuncSetAttribute((void*)soc_xw_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(cap * sizeof(cx<T>)))) != cudaSuccess)
-                return e;
-            attr[sizeof(T) == 8] = true;
+            if ((e = ensure_smem_attr((const void*)soc_xw_kernel<T>, cap * sizeof(cx<T>))) != cudaSuccess) return e;
         }
         count_launch();
         soc_xw_kernel<T><<<dim3((N2 + XW_ROWS - 1) / XW_ROWS, 1, nwk), 256, shm, sfl>>>(
@@ -1435,13 +1425,9 @@ cudaError_t soc_window(afqmc_soc_ctx* ctx, cudaStream_t st, int8_t* xl, const ui
     }
     {
         const size_t shm = (size_t)(FL_R + FL_C) * m2max * sizeof(cx<T>);
-        static bool attr[2] = {false, false};
-        if (!attr[sizeof(T) == 8]) {
-            if ((e = cudaFuncSetAttribute((void*)soc_flush_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)((FL_R + FL_C) * 2 * kmax * sizeof(cx<T>)))) != cudaSuccess)
-                return e;
-            attr[sizeof(T) == 8] = true;
-        }
+        if ((e = ensure_smem_attr((const void*)soc_flush_kernel<T>, (FL_R + FL_C) * 2 * kmax * sizeof(cx<T>))) !=
+            cudaSuccess)
+            return e;
         count_launch();
         soc_flush_kernel<T><<<dim3((N2 + FL_C - 1) / FL_C, (N2 + FL_R - 1) / FL_R, nwk), 256, shm, sfl>>>(
             Gsrc, Gdst, ctx->gstride(), ldz, N, ctx->sites[b], kmax, ctx->Kdev[b], (const cx<T>*)ctx->Xp[b]);
@@ -1502,11 +1488,9 @@ cudaError_t soc_propagate(afqmc_soc_ctx* ctx, cudaStream_t st, double* F, long w
                  fix = (size_t)(ctx->dP * ctx->dP + ctx->dQ * ctx->dQ + ctx->dP * ctx->dQ) * sizeof(cx<double>);
     const int vpc = (int)std::min<size_t>(PROP_VPC_MAX, (220 * 1024 - fix) / per);
     const size_t shm = vpc * per + fix;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute((void*)soc_prop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    {
+        cudaError_t e = ensure_smem_attr((const void*)soc_prop_kernel, 220 * 1024);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     count_launch();
     soc_prop_kernel<<<dim3((ctx->nv + vpc - 1) / vpc, ctx->nwk), 256, shm, st>>>(a, vpc);

@@ -59,134 +59,250 @@ __device__ __forceinline__ double hs_log_scalar(const SiteParams& sp, int x) {
 }
 
 // ---------------------------------------------------------------------------
-// local update: persistent cooperative kernel
+// local update: persistent cooperative kernel, one grid barrier per ACCEPT
 // ---------------------------------------------------------------------------
-// colbuf / rowbuf: [2 buffers][2 spins][N] snapshots of column i / row i of
-// the current G, written by the owners of the rows during the previous site
-// and read by every CTA after the grid barrier.
+// CTA b owns the rows [r0, r1) of both spins.  A phase handles one accepted site:
+//   1. every CTA scans the sites after the last accept with warp 0 (32 sites per round; a ballot
+//      finds the first acceptance) from a copy of the two diagonals in global memory.  Every CTA
+//      reads the same values and runs the same arithmetic, so all reach the same site b;
+//   2. every CTA reads row b of both spins (e_b^T - G[b, :]) and column b of its own rows;
+//   3. every CTA applies G_s[r, c] -= f_s G_s[r, b] (delta_bc - G_s[b, c]) to its own rows with
+//      16-byte accesses, and writes the new diagonal of its rows to the other diagonal buffer;
+//   4. one grid barrier.
+// A rejected site leaves G unchanged, so it costs a diagonal read and no barrier.  Two cross-CTA
+// hazards inside a phase are avoided without a second barrier:
+//   * the diagonals are double-buffered by phase parity: the scan reads the buffer the previous
+//     phase wrote, and the update writes the other one;
+//   * every CTA reads row b while its owner updates its rows, so the owner keeps its new row b in
+//     shared memory and stores it to G at the start of the next phase, after the barrier (no CTA
+//     reads row b again in this slice).
+// The diagonal copy is computed with the same fused multiply-add as the element of G, so the two
+// stay bit-identical.  diag: [2 buffers][2 spins][N].
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using V = float4; static constexpr int W = 4; };
+template <> struct Vec16<double> { using V = double2; static constexpr int W = 2; };
+
 template <typename T>
-__global__ void __launch_bounds__(512) local_kernel(T* Gu, T* Gd, int8_t* xl_g, const double* u,
-                                                    const uint8_t* replay, SiteParams sp, SliceOut so,
-                                                    T* colbuf, T* rowbuf, GridBar* bar, int* err) {
-    extern __shared__ unsigned char smem_raw[];
-    int8_t* xs = (int8_t*)smem_raw;
-    __shared__ int s_acc;
-    __shared__ T s_f[2];
+__device__ __forceinline__ void vfma_rank1(typename Vec16<T>::V& g, T a, const typename Vec16<T>::V& r);
+template <>
+__device__ __forceinline__ void vfma_rank1<float>(float4& g, float a, const float4& r) {
+    g.x = fmaf(a, r.x, g.x); g.y = fmaf(a, r.y, g.y); g.z = fmaf(a, r.z, g.z); g.w = fmaf(a, r.w, g.w);
+}
+template <>
+__device__ __forceinline__ void vfma_rank1<double>(double2& g, double a, const double2& r) {
+    g.x = fma(a, r.x, g.x); g.y = fma(a, r.y, g.y);
+}
+
+constexpr int LOCAL_THREADS = 1024;
+constexpr int LOCAL_UNROLL = 4;
+
+// Shared-memory layout of local_kernel (byte offsets, 16-byte aligned where vectors are read).
+struct LocalSmem {
+    size_t us, rowb, patch, colb, xs, rp, total;
+};
+template <typename T>
+__host__ __device__ inline LocalSmem local_smem(int N, long ld, int nrmax) {
+    auto al = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    LocalSmem s;
+    s.us = 0;                                              // double us[N]: the site uniforms
+    s.rowb = al(s.us + (size_t)N * sizeof(double));        // T rowb[2][ld]: e_b^T - G_s[b, :], 0 beyond N
+    s.patch = al(s.rowb + 2 * (size_t)ld * sizeof(T));     // T patch[2][ld]: the owner's new row b
+    s.colb = al(s.patch + 2 * (size_t)ld * sizeof(T));     // T colb[2][nrmax]: G_s[r, b] of the own rows
+    s.xs = al(s.colb + 2 * (size_t)nrmax * sizeof(T));     // int8 xs[N]: fields of the slice
+    s.rp = s.xs + (size_t)N;                               // uint8 rp[N]: forced decisions
+    s.total = al(s.rp + (size_t)N);
+    return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(LOCAL_THREADS, 1) local_kernel(T* Gu, T* Gd, int8_t* xl_g, const double* u,
+                                                                 const uint8_t* replay, SiteParams sp, SliceOut so,
+                                                                 T* diag, GridBar* bar, int* err, int nrmax) {
+    using V = typename Vec16<T>::V;
+    constexpr int VW = Vec16<T>::W;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = sp.N;
     const long ld = sp.ld;
     const int nblk = gridDim.x, b = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const int r0 = (int)((long)N * b / nblk), r1 = (int)((long)N * (b + 1) / nblk);
-    const int nrows = r1 - r0;
-    T* G[2] = {Gu, Gd};
-    for (int i = tid; i < N; i += nt) xs[i] = xl_g[i];
-    // snapshot of column 0 and row 0
-    for (int e = tid; e < 2 * nrows; e += nt) {
-        int s = e / nrows, r = r0 + e % nrows;
-        colbuf[(0 * 2 + s) * N + r] = G[s][(long)r * ld + 0];
+    const int nr = r1 - r0;
+    const int nv = (N + VW - 1) / VW;  // 16-byte vectors per row; VW nv <= ld (ld is padded to 32)
+    const LocalSmem L = local_smem<T>(N, ld, nrmax);
+    double* us = (double*)(smem_raw + L.us);
+    T* rowb = (T*)(smem_raw + L.rowb);
+    T* patch = (T*)(smem_raw + L.patch);
+    T* colb = (T*)(smem_raw + L.colb);
+    int8_t* xs = (int8_t*)(smem_raw + L.xs);
+    uint8_t* rp = (uint8_t*)(smem_raw + L.rp);
+    __shared__ int s_b, s_nneg;
+    __shared__ T s_f[2];
+    __shared__ double s_maxr;
+    for (int i = tid; i < N; i += nt) {
+        us[i] = u[i];
+        xs[i] = xl_g[i];
+        rp[i] = replay ? replay[i] : 0;
     }
-    if (r0 == 0 && nrows > 0)
-        for (int e = tid; e < 2 * N; e += nt) {
-            int s = e / N, c = e % N;
-            rowbuf[(0 * 2 + s) * N + c] = G[s][c];
-        }
+    if (tid == 0) {
+        s_nneg = 0;
+        s_maxr = 0.0;
+    }
+    for (int e = tid; e < 2 * nr; e += nt) {  // diagonals of the own rows into buffer 0
+        const int s = e / nr, r = r0 + e % nr;
+        diag[(0 * 2 + s) * N + r] = (s ? Gd : Gu)[(long)r * ld + r];
+    }
     if (!grid_barrier(bar, nblk, err)) return;
 
-    double sign = so.sign ? *so.sign : 1.0;
+    // flip constants in T (x = +1: index 0, x = -1: index 1), selected without local-memory indexing
+    const T df00 = (T)sp.dflip[0][0], df01 = (T)sp.dflip[0][1], df10 = (T)sp.dflip[1][0],
+            df11 = (T)sp.dflip[1][1], sf0 = (T)sp.sflip[0], sf1 = (T)sp.sflip[1];
     int n_acc = 0;
-    double maxr = 0.0;
-    const int per_spin = nrows * N;
-    // flip constants in T: {dflip[0][+], dflip[0][-], dflip[1][+], dflip[1][-], sflip[+], sflip[-]}
-    const T cd[6] = {(T)sp.dflip[0][0], (T)sp.dflip[0][1], (T)sp.dflip[1][0], (T)sp.dflip[1][1], (T)sp.sflip[0],
-                     (T)sp.sflip[1]};
-    for (int i = 0; i < N; ++i) {
-        const int cur = i & 1, nxt = cur ^ 1;
-        const T* col0 = colbuf + (cur * 2 + 0) * N;
-        const T* col1 = colbuf + (cur * 2 + 1) * N;
-        const T* row0 = rowbuf + (cur * 2 + 0) * N;
-        const T* row1 = rowbuf + (cur * 2 + 1) * N;
-        // one thread per CTA takes the Metropolis decision (every CTA reaches the same one)
-        if (tid == 0) {
-            // ratio arithmetic in the bulk precision T (no FP64 division on the FP32 path)
-            const int xi = xs[i] > 0 ? 0 : 1;
-            const T d0 = xi ? cd[1] : cd[0], d1 = xi ? cd[3] : cd[2], sfl = xi ? cd[5] : cd[4];
-            const T rr0 = T(1) + d0 * (T(1) - col0[i]);
-            const T rr1 = T(1) + d1 * (T(1) - col1[i]);
-            const T R = sfl * rr0 * rr1;
-            bool acc = replay ? (replay[i] != 0) : (u[i] < (double)fabs(R));
-            if (!isfinite(R)) {
-                if (b == 0) set_err(err, DEV_NUMERIC);
-                acc = false;
+    int p = 0;      // next site to test (warp 0)
+    int cur = 0;    // diagonal buffer the scan reads
+    int pend = -1;  // own row whose new values wait in `patch`
+    for (;;) {
+        if (pend >= 0) {  // every CTA has read row pend in the previous phase: store its new values
+            for (int e = tid; e < 2 * nv; e += nt) {
+                const int s = e / nv, v = e - s * nv;
+                *(V*)((s ? Gd : Gu) + (long)pend * ld + (long)v * VW) = *(const V*)(patch + (long)s * ld + (long)v * VW);
             }
-            s_acc = acc ? 1 : 0;
-            s_f[0] = d0 / rr0;
-            s_f[1] = d1 / rr1;
-            if (b == 0) {
-                so.dec[i] = acc ? 1 : 0;
-                so.ratio[i] = (double)R;
-                if (acc) {
-                    xl_g[i] = (int8_t)(-xs[i]);
-                    if (R < T(0)) sign = -sign;
-                    maxr = fmax(maxr, (double)fabs(R));
+            pend = -1;
+        }
+        if (tid < 32) {
+            const T* d0 = diag + (cur * 2 + 0) * N;
+            const T* d1 = diag + (cur * 2 + 1) * N;
+            int bsel = N;
+            while (p < N) {
+                const int q = p + tid;
+                bool acc = false;
+                T R = T(0), rr0 = T(1), rr1 = T(1), del0 = df00, del1 = df10;
+                int xi = 0;
+                if (q < N) {
+                    // ratio arithmetic in the bulk precision T (no FP64 division on the FP32 path)
+                    xi = xs[q] > 0 ? 0 : 1;
+                    del0 = xi ? df01 : df00;
+                    del1 = xi ? df11 : df10;
+                    rr0 = T(1) + del0 * (T(1) - __ldcg(d0 + q));
+                    rr1 = T(1) + del1 * (T(1) - __ldcg(d1 + q));
+                    R = (xi ? sf1 : sf0) * rr0 * rr1;
+                    acc = replay ? (rp[q] != 0) : (us[q] < (double)fabs(R));
+                    if (!isfinite(R)) {
+                        if (b == 0) set_err(err, DEV_NUMERIC);
+                        acc = false;
+                    }
                 }
+                const unsigned ball = __ballot_sync(0xffffffffu, acc);
+                const int first = ball ? __ffs(ball) - 1 : 32;
+                if (b == 0 && q < N && tid <= first) {
+                    so.dec[q] = (tid == first) ? 1 : 0;
+                    so.ratio[q] = (double)R;
+                }
+                if (tid == first) {
+                    s_f[0] = del0 / rr0;
+                    s_f[1] = del1 / rr1;
+                    if (b == 0) {
+                        xl_g[q] = (int8_t)(-xs[q]);
+                        if (R < T(0)) s_nneg += 1;
+                        s_maxr = fmax(s_maxr, (double)fabs(R));
+                    }
+                }
+                __syncwarp();
+                if (first < 32) {
+                    bsel = p + first;
+                    p = bsel + 1;
+                    break;
+                }
+                p += 32;
             }
+            if (tid == 0) s_b = bsel;
         }
         __syncthreads();
-        if (s_acc) {
-            ++n_acc;
-            // G_s[r, c] -= f_s * G_s[r, i] * (delta_ic - G_s[i, c]) over the own rows of both spins
-            for (int s = 0; s < 2; ++s) {
-                const T* cl = s ? col1 : col0;
-                const T* rw = s ? row1 : row0;
-                const T f = s_f[s];
-                T* Gsp = G[s];
-                int r = r0 + tid / N, c = tid % N;
-                const int rstep = nt / N, cstep = nt % N;
-                for (int e = tid; e < per_spin; e += nt) {
-                    const T rowv = (c == i ? T(1) : T(0)) - rw[c];
-                    T* gp = Gsp + (long)r * ld + c;
-                    const T nv = *gp - f * cl[r] * rowv;
-                    *gp = nv;
-                    if (c == i + 1) colbuf[(nxt * 2 + s) * N + r] = nv;
-                    if (r == i + 1) rowbuf[(nxt * 2 + s) * N + c] = nv;
-                    r += rstep;
-                    c += cstep;
-                    if (c >= N) { c -= N; ++r; }
-                }
+        const int bs = s_b;
+        if (bs >= N) break;
+        ++n_acc;
+        // row b of both spins (e_b^T - G[b, :], zero beyond N) and column b of the own rows.  Data
+        // written by other CTAs (row b, the diagonals) is read past L1 (ld.global.cg).
+        for (int e = tid; e < 2 * nv; e += nt) {
+            const int s = e / nv, v = e - s * nv;
+            T gv[VW];
+            *(V*)gv = __ldcg((const V*)((s ? Gd : Gu) + (long)bs * ld + (long)v * VW));
+            T* o = rowb + (long)s * ld + (long)v * VW;
+#pragma unroll
+            for (int l = 0; l < VW; ++l) {
+                const int c = v * VW + l;
+                o[l] = c < N ? ((c == bs ? T(1) : T(0)) - gv[l]) : T(0);
             }
-        } else if (i + 1 < N) {
-            for (int e = tid; e < 2 * nrows; e += nt) {
-                int s = e / nrows, r = r0 + e % nrows;
-                colbuf[(nxt * 2 + s) * N + r] = G[s][(long)r * ld + (i + 1)];
-            }
-            if (i + 1 >= r0 && i + 1 < r1)
-                for (int e = tid; e < 2 * N; e += nt) {
-                    int s = e / N, c = e % N;
-                    rowbuf[(nxt * 2 + s) * N + c] = G[s][(long)(i + 1) * ld + c];
-                }
         }
+        for (int e = tid; e < 2 * nr; e += nt) {
+            const int s = e / nr, r = e - s * nr;
+            colb[s * nrmax + r] = (s ? Gd : Gu)[(long)(r0 + r) * ld + bs];
+        }
+        __syncthreads();
+        // G_s[r, :] += (-f_s G_s[r, b]) (e_b^T - G_s[b, :]) on the own rows: 16-byte accesses, all
+        // LOCAL_UNROLL loads of a thread issued before its stores.  The owner's row b goes to `patch`.
+        const int per = nr * nv, tot = 2 * per;
+        for (int e0 = tid; e0 < tot; e0 += LOCAL_UNROLL * nt) {
+            V gv[LOCAL_UNROLL];
+            int sr[LOCAL_UNROLL], rr[LOCAL_UNROLL], vv[LOCAL_UNROLL];
+#pragma unroll
+            for (int q = 0; q < LOCAL_UNROLL; ++q) {
+                const int e = e0 + q * nt;
+                sr[q] = -1;
+                if (e < tot) {
+                    const int s = e >= per ? 1 : 0, rem = e - s * per;
+                    const int r = rem / nv;
+                    sr[q] = s;
+                    rr[q] = r;
+                    vv[q] = rem - r * nv;
+                    gv[q] = *(const V*)((s ? Gd : Gu) + (long)(r0 + r) * ld + (long)vv[q] * VW);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < LOCAL_UNROLL; ++q) {
+                if (sr[q] < 0) continue;
+                const int s = sr[q], r = rr[q], v = vv[q];
+                const T a = -s_f[s] * colb[s * nrmax + r];
+                vfma_rank1<T>(gv[q], a, *(const V*)(rowb + (long)s * ld + (long)v * VW));
+                if (r0 + r == bs) *(V*)(patch + (long)s * ld + (long)v * VW) = gv[q];
+                else *(V*)((s ? Gd : Gu) + (long)(r0 + r) * ld + (long)v * VW) = gv[q];
+            }
+        }
+        // the new diagonals of the own rows (the same fused multiply-add as the element of G)
+        for (int e = tid; e < 2 * nr; e += nt) {
+            const int s = e / nr, r = e - s * nr, gr = r0 + r;
+            const T a = -s_f[s] * colb[s * nrmax + r];
+            diag[((cur ^ 1) * 2 + s) * N + gr] = fma(a, rowb[(long)s * ld + gr], diag[(cur * 2 + s) * N + gr]);
+        }
+        if (bs >= r0 && bs < r1) pend = bs;
+        cur ^= 1;
         if (!grid_barrier(bar, nblk, err)) return;
     }
     if (b == 0 && tid == 0) {
-        if (so.sign) *so.sign = sign;
+        if (so.sign && (s_nneg & 1)) *so.sign = -*so.sign;
         so.stats[0] += N;
         so.stats[1] += n_acc;
         so.stats[2] += n_acc;
-        *so.maxr = fmax(*so.maxr, maxr);
+        *so.maxr = fmax(*so.maxr, s_maxr);
     }
 }
 
+// Grid size of the local kernel: at most max_blocks CTAs (one per SM) and at least one row each.
 template <typename T>
 cudaError_t launch_local(cudaStream_t st, T* Gu, T* Gd, int8_t* xl, const double* u, const uint8_t* replay,
                          const SiteParams& sp, SliceOut so, T* colbuf, T* rowbuf, GridBar* bar, int* err,
                          int max_blocks) {
-    int nblk = max_blocks < sp.N ? max_blocks : sp.N;
-    size_t shm = (size_t)sp.N;
+    (void)rowbuf;
+    const int nblk = max_blocks < sp.N ? max_blocks : sp.N;
+    if (nblk < 1) return cudaErrorInvalidValue;
+    const int nrmax = (sp.N + nblk - 1) / nblk;
+    const size_t shm = local_smem<T>(sp.N, sp.ld, nrmax).total;
+    cudaError_t e = ensure_smem_attr((const void*)local_kernel<T>, shm);
+    if (e != cudaSuccess) return e;
     SiteParams spc = sp;
-    void* args[] = {&Gu, &Gd, &xl, &u, &replay, &spc, &so, &colbuf, &rowbuf, &bar, &err};
+    int nrm = nrmax;
+    void* args[] = {&Gu, &Gd, &xl, &u, &replay, &spc, &so, &colbuf, &bar, &err, &nrm};
     count_launch();
-    return cudaLaunchCooperativeKernel((void*)local_kernel<T>, dim3(nblk), dim3(512), args, shm, st);
+    return cudaLaunchCooperativeKernel((void*)local_kernel<T>, dim3(nblk), dim3(LOCAL_THREADS), args, shm, st);
 }
-
 // ---------------------------------------------------------------------------
 // window chain: delayed (MODE 1) and block force-bias (MODE 2)
 // ---------------------------------------------------------------------------
@@ -722,15 +838,11 @@ cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T*
                                 int s0, int n, int nb, WindowBufs wb, const T* blk, int* err, Batch bt) {
     (void)Gd;  // spin down follows spin up (N x ld) in every walker's G
     size_t shm = window_smem<T>(n);
-    static bool attr_set[2] = {false, false};
-    const int mi = (mode == AFQMC_MODE_DELAYED) ? 0 : 1;
-    auto kfn = (mode == AFQMC_MODE_DELAYED) ? (void*)window_kernel<T, AFQMC_MODE_DELAYED>
-                                            : (void*)window_kernel<T, AFQMC_MODE_BLOCKFB>;
-    if (!attr_set[mi]) {
-        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)window_smem<T>(WinCap<T>::NW));
+    auto kfn = (mode == AFQMC_MODE_DELAYED) ? (const void*)window_kernel<T, AFQMC_MODE_DELAYED>
+                                            : (const void*)window_kernel<T, AFQMC_MODE_BLOCKFB>;
+    {
+        cudaError_t e = ensure_smem_attr(kfn, window_smem<T>(WinCap<T>::NW));
         if (e != cudaSuccess) return e;
-        attr_set[mi] = true;
     }
     if (bt.nwk < 1) bt.nwk = 1;
     count_launch();
@@ -873,12 +985,9 @@ cudaError_t launch_next_block(cudaStream_t st, const T* Gu, const T* Gd, const S
     (void)Gd;
     constexpr int NW = WinCap<T>::NW;
     const size_t shm = (2 * (size_t)NW + 2 * NB_ROWS) * (NW + 1) * sizeof(T);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t ea =
-            cudaFuncSetAttribute((void*)next_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    {
+        cudaError_t ea = ensure_smem_attr((const void*)next_block_kernel<T>, shm);
         if (ea != cudaSuccess) return ea;
-        attr = true;
     }
     count_launch();
     const int nbx = (nn + NB_ROWS - 1) / NB_ROWS;

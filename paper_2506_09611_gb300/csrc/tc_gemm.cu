@@ -506,12 +506,9 @@ bool cached_tmap(CUtensorMap* tm, const void* ptr, int es, int rows, int cols, l
 template <int BN, bool SPLIT>
 cudaError_t tc_launch(cudaStream_t st, const TcGemmArgs& g) {
     using Cfg = TcCfg<BN, SPLIT>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute((void*)tc_gemm_kernel<BN, SPLIT, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    {
+        cudaError_t e = ensure_smem_attr((const void*)tc_gemm_kernel<BN, SPLIT, false>, Cfg::SMEM);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     CUtensorMap tmA, tmB;
     const int ba = g.sA ? g.batch : 1, bb = g.sB ? g.batch : 1;
@@ -537,13 +534,9 @@ cudaError_t tc_launch(cudaStream_t st, const TcGemmArgs& g) {
 template <int BN>
 cudaError_t tc_oz_launch(cudaStream_t st, const TcOzArgs& g) {
     using Cfg = TcCfg<BN, false, true>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e =
-            cudaFuncSetAttribute((void*)tc_gemm_kernel<BN, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 Cfg::SMEM);
+    {
+        cudaError_t e = ensure_smem_attr((const void*)tc_gemm_kernel<BN, false, true>, Cfg::SMEM);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     CUtensorMap tmA, tmB;
     const long sa = (long)g.M * g.Kp, sb = (long)g.N * g.Kp;

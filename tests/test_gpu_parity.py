@@ -219,7 +219,8 @@ def test_full_size_40x40_fp32_replay():
 @pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
 def test_apply_flips_matches_oracle(precision, tol):
     """afqmc_apply_flips (stateless Woodbury rank-m update) = the oracle's sequential rank-1
-    updates with the same sites forced to accept; m = 0 and an out-of-range site are no-ops."""
+    updates with the same sites forced to accept; m = 0 is a no-op, and an out-of-range site is
+    reported as AFQMC_ERR_ARG with G left unchanged."""
     torch = pytest.importorskip("torch")
     L, ns, M, ell = 6, 15, 6, 3
     N = L * L
@@ -247,8 +248,10 @@ def test_apply_flips_matches_oracle(precision, tol):
     afqmc.afqmc_apply_flips(precision, N, ld, Gd_dev[0].data_ptr(), Gd_dev[1].data_ptr(), s_dev.data_ptr(),
                             d_dev.data_ptr(), 0, stream)
     bad = torch.tensor([3, N + 4], dtype=torch.int32, device="cuda")
-    afqmc.afqmc_apply_flips(precision, N, ld, Gd_dev[0].data_ptr(), Gd_dev[1].data_ptr(), bad.data_ptr(),
-                            d_dev.data_ptr(), 2, stream)
+    with pytest.raises(afqmc.AfqmcError) as ex:  # found on the device, reported, G untouched
+        afqmc.afqmc_apply_flips(precision, N, ld, Gd_dev[0].data_ptr(), Gd_dev[1].data_ptr(), bad.data_ptr(),
+                                d_dev.data_ptr(), 2, stream)
+    assert ex.value.code == -1
     torch.cuda.synchronize()
     for s, ref in enumerate((Gu_ref, Gd_ref)):
         got = Gd_dev[s][:, :N].double().cpu().numpy()

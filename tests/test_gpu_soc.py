@@ -153,10 +153,12 @@ def test_state_errors():
         ctx.sweep_slice(3, +1, "delayed", k=4)
 
 
-@pytest.mark.parametrize("mode,k,nb", [("blockfb", 1, 16), ("delayed", 64, 1)])
+@pytest.mark.parametrize("mode,k,nb", [("blockfb", 1, 16), ("blockfb", 1, 64), ("delayed", 64, 1)])
 def test_fp32_full_size_24x24_one_slice(mode, k, nb):
     """The 24 x 24 lattice (2N = 1152 complex orbitals, half filling) at the bench's launch
-    configuration: one replayed slice against the oracle, G within 1e-5."""
+    configurations: one replayed slice against the oracle, G within 1e-5.  nb = 64 is the block
+    size whose window (a 128 x 128 complex block, inverted by Gauss-Jordan with 2 x 2 pivots) runs
+    without the pipelined flush."""
     L, n_e, M, stab = 24, 576, 2, 2
     ctx, w = make(L, n_e, M, stab, precision="fp32", gemm="tc3", seed=29)
     N = L * L
