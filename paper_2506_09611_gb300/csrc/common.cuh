@@ -97,6 +97,32 @@ __device__ __forceinline__ bool grid_barrier(GridBar* b, unsigned int nblocks, i
     return s_ok != 0;
 }
 
+// Grid-wide arrival counter for cooperative (co-resident) launches, for one thread per CTA: the
+// k-th barrier adds one to *ctr with release semantics and completes when *ctr reaches k nblocks.
+// The counter starts at zero for the launch and only grows, so a barrier costs one reduction and
+// the polling, with no reset.  The caller synchronises its CTA before (so that every write of the
+// CTA precedes the arrival) and after.  The wait is bounded: after about two seconds of
+// %globaltimer, or once another CTA has recorded an error, it records DEV_TIMEOUT (or keeps the
+// error) and returns false.
+__device__ __forceinline__ bool grid_arrive_wait(unsigned int* ctr, unsigned int target, int* err) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
+    unsigned long long t0 = 0;
+    unsigned int polls = 0;
+    while (ld_acquire_u32(ctr) < target) {
+        if ((++polls & 255u) == 0u) {
+            if (read_err(err) != 0) return false;
+            unsigned long long t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > 2000000000ULL) {
+                set_err(err, DEV_TIMEOUT);
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
 // Barrier `id` (1..15) over the first `nthreads` threads of the block (whole warps).
 __device__ __forceinline__ void named_barrier_sync(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");

@@ -62,20 +62,21 @@ __device__ __forceinline__ double hs_log_scalar(const SiteParams& sp, int x) {
 // local update: persistent cooperative kernel, one grid barrier per ACCEPT
 // ---------------------------------------------------------------------------
 // CTA b owns the rows [r0, r1) of both spins.  A phase handles one accepted site:
-//   1. every CTA scans the sites after the last accept with warp 0 (32 sites per round; a ballot
-//      finds the first acceptance) from a copy of the two diagonals in global memory.  Every CTA
-//      reads the same values and runs the same arithmetic, so all reach the same site b;
+//   1. thread 0 of every CTA passes the grid barrier (one release reduction on an arrival counter,
+//      then polling), and warp 0 at once scans the sites after the last accept (32 sites per round;
+//      a ballot finds the first acceptance) from a copy of the two diagonals in global memory.
+//      Every CTA reads the same values and runs the same arithmetic, so all reach the same site b;
 //   2. every CTA reads row b of both spins (e_b^T - G[b, :]) and column b of its own rows;
 //   3. every CTA applies G_s[r, c] -= f_s G_s[r, b] (delta_bc - G_s[b, c]) to its own rows with
-//      16-byte accesses, and writes the new diagonal of its rows to the other diagonal buffer;
-//   4. one grid barrier.
+//      16-byte accesses and several loads in flight per thread, and writes the new diagonal of its
+//      rows to the other diagonal buffer.
 // A rejected site leaves G unchanged, so it costs a diagonal read and no barrier.  Two cross-CTA
-// hazards inside a phase are avoided without a second barrier:
+// hazards inside a phase are avoided without a second grid barrier:
 //   * the diagonals are double-buffered by phase parity: the scan reads the buffer the previous
 //     phase wrote, and the update writes the other one;
 //   * every CTA reads row b while its owner updates its rows, so the owner keeps its new row b in
-//     shared memory and stores it to G at the start of the next phase, after the barrier (no CTA
-//     reads row b again in this slice).
+//     shared memory and stores it to G in the next phase, after the barrier (no CTA reads row b
+//     again in this slice).
 // The diagonal copy is computed with the same fused multiply-add as the element of G, so the two
 // stay bit-identical.  diag: [2 buffers][2 spins][N].
 template <typename T> struct Vec16;
@@ -94,7 +95,8 @@ __device__ __forceinline__ void vfma_rank1<double>(double2& g, double a, const d
 }
 
 constexpr int LOCAL_THREADS = 1024;
-constexpr int LOCAL_UNROLL = 4;
+// Loads in flight per thread in the row update (the largest count that fits 64 registers)
+template <typename T> struct LocalUnroll { static constexpr int U = sizeof(T) == 4 ? 6 : 4; };
 
 // Shared-memory layout of local_kernel (byte offsets, 16-byte aligned where vectors are read).
 struct LocalSmem {
@@ -147,10 +149,15 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_kernel(T* Gu, T* Gd, i
         s_maxr = 0.0;
     }
     for (int e = tid; e < 2 * nr; e += nt) {  // diagonals of the own rows into buffer 0
-        const int s = e / nr, r = r0 + e % nr;
+        const int s = e >= nr ? 1 : 0, r = r0 + e - s * nr;
         diag[(0 * 2 + s) * N + r] = (s ? Gd : Gu)[(long)r * ld + r];
     }
-    if (!grid_barrier(bar, nblk, err)) return;
+    // This thread's elements of the own rows of both spins: e = tid + j nt over (row R < 2 nr,
+    // vector v < nv), walked without divisions.
+    const int rows2 = 2 * nr;
+    const int R0 = tid / nv, v0 = tid - R0 * nv, dR = nt / nv, dv = nt - dR * nv;
+    unsigned int* ctr = &bar->count;
+    unsigned int nbar = 0;  // grid barriers passed (thread 0)
 
     // flip constants in T (x = +1: index 0, x = -1: index 1), selected without local-memory indexing
     const T df00 = (T)sp.dflip[0][0], df01 = (T)sp.dflip[0][1], df10 = (T)sp.dflip[1][0],
@@ -159,26 +166,26 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_kernel(T* Gu, T* Gd, i
     int p = 0;      // next site to test (warp 0)
     int cur = 0;    // diagonal buffer the scan reads
     int pend = -1;  // own row whose new values wait in `patch`
+    __syncthreads();
     for (;;) {
-        if (pend >= 0) {  // every CTA has read row pend in the previous phase: store its new values
-            for (int e = tid; e < 2 * nv; e += nt) {
-                const int s = e / nv, v = e - s * nv;
-                *(V*)((s ? Gd : Gu) + (long)pend * ld + (long)v * VW) = *(const V*)(patch + (long)s * ld + (long)v * VW);
-            }
-            pend = -1;
-        }
+        // grid barrier (thread 0), then the scan for the next accept (warp 0); the other warps wait
+        // at the block barrier below
         if (tid < 32) {
+            int ok = 1;
+            if (tid == 0) ok = grid_arrive_wait(ctr, (++nbar) * (unsigned int)nblk, err) ? 1 : 0;
+            __syncwarp();
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            int bsel = ok ? N : -1;
             const T* d0 = diag + (cur * 2 + 0) * N;
             const T* d1 = diag + (cur * 2 + 1) * N;
-            int bsel = N;
-            while (p < N) {
+            while (ok && p < N) {
                 const int q = p + tid;
                 bool acc = false;
                 T R = T(0), rr0 = T(1), rr1 = T(1), del0 = df00, del1 = df10;
-                int xi = 0;
                 if (q < N) {
-                    // ratio arithmetic in the bulk precision T (no FP64 division on the FP32 path)
-                    xi = xs[q] > 0 ? 0 : 1;
+                    // ratio arithmetic in the bulk precision T (no FP64 division on the FP32 path);
+                    // the diagonals were written by other CTAs: read past L1
+                    const int xi = xs[q] > 0 ? 0 : 1;
                     del0 = xi ? df01 : df00;
                     del1 = xi ? df11 : df10;
                     rr0 = T(1) + del0 * (T(1) - __ldcg(d0 + q));
@@ -217,12 +224,19 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_kernel(T* Gu, T* Gd, i
         }
         __syncthreads();
         const int bs = s_b;
+        if (bs < 0) return;  // a bounded wait expired, or another CTA recorded an error
+        if (pend >= 0) {     // every CTA has read row pend in the previous phase: store its new values
+            for (int e = tid; e < 2 * nv; e += nt) {
+                const int s = e >= nv ? 1 : 0, v = e - s * nv;
+                *(V*)((s ? Gd : Gu) + (long)pend * ld + (long)v * VW) = *(const V*)(patch + (long)s * ld + (long)v * VW);
+            }
+        }
         if (bs >= N) break;
         ++n_acc;
-        // row b of both spins (e_b^T - G[b, :], zero beyond N) and column b of the own rows.  Data
-        // written by other CTAs (row b, the diagonals) is read past L1 (ld.global.cg).
+        // row b of both spins (e_b^T - G[b, :], zero beyond N; written by another CTA: read past L1)
+        // and column b of the own rows (row pend from `patch`, whose store above may be in flight)
         for (int e = tid; e < 2 * nv; e += nt) {
-            const int s = e / nv, v = e - s * nv;
+            const int s = e >= nv ? 1 : 0, v = e - s * nv;
             T gv[VW];
             *(V*)gv = __ldcg((const V*)((s ? Gd : Gu) + (long)bs * ld + (long)v * VW));
             T* o = rowb + (long)s * ld + (long)v * VW;
@@ -233,48 +247,55 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_kernel(T* Gu, T* Gd, i
             }
         }
         for (int e = tid; e < 2 * nr; e += nt) {
-            const int s = e / nr, r = e - s * nr;
-            colb[s * nrmax + r] = (s ? Gd : Gu)[(long)(r0 + r) * ld + bs];
+            const int s = e >= nr ? 1 : 0, r = e - s * nr;
+            colb[s * nrmax + r] = (r0 + r == pend) ? patch[(long)s * ld + bs] : (s ? Gd : Gu)[(long)(r0 + r) * ld + bs];
         }
+        pend = -1;
         __syncthreads();
         // G_s[r, :] += (-f_s G_s[r, b]) (e_b^T - G_s[b, :]) on the own rows: 16-byte accesses, all
-        // LOCAL_UNROLL loads of a thread issued before its stores.  The owner's row b goes to `patch`.
-        const int per = nr * nv, tot = 2 * per;
-        for (int e0 = tid; e0 < tot; e0 += LOCAL_UNROLL * nt) {
-            V gv[LOCAL_UNROLL];
-            int sr[LOCAL_UNROLL], rr[LOCAL_UNROLL], vv[LOCAL_UNROLL];
+        // LocalUnroll<T>::U loads of a thread issued before its stores.  The owner's row b goes to `patch`.
+        const T nf0 = -s_f[0], nf1 = -s_f[1];
+        {
+            int R = R0, v = v0;
+            while (R < rows2) {
+                V gv[LocalUnroll<T>::U];
+                int pk[LocalUnroll<T>::U];  // R * 4096 + v
 #pragma unroll
-            for (int q = 0; q < LOCAL_UNROLL; ++q) {
-                const int e = e0 + q * nt;
-                sr[q] = -1;
-                if (e < tot) {
-                    const int s = e >= per ? 1 : 0, rem = e - s * per;
-                    const int r = rem / nv;
-                    sr[q] = s;
-                    rr[q] = r;
-                    vv[q] = rem - r * nv;
-                    gv[q] = *(const V*)((s ? Gd : Gu) + (long)(r0 + r) * ld + (long)vv[q] * VW);
+                for (int q = 0; q < LocalUnroll<T>::U; ++q) {
+                    pk[q] = R * 4096 + v;
+                    if (R < rows2) {
+                        const int s = R >= nr ? 1 : 0, r = R - s * nr;
+                        gv[q] = *(const V*)((s ? Gd : Gu) + (long)(r0 + r) * ld + (long)v * VW);
+                    }
+                    v += dv;
+                    R += dR;
+                    if (v >= nv) {
+                        v -= nv;
+                        ++R;
+                    }
                 }
-            }
 #pragma unroll
-            for (int q = 0; q < LOCAL_UNROLL; ++q) {
-                if (sr[q] < 0) continue;
-                const int s = sr[q], r = rr[q], v = vv[q];
-                const T a = -s_f[s] * colb[s * nrmax + r];
-                vfma_rank1<T>(gv[q], a, *(const V*)(rowb + (long)s * ld + (long)v * VW));
-                if (r0 + r == bs) *(V*)(patch + (long)s * ld + (long)v * VW) = gv[q];
-                else *(V*)((s ? Gd : Gu) + (long)(r0 + r) * ld + (long)v * VW) = gv[q];
+                for (int q = 0; q < LocalUnroll<T>::U; ++q) {
+                    const int Rq = pk[q] >> 12, vq = pk[q] & 4095;
+                    if (Rq >= rows2) break;
+                    const int s = Rq >= nr ? 1 : 0, r = Rq - s * nr;
+                    const T a = (s ? nf1 : nf0) * colb[s * nrmax + r];
+                    vfma_rank1<T>(gv[q], a, *(const V*)(rowb + (long)s * ld + (long)vq * VW));
+                    T* dst = (r0 + r == bs) ? patch + (long)s * ld + (long)vq * VW
+                                            : (s ? Gd : Gu) + (long)(r0 + r) * ld + (long)vq * VW;
+                    *(V*)dst = gv[q];
+                }
             }
         }
         // the new diagonals of the own rows (the same fused multiply-add as the element of G)
         for (int e = tid; e < 2 * nr; e += nt) {
-            const int s = e / nr, r = e - s * nr, gr = r0 + r;
-            const T a = -s_f[s] * colb[s * nrmax + r];
+            const int s = e >= nr ? 1 : 0, r = e - s * nr, gr = r0 + r;
+            const T a = (s ? nf1 : nf0) * colb[s * nrmax + r];
             diag[((cur ^ 1) * 2 + s) * N + gr] = fma(a, rowb[(long)s * ld + gr], diag[(cur * 2 + s) * N + gr]);
         }
         if (bs >= r0 && bs < r1) pend = bs;
         cur ^= 1;
-        if (!grid_barrier(bar, nblk, err)) return;
+        __syncthreads();  // every write of the CTA precedes thread 0's arrival at the next barrier
     }
     if (b == 0 && tid == 0) {
         if (so.sign && (s_nneg & 1)) *so.sign = -*so.sign;
@@ -340,18 +361,55 @@ static size_t window_smem(int n) {
     return g + s1 + vec + misc;
 }
 
-// G_s[r][c] += f_s * G_s[r][a] * G_s[a][c] for r, c in (a, n), both spins; 32 x 32 thread tiles.
-template <typename T>
-__device__ __forceinline__ void trailing_update(T* Gs, int n, int P, int a, T f0, T f1, int tid, int nt) {
-    const int tx = tid & 31, ty = tid >> 5, ny = nt >> 5;
-    for (int s = 0; s < 2; ++s) {
-        T* Gb = Gs + (size_t)s * n * P;
-        const T f = s ? f1 : f0;
-        for (int r = a + 1 + ty; r < n; r += ny) {
-            const T g = f * Gb[r * P + a];
-            for (int c = a + 1 + tx; c < n; c += 32) Gb[r * P + c] = fma(g, Gb[a * P + c], Gb[r * P + c]);
+// G_s[r][c] += f_s G_s[r][a] G_s[a][c] for r, c in (a, n), both spins, by the warps [0, nw) of the
+// caller's numbering: a warp takes whole rows of the flattened (spin, row) range, its lanes the
+// columns a + 1 + lane + 32 j (j < CS).  Row a is not written by the update, so each lane keeps its
+// part of row a of both spins in registers, and two rows are loaded before either is stored (the
+// compiler cannot tell that the stores miss the next row's loads).  Column a is not written either,
+// which lets warp 0 of the delayed window read it while the other warps update.
+template <typename T, int CS>
+__device__ __forceinline__ void trailing_rows(T* Gs, int n, int P, int a, T f0, T f1, int warp, int nw, int lane) {
+    const int w = n - a - 1;
+    if (w <= 0) return;
+    T ra0[CS], ra1[CS];
+#pragma unroll
+    for (int j = 0; j < CS; ++j) {
+        const int c = a + 1 + lane + 32 * j;
+        ra0[j] = c < n ? Gs[a * P + c] : T(0);
+        ra1[j] = c < n ? Gs[(n + a) * P + c] : T(0);
+    }
+    for (int R = warp; R < 2 * w; R += 2 * nw) {
+        const int R2 = R + nw;
+        const bool two = R2 < 2 * w;
+        const int s1 = R >= w ? 1 : 0, s2 = R2 >= w ? 1 : 0;
+        T* row1 = Gs + (s1 * n + a + 1 + R - s1 * w) * P;
+        T* row2 = Gs + (s2 * n + a + 1 + R2 - s2 * w) * P;  // dereferenced only when `two`
+        const T g1 = (s1 ? f1 : f0) * row1[a];
+        const T g2 = two ? (s2 ? f1 : f0) * row2[a] : T(0);
+        T x1[CS], x2[CS];
+#pragma unroll
+        for (int j = 0; j < CS; ++j) {
+            const int c = a + 1 + lane + 32 * j;
+            x1[j] = c < n ? row1[c] : T(0);
+            x2[j] = (two && c < n) ? row2[c] : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < CS; ++j) {
+            const int c = a + 1 + lane + 32 * j;
+            if (c < n) {
+                row1[c] = fma(g1, s1 ? ra1[j] : ra0[j], x1[j]);
+                if (two) row2[c] = fma(g2, s2 ? ra1[j] : ra0[j], x2[j]);
+            }
         }
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void trailing_update(T* Gs, int n, int P, int a, T f0, T f1, int warp, int nw, int lane) {
+    constexpr int CSMAX = WinCap<T>::NW / 32;  // n <= NW
+    if (n <= 32) trailing_rows<T, 1>(Gs, n, P, a, f0, f1, warp, nw, lane);
+    else if (CSMAX == 2 || n <= 64) trailing_rows<T, 2>(Gs, n, P, a, f0, f1, warp, nw, lane);
+    else trailing_rows<T, CSMAX>(Gs, n, P, a, f0, f1, warp, nw, lane);
 }
 
 // W = -F U1^{-1} L1^{-1} of the window from the frozen coefficients in the block (see the window
@@ -625,7 +683,8 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                 // warps 1..31: G[r][c] += f G[r][a] G[a][c] for r, c > a, both spins.  Rows and
                 // columns <= a are never touched again, so the block keeps row a and column a as
                 // they were when site a was accepted (the coefficients of the flush recursion).
-                trailing_update(Gs, n, P, idx[pend], -s_fk[0][pend], -s_fk[1][pend], tid - 32, nt - 32);
+                trailing_update(Gs, n, P, idx[pend], -s_fk[0][pend], -s_fk[1][pend], (tid >> 5) - 1, (nt >> 5) - 1,
+                                tid & 31);
             }
             __syncthreads();
             const int np = s_pend[it & 1];
@@ -792,7 +851,7 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                     dl[1 * n + k] = -(double)s_phi[1][q];
                     xw[a] = (int8_t)(-xw[a]);
                 }
-                trailing_update(Gs, n, P, a, s_phi[0][q], s_phi[1][q], tid, nt);
+                trailing_update(Gs, n, P, a, s_phi[0][q], s_phi[1][q], tid >> 5, nt >> 5, tid & 31);
                 __syncthreads();
             }
             if (tid == 0) s_m = mb + nF;
