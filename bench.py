@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed walker population leg")
     ap.add_argument("--no-soc", action="store_true", help="skip the spin-orbit-coupled leg")
     ap.add_argument("--no-separable", action="store_true", help="skip the separable-wrap leg")
+    ap.add_argument("--no-precision", action="store_true", help="skip the per-precision accuracy report")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-bulk sweep")
+    ap.add_argument("--no-ksweep", action="store_true", help="skip the 40x40 delay-rank sweep")
+    ap.add_argument("--no-config16", action="store_true", help="skip the 16x16 local / delayed legs")
     ap.add_argument("--soc-slices", type=int, default=20, help="timed slice-steps per mode of the SOC leg")
     ap.add_argument("--gemm", default="tc3", choices=["tc3", "simt", "tf32"],
                     help="FP32 GEMM engine: tcgen05 three-term TF32 split, FP32 SIMT, or one TF32 pass")
@@ -288,40 +292,18 @@ def main():
     update_only = updates_per_step * args.steps / (upd_ms / 1e3)
 
     # ---------------- bounded comparison samples (same context, continuing the chain) ------------
-    cmp = {}
-    sample = [(l, +1) for l in range(1, args.cmp_slices + 1)]
-    back = [(l, -1) for l in range(args.cmp_slices, 0, -1)]
-    for mode, k, nb in (("local", args.k, args.nb), ("blockfb", args.k, args.nb), ("delayed", args.k, args.nb)):
-        ctx.set_profiling(True)
-        stats = []
-        for (ell, d) in sample:
-            st = ctx.sweep_slice(ell, d, mode, k=k, nb=nb, want_stats=True, stream=stream)
-            stats.append((st[0].proposals, st[0].accepts, st[0].flipped))
-            if ell % STAB == 0:
-                afqmc.afqmc_recompute_G(ctx.h, None, stream)
-        p = ctx.profile()
-        ctx.set_profiling(False)
-        # walk back to slice 0 so the next sample starts from the same position
-        for (ell, d) in back:
-            ctx.sweep_slice(ell, d, "delayed", k=args.k, nb=nb, stream=stream)
-            if (ell - 1) % STAB == 0:
-                afqmc.afqmc_recompute_G(ctx.h, None, stream)
-        umode = p["local"]["ms"] if mode == "local" else p["chain"]["ms"]
-        umode += p["prep"]["ms"]
-        n_upd = N * len(sample)
-        props = sum(s[0] for s in stats)
-        acc = sum(s[1] for s in stats)
-        cmp[mode] = {"update_only": n_upd / (umode / 1e3),
-                     "with_wrap": n_upd / ((umode + p["wrap"]["ms"]) / 1e3),
-                     "acceptance": acc / max(props, 1), "slices": len(sample),
-                     "k" if mode == "delayed" else ("nb" if mode == "blockfb" else "kind"):
-                         (k if mode == "delayed" else (nb if mode == "blockfb" else "rank-1 GER per accept"))}
+    cmp, cmp_prof = compare_modes(afqmc, ctx, stream, args.k, args.nb, args.cmp_slices)
     speedup = {m: cmp[m]["update_only"] / cmp["local"]["update_only"] for m in ("delayed", "blockfb")}
+    ksweep = None
+    if not args.no_ksweep:
+        ksweep = optional_leg("k_sweep", lambda: delayed_k_sweep(afqmc, ctx, stream, (32, 64, 128), 10, N))
 
     # ---------------- roofline of the dominant kernel ----------------
     pk, pk_src = peaks()
     kernels = kernel_rooflines(prof, args.gemm, pk, pk_src, args.steps)
     roof = dict(kernels[0]) if kernels else None
+    l2_gbs = optional_leg("l2_copy", lambda: l2_copy_bandwidth(torch))
+    kernels += local_and_chain_rooflines(cmp_prof, pk, pk_src, l2_gbs if isinstance(l2_gbs, float) else None)
 
     # ---------------- the same sweep with CUDA-graph replay (profiling off) ----------------
     ctx.set_graphs(True)
@@ -354,6 +336,15 @@ def main():
     if not args.no_separable:
         sep = optional_leg("separable_wrap", lambda: separable_wrap_leg(afqmc, torch, stream, args, seed,
                                                                         prof["wrap"]["ms"] / args.steps))
+    c16 = None
+    if not args.no_config16:
+        c16 = optional_leg("config_16x16", lambda: config_16x16_leg(afqmc, torch, stream, args, seed))
+    prec = None
+    if not args.no_precision:
+        prec = optional_leg("precision_report", lambda: precision_report(afqmc, stream, args, seed))
+    f64 = None
+    if not args.no_fp64:
+        f64 = optional_leg("fp64_bulk", lambda: fp64_bulk_leg(afqmc, torch, stream, args, seed))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         def cpu_leg():
@@ -376,6 +367,8 @@ def main():
                                    if k not in ("elim", "wrap_gemm", "flush_gemm", "lu_o", "solve", "dgemm")},
             "compare_sample": cmp,
             "speedup_update_only_vs_local": speedup,
+            "k_sweep_40x40": ksweep,
+            "config_16x16": c16,
             "G_err_fp32_vs_fp64_recompute": {"max": max(drifts) if drifts else None,
                                              "median": statistics.median(drifts) if drifts else None,
                                              "slices_between_recomputes": STAB},
@@ -388,11 +381,271 @@ def main():
             "batched_population": batch,
             "soc": soc_res,
             "separable_wrap": sep,
+            "precision_report": prec,
+            "fp64_bulk": f64,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def compare_modes(afqmc, ctx, stream, k, nb, n_slices, stab=STAB, elem_bytes=4):
+    """Local, block force-bias and delayed updates on the same walker: each mode sweeps slices
+    1..n_slices forward under the library's phase profiler (its recomputes included), then the walker
+    walks back to slice 0 with the delayed update so that the next mode starts from the same place.
+    update_only = sites / (prep + site loop) time, the paper's "time for update"; the window loop's
+    interval ends after the last rank-m product, so overlapped flushes count only where they delay
+    the loop.  Returns the per-mode summary and the raw per-mode profiles and counts."""
+    cmp, raw = {}, {}
+    sample = [(l, +1) for l in range(1, n_slices + 1)]
+    back = [(l, -1) for l in range(n_slices, 0, -1)]
+    for mode in ("local", "blockfb", "delayed"):
+        ctx.set_profiling(True)
+        stats = []
+        for (ell, d) in sample:
+            st = ctx.sweep_slice(ell, d, mode, k=k, nb=nb, want_stats=True, stream=stream)
+            stats.append((st[0].proposals, st[0].accepts, st[0].flipped))
+            if ell % stab == 0:
+                afqmc.afqmc_recompute_G(ctx.h, None, stream)
+        p = ctx.profile()
+        ctx.set_profiling(False)
+        for (ell, d) in back:
+            ctx.sweep_slice(ell, d, "delayed", k=k, nb=nb, stream=stream)
+            if (ell - 1) % stab == 0:
+                afqmc.afqmc_recompute_G(ctx.h, None, stream)
+        umode = (p["local"]["ms"] if mode == "local" else p["chain"]["ms"]) + p["prep"]["ms"]
+        n_upd = N * len(sample)
+        props = sum(x[0] for x in stats)
+        acc = sum(x[1] for x in stats)
+        flips = sum(x[2] for x in stats)
+        cmp[mode] = {"update_only": n_upd / (umode / 1e3),
+                     "with_wrap": n_upd / ((umode + p["wrap"]["ms"]) / 1e3),
+                     "acceptance": acc / max(props, 1), "slices": len(sample),
+                     "k" if mode == "delayed" else ("nb" if mode == "blockfb" else "kind"):
+                         (k if mode == "delayed" else (nb if mode == "blockfb" else "rank-1 update per accept"))}
+        raw[mode] = {"prof": p, "proposals": props, "accepts": acc, "flipped": flips, "slices": len(sample),
+                     "elem_bytes": elem_bytes}
+    return cmp, raw
+
+
+def local_and_chain_rooflines(raw, pk, pk_src, l2_gbs):
+    """The local update's rank-1 read-modify-write and the delayed window chain, from the comparison
+    sample's intervals.
+    * local_kernel: each accepted flip reads and writes both spins' G once: 2 x 2 x N^2 x s bytes
+      (s = element size); achieved = those bytes x accepts / the kernel's time (one launch per slice).
+      G of both spins (20.5 MB in FP32) stays in the 129 MB L2, so the fraction is given against the
+      measured HBM copy bandwidth and against an L2-resident copy measured in this run.
+    * window chain (window kernel + next-window block, one CTA per walker): latency-bound; reported as
+      time per proposed site and per accept."""
+    out = []
+    lo = raw["local"]
+    ph = lo["prof"]["local"]
+    if ph["intervals"] and lo["accepts"]:
+        per_acc = 2 * 2 * N * N * lo["elem_bytes"]
+        ach = per_acc * lo["accepts"] / (ph["ms"] / 1e3) / 1e9
+        out.append({"kernel": "local_kernel (rank-1 update per accepted flip, both spins, one cooperative launch "
+                              "per slice)", "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / pk["hbm_gbs"], "l2_copy_gbs": l2_gbs,
+                    "frac_of_l2_copy": (ach / l2_gbs) if l2_gbs else None,
+                    "traffic": None, "launches": ph["intervals"], "ms_per_launch": ph["ms"] / ph["intervals"],
+                    "us_per_accept": ph["ms"] * 1e3 / lo["accepts"], "work_per_accept": per_acc,
+                    "accepts_per_launch": lo["accepts"] / ph["intervals"],
+                    "peak_source": "measured HBM copy (of %s); G is L2-resident: l2_copy_gbs is a copy of a "
+                                   "32 MB working set timed in this run" % pk_src})
+    de = raw["delayed"]
+    ch = de["prof"]["chain"]
+    if ch["intervals"] and de["accepts"]:
+        out.append({"kernel": "window chain (window_kernel + next_block_kernel, delayed, one CTA)",
+                    "bound": "latency", "ns_per_site": ch["ms"] * 1e6 / de["proposals"],
+                    "ns_per_accept": ch["ms"] * 1e6 / de["accepts"], "ms_per_slice": ch["ms"] / de["slices"],
+                    "acceptance": de["accepts"] / max(de["proposals"], 1),
+                    "note": "the serial Metropolis chain of the delayed update; the bound it is compared "
+                            "with is stated in the design notes (one 1024-thread block barrier plus one "
+                            "warp scan per accept)"})
+    return out
+
+
+def l2_copy_bandwidth(torch, mb=16, reps=200):
+    """Copy bandwidth of an L2-resident working set (src + dst = 2 x mb MB < 129 MB L2): read + write
+    bytes / time, CUDA events over `reps` back-to-back copies after a warm-up."""
+    n = mb * 1024 * 1024 // 4
+    a = torch.ones(n, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    for _ in range(10):
+        b.copy_(a)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        b.copy_(a)
+    e1.record()
+    torch.cuda.synchronize()
+    return 2.0 * n * 4 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+
+PREC_SLICES = 10  # one recompute period of the headline workload
+
+
+def precision_report(afqmc, stream, args, seed):
+    """Accuracy of each FP32 bulk variant at the headline workload (40 x 40, U = 6, delayed k), over
+    one recompute period from the FP64 G(0): slices 1..10 forward, then the FP64 recompute.
+    Reference: an FP64-bulk walker running free (decisions, ratios and G after every slice).
+    For each variant (tc3: tensor-core three-term TF32 split; tf32: one TF32 pass; simt: FP32 FMA
+    pipes; separable: the L-point wrap passes, FP32):
+      replay: the variant replays the reference's decisions.  Per slice: ||G - G_64||_F / ||G_64||_F
+              (mean over the spins), the largest relative ratio error over the sites, and the number
+              of decisions that would flip (u < |R| with the variant's ratio against the reference's,
+              the same uniforms); at slice 10 the drift the FP64 recompute reports.
+      free:   the variant runs free with the reference's seed: the first (slice, site) whose decision
+              differs from the reference's, or null if none within the period."""
+    P = inputs.trial_state(L, L, NS)
+    X = inputs.initial_fields(M, N, seed=seed)
+    Pcat = np.concatenate([P.ravel(), P.ravel()])
+    S = min(PREC_SLICES, STAB)
+
+    def make(precision, gemm, wrap):
+        c = afqmc.Context(M, dtau=DTAU, U=U, t=T_HOP, precision=precision, stab_every=STAB, seed=seed, gemm=gemm)
+        c.init_walkers([L], [NS], [NS], Pcat, X, stream=stream)
+        if wrap:
+            c.set_wrap(wrap)
+        return c
+
+    ref = make("fp64", "tc3", None)
+    refG, refdec, refrat = [], [], []
+    try:
+        for ell in range(1, S + 1):
+            ref.sweep_slice(ell, +1, "delayed", k=min(args.k, 64), stream=stream)
+            refdec.append(ref.decisions(0)[:N].copy())
+            refrat.append(ref.ratios(0)[:N].copy())
+            refG.append([ref.G(0, 0), ref.G(0, 1)])
+    finally:
+        ref.close()
+    out = {}
+    for name, gemm, wrap in (("fp32_tc3", "tc3", None), ("tf32", "tf32", None), ("fp32_simt", "simt", None),
+                             ("fp32_separable_wrap", "tc3", "separable")):
+        c = make("fp32", gemm, wrap)
+        errs, rerr, flips = [], [], []
+        try:
+            for ell in range(1, S + 1):
+                rep = np.zeros(2 * N, np.uint8)
+                rep[:N] = refdec[ell - 1]
+                c.sweep_slice(ell, +1, "delayed", k=args.k, replay=rep, stream=stream)
+                r = c.ratios(0)[:N]
+                r64 = refrat[ell - 1]
+                u = inputs.uniforms(seed, 0, ell - 1, 2 * N)[:N]
+                rerr.append(float(np.max(np.abs(r - r64) / np.maximum(np.abs(r64), 1e-300))))
+                flips.append(int(np.sum((u < np.abs(r)) != (u < np.abs(r64)))))
+                errs.append(float(np.mean([np.linalg.norm(c.G(0, s) - refG[ell - 1][s]) /
+                                           np.linalg.norm(refG[ell - 1][s]) for s in range(2)])))
+            drift = float(c.recompute_G(stream=stream)[0]) if S == STAB else None
+        finally:
+            c.close()
+        c = make("fp32", gemm, wrap)
+        first = None
+        try:
+            for ell in range(1, S + 1):
+                c.sweep_slice(ell, +1, "delayed", k=args.k, stream=stream)
+                diff = np.nonzero(c.decisions(0)[:N] != refdec[ell - 1])[0]
+                if diff.size:
+                    first = {"slice": ell, "site": int(diff[0]), "decisions_before": (ell - 1) * N + int(diff[0])}
+                    break
+        finally:
+            c.close()
+        growth = [errs[i + 1] / errs[i] for i in range(len(errs) - 1) if errs[i] > 0]
+        out[name] = {"G_rel_err_per_slice": errs, "G_err_growth_per_slice_median":
+                     statistics.median(growth) if growth else None,
+                     "max_rel_ratio_err_per_slice": rerr, "decision_flips_per_slice": flips,
+                     "recompute_drift_at_period_end": drift, "first_divergence_free_running": first}
+    return {"workload": f"{L}x{L}, U={U}, delayed k={args.k}, slices 1..{S} from the FP64 G(0)",
+            "reference": "FP64 bulk on the GPU, free-running (its G matches the FP64 oracle to 1e-10 in the "
+                         "parity tests)", "sites_per_slice": N, "variants": out}
+
+
+def fp64_bulk_leg(afqmc, torch, stream, args, seed):
+    """The headline sweep at FP64 bulk (G, the window chain, the flush and the wrap all in FP64; the
+    paper's arithmetic is complex FP64): one full sweep (2M slice-steps + recomputes every 10
+    slices) timed with CUDA events after a warm-up of 2 slice-steps there and back, then the same
+    local / block force-bias / delayed comparison sample as the FP32 line (4 slices each)."""
+    P = inputs.trial_state(L, L, NS)
+    X = inputs.initial_fields(M, N, seed=seed)
+    c = afqmc.Context(M, dtau=DTAU, U=U, t=T_HOP, precision="fp64", stab_every=STAB, seed=seed, gemm=args.gemm)
+    try:
+        c.init_walkers([L], [NS], [NS], np.concatenate([P.ravel(), P.ravel()]), X, stream=stream)
+        k64 = min(args.k, 64)
+        for (ell, d) in ((1, +1), (2, +1), (2, -1), (1, -1)):
+            c.sweep_slice(ell, d, "delayed", k=k64, nb=args.nb, stream=stream)
+        order = [(l, +1) for l in range(1, M + 1)] + [(l, -1) for l in range(M, 0, -1)]
+
+        def sweep():
+            for (ell, d) in order:
+                c.sweep_slice(ell, d, "delayed", k=k64, nb=args.nb, stream=stream)
+                pos = ell if d > 0 else ell - 1
+                if pos % STAB == 0:
+                    afqmc.afqmc_recompute_G(c.h, None, stream)
+
+        ms = tune.time_on_stream(torch, stream, sweep)
+        cmp, _ = compare_modes(afqmc, c, stream, k64, args.nb, 4, elem_bytes=8)
+        return {"value": N * M * 2 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "k": k64,
+                "compare_sample": cmp,
+                "speedup_update_only_vs_local": {m: cmp[m]["update_only"] / cmp["local"]["update_only"]
+                                                 for m in ("delayed", "blockfb")},
+                "note": "one sweep of the headline workload with every step in FP64 (k <= 64: the FP64 window "
+                        "holds 64 sites)"}
+    finally:
+        c.close()
+
+
+def delayed_k_sweep(afqmc, ctx, stream, ks, n_slices, Nsites, stab=STAB):
+    """Update-only rate of the local update and of the delayed update at each delay rank k on one
+    walker: slices 1..n_slices forward under the phase profiler, then back to slice 0 (delayed,
+    untimed) so that every mode starts from the same place."""
+    out = {}
+    sample = [(l, +1) for l in range(1, n_slices + 1)]
+    back = [(l, -1) for l in range(n_slices, 0, -1)]
+    for mode, k in [("local", 1)] + [("delayed", k) for k in ks]:
+        ctx.set_profiling(True)
+        acc = prop = 0
+        for (ell, d) in sample:
+            st = ctx.sweep_slice(ell, d, mode, k=k, want_stats=True, stream=stream)
+            acc += st[0].accepts
+            prop += st[0].proposals
+            if ell % stab == 0:
+                afqmc.afqmc_recompute_G(ctx.h, None, stream)
+        p = ctx.profile()
+        ctx.set_profiling(False)
+        for (ell, d) in back:
+            ctx.sweep_slice(ell, d, "delayed", k=max(ks), stream=stream)
+            if (ell - 1) % stab == 0:
+                afqmc.afqmc_recompute_G(ctx.h, None, stream)
+        t = (p["local"]["ms"] if mode == "local" else p["chain"]["ms"]) + p["prep"]["ms"]
+        out["local" if mode == "local" else f"delayed_k{k}"] = {
+            "update_only": Nsites * n_slices / (t / 1e3),
+            "with_wrap": Nsites * n_slices / ((t + p["wrap"]["ms"]) / 1e3), "acceptance": acc / max(prop, 1)}
+    base = out["local"]["update_only"]
+    for v in out.values():
+        v["speedup_update_only_vs_local"] = v["update_only"] / base
+    return out
+
+
+def config_16x16_leg(afqmc, torch, stream, args, seed):
+    """The 16 x 16 workload (N = 256, U/t = 4, filling 0.875: 112 per spin, dtau = 0.05, M = 80):
+    local update against the delayed update with k in {8, 16, 32, 64}, FP64 and FP32 bulk, on
+    20-slice samples of one walker (its recomputes every 10 slices included)."""
+    L2, U2, M2 = 16, 4.0, 80
+    n2 = inputs.n_sigma_for(L2, FILLING)
+    P = inputs.trial_state(L2, L2, n2)
+    X = inputs.initial_fields(M2, L2 * L2, seed=seed)
+    res = {}
+    for prec in ("fp64", "fp32"):
+        c = afqmc.Context(M2, dtau=DTAU, U=U2, t=T_HOP, precision=prec, stab_every=STAB, seed=seed, gemm=args.gemm)
+        try:
+            c.init_walkers([L2], [n2], [n2], np.concatenate([P.ravel(), P.ravel()]), X, stream=stream)
+            res[prec] = delayed_k_sweep(afqmc, c, stream, (8, 16, 32, 64), 20, L2 * L2)
+        finally:
+            c.close()
+    return {"workload": f"{L2}x{L2} Hubbard, U/t={U2}, n={FILLING} ({n2} per spin), dtau={DTAU}, M={M2}",
+            "unit": UNIT, "by_precision": res}
 
 
 # Nominal dense FP64 rate of a GB300 (no measured FP64 peak is available): 1.25 TFLOP/s at
@@ -409,7 +662,7 @@ OZ_PAIRS = 45
 NCU_TRAFFIC = {"elim": None, "lu_o": None,
                "solve": 25.807104e6 + 0.080896e6,      # lu_solve_kernel, 700 x 700, 1600 right-hand sides
                "wrap_gemm": 30.749184e6 + 0.02432e6,   # tc_gemm_kernel<160, split3>, 1600^3, both spins
-               "flush_gemm": None}
+               "flush_gemm": 22.05568e6 + 0.0}         # gemm_kernel<float>, 1600 x 1600 x m, both spins
 
 
 def fp32_alu_peak(pk):

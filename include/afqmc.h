@@ -236,6 +236,12 @@ int afqmc_set_graphs(afqmc_ctx* ctx, int on);
 #define AFQMC_WRAP_DENSE 0
 #define AFQMC_WRAP_SEPARABLE 1
 int afqmc_set_wrap(afqmc_ctx* ctx, int mode);
+/* Tile width of the separable wrap: each thread block transforms `width` columns (rows) of G over all N
+ * rows (columns) in shared memory, so narrower tiles mean more, smaller blocks and more of them
+ * resident per SM.  width = 0 restores the default (the widest of 16, 8, 4 that fits); otherwise a
+ * multiple of 4 whose tile fits in shared memory for every walker's lattice, else AFQMC_ERR_ARG.
+ * A performance knob (the tuner times it); the result does not depend on it. */
+int afqmc_set_wrap_tile(afqmc_ctx* ctx, int width);
 /* Sync the last stream and return, per phase, the summed device milliseconds, the number of
  * bracketed intervals, and the number of library kernels launched in that phase.  Each array
  * has AFQMC_NPHASE entries; any pointer may be NULL. */

@@ -28,7 +28,7 @@ EXPORTS = ["afqmc_create", "afqmc_destroy", "afqmc_init_walkers", "afqmc_sweep_s
            "afqmc_get_ratios", "afqmc_get_info", "afqmc_debug_uniforms", "afqmc_set_profiling", "afqmc_set_graphs",
            "afqmc_get_profile", "afqmc_launch_count", "afqmc_apply_flips", "afqmc_apply_flips_noalloc",
            "afqmc_debug_gemm", "afqmc_debug_dgemm", "afqmc_debug_ozaki_plan", "afqmc_debug_wait_timeout",
-           "afqmc_set_wrap", "afqmc_strerror"]
+           "afqmc_set_wrap", "afqmc_set_wrap_tile", "afqmc_strerror"]
 WRAPS = {"dense": 0, "separable": 1}
 PHASES = ["prep", "wrap", "local", "chain", "flush", "recompute", "elim", "wrap_gemm", "flush_gemm", "lu_o",
           "solve", "dgemm"]
@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH):
     lib.afqmc_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.afqmc_set_graphs.argtypes = [vp, ctypes.c_int]
     lib.afqmc_set_wrap.argtypes = [vp, ctypes.c_int]
+    lib.afqmc_set_wrap_tile.argtypes = [vp, ctypes.c_int]
     lib.afqmc_get_profile.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.afqmc_launch_count.argtypes = []
     lib.afqmc_apply_flips.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, vp, vp, vp, vp, ctypes.c_int, vp]
@@ -231,6 +232,10 @@ def afqmc_set_wrap(ctx, mode):
     _ck("afqmc_set_wrap", load().afqmc_set_wrap(ctx, WRAPS.get(mode, mode)))
 
 
+def afqmc_set_wrap_tile(ctx, width):
+    _ck("afqmc_set_wrap_tile", load().afqmc_set_wrap_tile(ctx, int(width)))
+
+
 def afqmc_get_profile(ctx):
     n = len(PHASES)
     ms = np.zeros(n)
@@ -339,6 +344,10 @@ class Context:
     def set_wrap(self, mode):
         """"dense" (default) or "separable" (E = Ex (x) Ex, two L-point passes per product)."""
         afqmc_set_wrap(self.h, mode)
+
+    def set_wrap_tile(self, width):
+        """Tile width of the separable wrap (0: the default)."""
+        afqmc_set_wrap_tile(self.h, width)
 
     def profile(self):
         return afqmc_get_profile(self.h)

@@ -155,6 +155,7 @@ struct afqmc_ctx {
     int nsm = 0;
     bool graphs = false;  // replay captured slices (afqmc_set_graphs)
     bool sep_wrap = false;  // wrap with the separable L-point passes (afqmc_set_wrap)
+    int sep_tile = 0;       // their tile width (afqmc_set_wrap_tile; 0: the widest that fits)
     std::vector<Lattice*> lats;
     std::vector<Walker*> w;                        // walker groups
     std::vector<std::pair<int, int>> wmap;         // context walker -> (group, member)
@@ -951,6 +952,7 @@ static int sweep_impl(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int k,
             SepArgs a1, a2;
             sep_wrap_passes(direction, G0, ld, (long)N * ld, w->L, nb2, w->lat->Ex64, w->lat->Exi64, d, dinv, N, &a1,
                             &a2);
+            a1.w = a2.w = ctx->sep_tile;
             PhaseScope pg(ctx, AFQMC_PHASE_WRAP_GEMM, st);
             if ((e = launch_sep<T>(st, a1)) != cudaSuccess) return e;
             return launch_sep<T>(st, a2);
@@ -1424,6 +1426,18 @@ int afqmc_set_wrap(afqmc_ctx* ctx, int mode) {
         }
     }
     ctx->sep_wrap = mode == AFQMC_WRAP_SEPARABLE;
+    return AFQMC_OK;
+}
+
+int afqmc_set_wrap_tile(afqmc_ctx* ctx, int width) {
+    if (!ctx || width < 0) return AFQMC_ERR_ARG;
+    if (width > 0)
+        for (auto* w : ctx->w) {
+            const bool ok = ctx->p.precision == AFQMC_PREC_FP64 ? sep_width_fits<double>(w->L, w->N, width)
+                                                                : sep_width_fits<float>(w->L, w->N, width);
+            if (!ok) return AFQMC_ERR_ARG;
+        }
+    ctx->sep_tile = width;
     return AFQMC_OK;
 }
 

@@ -257,6 +257,8 @@ struct SepArgs;
 template <typename T>
 int sep_width(int L, int N);
 template <typename T>
+bool sep_width_fits(int L, int N, int w);  // a tile of w columns (w % 4 == 0) fits on chip
+template <typename T>
 cudaError_t launch_sep(cudaStream_t st, const SepArgs& a);
 
 template <typename T>

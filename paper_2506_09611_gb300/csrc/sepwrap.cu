@@ -33,13 +33,24 @@ int sep_width(int L, int N) {
 }
 
 template <typename T>
+bool sep_width_fits(int L, int N, int w) {
+    return w >= 4 && w % 4 == 0 && sep_smem_bytes<T>(L, N, w) <= SEP_SMEM_CAP;
+}
+
+template <typename T>
 cudaError_t launch_sep(cudaStream_t st, const SepArgs& a0) {
     SepArgs a = a0;
     const int ext = a.C > 0 ? a.C : a.N;  // the untransformed extent
     if (a.L < 2 || a.N != a.L * a.L || a.batch < 1 || a.C < 0 || (a.side != 0 && a.side != 1) || !a.G || !a.A)
         return cudaErrorInvalidValue;
     if (a.ld < (a.side == 0 ? ext : a.N)) return cudaErrorInvalidValue;
-    a.w = sep_width<T>(a.L, a.N);
+    // a.w > 0 asks for that tile width (a multiple of 4 whose tile fits on chip); 0 takes the widest
+    // tile that fits
+    if (a.w > 0) {
+        if (!sep_width_fits<T>(a.L, a.N, a.w)) return cudaErrorInvalidValue;
+    } else {
+        a.w = sep_width<T>(a.L, a.N);
+    }
     if (a.w == 0) return cudaErrorInvalidValue;  // the lattice is too large for an on-chip tile
     {
         cudaError_t e = ensure_smem_attr((const void*)sep_kernel<T>, SEP_SMEM_CAP);
@@ -52,6 +63,8 @@ cudaError_t launch_sep(cudaStream_t st, const SepArgs& a0) {
 
 template int sep_width<float>(int, int);
 template int sep_width<double>(int, int);
+template bool sep_width_fits<float>(int, int, int);
+template bool sep_width_fits<double>(int, int, int);
 template cudaError_t launch_sep<float>(cudaStream_t, const SepArgs&);
 template cudaError_t launch_sep<double>(cudaStream_t, const SepArgs&);
 

@@ -46,7 +46,7 @@ struct SepArgs {
                                 // matrices (e.g. U_R, N x N_sigma), side 1 C x N ones (U_L)
     const double* A = nullptr;  // L x L one-dimensional factor (symmetric)
     int side = 0;               // 0: left product on the row index, 1: right product on the column index
-    int w = 16;                 // tile width: columns (side 0) or rows (side 1)
+    int w = 0;                  // tile width: columns (side 0) or rows (side 1); 0: the launcher's choice
     const void* rs_in = nullptr;   // nullable scale vectors, one entry per row (rs) or column (cs)
     const void* cs_in = nullptr;   // of the matrix -- N for the transformed index, C for the other --
     const void* rs_out = nullptr;  // applied before (in) or after (out) the product; matrix z uses

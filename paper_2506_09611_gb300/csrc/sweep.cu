@@ -152,10 +152,14 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_kernel(T* Gu, T* Gd, i
         const int s = e >= nr ? 1 : 0, r = r0 + e - s * nr;
         diag[(0 * 2 + s) * N + r] = (s ? Gd : Gu)[(long)r * ld + r];
     }
-    // This thread's elements of the own rows of both spins: e = tid + j nt over (row R < 2 nr,
-    // vector v < nv), walked without divisions.
-    const int rows2 = 2 * nr;
-    const int R0 = tid / nv, v0 = tid - R0 * nv, dR = nt / nv, dv = nt - dR * nv;
+    // This thread's part of the own rows: the 16-byte column vectors v = vt, vt + vstep, ... of the
+    // rows r = g, g + ng, ... of each spin.  With fewer vectors per row than threads the block splits
+    // into ng = nt / nv row groups (one vector per thread, threads beyond ng nv idle); otherwise a
+    // single group whose threads stride over the vectors.
+    const int ng = nv >= nt ? 1 : nt / nv;
+    const int g = nv >= nt ? 0 : tid / nv;
+    const int vt = nv >= nt ? tid : tid - g * nv;
+    const int vstep = nv >= nt ? nt : nv;
     unsigned int* ctr = &bar->count;
     unsigned int nbar = 0;  // grid barriers passed (thread 0)
 
@@ -255,35 +259,29 @@ __global__ void __launch_bounds__(LOCAL_THREADS, 1) local_kernel(T* Gu, T* Gd, i
         // G_s[r, :] += (-f_s G_s[r, b]) (e_b^T - G_s[b, :]) on the own rows: 16-byte accesses, all
         // LocalUnroll<T>::U loads of a thread issued before its stores.  The owner's row b goes to `patch`.
         const T nf0 = -s_f[0], nf1 = -s_f[1];
-        {
-            int R = R0, v = v0;
-            while (R < rows2) {
-                V gv[LocalUnroll<T>::U];
-                int pk[LocalUnroll<T>::U];  // R * 4096 + v
+        constexpr int U = LocalUnroll<T>::U;
+        for (int v = vt; g < ng && v < nv; v += vstep) {
+            for (int sp_ = 0; sp_ < 2; ++sp_) {
+                const V rv = *(const V*)(rowb + (long)sp_ * ld + (long)v * VW);  // e_b^T - G[b, :] here
+                const T nf = sp_ ? nf1 : nf0;
+                const T* cb = colb + sp_ * nrmax;
+                T* base = (sp_ ? Gd : Gu) + (long)r0 * ld + (long)v * VW;
+                T* pb = patch + (long)sp_ * ld + (long)v * VW;
+                for (int r = g; r < nr; r += ng * U) {
+                    V gv[U];
 #pragma unroll
-                for (int q = 0; q < LocalUnroll<T>::U; ++q) {
-                    pk[q] = R * 4096 + v;
-                    if (R < rows2) {
-                        const int s = R >= nr ? 1 : 0, r = R - s * nr;
-                        gv[q] = *(const V*)((s ? Gd : Gu) + (long)(r0 + r) * ld + (long)v * VW);
+                    for (int q = 0; q < U; ++q) {
+                        const int rr = r + q * ng;
+                        if (rr < nr) gv[q] = *(const V*)(base + (long)rr * ld);
                     }
-                    v += dv;
-                    R += dR;
-                    if (v >= nv) {
-                        v -= nv;
-                        ++R;
-                    }
-                }
 #pragma unroll
-                for (int q = 0; q < LocalUnroll<T>::U; ++q) {
-                    const int Rq = pk[q] >> 12, vq = pk[q] & 4095;
-                    if (Rq >= rows2) break;
-                    const int s = Rq >= nr ? 1 : 0, r = Rq - s * nr;
-                    const T a = (s ? nf1 : nf0) * colb[s * nrmax + r];
-                    vfma_rank1<T>(gv[q], a, *(const V*)(rowb + (long)s * ld + (long)vq * VW));
-                    T* dst = (r0 + r == bs) ? patch + (long)s * ld + (long)vq * VW
-                                            : (s ? Gd : Gu) + (long)(r0 + r) * ld + (long)vq * VW;
-                    *(V*)dst = gv[q];
+                    for (int q = 0; q < U; ++q) {
+                        const int rr = r + q * ng;
+                        if (rr < nr) {
+                            vfma_rank1<T>(gv[q], nf * cb[rr], rv);
+                            *(V*)((r0 + rr == bs) ? pb : base + (long)rr * ld) = gv[q];
+                        }
+                    }
                 }
             }
         }
@@ -361,55 +359,18 @@ static size_t window_smem(int n) {
     return g + s1 + vec + misc;
 }
 
-// G_s[r][c] += f_s G_s[r][a] G_s[a][c] for r, c in (a, n), both spins, by the warps [0, nw) of the
-// caller's numbering: a warp takes whole rows of the flattened (spin, row) range, its lanes the
-// columns a + 1 + lane + 32 j (j < CS).  Row a is not written by the update, so each lane keeps its
-// part of row a of both spins in registers, and two rows are loaded before either is stored (the
-// compiler cannot tell that the stores miss the next row's loads).  Column a is not written either,
-// which lets warp 0 of the delayed window read it while the other warps update.
-template <typename T, int CS>
-__device__ __forceinline__ void trailing_rows(T* Gs, int n, int P, int a, T f0, T f1, int warp, int nw, int lane) {
-    const int w = n - a - 1;
-    if (w <= 0) return;
-    T ra0[CS], ra1[CS];
-#pragma unroll
-    for (int j = 0; j < CS; ++j) {
-        const int c = a + 1 + lane + 32 * j;
-        ra0[j] = c < n ? Gs[a * P + c] : T(0);
-        ra1[j] = c < n ? Gs[(n + a) * P + c] : T(0);
-    }
-    for (int R = warp; R < 2 * w; R += 2 * nw) {
-        const int R2 = R + nw;
-        const bool two = R2 < 2 * w;
-        const int s1 = R >= w ? 1 : 0, s2 = R2 >= w ? 1 : 0;
-        T* row1 = Gs + (s1 * n + a + 1 + R - s1 * w) * P;
-        T* row2 = Gs + (s2 * n + a + 1 + R2 - s2 * w) * P;  // dereferenced only when `two`
-        const T g1 = (s1 ? f1 : f0) * row1[a];
-        const T g2 = two ? (s2 ? f1 : f0) * row2[a] : T(0);
-        T x1[CS], x2[CS];
-#pragma unroll
-        for (int j = 0; j < CS; ++j) {
-            const int c = a + 1 + lane + 32 * j;
-            x1[j] = c < n ? row1[c] : T(0);
-            x2[j] = (two && c < n) ? row2[c] : T(0);
-        }
-#pragma unroll
-        for (int j = 0; j < CS; ++j) {
-            const int c = a + 1 + lane + 32 * j;
-            if (c < n) {
-                row1[c] = fma(g1, s1 ? ra1[j] : ra0[j], x1[j]);
-                if (two) row2[c] = fma(g2, s2 ? ra1[j] : ra0[j], x2[j]);
-            }
-        }
-    }
-}
-
+// G_s[r][c] += f_s * G_s[r][a] * G_s[a][c] for r, c in (a, n), both spins; 32 x 32 thread tiles.
 template <typename T>
-__device__ __forceinline__ void trailing_update(T* Gs, int n, int P, int a, T f0, T f1, int warp, int nw, int lane) {
-    constexpr int CSMAX = WinCap<T>::NW / 32;  // n <= NW
-    if (n <= 32) trailing_rows<T, 1>(Gs, n, P, a, f0, f1, warp, nw, lane);
-    else if (CSMAX == 2 || n <= 64) trailing_rows<T, 2>(Gs, n, P, a, f0, f1, warp, nw, lane);
-    else trailing_rows<T, CSMAX>(Gs, n, P, a, f0, f1, warp, nw, lane);
+__device__ __forceinline__ void trailing_update(T* Gs, int n, int P, int a, T f0, T f1, int tid, int nt) {
+    const int tx = tid & 31, ty = tid >> 5, ny = nt >> 5;
+    for (int s = 0; s < 2; ++s) {
+        T* Gb = Gs + (size_t)s * n * P;
+        const T f = s ? f1 : f0;
+        for (int r = a + 1 + ty; r < n; r += ny) {
+            const T g = f * Gb[r * P + a];
+            for (int c = a + 1 + tx; c < n; c += 32) Gb[r * P + c] = fma(g, Gb[a * P + c], Gb[r * P + c]);
+        }
+    }
 }
 
 // W = -F U1^{-1} L1^{-1} of the window from the frozen coefficients in the block (see the window
@@ -562,10 +523,29 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
     const T* G[2] = {Gu, Gd};
     // the n x n diagonal block of both spins: from G, or from the corrected snapshot the
     // previous window's flush prepared (pitch NW, spin stride NW^2)
-    for (int e = tid; e < 2 * n * n; e += nt) {
-        int s = e / (n * n), rem = e % (n * n), a = rem / n, c = rem % n;
-        Gs[(s * n + a) * P + c] = blk ? blk[((size_t)s * WinCap<T>::NW + a) * WinCap<T>::NW + c]
-                                      : G[s][(long)(s0 + a) * ld + (s0 + c)];
+    {  // eight loads in flight per thread before their shared-memory stores
+        constexpr int NL = 8;
+        const int nn2 = n * n;
+        for (int e0 = tid; e0 < 2 * nn2; e0 += NL * nt) {
+            T v[NL];
+#pragma unroll
+            for (int q = 0; q < NL; ++q) {
+                const int e = e0 + q * nt;
+                if (e < 2 * nn2) {
+                    const int s = e >= nn2 ? 1 : 0, rem = e - s * nn2, a = rem / n, c = rem - a * n;
+                    v[q] = blk ? blk[((size_t)s * WinCap<T>::NW + a) * WinCap<T>::NW + c]
+                               : G[s][(long)(s0 + a) * ld + (s0 + c)];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NL; ++q) {
+                const int e = e0 + q * nt;
+                if (e < 2 * nn2) {
+                    const int s = e >= nn2 ? 1 : 0, rem = e - s * nn2, a = rem / n, c = rem - a * n;
+                    Gs[(s * n + a) * P + c] = v[q];
+                }
+            }
+        }
     }
     for (int p = tid; p < n; p += nt) xw[p] = xl_g[s0 + p];
     // the window's site uniforms (and forced decisions) live in shared memory: the scan reads
@@ -683,8 +663,7 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                 // warps 1..31: G[r][c] += f G[r][a] G[a][c] for r, c > a, both spins.  Rows and
                 // columns <= a are never touched again, so the block keeps row a and column a as
                 // they were when site a was accepted (the coefficients of the flush recursion).
-                trailing_update(Gs, n, P, idx[pend], -s_fk[0][pend], -s_fk[1][pend], (tid >> 5) - 1, (nt >> 5) - 1,
-                                tid & 31);
+                trailing_update(Gs, n, P, idx[pend], -s_fk[0][pend], -s_fk[1][pend], tid - 32, nt - 32);
             }
             __syncthreads();
             const int np = s_pend[it & 1];
@@ -851,7 +830,7 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                     dl[1 * n + k] = -(double)s_phi[1][q];
                     xw[a] = (int8_t)(-xw[a]);
                 }
-                trailing_update(Gs, n, P, a, s_phi[0][q], s_phi[1][q], tid >> 5, nt >> 5, tid & 31);
+                trailing_update(Gs, n, P, a, s_phi[0][q], s_phi[1][q], tid, nt);
                 __syncthreads();
             }
             if (tid == 0) s_m = mb + nF;
@@ -992,7 +971,7 @@ template cudaError_t launch_window_chain<double>(cudaStream_t, int, const double
 // Y' = W Yraw and Yraw[l][sn + c] = -G[I_l][sn + c] (the next window's sites are not in I): the
 // block of the next window as it will be after this window's product.  Grid (row blocks of
 // NB_ROWS, spin); each CTA forms (X_blk W) and then (X_blk W) Yraw_n for its rows.
-constexpr int NB_ROWS = 16;
+constexpr int NB_ROWS = 4;
 template <typename T>
 __global__ void __launch_bounds__(256) next_block_kernel(const T* __restrict__ Gu0, long ld, int N, WindowBufs wb0,
                                                          int sn, int nn, T* snap0, long gstride) {
@@ -1013,10 +992,33 @@ __global__ void __launch_bounds__(256) next_block_kernel(const T* __restrict__ G
     for (int q = tid; q < m; q += nt) sidx[q] = wb.idx[q];
     __syncthreads();
     const T* W = (const T*)wb.Wx + (size_t)s * NW * NW;
-    for (int e = tid; e < m * m; e += nt) Ws[(e / m) * PP + e % m] = W[(e / m) * NW + e % m];
-    for (int e = tid; e < m * nn; e += nt) {
-        const int l = e / nn, c = e - l * nn;
-        Ys[l * PP + c] = -G[(long)sidx[l] * ld + sn + c];
+    // the three gathers, four loads in flight per thread before their shared-memory stores
+    constexpr int NL = 4;
+    for (int e0 = tid; e0 < m * m; e0 += NL * nt) {
+        T v[NL];
+#pragma unroll
+        for (int q = 0; q < NL; ++q) {
+            const int e = e0 + q * nt;
+            if (e < m * m) v[q] = W[(e / m) * NW + e % m];
+        }
+#pragma unroll
+        for (int q = 0; q < NL; ++q) {
+            const int e = e0 + q * nt;
+            if (e < m * m) Ws[(e / m) * PP + e % m] = v[q];
+        }
+    }
+    for (int e0 = tid; e0 < m * nn; e0 += NL * nt) {
+        T v[NL];
+#pragma unroll
+        for (int q = 0; q < NL; ++q) {
+            const int e = e0 + q * nt, l = e / nn;
+            if (e < m * nn) v[q] = G[(long)sidx[l] * ld + sn + e - l * nn];
+        }
+#pragma unroll
+        for (int q = 0; q < NL; ++q) {
+            const int e = e0 + q * nt, l = e / nn;
+            if (e < m * nn) Ys[l * PP + e - l * nn] = -v[q];
+        }
     }
     for (int e = tid; e < ra * m; e += nt) {
         const int a = e / m, k = e - a * m;

@@ -46,6 +46,8 @@ def main(argv=None):
     ap.add_argument("--lam", type=float, default=0.5)
     ap.add_argument("--wrap", default="dense", choices=["dense", "separable"],
                     help="wrap products: dense N x N, or two L-point passes with exp(-dtau K) = Ex (x) Ex")
+    ap.add_argument("--wrap-tile", type=int, default=0,
+                    help="tile width of the separable wrap (0: the default; --tune chooses it with --wrap separable)")
     ap.add_argument("--tune", metavar="CACHE", help="choose k and nb by timed trials (cached in this JSON file)")
     ap.add_argument("--tune-slices", type=int, default=10, help="slices of each trial walk (out and back)")
     ap.add_argument("--floor", type=float, default=tune.ACCEPTANCE_FLOOR, help="block force-bias acceptance floor")
@@ -68,16 +70,21 @@ def main(argv=None):
     ctx.init_walkers([L], [ns], [ns], np.concatenate([P.ravel(), P.ravel()]), X, stream=stream)
     if a.wrap != "dense":
         ctx.set_wrap(a.wrap)
+        if a.wrap_tile:
+            ctx.set_wrap_tile(a.wrap_tile)
     tuned = None
     if a.tune:
         key = tune.workload_key(device=torch.cuda.get_device_name(), L=L, n_up=ns, n_dn=ns, U=a.U, t=a.t,
-                                dtau=a.dtau, M=a.M, stab=a.stab, precision=a.precision, gemm=a.gemm)
+                                dtau=a.dtau, M=a.M, stab=a.stab, precision=a.precision, gemm=a.gemm, wrap=a.wrap)
         r = tune.autotune_walker(ctx, torch, stream, lambda st: afqmc.afqmc_recompute_G(ctx.h, None, st),
                                  min(a.tune_slices, a.M), a.stab, floor=a.floor, cache=tune.TuneCache(a.tune),
-                                 key=key, k_max=128 if a.precision == "fp32" else 64)
+                                 key=key, k_max=128 if a.precision == "fp32" else 64,
+                                 tile_candidates=(4, 8, 16) if a.wrap == "separable" else None)
         a.k, a.nb = r["k"].value, r["nb"].value
         tuned = {"k": r["k"].value, "k_ms": r["k"].ms, "nb": r["nb"].value, "nb_ms": r["nb"].ms,
                  "nb_acceptance": r["nb"].acceptance, "cached": not r["k_trials"] and not r["nb_trials"]}
+        if "tile" in r:
+            tuned["wrap_tile"] = r["tile"].value
     order = [(l, +1) for l in range(1, a.M + 1)] + [(l, -1) for l in range(a.M, 0, -1)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()

@@ -208,7 +208,8 @@ def _walk(ctx, stream, mode, k, nb, slices, stab_every, recompute, direction, wa
 
 def autotune_walker(ctx, torch, stream, recompute, slices: int, stab_every: int, k_candidates=None,
                     nb_candidates=None, floor: float = ACCEPTANCE_FLOOR, cache: Optional[TuneCache] = None,
-                    key: str = "", k_max: int = 128, nb_max: int = 32, counted=None) -> dict:
+                    key: str = "", k_max: int = 128, nb_max: int = 32, counted=None,
+                    tile_candidates=None) -> dict:
     """Delay rank and block size for the walkers of an afqmc Context that sit at slice 0.
 
     Each candidate walks slices 1..`slices` forward and back down to slice 0, so the context
@@ -218,8 +219,10 @@ def autotune_walker(ctx, torch, stream, recompute, slices: int, stab_every: int,
     walkers) on the block force-bias walk back.  `recompute(stream)` runs the FP64 recompute
     the context requires at every multiple of `stab_every` (afqmc_recompute_G).  Contexts whose
     sweep_slice reports no statistics (the spin-orbit-coupled one) pass `counted` (see _walk).
-    Returns {"k": Trial, "nb": Trial, "k_trials": [...], "nb_trials": [...]}; cached choices
-    skip their trials."""
+    With tile_candidates (tile widths of the separable wrap, ctx.set_wrap_tile), the width is
+    chosen last, by the time of the delayed walk with the chosen k, and left set on the context.
+    Returns {"k": Trial, "nb": Trial, "k_trials": [...], "nb_trials": [...]} (plus "tile" and
+    "tile_trials" when widths were given); cached choices skip their trials."""
     if not 1 <= slices:
         raise ValueError("slices must be >= 1")
     ks = list(k_candidates) if k_candidates is not None else delay_ranks(k_max, 16)
@@ -243,4 +246,14 @@ def autotune_walker(ctx, torch, stream, recompute, slices: int, stab_every: int,
 
     k, k_trials = tune(cache, key, "k", ks, measure_k)
     nb, nb_trials = tune(cache, key, "nb", nbs, measure_nb, rule=lambda t: block_size(t, floor))
-    return {"k": k, "nb": nb, "k_trials": k_trials, "nb_trials": nb_trials}
+    out = {"k": k, "nb": nb, "k_trials": k_trials, "nb_trials": nb_trials}
+    if tile_candidates is not None:
+        def measure_tile(w):
+            ctx.set_wrap_tile(w)
+            delayed_round_trip(k.value)  # warm-up with this width
+            return time_on_stream(torch, stream, lambda: delayed_round_trip(k.value))
+
+        tile, tile_trials = tune(cache, key, "wrap_tile", tile_candidates, measure_tile)
+        ctx.set_wrap_tile(tile.value)
+        out.update({"tile": tile, "tile_trials": tile_trials})
+    return out

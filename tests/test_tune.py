@@ -225,6 +225,32 @@ def test_autotune_walker_follows_the_sweep_rules_and_returns_to_slice_zero(slice
     assert ctx.calls == calls and r2["k"] == r["k"] and r2["nb"] == r["nb"]  # cached: no sweeps
 
 
+def test_autotune_walker_times_the_wrap_tile_widths_and_leaves_the_fastest_set(tmp_path):
+    class TiledContext(_FakeContext):
+        tile = 0
+
+        def set_wrap_tile(self, w):
+            assert w in (4, 8, 16)
+            self.tile = w
+
+        def sweep_slice(self, ell, direction, mode, k=32, nb=4, want_stats=False, stream=None):
+            if mode == "delayed":
+                self.clock += {0: 0.0, 4: 0.5, 8: 0.2, 16: 0.9}[self.tile]  # 8 is the fastest width
+            return super().sweep_slice(ell, direction, mode, k, nb, want_stats, stream)
+
+    ctx = TiledContext(M=20, stab=10)
+    cache = tune.TuneCache(str(tmp_path / "t.json"))
+    r = tune.autotune_walker(ctx, _ClockTorch(ctx), None, ctx.recompute, 10, 10, k_candidates=[16, 32],
+                             nb_candidates=[4], cache=cache, key="w", tile_candidates=(4, 8, 16))
+    assert r["tile"].value == 8 and ctx.tile == 8
+    assert [t.value for t in r["tile_trials"]] == [4, 8, 16]
+    assert ctx.pos == 0 and not ctx.owed
+    ctx.tile = 0
+    r2 = tune.autotune_walker(ctx, _ClockTorch(ctx), None, ctx.recompute, 10, 10, k_candidates=[16, 32],
+                              nb_candidates=[4], cache=cache, key="w", tile_candidates=(4, 8, 16))
+    assert r2["tile"].value == 8 and ctx.tile == 8 and r2["tile_trials"] == []  # from the cache
+
+
 def test_autotune_walker_with_a_lower_floor_takes_larger_blocks():
     ctx = _FakeContext(M=10, stab=5)
     r = tune.autotune_walker(ctx, _ClockTorch(ctx), None, ctx.recompute, 5, 5, k_candidates=[32],
