@@ -290,6 +290,9 @@ def test_run_cli_tunes_then_walks_with_the_choice(tmp_path, monkeypatch, capsys)
         def set_wrap(self, mode):
             self.wrap = mode
 
+        def set_wrap_tile(self, w):
+            self.tile = w
+
         def close(self):
             pass
 
@@ -324,6 +327,9 @@ def test_run_cli_tunes_then_walks_with_the_choice(tmp_path, monkeypatch, capsys)
     run.main(argv + ["--wrap", "separable"])
     out3 = json.loads(capsys.readouterr().out)
     assert out3["wrap"] == "separable" and made[-1].wrap == "separable"
+    # the separable wrap's walk is keyed apart from the dense one and tunes its tile width too
+    assert out3["tuned"]["cached"] is False and out3["tuned"]["wrap_tile"] in (4, 8, 16)
+    assert made[-1].tile == out3["tuned"]["wrap_tile"]
     with pytest.raises(SystemExit):
         run.main(["--soc", "--wrap", "separable"])
 
