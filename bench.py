@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed walker population leg")
     ap.add_argument("--no-soc", action="store_true", help="skip the spin-orbit-coupled leg")
-    ap.add_argument("--no-separable", action="store_true", help="skip the separable-wrap leg")
+    ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core wrap leg")
     ap.add_argument("--no-precision", action="store_true", help="skip the per-precision accuracy report")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-bulk sweep")
     ap.add_argument("--no-ksweep", action="store_true", help="skip the 40x40 delay-rank sweep")
@@ -194,7 +194,7 @@ def arm_config(k):
     """The workload both arms report (the reference arm times a bounded sample of it)."""
     return {"workload": f"{L}x{L} standard Hubbard, U/t={U}, n={FILLING} ({NS} per spin), "
                         f"dtau={DTAU}, M={M}, FP32 bulk G, delayed k={k}, FP64 recompute "
-                        f"every {STAB} slices",
+                        f"every {STAB} slices, separable wrap (exp(-dtau K) = Ex (x) Ex)",
             "step": "one full sweep (2M = 160 slice-steps: wrap + delayed update) + 16 FP64 recomputes",
             "walkers_per_gpu": 1, "l2": "flushed between timed steps (256 MB write)"}
 
@@ -332,10 +332,10 @@ def main():
     soc_res = None
     if not args.no_soc:
         soc_res = optional_leg("soc", lambda: soc_leg(torch, stream, args, seed))
-    sep = None
-    if not args.no_separable:
-        sep = optional_leg("separable_wrap", lambda: separable_wrap_leg(afqmc, torch, stream, args, seed,
-                                                                        prof["wrap"]["ms"] / args.steps))
+    dense = None
+    if not args.no_dense:
+        dense = optional_leg("dense_wrap", lambda: dense_wrap_leg(afqmc, torch, stream, args, seed,
+                                                                  prof["wrap"]["ms"] / args.steps))
     c16 = None
     if not args.no_config16:
         c16 = optional_leg("config_16x16", lambda: config_16x16_leg(afqmc, torch, stream, args, seed))
@@ -380,7 +380,7 @@ def main():
             "cuda_graphs": graphs,
             "batched_population": batch,
             "soc": soc_res,
-            "separable_wrap": sep,
+            "dense_wrap": dense,
             "precision_report": prec,
             "fp64_bulk": f64,
             "cpu_baseline": cpu,
@@ -662,7 +662,8 @@ OZ_PAIRS = 45
 NCU_TRAFFIC = {"elim": None, "lu_o": None,
                "solve": 25.807104e6 + 0.080896e6,      # lu_solve_kernel, 700 x 700, 1600 right-hand sides
                "wrap_gemm": 30.749184e6 + 0.02432e6,   # tc_gemm_kernel<160, split3>, 1600^3, both spins
-               "flush_gemm": 22.05568e6 + 0.0}         # gemm_kernel<float>, 1600 x 1600 x m, both spins
+               "flush_gemm": 22.05568e6 + 0.0,         # gemm_kernel<float>, 1600 x 1600 x m, both spins
+               "sep": None}
 
 
 def fp32_alu_peak(pk):
@@ -673,7 +674,7 @@ def fp64_alu_peak(pk):
     return 152 * FP64_FMA_PER_SM_CLK * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
-def kernel_rooflines(prof, gemm, pk, pk_src, steps):
+def kernel_rooflines(prof, gemm, pk, pk_src, steps, wrap="separable"):
     """Per-kernel rooflines from the nested per-launch intervals of the timed region:
     achieved = algorithmic work of the launches / their summed CUDA-event durations.
     Returns a list sorted by total time (the first entry is the dominant kernel)."""
@@ -712,7 +713,21 @@ def kernel_rooflines(prof, gemm, pk, pk_src, steps):
                     "peak_source": "measured bf16 burst (of %s); achieved counts every plane-pair pass, includes "
                                    "the digit split and the FP64 epilogues" % pk_src})
     wg = prof.get("wrap_gemm", {"ms": 0.0, "intervals": 0})
-    if wg["intervals"] > 0:
+    if wg["intervals"] > 0 and wrap == "separable":
+        # one launch = one side of the wrap for both spins: two L-point passes over N^2 elements each
+        flop = 2.0 * 2.0 * 2.0 * L * N * N
+        byts = 2 * 2 * N * N * 4
+        ach = flop * wg["intervals"] / (wg["ms"] / 1e3) / 1e12
+        peak = fp32_alu_peak(pk)
+        out.append({"kernel": "sep_kernel (separable wrap: one side, both spins per launch, FP32)", "bound": "alu",
+                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": NCU_TRAFFIC.get("sep"), "launches": wg["intervals"],
+                    "ms_per_launch": wg["ms"] / wg["intervals"], "ms_per_step": wg["ms"] / steps,
+                    "work_per_launch": flop, "bytes_per_launch": byts,
+                    "gbs": byts * wg["intervals"] / (wg["ms"] / 1e3) / 1e9,
+                    "peak_source": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x sm_max_mhz (derived); "
+                                   "arithmetic intensity 20 flop/B puts it above the HBM ridge"})
+    elif wg["intervals"] > 0:
         flop = 2.0 * 2.0 * N ** 3  # one launch = one N x N x N product for both spins
         ach = flop * wg["intervals"] / (wg["ms"] / 1e3) / 1e12
         if gemm == "simt":
@@ -939,19 +954,19 @@ def end_to_end(afqmc, torch, stream, args, seed, rank):
             "note": "create + init_walkers (FP64 left stack and G(0)) + 1 sweep + energy + fields readback"}
 
 
-def separable_wrap_leg(afqmc, torch, stream, args, seed, dense_wrap_ms):
-    """The same 40 x 40 sweep with the wrap through the separable lattice propagator
-    (afqmc_set_wrap: exp(-dtau K) = Ex (x) Ex, two L-point passes per product; not the default):
-    one warm-up sweep, then `steps` timed sweeps with CUDA events on the launching stream (L2
-    flushed between them), and the wrap phase from the library's profiler next to the dense
-    wrap's.  Reported beside the headline, which keeps the dense tensor-core wrap."""
+def dense_wrap_leg(afqmc, torch, stream, args, seed, sep_wrap_ms):
+    """The same 40 x 40 sweep with the dense wrap (afqmc_set_wrap(dense): two N x N x N products per
+    slice-step on the tcgen05 tensor cores, three-term TF32 split for FP32 accuracy): one warm-up
+    sweep, then `steps` timed sweeps with CUDA events on the launching stream (L2 flushed between
+    them), the wrap phase from the library's profiler next to the headline's separable wrap, and
+    the tensor-core product's roofline."""
     P = inputs.trial_state(L, L, NS)
     X = inputs.initial_fields(M, N, seed=seed)
     order = [(l, +1) for l in range(1, M + 1)] + [(l, -1) for l in range(M, 0, -1)]
     c = afqmc.Context(M, dtau=DTAU, U=U, t=T_HOP, precision="fp32", stab_every=STAB, seed=seed, gemm=args.gemm)
     try:
         c.init_walkers([L], [NS], [NS], np.concatenate([P.ravel(), P.ravel()]), X, stream=stream)
-        c.set_wrap("separable")
+        c.set_wrap("dense")
 
         def sweep():
             for (ell, d) in order:
@@ -971,10 +986,13 @@ def separable_wrap_leg(afqmc, torch, stream, args, seed, dense_wrap_ms):
         prof = c.profile()
         c.set_profiling(False)
         ms_sweep = statistics.median(ms)
+        pk, pk_src = peaks()
+        roof = [r for r in kernel_rooflines(prof, args.gemm, pk, pk_src, 1, wrap="dense")
+                if r["kernel"].startswith("wrap GEMM")]
         return {"value": N * M * 2 / (ms_sweep / 1e3), "unit": UNIT, "ms_per_step": ms_sweep,
-                "wrap_ms_per_step": prof["wrap"]["ms"], "dense_wrap_ms_per_step": dense_wrap_ms,
-                "note": "the headline workload with afqmc_set_wrap(separable); the headline keeps the dense "
-                        "tensor-core wrap until this path's GPU parity is confirmed"}
+                "wrap_ms_per_step": prof["wrap"]["ms"], "separable_wrap_ms_per_step": sep_wrap_ms,
+                "wrap_gemm_roofline": roof[0] if roof else None,
+                "note": "the headline workload with afqmc_set_wrap(dense): the tcgen05 tensor-core wrap"}
     finally:
         c.close()
 

@@ -227,18 +227,20 @@ int afqmc_set_profiling(afqmc_ctx* ctx, int on);
 int afqmc_set_graphs(afqmc_ctx* ctx, int on);
 
 /* How the wrap G <- B G B^{-1} (Eqs. BlMat, GrFMat) forms E G and G E^{-1}, E = exp(-dtau K):
- *   AFQMC_WRAP_DENSE      two dense N x N products (the default; tensor cores for FP32 bulk);
+ *   AFQMC_WRAP_DENSE      two dense N x N products (tensor cores for FP32 bulk);
  *   AFQMC_WRAP_SEPARABLE  the periodic L x L lattice has E = Ex (x) Ex, so each product is two
  *                         L-point passes over one index of G (2 L N^2 instead of N^3 multiply-adds),
  *                         in the bulk precision, with the field scalings folded into the passes.
- * Applies to the following slices.  AFQMC_ERR_ARG for a NULL ctx, an unknown mode, or (separable)
- * a walker lattice whose tile does not fit on chip. */
+ * A new context uses the separable wrap for every walker group whose lattice tile fits on chip
+ * (every lattice up to 64 x 64 in FP32) and the dense wrap otherwise; afqmc_set_wrap fixes one
+ * mode for all groups.  Applies to the following slices.  AFQMC_ERR_ARG for a NULL ctx, an unknown
+ * mode, or (separable) a walker lattice whose tile does not fit on chip. */
 #define AFQMC_WRAP_DENSE 0
 #define AFQMC_WRAP_SEPARABLE 1
 int afqmc_set_wrap(afqmc_ctx* ctx, int mode);
 /* Tile width of the separable wrap: each thread block transforms `width` columns (rows) of G over all N
  * rows (columns) in shared memory, so narrower tiles mean more, smaller blocks and more of them
- * resident per SM.  width = 0 restores the default (the widest of 16, 8, 4 that fits); otherwise a
+ * resident per SM.  width = 0 restores the default (4); otherwise a
  * multiple of 4 whose tile fits in shared memory for every walker's lattice, else AFQMC_ERR_ARG.
  * A performance knob (the tuner times it); the result does not depend on it. */
 int afqmc_set_wrap_tile(afqmc_ctx* ctx, int width);

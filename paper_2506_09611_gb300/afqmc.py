@@ -342,7 +342,8 @@ class Context:
         afqmc_set_graphs(self.h, on)
 
     def set_wrap(self, mode):
-        """"dense" (default) or "separable" (E = Ex (x) Ex, two L-point passes per product)."""
+        """"dense" or "separable" (E = Ex (x) Ex, two L-point passes per product); a new context uses
+        the separable wrap wherever the lattice's tile fits on chip."""
         afqmc_set_wrap(self.h, mode)
 
     def set_wrap_tile(self, width):

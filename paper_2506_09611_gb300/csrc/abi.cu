@@ -154,8 +154,8 @@ struct afqmc_ctx {
     int sticky = 0;
     int nsm = 0;
     bool graphs = false;  // replay captured slices (afqmc_set_graphs)
-    bool sep_wrap = false;  // wrap with the separable L-point passes (afqmc_set_wrap)
-    int sep_tile = 0;       // their tile width (afqmc_set_wrap_tile; 0: the widest that fits)
+    int wrap_mode = -1;     // AFQMC_WRAP_* set by afqmc_set_wrap; -1: separable where the lattice fits
+    int sep_tile = 0;       // tile width of the separable passes (afqmc_set_wrap_tile; 0: the default)
     std::vector<Lattice*> lats;
     std::vector<Walker*> w;                        // walker groups
     std::vector<std::pair<int, int>> wmap;         // context walker -> (group, member)
@@ -947,7 +947,9 @@ static int sweep_impl(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int k,
         PhaseScope ps(ctx, AFQMC_PHASE_WRAP, st);
         cudaError_t e = launch_field_scales_T<T>(st, xl, N, ctx->c, d, dinv, N, nwk, bt.xstride);
         if (e != cudaSuccess) return e;
-        if (ctx->sep_wrap) {
+        const bool sep = ctx->wrap_mode == AFQMC_WRAP_SEPARABLE ||
+                         (ctx->wrap_mode < 0 && sep_width<T>(w->L, N) > 0);
+        if (sep) {
             // E = Ex (x) Ex: two passes per product, in place, both spins of every walker
             SepArgs a1, a2;
             sep_wrap_passes(direction, G0, ld, (long)N * ld, w->L, nb2, w->lat->Ex64, w->lat->Exi64, d, dinv, N, &a1,
@@ -1425,7 +1427,7 @@ int afqmc_set_wrap(afqmc_ctx* ctx, int mode) {
             if (!ok) return AFQMC_ERR_ARG;
         }
     }
-    ctx->sep_wrap = mode == AFQMC_WRAP_SEPARABLE;
+    ctx->wrap_mode = mode;
     return AFQMC_OK;
 }
 

@@ -252,7 +252,7 @@ int window_max();      // largest window (sites) the chain kernel holds in share
 // Separable wrap products (sepwrap.cu, tile code in sepwrap.cuh): G <- (A (x) A) G (side 0) or
 // G <- G (A (x) A) (side 1) for the batch of N x N matrices of a SepArgs, with its optional row /
 // column scalings before and after.  cudaErrorInvalidValue when N != L^2 or no tile of at least
-// 4 columns fits on chip.  sep_width: the tile width launch_sep uses (0: none fits).
+// 4 columns fits on chip.  sep_width: the default tile width of launch_sep (0: none fits).
 struct SepArgs;
 template <typename T>
 int sep_width(int L, int N);

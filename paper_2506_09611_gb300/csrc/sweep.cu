@@ -971,10 +971,15 @@ template cudaError_t launch_window_chain<double>(cudaStream_t, int, const double
 // Y' = W Yraw and Yraw[l][sn + c] = -G[I_l][sn + c] (the next window's sites are not in I): the
 // block of the next window as it will be after this window's product.  Grid (row blocks of
 // NB_ROWS, spin); each CTA forms (X_blk W) and then (X_blk W) Yraw_n for its rows.
-constexpr int NB_ROWS = 4;
+constexpr int NB_ROWS = 16;
+constexpr int NB_THREADS = 1024;
+// One CTA per (row block of NB_ROWS rows, spin, walker).  The gathers depend on the accepted sites,
+// so the kernel takes two rounds of global loads: the sites, then every gather of W, Yraw_n and
+// X_blk in one batched pass (eight loads in flight per thread).
 template <typename T>
-__global__ void __launch_bounds__(256) next_block_kernel(const T* __restrict__ Gu0, long ld, int N, WindowBufs wb0,
-                                                         int sn, int nn, T* snap0, long gstride) {
+__global__ void __launch_bounds__(NB_THREADS) next_block_kernel(const T* __restrict__ Gu0, long ld, int N,
+                                                                WindowBufs wb0, int sn, int nn, T* snap0,
+                                                                long gstride) {
     constexpr int NW = WinCap<T>::NW, PP = NW + 1;
     const int wk = blockIdx.z;
     const WindowBufs wb = wb_walker<T>(wb0, wk, N);
@@ -992,37 +997,39 @@ __global__ void __launch_bounds__(256) next_block_kernel(const T* __restrict__ G
     for (int q = tid; q < m; q += nt) sidx[q] = wb.idx[q];
     __syncthreads();
     const T* W = (const T*)wb.Wx + (size_t)s * NW * NW;
-    // the three gathers, four loads in flight per thread before their shared-memory stores
-    constexpr int NL = 4;
-    for (int e0 = tid; e0 < m * m; e0 += NL * nt) {
+    // one index space over the three gathers: [W (m x m) | Yraw_n (m x nn) | X_blk (ra x m)]
+    const int n1 = m * m, n2 = n1 + m * nn, n3 = n2 + ra * m;
+    constexpr int NL = 8;
+    for (int e0 = tid; e0 < n3; e0 += NL * nt) {
         T v[NL];
 #pragma unroll
         for (int q = 0; q < NL; ++q) {
             const int e = e0 + q * nt;
-            if (e < m * m) v[q] = W[(e / m) * NW + e % m];
+            if (e < n1) {
+                const int r = e / m;
+                v[q] = W[r * NW + e - r * m];
+            } else if (e < n2) {
+                const int f = e - n1, l = f / nn;
+                v[q] = -G[(long)sidx[l] * ld + sn + f - l * nn];
+            } else if (e < n3) {
+                const int f = e - n2, aa = f / m;
+                v[q] = G[(long)(sn + a0 + aa) * ld + sidx[f - aa * m]];
+            }
         }
 #pragma unroll
         for (int q = 0; q < NL; ++q) {
             const int e = e0 + q * nt;
-            if (e < m * m) Ws[(e / m) * PP + e % m] = v[q];
+            if (e < n1) {
+                const int r = e / m;
+                Ws[r * PP + e - r * m] = v[q];
+            } else if (e < n2) {
+                const int f = e - n1, l = f / nn;
+                Ys[l * PP + f - l * nn] = v[q];
+            } else if (e < n3) {
+                const int f = e - n2, aa = f / m;
+                Xs[aa * PP + f - aa * m] = v[q];
+            }
         }
-    }
-    for (int e0 = tid; e0 < m * nn; e0 += NL * nt) {
-        T v[NL];
-#pragma unroll
-        for (int q = 0; q < NL; ++q) {
-            const int e = e0 + q * nt, l = e / nn;
-            if (e < m * nn) v[q] = G[(long)sidx[l] * ld + sn + e - l * nn];
-        }
-#pragma unroll
-        for (int q = 0; q < NL; ++q) {
-            const int e = e0 + q * nt, l = e / nn;
-            if (e < m * nn) Ys[l * PP + e - l * nn] = -v[q];
-        }
-    }
-    for (int e = tid; e < ra * m; e += nt) {
-        const int a = e / m, k = e - a * m;
-        Xs[a * PP + k] = G[(long)(sn + a0 + a) * ld + sidx[k]];
     }
     __syncthreads();
     for (int e = tid; e < ra * m; e += nt) {  // T = X_blk W
@@ -1052,7 +1059,8 @@ cudaError_t launch_next_block(cudaStream_t st, const T* Gu, const T* Gd, const S
     }
     count_launch();
     const int nbx = (nn + NB_ROWS - 1) / NB_ROWS;
-    next_block_kernel<T><<<dim3(nbx, 2, bt.nwk), 256, shm, st>>>(Gu, sp.ld, sp.N, wb, sn, nn, snap, bt.gstride);
+    next_block_kernel<T><<<dim3(nbx, 2, bt.nwk), NB_THREADS, shm, st>>>(Gu, sp.ld, sp.N, wb, sn, nn, snap,
+                                                                         bt.gstride);
     return cudaGetLastError();
 }
 

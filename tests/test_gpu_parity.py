@@ -25,11 +25,13 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-def make(L, ns, M, U=4.0, dtau=0.05, stab=4, precision="fp64", seed=11, hs=oracle.HS_SZ_REAL):
+def make(L, ns, M, U=4.0, dtau=0.05, stab=4, precision="fp64", seed=11, hs=oracle.HS_SZ_REAL, wrap=None):
     P = inputs.trial_state(L, L, ns)
     X = inputs.initial_fields(M, L * L, seed=seed)
     ctx = afqmc.Context(M, dtau=dtau, U=U, precision=precision, hs=hs, stab_every=stab, seed=seed)
     ctx.init_walkers([L], [ns], [ns], np.concatenate([P.ravel(), P.ravel()]), X)
+    if wrap is not None:
+        ctx.set_wrap(wrap)
     model = oracle.Model(L, L, 1.0, U, dtau, M, hs)
     w = oracle.Walker(model, P, P, X)
     return ctx, w, P, X
@@ -84,10 +86,11 @@ def _run_sweep(ctx, w, mode, k=16, nb=4, seed=11, slices=None, stab=4, tol=FP64_
     np.testing.assert_array_equal(ctx.fields(0), w.x)
 
 
+@pytest.mark.parametrize("wrap", ["dense", "separable"])
 @pytest.mark.parametrize("mode,k,nb", [("local", 16, 4), ("delayed", 1, 4), ("delayed", 5, 4), ("delayed", 16, 4),
                                        ("blockfb", 16, 1), ("blockfb", 16, 4), ("blockfb", 16, 7)])
-def test_sweep_fp64_free_running(mode, k, nb):
-    ctx, w, P, X = make(4, 7, 8, stab=4)
+def test_sweep_fp64_free_running(mode, k, nb, wrap):
+    ctx, w, P, X = make(4, 7, 8, stab=4, wrap=wrap)
     with ctx:
         _run_sweep(ctx, w, mode, k=k, nb=nb)
 
@@ -123,10 +126,12 @@ def test_delayed_matches_local_on_gpu_8x8():
     assert rel(out["delayed"][2], out["local"][2]) < FP64_TOL
 
 
+@pytest.mark.parametrize("wrap", ["dense", "separable"])
 @pytest.mark.parametrize("mode,k,nb", [("local", 32, 4), ("delayed", 32, 4), ("delayed", 128, 4),
                                        ("blockfb", 32, 8)])
-def test_sweep_fp32_replay(mode, k, nb):
-    """FP32 bulk with the oracle's decisions forced: G within 1e-5 between FP64 recomputes."""
+def test_sweep_fp32_replay(mode, k, nb, wrap):
+    """FP32 bulk with the oracle's decisions forced: G within 1e-5 between FP64 recomputes, with the
+    dense tensor-core wrap and with the separable wrap."""
     L, ns, M, stab = 8, 28, 10, 5
     P = inputs.trial_state(L, L, ns)
     X = inputs.initial_fields(M, L * L, seed=5)
@@ -135,6 +140,7 @@ def test_sweep_fp32_replay(mode, k, nb):
     N = L * L
     with afqmc.Context(M, precision="fp32", stab_every=stab, seed=5) as ctx:
         ctx.init_walkers([L], [ns], [ns], np.concatenate([P.ravel(), P.ravel()]), X)
+        ctx.set_wrap(wrap)
         for s in range(2):
             assert rel(ctx.G(0, s), w.G[s]) < 1e-6
         visit = 0
@@ -205,6 +211,7 @@ def test_full_size_40x40_fp32_replay():
     w = oracle.Walker(model, P, P, X)
     with afqmc.Context(M, U=6.0, precision="fp32", stab_every=stab, seed=2) as ctx:
         ctx.init_walkers([L], [ns], [ns], np.concatenate([P.ravel(), P.ravel()]), X)
+        ctx.set_wrap("dense")  # the tensor-core wrap at full size (the separable one: its own file)
         for ell in (1, 2, 3):
             u = inputs.uniforms(2, 0, ell - 1, 2 * N)
             dec, _, _ = w.sweep_slice(ell, +1, "delayed", u, k=64)
