@@ -65,9 +65,10 @@ def test_an_auxiliary_leg_that_fails_is_reported_in_the_line(capsys):
     assert "soc leg failed" in capsys.readouterr().err
 
 
-def test_separable_wrap_leg_times_whole_sweeps_with_that_wrap():
-    """bench.separable_wrap_leg on a fake device: it switches the context to the separable wrap
-    before the first slice, times whole sweeps (2M slice-steps) and closes the context."""
+def test_dense_wrap_leg_times_whole_sweeps_with_that_wrap():
+    """bench.dense_wrap_leg on a fake device: it switches the context from the default separable
+    wrap to the dense wrap before the first slice, times whole sweeps (2M slice-steps), reports the
+    tensor-core product's roofline from the profile, and closes the context."""
     import types
 
     sys.path.insert(0, ROOT)
@@ -88,7 +89,7 @@ def test_separable_wrap_leg_times_whole_sweeps_with_that_wrap():
 
     class Ctx:
         def __init__(self, M, **kw):
-            self.h, self.wrap, self.closed, self.slices = object(), "dense", False, 0
+            self.h, self.wrap, self.closed, self.slices = object(), "separable", False, 0
             made.append(self)
 
         def init_walkers(self, *a, **kw):
@@ -98,7 +99,7 @@ def test_separable_wrap_leg_times_whole_sweeps_with_that_wrap():
             self.wrap = mode
 
         def sweep_slice(self, ell, d, mode, k=32, nb=4, stream=None):
-            assert self.wrap == "separable" and mode == "delayed"
+            assert self.wrap == "dense" and mode == "delayed"
             self.slices += 1
             clock["t"] += 2.0
 
@@ -106,7 +107,7 @@ def test_separable_wrap_leg_times_whole_sweeps_with_that_wrap():
             pass
 
         def profile(self):
-            return {"wrap": {"ms": 7.5}}
+            return {"wrap": {"ms": 7.5}, "wrap_gemm": {"ms": 7.0, "intervals": 320}}
 
         def close(self):
             self.closed = True
@@ -116,10 +117,12 @@ def test_separable_wrap_leg_times_whole_sweeps_with_that_wrap():
         empty=lambda *a, **k: types.SimpleNamespace(zero_=lambda: None), float32=None)
     fake_afqmc = types.SimpleNamespace(Context=Ctx, afqmc_recompute_G=lambda h, n, s: None)
     args = types.SimpleNamespace(gemm="tc3", steps=2, k=64, nb=16)
-    r = bench.separable_wrap_leg(fake_afqmc, fake_torch, None, args, 1, 52.0)
+    r = bench.dense_wrap_leg(fake_afqmc, fake_torch, None, args, 1, 52.0)
     assert r["ms_per_step"] == 2.0 * 2 * bench.M
     assert r["value"] == bench.N * bench.M * 2 / (r["ms_per_step"] / 1e3)
-    assert r["wrap_ms_per_step"] == 7.5 and r["dense_wrap_ms_per_step"] == 52.0
+    assert r["wrap_ms_per_step"] == 7.5 and r["separable_wrap_ms_per_step"] == 52.0
+    roof = r["wrap_gemm_roofline"]
+    assert roof["bound"] == "tensor" and roof["work_per_launch"] == 2 * 2 * bench.N ** 3
     assert made[-1].closed and made[-1].slices == (1 + 2 + 1) * 2 * bench.M  # warm-up, timed, profiled
 
 
@@ -136,7 +139,7 @@ def test_kernel_rooflines_use_the_documented_work_per_launch():
     pk = {"hbm_gbs": 6789.6, "bf16_tflops": 1911.7, "sm_max_mhz": 2070.0}
     prof = {"wrap_gemm": {"ms": 52.0, "intervals": 320}, "flush_gemm": {"ms": 160.0, "intervals": 4000},
             "solve": {"ms": 13.0, "intervals": 16}, "elim": {"ms": 0.0, "intervals": 0}}
-    out = bench.kernel_rooflines(prof, "tc3", pk, "measured", steps=1)
+    out = bench.kernel_rooflines(prof, "tc3", pk, "measured", steps=1, wrap="dense")
     by = {r["kernel"].split(" ")[0]: r for r in out}
     wrap = by["wrap"]
     assert wrap["work_per_launch"] == 2 * 2 * 1600 ** 3 == 1.6384e10
@@ -151,3 +154,8 @@ def test_kernel_rooflines_use_the_documented_work_per_launch():
     assert "elim" not in {r["kernel"] for r in out} and len(out) == 3
     assert [r["ms_per_step"] for r in out] == sorted((r["ms_per_step"] for r in out), reverse=True)
     assert out[0] is flush  # 160 ms per step: the dominant entry
+    # the separable wrap: one side of the wrap per launch, two L-point passes over both spins' G
+    sep = {r["kernel"].split(" ")[0]: r for r in bench.kernel_rooflines(prof, "tc3", pk, "measured", steps=1)}
+    s = sep["sep_kernel"]
+    assert s["work_per_launch"] == 2 * 2 * 2 * 40 * 1600 ** 2 and s["bound"] == "alu"
+    assert s["peak"] == pytest.approx(152 * 128 * 2 * 2070e6 / 1e12)
