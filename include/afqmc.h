@@ -198,6 +198,25 @@ int afqmc_apply_flips(int precision, int N, long long ld, void* G_up, void* G_dn
 int afqmc_apply_flips_noalloc(int precision, int N, long long ld, void* G_up, void* G_dn, const int* sites,
                               const double* delta, int m, void* stream);
 
+/* Walker representation (Sec. II.C, Eq. GrFMatNew).
+ *   AFQMC_FORM_G  the equal-time Green's function G (N x N per spin) is the state: the wrap moves G
+ *                 (G <- B G B^{-1}) and every window's update is a rank-m product over all of G.
+ *   AFQMC_FORM_T  the paper's own state: U_R (N x Nsigma), U_L (Nsigma x N) and T = (U_L U_R)^{-1}
+ *                 (Nsigma x Nsigma) per spin, G = 1 - U_R T U_L formed only when asked for
+ *                 (afqmc_get_G, afqmc_measure_energy, the drift of afqmc_recompute_G).  The wrap moves
+ *                 the factors (U_R <- B U_R, U_L <- U_L B^{-1}) and leaves T; a window's accepted
+ *                 sites I update T <- T - (T U_L[:, I]) W (U_R[I, :] T) (Eqs. FinalDelay,
+ *                 BlkFrcBsTnew2) and scale the rows I of U_R (Eq. UpdateLTRMat); the recompute forms
+ *                 T = (U_L U_R)^{-1} from the FP64 factors.  The decisions and G equal the G form's.
+ *                 Requires n_up = n_dn for every walker; AFQMC_MODE_LOCAL is not offered (delayed
+ *                 with k = 1 is the local update); afqmc_set_G returns AFQMC_ERR_STATE; no CUDA-graph
+ *                 capture (afqmc_set_graphs is ignored).
+ * afqmc_set_form must come before afqmc_init_walkers (AFQMC_ERR_STATE after it); AFQMC_ERR_ARG for
+ * a NULL ctx or an unknown form.  The default is AFQMC_FORM_G. */
+#define AFQMC_FORM_G 0
+#define AFQMC_FORM_T 1
+int afqmc_set_form(afqmc_ctx* ctx, int form);
+
 /* Profiling.  With profiling on, every phase of afqmc_sweep_slice / afqmc_recompute_G is
  * bracketed by CUDA events recorded on the call's stream (the stream its kernels run on).
  * Phases: */

@@ -28,8 +28,9 @@ EXPORTS = ["afqmc_create", "afqmc_destroy", "afqmc_init_walkers", "afqmc_sweep_s
            "afqmc_get_ratios", "afqmc_get_info", "afqmc_debug_uniforms", "afqmc_set_profiling", "afqmc_set_graphs",
            "afqmc_get_profile", "afqmc_launch_count", "afqmc_apply_flips", "afqmc_apply_flips_noalloc",
            "afqmc_debug_gemm", "afqmc_debug_dgemm", "afqmc_debug_ozaki_plan", "afqmc_debug_wait_timeout",
-           "afqmc_set_wrap", "afqmc_set_wrap_tile", "afqmc_strerror"]
+           "afqmc_set_wrap", "afqmc_set_wrap_tile", "afqmc_set_form", "afqmc_strerror"]
 WRAPS = {"dense": 0, "separable": 1}
+FORMS = {"G": 0, "T": 1}
 PHASES = ["prep", "wrap", "local", "chain", "flush", "recompute", "elim", "wrap_gemm", "flush_gemm", "lu_o",
           "solve", "dgemm"]
 
@@ -82,6 +83,7 @@ def load(path: str = LIB_PATH):
     lib.afqmc_set_graphs.argtypes = [vp, ctypes.c_int]
     lib.afqmc_set_wrap.argtypes = [vp, ctypes.c_int]
     lib.afqmc_set_wrap_tile.argtypes = [vp, ctypes.c_int]
+    lib.afqmc_set_form.argtypes = [vp, ctypes.c_int]
     lib.afqmc_get_profile.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.afqmc_launch_count.argtypes = []
     lib.afqmc_apply_flips.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, vp, vp, vp, vp, ctypes.c_int, vp]
@@ -232,6 +234,10 @@ def afqmc_set_wrap(ctx, mode):
     _ck("afqmc_set_wrap", load().afqmc_set_wrap(ctx, WRAPS.get(mode, mode)))
 
 
+def afqmc_set_form(ctx, form):
+    _ck("afqmc_set_form", load().afqmc_set_form(ctx, FORMS.get(form, form)))
+
+
 def afqmc_set_wrap_tile(ctx, width):
     _ck("afqmc_set_wrap_tile", load().afqmc_set_wrap_tile(ctx, int(width)))
 
@@ -296,10 +302,12 @@ class Context:
     """Owns one afqmc_ctx; methods forward to the C entry points above."""
 
     def __init__(self, M, dtau=0.05, U=4.0, t=1.0, precision="fp64", hs=HS_SZ_REAL, stab_every=10, seed=1,
-                 gemm="tc3"):
+                 gemm="tc3", form="G"):
         self.M = M
         self.h = afqmc_create(hs, PRECS.get(precision, precision), M, stab_every, t, U, dtau, seed,
                               GEMMS.get(gemm, gemm))
+        if form != "G":
+            afqmc_set_form(self.h, form)
         self.n = 0
 
     def init_walkers(self, L, n_up, n_dn, P, fields=None, stream=None):

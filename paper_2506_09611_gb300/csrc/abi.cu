@@ -122,6 +122,14 @@ struct Walker {
     bool oz_Z = false, oz_G = false;  // U_L U_R, and U_R Z
     void* ozw = nullptr;              // digit planes, both products (the spin groups run in turn)
     double* ozs = nullptr;            // row / column scales
+    // T form (afqmc_set_form): U_R [nwk][2][N x nsm], U_L [nwk][2][nsm x N], T [nwk][2][nsm x nsm] in
+    // the bulk precision; the window gathers U_L[:, I] (nsm x NW) and U_R[I, :] (NW x nsm), the
+    // products V = T U_L[:, I], Y = U_R[I, :] T and Y' = W Y, the rows U_R[J, :] T of the next
+    // window (NW x nsm); an FP64 identity (nsm x nsm) for T = (U_L U_R)^{-1}
+    void *TUR = nullptr, *TUL = nullptr, *TT = nullptr;
+    void *ULI = nullptr, *URI = nullptr, *Vt = nullptr, *Yt = nullptr, *Ypt = nullptr, *Pt = nullptr;
+    double* Ieye = nullptr;
+    bool gvalid = true;  // the bulk G buffer holds the current G (the T form forms it on request)
     std::vector<void*> allocs;
     long gstride() const { return 2L * N * ld; }
     int rows_max() const { return N > nsm ? N : nsm; }
@@ -155,6 +163,7 @@ struct afqmc_ctx {
     int nsm = 0;
     bool graphs = false;  // replay captured slices (afqmc_set_graphs)
     int wrap_mode = -1;     // AFQMC_WRAP_* set by afqmc_set_wrap; -1: separable where the lattice fits
+    int form = AFQMC_FORM_G;  // walker representation (afqmc_set_form, before afqmc_init_walkers)
     int sep_tile = 0;       // tile width of the separable passes (afqmc_set_wrap_tile; 0: the default)
     std::vector<Lattice*> lats;
     std::vector<Walker*> w;                        // walker groups
@@ -446,10 +455,12 @@ static cudaError_t stab_cols(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const F
 // Z[b] = (U_L U_R)^{-1} U_L (ns x N) for every (walker, spin) of a spin group (Eq. GrFMatNew):
 // O = U_L U_R (FP64), its pivoted LU, then the substitutions with U_L as right-hand side.
 // sign[j] (nullable) is multiplied by sign(det O) of walker j's spins.
-static cudaError_t form_Z(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac& R, const Fac& Lf, int s0, int ng,
+// O = U_L U_R (FP64) for every (walker, spin) of a spin group, and its pivoted LU in place (Ob,
+// perm2).  sign[j] (nullable) is multiplied by sign(det O) of walker j's spins.
+static cudaError_t form_O(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac& R, const Fac& Lf, int s0, int ng,
                           double* sign) {
     const int N = w->N, ns = w->ns[s0], nmat = w->nwk * ng;
-    const long os = (long)w->nsm * w->nsm, zs = (long)w->nsm * N;
+    const long os = (long)w->nsm * w->nsm;
     cudaError_t e;
     if (w->oz_Z) {
         OzGemmArgs o;
@@ -475,6 +486,15 @@ static cudaError_t form_Z(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac&
         if ((e = launch_lu(st, a)) != cudaSuccess) return e;
     }
     if (sign && (e = launch_lu_sign(st, a, 1, sign, w->visited)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+static cudaError_t form_Z(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac& R, const Fac& Lf, int s0, int ng,
+                          double* sign) {
+    const int N = w->N, ns = w->ns[s0], nmat = w->nwk * ng;
+    const long os = (long)w->nsm * w->nsm, zs = (long)w->nsm * N;
+    cudaError_t e;
+    if ((e = form_O(ctx, w, st, R, Lf, s0, ng, sign)) != cudaSuccess) return e;
     SolveArgs sa;
     sa.LU0 = w->Ob;
     sa.ostride = os;
@@ -527,6 +547,66 @@ static cudaError_t finish_G(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fa
     if (drift && (e = launch_drift<T>(st, Gb, (const T*)w->Gnew, w->ld, N, w->acc2, nmat, bs, gs, ng)) != cudaSuccess)
         return e;
     return launch_cast<T>(st, w->Gnew, w->ld, Gb, w->ld, N, N, nmat, gs, bs);
+}
+
+// ---------------------------------------------------------------------------
+// T form (Sec. II.C: the walker carries U_R, U_L and T = (U_L U_R)^{-1}; G = 1 - U_R T U_L)
+// ---------------------------------------------------------------------------
+// T = O^{-1} for both spins after form_O (the LU solve with the identity as right-hand side, into
+// Z as ns x ns), then the bulk T, U_R and U_L from the FP64 factors R (N x ns) and Lf (ns x N).
+// The T form requires n_up = n_dn, so both spins form one group (ng = 2).
+template <typename T>
+static cudaError_t tform_set(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac& R, const Fac& Lf) {
+    const int N = w->N, ns = w->nsm, nmat = 2 * w->nwk;
+    const long os = (long)ns * ns;
+    SolveArgs sa;
+    sa.LU0 = w->Ob;
+    sa.ostride = os;
+    sa.perm0 = w->perm2;
+    sa.pstride = w->rows_max();
+    sa.B0 = w->Ieye;
+    sa.wstride = 0;
+    sa.sstride = 0;
+    sa.ng = 2;
+    sa.ldb = ns;
+    sa.Z0 = w->Z;
+    sa.zstride = os;
+    sa.ldl = ns;
+    sa.ns = ns;
+    sa.N = ns;
+    sa.nmat = nmat;
+    cudaError_t e;
+    {
+        PhaseScope pv(ctx, AFQMC_PHASE_SOLVE, st);
+        if ((e = launch_lu_solve(st, sa)) != cudaSuccess) return e;
+    }
+    if ((e = launch_cast<T>(st, w->Z, ns, (T*)w->TT, ns, ns, ns, nmat, os, os)) != cudaSuccess) return e;
+    if ((e = launch_cast<T>(st, R.at(0), ns, (T*)w->TUR, ns, N, ns, nmat, R.bstride(2), (long)N * ns)) != cudaSuccess)
+        return e;
+    return launch_cast<T>(st, Lf.at(0), N, (T*)w->TUL, N, ns, N, nmat, Lf.bstride(2), (long)N * ns);
+}
+
+// The bulk G of every walker from its T-form state: G = 1 - (U_R T) U_L, with U_R T in Tbuf.
+template <typename T>
+static cudaError_t tform_form_G(Walker* w, cudaStream_t st) {
+    const int N = w->N, ns = w->nsm, nmat = 2 * w->nwk;
+    const long fs = (long)N * ns;
+    GemmArgs<T> g;
+    g.M = N; g.N = ns; g.K = ns; g.batch = nmat;
+    g.A = (const T*)w->TUR; g.lda = ns; g.sA = fs;
+    g.B = (const T*)w->TT; g.ldb = ns; g.sB = (long)ns * ns;
+    g.C = (T*)w->Tbuf; g.ldc = ns; g.sC = (long)N * w->ld;
+    cudaError_t e = gemm<T>(st, g);
+    if (e != cudaSuccess) return e;
+    GemmArgs<T> h;
+    h.M = N; h.N = N; h.K = ns; h.batch = nmat;
+    h.A = (const T*)w->Tbuf; h.lda = ns; h.sA = (long)N * w->ld;
+    h.B = (const T*)w->TUL; h.ldb = N; h.sB = fs;
+    h.C = (T*)w->G; h.ldc = w->ld; h.sC = (long)N * w->ld;
+    if ((e = gemm<T>(st, h)) != cudaSuccess) return e;
+    if ((e = launch_identity_minus<T>(st, (T*)w->G, w->ld, N, nmat, (long)N * w->ld)) != cudaSuccess) return e;
+    w->gvalid = true;
+    return cudaSuccess;
 }
 
 // U (N x ns) <- B_l U for walker j, spin s, B_l = diag(exp(c_s x_l)) E.  E = Ex (x) Ex on the
@@ -685,6 +765,7 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
         if (L[wi] < 2 || L[wi] > 64) return AFQMC_ERR_ARG;
         int N = L[wi] * L[wi];
         if (n_up[wi] < 1 || n_up[wi] > N || n_dn[wi] < 1 || n_dn[wi] > N) return AFQMC_ERR_ARG;
+        if (ctx->form == AFQMC_FORM_T && n_up[wi] != n_dn[wi]) return AFQMC_ERR_ARG;
     }
     // host offsets of every walker's trial state and fields in the caller's arrays
     std::vector<size_t> poff(n_walkers), foff(n_walkers);
@@ -791,6 +872,22 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
         CK(dalloc(A, (char**)&w->flag2, (size_t)nwk * 2 * maxr));
         CK(dalloc(A, (char**)&w->visited, (size_t)nwk * maxr * sizeof(int)));
         CK(dalloc(A, &w->acc2, (size_t)nwk * 2 * 8));
+        if (ctx->form == AFQMC_FORM_T) {
+            const size_t fsb = (size_t)nwk * 2 * N * nsm * es, pan = (size_t)nwk * 2 * NW * nsm * es;
+            CK(dalloc(A, (char**)&w->TUR, fsb));
+            CK(dalloc(A, (char**)&w->TUL, fsb));
+            CK(dalloc(A, (char**)&w->TT, (size_t)nwk * 2 * nsm * nsm * es));
+            void** pans[] = {&w->ULI, &w->URI, &w->Vt, &w->Yt, &w->Ypt, &w->Pt};
+            for (void** p : pans) {
+                CK(dalloc(A, (char**)p, pan));
+                CK(cudaMemsetAsync(*p, 0, pan, st));
+            }
+            std::vector<double> eye((size_t)nsm * nsm, 0.0);
+            for (int i = 0; i < nsm; ++i) eye[(size_t)i * nsm + i] = 1.0;
+            CK(dalloc(A, &w->Ieye, eye.size() * 8));
+            CK(cudaMemcpyAsync(w->Ieye, eye.data(), eye.size() * 8, cudaMemcpyHostToDevice, st));
+            CK(cudaStreamSynchronize(st));  // the host identity goes out of scope
+        }
         if (ctx->p.gemm != AFQMC_GEMM_SIMT) {
             w->oz_Z = ozaki_pays(nsm, nsm, N, 2 * nwk);
             w->oz_G = ozaki_pays(N, N, nsm, 2 * nwk);
@@ -860,6 +957,12 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
             if (ctx->p.precision == AFQMC_PREC_FP64) CK(finish_G<double>(ctx, w, st, fac_R(w, 0), grp[gi][0], ng[gi], false));
             else CK(finish_G<float>(ctx, w, st, fac_R(w, 0), grp[gi][0], ng[gi], false));
         }
+        // T form: U_R(0), U_L(0) and T(0) = (U_L U_R)^{-1} (the LU of U_L U_R is still in Ob)
+        if (ctx->form == AFQMC_FORM_T) {
+            if (ctx->p.precision == AFQMC_PREC_FP64) CK(tform_set<double>(ctx, w, st, fac_R(w, 0), fac_L(w, 0)));
+            else CK(tform_set<float>(ctx, w, st, fac_R(w, 0), fac_L(w, 0)));
+        }
+        w->gvalid = true;
         w->pos = 0;
         w->last_dir = -1;
         w->need_recompute = false;
@@ -1126,6 +1229,182 @@ static int sweep_impl(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int k,
     return AFQMC_OK;
 }
 
+// One slice of the T form (Sec. II.C, Sec. III.A-B) for walker group gi, on stream st:
+//   wrap   U_R <- D E U_R, U_L <- U_L E^{-1} D^{-1} (forward; backward the inverse moves after the
+//          update) by the separable passes on the N x Nsigma and Nsigma x N factors; T is unchanged;
+//   per window of sites J: the block 1 - U_R[J, :] T U_L[:, J] of G, the window kernel (the same
+//          decisions, ratios and update matrix W as the G form), then the window's update
+//          T <- T - V W Y with V = T U_L[:, I], Y = U_R[I, :] T (the G form's W by the push-through
+//          identity, Eq. BlkFrcBsTnew2) and the rows I of U_R scaled by the field change
+//          (Eq. UpdateLTRMat).
+template <typename T>
+static int sweep_impl_T(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int k, int nb, const uint8_t* replay,
+                        cudaStream_t st) {
+    Walker* w = ctx->w[gi];
+    const int N = w->N, nwk = w->nwk, ns = w->nsm, nb2 = 2 * nwk;
+    int8_t* xl = w->x + (size_t)(ell - 1) * N;
+    T* d = (T*)w->dvec;
+    T* dinv = d + (size_t)nwk * 2 * N;
+    const int NW = window_max<T>();
+    const long fs = (long)N * ns;
+    T* UR = (T*)w->TUR;
+    T* UL = (T*)w->TUL;
+    T* TT = (T*)w->TT;
+    const uint8_t* rep = nullptr;
+    Batch bt;
+    bt.nwk = nwk;
+    bt.gstride = w->gstride();
+    bt.xstride = (long)ctx->p.M * N;
+    w->gvalid = false;
+    {
+        PhaseScope ps(ctx, AFQMC_PHASE_PREP, st);
+        CK(launch_uniforms(st, ctx->p.seed, w->gid_d, w->visit_d, 2 * N, w->u, nwk));
+        CK(cudaMemsetAsync(w->stats, 0, (size_t)nwk * 8 * sizeof(int), st));
+        CK(cudaMemsetAsync(w->maxr, 0, (size_t)nwk * 8, st));
+        if (replay) {
+            std::vector<uint8_t> h((size_t)nwk * 2 * N);
+            for (int j = 0; j < nwk; ++j)
+                memcpy(h.data() + (size_t)j * 2 * N, replay + (size_t)ctx_replay_offset(ctx, w->gid[j]), 2 * (size_t)N);
+            CK(cudaMemcpyAsync(w->replay, h.data(), h.size(), cudaMemcpyHostToDevice, st));
+            CK(cudaStreamSynchronize(st));
+            rep = w->replay;
+        }
+    }
+    auto wrap = [&](int direction) -> cudaError_t {
+        PhaseScope ps(ctx, AFQMC_PHASE_WRAP, st);
+        cudaError_t e = launch_field_scales_T<T>(st, xl, N, ctx->c, d, dinv, N, nwk, bt.xstride);
+        if (e != cudaSuccess) return e;
+        SepArgs r, l;
+        r.L = l.L = w->L;
+        r.N = l.N = N;
+        r.batch = l.batch = nb2;
+        r.C = l.C = ns;
+        r.sv = l.sv = N;
+        r.w = l.w = ctx->sep_tile;
+        r.G = UR; r.ld = ns; r.sG = fs; r.side = 0;
+        l.G = UL; l.ld = N; l.sG = fs; l.side = 1;
+        if (direction > 0) {  // U_R <- D (E U_R), U_L <- (U_L E^{-1}) D^{-1}
+            r.A = w->lat->Ex64; r.rs_out = d;
+            l.A = w->lat->Exi64; l.cs_out = dinv;
+        } else {              // U_R <- E^{-1} (D^{-1} U_R), U_L <- (U_L D) E
+            r.A = w->lat->Exi64; r.rs_in = dinv;
+            l.A = w->lat->Ex64; l.cs_in = d;
+        }
+        PhaseScope pg(ctx, AFQMC_PHASE_WRAP_GEMM, st);
+        if ((e = launch_sep<T>(st, r)) != cudaSuccess) return e;
+        return launch_sep<T>(st, l);
+    };
+    if (dir > 0) {
+        CK(wrap(+1));
+        CK(record_outside(w->ev_wrap, st));
+    }
+    SiteParams sp;
+    sp.N = N;
+    sp.ld = w->ld;
+    sp.c[0] = ctx->c[0];
+    sp.c[1] = ctx->c[1];
+    sp.lam = ctx->lam;
+    sp.hs = ctx->p.hs;
+    sp.seed = ctx->p.seed;
+    sp.walker = (uint64_t)w->gid[0];
+    sp.visit = w->visit;
+    for (int s = 0; s < 2; ++s)
+        for (int xi = 0; xi < 2; ++xi) {
+            const double x = xi == 0 ? 1.0 : -1.0;
+            sp.dflip[s][xi] = exp(-2.0 * ctx->c[s] * x) - 1.0;
+            sp.dstrip[s][xi] = exp(-ctx->c[s] * x) - 1.0;
+        }
+    for (int xi = 0; xi < 2; ++xi) {
+        const double x = xi == 0 ? 1.0 : -1.0;
+        sp.sflip[xi] = (ctx->p.hs == AFQMC_HS_CHARGE_REAL) ? exp(2.0 * ctx->lam * x) : 1.0;
+    }
+    SliceOut so;
+    so.dec = w->dec;
+    so.ratio = w->ratio;
+    so.stats = w->stats;
+    so.maxr = w->maxr;
+    so.sign = w->sign;
+    WindowBufs wb;
+    wb.m = w->wm[0];
+    wb.idx = w->widx[0];
+    wb.dtot = w->wdtot[0];
+    wb.Wm = w->Wm[0];
+    wb.Wx = w->Wx[0];
+    wb.X = w->X[0];
+    wb.Y = w->Y[0];
+    wb.nwk = nwk;
+    T* blk = (T*)w->snap[0];          // [nwk][2][NW x NW]: the window's block of G
+    T* P = (T*)w->Pt;                 // [nwk][2][NW x ns]: U_R[J, :] T
+    T* ULI = (T*)w->ULI;              // [nwk][2][ns x NW]
+    T* URI = (T*)w->URI;              // [nwk][2][NW x ns]
+    T* V = (T*)w->Vt;                 // [nwk][2][ns x NW]
+    T* Y = (T*)w->Yt;                 // [nwk][2][NW x ns]
+    T* Yp = (T*)w->Ypt;               // [nwk][2][NW x ns]
+    const long sB = (long)NW * NW, sP = (long)NW * ns, sT = (long)ns * ns;
+    {
+        PhaseScope ps(ctx, AFQMC_PHASE_CHAIN, st);
+        const int nw = (mode == AFQMC_MODE_DELAYED) ? k : (NW / nb) * nb;
+        for (int s0 = 0; s0 < N; s0 += nw) {
+            const int n = (N - s0 < nw) ? N - s0 : nw;
+            // the window's block of G: 1 - (U_R[J, :] T) U_L[:, J]
+            GemmArgs<T> g1;
+            g1.M = n; g1.N = ns; g1.K = ns; g1.batch = nb2;
+            g1.A = UR + (size_t)s0 * ns; g1.lda = ns; g1.sA = fs;
+            g1.B = TT; g1.ldb = ns; g1.sB = sT;
+            g1.C = P; g1.ldc = ns; g1.sC = sP;
+            CK(gemm<T>(st, g1));
+            GemmArgs<T> g2;
+            g2.M = n; g2.N = n; g2.K = ns; g2.batch = nb2;
+            g2.A = P; g2.lda = ns; g2.sA = sP;
+            g2.B = UL + s0; g2.ldb = N; g2.sB = fs;
+            g2.C = blk; g2.ldc = NW; g2.sC = sB;
+            CK(gemm<T>(st, g2));
+            CK(launch_identity_minus<T>(st, blk, NW, n, nb2, sB));
+            // decisions and the window's W
+            CK(launch_window_chain<T>(st, mode, (const T*)w->G, nullptr, xl, w->u, rep, sp, so, s0, n, nb, wb, blk,
+                                      w->err, bt));
+            // T <- T - (T U_L[:, I]) (W (U_R[I, :] T)), then the rows I of U_R
+            PhaseScope pf(ctx, AFQMC_PHASE_FLUSH, st);
+            CK(launch_tform_gather<T>(st, UR, UL, N, ns, ns, fs, fs, wb, ULI, URI, nb2));
+            GemmArgs<T> v;
+            v.M = ns; v.N = NW; v.K = ns; v.batch = nb2;
+            v.A = TT; v.lda = ns; v.sA = sT;
+            v.B = ULI; v.ldb = NW; v.sB = (long)ns * NW;
+            v.C = V; v.ldc = NW; v.sC = (long)ns * NW;
+            CK(gemm<T>(st, v));
+            GemmArgs<T> y;
+            y.M = NW; y.N = ns; y.K = ns; y.batch = nb2;
+            y.A = URI; y.lda = ns; y.sA = sP;
+            y.B = TT; y.ldb = ns; y.sB = sT;
+            y.C = Y; y.ldc = ns; y.sC = sP;
+            CK(gemm<T>(st, y));
+            GemmArgs<T> yp;  // Y' = W Y over the m accepted rows
+            yp.M = NW; yp.N = ns; yp.K = NW; yp.Kdev = wb.m; yp.kdiv = 2; yp.batch = nb2;
+            yp.A = (const T*)wb.Wx; yp.lda = NW; yp.sA = sB;
+            yp.B = Y; yp.ldb = ns; yp.sB = sP;
+            yp.C = Yp; yp.ldc = ns; yp.sC = sP;
+            CK(gemm<T>(st, yp));
+            GemmArgs<T> t;  // T -= V Y'
+            t.M = ns; t.N = ns; t.K = NW; t.Kdev = wb.m; t.kdiv = 2; t.batch = nb2;
+            t.A = V; t.lda = NW; t.sA = (long)ns * NW;
+            t.B = Yp; t.ldb = ns; t.sB = sP;
+            t.C = TT; t.ldc = ns; t.sC = sT;
+            t.alpha = T(-1); t.beta = T(1);
+            {
+                PhaseScope pg(ctx, AFQMC_PHASE_FLUSH_GEMM, st);
+                CK(gemm<T>(st, t));
+            }
+            CK(launch_tform_scale_rows<T>(st, UR, N, ns, ns, fs, wb, xl, bt.xstride, ctx->c, nb2));
+        }
+    }
+    if (dir < 0) {
+        CK(wrap(-1));
+        CK(record_outside(w->ev_wrap, st));
+    }
+    CK(launch_bump(st, w->visit_d));
+    return AFQMC_OK;
+}
+
 extern "C" {
 
 int afqmc_sweep_slice(afqmc_ctx* ctx, int slice, int dir, int mode, int k, int nb, const uint8_t* replay,
@@ -1138,6 +1417,7 @@ int afqmc_sweep_slice(afqmc_ctx* ctx, int slice, int dir, int mode, int k, int n
     if (mode == AFQMC_MODE_DELAYED && (k < 1 || k > NW)) return AFQMC_ERR_ARG;
     if (mode == AFQMC_MODE_BLOCKFB && (nb < 1 || nb > 32)) return AFQMC_ERR_ARG;
     if (mode != AFQMC_MODE_LOCAL && mode != AFQMC_MODE_DELAYED && mode != AFQMC_MODE_BLOCKFB) return AFQMC_ERR_ARG;
+    if (ctx->form == AFQMC_FORM_T && mode == AFQMC_MODE_LOCAL) return AFQMC_ERR_ARG;  // k = 1 delayed is local
     for (auto* w : ctx->w) {
         if (w->need_recompute) return AFQMC_ERR_STATE;
         if (dir > 0 && w->pos != slice - 1) return AFQMC_ERR_STATE;
@@ -1149,7 +1429,7 @@ int afqmc_sweep_slice(afqmc_ctx* ctx, int slice, int dir, int mode, int k, int n
     // With graphs on, a group's slice is captured once per (slice, dir, mode, k, nb) and then
     // replayed: every launch of the slice, the flush stream's included, in one graph launch.
     const bool fork = ctx->w.size() > 1;
-    const bool use_graph = ctx->graphs && !replay && !ctx->prof.on;
+    const bool use_graph = ctx->graphs && !replay && !ctx->prof.on && ctx->form == AFQMC_FORM_G;
     for (int gi = 0; gi < (int)ctx->w.size(); ++gi) {
         Walker* w = ctx->w[gi];
         cudaStream_t sg = st;
@@ -1183,6 +1463,10 @@ int afqmc_sweep_slice(afqmc_ctx* ctx, int slice, int dir, int mode, int k, int n
                 count_launch((int)it->second.launches);
             }
             CK(cudaGraphLaunch(it->second.exec, sg));
+        } else if (ctx->form == AFQMC_FORM_T) {
+            rc = f64 ? sweep_impl_T<double>(ctx, gi, slice, dir, mode, k, nb, replay, sg)
+                     : sweep_impl_T<float>(ctx, gi, slice, dir, mode, k, nb, replay, sg);
+            if (rc) return rc;
         } else {
             rc = f64 ? sweep_impl<double>(ctx, gi, slice, dir, mode, k, nb, replay, sg)
                      : sweep_impl<float>(ctx, gi, slice, dir, mode, k, nb, replay, sg);
@@ -1275,10 +1559,27 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
             }
             CK(to_stack(w, st, fwd, j));
         }
-        for (int gi = 0; gi < ngr; ++gi) {
-            CK(form_Z(ctx, w, st, fac_R(w, j), fac_L(w, j), grp[gi][0], ng[gi], nullptr));
-            if (f64) CK(finish_G<double>(ctx, w, st, fac_R(w, j), grp[gi][0], ng[gi], true));
-            else CK(finish_G<float>(ctx, w, st, fac_R(w, j), grp[gi][0], ng[gi], true));
+        if (ctx->form == AFQMC_FORM_T) {
+            // T = (U_L U_R)^{-1} and the bulk factors from the FP64 ones; with a drift requested, G is
+            // formed from the bulk state first and compared with the recomputed FP64 G
+            if (rel_drift) {
+                if (f64) CK(tform_form_G<double>(w, st));
+                else CK(tform_form_G<float>(w, st));
+                CK(form_Z(ctx, w, st, fac_R(w, j), fac_L(w, j), 0, 2, nullptr));
+                if (f64) CK(finish_G<double>(ctx, w, st, fac_R(w, j), 0, 2, true));
+                else CK(finish_G<float>(ctx, w, st, fac_R(w, j), 0, 2, true));
+            } else {
+                CK(form_O(ctx, w, st, fac_R(w, j), fac_L(w, j), 0, 2, nullptr));
+            }
+            if (f64) CK(tform_set<double>(ctx, w, st, fac_R(w, j), fac_L(w, j)));
+            else CK(tform_set<float>(ctx, w, st, fac_R(w, j), fac_L(w, j)));
+            w->gvalid = rel_drift != nullptr;
+        } else {
+            for (int gi = 0; gi < ngr; ++gi) {
+                CK(form_Z(ctx, w, st, fac_R(w, j), fac_L(w, j), grp[gi][0], ng[gi], nullptr));
+                if (f64) CK(finish_G<double>(ctx, w, st, fac_R(w, j), grp[gi][0], ng[gi], true));
+                else CK(finish_G<float>(ctx, w, st, fac_R(w, j), grp[gi][0], ng[gi], true));
+            }
         }
         w->need_recompute = false;
         if (fork) {
@@ -1308,6 +1609,10 @@ int afqmc_measure_energy(afqmc_ctx* ctx, double* energy, double* sign, void* str
     cudaStream_t st = (cudaStream_t)stream;
     ctx->last = st;
     for (auto* w : ctx->w) {
+        if (!w->gvalid) {
+            if (ctx->p.precision == AFQMC_PREC_FP64) CK(tform_form_G<double>(w, st));
+            else CK(tform_form_G<float>(w, st));
+        }
         CK(cudaMemsetAsync(w->acc2, 0, (size_t)w->nwk * 16, st));
         if (ctx->p.precision == AFQMC_PREC_FP64)
             CK(launch_energy<double>(st, (const double*)w->G, w->ld, w->L, ctx->p.t, ctx->p.U, w->acc2, w->nwk,
@@ -1342,6 +1647,10 @@ int afqmc_get_G(afqmc_ctx* ctx, int walker, int spin, double* host_out) {
     Walker* w;
     int j;
     if (!walker_of(ctx, walker, &w, &j) || spin < 0 || spin > 1 || !host_out) return AFQMC_ERR_ARG;
+    if (!w->gvalid) {  // T form: G = 1 - U_R T U_L on the stream of the last call
+        if (ctx->p.precision == AFQMC_PREC_FP64) CK(tform_form_G<double>(w, ctx->last));
+        else CK(tform_form_G<float>(w, ctx->last));
+    }
     CK(cudaStreamSynchronize(ctx->last));
     const size_t es = esize(ctx);
     std::vector<char> buf((size_t)w->N * w->ld * es);
@@ -1359,6 +1668,7 @@ int afqmc_set_G(afqmc_ctx* ctx, int walker, int spin, const double* host_in) {
     Walker* w;
     int j;
     if (!walker_of(ctx, walker, &w, &j) || spin < 0 || spin > 1 || !host_in) return AFQMC_ERR_ARG;
+    if (ctx->form == AFQMC_FORM_T) return AFQMC_ERR_STATE;  // the T form's state is not G
     CK(cudaStreamSynchronize(ctx->last));
     const size_t es = esize(ctx);
     std::vector<char> buf((size_t)w->N * w->ld * es, 0);
@@ -1428,6 +1738,13 @@ int afqmc_set_wrap(afqmc_ctx* ctx, int mode) {
         }
     }
     ctx->wrap_mode = mode;
+    return AFQMC_OK;
+}
+
+int afqmc_set_form(afqmc_ctx* ctx, int form) {
+    if (!ctx || (form != AFQMC_FORM_G && form != AFQMC_FORM_T)) return AFQMC_ERR_ARG;
+    if (!ctx->w.empty()) return AFQMC_ERR_STATE;
+    ctx->form = form;
     return AFQMC_OK;
 }
 

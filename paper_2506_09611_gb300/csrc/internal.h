@@ -281,6 +281,16 @@ cudaError_t launch_flush_panels(cudaStream_t sf, T* Gu, T* Gd, const SiteParams&
 template <typename T>
 cudaError_t launch_flush_gemm(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& sp, WindowBufs wb, int nw,
                               Batch bt = Batch());
+// T form: the gathers of the window's accepted sites I for every (walker, spin) z of the batch,
+// ULI[z] = UL[z][:, I] (ns x m, pitch window_max<T>()) and URI[z] = UR[z][I, :] (m x ns, pitch ldr),
+// and the row scaling UR[z][I_k, :] *= exp(2 c_s x'_{I_k}) with the slice's new fields.  UR: N x ns
+// (leading dimension ldr), UL: ns x N; batch strides sr, sl; z = 2 walker + spin.
+template <typename T>
+cudaError_t launch_tform_gather(cudaStream_t st, const T* UR, const T* UL, int N, int ns, long ldr, long sr, long sl,
+                                WindowBufs wb, T* ULI, T* URI, int nbatch);
+template <typename T>
+cudaError_t launch_tform_scale_rows(cudaStream_t st, T* UR, int N, int ns, long ldr, long sr, WindowBufs wb,
+                                    const int8_t* xl, long xstride, const double* c, int nbatch);
 // G_s[i][j] *= a_s[i] * b_s[j] for both spins (a, b: [2][N], spin stride N)
 template <typename T>
 cudaError_t launch_scale2(cudaStream_t st, T* G, long ld, int N, long sG, const T* a, const T* b, int nbatch = 2);

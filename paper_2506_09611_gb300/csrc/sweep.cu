@@ -1098,6 +1098,74 @@ cudaError_t launch_flush_gemm(cudaStream_t sf, T* Gu, T* Gd, const SiteParams& s
     h.batch = 2 * bt.nwk;
     return gemm<T>(sf, h);
 }
+// ---------------------------------------------------------------------------
+// T form (the paper's walker state: U_R, U_L, T = (U_L U_R)^{-1}; G = 1 - U_R T U_L)
+// ---------------------------------------------------------------------------
+// For every (walker, spin) z of the batch, with the window's accepted sites I (wb.idx, m = wb.m):
+//   ULI[z][a][k] = UL[z][a][I_k]   (ns x m, pitch NW)      URI[z][k][a] = UR[z][I_k][a]   (m x ns, pitch ldr)
+// UR: N x ns (leading dimension ldr), UL: ns x N (leading dimension N); batch strides sr, sl.
+template <typename T>
+__global__ void tform_gather_kernel(const T* __restrict__ UR, const T* __restrict__ UL, int N, int ns, long ldr,
+                                    long sr, long sl, WindowBufs wb0, T* ULI, T* URI) {
+    constexpr int NW = WinCap<T>::NW;
+    const int z = blockIdx.y, wk = z >> 1;
+    const WindowBufs wb = wb_walker<T>(wb0, wk, N);
+    const int m = *wb.m;
+    const T* ur = UR + (size_t)z * sr;
+    const T* ul = UL + (size_t)z * sl;
+    T* uli = ULI + (size_t)z * ns * NW;
+    T* uri = URI + (size_t)z * NW * ldr;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * ns; e += gridDim.x * blockDim.x) {
+        const int k = e / ns, a = e - k * ns;
+        const int I = wb.idx[k];
+        uri[(size_t)k * ldr + a] = ur[(size_t)I * ldr + a];
+        uli[(size_t)a * NW + k] = ul[(size_t)a * N + I];
+    }
+}
+
+// UR[z][I_k][:] *= exp(c_s (x' - x)) = exp(2 c_s x'_k) for the accepted sites (Eq. UpdateLTRMat: the
+// row of the slice's B in the right factor takes the new field), x' the field the window kernel
+// left in the slice (xl, batch stride xstride per walker).
+template <typename T>
+__global__ void tform_scale_rows_kernel(T* UR, int N, int ns, long ldr, long sr, WindowBufs wb0, const int8_t* xl,
+                                        long xstride, double c0, double c1) {
+    const int z = blockIdx.y, wk = z >> 1, s = z & 1;
+    const WindowBufs wb = wb_walker<T>(wb0, wk, N);
+    const int m = *wb.m;
+    T* ur = UR + (size_t)z * sr;
+    const int8_t* x = xl + (size_t)wk * xstride;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * ns; e += gridDim.x * blockDim.x) {
+        const int k = e / ns, a = e - k * ns;
+        const int I = wb.idx[k];
+        const T f = (T)exp(2.0 * (s ? c1 : c0) * (double)x[I]);
+        ur[(size_t)I * ldr + a] *= f;
+    }
+}
+
+template <typename T>
+cudaError_t launch_tform_gather(cudaStream_t st, const T* UR, const T* UL, int N, int ns, long ldr, long sr, long sl,
+                                WindowBufs wb, T* ULI, T* URI, int nbatch) {
+    count_launch();
+    tform_gather_kernel<T><<<dim3(64, nbatch), 256, 0, st>>>(UR, UL, N, ns, ldr, sr, sl, wb, ULI, URI);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tform_scale_rows(cudaStream_t st, T* UR, int N, int ns, long ldr, long sr, WindowBufs wb,
+                                    const int8_t* xl, long xstride, const double* c, int nbatch) {
+    count_launch();
+    tform_scale_rows_kernel<T><<<dim3(64, nbatch), 256, 0, st>>>(UR, N, ns, ldr, sr, wb, xl, xstride, c[0], c[1]);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_tform_gather<float>(cudaStream_t, const float*, const float*, int, int, long, long, long,
+                                                WindowBufs, float*, float*, int);
+template cudaError_t launch_tform_gather<double>(cudaStream_t, const double*, const double*, int, int, long, long,
+                                                 long, WindowBufs, double*, double*, int);
+template cudaError_t launch_tform_scale_rows<float>(cudaStream_t, float*, int, int, long, long, WindowBufs,
+                                                    const int8_t*, long, const double*, int);
+template cudaError_t launch_tform_scale_rows<double>(cudaStream_t, double*, int, int, long, long, WindowBufs,
+                                                     const int8_t*, long, const double*, int);
 template cudaError_t launch_flush_panels<float>(cudaStream_t, float*, float*, const SiteParams&, WindowBufs, int,
                                                Batch);
 template cudaError_t launch_flush_panels<double>(cudaStream_t, double*, double*, const SiteParams&, WindowBufs, int,

@@ -1,0 +1,146 @@
+"""GPU parity of the T form (Sec. II.C: the walker carries U_R, U_L and T = (U_L U_R)^{-1}) against the
+oracle's own T-form walker.
+
+* FP64 free-running: the decisions (and block force-bias proposals) are identical to the oracle
+  TWalker's, and G = 1 - U_R T U_L agrees to 1e-10 (relative Frobenius norm) after every slice of a
+  forward and backward sweep with its recomputes; one window per slice and several windows per
+  slice, the delayed update (Eqs. DelayRatio, DelayRgenk, FinalDelay) and the block force bias
+  (Eqs. BlkFrcBsTnew1, BlkFrcBsTnew2).
+* FP32 replay: the oracle's decisions forced, G within 1e-5 after every slice, 8 x 8 through a
+  recompute and the 40 x 40 workload for three slices (there against the G-form oracle, which takes
+  the same chain: the oracle pins show identical decisions and G).
+* The state rules of the T form.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_09611_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+afqmc = pytest.importorskip("paper_2506_09611_gb300.afqmc")
+
+FP64_TOL = 1e-10
+FP32_TOL = 1e-5
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _ctx(L, ns, M, stab, U, precision, seed):
+    P = inputs.trial_state(L, L, ns)
+    X = inputs.initial_fields(M, L * L, seed=seed)
+    ctx = afqmc.Context(M, U=U, precision=precision, stab_every=stab, seed=seed, form="T")
+    ctx.init_walkers([L], [ns], [ns], np.concatenate([P.ravel(), P.ravel()]), X)
+    return ctx, P, X
+
+
+def _rep(N, mode, nb, dec, extra):
+    rep = np.zeros(2 * N, np.uint8)
+    if mode == "blockfb":
+        rep[:N] = (extra["xprop"] > 0)
+        rep[N:N + (N + nb - 1) // nb] = dec
+    else:
+        rep[:N] = dec
+    return rep
+
+
+@pytest.mark.parametrize("L,ns,M,stab,mode,k,nb", [
+    (4, 7, 8, 4, "delayed", 1, 4), (4, 7, 8, 4, "delayed", 5, 4), (4, 7, 8, 4, "delayed", 16, 4),
+    (4, 7, 8, 4, "blockfb", 16, 1), (4, 7, 8, 4, "blockfb", 16, 4), (6, 15, 6, 3, "delayed", 16, 4),
+    (6, 15, 6, 3, "blockfb", 16, 7), (12, 63, 4, 2, "delayed", 16, 4), (12, 63, 4, 2, "blockfb", 16, 7)])
+def test_tform_fp64_free_running_matches_the_oracle_tform(L, ns, M, stab, mode, k, nb):
+    seed = 17
+    N = L * L
+    ctx, P, X = _ctx(L, ns, M, stab, 4.0, "fp64", seed)
+    model = oracle.Model(L, L, 1.0, 4.0, 0.05, M)
+    tw = oracle.TWalker(model, P, P, X, stab=stab)
+    with ctx:
+        for s in range(2):
+            assert rel(ctx.G(0, s), tw.G(s)) < FP64_TOL
+        order = [(ell, +1) for ell in range(1, M + 1)] + [(ell, -1) for ell in range(M, 0, -1)]
+        for visit, (ell, d) in enumerate(order):
+            u = inputs.uniforms(seed, 0, visit, 2 * N)
+            dec_o, ratio_o, extra = tw.sweep_slice(ell, d, mode, u, k=k, nb=nb, strategy=1)
+            st = ctx.sweep_slice(ell, d, mode, k=k, nb=nb, want_stats=True)
+            dec_g = ctx.decisions(0)
+            if mode == "blockfb":
+                nbk = (N + nb - 1) // nb
+                np.testing.assert_array_equal(dec_g[:N], (extra["xprop"] > 0).astype(np.uint8))
+                np.testing.assert_array_equal(dec_g[N:N + nbk], dec_o, err_msg=f"blocks, slice {ell} dir {d}")
+            else:
+                np.testing.assert_array_equal(dec_g[:N], dec_o, err_msg=f"decisions, slice {ell} dir {d}")
+                np.testing.assert_allclose(ctx.ratios(0)[:N], ratio_o, rtol=1e-9, atol=1e-12)
+            assert st[0].sign == tw.sign
+            for s in range(2):
+                r = rel(ctx.G(0, s), tw.G(s))
+                assert r < FP64_TOL, f"{mode} slice {ell} dir {d} spin {s}: {r}"
+            if tw.pos % stab == 0:
+                drift = ctx.recompute_G()
+                tw.recompute(stab)
+                assert drift[0] < FP64_TOL
+                for s in range(2):
+                    assert rel(ctx.G(0, s), tw.G(s)) < FP64_TOL
+        np.testing.assert_array_equal(ctx.fields(0), tw.x)
+        e, sg = ctx.measure_energy()
+        assert abs(e[0] - model.energy(tw.G(0), tw.G(1))) < 1e-9 * max(1.0, abs(e[0]))
+
+
+@pytest.mark.parametrize("mode,k,nb", [("delayed", 32, 4), ("delayed", 128, 4), ("blockfb", 32, 8)])
+def test_tform_fp32_replay_8x8(mode, k, nb):
+    L, ns, M, stab, seed = 8, 28, 10, 5, 23
+    N = L * L
+    ctx, P, X = _ctx(L, ns, M, stab, 4.0, "fp32", seed)
+    tw = oracle.TWalker(oracle.Model(L, L, 1.0, 4.0, 0.05, M), P, P, X, stab=stab)
+    with ctx:
+        for ell in range(1, M + 1):
+            dec, _, extra = tw.sweep_slice(ell, +1, mode, inputs.uniforms(seed, 0, ell - 1, 2 * N), k=k, nb=nb)
+            ctx.sweep_slice(ell, +1, mode, k=k, nb=nb, replay=_rep(N, mode, nb, dec, extra))
+            for s in range(2):
+                r = rel(ctx.G(0, s), tw.G(s))
+                assert r < FP32_TOL, f"slice {ell} spin {s}: {r}"
+            if ell % stab == 0:
+                drift = ctx.recompute_G()
+                tw.recompute(stab)
+                assert drift[0] < FP32_TOL
+        np.testing.assert_array_equal(ctx.fields(0), tw.x)
+
+
+@pytest.mark.parametrize("mode,k,nb", [("delayed", 64, 16), ("blockfb", 64, 16)])
+def test_tform_fp32_replay_40x40(mode, k, nb):
+    """The 40 x 40 workload (N = 1600, 700 per spin, U = 6) in the T form for three replayed slices."""
+    L, ns, M, stab, seed = 40, 700, 10, 10, 6
+    N = L * L
+    ctx, P, X = _ctx(L, ns, M, stab, 6.0, "fp32", seed)
+    w = oracle.Walker(oracle.Model(L, L, 1.0, 6.0, 0.05, M), P, P, X)
+    with ctx:
+        for ell in (1, 2, 3):
+            dec, _, extra = w.sweep_slice(ell, +1, mode, inputs.uniforms(seed, 0, ell - 1, 2 * N), k=k, nb=nb)
+            ctx.sweep_slice(ell, +1, mode, k=k, nb=nb, replay=_rep(N, mode, nb, dec, extra))
+            for s in range(2):
+                r = rel(ctx.G(0, s), w.G[s])
+                assert r < FP32_TOL, (mode, ell, s, r)
+        np.testing.assert_array_equal(ctx.fields(0), w.x)
+
+
+def test_tform_state_rules():
+    L, ns, M = 4, 7, 4
+    P = inputs.trial_state(L, L, ns)
+    X = inputs.initial_fields(M, L * L, seed=1)
+    with afqmc.Context(M, precision="fp64", stab_every=2, seed=1, form="T") as ctx:
+        with pytest.raises(afqmc.AfqmcError):  # n_up != n_dn
+            ctx.init_walkers([L], [ns], [ns - 1], np.concatenate([P.ravel(), P[:, :ns - 1].ravel()]), X)
+    with afqmc.Context(M, precision="fp64", stab_every=2, seed=1, form="T") as ctx:
+        ctx.init_walkers([L], [ns], [ns], np.concatenate([P.ravel(), P.ravel()]), X)
+        with pytest.raises(afqmc.AfqmcError) as e:
+            afqmc.afqmc_set_form(ctx.h, "G")  # after init
+        assert e.value.code == -6
+        with pytest.raises(afqmc.AfqmcError) as e:
+            ctx.sweep_slice(1, +1, "local")
+        assert e.value.code == -1
+        with pytest.raises(afqmc.AfqmcError) as e:
+            ctx.set_G(0, 0, np.eye(L * L))
+        assert e.value.code == -6
+        ctx.sweep_slice(1, +1, "delayed", k=1)  # the local update of the T form
