@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed walker population leg")
     ap.add_argument("--no-soc", action="store_true", help="skip the spin-orbit-coupled leg")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core wrap leg")
+    ap.add_argument("--no-tform", action="store_true", help="skip the T-form sweep")
     ap.add_argument("--no-precision", action="store_true", help="skip the per-precision accuracy report")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-bulk sweep")
     ap.add_argument("--no-ksweep", action="store_true", help="skip the 40x40 delay-rank sweep")
@@ -250,7 +251,7 @@ def main():
             pos = ell if d > 0 else ell - 1
             if pos % STAB == 0:  # FP64 re-orthonormalisation + recompute point
                 if drift is not None:
-                    drift.append(float(ctx.recompute_G(stream=stream)[0]))
+                    drift.append((float(ctx.recompute_G(stream=stream)[0]), pos, d))
                 else:
                     afqmc.afqmc_recompute_G(ctx.h, None, stream)
 
@@ -332,6 +333,9 @@ def main():
     soc_res = None
     if not args.no_soc:
         soc_res = optional_leg("soc", lambda: soc_leg(torch, stream, args, seed))
+    tf = None
+    if not args.no_tform:
+        tf = optional_leg("tform", lambda: tform_leg(afqmc, torch, stream, args, seed))
     dense = None
     if not args.no_dense:
         dense = optional_leg("dense_wrap", lambda: dense_wrap_leg(afqmc, torch, stream, args, seed,
@@ -369,9 +373,12 @@ def main():
             "speedup_update_only_vs_local": speedup,
             "k_sweep_40x40": ksweep,
             "config_16x16": c16,
-            "G_err_fp32_vs_fp64_recompute": {"max": max(drifts) if drifts else None,
-                                             "median": statistics.median(drifts) if drifts else None,
-                                             "slices_between_recomputes": STAB},
+            "G_err_fp32_vs_fp64_recompute": {"max": max(x[0] for x in drifts) if drifts else None,
+                                             "median": statistics.median(x[0] for x in drifts) if drifts else None,
+                                             "slices_between_recomputes": STAB,
+                                             "by_point": [{"slice": p, "dir": dd, "drift": v} for v, p, dd in drifts],
+                                             "note": "the warm-up sweeps' recompute points: ||G_fp32 - G_fp64|| / "
+                                                     "||G_fp64|| after the 10 slices since the previous one"},
             "roofline": roof,
             "roofline_kernels": kernels[1:],
             "clocks": clocks,
@@ -381,6 +388,7 @@ def main():
             "batched_population": batch,
             "soc": soc_res,
             "dense_wrap": dense,
+            "tform": tf,
             "precision_report": prec,
             "fp64_bulk": f64,
             "cpu_baseline": cpu,
@@ -451,8 +459,8 @@ def local_and_chain_rooflines(raw, pk, pk_src, l2_gbs):
                     "traffic": None, "launches": ph["intervals"], "ms_per_launch": ph["ms"] / ph["intervals"],
                     "us_per_accept": ph["ms"] * 1e3 / lo["accepts"], "work_per_accept": per_acc,
                     "accepts_per_launch": lo["accepts"] / ph["intervals"],
-                    "peak_source": "measured HBM copy (of %s); G is L2-resident: l2_copy_gbs is a copy of a "
-                                   "32 MB working set timed in this run" % pk_src})
+                    "peak_source": "measured HBM copy (of %s); G is L2-resident: l2_copy_gbs is a copy of an "
+                                   "80 MB working set (src + dst) timed in this run" % pk_src})
     de = raw["delayed"]
     ch = de["prof"]["chain"]
     if ch["intervals"] and de["accepts"]:
@@ -466,7 +474,7 @@ def local_and_chain_rooflines(raw, pk, pk_src, l2_gbs):
     return out
 
 
-def l2_copy_bandwidth(torch, mb=16, reps=200):
+def l2_copy_bandwidth(torch, mb=40, reps=100):
     """Copy bandwidth of an L2-resident working set (src + dst = 2 x mb MB < 129 MB L2): read + write
     bytes / time, CUDA events over `reps` back-to-back copies after a warm-up."""
     n = mb * 1024 * 1024 // 4
@@ -491,8 +499,8 @@ def precision_report(afqmc, stream, args, seed):
     """Accuracy of each FP32 bulk variant at the headline workload (40 x 40, U = 6, delayed k), over
     one recompute period from the FP64 G(0): slices 1..10 forward, then the FP64 recompute.
     Reference: an FP64-bulk walker running free (decisions, ratios and G after every slice).
-    For each variant (tc3: tensor-core three-term TF32 split; tf32: one TF32 pass; simt: FP32 FMA
-    pipes; separable: the L-point wrap passes, FP32):
+    For each variant (the dense wrap with the tensor-core three-term TF32 split, with one TF32 pass,
+    or on the FP32 FMA pipes; the separable wrap's L-point passes in FP32, the default):
       replay: the variant replays the reference's decisions.  Per slice: ||G - G_64||_F / ||G_64||_F
               (mean over the spins), the largest relative ratio error over the sites, and the number
               of decisions that would flip (u < |R| with the variant's ratio against the reference's,
@@ -522,8 +530,8 @@ def precision_report(afqmc, stream, args, seed):
     finally:
         ref.close()
     out = {}
-    for name, gemm, wrap in (("fp32_tc3", "tc3", None), ("tf32", "tf32", None), ("fp32_simt", "simt", None),
-                             ("fp32_separable_wrap", "tc3", "separable")):
+    for name, gemm, wrap in (("fp32_dense_tc3", "tc3", "dense"), ("tf32_dense", "tf32", "dense"),
+                             ("fp32_dense_simt", "simt", "dense"), ("fp32_separable", "tc3", "separable")):
         c = make("fp32", gemm, wrap)
         errs, rerr, flips = [], [], []
         try:
@@ -575,6 +583,7 @@ def fp64_bulk_leg(afqmc, torch, stream, args, seed):
         k64 = min(args.k, 64)
         for (ell, d) in ((1, +1), (2, +1), (2, -1), (1, -1)):
             c.sweep_slice(ell, d, "delayed", k=k64, nb=args.nb, stream=stream)
+        afqmc.afqmc_recompute_G(c.h, None, stream)  # back at slice 0: a recompute point
         order = [(l, +1) for l in range(1, M + 1)] + [(l, -1) for l in range(M, 0, -1)]
 
         def sweep():
@@ -952,6 +961,45 @@ def end_to_end(afqmc, torch, stream, args, seed, rank):
     return {"value": N * M * 2 / t, "unit": UNIT, "h2d_bytes_per_step": int(Ph.nbytes + Xh.nbytes),
             "d2h_bytes_per_step": int(Xout.nbytes + 16),
             "note": "create + init_walkers (FP64 left stack and G(0)) + 1 sweep + energy + fields readback"}
+
+
+def tform_leg(afqmc, torch, stream, args, seed):
+    """The headline workload in the paper's own walker state (afqmc_set_form(T): U_R, U_L and
+    T = (U_L U_R)^{-1} per spin, Sec. II.C): one warm-up sweep, `steps` timed sweeps with CUDA events
+    on the launching stream (L2 flushed between them), then one profiled sweep for the phases."""
+    P = inputs.trial_state(L, L, NS)
+    X = inputs.initial_fields(M, N, seed=seed)
+    order = [(l, +1) for l in range(1, M + 1)] + [(l, -1) for l in range(M, 0, -1)]
+    c = afqmc.Context(M, dtau=DTAU, U=U, t=T_HOP, precision="fp32", stab_every=STAB, seed=seed, gemm=args.gemm,
+                      form="T")
+    try:
+        c.init_walkers([L], [NS], [NS], np.concatenate([P.ravel(), P.ravel()]), X, stream=stream)
+
+        def sweep():
+            for (ell, d) in order:
+                c.sweep_slice(ell, d, "delayed", k=args.k, nb=args.nb, stream=stream)
+                pos = ell if d > 0 else ell - 1
+                if pos % STAB == 0:
+                    afqmc.afqmc_recompute_G(c.h, None, stream)
+
+        sweep()  # warm-up
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        ms = []
+        for _ in range(max(1, args.steps)):
+            flush.zero_()
+            ms.append(tune.time_on_stream(torch, stream, sweep))
+        c.set_profiling(True)
+        sweep()
+        prof = c.profile()
+        c.set_profiling(False)
+        ms_sweep = statistics.median(ms)
+        return {"value": N * M * 2 / (ms_sweep / 1e3), "unit": UNIT, "ms_per_step": ms_sweep,
+                "phases_ms_per_step": {k: v["ms"] for k, v in prof.items() if v["intervals"]},
+                "note": "T form: the window kernel of the G form on blocks 1 - U_R[J,:] T U_L[:,J]; each window's "
+                        "update T <- T - (T U_L[:,I]) W (U_R[I,:] T) and the rows I of U_R run on the main stream "
+                        "(no pipelined flush yet); the recompute forms T only"}
+    finally:
+        c.close()
 
 
 def dense_wrap_leg(afqmc, torch, stream, args, seed, sep_wrap_ms):
