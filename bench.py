@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-soc", action="store_true", help="skip the spin-orbit-coupled leg")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core wrap leg")
     ap.add_argument("--no-tform", action="store_true", help="skip the T-form sweep")
+    ap.add_argument("--no-stab-sweep", action="store_true", help="skip the FP32 recompute-period legs")
     ap.add_argument("--no-precision", action="store_true", help="skip the per-precision accuracy report")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-bulk sweep")
     ap.add_argument("--no-ksweep", action="store_true", help="skip the 40x40 delay-rank sweep")
@@ -326,6 +327,7 @@ def main():
     if not args.no_e2e:
         e2e = optional_leg("e2e", lambda: end_to_end(afqmc, torch, stream, args, seed, rank))
 
+    X_eq = ctx.fields(0).copy()  # the headline walker's fields after its sweeps (equilibrated)
     ctx.close()
     batch = None
     if not args.no_batch:
@@ -345,7 +347,15 @@ def main():
         c16 = optional_leg("config_16x16", lambda: config_16x16_leg(afqmc, torch, stream, args, seed))
     prec = None
     if not args.no_precision:
-        prec = optional_leg("precision_report", lambda: precision_report(afqmc, stream, args, seed))
+        prec = {"from_trial_fields": optional_leg("precision_report", lambda: precision_report(afqmc, stream, args,
+                                                                                              seed)),
+                "from_equilibrated_fields": optional_leg(
+                    "precision_report_eq", lambda: precision_report(afqmc, stream, args, seed, X=X_eq,
+                                                                    variants=(("fp32_separable", "tc3", "separable"),
+                                                                              ("fp32_dense_tc3", "tc3", "dense"))))}
+    stabs = None
+    if not args.no_stab_sweep:
+        stabs = optional_leg("stab_sweep", lambda: stab_sweep_leg(afqmc, torch, stream, args, seed, X_eq))
     f64 = None
     if not args.no_fp64:
         f64 = optional_leg("fp64_bulk", lambda: fp64_bulk_leg(afqmc, torch, stream, args, seed))
@@ -390,6 +400,7 @@ def main():
             "dense_wrap": dense,
             "tform": tf,
             "precision_report": prec,
+            "fp32_recompute_periods": stabs,
             "fp64_bulk": f64,
             "cpu_baseline": cpu,
         }
@@ -495,7 +506,7 @@ def l2_copy_bandwidth(torch, mb=40, reps=100):
 PREC_SLICES = 10  # one recompute period of the headline workload
 
 
-def precision_report(afqmc, stream, args, seed):
+def precision_report(afqmc, stream, args, seed, X=None, variants=None):
     """Accuracy of each FP32 bulk variant at the headline workload (40 x 40, U = 6, delayed k), over
     one recompute period from the FP64 G(0): slices 1..10 forward, then the FP64 recompute.
     Reference: an FP64-bulk walker running free (decisions, ratios and G after every slice).
@@ -508,7 +519,8 @@ def precision_report(afqmc, stream, args, seed):
       free:   the variant runs free with the reference's seed: the first (slice, site) whose decision
               differs from the reference's, or null if none within the period."""
     P = inputs.trial_state(L, L, NS)
-    X = inputs.initial_fields(M, N, seed=seed)
+    if X is None:
+        X = inputs.initial_fields(M, N, seed=seed)
     Pcat = np.concatenate([P.ravel(), P.ravel()])
     S = min(PREC_SLICES, STAB)
 
@@ -530,8 +542,9 @@ def precision_report(afqmc, stream, args, seed):
     finally:
         ref.close()
     out = {}
-    for name, gemm, wrap in (("fp32_dense_tc3", "tc3", "dense"), ("tf32_dense", "tf32", "dense"),
-                             ("fp32_dense_simt", "simt", "dense"), ("fp32_separable", "tc3", "separable")):
+    for name, gemm, wrap in (variants or (("fp32_dense_tc3", "tc3", "dense"), ("tf32_dense", "tf32", "dense"),
+                                          ("fp32_dense_simt", "simt", "dense"),
+                                          ("fp32_separable", "tc3", "separable"))):
         c = make("fp32", gemm, wrap)
         errs, rerr, flips = [], [], []
         try:
@@ -565,9 +578,44 @@ def precision_report(afqmc, stream, args, seed):
                      statistics.median(growth) if growth else None,
                      "max_rel_ratio_err_per_slice": rerr, "decision_flips_per_slice": flips,
                      "recompute_drift_at_period_end": drift, "first_divergence_free_running": first}
-    return {"workload": f"{L}x{L}, U={U}, delayed k={args.k}, slices 1..{S} from the FP64 G(0)",
+    return {"workload": f"{L}x{L}, U={U}, delayed k={args.k}, slices 1..{S} from the FP64 G(0) of the given fields",
             "reference": "FP64 bulk on the GPU, free-running (its G matches the FP64 oracle to 1e-10 in the "
                          "parity tests)", "sites_per_slice": N, "variants": out}
+
+
+def stab_sweep_leg(afqmc, torch, stream, args, seed, X, stabs=(2, 5)):
+    """The FP32 headline sweep at shorter recompute periods, from the equilibrated fields X of the
+    headline walker: per period, one untimed sweep, then one sweep timed with CUDA events on the
+    launching stream and the drift ||G_fp32 - G_fp64|| / ||G_fp64|| at each of its recompute points
+    (median and max) -- the accuracy bought by recomputing more often, and its cost."""
+    P = inputs.trial_state(L, L, NS)
+    order = [(l, +1) for l in range(1, M + 1)] + [(l, -1) for l in range(M, 0, -1)]
+    out = {}
+    for stab in stabs:
+        c = afqmc.Context(M, dtau=DTAU, U=U, t=T_HOP, precision="fp32", stab_every=stab, seed=seed, gemm=args.gemm)
+        try:
+            c.init_walkers([L], [NS], [NS], np.concatenate([P.ravel(), P.ravel()]), X, stream=stream)
+            drifts = []
+
+            def sweep(collect):
+                for (ell, d) in order:
+                    c.sweep_slice(ell, d, "delayed", k=args.k, nb=args.nb, stream=stream)
+                    pos = ell if d > 0 else ell - 1
+                    if pos % stab == 0:
+                        if collect:
+                            drifts.append(float(c.recompute_G(stream=stream)[0]))
+                        else:
+                            afqmc.afqmc_recompute_G(c.h, None, stream)
+
+            sweep(False)
+            ms = tune.time_on_stream(torch, stream, lambda: sweep(False))
+            sweep(True)
+            out[f"stab_{stab}"] = {"value": N * M * 2 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                                   "recomputes_per_sweep": 2 * M // stab,
+                                   "drift_median": statistics.median(drifts), "drift_max": max(drifts)}
+        finally:
+            c.close()
+    return out
 
 
 def fp64_bulk_leg(afqmc, torch, stream, args, seed):

@@ -971,20 +971,22 @@ template cudaError_t launch_window_chain<double>(cudaStream_t, int, const double
 // Y' = W Yraw and Yraw[l][sn + c] = -G[I_l][sn + c] (the next window's sites are not in I): the
 // block of the next window as it will be after this window's product.  Grid (row blocks of
 // NB_ROWS, spin); each CTA forms (X_blk W) and then (X_blk W) Yraw_n for its rows.
-constexpr int NB_ROWS = 16;
-constexpr int NB_THREADS = 1024;
+constexpr int NB_ROWS = 4;
+constexpr int NB_THREADS = 512;
 // One CTA per (row block of NB_ROWS rows, spin, walker).  The gathers depend on the accepted sites,
-// so the kernel takes two rounds of global loads: the sites, then every gather of W, Yraw_n and
-// X_blk in one batched pass (eight loads in flight per thread).
+// so the kernel takes two rounds of global loads: the sites, then W, Yraw_n and X_blk, each mapped
+// as warps over rows and lanes over columns (no index divisions, every load of a thread in flight
+// before its shared-memory stores).
 template <typename T>
 __global__ void __launch_bounds__(NB_THREADS) next_block_kernel(const T* __restrict__ Gu0, long ld, int N,
                                                                 WindowBufs wb0, int sn, int nn, T* snap0,
                                                                 long gstride) {
-    constexpr int NW = WinCap<T>::NW, PP = NW + 1;
+    constexpr int NW = WinCap<T>::NW, PP = NW + 1, CS = NW / 32;
     const int wk = blockIdx.z;
     const WindowBufs wb = wb_walker<T>(wb0, wk, N);
     const int m = *wb.m;
-    const int s = blockIdx.y, a0 = blockIdx.x * NB_ROWS, tid = threadIdx.x, nt = blockDim.x;
+    const int s = blockIdx.y, a0 = blockIdx.x * NB_ROWS, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     const int ra = min(NB_ROWS, nn - a0);
     const T* G = Gu0 + (size_t)wk * gstride + (size_t)s * N * ld;
     T* out = snap0 + (size_t)wk * 2 * NW * NW + (size_t)s * NW * NW;
@@ -994,52 +996,51 @@ __global__ void __launch_bounds__(NB_THREADS) next_block_kernel(const T* __restr
     T* Xs = Ys + NW * PP;        // [NB_ROWS][PP]
     T* Ts = Xs + NB_ROWS * PP;   // [NB_ROWS][PP]  X_blk W
     __shared__ int sidx[NW];
-    for (int q = tid; q < m; q += nt) sidx[q] = wb.idx[q];
+    for (int q = tid; q < m; q += blockDim.x) sidx[q] = wb.idx[q];
     __syncthreads();
     const T* W = (const T*)wb.Wx + (size_t)s * NW * NW;
-    // one index space over the three gathers: [W (m x m) | Yraw_n (m x nn) | X_blk (ra x m)]
-    const int n1 = m * m, n2 = n1 + m * nn, n3 = n2 + ra * m;
-    constexpr int NL = 8;
-    for (int e0 = tid; e0 < n3; e0 += NL * nt) {
-        T v[NL];
+    // rows r of W and Yraw_n (r < m) and of X_blk (r < ra) by warps, columns by lanes
+    for (int r = warp; r < m; r += nwarp) {
+        const T* wrow = W + (size_t)r * NW;
+        const T* grow = G + (long)sidx[r] * ld + sn;
+        T vw[CS], vy[CS];
 #pragma unroll
-        for (int q = 0; q < NL; ++q) {
-            const int e = e0 + q * nt;
-            if (e < n1) {
-                const int r = e / m;
-                v[q] = W[r * NW + e - r * m];
-            } else if (e < n2) {
-                const int f = e - n1, l = f / nn;
-                v[q] = -G[(long)sidx[l] * ld + sn + f - l * nn];
-            } else if (e < n3) {
-                const int f = e - n2, aa = f / m;
-                v[q] = G[(long)(sn + a0 + aa) * ld + sidx[f - aa * m]];
-            }
+        for (int j = 0; j < CS; ++j) {
+            const int c = lane + 32 * j;
+            vw[j] = c < m ? wrow[c] : T(0);
+            vy[j] = c < nn ? grow[c] : T(0);
         }
 #pragma unroll
-        for (int q = 0; q < NL; ++q) {
-            const int e = e0 + q * nt;
-            if (e < n1) {
-                const int r = e / m;
-                Ws[r * PP + e - r * m] = v[q];
-            } else if (e < n2) {
-                const int f = e - n1, l = f / nn;
-                Ys[l * PP + f - l * nn] = v[q];
-            } else if (e < n3) {
-                const int f = e - n2, aa = f / m;
-                Xs[aa * PP + f - aa * m] = v[q];
-            }
+        for (int j = 0; j < CS; ++j) {
+            const int c = lane + 32 * j;
+            if (c < m) Ws[r * PP + c] = vw[j];
+            if (c < nn) Ys[r * PP + c] = -vy[j];
+        }
+    }
+    for (int a = warp; a < ra; a += nwarp) {
+        const T* grow = G + (long)(sn + a0 + a) * ld;
+        T vx[CS];
+#pragma unroll
+        for (int j = 0; j < CS; ++j) {
+            const int k = lane + 32 * j;
+            vx[j] = k < m ? grow[sidx[k]] : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < CS; ++j) {
+            const int k = lane + 32 * j;
+            if (k < m) Xs[a * PP + k] = vx[j];
         }
     }
     __syncthreads();
-    for (int e = tid; e < ra * m; e += nt) {  // T = X_blk W
-        const int a = e / m, k = e - a * m;
-        T acc = T(0);
-        for (int l = 0; l < m; ++l) acc += Xs[a * PP + l] * Ws[l * PP + k];
-        Ts[a * PP + k] = acc;
+    for (int a = warp; a < ra; a += nwarp) {  // T = X_blk W
+        for (int k = lane; k < m; k += 32) {
+            T acc = T(0);
+            for (int l = 0; l < m; ++l) acc += Xs[a * PP + l] * Ws[l * PP + k];
+            Ts[a * PP + k] = acc;
+        }
     }
     __syncthreads();
-    for (int e = tid; e < ra * nn; e += nt) {  // snap = G_nn - T Yraw_n
+    for (int e = tid; e < ra * nn; e += blockDim.x) {  // snap = G_nn - T Yraw_n
         const int a = e / nn, c = e - a * nn;
         T acc = T(0);
         for (int l = 0; l < m; ++l) acc += Ts[a * PP + l] * Ys[l * PP + c];
