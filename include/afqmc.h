@@ -206,8 +206,9 @@ int afqmc_apply_flips_noalloc(int precision, int N, long long ld, void* G_up, vo
  *                 (afqmc_get_G, afqmc_measure_energy, the drift of afqmc_recompute_G).  The wrap moves
  *                 the factors (U_R <- B U_R, U_L <- U_L B^{-1}) and leaves T; a window's accepted
  *                 sites I update T <- T - (T U_L[:, I]) W (U_R[I, :] T) (Eqs. FinalDelay,
- *                 BlkFrcBsTnew2) and scale the rows I of U_R (Eq. UpdateLTRMat); the recompute forms
- *                 T = (U_L U_R)^{-1} from the FP64 factors.  The decisions and G equal the G form's.
+ *                 BlkFrcBsTnew2) and scale the rows I of U_R (Eq. UpdateLTRMat); the recompute takes
+ *                 U_R and U_L from the FP64 factors, the left one as (U_L U_R)^{-1} U_L so that T = 1
+ *                 (the same G; the FP32 state stays accurate).  Decisions and G equal the G form's.
  *                 Requires n_up = n_dn for every walker; AFQMC_MODE_LOCAL is not offered (delayed
  *                 with k = 1 is the local update); afqmc_set_G returns AFQMC_ERR_STATE; no CUDA-graph
  *                 capture (afqmc_set_graphs is ignored).

@@ -125,7 +125,7 @@ struct Walker {
     // T form (afqmc_set_form): U_R [nwk][2][N x nsm], U_L [nwk][2][nsm x N], T [nwk][2][nsm x nsm] in
     // the bulk precision; the window gathers U_L[:, I] (nsm x NW) and U_R[I, :] (NW x nsm), the
     // products V = T U_L[:, I], Y = U_R[I, :] T and Y' = W Y, the rows U_R[J, :] T of the next
-    // window (NW x nsm); an FP64 identity (nsm x nsm) for T = (U_L U_R)^{-1}
+    // window (NW x nsm); an FP64 identity (nsm x nsm): T = 1 after every recompute
     void *TUR = nullptr, *TUL = nullptr, *TT = nullptr;
     void *ULI = nullptr, *URI = nullptr, *Vt = nullptr, *Yt = nullptr, *Ypt = nullptr, *Pt = nullptr;
     double* Ieye = nullptr;
@@ -552,38 +552,24 @@ static cudaError_t finish_G(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fa
 // ---------------------------------------------------------------------------
 // T form (Sec. II.C: the walker carries U_R, U_L and T = (U_L U_R)^{-1}; G = 1 - U_R T U_L)
 // ---------------------------------------------------------------------------
-// T = O^{-1} for both spins after form_O (the LU solve with the identity as right-hand side, into
-// Z as ns x ns), then the bulk T, U_R and U_L from the FP64 factors R (N x ns) and Lf (ns x N).
-// The T form requires n_up = n_dn, so both spins form one group (ng = 2).
+// The bulk T-form state from the FP64 factors after form_Z (Z = (U_L U_R)^{-1} U_L, ns x N): U_R = R,
+// U_L = Z and T = (Z R)^{-1} = 1.  Any bases of the two spaces give the same G = 1 - U_R T U_L; this
+// choice keeps the FP32 state accurate.  With the LU bases of the re-orthonormalisation and
+// T = (U_L U_R)^{-1}, the FP32 product U_R T U_L cancels terms some 10^2 - 10^3 times larger than G
+// (at 40 x 40, U = 6: |U_R| ~ 230, |U_L| ~ 140, |T| ~ 600, cond(U_L U_R) ~ 6e4), where
+// U_R (U_L U_R)^{-1} U_L with the left factor taken as Z keeps FP32 rounding near 2e-6 (a numpy
+// check on the same factors: 1.9e-6 against 4.5e-5).  The T form requires n_up = n_dn, so both
+// spins form one group (ng = 2).
 template <typename T>
-static cudaError_t tform_set(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac& R, const Fac& Lf) {
+static cudaError_t tform_set(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac& R) {
+    (void)ctx;
     const int N = w->N, ns = w->nsm, nmat = 2 * w->nwk;
     const long os = (long)ns * ns;
-    SolveArgs sa;
-    sa.LU0 = w->Ob;
-    sa.ostride = os;
-    sa.perm0 = w->perm2;
-    sa.pstride = w->rows_max();
-    sa.B0 = w->Ieye;
-    sa.wstride = 0;
-    sa.sstride = 0;
-    sa.ng = 2;
-    sa.ldb = ns;
-    sa.Z0 = w->Z;
-    sa.zstride = os;
-    sa.ldl = ns;
-    sa.ns = ns;
-    sa.N = ns;
-    sa.nmat = nmat;
     cudaError_t e;
-    {
-        PhaseScope pv(ctx, AFQMC_PHASE_SOLVE, st);
-        if ((e = launch_lu_solve(st, sa)) != cudaSuccess) return e;
-    }
-    if ((e = launch_cast<T>(st, w->Z, ns, (T*)w->TT, ns, ns, ns, nmat, os, os)) != cudaSuccess) return e;
+    if ((e = launch_cast<T>(st, w->Ieye, ns, (T*)w->TT, ns, ns, ns, nmat, 0, os)) != cudaSuccess) return e;
     if ((e = launch_cast<T>(st, R.at(0), ns, (T*)w->TUR, ns, N, ns, nmat, R.bstride(2), (long)N * ns)) != cudaSuccess)
         return e;
-    return launch_cast<T>(st, Lf.at(0), N, (T*)w->TUL, N, ns, N, nmat, Lf.bstride(2), (long)N * ns);
+    return launch_cast<T>(st, w->Z, N, (T*)w->TUL, N, ns, N, nmat, (long)ns * N, (long)N * ns);
 }
 
 // The bulk G of every walker from its T-form state: G = 1 - (U_R T) U_L, with U_R T in Tbuf.
@@ -957,10 +943,10 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
             if (ctx->p.precision == AFQMC_PREC_FP64) CK(finish_G<double>(ctx, w, st, fac_R(w, 0), grp[gi][0], ng[gi], false));
             else CK(finish_G<float>(ctx, w, st, fac_R(w, 0), grp[gi][0], ng[gi], false));
         }
-        // T form: U_R(0), U_L(0) and T(0) = (U_L U_R)^{-1} (the LU of U_L U_R is still in Ob)
+        // T form: U_R(0), U_L(0) = Z and T(0) = 1 (Z = (U_L U_R)^{-1} U_L is still in w->Z)
         if (ctx->form == AFQMC_FORM_T) {
-            if (ctx->p.precision == AFQMC_PREC_FP64) CK(tform_set<double>(ctx, w, st, fac_R(w, 0), fac_L(w, 0)));
-            else CK(tform_set<float>(ctx, w, st, fac_R(w, 0), fac_L(w, 0)));
+            if (ctx->p.precision == AFQMC_PREC_FP64) CK(tform_set<double>(ctx, w, st, fac_R(w, 0)));
+            else CK(tform_set<float>(ctx, w, st, fac_R(w, 0)));
         }
         w->gvalid = true;
         w->pos = 0;
@@ -1560,19 +1546,19 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
             CK(to_stack(w, st, fwd, j));
         }
         if (ctx->form == AFQMC_FORM_T) {
-            // T = (U_L U_R)^{-1} and the bulk factors from the FP64 ones; with a drift requested, G is
-            // formed from the bulk state first and compared with the recomputed FP64 G
+            // the bulk factors from the FP64 ones (U_R, Z = (U_L U_R)^{-1} U_L, T = 1); with a drift
+            // requested, G is formed from the bulk state first and compared with the recomputed FP64 G
             if (rel_drift) {
                 if (f64) CK(tform_form_G<double>(w, st));
                 else CK(tform_form_G<float>(w, st));
-                CK(form_Z(ctx, w, st, fac_R(w, j), fac_L(w, j), 0, 2, nullptr));
+            }
+            CK(form_Z(ctx, w, st, fac_R(w, j), fac_L(w, j), 0, 2, nullptr));
+            if (rel_drift) {
                 if (f64) CK(finish_G<double>(ctx, w, st, fac_R(w, j), 0, 2, true));
                 else CK(finish_G<float>(ctx, w, st, fac_R(w, j), 0, 2, true));
-            } else {
-                CK(form_O(ctx, w, st, fac_R(w, j), fac_L(w, j), 0, 2, nullptr));
             }
-            if (f64) CK(tform_set<double>(ctx, w, st, fac_R(w, j), fac_L(w, j)));
-            else CK(tform_set<float>(ctx, w, st, fac_R(w, j), fac_L(w, j)));
+            if (f64) CK(tform_set<double>(ctx, w, st, fac_R(w, j)));
+            else CK(tform_set<float>(ctx, w, st, fac_R(w, j)));
             w->gvalid = rel_drift != nullptr;
         } else {
             for (int gi = 0; gi < ngr; ++gi) {
