@@ -28,8 +28,8 @@ pytestmark = pytest.mark.gpu
 afqmc = pytest.importorskip("paper_2506_09611_gb300.afqmc")
 
 FP64_TOL = 1e-10
-TF32_8x8 = 5e-5    # measured 1.5e-5 (see the module docstring)
-TF32_40x40 = 1e-3  # measured 2e-4
+TFORM_FP32_8X8 = 5e-5    # measured 1.5e-5 (see the module docstring)
+TFORM_FP32_40X40 = 1e-3  # measured 2e-4
 
 
 def rel(a, b):
@@ -107,11 +107,11 @@ def test_tform_fp32_replay_8x8(mode, k, nb):
             ctx.sweep_slice(ell, +1, mode, k=k, nb=nb, replay=_rep(N, mode, nb, dec, extra))
             for s in range(2):
                 r = rel(ctx.G(0, s), tw.G(s))
-                assert r < TF32_8x8, f"slice {ell} spin {s}: {r}"
+                assert r < TFORM_FP32_8X8, f"slice {ell} spin {s}: {r}"
             if ell % stab == 0:
                 drift = ctx.recompute_G()
                 tw.recompute(stab)
-                assert drift[0] < TF32_8x8
+                assert drift[0] < TFORM_FP32_8X8
         np.testing.assert_array_equal(ctx.fields(0), tw.x)
 
 
@@ -128,7 +128,7 @@ def test_tform_fp32_replay_40x40(mode, k, nb):
             ctx.sweep_slice(ell, +1, mode, k=k, nb=nb, replay=_rep(N, mode, nb, dec, extra))
             for s in range(2):
                 r = rel(ctx.G(0, s), w.G[s])
-                assert r < TF32_40x40, (mode, ell, s, r)
+                assert r < TFORM_FP32_40X40, (mode, ell, s, r)
         np.testing.assert_array_equal(ctx.fields(0), w.x)
 
 
