@@ -1190,9 +1190,10 @@ static int sweep_impl(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int k,
             const T* blk = (wi > 0) ? (const T*)w->snap[par ^ 1] : nullptr;
             CK(launch_window_chain<T>(st, mode, G0, G1, xl, w->u, rep, sp, so, s0, n, nb, wb[par], blk, w->err, bt));
             const int sn = s0 + n, nn = (sn < N) ? ((N - sn < nw) ? N - sn : nw) : 0;
-            // the window's W and the next window's block (nn = 0: W only)
-            if (nn > 0 && wi > 0) CK(cudaStreamWaitEvent(st, w->ev_prod[par ^ 1], 0));
-            CK(launch_next_block<T>(st, G0, G1, sp, wb[par], sn, nn, (T*)w->snap[par], bt));
+            if (nn > 0) {  // the next window's block
+                if (wi > 0) CK(cudaStreamWaitEvent(st, w->ev_prod[par ^ 1], 0));
+                CK(launch_next_block<T>(st, G0, G1, sp, wb[par], sn, nn, (T*)w->snap[par], bt));
+            }
             CK(cudaEventRecord(w->ev_chain[par], st));
             CK(cudaStreamWaitEvent(w->sf, w->ev_chain[par], 0));
             PhaseScope pf(ctx, AFQMC_PHASE_FLUSH, w->sf);
@@ -1345,10 +1346,9 @@ static int sweep_impl_T(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int 
             g2.C = blk; g2.ldc = NW; g2.sC = sB;
             CK(gemm<T>(st, g2));
             CK(launch_identity_minus<T>(st, blk, NW, n, nb2, sB));
-            // decisions, then the window's W from its frozen coefficients
+            // decisions and the window's W
             CK(launch_window_chain<T>(st, mode, (const T*)w->G, nullptr, xl, w->u, rep, sp, so, s0, n, nb, wb, blk,
                                       w->err, bt));
-            CK(launch_next_block<T>(st, (const T*)w->G, nullptr, sp, wb, 0, 0, blk, bt));
             // T <- T - (T U_L[:, I]) (W (U_R[I, :] T)), then the rows I of U_R
             PhaseScope pf(ctx, AFQMC_PHASE_FLUSH, st);
             CK(launch_tform_gather<T>(st, UR, UL, N, ns, ns, fs, fs, wb, ULI, URI, nb2));

@@ -380,7 +380,7 @@ __device__ __forceinline__ void trailing_update(T* Gs, int n, int P, int a, T f0
 // pass of a warp starts at its first column (identity columns are zero above the diagonal).
 template <typename T, int RPL>
 __device__ __forceinline__ void window_w_rpl(const T* Gs, int n, int P, const int* idx, const T (*fk)[WinCap<T>::NW],
-                                             int m, T* Wx, int lane, int w, int ldw = WinCap<T>::NW) {
+                                             int m, T* Wx, int lane, int w) {
     constexpr int NW = WinCap<T>::NW, WCPW = NW / 16;
     const int s = w >> 4, j0 = (w & 15) * WCPW;
     if (j0 >= m) return;
@@ -453,7 +453,7 @@ __device__ __forceinline__ void window_w_rpl(const T* Gs, int n, int P, const in
 #pragma unroll
         for (int r = 0; r < RPL; ++r) cf[r] = cfn[r];
     }
-    T* Wd = Wx + (size_t)s * NW * ldw;
+    T* Wd = Wx + (size_t)s * NW * NW;
 #pragma unroll
     for (int r = 0; r < RPL; ++r) {
         const int k = lane + 32 * r;
@@ -461,21 +461,21 @@ __device__ __forceinline__ void window_w_rpl(const T* Gs, int n, int P, const in
             const T fkk = -fks[k];
 #pragma unroll
             for (int c = 0; c < WCPW; ++c)
-                if (j0 + c < m) Wd[k * ldw + j0 + c] = fkk * y[r][c];
+                if (j0 + c < m) Wd[k * NW + j0 + c] = fkk * y[r][c];
         }
     }
 }
 
 template <typename T>
 __device__ __forceinline__ void window_w(const T* Gs, int n, int P, const int* idx, const T (*fk)[WinCap<T>::NW],
-                                         int m, T* Wx, int tid, int ldw = WinCap<T>::NW) {
+                                         int m, T* Wx, int tid) {
     constexpr int NW = WinCap<T>::NW;
     const int lane = tid & 31, w = tid >> 5;
     if (w >= 32) return;
-    if (m <= 32) window_w_rpl<T, 1>(Gs, n, P, idx, fk, m, Wx, lane, w, ldw);
-    else if (m <= 64) window_w_rpl<T, 2>(Gs, n, P, idx, fk, m, Wx, lane, w, ldw);
-    else if (NW > 64 && m <= 96) window_w_rpl<T, (NW > 64 ? 3 : 2)>(Gs, n, P, idx, fk, m, Wx, lane, w, ldw);
-    else window_w_rpl<T, NW / 32>(Gs, n, P, idx, fk, m, Wx, lane, w, ldw);
+    if (m <= 32) window_w_rpl<T, 1>(Gs, n, P, idx, fk, m, Wx, lane, w);
+    else if (m <= 64) window_w_rpl<T, 2>(Gs, n, P, idx, fk, m, Wx, lane, w);
+    else if (NW > 64 && m <= 96) window_w_rpl<T, (NW > 64 ? 3 : 2)>(Gs, n, P, idx, fk, m, Wx, lane, w);
+    else window_w_rpl<T, NW / 32>(Gs, n, P, idx, fk, m, Wx, lane, w);
 }
 
 template <typename T, int MODE>
@@ -849,19 +849,16 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
         wb.dtot[q] = dl[q];
         wb.dtot[WinCap<T>::NW + q] = dl[n + q];
     }
-    // The frozen coefficients of the window's update: C[k][k'] = Gs[idx[k]][idx[k']], the block
-    // entries between accepted sites as they were at acceptance (rows and columns at or before an
-    // accepted site are never touched again), to wb.Wm (pitch NW, per spin); the factors
-    // f_k = -Delta_k / r_k went to wb.dtot above.  next_block_kernel forms the update matrix W from
-    // them (its CTAs run without this kernel's 64-register limit).
-    {
-        constexpr int NWC = WinCap<T>::NW;
-        T* Cg = (T*)wb.Wm;
-        for (int e = tid; e < 2 * m * m; e += nt) {
-            const int sp_ = e >= m * m ? 1 : 0, rem = e - sp_ * m * m, k = rem / m, kk = rem - k * m;
-            Cg[((size_t)sp_ * NWC + k) * NWC + kk] = Gs[(sp_ * n + idx[k]) * P + idx[kk]];
-        }
-    }
+    // The window's update matrix W (Eq. DelayRgenk in G form).  With C[k][k'] = Gs[idx[k]][idx[k']]
+    // the block entries frozen at acceptance time (rows and columns at or before an accepted site
+    // are never touched again), f_k = -Delta_k / r_k, L1 = I + Cl F and U1 = I + Cu F (Cl, Cu the
+    // strictly lower / upper parts of C, F = diag f), the delayed-update recursions give
+    // W = -F U1^{-1} L1^{-1}: per column of the identity a forward and a backward substitution,
+    //   y_k = b_k - sum_{k'<k} C[k][k'] f_k' y_k',   z_k = y_k - sum_{k'>k} C[k][k'] f_k' z_k',
+    //   W_k = -f_k z_k.
+    // Each warp owns WCPW columns of one spin in registers (lane l holds rows l, l + 32, ...) and
+    // broadcasts the finished row of every step with a shuffle: no block-wide barrier per step.
+    window_w<T>(Gs, n, P, idx, s_fk, m, (T*)wb.Wx, tid);
     if (tid == 0) {
         *wb.m = m;
         if (so.sign) *so.sign = s_sign;
@@ -975,21 +972,11 @@ template cudaError_t launch_window_chain<double>(cudaStream_t, int, const double
 // block of the next window as it will be after this window's product.  Grid (row blocks of
 // NB_ROWS, spin); each CTA forms (X_blk W) and then (X_blk W) Yraw_n for its rows.
 constexpr int NB_ROWS = 4;
-constexpr int NB_THREADS = 512;  // 16 warps: the W substitutions give each warp WCPW columns of one spin
-// One CTA per (row block of NB_ROWS rows, spin, walker).
-//   1. The window's update matrix W (Eq. DelayRgenk in G form) from the frozen coefficients the window
-//      kernel exported: with C[k][k'] the block entries between accepted sites as they were at
-//      acceptance, f_k = -Delta_k / r_k, L1 = I + Cl F and U1 = I + Cu F (Cl, Cu the strictly lower /
-//      upper parts of C, F = diag f), the delayed-update recursions give W = -F U1^{-1} L1^{-1}: per
-//      column of the identity a forward and a backward substitution,
-//        y_k = b_k - sum_{k'<k} C[k][k'] f_k' y_k',   z_k = y_k - sum_{k'>k} C[k][k'] f_k' z_k',
-//        W_k = -f_k z_k.
-//      Each warp owns WCPW columns in registers (lane l holds rows l, l + 32, ...) and broadcasts the
-//      finished row of every step with a shuffle.  Every CTA forms W for its spin (in parallel); CTA 0
-//      of each spin stores it for the flush.  nn = 0 (the slice's last window) stops here.
-//   2. The next window's block as it will be after this window's update, snap = G_nn - (X_blk W) Yraw_n:
-//      the accepted sites, then the gathers of Yraw_n and X_blk mapped as warps over rows and lanes
-//      over columns (every load of a thread in flight before its shared-memory stores).
+constexpr int NB_THREADS = 512;
+// One CTA per (row block of NB_ROWS rows, spin, walker).  The gathers depend on the accepted sites,
+// so the kernel takes two rounds of global loads: the sites, then W, Yraw_n and X_blk, each mapped
+// as warps over rows and lanes over columns (no index divisions, every load of a thread in flight
+// before its shared-memory stores).
 template <typename T>
 __global__ void __launch_bounds__(NB_THREADS) next_block_kernel(const T* __restrict__ Gu0, long ld, int N,
                                                                 WindowBufs wb0, int sn, int nn, T* snap0,
@@ -1004,50 +991,29 @@ __global__ void __launch_bounds__(NB_THREADS) next_block_kernel(const T* __restr
     const T* G = Gu0 + (size_t)wk * gstride + (size_t)s * N * ld;
     T* out = snap0 + (size_t)wk * 2 * NW * NW + (size_t)s * NW * NW;
     extern __shared__ __align__(16) unsigned char nb_smem[];
-    T* Ws = (T*)nb_smem;         // [m][PP]   W
+    T* Ws = (T*)nb_smem;         // [m][PP]
     T* Ys = Ws + NW * PP;        // [m][PP]   Yraw_n
-    T* Cs = Ys + NW * PP;        // [m][PP]   frozen coefficients
-    T* Xs = Cs + NW * PP;        // [NB_ROWS][PP]
+    T* Xs = Ys + NW * PP;        // [NB_ROWS][PP]
     T* Ts = Xs + NB_ROWS * PP;   // [NB_ROWS][PP]  X_blk W
-    __shared__ int sidx[NW], iota[NW];
-    __shared__ T sf[NW];
-    for (int q = tid; q < m; q += blockDim.x) {
-        sidx[q] = wb.idx[q];
-        iota[q] = q;
-        sf[q] = (T)wb.dtot[(size_t)s * NW + q];
-    }
-    const T* Cg = (const T*)wb.Wm + (size_t)s * NW * NW;
-    for (int r = warp; r < m; r += nwarp) {
-        T vc[CS];
-#pragma unroll
-        for (int j = 0; j < CS; ++j) vc[j] = (lane + 32 * j < m) ? Cg[(size_t)r * NW + lane + 32 * j] : T(0);
-#pragma unroll
-        for (int j = 0; j < CS; ++j)
-            if (lane + 32 * j < m) Cs[r * PP + lane + 32 * j] = vc[j];
-    }
+    __shared__ int sidx[NW];
+    for (int q = tid; q < m; q += blockDim.x) sidx[q] = wb.idx[q];
     __syncthreads();
-    window_w<T>(Cs, 0, PP, iota, (const T(*)[NW])sf, m, Ws, tid, PP);
-    __syncthreads();
-    if (blockIdx.x == 0) {  // W for the flush
-        T* W = (T*)wb.Wx + (size_t)s * NW * NW;
-        for (int e = tid; e < m * m; e += blockDim.x) {
-            const int r = e / m, c = e - r * m;
-            W[(size_t)r * NW + c] = Ws[r * PP + c];
-        }
-    }
-    if (ra <= 0) return;
-    // rows r of Yraw_n (r < m) and of X_blk (r < ra) by warps, columns by lanes
+    const T* W = (const T*)wb.Wx + (size_t)s * NW * NW;
+    // rows r of W and Yraw_n (r < m) and of X_blk (r < ra) by warps, columns by lanes
     for (int r = warp; r < m; r += nwarp) {
+        const T* wrow = W + (size_t)r * NW;
         const T* grow = G + (long)sidx[r] * ld + sn;
-        T vy[CS];
+        T vw[CS], vy[CS];
 #pragma unroll
         for (int j = 0; j < CS; ++j) {
             const int c = lane + 32 * j;
+            vw[j] = c < m ? wrow[c] : T(0);
             vy[j] = c < nn ? grow[c] : T(0);
         }
 #pragma unroll
         for (int j = 0; j < CS; ++j) {
             const int c = lane + 32 * j;
+            if (c < m) Ws[r * PP + c] = vw[j];
             if (c < nn) Ys[r * PP + c] = -vy[j];
         }
     }
@@ -1082,19 +1048,18 @@ __global__ void __launch_bounds__(NB_THREADS) next_block_kernel(const T* __restr
     }
 }
 
-// nn = 0 forms only the window's W (the slice's last window).
 template <typename T>
 cudaError_t launch_next_block(cudaStream_t st, const T* Gu, const T* Gd, const SiteParams& sp, WindowBufs wb, int sn,
                               int nn, T* snap, Batch bt) {
     (void)Gd;
     constexpr int NW = WinCap<T>::NW;
-    const size_t shm = (3 * (size_t)NW + 2 * NB_ROWS) * (NW + 1) * sizeof(T);
+    const size_t shm = (2 * (size_t)NW + 2 * NB_ROWS) * (NW + 1) * sizeof(T);
     {
         cudaError_t ea = ensure_smem_attr((const void*)next_block_kernel<T>, shm);
         if (ea != cudaSuccess) return ea;
     }
     count_launch();
-    const int nbx = nn > 0 ? (nn + NB_ROWS - 1) / NB_ROWS : 1;
+    const int nbx = (nn + NB_ROWS - 1) / NB_ROWS;
     next_block_kernel<T><<<dim3(nbx, 2, bt.nwk), NB_THREADS, shm, st>>>(Gu, sp.ld, sp.N, wb, sn, nn, snap,
                                                                          bt.gstride);
     return cudaGetLastError();
