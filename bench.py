@@ -731,7 +731,7 @@ def fp64_alu_peak(pk):
     return 152 * FP64_FMA_PER_SM_CLK * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
-def kernel_rooflines(prof, gemm, pk, pk_src, steps, wrap="separable"):
+def kernel_rooflines(prof, gemm, pk, pk_src, steps, wrap="separable", wrap_tile=0):
     """Per-kernel rooflines from the nested per-launch intervals of the timed region:
     achieved = algorithmic work of the launches / their summed CUDA-event durations.
     Returns a list sorted by total time (the first entry is the dominant kernel)."""
@@ -771,19 +771,27 @@ def kernel_rooflines(prof, gemm, pk, pk_src, steps, wrap="separable"):
                                    "the digit split and the FP64 epilogues" % pk_src})
     wg = prof.get("wrap_gemm", {"ms": 0.0, "intervals": 0})
     if wg["intervals"] > 0 and wrap == "separable":
-        # one launch = one side of the wrap for both spins: two L-point passes over N^2 elements each
-        flop = 2.0 * 2.0 * 2.0 * L * N * N
-        byts = 2 * 2 * N * N * 4
+        # one interval = one wrap (both sides) of both spins: four L-point passes over N^2 elements,
+        # each L multiply-adds per element.  The line passes (the default) are four launches that
+        # each read and write G; the tile form two.
+        flop = 2.0 * 2.0 * 4.0 * L * N * N
+        npass = 4 if wrap_tile == 0 else 2
+        byts = npass * 2 * 2 * N * N * 4
         ach = flop * wg["intervals"] / (wg["ms"] / 1e3) / 1e12
         peak = fp32_alu_peak(pk)
-        out.append({"kernel": "sep_kernel (separable wrap: one side, both spins per launch, FP32)", "bound": "alu",
+        name = ("sep_line_kernel (separable wrap: 4 line passes, both spins, FP32)" if wrap_tile == 0 else
+                "sep_kernel (separable wrap: 2 tile passes of width %d, both spins, FP32)" % wrap_tile)
+        out.append({"kernel": name, "bound": "alu",
                     "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": NCU_TRAFFIC.get("sep"), "launches": wg["intervals"],
+                    "traffic": NCU_TRAFFIC.get("sep") if wrap_tile == 0 else None, "launches": wg["intervals"],
+                    "launches_per_interval": npass,
                     "ms_per_launch": wg["ms"] / wg["intervals"], "ms_per_step": wg["ms"] / steps,
                     "work_per_launch": flop, "bytes_per_launch": byts,
                     "gbs": byts * wg["intervals"] / (wg["ms"] / 1e3) / 1e9,
                     "peak_source": "FP32 FMA pipes: 152 SMs x 128 lanes x 2 flop x sm_max_mhz (derived); "
-                                   "arithmetic intensity 20 flop/B puts it above the HBM ridge"})
+                                   "one 'launch' here is one wrap (both sides, %d kernel launches); "
+                                   "arithmetic intensity %.0f flop/B puts it above the HBM ridge"
+                                   % (npass, flop / byts)})
     elif wg["intervals"] > 0:
         flop = 2.0 * 2.0 * N ** 3  # one launch = one N x N x N product for both spins
         ach = flop * wg["intervals"] / (wg["ms"] / 1e3) / 1e12

@@ -251,18 +251,21 @@ int afqmc_set_graphs(afqmc_ctx* ctx, int on);
  *   AFQMC_WRAP_SEPARABLE  the periodic L x L lattice has E = Ex (x) Ex, so each product is two
  *                         L-point passes over one index of G (2 L N^2 instead of N^3 multiply-adds),
  *                         in the bulk precision, with the field scalings folded into the passes.
- * A new context uses the separable wrap for every walker group whose lattice tile fits on chip
- * (every lattice up to 64 x 64 in FP32) and the dense wrap otherwise; afqmc_set_wrap fixes one
- * mode for all groups.  Applies to the following slices.  AFQMC_ERR_ARG for a NULL ctx, an unknown
- * mode, or (separable) a walker lattice whose tile does not fit on chip. */
+ * A new context uses the separable wrap for every walker group whose lattice it covers (every
+ * lattice up to 64 x 64: four line passes of one lattice coordinate each; larger ones while a tile
+ * of 4 columns fits on chip) and the dense wrap otherwise; afqmc_set_wrap fixes one mode for all
+ * groups.  Applies to the following slices.  AFQMC_ERR_ARG for a NULL ctx, an unknown mode, or
+ * (separable) a walker lattice it does not cover. */
 #define AFQMC_WRAP_DENSE 0
 #define AFQMC_WRAP_SEPARABLE 1
 int afqmc_set_wrap(afqmc_ctx* ctx, int mode);
-/* Tile width of the separable wrap: each thread block transforms `width` columns (rows) of G over all N
- * rows (columns) in shared memory, so narrower tiles mean more, smaller blocks and more of them
- * resident per SM.  width = 0 restores the default (4); otherwise a
- * multiple of 4 whose tile fits in shared memory for every walker's lattice, else AFQMC_ERR_ARG.
- * A performance knob (the tuner times it); the result does not depend on it. */
+/* Form of the separable wrap.  width = 0 (the default): four line passes per wrap, each applying Ex
+ * along one lattice coordinate of G's row or column index, one L-point line per thread in
+ * registers (lattices up to 64 x 64; larger ones take tiles of 4).  width > 0: two tile passes,
+ * each thread block transforming `width` columns (rows) of G over all N rows (columns) in shared
+ * memory; width must be a multiple of 4 whose tile fits in shared memory for every walker's
+ * lattice, else AFQMC_ERR_ARG.  A performance knob (the tuner times it); the result agrees to
+ * rounding. */
 int afqmc_set_wrap_tile(afqmc_ctx* ctx, int width);
 /* Sync the last stream and return, per phase, the summed device milliseconds, the number of
  * bracketed intervals, and the number of library kernels launched in that phase.  Each array

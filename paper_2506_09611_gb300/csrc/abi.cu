@@ -100,6 +100,7 @@ struct Walker {
     cudaStream_t sm = nullptr;  // the group's main stream (forked from the caller's stream)
     cudaEvent_t ev_chain[2] = {nullptr, nullptr}, ev_prod[2] = {nullptr, nullptr}, ev_done = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_rc = nullptr;  // after a recompute's last read of the propagated factor (deferred LU)
     unsigned long long* visit_d = nullptr;  // device visit counter (keys the uniforms)
     struct Graph {
         cudaGraphExec_t exec = nullptr;
@@ -720,6 +721,7 @@ int afqmc_destroy(afqmc_ctx* ctx) {
         if (w->ev_prop) cudaEventDestroy(w->ev_prop);
         if (w->ev_fork) cudaEventDestroy(w->ev_fork);
         if (w->ev_join) cudaEventDestroy(w->ev_join);
+        if (w->ev_rc) cudaEventDestroy(w->ev_rc);
         for (auto& kv : w->graphs)
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         if (w->sf) cudaStreamDestroy(w->sf);
@@ -837,11 +839,14 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
         CK(cudaEventCreateWithFlags(&w->ev_prop, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&w->ev_rc, cudaEventDisableTiming));
         {
             int lo = 0, hi = 0;
             CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
             CK(cudaStreamCreateWithPriority(&w->sf, cudaStreamNonBlocking, lo));
-            CK(cudaStreamCreateWithFlags(&w->sm, cudaStreamNonBlocking));
+            // the group's main stream (the accept chain, the wrap, the recompute) outranks the flush
+            // and propagation streams, so their blocks never hold back a window kernel's launch
+            CK(cudaStreamCreateWithPriority(&w->sm, cudaStreamNonBlocking, hi));
             CK(cudaStreamCreateWithPriority(&w->sp, cudaStreamNonBlocking, lo));
         }
         CK(dalloc(A, &w->visit_d, sizeof(unsigned long long)));
@@ -1037,7 +1042,7 @@ static int sweep_impl(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int k,
         cudaError_t e = launch_field_scales_T<T>(st, xl, N, ctx->c, d, dinv, N, nwk, bt.xstride);
         if (e != cudaSuccess) return e;
         const bool sep = ctx->wrap_mode == AFQMC_WRAP_SEPARABLE ||
-                         (ctx->wrap_mode < 0 && sep_width<T>(w->L, N) > 0);
+                         (ctx->wrap_mode < 0 && sep_available<T>(w->L, N));
         if (sep) {
             // E = Ex (x) Ex: two passes per product, in place, both spins of every walker
             SepArgs a1, a2;
@@ -1411,19 +1416,16 @@ int afqmc_sweep_slice(afqmc_ctx* ctx, int slice, int dir, int mode, int k, int n
     }
     cudaStream_t st = (cudaStream_t)stream;
     ctx->last = st;
-    // Groups run concurrently, each on its own stream forked from (and joined back into) st.
-    // With graphs on, a group's slice is captured once per (slice, dir, mode, k, nb) and then
-    // replayed: every launch of the slice, the flush stream's included, in one graph launch.
-    const bool fork = ctx->w.size() > 1;
+    // Every group runs on its own high-priority stream forked from (and joined back into) st, so
+    // groups run concurrently.  With graphs on, a group's slice is captured once per (slice, dir,
+    // mode, k, nb) and then replayed: every launch of the slice, the flush stream's included, in
+    // one graph launch.
     const bool use_graph = ctx->graphs && !replay && !ctx->prof.on && ctx->form == AFQMC_FORM_G;
     for (int gi = 0; gi < (int)ctx->w.size(); ++gi) {
         Walker* w = ctx->w[gi];
-        cudaStream_t sg = st;
-        if (fork || use_graph) {
-            CK(cudaEventRecord(w->ev_fork, st));
-            CK(cudaStreamWaitEvent(w->sm, w->ev_fork, 0));
-            sg = w->sm;
-        }
+        CK(cudaEventRecord(w->ev_fork, st));
+        CK(cudaStreamWaitEvent(w->sm, w->ev_fork, 0));
+        cudaStream_t sg = w->sm;
         if (use_graph) {
             const long long key = ((((long long)slice * 4 + (dir > 0 ? 1 : 0)) * 4 + mode) * 512 + k) * 64 + nb;
             auto it = w->graphs.find(key);
@@ -1511,21 +1513,26 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     ctx->last = st;
     const bool f64 = ctx->p.precision == AFQMC_PREC_FP64;
-    const bool fork = ctx->w.size() > 1;
     cudaStream_t st0 = st;
     for (auto* w : ctx->w) {
         const int j = w->pos / S;
-        if (fork) {  // groups recompute concurrently
-            CK(cudaEventRecord(w->ev_fork, st0));
-            CK(cudaStreamWaitEvent(w->sm, w->ev_fork, 0));
-            st = w->sm;
-        }
+        // groups recompute concurrently, each on its high-priority main stream
+        CK(cudaEventRecord(w->ev_fork, st0));
+        CK(cudaStreamWaitEvent(w->sm, w->ev_fork, 0));
+        st = w->sm;
         PhaseScope ps(ctx, AFQMC_PHASE_RECOMPUTE, st);
         CK(cudaMemsetAsync(w->acc2, 0, (size_t)w->nwk * 16, st));
         // the factors of the current position: one side from the stacks, the other propagated
-        // over the last S slices from the previous stack entry and re-orthonormalised
+        // over the last S slices from the previous stack entry and re-orthonormalised.  With an
+        // FP32 bulk G (G form) the re-orthonormalisation leaves the critical path: G is formed
+        // from the propagated factor itself (S slices from an orthonormal basis, so its column
+        // scales spread by at most cond(B)^S and G keeps far more than FP32 accuracy; Eq.
+        // GrFMatNew holds for any basis of the same space), and the LU that makes the stack
+        // entry runs afterwards on the propagation stream, where the next interval's propagation
+        // starts from it.
         const bool fwd = w->last_dir > 0;
         const bool prop = fwd ? (j > 0) : (w->pos != ctx->p.M);
+        const bool defer = prop && !f64 && ctx->form == AFQMC_FORM_G;
         int grp[2][2], ng[2];
         const int ngr = spin_groups(w, grp, ng);
         if (prop) {
@@ -1539,11 +1546,13 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
                 if (fwd) CK(propagate(ctx, w, st, 0, w->pos - S + 1, 1, S));
                 else CK(propagate(ctx, w, st, 1, w->pos + S, -1, S));
             }
-            for (int gi = 0; gi < ngr; ++gi) {
-                if (fwd) CK(stab_rows(ctx, w, st, fac_cur(w), grp[gi][0], ng[gi], nullptr));
-                else CK(stab_cols(ctx, w, st, fac_cur(w), grp[gi][0], ng[gi], nullptr));
+            if (!defer) {
+                for (int gi = 0; gi < ngr; ++gi) {
+                    if (fwd) CK(stab_rows(ctx, w, st, fac_cur(w), grp[gi][0], ng[gi], nullptr));
+                    else CK(stab_cols(ctx, w, st, fac_cur(w), grp[gi][0], ng[gi], nullptr));
+                }
+                CK(to_stack(w, st, fwd, j));
             }
-            CK(to_stack(w, st, fwd, j));
         }
         if (ctx->form == AFQMC_FORM_T) {
             // the bulk factors from the FP64 ones (U_R, Z = (U_L U_R)^{-1} U_L, T = 1); with a drift
@@ -1561,17 +1570,27 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
             else CK(tform_set<float>(ctx, w, st, fac_R(w, j)));
             w->gvalid = rel_drift != nullptr;
         } else {
+            const Fac R = (defer && fwd) ? fac_cur(w) : fac_R(w, j);
+            const Fac Lf = (defer && !fwd) ? fac_cur(w) : fac_L(w, j);
             for (int gi = 0; gi < ngr; ++gi) {
-                CK(form_Z(ctx, w, st, fac_R(w, j), fac_L(w, j), grp[gi][0], ng[gi], nullptr));
-                if (f64) CK(finish_G<double>(ctx, w, st, fac_R(w, j), grp[gi][0], ng[gi], true));
-                else CK(finish_G<float>(ctx, w, st, fac_R(w, j), grp[gi][0], ng[gi], true));
+                CK(form_Z(ctx, w, st, R, Lf, grp[gi][0], ng[gi], nullptr));
+                if (f64) CK(finish_G<double>(ctx, w, st, R, grp[gi][0], ng[gi], true));
+                else CK(finish_G<float>(ctx, w, st, R, grp[gi][0], ng[gi], true));
+            }
+            if (defer) {  // the stack entry, off the critical path
+                CK(cudaEventRecord(w->ev_rc, st));
+                CK(cudaStreamWaitEvent(w->sp, w->ev_rc, 0));
+                for (int gi = 0; gi < ngr; ++gi) {
+                    if (fwd) CK(stab_rows(ctx, w, w->sp, fac_cur(w), grp[gi][0], ng[gi], nullptr));
+                    else CK(stab_cols(ctx, w, w->sp, fac_cur(w), grp[gi][0], ng[gi], nullptr));
+                }
+                CK(to_stack(w, w->sp, fwd, j));
+                CK(cudaEventRecord(w->ev_prop, w->sp));
             }
         }
         w->need_recompute = false;
-        if (fork) {
-            CK(cudaEventRecord(w->ev_join, st));
-            CK(cudaStreamWaitEvent(st0, w->ev_join, 0));
-        }
+        CK(cudaEventRecord(w->ev_join, st));
+        CK(cudaStreamWaitEvent(st0, w->ev_join, 0));
     }
     st = st0;
     if (rel_drift) {
@@ -1719,7 +1738,7 @@ int afqmc_set_wrap(afqmc_ctx* ctx, int mode) {
     if (!ctx || (mode != AFQMC_WRAP_DENSE && mode != AFQMC_WRAP_SEPARABLE)) return AFQMC_ERR_ARG;
     if (mode == AFQMC_WRAP_SEPARABLE) {
         for (auto* w : ctx->w) {
-            const int ok = ctx->p.precision == AFQMC_PREC_FP64 ? sep_width<double>(w->L, w->N) : sep_width<float>(w->L, w->N);
+            const bool ok = ctx->p.precision == AFQMC_PREC_FP64 ? sep_available<double>(w->L, w->N) : sep_available<float>(w->L, w->N);
             if (!ok) return AFQMC_ERR_ARG;
         }
     }

@@ -249,15 +249,18 @@ struct Batch {
 template <typename T>
 int window_max();      // largest window (sites) the chain kernel holds in shared memory
 
-// Separable wrap products (sepwrap.cu, tile code in sepwrap.cuh): G <- (A (x) A) G (side 0) or
+// Separable wrap products (sepwrap.cu, code in sepwrap.cuh): G <- (A (x) A) G (side 0) or
 // G <- G (A (x) A) (side 1) for the batch of N x N matrices of a SepArgs, with its optional row /
-// column scalings before and after.  cudaErrorInvalidValue when N != L^2 or no tile of at least
-// 4 columns fits on chip.  sep_width: the default tile width of launch_sep (0: none fits).
+// column scalings before and after.  SepArgs::w == 0 takes the line passes where L <= 64 (else
+// tiles of the default width), w > 0 tiles of w columns.  cudaErrorInvalidValue when N != L^2 or
+// the requested tiles do not fit on chip.  sep_width: the default tile width (0: none fits).
 struct SepArgs;
 template <typename T>
 int sep_width(int L, int N);
 template <typename T>
 bool sep_width_fits(int L, int N, int w);  // a tile of w columns (w % 4 == 0) fits on chip
+template <typename T>
+bool sep_available(int L, int N);          // launch_sep with w = 0 applies (line passes or tiles)
 template <typename T>
 cudaError_t launch_sep(cudaStream_t st, const SepArgs& a);
 

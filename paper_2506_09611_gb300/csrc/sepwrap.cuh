@@ -52,6 +52,9 @@ struct SepArgs {
     const void* rs_out = nullptr;  // applied before (in) or after (out) the product; matrix z uses
     const void* cs_out = nullptr;  // the vector at offset z * sv (sv >= the vector's length)
     long sv = 0;
+    int circ = 0;  // A is circulant (A[x][x'] = A[0][(x' - x) mod L]), as the periodic chain's
+                   // factors exp(-+tau K_1d) are: the line passes may then keep its first row in
+                   // registers
 };
 
 // Shared memory of one tile: A, and the two N x w buffers.
@@ -234,6 +237,242 @@ SEP_HD inline void sep_tile(const SepArgs& a, int t, int z, int tid, int nt, uns
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Line passes.  One launch applies A along ONE of the four lattice coordinates of G's two site
+// indices (i = x + L y for the row, k = x' + L y' for the column):
+//   axis 0: x of the row index     G[(x, y)][j]   <- sum_x'' A[x][x''] G[(x'', y)][j]
+//   axis 1: y of the row index     G[(x, y)][j]   <- sum_y'' A[y][y''] G[(x, y'')][j]
+//   axis 2: x of the column index  G[r][(x', y')] <- sum_x'' G[r][(x'', y')] A[x''][x']
+//   axis 3: y of the column index  G[r][(x', y')] <- sum_y'' G[r][(x', y'')] A[y''][y']
+// The L elements one pass mixes form a line; each thread owns one line, loads it into registers
+// (all L loads in flight), forms the L outputs four at a time from one broadcast 16-byte
+// shared-memory read of A per step (A is symmetric, so row p holds A[p][x..x+3] = A[x..x+3][p]),
+// and writes them back in place (no other thread touches the line).  Consecutive threads take
+// consecutive columns j (axes 0, 1), consecutive y' of one row (axis 2, each thread reading 4L
+// contiguous bytes) or consecutive x' of one row (axis 3), so the warp's loads coalesce.  A side
+// of the wrap is two launches (axes 0 and 1, or 2 and 3); the input scaling is applied by the
+// first one on load and the output scaling by the second one on store.  LM (a multiple of 4,
+// L <= LM) is the compile-time line length: A is zero-padded to LM x LM and the line's elements
+// beyond L are zero.
+struct SepLineArgs {
+    void* G = nullptr;          // batch matrices R x C, row-major, leading dimension ld, batch stride sG
+    long ld = 0, sG = 0;
+    int L = 0, R = 0, C = 0, batch = 1;
+    int axis = 0;
+    const void* rs_in = nullptr, *cs_in = nullptr;    // as in SepArgs (matrix z: offset z * sv)
+    const void* rs_out = nullptr, *cs_out = nullptr;
+    long sv = 0;
+    int circ = 0;  // as in SepArgs
+};
+
+// Lines of one matrix: L per column on the row axes, L per row on the column axes.
+SEP_HD inline long sep_line_count(const SepLineArgs& a) {
+    return a.axis < 2 ? (long)a.L * a.C : (long)a.R * a.L;
+}
+
+// The compile-time line length for a lattice side L (0: L > 64, no line kernel).
+SEP_HD inline int sep_line_lm(int L) {
+    const int lms[9] = {8, 12, 16, 20, 24, 32, 40, 48, 64};
+    for (int q = 0; q < 9; ++q)
+        if (L <= lms[q]) return lms[q];
+    return 0;
+}
+
+// Line `line` (matrix z = line / lines per matrix) of a pass; As is A as LM x LM in T, zero-padded.
+template <typename T, int LM>
+SEP_HD inline void sep_line(const SepLineArgs& a, long line, const T* As) {
+    const int L = a.L;
+    const long nl = sep_line_count(a);
+    const int z = (int)(line / nl);
+    const long l = line - (long)z * nl;
+    T* G = (T*)a.G + (size_t)z * a.sG;
+    const T* ri = a.rs_in ? (const T*)a.rs_in + (size_t)z * a.sv : nullptr;
+    const T* ci = a.cs_in ? (const T*)a.cs_in + (size_t)z * a.sv : nullptr;
+    const T* ro = a.rs_out ? (const T*)a.rs_out + (size_t)z * a.sv : nullptr;
+    const T* co = a.cs_out ? (const T*)a.cs_out + (size_t)z * a.sv : nullptr;
+    // element p of the line: G[base + p * stride], row index i0 + p * di, column index k0 + p * dk
+    long base, stride;
+    int i0, di, k0, dk;
+    if (a.axis < 2) {
+        const int j = (int)(l % a.C), o = (int)(l / a.C);  // o = y (axis 0) or x (axis 1)
+        i0 = a.axis == 0 ? L * o : o;
+        di = a.axis == 0 ? 1 : L;
+        k0 = j; dk = 0;
+        base = (long)i0 * a.ld + j;
+        stride = (long)di * a.ld;
+    } else {
+        const int o = (int)(l % L), r = (int)(l / L);      // o = y' (axis 2) or x' (axis 3)
+        k0 = a.axis == 2 ? L * o : o;
+        dk = a.axis == 2 ? 1 : L;
+        i0 = r; di = 0;
+        base = (long)r * a.ld + k0;
+        stride = dk;
+    }
+    T* g = G + base;
+    // the fixed factor of the scalings (the column on the row axes, the row on the column axes)
+    T fin = 1, fout = 1;
+    if (a.axis < 2) {
+        if (ci) fin = ci[k0];
+        if (co) fout = co[k0];
+    } else {
+        if (ri) fin = ri[i0];
+        if (ro) fout = ro[i0];
+    }
+    const T* vin = a.axis < 2 ? ri : ci;    // the scalings along the line
+    const T* vout = a.axis < 2 ? ro : co;
+    const int vo = a.axis < 2 ? i0 : k0, vd = a.axis < 2 ? di : dk;
+    T v[LM];
+    const bool vec = stride == 1 && L % 4 == 0 && a.ld % 4 == 0 && a.sG % 4 == 0 && ((size_t)a.G) % 16 == 0;
+    if (vec) {
+#pragma unroll
+        for (int p = 0; p < LM; p += 4) {
+            if (p < L) {
+                sep_ld4(g + p, v + p);
+            } else {
+                v[p] = v[p + 1] = v[p + 2] = v[p + 3] = 0;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < LM; ++p) v[p] = p < L ? g[(long)p * stride] : (T)0;
+    }
+#pragma unroll
+    for (int p = 0; p < LM; ++p) {
+        if (p < L) v[p] *= vin ? fin * vin[vo + p * vd] : fin;
+    }
+#pragma unroll 1
+    for (int q = 0; q < L; q += 4) {
+        T acc[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int p = 0; p < LM; ++p) {
+            T a4[4];
+            sep_ld4(As + (size_t)p * LM + q, a4);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[r] += a4[r] * v[p];
+        }
+        if (vec) {
+            T o4[4];
+            for (int r = 0; r < 4; ++r) o4[r] = acc[r] * (vout ? fout * vout[vo + (q + r) * vd] : fout);
+            sep_st4(g + q, o4);
+        } else {
+            for (int r = 0; r < 4 && q + r < L; ++r)
+                g[(long)(q + r) * stride] = acc[r] * (vout ? fout * vout[vo + (q + r) * vd] : fout);
+        }
+    }
+}
+
+// The same line for a circulant A of compile-time side L, given by its first row c[d] = A[0][d]
+// (A[x][p] = c[(p - x) mod L]; A is symmetric, so the column passes use the same formula):
+//   out[x] = sum_d c[d] v[(x + d) mod L].
+// The loop runs over d outside and x inside, with the line and its L outputs in registers, so a
+// line costs L shared-memory reads (one broadcast scalar per d) against L^2 multiply-adds.
+template <typename T, int L>
+SEP_HD inline void sep_line_circ(const SepLineArgs& a, long line, const T* c) {
+    const long nl = sep_line_count(a);
+    const int z = (int)(line / nl);
+    const long l = line - (long)z * nl;
+    T* G = (T*)a.G + (size_t)z * a.sG;
+    const T* ri = a.rs_in ? (const T*)a.rs_in + (size_t)z * a.sv : nullptr;
+    const T* ci = a.cs_in ? (const T*)a.cs_in + (size_t)z * a.sv : nullptr;
+    const T* ro = a.rs_out ? (const T*)a.rs_out + (size_t)z * a.sv : nullptr;
+    const T* co = a.cs_out ? (const T*)a.cs_out + (size_t)z * a.sv : nullptr;
+    long base, stride;
+    int i0, di, k0, dk;
+    if (a.axis < 2) {
+        const int j = (int)(l % a.C), o = (int)(l / a.C);
+        i0 = a.axis == 0 ? L * o : o;
+        di = a.axis == 0 ? 1 : L;
+        k0 = j; dk = 0;
+        base = (long)i0 * a.ld + j;
+        stride = (long)di * a.ld;
+    } else {
+        const int o = (int)(l % L), r = (int)(l / L);
+        k0 = a.axis == 2 ? L * o : o;
+        dk = a.axis == 2 ? 1 : L;
+        i0 = r; di = 0;
+        base = (long)r * a.ld + k0;
+        stride = dk;
+    }
+    T* g = G + base;
+    T fin = 1, fout = 1;
+    if (a.axis < 2) {
+        if (ci) fin = ci[k0];
+        if (co) fout = co[k0];
+    } else {
+        if (ri) fin = ri[i0];
+        if (ro) fout = ro[i0];
+    }
+    const T* vin = a.axis < 2 ? ri : ci;
+    const T* vout = a.axis < 2 ? ro : co;
+    const int vo = a.axis < 2 ? i0 : k0, vd = a.axis < 2 ? di : dk;
+    T v[L];
+    const bool vec = stride == 1 && L % 4 == 0 && a.ld % 4 == 0 && a.sG % 4 == 0 && ((size_t)a.G) % 16 == 0;
+    if (vec) {
+#pragma unroll
+        for (int p = 0; p < L; p += 4) sep_ld4(g + p, v + p);
+    } else {
+#pragma unroll
+        for (int p = 0; p < L; ++p) v[p] = g[(long)p * stride];
+    }
+#pragma unroll
+    for (int p = 0; p < L; ++p) v[p] *= vin ? fin * vin[vo + p * vd] : fin;
+    T o[L];
+#pragma unroll
+    for (int x = 0; x < L; ++x) o[x] = 0;
+#pragma unroll
+    for (int d = 0; d < L; ++d) {
+        const T cd = c[d];
+#pragma unroll
+        for (int x = 0; x < L; ++x) o[x] += cd * v[(x + d) % L];
+    }
+#pragma unroll
+    for (int x = 0; x < L; ++x) o[x] *= vout ? fout * vout[vo + x * vd] : fout;
+    if (vec) {
+#pragma unroll
+        for (int x = 0; x < L; x += 4) sep_st4(g + x, o + x);
+    } else {
+#pragma unroll
+        for (int x = 0; x < L; ++x) g[(long)x * stride] = o[x];
+    }
+}
+
+// The lattice sides with a circulant line kernel (FP64 up to 24: the line and its outputs, two
+// arrays of L doubles per thread, stay in registers); other sides take the LM kernel.
+template <typename T>
+SEP_HD inline bool sep_circ_side(int L) {
+    switch (L) {
+        case 4: case 6: case 8: case 12: case 16: case 20: case 24: return true;
+        case 32: case 40: return sizeof(T) == 4;
+        default: return false;
+    }
+}
+
+// A (FP64, L x L) into the LM x LM shared-memory copy in T, zero-padded; thread tid of nt.
+template <typename T>
+SEP_HD inline void sep_line_load_A(const double* A, int L, int LM, T* As, int tid, int nt) {
+    for (int e = tid; e < LM * LM; e += nt) {
+        const int p = e / LM, q = e - p * LM;
+        As[e] = (p < L && q < L) ? (T)A[p * L + q] : (T)0;
+    }
+}
+
+// The two line passes of one side of a SepArgs (side 0: axes 0 then 1 on N x C matrices; side 1:
+// axes 2 then 3 on C x N ones), with the input scaling on the first and the output scaling on
+// the second.
+inline void sep_line_passes(const SepArgs& s, SepLineArgs* p1, SepLineArgs* p2) {
+    SepLineArgs a;
+    a.G = s.G; a.ld = s.ld; a.sG = s.sG; a.L = s.L; a.batch = s.batch; a.sv = s.sv; a.circ = s.circ;
+    const int ext = s.C > 0 ? s.C : s.N;
+    a.R = s.side == 0 ? s.N : ext;
+    a.C = s.side == 0 ? ext : s.N;
+    *p1 = a;
+    *p2 = a;
+    p1->axis = s.side == 0 ? 0 : 2;
+    p2->axis = s.side == 0 ? 1 : 3;
+    p1->rs_in = s.rs_in; p1->cs_in = s.cs_in;
+    p2->rs_out = s.rs_out; p2->cs_out = s.cs_out;
+}
+
 // The two passes of the wrap for a batch of matrices G (N = L^2, leading dimension ld, batch
 // stride sG), with Ex = exp(-dtau K_1d), Exi = exp(+dtau K_1d) and the field scales
 // d = exp(c x), dinv = exp(-c x) ([batch][N], stride sv):
@@ -245,6 +484,7 @@ inline void sep_wrap_passes(int direction, void* G, long ld, long sG, int L, int
                             const double* Exi, const void* d, const void* dinv, long sv, SepArgs* a1, SepArgs* a2) {
     SepArgs a;
     a.G = G; a.ld = ld; a.sG = sG; a.L = L; a.N = L * L; a.batch = batch; a.sv = sv;
+    a.circ = 1;  // Ex and Exi of the periodic chain
     *a1 = a;
     *a2 = a;
     if (direction > 0) {

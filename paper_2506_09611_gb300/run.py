@@ -44,16 +44,19 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--soc", action="store_true", help="the spin-orbit-coupled model at half filling")
     ap.add_argument("--lam", type=float, default=0.5)
-    ap.add_argument("--wrap", default="dense", choices=["dense", "separable"],
-                    help="wrap products: dense N x N, or two L-point passes with exp(-dtau K) = Ex (x) Ex")
+    ap.add_argument("--wrap", default=None, choices=["dense", "separable"],
+                    help="wrap products: dense N x N, or L-point passes with exp(-dtau K) = Ex (x) Ex (the "
+                         "default for the Hubbard model)")
     ap.add_argument("--wrap-tile", type=int, default=0,
-                    help="tile width of the separable wrap (0: the default; --tune chooses it with --wrap separable)")
+                    help="tile width of the separable wrap (0: the default line passes; --tune chooses it with --wrap separable)")
     ap.add_argument("--tune", metavar="CACHE", help="choose k and nb by timed trials (cached in this JSON file)")
     ap.add_argument("--tune-slices", type=int, default=10, help="slices of each trial walk (out and back)")
     ap.add_argument("--floor", type=float, default=tune.ACCEPTANCE_FLOOR, help="block force-bias acceptance floor")
     a = ap.parse_args(argv)
-    if a.soc and a.wrap != "dense":
-        ap.error("--wrap covers the Hubbard model only (the spin-orbit propagator does not factor)")
+    if a.soc and a.wrap == "separable":
+        ap.error("--wrap separable covers the Hubbard model only (the spin-orbit propagator does not factor)")
+    if a.wrap is None:
+        a.wrap = "dense" if a.soc else "separable"
     if a.soc:
         return main_soc(a)
 
@@ -68,10 +71,9 @@ def main(argv=None):
     ctx = afqmc.Context(a.M, dtau=a.dtau, U=a.U, t=a.t, precision=a.precision, stab_every=a.stab, seed=a.seed,
                         gemm=a.gemm)
     ctx.init_walkers([L], [ns], [ns], np.concatenate([P.ravel(), P.ravel()]), X, stream=stream)
-    if a.wrap != "dense":
-        ctx.set_wrap(a.wrap)
-        if a.wrap_tile:
-            ctx.set_wrap_tile(a.wrap_tile)
+    ctx.set_wrap(a.wrap)
+    if a.wrap == "separable" and a.wrap_tile:
+        ctx.set_wrap_tile(a.wrap_tile)
     tuned = None
     if a.tune:
         key = tune.workload_key(device=torch.cuda.get_device_name(), L=L, n_up=ns, n_dn=ns, U=a.U, t=a.t,
@@ -79,7 +81,7 @@ def main(argv=None):
         r = tune.autotune_walker(ctx, torch, stream, lambda st: afqmc.afqmc_recompute_G(ctx.h, None, st),
                                  min(a.tune_slices, a.M), a.stab, floor=a.floor, cache=tune.TuneCache(a.tune),
                                  key=key, k_max=128 if a.precision == "fp32" else 64,
-                                 tile_candidates=(4, 8, 16) if a.wrap == "separable" else None)
+                                 tile_candidates=(0, 4, 8, 16) if a.wrap == "separable" else None)
         a.k, a.nb = r["k"].value, r["nb"].value
         tuned = {"k": r["k"].value, "k_ms": r["k"].ms, "nb": r["nb"].value, "nb_ms": r["nb"].ms,
                  "nb_acceptance": r["nb"].acceptance, "cached": not r["k_trials"] and not r["nb_trials"]}
@@ -99,7 +101,7 @@ def main(argv=None):
     e, s = ctx.measure_energy(stream=stream)
     ctx.close()
     out = {"L": L, "slices": a.slices, "mode": a.mode, "k": a.k, "nb": a.nb, "precision": a.precision,
-           "gemm": a.gemm, "wrap": a.wrap, "seconds": dt, "field_updates_per_s": N * a.slices / dt,
+           "gemm": a.gemm, "wrap": a.wrap, "wrap_tile": a.wrap_tile, "seconds": dt, "field_updates_per_s": N * a.slices / dt,
            "energy": float(e[0])}
     if tuned is not None:
         out["tuned"] = tuned

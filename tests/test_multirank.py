@@ -154,8 +154,13 @@ def test_kernel_rooflines_use_the_documented_work_per_launch():
     assert "elim" not in {r["kernel"] for r in out} and len(out) == 3
     assert [r["ms_per_step"] for r in out] == sorted((r["ms_per_step"] for r in out), reverse=True)
     assert out[0] is flush  # 160 ms per step: the dominant entry
-    # the separable wrap: one side of the wrap per launch, two L-point passes over both spins' G
+    # the separable wrap: one interval is one wrap, four L-point passes over both spins' G, each
+    # pass a kernel launch that reads and writes G (line passes) or two tile launches
     sep = {r["kernel"].split(" ")[0]: r for r in bench.kernel_rooflines(prof, "tc3", pk, "measured", steps=1)}
-    s = sep["sep_kernel"]
-    assert s["work_per_launch"] == 2 * 2 * 2 * 40 * 1600 ** 2 and s["bound"] == "alu"
+    s = sep["sep_line_kernel"]
+    assert s["work_per_launch"] == 2 * 2 * 4 * 40 * 1600 ** 2 and s["bound"] == "alu"
+    assert s["bytes_per_launch"] == 4 * 2 * 2 * 1600 ** 2 * 4 and s["launches_per_interval"] == 4
     assert s["peak"] == pytest.approx(152 * 128 * 2 * 2070e6 / 1e12)
+    t = {r["kernel"].split(" ")[0]: r for r in
+         bench.kernel_rooflines(prof, "tc3", pk, "measured", steps=1, wrap_tile=8)}["sep_kernel"]
+    assert t["work_per_launch"] == s["work_per_launch"] and t["bytes_per_launch"] == s["bytes_per_launch"] / 2

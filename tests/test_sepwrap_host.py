@@ -23,7 +23,7 @@ def lib(tmp_path_factory):
                            os.path.join(ROOT, "tests", "sepwrap_host.cpp")])
     h = ctypes.CDLL(str(out))
     vp, i, l = ctypes.c_void_p, ctypes.c_int, ctypes.c_long
-    h.sep_host_pass.argtypes = [i, i, i, i, i, i, vp, l, l, vp, vp, vp, vp, vp, l]
+    h.sep_host_pass.argtypes = [i, i, i, i, i, i, vp, l, l, vp, vp, vp, vp, vp, l, i]
     h.sep_host_wrap.argtypes = [i, i, i, i, i, vp, l, l, vp, vp, vp, vp, l]
     yield h
     assert h.sep_host_misaligned() == 0  # no vector access that would fault on the device
@@ -57,19 +57,28 @@ def _padded(G, pad, dt):
 @pytest.mark.parametrize("fp64", [1, 0])
 @pytest.mark.parametrize("side", [0, 1])
 @pytest.mark.parametrize("L,w", [(2, 16), (3, 4), (4, 16), (5, 16), (5, 4), (6, 5), (8, 16), (8, 8), (12, 16),
-                                 (12, 4)])
+                                 (12, 4), (2, 0), (3, 0), (4, 0), (5, 0), (6, 0), (8, 0), (9, 0), (12, 0),
+                                 (13, 0), (16, 0), (20, 0), (24, 0), (32, 0), (40, 0)])
 @pytest.mark.parametrize("scaled", [False, True])
-def test_pass_is_the_kronecker_product(lib, fp64, side, L, w, scaled):
+@pytest.mark.parametrize("circ", [1, 0])
+def test_pass_is_the_kronecker_product(lib, fp64, side, L, w, scaled, circ):
+    """circ = 1: A is the periodic chain's factor, passed as circulant (the line passes keep its
+    first row); circ = 0: a symmetric A that is not circulant, through the general passes."""
     rng = np.random.default_rng(100 * L + 10 * w + side)
     N, batch = L * L, 2
     pad = 4 if L % 2 == 0 else 3  # ld % 4 == 0 takes the vector path of the row tiles
     dt = np.float64 if fp64 else np.float32
-    A = chain_factor(L, 1.0, 0.05 * (1 + L % 3))
+    if circ:
+        A = chain_factor(L, 1.0, 0.05 * (1 + L % 3))
+    else:
+        S = rng.standard_normal((L, L))
+        A = np.eye(L) + 0.1 * (S + S.T)
     G = rng.standard_normal((batch, N, N))
     sc = [rng.uniform(0.5, 2.0, (batch, N)) if scaled else None for _ in range(4)]  # rs_in, cs_in, rs_out, cs_out
     buf = _padded(G, pad, dt)
     scd = [None if s is None else np.ascontiguousarray(s, dt) for s in sc]
-    lib.sep_host_pass(fp64, side, L, 0, w, batch, _p(buf), N + pad, N * (N + pad), _p(A), *[_p(s) for s in scd], N)
+    lib.sep_host_pass(fp64, side, L, 0, w, batch, _p(buf), N + pad, N * (N + pad), _p(A), *[_p(s) for s in scd], N,
+                      circ)
     E = np.kron(A, A)  # site i = x + L y
     for z in range(batch):
         one = np.ones(N)
@@ -84,7 +93,8 @@ def test_pass_is_the_kronecker_product(lib, fp64, side, L, w, scaled):
 
 @pytest.mark.parametrize("fp64", [1, 0])
 @pytest.mark.parametrize("direction", [+1, -1])
-@pytest.mark.parametrize("L,w", [(3, 16), (4, 16), (6, 16), (6, 4), (8, 16), (8, 8)])
+@pytest.mark.parametrize("L,w", [(3, 16), (4, 16), (6, 16), (6, 4), (8, 16), (8, 8), (3, 0), (4, 0), (5, 0),
+                                 (6, 0), (8, 0), (12, 0), (16, 0), (20, 0)])
 def test_wrap_matches_the_oracle(lib, fp64, direction, L, w):
     rng = np.random.default_rng(7 * L + w + (direction > 0))
     N, t, U, dtau = L * L, 1.0, 4.0, 0.05
@@ -107,7 +117,8 @@ def test_wrap_matches_the_oracle(lib, fp64, direction, L, w):
 
 
 @pytest.mark.parametrize("fp64", [1, 0])
-@pytest.mark.parametrize("L,C,w", [(4, 7, 16), (6, 13, 16), (8, 28, 16), (8, 3, 4), (5, 11, 5)])
+@pytest.mark.parametrize("L,C,w", [(4, 7, 16), (6, 13, 16), (8, 28, 16), (8, 3, 4), (5, 11, 5), (4, 7, 0),
+                                   (6, 13, 0), (8, 28, 0), (8, 3, 0), (5, 11, 0), (12, 9, 0)])
 def test_factor_passes_move_the_t_form_factors(lib, fp64, L, C, w):
     """The T form's factor wrap (forward slice l): U_R <- D E U_R (N x N_sigma, side 0 with the
     rows scaled by d after) and U_L <- U_L E^{-1} D^{-1} (N_sigma x N, side 1 with the columns
@@ -128,8 +139,8 @@ def test_factor_passes_move_the_t_form_factors(lib, fp64, L, C, w):
     bL = np.full((1, C, ldl), np.nan, dt)
     bL[0, :, :N] = UL
     dd, di = d.astype(dt), dinv.astype(dt)
-    lib.sep_host_pass(fp64, 0, L, C, w, 1, _p(bR), ldr, N * ldr, _p(Ex), None, None, _p(dd), None, N)
-    lib.sep_host_pass(fp64, 1, L, C, w, 1, _p(bL), ldl, C * ldl, _p(Exi), None, None, None, _p(di), N)
+    lib.sep_host_pass(fp64, 0, L, C, w, 1, _p(bR), ldr, N * ldr, _p(Ex), None, None, _p(dd), None, N, 1)
+    lib.sep_host_pass(fp64, 1, L, C, w, 1, _p(bL), ldl, C * ldl, _p(Exi), None, None, None, _p(di), N, 1)
     refR = d[:, None] * (E @ UR)
     refL = (UL @ Einv) * dinv[None, :]
     tol = 1e-12 if fp64 else 1e-5

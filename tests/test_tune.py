@@ -315,7 +315,7 @@ def test_run_cli_tunes_then_walks_with_the_choice(tmp_path, monkeypatch, capsys)
     monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "fake")
     cache = str(tmp_path / "tune.json")
     argv = ["--L", "4", "--M", "10", "--stab", "5", "--slices", "4", "--mode", "blockfb", "--tune", cache,
-            "--tune-slices", "5"]
+            "--tune-slices", "5", "--wrap", "dense"]
     run.main(argv)
     out = json.loads(capsys.readouterr().out)
     assert (out["k"], out["nb"]) == (16, 8) and out["tuned"]["cached"] is False
@@ -324,11 +324,11 @@ def test_run_cli_tunes_then_walks_with_the_choice(tmp_path, monkeypatch, capsys)
     out2 = json.loads(capsys.readouterr().out)
     assert (out2["k"], out2["nb"]) == (16, 8) and out2["tuned"]["cached"] is True
     assert made[-1].modes == [("blockfb", 16, 8)] * 4  # no trial walks with a cached choice
-    run.main(argv + ["--wrap", "separable"])
+    run.main(argv[:-1] + ["separable"])
     out3 = json.loads(capsys.readouterr().out)
     assert out3["wrap"] == "separable" and made[-1].wrap == "separable"
     # the separable wrap's walk is keyed apart from the dense one and tunes its tile width too
-    assert out3["tuned"]["cached"] is False and out3["tuned"]["wrap_tile"] in (4, 8, 16)
+    assert out3["tuned"]["cached"] is False and out3["tuned"]["wrap_tile"] in (0, 4, 8, 16)
     assert made[-1].tile == out3["tuned"]["wrap_tile"]
     with pytest.raises(SystemExit):
         run.main(["--soc", "--wrap", "separable"])
