@@ -77,8 +77,11 @@ class SocParams(ctypes.Structure):
     _fields_ = [
         ("L", ctypes.c_int), ("N", ctypes.c_int),
         ("t", ctypes.c_double), ("lam", ctypes.c_double), ("U", ctypes.c_double), ("dtau", ctypes.c_double),
-        ("gamma", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("hs", ctypes.c_int),
     ]
+
+
+SOC_HS = {"sy": 0, "sz": 1}
 
 
 def build(force: bool = False) -> str:
@@ -471,12 +474,15 @@ def _vp(a):
 class SocModel:
     """Spin-orbit-coupled Hubbard model on the 2N x 2N complex orbital basis (Appendix A,
     Eq. 2DSocHubbard): orbitals i (spin up) and N + i (spin down).  E = exp(-dtau H0),
-    Einv = exp(+dtau H0) from the closed-form 2 x 2 exponential per momentum."""
+    Einv = exp(+dtau H0) from the closed-form 2 x 2 exponential per momentum.  hs: the
+    decoupling channel, "sy" (spin-y, Eq. HSspinSyDep) or "sz" (the imaginary spin-z channel of
+    Eqs. HSspinDecomp, BIOpForHubbard; with lam = 0 the attractive Hubbard model of Sec. II.B)."""
 
-    def __init__(self, L, t, lam, U, dtau, M):
-        self.p = SocParams(L=L, N=L * L, t=t, lam=lam, U=U, dtau=dtau)
+    def __init__(self, L, t, lam, U, dtau, M, hs="sy"):
+        self.p = SocParams(L=L, N=L * L, t=t, lam=lam, U=U, dtau=dtau, hs=SOC_HS[hs])
+        self.hs = hs
         if _load().soc_setup(ctypes.byref(self.p)) != 0:
-            raise ValueError("the spin-y decoupling needs U <= 0")
+            raise ValueError("the decoupling needs U <= 0")
         self.N = L * L
         self.M = M
         self.H0 = np.zeros((2 * self.N, 2 * self.N), np.complex128)
@@ -513,7 +519,8 @@ class SocModel:
         [L_k, eps_k]] in (up, down), eps_k = -2t (cos kx + cos ky), L_k = 2 lam (sin ky - i sin kx).
         E X = F^{-1} (exp(-dtau h_k) (F X)_k) for every column of X (numpy's FFT over the site index
         of each spin block, exp by numpy's batched eigh); X E^{-1} = (E^{-1} X^+)^+ since E is
-        Hermitian.  D(x) rotates each pair (i, N + i) by A(gamma x_i)."""
+        Hermitian.  D(x) mixes each pair (i, N + i) by A(gamma x_i): a rotation (spin-y) or the phases
+        diag(e^{i gamma x_i}, e^{-i gamma x_i}) (spin-z)."""
         L, N = self.p.L, self.N
         k = 2 * np.pi * np.arange(L) / L
         kx, ky = k[None, :], k[:, None]  # (ky, kx) grid, site index x + L y
@@ -537,12 +544,21 @@ class SocModel:
         th = self.p.gamma * np.asarray(xl, dtype=np.float64)
         c, s = np.cos(th), np.sin(th)
 
-        def rot_rows(X, sgn):  # D(sgn x) X
-            up, dn = X[:N].copy(), X[N:].copy()
-            return np.concatenate([c[:, None] * up + sgn * s[:, None] * dn, -sgn * s[:, None] * up + c[:, None] * dn])
+        if self.hs == "sz":
+            def rot_rows(X, sgn):  # D(sgn x) X
+                ph = np.exp(1j * sgn * th)[:, None]
+                return np.concatenate([ph * X[:N], np.conj(ph) * X[N:]])
 
-        def rot_cols(X, sgn):  # X D(sgn x)
-            return rot_rows(X.T, -sgn).T  # (X D)^T = D^T X^T and A(t)^T = A(-t)
+            def rot_cols(X, sgn):  # X D(sgn x), D diagonal
+                return rot_rows(X.T, sgn).T
+        else:
+            def rot_rows(X, sgn):  # D(sgn x) X
+                up, dn = X[:N].copy(), X[N:].copy()
+                return np.concatenate([c[:, None] * up + sgn * s[:, None] * dn,
+                                       -sgn * s[:, None] * up + c[:, None] * dn])
+
+            def rot_cols(X, sgn):  # X D(sgn x)
+                return rot_rows(X.T, -sgn).T  # (X D)^T = D^T X^T and A(t)^T = A(-t)
 
         G = _c128(G)
         tau = self.p.dtau

@@ -12,9 +12,15 @@
  *        eps_k = -2t(cos kx + cos ky), L_k = 2 lam (sin ky - i sin kx) the coefficient of
  *        c_{k,down}^+ c_{k,up}.
  *   G_ab = <c_a c_b^+>, A = 1 - G, A_ab = <c_b^+ c_a>.
- *   HS in the spin-y channel (U < 0): gamma = arccos(exp(dtau U / 2)); the field x_i = +-1
- *   acts on the pair (i, N + i) with the real rotation A(x) = [[cos gx, sin gx], [-sin gx, cos gx]]
- *   (uniform prior 1/2).  B_l = D_l E with D_l = (+)_i A(x_{l,i}) and E = exp(-dtau H0).
+ *   HS (U < 0, uniform prior 1/2, gamma = arccos(exp(dtau U / 2))): the field x_i = +-1 acts on
+ *   the pair (i, N + i) with the 2 x 2 matrix A(gamma x_i), A(t) = exp(t g) for the generator g
+ *   of the decoupling channel:
+ *     spin-y (hs = 0, Eq. HSspinSyDep):  g = [[0, 1], [-1, 0]],  A(t) = [[cos t, sin t], [-sin t, cos t]];
+ *     spin-z (hs = 1, Eqs. HSspinDecomp, BIOpForHubbard, the imaginary s^z channel of the Hubbard
+ *             model): g = diag(i, -i),  A(t) = diag(e^{it}, e^{-it}).
+ *   Both satisfy A(t) A(t') = A(t + t').  With lam = 0 and hs = 1 this is the paper's attractive
+ *   Hubbard model: G stays block diagonal in spin with G_dn = conj(G_up).
+ *   B_l = D_l E with D_l = (+)_i A(gamma x_{l,i}) and E = exp(-dtau H0).
  *   Matrices are row-major double complex.
  *
  * G form of the updates (Eq. GrFMatNew: G = 1 - U_R T U_L):
@@ -33,14 +39,15 @@ typedef double complex cplx;
 typedef struct {
     int L, N;           /* N sites, 2N orbitals */
     double t, lam, U, dtau;
-    double gamma;       /* HS coupling of the spin-y channel */
+    double gamma;       /* HS coupling */
+    int hs;             /* 0: spin-y channel, 1: spin-z channel (imaginary coupling) */
 } soc_params;
 
-/* gamma = arccos(exp(dtau U / 2)) (Eq. HSspinSyDep); needs U <= 0 (U = 0 gives gamma = 0, the
- * free system).  Returns 0 or -1. */
+/* gamma = arccos(exp(dtau U / 2)) (Eqs. HSspinSyDep, HSspinDecomp); needs U <= 0 (U = 0 gives
+ * gamma = 0, the free system) and hs in {0, 1}.  Returns 0 or -1. */
 int soc_setup(soc_params* p) {
     p->N = p->L * p->L;
-    if (!(p->U <= 0.0)) return -1;
+    if (!(p->U <= 0.0) || (p->hs != 0 && p->hs != 1)) return -1;
     p->gamma = acos(exp(p->dtau * p->U / 2.0));
     return 0;
 }
@@ -112,8 +119,15 @@ void soc_expH(const soc_params* p, double tau, cplx* E) {
     free(ek);
 }
 
-/* The rotation of the decoupling at angle theta = gamma x on the pair (i, N + i). */
-static void rot(double theta, double r[2][2]) {
+/* The decoupling's 2 x 2 matrix A(theta) on the pair (i, N + i), theta = gamma x. */
+static void site_mat(const soc_params* p, double theta, cplx r[2][2]) {
+    if (p->hs == 1) {
+        r[0][0] = cos(theta) + I * sin(theta);
+        r[0][1] = 0;
+        r[1][0] = 0;
+        r[1][1] = cos(theta) - I * sin(theta);
+        return;
+    }
     r[0][0] = cos(theta);
     r[0][1] = sin(theta);
     r[1][0] = -sin(theta);
@@ -209,13 +223,13 @@ static cplx zorth(cplx* a, int m, int n, size_t rs, size_t cs, double* logabs) {
     return ph;  /* the factor R of modified Gram-Schmidt has a positive real diagonal */
 }
 
-/* v (2N x ncol, row-major) <- D(x) v: rows i and N + i rotated by A(x_i). */
+/* v (2N x ncol, row-major) <- D(x) v: rows i and N + i mixed by A(sgn gamma x_i). */
 static void rot_rows(const soc_params* p, const int8_t* xl, double sgn, cplx* v, int ncol) {
     const int N = p->N;
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < N; i++) {
-        double r[2][2];
-        rot(sgn * p->gamma * xl[i], r);
+        cplx r[2][2];
+        site_mat(p, sgn * p->gamma * xl[i], r);
         for (int c = 0; c < ncol; c++) {
             const cplx a = v[(size_t)i * ncol + c], b = v[(size_t)(N + i) * ncol + c];
             v[(size_t)i * ncol + c] = r[0][0] * a + r[0][1] * b;
@@ -230,8 +244,8 @@ static void rot_cols(const soc_params* p, const int8_t* xl, double sgn, cplx* v,
 #pragma omp parallel for schedule(static)
     for (int r0 = 0; r0 < nrow; r0++)
         for (int i = 0; i < N; i++) {
-            double r[2][2];
-            rot(sgn * p->gamma * xl[i], r);
+            cplx r[2][2];
+            site_mat(p, sgn * p->gamma * xl[i], r);
             const cplx a = v[(size_t)r0 * N2 + i], b = v[(size_t)r0 * N2 + N + i];
             v[(size_t)r0 * N2 + i] = a * r[0][0] + b * r[1][0];
             v[(size_t)r0 * N2 + N + i] = a * r[0][1] + b * r[1][1];
@@ -310,9 +324,9 @@ static cplx det2(const cplx m[2][2]) { return m[0][0] * m[1][1] - m[0][1] * m[1]
 /* The flip at site i: delta = A(-2x) - 1, ratio R = det(1 + delta A_SS) and W = delta (1 + A_SS delta)^{-1},
  * from the current 2 x 2 block g of G on (i, N + i). */
 static cplx flip_ratio(const soc_params* p, int x, const cplx g[2][2], cplx W[2][2]) {
-    double r[2][2];
-    rot(-2.0 * p->gamma * x, r);
-    const double dl[2][2] = {{r[0][0] - 1.0, r[0][1]}, {r[1][0], r[1][1] - 1.0}};
+    cplx r[2][2];
+    site_mat(p, -2.0 * p->gamma * x, r);
+    const cplx dl[2][2] = {{r[0][0] - 1.0, r[0][1]}, {r[1][0], r[1][1] - 1.0}};
     cplx Ass[2][2];
     for (int a = 0; a < 2; a++)
         for (int b = 0; b < 2; b++) Ass[a][b] = (a == b ? 1.0 : 0.0) - g[a][b];
@@ -445,8 +459,8 @@ static void delta_block(const soc_params* p, const int8_t* x, const int8_t* xnew
     const int n2 = 2 * n;
     for (int e = 0; e < n2 * n2; e++) D[e] = 0;
     for (int a = 0; a < n; a++) {
-        double r[2][2];
-        rot(p->gamma * ((double)xnew[a] - (double)x[a]), r);
+        cplx r[2][2];
+        site_mat(p, p->gamma * ((double)xnew[a] - (double)x[a]), r);
         const int o[2] = {a, n + a};
         for (int s = 0; s < 2; s++)
             for (int t = 0; t < 2; t++) D[o[s] * n2 + o[t]] = r[s][t] - (s == t ? 1.0 : 0.0);
@@ -456,8 +470,10 @@ static void delta_block(const soc_params* p, const int8_t* x, const int8_t* xnew
 /* Stripped force bias of the block of sites [s0, s0 + n) (Appendix A with Eq. BlkFrcBsTnew1 in G form):
  * with the block's current fields taken out of R, Delta_b = A(-x) - 1 on the block orbitals, the
  * stripped one-body matrix on the block is  Abar = (1 + Delta_b)(1 + A_bb Delta_b)^{-1} A_bb  (A = 1 - G),
- * and the spin-flip expectation entering the bias is
- *   obar_i = <c+_{i,up} c_{i,dn}> - <c+_{i,dn} c_{i,up}> = Abar[dn i, up i] - Abar[up i, dn i].
+ * and obar_i is the stripped expectation of the field's generator g on site i (the field enters
+ * as exp(gamma x g)), which sets the bias:
+ *   spin-y: obar_i = <c+_{i,up} c_{i,dn}> - <c+_{i,dn} c_{i,up}> = Abar[dn i, up i] - Abar[up i, dn i];
+ *   spin-z: obar_i = i (<n_{i,up}> - <n_{i,dn}>) = i (Abar[up i, up i] - Abar[dn i, dn i]).
  * obar holds n complex values. */
 void soc_block_force_bias(const soc_params* p, const cplx* G, const int8_t* xl, int s0, int n, cplx* obar) {
     const int N = p->N, N2 = 2 * N, n2 = 2 * n;
@@ -485,16 +501,19 @@ void soc_block_force_bias(const soc_params* p, const cplx* G, const int8_t* xl, 
     for (int a = 0; a < n; a++) {
         /* rows dn a and up a of (1 + Delta) Abb */
         cplx dn_up = Abb[(n + a) * n2 + a], up_dn = Abb[a * n2 + n + a];
+        cplx up_up = Abb[a * n2 + a], dn_dn = Abb[(n + a) * n2 + n + a];
         for (int q = 0; q < n2; q++) {
             dn_up += D[(n + a) * n2 + q] * Abb[q * n2 + a];
             up_dn += D[a * n2 + q] * Abb[q * n2 + n + a];
+            up_up += D[a * n2 + q] * Abb[q * n2 + a];
+            dn_dn += D[(n + a) * n2 + q] * Abb[q * n2 + n + a];
         }
-        obar[a] = dn_up - up_dn;
+        obar[a] = p->hs == 1 ? I * (up_up - dn_dn) : dn_up - up_dn;
     }
     free(sites); free(F); free(zero); free(D); free(Abb); free(Mx); free(piv);
 }
 
-/* Block force-bias update of one slice (Sec. III.B with the spin-flip bias of Appendix A), blocks of
+/* Block force-bias update of one slice (Sec. III.B with the bias of the decoupling channel), blocks of
  * nb consecutive sites (the last one partial).  Per block: h_i = gamma Re(obar_i); proposal
  * lambda(x') = e^{x' h} / (e^{h} + e^{-h}) drawn with u_prop[i] (x' = +1 iff u_prop[i] < lambda(+1));
  * on the flipped set F the Metropolis ratio is

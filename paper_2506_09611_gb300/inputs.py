@@ -114,3 +114,16 @@ def soc_trial_state(L: int, n_e: int, t: float = 1.0, lam: float = 0.5, seed: in
     H = soc_hamiltonian(L, t, lam) + 1e-6 * soc_trs_perturbation(L * L, seed)
     w, v = np.linalg.eigh(H)
     return np.ascontiguousarray(v[:, :n_e])
+
+
+def sz_trial_state(L: int, n_sigma: int, t: float = 1.0, seed: int = 0) -> np.ndarray:
+    """The spin-balanced trial determinant of the Hubbard model on the 2N spin orbitals (up block
+    first): P = [[P_s, 0], [0, P_s]] with P_s = trial_state(L, L, n_sigma) real, so P_dn = conj(P_up)
+    (the condition of Sec. II.B under which the imaginary spin-z decoupling has no sign problem).
+    2N x 2 n_sigma complex, orthonormal columns."""
+    Ps = trial_state(L, L, n_sigma, t, seed)
+    N = L * L
+    P = np.zeros((2 * N, 2 * n_sigma), np.complex128)
+    P[:N, :n_sigma] = Ps
+    P[N:, n_sigma:] = Ps
+    return P

@@ -95,41 +95,47 @@ def fock_energy(K, U, Ru, Lu, Rd, Ld):
 
 # ---------------- spin-orbit-coupled model (Appendix A) ----------------
 
-def soc_HI(gamma, xl):
-    """Exponent matrix of B_I(x_l) on the 2N orbitals (Eq. BIOpForSy):
-    gamma x_i (c+_{i,up} c_{i,dn} - c+_{i,dn} c_{i,up}) has entries +gamma x_i at (up i, dn i) and
-    -gamma x_i at (dn i, up i)."""
+def soc_HI(gamma, xl, hs="sy"):
+    """Exponent matrix of B_I(x_l) on the 2N orbitals.
+    hs = "sy" (Eq. BIOpForSy): gamma x_i (c+_{i,up} c_{i,dn} - c+_{i,dn} c_{i,up}) has entries
+    +gamma x_i at (up i, dn i) and -gamma x_i at (dn i, up i);
+    hs = "sz" (Eq. BIOpForHubbard): i gamma x_i (n_{i,up} - n_{i,dn}) has +i gamma x_i at
+    (up i, up i) and -i gamma x_i at (dn i, dn i)."""
     N = xl.shape[0]
-    H = np.zeros((2 * N, 2 * N))
+    H = np.zeros((2 * N, 2 * N), np.complex128 if hs == "sz" else np.float64)
     for i in range(N):
-        H[i, N + i] = gamma * xl[i]
-        H[N + i, i] = -gamma * xl[i]
+        if hs == "sz":
+            H[i, i] = 1j * gamma * xl[i]
+            H[N + i, N + i] = -1j * gamma * xl[i]
+        else:
+            H[i, N + i] = gamma * xl[i]
+            H[N + i, i] = -gamma * xl[i]
     return H
 
 
-def soc_B(E, gamma, xl):
-    return scipy.linalg.expm(soc_HI(gamma, xl.astype(np.float64))) @ E
+def soc_B(E, gamma, xl, hs="sy"):
+    return scipy.linalg.expm(soc_HI(gamma, xl.astype(np.float64), hs)) @ E
 
 
-def soc_products(E, gamma, X, P, ell):
+def soc_products(E, gamma, X, P, ell, hs="sy"):
     M = X.shape[0]
     R = P.copy()
     for j in range(1, ell + 1):
-        R = soc_B(E, gamma, X[j - 1]) @ R
+        R = soc_B(E, gamma, X[j - 1], hs) @ R
     L = P.conj().T.copy()
     for j in range(M, ell, -1):
-        L = L @ soc_B(E, gamma, X[j - 1])
+        L = L @ soc_B(E, gamma, X[j - 1], hs)
     return R, L
 
 
-def soc_green(E, gamma, X, P, ell):
-    R, L = soc_products(E, gamma, X, P, ell)
+def soc_green(E, gamma, X, P, ell, hs="sy"):
+    R, L = soc_products(E, gamma, X, P, ell, hs)
     return np.eye(E.shape[0]) - R @ np.linalg.solve(L @ R, L)
 
 
-def soc_overlap(E, gamma, X, P):
+def soc_overlap(E, gamma, X, P, hs="sy"):
     """det(P^+ B_M ... B_1 P): the configuration weight up to the uniform prior."""
-    R, L = soc_products(E, gamma, X, P, 0)
+    R, L = soc_products(E, gamma, X, P, 0, hs)
     return np.linalg.det(L @ R)
 
 
