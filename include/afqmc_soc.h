@@ -8,9 +8,14 @@
  *   L x L periodic lattice, N = L*L.  H0 = sum_k c_k^+ h_k c_k with
  *   h_k = [[eps_k, conj(L_k)], [L_k, eps_k]], eps_k = -2t(cos kx + cos ky),
  *   L_k = 2 lam (sin ky - i sin kx) (the coefficient of c_{k,dn}^+ c_{k,up}).
- *   Interaction U sum_i [n_iu n_id - (n_iu + n_id)/2], U <= 0, decoupled in the spin-y
- *   channel: gamma = arccos(exp(dtau U / 2)); the field x_{l,i} = +-1 rotates the pair of
- *   orbitals (i, N + i) by A(x) = [[cos gx, sin gx], [-sin gx, cos gx]].
+ *   Interaction U sum_i [n_iu n_id - (n_iu + n_id)/2], U <= 0, gamma = arccos(exp(dtau U / 2)),
+ *   decoupled (afqmc_soc_params.hs) in
+ *     the spin-y channel (AFQMC_SOC_HS_SY, Eq. HSspinSyDep): the field x_{l,i} = +-1 rotates the
+ *       pair of orbitals (i, N + i) by A(x) = [[cos gx, sin gx], [-sin gx, cos gx]];
+ *     the imaginary spin-z channel (AFQMC_SOC_HS_SZ, Eqs. HSspinDecomp, BIOpForHubbard): the pair
+ *       takes the phases A(x) = diag(e^{i g x}, e^{-i g x}).  With lam = 0 and a trial state with
+ *       P_dn = conj(P_up) this is the paper's attractive Hubbard model (Sec. II.B), sign-free, with
+ *       G_dn = conj(G_up) and no spin-mixing block.
  *   B_l = D(x_l) exp(-dtau H0), D(x_l) = (+)_i A(x_{l,i}).
  *   G_ab = <c_a c_b^+>, A = 1 - G.  Updates are rank 2 per site: with S = {i, N + i},
  *   delta = A(-x) A(x)^{-1} - 1 (the flip), the ratio is R = det(1_2 + delta A_SS)
@@ -47,7 +52,11 @@ typedef struct {
     double U;           /* Hubbard U <= 0 (the spin-y decoupling) */
     double dtau;        /* imaginary-time step */
     uint64_t seed;      /* Philox4x64-10 key word 0 (word 1 = walker index) */
+    int hs;             /* AFQMC_SOC_HS_SY (0, the default) or AFQMC_SOC_HS_SZ (1) */
 } afqmc_soc_params;
+
+#define AFQMC_SOC_HS_SY 0
+#define AFQMC_SOC_HS_SZ 1
 
 /* Largest window (sites) of the delayed update, and largest block of the block force-bias
  * update, per bulk precision. */
@@ -56,7 +65,8 @@ typedef struct {
 
 /* Create a context and build its constants: exp(-+dtau H0) from the closed-form 2 x 2
  * exponential of h_k, in the bulk precision.  p is copied.  AFQMC_ERR_ARG for sizes out of
- * range, U > 0, or stab_every not dividing M; AFQMC_ERR_NODEV without an sm_103 device. */
+ * range, U > 0, an unknown hs, or stab_every not dividing M; AFQMC_ERR_NODEV without an sm_103
+ * device. */
 int afqmc_soc_create(afqmc_soc_ctx** out, const afqmc_soc_params* p);
 
 /* Free every resource of the context.  NULL is a no-op. */
@@ -76,8 +86,9 @@ int afqmc_soc_init(afqmc_soc_ctx* ctx, const double* P, const int8_t* fields, vo
  *   mode  AFQMC_MODE_LOCAL (rank-2 update of G per accepted site), AFQMC_MODE_DELAYED (windows
  *         of k sites, 1 <= k <= KMAX: decisions on the window's 2k x 2k block, one rank-2m
  *         product per window), AFQMC_MODE_BLOCKFB (blocks of nb sites, 1 <= nb <= KMAX:
- *         stripped spin-flip force bias, joint proposal, one ratio and one rank-2m product per
- *         block; Sec. III.B with the bias of Appendix A).
+ *         stripped force bias of the decoupling channel -- h_i = gamma Re<g_i> with g the field's
+ *         generator, spin-y <c+_up c_dn - c+_dn c_up>, spin-z i <n_up - n_dn> -- joint proposal,
+ *         one ratio and one rank-2m product per block; Sec. III.B).
  *   replay  host, nullable, 2N bytes per walker: local / delayed replay[i] = accept site i;
  *         block FB replay[i] = propose x'_i = +1 (else -1), replay[N + b] = accept block b.
  * Uniforms: Philox4x64-10, key (seed, walker), counter (j + 1, visit, 0, 0), visit = the number

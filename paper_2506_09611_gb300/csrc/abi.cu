@@ -1765,9 +1765,21 @@ int afqmc_set_wrap_tile(afqmc_ctx* ctx, int width) {
     return AFQMC_OK;
 }
 
+// Wait for every stream a phase interval may sit on: the caller's last stream and each group's
+// main, flush and propagation streams (the recompute's deferred re-orthonormalisation runs on
+// the last).
+static cudaError_t sync_profiled_streams(afqmc_ctx* ctx) {
+    cudaError_t e = cudaSuccess;
+    if (ctx->last && (e = cudaStreamSynchronize(ctx->last)) != cudaSuccess) return e;
+    for (auto* w : ctx->w)
+        for (cudaStream_t q : {w->sm, w->sf, w->sp})
+            if (q && (e = cudaStreamSynchronize(q)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
 int afqmc_set_profiling(afqmc_ctx* ctx, int on) {
     if (!ctx) return AFQMC_ERR_ARG;
-    if (ctx->last) cudaStreamSynchronize(ctx->last);
+    CK(sync_profiled_streams(ctx));
     for (auto& pe : ctx->prof.pending) {
         ctx->prof.pool.push_back(pe.a);
         ctx->prof.pool.push_back(pe.b);
@@ -1784,18 +1796,19 @@ int afqmc_set_profiling(afqmc_ctx* ctx, int on) {
 
 int afqmc_get_profile(afqmc_ctx* ctx, double* ms, int64_t* intervals, int64_t* launches) {
     if (!ctx) return AFQMC_ERR_ARG;
-    CK(cudaStreamSynchronize(ctx->last));
-    for (auto* w : ctx->w)
-        if (w->sf) CK(cudaStreamSynchronize(w->sf));
-    for (auto& pe : ctx->prof.pending) {
+    CK(sync_profiled_streams(ctx));
+    // an interval leaves the pending list as its events return to the pool, so an error part way
+    // leaves each event in exactly one of the two lists (both are destroyed with the context)
+    while (!ctx->prof.pending.empty()) {
+        const auto pe = ctx->prof.pending.back();
         float t = 0.0f;
         CK(cudaEventElapsedTime(&t, pe.a, pe.b));
         ctx->prof.ms[pe.phase] += t;
         ctx->prof.intervals[pe.phase] += 1;
+        ctx->prof.pending.pop_back();
         ctx->prof.pool.push_back(pe.a);
         ctx->prof.pool.push_back(pe.b);
     }
-    ctx->prof.pending.clear();
     for (int i = 0; i < AFQMC_NPHASE; ++i) {
         if (ms) ms[i] = ctx->prof.ms[i];
         if (intervals) intervals[i] = ctx->prof.intervals[i];

@@ -1,6 +1,8 @@
 // soc.cu -- the spin-orbit-coupled sweep (Appendix A): the complex Green's function of the 2N
-// orbitals (i spin up, N + i spin down), spin-y auxiliary fields acting as real 2 x 2 rotations
-// on the pairs (i, N + i), rank-2 updates per site.
+// orbitals (i spin up, N + i spin down), auxiliary fields acting as 2 x 2 matrices on the pairs
+// (i, N + i) -- real rotations (the spin-y channel) or the phases diag(e^{i gamma x}, e^{-i gamma x})
+// of the imaginary spin-z channel (Eqs. HSspinDecomp, BIOpForHubbard; with lam = 0 the paper's
+// attractive Hubbard model) -- and rank-2 updates per site.
 //
 // Layout.  A complex matrix with C columns is stored "row-split": row r holds the real parts of
 // its C entries, padded to ldz, then the imaginary parts, padded to ldz (2 ldz elements per row).
@@ -85,20 +87,32 @@ struct c22 {
     cx<T> a[2][2];
 };
 
-// The flip of site field x (-> -x): delta = A(-2 gamma x) - 1 = [[c2m1, -x s2], [x s2, c2m1]];
-// stripping the field (x -> 0): A(-gamma x) - 1 = [[c1m1, -x s1], [x s1, c1m1]].
+// The field's 2 x 2 matrix is A(t) = exp(t g), t = gamma x: the spin-y channel (hs = 0,
+// g = [[0, 1], [-1, 0]]) gives the rotation [[cos t, sin t], [-sin t, cos t]], the spin-z channel
+// (hs = 1, g = diag(i, -i)) the phases diag(e^{it}, e^{-it}).
+// The flip of site field x (-> -x): delta = A(-2 gamma x) - 1; stripping the field (x -> 0):
+// A(-gamma x) - 1.  With (cm1, s) = (cos 2gamma - 1, sin 2gamma) or (cos gamma - 1, sin gamma):
+//   spin-y: [[cm1, -x s], [x s, cm1]];   spin-z: diag(cm1 - i x s, cm1 + i x s).
 struct SocConsts {
     double c2m1, s2;  // cos(2 gamma) - 1, sin(2 gamma)
     double c1m1, s1;  // cos(gamma) - 1, sin(gamma)
     double gamma;
+    int hs;           // AFQMC_SOC_HS_SY or AFQMC_SOC_HS_SZ
 };
 
 template <typename T>
-__device__ __forceinline__ void real_delta(double cm1, double s, int x, T d[2][2]) {
-    d[0][0] = (T)cm1;
-    d[1][1] = (T)cm1;
-    d[0][1] = (T)(-x * s);
-    d[1][0] = (T)(x * s);
+__device__ __forceinline__ void site_delta(int hs, double cm1, double s, int x, cx<T> d[2][2]) {
+    if (hs == AFQMC_SOC_HS_SZ) {
+        d[0][0] = cmk((T)cm1, (T)(-x * s));
+        d[1][1] = cmk((T)cm1, (T)(x * s));
+        d[0][1] = cmk((T)0, (T)0);
+        d[1][0] = cmk((T)0, (T)0);
+        return;
+    }
+    d[0][0] = cmk((T)cm1, (T)0);
+    d[1][1] = cmk((T)cm1, (T)0);
+    d[0][1] = cmk((T)(-x * s), (T)0);
+    d[1][0] = cmk((T)(x * s), (T)0);
 }
 
 // ---------------------------------------------------------------------------
@@ -107,10 +121,11 @@ __device__ __forceinline__ void real_delta(double cm1, double s, int x, T d[2][2
 
 // G <- A_r G A_c on every pair block {i, N+i} x {j, N+j}, both parts: rows by A(rs gamma x_i),
 // columns by right multiplication with A(cs gamma x_j).  Forward wrap: rs = +1, cs = -1
-// (D G D^{-1}); backward: rs = -1, cs = +1.
+// (D G D^{-1}); backward: rs = -1, cs = +1.  Spin-y: a real rotation of each part; spin-z: the
+// entry (s i, s' j) times e^{i gamma (f_s rs x_i + f_s' cs x_j)}, f_up = 1, f_dn = -1.
 template <typename T>
 __global__ void soc_rot_kernel(T* G0, long ldz, int N, long gstride, const int8_t* x0, long xstride, T cg, T sg,
-                               int rs, int cs) {
+                               int rs, int cs, int hs) {
     const int j = blockIdx.x * 32 + threadIdx.x;
     const int i = blockIdx.y * 8 + threadIdx.y;
     if (i >= N || j >= N) return;
@@ -118,6 +133,20 @@ __global__ void soc_rot_kernel(T* G0, long ldz, int N, long gstride, const int8_
     const int8_t* x = x0 + (long)blockIdx.z * xstride;
     const T sr = (T)(rs * x[i]) * sg, sc = (T)(cs * x[j]) * sg;
     const long ld2 = 2 * ldz;
+    if (hs == AFQMC_SOC_HS_SZ) {
+        // row phase e^{i f_s t_r} = cg + i f_s sr, column phase cg + i f_s' sc
+        const cx<T> pr[2] = {cmk(cg, sr), cmk(cg, -sr)}, pc[2] = {cmk(cg, sc), cmk(cg, -sc)};
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const long o = (long)(s * N + i) * ld2 + t * N + j;
+                const cx<T> v = cmul(cmul(cmk(G[o], G[o + ldz]), pr[s]), pc[t]);
+                G[o] = v.r;
+                G[o + ldz] = v.i;
+            }
+        return;
+    }
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         T* g = G + p * ldz;
@@ -263,13 +292,14 @@ __device__ bool gj_inverse_2x2(cx<T>* M, int m2, int ldm, cx<T>* colF, cx<T>* de
 }
 
 // W = Delta_F Minv (2m x 2m complex, leading dimension ldw).  Delta_F is block diagonal: the
-// 2 x 2 block dl[t] of flipped site t (real).
+// 2 x 2 block dl[t] of flipped site t.
 template <typename T>
-__device__ void write_W(const cx<T>* Minv, int m2, int ldm, const T (*dl)[2][2], cx<T>* W, int ldw) {
+__device__ void write_W(const cx<T>* Minv, int m2, int ldm, const cx<T> (*dl)[2][2], cx<T>* W, int ldw) {
     for (int e = threadIdx.x; e < m2 * m2; e += blockDim.x) {
         const int q = e / m2, qq = e - q * m2;
         const int t = q >> 1, p = q & 1;
-        const cx<T> w = cadd(cscale(Minv[(2 * t) * ldm + qq], dl[t][p][0]), cscale(Minv[(2 * t + 1) * ldm + qq], dl[t][p][1]));
+        cx<T> w = cmul(dl[t][p][0], Minv[(2 * t) * ldm + qq]);
+        cfma(w, dl[t][p][1], Minv[(2 * t + 1) * ldm + qq]);
         W[(long)q * ldw + qq] = w;
     }
 }
@@ -277,7 +307,7 @@ __device__ void write_W(const cx<T>* Minv, int m2, int ldm, const T (*dl)[2][2],
 // The flip delta of site field x and the 2 x 2 test of the site block g (all in registers):
 // R = det(1 + delta A), W2 = delta (1 + A delta)^{-1}, A = 1 - g.
 template <typename T>
-__device__ __forceinline__ cx<T> site_test(const cx<T> g[2][2], const T dl[2][2], c22<T>& w2) {
+__device__ __forceinline__ cx<T> site_test(const cx<T> g[2][2], const cx<T> dl[2][2], c22<T>& w2) {
     cx<T> A[2][2], m1[2][2], m2[2][2];
     for (int p = 0; p < 2; ++p)
         for (int q = 0; q < 2; ++q) A[p][q] = cmk((p == q ? (T)1 : (T)0) - g[p][q].r, -g[p][q].i);
@@ -286,8 +316,8 @@ __device__ __forceinline__ cx<T> site_test(const cx<T> g[2][2], const T dl[2][2]
             m1[p][q] = cmk(p == q ? (T)1 : (T)0, (T)0);
             m2[p][q] = m1[p][q];
             for (int r = 0; r < 2; ++r) {
-                m1[p][q] = cadd(m1[p][q], cscale(A[r][q], dl[p][r]));
-                m2[p][q] = cadd(m2[p][q], cscale(A[p][r], dl[r][q]));
+                cfma(m1[p][q], dl[p][r], A[r][q]);
+                cfma(m2[p][q], A[p][r], dl[r][q]);
             }
         }
     const cx<T> R = csub(cmul(m1[0][0], m1[1][1]), cmul(m1[0][1], m1[1][0]));
@@ -296,7 +326,10 @@ __device__ __forceinline__ cx<T> site_test(const cx<T> g[2][2], const T dl[2][2]
     const cx<T> inv[2][2] = {{cmul(m2[1][1], di), cmul(cmk(-m2[0][1].r, -m2[0][1].i), di)},
                              {cmul(cmk(-m2[1][0].r, -m2[1][0].i), di), cmul(m2[0][0], di)}};
     for (int p = 0; p < 2; ++p)
-        for (int q = 0; q < 2; ++q) w2.a[p][q] = cadd(cscale(inv[0][q], dl[p][0]), cscale(inv[1][q], dl[p][1]));
+        for (int q = 0; q < 2; ++q) {
+            w2.a[p][q] = cmul(dl[p][0], inv[0][q]);
+            cfma(w2.a[p][q], dl[p][1], inv[1][q]);
+        }
     return R;
 }
 
@@ -322,7 +355,7 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
     cx<T>* aux = Mw + 4 * a.kmax * a.kmax;      // 8 kmax: column / row snapshots, GJ scratch
     cx<T>* Ys = aux + 8 * a.kmax;               // (2 SOC_PIPE_N)^2: staging of the correction
     cx<T>* Gw = (cx<T>*)a.Gw0 + (long)z * 4 * a.kmax * a.kmax;  // n2 x n2: the block of the current G
-    __shared__ T s_dl[64][2][2];                // flip deltas of the flipped sites
+    __shared__ cx<T> s_dl[64][2][2];            // flip deltas of the flipped sites
     __shared__ int s_site[64];
     __shared__ T s_uT[64];
     __shared__ int s_x[64], s_rep[64];
@@ -420,11 +453,11 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
                 bool acc = false, fin = true;
                 cx<T> R = cmk((T)0, (T)0);
                 c22<T> w2;
-                T dl[2][2];
+                cx<T> dl[2][2];
                 int xi = 0;
                 if (q < n) {
                     xi = s_x[q];
-                    real_delta<T>(a.k.c2m1, a.k.s2, xi, dl);
+                    site_delta<T>(a.k.hs, a.k.c2m1, a.k.s2, xi, dl);
                     cx<T> g[2][2];
                     for (int p = 0; p < 2; ++p)
                         for (int qq = 0; qq < 2; ++qq) g[p][qq] = Mw[(2 * q + p) * n2 + 2 * q + qq];
@@ -519,7 +552,7 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
                 const int lc = 2 * (s_site[t2] - s0) + p;
                 const cx<T> gg = gl(lq, lc);
                 const cx<T> Aq = cmk((lq == lc ? (T)1 : (T)0) - gg.r, -gg.i);
-                v = cadd(v, cscale(Aq, s_dl[t2][p][p2]));
+                cfma(v, Aq, s_dl[t2][p][p2]);
             }
             Mw[e] = v;
         }
@@ -537,14 +570,14 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
         for (int e = tid; e < n2 * n2; e += nt) {
             const int q = e / n2, qq = e - q * n2;
             const int t2 = qq >> 1, p2 = qq & 1;
-            T ds[2][2];
-            real_delta<T>(a.k.c1m1, a.k.s1, s_x[t2], ds);
+            cx<T> ds[2][2];
+            site_delta<T>(a.k.hs, a.k.c1m1, a.k.s1, s_x[t2], ds);
             cx<T> v = cmk((q == qq) ? (T)1 : (T)0, (T)0);
             for (int p = 0; p < 2; ++p) {
                 const int cq = 2 * t2 + p;
                 const cx<T> g = gl(q, cq);
                 const cx<T> Aq = cmk((q == cq ? (T)1 : (T)0) - g.r, -g.i);
-                v = cadd(v, cscale(Aq, ds[p][p2]));
+                cfma(v, Aq, ds[p][p2]);
             }
             Mw[e] = v;
         }
@@ -576,24 +609,32 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
         }
         __syncthreads();
         if (tid == 0) {
-            // obar_t = Abar[dn t, up t] - Abar[up t, dn t], Abar = (1 + Delta_s) Minv A, 1 + Delta_s = A(-gamma x);
-            // the proposal weight of x' is exp(x' h), h = gamma Re(obar) (bulk precision)
+            // obar_t = the stripped expectation of the field's generator, Abar = (1 + Delta_s) Minv A,
+            // 1 + Delta_s = A(-gamma x): spin-y Abar[dn t, up t] - Abar[up t, dn t], spin-z
+            // i (Abar[up t, up t] - Abar[dn t, dn t]); the proposal weight of x' is exp(x' h),
+            // h = gamma Re(obar) (bulk precision)
             T logq = 0;
             int m = 0;
             for (int t = 0; t < n; ++t) {
                 const int i = s0 + t, xi = s_x[t];
-                const T c = (T)(a.k.c1m1 + 1.0), s = (T)(-xi * a.k.s1);  // A(-gamma x) = [[c, s], [-s, c]]
+                const T c = (T)(a.k.c1m1 + 1.0), s = (T)(-xi * a.k.s1);  // spin-y A(-gamma x) = [[c, s], [-s, c]]
                 const cx<T> MA00 = aux[4 * t], MA01 = aux[4 * t + 1], MA10 = aux[4 * t + 2], MA11 = aux[4 * t + 3];
-                const cx<T> dn_up = cadd(cscale(MA00, -s), cscale(MA10, c));
-                const cx<T> up_dn = cadd(cscale(MA01, c), cscale(MA11, s));
-                const T h = (T)a.k.gamma * (dn_up.r - up_dn.r);
+                T h;
+                if (a.k.hs == AFQMC_SOC_HS_SZ) {  // spin-z A(-gamma x) = diag(c + i s, c - i s)
+                    const cx<T> uu = cmul(cmk(c, s), MA00), dd = cmul(cmk(c, -s), MA11);
+                    h = -(T)a.k.gamma * (uu.i - dd.i);
+                } else {
+                    const cx<T> dn_up = cadd(cscale(MA00, -s), cscale(MA10, c));
+                    const cx<T> up_dn = cadd(cscale(MA01, c), cscale(MA11, s));
+                    h = (T)a.k.gamma * (dn_up.r - up_dn.r);
+                }
                 const T lp = (T)1 / ((T)1 + exp((T)-2 * h));
                 lam[i] = (double)lp;
                 const int xp = s_rep[t] >= 0 ? (s_rep[t] ? 1 : -1) : (s_uT[t] < lp ? 1 : -1);
                 dec[i] = (uint8_t)(xp > 0);
                 if (xp != xi) {
-                    T dl[2][2];
-                    real_delta<T>(a.k.c2m1, a.k.s2, xi, dl);
+                    cx<T> dl[2][2];
+                    site_delta<T>(a.k.hs, a.k.c2m1, a.k.s2, xi, dl);
                     for (int p = 0; p < 2; ++p)
                         for (int q = 0; q < 2; ++q) s_dl[m][p][q] = dl[p][q];
                     s_site[m] = i;
@@ -625,7 +666,7 @@ __global__ void __launch_bounds__(512) soc_window_kernel(SocWinArgs a) {
                 const int lc = 2 * (s_site[t2] - s0) + p;
                 const cx<T> g = gl(lq, lc);
                 const cx<T> Aq = cmk((lq == lc ? (T)1 : (T)0) - g.r, -g.i);
-                v = cadd(v, cscale(Aq, s_dl[t2][p][p2]));
+                cfma(v, Aq, s_dl[t2][p][p2]);
             }
             Mw[e] = v;
         }
@@ -774,6 +815,7 @@ struct SocPropArgs {
     int l_first, l_step, nsl;
     int left;                 // 0: v <- D_l E v (right factor); 1: v <- E D_l^T v (left factor, transposed)
     double cg, sg;
+    int hs;                   // AFQMC_SOC_HS_SY (D_l a rotation) or AFQMC_SOC_HS_SZ (D_l = D_l^T phases)
 };
 
 constexpr int PROP_VPC_MAX = 4;
@@ -870,13 +912,19 @@ __global__ void __launch_bounds__(256) soc_prop_kernel(SocPropArgs a, int vpc) {
     for (int q = 0; q < a.nsl; ++q) {
         const int ell = a.l_first + q * a.l_step;
         const int8_t* xl = xw + (long)(ell - 1) * N;
-        if (a.left) {  // v <- D^T v: rotation by A(-gamma x)
+        if (a.left) {  // v <- D^T v: spin-y the rotation A(-gamma x), spin-z the phases of D
             for (int e = threadIdx.x; e < vpc * N; e += blockDim.x) {
                 const int v = e / N, i = e - v * N;
-                const double s = -xl[i] * a.sg;
                 const cx<double> p0 = b0[v * n2 + i], p1 = b0[v * n2 + N + i];
-                b0[v * n2 + i] = cadd(cscale(p0, a.cg), cscale(p1, s));
-                b0[v * n2 + N + i] = csub(cscale(p1, a.cg), cscale(p0, s));
+                if (a.hs == AFQMC_SOC_HS_SZ) {
+                    const double s = xl[i] * a.sg;
+                    b0[v * n2 + i] = cmul(p0, cmk(a.cg, s));
+                    b0[v * n2 + N + i] = cmul(p1, cmk(a.cg, -s));
+                } else {
+                    const double s = -xl[i] * a.sg;
+                    b0[v * n2 + i] = cadd(cscale(p0, a.cg), cscale(p1, s));
+                    b0[v * n2 + N + i] = csub(cscale(p1, a.cg), cscale(p0, s));
+                }
             }
             __syncthreads();
         }
@@ -900,13 +948,18 @@ __global__ void __launch_bounds__(256) soc_prop_kernel(SocPropArgs a, int vpc) {
         }
         dft(1, 1);
         dft(0, 1);
-        if (!a.left) {  // v <- D v: rotation by A(gamma x)
+        if (!a.left) {  // v <- D v: A(gamma x) on each pair
             for (int e = threadIdx.x; e < vpc * N; e += blockDim.x) {
                 const int v = e / N, i = e - v * N;
                 const double s = xl[i] * a.sg;
                 const cx<double> p0 = b0[v * n2 + i], p1 = b0[v * n2 + N + i];
-                b0[v * n2 + i] = cadd(cscale(p0, a.cg), cscale(p1, s));
-                b0[v * n2 + N + i] = csub(cscale(p1, a.cg), cscale(p0, s));
+                if (a.hs == AFQMC_SOC_HS_SZ) {
+                    b0[v * n2 + i] = cmul(p0, cmk(a.cg, s));
+                    b0[v * n2 + N + i] = cmul(p1, cmk(a.cg, -s));
+                } else {
+                    b0[v * n2 + i] = cadd(cscale(p0, a.cg), cscale(p1, s));
+                    b0[v * n2 + N + i] = csub(cscale(p1, a.cg), cscale(p0, s));
+                }
             }
         }
         __syncthreads();
@@ -1308,7 +1361,7 @@ cudaError_t soc_wrap(afqmc_soc_ctx* ctx, cudaStream_t st, const int8_t* xl, int 
     cudaError_t e;
     if (dir < 0) {  // G <- D^{-1} G D first
         count_launch();
-        soc_rot_kernel<T><<<rgrid, rblk, 0, st>>>(G, ldz, N, gs, xl, xs, cg, sg, -1, +1);
+        soc_rot_kernel<T><<<rgrid, rblk, 0, st>>>(G, ldz, N, gs, xl, xs, cg, sg, -1, +1, ctx->k.hs);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const T* Cright = (const T*)(dir > 0 ? ctx->Einvch : ctx->Ech);  // S = G E^{-1} (fwd) / G E (bwd)
@@ -1360,7 +1413,7 @@ cudaError_t soc_wrap(afqmc_soc_ctx* ctx, cudaStream_t st, const int8_t* xl, int 
     }
     if (dir > 0) {  // G <- D G D^{-1}
         count_launch();
-        soc_rot_kernel<T><<<rgrid, rblk, 0, st>>>(G, ldz, N, gs, xl, xs, cg, sg, +1, -1);
+        soc_rot_kernel<T><<<rgrid, rblk, 0, st>>>(G, ldz, N, gs, xl, xs, cg, sg, +1, -1, ctx->k.hs);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -1482,7 +1535,7 @@ cudaError_t soc_propagate(afqmc_soc_ctx* ctx, cudaStream_t st, double* F, long w
     a.tab = ctx->dft; a.P = ctx->dP; a.Q = ctx->dQ; a.lam = ctx->lamk;
     a.x = ctx->x; a.xstride = (long)ctx->p.M * ctx->N;
     a.l_first = l_first; a.l_step = l_step; a.nsl = nsl; a.left = left;
-    a.cg = ctx->k.c1m1 + 1.0; a.sg = ctx->k.s1;
+    a.cg = ctx->k.c1m1 + 1.0; a.sg = ctx->k.s1; a.hs = ctx->k.hs;
     // vectors per CTA: as many (<= 4) as two buffers of 2N complex doubles allow in 220 KB
     const size_t per = (size_t)2 * ctx->N2 * sizeof(cx<double>),
                  fix = (size_t)(ctx->dP * ctx->dP + ctx->dQ * ctx->dQ + ctx->dP * ctx->dQ) * sizeof(cx<double>);
@@ -1609,7 +1662,8 @@ int afqmc_soc_create(afqmc_soc_ctx** out, const afqmc_soc_params* p) {
     *out = nullptr;
     const int L = p->L, N = L * L;
     if (L < 2 || L > 48 || p->M < 1 || p->stab_every < 1 || p->M % p->stab_every != 0 || p->n_e < 1 ||
-        p->n_e > 2 * N || p->n_walkers < 1 || !(p->U <= 0.0) || !(p->dtau > 0.0))
+        p->n_e > 2 * N || p->n_walkers < 1 || !(p->U <= 0.0) || !(p->dtau > 0.0) ||
+        (p->hs != AFQMC_SOC_HS_SY && p->hs != AFQMC_SOC_HS_SZ))
         return AFQMC_ERR_ARG;
     if (p->precision != AFQMC_PREC_FP64 && p->precision != AFQMC_PREC_FP32) return AFQMC_ERR_ARG;
     int dev = 0, major = 0, minor = 0;
@@ -1644,6 +1698,7 @@ int afqmc_soc_create(afqmc_soc_ctx** out, const afqmc_soc_params* p) {
     c->k.s2 = sin(2.0 * g);
     c->k.c1m1 = cos(g) - 1.0;
     c->k.s1 = sin(g);
+    c->k.hs = p->hs;
     *out = c;
     return AFQMC_OK;
 }

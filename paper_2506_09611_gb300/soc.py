@@ -21,7 +21,10 @@ class afqmc_soc_params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("M", ctypes.c_int), ("n_e", ctypes.c_int), ("n_walkers", ctypes.c_int),
                 ("precision", ctypes.c_int), ("gemm", ctypes.c_int), ("stab_every", ctypes.c_int),
                 ("t", ctypes.c_double), ("lam", ctypes.c_double), ("U", ctypes.c_double),
-                ("dtau", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("dtau", ctypes.c_double), ("seed", ctypes.c_uint64), ("hs", ctypes.c_int)]
+
+
+HS = {"sy": 0, "sz": 1}  # AFQMC_SOC_HS_SY, AFQMC_SOC_HS_SZ
 
 
 _done = False
@@ -57,9 +60,10 @@ def load():
 
 
 def afqmc_soc_create(L, M, n_e, n_walkers=1, precision="fp64", gemm="tc3", stab_every=10, t=1.0, lam=0.5, U=-4.0,
-                     dtau=0.05, seed=1):
+                     dtau=0.05, seed=1, hs="sy"):
     p = afqmc_soc_params(L=L, M=M, n_e=n_e, n_walkers=n_walkers, precision=PRECS.get(precision, precision),
-                         gemm=GEMMS.get(gemm, gemm), stab_every=stab_every, t=t, lam=lam, U=U, dtau=dtau, seed=seed)
+                         gemm=GEMMS.get(gemm, gemm), stab_every=stab_every, t=t, lam=lam, U=U, dtau=dtau, seed=seed,
+                         hs=HS.get(hs, hs))
     h = ctypes.c_void_p()
     _ck("afqmc_soc_create", load().afqmc_soc_create(ctypes.byref(h), ctypes.byref(p)))
     return h
@@ -156,12 +160,13 @@ def afqmc_soc_get_profile(ctx):
 
 
 class SocContext:
-    """Owns one afqmc_soc_ctx; methods forward to the C entry points above."""
+    """Owns one afqmc_soc_ctx; methods forward to the C entry points above.  hs: "sy" (spin-y
+    channel) or "sz" (the imaginary spin-z channel; with lam = 0 the attractive Hubbard model)."""
 
     def __init__(self, L, M, n_e, n_walkers=1, precision="fp64", gemm="tc3", stab_every=10, t=1.0, lam=0.5, U=-4.0,
-                 dtau=0.05, seed=1):
+                 dtau=0.05, seed=1, hs="sy"):
         self.M, self.n = M, n_walkers
-        self.h = afqmc_soc_create(L, M, n_e, n_walkers, precision, gemm, stab_every, t, lam, U, dtau, seed)
+        self.h = afqmc_soc_create(L, M, n_e, n_walkers, precision, gemm, stab_every, t, lam, U, dtau, seed, hs)
 
     def init(self, P, fields=None, stream=None):
         afqmc_soc_init(self.h, P, fields, stream)
