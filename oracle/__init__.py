@@ -136,6 +136,7 @@ def _load():
         lib.soc_block_force_bias.argtypes = [sp, vp, i8p, ctypes.c_int, ctypes.c_int, vp]
         lib.soc_blockfb_slice.argtypes = [sp, vp, i8p, dp, dp, ctypes.c_int, u8p, i8p, dp, u8p, dp]
         lib.soc_energy.argtypes = [sp, vp, vp, dp]
+        lib.soc_pairing.argtypes = [sp, vp, dp, vp, vp]
         _lib = lib
     return _lib
 
@@ -629,6 +630,22 @@ class SocModel:
         H0 = self.H0 if H0 is None else _c128(H0)
         _load().soc_energy(ctypes.byref(self.p), _vp(H0), _vp(_c128(G)), _d(r))
         return complex(r[0], r[1])
+
+
+    def pairing(self, G, want_k=True):
+        """The pairing observables of Sec. IV from G (soc_oracle.c soc_pairing): a dict with the
+        double occupancy D, the pairing correlator <Delta^2> (both complex mixed estimators), and
+        with want_k the momentum occupations nk (2N: spin up, then spin down) and the raw pairing
+        matrix Mk[k][k'] = <D+_k D_k'> (N x N), D+_k = c+_{k up} c+_{-k dn}."""
+        N = self.N
+        out = np.zeros(4)
+        nk = np.zeros(2 * N, np.complex128) if want_k else None
+        Mk = np.zeros((N, N), np.complex128) if want_k else None
+        _load().soc_pairing(ctypes.byref(self.p), _vp(_c128(G)), _d(out), _vp(nk), _vp(Mk))
+        r = {"D": complex(out[0], out[1]), "Delta2": complex(out[2], out[3])}
+        if want_k:
+            r["nk"], r["Mk"] = nk, Mk
+        return r
 
 
 class SocWalker:

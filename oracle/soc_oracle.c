@@ -628,3 +628,91 @@ void soc_energy(const soc_params* p, const cplx* H0, const cplx* G, double* out)
     out[0] = creal(e);
     out[1] = cimag(e);
 }
+
+/* Pairing observables of Sec. IV (the attractive Hubbard benchmarks), mixed estimator from G by the
+ * spin-coupled Wick contraction (A = 1 - G, A_ab = <c_b^+ c_a>, G_ab = <c_a c_b^+>; orbitals
+ * u = i, d = N + i):
+ *   double occupancy   D = N^{-1} sum_i <n_iu n_id> = N^{-1} sum_i (A_uu A_dd - A_du A_ud);
+ *   pairing            <Delta^2> = L^{-2} sum_r P(r), P(r) = L^{-2} sum_i <D+_i D_{i+r} + D_i D+_{i+r}> / 4,
+ *                      D+_i = c+_iu c+_id, with
+ *                      <D+_i D_j> = A_{ju,iu} A_{jd,id} - A_{jd,iu} A_{ju,id},
+ *                      <D_i D+_j> = G_{iu,ju} G_{id,jd} - G_{id,ju} G_{iu,jd};
+ *   momentum space     c_{k s} = N^{-1/2} sum_j e^{-i k.r_j} c_{j s}, k = 2 pi (nx, ny) / L, index
+ *                      nx + L ny; At_{(p s),(q t)} = <c+_{q t} c_{p s}> = (F A F^+) with
+ *                      F_{p j} = N^{-1/2} e^{-i p.r_j} on each spin block;
+ *                      nk[k] = <n_{k u}> = At_{ku,ku}, nk[N + k] = <n_{k d}> = At_{kd,kd};
+ *                      Mk[k][k'] = <D+_k D_k'>, D+_k = c+_{k u} c+_{-k d}:
+ *                                = At_{k'u,ku} At_{-k'd,-kd} - At_{-k'd,ku} At_{k'u,-kd}.
+ * The condensate fraction n_c = lambda_max(M) / (N_e / 2) (Sec. IV) takes the Monte Carlo average
+ * of Mk minus delta_kk' <n_{ku}> <n_{-kd}>; that average is the caller's.
+ * out: Re D, Im D, Re <Delta^2>, Im <Delta^2>; nk: 2N complex; Mk: N x N complex (both nullable). */
+void soc_pairing(const soc_params* p, const cplx* G, double* out, cplx* nk, cplx* Mk) {
+    const int L = p->L, N = p->N, N2 = 2 * N;
+    cplx* A = malloc((size_t)N2 * N2 * sizeof(cplx));
+    for (int a = 0; a < N2; a++)
+        for (int b = 0; b < N2; b++) A[(size_t)a * N2 + b] = (a == b ? 1.0 : 0.0) - G[(size_t)a * N2 + b];
+#define AE(a, b) A[(size_t)(a) * N2 + (b)]
+#define GE(a, b) G[(size_t)(a) * N2 + (b)]
+    cplx d = 0, pd = 0;
+    for (int i = 0; i < N; i++) d += AE(i, i) * AE(N + i, N + i) - AE(N + i, i) * AE(i, N + i);
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            const cplx dpd = AE(j, i) * AE(N + j, N + i) - AE(N + j, i) * AE(j, N + i);
+            const cplx ddp = GE(i, j) * GE(N + i, N + j) - GE(N + i, j) * GE(i, N + j);
+            pd += 0.25 * (dpd + ddp);
+        }
+    out[0] = creal(d) / N;
+    out[1] = cimag(d) / N;
+    out[2] = creal(pd) / ((double)N * N);
+    out[3] = cimag(pd) / ((double)N * N);
+    if (nk || Mk) {
+        /* F (N x N) and At = F2 A F2^+ with F2 = diag(F, F) */
+        cplx* F = malloc((size_t)N * N * sizeof(cplx));
+        for (int q = 0; q < N; q++)
+            for (int j = 0; j < N; j++) {
+                const double ph = -2.0 * M_PI * ((double)(q % L) * (j % L) + (double)(q / L) * (j / L)) / L;
+                F[(size_t)q * N + j] = (cos(ph) + I * sin(ph)) / sqrt((double)N);
+            }
+        cplx* T = malloc((size_t)N2 * N2 * sizeof(cplx));
+        cplx* At = malloc((size_t)N2 * N2 * sizeof(cplx));
+        /* T = A F2^+ : T[a][(q t)] = sum_j A[a][(j t)] conj(F[q][j]) */
+#pragma omp parallel for schedule(static)
+        for (int a = 0; a < N2; a++)
+            for (int t = 0; t < 2; t++)
+                for (int q = 0; q < N; q++) {
+                    cplx v = 0;
+                    for (int j = 0; j < N; j++) v += AE(a, t * N + j) * conj(F[(size_t)q * N + j]);
+                    T[(size_t)a * N2 + t * N + q] = v;
+                }
+        /* At = F2 T : At[(p s)][b] = sum_i F[p][i] T[(i s)][b] */
+#pragma omp parallel for schedule(static)
+        for (int s = 0; s < 2; s++)
+            for (int pp = 0; pp < N; pp++)
+                for (int b = 0; b < N2; b++) {
+                    cplx v = 0;
+                    for (int i = 0; i < N; i++) v += F[(size_t)pp * N + i] * T[(size_t)(s * N + i) * N2 + b];
+                    At[(size_t)(s * N + pp) * N2 + b] = v;
+                }
+#define AT(a, b) At[(size_t)(a) * N2 + (b)]
+        if (nk)
+            for (int k = 0; k < N; k++) {
+                nk[k] = AT(k, k);
+                nk[N + k] = AT(N + k, N + k);
+            }
+        if (Mk)
+            for (int k = 0; k < N; k++) {
+                const int mk = (L - k % L) % L + L * ((L - k / L) % L);
+                for (int k2 = 0; k2 < N; k2++) {
+                    const int mk2 = (L - k2 % L) % L + L * ((L - k2 / L) % L);
+                    Mk[(size_t)k * N + k2] = AT(k2, k) * AT(N + mk2, N + mk) - AT(N + mk2, k) * AT(k2, N + mk);
+                }
+            }
+#undef AT
+        free(F);
+        free(T);
+        free(At);
+    }
+#undef AE
+#undef GE
+    free(A);
+}
