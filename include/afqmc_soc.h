@@ -109,7 +109,27 @@ int afqmc_soc_recompute_G(afqmc_soc_ctx* ctx, double* rel_drift, void* stream);
  * energy: host, 2 doubles (re, im) per walker.  Syncs the stream. */
 int afqmc_soc_measure_energy(afqmc_soc_ctx* ctx, double* energy, void* stream);
 
-/* Accessors (sync the stream of the last call). */
+/* Pairing observables of Sec. IV for every walker, mixed estimator at the current slice from the
+ * bulk G by the spin-coupled Wick contraction, in FP64 (A = 1 - G, A_ab = <c_b^+ c_a>; u = i, d = N + i):
+ *   D = N^{-1} sum_i <n_iu n_id>,  <n_iu n_id> = A_uu A_dd - A_du A_ud (the double occupancy);
+ *   <Delta^2> = L^{-2} sum_r P(r), P(r) = L^{-2} sum_i <D+_i D_{i+r} + D_i D+_{i+r}> / 4 (the on-site
+ *     pairing correlator), D+_i = c+_iu c+_id, <D+_i D_j> = A_{ju,iu} A_{jd,id} - A_{jd,iu} A_{ju,id},
+ *     <D_i D+_j> = G_{iu,ju} G_{id,jd} - G_{id,ju} G_{iu,jd};
+ *   in momentum space (c_ks = N^{-1/2} sum_j e^{-i k.r_j} c_js, k = 2 pi (nx, ny) / L, index nx + L ny,
+ *   At = F2 A F2^+ with F2 the DFT on each spin block): <n_ku> = At_{ku,ku}, <n_kd> = At_{kd,kd}, and
+ *   the pairing matrix Mk[k][k'] = <D+_k D_k'>, D+_k = c+_{k u} c+_{-k d},
+ *     = At_{k'u,ku} At_{-k'd,-kd} - At_{-k'd,ku} At_{k'u,-kd}.
+ * The condensate fraction n_c is the largest eigenvalue of the Monte Carlo average of
+ * Mk[k][k'] - delta_kk' <n_ku> <n_{-k d}>, divided by N_e / 2 (Sec. IV); the averaging is the caller's.
+ *   scalars  host, 4 doubles per walker: Re D, Im D, Re <Delta^2>, Im <Delta^2>.
+ *   nk       host, nullable: 4N doubles per walker, <n_ku> (N complex) then <n_kd> (N complex).
+ *   Mk       host, nullable: N x N complex (re, im interleaved), the SUM over the walkers.
+ * The first call allocates the DFT tables (2 x (2 ldz)^2 + 2N 2 ldz doubles, ldz = 2N rounded up to
+ * 32) and scratch of the same order.  Syncs the stream.  AFQMC_ERR_ARG before init or for a NULL
+ * scalars. */
+int afqmc_soc_measure_pairing(afqmc_soc_ctx* ctx, double* scalars, double* nk, double* Mk, void* stream);
+
+/* Accessors (sync the stream of the last call). *//* Accessors (sync the stream of the last call). */
 int afqmc_soc_get_G(afqmc_soc_ctx* ctx, int walker, double* host_out);       /* 2N x 2N complex */
 int afqmc_soc_set_G(afqmc_soc_ctx* ctx, int walker, const double* host_in);  /* 2N x 2N complex */
 int afqmc_soc_get_fields(afqmc_soc_ctx* ctx, int walker, int8_t* host_out);  /* M x N */

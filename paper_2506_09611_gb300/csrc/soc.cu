@@ -1079,6 +1079,82 @@ __global__ void soc_energy_kernel(const T* G0, long ldz, long gstride, int L, do
     }
 }
 
+// ---------------------------------------------------------------------------
+// pairing observables (Sec. IV), FP64 from the bulk G of one walker
+// ---------------------------------------------------------------------------
+// A = 1 - G in FP64, row-split like G (2N rows of 2 ldz; grid: (columns, 2N rows)).
+template <typename T>
+__global__ void soc_one_minus_kernel(const T* G, long ldz, double* A) {
+    const long ld2 = 2 * ldz;
+    const int r = blockIdx.y;
+    for (long c = blockIdx.x * blockDim.x + threadIdx.x; c < ld2; c += (long)gridDim.x * blockDim.x)
+        A[(long)r * ld2 + c] = (c == r ? 1.0 : 0.0) - (double)G[(long)r * ld2 + c];
+}
+
+// The real-space estimators by Wick's theorem (A_ab = <c_b^+ c_a>, G = 1 - A; u = i, d = N + i):
+//   D terms     <n_iu n_id>  = A_uu A_dd - A_du A_ud;
+//   pair terms  <D+_i D_j>   = A_{ju,iu} A_{jd,id} - A_{jd,iu} A_{ju,id},
+//               <D_i D+_j>   = G_{iu,ju} G_{id,jd} - G_{id,ju} G_{iu,jd};
+// out[0..1] += sum_i <n_iu n_id>, out[2..3] += sum_ij (<D+_i D_j> + <D_i D+_j>) (complex; FP64 atomics).
+__global__ void __launch_bounds__(256) soc_pair_scalars_kernel(const double* A, long ldz, int N, double* out) {
+    const long ld2 = 2 * ldz;
+    auto a = [&](int r, int c) { return cmk(A[(long)r * ld2 + c], A[(long)r * ld2 + ldz + c]); };
+    auto g = [&](int r, int c) {
+        const cx<double> v = a(r, c);
+        return cmk((r == c ? 1.0 : 0.0) - v.r, -v.i);
+    };
+    cx<double> d = cmk(0.0, 0.0), pp = cmk(0.0, 0.0);
+    const long NN = (long)N * N;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < NN; e += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / N), j = (int)(e - (long)i * N);
+        cx<double> t = cmul(a(j, i), a(N + j, N + i));
+        t = csub(t, cmul(a(N + j, i), a(j, N + i)));
+        cfma(t, g(i, j), g(N + i, N + j));
+        t = csub(t, cmul(g(N + i, j), g(i, N + j)));
+        pp = cadd(pp, t);
+        if (i == j) d = cadd(d, csub(cmul(a(i, i), a(N + i, N + i)), cmul(a(N + i, i), a(i, N + i))));
+    }
+    __shared__ double red[4][8];
+    double v[4] = {d.r, d.i, pp.r, pp.i};
+    for (int q = 0; q < 4; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int q = 0; q < 4; ++q) red[q][warp] = v[q];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+        atomicAdd(out + threadIdx.x, s);
+    }
+}
+
+// From At = F2 A F2^+ (row-split, At_{(p s),(q t)} = <c+_{q t} c_{p s}>): nk[k] = At_{ku,ku},
+// nk[N + k] = At_{kd,kd} (complex), and Mk[k][k'] += At_{k'u,ku} At_{-k'd,-kd} - At_{-k'd,ku} At_{k'u,-kd}
+// (the walker sum of <D+_k D_k'>, D+_k = c+_{k u} c+_{-k d}; -k = (-kx, -ky) mod L).
+__global__ void __launch_bounds__(256) soc_pair_k_kernel(const double* At, long ldz, int L, double* Mk, double* nk) {
+    const long ld2 = 2 * ldz;
+    const int N = L * L;
+    auto at = [&](int r, int c) { return cmk(At[(long)r * ld2 + c], At[(long)r * ld2 + ldz + c]); };
+    auto neg = [&](int k) { return (L - k % L) % L + L * ((L - k / L) % L); };
+    const long NN = (long)N * N;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < NN; e += (long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / N), k2 = (int)(e - (long)k * N);
+        const int mk = neg(k), mk2 = neg(k2);
+        cx<double> t = cmul(at(k2, k), at(N + mk2, N + mk));
+        t = csub(t, cmul(at(N + mk2, k), at(k2, N + mk)));
+        Mk[2 * e] += t.r;
+        Mk[2 * e + 1] += t.i;
+        if (k2 == 0) {
+            const cx<double> u = at(k, k), dd = at(N + k, N + k);
+            nk[2 * k] = u.r;
+            nk[2 * k + 1] = u.i;
+            nk[2 * (N + k)] = dd.r;
+            nk[2 * (N + k) + 1] = dd.i;
+        }
+    }
+}
+
 __global__ void soc_fields_kernel(uint64_t seed, long count, int8_t* x) {
     const long j = blockIdx.x * (long)blockDim.x + threadIdx.x;
     const int w = blockIdx.y;
@@ -1140,6 +1216,11 @@ struct afqmc_soc_ctx {
     bool oz_O = false, oz_G = false;
     void* ozw = nullptr;
     double* ozs = nullptr;
+    // pairing observables (allocated at the first afqmc_soc_measure_pairing): [Re F2 | Im F2] rows,
+    // the realified F2^+ (2 ldz x 2 ldz), FP64 scratch A (2N x 2 ldz), S~ (2 ldz x 2 ldz),
+    // At (2N x 2 ldz), the walker-summed Mk (N x N complex) and the per-walker outputs
+    double *Frs = nullptr, *Fh = nullptr, *pA = nullptr, *pS = nullptr, *pAt = nullptr, *pMk = nullptr,
+           *pOut = nullptr;
     // profiling
     struct Ev {
         int ph;
@@ -1884,6 +1965,99 @@ int afqmc_soc_recompute_G(afqmc_soc_ctx* ctx, double* rel_drift, void* stream) {
         std::vector<double> h((size_t)ctx->nwk * 2);
         SCK(cudaMemcpy(h.data(), ctx->acc2, h.size() * 8, cudaMemcpyDeviceToHost));
         for (int w = 0; w < ctx->nwk; ++w) rel_drift[w] = h[2 * w + 1] > 0 ? sqrt(h[2 * w] / h[2 * w + 1]) : 0.0;
+    }
+    return AFQMC_OK;
+}
+
+int afqmc_soc_measure_pairing(afqmc_soc_ctx* ctx, double* scalars, double* nk, double* Mk, void* stream) {
+    int rc = check(ctx);
+    if (rc) return rc;
+    if (!ctx->inited || !scalars) return AFQMC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->last = st;
+    const int L = ctx->p.L, N = ctx->N, N2 = ctx->N2, nwk = ctx->nwk;
+    const long ldz = ctx->ldz, ld2 = 2 * ldz;
+    if (!ctx->Frs) {
+        // F2 = diag(F, F), F_{q j} = N^{-1/2} e^{-i q.r_j}: its rows for the left product and the
+        // realified right operand of the product by F2^+ (C~ = [[Re C, Im C], [-Im C, Re C]])
+        std::vector<double> frs((size_t)N2 * ld2, 0.0), fh((size_t)ld2 * ld2, 0.0);
+        const double sN = 1.0 / sqrt((double)N);
+        for (int q = 0; q < N; ++q)
+            for (int jj = 0; jj < N; ++jj) {
+                const double ph = -2.0 * M_PI * ((double)(q % L) * (jj % L) + (double)(q / L) * (jj / L)) / L;
+                const double fr = cos(ph) * sN, fi = sin(ph) * sN;
+                for (int sp = 0; sp < 2; ++sp) {
+                    const long r = sp * N + q, c = sp * N + jj;  // F2[r][c] = F[q][jj]
+                    frs[(size_t)r * ld2 + c] = fr;
+                    frs[(size_t)r * ld2 + ldz + c] = fi;
+                    // C = F2^+: C[c][r] = conj(F2[r][c])
+                    fh[(size_t)c * ld2 + r] = fr;
+                    fh[(size_t)c * ld2 + ldz + r] = -fi;
+                    fh[(size_t)(ldz + c) * ld2 + r] = fi;
+                    fh[(size_t)(ldz + c) * ld2 + ldz + r] = fr;
+                }
+            }
+        SCK(soc_alloc(ctx, &ctx->Frs, frs.size() * 8, st));
+        SCK(soc_alloc(ctx, &ctx->Fh, fh.size() * 8, st));
+        SCK(soc_alloc(ctx, &ctx->pA, (size_t)N2 * ld2 * 8, st));
+        SCK(soc_alloc(ctx, &ctx->pS, (size_t)ld2 * ld2 * 8, st));
+        SCK(soc_alloc(ctx, &ctx->pAt, (size_t)N2 * ld2 * 8, st));
+        SCK(soc_alloc(ctx, &ctx->pMk, (size_t)N * N * 16, st));
+        SCK(soc_alloc(ctx, &ctx->pOut, (size_t)nwk * (4 + 4 * N) * 8, st));
+        SCK(cudaMemcpyAsync(ctx->Frs, frs.data(), frs.size() * 8, cudaMemcpyHostToDevice, st));
+        SCK(cudaMemcpyAsync(ctx->Fh, fh.data(), fh.size() * 8, cudaMemcpyHostToDevice, st));
+        SCK(cudaStreamSynchronize(st));  // the host tables go out of scope
+    }
+    SCK(cudaMemsetAsync(ctx->pMk, 0, (size_t)N * N * 16, st));
+    SCK(cudaMemsetAsync(ctx->pOut, 0, (size_t)nwk * (4 + 4 * N) * 8, st));
+    const size_t es = ctx->f64 ? 8 : 4;
+    for (int w = 0; w < nwk; ++w) {
+        const void* Gw = (const char*)ctx->G + (size_t)w * ctx->gstride() * es;
+        double* out = ctx->pOut + (size_t)w * 4;
+        double* nkw = ctx->pOut + (size_t)nwk * 4 + (size_t)w * 4 * N;
+        const dim3 grid((unsigned)((ld2 + 255) / 256), N2);
+        count_launch();
+        if (ctx->f64) soc_one_minus_kernel<double><<<grid, 256, 0, st>>>((const double*)Gw, ldz, ctx->pA);
+        else soc_one_minus_kernel<float><<<grid, 256, 0, st>>>((const float*)Gw, ldz, ctx->pA);
+        SCK(cudaGetLastError());
+        count_launch();
+        soc_pair_scalars_kernel<<<(unsigned)std::min<long>(((long)N * N + 255) / 256, 1024), 256, 0, st>>>(
+            ctx->pA, ldz, N, out);
+        SCK(cudaGetLastError());
+        if (!nk && !Mk) continue;
+        // At = F2 A F2^+: S~ rows [0, 2N) = A (F2^+)~, the realified S~, then [Re F2 | Im F2] S~
+        GemmArgs<double> g1;
+        g1.M = N2; g1.N = (int)ld2; g1.K = (int)ld2;
+        g1.A = ctx->pA; g1.lda = ld2;
+        g1.B = ctx->Fh; g1.ldb = ld2;
+        g1.C = ctx->pS; g1.ldc = ld2;
+        SCK(gemm<double>(st, g1));
+        count_launch();
+        soc_realify_kernel<double><<<dim3((unsigned)((ld2 + 255) / 256), N2, 1), 256, 0, st>>>(ctx->pS, ldz, N2, 0, 1);
+        SCK(cudaGetLastError());
+        GemmArgs<double> g2;
+        g2.M = N2; g2.N = (int)ld2; g2.K = (int)ld2;
+        g2.A = ctx->Frs; g2.lda = ld2;
+        g2.B = ctx->pS; g2.ldb = ld2;
+        g2.C = ctx->pAt; g2.ldc = ld2;
+        SCK(gemm<double>(st, g2));
+        count_launch();
+        soc_pair_k_kernel<<<(unsigned)std::min<long>(((long)N * N + 255) / 256, 4096), 256, 0, st>>>(
+            ctx->pAt, ldz, L, ctx->pMk, nkw);
+        SCK(cudaGetLastError());
+    }
+    std::vector<double> h((size_t)nwk * (4 + 4 * N));
+    SCK(cudaMemcpyAsync(h.data(), ctx->pOut, h.size() * 8, cudaMemcpyDeviceToHost, st));
+    if (Mk) SCK(cudaMemcpyAsync(Mk, ctx->pMk, (size_t)N * N * 16, cudaMemcpyDeviceToHost, st));
+    SCK(cudaStreamSynchronize(st));
+    rc = read_err(ctx);
+    if (rc) return rc;
+    for (int w = 0; w < nwk; ++w) {
+        scalars[4 * w + 0] = h[4 * w + 0] / N;
+        scalars[4 * w + 1] = h[4 * w + 1] / N;
+        scalars[4 * w + 2] = h[4 * w + 2] / (4.0 * N * N);
+        scalars[4 * w + 3] = h[4 * w + 3] / (4.0 * N * N);
+        if (nk) memcpy(nk + (size_t)w * 4 * N, h.data() + (size_t)nwk * 4 + (size_t)w * 4 * N, (size_t)4 * N * 8);
     }
     return AFQMC_OK;
 }

@@ -13,7 +13,7 @@ from .afqmc import MODES, PRECS, GEMMS, PHASES, _ck, _ptr, _stream
 EXPORTS = ["afqmc_soc_create", "afqmc_soc_destroy", "afqmc_soc_init", "afqmc_soc_sweep_slice",
            "afqmc_soc_recompute_G", "afqmc_soc_measure_energy", "afqmc_soc_get_G", "afqmc_soc_set_G",
            "afqmc_soc_get_fields", "afqmc_soc_get_decisions", "afqmc_soc_get_ratios", "afqmc_soc_get_lam_plus",
-           "afqmc_soc_get_info", "afqmc_soc_set_profiling", "afqmc_soc_get_profile"]
+           "afqmc_soc_get_info", "afqmc_soc_set_profiling", "afqmc_soc_get_profile", "afqmc_soc_measure_pairing"]
 KMAX = {"fp32": 64, "fp64": 32}
 
 
@@ -44,6 +44,7 @@ def load():
                                           ctypes.POINTER(ctypes.c_uint8), vp]
     lib.afqmc_soc_recompute_G.argtypes = [vp, dp, vp]
     lib.afqmc_soc_measure_energy.argtypes = [vp, dp, vp]
+    lib.afqmc_soc_measure_pairing.argtypes = [vp, dp, dp, dp, vp]
     lib.afqmc_soc_get_G.argtypes = [vp, ctypes.c_int, dp]
     lib.afqmc_soc_set_G.argtypes = [vp, ctypes.c_int, dp]
     lib.afqmc_soc_get_fields.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int8)]
@@ -159,13 +160,28 @@ def afqmc_soc_get_profile(ctx):
     return {p: {"ms": float(ms[i]), "intervals": int(iv[i]), "launches": int(la[i])} for i, p in enumerate(PHASES)}
 
 
+def afqmc_soc_measure_pairing(ctx, n_walkers, N, want_k=True, stream=None):
+    """Per walker D and <Delta^2> (complex arrays), and with want_k the momentum occupations nk
+    (n_walkers x 2N complex) and the walker sum of the pairing matrix Mk (N x N complex)."""
+    sc = np.zeros(4 * n_walkers)
+    nk = np.zeros(4 * N * n_walkers) if want_k else None
+    Mk = np.zeros(2 * N * N) if want_k else None
+    _ck("afqmc_soc_measure_pairing", load().afqmc_soc_measure_pairing(
+        ctx, _ptr(sc, ctypes.c_double), _ptr(nk, ctypes.c_double), _ptr(Mk, ctypes.c_double), _stream(stream)))
+    r = {"D": sc[0::4] + 1j * sc[1::4], "Delta2": sc[2::4] + 1j * sc[3::4]}
+    if want_k:
+        r["nk"] = nk.view(np.complex128).reshape(n_walkers, 2 * N)
+        r["Mk"] = Mk.view(np.complex128).reshape(N, N)
+    return r
+
+
 class SocContext:
     """Owns one afqmc_soc_ctx; methods forward to the C entry points above.  hs: "sy" (spin-y
     channel) or "sz" (the imaginary spin-z channel; with lam = 0 the attractive Hubbard model)."""
 
     def __init__(self, L, M, n_e, n_walkers=1, precision="fp64", gemm="tc3", stab_every=10, t=1.0, lam=0.5, U=-4.0,
                  dtau=0.05, seed=1, hs="sy"):
-        self.M, self.n = M, n_walkers
+        self.M, self.n, self.N = M, n_walkers, L * L
         self.h = afqmc_soc_create(L, M, n_e, n_walkers, precision, gemm, stab_every, t, lam, U, dtau, seed, hs)
 
     def init(self, P, fields=None, stream=None):
@@ -179,6 +195,9 @@ class SocContext:
 
     def measure_energy(self, stream=None):
         return afqmc_soc_measure_energy(self.h, self.n, stream)
+
+    def measure_pairing(self, want_k=True, stream=None):
+        return afqmc_soc_measure_pairing(self.h, self.n, self.N, want_k, stream)
 
     def G(self, walker=0):
         return afqmc_soc_get_G(self.h, walker)

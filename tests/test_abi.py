@@ -92,7 +92,8 @@ def test_soc_create_rejects_bad_arguments_before_touching_the_device():
     h = ctypes.c_void_p()
     good = dict(L=4, M=10, n_e=8, n_walkers=1, precision=0, gemm=0, stab_every=5, t=1.0, lam=0.5, U=-4.0,
                 dtau=0.05, seed=1)
-    for bad in (dict(U=4.0), dict(stab_every=3), dict(L=1), dict(n_e=33), dict(precision=7), dict(n_walkers=0)):
+    for bad in (dict(U=4.0), dict(stab_every=3), dict(L=1), dict(n_e=33), dict(precision=7), dict(n_walkers=0),
+                dict(hs=2), dict(hs=-1)):
         p = soc.afqmc_soc_params(**{**good, **bad})
         assert lib.afqmc_soc_create(ctypes.byref(h), ctypes.byref(p)) == -1, bad
     assert lib.afqmc_soc_destroy(None) == 0
@@ -131,6 +132,7 @@ def test_every_entry_point_rejects_a_null_context_without_the_device():
     assert lib.afqmc_soc_sweep_slice(None, 1, 1, 1, 8, 4, None, None) == ARG
     assert lib.afqmc_soc_recompute_G(None, None, None) == ARG
     assert lib.afqmc_soc_measure_energy(None, p(d), None) == ARG
+    assert lib.afqmc_soc_measure_pairing(None, p(d), None, None, None) == ARG
     assert lib.afqmc_soc_get_G(None, 0, p(d)) == ARG
     assert lib.afqmc_soc_set_G(None, 0, p(d)) == ARG
     assert lib.afqmc_soc_get_fields(None, 0, p(i8)) == ARG

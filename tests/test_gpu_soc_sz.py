@@ -89,3 +89,33 @@ def test_fp32_replay_within_tolerance(mode, k, nb):
             if w.pos % stab == 0:
                 ctx.recompute_G()
                 w.recompute()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("L,ns", [(4, 7), (6, 15)])
+def test_pairing_observables_match_oracle(precision, L, ns):
+    """afqmc_soc_measure_pairing (Sec. IV's D, <Delta^2>, n_k and the pairing matrix, FP64 from the bulk
+    G) against the oracle's soc_pairing evaluated on the same G read back from the device, for two
+    walkers after a few free-running slices; the pairing matrix is their sum."""
+    M, stab, nw = 4, 2, 2
+    N = L * L
+    P = inputs.sz_trial_state(L, ns)
+    X = np.concatenate([inputs.initial_fields(M, N, seed=40 + w) for w in range(nw)])
+    ctx = soc.SocContext(L, M, 2 * ns, nw, precision, "tc3", stab, 1.0, 0.0, -4.0, 0.05, 31, hs="sz")
+    model = oracle.SocModel(L, 1.0, 0.0, -4.0, 0.05, M, hs="sz")
+    with ctx:
+        ctx.init(P, X)
+        for ell in (1, 2):
+            ctx.sweep_slice(ell, +1, "delayed", k=8)
+        got = ctx.measure_pairing()
+        Msum = np.zeros((N, N), np.complex128)
+        for w in range(nw):
+            ref = model.pairing(ctx.G(w))
+            assert abs(got["D"][w] - ref["D"]) < 1e-11
+            assert abs(got["Delta2"][w] - ref["Delta2"]) < 1e-11
+            np.testing.assert_allclose(got["nk"][w], ref["nk"], atol=1e-11)
+            Msum += ref["Mk"]
+            assert abs(ref["D"].imag) < 1e-6 and 0 < ref["D"].real < 1
+        np.testing.assert_allclose(got["Mk"], Msum, atol=1e-11)
+        only = ctx.measure_pairing(want_k=False)
+        np.testing.assert_array_equal(only["D"], got["D"])
