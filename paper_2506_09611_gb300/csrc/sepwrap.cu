@@ -41,16 +41,13 @@ __global__ void __launch_bounds__(SEP_LINE_THREADS) sep_line_kernel(SepLineArgs 
         sep_line<T, LM>(a, line, As);
 }
 
-// Circulant A (SepArgs::circ) with a compile-time lattice side: its first row in shared memory.
-// Lines longer than 96 bytes (FP32 L >= 32, FP64 L >= 16) keep the line, the L accumulators and
-// the operands the unrolled loop has in flight in up to 255 registers (one block per SM, eight
-// warps, each with L independent accumulators); shorter ones run two blocks per SM.
+// Circulant A (SepArgs::circ) with a compile-time lattice side: its first row in registers, loaded
+// once per thread; two blocks per SM (128 registers: c, the line and a chunk of outputs).
 template <typename T, int L>
-__global__ void __launch_bounds__(SEP_LINE_THREADS, sizeof(T) * L > 96 ? 1 : 2)
-    sep_line_circ_kernel(SepLineArgs a, const double* A) {
-    __shared__ T c[L];
-    for (int d = threadIdx.x; d < L; d += blockDim.x) c[d] = (T)A[d];
-    __syncthreads();
+__global__ void __launch_bounds__(SEP_LINE_THREADS, 2) sep_line_circ_kernel(SepLineArgs a, const double* A) {
+    T c[L];
+#pragma unroll
+    for (int d = 0; d < L; ++d) c[d] = (T)__ldg(A + d);
     const long total = sep_line_count(a) * a.batch;
     for (long line = (long)blockIdx.x * blockDim.x + threadIdx.x; line < total; line += (long)gridDim.x * blockDim.x)
         sep_line_circ<T, L>(a, line, c);

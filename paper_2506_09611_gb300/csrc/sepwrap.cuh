@@ -364,10 +364,17 @@ SEP_HD inline void sep_line(const SepLineArgs& a, long line, const T* As) {
 // The same line for a circulant A of compile-time side L, given by its first row c[d] = A[0][d]
 // (A[x][p] = c[(p - x) mod L]; A is symmetric, so the column passes use the same formula):
 //   out[x] = sum_d c[d] v[(x + d) mod L].
-// The loop runs over d outside and x inside, with the line and its L outputs in registers, so a
-// line costs L shared-memory reads (one broadcast scalar per d) against L^2 multiply-adds.
+// c (the caller keeps it in registers across lines), the line and a chunk of H outputs are
+// register operands, so the pass runs on the FMA pipes: L^2 multiply-adds per line and no memory
+// access besides the line's own loads and stores.  H = L for lines up to 80 bytes, else L / 2
+// rounded up to a multiple of 4 (fewer live registers, so two blocks fit per SM).
 template <typename T, int L>
-SEP_HD inline void sep_line_circ(const SepLineArgs& a, long line, const T* c) {
+SEP_HD constexpr int sep_circ_chunk() {
+    return sizeof(T) * L <= 80 ? L : ((L / 2 + 3) / 4) * 4;
+}
+
+template <typename T, int L>
+SEP_HD inline void sep_line_circ(const SepLineArgs& a, long line, const T (&c)[L]) {
     const long nl = sep_line_count(a);
     const int z = (int)(line / nl);
     const long l = line - (long)z * nl;
@@ -416,23 +423,29 @@ SEP_HD inline void sep_line_circ(const SepLineArgs& a, long line, const T* c) {
     }
 #pragma unroll
     for (int p = 0; p < L; ++p) v[p] *= vin ? fin * vin[vo + p * vd] : fin;
-    T o[L];
+    constexpr int H = sep_circ_chunk<T, L>();
 #pragma unroll
-    for (int x = 0; x < L; ++x) o[x] = 0;
+    for (int x0 = 0; x0 < L; x0 += H) {
+        T o[H];
 #pragma unroll
-    for (int d = 0; d < L; ++d) {
-        const T cd = c[d];
+        for (int x = 0; x < H; ++x) o[x] = 0;
 #pragma unroll
-        for (int x = 0; x < L; ++x) o[x] += cd * v[(x + d) % L];
-    }
+        for (int d = 0; d < L; ++d)
 #pragma unroll
-    for (int x = 0; x < L; ++x) o[x] *= vout ? fout * vout[vo + x * vd] : fout;
-    if (vec) {
+            for (int x = 0; x < H; ++x)
+                if (x0 + x < L) o[x] += c[d] * v[(x0 + x + d) % L];
 #pragma unroll
-        for (int x = 0; x < L; x += 4) sep_st4(g + x, o + x);
-    } else {
+        for (int x = 0; x < H; ++x)
+            if (x0 + x < L) o[x] *= vout ? fout * vout[vo + (x0 + x) * vd] : fout;
+        if (vec) {
 #pragma unroll
-        for (int x = 0; x < L; ++x) g[(long)x * stride] = o[x];
+            for (int x = 0; x < H; x += 4)
+                if (x0 + x < L) sep_st4(g + x0 + x, o + x);
+        } else {
+#pragma unroll
+            for (int x = 0; x < H; ++x)
+                if (x0 + x < L) g[(long)(x0 + x) * stride] = o[x];
+        }
     }
 }
 

@@ -813,9 +813,11 @@ struct SocPropArgs {
     const int8_t* x;
     long xstride;             // fields M x N of walker j at x + j xstride
     int l_first, l_step, nsl;
-    int left;                 // 0: v <- D_l E v (right factor); 1: v <- E D_l^T v (left factor, transposed)
+    int left;                 // 0: v <- D_l E v (right factor); 1: v <- E D_l^+ v (the left factor carried
+                              // as U_L^+: (U_L B_l)^+ = E^+ D_l^+ U_L^+, E Hermitian)
     double cg, sg;
-    int hs;                   // AFQMC_SOC_HS_SY (D_l a rotation) or AFQMC_SOC_HS_SZ (D_l = D_l^T phases)
+    int hs;                   // AFQMC_SOC_HS_SY (D_l a real rotation, D_l^+ = D_l^T) or AFQMC_SOC_HS_SZ
+                              // (D_l phases, D_l^+ their conjugates)
 };
 
 constexpr int PROP_VPC_MAX = 4;
@@ -912,14 +914,14 @@ __global__ void __launch_bounds__(256) soc_prop_kernel(SocPropArgs a, int vpc) {
     for (int q = 0; q < a.nsl; ++q) {
         const int ell = a.l_first + q * a.l_step;
         const int8_t* xl = xw + (long)(ell - 1) * N;
-        if (a.left) {  // v <- D^T v: spin-y the rotation A(-gamma x), spin-z the phases of D
+        if (a.left) {  // v <- D^+ v: spin-y the rotation A(-gamma x), spin-z the conjugate phases
             for (int e = threadIdx.x; e < vpc * N; e += blockDim.x) {
                 const int v = e / N, i = e - v * N;
                 const cx<double> p0 = b0[v * n2 + i], p1 = b0[v * n2 + N + i];
                 if (a.hs == AFQMC_SOC_HS_SZ) {
                     const double s = xl[i] * a.sg;
-                    b0[v * n2 + i] = cmul(p0, cmk(a.cg, s));
-                    b0[v * n2 + N + i] = cmul(p1, cmk(a.cg, -s));
+                    b0[v * n2 + i] = cmul(p0, cmk(a.cg, -s));
+                    b0[v * n2 + N + i] = cmul(p1, cmk(a.cg, s));
                 } else {
                     const double s = -xl[i] * a.sg;
                     b0[v * n2 + i] = cadd(cscale(p0, a.cg), cscale(p1, s));

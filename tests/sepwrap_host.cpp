@@ -22,7 +22,7 @@ void run_line(const afq::SepLineArgs& p, const double* A) {
 template <typename T, int L>
 void run_circ(const afq::SepLineArgs& p, const double* A) {
     T c[L];
-    for (int d = 0; d < L; ++d) c[d] = (T)A[d];
+    for (int d = 0; d < L; ++d) c[d] = (T)A[d];  // the kernel's registers
     const long total = afq::sep_line_count(p) * p.batch;
     for (long line = 0; line < total; ++line) afq::sep_line_circ<T, L>(p, line, c);
 }
