@@ -1,0 +1,94 @@
+"""The pairing production run (paper_2506_09611_gb300.pairing: the attractive Hubbard model with the
+imaginary spin-z decoupling, Sec. II.B; D, <Delta^2> and n_c of Sec. IV) end to end on the GPU.
+
+On the 2 x 2 lattice the estimators have an exact reference for the same M and dtau: the Fock-space
+mixed expectation <psi_T| T^{M/2} O T^{M/2} |psi_T> / <psi_T| T^M |psi_T>, T = e^{-dtau H_I} e^{-dtau K}
+(the decoupling is exact for every Trotter factor), with n_c from the exact pairing matrix.  Free-
+running chains must reproduce it within their error bars (Eq. GSObsQMC).
+
+The comparison with the paper's own L = 20 values (Table C1, tests/golden/table_c1.txt) is a long
+run (about ten minutes of one GPU per parameter set); it runs only with AFQMC_TABLE_C1=1.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from paper_2506_09611_gb300 import inputs
+from tests import bruteforce as bf
+
+pytestmark = pytest.mark.gpu
+
+pairing = pytest.importorskip("paper_2506_09611_gb300.pairing")
+
+
+def _exact_2x2(L, ns, U, dtau, M):
+    N = L * L
+    cs = [C.astype(np.complex128) for C in bf.fock_ops(2 * N)]
+    cd = [C.T for C in cs]
+    K = np.kron(np.eye(2), inputs.hopping_matrix(L, L, 1.0))
+    Kf = sum(K[a, b] * cd[a] @ cs[b] for a in range(2 * N) for b in range(2 * N) if K[a, b] != 0)
+    HI = np.zeros_like(Kf)
+    for i in range(N):
+        nu, nd = cd[i] @ cs[i], cd[N + i] @ cs[N + i]
+        HI = HI + U * (nu @ nd - 0.5 * (nu + nd))
+    T = scipy.linalg.expm(-dtau * HI) @ scipy.linalg.expm(-dtau * Kf)
+    P = inputs.sz_trial_state(L, ns)
+    psi = np.zeros(1 << (2 * N), np.complex128)
+    psi[0] = 1.0
+    for col in range(P.shape[1]):
+        psi = sum(P[a, col] * cd[a] for a in range(2 * N)) @ psi
+    right = np.linalg.matrix_power(T, M // 2) @ psi
+    left = psi.conj() @ np.linalg.matrix_power(T, M - M // 2)
+    norm = left @ right
+
+    def ev(O):
+        return complex(left @ O @ right / norm)
+
+    D = sum(ev(cd[i] @ cs[i] @ cd[N + i] @ cs[N + i]) for i in range(N)).real / N
+    Dp = [cd[i] @ cd[N + i] for i in range(N)]
+    Dm = [cs[N + i] @ cs[i] for i in range(N)]
+    P2 = sum(ev(Dp[i] @ Dm[j] + Dm[i] @ Dp[j]) for i in range(N) for j in range(N)).real / 4 / N ** 2
+    xs, ys = np.arange(N) % L, np.arange(N) // L
+
+    def ck(k, s):
+        ph = np.exp(-1j * (2 * np.pi * (k % L) / L * xs + 2 * np.pi * (k // L) / L * ys)) / np.sqrt(N)
+        return sum(ph[j] * cs[s * N + j] for j in range(N))
+
+    def minus(k):
+        return (L - k % L) % L + L * ((L - k // L) % L)
+
+    cu, cdn = [ck(k, 0) for k in range(N)], [ck(k, 1) for k in range(N)]
+    nk = np.array([ev(cu[k].conj().T @ cu[k]) for k in range(N)] + [ev(cdn[k].conj().T @ cdn[k]) for k in range(N)])
+    Mk = np.array([[ev(cu[k].conj().T @ cdn[minus(k)].conj().T @ cdn[minus(k2)] @ cu[k2]) for k2 in range(N)]
+                   for k in range(N)])
+    return D, P2, pairing.n_c(Mk, nk, L, 2 * ns)
+
+
+@pytest.mark.parametrize("mode", ["delayed", "blockfb"])
+def test_free_running_estimators_match_the_exact_2x2_projection(mode):
+    L, ns, U, dtau, two_theta = 2, 2, -4.0, 0.05, 2.0
+    M = int(round(two_theta / dtau))
+    D, P2, nc = _exact_2x2(L, ns, U, dtau, M)
+    out = pairing.main(["--L", str(L), "--ns", str(ns), "--U", str(U), "--dtau", str(dtau), "--two-theta",
+                        str(two_theta), "--walkers", "64", "--warmup", "4", "--sweeps", "24", "--bins", "12",
+                        "--mode", mode, "--k", "4", "--nb", "2", "--stab", "10", "--precision", "fp64", "--seed", "3"])
+    for name, exact in (("D", D), ("Delta2", P2), ("n_c", nc)):
+        mean, err = out[name]
+        assert err > 0 and abs(mean - exact) < 4 * err + 1e-4, (name, mean, err, exact)
+
+
+@pytest.mark.skipif(os.environ.get("AFQMC_TABLE_C1") != "1", reason="long run: set AFQMC_TABLE_C1=1")
+def test_table_c1_delayed_32_u_minus_4_half_filling():
+    rows = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "table_c1.txt")):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            rows[(f[0], f[1])] = [float(v) for v in f[2:]]
+    ref = rows[("A", "delayed32")]
+    out = pairing.main(["--L", "20", "--U", "-4", "--filling", "1.0", "--dtau", "0.05", "--two-theta", "46",
+                        "--walkers", "32", "--warmup", "20", "--sweeps", "40", "--mode", "delayed", "--k", "32"])
+    for q, (name, (mean, err)) in enumerate((("D", out["D"]), ("Delta2", out["Delta2"]), ("n_c", out["n_c"]))):
+        val, sig = ref[2 * q], ref[2 * q + 1]
+        assert abs(mean - val) < 2 * np.hypot(err, sig), (name, mean, err, val, sig)
