@@ -218,6 +218,46 @@ int afqmc_apply_flips_noalloc(int precision, int N, long long ld, void* G_up, vo
 #define AFQMC_FORM_T 1
 int afqmc_set_form(afqmc_ctx* ctx, int form);
 
+/* ---- Ground-state constrained-path AFQMC (CPQMC, Sec. IV.D, Eqs. CPWvfct1, CPWvfct2, ptilde) ----
+ * The ensemble |Psi> = sum_k w_k |phi_k> / <psi_T|phi_k> of the context's walkers, each a Slater
+ * determinant phi_k per spin (N x n_s, n_s = n_up = n_dn) carried in the T form: U_R = phi_k,
+ * U_L = psi_T^+ (fixed), T = (U_L U_R)^{-1}.  Requires a context with AFQMC_FORM_T, FP64 precision
+ * and one lattice for all walkers (afqmc_init_walkers builds the buffers; its fields are scratch
+ * for the current step).  AFQMC_ERR_STATE otherwise.
+ *
+ * afqmc_cp_init: psi_T = P (host, N x n_s row-major, the same for both spins and every walker),
+ *   phi_k = phi0 (host, nullable: per walker (in afqmc_init_walkers order) spin up then spin down,
+ *   each N x n_s; NULL starts every walker at P); weights 1.
+ * afqmc_cp_step: one projection step e^{-dtau K} then the fields of one slice for every walker:
+ *   the kinetic step multiplies w_k by <psi_T|e^{-dtau K} phi_k> / <psi_T|phi_k> (determinants of
+ *   U_L U_R before and after, from a fresh pivoted LU that also gives T); then every site i in
+ *   order draws its field from lambda(x) = p(x) s(x) r_up(x) r_dn(x), p = 1/2, s(x) the
+ *   decoupling's scalar (e^{-lam x} charge channel, 1 spin channel), r_s(x) = 1 + (e^{c_s x} - 1)
+ *   A_s[i][i] with A = U_R T U_L, negative lambda clamped to 0 (the constrained path),
+ *   x = +1 iff u_i < lambda(+1) / N_i, N_i = lambda(+1) + lambda(-1) (heat bath, Philox uniform
+ *   u_i of the walker's visit as in afqmc_sweep_slice), w_k <- w_k N_i; the chosen field updates
+ *   T and U_R as an accept of the delayed update: mode AFQMC_MODE_LOCAL (one site per window) or
+ *   AFQMC_MODE_DELAYED (windows of k sites, rank-k updates of T; the same fields and weights).
+ *   A walker whose overlap would change sign or whose N_i vanishes is removed (weight 0; its slot
+ *   holds a copy of a live walker's basis until the next afqmc_cp_comb).  logw_step (host,
+ *   nullable, one per walker): ln of the step's weight factor (-inf when removed).
+ *   AFQMC_ERR_NUMERIC when every walker is removed.
+ * afqmc_cp_comb: population control by the comb: with W the total weight, positions (q + u0) W / n_w
+ *   (0 <= u0 < 1) in the cumulative weights select walker idx[q] for slot q; every new weight is
+ *   W / n_w.  idx_out (host, nullable, n_w).
+ * afqmc_cp_reorth: re-orthonormalise every phi_k (pivoted LU basis of its columns), which changes
+ *   no weight (Eq. CPWvfct1 divides the scale out).
+ * afqmc_cp_energy: the mixed estimator E_L(k) = <psi_T|H|phi_k> / <psi_T|phi_k> per walker
+ *   (e_local, host, nullable) and sum_k w_k E_L(k) / sum_k w_k (e_mean, host, nullable).
+ * afqmc_cp_get_walker: phi_k (host, 2 N n_s doubles, nullable) and ln w_k (nullable).
+ * All sync the stream. */
+int afqmc_cp_init(afqmc_ctx* ctx, const double* P, const double* phi0, void* stream);
+int afqmc_cp_step(afqmc_ctx* ctx, int mode, int k, double* logw_step, void* stream);
+int afqmc_cp_comb(afqmc_ctx* ctx, double u0, int* idx_out, void* stream);
+int afqmc_cp_reorth(afqmc_ctx* ctx, void* stream);
+int afqmc_cp_energy(afqmc_ctx* ctx, double* e_local, double* e_mean, void* stream);
+int afqmc_cp_get_walker(afqmc_ctx* ctx, int walker, double* phi, double* logw);
+
 /* Profiling.  With profiling on, every phase of afqmc_sweep_slice / afqmc_recompute_G is
  * bracketed by CUDA events recorded on the call's stream (the stream its kernels run on).
  * Phases: */

@@ -28,7 +28,8 @@ EXPORTS = ["afqmc_create", "afqmc_destroy", "afqmc_init_walkers", "afqmc_sweep_s
            "afqmc_get_ratios", "afqmc_get_info", "afqmc_debug_uniforms", "afqmc_set_profiling", "afqmc_set_graphs",
            "afqmc_get_profile", "afqmc_launch_count", "afqmc_apply_flips", "afqmc_apply_flips_noalloc",
            "afqmc_debug_gemm", "afqmc_debug_dgemm", "afqmc_debug_ozaki_plan", "afqmc_debug_wait_timeout",
-           "afqmc_set_wrap", "afqmc_set_wrap_tile", "afqmc_set_form", "afqmc_strerror"]
+           "afqmc_set_wrap", "afqmc_set_wrap_tile", "afqmc_set_form", "afqmc_strerror", "afqmc_cp_init",
+           "afqmc_cp_step", "afqmc_cp_comb", "afqmc_cp_reorth", "afqmc_cp_energy", "afqmc_cp_get_walker"]
 WRAPS = {"dense": 0, "separable": 1}
 FORMS = {"G": 0, "T": 1}
 PHASES = ["prep", "wrap", "local", "chain", "flush", "recompute", "elim", "wrap_gemm", "flush_gemm", "lu_o",
@@ -84,6 +85,12 @@ def load(path: str = LIB_PATH):
     lib.afqmc_set_wrap.argtypes = [vp, ctypes.c_int]
     lib.afqmc_set_wrap_tile.argtypes = [vp, ctypes.c_int]
     lib.afqmc_set_form.argtypes = [vp, ctypes.c_int]
+    lib.afqmc_cp_init.argtypes = [vp, dp, dp, vp]
+    lib.afqmc_cp_step.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, vp]
+    lib.afqmc_cp_comb.argtypes = [vp, ctypes.c_double, ip, vp]
+    lib.afqmc_cp_reorth.argtypes = [vp, vp]
+    lib.afqmc_cp_energy.argtypes = [vp, dp, dp, vp]
+    lib.afqmc_cp_get_walker.argtypes = [vp, ctypes.c_int, dp, dp]
     lib.afqmc_get_profile.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.afqmc_launch_count.argtypes = []
     lib.afqmc_apply_flips.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, vp, vp, vp, vp, ctypes.c_int, vp]
@@ -238,6 +245,46 @@ def afqmc_set_form(ctx, form):
     _ck("afqmc_set_form", load().afqmc_set_form(ctx, FORMS.get(form, form)))
 
 
+def afqmc_cp_init(ctx, P, phi0=None, stream=None):
+    P = np.ascontiguousarray(P, np.float64)
+    phi = None if phi0 is None else np.ascontiguousarray(phi0, np.float64)
+    _ck("afqmc_cp_init", load().afqmc_cp_init(ctx, _ptr(P, ctypes.c_double), _ptr(phi, ctypes.c_double),
+                                              _stream(stream)))
+
+
+def afqmc_cp_step(ctx, n, mode, k=32, stream=None):
+    out = np.zeros(n)
+    _ck("afqmc_cp_step", load().afqmc_cp_step(ctx, MODES.get(mode, mode), int(k), _ptr(out, ctypes.c_double),
+                                              _stream(stream)))
+    return out
+
+
+def afqmc_cp_comb(ctx, n, u0, stream=None):
+    idx = np.zeros(n, np.int32)
+    _ck("afqmc_cp_comb", load().afqmc_cp_comb(ctx, float(u0), _ptr(idx, ctypes.c_int), _stream(stream)))
+    return idx
+
+
+def afqmc_cp_reorth(ctx, stream=None):
+    _ck("afqmc_cp_reorth", load().afqmc_cp_reorth(ctx, _stream(stream)))
+
+
+def afqmc_cp_energy(ctx, n, stream=None):
+    el = np.zeros(n)
+    em = np.zeros(1)
+    _ck("afqmc_cp_energy", load().afqmc_cp_energy(ctx, _ptr(el, ctypes.c_double), _ptr(em, ctypes.c_double),
+                                                  _stream(stream)))
+    return el, float(em[0])
+
+
+def afqmc_cp_get_walker(ctx, walker, N, ns):
+    phi = np.zeros((2, N, ns))
+    lw = np.zeros(1)
+    _ck("afqmc_cp_get_walker", load().afqmc_cp_get_walker(ctx, walker, _ptr(phi, ctypes.c_double),
+                                                          _ptr(lw, ctypes.c_double)))
+    return phi, float(lw[0])
+
+
 def afqmc_set_wrap_tile(ctx, width):
     _ck("afqmc_set_wrap_tile", load().afqmc_set_wrap_tile(ctx, int(width)))
 
@@ -377,3 +424,48 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+class CPContext:
+    """A constrained-path AFQMC ensemble (Sec. IV.D) of n_walkers determinants on an L x L lattice
+    with n_s particles per spin, guided by the trial determinant P (N x n_s, both spins): a
+    T-form FP64 context with one slice (its fields hold the current step's fields) and the
+    afqmc_cp_* entry points."""
+
+    def __init__(self, L, ns, n_walkers, P, phi0=None, dtau=0.05, U=4.0, t=1.0, hs=HS_SZ_REAL, seed=1,
+                 stream=None):
+        N = L * L
+        self.L, self.N, self.ns, self.n = L, N, ns, n_walkers
+        self.ctx = Context(1, dtau=dtau, U=U, t=t, precision="fp64", hs=hs, stab_every=1, seed=seed, form="T")
+        P = np.ascontiguousarray(P, np.float64)
+        Pw = np.concatenate([np.concatenate([P.ravel(), P.ravel()]) for _ in range(n_walkers)])
+        X = np.ones((n_walkers, 1, N), np.int8)
+        self.ctx.init_walkers([L] * n_walkers, [ns] * n_walkers, [ns] * n_walkers, Pw, X, stream)
+        afqmc_cp_init(self.ctx.h, P, phi0, stream)
+
+    def step(self, mode="delayed", k=16, stream=None):
+        return afqmc_cp_step(self.ctx.h, self.n, mode, k, stream)
+
+    def comb(self, u0, stream=None):
+        return afqmc_cp_comb(self.ctx.h, self.n, u0, stream)
+
+    def reorth(self, stream=None):
+        afqmc_cp_reorth(self.ctx.h, stream)
+
+    def energy(self, stream=None):
+        return afqmc_cp_energy(self.ctx.h, self.n, stream)
+
+    def walker(self, j):
+        return afqmc_cp_get_walker(self.ctx.h, j, self.N, self.ns)
+
+    def fields(self, j):
+        return self.ctx.fields(j)[0]
+
+    def close(self):
+        self.ctx.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

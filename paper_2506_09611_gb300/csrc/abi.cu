@@ -3,7 +3,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -131,6 +133,13 @@ struct Walker {
     void *ULI = nullptr, *URI = nullptr, *Vt = nullptr, *Yt = nullptr, *Ypt = nullptr, *Pt = nullptr;
     double* Ieye = nullptr;
     bool gvalid = true;  // the bulk G buffer holds the current G (the T form forms it on request)
+    // constrained-path AFQMC (afqmc_cp_*): per walker [sum ln N_i, sum ln |r_up r_dn|, removed, kinetic
+    // ln ratio], the tracked ln |det U_L U_R| (both spins), per matrix ln |det|, per walker the sign,
+    // and the walkers' ln weights (host)
+    double *cpl = nullptr, *cpdet = nullptr, *cpla = nullptr, *cpsg = nullptr, *cpsref = nullptr;
+    double* cptmp = nullptr;  // population control: [nwk][2 N n_s + 2 n_s^2 + 2] gather scratch
+    std::vector<double> cp_logw;
+    bool cp = false;
     std::vector<void*> allocs;
     long gstride() const { return 2L * N * ld; }
     int rows_max() const { return N > nsm ? N : nsm; }
@@ -1228,6 +1237,162 @@ static int sweep_impl(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int k,
 //          T <- T - V W Y with V = T U_L[:, I], Y = U_R[I, :] T (the G form's W by the push-through
 //          identity, Eq. BlkFrcBsTnew2) and the rows I of U_R scaled by the field change
 //          (Eq. UpdateLTRMat).
+// ---- constrained-path AFQMC helpers (Sec. IV.D) ----
+// la[z] = ln |det O_z| of the O = U_L U_R factored by launch_lu (U entries at the pivot rows).
+__global__ void cp_logdet_kernel(const double* O0, long os, const int* perm0, long ps, int ns, double* la) {
+    const int z = blockIdx.x;
+    const double* O = O0 + (size_t)z * os;
+    const int* perm = perm0 + (size_t)z * ps;
+    double acc = 0.0;
+    for (int c = threadIdx.x; c < ns; c += blockDim.x) acc += log(fabs(O[(size_t)perm[c] * ns + c]));
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        la[z] = s;
+    }
+}
+
+// Start of a step: clear the per-step sums (the removed flag stays) and the sign accumulator.
+__global__ void cp_begin_kernel(double* cpl, double* sg, int nwk) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nwk) return;
+    cpl[4 * j + 0] = 0.0;
+    cpl[4 * j + 1] = 0.0;
+    cpl[4 * j + 3] = 0.0;
+    sg[j] = 1.0;
+}
+
+// After the kinetic step's fresh determinant: the kinetic ln ratio against the tracked one, the
+// constraint (the overlap keeps the sign sref it had when the walker's basis was last set), and the
+// new tracked value.  set_ref (a new basis): only take the determinant and its sign as the reference.
+__global__ void cp_kinetic_kernel(double* cpl, double* det, const double* la, const double* sg, double* sref,
+                                  int nwk, int set_ref) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nwk) return;
+    const double now = la[2 * j] + la[2 * j + 1];
+    if (set_ref) {
+        sref[j] = sg[j];
+    } else {
+        cpl[4 * j + 3] = now - det[j];
+        if (!(sg[j] * sref[j] > 0.0)) cpl[4 * j + 2] = 1.0;
+    }
+    det[j] = now;
+}
+
+// End of a step: the tracked determinant follows the fields' ratios; out[j] = the step's ln weight
+// factor (-inf for a removed walker).
+__global__ void cp_finish_kernel(double* cpl, double* det, double* out, int nwk) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nwk) return;
+    det[j] += cpl[4 * j + 1];
+    out[j] = cpl[4 * j + 2] != 0.0 ? -INFINITY : cpl[4 * j + 3] + cpl[4 * j + 0];
+}
+
+// The window loop of the T form over the N sites of slice ell (Sec. II.C): per window J the block
+// 1 - (U_R[J, :] T) U_L[:, J], the window kernel (Metropolis modes, or the constrained-path heat bath
+// WIN_MODE_CP), then T <- T - (T U_L[:, I]) (W (U_R[I, :] T)) and the rows I of U_R times
+// exp(mul c_s x'_I) (mul = 2 for a flip, 1 for a field set from none).
+template <typename T>
+static int tform_windows(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int8_t* xl, int mode, int k, int nb,
+                         const SiteParams& sp, const uint8_t* rep, double* cp, double mul) {
+    const int N = w->N, nwk = w->nwk, ns = w->nsm, nb2 = 2 * nwk;
+    const int NW = window_max<T>();
+    const long fs = (long)N * ns;
+    T* UR = (T*)w->TUR;
+    T* UL = (T*)w->TUL;
+    T* TT = (T*)w->TT;
+    Batch bt;
+    bt.nwk = nwk;
+    bt.gstride = w->gstride();
+    bt.xstride = (long)ctx->p.M * N;
+    const double cm[2] = {mul * 0.5 * ctx->c[0], mul * 0.5 * ctx->c[1]};  // the scaling kernel applies exp(2 c x)
+    SliceOut so;
+    so.dec = w->dec;
+    so.ratio = w->ratio;
+    so.stats = w->stats;
+    so.maxr = w->maxr;
+    so.sign = w->sign;
+    so.cp = cp;
+    WindowBufs wb;
+    wb.m = w->wm[0];
+    wb.idx = w->widx[0];
+    wb.dtot = w->wdtot[0];
+    wb.Wm = w->Wm[0];
+    wb.Wx = w->Wx[0];
+    wb.X = w->X[0];
+    wb.Y = w->Y[0];
+    wb.nwk = nwk;
+    T* blk = (T*)w->snap[0];          // [nwk][2][NW x NW]: the window's block of G
+    T* P = (T*)w->Pt;                 // [nwk][2][NW x ns]: U_R[J, :] T
+    T* ULI = (T*)w->ULI;              // [nwk][2][ns x NW]
+    T* URI = (T*)w->URI;              // [nwk][2][NW x ns]
+    T* V = (T*)w->Vt;                 // [nwk][2][ns x NW]
+    T* Y = (T*)w->Yt;                 // [nwk][2][NW x ns]
+    T* Yp = (T*)w->Ypt;               // [nwk][2][NW x ns]
+    const long sB = (long)NW * NW, sP = (long)NW * ns, sT = (long)ns * ns;
+    {
+        PhaseScope ps(ctx, AFQMC_PHASE_CHAIN, st);
+        const int nw = (mode == AFQMC_MODE_BLOCKFB) ? (NW / nb) * nb : k;
+        for (int s0 = 0; s0 < N; s0 += nw) {
+            const int n = (N - s0 < nw) ? N - s0 : nw;
+            // the window's block of G: 1 - (U_R[J, :] T) U_L[:, J]
+            GemmArgs<T> g1;
+            g1.M = n; g1.N = ns; g1.K = ns; g1.batch = nb2;
+            g1.A = UR + (size_t)s0 * ns; g1.lda = ns; g1.sA = fs;
+            g1.B = TT; g1.ldb = ns; g1.sB = sT;
+            g1.C = P; g1.ldc = ns; g1.sC = sP;
+            CK(gemm<T>(st, g1));
+            GemmArgs<T> g2;
+            g2.M = n; g2.N = n; g2.K = ns; g2.batch = nb2;
+            g2.A = P; g2.lda = ns; g2.sA = sP;
+            g2.B = UL + s0; g2.ldb = N; g2.sB = fs;
+            g2.C = blk; g2.ldc = NW; g2.sC = sB;
+            CK(gemm<T>(st, g2));
+            CK(launch_identity_minus<T>(st, blk, NW, n, nb2, sB));
+            // decisions and the window's W
+            CK(launch_window_chain<T>(st, mode, (const T*)w->G, nullptr, xl, w->u, rep, sp, so, s0, n, nb, wb, blk,
+                                      w->err, bt));
+            // T <- T - (T U_L[:, I]) (W (U_R[I, :] T)), then the rows I of U_R
+            PhaseScope pf(ctx, AFQMC_PHASE_FLUSH, st);
+            CK(launch_tform_gather<T>(st, UR, UL, N, ns, ns, fs, fs, wb, ULI, URI, nb2));
+            GemmArgs<T> v;
+            v.M = ns; v.N = NW; v.K = ns; v.batch = nb2;
+            v.A = TT; v.lda = ns; v.sA = sT;
+            v.B = ULI; v.ldb = NW; v.sB = (long)ns * NW;
+            v.C = V; v.ldc = NW; v.sC = (long)ns * NW;
+            CK(gemm<T>(st, v));
+            GemmArgs<T> y;
+            y.M = NW; y.N = ns; y.K = ns; y.batch = nb2;
+            y.A = URI; y.lda = ns; y.sA = sP;
+            y.B = TT; y.ldb = ns; y.sB = sT;
+            y.C = Y; y.ldc = ns; y.sC = sP;
+            CK(gemm<T>(st, y));
+            GemmArgs<T> yp;  // Y' = W Y over the m accepted rows
+            yp.M = NW; yp.N = ns; yp.K = NW; yp.Kdev = wb.m; yp.kdiv = 2; yp.batch = nb2;
+            yp.A = (const T*)wb.Wx; yp.lda = NW; yp.sA = sB;
+            yp.B = Y; yp.ldb = ns; yp.sB = sP;
+            yp.C = Yp; yp.ldc = ns; yp.sC = sP;
+            CK(gemm<T>(st, yp));
+            GemmArgs<T> t;  // T -= V Y'
+            t.M = ns; t.N = ns; t.K = NW; t.Kdev = wb.m; t.kdiv = 2; t.batch = nb2;
+            t.A = V; t.lda = NW; t.sA = (long)ns * NW;
+            t.B = Yp; t.ldb = ns; t.sB = sP;
+            t.C = TT; t.ldc = ns; t.sC = sT;
+            t.alpha = T(-1); t.beta = T(1);
+            {
+                PhaseScope pg(ctx, AFQMC_PHASE_FLUSH_GEMM, st);
+                CK(gemm<T>(st, t));
+            }
+            CK(launch_tform_scale_rows<T>(st, UR, N, ns, ns, fs, wb, xl, bt.xstride, cm, nb2));
+        }
+    }
+    return AFQMC_OK;
+}
+
 template <typename T>
 static int sweep_impl_T(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int k, int nb, const uint8_t* replay,
                         cudaStream_t st) {
@@ -1240,7 +1405,6 @@ static int sweep_impl_T(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int 
     const long fs = (long)N * ns;
     T* UR = (T*)w->TUR;
     T* UL = (T*)w->TUL;
-    T* TT = (T*)w->TT;
     const uint8_t* rep = nullptr;
     Batch bt;
     bt.nwk = nwk;
@@ -1309,84 +1473,9 @@ static int sweep_impl_T(afqmc_ctx* ctx, int gi, int ell, int dir, int mode, int 
         const double x = xi == 0 ? 1.0 : -1.0;
         sp.sflip[xi] = (ctx->p.hs == AFQMC_HS_CHARGE_REAL) ? exp(2.0 * ctx->lam * x) : 1.0;
     }
-    SliceOut so;
-    so.dec = w->dec;
-    so.ratio = w->ratio;
-    so.stats = w->stats;
-    so.maxr = w->maxr;
-    so.sign = w->sign;
-    WindowBufs wb;
-    wb.m = w->wm[0];
-    wb.idx = w->widx[0];
-    wb.dtot = w->wdtot[0];
-    wb.Wm = w->Wm[0];
-    wb.Wx = w->Wx[0];
-    wb.X = w->X[0];
-    wb.Y = w->Y[0];
-    wb.nwk = nwk;
-    T* blk = (T*)w->snap[0];          // [nwk][2][NW x NW]: the window's block of G
-    T* P = (T*)w->Pt;                 // [nwk][2][NW x ns]: U_R[J, :] T
-    T* ULI = (T*)w->ULI;              // [nwk][2][ns x NW]
-    T* URI = (T*)w->URI;              // [nwk][2][NW x ns]
-    T* V = (T*)w->Vt;                 // [nwk][2][ns x NW]
-    T* Y = (T*)w->Yt;                 // [nwk][2][NW x ns]
-    T* Yp = (T*)w->Ypt;               // [nwk][2][NW x ns]
-    const long sB = (long)NW * NW, sP = (long)NW * ns, sT = (long)ns * ns;
     {
-        PhaseScope ps(ctx, AFQMC_PHASE_CHAIN, st);
-        const int nw = (mode == AFQMC_MODE_DELAYED) ? k : (NW / nb) * nb;
-        for (int s0 = 0; s0 < N; s0 += nw) {
-            const int n = (N - s0 < nw) ? N - s0 : nw;
-            // the window's block of G: 1 - (U_R[J, :] T) U_L[:, J]
-            GemmArgs<T> g1;
-            g1.M = n; g1.N = ns; g1.K = ns; g1.batch = nb2;
-            g1.A = UR + (size_t)s0 * ns; g1.lda = ns; g1.sA = fs;
-            g1.B = TT; g1.ldb = ns; g1.sB = sT;
-            g1.C = P; g1.ldc = ns; g1.sC = sP;
-            CK(gemm<T>(st, g1));
-            GemmArgs<T> g2;
-            g2.M = n; g2.N = n; g2.K = ns; g2.batch = nb2;
-            g2.A = P; g2.lda = ns; g2.sA = sP;
-            g2.B = UL + s0; g2.ldb = N; g2.sB = fs;
-            g2.C = blk; g2.ldc = NW; g2.sC = sB;
-            CK(gemm<T>(st, g2));
-            CK(launch_identity_minus<T>(st, blk, NW, n, nb2, sB));
-            // decisions and the window's W
-            CK(launch_window_chain<T>(st, mode, (const T*)w->G, nullptr, xl, w->u, rep, sp, so, s0, n, nb, wb, blk,
-                                      w->err, bt));
-            // T <- T - (T U_L[:, I]) (W (U_R[I, :] T)), then the rows I of U_R
-            PhaseScope pf(ctx, AFQMC_PHASE_FLUSH, st);
-            CK(launch_tform_gather<T>(st, UR, UL, N, ns, ns, fs, fs, wb, ULI, URI, nb2));
-            GemmArgs<T> v;
-            v.M = ns; v.N = NW; v.K = ns; v.batch = nb2;
-            v.A = TT; v.lda = ns; v.sA = sT;
-            v.B = ULI; v.ldb = NW; v.sB = (long)ns * NW;
-            v.C = V; v.ldc = NW; v.sC = (long)ns * NW;
-            CK(gemm<T>(st, v));
-            GemmArgs<T> y;
-            y.M = NW; y.N = ns; y.K = ns; y.batch = nb2;
-            y.A = URI; y.lda = ns; y.sA = sP;
-            y.B = TT; y.ldb = ns; y.sB = sT;
-            y.C = Y; y.ldc = ns; y.sC = sP;
-            CK(gemm<T>(st, y));
-            GemmArgs<T> yp;  // Y' = W Y over the m accepted rows
-            yp.M = NW; yp.N = ns; yp.K = NW; yp.Kdev = wb.m; yp.kdiv = 2; yp.batch = nb2;
-            yp.A = (const T*)wb.Wx; yp.lda = NW; yp.sA = sB;
-            yp.B = Y; yp.ldb = ns; yp.sB = sP;
-            yp.C = Yp; yp.ldc = ns; yp.sC = sP;
-            CK(gemm<T>(st, yp));
-            GemmArgs<T> t;  // T -= V Y'
-            t.M = ns; t.N = ns; t.K = NW; t.Kdev = wb.m; t.kdiv = 2; t.batch = nb2;
-            t.A = V; t.lda = NW; t.sA = (long)ns * NW;
-            t.B = Yp; t.ldb = ns; t.sB = sP;
-            t.C = TT; t.ldc = ns; t.sC = sT;
-            t.alpha = T(-1); t.beta = T(1);
-            {
-                PhaseScope pg(ctx, AFQMC_PHASE_FLUSH_GEMM, st);
-                CK(gemm<T>(st, t));
-            }
-            CK(launch_tform_scale_rows<T>(st, UR, N, ns, ns, fs, wb, xl, bt.xstride, ctx->c, nb2));
-        }
+        const int rc = tform_windows<T>(ctx, w, st, xl, mode, k, nb, sp, rep, nullptr, 2.0);
+        if (rc) return rc;
     }
     if (dir < 0) {
         CK(wrap(-1));
@@ -1604,6 +1693,299 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
                 rel_drift[w->gid[jw]] = h[2 * jw + 1] > 0 ? sqrt(h[2 * jw] / h[2 * jw + 1]) : 0.0;
         }
     }
+    return AFQMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// constrained-path AFQMC (Sec. IV.D) on the T-form walkers: U_R = phi_k, U_L = psi_T^+ fixed,
+// T = (U_L U_R)^{-1}; fields drawn by the window kernel's heat bath (WIN_MODE_CP)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+static int cp_check(afqmc_ctx* ctx, bool need_init) {
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (ctx->form != AFQMC_FORM_T || ctx->p.precision != AFQMC_PREC_FP64 || ctx->w.size() != 1) return AFQMC_ERR_STATE;
+    if (need_init && !ctx->w[0]->cp) return AFQMC_ERR_STATE;
+    return AFQMC_OK;
+}
+
+// O = U_L U_R (FP64), its pivoted LU, ln |det| per matrix and the sign per walker, T = O^{-1}, and
+// (cp_kinetic_kernel) the determinant bookkeeping.  set_ref: a new basis (init, re-orthonormalisation).
+static int cp_refresh(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int set_ref) {
+    const int N = w->N, ns = w->nsm, nwk = w->nwk, nb2 = 2 * nwk;
+    const long fs = (long)N * ns, os = (long)ns * ns;
+    GemmArgs<double> g;
+    g.M = ns; g.N = ns; g.K = N; g.batch = nb2;
+    g.A = (const double*)w->TUL; g.lda = N; g.sA = fs;
+    g.B = (const double*)w->TUR; g.ldb = ns; g.sB = fs;
+    g.C = w->Ob; g.ldc = ns; g.sC = os;
+    CK(gemm<double>(st, g));
+    const Fac O{w->Ob, 2 * os, os};
+    LuArgs a = lu_args(w, O, 0, 2, ns, ns, ns);
+    CK(launch_lu(st, a));
+    count_launch();
+    cp_begin_kernel<<<(nwk + 127) / 128, 128, 0, st>>>(w->cpl, w->cpsg, nwk);  // (re)sets the sign product
+    CK(cudaGetLastError());
+    CK(launch_lu_sign(st, a, 1, w->cpsg, w->visited));
+    count_launch();
+    cp_logdet_kernel<<<nb2, 256, 0, st>>>(w->Ob, os, w->perm2, w->rows_max(), ns, w->cpla);
+    CK(cudaGetLastError());
+    SolveArgs sa;
+    sa.LU0 = w->Ob; sa.ostride = os;
+    sa.perm0 = w->perm2; sa.pstride = w->rows_max();
+    sa.B0 = w->Ieye; sa.wstride = 0; sa.sstride = 0; sa.ng = 2;
+    sa.Z0 = (double*)w->TT; sa.zstride = os;
+    sa.ldl = ns; sa.ldb = ns; sa.ns = ns; sa.N = ns; sa.nmat = nb2;
+    CK(launch_lu_solve(st, sa));
+    count_launch();
+    cp_kinetic_kernel<<<(nwk + 127) / 128, 128, 0, st>>>(w->cpl, w->cpdet, w->cpla, w->cpsg, w->cpsref, nwk, set_ref);
+    CK(cudaGetLastError());
+    return AFQMC_OK;
+}
+
+extern "C" {
+
+int afqmc_cp_init(afqmc_ctx* ctx, const double* P, const double* phi0, void* stream) {
+    int rc = cp_check(ctx, false);
+    if (rc) return rc;
+    if (!P) return AFQMC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->last = st;
+    Walker* w = ctx->w[0];
+    const int N = w->N, ns = w->nsm, nwk = w->nwk;
+    const size_t fs = (size_t)N * ns;
+    if (!w->cpl) {
+        std::vector<void*>& A = w->allocs;
+        CK(dalloc(A, &w->cpl, (size_t)nwk * 4 * 8));
+        CK(dalloc(A, &w->cpdet, (size_t)nwk * 8));
+        CK(dalloc(A, &w->cpla, (size_t)nwk * 2 * 8));
+        CK(dalloc(A, &w->cpsg, (size_t)nwk * 8));
+        CK(dalloc(A, &w->cpsref, (size_t)nwk * 8));
+        CK(dalloc(A, &w->cptmp, (size_t)nwk * (2 * fs + 2 * (size_t)ns * ns + 2) * 8));
+    }
+    // U_L = P^T for every walker and spin; U_R = phi0 (or P)
+    std::vector<double> ul((size_t)nwk * 2 * fs), ur((size_t)nwk * 2 * fs);
+    for (int j = 0; j < nwk; ++j)
+        for (int sp = 0; sp < 2; ++sp) {
+            double* l = ul.data() + ((size_t)j * 2 + sp) * fs;
+            double* r = ur.data() + ((size_t)j * 2 + sp) * fs;
+            const double* src = phi0 ? phi0 + ((size_t)w->gid[j] * 2 + sp) * fs : P;
+            for (int i = 0; i < N; ++i)
+                for (int c = 0; c < ns; ++c) {
+                    l[(size_t)c * N + i] = P[(size_t)i * ns + c];
+                    r[(size_t)i * ns + c] = src[(size_t)i * ns + c];
+                }
+        }
+    CK(cudaMemcpyAsync(w->TUL, ul.data(), ul.size() * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w->TUR, ur.data(), ur.size() * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(w->cpl, 0, (size_t)nwk * 4 * 8, st));
+    CK(cudaMemsetAsync(w->cpdet, 0, (size_t)nwk * 8, st));
+    rc = cp_refresh(ctx, w, st, 1);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(st));  // the host staging goes out of scope
+    rc = read_dev_err(ctx, w);
+    if (rc) return rc;
+    w->cp_logw.assign(nwk, 0.0);
+    w->cp = true;
+    w->gvalid = false;
+    return AFQMC_OK;
+}
+
+int afqmc_cp_step(afqmc_ctx* ctx, int mode, int k, double* logw_step, void* stream) {
+    int rc = cp_check(ctx, true);
+    if (rc) return rc;
+    const int NW = window_max<double>();
+    if (mode == AFQMC_MODE_LOCAL) k = 1;
+    else if (mode != AFQMC_MODE_DELAYED || k < 1 || k > NW) return AFQMC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->last = st;
+    Walker* w = ctx->w[0];
+    const int N = w->N, ns = w->nsm, nwk = w->nwk;
+    const long fs = (long)N * ns, os = (long)ns * ns;
+    w->gvalid = false;
+    {
+        PhaseScope ps(ctx, AFQMC_PHASE_PREP, st);
+        CK(launch_uniforms(st, ctx->p.seed, w->gid_d, w->visit_d, 2 * N, w->u, nwk));
+        CK(cudaMemsetAsync(w->stats, 0, (size_t)nwk * 8 * sizeof(int), st));
+        CK(cudaMemsetAsync(w->maxr, 0, (size_t)nwk * 8, st));
+    }
+    {  // e^{-dtau K} phi: the separable passes over the site index of U_R (N x n_s)
+        PhaseScope ps(ctx, AFQMC_PHASE_WRAP, st);
+        SepArgs r;
+        r.G = w->TUR; r.ld = ns; r.sG = fs;
+        r.L = w->L; r.N = N; r.C = ns; r.batch = 2 * nwk; r.side = 0;
+        r.A = w->lat->Ex64; r.circ = 1; r.sv = N; r.w = ctx->sep_tile;
+        CK(launch_sep<double>(st, r));
+    }
+    {
+        PhaseScope ps(ctx, AFQMC_PHASE_RECOMPUTE, st);
+        rc = cp_refresh(ctx, w, st, 0);
+        if (rc) return rc;
+    }
+    SiteParams sp;
+    sp.N = N;
+    sp.ld = w->ld;
+    sp.c[0] = ctx->c[0];
+    sp.c[1] = ctx->c[1];
+    sp.lam = ctx->lam;
+    sp.hs = ctx->p.hs;
+    sp.seed = ctx->p.seed;
+    sp.walker = (uint64_t)w->gid[0];
+    sp.visit = w->visit;
+    for (int s = 0; s < 2; ++s)
+        for (int xi = 0; xi < 2; ++xi) {
+            const double x = xi == 0 ? 1.0 : -1.0;
+            sp.dflip[s][xi] = exp(ctx->c[s] * x) - 1.0;  // the field set from none
+            sp.dstrip[s][xi] = 0.0;
+        }
+    for (int xi = 0; xi < 2; ++xi) {
+        const double x = xi == 0 ? 1.0 : -1.0;
+        sp.sflip[xi] = 0.5 * ((ctx->p.hs == AFQMC_HS_CHARGE_REAL) ? exp(-ctx->lam * x) : 1.0);  // p(x) s(x)
+    }
+    rc = tform_windows<double>(ctx, w, st, w->x, WIN_MODE_CP, k, 0, sp, nullptr, w->cpl, 1.0);
+    if (rc) return rc;
+    count_launch();
+    cp_finish_kernel<<<(nwk + 127) / 128, 128, 0, st>>>(w->cpl, w->cpdet, w->acc2, nwk);
+    CK(cudaGetLastError());
+    CK(launch_bump(st, w->visit_d));
+    w->visit++;
+    CK(cudaStreamSynchronize(st));
+    rc = read_dev_err(ctx, w);
+    if (rc) return rc;
+    std::vector<double> h(nwk);
+    CK(cudaMemcpy(h.data(), w->acc2, (size_t)nwk * 8, cudaMemcpyDeviceToHost));
+    int src = -1;
+    for (int j = 0; j < nwk; ++j) {
+        w->cp_logw[j] += h[j];
+        if (logw_step) logw_step[w->gid[j]] = h[j];
+        if (src < 0 && std::isfinite(w->cp_logw[j])) src = j;
+    }
+    if (src < 0) return AFQMC_ERR_NUMERIC;  // every walker removed
+    // a removed walker keeps weight zero; its slot takes a copy of a live walker's basis so that its
+    // matrices stay regular until the next population control drops it
+    for (int j = 0; j < nwk; ++j) {
+        if (std::isfinite(w->cp_logw[j])) continue;
+        for (int sp2 = 0; sp2 < 2; ++sp2) {
+            CK(cudaMemcpyAsync((double*)w->TUR + ((size_t)j * 2 + sp2) * fs,
+                               (const double*)w->TUR + ((size_t)src * 2 + sp2) * fs, fs * 8,
+                               cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync((double*)w->TT + ((size_t)j * 2 + sp2) * os,
+                               (const double*)w->TT + ((size_t)src * 2 + sp2) * os, os * 8,
+                               cudaMemcpyDeviceToDevice, st));
+        }
+        CK(cudaMemcpyAsync(w->cpdet + j, w->cpdet + src, 8, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(w->cpsref + j, w->cpsref + src, 8, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemsetAsync(w->cpl + 4 * j + 2, 0, 8, st));
+    }
+    return AFQMC_OK;
+}
+
+int afqmc_cp_comb(afqmc_ctx* ctx, double u0, int* idx_out, void* stream) {
+    int rc = cp_check(ctx, true);
+    if (rc) return rc;
+    if (!(u0 >= 0.0 && u0 < 1.0)) return AFQMC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->last = st;
+    Walker* w = ctx->w[0];
+    const int nwk = w->nwk, N = w->N, ns = w->nsm;
+    const long fs = (long)N * ns, os = (long)ns * ns;
+    double mx = -INFINITY;
+    for (double v : w->cp_logw) mx = std::max(mx, v);
+    if (!std::isfinite(mx)) return AFQMC_ERR_NUMERIC;
+    std::vector<double> cum(nwk);
+    double tot = 0.0;
+    for (int j = 0; j < nwk; ++j) {
+        tot += std::isfinite(w->cp_logw[j]) ? exp(w->cp_logw[j] - mx) : 0.0;
+        cum[j] = tot;
+    }
+    std::vector<int> idx(nwk);
+    for (int q = 0; q < nwk; ++q) {
+        const double pos = (q + u0) * tot / nwk;
+        int j = (int)(std::upper_bound(cum.begin(), cum.end(), pos) - cum.begin());
+        idx[q] = std::min(j, nwk - 1);
+    }
+    double* tmp = w->cptmp;  // gather through scratch
+    const long per = 2 * fs + 2 * os + 2;
+    for (int q = 0; q < nwk; ++q) {
+        const int j = idx[q];
+        double* t = tmp + (size_t)q * per;
+        CK(cudaMemcpyAsync(t, (const double*)w->TUR + (size_t)j * 2 * fs, 2 * fs * 8, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(t + 2 * fs, (const double*)w->TT + (size_t)j * 2 * os, 2 * os * 8, cudaMemcpyDeviceToDevice,
+                           st));
+        CK(cudaMemcpyAsync(t + 2 * fs + 2 * os, w->cpdet + j, 8, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(t + 2 * fs + 2 * os + 1, w->cpsref + j, 8, cudaMemcpyDeviceToDevice, st));
+    }
+    for (int q = 0; q < nwk; ++q) {
+        const double* t = tmp + (size_t)q * per;
+        CK(cudaMemcpyAsync((double*)w->TUR + (size_t)q * 2 * fs, t, 2 * fs * 8, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync((double*)w->TT + (size_t)q * 2 * os, t + 2 * fs, 2 * os * 8, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(w->cpdet + q, t + 2 * fs + 2 * os, 8, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(w->cpsref + q, t + 2 * fs + 2 * os + 1, 8, cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaMemsetAsync(w->cpl, 0, (size_t)nwk * 4 * 8, st));
+    const double lw = mx + log(tot / nwk);
+    for (int q = 0; q < nwk; ++q) w->cp_logw[q] = lw;
+    w->gvalid = false;
+    if (idx_out)
+        for (int q = 0; q < nwk; ++q) idx_out[q] = w->gid[idx[q]];
+    CK(cudaStreamSynchronize(st));
+    return read_dev_err(ctx, w);
+}
+
+int afqmc_cp_reorth(afqmc_ctx* ctx, void* stream) {
+    int rc = cp_check(ctx, true);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->last = st;
+    Walker* w = ctx->w[0];
+    const Fac R{(double*)w->TUR, 2 * (long)w->N * w->nsm, (long)w->N * w->nsm};
+    CK(stab_rows(ctx, w, st, R, 0, 2, nullptr));
+    rc = cp_refresh(ctx, w, st, 1);
+    if (rc) return rc;
+    w->gvalid = false;
+    CK(cudaStreamSynchronize(st));
+    return read_dev_err(ctx, w);
+}
+
+int afqmc_cp_energy(afqmc_ctx* ctx, double* e_local, double* e_mean, void* stream) {
+    int rc = cp_check(ctx, true);
+    if (rc) return rc;
+    if (!e_local && !e_mean) return AFQMC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->last = st;
+    Walker* w = ctx->w[0];
+    CK(tform_form_G<double>(w, st));  // the mixed G = 1 - U_R T U_L
+    CK(cudaMemsetAsync(w->acc2, 0, (size_t)w->nwk * 16, st));
+    CK(launch_energy<double>(st, (const double*)w->G, w->ld, w->L, ctx->p.t, ctx->p.U, w->acc2, w->nwk,
+                             w->gstride()));
+    CK(cudaStreamSynchronize(st));
+    rc = read_dev_err(ctx, w);
+    if (rc) return rc;
+    std::vector<double> e(w->nwk);
+    CK(cudaMemcpy(e.data(), w->acc2, (size_t)w->nwk * 8, cudaMemcpyDeviceToHost));
+    double mx = -INFINITY, num = 0.0, den = 0.0;
+    for (double v : w->cp_logw) mx = std::max(mx, v);
+    for (int j = 0; j < w->nwk; ++j) {
+        if (e_local) e_local[w->gid[j]] = e[j];
+        const double wt = std::isfinite(w->cp_logw[j]) ? exp(w->cp_logw[j] - mx) : 0.0;
+        num += wt * e[j];
+        den += wt;
+    }
+    if (e_mean) *e_mean = den > 0.0 ? num / den : NAN;
+    return AFQMC_OK;
+}
+
+int afqmc_cp_get_walker(afqmc_ctx* ctx, int walker, double* phi, double* logw) {
+    int rc = cp_check(ctx, true);
+    if (rc) return rc;
+    if (walker < 0 || walker >= (int)ctx->wmap.size()) return AFQMC_ERR_ARG;
+    Walker* w = ctx->w[ctx->wmap[walker].first];
+    const int j = ctx->wmap[walker].second;
+    if (ctx->last) CK(cudaStreamSynchronize(ctx->last));
+    const size_t fs = (size_t)w->N * w->nsm;
+    if (phi) CK(cudaMemcpy(phi, (const double*)w->TUR + (size_t)j * 2 * fs, 2 * fs * 8, cudaMemcpyDeviceToHost));
+    if (logw) *logw = w->cp_logw[j];
     return AFQMC_OK;
 }
 

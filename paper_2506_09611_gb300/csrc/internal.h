@@ -214,7 +214,15 @@ struct SliceOut {      // device-side per-walker outputs of one slice
     int* stats;        // [proposals, accepts, flipped, flushes]
     double* maxr;      // max |R|
     double* sign;      // walker sign (updated in place)
+    double* cp = nullptr;  // constrained-path heat bath: per walker [sum ln N_i, sum ln |r_up r_dn|,
+                           // removed flag] (nullable; accumulated)
 };
+
+// The window kernel's constrained-path heat bath (Sec. IV.D; not a public sweep mode): every site
+// of the window gets a field drawn from lambda(x) = dflip-style constants -- SiteParams.dflip[s][xi]
+// = e^{c_s x} - 1 (the field set from none) and sflip[xi] = p(x) s(x) -- with the chosen one applied
+// as an accept of the delayed update.
+constexpr int WIN_MODE_CP = 16;
 
 // u[j][0..count) for the walkers gid[j] (device array), j < nwk, at the device visit counter;
 // launch_bump advances the counter by one.

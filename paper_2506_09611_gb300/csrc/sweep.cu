@@ -51,6 +51,7 @@ __device__ __forceinline__ SliceOut so_walker(SliceOut so, int j, int N) {
     so.stats += (size_t)j * 8;
     so.maxr += j;
     if (so.sign) so.sign += j;
+    if (so.cp) so.cp += (size_t)j * 4;
     return so;
 }
 
@@ -585,7 +586,16 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
     __syncthreads();
     int n_prop = 0, n_acc = 0, n_flip = 0;
 
-    if (MODE == AFQMC_MODE_DELAYED) {
+    __shared__ int8_t s_xch[WinCap<float>::NW];  // constrained path: the field chosen at each site
+    __shared__ double s_cpl[2];                  // constrained path: sum ln N_i, sum ln |r_up r_dn|
+    __shared__ int s_dead;
+    if (MODE == WIN_MODE_CP && tid == 0) {
+        s_cpl[0] = 0.0;
+        s_cpl[1] = 0.0;
+        s_dead = so.cp ? (so.cp[2] != 0.0) : 0;
+    }
+    __syncthreads();
+    if (MODE == AFQMC_MODE_DELAYED || MODE == WIN_MODE_CP) {
         // Warp-serial Metropolis, one accept ahead of the block update: warp 0 keeps its own copy
         // of the two diagonals, applies each accept's effect on them itself, and scans the next
         // sites (32 at a time: a rejection leaves G unchanged, a ballot finds the first
@@ -612,7 +622,49 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                     __syncwarp();
                 }
                 int next = -1;
-                while (p < n) {
+                if (MODE == WIN_MODE_CP) {
+                    // constrained-path heat bath (Sec. IV.D, Eq. ptilde): lane 0 draws the field of
+                    // site p from lambda(x) = p(x) s(x) r_up(x) r_dn(x), r_s(x) = 1 + (e^{c_s x} - 1)
+                    // (1 - G_pp), negative lambda clamped to zero (the constraint); the walker is
+                    // removed when both vanish.  Every site is an accept of the delayed update.
+                    if (p < n && !s_dead) {
+                        if (tid == 0) {
+                            const int q = p;
+                            const T a0 = T(1) - dg[q], a1 = T(1) - dg[n + q];
+                            const T rp0 = T(1) + c_dflipT[0][0] * a0, rp1 = T(1) + c_dflipT[1][0] * a1;
+                            const T rm0 = T(1) + c_dflipT[0][1] * a0, rm1 = T(1) + c_dflipT[1][1] * a1;
+                            const T lp = fmax(c_sflipT[0] * rp0 * rp1, T(0));
+                            const T lm = fmax(c_sflipT[1] * rm0 * rm1, T(0));
+                            const T nrm = lp + lm;
+                            if (!(nrm > T(0)) || !isfinite(nrm)) {
+                                s_dead = 1;
+                                if (!isfinite(nrm)) set_err(err, DEV_NUMERIC);
+                            } else {
+                                const bool plus = replay ? (s_rep[q] != 0) : (s_u[q] < lp / nrm);
+                                const int xi = plus ? 0 : 1;
+                                const T r0 = plus ? rp0 : rm0, r1 = plus ? rp1 : rm1;
+                                s_fk[0][m_w0] = -(c_dflipT[0][xi] / r0);
+                                s_fk[1][m_w0] = -(c_dflipT[1][xi] / r1);
+                                idx[m_w0] = q;
+                                s_xch[m_w0] = plus ? 1 : -1;
+                                s_dec[q] = plus ? 1 : 0;
+                                s_rat[q] = nrm;
+                                s_cpl[0] += log((double)nrm);
+                                s_cpl[1] += log(fabs((double)r0 * (double)r1));
+                                next = m_w0;
+                            }
+                        }
+                        next = __shfl_sync(0xffffffffu, next, 0);
+                        if (next >= 0) {
+                            ++m_w0;
+                            ++n_acc;
+                            ++n_flip;
+                        }
+                        ++n_prop;
+                        p = (next >= 0) ? p + 1 : n;
+                    }
+                }
+                while (MODE == AFQMC_MODE_DELAYED && p < n) {
                     // ratio arithmetic in the bulk precision T (FP64 division on this critical path
                     // would cost thousands of cycles on GB300's FP64 pipe)
                     const int q = p + tid;
@@ -843,6 +895,15 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
         for (int q = tid; q < m; q += nt) xw[idx[q]] = (int8_t)(-xw[idx[q]]);
         __syncthreads();
     }
+    if (MODE == WIN_MODE_CP) {  // the chosen fields, and the walker's weight factors
+        for (int q = tid; q < m; q += nt) xw[idx[q]] = s_xch[q];
+        if (tid == 0 && so.cp) {
+            so.cp[0] += s_cpl[0];
+            so.cp[1] += s_cpl[1];
+            if (s_dead) so.cp[2] = 1.0;
+        }
+        __syncthreads();
+    }
     for (int p = tid; p < n; p += nt) xl_g[s0 + p] = xw[p];
     for (int q = tid; q < m; q += nt) {
         wb.idx[q] = s0 + idx[q];
@@ -877,6 +938,7 @@ cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T*
     (void)Gd;  // spin down follows spin up (N x ld) in every walker's G
     size_t shm = window_smem<T>(n);
     auto kfn = (mode == AFQMC_MODE_DELAYED) ? (const void*)window_kernel<T, AFQMC_MODE_DELAYED>
+               : (mode == WIN_MODE_CP)     ? (const void*)window_kernel<T, WIN_MODE_CP>
                                             : (const void*)window_kernel<T, AFQMC_MODE_BLOCKFB>;
     {
         cudaError_t e = ensure_smem_attr(kfn, window_smem<T>(WinCap<T>::NW));
@@ -887,6 +949,9 @@ cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T*
     if (mode == AFQMC_MODE_DELAYED)
         window_kernel<T, AFQMC_MODE_DELAYED><<<bt.nwk, WIN_THREADS, shm, st>>>(Gu, xl, u, replay, sp, so, s0, n, nb,
                                                                               wb, blk, err, bt);
+    else if (mode == WIN_MODE_CP)
+        window_kernel<T, WIN_MODE_CP><<<bt.nwk, WIN_THREADS, shm, st>>>(Gu, xl, u, replay, sp, so, s0, n, nb, wb,
+                                                                       blk, err, bt);
     else
         window_kernel<T, AFQMC_MODE_BLOCKFB><<<bt.nwk, WIN_THREADS, shm, st>>>(Gu, xl, u, replay, sp, so, s0, n, nb,
                                                                               wb, blk, err, bt);
