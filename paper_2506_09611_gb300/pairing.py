@@ -8,10 +8,11 @@ from which the condensate fraction n_c = lambda_max / (N_e / 2) follows (afqmc_s
     python -m paper_2506_09611_gb300.pairing --L 20 --U -4 --filling 1.0 --dtau 0.05 --two-theta 46 \\
         --walkers 32 --warmup 20 --sweeps 40 --mode delayed --k 32 --out pairing.json
 
-Statistics.  Walkers are independent chains; the measurements of all walkers at one half sweep form
-a round, consecutive rounds are grouped into `--bins` blocks, and D, <Delta^2> and n_c take their
-mean and a jackknife error over the blocks (n_c from each jackknife sample's averaged matrix
-M[k][k'] - delta_kk' <n_{k up}> <n_{-k dn}>, Hermitian part, largest eigenvalue).
+Statistics.  Walkers are independent chains: D and <Delta^2> take the mean over the walkers of each
+walker's time average and its standard error.  The pairing matrix comes summed over the walkers, so
+n_c takes a jackknife over `--bins` consecutive blocks of half sweeps (each block's averaged
+M[k][k'] - delta_kk' <n_{k up}> <n_{-k dn}>, Hermitian part, largest eigenvalue); blocks several
+sweeps long keep their correlation small.
 """
 import argparse
 import json
@@ -69,7 +70,7 @@ def run(a):
                     ctx.recompute_G(stream=stream)
                 if pos == mid and sweep >= a.warmup:
                     r = ctx.measure_pairing(stream=stream)
-                    rounds.append((r["D"].real.mean(), r["Delta2"].real.mean(), r["Mk"] / a.walkers,
+                    rounds.append((r["D"].real.copy(), r["Delta2"].real.copy(), r["Mk"] / a.walkers,
                                    r["nk"].mean(axis=0)))
                     dec = np.concatenate([ctx.decisions(w)[:N] for w in range(a.walkers)])
                     if a.mode != "blockfb":
@@ -78,14 +79,14 @@ def run(a):
             if a.verbose:
                 print(f"sweep {sweep + 1}/{a.warmup + a.sweeps}: {time.perf_counter() - t0:.1f} s", flush=True)
     secs = time.perf_counter() - t0
+    Dw = np.mean([r[0] for r in rounds], axis=0)  # per-walker time averages
+    Pw = np.mean([r[1] for r in rounds], axis=0)
+    D = (float(Dw.mean()), float(Dw.std(ddof=1) / np.sqrt(len(Dw))) if len(Dw) > 1 else float("nan"))
+    P2 = (float(Pw.mean()), float(Pw.std(ddof=1) / np.sqrt(len(Pw))) if len(Pw) > 1 else float("nan"))
     nb = max(1, min(a.bins, len(rounds)))
     blocks = np.array_split(np.arange(len(rounds)), nb)
-    Db = np.array([np.mean([rounds[i][0] for i in b]) for b in blocks])
-    Pb = np.array([np.mean([rounds[i][1] for i in b]) for b in blocks])
     Mb = np.array([np.mean([rounds[i][2] for i in b], axis=0) for b in blocks])
     nkb = np.array([np.mean([rounds[i][3] for i in b], axis=0) for b in blocks])
-    D = jackknife(Db, lambda x: x)
-    P2 = jackknife(Pb, lambda x: x)
     packed = np.concatenate([Mb.reshape(nb, -1), nkb], axis=1)
     nc = jackknife(packed, lambda x: n_c(x[:N * N].reshape(N, N), x[N * N:], L, 2 * ns))
     out = {"model": "attractive Hubbard, imaginary spin-z decoupling (spin-coupled engine, lam = 0)",
@@ -108,7 +109,7 @@ def main(argv=None):
     ap.add_argument("--walkers", type=int, default=32)
     ap.add_argument("--warmup", type=int, default=20, help="sweeps (out and back) before measuring")
     ap.add_argument("--sweeps", type=int, default=40, help="measured sweeps")
-    ap.add_argument("--bins", type=int, default=10)
+    ap.add_argument("--bins", type=int, default=5)
     ap.add_argument("--mode", default="delayed", choices=["local", "delayed", "blockfb"])
     ap.add_argument("--k", type=int, default=32)
     ap.add_argument("--nb", type=int, default=16)

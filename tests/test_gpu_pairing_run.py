@@ -7,7 +7,8 @@ mixed expectation <psi_T| T^{M/2} O T^{M/2} |psi_T> / <psi_T| T^M |psi_T>, T = e
 running chains must reproduce it within their error bars (Eq. GSObsQMC).
 
 The comparison with the paper's own L = 20 values (Table C1, tests/golden/table_c1.txt) is a long
-run (about ten minutes of one GPU per parameter set); it runs only with AFQMC_TABLE_C1=1.
+run (about 55 s of one GPU per sweep of 32 walkers, M = 920, so some 35 minutes for 12 + 24 sweeps);
+it runs only with AFQMC_TABLE_C1=1.
 """
 import os
 
@@ -72,7 +73,7 @@ def test_free_running_estimators_match_the_exact_2x2_projection(mode):
     M = int(round(two_theta / dtau))
     D, P2, nc = _exact_2x2(L, ns, U, dtau, M)
     out = pairing.main(["--L", str(L), "--ns", str(ns), "--U", str(U), "--dtau", str(dtau), "--two-theta",
-                        str(two_theta), "--walkers", "64", "--warmup", "4", "--sweeps", "24", "--bins", "12",
+                        str(two_theta), "--walkers", "64", "--warmup", "4", "--sweeps", "24", "--bins", "4",
                         "--mode", mode, "--k", "4", "--nb", "2", "--stab", "10", "--precision", "fp64", "--seed", "3"])
     for name, exact in (("D", D), ("Delta2", P2), ("n_c", nc)):
         mean, err = out[name]
@@ -88,7 +89,7 @@ def test_table_c1_delayed_32_u_minus_4_half_filling():
             rows[(f[0], f[1])] = [float(v) for v in f[2:]]
     ref = rows[("A", "delayed32")]
     out = pairing.main(["--L", "20", "--U", "-4", "--filling", "1.0", "--dtau", "0.05", "--two-theta", "46",
-                        "--walkers", "32", "--warmup", "20", "--sweeps", "40", "--mode", "delayed", "--k", "32"])
+                        "--walkers", "32", "--warmup", "12", "--sweeps", "24", "--mode", "delayed", "--k", "32"])
     for q, (name, (mean, err)) in enumerate((("D", out["D"]), ("Delta2", out["Delta2"]), ("n_c", out["n_c"]))):
         val, sig = ref[2 * q], ref[2 * q + 1]
         assert abs(mean - val) < 2 * np.hypot(err, sig), (name, mean, err, val, sig)
