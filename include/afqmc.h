@@ -238,6 +238,11 @@ int afqmc_set_form(afqmc_ctx* ctx, int form);
  *   u_i of the walker's visit as in afqmc_sweep_slice), w_k <- w_k N_i; the chosen field updates
  *   T and U_R as an accept of the delayed update: mode AFQMC_MODE_LOCAL (one site per window) or
  *   AFQMC_MODE_DELAYED (windows of k sites, rank-k updates of T; the same fields and weights).
+ *   AFQMC_MODE_BLOCKFB (blocks of nb <= 32 sites): the force bias F_i of a block's sites before any
+ *   is set (spin channel sum_s c_s A_s[i][i], charge channel lam (A_up + A_dn - 1)[i][i]), each
+ *   x_i drawn from e^{x_i F_i} / (2 cosh F_i) (site uniforms), and w_k times
+ *   prod_i s(x_i) cosh F_i e^{-x_i F_i} prod_s det(1 + Delta_s A_s[S][S]), removed when that
+ *   factor is <= 0 (nb = 1 is a heat bath with the linearised weights).
  *   A walker whose overlap would change sign or whose N_i vanishes is removed (weight 0; its slot
  *   holds a copy of a live walker's basis until the next afqmc_cp_comb).  logw_step (host,
  *   nullable, one per walker): ln of the step's weight factor (-inf when removed).
@@ -252,7 +257,7 @@ int afqmc_set_form(afqmc_ctx* ctx, int form);
  * afqmc_cp_get_walker: phi_k (host, 2 N n_s doubles, nullable) and ln w_k (nullable).
  * All sync the stream. */
 int afqmc_cp_init(afqmc_ctx* ctx, const double* P, const double* phi0, void* stream);
-int afqmc_cp_step(afqmc_ctx* ctx, int mode, int k, double* logw_step, void* stream);
+int afqmc_cp_step(afqmc_ctx* ctx, int mode, int k, int nb, double* logw_step, void* stream);
 int afqmc_cp_comb(afqmc_ctx* ctx, double u0, int* idx_out, void* stream);
 int afqmc_cp_reorth(afqmc_ctx* ctx, void* stream);
 int afqmc_cp_energy(afqmc_ctx* ctx, double* e_local, double* e_mean, void* stream);

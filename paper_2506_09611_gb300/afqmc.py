@@ -86,7 +86,7 @@ def load(path: str = LIB_PATH):
     lib.afqmc_set_wrap_tile.argtypes = [vp, ctypes.c_int]
     lib.afqmc_set_form.argtypes = [vp, ctypes.c_int]
     lib.afqmc_cp_init.argtypes = [vp, dp, dp, vp]
-    lib.afqmc_cp_step.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, vp]
+    lib.afqmc_cp_step.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, vp]
     lib.afqmc_cp_comb.argtypes = [vp, ctypes.c_double, ip, vp]
     lib.afqmc_cp_reorth.argtypes = [vp, vp]
     lib.afqmc_cp_energy.argtypes = [vp, dp, dp, vp]
@@ -252,10 +252,10 @@ def afqmc_cp_init(ctx, P, phi0=None, stream=None):
                                               _stream(stream)))
 
 
-def afqmc_cp_step(ctx, n, mode, k=32, stream=None):
+def afqmc_cp_step(ctx, n, mode, k=32, nb=4, stream=None):
     out = np.zeros(n)
-    _ck("afqmc_cp_step", load().afqmc_cp_step(ctx, MODES.get(mode, mode), int(k), _ptr(out, ctypes.c_double),
-                                              _stream(stream)))
+    _ck("afqmc_cp_step", load().afqmc_cp_step(ctx, MODES.get(mode, mode), int(k), int(nb),
+                                              _ptr(out, ctypes.c_double), _stream(stream)))
     return out
 
 
@@ -443,8 +443,8 @@ class CPContext:
         self.ctx.init_walkers([L] * n_walkers, [ns] * n_walkers, [ns] * n_walkers, Pw, X, stream)
         afqmc_cp_init(self.ctx.h, P, phi0, stream)
 
-    def step(self, mode="delayed", k=16, stream=None):
-        return afqmc_cp_step(self.ctx.h, self.n, mode, k, stream)
+    def step(self, mode="delayed", k=16, nb=4, stream=None):
+        return afqmc_cp_step(self.ctx.h, self.n, mode, k, nb, stream)
 
     def comb(self, u0, stream=None):
         return afqmc_cp_comb(self.ctx.h, self.n, u0, stream)

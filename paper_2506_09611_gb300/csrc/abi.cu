@@ -1336,7 +1336,7 @@ static int tform_windows(afqmc_ctx* ctx, Walker* w, cudaStream_t st, int8_t* xl,
     const long sB = (long)NW * NW, sP = (long)NW * ns, sT = (long)ns * ns;
     {
         PhaseScope ps(ctx, AFQMC_PHASE_CHAIN, st);
-        const int nw = (mode == AFQMC_MODE_BLOCKFB) ? (NW / nb) * nb : k;
+        const int nw = (mode == AFQMC_MODE_BLOCKFB || mode == WIN_MODE_CPB) ? (NW / nb) * nb : k;
         for (int s0 = 0; s0 < N; s0 += nw) {
             const int n = (N - s0 < nw) ? N - s0 : nw;
             // the window's block of G: 1 - (U_R[J, :] T) U_L[:, J]
@@ -1792,12 +1792,14 @@ int afqmc_cp_init(afqmc_ctx* ctx, const double* P, const double* phi0, void* str
     return AFQMC_OK;
 }
 
-int afqmc_cp_step(afqmc_ctx* ctx, int mode, int k, double* logw_step, void* stream) {
+int afqmc_cp_step(afqmc_ctx* ctx, int mode, int k, int nb, double* logw_step, void* stream) {
     int rc = cp_check(ctx, true);
     if (rc) return rc;
     const int NW = window_max<double>();
     if (mode == AFQMC_MODE_LOCAL) k = 1;
-    else if (mode != AFQMC_MODE_DELAYED || k < 1 || k > NW) return AFQMC_ERR_ARG;
+    else if (mode == AFQMC_MODE_BLOCKFB && (nb < 1 || nb > 32)) return AFQMC_ERR_ARG;
+    else if (mode == AFQMC_MODE_DELAYED && (k < 1 || k > NW)) return AFQMC_ERR_ARG;
+    else if (mode != AFQMC_MODE_DELAYED && mode != AFQMC_MODE_BLOCKFB) return AFQMC_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     ctx->last = st;
     Walker* w = ctx->w[0];
@@ -1843,7 +1845,8 @@ int afqmc_cp_step(afqmc_ctx* ctx, int mode, int k, double* logw_step, void* stre
         const double x = xi == 0 ? 1.0 : -1.0;
         sp.sflip[xi] = 0.5 * ((ctx->p.hs == AFQMC_HS_CHARGE_REAL) ? exp(-ctx->lam * x) : 1.0);  // p(x) s(x)
     }
-    rc = tform_windows<double>(ctx, w, st, w->x, WIN_MODE_CP, k, 0, sp, nullptr, w->cpl, 1.0);
+    rc = tform_windows<double>(ctx, w, st, w->x, mode == AFQMC_MODE_BLOCKFB ? WIN_MODE_CPB : WIN_MODE_CP, k, nb, sp,
+                               nullptr, w->cpl, 1.0);
     if (rc) return rc;
     count_launch();
     cp_finish_kernel<<<(nwk + 127) / 128, 128, 0, st>>>(w->cpl, w->cpdet, w->acc2, nwk);

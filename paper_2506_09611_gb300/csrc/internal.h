@@ -223,6 +223,9 @@ struct SliceOut {      // device-side per-walker outputs of one slice
 // = e^{c_s x} - 1 (the field set from none) and sflip[xi] = p(x) s(x) -- with the chosen one applied
 // as an accept of the delayed update.
 constexpr int WIN_MODE_CP = 16;
+// ... and its block force bias (blocks of nb sites drawn from the force bias, weight factor by the
+// block's determinant; the same constants).
+constexpr int WIN_MODE_CPB = 17;
 
 // u[j][0..count) for the walkers gid[j] (device array), j < nwk, at the device visit counter;
 // launch_bump advances the counter by one.

@@ -736,6 +736,98 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
             s_maxr = fmax(s_maxr, (double)s_maxrT);
         }
         __syncthreads();
+    } else if (MODE == WIN_MODE_CPB) {
+        // ---- constrained-path block force bias (Sec. IV.D) ----
+        // Per block S of nb sites (no field set yet): the force bias F_i of the current block's
+        // diagonal (spin channel sum_s c_s A_s[i][i], charge channel lam (A_up + A_dn - 1)[i][i]),
+        // each x_i from q(x_i) = e^{x_i F_i} / (2 cosh F_i); the weight factor
+        // prod_i s(x_i) cosh F_i e^{-x_i F_i} prod_s det(1 + Delta_s A_s[S][S]) (the determinant as the
+        // product of the sequential rank-1 ratios on a copy of the block); a factor <= 0 removes the
+        // walker; the fields are then applied as accepts of the delayed update.
+        __shared__ T s_phi2[2][NBMAX];
+        __shared__ double s_rs2[2];
+        T* strow = stc + 2 * n;  // [2][n]
+        for (int p0 = 0; p0 < n && !s_dead; p0 += nb) {
+            const int nbk = min(nb, n - p0);
+            if (tid < nbk) {
+                const int a = tid, i = s0 + p0 + a;
+                const double a0 = 1.0 - (double)Gs[(0 * n + p0 + a) * P + p0 + a];
+                const double a1 = 1.0 - (double)Gs[(1 * n + p0 + a) * P + p0 + a];
+                const double F = sp.hs == AFQMC_HS_CHARGE_REAL ? sp.lam * (a0 + a1 - 1.0) : sp.c[0] * a0 + sp.c[1] * a1;
+                const double lamp = 1.0 / (1.0 + exp(-2.0 * F));
+                const int xp = replay ? (replay[i] ? 1 : -1) : (u[i] < lamp ? 1 : -1);
+                so.dec[i] = xp > 0 ? 1 : 0;
+                so.ratio[i] = lamp;
+                fb[0 * NBMAX + a] = hs_log_scalar(sp, xp) + log(cosh(F)) - xp * F;
+                s_xch[s_m + a] = (int8_t)xp;
+            }
+            for (int e = tid; e < 2 * nbk * nbk; e += nt) {
+                int sp2 = e / (nbk * nbk), rem = e % (nbk * nbk), a = rem / nbk, c = rem % nbk;
+                S1[(sp2 * NBMAX + a) * (NBMAX + 1) + c] = Gs[(sp2 * n + p0 + a) * P + p0 + c];
+            }
+            if (tid == 0) {
+                s_rs2[0] = 1.0;
+                s_rs2[1] = 1.0;
+            }
+            __syncthreads();
+            const int mb = s_m;
+            for (int q = 0; q < nbk; ++q) {
+                for (int e = tid; e < 2 * nbk; e += nt) {
+                    int sp2 = e / nbk, c = e % nbk;
+                    T* Sb = S1 + sp2 * NBMAX * (NBMAX + 1);
+                    stb[sp2 * NBMAX + c] = Sb[c * (NBMAX + 1) + q];
+                    strow[sp2 * n + c] = (c == q ? T(1) : T(0)) - Sb[q * (NBMAX + 1) + c];
+                }
+                if (tid < 2) {
+                    const int xi = s_xch[mb + q] > 0 ? 0 : 1;
+                    const T dd = c_dflipT[tid][xi];
+                    const T rr = T(1) + dd * (T(1) - S1[(tid * NBMAX + q) * (NBMAX + 1) + q]);
+                    s_rs2[tid] *= (double)rr;
+                    s_phi2[tid][q] = dd / rr;
+                }
+                __syncthreads();
+                for (int e = tid; e < 2 * nbk * nbk; e += nt) {
+                    int sp2 = e / (nbk * nbk), rem = e % (nbk * nbk), r = rem / nbk, c = rem % nbk;
+                    T* Sb = S1 + sp2 * NBMAX * (NBMAX + 1);
+                    Sb[r * (NBMAX + 1) + c] -= s_phi2[sp2][q] * stb[sp2 * NBMAX + r] * strow[sp2 * n + c];
+                }
+                __syncthreads();
+            }
+            if (tid == 0) {
+                double lw = 0.0;
+                for (int a = 0; a < nbk; ++a) lw += fb[0 * NBMAX + a];
+                const double det = s_rs2[0] * s_rs2[1];
+                const int blk = (s0 + p0) / nb;
+                so.ratio[N + blk] = det;
+                if (!(det > 0.0) || !isfinite(det)) {
+                    s_dead = 1;
+                    if (!isfinite(det)) set_err(err, DEV_NUMERIC);
+                } else {
+                    s_cpl[0] += lw + log(det);
+                    s_cpl[1] += log(det);
+                }
+                so.dec[N + blk] = s_dead ? 0 : 1;
+            }
+            __syncthreads();
+            if (s_dead) break;
+            ++n_prop;
+            ++n_acc;
+            n_flip += nbk;
+            for (int q = 0; q < nbk; ++q) {
+                const int a = p0 + q, k = mb + q;
+                if (tid == 0) {
+                    idx[k] = a;
+                    s_fk[0][k] = -s_phi2[0][q];
+                    s_fk[1][k] = -s_phi2[1][q];
+                    dl[0 * n + k] = -(double)s_phi2[0][q];
+                    dl[1 * n + k] = -(double)s_phi2[1][q];
+                }
+                trailing_update(Gs, n, P, a, s_phi2[0][q], s_phi2[1][q], tid, nt);
+                __syncthreads();
+            }
+            if (tid == 0) s_m = mb + nbk;
+            __syncthreads();
+        }
     } else {
         // ---- block force-bias (Sec. III.B) ----
         __shared__ T s_fs[2];
@@ -895,7 +987,7 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
         for (int q = tid; q < m; q += nt) xw[idx[q]] = (int8_t)(-xw[idx[q]]);
         __syncthreads();
     }
-    if (MODE == WIN_MODE_CP) {  // the chosen fields, and the walker's weight factors
+    if (MODE == WIN_MODE_CP || MODE == WIN_MODE_CPB) {  // the chosen fields, and the walker's weight factors
         for (int q = tid; q < m; q += nt) xw[idx[q]] = s_xch[q];
         if (tid == 0 && so.cp) {
             so.cp[0] += s_cpl[0];
@@ -939,6 +1031,7 @@ cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T*
     size_t shm = window_smem<T>(n);
     auto kfn = (mode == AFQMC_MODE_DELAYED) ? (const void*)window_kernel<T, AFQMC_MODE_DELAYED>
                : (mode == WIN_MODE_CP)     ? (const void*)window_kernel<T, WIN_MODE_CP>
+               : (mode == WIN_MODE_CPB)    ? (const void*)window_kernel<T, WIN_MODE_CPB>
                                             : (const void*)window_kernel<T, AFQMC_MODE_BLOCKFB>;
     {
         cudaError_t e = ensure_smem_attr(kfn, window_smem<T>(WinCap<T>::NW));
@@ -952,6 +1045,9 @@ cudaError_t launch_window_chain(cudaStream_t st, int mode, const T* Gu, const T*
     else if (mode == WIN_MODE_CP)
         window_kernel<T, WIN_MODE_CP><<<bt.nwk, WIN_THREADS, shm, st>>>(Gu, xl, u, replay, sp, so, s0, n, nb, wb,
                                                                        blk, err, bt);
+    else if (mode == WIN_MODE_CPB)
+        window_kernel<T, WIN_MODE_CPB><<<bt.nwk, WIN_THREADS, shm, st>>>(Gu, xl, u, replay, sp, so, s0, n, nb, wb,
+                                                                        blk, err, bt);
     else
         window_kernel<T, AFQMC_MODE_BLOCKFB><<<bt.nwk, WIN_THREADS, shm, st>>>(Gu, xl, u, replay, sp, so, s0, n, nb,
                                                                               wb, blk, err, bt);

@@ -128,7 +128,7 @@ def test_every_entry_point_rejects_a_null_context_without_the_device():
     assert lib.afqmc_set_profiling(None, 1) == ARG
     assert lib.afqmc_get_profile(None, p(d), p(i64), p(i64)) == ARG
     assert lib.afqmc_cp_init(None, p(d), None, None) == ARG
-    assert lib.afqmc_cp_step(None, 1, 4, None, None) == ARG
+    assert lib.afqmc_cp_step(None, 1, 4, 4, None, None) == ARG
     assert lib.afqmc_cp_comb(None, 0.5, None, None) == ARG
     assert lib.afqmc_cp_reorth(None, None) == ARG
     assert lib.afqmc_cp_energy(None, p(d), p(d), None) == ARG

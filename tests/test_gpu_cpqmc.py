@@ -4,7 +4,8 @@ every step.  After every projection step the sampled fields are identical, the l
 agree to 1e-10, the walkers' determinants to 1e-10 (relative Frobenius norm) and the mixed local
 energies to 1e-9; the comb selects the same walkers; after a re-orthonormalisation the basis
 differs, so the mixed one-body matrices U_R (U_L U_R)^{-1} U_L are compared instead.  Local heat bath
-(one site per window) and the delayed scheme (windows of k sites) give the same fields and weights.
+(one site per window) and the delayed scheme (windows of k sites) give the same fields and weights;
+block force bias (n_b = 1, 4, 7, ragged last blocks) draws the oracle's proposals and weights.
 """
 import numpy as np
 import pytest
@@ -33,11 +34,12 @@ def make(L, ns, nw, U, hs, dtau=0.05, seed=7):
     return ctx, ens, seed
 
 
-def _oracle_step(ens, seed, visit, mode):
+def _oracle_step(ens, seed, visit, mode, nb=4):
     N, nw = ens.m.N, len(ens.w)
     u = np.stack([inputs.uniforms(seed, j, visit, 2 * N)[:N] for j in range(nw)])
     w0 = ens.w.copy()
-    out = ens.step("local", u)  # the delayed scheme draws the same fields
+    # the delayed scheme draws the local heat bath's fields
+    out = ens.step("blockfb" if mode == "blockfb" else "local", u, nb=nb)
     with np.errstate(divide="ignore"):
         return np.log(ens.w) - np.log(w0), [o[0] for o in out]
 
@@ -58,15 +60,16 @@ def _compare(ctx, ens, lw_gpu, lw_o, x_o, basis=True):
         assert abs(el[j] - ens.local_energy(j)) < 1e-9 * max(1.0, abs(el[j]))
 
 
-@pytest.mark.parametrize("mode,k", [("local", 1), ("delayed", 4), ("delayed", 16)])
+@pytest.mark.parametrize("mode,k,nb", [("local", 1, 1), ("delayed", 4, 1), ("delayed", 16, 1), ("blockfb", 1, 1),
+                                       ("blockfb", 1, 4), ("blockfb", 1, 7)])
 @pytest.mark.parametrize("L,ns,U,hs", [(4, 7, 4.0, oracle.HS_SZ_REAL), (3, 4, -4.0, oracle.HS_CHARGE_REAL)])
-def test_steps_match_the_oracle(mode, k, L, ns, U, hs):
+def test_steps_match_the_oracle(mode, k, nb, L, ns, U, hs):
     nw = 3
     ctx, ens, seed = make(L, ns, nw, U, hs)
     with ctx:
         for v in range(4):
-            lw_o, x_o = _oracle_step(ens, seed, v, mode)
-            lw_g = ctx.step(mode, k)
+            lw_o, x_o = _oracle_step(ens, seed, v, mode, nb)
+            lw_g = ctx.step(mode, k, nb)
             _compare(ctx, ens, lw_g, lw_o, x_o)
 
 
@@ -104,6 +107,6 @@ def test_state_rules():
     ctx, ens, seed = make(L, ns, 2, 4.0, oracle.HS_SZ_REAL)
     with ctx:
         with pytest.raises(afqmc.AfqmcError):
-            ctx.step("blockfb", 4)  # the heat bath comes as local or delayed
+            ctx.step("blockfb", 1, 33)  # blocks of at most 32 sites
         with pytest.raises(afqmc.AfqmcError):
             ctx.comb(1.0)  # u0 in [0, 1)
