@@ -720,7 +720,9 @@ NCU_TRAFFIC = {"elim": None, "lu_o": None,
                "solve": 25.807104e6 + 0.080896e6,      # lu_solve_kernel, 700 x 700, 1600 right-hand sides
                "wrap_gemm": 30.749184e6 + 0.02432e6,   # tc_gemm_kernel<160, split3>, 1600^3, both spins
                "flush_gemm": 22.05568e6 + 0.0,         # gemm_kernel<float>, 1600 x 1600 x m, both spins
-               "sep": None}
+               # sep_line_circ_kernel<float, 40>: four passes of one wrap (ncu, cold cache: 20.53 MB read,
+               # writes absorbed by L2, per pass)
+               "sep": 4 * 20.53e6}
 
 
 def fp32_alu_peak(pk):

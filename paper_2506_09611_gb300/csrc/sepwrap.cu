@@ -41,13 +41,15 @@ __global__ void __launch_bounds__(SEP_LINE_THREADS) sep_line_kernel(SepLineArgs 
         sep_line<T, LM>(a, line, As);
 }
 
-// Circulant A (SepArgs::circ) with a compile-time lattice side: its first row in registers, loaded
-// once per thread; two blocks per SM (128 registers: c, the line and a chunk of outputs).
+// Circulant A (SepArgs::circ) with a compile-time lattice side: its first row converted to T once
+// per block into shared memory (the inner loop reads it as register operands or broadcast shared
+// loads, never as FP64 loads with a conversion); two blocks per SM (128 registers: the line and a
+// chunk of outputs).
 template <typename T, int L>
 __global__ void __launch_bounds__(SEP_LINE_THREADS, 2) sep_line_circ_kernel(SepLineArgs a, const double* A) {
-    T c[L];
-#pragma unroll
-    for (int d = 0; d < L; ++d) c[d] = (T)__ldg(A + d);
+    __shared__ T c[L];
+    for (int d = threadIdx.x; d < L; d += blockDim.x) c[d] = (T)A[d];
+    __syncthreads();
     const long total = sep_line_count(a) * a.batch;
     for (long line = (long)blockIdx.x * blockDim.x + threadIdx.x; line < total; line += (long)gridDim.x * blockDim.x)
         sep_line_circ<T, L>(a, line, c);
@@ -75,7 +77,7 @@ cudaError_t launch_line(cudaStream_t st, const SepLineArgs& a, const double* A) 
     if (a.circ && sep_circ_side<T>(a.L)) {
         switch (a.L) {
 #define SEP_CIRC_CASE(LV) \
-    case LV: sep_line_circ_kernel<T, (sizeof(T) == 4 || LV <= 24) ? LV : 4><<<grid, SEP_LINE_THREADS, 0, st>>>(a, A); break;
+    case LV: sep_line_circ_kernel<T, (sizeof(T) == 4 || LV <= 16) ? LV : 4><<<grid, SEP_LINE_THREADS, 0, st>>>(a, A); break;
             SEP_CIRC_CASE(4)
             SEP_CIRC_CASE(6)
             SEP_CIRC_CASE(8)

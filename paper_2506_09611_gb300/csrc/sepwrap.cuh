@@ -364,6 +364,7 @@ SEP_HD inline void sep_line(const SepLineArgs& a, long line, const T* As) {
 // The same line for a circulant A of compile-time side L, given by its first row c[d] = A[0][d]
 // (A[x][p] = c[(p - x) mod L]; A is symmetric, so the column passes use the same formula):
 //   out[x] = sum_d c[d] v[(x + d) mod L].
+// A symmetric circulant A has c[d] = c[L - d], so only c[0..L/2] is read (half the registers).
 // c (the caller keeps it in registers across lines), the line and a chunk of H outputs are
 // register operands, so the pass runs on the FMA pipes: L^2 multiply-adds per line and no memory
 // access besides the line's own loads and stores.  H = L for lines up to 80 bytes, else L / 2
@@ -433,7 +434,7 @@ SEP_HD inline void sep_line_circ(const SepLineArgs& a, long line, const T (&c)[L
         for (int d = 0; d < L; ++d)
 #pragma unroll
             for (int x = 0; x < H; ++x)
-                if (x0 + x < L) o[x] += c[d] * v[(x0 + x + d) % L];
+                if (x0 + x < L) o[x] += c[d <= L / 2 ? d : L - d] * v[(x0 + x + d) % L];
 #pragma unroll
         for (int x = 0; x < H; ++x)
             if (x0 + x < L) o[x] *= vout ? fout * vout[vo + (x0 + x) * vd] : fout;
@@ -449,13 +450,13 @@ SEP_HD inline void sep_line_circ(const SepLineArgs& a, long line, const T (&c)[L
     }
 }
 
-// The lattice sides with a circulant line kernel (FP64 up to 24: the line and its outputs, two
-// arrays of L doubles per thread, stay in registers); other sides take the LM kernel.
+// The lattice sides with a circulant line kernel (FP64 up to 16: the line and its outputs stay in
+// registers without spills); other sides take the LM kernel.
 template <typename T>
 SEP_HD inline bool sep_circ_side(int L) {
     switch (L) {
-        case 4: case 6: case 8: case 12: case 16: case 20: case 24: return true;
-        case 32: case 40: return sizeof(T) == 4;
+        case 4: case 6: case 8: case 12: case 16: return true;
+        case 20: case 24: case 32: case 40: return sizeof(T) == 4;
         default: return false;
     }
 }
