@@ -123,7 +123,7 @@ int afqmc_soc_measure_energy(afqmc_soc_ctx* ctx, double* energy, void* stream);
  * Mk[k][k'] - delta_kk' <n_ku> <n_{-k d}>, divided by N_e / 2 (Sec. IV); the averaging is the caller's.
  *   scalars  host, 4 doubles per walker: Re D, Im D, Re <Delta^2>, Im <Delta^2>.
  *   nk       host, nullable: 4N doubles per walker, <n_ku> (N complex) then <n_kd> (N complex).
- *   Mk       host, nullable: N x N complex (re, im interleaved), the SUM over the walkers.
+ *   Mk       host, nullable: N x N complex (re, im interleaved) per walker.
  * The first call allocates the DFT tables (2 x (2 ldz)^2 + 2N 2 ldz doubles, ldz = 2N rounded up to
  * 32) and scratch of the same order.  Syncs the stream.  AFQMC_ERR_ARG before init or for a NULL
  * scalars. */

@@ -1132,8 +1132,8 @@ __global__ void __launch_bounds__(256) soc_pair_scalars_kernel(const double* A, 
 }
 
 // From At = F2 A F2^+ (row-split, At_{(p s),(q t)} = <c+_{q t} c_{p s}>): nk[k] = At_{ku,ku},
-// nk[N + k] = At_{kd,kd} (complex), and Mk[k][k'] += At_{k'u,ku} At_{-k'd,-kd} - At_{-k'd,ku} At_{k'u,-kd}
-// (the walker sum of <D+_k D_k'>, D+_k = c+_{k u} c+_{-k d}; -k = (-kx, -ky) mod L).
+// nk[N + k] = At_{kd,kd} (complex), and Mk[k][k'] = At_{k'u,ku} At_{-k'd,-kd} - At_{-k'd,ku} At_{k'u,-kd}
+// (<D+_k D_k'> of one walker, D+_k = c+_{k u} c+_{-k d}; -k = (-kx, -ky) mod L).
 __global__ void __launch_bounds__(256) soc_pair_k_kernel(const double* At, long ldz, int L, double* Mk, double* nk) {
     const long ld2 = 2 * ldz;
     const int N = L * L;
@@ -1145,8 +1145,8 @@ __global__ void __launch_bounds__(256) soc_pair_k_kernel(const double* At, long 
         const int mk = neg(k), mk2 = neg(k2);
         cx<double> t = cmul(at(k2, k), at(N + mk2, N + mk));
         t = csub(t, cmul(at(N + mk2, k), at(k2, N + mk)));
-        Mk[2 * e] += t.r;
-        Mk[2 * e + 1] += t.i;
+        Mk[2 * e] = t.r;
+        Mk[2 * e + 1] = t.i;
         if (k2 == 0) {
             const cx<double> u = at(k, k), dd = at(N + k, N + k);
             nk[2 * k] = u.r;
@@ -1220,7 +1220,7 @@ struct afqmc_soc_ctx {
     double* ozs = nullptr;
     // pairing observables (allocated at the first afqmc_soc_measure_pairing): [Re F2 | Im F2] rows,
     // the realified F2^+ (2 ldz x 2 ldz), FP64 scratch A (2N x 2 ldz), S~ (2 ldz x 2 ldz),
-    // At (2N x 2 ldz), the walker-summed Mk (N x N complex) and the per-walker outputs
+    // At (2N x 2 ldz), Mk per walker (N x N complex each) and the per-walker outputs
     double *Frs = nullptr, *Fh = nullptr, *pA = nullptr, *pS = nullptr, *pAt = nullptr, *pMk = nullptr,
            *pOut = nullptr;
     // profiling
@@ -2004,13 +2004,12 @@ int afqmc_soc_measure_pairing(afqmc_soc_ctx* ctx, double* scalars, double* nk, d
         SCK(soc_alloc(ctx, &ctx->pA, (size_t)N2 * ld2 * 8, st));
         SCK(soc_alloc(ctx, &ctx->pS, (size_t)ld2 * ld2 * 8, st));
         SCK(soc_alloc(ctx, &ctx->pAt, (size_t)N2 * ld2 * 8, st));
-        SCK(soc_alloc(ctx, &ctx->pMk, (size_t)N * N * 16, st));
+        SCK(soc_alloc(ctx, &ctx->pMk, (size_t)nwk * N * N * 16, st));
         SCK(soc_alloc(ctx, &ctx->pOut, (size_t)nwk * (4 + 4 * N) * 8, st));
         SCK(cudaMemcpyAsync(ctx->Frs, frs.data(), frs.size() * 8, cudaMemcpyHostToDevice, st));
         SCK(cudaMemcpyAsync(ctx->Fh, fh.data(), fh.size() * 8, cudaMemcpyHostToDevice, st));
         SCK(cudaStreamSynchronize(st));  // the host tables go out of scope
     }
-    SCK(cudaMemsetAsync(ctx->pMk, 0, (size_t)N * N * 16, st));
     SCK(cudaMemsetAsync(ctx->pOut, 0, (size_t)nwk * (4 + 4 * N) * 8, st));
     const size_t es = ctx->f64 ? 8 : 4;
     for (int w = 0; w < nwk; ++w) {
@@ -2045,12 +2044,12 @@ int afqmc_soc_measure_pairing(afqmc_soc_ctx* ctx, double* scalars, double* nk, d
         SCK(gemm<double>(st, g2));
         count_launch();
         soc_pair_k_kernel<<<(unsigned)std::min<long>(((long)N * N + 255) / 256, 4096), 256, 0, st>>>(
-            ctx->pAt, ldz, L, ctx->pMk, nkw);
+            ctx->pAt, ldz, L, ctx->pMk + (size_t)w * 2 * N * N, nkw);
         SCK(cudaGetLastError());
     }
     std::vector<double> h((size_t)nwk * (4 + 4 * N));
     SCK(cudaMemcpyAsync(h.data(), ctx->pOut, h.size() * 8, cudaMemcpyDeviceToHost, st));
-    if (Mk) SCK(cudaMemcpyAsync(Mk, ctx->pMk, (size_t)N * N * 16, cudaMemcpyDeviceToHost, st));
+    if (Mk) SCK(cudaMemcpyAsync(Mk, ctx->pMk, (size_t)nwk * N * N * 16, cudaMemcpyDeviceToHost, st));
     SCK(cudaStreamSynchronize(st));
     rc = read_err(ctx);
     if (rc) return rc;

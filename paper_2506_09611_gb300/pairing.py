@@ -9,10 +9,8 @@ from which the condensate fraction n_c = lambda_max / (N_e / 2) follows (afqmc_s
         --walkers 32 --warmup 20 --sweeps 40 --mode delayed --k 32 --out pairing.json
 
 Statistics.  Walkers are independent chains: D and <Delta^2> take the mean over the walkers of each
-walker's time average and its standard error.  The pairing matrix comes summed over the walkers, so
-n_c takes a jackknife over `--bins` consecutive blocks of half sweeps (each block's averaged
-M[k][k'] - delta_kk' <n_{k up}> <n_{-k dn}>, Hermitian part, largest eigenvalue); blocks several
-sweeps long keep their correlation small.
+walker's time average and its standard error; n_c (largest eigenvalue of the Hermitian part of the
+averaged M[k][k'] - delta_kk' <n_{k up}> <n_{-k dn}>) takes a jackknife over the walkers.
 """
 import argparse
 import json
@@ -56,7 +54,11 @@ def run(a):
     mid = M // 2
     ctx = soc.SocContext(L, M, 2 * ns, a.walkers, a.precision, a.gemm, a.stab, 1.0, 0.0, a.U, a.dtau, a.seed, hs="sz")
     P = inputs.sz_trial_state(L, ns)
-    rounds = []  # per round: D (walker mean), Delta2, Mk (walker mean), nk (walker mean)
+    Dsum = np.zeros(a.walkers)
+    Psum = np.zeros(a.walkers)
+    Msum = np.zeros((a.walkers, N, N), np.complex128)
+    nksum = np.zeros((a.walkers, 2 * N), np.complex128)
+    rounds = 0
     acc = {"proposals": 0, "accepts": 0}
     t0 = time.perf_counter()
     with ctx:
@@ -70,8 +72,11 @@ def run(a):
                     ctx.recompute_G(stream=stream)
                 if pos == mid and sweep >= a.warmup:
                     r = ctx.measure_pairing(stream=stream)
-                    rounds.append((r["D"].real.copy(), r["Delta2"].real.copy(), r["Mk"] / a.walkers,
-                                   r["nk"].mean(axis=0)))
+                    Dsum += r["D"].real
+                    Psum += r["Delta2"].real
+                    Msum += r["Mk"]
+                    nksum += r["nk"]
+                    rounds += 1
                     dec = np.concatenate([ctx.decisions(w)[:N] for w in range(a.walkers)])
                     if a.mode != "blockfb":
                         acc["proposals"] += dec.size
@@ -79,20 +84,15 @@ def run(a):
             if a.verbose:
                 print(f"sweep {sweep + 1}/{a.warmup + a.sweeps}: {time.perf_counter() - t0:.1f} s", flush=True)
     secs = time.perf_counter() - t0
-    Dw = np.mean([r[0] for r in rounds], axis=0)  # per-walker time averages
-    Pw = np.mean([r[1] for r in rounds], axis=0)
+    Dw, Pw = Dsum / rounds, Psum / rounds  # per-walker time averages
     D = (float(Dw.mean()), float(Dw.std(ddof=1) / np.sqrt(len(Dw))) if len(Dw) > 1 else float("nan"))
     P2 = (float(Pw.mean()), float(Pw.std(ddof=1) / np.sqrt(len(Pw))) if len(Pw) > 1 else float("nan"))
-    nb = max(1, min(a.bins, len(rounds)))
-    blocks = np.array_split(np.arange(len(rounds)), nb)
-    Mb = np.array([np.mean([rounds[i][2] for i in b], axis=0) for b in blocks])
-    nkb = np.array([np.mean([rounds[i][3] for i in b], axis=0) for b in blocks])
-    packed = np.concatenate([Mb.reshape(nb, -1), nkb], axis=1)
+    packed = np.concatenate([(Msum / rounds).reshape(a.walkers, -1), nksum / rounds], axis=1)
     nc = jackknife(packed, lambda x: n_c(x[:N * N].reshape(N, N), x[N * N:], L, 2 * ns))
     out = {"model": "attractive Hubbard, imaginary spin-z decoupling (spin-coupled engine, lam = 0)",
            "L": L, "U": a.U, "filling": 2 * ns / N, "n_sigma": ns, "dtau": a.dtau, "two_theta": M * a.dtau, "M": M,
            "stab_every": a.stab, "mode": a.mode, "k": a.k, "nb": a.nb, "precision": a.precision, "gemm": a.gemm,
-           "walkers": a.walkers, "warmup_sweeps": a.warmup, "sweeps": a.sweeps, "rounds": len(rounds), "bins": nb,
+           "walkers": a.walkers, "warmup_sweeps": a.warmup, "sweeps": a.sweeps, "rounds": rounds,
            "seconds": secs, "D": D, "Delta2": P2, "n_c": nc,
            "acceptance": acc["accepts"] / acc["proposals"] if acc["proposals"] else None}
     return out
@@ -109,7 +109,6 @@ def main(argv=None):
     ap.add_argument("--walkers", type=int, default=32)
     ap.add_argument("--warmup", type=int, default=20, help="sweeps (out and back) before measuring")
     ap.add_argument("--sweeps", type=int, default=40, help="measured sweeps")
-    ap.add_argument("--bins", type=int, default=5)
     ap.add_argument("--mode", default="delayed", choices=["local", "delayed", "blockfb"])
     ap.add_argument("--k", type=int, default=32)
     ap.add_argument("--nb", type=int, default=16)

@@ -162,16 +162,16 @@ def afqmc_soc_get_profile(ctx):
 
 def afqmc_soc_measure_pairing(ctx, n_walkers, N, want_k=True, stream=None):
     """Per walker D and <Delta^2> (complex arrays), and with want_k the momentum occupations nk
-    (n_walkers x 2N complex) and the walker sum of the pairing matrix Mk (N x N complex)."""
+    (n_walkers x 2N complex) and the pairing matrices Mk (n_walkers x N x N complex)."""
     sc = np.zeros(4 * n_walkers)
     nk = np.zeros(4 * N * n_walkers) if want_k else None
-    Mk = np.zeros(2 * N * N) if want_k else None
+    Mk = np.zeros(2 * N * N * n_walkers) if want_k else None
     _ck("afqmc_soc_measure_pairing", load().afqmc_soc_measure_pairing(
         ctx, _ptr(sc, ctypes.c_double), _ptr(nk, ctypes.c_double), _ptr(Mk, ctypes.c_double), _stream(stream)))
     r = {"D": sc[0::4] + 1j * sc[1::4], "Delta2": sc[2::4] + 1j * sc[3::4]}
     if want_k:
         r["nk"] = nk.view(np.complex128).reshape(n_walkers, 2 * N)
-        r["Mk"] = Mk.view(np.complex128).reshape(N, N)
+        r["Mk"] = Mk.view(np.complex128).reshape(n_walkers, N, N)
     return r
 
 

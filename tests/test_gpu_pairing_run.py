@@ -73,7 +73,7 @@ def test_free_running_estimators_match_the_exact_2x2_projection(mode):
     M = int(round(two_theta / dtau))
     D, P2, nc = _exact_2x2(L, ns, U, dtau, M)
     out = pairing.main(["--L", str(L), "--ns", str(ns), "--U", str(U), "--dtau", str(dtau), "--two-theta",
-                        str(two_theta), "--walkers", "64", "--warmup", "4", "--sweeps", "24", "--bins", "4",
+                        str(two_theta), "--walkers", "64", "--warmup", "4", "--sweeps", "24",
                         "--mode", mode, "--k", "4", "--nb", "2", "--stab", "10", "--precision", "fp64", "--seed", "3"])
     for name, exact in (("D", D), ("Delta2", P2), ("n_c", nc)):
         mean, err = out[name]
