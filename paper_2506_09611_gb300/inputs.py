@@ -116,14 +116,40 @@ def soc_trial_state(L: int, n_e: int, t: float = 1.0, lam: float = 0.5, seed: in
     return np.ascontiguousarray(v[:, :n_e])
 
 
-def sz_trial_state(L: int, n_sigma: int, t: float = 1.0, seed: int = 0) -> np.ndarray:
-    """The spin-balanced trial determinant of the Hubbard model on the 2N spin orbitals (up block
-    first): P = [[P_s, 0], [0, P_s]] with P_s = trial_state(L, L, n_sigma) real, so P_dn = conj(P_up)
-    (the condition of Sec. II.B under which the imaginary spin-z decoupling has no sign problem).
-    2N x 2 n_sigma complex, orthonormal columns."""
-    Ps = trial_state(L, L, n_sigma, t, seed)
+def twisted_hopping_matrix(L: int, twist, t: float = 1.0) -> np.ndarray:
+    """Nearest-neighbour hopping on the periodic L x L lattice threaded by a flux: the bond from site
+    i to its +x (+y) neighbour carries the phase e^{i twist[0] / L} (e^{i twist[1] / L}), so the
+    eigenvectors are the plane waves e^{ik.r} with energies -2t (cos(kx + twist[0]/L) +
+    cos(ky + twist[1]/L)).  Hermitian; K_ij is the amplitude of c+_i c_j."""
     N = L * L
+    K = np.zeros((N, N), np.complex128)
+    for y in range(L):
+        for x in range(L):
+            i = x + L * y
+            for (xx, yy), ph in ((((x + 1) % L, y), twist[0] / L), ((x, (y + 1) % L), twist[1] / L)):
+                j = xx + L * yy
+                K[i, j] -= t * np.exp(-1j * ph)
+                K[j, i] -= t * np.exp(1j * ph)
+    return K
+
+
+def sz_trial_state(L: int, n_sigma: int, t: float = 1.0, seed: int = 0, twist=None) -> np.ndarray:
+    """The spin-balanced trial determinant of the Hubbard model on the 2N spin orbitals (up block
+    first): P = [[P_up, 0], [0, conj(P_up)]], the condition of Sec. II.B under which the imaginary
+    spin-z decoupling has no sign problem.  2N x 2 n_sigma complex, orthonormal columns.
+
+    twist None: P_up = trial_state(L, L, n_sigma) (real; the open shell's degeneracy broken by a
+    fixed random 1e-6 perturbation).  twist = (theta_x, theta_y): P_up = the lowest n_sigma
+    eigenvectors of twisted_hopping_matrix(L, twist), i.e. the plane waves of the n_sigma lowest
+    twisted energies (an open shell filled by the flux's ordering), and P_dn holds the opposite
+    momenta."""
+    N = L * L
+    if twist is None:
+        Ps = trial_state(L, L, n_sigma, t, seed)
+    else:
+        w, v = np.linalg.eigh(twisted_hopping_matrix(L, twist, t))
+        Ps = v[:, :n_sigma]
     P = np.zeros((2 * N, 2 * n_sigma), np.complex128)
     P[:N, :n_sigma] = Ps
-    P[N:, n_sigma:] = Ps
+    P[N:, n_sigma:] = np.conj(Ps)
     return P

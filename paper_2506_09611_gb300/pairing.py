@@ -20,6 +20,22 @@ import numpy as np
 
 from . import afqmc, inputs, soc
 
+# Flux (theta_x, theta_y) whose ordering of the twisted plane waves fills the open shell of the trial
+# determinant: small and incommensurate, so that it splits every degenerate level without moving any
+# across a shell.
+TWIST = (0.1, 0.07)
+
+
+def trial(L, ns, kind="twist"):
+    """The trial determinant of a pairing run (2N x 2 ns, P_dn = conj(P_up)).  "twist": the plane
+    waves of the ns lowest twisted energies for spin up and the opposite momenta for spin down.  At
+    half filling it is a pseudospin singlet: eta^2 = 0 for the eta-pairing operators
+    eta+ = sum_i (-1)^i c+_iup c+_idn, which commute with H, and the half-filled ground state has
+    eta = 0.  "random": the lowest eigenvectors of the hopping plus a fixed 1e-6 random perturbation
+    (real, the same for both spins); at half filling it has components with eta > 0, which the
+    projection removes only at the rate of their small finite-size gap."""
+    return inputs.sz_trial_state(L, ns, twist=TWIST if kind == "twist" else None)
+
 
 def n_c(Mk, nk, L, n_e):
     """Condensate fraction from averaged Mk (N x N) and averaged nk (2N: up, then down)."""
@@ -53,7 +69,7 @@ def run(a):
         raise SystemExit(f"M = {M} must be even and a multiple of --stab {a.stab}")
     mid = M // 2
     ctx = soc.SocContext(L, M, 2 * ns, a.walkers, a.precision, a.gemm, a.stab, 1.0, 0.0, a.U, a.dtau, a.seed, hs="sz")
-    P = inputs.sz_trial_state(L, ns)
+    P = trial(L, ns, a.trial)
     Dsum = np.zeros(a.walkers)
     Psum = np.zeros(a.walkers)
     Msum = np.zeros((a.walkers, N, N), np.complex128)
@@ -91,7 +107,7 @@ def run(a):
     nc = jackknife(packed, lambda x: n_c(x[:N * N].reshape(N, N), x[N * N:], L, 2 * ns))
     out = {"model": "attractive Hubbard, imaginary spin-z decoupling (spin-coupled engine, lam = 0)",
            "L": L, "U": a.U, "filling": 2 * ns / N, "n_sigma": ns, "dtau": a.dtau, "two_theta": M * a.dtau, "M": M,
-           "stab_every": a.stab, "mode": a.mode, "k": a.k, "nb": a.nb, "precision": a.precision, "gemm": a.gemm,
+           "trial": a.trial, "twist": TWIST if a.trial == "twist" else None, "stab_every": a.stab, "mode": a.mode, "k": a.k, "nb": a.nb, "precision": a.precision, "gemm": a.gemm,
            "walkers": a.walkers, "warmup_sweeps": a.warmup, "sweeps": a.sweeps, "rounds": rounds,
            "seconds": secs, "D": D, "Delta2": P2, "n_c": nc,
            "acceptance": acc["accepts"] / acc["proposals"] if acc["proposals"] else None}
@@ -115,6 +131,7 @@ def main(argv=None):
     ap.add_argument("--stab", type=int, default=10)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--gemm", default="tc3", choices=["tc3", "simt", "tf32"])
+    ap.add_argument("--trial", default="twist", choices=["twist", "random"], help="trial determinant (see trial())")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--out", default=None)
     ap.add_argument("--verbose", action="store_true")

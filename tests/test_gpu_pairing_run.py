@@ -35,7 +35,7 @@ def _exact_2x2(L, ns, U, dtau, M):
         nu, nd = cd[i] @ cs[i], cd[N + i] @ cs[N + i]
         HI = HI + U * (nu @ nd - 0.5 * (nu + nd))
     T = scipy.linalg.expm(-dtau * HI) @ scipy.linalg.expm(-dtau * Kf)
-    P = inputs.sz_trial_state(L, ns)
+    P = pairing.trial(L, ns)  # the run's default trial determinant
     psi = np.zeros(1 << (2 * N), np.complex128)
     psi[0] = 1.0
     for col in range(P.shape[1]):
