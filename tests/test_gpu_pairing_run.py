@@ -67,14 +67,15 @@ def _exact_2x2(L, ns, U, dtau, M):
     return D, P2, pairing.n_c(Mk, nk, L, 2 * ns)
 
 
-@pytest.mark.parametrize("mode", ["delayed", "blockfb"])
-def test_free_running_estimators_match_the_exact_2x2_projection(mode):
+@pytest.mark.parametrize("mode,nb", [("delayed", 2), ("blockfb", 2), ("blockfb", 4)])
+def test_free_running_estimators_match_the_exact_2x2_projection(mode, nb):
+    """nb = 4 = N is the full force-bias update."""
     L, ns, U, dtau, two_theta = 2, 2, -4.0, 0.05, 2.0
     M = int(round(two_theta / dtau))
     D, P2, nc = _exact_2x2(L, ns, U, dtau, M)
     out = pairing.main(["--L", str(L), "--ns", str(ns), "--U", str(U), "--dtau", str(dtau), "--two-theta",
                         str(two_theta), "--walkers", "64", "--warmup", "4", "--sweeps", "24",
-                        "--mode", mode, "--k", "4", "--nb", "2", "--stab", "10", "--precision", "fp64", "--seed", "3"])
+                        "--mode", mode, "--k", "4", "--nb", str(nb), "--stab", "10", "--precision", "fp64", "--seed", "3"])
     for name, exact in (("D", D), ("Delta2", P2), ("n_c", nc)):
         mean, err = out[name]
         assert err > 0 and abs(mean - exact) < 4 * err + 1e-4, (name, mean, err, exact)

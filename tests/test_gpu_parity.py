@@ -55,6 +55,15 @@ def test_init_G0_matches_oracle(L, ns, M, stab):
         assert sg[0] == w.sign
 
 
+def _replay(N, nb, dec, extra):
+    """Replay bytes of a block force-bias slice: the proposed fields (x' = +1) of the N sites, then
+    the decision of each block."""
+    rep = np.zeros(2 * N, np.uint8)
+    rep[:N] = (extra["xprop"] > 0)
+    rep[N:N + (N + nb - 1) // nb] = dec
+    return rep
+
+
 def _run_sweep(ctx, w, mode, k=16, nb=4, seed=11, slices=None, stab=4, tol=FP64_TOL, check_every=True):
     M = w.m.M
     N = w.m.N
@@ -88,8 +97,10 @@ def _run_sweep(ctx, w, mode, k=16, nb=4, seed=11, slices=None, stab=4, tol=FP64_
 
 @pytest.mark.parametrize("wrap", ["dense", "separable"])
 @pytest.mark.parametrize("mode,k,nb", [("local", 16, 4), ("delayed", 1, 4), ("delayed", 5, 4), ("delayed", 16, 4),
-                                       ("blockfb", 16, 1), ("blockfb", 16, 4), ("blockfb", 16, 7)])
+                                       ("blockfb", 16, 1), ("blockfb", 16, 4), ("blockfb", 16, 7),
+                                       ("blockfb", 16, 16)])
 def test_sweep_fp64_free_running(mode, k, nb, wrap):
+    """nb = 16 = N is the full force-bias update (Sec. II.D): one block holds the whole slice."""
     ctx, w, P, X = make(4, 7, 8, stab=4, wrap=wrap)
     with ctx:
         _run_sweep(ctx, w, mode, k=k, nb=nb)
@@ -353,3 +364,29 @@ def test_graph_replay_matches_direct_launches(precision):
     finally:
         for c in ctxs:
             c.close()
+
+
+@pytest.mark.parametrize("precision,L,ns,nb", [("fp64", 8, 28, 64), ("fp32", 8, 28, 64), ("fp32", 11, 53, 121)])
+def test_full_force_bias_one_block_per_slice(precision, L, ns, nb):
+    """The full force-bias update (Sec. II.D, Eqs. FullFrcbsPhiLPhiR, RatioApprox, AcceptRatio): block
+    force bias with n_b = N, one proposal and one N x N-site determinant per slice, on the largest
+    lattices whose slice fits one window (FP64: 64 sites, FP32: 128).  FP64 runs free against the
+    oracle (identical decisions, G within 1e-10 per slice); FP32 replays the oracle's proposals and
+    decisions (G within 1e-5 per slice)."""
+    M, stab = 4, 2
+    N = L * L
+    assert nb == N
+    ctx, w, P, X = make(L, ns, M, stab=stab, precision=precision, U=4.0)
+    with ctx:
+        if precision == "fp64":
+            _run_sweep(ctx, w, "blockfb", k=16, nb=nb, stab=stab)
+            return
+        for ell in range(1, M + 1):
+            u = inputs.uniforms(11, 0, ell - 1, 2 * N)
+            dec, _, extra = w.sweep_slice(ell, +1, "blockfb", u, k=16, nb=nb)
+            ctx.sweep_slice(ell, +1, "blockfb", k=16, nb=nb, replay=_replay(N, nb, dec, extra))
+            for s_ in range(2):
+                assert rel(ctx.G(0, s_), w.G[s_]) < FP32_TOL, (ell, s_)
+            if ell % stab == 0:
+                ctx.recompute_G()
+                w.recompute()

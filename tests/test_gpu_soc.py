@@ -76,8 +76,9 @@ def _free_run(ctx, w, mode, k, nb, seed, steps, stab, tol):
 
 
 @pytest.mark.parametrize("mode,k,nb", [("local", 1, 1), ("delayed", 5, 1), ("delayed", 32, 1),
-                                       ("blockfb", 1, 1), ("blockfb", 1, 4), ("blockfb", 1, 7)])
+                                       ("blockfb", 1, 1), ("blockfb", 1, 4), ("blockfb", 1, 7), ("blockfb", 1, 16)])
 def test_fp64_free_run_matches_oracle(mode, k, nb):
+    """nb = 16 = N: the full force-bias update, one block per slice."""
     L, n_e, M, stab = 4, 14, 4, 2
     ctx, w = make(L, n_e, M, stab, seed=5)
     with ctx:
