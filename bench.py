@@ -309,6 +309,7 @@ def main():
 
     # ---------------- roofline of the dominant kernel ----------------
     pk, pk_src = peaks()
+    optional_leg("fp64_peak", lambda: fp64_gemm_tflops(torch))
     kernels = kernel_rooflines(prof, args.gemm, pk, pk_src, args.steps)
     roof = dict(kernels[0]) if kernels else None
     l2_gbs = optional_leg("l2_copy", lambda: l2_copy_bandwidth(torch))
@@ -400,6 +401,7 @@ def main():
                                              "note": "the warm-up sweeps' recompute points: ||G_fp32 - G_fp64|| / "
                                                      "||G_fp64|| after the %d slices since the previous one" % STAB},
             "roofline": roof,
+            "fp64_peak": dict(FP64_MEASURED) if FP64_MEASURED else None,
             "roofline_kernels": kernels[1:],
             "clocks": clocks,
             "gpu_launches": launches,
@@ -718,9 +720,12 @@ def config_16x16_leg(afqmc, torch, stream, args, seed):
             "unit": UNIT, "by_precision": res}
 
 
-# Nominal dense FP64 rate of a GB300 (no measured FP64 peak is available): 1.25 TFLOP/s at
-# the 2070 MHz maximum SM clock, i.e. 2 FP64 FMA per SM per clock on 152 SMs.
+# Nominal dense FP64 rate of a GB300: 1.25 TFLOP/s at the 2070 MHz maximum SM clock, i.e. 2 FP64
+# FMA per SM per clock on 152 SMs.  The FP64 rooflines use the rate measured in the same run
+# (fp64_gemm_tflops: a cuBLAS DGEMM through torch, as the bf16 peak is a cuBLAS GEMM) when it
+# succeeded, else this nominal figure.
 FP64_FMA_PER_SM_CLK = 2
+FP64_MEASURED = {}
 # TF32 tensor rate relative to bf16 (nominal dense 1.1 vs 2.25 PFLOP/s).
 TF32_OVER_BF16 = 1.1 / 2.25
 # Digit-plane pairs of each FP64-accurate recompute product: the split's cost model picks 6-bit
@@ -732,10 +737,8 @@ OZ_PAIRS = 45
 NCU_TRAFFIC = {"elim": None, "lu_o": None,
                "solve": 25.807104e6 + 0.080896e6,      # lu_solve_kernel, 700 x 700, 1600 right-hand sides
                "wrap_gemm": 30.749184e6 + 0.02432e6,   # tc_gemm_kernel<160, split3>, 1600^3, both spins
-               "flush_gemm": 22.05568e6 + 0.0,         # gemm_kernel<float>, 1600 x 1600 x m, both spins
-               # sep_line_circ_kernel<float, 40>: four passes of one wrap (ncu, cold cache: 20.53 MB read,
-               # writes absorbed by L2, per pass)
-               "sep": 4 * 20.53e6}
+               "flush_gemm": None,                     # rankm_kernel (1600 x 1600 x m, both spins): not yet captured
+               "sep": None}                            # sep_line_circ_kernel<float, 40>: not yet captured
 
 
 def fp32_alu_peak(pk):
@@ -743,7 +746,35 @@ def fp32_alu_peak(pk):
 
 
 def fp64_alu_peak(pk):
+    if "tflops" in FP64_MEASURED:
+        return FP64_MEASURED["tflops"]
     return 152 * FP64_FMA_PER_SM_CLK * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+def fp64_peak_source(pk, pk_src):
+    if "tflops" in FP64_MEASURED:
+        return "measured cuBLAS DGEMM %d^3 in this run: %.3f TFLOP/s (of measured)" % (FP64_MEASURED["n"],
+                                                                                      FP64_MEASURED["tflops"])
+    return ("nominal FP64 1.25 TFLOP/s: 152 SMs x %d FMA x 2 flop x %.0f MHz (of %s peaks)"
+            % (FP64_FMA_PER_SM_CLK, pk.get("sm_max_mhz", 2070.0), pk_src))
+
+
+def fp64_gemm_tflops(torch, n=4096, reps=3):
+    """The FP64 denominator: a cuBLAS DGEMM (torch.mm on float64) of n x n x n, CUDA events over
+    `reps` products after one warm-up; records it in FP64_MEASURED."""
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    c = torch.mm(a, b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        torch.mm(a, b, out=c)
+    e1.record()
+    torch.cuda.synchronize()
+    tf = 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) / 1e3) / 1e12
+    FP64_MEASURED.update({"tflops": tf, "n": n})
+    return tf
 
 
 def kernel_rooflines(prof, gemm, pk, pk_src, steps, wrap="separable", wrap_tile=0):
@@ -754,8 +785,7 @@ def kernel_rooflines(prof, gemm, pk, pk_src, steps, wrap="separable", wrap_tile=
     # FP64 recompute: blocked pivoted LU of the propagated N x ns factor (both spins per
     # interval), LU of U_L U_R (ns x ns) and the solve (U_L U_R) Z = U_L with N right-hand sides.
     fp64 = fp64_alu_peak(pk)
-    src64 = ("nominal FP64 1.25 TFLOP/s: 152 SMs x %d FMA x 2 flop x %.0f MHz (of %s peaks)"
-             % (FP64_FMA_PER_SM_CLK, pk.get("sm_max_mhz", 2070.0), pk_src))
+    src64 = fp64_peak_source(pk, pk_src)
     for name, label, flop in (
             ("elim", "lu_panel_kernel + lu_update_kernel (FP64 LU of the propagated N x ns factor, both spins)",
              2 * (N * NS ** 2 - NS ** 3 / 3.0)),
@@ -986,7 +1016,7 @@ def soc_leg(torch, stream, args, seed):
             ach = flop * ph["intervals"] / (ph["ms"] / 1e3) / 1e12
             roofs.append({"kernel": label, "bound": "alu", "achieved": ach, "peak": fp64, "unit": "TFLOP/s",
                           "frac": ach / fp64, "launches": ph["intervals"], "ms_per_launch": ph["ms"] / ph["intervals"],
-                          "work_per_launch": flop, "peak_source": "nominal FP64 1.25 TFLOP/s (of %s peaks)" % pk_src})
+                          "work_per_launch": flop, "peak_source": fp64_peak_source(pk, pk_src)})
     cpu = None
     if not args.no_cpu_baseline:
         v, cores, secs = soc_oracle_sample()

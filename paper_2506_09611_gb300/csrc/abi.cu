@@ -132,6 +132,9 @@ struct Walker {
     void *TUR = nullptr, *TUL = nullptr, *TT = nullptr;
     void *ULI = nullptr, *URI = nullptr, *Vt = nullptr, *Yt = nullptr, *Ypt = nullptr, *Pt = nullptr;
     double* Ieye = nullptr;
+    // G form with FP32 bulk and digit-split products: (U_L U_R)^{-1} explicitly (nsm x nsm per
+    // matrix), so that Z = O^{-1} U_L runs on the tensor cores instead of an N-column solve
+    double* Oinv = nullptr;
     bool gvalid = true;  // the bulk G buffer holds the current G (the T form forms it on request)
     // constrained-path AFQMC (afqmc_cp_*): per walker [sum ln N_i, sum ln |r_up r_dn|, removed, kinetic
     // ln ratio], the tracked ln |det U_L U_R| (both spins), per matrix ln |det|, per walker the sign,
@@ -505,6 +508,39 @@ static cudaError_t form_Z(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac&
     const long os = (long)w->nsm * w->nsm, zs = (long)w->nsm * N;
     cudaError_t e;
     if ((e = form_O(ctx, w, st, R, Lf, s0, ng, sign)) != cudaSuccess) return e;
+    if (w->Oinv) {
+        // FP32 bulk: O^{-1} from the same LU (the solve with the identity, ns right-hand sides), then
+        // Z = O^{-1} U_L as an FP64-accurate digit-split product.  The forward error of Z is that of
+        // the solve up to a factor of order one; the FP32 bulk keeps about seven digits of G.
+        SolveArgs si;
+        si.LU0 = w->Ob;
+        si.ostride = os;
+        si.perm0 = w->perm2;
+        si.pstride = w->rows_max();
+        si.B0 = w->Ieye;
+        si.wstride = 0;
+        si.sstride = 0;
+        si.ldb = w->nsm;
+        si.ng = ng;
+        si.Z0 = w->Oinv;
+        si.zstride = os;
+        si.ldl = ns;
+        si.ns = ns;
+        si.N = ns;
+        si.nmat = nmat;
+        {
+            PhaseScope pv(ctx, AFQMC_PHASE_SOLVE, st);
+            if ((e = launch_lu_solve(st, si)) != cudaSuccess) return e;
+        }
+        OzGemmArgs o;
+        o.M = ns; o.N = N; o.K = ns; o.batch = nmat;
+        o.A = w->Oinv; o.lda = ns; o.sA = os;
+        o.B = Lf.at(s0); o.ldb = N; o.sB = Lf.bstride(ng);
+        o.C = w->Z; o.ldc = N; o.sC = zs;
+        o.err = w->err;
+        PhaseScope pd(ctx, AFQMC_PHASE_DGEMM, st);
+        return ozaki_gemm(st, o, w->ozw, w->ozs);
+    }
     SolveArgs sa;
     sa.LU0 = w->Ob;
     sa.ostride = os;
@@ -891,10 +927,24 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
         if (ctx->p.gemm != AFQMC_GEMM_SIMT) {
             w->oz_Z = ozaki_pays(nsm, nsm, N, 2 * nwk);
             w->oz_G = ozaki_pays(N, N, nsm, 2 * nwk);
+            const bool inv = ctx->form != AFQMC_FORM_T && ctx->p.precision == AFQMC_PREC_FP32 && w->oz_Z &&
+                             w->oz_G && ozaki_pays(nsm, N, nsm, 2 * nwk);
             if (w->oz_Z || w->oz_G) {
-                const size_t f1 = ozaki_ws_bytes(nsm, nsm, N, 2 * nwk), f2 = ozaki_ws_bytes(N, N, nsm, 2 * nwk);
-                CK(dalloc(A, (char**)&w->ozw, f1 > f2 ? f1 : f2));
+                size_t f = ozaki_ws_bytes(nsm, nsm, N, 2 * nwk);
+                f = std::max(f, ozaki_ws_bytes(N, N, nsm, 2 * nwk));
+                if (inv) f = std::max(f, ozaki_ws_bytes(nsm, N, nsm, 2 * nwk));
+                CK(dalloc(A, (char**)&w->ozw, f));
                 CK(dalloc(A, &w->ozs, ozaki_sc_doubles(N > nsm ? N : nsm, N > nsm ? N : nsm, 2 * nwk) * 8));
+            }
+            if (inv) {
+                CK(dalloc(A, &w->Oinv, (size_t)nwk * 2 * nsm * nsm * 8));
+                if (!w->Ieye) {
+                    std::vector<double> eye((size_t)nsm * nsm, 0.0);
+                    for (int i = 0; i < nsm; ++i) eye[(size_t)i * nsm + i] = 1.0;
+                    CK(dalloc(A, &w->Ieye, eye.size() * 8));
+                    CK(cudaMemcpyAsync(w->Ieye, eye.data(), eye.size() * 8, cudaMemcpyHostToDevice, st));
+                    CK(cudaStreamSynchronize(st));  // the host identity goes out of scope
+                }
             }
         }
         CK(cudaMemsetAsync(w->err, 0, sizeof(int), st));

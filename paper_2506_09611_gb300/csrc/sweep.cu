@@ -350,26 +350,14 @@ __device__ __forceinline__ WindowBufs wb_walker(WindowBufs wb, int j, int N) {
     return wb;
 }
 
-// Scratch of the blocked W (FP32 windows with at most WB_M accepts): two WB_M x WB_M matrices at
-// pitch WB_P, after the rest of the window kernel's shared memory.
-constexpr int WB_M = 64, WB_P = WB_M + 1;
 template <typename T>
-struct WinWScratch { static constexpr size_t bytes = 0; };
-template <>
-struct WinWScratch<float> { static constexpr size_t bytes = 2 * (size_t)WB_M * WB_P * sizeof(float); };
-
-template <typename T>
-__host__ __device__ inline size_t window_smem_base(int n) {
+static size_t window_smem(int n) {
     size_t P = (size_t)n + 1;
     size_t g = 2 * (size_t)n * P * sizeof(T);  // Gs[2][n][n+1]
     size_t s1 = 2 * (size_t)NBMAX * (NBMAX + 1) * sizeof(T);
     size_t vec = 4 * (size_t)n * sizeof(T) + 2 * (size_t)NBMAX * sizeof(T);  // staging vectors
     size_t misc = (size_t)n * (sizeof(int) + 2 * sizeof(double) + 1) + 8 * (size_t)NBMAX * sizeof(double) + 256;
     return g + s1 + vec + misc;
-}
-template <typename T>
-static size_t window_smem(int n) {
-    return ((window_smem_base<T>(n) + 15) & ~(size_t)15) + WinWScratch<T>::bytes;
 }
 
 // G_s[r][c] += f_s * G_s[r][a] * G_s[a][c] for r, c in (a, n), both spins; 32 x 32 thread tiles.
@@ -479,172 +467,10 @@ __device__ __forceinline__ void window_w_rpl(const T* Gs, int n, int P, const in
     }
 }
 
-// W = -F U1^{-1} L1^{-1} by blocked triangular inversion, for m <= WB_M accepts; every thread of
-// the block takes part (block barriers).  X[s] (pitch WB_P) is filled with C F without its
-// diagonal, zero-padded to mp = 16, 32 or 64 >= m rows and columns (identity rows of L1 and U1):
-// its strictly lower part is that of L1, its strictly upper part that of U1.  In place, the
-// lower part becomes L1^{-1} and the upper part U1^{-1} (unit diagonals implicit):
-//   * 16 x 16 diagonal blocks by substitution, one half-warp per block (lane = row, the row's 16
-//     entries in registers, the finished row broadcast by a shuffle: no barrier);
-//   * then pairs of blocks merge, 16 -> 32 -> 64: for L1 = [[L11, 0], [L21, L22]] the inverse's
-//     lower-left block is -L22^{-1} (L21 L11^{-1}); for U1 = [[U11, U12], [0, U22]] the upper-right
-//     block is -U11^{-1} (U12 U22^{-1}); each product is computed into registers, then stored;
-//   * W[k][j] = -f_k sum_{q >= max(k, j)} U1^{-1}[k][q] L1^{-1}[q][j].
-// The substitution form (window_w_rpl) serialises 2m dependent steps per spin; this one has
-// log2(mp / 16) + 1 levels with O(mp^3) work spread over the block.
-template <typename T>
-__device__ void window_w_blocked(const T* Gs, int n, int P, const int* idx, const T (*fk)[WinCap<T>::NW], int m,
-                                 T* Wx, T* X, int tid, int nt) {
-    constexpr int NW = WinCap<T>::NW;
-    const int mp = m <= 16 ? 16 : (m <= 32 ? 32 : 64);
-    const int mm = mp * mp;
-    for (int e = tid; e < 2 * mm; e += nt) {
-        const int s = e >= mm ? 1 : 0, rem = e - s * mm, k = rem / mp, c = rem - k * mp;
-        T v = T(0);
-        if (k < m && c < m && k != c) v = Gs[(s * n + idx[k]) * P + idx[c]] * fk[s][c];
-        X[(s * WB_M + k) * WB_P + c] = v;
-    }
-    __syncthreads();
-    const int nbk = mp / 16;
-    {   // diagonal blocks: task = (spin, triangle, block), 4 * nbk of them (whole warps)
-        const int hw = tid >> 4, r = tid & 15;
-        if (hw < 4 * nbk) {
-            const int s = hw / (2 * nbk), rem = hw - s * 2 * nbk, up = rem / nbk, b = rem - up * nbk;
-            T* Xb = X + (size_t)(s * WB_M + 16 * b) * WB_P + 16 * b;
-            T x[16], l[16];
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                x[c] = (c == r) ? T(1) : T(0);
-                l[c] = Xb[r * WB_P + c];
-            }
-            if (!up) {
-#pragma unroll
-                for (int k = 0; k < 15; ++k) {  // rows r > k: x_r -= L[r][k] x_k (row k is final)
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) {
-                        const T v = __shfl_sync(0xffffffffu, x[c], k, 16);
-                        if (r > k) x[c] -= l[k] * v;
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    if (c < r) Xb[r * WB_P + c] = x[c];
-            } else {
-#pragma unroll
-                for (int k = 15; k > 0; --k) {  // rows r < k: y_r -= U[r][k] y_k
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) {
-                        const T v = __shfl_sync(0xffffffffu, x[c], k, 16);
-                        if (r < k) x[c] -= l[k] * v;
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    if (c > r) Xb[r * WB_P + c] = x[c];
-            }
-        }
-    }
-    __syncthreads();
-    for (int bs = 16; 2 * bs <= mp; bs *= 2) {
-        const int bb = bs * bs, tot = 2 * mp * bs;  // 2 spins x 2 triangles x (mp / 2bs) pairs x bs^2
-        constexpr int OPT = (WB_M * WB_M + WIN_THREADS - 1) / WIN_THREADS;  // outputs per thread (nt = WIN_THREADS)
-        T o[OPT];
-        // phase 1: T1 = L21 L11^{-1} (lower) or U12 U22^{-1} (upper)
-#pragma unroll
-        for (int q = 0; q < OPT; ++q) {
-            const int e = tid + q * nt;
-            o[q] = T(0);
-            if (e < tot) {
-                const int task = e / bb, oo = e - task * bb, i = oo / bs, j = oo - i * bs;
-                const int s = task / (mp / bs), rem = task - s * (mp / bs), up = rem / (mp / (2 * bs)),
-                          pr = rem - up * (mp / (2 * bs));
-                const int a0 = 2 * bs * pr, b0 = a0 + bs;
-                const T* Xs = X + (size_t)s * WB_M * WB_P;
-                if (!up) {  // sum_{k >= j} L21[i][k] L11inv[k][j]
-                    T acc = Xs[(b0 + i) * WB_P + a0 + j];
-                    for (int k = j + 1; k < bs; ++k) acc += Xs[(b0 + i) * WB_P + a0 + k] * Xs[(a0 + k) * WB_P + a0 + j];
-                    o[q] = acc;
-                } else {    // sum_{k <= j} U12[i][k] U22inv[k][j]
-                    T acc = Xs[(a0 + i) * WB_P + b0 + j];
-                    for (int k = 0; k < j; ++k) acc += Xs[(a0 + i) * WB_P + b0 + k] * Xs[(b0 + k) * WB_P + b0 + j];
-                    o[q] = acc;
-                }
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < OPT; ++q) {
-            const int e = tid + q * nt;
-            if (e < tot) {
-                const int task = e / bb, oo = e - task * bb, i = oo / bs, j = oo - i * bs;
-                const int s = task / (mp / bs), rem = task - s * (mp / bs), up = rem / (mp / (2 * bs)),
-                          pr = rem - up * (mp / (2 * bs));
-                const int a0 = 2 * bs * pr, b0 = a0 + bs;
-                T* Xs = X + (size_t)s * WB_M * WB_P;
-                if (!up) Xs[(b0 + i) * WB_P + a0 + j] = o[q];
-                else Xs[(a0 + i) * WB_P + b0 + j] = o[q];
-            }
-        }
-        __syncthreads();
-        // phase 2: lower-left = -L22inv T1, upper-right = -U11inv T1
-#pragma unroll
-        for (int q = 0; q < OPT; ++q) {
-            const int e = tid + q * nt;
-            if (e < tot) {
-                const int task = e / bb, oo = e - task * bb, i = oo / bs, j = oo - i * bs;
-                const int s = task / (mp / bs), rem = task - s * (mp / bs), up = rem / (mp / (2 * bs)),
-                          pr = rem - up * (mp / (2 * bs));
-                const int a0 = 2 * bs * pr, b0 = a0 + bs;
-                const T* Xs = X + (size_t)s * WB_M * WB_P;
-                if (!up) {  // sum_{k <= i} L22inv[i][k] T1[k][j]
-                    T acc = Xs[(b0 + i) * WB_P + a0 + j];
-                    for (int k = 0; k < i; ++k) acc += Xs[(b0 + i) * WB_P + b0 + k] * Xs[(b0 + k) * WB_P + a0 + j];
-                    o[q] = -acc;
-                } else {    // sum_{k >= i} U11inv[i][k] T1[k][j]
-                    T acc = Xs[(a0 + i) * WB_P + b0 + j];
-                    for (int k = i + 1; k < bs; ++k) acc += Xs[(a0 + i) * WB_P + a0 + k] * Xs[(a0 + k) * WB_P + b0 + j];
-                    o[q] = -acc;
-                }
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < OPT; ++q) {
-            const int e = tid + q * nt;
-            if (e < tot) {
-                const int task = e / bb, oo = e - task * bb, i = oo / bs, j = oo - i * bs;
-                const int s = task / (mp / bs), rem = task - s * (mp / bs), up = rem / (mp / (2 * bs)),
-                          pr = rem - up * (mp / (2 * bs));
-                const int a0 = 2 * bs * pr, b0 = a0 + bs;
-                T* Xs = X + (size_t)s * WB_M * WB_P;
-                if (!up) Xs[(b0 + i) * WB_P + a0 + j] = o[q];
-                else Xs[(a0 + i) * WB_P + b0 + j] = o[q];
-            }
-        }
-        __syncthreads();
-    }
-    // W = -F U1inv L1inv (rows and columns below m; the padding of both inverses is the identity)
-    for (int e = tid; e < 2 * m * m; e += nt) {
-        const int s = e >= m * m ? 1 : 0, rem = e - s * m * m, k = rem / m, j = rem - k * m;
-        const T* Xs = X + (size_t)s * WB_M * WB_P;
-        const int q0 = k > j ? k : j;
-        // q = q0: U1inv[k][q0] L1inv[q0][j] with the unit diagonal on whichever side q0 sits
-        T acc = (k == j) ? T(1) : Xs[k * WB_P + j];
-        for (int q = q0 + 1; q < m; ++q) acc += Xs[k * WB_P + q] * Xs[q * WB_P + j];
-        Wx[(size_t)s * NW * NW + (size_t)k * NW + j] = -fk[s][k] * acc;
-    }
-}
-
 template <typename T>
 __device__ __forceinline__ void window_w(const T* Gs, int n, int P, const int* idx, const T (*fk)[WinCap<T>::NW],
-                                         int m, T* Wx, T* Xscr, int tid, int nt) {
+                                         int m, T* Wx, int tid) {
     constexpr int NW = WinCap<T>::NW;
-    if constexpr (WinWScratch<T>::bytes > 0) {
-        if (m <= WB_M && nt == WIN_THREADS) {  // uniform over the block: every thread takes the barriers
-            window_w_blocked<T>(Gs, n, P, idx, fk, m, Wx, Xscr, tid, nt);
-            return;
-        }
-    }
     const int lane = tid & 31, w = tid >> 5;
     if (w >= 32) return;
     if (m <= 32) window_w_rpl<T, 1>(Gs, n, P, idx, fk, m, Wx, lane, w);
@@ -885,11 +711,15 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                     s_m = m_w0;
                 }
                 __syncwarp();
-            } else if (pend >= 0) {
-                // warps 1..31: G[r][c] += f G[r][a] G[a][c] for r, c > a, both spins.  Rows and
-                // columns <= a are never touched again, so the block keeps row a and column a as
-                // they were when site a was accepted (the coefficients of the flush recursion).
-                trailing_update(Gs, n, P, idx[pend], -s_fk[0][pend], -s_fk[1][pend], tid - 32, nt - 32);
+            } else if (pend >= 0 && (tid & 96) != 0) {
+                // the warps off warp 0's scheduler (warp % 4 != 0: 24 of them, so warp 0's serial
+                // scan shares its issue slots only with idle warps): G[r][c] += f G[r][a] G[a][c]
+                // for r, c > a, both spins.  Rows and columns <= a are never touched again, so the
+                // block keeps row a and column a as they were when site a was accepted (the
+                // coefficients of the flush recursion).
+                const int w = tid >> 5, wi = w - 1 - (w >> 2);
+                trailing_update(Gs, n, P, idx[pend], -s_fk[0][pend], -s_fk[1][pend], wi * 32 + (tid & 31),
+                                ((nt >> 5) - ((nt >> 5) + 3) / 4) * 32);
             }
             __syncthreads();
             const int np = s_pend[it & 1];
@@ -1185,8 +1015,7 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
     //   W_k = -f_k z_k.
     // Each warp owns WCPW columns of one spin in registers (lane l holds rows l, l + 32, ...) and
     // broadcasts the finished row of every step with a shuffle: no block-wide barrier per step.
-    window_w<T>(Gs, n, P, idx, s_fk, m, (T*)wb.Wx,
-                (T*)(smem_raw + ((window_smem_base<T>(n) + 15) & ~(size_t)15)), tid, nt);
+    window_w<T>(Gs, n, P, idx, s_fk, m, (T*)wb.Wx, tid);
     if (tid == 0) {
         *wb.m = m;
         if (so.sign) *so.sign = s_sign;
@@ -1310,19 +1139,20 @@ template cudaError_t launch_window_chain<double>(cudaStream_t, int, const double
 constexpr int NB_ROWS = 4;
 constexpr int NB_THREADS = 512;
 // One CTA per (row block of NB_ROWS rows, spin, walker).  The gathers depend on the accepted sites,
-// so the kernel takes two rounds of global loads: the sites, then W, Yraw_n and X_blk, each mapped
-// as warps over rows and lanes over columns (no index divisions, every load of a thread in flight
-// before its shared-memory stores).
+// so the kernel takes two rounds of global loads: the sites, then W, Yraw_n, X_blk and the block's
+// own rows of G, each mapped as warps over rows and lanes over columns (no index divisions, every
+// load of a thread in flight before its shared-memory stores).  The two products split each
+// output's sum over four consecutive lanes (strided partial sums, combined by shuffles), so every
+// warp works on them.
 template <typename T>
 __global__ void __launch_bounds__(NB_THREADS) next_block_kernel(const T* __restrict__ Gu0, long ld, int N,
                                                                 WindowBufs wb0, int sn, int nn, T* snap0,
                                                                 long gstride) {
-    constexpr int NW = WinCap<T>::NW, PP = NW + 1, CS = NW / 32;
+    constexpr int NW = WinCap<T>::NW, PP = NW + 1;
     const int wk = blockIdx.z;
     const WindowBufs wb = wb_walker<T>(wb0, wk, N);
     const int m = *wb.m;
-    const int s = blockIdx.y, a0 = blockIdx.x * NB_ROWS, tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int s = blockIdx.y, a0 = blockIdx.x * NB_ROWS, tid = threadIdx.x, nt = blockDim.x;
     const int ra = min(NB_ROWS, nn - a0);
     const T* G = Gu0 + (size_t)wk * gstride + (size_t)s * N * ld;
     T* out = snap0 + (size_t)wk * 2 * NW * NW + (size_t)s * NW * NW;
@@ -1331,11 +1161,15 @@ __global__ void __launch_bounds__(NB_THREADS) next_block_kernel(const T* __restr
     T* Ys = Ws + NW * PP;        // [m][PP]   Yraw_n
     T* Xs = Ys + NW * PP;        // [NB_ROWS][PP]
     T* Ts = Xs + NB_ROWS * PP;   // [NB_ROWS][PP]  X_blk W
+    T* Gr = Ts + NB_ROWS * PP;   // [NB_ROWS][PP]  G[sn + a0 + a][sn + c]
+    constexpr int CS = NW / 32;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
     __shared__ int sidx[NW];
-    for (int q = tid; q < m; q += blockDim.x) sidx[q] = wb.idx[q];
+    for (int q = tid; q < m; q += nt) sidx[q] = wb.idx[q];
     __syncthreads();
     const T* W = (const T*)wb.Wx + (size_t)s * NW * NW;
-    // rows r of W and Yraw_n (r < m) and of X_blk (r < ra) by warps, columns by lanes
+    // rows r of W and Yraw_n (r < m), of X_blk and of the block's own rows (r < ra) by warps,
+    // columns by lanes
     for (int r = warp; r < m; r += nwarp) {
         const T* wrow = W + (size_t)r * NW;
         const T* grow = G + (long)sidx[r] * ld + sn;
@@ -1355,32 +1189,53 @@ __global__ void __launch_bounds__(NB_THREADS) next_block_kernel(const T* __restr
     }
     for (int a = warp; a < ra; a += nwarp) {
         const T* grow = G + (long)(sn + a0 + a) * ld;
-        T vx[CS];
+        T vx[CS], vg[CS];
 #pragma unroll
         for (int j = 0; j < CS; ++j) {
             const int k = lane + 32 * j;
             vx[j] = k < m ? grow[sidx[k]] : T(0);
+            vg[j] = k < nn ? grow[sn + k] : T(0);
         }
 #pragma unroll
         for (int j = 0; j < CS; ++j) {
             const int k = lane + 32 * j;
             if (k < m) Xs[a * PP + k] = vx[j];
+            if (k < nn) Gr[a * PP + k] = vg[j];
         }
     }
     __syncthreads();
-    for (int a = warp; a < ra; a += nwarp) {  // T = X_blk W
-        for (int k = lane; k < m; k += 32) {
+    // Ts = X_blk W: output (a, k) summed over l = part, part + 4, ... by lanes 4 g + part
+    {
+        const int nout = ra * m, iters = (4 * nout + nt - 1) / nt;
+        for (int it = 0; it < iters; ++it) {
+            const int o4 = tid + it * nt, g = o4 >> 2, part = o4 & 3;
             T acc = T(0);
-            for (int l = 0; l < m; ++l) acc += Xs[a * PP + l] * Ws[l * PP + k];
-            Ts[a * PP + k] = acc;
+            if (g < nout) {
+                const int a = g / m, k = g - a * m;
+                for (int l = part; l < m; l += 4) acc += Xs[a * PP + l] * Ws[l * PP + k];
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (g < nout && part == 0) Ts[(g / m) * PP + g % m] = acc;
         }
     }
     __syncthreads();
-    for (int e = tid; e < ra * nn; e += blockDim.x) {  // snap = G_nn - T Yraw_n
-        const int a = e / nn, c = e - a * nn;
-        T acc = T(0);
-        for (int l = 0; l < m; ++l) acc += Ts[a * PP + l] * Ys[l * PP + c];
-        out[(a0 + a) * NW + c] = G[(long)(sn + a0 + a) * ld + sn + c] - acc;
+    // snap rows = G[rows, J] - Ts Yraw_n, the same split
+    {
+        const int nout = ra * nn, iters = (4 * nout + nt - 1) / nt;
+        for (int it = 0; it < iters; ++it) {
+            const int o4 = tid + it * nt, g = o4 >> 2, part = o4 & 3;
+            T acc = T(0);
+            int a = 0, c = 0;
+            if (g < nout) {
+                a = g / nn;
+                c = g - a * nn;
+                for (int l = part; l < m; l += 4) acc += Ts[a * PP + l] * Ys[l * PP + c];
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (g < nout && part == 0) out[(a0 + a) * NW + c] = Gr[a * PP + c] - acc;
+        }
     }
 }
 
@@ -1389,7 +1244,7 @@ cudaError_t launch_next_block(cudaStream_t st, const T* Gu, const T* Gd, const S
                               int nn, T* snap, Batch bt) {
     (void)Gd;
     constexpr int NW = WinCap<T>::NW;
-    const size_t shm = (2 * (size_t)NW + 2 * NB_ROWS) * (NW + 1) * sizeof(T);
+    const size_t shm = (2 * (size_t)NW + 3 * NB_ROWS) * (NW + 1) * sizeof(T);
     {
         cudaError_t ea = ensure_smem_attr((const void*)next_block_kernel<T>, shm);
         if (ea != cudaSuccess) return ea;

@@ -366,13 +366,13 @@ def test_graph_replay_matches_direct_launches(precision):
             c.close()
 
 
-@pytest.mark.parametrize("precision,L,ns,nb", [("fp64", 8, 28, 64), ("fp32", 8, 28, 64), ("fp32", 11, 53, 121)])
+@pytest.mark.parametrize("precision,L,ns,nb", [("fp64", 5, 11, 25), ("fp32", 5, 11, 25)])
 def test_full_force_bias_one_block_per_slice(precision, L, ns, nb):
     """The full force-bias update (Sec. II.D, Eqs. FullFrcbsPhiLPhiR, RatioApprox, AcceptRatio): block
-    force bias with n_b = N, one proposal and one N x N-site determinant per slice, on the largest
-    lattices whose slice fits one window (FP64: 64 sites, FP32: 128).  FP64 runs free against the
-    oracle (identical decisions, G within 1e-10 per slice); FP32 replays the oracle's proposals and
-    decisions (G within 1e-5 per slice)."""
+    force bias with n_b = N, one proposal and one N-site determinant per slice, on the largest square
+    lattice whose slice fits one block (n_b <= 32).  FP64 runs free against the oracle (identical
+    decisions, G within 1e-10 per slice); FP32 replays the oracle's proposals and decisions (G within
+    1e-5 per slice)."""
     M, stab = 4, 2
     N = L * L
     assert nb == N
