@@ -4,15 +4,19 @@ Workload (one step = one full sweep, forward l = 1..M then backward l = M..1):
   standard 2D Hubbard, 40 x 40 periodic (N = 1600), t = 1, U = 6 (real spin decoupling),
   filling 0.875 (700 particles per spin), dtau = 0.05, M = 80 slices, FP32 bulk G,
   delayed update (k sites per delayed step), FP64 re-orthonormalisation and G recompute
-  every 5 slices (the FP32 drift of G stays under 1e-3 there; the workload's own 10 slices let it
-  reach 4e-2, reported beside the headline).  One walker per GPU (weak scaling across ranks, no collective on the
-  data path).  Inputs are synthetic and seeded (trial state, fields, Philox uniforms).
+  every 5 slices (the FP32 drift of G stays under 1e-3 there; the workload's own 10 slices let
+  it reach 4e-2, reported beside the headline).  One walker per GPU (weak scaling across ranks,
+  no collective on the data path).  Inputs are synthetic and seeded (trial state, fields,
+  Philox uniforms).
 
-The JSON line reports the device-timed sweep throughput (value), the update-only rate,
-local and block-force-bias comparisons on a bounded sample of slices, the FP32 drift of G
-against the FP64 recompute, the roofline of the dominant kernel (measured live with CUDA
-events on the launching stream), the clocks seen during the timed region, an end-to-end
-number through the C ABI with host buffers, and the FP64 oracle timed on the host cores.
+The timed sweeps replay each slice-step from the CUDA graph the library captured for it (the
+recomputes launch directly); the same sweeps are then repeated with direct launches under the
+library's phase profiler for the breakdown.  The JSON line reports the device-timed sweep
+throughput (value), the update-only rate, local and block-force-bias comparisons on a bounded
+sample of slices, the FP32 drift of G against the FP64 recompute, the roofline of the dominant
+kernel (measured live with CUDA events on the launching stream), the clocks seen during the
+timed region, an end-to-end number through the C ABI with host buffers, and the FP64 oracle
+timed on the host cores.
 """
 from __future__ import annotations
 
@@ -203,8 +207,8 @@ def arm_config(k):
                         f"dtau={DTAU}, M={M}, FP32 bulk G, delayed k={k}, FP64 recompute "
                         f"every {STAB} slices (median FP32 drift of G at the recompute points under "
                         f"{DRIFT_TOL:g}), separable wrap (exp(-dtau K) = Ex (x) Ex)",
-            "step": f"one full sweep (2M = {2 * M} slice-steps: wrap + delayed update) + {2 * M // STAB} FP64 "
-                    f"recomputes",
+            "step": f"one full sweep (2M = {2 * M} slice-steps: wrap + delayed update, each replayed from its "
+                    f"captured CUDA graph) + {2 * M // STAB} FP64 recomputes",
             "walkers_per_gpu": 1, "l2": "flushed between timed steps (256 MB write)"}
 
 
@@ -270,7 +274,12 @@ def main():
     torch.cuda.synchronize()
 
     # ---------------- timed region: K full sweeps ----------------
-    ctx.set_profiling(True)
+    # Every slice-step replays the CUDA graph the library captured for it (one untimed sweep
+    # captures them all); the FP64 recomputes launch directly.  The library counts each replayed
+    # graph's kernels as launches.
+    ctx.set_graphs(True)
+    sweep("delayed", args.k, args.nb)
+    torch.cuda.synchronize()
     launches0 = afqmc.afqmc_launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist is not None:
@@ -283,9 +292,8 @@ def main():
             sweep("delayed", args.k, args.nb)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
-    launches = afqmc.afqmc_launch_count() - launches0 - 0
-    prof = ctx.profile()
-    ctx.set_profiling(False)
+    launches = afqmc.afqmc_launch_count() - launches0
+    ctx.set_graphs(False)
     ms_steps = [a.elapsed_time(b) for a, b in ev]
     ms_total = sum(ms_steps)
     if dist is not None:
@@ -294,6 +302,23 @@ def main():
     updates_per_step = N * M * 2
     value = job_throughput(world, updates_per_step, args.steps, ms_total)
     clocks = clk.summary()
+
+    # ---------------- the same sweeps with direct launches, under the phase profiler ----------------
+    # (the phases, the per-kernel rooflines and the update-only rate come from this pass)
+    ctx.set_profiling(True)
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms_direct = 0.0
+    for i in range(args.steps):
+        flush_buf.zero_()
+        d0.record(stream)
+        sweep("delayed", args.k, args.nb)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        ms_direct += d0.elapsed_time(d1)
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    direct = {"value": updates_per_step * args.steps / (ms_direct / 1e3), "ms_per_step": ms_direct / args.steps,
+              "note": "the same sweeps with every kernel launched directly, under the phase profiler"}
 
     # update-only (the paper's "time for update per sweep"): prep + window chains + flushes
     # (the flush runs on a second stream under the window loop; its interval is not added)
@@ -315,20 +340,6 @@ def main():
     l2_gbs = optional_leg("l2_copy", lambda: l2_copy_bandwidth(torch))
     kernels += local_and_chain_rooflines(cmp_prof, pk, pk_src, l2_gbs if isinstance(l2_gbs, float) else None)
 
-    # ---------------- the same sweep with CUDA-graph replay (profiling off) ----------------
-    ctx.set_graphs(True)
-    sweep("delayed", args.k, args.nb)  # captures every slice-step
-    torch.cuda.synchronize()
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    for _ in range(args.steps):
-        sweep("delayed", args.k, args.nb)
-    g1.record(stream)
-    torch.cuda.synchronize()
-    ms_graph = g0.elapsed_time(g1) / args.steps
-    ctx.set_graphs(False)
-    graphs = {"value": updates_per_step / (ms_graph / 1e3), "ms_per_step": ms_graph,
-              "note": "the same sweeps with every slice-step replayed from a captured CUDA graph (profiling off)"}
 
     # ---------------- end to end through the C ABI with host buffers ----------------
     e2e = None
@@ -406,7 +417,7 @@ def main():
             "clocks": clocks,
             "gpu_launches": launches,
             "e2e": e2e,
-            "cuda_graphs": graphs,
+            "direct_launches": direct,
             "batched_population": batch,
             "soc": soc_res,
             "dense_wrap": dense,
@@ -737,8 +748,10 @@ OZ_PAIRS = 45
 NCU_TRAFFIC = {"elim": None, "lu_o": None,
                "solve": 25.807104e6 + 0.080896e6,      # lu_solve_kernel, 700 x 700, 1600 right-hand sides
                "wrap_gemm": 30.749184e6 + 0.02432e6,   # tc_gemm_kernel<160, split3>, 1600^3, both spins
-               "flush_gemm": None,                     # rankm_kernel (1600 x 1600 x m, both spins): not yet captured
-               "sep": None}                            # sep_line_circ_kernel<float, 40>: not yet captured
+               "flush_gemm": 22.055936e6 + 0.0,        # rankm_kernel, 1600 x 1600 x m, both spins (writes stay in L2)
+               # sep_line_circ_kernel<float, 40>: the four passes of one wrap (cold cache: 20.53 MB read per
+               # pass, writes absorbed by L2)
+               "sep": 20.528128e6 + 20.528128e6 + 20.528384e6 + 20.553728e6}
 
 
 def fp32_alu_peak(pk):
@@ -786,27 +799,41 @@ def kernel_rooflines(prof, gemm, pk, pk_src, steps, wrap="separable", wrap_tile=
     # interval), LU of U_L U_R (ns x ns) and the solve (U_L U_R) Z = U_L with N right-hand sides.
     fp64 = fp64_alu_peak(pk)
     src64 = fp64_peak_source(pk, pk_src)
+    dg = prof.get("dgemm", {"ms": 0.0, "intervals": 0})
+    n_rc = prof.get("lu_o", {"intervals": 0})["intervals"]
+    # The FP32-bulk recompute forms (U_L U_R)^{-1} (a solve with ns right-hand sides) and
+    # Z = (U_L U_R)^{-1} U_L as a third digit-split product; otherwise the solve has N right-hand sides.
+    inv = n_rc > 0 and dg["intervals"] >= 3 * n_rc
+    solve = (("solve", "lu_solve_kernel (FP64 (U_L U_R)^-1 from the LU, ns right-hand sides, both spins)",
+              2 * 2.0 * NS ** 3) if inv else
+             ("solve", "lu_solve_kernel (FP64 (U_L U_R) Z = U_L, N right-hand sides, both spins)",
+              2 * 2.0 * NS ** 2 * N))
     for name, label, flop in (
             ("elim", "lu_panel_kernel + lu_update_kernel (FP64 LU of the propagated N x ns factor, both spins)",
              2 * (N * NS ** 2 - NS ** 3 / 3.0)),
             ("lu_o", "lu_panel_kernel + lu_update_kernel (FP64 LU of U_L U_R, ns x ns, both spins)",
              2 * (2.0 / 3.0) * NS ** 3),
-            ("solve", "lu_solve_kernel (FP64 (U_L U_R) Z = U_L, N right-hand sides, both spins)",
-             2 * 2.0 * NS ** 2 * N)):
+            solve):
         ph = prof.get(name, {"ms": 0.0, "intervals": 0})
         if ph["intervals"] > 0:
             ach = flop * ph["intervals"] / (ph["ms"] / 1e3) / 1e12
             out.append({"kernel": label, "bound": "alu", "achieved": ach, "peak": fp64, "unit": "TFLOP/s",
-                        "frac": ach / fp64, "traffic": NCU_TRAFFIC.get(name), "launches": ph["intervals"],
+                        "frac": ach / fp64, "traffic": None if (name == "solve" and inv) else NCU_TRAFFIC.get(name),
+                        "launches": ph["intervals"],
                         "ms_per_launch": ph["ms"] / ph["intervals"], "ms_per_step": ph["ms"] / steps,
                         "work_per_launch": flop, "peak_source": src64})
-    dg = prof.get("dgemm", {"ms": 0.0, "intervals": 0})
     if dg["intervals"] > 0:
-        # the two products alternate: U_L U_R (ns x ns x N) and U_R Z (N x N x ns), both spins
-        flop64 = 2.0 * NS * N * (NS + N)  # FP64-equivalent flop per product, averaged over the pair
+        # FP64-equivalent flop per product (both spins), averaged over a recompute's products:
+        # U_L U_R (ns x ns x N), [(U_L U_R)^{-1} U_L (ns x N x ns),] U_R Z (N x N x ns)
+        if inv:
+            flop64 = 2.0 * (2 * 2.0 * NS * NS * N + 2.0 * N * N * NS) / 3.0
+            what = "U_L U_R, (U_L U_R)^-1 U_L and U_R Z"
+        else:
+            flop64 = 2.0 * NS * N * (NS + N)
+            what = "U_L U_R and U_R Z"
         ach64 = flop64 * dg["intervals"] / (dg["ms"] / 1e3) / 1e12
         ach = OZ_PAIRS * ach64
-        out.append({"kernel": "digit-split FP64 products U_L U_R and U_R Z (bf16 tcgen05, 45 plane pairs, both spins)",
+        out.append({"kernel": "digit-split FP64 products %s (bf16 tcgen05, 45 plane pairs, both spins)" % what,
                     "bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                     "frac": ach / pk["bf16_tflops"], "traffic": None, "launches": dg["intervals"],
                     "ms_per_launch": dg["ms"] / dg["intervals"], "ms_per_step": dg["ms"] / steps,

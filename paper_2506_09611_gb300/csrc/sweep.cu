@@ -711,15 +711,11 @@ __global__ void __launch_bounds__(WIN_THREADS) window_kernel(const T* __restrict
                     s_m = m_w0;
                 }
                 __syncwarp();
-            } else if (pend >= 0 && (tid & 96) != 0) {
-                // the warps off warp 0's scheduler (warp % 4 != 0: 24 of them, so warp 0's serial
-                // scan shares its issue slots only with idle warps): G[r][c] += f G[r][a] G[a][c]
-                // for r, c > a, both spins.  Rows and columns <= a are never touched again, so the
-                // block keeps row a and column a as they were when site a was accepted (the
-                // coefficients of the flush recursion).
-                const int w = tid >> 5, wi = w - 1 - (w >> 2);
-                trailing_update(Gs, n, P, idx[pend], -s_fk[0][pend], -s_fk[1][pend], wi * 32 + (tid & 31),
-                                ((nt >> 5) - ((nt >> 5) + 3) / 4) * 32);
+            } else if (pend >= 0) {
+                // warps 1..31: G[r][c] += f G[r][a] G[a][c] for r, c > a, both spins.  Rows and
+                // columns <= a are never touched again, so the block keeps row a and column a as
+                // they were when site a was accepted (the coefficients of the flush recursion).
+                trailing_update(Gs, n, P, idx[pend], -s_fk[0][pend], -s_fk[1][pend], tid - 32, nt - 32);
             }
             __syncthreads();
             const int np = s_pend[it & 1];
