@@ -883,7 +883,7 @@ def kernel_rooflines(prof, gemm, pk, pk_src, steps, wrap="separable", wrap_tile=
     if fg["intervals"] > 0:
         byts = 2 * 2 * N * N * 4  # read + write of both spins' G (FP32); X and Y' panels are O(N m)
         ach = byts * fg["intervals"] / (fg["ms"] / 1e3) / 1e9
-        out.append({"kernel": "rank-m flush product G -= X Y' (SIMT FP32, both spins)", "bound": "hbm",
+        out.append({"kernel": "rankm_kernel: the rank-m flush product G -= X Y' (SIMT FP32, both spins)", "bound": "hbm",
                     "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
                     "traffic": NCU_TRAFFIC["flush_gemm"], "launches": fg["intervals"],
                     "ms_per_launch": fg["ms"] / fg["intervals"], "ms_per_step": fg["ms"] / steps,
