@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--no-soc", action="store_true", help="skip the spin-orbit-coupled leg")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core wrap leg")
     ap.add_argument("--no-tform", action="store_true", help="skip the T-form sweep")
+    ap.add_argument("--no-cpqmc", action="store_true", help="skip the constrained-path AFQMC leg")
     ap.add_argument("--no-stab-sweep", action="store_true", help="skip the FP32 recompute-period legs")
     ap.add_argument("--no-precision", action="store_true", help="skip the per-precision accuracy report")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-bulk sweep")
@@ -357,6 +358,9 @@ def main():
     tf = None
     if not args.no_tform:
         tf = optional_leg("tform", lambda: tform_leg(afqmc, torch, stream, args, seed))
+    cpq = None
+    if not args.no_cpqmc:
+        cpq = optional_leg("cpqmc", lambda: cpqmc_leg(afqmc, torch, stream, seed))
     dense = None
     if not args.no_dense:
         dense = optional_leg("dense_wrap", lambda: dense_wrap_leg(afqmc, torch, stream, args, seed,
@@ -422,6 +426,7 @@ def main():
             "soc": soc_res,
             "dense_wrap": dense,
             "tform": tf,
+            "cpqmc": cpq,
             "precision_report": prec,
             "fp32_recompute_periods": stabs,
             "fp64_bulk": f64,
@@ -1089,6 +1094,51 @@ def end_to_end(afqmc, torch, stream, args, seed, rank):
     return {"value": N * M * 2 / t, "unit": UNIT, "h2d_bytes_per_step": int(Ph.nbytes + Xh.nbytes),
             "d2h_bytes_per_step": int(Xout.nbytes + 16),
             "note": "create + init_walkers (FP64 left stack and G(0)) + 1 sweep + energy + fields readback"}
+
+
+CP_L, CP_U, CP_WALKERS, CP_STEPS, CP_EVERY = 16, 4.0, 32, 10, 5
+
+
+def cpqmc_leg(afqmc, torch, stream, seed):
+    """Constrained-path AFQMC (Sec. IV.D): an ensemble of CP_WALKERS walkers on the 16 x 16 Hubbard
+    model (U = 4, n = 0.875, dtau = 0.05, FP64) guided by the trial determinant, each step
+    e^{-dtau K} with its overlap weight and then the slice's fields by the heat bath (local: one
+    site per window; delayed: windows of k sites) or by block force bias, with the comb and a
+    re-orthonormalisation every CP_EVERY steps.  Per scheme: two untimed steps, then CP_STEPS steps
+    timed with CUDA events on the stream (afqmc_cp_step returns the weights to the host, so each
+    step ends synchronised).  Rate = walkers x N field draws per step / time."""
+    ns = inputs.n_sigma_for(CP_L, FILLING)
+    P = inputs.trial_state(CP_L, CP_L, ns)
+    n = CP_L * CP_L
+    out = {"workload": f"{CP_L}x{CP_L} Hubbard, U/t={CP_U}, n={FILLING} ({ns} per spin), dtau={DTAU}, "
+                       f"{CP_WALKERS} walkers, FP64, comb + re-orthonormalisation every {CP_EVERY} steps",
+           "unit": "field updates/s", "steps": CP_STEPS}
+    rng = np.random.default_rng(seed)
+    for mode, k, nb in (("local", 1, 1), ("delayed", 16, 1), ("delayed", 32, 1), ("blockfb", 1, 8)):
+        cp = afqmc.CPContext(CP_L, ns, CP_WALKERS, P, dtau=DTAU, U=CP_U, t=T_HOP, seed=seed)
+        try:
+            for _ in range(2):
+                cp.step(mode, k, nb, stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for i in range(CP_STEPS):
+                cp.step(mode, k, nb, stream=stream)
+                if (i + 1) % CP_EVERY == 0:
+                    cp.comb(float(rng.uniform()), stream=stream)
+                    cp.reorth(stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            el, emean = cp.energy(stream=stream)
+            key = mode if mode == "local" else (f"delayed_k{k}" if mode == "delayed" else f"blockfb_nb{nb}")
+            out[key] = {"value": CP_WALKERS * n * CP_STEPS / (ms / 1e3), "ms_per_step": ms / CP_STEPS,
+                        "energy_per_site": float(emean) / n}
+        finally:
+            cp.close()
+    base = out["local"]["value"]
+    out["speedup_vs_local"] = {k: v["value"] / base for k, v in out.items() if isinstance(v, dict) and "value" in v}
+    return out
 
 
 def tform_leg(afqmc, torch, stream, args, seed):
