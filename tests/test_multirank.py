@@ -146,7 +146,7 @@ def test_kernel_rooflines_use_the_documented_work_per_launch():
     assert wrap["achieved"] == pytest.approx(1.6384e10 * 320 / 0.052 / 1e12)
     assert wrap["peak"] == pytest.approx(1911.7 * 1.1 / 2.25) and wrap["bound"] == "tensor"
     assert wrap["frac"] == pytest.approx(wrap["achieved"] / wrap["peak"])
-    flush = by["rank-m"]
+    flush = by["rankm_kernel:"]
     assert flush["work_per_launch"] == 2 * 2 * 1600 * 1600 * 4 == 40960000
     assert flush["achieved"] == pytest.approx(40960000 * 4000 / 0.160 / 1e9) and flush["unit"] == "GB/s"
     solve = by["lu_solve_kernel"]
