@@ -509,7 +509,8 @@ static cudaError_t form_Z(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac&
     cudaError_t e;
     if ((e = form_O(ctx, w, st, R, Lf, s0, ng, sign)) != cudaSuccess) return e;
     if (w->Oinv) {
-        // FP32 bulk: O^{-1} from the same LU (the solve with the identity, ns right-hand sides), then
+        // FP32 bulk: O^{-1} from the same LU (the solve with the identity in pivot order, ns
+        // right-hand sides: the forward substitution of column c starts at row c), then
         // Z = O^{-1} U_L as an FP64-accurate digit-split product.  The forward error of Z is that of
         // the solve up to a factor of order one; the FP32 bulk keeps about seven digits of G.
         SolveArgs si;
@@ -517,10 +518,7 @@ static cudaError_t form_Z(afqmc_ctx* ctx, Walker* w, cudaStream_t st, const Fac&
         si.ostride = os;
         si.perm0 = w->perm2;
         si.pstride = w->rows_max();
-        si.B0 = w->Ieye;
-        si.wstride = 0;
-        si.sstride = 0;
-        si.ldb = w->nsm;
+        si.eye = 1;  // the identity in pivot order, generated in the kernel
         si.ng = ng;
         si.Z0 = w->Oinv;
         si.zstride = os;
@@ -936,16 +934,7 @@ int afqmc_init_walkers(afqmc_ctx* ctx, int n_walkers, const int* L, const int* n
                 CK(dalloc(A, (char**)&w->ozw, f));
                 CK(dalloc(A, &w->ozs, ozaki_sc_doubles(N > nsm ? N : nsm, N > nsm ? N : nsm, 2 * nwk) * 8));
             }
-            if (inv) {
-                CK(dalloc(A, &w->Oinv, (size_t)nwk * 2 * nsm * nsm * 8));
-                if (!w->Ieye) {
-                    std::vector<double> eye((size_t)nsm * nsm, 0.0);
-                    for (int i = 0; i < nsm; ++i) eye[(size_t)i * nsm + i] = 1.0;
-                    CK(dalloc(A, &w->Ieye, eye.size() * 8));
-                    CK(cudaMemcpyAsync(w->Ieye, eye.data(), eye.size() * 8, cudaMemcpyHostToDevice, st));
-                    CK(cudaStreamSynchronize(st));  // the host identity goes out of scope
-                }
-            }
+            if (inv) CK(dalloc(A, &w->Oinv, (size_t)nwk * 2 * nsm * nsm * 8));
         }
         CK(cudaMemsetAsync(w->err, 0, sizeof(int), st));
         CK(cudaMemsetAsync(w->dec, 0, (size_t)nwk * 2 * N, st));  // the block half stays 0 outside block FB

@@ -178,6 +178,10 @@ struct SolveArgs {
     long ldl = 0;
     long ldb = 0;  // row stride of B (0: N)
     int ns = 0, N = 0, nmat = 1;
+    // eye != 0: B is the identity with its columns in pivot order (column c = e_{perm[c]}, N = ns,
+    // B0 unused), so the forward substitution of column c starts at row c; the solution's column c
+    // is stored at column perm[c], which makes Z = O^{-1}
+    int eye = 0;
 };
 cudaError_t launch_lu_solve(cudaStream_t st, const SolveArgs& a);
 template <typename T>

@@ -422,16 +422,19 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(SolveArgs a) {
     int* sp = (int*)(rinv + ns);                // [ns]
     for (int j = tid; j < ns; j += nt) sp[j] = perm[j];
     __syncthreads();
+    const bool eye = a.eye != 0;
     for (int e = tid; e < ns * SV_COLS; e += nt) {
         const int j = e / SV_COLS, c = e - j * SV_COLS;
-        y[j * SV_YP + c] = (c < nc) ? B[(long)sp[j] * ldb + c0 + c] : 0.0;
+        y[j * SV_YP + c] = (c < nc) ? (eye ? (j == c0 + c ? 1.0 : 0.0) : B[(long)sp[j] * ldb + c0 + c]) : 0.0;
     }
     for (int j = tid; j < ns; j += nt) rinv[j] = 1.0 / LU[(long)sp[j] * ldl + j];
     __syncthreads();
-    // forward substitution (unit lower L)
-    for (int J0 = 0; J0 < ns; J0 += 32) {
+    // forward substitution (unit lower L); with the pivot-ordered identity every y_j with j < c0
+    // is zero in this block of columns, so the rows above c0 and their products are skipped
+    const int j_first = eye ? c0 : 0;
+    for (int J0 = (j_first / 32) * 32; J0 < ns; J0 += 32) {
         const int jb = min(32, ns - J0);
-        for (int k0 = 0; k0 < J0; k0 += SV_KB) {
+        for (int k0 = (j_first / SV_KB) * SV_KB; k0 < J0; k0 += SV_KB) {
             const int kb = min(SV_KB, J0 - k0);
             for (int e = tid; e < jb * SV_KB; e += nt) {
                 const int r = e / SV_KB, k = e - r * SV_KB;
@@ -512,7 +515,7 @@ __global__ void __launch_bounds__(256) lu_solve_kernel(SolveArgs a) {
     }
     for (int e = tid; e < ns * SV_COLS; e += nt) {
         const int j = e / SV_COLS, c = e - j * SV_COLS;
-        if (c < nc) Z[(long)j * N + c0 + c] = y[j * SV_YP + c];
+        if (c < nc) Z[(long)j * N + (eye ? sp[c0 + c] : c0 + c)] = y[j * SV_YP + c];
     }
 }
 
