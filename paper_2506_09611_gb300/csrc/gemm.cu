@@ -2,7 +2,9 @@
 //
 // Used by the wrap G <- D E G E^{-1} D^{-1} (Eqs. BlMat, GrFMat), the rank-m
 // flush of the delayed and block force-bias updates (Eqs. FinalDelay,
-// BlkFrcBsTnew2 in G form) and the FP64 recompute (Eq. GrFMatNew).
+// BlkFrcBsTnew2 in G form) and the FP64 recompute (Eq. GrFMatNew).  An FP32
+// update C += alpha A B with a small inner dimension (K <= 64: a window's flush)
+// takes rankm_kernel, written for that shape; everything else the general tile.
 #include "internal.h"
 
 namespace afq {
