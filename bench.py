@@ -809,8 +809,10 @@ def kernel_rooflines(prof, gemm, pk, pk_src, steps, wrap="separable", wrap_tile=
     # The FP32-bulk recompute forms (U_L U_R)^{-1} (a solve with ns right-hand sides) and
     # Z = (U_L U_R)^{-1} U_L as a third digit-split product; otherwise the solve has N right-hand sides.
     inv = n_rc > 0 and dg["intervals"] >= 3 * n_rc
-    solve = (("solve", "lu_solve_kernel (FP64 (U_L U_R)^-1 from the LU, ns right-hand sides, both spins)",
-              2 * 2.0 * NS ** 3) if inv else
+    # (the pivot-ordered identity: column c's forward substitution starts at row c, ns^3 / 3 flop
+    # forward and ns^3 backward per matrix)
+    solve = (("solve", "lu_solve_kernel (FP64 (U_L U_R)^-1 from the LU, the identity in pivot order, both spins)",
+              2 * (4.0 / 3.0) * NS ** 3) if inv else
              ("solve", "lu_solve_kernel (FP64 (U_L U_R) Z = U_L, N right-hand sides, both spins)",
               2 * 2.0 * NS ** 2 * N))
     for name, label, flop in (
