@@ -99,6 +99,9 @@ struct Walker {
     cudaEvent_t ev_wrap = nullptr, ev_prop = nullptr;  // after each slice's wrap; after the last propagation
     int prop_pos = -1, prop_dir = 0;  // Ucur holds the factor at prop_pos (direction prop_dir) after ev_prop
     int pend_slice = 0;               // forward slice whose propagation waits for the next slice's wrap
+    // FP32 bulk, G form: slices of propagation in the current factor since its last
+    // re-orthonormalisation (reset when the sweep turns), and the direction it counts for
+    int orth_since = 0, orth_dir = 0;
     cudaStream_t sm = nullptr;  // the group's main stream (forked from the caller's stream)
     cudaEvent_t ev_chain[2] = {nullptr, nullptr}, ev_prod[2] = {nullptr, nullptr}, ev_done = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -698,6 +701,10 @@ static cudaError_t from_stack(Walker* w, cudaStream_t st, bool right, int j) {
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+// FP32 bulk, G form: the most slices of propagation a stack basis carries between two
+// re-orthonormalisations (the recompute may come more often; see afqmc_recompute_G).
+constexpr int ORTHO_SLICES = 10;
+
 extern "C" {
 
 const char* afqmc_strerror(int code) {
@@ -1653,11 +1660,11 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
         // the factors of the current position: one side from the stacks, the other propagated
         // over the last S slices from the previous stack entry and re-orthonormalised.  With an
         // FP32 bulk G (G form) the re-orthonormalisation leaves the critical path: G is formed
-        // from the propagated factor itself (S slices from an orthonormal basis, so its column
-        // scales spread by at most cond(B)^S and G keeps far more than FP32 accuracy; Eq.
-        // GrFMatNew holds for any basis of the same space), and the LU that makes the stack
-        // entry runs afterwards on the propagation stream, where the next interval's propagation
-        // starts from it.
+        // from the propagated factor itself (at most ORTHO_SLICES slices from an orthonormal
+        // basis, so its column scales spread by at most cond(B)^ORTHO_SLICES and G keeps far more
+        // than FP32 accuracy; Eq. GrFMatNew holds for any basis of the same space), and the LU
+        // that makes the stack entry, when one is due, runs afterwards on the propagation stream,
+        // where the next interval's propagation starts from it.
         const bool fwd = w->last_dir > 0;
         const bool prop = fwd ? (j > 0) : (w->pos != ctx->p.M);
         const bool defer = prop && !f64 && ctx->form == AFQMC_FORM_G;
@@ -1706,11 +1713,24 @@ int afqmc_recompute_G(afqmc_ctx* ctx, double* rel_drift, void* stream) {
                 else CK(finish_G<float>(ctx, w, st, R, grp[gi][0], ng[gi], true));
             }
             if (defer) {  // the stack entry, off the critical path
+                // Re-orthonormalise only when the next interval would otherwise propagate the basis
+                // over more than ORTHO_SLICES slices: its column scales then spread by at most
+                // cond(B)^ORTHO_SLICES, as at a recompute period of that length, which G formed in
+                // FP64 from that basis absorbs far below FP32 rounding.
+                if (w->orth_dir != w->last_dir) {
+                    w->orth_dir = w->last_dir;
+                    w->orth_since = 0;
+                }
+                w->orth_since += S;
+                const bool ortho = w->orth_since + S > ORTHO_SLICES;
                 CK(cudaEventRecord(w->ev_rc, st));
                 CK(cudaStreamWaitEvent(w->sp, w->ev_rc, 0));
-                for (int gi = 0; gi < ngr; ++gi) {
-                    if (fwd) CK(stab_rows(ctx, w, w->sp, fac_cur(w), grp[gi][0], ng[gi], nullptr));
-                    else CK(stab_cols(ctx, w, w->sp, fac_cur(w), grp[gi][0], ng[gi], nullptr));
+                if (ortho) {
+                    for (int gi = 0; gi < ngr; ++gi) {
+                        if (fwd) CK(stab_rows(ctx, w, w->sp, fac_cur(w), grp[gi][0], ng[gi], nullptr));
+                        else CK(stab_cols(ctx, w, w->sp, fac_cur(w), grp[gi][0], ng[gi], nullptr));
+                    }
+                    w->orth_since = 0;
                 }
                 CK(to_stack(w, w->sp, fwd, j));
                 CK(cudaEventRecord(w->ev_prop, w->sp));

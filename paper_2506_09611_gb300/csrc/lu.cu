@@ -403,7 +403,7 @@ cudaError_t launch_lu_sign(cudaStream_t st, const LuArgs& a, int parity, double*
 // walks the rows in blocks of 32 (a product with the finished rows, then the 32 x 32 diagonal
 // block column by column).  Grid (column blocks, matrix).
 // ---------------------------------------------------------------------------
-constexpr int SV_COLS = 11, SV_YP = SV_COLS + 1, SV_KB = 64;
+constexpr int SV_COLS = 10, SV_YP = SV_COLS + 1, SV_KB = 64;
 
 __global__ void __launch_bounds__(256) lu_solve_kernel(SolveArgs a) {
     const int mat = blockIdx.y;
