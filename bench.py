@@ -349,6 +349,9 @@ def main():
 
     X_eq = ctx.fields(0).copy()  # the headline walker's fields after its sweeps (equilibrated)
     ctx.close()
+    multi = None
+    if not args.no_batch:
+        multi = optional_leg("walkers_40x40", lambda: walkers_40x40_leg(afqmc, torch, stream, args, seed))
     batch = None
     if not args.no_batch:
         batch = optional_leg("batched_population", lambda: batched_population(afqmc, torch, stream, args, seed))
@@ -422,6 +425,7 @@ def main():
             "gpu_launches": launches,
             "e2e": e2e,
             "direct_launches": direct,
+            "walkers_40x40": multi,
             "batched_population": batch,
             "soc": soc_res,
             "dense_wrap": dense,
@@ -897,6 +901,39 @@ def kernel_rooflines(prof, gemm, pk, pk_src, steps, wrap="separable", wrap_tile=
                     "work_per_launch": byts,
                     "peak_source": "measured copy bandwidth (of %s); G (2 x 10 MB) is L2-resident" % pk_src})
     out.sort(key=lambda r: -r["ms_per_step"])
+    return out
+
+
+def walkers_40x40_leg(afqmc, torch, stream, args, seed, counts=(4, 8)):
+    """The headline workload with several walkers per GPU: n independent 40 x 40 walkers (seeds
+    per walker) in one group, so every launch of a slice covers all of them (n window chains side by
+    side, one flush product over 2n matrices, one batched recompute).  Per n: one untimed sweep
+    that also captures the slice-steps' graphs, then one sweep timed with CUDA events on the
+    stream.  Rate = n x N x 2M / time."""
+    P = inputs.trial_state(L, L, NS)
+    order = [(l, +1) for l in range(1, M + 1)] + [(l, -1) for l in range(M, 0, -1)]
+    out = {"workload": "n walkers of the headline workload (40x40, U=6, n=0.875, k=64, FP32 bulk, recompute "
+                       "every %d slices) in one group per GPU" % STAB, "unit": UNIT}
+    for n in counts:
+        X = np.concatenate([inputs.initial_fields(M, N, seed=seed, walker=wi).ravel() for wi in range(n)])
+        c = afqmc.Context(M, dtau=DTAU, U=U, t=T_HOP, precision="fp32", stab_every=STAB, seed=seed, gemm=args.gemm)
+        try:
+            c.init_walkers([L] * n, [NS] * n, [NS] * n, np.concatenate([np.concatenate([P.ravel(), P.ravel()])] * n),
+                           X, stream=stream)
+
+            def sweep():
+                for (ell, d) in order:
+                    c.sweep_slice(ell, d, "delayed", k=args.k, nb=args.nb, stream=stream)
+                    pos = ell if d > 0 else ell - 1
+                    if pos % STAB == 0:
+                        afqmc.afqmc_recompute_G(c.h, None, stream)
+
+            c.set_graphs(True)
+            sweep()
+            ms = tune.time_on_stream(torch, stream, sweep)
+            out[f"walkers_{n}"] = {"value": n * N * M * 2 / (ms / 1e3), "ms_per_step": ms}
+        finally:
+            c.close()
     return out
 
 
