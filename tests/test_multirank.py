@@ -164,3 +164,116 @@ def test_kernel_rooflines_use_the_documented_work_per_launch():
     t = {r["kernel"].split(" ")[0]: r for r in
          bench.kernel_rooflines(prof, "tc3", pk, "measured", steps=1, wrap_tile=8)}["sep_kernel"]
     assert t["work_per_launch"] == s["work_per_launch"] and t["bytes_per_launch"] == s["bytes_per_launch"] / 2
+
+
+def _fake_clock_torch(clock):
+    import types
+
+    class Ev:
+        def __init__(self, enable_timing=True):
+            self.t = 0.0
+
+        def record(self, stream=None):
+            self.t = clock["t"]
+
+        def elapsed_time(self, other):
+            return other.t - self.t
+
+    return types.SimpleNamespace(cuda=types.SimpleNamespace(Event=Ev, synchronize=lambda: None))
+
+
+def test_walkers_leg_times_one_sweep_of_n_walkers_with_graphs():
+    """bench.walkers_40x40_leg on a fake device: per walker count one context with n walkers of the
+    headline lattice, graphs on before the untimed sweep, one timed sweep (2M slice-steps with a
+    recompute at every multiple of the period), rate = n N 2M / time, and the context closed."""
+    import types
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    clock = {"t": 0.0}
+    made = []
+
+    class Ctx:
+        def __init__(self, M, **kw):
+            self.h, self.graphs, self.closed, self.slices, self.n = object(), False, False, 0, 0
+            assert kw["stab_every"] == bench.STAB and kw["precision"] == "fp32"
+            made.append(self)
+
+        def init_walkers(self, Ls, nu, nd, P, X, stream=None):
+            self.n = len(Ls)
+            assert Ls == [bench.L] * self.n and len(X) == self.n * bench.M * bench.N
+
+        def set_graphs(self, on):
+            self.graphs = on
+
+        def sweep_slice(self, ell, d, mode, k=32, nb=4, stream=None):
+            assert self.graphs and mode == "delayed"
+            self.slices += 1
+            clock["t"] += 1.0 + 0.25 * self.n
+
+        def close(self):
+            self.closed = True
+
+    recs = []
+    fake_afqmc = types.SimpleNamespace(Context=Ctx, afqmc_recompute_G=lambda h, n, s: recs.append(h))
+    args = types.SimpleNamespace(gemm="tc3", k=64, nb=16)
+    r = bench.walkers_40x40_leg(fake_afqmc, _fake_clock_torch(clock), None, args, 1, counts=(2, 4))
+    for n, ctx in zip((2, 4), made):
+        ms = 2 * bench.M * (1.0 + 0.25 * n)
+        assert r[f"walkers_{n}"]["ms_per_step"] == ms
+        assert r[f"walkers_{n}"]["value"] == n * bench.N * bench.M * 2 / (ms / 1e3)
+        assert ctx.closed and ctx.slices == 2 * 2 * bench.M  # capture sweep + timed sweep
+    # one recompute at every multiple of the period, both directions, in both sweeps of both counts
+    per_sweep = 2 * (bench.M // bench.STAB)
+    assert len(recs) == 2 * 2 * per_sweep
+
+
+def test_cpqmc_leg_reports_each_scheme_and_its_speedup():
+    """bench.cpqmc_leg on a fake device: every scheme (local heat bath, delayed k = 16 and 32, block
+    force bias n_b = 8) gets its own ensemble, two untimed steps, CP_STEPS timed steps with the comb
+    and a re-orthonormalisation every CP_EVERY steps, rate = walkers N steps / time, and the
+    speed-ups are relative to the local scheme."""
+    import types
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    clock = {"t": 0.0}
+    cost = {"local": 10.0, "delayed": 1.0, "blockfb": 0.5}
+    made = []
+
+    class CP:
+        def __init__(self, L, ns, n, P, **kw):
+            self.steps, self.combs, self.reorths, self.closed = [], 0, 0, False
+            assert (L, n) == (bench.CP_L, bench.CP_WALKERS)
+            made.append(self)
+
+        def step(self, mode, k, nb, stream=None):
+            self.steps.append((mode, k, nb))
+            clock["t"] += cost[mode] * (32.0 / k if mode == "delayed" else 1.0)
+
+        def comb(self, u0, stream=None):
+            assert 0.0 <= u0 < 1.0
+            self.combs += 1
+
+        def reorth(self, stream=None):
+            self.reorths += 1
+
+        def energy(self, stream=None):
+            return [0.0], -1.0
+
+        def close(self):
+            self.closed = True
+
+    fake_afqmc = types.SimpleNamespace(CPContext=CP)
+    r = bench.cpqmc_leg(fake_afqmc, _fake_clock_torch(clock), None, 1)
+    n = bench.CP_L * bench.CP_L
+    expect = {"local": 10.0, "delayed_k16": 2.0, "delayed_k32": 1.0, "blockfb_nb8": 0.5}
+    for key, c in expect.items():
+        assert r[key]["ms_per_step"] == pytest.approx(c)
+        assert r[key]["value"] == pytest.approx(bench.CP_WALKERS * n * bench.CP_STEPS / (c * bench.CP_STEPS / 1e3))
+        assert r["speedup_vs_local"][key] == pytest.approx(10.0 / c)
+    for cp in made:
+        assert cp.closed and len(cp.steps) == 2 + bench.CP_STEPS
+        assert cp.combs == cp.reorths == bench.CP_STEPS // bench.CP_EVERY
