@@ -133,7 +133,7 @@ int afqmc_sweep_slice(afqmc_ctx* ctx, int slice, int dir, int mode, int k, int n
  * it (pivoted LU in FP64), and form G = 1 - U_R (U_L U_R)^{-1} U_L, replacing the bulk G.  With an
  * FP32 bulk G (G form) G is formed from the propagated factor first and the re-orthonormalisation
  * follows on a side stream, only when the next interval would otherwise carry the basis over more
- * than 10 slices of propagation. 
+ * than 10 slices of propagation.
  * Must be called whenever the walker sits at a multiple of stab_every (and may be called only
  * there).  rel_drift (host, nullable, one per walker): ||G_bulk - G_new||_F / ||G_new||_F,
  * averaged over the spins (the call syncs the stream). */
