@@ -7,7 +7,7 @@ mixed expectation <psi_T| T^{M/2} O T^{M/2} |psi_T> / <psi_T| T^M |psi_T>, T = e
 running chains must reproduce it within their error bars (Eq. GSObsQMC).
 
 The comparison with the paper's own L = 20 values (Table C1, tests/golden/table_c1.txt) is a long
-run (about 55 s of one GPU per sweep of 32 walkers, M = 920, so some 35 minutes for 12 + 24 sweeps);
+run (about 50 s of one GPU per sweep of 32 walkers, M = 920, so some 30 minutes for 12 + 24 sweeps);
 it runs only with AFQMC_TABLE_C1=1.
 """
 import os
